@@ -1,0 +1,768 @@
+/*
+ * FPIC oracle: plain, serial, FP64 CPU restatement of the GRPIC particle
+ * path of "FPIC: a new Particle-In-Cell code for stationary and
+ * axisymmetric black-hole spacetimes" (Meringolo & Rezzolla, arXiv
+ * 2602.07452).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path links, loads or
+ * calls this file; only the test-suite, the smoke check and the CPU-baseline
+ * leg of the benchmark do.  It shares no code, header, table or constant with
+ * the CUDA library.  Compiled with -O2 -ffp-contract=off so that every
+ * multiply and add rounds separately.
+ *
+ * Every function names the passage of the paper it restates.  Where the
+ * paper is silent, garbled or inconsistent the reading taken is stated at
+ * the function ("Reading: ...").
+ *
+ * Units: geometrised, G = c = 1.  The black-hole mass M and spin a (a
+ * length, |a| <= M) are parameters.
+ * Particle state z = (r, th, ph, u_r, u_th, u_ph): contravariant position,
+ * covariant momentum per unit mass (Sec. 2.2).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Appendix A: Kerr metric in spherical Kerr-Schild coordinates, 3+1 split. */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    double s, c;                      /* sin th, cos th */
+    double rho2;                      /* rho^2 = r^2 + a^2 cos^2 th */
+    double xi;                        /* xi = 1 + 2 M r / rho^2 */
+    double alpha;                     /* lapse = xi^{-1/2} */
+    double beta;                      /* shift beta^r = (xi - 1)/xi */
+    double g_rr, g_rp, g_tt, g_pp;    /* gamma_ij */
+    double gu_rr, gu_rp, gu_tt, gu_pp;/* gamma^ij */
+    double sqrtg;                     /* sqrt(gamma) = rho^2 sqrt(xi) sin th */
+} om_t;
+
+/* Appendix A, Eqs. (gsf), (gsf_2), lapse/shift and (det).
+ * Reading: the printed gamma_{r phi} = -a^2 xi sin^2 th is a misprint; the
+ * inverse of the printed gamma^{ij} requires gamma_{r phi} = -a xi sin^2 th,
+ * which is what is used (and what the inverse-relation test pins). */
+static void om_eval(double M, double a, double r, double th, om_t *m)
+{
+    double s = sin(th), c = cos(th);
+    double s2 = s * s, c2 = c * c;
+    m->s = s;
+    m->c = c;
+    m->rho2 = r * r + a * a * c2;
+    m->xi = 1.0 + 2.0 * M * r / m->rho2;
+    m->alpha = 1.0 / sqrt(m->xi);
+    m->beta = (m->xi - 1.0) / m->xi;
+    m->g_rr = m->xi;
+    m->g_rp = -a * m->xi * s2;
+    m->g_tt = m->rho2;
+    m->g_pp = s2 * (m->rho2 + a * a * m->xi * s2);
+    m->gu_rr = a * a * s2 / m->rho2 + 1.0 / m->xi;
+    m->gu_rp = a / m->rho2;
+    m->gu_tt = 1.0 / m->rho2;
+    m->gu_pp = 1.0 / (m->rho2 * s2);
+    m->sqrtg = m->rho2 * sqrt(m->xi) * s;
+}
+
+/* Radial and polar derivatives of alpha, beta^r and gamma^{ij}, taken
+ * analytically at the particle as Sec. 2.2 prescribes ("both the metric
+ * components ... and their derivatives are computed analytically at the
+ * position of the particle").  Derived by hand from Appendix A:
+ *   d rho^2/dr = 2r,  d rho^2/dth = -2 a^2 s c
+ *   d xi = 2M d(r/rho^2)
+ *   d alpha = -alpha^3 d xi / 2,  d beta = d xi / xi^2.
+ * Layout of d[0..11]: (dr, dth) of alpha, beta, g^rr, g^rp, g^tt, g^pp. */
+static void om_deriv(double M, double a, double r, double th, double d[12])
+{
+    om_t m;
+    om_eval(M, a, r, th, &m);
+    double s = m.s, c = m.c, s2 = s * s;
+    double P = m.rho2, P2 = P * P;
+    double dPr = 2.0 * r, dPt = -2.0 * a * a * s * c;
+    double dxir = 2.0 * M * (P - r * dPr) / P2;
+    double dxit = -2.0 * M * r * dPt / P2;
+    double a3 = m.alpha * m.alpha * m.alpha;
+    double xi2 = m.xi * m.xi;
+    d[0] = -0.5 * a3 * dxir;
+    d[1] = -0.5 * a3 * dxit;
+    d[2] = dxir / xi2;
+    d[3] = dxit / xi2;
+    /* g^rr = a^2 s^2 / P + 1/xi */
+    d[4] = -a * a * s2 * dPr / P2 - dxir / xi2;
+    d[5] = a * a * 2.0 * s * c / P - a * a * s2 * dPt / P2 - dxit / xi2;
+    /* g^rp = a / P */
+    d[6] = -a * dPr / P2;
+    d[7] = -a * dPt / P2;
+    /* g^tt = 1 / P */
+    d[8] = -dPr / P2;
+    d[9] = -dPt / P2;
+    /* g^pp = 1 / (P s^2) */
+    d[10] = -dPr / (P2 * s2);
+    d[11] = -(dPt * s2 + P * 2.0 * s * c) / (P2 * s2 * s2);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Appendix B.1 and Sec. 3.1.3: the Wald electro-vacuum field (M = 1 units, */
+/* as printed).                                                             */
+/* ------------------------------------------------------------------------ */
+
+/* A_0 and A_phi as printed in Sec. 3.1.3 (the H and L definitions).
+ * Reading: the printed A_phi lacks the overall factor B0 that Eq. (Amu)
+ * gives it; the factor is restored.  A_0 is used exactly as printed (no
+ * -a B0 gauge constant), so H is defined up to that constant. */
+static double wald_A0(double a, double B0, double r, double th)
+{
+    double c = cos(th);
+    double rho2 = r * r + a * a * c * c;
+    return B0 * a * r * (1.0 + c * c) / rho2;
+}
+
+static double wald_Aph(double a, double B0, double r, double th)
+{
+    double s = sin(th), c = cos(th);
+    double rho2 = r * r + a * a * c * c;
+    return 0.5 * B0 * s * s * (r * r + a * a - 2.0 * a * a * r * (1.0 + c * c) / rho2);
+}
+
+/* Appendix B.1, Eqs. (wald1)-(wald6): contravariant B^i and covariant E_i.
+ * Reading: the printed E_theta carries an extra factor a; the value used,
+ * E_theta = 2 B0 a r (a^2 - r^2) sin th cos th / rho^4, is the one that
+ * equals dA_0/dth for the printed A_0 (pinned by finite differences of
+ * A_0).  Sign convention E_i = F_{i0} = +d_i A_0 (Eq. Ei); Eq. (wald1_0)'s
+ * minus sign is taken as a typo because App. B's E_r carries the + sign. */
+static void wald_BE(double a, double B0, double r, double th,
+                    double B[3], double E[3])
+{
+    double s = sin(th), c = cos(th);
+    double rho2 = r * r + a * a * c * c, rho4 = rho2 * rho2;
+    double xi = 1.0 + 2.0 * r / rho2;
+    double sqrtg = rho2 * sqrt(xi) * s;
+    double a2 = a * a;
+    B[0] = B0 / sqrtg * (r * r + a2 - 2.0 * r + 2.0 * r * (r * r * r * r - a2 * a2) / rho4) * s * c;
+    B[1] = -B0 / sqrtg * (r + a2 * (1.0 + c * c) * (2.0 * r * r - rho2) / rho4) * s * s;
+    B[2] = -B0 / sqrtg * (2.0 * a * r * (a2 - r * r) / rho4 - a) * s * c;
+    E[0] = B0 * a * (1.0 + c * c) * (a2 * c * c - r * r) / rho4;
+    E[1] = B0 * 2.0 * a * r * (a2 - r * r) / rho4 * s * c;
+    E[2] = 0.0;
+}
+
+/* FIDO electric field D^i from E_i and B^i via Eq. (Ei):
+ * E_i = alpha D_i + sqrt(gamma) eta_ijk beta^j B^k with beta = (beta^r,0,0),
+ * i.e. D_r = E_r/alpha, D_th = (E_th + sqrtg beta B^ph)/alpha,
+ * D_ph = (E_ph - sqrtg beta B^th)/alpha;  D^i = gamma^ij D_j. */
+static void wald_D(double a, double B0, double r, double th, double D[3], double B[3])
+{
+    double E[3];
+    om_t m;
+    wald_BE(a, B0, r, th, B, E);
+    om_eval(1.0, a, r, th, &m);
+    double Dr_ = E[0] / m.alpha;
+    double Dt_ = (E[1] + m.sqrtg * m.beta * B[2]) / m.alpha;
+    double Dp_ = (E[2] - m.sqrtg * m.beta * B[1]) / m.alpha;
+    D[0] = m.gu_rr * Dr_ + m.gu_rp * Dp_;
+    D[1] = m.gu_tt * Dt_;
+    D[2] = m.gu_rp * Dr_ + m.gu_pp * Dp_;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 2.2: Hamiltonian and equations of motion.                           */
+/* ------------------------------------------------------------------------ */
+
+/* Eq. (Ham) with the static potential of Sec. 3.1.3:
+ * H = alpha Gamma - beta^r u_r - (q/m) A_0,  Gamma = sqrt(1 + g^ij u_i u_j). */
+static double gamma_lorentz(const om_t *m, const double *u)
+{
+    double q = m->gu_rr * u[0] * u[0] + 2.0 * m->gu_rp * u[0] * u[2]
+             + m->gu_tt * u[1] * u[1] + m->gu_pp * u[2] * u[2];
+    return sqrt(1.0 + q);
+}
+
+typedef struct {
+    double M, a;
+    double B0pot;    /* B0 of the Wald potential entering H and L; 0 = none */
+} or_bh;
+
+static double ham(const or_bh *bh, double qm, const double *z)
+{
+    om_t m;
+    om_eval(bh->M, bh->a, z[0], z[1], &m);
+    double G = gamma_lorentz(&m, z + 3);
+    double h = m.alpha * G - m.beta * z[3];
+    if (bh->B0pot != 0.0 && qm != 0.0)
+        h -= qm * wald_A0(bh->a, bh->B0pot, z[0], z[1]);
+    return h;
+}
+
+/* Normaliser of the relative energy error.  Reading: the paper divides by
+ * H_0 (Sec. 3.1.2), which for charged particles can be ~0 or negative; the
+ * denominator used is |alpha Gamma - beta u_r|_0 + |(q/m) A_0|_0, equal to
+ * |H_0| for neutral particles. */
+static double ham_norm(const or_bh *bh, double qm, const double *z)
+{
+    om_t m;
+    om_eval(bh->M, bh->a, z[0], z[1], &m);
+    double G = gamma_lorentz(&m, z + 3);
+    double d = fabs(m.alpha * G - m.beta * z[3]);
+    if (bh->B0pot != 0.0 && qm != 0.0)
+        d += fabs(qm * wald_A0(bh->a, bh->B0pot, z[0], z[1]));
+    return d;
+}
+
+/* Conserved angular momentum of Sec. 3.1.3: L = u_ph + (q/m) A_ph. */
+static double angmom(const or_bh *bh, double qm, const double *z)
+{
+    double l = z[5];
+    if (bh->B0pot != 0.0 && qm != 0.0)
+        l += qm * wald_Aph(bh->a, bh->B0pot, z[0], z[1]);
+    return l;
+}
+
+/* Eqs. (p1), (p2), (O1), (O2): dz/dt at z given FIDO fields D^i, B^i at the
+ * particle.  eta_{r th ph} = +1.  A^(g)_ph = 0 because d_ph = 0. */
+static void rhs(double M, double a, double qm, const double *z,
+                const double *D, const double *B, double *f)
+{
+    om_t m;
+    double d[12];
+    om_eval(M, a, z[0], z[1], &m);
+    om_deriv(M, a, z[0], z[1], d);
+    double ur = z[3], ut = z[4], up = z[5];
+    double Ur = m.gu_rr * ur + m.gu_rp * up;   /* u^r */
+    double Ut = m.gu_tt * ut;                  /* u^th */
+    double Up = m.gu_rp * ur + m.gu_pp * up;   /* u^ph */
+    double G = sqrt(1.0 + ur * Ur + ut * Ut + up * Up);
+    f[0] = m.alpha * Ur / G - m.beta;
+    f[1] = m.alpha * Ut / G;
+    f[2] = m.alpha * Up / G;
+    for (int i = 0; i < 2; ++i) {
+        double dal = d[0 + i], dbe = d[2 + i];
+        double dgrr = d[4 + i], dgrp = d[6 + i], dgtt = d[8 + i], dgpp = d[10 + i];
+        double quad = ur * ur * dgrr + 2.0 * ur * up * dgrp + ut * ut * dgtt + up * up * dgpp;
+        f[3 + i] = -G * dal + ur * dbe - m.alpha / (2.0 * G) * quad;
+    }
+    f[5] = 0.0;
+    if (qm != 0.0 && D && B) {
+        double k = qm * m.alpha;
+        double cr = Ut * B[2] - Up * B[1];
+        double ct = Up * B[0] - Ur * B[2];
+        double cp = Ur * B[1] - Ut * B[0];
+        f[3] += k * (m.g_rr * D[0] + m.g_rp * D[2] + m.sqrtg * cr / G);
+        f[4] += k * (m.g_tt * D[1] + m.sqrtg * ct / G);
+        f[5] += k * (m.g_rp * D[0] + m.g_pp * D[2] + m.sqrtg * cp / G);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Grid, cell location and field gather.                                    */
+/* ------------------------------------------------------------------------ */
+
+/* Yee layout (Sec. 2.1, Fig. 1 caption and the B^r / B^ph example):
+ *   D^r (i+1/2, j)   D^th (i, j+1/2)   D^ph (i, j)
+ *   B^r (i, j+1/2)   B^th (i+1/2, j)   B^ph (i+1/2, j+1/2)
+ * A component array is indexed [i*ld + j]; i counts r nodes (integer or
+ * half), j counts th nodes.  ld >= Nth + 1. */
+typedef struct {
+    int Nr, Nth, ld;
+    const double *rn;   /* r_i,        i = 0..Nr   */
+    const double *rh;   /* r_{i+1/2},  i = 0..Nr-1 */
+    const double *tn;   /* th_j,       j = 0..Nth  */
+    const double *th;   /* th_{j+1/2}, j = 0..Nth-1 */
+} or_grid;
+
+static const int yee_roff[6] = {1, 0, 0, 0, 1, 1};
+static const int yee_toff[6] = {0, 1, 0, 1, 0, 1};
+
+/* Cell location against a node list X[0..m-1], m >= 2 (Sec. 2.3: a particle
+ * "located between nodes r_ir <= r <= r_ir+1").  Reading: the lower bound is
+ * inclusive, the upper exclusive (a point on a node belongs to the upper
+ * cell); outside the list the first/last cell is taken. */
+static int locate(const double *X, int m, double x)
+{
+    if (!(x >= X[0])) return 0;
+    if (x >= X[m - 1]) return m - 2;
+    int lo = 0, hi = m - 1;          /* X[lo] <= x < X[hi] */
+    while (hi - lo > 1) {
+        int mid = (lo + hi) / 2;
+        if (x >= X[mid]) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+/* Linear weight of x in [X[i], X[i+1]], clamped to [0,1] (constant
+ * extrapolation beyond the end nodes). */
+static double lin_w(const double *X, int i, double x)
+{
+    double w = (x - X[i]) / (X[i + 1] - X[i]);
+    if (w < 0.0) w = 0.0;
+    if (w > 1.0) w = 1.0;
+    return w;
+}
+
+/* Field gather (grid -> particle).  Reading: the paper does not state its
+ * gather; each component is interpolated bilinearly in (r, th) on its own
+ * staggered sub-grid. */
+static void gather(const or_grid *g, const double *const F[6], double r, double t,
+                   double D[3], double B[3])
+{
+    double v[6];
+    for (int k = 0; k < 6; ++k) {
+        const double *X = yee_roff[k] ? g->rh : g->rn;
+        const double *Y = yee_toff[k] ? g->th : g->tn;
+        int mx = yee_roff[k] ? g->Nr : g->Nr + 1;
+        int my = yee_toff[k] ? g->Nth : g->Nth + 1;
+        int i = locate(X, mx, r), j = locate(Y, my, t);
+        double wr = lin_w(X, i, r), wt = lin_w(Y, j, t);
+        const double *f = F[k];
+        v[k] = (1.0 - wr) * (1.0 - wt) * f[i * g->ld + j]
+             + wr * (1.0 - wt) * f[(i + 1) * g->ld + j]
+             + (1.0 - wr) * wt * f[i * g->ld + j + 1]
+             + wr * wt * f[(i + 1) * g->ld + j + 1];
+    }
+    D[0] = v[0]; D[1] = v[1]; D[2] = v[2];
+    B[0] = v[3]; B[1] = v[4]; B[2] = v[5];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Pushers (Sec. 2.2.1-2.2.3) and the hybrid switch (Sec. 3.1.2).           */
+/* ------------------------------------------------------------------------ */
+
+enum { OR_FIELD_NONE = 0, OR_FIELD_GRID = 1, OR_FIELD_WALD = 2 };
+enum { OR_RK4 = 0, OR_IMR = 1, OR_HAM = 2, OR_HYB1 = 3, OR_HYB2 = 4 };
+
+typedef struct {
+    double M, a;
+    double B0pot;          /* Wald B0 entering H and L (0: no potential) */
+    int field_kind;        /* OR_FIELD_* */
+    double B0field;        /* analytic Wald field strength (OR_FIELD_WALD) */
+    double dt;
+    int scheme;            /* OR_RK4 .. OR_HYB2 */
+    int implicit_kind;     /* OR_IMR or OR_HAM: partner of the hybrid */
+    double thr;            /* Hyb2: Htilde_max;  Hyb1: (d Htilde/dt)_max */
+    double tol;            /* implicit convergence tolerance */
+    int max_iter;          /* implicit iteration cap */
+    double r_h, r_max;     /* particle removal radii */
+    double dg_eps;         /* discrete-gradient increment threshold */
+} or_push_params;
+
+typedef struct {
+    const or_push_params *p;
+    const or_grid *g;
+    const double *const *F;
+    double qm;
+} or_ctx;
+
+static void field_at(const or_ctx *c, const double *z, double D[3], double B[3], int *have)
+{
+    *have = 0;
+    if (c->qm == 0.0) return;
+    if (c->p->field_kind == OR_FIELD_GRID) {
+        gather(c->g, c->F, z[0], z[1], D, B);
+        *have = 1;
+    } else if (c->p->field_kind == OR_FIELD_WALD) {
+        wald_D(c->p->a, c->p->B0field, z[0], z[1], D, B);
+        *have = 1;
+    }
+}
+
+static void F_eval(const or_ctx *c, const double *z, double *f)
+{
+    double D[3], B[3];
+    int have;
+    field_at(c, z, D, B, &have);
+    rhs(c->p->M, c->p->a, c->qm, z, have ? D : NULL, have ? B : NULL, f);
+}
+
+/* Sec. 2.2.1: classical RK4; fields frozen over the step. */
+static void step_rk4(const or_ctx *c, const double *z0, double *z1)
+{
+    double k1[6], k2[6], k3[6], k4[6], y[6];
+    double h = c->p->dt;
+    F_eval(c, z0, k1);
+    for (int i = 0; i < 6; ++i) y[i] = z0[i] + 0.5 * h * k1[i];
+    F_eval(c, y, k2);
+    for (int i = 0; i < 6; ++i) y[i] = z0[i] + 0.5 * h * k2[i];
+    F_eval(c, y, k3);
+    for (int i = 0; i < 6; ++i) y[i] = z0[i] + h * k3[i];
+    F_eval(c, y, k4);
+    for (int i = 0; i < 6; ++i)
+        z1[i] = z0[i] + h / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+}
+
+/* Convergence test of the implicit iterations.  Reading: the paper iterates
+ * "to machine round-off"; the stop is max_i |dz_i| / (|z_i| + 1) <= tol. */
+static int converged(const double *a, const double *b, double tol)
+{
+    for (int i = 0; i < 6; ++i)
+        if (!(fabs(a[i] - b[i]) <= tol * (fabs(a[i]) + 1.0))) return 0;
+    return 1;
+}
+
+/* Sec. 2.2.2, Eqs. (imr1)-(imr2): implicit midpoint rule, solved by the
+ * fixed-point iteration z^[k] = z^n + dt F((z^n + z^[k-1])/2).
+ * Reading: Eq. (imr2) prints dt/2 F(z^n + z^[k-1]); the argument is read as
+ * the midpoint (Eq. imr1), and the "Newton" of the text as this fixed-point
+ * update (the one the equation shows).  Returns the iteration count, or
+ * -max_iter if the cap was reached. */
+static int step_imr(const or_ctx *c, const double *z0, const double *guess, double *z1)
+{
+    double zk[6], y[6], f[6], zn[6];
+    memcpy(zk, guess, sizeof zk);
+    for (int k = 1; k <= c->p->max_iter; ++k) {
+        for (int i = 0; i < 6; ++i) y[i] = 0.5 * (z0[i] + zk[i]);
+        F_eval(c, y, f);
+        for (int i = 0; i < 6; ++i) zn[i] = z0[i] + c->p->dt * f[i];
+        int ok = converged(zn, zk, c->p->tol);
+        memcpy(zk, zn, sizeof zk);
+        if (ok) { memcpy(z1, zk, sizeof zk); return k; }
+    }
+    memcpy(z1, zk, sizeof zk);
+    return -c->p->max_iter;
+}
+
+/* Geodesic Hamiltonian of Appendix D: H = alpha sqrt(1 + g^lm u_l u_m) - beta u_r. */
+static double ham_geo(double M, double a, const double *z)
+{
+    om_t m;
+    om_eval(M, a, z[0], z[1], &m);
+    return m.alpha * gamma_lorentz(&m, z + 3) - m.beta * z[3];
+}
+
+/* Analytic partial dH/dz_v of the geodesic Hamiltonian: (dx/dt, -du/dt)
+ * of Eqs. (p1)-(p2) with q = 0. */
+static double ham_geo_partial(double M, double a, const double *z, int v)
+{
+    double f[6];
+    rhs(M, a, 0.0, z, NULL, NULL, f);
+    if (v >= 3) return f[v - 3];   /* dH/du_i = dx^i/dt */
+    return -f[3 + v];              /* dH/dx^i = -du_i/dt */
+}
+
+/* Coordinate-increment discrete gradient along one ordering of the six
+ * variables (Sec. 2.2.3, Eq. hh and the displayed quotients): variable
+ * ord[k] is moved from z0 to z1 in turn, and its component is the
+ * difference quotient of H across that single move, so that the components
+ * telescope: sum_v G_v (z1_v - z0_v) = H(z1) - H(z0) exactly.  When
+ * |z1_v - z0_v| < eps the quotient is replaced by the analytic partial at
+ * the midpoint of the move (Appendix D, closing paragraph). */
+static void dg_path(double M, double a, const double *z0, const double *z1,
+                    const int *ord, double eps, double *G)
+{
+    double zc[6];
+    memcpy(zc, z0, sizeof zc);
+    double Hc = ham_geo(M, a, zc);
+    for (int k = 0; k < 6; ++k) {
+        int v = ord[k];
+        double dz = z1[v] - z0[v];
+        if (fabs(dz) < eps) {
+            double zm[6];
+            memcpy(zm, zc, sizeof zm);
+            zm[v] = 0.5 * (z0[v] + z1[v]);
+            G[v] = ham_geo_partial(M, a, zm, v);
+            zc[v] = z1[v];
+            Hc = ham_geo(M, a, zc);
+        } else {
+            zc[v] = z1[v];
+            double Hn = ham_geo(M, a, zc);
+            G[v] = (Hn - Hc) / dz;
+            Hc = Hn;
+        }
+    }
+}
+
+/* The symmetrised discrete gradient.  Reading: Appendix D prints a 1/6
+ * average over update orders that is visibly garbled; the scheme is taken
+ * from its principle: the average over all 12 orderings made of the 3! orders
+ * of the coordinate pairs (r,u_r), (th,u_th), (ph,u_ph) times the two
+ * within-pair orders (coordinate first, or momentum first, for every pair).
+ * Each ordering telescopes exactly, so their average conserves H exactly;
+ * the set is closed under reversal, which makes the scheme time-symmetric. */
+static void dg_grad(double M, double a, const double *z0, const double *z1, double eps, double *G)
+{
+    static const int pairs[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    double acc[6] = {0, 0, 0, 0, 0, 0}, g[6];
+    for (int p = 0; p < 6; ++p)
+        for (int xf = 0; xf < 2; ++xf) {
+            int ord[6];
+            for (int q = 0; q < 3; ++q) {
+                int x = pairs[p][q], u = 3 + pairs[p][q];
+                ord[2 * q] = xf ? x : u;
+                ord[2 * q + 1] = xf ? u : x;
+            }
+            dg_path(M, a, z0, z1, ord, eps, g);
+            for (int i = 0; i < 6; ++i) acc[i] += g[i];
+        }
+    for (int i = 0; i < 6; ++i) G[i] = acc[i] / 12.0;
+}
+
+/* Sec. 2.2.3: discrete-gradient Hamiltonian step for geodesics,
+ * dx/dt = D_u H, du/dt = -D_x H, solved by fixed-point iteration on z^{n+1}
+ * (same stop rule as the IMR). */
+static int step_ham(const or_ctx *c, const double *z0, const double *guess, double *z1)
+{
+    double zk[6], G[6], zn[6];
+    memcpy(zk, guess, sizeof zk);
+    for (int k = 1; k <= c->p->max_iter; ++k) {
+        dg_grad(c->p->M, c->p->a, z0, zk, c->p->dg_eps, G);
+        for (int i = 0; i < 3; ++i) {
+            zn[i] = z0[i] + c->p->dt * G[3 + i];
+            zn[3 + i] = z0[3 + i] - c->p->dt * G[i];
+        }
+        int ok = converged(zn, zk, c->p->tol);
+        memcpy(zk, zn, sizeof zk);
+        if (ok) { memcpy(z1, zk, sizeof zk); return k; }
+    }
+    memcpy(z1, zk, sizeof zk);
+    return -c->p->max_iter;
+}
+
+/* Particle boundary conditions (Sec. 2.5, closing paragraph), half-th
+ * domain.  Reading: crossing a pole maps th -> -th (or 2 pi - th), flips
+ * u_th and adds pi to ph (the paper states only the u_th flip).
+ * Returns 0 if the particle is removed (r < r_h or r > r_max). */
+static int particle_bc(const or_push_params *p, double *z)
+{
+    if (z[1] < 0.0) {
+        z[1] = -z[1];
+        z[4] = -z[4];
+        z[2] += M_PI;
+    } else if (z[1] > M_PI) {
+        z[1] = 2.0 * M_PI - z[1];
+        z[4] = -z[4];
+        z[2] += M_PI;
+    }
+    if (!(z[0] >= p->r_h) || !(z[0] <= p->r_max)) return 0;
+    return 1;
+}
+
+/* One step of one particle.  Hybrid (Sec. 3.1.2): RK4 trial, then
+ *   Hyb2: accept iff Ht^{n+1} < Ht_max,
+ *   Hyb1: accept iff (Ht^{n+1} - Ht^n)/dt < (dHt/dt)_max,
+ * with Ht = |H - H_0| / D_0; otherwise the step is redone from z^n by the
+ * implicit scheme (IMR for any particle, or the discrete-gradient scheme
+ * for geodesics), started from the rejected trial, and always accepted.
+ * A NaN test value rejects.  Returns 1 if the implicit iteration hit its
+ * cap, else 0. */
+static int push_one(const or_ctx *c, double *z, double H0, double D0, double *Hn,
+                    uint8_t *scheme_out, uint8_t *iters_out)
+{
+    const or_push_params *p = c->p;
+    or_bh bh = {p->M, p->a, p->B0pot};
+    double z0[6], z1[6], trial[6];
+    memcpy(z0, z, sizeof z0);
+    int it = 0, implicit = 0;
+    if (p->scheme == OR_RK4) {
+        step_rk4(c, z0, z1);
+    } else if (p->scheme == OR_IMR) {
+        it = step_imr(c, z0, z0, z1);
+        implicit = 1;
+    } else if (p->scheme == OR_HAM) {
+        it = step_ham(c, z0, z0, z1);
+        implicit = 1;
+    } else {
+        step_rk4(c, z0, trial);
+        double H1 = ham(&bh, c->qm, trial);
+        double Ht1 = fabs(H1 - H0) / D0;
+        int accept;
+        if (p->scheme == OR_HYB2) {
+            accept = Ht1 < p->thr;
+        } else {
+            double Htn = fabs(*Hn - H0) / D0;
+            accept = (Ht1 - Htn) / p->dt < p->thr;
+        }
+        if (accept) {
+            memcpy(z1, trial, sizeof z1);
+        } else {
+            implicit = 1;
+            if (p->implicit_kind == OR_HAM) it = step_ham(c, z0, trial, z1);
+            else it = step_imr(c, z0, trial, z1);
+        }
+    }
+    *Hn = ham(&bh, c->qm, z1);
+    memcpy(z, z1, sizeof z1);
+    *scheme_out = (uint8_t)implicit;
+    int a = it < 0 ? -it : it;
+    *iters_out = (uint8_t)(a > 255 ? 255 : a);
+    return it < 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exported entry points (called through ctypes by the test-suite).         */
+/* ------------------------------------------------------------------------ */
+
+void or_metric(double M, double a, int64_t n, const double *r, const double *th, double *out)
+{
+    for (int64_t p = 0; p < n; ++p) {
+        om_t m;
+        om_eval(M, a, r[p], th[p], &m);
+        double *o = out + 13 * p;
+        o[0] = m.rho2; o[1] = m.xi; o[2] = m.alpha; o[3] = m.beta;
+        o[4] = m.g_rr; o[5] = m.g_rp; o[6] = m.g_tt; o[7] = m.g_pp;
+        o[8] = m.gu_rr; o[9] = m.gu_rp; o[10] = m.gu_tt; o[11] = m.gu_pp;
+        o[12] = m.sqrtg;
+    }
+}
+
+void or_metric_deriv(double M, double a, int64_t n, const double *r, const double *th, double *out)
+{
+    for (int64_t p = 0; p < n; ++p) om_deriv(M, a, r[p], th[p], out + 12 * p);
+}
+
+void or_wald(double a, double B0, int64_t n, const double *r, const double *th,
+             double *B, double *E, double *D, double *A0, double *Aph)
+{
+    for (int64_t p = 0; p < n; ++p) {
+        double Bx[3];
+        wald_BE(a, B0, r[p], th[p], B + 3 * p, E + 3 * p);
+        wald_D(a, B0, r[p], th[p], D + 3 * p, Bx);
+        A0[p] = wald_A0(a, B0, r[p], th[p]);
+        Aph[p] = wald_Aph(a, B0, r[p], th[p]);
+    }
+}
+
+/* H, L and the normaliser D_0 for n states (n x 6). */
+void or_hamiltonian(double M, double a, double B0pot, int64_t n, const double *z,
+                    const double *qm, double *H, double *L, double *Dn)
+{
+    or_bh bh = {M, a, B0pot};
+    for (int64_t p = 0; p < n; ++p) {
+        if (H) H[p] = ham(&bh, qm[p], z + 6 * p);
+        if (L) L[p] = angmom(&bh, qm[p], z + 6 * p);
+        if (Dn) Dn[p] = ham_norm(&bh, qm[p], z + 6 * p);
+    }
+}
+
+/* Right-hand side at n states with fields given per state (D,B n x 3 each;
+ * NULL = no field). */
+void or_rhs(double M, double a, int64_t n, const double *z, const double *qm,
+            const double *D, const double *B, double *f)
+{
+    for (int64_t p = 0; p < n; ++p)
+        rhs(M, a, qm[p], z + 6 * p, D ? D + 3 * p : NULL, B ? B + 3 * p : NULL, f + 6 * p);
+}
+
+void or_gather(int Nr, int Nth, int ld, const double *rn, const double *rh,
+               const double *tn, const double *th, const double *const *F,
+               int64_t n, const double *r, const double *t, double *DB)
+{
+    or_grid g = {Nr, Nth, ld, rn, rh, tn, th};
+    for (int64_t p = 0; p < n; ++p) gather(&g, F, r[p], t[p], DB + 6 * p, DB + 6 * p + 3);
+}
+
+/* Integer-grid cell index ir * Nth + ith (Sec. 2.3, "located between nodes"). */
+void or_cell_index(int Nr, int Nth, const double *rn, const double *tn, int64_t n,
+                   const double *r, const double *t, uint32_t *cell)
+{
+    for (int64_t p = 0; p < n; ++p) {
+        int i = locate(rn, Nr + 1, r[p]);
+        int j = locate(tn, Nth + 1, t[p]);
+        cell[p] = (uint32_t)i * (uint32_t)Nth + (uint32_t)j;
+    }
+}
+
+/* Discrete gradient between two states (exposed for the conservation pins). */
+void or_dg_grad(double M, double a, const double *z0, const double *z1, double eps, double *G)
+{
+    dg_grad(M, a, z0, z1, eps, G);
+}
+
+/* One step of n particles.  F: six field arrays (Yee layout) when
+ * field_kind == OR_FIELD_GRID.  Returns the number of particles whose
+ * implicit iteration reached the cap. */
+int64_t or_push(const or_push_params *p, int Nr, int Nth, int ld, const double *rn,
+                const double *rh, const double *tn, const double *th,
+                const double *const *F, int64_t n, double *z, const double *qm,
+                const double *H0, const double *D0, double *Hn, uint8_t *alive,
+                uint8_t *scheme_out, uint8_t *iters_out)
+{
+    or_grid g = {Nr, Nth, ld, rn, rh, tn, th};
+    int64_t notconv = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        scheme_out[k] = 0;
+        iters_out[k] = 0;
+        if (!alive[k]) continue;
+        or_ctx c = {p, &g, F, qm[k]};
+        notconv += push_one(&c, z + 6 * k, H0[k], D0[k], Hn + k, scheme_out + k, iters_out + k);
+        if (!particle_bc(p, z + 6 * k)) alive[k] = 0;
+    }
+    return notconv;
+}
+
+/* Wald field sampled at every Yee point (Appendix B.1; each component at its
+ * own staggered location).  F: six arrays of size (Nr+1)*ld. */
+void or_wald_on_grid(double a, double B0, int Nr, int Nth, int ld, const double *rn,
+                     const double *rh, const double *tn, const double *th, double *const *F)
+{
+    for (int k = 0; k < 6; ++k) {
+        int mx = yee_roff[k] ? Nr : Nr + 1;
+        int my = yee_toff[k] ? Nth : Nth + 1;
+        for (int i = 0; i < mx; ++i)
+            for (int j = 0; j < my; ++j) {
+                double r = yee_roff[k] ? rh[i] : rn[i];
+                double t = yee_toff[k] ? th[j] : tn[j];
+                double D[3], B[3];
+                wald_D(a, B0, r, t, D, B);
+                F[k][i * ld + j] = k < 3 ? D[k] : B[k - 3];
+            }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Particle initialisation from caller-supplied random draws.               */
+/* ------------------------------------------------------------------------ */
+
+/* Bound-orbit seeding (test-particle workload): for each candidate
+ * (r, th, E, L, sgn) solve H(r, th, u_r, u_th = 0, u_ph = L) = E for u_r,
+ * i.e. alpha^2 (1 + g^rr u_r^2 + 2 g^rp L u_r + g^pp L^2) = (E + beta u_r)^2
+ * with E + beta u_r > 0, taking the root picked by sgn.  The first
+ * candidate with a valid root is used.  cand: n x K x 5.  Returns the number
+ * of particles without a valid candidate (their state is left NaN). */
+int64_t or_seed_orbits(double M, double a, int64_t n, int K, const double *cand, double *z)
+{
+    int64_t bad = 0;
+    for (int64_t p = 0; p < n; ++p) {
+        int done = 0;
+        for (int k = 0; k < K && !done; ++k) {
+            const double *c = cand + ((size_t)p * K + k) * 5;
+            double r = c[0], th = c[1], E = c[2], L = c[3], sg = c[4];
+            om_t m;
+            om_eval(M, a, r, th, &m);
+            double a2 = m.alpha * m.alpha;
+            double A = a2 * m.gu_rr - m.beta * m.beta;
+            double Bq = a2 * m.gu_rp * L - E * m.beta;
+            double C = a2 * (1.0 + m.gu_pp * L * L) - E * E;
+            double disc = Bq * Bq - A * C;
+            if (!(disc >= 0.0) || !(A > 0.0)) continue;
+            double ur = (-Bq + (sg >= 0.0 ? 1.0 : -1.0) * sqrt(disc)) / A;
+            if (!(E + m.beta * ur > 0.0)) continue;
+            double *o = z + 6 * p;
+            o[0] = r; o[1] = th; o[2] = 0.0; o[3] = ur; o[4] = 0.0; o[5] = L;
+            done = 1;
+        }
+        if (!done) {
+            for (int i = 0; i < 6; ++i) z[6 * p + i] = NAN;
+            ++bad;
+        }
+    }
+    return bad;
+}
+
+/* Thermal seeding: a FIDO-frame momentum uhat (orthonormal triad
+ * components) is mapped to covariant u_i = L_ia uhat_a with gamma_ij = L L^T
+ * (Cholesky, order r, th, ph), so that g^ij u_i u_j = |uhat|^2.
+ * draws: n x 6 = (r, th, ph, uhat_1, uhat_2, uhat_3). */
+void or_seed_fido(double M, double a, int64_t n, const double *draws, double *z)
+{
+    for (int64_t p = 0; p < n; ++p) {
+        const double *d = draws + 6 * p;
+        om_t m;
+        om_eval(M, a, d[0], d[1], &m);
+        double L11 = sqrt(m.g_rr);
+        double L31 = m.g_rp / L11;
+        double L22 = sqrt(m.g_tt);
+        double L33 = sqrt(m.g_pp - L31 * L31);
+        double *o = z + 6 * p;
+        o[0] = d[0]; o[1] = d[1]; o[2] = d[2];
+        o[3] = L11 * d[3];
+        o[4] = L22 * d[4];
+        o[5] = L31 * d[3] + L33 * d[5];
+    }
+}

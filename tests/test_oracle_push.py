@@ -1,0 +1,324 @@
+"""Pins of the oracle's equations of motion, pushers and hybrid switch against
+what the paper and the mathematics fix (no GPU)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from conftest import golden
+from paper_2602_07452_gb300 import inputs as I
+
+
+def _fd_grad(fun, z, h=1e-4):
+    g = np.zeros(6)
+    for k in range(6):
+        e = np.zeros(6)
+        e[k] = h
+        g[k] = (4 * (fun(z + e / 2) - fun(z - e / 2)) / h - (fun(z + e) - fun(z - e)) / (2 * h)) / 3
+    return g
+
+
+def _H(a, qm=0.0, B0=0.0):
+    return lambda z: O.hamiltonian(1.0, a, B0, z[None, :], qm)[0][0]
+
+
+@pytest.mark.parametrize("a", [0.0, 0.9, 0.999])
+def test_geodesic_rhs_is_hamiltons_equations(a):
+    """Eqs. (p1)-(p2): dx/dt = dH/du, du/dt = -dH/dx (q = 0), checked against
+    finite differences of H."""
+    rng = np.random.default_rng(11)
+    for _ in range(8):
+        z = np.array([rng.uniform(1.6, 30), rng.uniform(0.2, 2.9), rng.uniform(0, 6),
+                      rng.normal(), rng.normal() * 3, rng.normal() * 3])
+        f = O.rhs(1.0, a, z, 0.0)[0]
+        g = _fd_grad(_H(a), z)
+        exp = np.concatenate([g[3:], -g[:3]])
+        assert np.abs(f - exp).max() < 1e-8 * (np.abs(exp).max() + 1)
+
+
+@pytest.mark.parametrize("a", [0.0, 0.7, 0.9])
+@pytest.mark.parametrize("qm", [-100.0, 1.0, 100.0])
+def test_conserved_H_L_in_exact_wald_field(a, qm):
+    """Sec. 3.1.3: in the static Wald field H = -u_0 - (q/m) A_0 and
+    L = u_ph + (q/m) A_ph are integrals of the motion, so grad H . dz/dt = 0
+    and grad L . dz/dt = 0 pointwise (pins the Lorentz force and its signs)."""
+    rng = np.random.default_rng(12)
+    B0 = 1.0
+    for _ in range(6):
+        z = np.array([rng.uniform(1.9, 20), rng.uniform(0.2, 2.9), 0.3,
+                      rng.normal(), rng.normal() * 2, rng.normal() * 2])
+        _, _, D, _, _ = O.wald(a, B0, z[:1], z[1:2])
+        B = O.wald(a, B0, z[:1], z[1:2])[0]
+        f = O.rhs(1.0, a, z, qm, D, B)[0]
+        gH = _fd_grad(lambda y: O.hamiltonian(1.0, a, B0, y[None, :], qm)[0][0], z)
+        gL = _fd_grad(lambda y: O.hamiltonian(1.0, a, B0, y[None, :], qm)[1][0], z)
+        sH = np.abs(gH * f).sum()
+        sL = np.abs(gL * f).sum()
+        assert abs(gH @ f) < 1e-8 * sH
+        assert abs(gL @ f) < 1e-8 * sL
+
+
+def _run(p, z0, steps, qm=0.0, g=None, F=None):
+    z = np.ascontiguousarray(np.atleast_2d(z0).astype(float))
+    n = z.shape[0]
+    qmv = np.full(n, qm)
+    H0, _, D0 = O.hamiltonian(p.M, p.a, p.B0pot, z, qmv)
+    Hn = H0.copy()
+    alive = np.ones(n, np.uint8)
+    for _ in range(steps):
+        O.push(p, z, qmv, H0, D0, Hn, alive, g, F)
+    return z, H0, Hn, alive
+
+
+def _kerr_orbit_state():
+    return np.array([8.0, 1.2, 0.0, 0.05, 0.4, 3.3])
+
+
+def _ref(a, z0, T):
+    p = O.push_params(a=a, dt=T / 4000, scheme=O.RK4)
+    return _run(p, z0, 4000)[0][0]
+
+
+@pytest.mark.parametrize("scheme,order", [(O.RK4, 4), (O.IMR, 2), (O.HAM, 2)])
+def test_convergence_order(scheme, order):
+    """RK4 is 4th order (Sec. 2.2.1); the IMR and the discrete-gradient scheme
+    are 2nd order (Secs. 2.2.2, 2.2.3).  Global error at fixed T, dt halved."""
+    a, T = 0.9, 4.0
+    z0 = _kerr_orbit_state()
+    ref = _ref(a, z0, T)
+    errs = []
+    for nsteps in (20, 40, 80):
+        p = O.push_params(a=a, dt=T / nsteps, scheme=scheme)
+        z = _run(p, z0, nsteps)[0][0]
+        errs.append(np.abs(z - ref).max())
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(abs(q - order) < 0.35 for q in rates), rates
+
+
+@pytest.mark.parametrize("scheme", [O.IMR, O.HAM])
+def test_implicit_schemes_are_time_symmetric(scheme):
+    """Both implicit schemes are symmetric: a step of +dt followed by -dt
+    returns to the start (to the iteration tolerance)."""
+    z0 = _kerr_orbit_state()
+    p = O.push_params(a=0.9, dt=0.3, scheme=scheme, tol=1e-15)
+    z1 = _run(p, z0, 1)[0]
+    p2 = O.push_params(a=0.9, dt=-0.3, scheme=scheme, tol=1e-15, r_max=1e300)
+    z2 = _run(p2, z1[0], 1)[0][0]
+    assert np.abs(z2 - z0).max() < 1e-12
+
+
+@pytest.mark.parametrize("a", [0.0, 0.9, 0.995])
+@pytest.mark.parametrize("dt", [0.01, 0.3, 1.0])
+def test_discrete_gradient_conserves_H_exactly(a, dt):
+    """Sec. 2.2.3: the Hamiltonian scheme conserves H to round-off for any dt
+    (the paper reports |dH|/H <~ 1e-15); u_ph never changes."""
+    z0 = np.array([9.0, 1.4, 0.0, 0.12, 0.3, 3.1])
+    p = O.push_params(a=a, dt=dt, scheme=O.HAM, tol=1e-15)
+    z, H0, Hn, alive = _run(p, z0, 30)
+    assert alive[0] == 1
+    assert abs(Hn[0] - H0[0]) / H0[0] < 2e-14
+    assert z[0, 5] == z0[5]
+
+
+def test_discrete_gradient_identity():
+    """Each telescoped ordering satisfies sum G_v (z1_v - z0_v) = H(z1) - H(z0);
+    so does the symmetrised average."""
+    rng = np.random.default_rng(5)
+    for a in (0.0, 0.9):
+        for _ in range(10):
+            z0 = np.array([rng.uniform(3, 15), rng.uniform(0.4, 2.7), 0.1,
+                           rng.normal() * 0.3, rng.normal(), 2 + rng.random()])
+            z1 = z0 + rng.normal(size=6) * 0.05
+            z1[5] = z0[5]
+            G = O.dg_grad(1.0, a, z0, z1)
+            dH = _H(a)(z1) - _H(a)(z0)
+            assert abs(G @ (z1 - z0) - dH) < 1e-14
+
+
+def test_table_c1_neutral_orbits_energy_drift():
+    """Sec. 3.1.1 / Fig. part0: the three neutral orbits of Table C.1 keep H
+    at round-off with the Hamiltonian scheme (dt = 0.1) and at small drift
+    with RK4 over t = 200 M."""
+    for name, (a, E, L, r0, ur, ut, up) in golden("table_c1_neutral.txt"):
+        z0 = np.array([r0, math.pi / 2, 0.0, ur, ut, up])
+        pH = O.push_params(a=a, dt=0.1, scheme=O.HAM, tol=1e-15)
+        _, H0, Hn, _ = _run(pH, z0, 2000)
+        assert abs(Hn[0] - H0[0]) / H0[0] < 1e-13, name
+        pR = O.push_params(a=a, dt=0.1, scheme=O.RK4)
+        _, H0, Hn, _ = _run(pR, z0, 2000)
+        assert abs(Hn[0] - H0[0]) / H0[0] < 1e-6, name
+
+
+def _circular(a, r):
+    """Bardeen, Press & Teukolsky (1972): prograde equatorial circular orbit."""
+    s = r ** 1.5 - 3 * r ** 0.5 + 2 * a
+    E = (r ** 1.5 - 2 * r ** 0.5 + a) / (r ** 0.75 * math.sqrt(s))
+    L = (r * r - 2 * a * r ** 0.5 + a * a) / (r ** 0.75 * math.sqrt(s))
+    Om = 1.0 / (r ** 1.5 + a)
+    return E, L, Om
+
+
+@pytest.mark.parametrize("a,r", [(0.9, 6.0), (0.9, 3.0), (0.0, 8.0)])
+def test_circular_orbit_closed_form(a, r):
+    """Kerr circular equatorial orbits (textbook closed forms; KS and BL share
+    r, E = -u_t, L = u_ph and dph/dt at fixed r): the orbit seeded with dr/dt = 0
+    stays at r and advances ph at Omega.  Printed values (a=0.9, r=6):
+    E=0.922599626, L=2.794278361, Omega=0.064115147."""
+    E, L, Om = _circular(a, r)
+    if (a, r) == (0.9, 6.0):
+        assert abs(E - 0.922599626) < 1e-9 and abs(L - 2.794278361) < 1e-9
+        assert abs(Om - 0.064115147) < 1e-9
+    m = O.metric(1.0, a, [r], [math.pi / 2])[0]
+    al2, be, grr, grp = m[2] ** 2, m[3], m[8], m[9]
+    ur = (be * E - al2 * grp * L) / (al2 * grr - be * be)      # dr/dt = 0
+    z0 = np.array([r, math.pi / 2, 0.0, ur, 0.0, L])
+    assert abs(_H(a)(z0) - E) < 1e-13
+    T = 100.0
+    p = O.push_params(a=a, dt=0.02, scheme=O.RK4)
+    z, H0, Hn, _ = _run(p, z0, int(T / 0.02))
+    assert abs(z[0, 0] - r) < 1e-6 * r
+    assert abs(z[0, 2] - Om * T) < 1e-6 * Om * T
+    assert abs(z[0, 1] - math.pi / 2) < 1e-12
+
+
+def test_charged_orbit_exact_wald_conserves_H_L():
+    """Sec. 3.1.3: charged orbits (Table C.1 RKA initial states) in the exact
+    Wald field conserve H and L; RK4 at dt = 1e-3 keeps both to ~1e-10."""
+    for name, (a, B0, r0, dth, ur, ut, up) in golden("table_c1_charged.txt"):
+        z0 = np.array([r0, math.pi / 2 - dth, 0.0, ur, ut, up])
+        p = O.push_params(a=a, dt=1e-3, scheme=O.RK4, B0pot=B0, field_kind=O.FIELD_WALD,
+                          B0field=B0)
+        z, H0, Hn, alive = _run(p, z0, 3000, qm=1.0)
+        assert alive[0] == 1
+        L0 = O.hamiltonian(1.0, a, B0, z0[None, :], 1.0)[1][0]
+        L1 = O.hamiltonian(1.0, a, B0, z, 1.0)[1][0]
+        assert abs(Hn[0] - H0[0]) < 1e-10 * abs(H0[0]), name
+        assert abs(L1 - L0) < 1e-10 * abs(L0), name
+
+
+def test_interpolation_dominates_charged_error():
+    """Sec. 3.1.3 (Fig. 3d discussion): with the Wald field sampled on the grid
+    the H error is set by the interpolation: it falls with the resolution N
+    and does not change when dt is halved."""
+    a, B0 = 0.9, 1.0
+    z0 = np.array([6.0, 1.2, 0.0, 0.3, 0.5, 0.8])
+    errs = {}
+    for N in (64, 128, 256):
+        g = I.log_grid(N, N, 1.3, 12.0)
+        F = O.wald_on_grid(a, B0, g)
+        for dt in (2e-3, 1e-3):
+            p = O.push_params(a=a, dt=dt, scheme=O.RK4, B0pot=B0, field_kind=O.FIELD_GRID)
+            _, H0, Hn, _ = _run(p, z0, int(round(2.0 / dt)), qm=10.0, g=g, F=F)
+            errs[N, dt] = abs(Hn[0] - H0[0])
+    assert errs[64, 1e-3] > 1.8 * errs[128, 1e-3] > 1.8 * 1.8 * errs[256, 1e-3]
+    for N in (64, 128, 256):
+        assert abs(errs[N, 1e-3] - errs[N, 2e-3]) < 0.01 * errs[N, 1e-3]
+
+
+def test_gather_exact_for_bilinear_fields():
+    """The (r, th)-bilinear gather reproduces fields bilinear in (r, th) on every
+    staggered sub-grid, and extrapolates as a constant beyond the end nodes."""
+    g = I.log_grid(13, 9, 1.5, 30.0)
+    F = []
+    coef = [(0.3, -1.2, 0.7, 0.05), (1.0, 0.2, -0.4, 0.3), (-0.5, 0.1, 0.9, -0.2),
+            (2.0, 0.0, 1.0, 0.1), (0.1, 0.3, 0.0, 0.5), (0.0, -0.7, 0.2, 0.02)]
+    roff, toff = [1, 0, 0, 0, 1, 1], [0, 1, 0, 1, 0, 1]
+    for k in range(6):
+        X = g.rh if roff[k] else g.rn
+        Y = g.th if toff[k] else g.tn
+        f = np.zeros((g.Nr + 1, g.ld))
+        c = coef[k]
+        f[:X.size, :Y.size] = c[0] + c[1] * X[:, None] + c[2] * Y[None, :] + c[3] * X[:, None] * Y[None, :]
+        F.append(f.ravel())
+    rng = np.random.default_rng(3)
+    r = rng.uniform(g.rh[0], g.rh[-1], 200)
+    t = rng.uniform(g.th[0], g.th[-1], 200)
+    out = O.gather(g, F, r, t)
+    for k in range(6):
+        c = coef[k]
+        exp = c[0] + c[1] * r + c[2] * t + c[3] * r * t
+        assert np.abs(out[:, k] - exp).max() < 1e-12
+    # constant extrapolation below the first half node in r
+    t0 = g.th[0]
+    o2 = O.gather(g, F, np.array([g.rn[0]]), np.array([t0]))
+    c = coef[4]
+    assert abs(o2[0, 4] - (c[0] + c[1] * g.rh[0] + c[2] * t0 + c[3] * g.rh[0] * t0)) < 1e-12
+
+
+def test_cell_index_brute_force():
+    """Cell location: the cell (i, j) with r_i <= r < r_{i+1}, th_j <= th <
+    th_{j+1} (clamped), found by exhaustive search over the nodes; points on
+    nodes belong to the upper cell."""
+    g = I.log_grid(7, 5, 1.2, 9.0)
+    rng = np.random.default_rng(4)
+    r = np.concatenate([rng.uniform(0.5, 12, 300), g.rn, g.rn[:-1] * (1 + 1e-16)])
+    t = np.concatenate([rng.uniform(-0.1, 3.3, 300), rng.choice(g.tn, g.rn.size), rng.choice(g.tn, g.rn.size - 1)])
+    got = O.cell_index(g, r, t)
+    for k in range(r.size):
+        i = max([ii for ii in range(g.Nr) if g.rn[ii] <= r[k]] or [0])
+        j = max([jj for jj in range(g.Nth) if g.tn[jj] <= t[k]] or [0])
+        assert got[k] == i * g.Nth + j
+
+
+@pytest.mark.parametrize("scheme", [O.HYB1, O.HYB2])
+def test_hybrid_choice_equals_brute_force(scheme):
+    """Sec. 3.1.2: the hybrid accepts the RK4 trial iff its H-violation test
+    passes (Hyb2: Ht < Ht_max; Hyb1: dHt/dt < max) and otherwise returns the
+    implicit step from z^n (here the discrete-gradient scheme, which then
+    leaves H where it was); recomputed from separate RK4 pushes and H."""
+    a, dt = 0.9, 0.5
+    cand = I.orbit_candidates(64, seed=9)
+    z0, bad = O.seed_orbits(1.0, a, cand)
+    assert bad == 0
+    n = z0.shape[0]
+    qm = np.zeros(n)
+    H0, _, D0 = O.hamiltonian(1.0, a, 0.0, z0, qm)
+    Hprev = H0 * (1 + 1e-10 * np.sin(np.arange(n)))
+    pr = O.push_params(a=a, dt=dt, scheme=O.RK4)
+    zr = z0.copy(); Hr = Hprev.copy()
+    O.push(pr, zr, qm, H0, D0, Hr, np.ones(n, np.uint8))
+    Ht1 = np.abs(Hr - H0) / D0
+    stat = Ht1 if scheme == O.HYB2 else (Ht1 - np.abs(Hprev - H0) / D0) / dt
+    thr = float(np.median(stat))
+    acc = stat < thr
+    ph = O.push_params(a=a, dt=dt, scheme=scheme, implicit_kind=O.HAM, thr=thr, tol=1e-15)
+    zh = z0.copy(); Hh = Hprev.copy()
+    _, sch, its = O.push(ph, zh, qm, H0, D0, Hh, np.ones(n, np.uint8))
+    assert np.array_equal(sch == 0, acc)
+    assert 0 < acc.sum() < n
+    assert np.array_equal(zh[acc], zr[acc])
+    assert np.abs(Hh[~acc] - H0[~acc]).max() < 1e-14 * np.abs(H0).max()
+    assert np.all(its[~acc] > 0) and np.all(its[acc] == 0)
+
+
+def test_seeding_orbits_and_fido():
+    """Seeding: orbit candidates give H = E exactly (to round-off) with
+    u_th = 0, u_ph = L; FIDO-frame momenta give Gamma = sqrt(1 + |uhat|^2)."""
+    cand = I.orbit_candidates(256, seed=1)
+    z, bad = O.seed_orbits(1.0, 0.9, cand)
+    assert bad == 0
+    H = O.hamiltonian(1.0, 0.9, 0.0, z, 0.0)[0]
+    Es = np.array([cand[p, [k for k in range(cand.shape[1])
+                            if abs(cand[p, k, 0] - z[p, 0]) == 0][0], 2] for p in range(256)])
+    assert np.abs(H - Es).max() < 1e-12
+    g = I.wald_grid(32, 0.9)
+    d, q, w = I.thermal_draws(500, g, 1.6, 40.0, 0.1, seed=3)
+    zf = O.seed_fido(1.0, 0.9, d)
+    m = O.metric(1.0, 0.9, zf[:, 0], zf[:, 1])
+    u = zf[:, 3:]
+    quad = m[:, 8] * u[:, 0] ** 2 + 2 * m[:, 9] * u[:, 0] * u[:, 2] + m[:, 10] * u[:, 1] ** 2 + m[:, 11] * u[:, 2] ** 2
+    assert np.allclose(quad, (d[:, 3:] ** 2).sum(1), rtol=1e-12, atol=1e-15)
+
+
+def test_particle_boundaries():
+    """Sec. 2.5: particles inside r_h or beyond r_max are removed; crossing a
+    pole reflects (th -> -th, u_th -> -u_th, ph -> ph + pi)."""
+    a = 0.5
+    z = np.array([[1.5, 0.3, 0.0, -3.0, 0.0, 0.0],       # falls in
+                  [6.0, 0.002, 0.0, 0.0, -2.0, 0.0],     # crosses th = 0
+                  [19.99, 1.0, 0.0, 5.0, 0.0, 0.0]])     # leaves r_max = 20
+    p = O.push_params(a=a, dt=0.1, scheme=O.RK4, r_max=20.0)
+    z1, _, _, alive = _run(p, z, 3)
+    assert alive.tolist() == [0, 1, 0]
+    assert z1[1, 1] > 0 and z1[1, 4] > 0 and abs(z1[1, 2] - math.pi) < 1e-3
