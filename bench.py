@@ -1,0 +1,341 @@
+#!/usr/bin/env python
+"""Benchmark of the GRPIC push on GB300: charged e-/e+ test particles in the
+analytic Wald field (a = 0.9, B0 = 1) sampled on a 512 x 512 (ln r, th) FP64
+Yee grid, r in [0.9 r_+, 50 M], 2^20 particles per GPU, thermal
+Maxwell-Juettner theta_T = 0.1 seeds, q/m = -/+100, dt = 1e-3, hybrid
+RK4 <-> implicit-midpoint switch (Hyb1 criterion).
+
+One step = one fpic_push of every particle (RK4 trial + H test on all, IMR
+on the rejected ones, boundaries, cell index).  Metric: particle-steps/s.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fpic|reference]
+
+Under torchrun each rank pushes its own 2^20 particles (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s at fixed max |ΔH|/H; learned-guess vs plain hybrid, % roofline"
+UNIT = "particle-steps/s"
+A_SPIN, B0, THETA_T, QM, DT, NGRID = 0.9, 1.0, 0.1, 100.0, 1e-3, 512
+HYB1_THR = 3.5e-6          # (d Htilde/dt)_max of the Hyb1 test
+# Algorithmic FP64 flops (FMA = 2, add/mul/div/sqrt/rsqrt = 1, sin+cos = 2),
+# counted from the formulas of the push ("Roofline").
+FLOP_EVAL = 230            # metric + derivatives + gather + RHS + H at one point
+FLOP_RK4_TRIAL = 4 * FLOP_EVAL + 79 + 56 + 5
+FLOP_IMR_ITER = FLOP_EVAL + 48
+FLOP_IMR_FINAL = FLOP_EVAL
+NOMINAL_FP64_GFLOPS = 1250.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="fpic", choices=["fpic", "reference"])
+    ap.add_argument("--n", type=int, default=1 << 20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=4)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands, on a bounded sample, all host cores
+# ---------------------------------------------------------------------------
+
+def _oracle_chunk(args):
+    lo, hi, n_total, steps, seed = args
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import oracle as O
+    from paper_2602_07452_gb300 import inputs as I
+    g = I.wald_grid(NGRID, A_SPIN)
+    Fo = O.wald_on_grid(A_SPIN, B0, g)
+    d, q, w = I.thermal_draws(n_total, g, 1.02 * I.horizon(1.0, A_SPIN), 49.0, THETA_T, seed=seed, qm=QM)
+    d, q = d[lo:hi], q[lo:hi]
+    z = np.ascontiguousarray(O.seed_fido(1.0, A_SPIN, d))
+    H0, _, D0 = O.hamiltonian(1.0, A_SPIN, B0, z, q)
+    Hn = H0.copy()
+    alive = np.ones(len(q), np.uint8)
+    p = O.push_params(a=A_SPIN, dt=DT, scheme=O.HYB1, implicit_kind=O.IMR, thr=HYB1_THR, r_max=g.rn[-1],
+                      B0pot=B0, field_kind=O.FIELD_GRID)
+    t0 = time.perf_counter()
+    ps = 0
+    for _ in range(steps):
+        ps += int(alive.sum())
+        O.push(p, z, q, H0, D0, Hn, alive, g, Fo)
+    return ps, time.perf_counter() - t0
+
+
+def cpu_baseline(n, steps, pool=None, cores=None):
+    """Time the oracle on n particles x steps over all host cores."""
+    import multiprocessing as mp
+    cores = cores or os.cpu_count() or 1
+    chunks = [(i * n // cores, (i + 1) * n // cores, n, steps, 2) for i in range(cores)]
+    own = pool is None
+    if own:
+        pool = mp.get_context("spawn").Pool(cores)
+    try:
+        pool.map(_oracle_chunk, [(0, 64, 64, 1, 2)] * cores)   # import + build in every worker
+        res = pool.map(_oracle_chunk, chunks)
+        wall = max(r[1] for r in res)      # the workers push concurrently; set-up is not timed
+    finally:
+        if own:
+            pool.close()
+            pool.join()
+    ps = sum(r[0] for r in res)
+    return {"value": ps / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} particles x {steps} steps of the same workload (serial C oracle, "
+                      f"one spawn process per core)", "wall_s": round(wall, 3)}
+
+
+# ---------------------------------------------------------------------------
+# GPU clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def setup(n, rank, device):
+    import numpy as np
+    import torch
+    from paper_2602_07452_gb300 import fpic as F
+    from paper_2602_07452_gb300 import inputs as I
+    g = I.wald_grid(NGRID, A_SPIN)
+    ctx = F.fpic_init_metric(1.0, A_SPIN)
+    F.fpic_set_grid(ctx, g)
+    fields = [torch.zeros(g.size, dtype=torch.float64, device=device) for _ in range(6)]
+    F.fpic_init_wald(ctx, fields, B0)
+    d, q, w = I.thermal_draws(n, g, 1.02 * I.horizon(1.0, A_SPIN), 49.0, THETA_T, seed=2 + rank, qm=QM)
+    p = F.Particles.empty(n, device)
+    p.qm.copy_(torch.as_tensor(q, device=device))
+    p.w.copy_(torch.as_tensor(w, device=device))
+    F.fpic_init_particles(ctx, p, F.FPIC_SEED_FIDO, torch.as_tensor(d, device=device), B0pot=B0)
+    torch.cuda.synchronize()
+    return F, g, ctx, fields, p
+
+
+def run_gpu(args, ws, rank, local):
+    import torch
+    import torch.distributed as dist
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    F, g, ctx, fields, p = setup(args.n, rank, device)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    prm = F.push_params(DT, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=HYB1_THR, r_max=float(g.rn[-1]),
+                        B0pot=B0, events=ev[1:5])
+    for _ in range(args.warmup):
+        F.fpic_push(ctx, p, fields, prm, stats=True)
+    fp64_gflops = F.fpic_probe_fp64(3000)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)   # > 129 MB L2
+    t_step = t_ex = t_im = 0.0
+    psteps = 0
+    flops_ex = flops_im = 0.0
+    n_impl = n_iter = 0
+    launches = 0
+    clocks = Clocks(local)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(args.steps):
+        flush.fill_(k & 255)
+        ev[0].record()
+        st = F.fpic_push(ctx, p, fields, prm, stats=True)
+        ev[5].record()
+        torch.cuda.synchronize()
+        t_step += ev[0].elapsed_time(ev[5]) * 1e-3
+        t_ex += ev[1].elapsed_time(ev[2]) * 1e-3
+        t_im += ev[3].elapsed_time(ev[4]) * 1e-3
+        psteps += st["n_alive_before"]
+        n_impl += st["n_implicit"]
+        n_iter += st["n_iter_total"]
+        flops_ex += st["n_alive_before"] * FLOP_RK4_TRIAL
+        flops_im += st["n_iter_total"] * FLOP_IMR_ITER + st["n_implicit"] * FLOP_IMR_FINAL
+        launches += 3
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    # max over ranks of the device time, sum of the work
+    tot = torch.tensor([t_step], dtype=torch.float64, device=device)
+    work = torch.tensor([float(psteps)], dtype=torch.float64, device=device)
+    if ws > 1:
+        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+        dist.all_reduce(work, op=dist.ReduceOp.SUM)
+    T, W = float(tot.item()), float(work.item())
+    # energy error at the end of the timed region
+    H, _ = F.fpic_hamiltonian(ctx, p, B0pot=B0)
+    alive = p.alive.bool()
+    dH = ((H - p.H0).abs() / p.D0)[alive]
+    max_dH = float(dH.max().item()) if dH.numel() else 0.0
+    # end to end through the host-buffer C ABI: H2D inputs + push + D2H result, every step
+    hp = F.HostParticles(p.n)
+    for f in F.HostParticles.FIELDS_D:
+        getattr(hp, f).copy_(getattr(p, f).cpu())
+    hp.alive.copy_(p.alive.cpu())
+    prm_h = F.push_params(DT, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=HYB1_THR, r_max=float(g.rn[-1]),
+                          B0pot=B0)
+    e2e_steps = max(1, min(args.steps, 5))
+    F.fpic_push_host(ctx, hp, fields, prm_h)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_ps = 0
+    for _ in range(e2e_steps):
+        e2e_ps += int(hp.alive.sum().item())
+        F.fpic_push_host(ctx, hp, fields, prm_h)
+    e2e_t = time.perf_counter() - t0
+    e2e = torch.tensor([e2e_t], dtype=torch.float64, device=device)
+    e2e_w = torch.tensor([float(e2e_ps)], dtype=torch.float64, device=device)
+    if ws > 1:
+        dist.all_reduce(e2e, op=dist.ReduceOp.MAX)
+        dist.all_reduce(e2e_w, op=dist.ReduceOp.SUM)
+    dom = "k_explicit" if t_ex >= t_im else "k_imr"
+    ach = (flops_ex / t_ex if dom == "k_explicit" else flops_im / max(t_im, 1e-30)) / 1e9
+    line = {
+        "metric": METRIC, "value": W / T, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded thermal e-/e+ in the analytic Wald field)",
+        "config": {"workload": "wald-charged-test-particles (push only)", "a": A_SPIN, "B0": B0,
+                   "grid": f"{NGRID}x{NGRID} (ln r, theta), r in [0.9 r_+, 50 M]",
+                   "particles_per_gpu": args.n, "theta_T": THETA_T, "q_over_m": QM, "dt": DT,
+                   "scheme": "Hyb1 RK4<->IMR", "hyb1_thr": HYB1_THR, "tol": 1e-14,
+                   "implicit_fraction": n_impl / max(psteps, 1),
+                   "mean_imr_iterations": n_iter / max(n_impl, 1),
+                   "max_dH_over_D0": max_dH, "parallelism": f"dp{ws} (independent particle sets)",
+                   "l2": "256 MB buffer written between timed steps (outside the events)"},
+        "e2e": {"value": float(e2e_w.item()) / float(e2e.item()), "unit": UNIT,
+                "h2d_bytes_per_step": hp.bytes_in(), "d2h_bytes_per_step": hp.bytes_out(),
+                "api": "fpic_push_host (pinned host SoA in, result out, every step)"},
+        "roofline": {"bound": "alu", "kernel": dom, "achieved": ach, "peak": fp64_gflops,
+                     "peak_source": "FP64 FMA probe (fpic_probe_fp64) in this run; nominal 1250",
+                     "unit": "GFLOP/s", "frac": ach / fp64_gflops, "traffic": None,
+                     "share_explicit": t_ex / max(t_ex + t_im, 1e-30)},
+        "clocks": clk,
+        "gpu_launches": launches,
+    }
+    return line
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        n = 1 << 16
+        import multiprocessing as mp
+        cores = os.cpu_count() or 1
+        pool = mp.get_context("spawn").Pool(cores)
+        try:
+            for _ in range(args.warmup):
+                cpu_baseline(n, 1, pool, cores)
+            vals, walls = [], 0.0
+            tot_ps = 0.0
+            for _ in range(args.steps):
+                r = cpu_baseline(n, 1, pool, cores)
+                vals.append(r["value"])
+                walls += r["wall_s"]
+                tot_ps += r["value"] * r["wall_s"]
+        finally:
+            pool.close()
+            pool.join()
+        v = tot_ps / walls
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * walls / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic (seeded thermal e-/e+ in the analytic Wald field)",
+                "config": {"workload": "wald-charged-test-particles (push only)", "a": A_SPIN,
+                           "grid": f"{NGRID}x{NGRID} (ln r, theta)", "sample_particles": n,
+                           "scheme": "Hyb1 RK4<->IMR", "dt": DT},
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                 "sample": f"{n} particles x 1 step per timed step"},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+    pool = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import multiprocessing as mp
+        pool = mp.get_context("spawn").Pool(os.cpu_count() or 1)   # before any GPU call
+    import torch
+    import torch.distributed as dist
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    line = run_gpu(args, ws, rank, local)
+    if rank == 0:
+        if pool is not None:
+            try:
+                line["cpu_baseline"] = cpu_baseline(1 << 20, args.cpu_steps, pool)
+            finally:
+                pool.close()
+                pool.join()
+        print(json.dumps(line))
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

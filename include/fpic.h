@@ -1,0 +1,199 @@
+/*
+ * fpic.h -- C ABI of the GB300 (sm_103a) GRPIC hot path.
+ *
+ * Method: "FPIC: a new Particle-In-Cell code for stationary and axisymmetric
+ * black-hole spacetimes" (Meringolo & Rezzolla, arXiv 2602.07452).
+ *
+ * Conventions shared by every entry point
+ *   - Geometrised units G = c = 1; black-hole mass M, spin a (a length).
+ *   - Particle state (Sec. 2.2): contravariant position (r, th, ph) and
+ *     covariant momentum per unit mass (u_r, u_th, u_ph), FP64, SoA.
+ *   - Axisymmetric (r, th) Yee grid (Sec. 2.1, Fig. 1): Nr x Nth cells, node
+ *     tables r_i (Nr+1), r_{i+1/2} (Nr), th_j (Nth+1), th_{j+1/2} (Nth).
+ *     Component placement:
+ *        D^r, J^r (i+1/2, j)   D^th, J^th (i, j+1/2)   D^ph, J^ph, rho (i, j)
+ *        B^r      (i, j+1/2)   B^th       (i+1/2, j)   B^ph (i+1/2, j+1/2)
+ *     Every grid array is FP64, row-major [i * ld + j] with ld = Nth + 1 and
+ *     (Nr + 1) * ld elements (rows/columns a staggered component does not
+ *     use are padding, left untouched).
+ *   - Device pointers are owned by the caller (e.g. torch tensors); the
+ *     library never frees them.  The library owns the context, its node
+ *     tables, metric tables and scratch buffers.
+ *   - Every call is asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *     default stream) unless its comment says it synchronises.
+ *   - Return value: FPIC_OK (0), or a negative error code; the message of the
+ *     last error on the calling thread is returned by fpic_last_error().
+ *     Arguments are validated on the host before anything is launched; the
+ *     kernels never trap.
+ */
+#ifndef FPIC_H
+#define FPIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FPIC_OK 0
+#define FPIC_EINVAL (-1)        /* bad argument (message says which) */
+#define FPIC_ECUDA (-2)         /* a CUDA call failed */
+#define FPIC_ENOMEM (-3)        /* device allocation of library scratch failed */
+#define FPIC_ETIMEOUT (-4)      /* a bounded device wait ran out */
+#define FPIC_ENOTCONVERGED 1    /* non-fatal: some implicit solves hit max_iter */
+
+/* Pushers: Sec. 2.2.1 (RK4), Sec. 2.2.2 (IMR), Sec. 2.2.3 (Hamiltonian,
+ * geodesics only) and the hybrid of Sec. 3.1.2 (Hyb1 / Hyb2). */
+enum { FPIC_RK4 = 0, FPIC_IMR = 1, FPIC_HAM = 2, FPIC_HYB1 = 3, FPIC_HYB2 = 4 };
+
+/* Particle initialisation kinds for fpic_init_particles. */
+enum { FPIC_SEED_ORBIT = 0, FPIC_SEED_FIDO = 1 };
+
+typedef struct fpic_ctx fpic_ctx;
+
+/* Particle set, SoA, all device pointers of length n (caller-owned).
+ *   r, th, ph, ur, uth, uph : state, updated in place by fpic_push
+ *   qm     : charge-to-mass ratio q/m (0 = neutral)
+ *   w      : macro-particle weight (Sec. 2.3)
+ *   H0, D0 : initial energy H(x0,u0) and its error normaliser
+ *            D0 = |alpha Gamma - beta u_r|_0 + |(q/m) A_0|_0
+ *   Hn     : H after the last step (read by Hyb1, written by every push)
+ *   alive  : 1 = in the domain, 0 = removed (Sec. 2.5)
+ *   scheme : written by fpic_push: 0 = explicit step kept, 1 = implicit
+ *   iters  : written by fpic_push: implicit iteration count (saturates at 255)
+ *   cell   : written by fpic_cell_index / fpic_push: ir * Nth + ith           */
+typedef struct {
+    int64_t n;
+    double *r, *th, *ph, *ur, *uth, *uph;
+    double *qm, *w;
+    double *H0, *D0, *Hn;
+    uint8_t *alive, *scheme, *iters;
+    uint32_t *cell;
+} fpic_particles;
+
+/* Parameters of one push.
+ *   dt        : time step (finite, nonzero)
+ *   scheme    : FPIC_RK4 .. FPIC_HYB2
+ *   implicit  : FPIC_IMR or FPIC_HAM, the implicit partner of the hybrid
+ *   thr       : Hyb2: Htilde_max; Hyb1: (d Htilde / dt)_max   (Sec. 3.1.2)
+ *   tol       : implicit stop: max_i |dz_i| / (|z_i| + 1) <= tol
+ *   max_iter  : implicit iteration cap (1..255)
+ *   r_max     : outer removal radius; the inner one is the horizon r_+
+ *   dg_eps    : increment below which the discrete gradient takes the
+ *               analytic partial (App. D uses 1e-10)
+ *   B0pot     : B0 of the Wald potential A_0 entering H (0 = none)
+ *   guess     : nullable device array (n x 8, FP32) of learned implicit
+ *               guesses and scheme logits (see fpic_mlp_infer); NULL = plain
+ *   events    : nullable array of 4 cudaEvent_t recorded on the stream
+ *               around the explicit kernel ([0], [1]) and the implicit
+ *               kernel ([2], [3]) for per-kernel timing; NULL = none */
+typedef struct {
+    double dt;
+    int scheme;
+    int implicit;
+    double thr;
+    double tol;
+    int max_iter;
+    double r_max;
+    double dg_eps;
+    double B0pot;
+    const float *guess;
+    void *const *events;
+} fpic_push_params;
+
+/* Host-side counters of one push (filled only when a pointer is passed;
+ * that makes fpic_push synchronise the stream). */
+typedef struct {
+    int64_t n_alive_before;
+    int64_t n_implicit;       /* particles that took the implicit scheme */
+    int64_t n_iter_total;     /* sum of implicit iterations */
+    int64_t n_notconv;        /* implicit solves stopped by max_iter */
+    int64_t n_removed;        /* particles removed by the boundaries */
+    int64_t n_rhs_evals;      /* right-hand-side evaluations performed */
+} fpic_push_stats;
+
+/* Create a context for the Kerr spacetime of mass M > 0 and spin |a| <= M
+ * (Appendix A).  *ctx receives a library-owned handle; release it with
+ * fpic_destroy.  Binds to the current CUDA device.
+ * Errors: FPIC_EINVAL (M <= 0, |a| > M, ctx NULL), FPIC_ENOMEM. */
+int fpic_init_metric(fpic_ctx **ctx, double M, double a);
+
+/* Release the context and every buffer the library allocated for it. */
+void fpic_destroy(fpic_ctx *ctx);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char *fpic_last_error(void);
+
+/* Set the (r, th) grid (Sec. 2.1; half-th domain, Sec. 2.5).  rn (Nr+1),
+ * rh (Nr), tn (Nth+1), th (Nth) are HOST arrays of strictly increasing node
+ * coordinates with rn[0] > 0, copied into the context; cell location against
+ * them is exact (FP64 comparisons only).  Also builds the metric tables at
+ * every Yee point (Sec. 2.1: "computed only initially and stored").
+ * Synchronises the device.  Errors: FPIC_EINVAL (sizes < 2, non-monotone or
+ * non-positive nodes), FPIC_ENOMEM, FPIC_ECUDA. */
+int fpic_set_grid(fpic_ctx *ctx, int Nr, int Nth, const double *rn, const double *rh,
+                  const double *tn, const double *th);
+
+/* Sample the Wald electro-vacuum field of strength B0 (Appendix B.1) at
+ * every Yee point: fields[0..5] = D^r, D^th, D^ph, B^r, B^th, B^ph, device
+ * arrays in the grid layout.  Requires fpic_set_grid and M = 1 (the
+ * appendix's units).  Errors: FPIC_EINVAL. */
+int fpic_init_wald(fpic_ctx *ctx, double *const fields[6], double B0, void *stream);
+
+/* Initialise particles from caller-supplied random draws (device arrays):
+ *   FPIC_SEED_ORBIT: draws is n x K x 5 (r, th, E, L, root sign); the first
+ *     candidate for which H(r, th, u_r, 0, L) = E has a root with
+ *     E + beta u_r > 0 is used; u_th = 0, u_ph = L, ph = 0.
+ *   FPIC_SEED_FIDO : draws is n x 6 (r, th, ph, uhat): FIDO-frame momentum
+ *     mapped to u_i = L_ia uhat_a with gamma_ij = L L^T (Cholesky).
+ * Then sets H0 = Hn = H and D0 (B0pot as in fpic_push_params), alive = 1.
+ * qm and w must already be filled by the caller.  Particles without a valid
+ * orbit candidate get alive = 0.  Errors: FPIC_EINVAL. */
+int fpic_init_particles(fpic_ctx *ctx, fpic_particles *p, int kind, const double *draws,
+                        int K, double B0pot, void *stream);
+
+/* One step of every alive particle (Sec. 2.2 and Sec. 3.1.2): the fields
+ * D^i, B^i (fields[0..5], Yee layout, NULL = no field) are gathered at the
+ * particle by bilinear interpolation in (r, th) on each component's own
+ * sub-grid and held fixed over the step.  Hybrid schemes take an RK4 trial
+ * and redo rejected particles with the implicit scheme from z^n, starting
+ * from the trial (or from the learned guess when prm->guess is set).
+ * After the step: particle boundaries (Sec. 2.5), Hn, scheme, iters, cell.
+ * FPIC_HAM (and a hybrid with implicit = FPIC_HAM) pushes geodesics: q/m and
+ * fields are ignored by its implicit part.  Uses library scratch (grown on
+ * demand).  Returns FPIC_ENOTCONVERGED (> 0) if stats was given and some
+ * implicit solve hit max_iter.  Errors: FPIC_EINVAL, FPIC_ENOMEM, FPIC_ECUDA. */
+int fpic_push(fpic_ctx *ctx, fpic_particles *p, const double *const fields[6],
+              const fpic_push_params *prm, fpic_push_stats *stats, void *stream);
+
+/* fpic_push on a particle set held in HOST memory (pinned or pageable):
+ * the arrays of *host_p are copied to library-owned device buffers, pushed
+ * exactly as fpic_push does, and the state, Hn, alive, scheme, iters and
+ * cell arrays are copied back; synchronises the stream before returning.
+ * fields stay device arrays.  Errors: as fpic_push. */
+int fpic_push_host(fpic_ctx *ctx, fpic_particles *host_p, const double *const fields[6],
+                   const fpic_push_params *prm, fpic_push_stats *stats, void *stream);
+
+/* Measurement helper (not part of the method): sustained FP64 fused
+ * multiply-add rate of the current device, in GFLOP/s (2 flops per FMA),
+ * from a kernel of independent FMA chains on every SM, timed with CUDA
+ * events.  Synchronises the device.  Errors: FPIC_EINVAL (out NULL),
+ * FPIC_ECUDA. */
+int fpic_probe_fp64(double *gflops_out, int reps);
+
+/* H (Eq. Ham with the Wald A_0 of Sec. 3.1.3 when B0pot != 0) and
+ * L = u_ph + (q/m) A_ph for every particle.  H_out, L_out: device arrays of
+ * length n, either may be NULL.  Errors: FPIC_EINVAL. */
+int fpic_hamiltonian(fpic_ctx *ctx, const fpic_particles *p, double B0pot, double *H_out,
+                     double *L_out, void *stream);
+
+/* Cell index ir * Nth + ith of every particle (r_i <= r < r_{i+1}, clamped to
+ * the grid), written to p->cell.  Exact: FP64 comparisons against the node
+ * tables.  Errors: FPIC_EINVAL. */
+int fpic_cell_index(fpic_ctx *ctx, fpic_particles *p, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FPIC_H */

@@ -1,0 +1,226 @@
+// Device-side building blocks of the GRPIC push: closed-form Kerr-Schild
+// metric and derivatives (Appendix A), the equations of motion (Eqs. p1, p2,
+// O1, O2), the Hamiltonian (Eq. Ham) and the staggered-grid field gather.
+//
+// GB300 note: FP64 issues at a small fraction of the FP32 rate, so these
+// helpers are written to minimise FP64-pipe instructions: one sincos, one
+// reciprocal and two reciprocal square roots per evaluation, fused
+// multiply-adds throughout, and cell location by integer comparison of the
+// IEEE bit patterns (order-preserving) instead of FP64 compares.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fpic {
+
+struct BH {
+    double M, a, a2, twoM;
+};
+
+// Metric at a point (r, th) given sin/cos th.
+struct Geo {
+    double s, c, rho2, irho2, t;      // t = 1/(rho^2 sin^2 th)
+    double xi, alpha, ixi, beta;
+    double gurr, gurp, gutt, gupp;
+    double grr, grp, gtt, gpp, sqrtg;
+};
+
+__device__ __forceinline__ void geo_eval(const BH& bh, double r, double s, double c, Geo& g)
+{
+    const double s2 = s * s, c2 = c * c;
+    g.s = s;
+    g.c = c;
+    g.rho2 = fma(bh.a2, c2, r * r);
+    g.t = 1.0 / (g.rho2 * s2);
+    g.irho2 = g.t * s2;
+    g.xi = fma(bh.twoM * r, g.irho2, 1.0);
+    g.alpha = rsqrt(g.xi);
+    g.ixi = g.alpha * g.alpha;
+    g.beta = (bh.twoM * r) * g.irho2 * g.ixi;
+    g.gurr = fma(bh.a2 * s2, g.irho2, g.ixi);
+    g.gurp = bh.a * g.irho2;
+    g.gutt = g.irho2;
+    g.gupp = g.t;
+    g.grr = g.xi;
+    g.grp = -bh.a * g.xi * s2;
+    g.gtt = g.rho2;
+    g.gpp = s2 * fma(bh.a2 * g.xi, s2, g.rho2);
+    g.sqrtg = g.rho2 * g.xi * g.alpha * s;
+}
+
+// d_r and d_th of alpha, beta^r, g^rr, g^rp, g^tt, g^pp.
+struct GeoD {
+    double al[2], be[2], rr[2], rp[2], tt[2], pp[2];
+};
+
+__device__ __forceinline__ void geo_deriv(const BH& bh, double r, const Geo& g, GeoD& d)
+{
+    const double s = g.s, c = g.c, s2 = s * s;
+    const double iP = g.irho2, iP2 = iP * iP;
+    const double sc = s * c;
+    const double dPr = 2.0 * r;
+    const double dPt = -2.0 * bh.a2 * sc;
+    // d xi = 2M d(r / rho^2)
+    const double dxir = bh.twoM * fma(-r, dPr, g.rho2) * iP2;
+    const double dxit = -bh.twoM * r * dPt * iP2;
+    const double a3h = -0.5 * g.alpha * g.ixi;      // -alpha^3 / 2
+    const double ixi2 = g.ixi * g.ixi;
+    d.al[0] = a3h * dxir;
+    d.al[1] = a3h * dxit;
+    d.be[0] = dxir * ixi2;
+    d.be[1] = dxit * ixi2;
+    const double a2s2 = bh.a2 * s2;
+    d.rr[0] = -a2s2 * dPr * iP2 - dxir * ixi2;
+    d.rr[1] = fma(2.0 * bh.a2 * sc, iP, -a2s2 * dPt * iP2) - dxit * ixi2;
+    d.rp[0] = -bh.a * dPr * iP2;
+    d.rp[1] = -bh.a * dPt * iP2;
+    d.tt[0] = -dPr * iP2;
+    d.tt[1] = -dPt * iP2;
+    // g^pp = t = 1/(rho^2 s^2):  d t = -t^2 d(rho^2 s^2)
+    const double t2 = g.t * g.t;
+    d.pp[0] = -t2 * dPr * s2;
+    d.pp[1] = -t2 * fma(dPt, s2, 2.0 * g.rho2 * sc);
+}
+
+// Order-preserving integer key of a double (monotone for all non-NaN values).
+__device__ __forceinline__ long long okey(double x)
+{
+    long long b = __double_as_longlong(x);
+    return b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
+}
+
+// Grid as seen by the kernels.  Node tables and their inverse spacings
+// 1/(X[i+1]-X[i]) live in library-owned device memory.
+struct GridDev {
+    int Nr, Nth, ld;
+    const double *rn, *rh, *tn, *th;
+    const double *irn, *irh, *itn, *ith;
+    float lr0, lrh0, ilr;        // FP32 index estimate in ln r
+    float t0, th0, it;           // FP32 index estimate in th
+};
+
+// Locate x in node list X[0..m-1]: X[i] <= x < X[i+1], clamped to
+// [0, m-2]; w is the clamped linear weight.  est: FP32 index estimate.
+__device__ __forceinline__ void locate(const double* __restrict__ X, const double* __restrict__ iX,
+                                       int m, double x, float est, int& i, double& w)
+{
+    int k = __float2int_rd(est);
+    k = max(0, min(k, m - 2));
+    const long long kx = okey(x);
+    // walk to the right cell (the estimate is within one cell on uniform grids)
+    for (int it = 0; it < m && k > 0 && kx < okey(__ldg(X + k)); ++it) --k;
+    for (int it = 0; it < m && k < m - 2 && kx >= okey(__ldg(X + k + 1)); ++it) ++k;
+    i = k;
+    const double x0 = __ldg(X + k);
+    double ww = (x - x0) * __ldg(iX + k);
+    const bool below = kx < okey(x0);
+    const bool above = kx >= okey(__ldg(X + k + 1));
+    ww = below ? 0.0 : ww;
+    ww = above ? 1.0 : ww;
+    w = ww;
+}
+
+struct Fields {
+    const double* f[6];   // D^r, D^th, D^ph, B^r, B^th, B^ph (Yee layout)
+};
+
+// Bilinear (r, th) gather of the six components at (r, th).
+__device__ __forceinline__ void gather(const GridDev& G, const Fields& F, double r, double th,
+                                       double D[3], double B[3])
+{
+    const float lr = __logf((float)r);
+    const float tf = (float)th;
+    int i0, i1, j0, j1;
+    double wr0, wr1, wt0, wt1;
+    locate(G.rn, G.irn, G.Nr + 1, r, (lr - G.lr0) * G.ilr, i0, wr0);
+    locate(G.rh, G.irh, G.Nr, r, (lr - G.lrh0) * G.ilr, i1, wr1);
+    locate(G.tn, G.itn, G.Nth + 1, th, (tf - G.t0) * G.it, j0, wt0);
+    locate(G.th, G.ith, G.Nth, th, (tf - G.th0) * G.it, j1, wt1);
+    const int ld = G.ld;
+    // component k sits at (roff, toff): D^r (1,0) D^th (0,1) D^ph (0,0)
+    //                                    B^r (0,1) B^th (1,0) B^ph (1,1)
+    double v[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const bool ro = (k == 0 || k == 4 || k == 5);
+        const bool to = (k == 1 || k == 3 || k == 5);
+        const int i = ro ? i1 : i0, j = to ? j1 : j0;
+        const double wr = ro ? wr1 : wr0, wt = to ? wt1 : wt0;
+        const double* p = F.f[k] + i * ld + j;
+        const double f00 = __ldg(p), f01 = __ldg(p + 1);
+        const double f10 = __ldg(p + ld), f11 = __ldg(p + ld + 1);
+        const double lo = fma(wt, f01 - f00, f00);
+        const double hi = fma(wt, f11 - f10, f10);
+        v[k] = fma(wr, hi - lo, lo);
+    }
+    D[0] = v[0]; D[1] = v[1]; D[2] = v[2];
+    B[0] = v[3]; B[1] = v[4]; B[2] = v[5];
+}
+
+// Equations of motion at y (Eqs. p1, p2, O1, O2) and, as a by-product, the
+// Hamiltonian H(y) = alpha Gamma - beta u_r - (q/m) A_0 (Eq. Ham with the
+// Wald A_0 when B0pot != 0).  D, B: FIDO fields at y (ignored if !em).
+__device__ __forceinline__ void eval_rhs(const BH& bh, const double y[6], double qm, bool em,
+                                         const double D[3], const double B[3], double B0pot,
+                                         double f[6], double& H)
+{
+    double s, c;
+    sincos(y[1], &s, &c);
+    Geo g;
+    geo_eval(bh, y[0], s, c, g);
+    GeoD d;
+    geo_deriv(bh, y[0], g, d);
+    const double ur = y[3], ut = y[4], up = y[5];
+    const double Ur = fma(g.gurr, ur, g.gurp * up);
+    const double Ut = g.gutt * ut;
+    const double Up = fma(g.gurp, ur, g.gupp * up);
+    const double G2 = fma(ur, Ur, fma(ut, Ut, fma(up, Up, 1.0)));
+    const double iG = rsqrt(G2);
+    const double G = G2 * iG;
+    const double aiG = g.alpha * iG;
+    f[0] = fma(aiG, Ur, -g.beta);
+    f[1] = aiG * Ut;
+    f[2] = aiG * Up;
+    const double h = -0.5 * aiG;   // -alpha / (2 Gamma)
+    const double urur = ur * ur, urup2 = 2.0 * ur * up, utut = ut * ut, upup = up * up;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const double quad = fma(urur, d.rr[i], fma(urup2, d.rp[i], fma(utut, d.tt[i], upup * d.pp[i])));
+        f[3 + i] = fma(h, quad, fma(-G, d.al[i], ur * d.be[i]));
+    }
+    f[5] = 0.0;
+    if (em) {
+        const double k = qm * g.alpha;
+        const double ks = k * g.sqrtg * iG;
+        const double cr = fma(Ut, B[2], -Up * B[1]);
+        const double ct = fma(Up, B[0], -Ur * B[2]);
+        const double cp = fma(Ur, B[1], -Ut * B[0]);
+        f[3] = fma(k, fma(g.grr, D[0], g.grp * D[2]), fma(ks, cr, f[3]));
+        f[4] = fma(k, g.gtt * D[1], fma(ks, ct, f[4]));
+        f[5] = fma(k, fma(g.grp, D[0], g.gpp * D[2]), ks * cp);
+    }
+    H = fma(g.alpha, G, -g.beta * ur);
+    if (B0pot != 0.0 && qm != 0.0) {
+        // A_0 = B0 a r (1 + cos^2 th) / rho^2   (Sec. 3.1.3)
+        H = fma(-qm * B0pot * bh.a * y[0], (1.0 + c * c) * g.irho2, H);
+    }
+}
+
+// Hamiltonian only (no derivatives, no force).
+__device__ __forceinline__ double eval_H(const BH& bh, const double y[6], double qm, double B0pot)
+{
+    double s, c;
+    sincos(y[1], &s, &c);
+    Geo g;
+    geo_eval(bh, y[0], s, c, g);
+    const double ur = y[3], ut = y[4], up = y[5];
+    const double Ur = fma(g.gurr, ur, g.gurp * up);
+    const double Ut = g.gutt * ut;
+    const double Up = fma(g.gurp, ur, g.gupp * up);
+    const double G = sqrt(fma(ur, Ur, fma(ut, Ut, fma(up, Up, 1.0))));
+    double H = fma(g.alpha, G, -g.beta * ur);
+    if (B0pot != 0.0 && qm != 0.0) H = fma(-qm * B0pot * bh.a * y[0], (1.0 + c * c) * g.irho2, H);
+    return H;
+}
+
+}  // namespace fpic

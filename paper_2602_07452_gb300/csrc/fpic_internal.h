@@ -1,0 +1,55 @@
+// Library-internal context and helpers shared by the translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/fpic.h"
+#include "fpic_device.cuh"
+
+struct fpic_ctx {
+    int device = 0;
+    int sm_count = 0;
+    double M = 1.0, a = 0.0;
+    fpic::BH bh{};
+    double r_h = 0.0;
+    // grid
+    bool has_grid = false;
+    int Nr = 0, Nth = 0, ld = 0;
+    double* d_nodes = nullptr;       // rn rh tn th irn irh itn ith (library-owned)
+    fpic::GridDev G{};
+    // host copies of the node tables
+    std::string h_nodes;             // raw bytes of rn, rh, tn, th
+    // metric tables at the Yee points (library-owned), see pic.cu
+    double* d_metric = nullptr;
+    size_t metric_stride = 0;        // elements per table
+    // device counters (library-owned) and their pinned host mirror
+    long long* d_cnt = nullptr;
+    long long* h_cnt = nullptr;
+    // scratch grown on demand
+    void* d_scratch = nullptr;
+    size_t scratch_bytes = 0;
+    // second scratch (sort / deposit)
+    void* d_scratch2 = nullptr;
+    size_t scratch2_bytes = 0;
+};
+
+namespace fpic {
+
+enum { CNT_QUEUE = 0, CNT_HEAD = 1, CNT_ITERS = 2, CNT_NOTCONV = 3, CNT_REMOVED = 4,
+       CNT_ALIVE = 5, CNT_EVALS = 6, CNT_ERR = 7, CNT_N = 8 };
+
+int set_error(int code, const char* fmt, ...);
+int check_cuda(cudaError_t e, const char* what);
+int ensure_scratch(fpic_ctx* c, size_t bytes);
+int ensure_scratch2(fpic_ctx* c, size_t bytes);
+bool particles_ok(const fpic_particles* p, bool need_state);
+
+}  // namespace fpic
+
+#define FPIC_CUDA(call)                                                   \
+    do {                                                                  \
+        int _rc = fpic::check_cuda((call), #call);                        \
+        if (_rc) return _rc;                                              \
+    } while (0)

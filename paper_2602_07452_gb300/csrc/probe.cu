@@ -1,0 +1,52 @@
+// Measurement helper: sustained FP64 FMA throughput of the device.  Eight
+// independent FMA chains per thread keep the FP64 pipe fed; the result is
+// stored so the chains cannot be removed.
+#include "fpic_internal.h"
+
+namespace fpic {
+
+__global__ void __launch_bounds__(256) k_fma64(double* out, int reps, double x)
+{
+    double a0 = x + threadIdx.x, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3;
+    double a4 = a0 + 4, a5 = a0 + 5, a6 = a0 + 6, a7 = a0 + 7;
+    const double m = 0.999999999, c = 1e-9;
+    for (int i = 0; i < reps; ++i) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            a0 = fma(a0, m, c); a1 = fma(a1, m, c); a2 = fma(a2, m, c); a3 = fma(a3, m, c);
+            a4 = fma(a4, m, c); a5 = fma(a5, m, c); a6 = fma(a6, m, c); a7 = fma(a7, m, c);
+        }
+    }
+    out[blockIdx.x * blockDim.x + threadIdx.x] = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+}
+
+}  // namespace fpic
+
+extern "C" int fpic_probe_fp64(double* gflops_out, int reps)
+{
+    using namespace fpic;
+    if (!gflops_out || reps < 1) return set_error(FPIC_EINVAL, "fpic_probe_fp64: bad argument");
+    int dev, sms;
+    FPIC_CUDA(cudaGetDevice(&dev));
+    FPIC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = sms * 8, threads = 256;
+    double* out = nullptr;
+    FPIC_CUDA(cudaMalloc(&out, (size_t)blocks * threads * sizeof(double)));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    k_fma64<<<blocks, threads>>>(out, 4, 1.0);   // warm-up
+    cudaEventRecord(e0);
+    k_fma64<<<blocks, threads>>>(out, reps, 1.0);
+    cudaEventRecord(e1);
+    cudaError_t err = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    FPIC_CUDA(err);
+    const double flops = 2.0 * 8 * 16 * (double)reps * blocks * threads;
+    *gflops_out = flops / (ms * 1e-3) / 1e9;
+    return FPIC_OK;
+}

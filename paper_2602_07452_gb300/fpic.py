@@ -1,0 +1,284 @@
+"""Thin ctypes binding of libfpic.so: the C ABI of include/fpic.h, same names.
+
+Argument marshalling only -- every step runs in the library's CUDA kernels.
+PyTorch supplies device memory and streams.  Importing this module does not
+load the library; the first call does, and it raises if libfpic.so is
+missing (build it with ``paper_2602_07452_gb300.build.build()``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from dataclasses import dataclass
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libfpic.so")
+
+FPIC_OK, FPIC_EINVAL, FPIC_ECUDA, FPIC_ENOMEM, FPIC_ETIMEOUT = 0, -1, -2, -3, -4
+FPIC_ENOTCONVERGED = 1
+FPIC_RK4, FPIC_IMR, FPIC_HAM, FPIC_HYB1, FPIC_HYB2 = 0, 1, 2, 3, 4
+FPIC_SEED_ORBIT, FPIC_SEED_FIDO = 0, 1
+
+_lib = None
+_lock = threading.Lock()
+
+
+class FpicError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"fpic error {code}: {msg}")
+        self.code = code
+
+
+_D = C.POINTER(C.c_double)
+_U8 = C.POINTER(C.c_uint8)
+_U32 = C.POINTER(C.c_uint32)
+
+
+class fpic_particles(C.Structure):
+    _fields_ = [("n", C.c_int64), ("r", _D), ("th", _D), ("ph", _D), ("ur", _D), ("uth", _D),
+                ("uph", _D), ("qm", _D), ("w", _D), ("H0", _D), ("D0", _D), ("Hn", _D),
+                ("alive", _U8), ("scheme", _U8), ("iters", _U8), ("cell", _U32)]
+
+
+class fpic_push_params(C.Structure):
+    _fields_ = [("dt", C.c_double), ("scheme", C.c_int), ("implicit", C.c_int), ("thr", C.c_double),
+                ("tol", C.c_double), ("max_iter", C.c_int), ("r_max", C.c_double),
+                ("dg_eps", C.c_double), ("B0pot", C.c_double), ("guess", C.c_void_p),
+                ("events", C.c_void_p)]
+
+
+class fpic_push_stats(C.Structure):
+    _fields_ = [("n_alive_before", C.c_int64), ("n_implicit", C.c_int64), ("n_iter_total", C.c_int64),
+                ("n_notconv", C.c_int64), ("n_removed", C.c_int64), ("n_rhs_evals", C.c_int64)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "fpic_init_metric": (C.c_int, [C.POINTER(C.c_void_p), C.c_double, C.c_double]),
+    "fpic_destroy": (None, [C.c_void_p]),
+    "fpic_last_error": (C.c_char_p, []),
+    "fpic_set_grid": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _D, _D, _D, _D]),
+    "fpic_init_wald": (C.c_int, [C.c_void_p, C.POINTER(_D), C.c_double, C.c_void_p]),
+    "fpic_init_particles": (C.c_int, [C.c_void_p, C.POINTER(fpic_particles), C.c_int, _D, C.c_int,
+                                      C.c_double, C.c_void_p]),
+    "fpic_push": (C.c_int, [C.c_void_p, C.POINTER(fpic_particles), C.POINTER(_D),
+                            C.POINTER(fpic_push_params), C.POINTER(fpic_push_stats), C.c_void_p]),
+    "fpic_push_host": (C.c_int, [C.c_void_p, C.POINTER(fpic_particles), C.POINTER(_D),
+                                 C.POINTER(fpic_push_params), C.POINTER(fpic_push_stats), C.c_void_p]),
+    "fpic_probe_fp64": (C.c_int, [C.POINTER(C.c_double), C.c_int]),
+    "fpic_hamiltonian": (C.c_int, [C.c_void_p, C.POINTER(fpic_particles), C.c_double, _D, _D, C.c_void_p]),
+    "fpic_cell_index": (C.c_int, [C.c_void_p, C.POINTER(fpic_particles), C.c_void_p]),
+}
+
+
+def declared_symbols():
+    """Every entry point the binding declares (include/fpic.h)."""
+    return sorted(_SIGS)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise FpicError(FPIC_EINVAL, f"libfpic.so not built ({LIB_PATH}); run build()")
+            L = C.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(rc, allow_notconv=True):
+    if rc == FPIC_OK or (allow_notconv and rc == FPIC_ENOTCONVERGED):
+        return rc
+    raise FpicError(rc, lib().fpic_last_error().decode())
+
+
+def _dp(t):
+    """Device pointer of a tensor as a typed ctypes pointer (None for None)."""
+    if t is None:
+        return None
+    return C.cast(C.c_void_p(t.data_ptr()), _D)
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+@dataclass
+class Particles:
+    """SoA particle set in device memory (torch tensors)."""
+    r: torch.Tensor
+    th: torch.Tensor
+    ph: torch.Tensor
+    ur: torch.Tensor
+    uth: torch.Tensor
+    uph: torch.Tensor
+    qm: torch.Tensor
+    w: torch.Tensor
+    H0: torch.Tensor
+    D0: torch.Tensor
+    Hn: torch.Tensor
+    alive: torch.Tensor
+    scheme: torch.Tensor
+    iters: torch.Tensor
+    cell: torch.Tensor
+
+    @staticmethod
+    def empty(n, device="cuda"):
+        f = lambda: torch.zeros(n, dtype=torch.float64, device=device)
+        u = lambda: torch.zeros(n, dtype=torch.uint8, device=device)
+        return Particles(f(), f(), f(), f(), f(), f(), f(), f(), f(), f(), f(), u(), u(), u(),
+                         torch.zeros(n, dtype=torch.int32, device=device))
+
+    @property
+    def n(self):
+        return self.r.numel()
+
+    def state(self):
+        return torch.stack([self.r, self.th, self.ph, self.ur, self.uth, self.uph], dim=1)
+
+    def set_state(self, z):
+        for k, name in enumerate(("r", "th", "ph", "ur", "uth", "uph")):
+            getattr(self, name).copy_(z[:, k])
+
+    def struct(self):
+        return fpic_particles(self.n, _dp(self.r), _dp(self.th), _dp(self.ph), _dp(self.ur), _dp(self.uth),
+                              _dp(self.uph), _dp(self.qm), _dp(self.w), _dp(self.H0), _dp(self.D0), _dp(self.Hn),
+                              C.cast(C.c_void_p(self.alive.data_ptr()), _U8),
+                              C.cast(C.c_void_p(self.scheme.data_ptr()), _U8),
+                              C.cast(C.c_void_p(self.iters.data_ptr()), _U8),
+                              C.cast(C.c_void_p(self.cell.data_ptr()), _U32))
+
+
+class Ctx:
+    """Owns an fpic_ctx handle."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            _lib.fpic_destroy(h)
+
+
+def fpic_init_metric(M: float, a: float) -> Ctx:
+    h = C.c_void_p()
+    _check(lib().fpic_init_metric(C.byref(h), M, a))
+    return Ctx(h)
+
+
+def fpic_set_grid(ctx: Ctx, grid) -> None:
+    import numpy as np
+    arrs = [np.ascontiguousarray(x, dtype=np.float64) for x in (grid.rn, grid.rh, grid.tn, grid.th)]
+    _check(lib().fpic_set_grid(ctx.handle, grid.Nr, grid.Nth, *[a.ctypes.data_as(_D) for a in arrs]))
+
+
+def _fields_arg(fields):
+    if fields is None:
+        return None
+    assert len(fields) == 6
+    for f in fields:
+        assert f.dtype == torch.float64 and f.is_cuda and f.is_contiguous()
+    return (_D * 6)(*[_dp(f) for f in fields])
+
+
+def fpic_init_wald(ctx: Ctx, fields, B0: float, stream=None) -> None:
+    _check(lib().fpic_init_wald(ctx.handle, _fields_arg(fields), B0, _stream(stream)))
+
+
+def fpic_init_particles(ctx: Ctx, p: Particles, kind: int, draws: torch.Tensor, K: int = 1,
+                        B0pot: float = 0.0, stream=None) -> None:
+    s = p.struct()
+    _check(lib().fpic_init_particles(ctx.handle, C.byref(s), kind, _dp(draws.contiguous()), K, B0pot,
+                                     _stream(stream)))
+
+
+def push_params(dt, scheme=FPIC_RK4, implicit=FPIC_IMR, thr=1e-12, tol=1e-14, max_iter=50,
+                r_max=1e300, dg_eps=1e-10, B0pot=0.0, guess=None, events=None):
+    """events: optional list of 4 torch.cuda.Event(enable_timing=True)."""
+    prm = fpic_push_params(dt, scheme, implicit, thr, tol, max_iter, r_max, dg_eps, B0pot,
+                           None if guess is None else guess.data_ptr(), None)
+    if events is not None:
+        arr = (C.c_void_p * 4)(*[C.c_void_p(e.cuda_event) for e in events])
+        prm._events_keepalive = arr
+        prm.events = C.cast(arr, C.c_void_p)
+    return prm
+
+
+def fpic_push(ctx: Ctx, p: Particles, fields, prm: fpic_push_params, stats: bool = False, stream=None):
+    """One push of every alive particle; returns the stats dict if asked."""
+    s = p.struct()
+    st = fpic_push_stats() if stats else None
+    rc = lib().fpic_push(ctx.handle, C.byref(s), _fields_arg(fields), C.byref(prm),
+                         C.byref(st) if st is not None else None, _stream(stream))
+    _check(rc)
+    return st.as_dict() if st is not None else None
+
+
+def fpic_hamiltonian(ctx: Ctx, p: Particles, B0pot: float = 0.0, stream=None):
+    H = torch.empty(p.n, dtype=torch.float64, device=p.r.device)
+    L = torch.empty_like(H)
+    s = p.struct()
+    _check(lib().fpic_hamiltonian(ctx.handle, C.byref(s), B0pot, _dp(H), _dp(L), _stream(stream)))
+    return H, L
+
+
+def fpic_cell_index(ctx: Ctx, p: Particles, stream=None) -> torch.Tensor:
+    s = p.struct()
+    _check(lib().fpic_cell_index(ctx.handle, C.byref(s), _stream(stream)))
+    return p.cell
+
+
+class HostParticles:
+    """Particle set in pinned host memory (numpy views of pinned tensors)."""
+
+    FIELDS_D = ("r", "th", "ph", "ur", "uth", "uph", "qm", "w", "H0", "D0", "Hn")
+    FIELDS_B = ("alive", "scheme", "iters")
+
+    def __init__(self, n):
+        self.n = n
+        for f in self.FIELDS_D:
+            setattr(self, f, torch.zeros(n, dtype=torch.float64).pin_memory())
+        for f in self.FIELDS_B:
+            setattr(self, f, torch.zeros(n, dtype=torch.uint8).pin_memory())
+        self.cell = torch.zeros(n, dtype=torch.int32).pin_memory()
+
+    def struct(self):
+        hp = lambda t, ty: C.cast(C.c_void_p(t.data_ptr()), ty)
+        return fpic_particles(self.n, *[hp(getattr(self, f), _D) for f in self.FIELDS_D],
+                              *[hp(getattr(self, f), _U8) for f in self.FIELDS_B], hp(self.cell, _U32))
+
+    def bytes_in(self):
+        return self.n * (8 * len(self.FIELDS_D) + 1)
+
+    def bytes_out(self):
+        return self.n * (8 * 7 + 3 + 4)
+
+
+def fpic_push_host(ctx: Ctx, hp: HostParticles, fields, prm: fpic_push_params, stats: bool = False,
+                   stream=None):
+    s = hp.struct()
+    st = fpic_push_stats() if stats else None
+    rc = lib().fpic_push_host(ctx.handle, C.byref(s), _fields_arg(fields), C.byref(prm),
+                              C.byref(st) if st is not None else None, _stream(stream))
+    _check(rc)
+    return st.as_dict() if st is not None else None
+
+
+def fpic_probe_fp64(reps: int = 2000) -> float:
+    out = C.c_double()
+    _check(lib().fpic_probe_fp64(C.byref(out), reps))
+    return out.value

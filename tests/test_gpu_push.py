@@ -1,0 +1,300 @@
+"""GPU parity of the push path against the oracle, element by element, on the
+same seeded inputs, through the C ABI.
+
+Bar (per step from an identical state): |z_gpu - z_oracle| <= 1e-12 (|z| + 1)
+per component; cell indices and plain-path scheme choices bit-exact (except
+states within 1e-12 relative of a node or of the threshold, counted)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2602_07452_gb300 import inputs as I
+from helpers import (assert_state_close, cuda_or_skip, dev, fields_dev, fpic, make_particles,
+                     thermal_state, to_np)
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def F():
+    cuda_or_skip()
+    return fpic()
+
+
+def _ctx(F, a, g=None):
+    ctx = F.fpic_init_metric(1.0, a)
+    if g is not None:
+        F.fpic_set_grid(ctx, g)
+    return ctx
+
+
+@pytest.fixture(scope="module")
+def wald128(F):
+    a = 0.9
+    g = I.wald_grid(128, a, r_max=50.0)
+    Fo = O.wald_on_grid(a, 1.0, g)
+    ctx = _ctx(F, a, g)
+    return a, g, Fo, ctx
+
+
+def test_wald_on_grid_matches_oracle(F, wald128):
+    a, g, Fo, ctx = wald128
+    Fg = [dev(np.zeros_like(f)) for f in Fo]
+    F.fpic_init_wald(ctx, Fg, 1.0)
+    for k in range(6):
+        got = Fg[k].cpu().numpy()
+        scale = np.abs(Fo[k]).max()
+        assert np.abs(got - Fo[k]).max() <= 1e-13 * scale, k
+
+
+def test_hamiltonian_matches_oracle(F, wald128):
+    a, g, Fo, ctx = wald128
+    d, z, q = thermal_state(3001, g, a)
+    p = make_particles(z, q)
+    H, L = F.fpic_hamiltonian(ctx, p, B0pot=1.0)
+    Ho, Lo, _ = O.hamiltonian(1.0, a, 1.0, z, q)
+    assert np.abs(H.cpu().numpy() - Ho).max() <= 1e-13 * (np.abs(Ho).max())
+    assert np.abs(L.cpu().numpy() - Lo).max() <= 1e-13 * (np.abs(Lo).max())
+
+
+def test_cell_index_bit_exact(F, wald128):
+    a, g, Fo, ctx = wald128
+    rng = np.random.default_rng(7)
+    r = np.concatenate([rng.uniform(g.rn[0] * 0.5, g.rn[-1] * 1.5, 5000), g.rn,
+                        np.nextafter(g.rn, 0), np.nextafter(g.rn, 1e9)])
+    t = np.concatenate([rng.uniform(-0.2, math.pi + 0.2, 5000), rng.choice(g.tn, 3 * g.rn.size)])
+    t[5000:5000 + g.tn.size] = g.tn
+    z = np.zeros((r.size, 6)); z[:, 0] = r; z[:, 1] = t
+    p = make_particles(z, np.zeros(r.size))
+    got = F.fpic_cell_index(ctx, p).cpu().numpy().view(np.uint32)
+    assert np.array_equal(got, O.cell_index(g, r, t))
+
+
+def test_seeding_matches_oracle(F):
+    a = 0.9
+    ctx = _ctx(F, a)
+    cand = I.orbit_candidates(777, seed=1)
+    zo, bad = O.seed_orbits(1.0, a, cand)
+    p = make_particles(np.zeros((777, 6)), np.zeros(777))
+    F.fpic_init_particles(ctx, p, F.FPIC_SEED_ORBIT, dev(cand), K=cand.shape[1])
+    zg = p.state().cpu().numpy()
+    assert bad == 0 and p.alive.cpu().numpy().all()
+    assert_state_close(zg, zo, 1e-13)
+    H0 = O.hamiltonian(1.0, a, 0.0, zo, 0.0)
+    assert np.abs(p.H0.cpu().numpy() - H0[0]).max() < 1e-14
+    g = I.wald_grid(64, a)
+    d, q, w = I.thermal_draws(1001, g, 1.5, 40.0, 0.1, seed=5)
+    zo = O.seed_fido(1.0, a, d)
+    p = make_particles(np.zeros((1001, 6)), q)
+    F.fpic_init_particles(ctx, p, F.FPIC_SEED_FIDO, dev(d), B0pot=1.0)
+    assert_state_close(p.state().cpu().numpy(), zo, 1e-13)
+    Ho, _, Do = O.hamiltonian(1.0, a, 1.0, zo, q)
+    assert np.abs(p.H0.cpu().numpy() - Ho).max() <= 1e-13 * np.abs(Ho).max()
+    assert np.abs(p.D0.cpu().numpy() - Do).max() <= 1e-13 * np.abs(Do).max()
+
+
+def _one_step(F, ctx, g, Fo, z, q, scheme, dt, thr=1e-12, implicit=None, B0pot=1.0, r_max=None,
+              max_iter=50, alive=None, tol=1e-14):
+    n = z.shape[0]
+    H0, _, D0 = O.hamiltonian(1.0, _A[id(ctx)], B0pot, z, q)
+    Hn = H0 * (1.0 + 1e-9 * np.cos(np.arange(n)))
+    implicit = implicit if implicit is not None else F.FPIC_IMR
+    r_max = r_max if r_max is not None else (g.rn[-1] if g is not None else 1e300)
+    alive = np.ones(n, np.uint8) if alive is None else alive
+    p = make_particles(z, q, H0, D0, Hn, alive)
+    prm = F.push_params(dt, scheme=scheme, implicit=implicit, thr=thr, tol=tol, max_iter=max_iter,
+                        r_max=r_max, B0pot=B0pot)
+    st = F.fpic_push(ctx, p, fields_dev(Fo) if Fo is not None else None, prm, stats=True)
+    po = O.push_params(a=_A[id(ctx)], dt=dt, scheme=scheme, implicit_kind=implicit, thr=thr, tol=tol,
+                       max_iter=max_iter, r_max=r_max, B0pot=B0pot,
+                       field_kind=O.FIELD_GRID if Fo is not None else O.FIELD_NONE)
+    zo = np.ascontiguousarray(z.copy()); Ho = Hn.copy(); ao = alive.copy()
+    nc, so, io = O.push(po, zo, q, H0, D0, Ho, ao, g, Fo)
+    return p, st, (zo, Ho, ao, so, io, nc), (H0, D0, Hn)
+
+
+_A = {}
+
+
+def _mk(F, a, g=None):
+    ctx = _ctx(F, a, g)
+    _A[id(ctx)] = a
+    return ctx
+
+
+@pytest.mark.parametrize("scheme", ["RK4", "IMR", "HYB1", "HYB2"])
+def test_charged_push_one_step_matches_oracle(F, scheme):
+    """Wald field on a 128 x 128 (ln r, th) grid, e-/e+ q/m = -/+100,
+    4741 particles (37 blocks of 128 plus a ragged tail), dt = 1e-3."""
+    a = 0.9
+    g = I.wald_grid(128, a)
+    Fo = O.wald_on_grid(a, 1.0, g)
+    ctx = _mk(F, a, g)
+    d, z, q = thermal_state(4741, g, a, theta=0.1, seed=11)
+    sch = getattr(F, "FPIC_" + scheme)
+    thr = {"HYB1": 8e-5, "HYB2": 8e-8}.get(scheme, 1e-12)
+    p, st, (zo, Ho, ao, so, io, nc), (H0, D0, Hn) = _one_step(F, ctx, g, Fo, z, q, sch, 1e-3, thr=thr)
+    zg, Hg, ag, sg, ig, cg = to_np(p)
+    assert np.array_equal(ag, ao)
+    if scheme.startswith("HYB"):
+        # exclude particles whose test statistic lies within 1e-12 of the threshold
+        pr = O.push_params(a=a, dt=1e-3, scheme=O.RK4, B0pot=1.0, field_kind=O.FIELD_GRID, r_max=g.rn[-1])
+        zr = np.ascontiguousarray(z.copy()); Hr = Hn.copy()
+        O.push(pr, zr, q, H0, D0, Hr, np.ones(len(q), np.uint8), g, Fo)
+        Ht1 = np.abs(Hr - H0) / D0
+        stat = Ht1 if scheme == "HYB2" else (Ht1 - np.abs(Hn - H0) / D0) / 1e-3
+        near = np.abs(stat - thr) <= 1e-12 * abs(thr) + 1e-12 * np.abs(stat)
+        assert near.sum() <= 2
+        assert np.array_equal(sg[~near], so[~near])
+        frac = so.mean()
+        assert 0.02 < frac < 0.8, frac
+        assert st["n_implicit"] == int(so.sum())
+        ok = ~near
+    else:
+        ok = np.ones(len(q), bool)
+        assert np.array_equal(sg, so)
+    assert_state_close(zg, zo, TOL, ok)
+    assert np.abs(Hg - Ho)[ok].max() <= 1e-12 * np.abs(Ho).max()
+    # cells bit-exact except states within 1e-12 of a node
+    rel = np.minimum(np.abs(zo[:, 0, None] / g.rn[None, :] - 1).min(1),
+                     np.abs(zo[:, 1, None] - g.tn[None, :]).min(1))
+    cell_o = O.cell_index(g, zo[:, 0], zo[:, 1])
+    far = rel > 1e-11
+    assert np.array_equal(cg[far & (ao == 1)], cell_o[far & (ao == 1)])
+    if scheme in ("IMR",) or scheme.startswith("HYB"):
+        imp = so == 1
+        assert np.abs(ig[imp].astype(int) - io[imp].astype(int)).max() <= 1
+
+
+def dg_conditioning(z0, z1, H, dt, eps=1e-10):
+    """Rounding bound of the discrete-gradient step.  Its position components
+    are difference quotients of H over the position increments, so one ulp of
+    H becomes ulp(H)/|dx| in the quotient and dt times that in the momenta;
+    64 ulps cover the 16 quotients and the Picard feedback."""
+    dr = np.maximum(np.abs(z1[:, 0] - z0[:, 0]), eps)
+    dth = np.maximum(np.abs(z1[:, 1] - z0[:, 1]), eps)
+    return 64 * 2.0 ** -53 * np.maximum(np.abs(H), 1.0) * abs(dt) * (1 / dr + 1 / dth)
+
+
+@pytest.mark.parametrize("scheme", ["RK4", "HAM", "HYB2"])
+def test_neutral_push_one_step_matches_oracle(F, scheme):
+    """Geodesics (no fields), bound-orbit seeds, a = 0.9, dt = 0.5 and 1.0;
+    hybrid partner = the discrete-gradient scheme.  Explicit steps: 1e-12;
+    discrete-gradient steps: 1e-12 plus the conditioning bound of its
+    position quotients (dg_conditioning)."""
+    a = 0.9
+    ctx = _mk(F, a)
+    cand = I.orbit_candidates(1000, seed=3)
+    z, bad = O.seed_orbits(1.0, a, cand)
+    q = np.zeros(len(z))
+    H0 = O.hamiltonian(1.0, a, 0.0, z, q)[0]
+    for dt in (0.5, 1.0):
+        sch = getattr(F, "FPIC_" + scheme)
+        pr = O.push_params(a=a, dt=dt, scheme=O.RK4)
+        zr = np.ascontiguousarray(z.copy()); Hr = H0.copy()
+        O.push(pr, zr, q, H0, H0, Hr, np.ones(len(q), np.uint8))
+        stat = np.abs(Hr - H0) / H0
+        thr = float(np.median(stat))
+        p, st, (zo, Ho, ao, so, io, nc), _ = _one_step(F, ctx, None, None, z, q, sch, dt, thr=thr,
+                                                      implicit=F.FPIC_HAM, B0pot=0.0, tol=1e-15)
+        zg, Hg, ag, sg, ig, cg = to_np(p)
+        near = np.abs(stat - thr) <= 1e-10 * thr + 1e-15
+        if scheme == "HYB2":
+            assert near.sum() <= 10
+            assert np.array_equal(sg[~near], so[~near])
+            assert 0 < so.sum() < len(q)
+        else:
+            near[:] = False
+            assert np.array_equal(sg, so)
+        bound = TOL + np.where(so == 1, dg_conditioning(z, zo, H0, dt), 0.0)
+        err = (np.abs(zg - zo) / (np.abs(zo) + 1.0)).max(axis=1)
+        assert np.all(err[~near] <= bound[~near]), (err / bound).max()
+        if scheme == "HAM":
+            assert np.abs(Hg - H0).max() < 2e-14
+
+
+def test_removal_reflection_and_edges(F):
+    """Boundaries: particles falling through r_+ or crossing r_max are removed,
+    pole crossings reflect; particles outside the grid use the clamped gather;
+    dead particles are left untouched; n = 0 is a no-op."""
+    a = 0.5
+    g = I.log_grid(40, 30, 1.0, 20.0)
+    Fo = O.wald_on_grid(a, 1.0, g)
+    ctx = _mk(F, a, g)
+    z = np.array([[1.9, 0.3, 0.0, -3.0, 0.0, 0.0],
+                  [6.0, 0.002, 0.0, 0.0, -2.0, 0.0],
+                  [19.99, 1.0, 0.0, 5.0, 0.0, 0.0],
+                  [8.0, 0.01, 0.0, 0.1, 0.3, 0.2],        # between the pole and the first node
+                  [7.0, 1.0, 0.0, 0.1, 0.1, 0.1]])
+    q = np.array([0.0, 0.0, 1.0, 10.0, -10.0])
+    alive = np.array([1, 1, 1, 1, 0], np.uint8)
+    p, st, (zo, Ho, ao, so, io, nc), _ = _one_step(F, ctx, g, Fo, z, q, F.FPIC_RK4, 0.1, r_max=20.0,
+                                                  alive=alive)
+    zg, Hg, ag, sg, ig, cg = to_np(p)
+    assert ag.tolist() == [0, 1, 0, 1, 0] == ao.tolist()
+    assert_state_close(zg, zo, TOL)
+    assert np.array_equal(zg[4], z[4])
+    assert st["n_removed"] == 2 and st["n_alive_before"] == 4
+    p0 = make_particles(np.zeros((0, 6)), np.zeros(0))
+    assert F.fpic_push(ctx, p0, None, F.push_params(0.1), stats=True)["n_alive_before"] == 0
+
+
+def test_iteration_cap_is_reported(F):
+    """An implicit solve stopped by max_iter is counted (FPIC_ENOTCONVERGED),
+    and the state equals the oracle's capped iterate."""
+    a = 0.9
+    g = I.wald_grid(64, a)
+    Fo = O.wald_on_grid(a, 1.0, g)
+    ctx = _mk(F, a, g)
+    d, z, q = thermal_state(300, g, a, seed=4)
+    p, st, (zo, Ho, ao, so, io, nc), _ = _one_step(F, ctx, g, Fo, z, q, F.FPIC_IMR, 1e-3, max_iter=2)
+    assert st["n_notconv"] == nc > 0
+    assert_state_close(to_np(p)[0], zo, TOL)
+
+
+def test_invalid_arguments_raise(F):
+    ctx = _mk(F, 0.9)
+    p = make_particles(np.ones((3, 6)), np.zeros(3))
+    with pytest.raises(F.FpicError):
+        F.fpic_push(ctx, p, None, F.push_params(float("nan")))
+    with pytest.raises(F.FpicError):
+        F.fpic_push(ctx, p, None, F.push_params(0.1, scheme=9))
+    with pytest.raises(F.FpicError):
+        F.fpic_push(ctx, p, None, F.push_params(0.1, max_iter=0))
+    with pytest.raises(F.FpicError):
+        F.fpic_init_metric(1.0, 1.5)
+    with pytest.raises(F.FpicError):
+        F.fpic_cell_index(ctx, p)   # no grid
+
+
+def test_full_size_charged_workload_sampled(F):
+    """Charged Wald workload at full size (512 x 512 grid, 2^20 particles,
+    hybrid RK4 <-> IMR, dt = 1e-3) in the launch configuration the benchmark
+    times; 3000 sampled particles are recomputed by the oracle."""
+    a = 0.9
+    n = 1 << 20
+    g = I.wald_grid(512, a)
+    ctx = _mk(F, a, g)
+    Fg = [dev(np.zeros(g.size)) for _ in range(6)]
+    F.fpic_init_wald(ctx, Fg, 1.0)
+    d, q, w = I.thermal_draws(n, g, 1.02 * I.horizon(1.0, a), 49.0, 0.1, seed=2)
+    p = make_particles(np.zeros((n, 6)), q)
+    F.fpic_init_particles(ctx, p, F.FPIC_SEED_FIDO, dev(d), B0pot=1.0)
+    rng = np.random.default_rng(0)
+    idx = np.sort(rng.choice(n, 3000, replace=False))
+    z0 = p.state().cpu().numpy()[idx]
+    H0 = p.H0.cpu().numpy()[idx]; D0 = p.D0.cpu().numpy()[idx]; Hn = p.Hn.cpu().numpy()[idx]
+    thr = 5e-6
+    prm = F.push_params(1e-3, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=thr, r_max=g.rn[-1], B0pot=1.0)
+    st = F.fpic_push(ctx, p, Fg, prm, stats=True)
+    zg, Hg, ag, sg, ig, cg = to_np(p)
+    Fo = [f.cpu().numpy() for f in Fg]
+    po = O.push_params(a=a, dt=1e-3, scheme=O.HYB1, implicit_kind=O.IMR, thr=thr, r_max=g.rn[-1],
+                       B0pot=1.0, field_kind=O.FIELD_GRID)
+    zo = np.ascontiguousarray(z0.copy()); Ho = Hn.copy(); ao = np.ones(len(idx), np.uint8)
+    O.push(po, zo, q[idx], H0, D0, Ho, ao, g, Fo)
+    assert_state_close(zg[idx], zo, TOL)
+    assert st["n_alive_before"] == n
