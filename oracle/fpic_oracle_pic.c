@@ -1,0 +1,509 @@
+/*
+ * FPIC oracle, grid side: charge/current deposition (Sec. 2.3) and the FDTD
+ * leapfrog of the Maxwell equations (Sec. 2.1, Sec. 2.5).
+ *
+ * TEST INFRASTRUCTURE ONLY (see fpic_oracle.c).  Plain serial FP64 loops,
+ * compiled with -ffp-contract=off; shares nothing with the CUDA library.
+ *
+ * Grid conventions as in fpic_oracle.c: arrays [i * ld + j], integer nodes
+ * rn (Nr+1), tn (Nth+1), half nodes rh (Nr), th (Nth).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---- Appendix A metric (restated locally; this file is self-contained) --- */
+typedef struct {
+    double alpha, beta, sqrtg, g_rr, g_rp, g_tt, g_pp, gu_rr, gu_rp, gu_tt, gu_pp;
+} pm_t;
+
+static void pm_eval(double M, double a, double r, double th, pm_t *m)
+{
+    double s = sin(th), c = cos(th), s2 = s * s;
+    double rho2 = r * r + a * a * c * c;
+    double xi = 1.0 + 2.0 * M * r / rho2;
+    m->alpha = 1.0 / sqrt(xi);
+    m->beta = (xi - 1.0) / xi;
+    m->sqrtg = rho2 * sqrt(xi) * s;
+    m->g_rr = xi;
+    m->g_rp = -a * xi * s2;
+    m->g_tt = rho2;
+    m->g_pp = s2 * (rho2 + a * a * xi * s2);
+    m->gu_rr = a * a * s2 / rho2 + 1.0 / xi;
+    m->gu_rp = a / rho2;
+    m->gu_tt = 1.0 / rho2;
+    m->gu_pp = 1.0 / (rho2 * s2);
+}
+
+static double sqrtg_at(double M, double a, double r, double th)
+{
+    double s = sin(th), c = cos(th);
+    double rho2 = r * r + a * a * c * c;
+    return rho2 * sqrt(1.0 + 2.0 * M * r / rho2) * s;
+}
+
+typedef struct {
+    int Nr, Nth, ld;
+    const double *rn, *rh, *tn, *th;
+} pg_t;
+
+static int loc(const double *X, int m, double x)
+{
+    if (!(x >= X[0])) return 0;
+    if (x >= X[m - 1]) return m - 2;
+    int lo = 0, hi = m - 1;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) / 2;
+        if (x >= X[mid]) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 2.3: volume-weighted deposition.                                    */
+/* ------------------------------------------------------------------------ */
+
+/* 2D trapezoidal rule of sqrt(gamma) over [x0,x1] x [y0,y1] with 4 x 4
+ * points (Sec. 2.3: "discretising each cell into 4 x 4 points").
+ * Reading: the 4 x 4 rule is applied to each sub-rectangle. */
+static double trap16(double M, double a, double x0, double x1, double y0, double y1, int unit)
+{
+    static const double wt[4] = {0.5, 1.0, 1.0, 0.5};
+    double hx = (x1 - x0) / 3.0, hy = (y1 - y0) / 3.0, acc = 0.0;
+    for (int k = 0; k < 4; ++k)
+        for (int l = 0; l < 4; ++l) {
+            double x = x0 + k * hx, y = y0 + l * hy;
+            double f = unit ? 1.0 : sqrtg_at(M, a, x, y);
+            acc += wt[k] * wt[l] * f;
+        }
+    return acc * hx * hy;
+}
+
+/* Node weights of a particle at (r, t) on the sub-grid with node lists X, Y
+ * (Eqs. v1-v5 and the four q_(.,.) relations): the node (i+a, j+b) receives
+ * the subvolume of the opposite corner over V.  Reading: V is the sum of the
+ * four subvolumes (so the weights sum to one); the point is clamped into the
+ * sub-grid's node range.  Returns i, j and w[b][a] (a = r offset). */
+static void vol_weights(double M, double a, const double *X, int mx, const double *Y, int my,
+                        double r, double t, int unit, int *io, int *jo, double w[2][2])
+{
+    if (r < X[0]) r = X[0];
+    if (r > X[mx - 1]) r = X[mx - 1];
+    if (t < Y[0]) t = Y[0];
+    if (t > Y[my - 1]) t = Y[my - 1];
+    int i = loc(X, mx, r), j = loc(Y, my, t);
+    double r0 = X[i], r1 = X[i + 1], t0 = Y[j], t1 = Y[j + 1];
+    double V00 = trap16(M, a, r0, r, t0, t, unit);   /* V_(i,j):     [r_i, r] x [t_j, t]   */
+    double V10 = trap16(M, a, r, r1, t0, t, unit);   /* V_(i+1,j):   [r, r_i+1] x [t_j, t] */
+    double V01 = trap16(M, a, r0, r, t, t1, unit);   /* V_(i,j+1)                          */
+    double V11 = trap16(M, a, r, r1, t, t1, unit);   /* V_(i+1,j+1)                        */
+    double V = V00 + V10 + V01 + V11;
+    w[0][0] = V11 / V;   /* q_(i,j)     */
+    w[0][1] = V01 / V;   /* q_(i+1,j)   */
+    w[1][0] = V10 / V;   /* q_(i,j+1)   */
+    w[1][1] = V00 / V;   /* q_(i+1,j+1) */
+    *io = i;
+    *jo = j;
+}
+
+/* Dual-cell volume of every node of a sub-grid: 2 pi times the 4 x 4
+ * trapezoid of sqrt(gamma) over [X_{i-1/2}, X_{i+1/2}] x [Y_{j-1/2}, Y_{j+1/2}],
+ * where the half points are the neighbouring nodes' midpoints in the list
+ * (node midpoints of the other staggering), clipped to the list's ends.
+ * Reading: the paper does not normalise the deposit; densities per unit
+ * (axisymmetric) proper volume need this volume. */
+static double dual_edge(const double *X, const double *Xo, int mx, int off, int i, int lo)
+{
+    /* X: this sub-grid's nodes (mx of them); Xo: the other staggering.
+     * off = 1 if this list is the half-node list. */
+    if (lo) {
+        if (off) return Xo[i];                  /* half node i+1/2: lower edge r_i        */
+        return i == 0 ? X[0] : Xo[i - 1];       /* integer node i: lower edge r_{i-1/2}   */
+    }
+    if (off) return Xo[i + 1];
+    return i == mx - 1 ? X[mx - 1] : Xo[i];
+}
+
+/* Deposit: rho and the FIDO current j^i = sum Q v^i W / (2 pi V_dual), with
+ * Q = w (q/m) and v^j = gamma^ij u_i / Gamma (Sec. 2.3), each on its Yee
+ * sub-grid: rho, j^ph at (i, j), j^r at (i+1/2, j), j^th at (i, j+1/2).
+ * Outputs are zeroed first.  unit != 0 replaces sqrt(gamma) by 1 in the
+ * weights (tests only). */
+void or_deposit(double M, double a, int Nr, int Nth, int ld, const double *rn, const double *rh,
+                const double *tn, const double *th, int64_t n, const double *z, const double *qm,
+                const double *w, const uint8_t *alive, double *rho, double *jr, double *jt, double *jp,
+                int unit, int normalise)
+{
+    size_t sz = (size_t)(Nr + 1) * ld;
+    memset(rho, 0, sz * sizeof(double));
+    memset(jr, 0, sz * sizeof(double));
+    memset(jt, 0, sz * sizeof(double));
+    memset(jp, 0, sz * sizeof(double));
+    for (int64_t p = 0; p < n; ++p) {
+        if (!alive[p]) continue;
+        const double *s = z + 6 * p;
+        double r = s[0], t = s[1];
+        pm_t m;
+        pm_eval(M, a, r, t, &m);
+        double ur = s[3], ut = s[4], up = s[5];
+        double Ur = m.gu_rr * ur + m.gu_rp * up, Ut = m.gu_tt * ut, Up = m.gu_rp * ur + m.gu_pp * up;
+        double G = sqrt(1.0 + ur * Ur + ut * Ut + up * Up);
+        double Q = w[p] * qm[p];
+        double v[3] = {Ur / G, Ut / G, Up / G};
+        int i, j;
+        double W[2][2];
+        /* (i, j): rho and j^ph */
+        vol_weights(M, a, rn, Nr + 1, tn, Nth + 1, r, t, unit, &i, &j, W);
+        for (int b = 0; b < 2; ++b)
+            for (int c = 0; c < 2; ++c) {
+                rho[(i + c) * ld + j + b] += Q * W[b][c];
+                jp[(i + c) * ld + j + b] += Q * v[2] * W[b][c];
+            }
+        /* (i+1/2, j): j^r */
+        vol_weights(M, a, rh, Nr, tn, Nth + 1, r, t, unit, &i, &j, W);
+        for (int b = 0; b < 2; ++b)
+            for (int c = 0; c < 2; ++c) jr[(i + c) * ld + j + b] += Q * v[0] * W[b][c];
+        /* (i, j+1/2): j^th */
+        vol_weights(M, a, rn, Nr + 1, th, Nth, r, t, unit, &i, &j, W);
+        for (int b = 0; b < 2; ++b)
+            for (int c = 0; c < 2; ++c) jt[(i + c) * ld + j + b] += Q * v[1] * W[b][c];
+    }
+    if (!normalise) return;
+    /* divide by 2 pi V_dual of each node */
+    for (int k = 0; k < 4; ++k) {
+        int ro = (k == 2), to = (k == 3);     /* rho, j^ph: (0,0); j^r: (1,0); j^th: (0,1) */
+        double *f = k == 0 ? rho : k == 1 ? jp : k == 2 ? jr : jt;
+        const double *X = ro ? rh : rn, *Xo = ro ? rn : rh;
+        const double *Y = to ? th : tn, *Yo = to ? tn : th;
+        int mx = ro ? Nr : Nr + 1, my = to ? Nth : Nth + 1;
+        for (int ii = 0; ii < mx; ++ii)
+            for (int jj = 0; jj < my; ++jj) {
+                double x0 = dual_edge(X, Xo, mx, ro, ii, 1), x1 = dual_edge(X, Xo, mx, ro, ii, 0);
+                double y0 = dual_edge(Y, Yo, my, to, jj, 1), y1 = dual_edge(Y, Yo, my, to, jj, 0);
+                double V = 2.0 * M_PI * trap16(M, a, x0, x1, y0, y1, unit);
+                f[ii * ld + jj] /= V;
+            }
+    }
+}
+
+/* Dual volumes (2 pi x trapezoid) of the four sub-grids, exposed for tests:
+ * out: 4 arrays (rho/j^ph, j^ph, j^r, j^th layouts). */
+void or_dual_volumes(double M, double a, int Nr, int Nth, int ld, const double *rn, const double *rh,
+                     const double *tn, const double *th, double *vol00, double *vol10, double *vol01)
+{
+    double *outs[3] = {vol00, vol10, vol01};
+    for (int k = 0; k < 3; ++k) {
+        int ro = (k == 1), to = (k == 2);
+        const double *X = ro ? rh : rn, *Xo = ro ? rn : rh;
+        const double *Y = to ? th : tn, *Yo = to ? tn : th;
+        int mx = ro ? Nr : Nr + 1, my = to ? Nth : Nth + 1;
+        for (int ii = 0; ii < mx; ++ii)
+            for (int jj = 0; jj < my; ++jj) {
+                double x0 = dual_edge(X, Xo, mx, ro, ii, 1), x1 = dual_edge(X, Xo, mx, ro, ii, 0);
+                double y0 = dual_edge(Y, Yo, my, to, jj, 1), y1 = dual_edge(Y, Yo, my, to, jj, 0);
+                outs[k][ii * ld + jj] = 2.0 * M_PI * trap16(M, a, x0, x1, y0, y1, 0);
+            }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 2.1: FDTD leapfrog on the Yee grid, Sec. 2.5: boundaries.           */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    double M, a, dt;
+    double chi0, lam, r_abs, r_max;   /* absorbing layer, Eqs. (abs0)-(abs2) */
+} or_fdtd_params;
+
+typedef struct {
+    const or_fdtd_params *p;
+    pg_t g;
+} fctx;
+
+/* Coordinates of a point of staggering (ro, to) and index (i, j). */
+static double R(const fctx *c, int ro, int i) { return ro ? c->g.rh[i] : c->g.rn[i]; }
+static double T(const fctx *c, int to, int j) { return to ? c->g.th[j] : c->g.tn[j]; }
+static int NR(const fctx *c, int ro) { return ro ? c->g.Nr : c->g.Nr + 1; }
+static int NT(const fctx *c, int to) { return to ? c->g.Nth : c->g.Nth + 1; }
+
+/* Eq. (abs2): chi(r) = chi0 ((r - r_abs)/(r_max - r_abs))^lambda beyond r_abs.
+ * Reading: the damping term -chi F is integrated exactly over the step, i.e.
+ * the updated value is multiplied by exp(-chi dt) ("exponentially damp"). */
+static double damp(const fctx *c, double r)
+{
+    const or_fdtd_params *p = c->p;
+    if (p->chi0 <= 0.0 || r <= p->r_abs) return 1.0;
+    double x = (r - p->r_abs) / (p->r_max - p->r_abs);
+    return exp(-p->chi0 * pow(x, p->lam) * p->dt);
+}
+
+/* Metric-weighted average of F (staggering (ro,to)) at the point (ro2,to2)
+ * displaced by half a cell along one axis (Sec. 2.1, the B^r example):
+ * F_target = [(sqrtg F)_a + (sqrtg F)_b] / (2 sqrtg_target); a neighbour
+ * outside the array is replaced by the one inside (zero gradient). */
+static double avg_r(const fctx *c, const double *F, int ro, int to, int i2, int j)
+{
+    /* F has r staggering ro; the target has r staggering 1 - ro, index i2.
+     * Neighbours in F: if target is half (ro = 0): i2 and i2+1; if target is
+     * integer (ro = 1): i2-1 and i2. */
+    const fctx *cc = c;
+    int ia = ro ? i2 - 1 : i2, ib = ro ? i2 : i2 + 1;
+    int m = NR(cc, ro);
+    if (ia < 0) ia = ib;
+    if (ib > m - 1) ib = ia;
+    double t = T(cc, to, j);
+    double sa = sqrtg_at(cc->p->M, cc->p->a, R(cc, ro, ia), t);
+    double sb = sqrtg_at(cc->p->M, cc->p->a, R(cc, ro, ib), t);
+    double st = sqrtg_at(cc->p->M, cc->p->a, R(cc, 1 - ro, i2), t);
+    return (sa * F[ia * cc->g.ld + j] + sb * F[ib * cc->g.ld + j]) / (2.0 * st);
+}
+
+/* Eq. (Ei): E_i = alpha D_i + sqrtg eta_ijk beta^j B^k, beta = (beta^r,0,0):
+ *   E_r  (i+1/2, j)   = alpha (g_rr D^r + g_rp <D^ph>)
+ *   E_th (i, j+1/2)   = alpha g_tt D^th - sqrtg beta <B^ph>
+ *   E_ph (i, j)       = alpha (g_rp <D^r> + g_pp D^ph) + sqrtg beta <B^th>  */
+static void make_E(const fctx *c, const double *const D[3], const double *const B[3], double *const E[3])
+{
+    const or_fdtd_params *p = c->p;
+    int ld = c->g.ld;
+    for (int i = 0; i < c->g.Nr; ++i)
+        for (int j = 0; j <= c->g.Nth; ++j) {
+            pm_t m;
+            pm_eval(p->M, p->a, c->g.rh[i], c->g.tn[j], &m);
+            double Dp = avg_r(c, D[2], 0, 0, i, j);
+            E[0][i * ld + j] = m.alpha * (m.g_rr * D[0][i * ld + j] + m.g_rp * Dp);
+        }
+    for (int i = 0; i <= c->g.Nr; ++i)
+        for (int j = 0; j < c->g.Nth; ++j) {
+            pm_t m;
+            pm_eval(p->M, p->a, c->g.rn[i], c->g.th[j], &m);
+            double Bp = avg_r(c, B[2], 1, 1, i, j);
+            E[1][i * ld + j] = m.alpha * m.g_tt * D[1][i * ld + j] - m.sqrtg * m.beta * Bp;
+        }
+    for (int i = 0; i <= c->g.Nr; ++i)
+        for (int j = 0; j <= c->g.Nth; ++j) {
+            pm_t m;
+            pm_eval(p->M, p->a, c->g.rn[i], c->g.tn[j], &m);
+            double Dr = avg_r(c, D[0], 1, 0, i, j);
+            double Bt = avg_r(c, B[1], 1, 0, i, j);
+            E[2][i * ld + j] = m.alpha * (m.g_rp * Dr + m.g_pp * D[2][i * ld + j]) + m.sqrtg * m.beta * Bt;
+        }
+}
+
+/* H_i = alpha B_i - sqrtg eta_ijk beta^j D^k:
+ *   H_r  (i, j+1/2)     = alpha (g_rr B^r + g_rp <B^ph>)
+ *   H_th (i+1/2, j)     = alpha g_tt B^th + sqrtg beta <D^ph>
+ *   H_ph (i+1/2, j+1/2) = alpha (g_rp <B^r> + g_pp B^ph) - sqrtg beta <D^th> */
+static void make_H(const fctx *c, const double *const D[3], const double *const B[3], double *const H[3])
+{
+    const or_fdtd_params *p = c->p;
+    int ld = c->g.ld;
+    for (int i = 0; i <= c->g.Nr; ++i)
+        for (int j = 0; j < c->g.Nth; ++j) {
+            pm_t m;
+            pm_eval(p->M, p->a, c->g.rn[i], c->g.th[j], &m);
+            double Bp = avg_r(c, B[2], 1, 1, i, j);
+            H[0][i * ld + j] = m.alpha * (m.g_rr * B[0][i * ld + j] + m.g_rp * Bp);
+        }
+    for (int i = 0; i < c->g.Nr; ++i)
+        for (int j = 0; j <= c->g.Nth; ++j) {
+            pm_t m;
+            pm_eval(p->M, p->a, c->g.rh[i], c->g.tn[j], &m);
+            double Dp = avg_r(c, D[2], 0, 0, i, j);
+            H[1][i * ld + j] = m.alpha * m.g_tt * B[1][i * ld + j] + m.sqrtg * m.beta * Dp;
+        }
+    for (int i = 0; i < c->g.Nr; ++i)
+        for (int j = 0; j < c->g.Nth; ++j) {
+            pm_t m;
+            pm_eval(p->M, p->a, c->g.rh[i], c->g.th[j], &m);
+            double Br = avg_r(c, B[0], 0, 1, i, j);
+            double Dt = avg_r(c, D[1], 0, 1, i, j);
+            H[2][i * ld + j] = m.alpha * (m.g_rp * Br + m.g_pp * B[2][i * ld + j]) - m.sqrtg * m.beta * Dt;
+        }
+}
+
+/* Eq. (m4) with Eq. (abs0): B_out = (B_in - dt curl E / sqrtg) exp(-chi dt),
+ *   (curl E)^r = d_th E_ph,  (curl E)^th = -d_r E_ph,  (curl E)^ph = d_r E_th - d_th E_r,
+ * every component by its own two-point differences (no boundary rows). */
+static void update_B(const fctx *c, const double *const Bin[3], const double *const E[3], double *const Bout[3])
+{
+    const or_fdtd_params *p = c->p;
+    int ld = c->g.ld;
+    for (int i = 0; i <= c->g.Nr; ++i)              /* B^r (i, j+1/2) */
+        for (int j = 0; j < c->g.Nth; ++j) {
+            double r = c->g.rn[i], t = c->g.th[j];
+            double sg = sqrtg_at(p->M, p->a, r, t);
+            double curl = (E[2][i * ld + j + 1] - E[2][i * ld + j]) / (c->g.tn[j + 1] - c->g.tn[j]);
+            Bout[0][i * ld + j] = (Bin[0][i * ld + j] - p->dt * curl / sg) * damp(c, r);
+        }
+    for (int i = 0; i < c->g.Nr; ++i)               /* B^th (i+1/2, j) */
+        for (int j = 0; j <= c->g.Nth; ++j) {
+            double r = c->g.rh[i], t = c->g.tn[j];
+            double sg = sqrtg_at(p->M, p->a, r, t);
+            double curl = -(E[2][(i + 1) * ld + j] - E[2][i * ld + j]) / (c->g.rn[i + 1] - c->g.rn[i]);
+            Bout[1][i * ld + j] = (Bin[1][i * ld + j] - p->dt * curl / sg) * damp(c, r);
+        }
+    for (int i = 0; i < c->g.Nr; ++i)               /* B^ph (i+1/2, j+1/2) */
+        for (int j = 0; j < c->g.Nth; ++j) {
+            double r = c->g.rh[i], t = c->g.th[j];
+            double sg = sqrtg_at(p->M, p->a, r, t);
+            double dEt = (E[1][(i + 1) * ld + j] - E[1][i * ld + j]) / (c->g.rn[i + 1] - c->g.rn[i]);
+            double dEr = (E[0][i * ld + j + 1] - E[0][i * ld + j]) / (c->g.tn[j + 1] - c->g.tn[j]);
+            Bout[2][i * ld + j] = (Bin[2][i * ld + j] - p->dt * (dEt - dEr) / sg) * damp(c, r);
+        }
+}
+
+/* Source J = alpha j - rho beta (Sec. 2.1, below Eq. m4) at the J^i points;
+ * rho enters J^r through its metric-weighted average to (i+1/2, j). */
+static double Jsrc(const fctx *c, int k, int i, int j, const double *const jv[3], const double *rho)
+{
+    const or_fdtd_params *p = c->p;
+    pm_t m;
+    int ld = c->g.ld;
+    if (k == 0) {
+        pm_eval(p->M, p->a, c->g.rh[i], c->g.tn[j], &m);
+        double rb = avg_r(c, rho, 0, 0, i, j);
+        return m.alpha * jv[0][i * ld + j] - rb * m.beta;
+    }
+    if (k == 1) {
+        pm_eval(p->M, p->a, c->g.rn[i], c->g.th[j], &m);
+        return m.alpha * jv[1][i * ld + j];
+    }
+    pm_eval(p->M, p->a, c->g.rn[i], c->g.tn[j], &m);
+    return m.alpha * jv[2][i * ld + j];
+}
+
+/* Eq. (m3) with Eq. (abs1):
+ *   D_out = (D_in + dt [curl H / sqrtg - 4 pi J]) exp(-chi dt),
+ *   (curl H)^r = d_th H_ph,  (curl H)^th = -d_r H_ph,  (curl H)^ph = d_r H_th - d_th H_r,
+ * J = w0 J(j0, rho0) + w1 J(j1, rho1).  Boundaries (Sec. 2.5, reading):
+ * components without a two-sided stencil copy their neighbour (zero
+ * gradient) -- D^th, D^ph at i = 0 and i = Nr, D^r at j = 0 and j = Nth --
+ * and D^ph = 0 on the axis rows j = 0, Nth. */
+static void update_D(const fctx *c, const double *const Din[3], const double *const H[3],
+                     const double *const j0[3], const double *rho0, double w0,
+                     const double *const j1[3], const double *rho1, double w1, double *const Dout[3])
+{
+    const or_fdtd_params *p = c->p;
+    int ld = c->g.ld, Nr = c->g.Nr, Nth = c->g.Nth;
+    for (int i = 0; i < Nr; ++i)                    /* D^r (i+1/2, j) */
+        for (int j = 1; j < Nth; ++j) {
+            double r = c->g.rh[i], t = c->g.tn[j];
+            double sg = sqrtg_at(p->M, p->a, r, t);
+            double curl = (H[2][i * ld + j] - H[2][i * ld + j - 1]) / (c->g.th[j] - c->g.th[j - 1]);
+            double J = 0.0;
+            if (w0 != 0.0) J += w0 * Jsrc(c, 0, i, j, j0, rho0);
+            if (w1 != 0.0) J += w1 * Jsrc(c, 0, i, j, j1, rho1);
+            Dout[0][i * ld + j] = (Din[0][i * ld + j] + p->dt * (curl / sg - 4.0 * M_PI * J)) * damp(c, r);
+        }
+    for (int i = 1; i < Nr; ++i)                    /* D^th (i, j+1/2) */
+        for (int j = 0; j < Nth; ++j) {
+            double r = c->g.rn[i], t = c->g.th[j];
+            double sg = sqrtg_at(p->M, p->a, r, t);
+            double curl = -(H[2][i * ld + j] - H[2][(i - 1) * ld + j]) / (c->g.rh[i] - c->g.rh[i - 1]);
+            double J = 0.0;
+            if (w0 != 0.0) J += w0 * Jsrc(c, 1, i, j, j0, rho0);
+            if (w1 != 0.0) J += w1 * Jsrc(c, 1, i, j, j1, rho1);
+            Dout[1][i * ld + j] = (Din[1][i * ld + j] + p->dt * (curl / sg - 4.0 * M_PI * J)) * damp(c, r);
+        }
+    for (int i = 1; i < Nr; ++i)                    /* D^ph (i, j) */
+        for (int j = 1; j < Nth; ++j) {
+            double r = c->g.rn[i], t = c->g.tn[j];
+            double sg = sqrtg_at(p->M, p->a, r, t);
+            double dHt = (H[1][i * ld + j] - H[1][(i - 1) * ld + j]) / (c->g.rh[i] - c->g.rh[i - 1]);
+            double dHr = (H[0][i * ld + j] - H[0][i * ld + j - 1]) / (c->g.th[j] - c->g.th[j - 1]);
+            double J = 0.0;
+            if (w0 != 0.0) J += w0 * Jsrc(c, 2, i, j, j0, rho0);
+            if (w1 != 0.0) J += w1 * Jsrc(c, 2, i, j, j1, rho1);
+            Dout[2][i * ld + j] = (Din[2][i * ld + j] + p->dt * ((dHt - dHr) / sg - 4.0 * M_PI * J)) * damp(c, r);
+        }
+    /* boundaries */
+    for (int i = 0; i < Nr; ++i) {
+        Dout[0][i * ld + 0] = Dout[0][i * ld + 1];
+        Dout[0][i * ld + Nth] = Dout[0][i * ld + Nth - 1];
+    }
+    for (int j = 0; j < Nth; ++j) {
+        Dout[1][0 * ld + j] = Dout[1][1 * ld + j];
+        Dout[1][Nr * ld + j] = Dout[1][(Nr - 1) * ld + j];
+    }
+    for (int j = 1; j < Nth; ++j) {
+        Dout[2][0 * ld + j] = Dout[2][1 * ld + j];
+        Dout[2][Nr * ld + j] = Dout[2][(Nr - 1) * ld + j];
+    }
+    for (int i = 0; i <= Nr; ++i) {
+        Dout[2][i * ld + 0] = 0.0;
+        Dout[2][i * ld + Nth] = 0.0;
+    }
+}
+
+/* The ten sub-steps of Sec. 2.1, split around the particle push:
+ *   stage 1:  E <- alpha <D> + beta x B1           (<D> = (D0 + D1)/2)     [1]
+ *             Bh <- (B0 + B1)/2 - dt curl E          -> B^{n+3/2}         [2]
+ *             E <- alpha D1 + beta x Bh                                   [3]
+ *             B0 <- B1 - dt curl E                   -> B^{n+2}            [4]
+ *   (push with D1, Bh; deposit j1, rho1)                                [5,6]
+ *   stage 2:  H <- alpha Bh - beta x D1                                   [7]
+ *             Dw <- <D> + dt [curl H - 4 pi (J0 + J1)/2] -> D^{n+2}       [8]
+ *             H <- alpha B0 - beta x Dw                                   [9]
+ *             D0 <- D1 + dt [curl H - 4 pi J1]       -> D^{n+5/2}         [10]
+ * On entry B0 = B^n, B1 = B^{n+1}, D0 = D^{n+1/2}, D1 = D^{n+3/2}, (j0, rho0)
+ * at n+1 and (j1, rho1) at n+2.  After stage 2 the caller swaps B0/B1,
+ * D0/D1 and (j0,rho0)/(j1,rho1) for the next step.  E, H, Bh, Dw are work
+ * arrays (3 each).  Every array is (Nr+1) * ld. */
+void or_fdtd(const or_fdtd_params *p, int Nr, int Nth, int ld, const double *rn, const double *rh,
+             const double *tn, const double *th, int stage, double *const B0[3], double *const B1[3],
+             double *const D0[3], double *const D1[3], double *const j0[3], double *rho0,
+             double *const j1[3], double *rho1, double *const E[3], double *const H[3],
+             double *const Bh[3], double *const Dw[3])
+{
+    fctx c = {p, {Nr, Nth, ld, rn, rh, tn, th}};
+    size_t sz = (size_t)(Nr + 1) * ld;
+    double *avg[3];
+    for (int k = 0; k < 3; ++k) avg[k] = (double *)malloc(sz * sizeof(double));
+    if (stage == 1) {
+        for (int k = 0; k < 3; ++k)
+            for (size_t q = 0; q < sz; ++q) avg[k][q] = 0.5 * (D0[k][q] + D1[k][q]);
+        make_E(&c, (const double *const *)avg, (const double *const *)B1, E);
+        for (int k = 0; k < 3; ++k)
+            for (size_t q = 0; q < sz; ++q) avg[k][q] = 0.5 * (B0[k][q] + B1[k][q]);
+        update_B(&c, (const double *const *)avg, (const double *const *)E, Bh);
+        make_E(&c, (const double *const *)D1, (const double *const *)Bh, E);
+        update_B(&c, (const double *const *)B1, (const double *const *)E, B0);
+    } else {
+        make_H(&c, (const double *const *)D1, (const double *const *)Bh, H);
+        for (int k = 0; k < 3; ++k)
+            for (size_t q = 0; q < sz; ++q) avg[k][q] = 0.5 * (D0[k][q] + D1[k][q]);
+        update_D(&c, (const double *const *)avg, (const double *const *)H, (const double *const *)j0, rho0,
+                 0.5, (const double *const *)j1, rho1, 0.5, Dw);
+        make_H(&c, (const double *const *)Dw, (const double *const *)B0, H);
+        update_D(&c, (const double *const *)D1, (const double *const *)H, (const double *const *)j0, rho0,
+                 0.0, (const double *const *)j1, rho1, 1.0, D0);
+    }
+    for (int k = 0; k < 3; ++k) free(avg[k]);
+}
+
+/* Discrete divergences (tests): div B at cell centres (i+1/2, j+1/2) and
+ * div D at interior integer nodes, both as sqrtg-weighted two-point
+ * differences (the Yee forms of Eqs. m1-m2), times sqrtg at the point. */
+void or_div(double M, double a, int Nr, int Nth, int ld, const double *rn, const double *rh,
+            const double *tn, const double *th, const double *const B[3], const double *const D[3],
+            double *divB, double *divD)
+{
+    for (int i = 0; i < Nr; ++i)
+        for (int j = 0; j < Nth; ++j) {
+            double fr1 = sqrtg_at(M, a, rn[i + 1], th[j]) * B[0][(i + 1) * ld + j];
+            double fr0 = sqrtg_at(M, a, rn[i], th[j]) * B[0][i * ld + j];
+            double ft1 = sqrtg_at(M, a, rh[i], tn[j + 1]) * B[1][i * ld + j + 1];
+            double ft0 = sqrtg_at(M, a, rh[i], tn[j]) * B[1][i * ld + j];
+            divB[i * ld + j] = (fr1 - fr0) / (rn[i + 1] - rn[i]) + (ft1 - ft0) / (tn[j + 1] - tn[j]);
+        }
+    for (int i = 1; i < Nr; ++i)
+        for (int j = 1; j < Nth; ++j) {
+            double fr1 = sqrtg_at(M, a, rh[i], tn[j]) * D[0][i * ld + j];
+            double fr0 = sqrtg_at(M, a, rh[i - 1], tn[j]) * D[0][(i - 1) * ld + j];
+            double ft1 = sqrtg_at(M, a, rn[i], th[j]) * D[1][i * ld + j];
+            double ft0 = sqrtg_at(M, a, rn[i], th[j - 1]) * D[1][i * ld + j - 1];
+            divD[i * ld + j] = (fr1 - fr0) / (rh[i] - rh[i - 1]) + (ft1 - ft0) / (th[j] - th[j - 1]);
+        }
+}

@@ -1,0 +1,182 @@
+"""Pins of the oracle's deposition and FDTD leapfrog (no GPU)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import pic as P
+from paper_2602_07452_gb300 import inputs as I
+
+
+def _particles(g, n, seed, a=0.9):
+    d, q, w = I.thermal_draws(n, g, g.rn[0], g.rn[-1], 0.3, seed=seed)
+    z = O.seed_fido(1.0, a, d)
+    w = np.random.default_rng(seed).uniform(0.5, 2.0, n)
+    return z, q, w
+
+
+def test_deposit_weights_partition_unity():
+    """Sec. 2.3: the four node shares of a particle are the four subvolumes
+    over their sum, so each sub-grid receives exactly the particle's charge
+    Q = w q/m (and Q v^i for the currents)."""
+    a = 0.9
+    g = I.log_grid(12, 10, 1.5, 20.0)
+    z, q, w = _particles(g, 300, 1, a)
+    rho, jr, jt, jp = P.deposit(1.0, a, g, z, q, w, normalise=False)
+    Q = (q * w).sum()
+    assert abs(rho.sum() - Q) < 1e-11 * np.abs(q * w).sum()
+    m = O.metric(1.0, a, z[:, 0], z[:, 1])
+    Ur = m[:, 8] * z[:, 3] + m[:, 9] * z[:, 5]
+    Ut = m[:, 10] * z[:, 4]
+    Up = m[:, 9] * z[:, 3] + m[:, 11] * z[:, 5]
+    G = np.sqrt(1 + z[:, 3] * Ur + z[:, 4] * Ut + z[:, 5] * Up)
+    for arr, v in ((jr, Ur / G), (jt, Ut / G), (jp, Up / G)):
+        tot = (q * w * v).sum()
+        assert abs(arr.sum() - tot) < 1e-11 * np.abs(q * w * v).sum()
+
+
+def test_deposit_unit_density_is_bilinear():
+    """With sqrt(gamma) replaced by 1 the subvolumes are areas and the
+    opposite-volume weights reduce to bilinear cloud-in-cell weights."""
+    a = 0.9
+    g = I.log_grid(6, 5, 2.0, 9.0)
+    rng = np.random.default_rng(2)
+    for _ in range(20):
+        r = rng.uniform(g.rn[0], g.rn[-1]); t = rng.uniform(g.tn[0], g.tn[-1])
+        z = np.array([[r, t, 0, 0, 0, 0]])
+        rho, _, _, _ = P.deposit(1.0, a, g, z, [1.0], [1.0], unit=True, normalise=False)
+        i = np.searchsorted(g.rn, r, side="right") - 1
+        j = np.searchsorted(g.tn, t, side="right") - 1
+        wr = (r - g.rn[i]) / (g.rn[i + 1] - g.rn[i]); wt = (t - g.tn[j]) / (g.tn[j + 1] - g.tn[j])
+        exp = np.zeros(g.size)
+        exp[i * g.ld + j] = (1 - wr) * (1 - wt); exp[(i + 1) * g.ld + j] = wr * (1 - wt)
+        exp[i * g.ld + j + 1] = (1 - wr) * wt; exp[(i + 1) * g.ld + j + 1] = wr * wt
+        assert np.abs(rho - exp).max() < 1e-14
+
+
+def test_deposit_particle_on_node():
+    """A particle on a node puts its whole charge on that node."""
+    a = 0.5
+    g = I.log_grid(6, 5, 2.0, 9.0)
+    z = np.array([[g.rn[3], g.tn[2], 0, 0.1, 0.2, 0.3]])
+    rho, _, _, _ = P.deposit(1.0, a, g, z, [2.0], [1.5], normalise=False)
+    assert abs(rho[3 * g.ld + 2] - 3.0) < 1e-15 and abs(rho.sum() - 3.0) < 1e-15
+
+
+def test_deposit_normalisation_conserves_charge():
+    """Normalised densities times the 2 pi dual volumes give back the charge,
+    and the dual cells tile the domain (their volumes sum to the domain's)."""
+    a = 0.9
+    g = I.log_grid(16, 12, 1.6, 25.0)
+    z, q, w = _particles(g, 500, 3, a)
+    rho, jr, jt, jp = P.deposit(1.0, a, g, z, q, w)
+    v00, v10, v01 = P.dual_volumes(1.0, a, g)
+    assert abs((rho * v00).sum() - (q * w).sum()) < 1e-11 * np.abs(q * w).sum()
+    tot = [v00[:].reshape(g.Nr + 1, g.ld)[:, :g.Nth + 1].sum(),
+           v10.reshape(g.Nr + 1, g.ld)[:g.Nr, :g.Nth + 1].sum(),
+           v01.reshape(g.Nr + 1, g.ld)[:, :g.Nth].sum()]
+    assert max(tot) - min(tot) < 1e-3 * max(tot)
+
+
+def _rand_fields(g, seed):
+    rng = np.random.default_rng(seed)
+    s = P.FdtdState(g)
+    for arrs in (s.B0, s.B1, s.D0, s.D1):
+        for x in arrs:
+            x[:] = rng.normal(size=g.size)
+    s.B0 = [x.copy() for x in s.B1]
+    return s
+
+
+@pytest.mark.parametrize("a", [0.0, 0.9])
+def test_fdtd_vacuum_preserves_divergences(a):
+    """Sec. 2.1: on the Yee grid the curl updates leave div B unchanged to
+    round-off (and div D in vacuum), for arbitrary fields, away from the
+    absorbing layer."""
+    g = I.log_grid(24, 20, 1.9, 30.0)
+    s = _rand_fields(g, 5)
+    p = P.FdtdParams(1.0, a, 0.002, 1e4, 5.0, 0.9 * g.rn[-1], g.rn[-1])
+    dB0, dD0 = P.div(1.0, a, g, s.B1, s.D1)
+    for _ in range(3):
+        P.fdtd(p, s, 1)
+        P.fdtd(p, s, 2)
+        s.swap()
+    dB1, dD1 = P.div(1.0, a, g, s.B1, s.D1)
+    rm = g.rh < 0.9 * g.rn[-1] * 0.999
+    ii = np.arange(g.Nr)[rm[:g.Nr]]
+    ii = ii[ii < g.Nr - 2]
+    sel = np.zeros((g.Nr + 1, g.ld), bool)
+    sel[ii, :g.Nth] = True
+    scale = np.abs(dB0).max()
+    assert np.abs((dB1 - dB0).reshape(g.Nr + 1, g.ld)[sel]).max() < 1e-12 * scale
+    seld = np.zeros((g.Nr + 1, g.ld), bool)
+    seld[2:ii.max(), 2:g.Nth - 1] = True
+    scale = np.abs(dD0).max()
+    assert np.abs((dD1 - dD0).reshape(g.Nr + 1, g.ld)[seld]).max() < 1e-12 * scale
+
+
+def test_fdtd_gauss_law_with_sources():
+    """Ampere's law with sources (sub-step 10): the node divergence of D
+    changes by exactly -4 pi dt times the Yee divergence of sqrt(gamma) J."""
+    a = 0.9
+    g = I.log_grid(20, 16, 1.9, 30.0)
+    s = _rand_fields(g, 6)
+    rng = np.random.default_rng(7)
+    for x in s.j1 + [s.rho1]:
+        x[:] = rng.normal(size=g.size)
+    for x in s.j0 + [s.rho0]:
+        x[:] = 0.0
+    p = P.FdtdParams(1.0, a, 0.003, 0.0, 5.0, g.rn[-1], g.rn[-1])
+    P.fdtd(p, s, 1)
+    D15 = [x.copy() for x in s.D1]
+    P.fdtd(p, s, 2)      # D0 <- D^{n+5/2} = D1 + dt (curl H - 4 pi J1)
+    _, dA = P.div(1.0, a, g, s.B0, D15)
+    _, dB = P.div(1.0, a, g, s.B0, s.D0)
+    # J from the same definition as the oracle (alpha j - rho beta) at the Yee points
+    m_r = O.metric(1.0, a, np.repeat(g.rh, g.Nth + 1), np.tile(g.tn, g.Nr))
+    Jr = np.zeros(g.size); Jt = np.zeros(g.size)
+    R = s.rho1.reshape(g.Nr + 1, g.ld)
+    for i in range(g.Nr):
+        for j in range(g.Nth + 1):
+            mm = m_r[i * (g.Nth + 1) + j]
+            sa = O.metric(1.0, a, [g.rn[i]], [g.tn[j]])[0, 12]
+            sb = O.metric(1.0, a, [g.rn[i + 1]], [g.tn[j]])[0, 12]
+            rb = (sa * R[i, j] + sb * R[i + 1, j]) / (2 * mm[12])
+            Jr[i * g.ld + j] = mm[2] * s.j1[0][i * g.ld + j] - rb * mm[3]
+    mt = O.metric(1.0, a, np.repeat(g.rn, g.Nth), np.tile(g.th, g.Nr + 1))
+    for i in range(g.Nr + 1):
+        for j in range(g.Nth):
+            Jt[i * g.ld + j] = mt[i * g.Nth + j, 2] * s.j1[1][i * g.ld + j]
+    _, dJ = P.div(1.0, a, g, s.B0, [Jr, Jt, np.zeros(g.size)])
+    sel = np.zeros((g.Nr + 1, g.ld), bool)
+    sel[2:g.Nr - 1, 2:g.Nth - 1] = True
+    lhs = (dB - dA).reshape(g.Nr + 1, g.ld)[sel]
+    rhs = (-4 * math.pi * p.dt * dJ).reshape(g.Nr + 1, g.ld)[sel]
+    assert np.abs(lhs - rhs).max() < 1e-10 * np.abs(rhs).max()
+
+
+def test_fdtd_static_wald_schwarzschild_stays_static():
+    """Sec. 3.2 / App. B.1: the a = 0 Wald field (E_i = 0, D = -beta x B /
+    alpha) is a static vacuum solution; the leapfrog keeps it static up to
+    the truncation error of the grid, which falls with resolution."""
+    a = 0.0
+    errs = []
+    for N in (32, 64):
+        g = I.log_grid(N, N, 2.2, 12.0)
+        F = O.wald_on_grid(a, 1.0, g)
+        s = P.FdtdState(g)
+        for k in range(3):
+            s.D0[k][:] = F[k]; s.D1[k][:] = F[k]
+            s.B0[k][:] = F[3 + k]; s.B1[k][:] = F[3 + k]
+        p = P.FdtdParams(1.0, a, 0.2 * (g.rn[1] - g.rn[0]), 0.0, 5.0, 1e9, 2e9)
+        nst = int(round(0.5 / p.dt))
+        for _ in range(nst):
+            P.fdtd(p, s, 1); P.fdtd(p, s, 2); s.swap()
+        # a region the boundary perturbations cannot reach in t = 0.5
+        ri = (g.rn >= 4.0) & (g.rn <= 8.0)
+        tj = (g.th >= 0.5) & (g.th <= math.pi - 0.5)
+        Br = s.B1[0].reshape(g.Nr + 1, g.ld)[ri][:, :g.Nth][:, tj]
+        Br0 = F[3].reshape(g.Nr + 1, g.ld)[ri][:, :g.Nth][:, tj]
+        errs.append(np.abs(Br - Br0).max() / np.abs(Br0).max())
+    assert errs[0] < 2e-2 and errs[1] < 0.6 * errs[0], errs
