@@ -43,7 +43,7 @@ NOMINAL_FP64_GFLOPS = 1250.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="fpic", choices=["fpic", "reference"])
     ap.add_argument("--n", type=int, default=1 << 20)
@@ -183,6 +183,9 @@ def run_gpu(args, ws, rank, local):
     torch.cuda.set_device(device)
     F, g, ctx, fields, p = setup(args.n, rank, device)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    for e in ev:            # torch creates the CUDA event on its first record
+        e.record()
+    torch.cuda.synchronize()
     prm = F.push_params(DT, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=HYB1_THR, r_max=float(g.rn[-1]),
                         B0pot=B0, events=ev[1:5])
     for _ in range(args.warmup):
