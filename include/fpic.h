@@ -175,6 +175,34 @@ int fpic_push(fpic_ctx *ctx, fpic_particles *p, const double *const fields[6],
 int fpic_push_host(fpic_ctx *ctx, fpic_particles *host_p, const double *const fields[6],
                    const fpic_push_params *prm, fpic_push_stats *stats, void *stream);
 
+/* Fixed capacity of fpic_push_noalloc's scratch, in particles. */
+#define FPIC_NOALLOC_MAX_PARTICLES 65536
+
+/* Allocation-free variant of fpic_push for geodesic (field-free) pushes.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory -- code whose device memory belongs to a
+ * host framework or custom allocator that forbids direct cudaMalloc,
+ * real-time loops where an allocation (or the synchronisation of a
+ * cudaFree) is not allowed, plugin builds without an allocator.  It needs
+ * no context (M, a given directly), calls no cudaMalloc, cudaFree or other
+ * allocating routine, and keeps its scratch (implicit guesses, queue of
+ * rejected particles, counters) in one file-scope device array of fixed
+ * size, FPIC_NOALLOC_MAX_PARTICLES * 52 + 256 bytes (about 3.4 MB), that
+ * every device which loads the library holds until the process exits.
+ *   p, prm, stats, stream : as fpic_push (no fields; prm->guess must be
+ *     NULL).  Neutral and charged particles move on geodesics of the Kerr
+ *     metric (M, a).
+ *   Errors: FPIC_EINVAL if p->n > FPIC_NOALLOC_MAX_PARTICLES (nothing is
+ *     launched) or for the argument errors of fpic_push; FPIC_ECUDA.
+ * The first call on each device looks up the device address of the
+ * scratch array (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  Every call on a device shares the
+ * one array and the counters are cleared at the start of each call, so
+ * calls whose work overlaps on the GPU (other streams, other threads)
+ * race: serialise them on one stream.  Results equal fpic_push's. */
+int fpic_push_noalloc(double M, double a, fpic_particles *p, const fpic_push_params *prm,
+                      fpic_push_stats *stats, void *stream);
+
 /* Measurement helper (not part of the method): sustained FP64 fused
  * multiply-add rate of the current device, in GFLOP/s (2 flops per FMA),
  * from a kernel of independent FMA chains on every SM, timed with CUDA

@@ -556,3 +556,135 @@ extern "C" int fpic_push_host(fpic_ctx* c, fpic_particles* hp, const double* con
     FPIC_CUDA(cudaStreamSynchronize(s));
     return rc;
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free geodesic push.
+//
+// For callers that must not allocate device memory themselves or through
+// this library: code that runs where the process's device memory is owned
+// by someone else (a host framework or a custom allocator that forbids
+// direct cudaMalloc), real-time loops in which an allocation (and the
+// device synchronisation a cudaFree implies) is not allowed, and embedded
+// or plugin builds linked without an allocator.  The scratch that
+// fpic_push keeps in the context (implicit-solver guesses, the queue of
+// rejected particles, counters) lives here in one file-scope device array
+// of fixed size instead, so no context and no allocation are needed.
+// ---------------------------------------------------------------------------
+
+namespace fpic {
+
+constexpr long long kNoAllocMax = FPIC_NOALLOC_MAX_PARTICLES;
+constexpr size_t kNoAllocCountersBytes = 256;   // CNT_N counters, padded for alignment
+constexpr size_t kNoAllocBytes = kNoAllocCountersBytes + (size_t)kNoAllocMax * (6 * sizeof(double) + sizeof(uint32_t));
+
+// Shared by every call on a device and held until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Per-device set-up cache: the device address of g_noalloc_scratch (the host
+// symbol is only a stand-in and must never be passed to a kernel) and the
+// SM count.  Filled by the first call on each device.
+constexpr int kNoAllocMaxDevices = 64;
+static void* g_noalloc_dev_ptr[kNoAllocMaxDevices];
+static int g_noalloc_sms[kNoAllocMaxDevices];
+
+static int noalloc_setup(int dev)
+{
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return set_error(FPIC_EINVAL, "fpic_push_noalloc: device id %d out of range", dev);
+    if (g_noalloc_dev_ptr[dev]) return 0;
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr)
+        return set_error(FPIC_ECUDA, "fpic_push_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    int sms = 0;
+    FPIC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    g_noalloc_sms[dev] = sms;
+    g_noalloc_dev_ptr[dev] = ptr;
+    return 0;
+}
+
+}  // namespace fpic
+
+extern "C" int fpic_push_noalloc(double M, double a, fpic_particles* p, const fpic_push_params* prm,
+                                 fpic_push_stats* stats, void* stream)
+{
+    if (!p || !prm) return set_error(FPIC_EINVAL, "fpic_push_noalloc: NULL particles/params");
+    if (!(M > 0.0) || !std::isfinite(M) || !(fabs(a) <= M))
+        return set_error(FPIC_EINVAL, "fpic_push_noalloc: need M > 0 and |a| <= M");
+    if (p->n < 0) return set_error(FPIC_EINVAL, "fpic_push_noalloc: n < 0");
+    if (p->n > kNoAllocMax)
+        return set_error(FPIC_EINVAL, "fpic_push_noalloc: n = %lld exceeds the fixed scratch capacity of %lld particles",
+                         (long long)p->n, (long long)kNoAllocMax);
+    if (!particles_ok(p, true)) return set_error(FPIC_EINVAL, "fpic_push_noalloc: a particle array is NULL");
+    if (!(std::isfinite(prm->dt)) || prm->dt == 0.0) return set_error(FPIC_EINVAL, "fpic_push_noalloc: dt must be finite and nonzero");
+    if (prm->scheme < FPIC_RK4 || prm->scheme > FPIC_HYB2) return set_error(FPIC_EINVAL, "fpic_push_noalloc: unknown scheme %d", prm->scheme);
+    if (prm->scheme >= FPIC_HYB1 && prm->implicit != FPIC_IMR && prm->implicit != FPIC_HAM)
+        return set_error(FPIC_EINVAL, "fpic_push_noalloc: implicit partner must be FPIC_IMR or FPIC_HAM");
+    if (prm->max_iter < 1 || prm->max_iter > 255) return set_error(FPIC_EINVAL, "fpic_push_noalloc: max_iter must be in [1, 255]");
+    if (!(prm->tol >= 0.0)) return set_error(FPIC_EINVAL, "fpic_push_noalloc: tol must be >= 0");
+    if (prm->guess) return set_error(FPIC_EINVAL, "fpic_push_noalloc: learned guesses are not supported here");
+    int dev = 0;
+    FPIC_CUDA(cudaGetDevice(&dev));
+    int rc = noalloc_setup(dev);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long n = p->n;
+    unsigned char* base = (unsigned char*)g_noalloc_dev_ptr[dev];
+    PushK k{};
+    k.bh = BH{M, a, a * a, 2.0 * M};
+    k.has_grid = 0;
+    k.has_fields = 0;
+    k.dt = prm->dt;
+    k.thr = prm->thr;
+    k.tol = prm->tol;
+    k.dg_eps = prm->dg_eps;
+    k.B0pot = prm->B0pot;
+    k.r_h = M + sqrt(M * M - a * a);
+    k.r_max = prm->r_max;
+    k.scheme = prm->scheme;
+    k.max_iter = prm->max_iter;
+    k.n = n;
+    k.P = PartDev{p->r, p->th, p->ph, p->ur, p->uth, p->uph, p->qm, p->H0, p->D0, p->Hn,
+                  p->alive, p->scheme, p->iters, p->cell};
+    k.cnt = (long long*)base;
+    k.guess = (double*)(base + kNoAllocCountersBytes);
+    k.queue = (uint32_t*)(base + kNoAllocCountersBytes + (size_t)n * 6 * sizeof(double));
+    k.learned = nullptr;
+    // the counters (queue length and head among them) must start at zero
+    FPIC_CUDA(cudaMemsetAsync(k.cnt, 0, CNT_N * sizeof(long long), s));
+    if (n == 0) {
+        if (stats) *stats = fpic_push_stats{};
+        return FPIC_OK;
+    }
+    const int TB = 128;
+    const unsigned nb = (unsigned)((n + TB - 1) / TB);
+    const unsigned persist = (unsigned)g_noalloc_sms[dev] * 8u;
+    cudaEvent_t* ev = prm->events ? (cudaEvent_t*)prm->events : nullptr;
+    if (stats) k_count_alive<<<persist, 256, 0, s>>>(k.P, n, k.cnt);
+    if (ev) FPIC_CUDA(cudaEventRecord(ev[0], s));
+    if (prm->scheme == FPIC_RK4) k_explicit<0><<<nb, TB, 0, s>>>(k);
+    else if (prm->scheme >= FPIC_HYB1) k_explicit<1><<<nb, TB, 0, s>>>(k);
+    if (ev) {
+        FPIC_CUDA(cudaEventRecord(ev[1], s));
+        FPIC_CUDA(cudaEventRecord(ev[2], s));
+    }
+    if (prm->scheme == FPIC_IMR) k_imr<<<persist, TB, 0, s>>>(k, 1);
+    else if (prm->scheme == FPIC_HAM) k_dg<<<nb, TB, 0, s>>>(k, 1);
+    else if (prm->scheme >= FPIC_HYB1 && prm->implicit == FPIC_IMR) k_imr<<<persist, TB, 0, s>>>(k, 0);
+    else if (prm->scheme >= FPIC_HYB1) k_dg<<<nb, TB, 0, s>>>(k, 0);
+    if (ev) FPIC_CUDA(cudaEventRecord(ev[3], s));
+    FPIC_CUDA(cudaGetLastError());
+    if (stats) {
+        long long h[CNT_N];
+        FPIC_CUDA(cudaMemcpyAsync(h, k.cnt, sizeof h, cudaMemcpyDeviceToHost, s));
+        FPIC_CUDA(cudaStreamSynchronize(s));
+        const bool explicit_pass = prm->scheme == FPIC_RK4 || prm->scheme >= FPIC_HYB1;
+        stats->n_alive_before = h[CNT_ALIVE];
+        stats->n_implicit = prm->scheme == FPIC_RK4 ? 0 : (prm->scheme >= FPIC_HYB1 ? h[CNT_QUEUE] : h[CNT_ALIVE]);
+        stats->n_iter_total = h[CNT_ITERS];
+        stats->n_notconv = h[CNT_NOTCONV];
+        stats->n_removed = h[CNT_REMOVED];
+        stats->n_rhs_evals = h[CNT_EVALS] + (explicit_pass ? 4 * h[CNT_ALIVE] : 0);
+        if (h[CNT_NOTCONV] > 0) return FPIC_ENOTCONVERGED;
+    }
+    return FPIC_OK;
+}

@@ -72,6 +72,8 @@ _SIGS = {
     "fpic_push_host": (C.c_int, [C.c_void_p, C.POINTER(fpic_particles), C.POINTER(_D),
                                  C.POINTER(fpic_push_params), C.POINTER(fpic_push_stats), C.c_void_p]),
     "fpic_probe_fp64": (C.c_int, [C.POINTER(C.c_double), C.c_int]),
+    "fpic_push_noalloc": (C.c_int, [C.c_double, C.c_double, C.POINTER(fpic_particles),
+                                    C.POINTER(fpic_push_params), C.POINTER(fpic_push_stats), C.c_void_p]),
     "fpic_hamiltonian": (C.c_int, [C.c_void_p, C.POINTER(fpic_particles), C.c_double, _D, _D, C.c_void_p]),
     "fpic_cell_index": (C.c_int, [C.c_void_p, C.POINTER(fpic_particles), C.c_void_p]),
 }
@@ -282,3 +284,17 @@ def fpic_probe_fp64(reps: int = 2000) -> float:
     out = C.c_double()
     _check(lib().fpic_probe_fp64(C.byref(out), reps))
     return out.value
+
+
+FPIC_NOALLOC_MAX_PARTICLES = 65536
+
+
+def fpic_push_noalloc(M: float, a: float, p: Particles, prm: fpic_push_params, stats: bool = False,
+                      stream=None):
+    """Allocation-free geodesic push (no context; fixed scratch capacity)."""
+    s = p.struct()
+    st = fpic_push_stats() if stats else None
+    rc = lib().fpic_push_noalloc(M, a, C.byref(s), C.byref(prm), C.byref(st) if st is not None else None,
+                                 _stream(stream))
+    _check(rc)
+    return st.as_dict() if st is not None else None

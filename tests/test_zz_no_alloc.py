@@ -1,0 +1,59 @@
+"""The allocation-free push (fpic_push_noalloc) against the regular
+fpic_push, through the C ABI, on two calls in a row.
+
+fpic_push_noalloc serves callers that may not allocate device memory (their
+device memory is owned by a host framework or allocator, or allocation is
+forbidden in their loop); it keeps its scratch in a fixed file-scope device
+array instead of the context.  This file is collected last on purpose."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2602_07452_gb300 import inputs as I
+from helpers import cuda_or_skip, fpic, make_particles, to_np
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+def _pair(n, a, seed):
+    cand = I.orbit_candidates(n, seed=seed)
+    z, bad = O.seed_orbits(1.0, a, cand)
+    assert bad == 0
+    q = np.zeros(n)
+    H0 = O.hamiltonian(1.0, a, 0.0, z, q)[0]
+    mk = lambda: make_particles(z, q, H0, H0, H0.copy())
+    return mk(), mk()
+
+
+@pytest.mark.parametrize("scheme,implicit", [("HYB2", "IMR"), ("HYB1", "HAM"), ("RK4", "IMR")])
+def test_noalloc_matches_regular_push_two_calls(scheme, implicit):
+    cuda_or_skip()
+    F = fpic()
+    a, dt, n = 0.9, 0.5, 3001
+    p_ref, p_na = _pair(n, a, seed=21)
+    ctx = F.fpic_init_metric(1.0, a)
+    thr = 1e-10 if scheme == "HYB2" else 1e-11
+    prm = F.push_params(dt, scheme=getattr(F, "FPIC_" + scheme), implicit=getattr(F, "FPIC_" + implicit),
+                        thr=thr, tol=1e-14)
+    for _ in range(2):                     # two calls in a row
+        st_ref = F.fpic_push(ctx, p_ref, None, prm, stats=True)
+        st_na = F.fpic_push_noalloc(1.0, a, p_na, prm, stats=True)
+        zr, Hr, ar, sr, ir, _ = to_np(p_ref)
+        zn, Hn, an, sn, iN, _ = to_np(p_na)
+        err = (np.abs(zn - zr) / (np.abs(zr) + 1.0)).max()
+        assert err <= TOL, err
+        assert np.abs(Hn - Hr).max() <= TOL * np.abs(Hr).max()
+        assert np.array_equal(an, ar) and np.array_equal(sn, sr) and np.array_equal(iN, ir)
+        assert st_na == st_ref
+    if scheme != "RK4":
+        assert 0 < st_ref["n_implicit"] < n
+
+
+def test_noalloc_rejects_more_than_capacity():
+    cuda_or_skip()
+    F = fpic()
+    n = F.FPIC_NOALLOC_MAX_PARTICLES + 1
+    p = make_particles(np.tile([[8.0, 1.0, 0.0, 0.0, 0.0, 3.0]], (n, 1)), np.zeros(n))
+    with pytest.raises(F.FpicError, match="capacity"):
+        F.fpic_push_noalloc(1.0, 0.9, p, F.push_params(0.1))
