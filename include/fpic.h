@@ -221,6 +221,58 @@ int fpic_hamiltonian(fpic_ctx *ctx, const fpic_particles *p, double B0pot, doubl
  * tables.  Errors: FPIC_EINVAL. */
 int fpic_cell_index(fpic_ctx *ctx, fpic_particles *p, void *stream);
 
+/* Field storage of the FDTD leapfrog (Sec. 2.1), all device arrays in the
+ * grid layout, caller-owned:
+ *   B0, B1 : B^n and B^{n+1} (3 components each: r, th, ph)
+ *   D0, D1 : D^{n+1/2} and D^{n+3/2}
+ *   j0, rho0 / j1, rho1 : FIDO current j^i and charge density at n+1 / n+2
+ *                          (the deposit of the previous / current step)
+ *   E, H, Bh, Dw : work arrays; after stage 1 Bh holds B^{n+3/2} (the field
+ *                  the push uses with D1), after stage 2 Dw holds D^{n+2}. */
+typedef struct {
+    double *B0[3], *B1[3], *D0[3], *D1[3];
+    double *j0[3], *rho0, *j1[3], *rho1;
+    double *E[3], *H[3], *Bh[3], *Dw[3];
+} fpic_fields;
+
+/* FDTD parameters: time step dt and the absorbing layer of Eqs. (abs0)-(abs2):
+ * chi(r) = chi0 ((r - r_abs)/(r_max - r_abs))^lambda for r > r_abs (chi0 = 0
+ * switches it off); the damping is applied as a factor exp(-chi dt). */
+typedef struct {
+    double dt, chi0, lambda, r_abs, r_max;
+} fpic_fdtd_params;
+
+/* Stable sort of the particles by cell index ir * Nth + ith (removed
+ * particles last), permuting every array of *p in place (Sec. 2.3 needs the
+ * particles of a cell together; the order inside a cell is the previous
+ * order).  Also writes p->cell.  Uses library scratch.
+ * Errors: FPIC_EINVAL (no grid, NULL arrays), FPIC_ENOMEM, FPIC_ECUDA. */
+int fpic_sort(fpic_ctx *ctx, fpic_particles *p, void *stream);
+
+/* Charge and current deposition (Sec. 2.3): each alive particle of charge
+ * Q = w (q/m) and FIDO velocity v^i = gamma^ij u_j / Gamma is shared between
+ * the four nodes of its cell on each Yee sub-grid in proportion to the
+ * opposite subvolume (4 x 4-point trapezoid of sqrt(gamma) on each
+ * sub-rectangle), summed per node in a fixed order (deterministic, no
+ * floating-point atomics) and divided by 2 pi times the node's dual-cell
+ * volume.  Outputs (device, grid layout, overwritten): rho and j^ph at
+ * (i, j), j^r at (i+1/2, j), j^th at (i, j+1/2).  Sorts the particles first
+ * (fpic_sort).  Errors: FPIC_EINVAL, FPIC_ENOMEM, FPIC_ECUDA. */
+int fpic_deposit(fpic_ctx *ctx, fpic_particles *p, double *rho, double *jr, double *jth, double *jph,
+                 void *stream);
+
+/* One half of the FDTD leapfrog step of Sec. 2.1 (Eqs. m3, m4, Ei, and the
+ * absorbing layer and boundaries of Sec. 2.5):
+ *   stage 1 (sub-steps 1-4): E^{n+1} -> B^{n+3/2} (into Bh) -> E^{n+3/2} ->
+ *            B^{n+2} (into B0);
+ *   stage 2 (sub-steps 7-10, after the push and the deposit of j1, rho1):
+ *            H^{n+3/2} -> D^{n+2} (into Dw, with <J>^{n+3/2}) -> H^{n+2} ->
+ *            D^{n+5/2} (into D0, with J^{n+2}),
+ * with J = alpha j - rho beta.  After stage 2 the caller swaps B0/B1, D0/D1
+ * and (j0, rho0)/(j1, rho1).  Errors: FPIC_EINVAL (no grid, stage not 1 or
+ * 2, NULL array, dt not finite). */
+int fpic_fdtd_step(fpic_ctx *ctx, fpic_fields *f, const fpic_fdtd_params *prm, int stage, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

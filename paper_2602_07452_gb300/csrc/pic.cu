@@ -1,12 +1,854 @@
-// Grid-side kernels of the PIC step: metric tables at the Yee points.
+// Grid side of the PIC step: metric tables at the Yee points (Sec. 2.1),
+// the stable sort of particles by cell, the deterministic volume-weighted
+// deposit (Sec. 2.3) and the FDTD leapfrog (Sec. 2.1, 2.5).
+//
+// Deposit pipeline (no floating-point atomics, bitwise reproducible):
+//   k_dep_particle  one thread per particle (in cell order): the 4x4
+//                   trapezoidal subvolumes of sqrt(gamma) on each sub-grid
+//                   -> 16 node shares (rho, j^ph, j^r, j^th);
+//   k_dep_cell      one warp per cell: fixed-order tree sum of its particles'
+//                   shares into 20 stencil slots;
+//   k_dep_node      one thread per node: fixed-order sum of the slots of the
+//                   (up to six) cells touching it, / (2 pi V_dual).
+// The FDTD is HBM-bound; its metric factors come from tables built once.
+#include <math.h>
+
 #include "fpic_internal.h"
 
 namespace fpic {
 
+// ---------------------------------------------------------------------------
+// Metric tables
+// ---------------------------------------------------------------------------
+// type t: 0 (i, j), 1 (i+1/2, j), 2 (i, j+1/2), 3 (i+1/2, j+1/2)
+// quantity q: 0 alpha, 1 beta, 2 sqrt(gamma), 3 g_rr, 4 g_rp, 5 g_tt, 6 g_pp
+// tables 28..30: 2 pi x dual-cell volume of the (i,j), (i+1/2,j), (i,j+1/2) grids
+// then sin/cos of the integer and half th nodes.
+enum { MT_Q = 7, MT_DUAL = 28, MT_N = 31 };
+
+struct Tabs {
+    const double* m;   // MT_N tables of size sz, then 2 (Nth+1) + 2 Nth trig values
+    size_t sz;
+    int ld;
+    __device__ __forceinline__ double at(int t, int q, int i, int j) const
+    {
+        return m[(size_t)(t * MT_Q + q) * sz + (size_t)i * ld + j];
+    }
+    __device__ __forceinline__ double dual(int t, int i, int j) const
+    {
+        return m[(size_t)(MT_DUAL + t) * sz + (size_t)i * ld + j];
+    }
+};
+
+__device__ __forceinline__ double sqrtg_sc(const BH& bh, double r, double s, double c)
+{
+    // sqrt(gamma) = rho^2 sqrt(xi) sin th = sin th sqrt(rho^2 (rho^2 + 2 M r))
+    const double rho2 = fma(bh.a2, c * c, r * r);
+    return s * sqrt(rho2 * fma(bh.twoM, r, rho2));
+}
+
+__device__ double trap16_dev(const BH& bh, double x0, double x1, double y0, double y1)
+{
+    const double wt[4] = {0.5, 1.0, 1.0, 0.5};
+    const double hx = (x1 - x0) / 3.0, hy = (y1 - y0) / 3.0;
+    double acc = 0.0;
+    for (int l = 0; l < 4; ++l) {
+        double s, c;
+        sincos(y0 + l * hy, &s, &c);
+        double row = 0.0;
+        for (int k = 0; k < 4; ++k) row = fma(wt[k], sqrtg_sc(bh, x0 + k * hx, s, c), row);
+        acc = fma(wt[l], row, acc);
+    }
+    return acc * hx * hy;
+}
+
+__global__ void k_metric_tables(BH bh, GridDev G, double* m, size_t sz)
+{
+    const int i = blockIdx.y;
+    for (int j = threadIdx.x; j <= G.Nth; j += blockDim.x) {
+        for (int t = 0; t < 4; ++t) {
+            const bool ro = t & 1, to = t & 2;
+            if ((ro && i >= G.Nr) || (to && j >= G.Nth)) continue;
+            const double r = ro ? G.rh[i] : G.rn[i];
+            const double th = to ? G.th[j] : G.tn[j];
+            double s, c;
+            sincos(th, &s, &c);
+            Geo g;
+            geo_eval(bh, r, s, c, g);
+            const double v[MT_Q] = {g.alpha, g.beta, g.sqrtg, g.grr, g.grp, g.gtt, g.gpp};
+            for (int q = 0; q < MT_Q; ++q) m[(size_t)(t * MT_Q + q) * sz + (size_t)i * G.ld + j] = v[q];
+        }
+        // dual-cell volumes of the (i,j), (i+1/2,j), (i,j+1/2) sub-grids
+        for (int t = 0; t < 3; ++t) {
+            const bool ro = (t == 1), to = (t == 2);
+            if ((ro && i >= G.Nr) || (to && j >= G.Nth)) continue;
+            double x0, x1, y0, y1;
+            if (ro) { x0 = G.rn[i]; x1 = G.rn[i + 1]; }
+            else { x0 = i == 0 ? G.rn[0] : G.rh[i - 1]; x1 = i == G.Nr ? G.rn[G.Nr] : G.rh[i]; }
+            if (to) { y0 = G.tn[j]; y1 = G.tn[j + 1]; }
+            else { y0 = j == 0 ? G.tn[0] : G.th[j - 1]; y1 = j == G.Nth ? G.tn[G.Nth] : G.th[j]; }
+            m[(size_t)(MT_DUAL + t) * sz + (size_t)i * G.ld + j] = 2.0 * M_PI * trap16_dev(bh, x0, x1, y0, y1);
+        }
+    }
+    if (i == 0) {
+        double* trig = m + (size_t)MT_N * sz;
+        for (int j = threadIdx.x; j <= G.Nth; j += blockDim.x) {
+            double s, c;
+            sincos(G.tn[j], &s, &c);
+            trig[j] = s;
+            trig[(G.Nth + 1) + j] = c;
+            if (j < G.Nth) {
+                sincos(G.th[j], &s, &c);
+                trig[2 * (G.Nth + 1) + j] = s;
+                trig[2 * (G.Nth + 1) + G.Nth + j] = c;
+            }
+        }
+    }
+}
+
 int build_metric_tables(fpic_ctx* c)
 {
-    (void)c;
+    const size_t sz = (size_t)(c->Nr + 1) * c->ld;
+    const size_t tot = (size_t)MT_N * sz + 2 * (size_t)(c->Nth + 1) + 2 * (size_t)c->Nth;
+    if (c->d_metric) FPIC_CUDA(cudaFree(c->d_metric));
+    c->d_metric = nullptr;
+    FPIC_CUDA(cudaMalloc(&c->d_metric, tot * sizeof(double)));
+    c->metric_stride = sz;
+    dim3 grid(1, c->Nr + 1);
+    k_metric_tables<<<grid, 128>>>(c->bh, c->G, c->d_metric, sz);
+    FPIC_CUDA(cudaGetLastError());
     return 0;
 }
 
+// ---------------------------------------------------------------------------
+// Stable sort by cell
+// ---------------------------------------------------------------------------
+struct SortBufs {
+    uint32_t *key, *perm, *perm2, *count, *cursor, *off, *bsum;
+    void* tmp;
+};
+
+__global__ void k_keys(GridDev G, const double* r, const double* th, const uint8_t* alive, uint32_t* key,
+                       uint32_t* cell, uint32_t* count, long long n, uint32_t C)
+{
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    int i, j;
+    double w;
+    const double rr = r[p], tt = th[p];
+    const float lr = __logf((float)rr);
+    locate(G.rn, G.irn, G.Nr + 1, rr, (lr - G.lr0) * G.ilr, i, w);
+    locate(G.tn, G.itn, G.Nth + 1, tt, ((float)tt - G.t0) * G.it, j, w);
+    const uint32_t c = (uint32_t)i * (uint32_t)G.Nth + (uint32_t)j;
+    if (cell) cell[p] = c;
+    const uint32_t k = alive[p] ? c : C;
+    key[p] = k;
+    atomicAdd(&count[k], 1u);
+}
+
+// exclusive scan of count[0..m) into off[0..m], m + 1 outputs; three phases
+constexpr int SCAN_B = 1024, SCAN_PER = 4;
+__global__ void k_scan_blocks(const uint32_t* in, uint32_t* out, uint32_t* bsum, long long m)
+{
+    __shared__ uint32_t sh[SCAN_B];
+    const long long base = (long long)blockIdx.x * SCAN_B * SCAN_PER;
+    uint32_t v[SCAN_PER], tot = 0;
+    for (int k = 0; k < SCAN_PER; ++k) {
+        const long long idx = base + (long long)threadIdx.x * SCAN_PER + k;
+        v[k] = idx < m ? in[idx] : 0u;
+        tot += v[k];
+    }
+    sh[threadIdx.x] = tot;
+    __syncthreads();
+    for (int o = 1; o < SCAN_B; o <<= 1) {
+        uint32_t t = threadIdx.x >= (unsigned)o ? sh[threadIdx.x - o] : 0u;
+        __syncthreads();
+        sh[threadIdx.x] += t;
+        __syncthreads();
+    }
+    uint32_t run = sh[threadIdx.x] - tot;   // exclusive prefix of this thread
+    for (int k = 0; k < SCAN_PER; ++k) {
+        const long long idx = base + (long long)threadIdx.x * SCAN_PER + k;
+        if (idx < m) out[idx] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == SCAN_B - 1) bsum[blockIdx.x] = sh[SCAN_B - 1];
+}
+
+__global__ void k_scan_bsum(uint32_t* bsum, int nb)
+{
+    // single thread: nb is at most a few thousand
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        uint32_t run = 0;
+        for (int b = 0; b < nb; ++b) {
+            const uint32_t t = bsum[b];
+            bsum[b] = run;
+            run += t;
+        }
+        bsum[nb] = run;
+    }
+}
+
+__global__ void k_scan_add(uint32_t* out, const uint32_t* bsum, long long m, int nb)
+{
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx < m) out[idx] += bsum[idx / (SCAN_B * SCAN_PER)];
+    if (idx == 0) out[m] = bsum[nb];
+}
+
+__global__ void k_scatter(const uint32_t* key, const uint32_t* off, uint32_t* cursor, uint32_t* perm, long long n)
+{
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const uint32_t k = key[p];
+    perm[off[k] + atomicAdd(&cursor[k], 1u)] = (uint32_t)p;
+}
+
+// Order every bucket by particle index (rank = number of smaller indices in
+// the bucket): one warp per bucket.  Removed particles (last bucket) are
+// handled by k_dead_rank.
+__global__ void k_bucket_rank(const uint32_t* off, const uint32_t* perm, uint32_t* perm2, uint32_t C)
+{
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= C) return;
+    const uint32_t b0 = off[warp], b1 = off[warp + 1];
+    for (uint32_t a = b0 + lane; a < b1; a += 32) {
+        const uint32_t x = perm[a];
+        uint32_t rank = 0;
+        for (uint32_t b = b0; b < b1; ++b) rank += perm[b] < x ? 1u : 0u;
+        perm2[b0 + rank] = x;
+    }
+}
+
+// Removed particles keep their relative order: position = off[C] + number of
+// removed particles with a smaller index (block scan of the flags).
+__global__ void k_dead_flags(const uint8_t* alive, uint32_t* flag, long long n)
+{
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p < n) flag[p] = alive[p] ? 0u : 1u;
+}
+
+__global__ void k_dead_place(const uint8_t* alive, const uint32_t* pos, const uint32_t* off, uint32_t* perm2,
+                             long long n, uint32_t C)
+{
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p < n && !alive[p]) perm2[off[C] + pos[p]] = (uint32_t)p;
+}
+
+template <typename T>
+__global__ void k_gather_perm(const T* __restrict__ src, T* __restrict__ dst, const uint32_t* __restrict__ perm,
+                              long long n)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = src[perm[i]];
+}
+
+static int scan_u32(const uint32_t* in, uint32_t* out, uint32_t* bsum, long long m, cudaStream_t s)
+{
+    const int nb = (int)((m + SCAN_B * SCAN_PER - 1) / (SCAN_B * SCAN_PER));
+    k_scan_blocks<<<nb, SCAN_B, 0, s>>>(in, out, bsum, m);
+    k_scan_bsum<<<1, 32, 0, s>>>(bsum, nb);
+    k_scan_add<<<(unsigned)((m + 255) / 256 + 1), 256, 0, s>>>(out, bsum, m, nb);
+    return check_cuda(cudaGetLastError(), "scan");
+}
+
+// Scratch2 layout for sort + deposit.
+struct Work {
+    uint32_t *key, *perm, *perm2, *count, *cursor, *off, *bsum, *flag, *pos;
+    double* tmp;        // n doubles (permutation buffer)
+    double* rec;        // 16 x n deposit shares
+    uint32_t* code;     // n stencil offsets
+    double* part;       // 20 x C cell partials
+};
+
+static int work_layout(fpic_ctx* c, long long n, bool deposit, Work& w)
+{
+    const long long C = (long long)c->Nr * c->Nth;
+    const long long nbs = (n > C + 2 ? n : C + 2) / (SCAN_B * SCAN_PER) + 2;
+    size_t bytes = 0;
+    auto take = [&](size_t b) { size_t o = bytes; bytes += (b + 255) & ~(size_t)255; return o; };
+    size_t o_key = take(4 * n), o_perm = take(4 * n), o_perm2 = take(4 * n), o_count = take(4 * (C + 2)),
+           o_cursor = take(4 * (C + 2)), o_off = take(4 * (C + 2)), o_bsum = take(4 * nbs), o_flag = take(4 * n),
+           o_pos = take(4 * (n + 1)), o_tmp = take(8 * n);
+    size_t o_rec = 0, o_code = 0, o_part = 0;
+    if (deposit) {
+        o_rec = take(16 * 8 * (size_t)n);
+        o_code = take(4 * n);
+        o_part = take(20 * 8 * (size_t)C);
+    }
+    int rc = ensure_scratch2(c, bytes);
+    if (rc) return rc;
+    char* b = (char*)c->d_scratch2;
+    w.key = (uint32_t*)(b + o_key);
+    w.perm = (uint32_t*)(b + o_perm);
+    w.perm2 = (uint32_t*)(b + o_perm2);
+    w.count = (uint32_t*)(b + o_count);
+    w.cursor = (uint32_t*)(b + o_cursor);
+    w.off = (uint32_t*)(b + o_off);
+    w.bsum = (uint32_t*)(b + o_bsum);
+    w.flag = (uint32_t*)(b + o_flag);
+    w.pos = (uint32_t*)(b + o_pos);
+    w.tmp = (double*)(b + o_tmp);
+    w.rec = deposit ? (double*)(b + o_rec) : nullptr;
+    w.code = deposit ? (uint32_t*)(b + o_code) : nullptr;
+    w.part = deposit ? (double*)(b + o_part) : nullptr;
+    return 0;
+}
+
+static int sort_impl(fpic_ctx* c, fpic_particles* p, Work& w, cudaStream_t s)
+{
+    const long long n = p->n;
+    const uint32_t C = (uint32_t)c->Nr * (uint32_t)c->Nth;
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    FPIC_CUDA(cudaMemsetAsync(w.count, 0, 4 * ((size_t)C + 2), s));
+    FPIC_CUDA(cudaMemsetAsync(w.cursor, 0, 4 * ((size_t)C + 2), s));
+    k_keys<<<nb, 256, 0, s>>>(c->G, p->r, p->th, p->alive, w.key, p->cell, w.count, n, C);
+    int rc = scan_u32(w.count, w.off, w.bsum, (long long)C + 1, s);
+    if (rc) return rc;
+    k_scatter<<<nb, 256, 0, s>>>(w.key, w.off, w.cursor, w.perm, n);
+    k_bucket_rank<<<(unsigned)(((long long)C * 32 + 255) / 256), 256, 0, s>>>(w.off, w.perm, w.perm2, C);
+    k_dead_flags<<<nb, 256, 0, s>>>(p->alive, w.flag, n);
+    rc = scan_u32(w.flag, w.pos, w.bsum, n, s);
+    if (rc) return rc;
+    k_dead_place<<<nb, 256, 0, s>>>(p->alive, w.pos, w.off, w.perm2, n, C);
+    FPIC_CUDA(cudaGetLastError());
+    double* d8[] = {p->r, p->th, p->ph, p->ur, p->uth, p->uph, p->qm, p->w, p->H0, p->D0, p->Hn};
+    for (double* a : d8) {
+        if (!a) continue;
+        k_gather_perm<double><<<nb, 256, 0, s>>>(a, w.tmp, w.perm2, n);
+        FPIC_CUDA(cudaMemcpyAsync(a, w.tmp, 8 * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    }
+    uint8_t* d1[] = {p->alive, p->scheme, p->iters};
+    for (uint8_t* a : d1) {
+        if (!a) continue;
+        k_gather_perm<uint8_t><<<nb, 256, 0, s>>>(a, (uint8_t*)w.tmp, w.perm2, n);
+        FPIC_CUDA(cudaMemcpyAsync(a, w.tmp, (size_t)n, cudaMemcpyDeviceToDevice, s));
+    }
+    if (p->cell) {
+        k_gather_perm<uint32_t><<<nb, 256, 0, s>>>(p->cell, (uint32_t*)w.tmp, w.perm2, n);
+        FPIC_CUDA(cudaMemcpyAsync(p->cell, w.tmp, 4 * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    }
+    FPIC_CUDA(cudaGetLastError());
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Deposit (Sec. 2.3)
+// ---------------------------------------------------------------------------
+
+// 4x4 trapezoid lattice of a sub-grid cell [x0, x1] x [y0, y1] split at
+// (r, t): the four subvolumes V00 = [x0,r]x[y0,t], V10 = [r,x1]x[y0,t],
+// V01 = [x0,r]x[t,y1], V11 = [r,x1]x[t,y1], each by its own 4 x 4 rule; the
+// points of the 7 x 7 lattice are evaluated once.
+__device__ __forceinline__ void subvolumes(const BH& bh, double x0, double x1, double r, double y0, double y1,
+                                           double t, const double sy[7], const double cy[7], double V[4])
+{
+    double xs[7];
+    const double ha = (r - x0) / 3.0, hb = (x1 - r) / 3.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) xs[k] = x0 + k * ha;
+#pragma unroll
+    for (int k = 1; k < 4; ++k) xs[3 + k] = r + k * hb;
+    const double hc = (t - y0) / 3.0, hd = (y1 - t) / 3.0;
+    const double wt[4] = {0.5, 1.0, 1.0, 0.5};
+    double S00 = 0, S10 = 0, S01 = 0, S11 = 0;
+#pragma unroll
+    for (int l = 0; l < 7; ++l) {
+        double ra = 0.0, rb = 0.0;    // rows over the lower (a) and upper (b) r halves
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+            const double f = sqrtg_sc(bh, xs[k], sy[l], cy[l]);
+            if (k <= 3) ra = fma(wt[k], f, ra);
+            if (k >= 3) rb = fma(wt[k - 3], f, rb);
+        }
+        if (l <= 3) { S00 = fma(wt[l], ra, S00); S10 = fma(wt[l], rb, S10); }
+        if (l >= 3) { S01 = fma(wt[l - 3], ra, S01); S11 = fma(wt[l - 3], rb, S11); }
+    }
+    V[0] = S00 * (ha * hc);
+    V[1] = S10 * (hb * hc);
+    V[2] = S01 * (ha * hd);
+    V[3] = S11 * (hb * hd);
+}
+
+// sin/cos at the 7 lattice th values of the th cell [y0, y1] split at t.
+__device__ __forceinline__ void theta_lattice(double y0, double y1, double t, double sy[7], double cy[7])
+{
+    const double hc = (t - y0) / 3.0, hd = (y1 - t) / 3.0;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) sincos(y0 + l * hc, &sy[l], &cy[l]);
+#pragma unroll
+    for (int l = 1; l < 4; ++l) sincos(t + l * hd, &sy[3 + l], &cy[3 + l]);
+}
+
+struct DepK {
+    BH bh;
+    GridDev G;
+    const double *r, *th, *ur, *uth, *uph, *qm, *w;
+    long long n_alive;
+    double* rec;     // 16 x n
+    uint32_t* code;  // (i1 - i0 + 1) | (j1 - j0 + 1) << 2
+};
+
+__device__ __forceinline__ double clampd(double x, double lo, double hi)
+{
+    return x < lo ? lo : (x > hi ? hi : x);
+}
+
+__global__ void __launch_bounds__(128) k_dep_particle(DepK k)
+{
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= k.n_alive) return;
+    const GridDev& G = k.G;
+    const double r = k.r[p], t = k.th[p];
+    // FIDO three-velocity v^i = gamma^ij u_j / Gamma at the particle
+    double s, c;
+    sincos(t, &s, &c);
+    Geo g;
+    geo_eval(k.bh, r, s, c, g);
+    const double ur = k.ur[p], ut = k.uth[p], up = k.uph[p];
+    const double Ur = fma(g.gurr, ur, g.gurp * up), Ut = g.gutt * ut, Up = fma(g.gurp, ur, g.gupp * up);
+    const double iG = rsqrt(fma(ur, Ur, fma(ut, Ut, fma(up, Up, 1.0))));
+    const double Q = k.w[p] * k.qm[p];
+    const double vr = Ur * iG, vt = Ut * iG, vp = Up * iG;
+    // clamped positions and cells on the integer and half node lists
+    const double rn_c = clampd(r, G.rn[0], G.rn[G.Nr]), rh_c = clampd(r, G.rh[0], G.rh[G.Nr - 1]);
+    const double tn_c = clampd(t, G.tn[0], G.tn[G.Nth]), th_c = clampd(t, G.th[0], G.th[G.Nth - 1]);
+    int i0, i1, j0, j1;
+    double wd;
+    const float lr = __logf((float)r);
+    locate(G.rn, G.irn, G.Nr + 1, rn_c, (lr - G.lr0) * G.ilr, i0, wd);
+    locate(G.rh, G.irh, G.Nr, rh_c, (lr - G.lrh0) * G.ilr, i1, wd);
+    locate(G.tn, G.itn, G.Nth + 1, tn_c, ((float)t - G.t0) * G.it, j0, wd);
+    locate(G.th, G.ith, G.Nth, th_c, ((float)t - G.th0) * G.it, j1, wd);
+    double sy[7], cy[7], V[4];
+    const long long n = k.n_alive;
+    // (i, j): rho and j^ph
+    theta_lattice(G.tn[j0], G.tn[j0 + 1], tn_c, sy, cy);
+    subvolumes(k.bh, G.rn[i0], G.rn[i0 + 1], rn_c, G.tn[j0], G.tn[j0 + 1], tn_c, sy, cy, V);
+    double iV = 1.0 / (V[0] + V[1] + V[2] + V[3]);
+    // share of node (i+a, j+b) = V(opposite corner) / V
+    const double w00 = V[3] * iV, w10 = V[2] * iV, w01 = V[1] * iV, w11 = V[0] * iV;
+    k.rec[0 * n + p] = Q * w00; k.rec[1 * n + p] = Q * w10; k.rec[2 * n + p] = Q * w01; k.rec[3 * n + p] = Q * w11;
+    const double Qp = Q * vp;
+    k.rec[4 * n + p] = Qp * w00; k.rec[5 * n + p] = Qp * w10; k.rec[6 * n + p] = Qp * w01; k.rec[7 * n + p] = Qp * w11;
+    // (i+1/2, j): j^r  (same th lattice)
+    subvolumes(k.bh, G.rh[i1], G.rh[i1 + 1], rh_c, G.tn[j0], G.tn[j0 + 1], tn_c, sy, cy, V);
+    iV = 1.0 / (V[0] + V[1] + V[2] + V[3]);
+    const double Qr = Q * vr;
+    k.rec[8 * n + p] = Qr * (V[3] * iV); k.rec[9 * n + p] = Qr * (V[2] * iV);
+    k.rec[10 * n + p] = Qr * (V[1] * iV); k.rec[11 * n + p] = Qr * (V[0] * iV);
+    // (i, j+1/2): j^th
+    theta_lattice(G.th[j1], G.th[j1 + 1], th_c, sy, cy);
+    subvolumes(k.bh, G.rn[i0], G.rn[i0 + 1], rn_c, G.th[j1], G.th[j1 + 1], th_c, sy, cy, V);
+    iV = 1.0 / (V[0] + V[1] + V[2] + V[3]);
+    const double Qt = Q * vt;
+    k.rec[12 * n + p] = Qt * (V[3] * iV); k.rec[13 * n + p] = Qt * (V[2] * iV);
+    k.rec[14 * n + p] = Qt * (V[1] * iV); k.rec[15 * n + p] = Qt * (V[0] * iV);
+    k.code[p] = (uint32_t)(i1 - i0 + 1) | ((uint32_t)(j1 - j0 + 1) << 2);
+}
+
+// Slots of a cell (i0, j0): rho[a + 2b] (0..3), j^ph[a + 2b] (4..7),
+// j^r[k + 3b] at half-r node i0 - 1 + k (8..13), j^th[a + 2k] at half-th
+// node j0 - 1 + k (14..19).
+__global__ void __launch_bounds__(256) k_dep_cell(const double* __restrict__ rec, const uint32_t* __restrict__ code,
+                                                   const uint32_t* __restrict__ off, double* __restrict__ part,
+                                                   long long n, uint32_t C)
+{
+    const long long cell = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (cell >= C) return;
+    const uint32_t b0 = off[cell], b1 = off[cell + 1];
+    double acc[20];
+#pragma unroll
+    for (int q = 0; q < 20; ++q) acc[q] = 0.0;
+    for (uint32_t a = b0 + lane; a < b1; a += 32) {
+        const uint32_t cd = code[a];
+        const int ko = cd & 3, kt = (cd >> 2) & 3;     // half-r / half-th slot offsets (0 or 1)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q] += rec[(size_t)q * n + a];
+        const double r0 = rec[8 * n + a], r1 = rec[9 * n + a], r2 = rec[10 * n + a], r3 = rec[11 * n + a];
+        // j^r shares: (node i1, j0), (i1+1, j0), (i1, j0+1), (i1+1, j0+1); i1 = i0 - 1 + ko
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk) {
+            acc[8 + kk] += (kk == ko ? r0 : 0.0) + (kk == ko + 1 ? r1 : 0.0);
+            acc[11 + kk] += (kk == ko ? r2 : 0.0) + (kk == ko + 1 ? r3 : 0.0);
+        }
+        const double t0 = rec[12 * n + a], t1 = rec[13 * n + a], t2 = rec[14 * n + a], t3 = rec[15 * n + a];
+        // j^th shares: (i0, j1), (i0+1, j1), (i0, j1+1), (i0+1, j1+1); j1 = j0 - 1 + kt
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk) {
+            acc[14 + 2 * kk] += (kk == kt ? t0 : 0.0) + (kk == kt + 1 ? t2 : 0.0);
+            acc[15 + 2 * kk] += (kk == kt ? t1 : 0.0) + (kk == kt + 1 ? t3 : 0.0);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 20; ++q) {
+        double v = acc[q];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) part[(size_t)q * C + cell] = v;
+    }
+}
+
+struct NodeK {
+    int Nr, Nth, ld;
+    const double* part;
+    uint32_t C;
+    Tabs T;
+    double *rho, *jr, *jt, *jp;
+};
+
+__global__ void k_dep_node(NodeK k)
+{
+    const int i = blockIdx.y;
+    const int Nr = k.Nr, Nth = k.Nth;
+    auto P = [&](int q, int ci, int cj) -> double {
+        return k.part[(size_t)q * k.C + (size_t)ci * Nth + cj];
+    };
+    for (int j = threadIdx.x; j <= Nth; j += blockDim.x) {
+        const size_t o = (size_t)i * k.ld + j;
+        // rho, j^ph at (i, j): cells (i - a, j - b), slot a + 2b
+        double sr = 0.0, sp = 0.0;
+        for (int b = 0; b < 2; ++b)
+            for (int a = 0; a < 2; ++a) {
+                const int ci = i - a, cj = j - b;
+                if (ci < 0 || ci >= Nr || cj < 0 || cj >= Nth) continue;
+                sr += P(a + 2 * b, ci, cj);
+                sp += P(4 + a + 2 * b, ci, cj);
+            }
+        k.rho[o] = sr / k.T.dual(0, i, j);
+        k.jp[o] = sp / k.T.dual(0, i, j);
+        // j^r at (i+1/2, j): cells (i + 1 - kk, j - b), slot kk + 3b
+        if (i < Nr) {
+            double sj = 0.0;
+            for (int b = 0; b < 2; ++b)
+                for (int kk = 0; kk < 3; ++kk) {
+                    const int ci = i + 1 - kk, cj = j - b;
+                    if (ci < 0 || ci >= Nr || cj < 0 || cj >= Nth) continue;
+                    sj += P(8 + kk + 3 * b, ci, cj);
+                }
+            k.jr[o] = sj / k.T.dual(1, i, j);
+        }
+        // j^th at (i, j+1/2): cells (i - a, j + 1 - kk), slot a + 2 kk
+        if (j < Nth) {
+            double sj = 0.0;
+            for (int kk = 0; kk < 3; ++kk)
+                for (int a = 0; a < 2; ++a) {
+                    const int ci = i - a, cj = j + 1 - kk;
+                    if (ci < 0 || ci >= Nr || cj < 0 || cj >= Nth) continue;
+                    sj += P(14 + a + 2 * kk, ci, cj);
+                }
+            k.jt[o] = sj / k.T.dual(2, i, j);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FDTD (Sec. 2.1, Eqs. m3, m4, Ei; Sec. 2.5)
+// ---------------------------------------------------------------------------
+struct FK {
+    int Nr, Nth, ld;
+    GridDev G;
+    Tabs T;
+    double dt, chi0, lam, r_abs, r_max;
+};
+
+__device__ __forceinline__ double damp(const FK& k, double r)
+{
+    if (k.chi0 <= 0.0 || r <= k.r_abs) return 1.0;
+    const double x = (r - k.r_abs) / (k.r_max - k.r_abs);
+    return exp(-k.chi0 * pow(x, k.lam) * k.dt);
+}
+
+// metric-weighted average of F (staggering ro, to) to the point of the other
+// r staggering at index i2 (zero-gradient beyond the ends)
+__device__ __forceinline__ double avg_r(const FK& k, const double* F, int ro, int to, int i2, int j)
+{
+    int ia = ro ? i2 - 1 : i2, ib = ro ? i2 : i2 + 1;
+    const int m = ro ? k.Nr : k.Nr + 1;
+    if (ia < 0) ia = ib;
+    if (ib > m - 1) ib = ia;
+    const int tF = (ro ? 1 : 0) | (to ? 2 : 0), tT = (ro ? 0 : 1) | (to ? 2 : 0);
+    const double sa = k.T.at(tF, 2, ia, j), sb = k.T.at(tF, 2, ib, j), st = k.T.at(tT, 2, i2, j);
+    return fma(sa, F[(size_t)ia * k.ld + j], sb * F[(size_t)ib * k.ld + j]) / (2.0 * st);
+}
+
+struct F3 {
+    const double *a[3], *b[3];   // value = b ? 0.5 (a + b) : a  (pointwise level average)
+    __device__ __forceinline__ double v(int c, size_t o) const
+    {
+        return b[c] ? 0.5 * (a[c][o] + b[c][o]) : a[c][o];
+    }
+};
+
+struct O3 {
+    double* p[3];
+};
+
+__global__ void k_avg3(F3 in, O3 out, size_t sz)
+{
+    for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < sz; o += (size_t)gridDim.x * blockDim.x)
+        for (int c = 0; c < 3; ++c) out.p[c][o] = in.v(c, o);
+}
+
+// Eq. (Ei): E_r (i+1/2,j) = alpha (g_rr D^r + g_rp <D^ph>);
+// E_th (i,j+1/2) = alpha g_tt D^th - sqrtg beta <B^ph>;
+// E_ph (i,j) = alpha (g_rp <D^r> + g_pp D^ph) + sqrtg beta <B^th>.
+__global__ void k_make_E(FK k, F3 D, F3 B, O3 E)
+{
+    const int i = blockIdx.y;
+    for (int j = threadIdx.x; j <= k.Nth; j += blockDim.x) {
+        const size_t o = (size_t)i * k.ld + j;
+        if (i < k.Nr) {
+            const double Dp = avg_r(k, D.a[2], 0, 0, i, j);
+            E.p[0][o] = k.T.at(1, 0, i, j) * fma(k.T.at(1, 3, i, j), D.a[0][o], k.T.at(1, 4, i, j) * Dp);
+        }
+        if (j < k.Nth) {
+            const double Bp = avg_r(k, B.a[2], 1, 1, i, j);
+            E.p[1][o] = fma(k.T.at(2, 0, i, j) * k.T.at(2, 5, i, j), D.a[1][o],
+                            -k.T.at(2, 2, i, j) * k.T.at(2, 1, i, j) * Bp);
+        }
+        const double Dr = avg_r(k, D.a[0], 1, 0, i, j);
+        const double Bt = avg_r(k, B.a[1], 1, 0, i, j);
+        E.p[2][o] = fma(k.T.at(0, 0, i, j), fma(k.T.at(0, 4, i, j), Dr, k.T.at(0, 6, i, j) * D.a[2][o]),
+                        k.T.at(0, 2, i, j) * k.T.at(0, 1, i, j) * Bt);
+    }
+}
+
+// H_r (i,j+1/2) = alpha (g_rr B^r + g_rp <B^ph>);  H_th (i+1/2,j) = alpha g_tt
+// B^th + sqrtg beta <D^ph>;  H_ph (i+1/2,j+1/2) = alpha (g_rp <B^r> + g_pp B^ph)
+// - sqrtg beta <D^th>.
+__global__ void k_make_H(FK k, F3 D, F3 B, O3 H)
+{
+    const int i = blockIdx.y;
+    for (int j = threadIdx.x; j <= k.Nth; j += blockDim.x) {
+        const size_t o = (size_t)i * k.ld + j;
+        if (j < k.Nth) {
+            const double Bp = avg_r(k, B.a[2], 1, 1, i, j);
+            H.p[0][o] = k.T.at(2, 0, i, j) * fma(k.T.at(2, 3, i, j), B.a[0][o], k.T.at(2, 4, i, j) * Bp);
+        }
+        if (i < k.Nr) {
+            const double Dp = avg_r(k, D.a[2], 0, 0, i, j);
+            H.p[1][o] = fma(k.T.at(1, 0, i, j) * k.T.at(1, 5, i, j), B.a[1][o],
+                            k.T.at(1, 2, i, j) * k.T.at(1, 1, i, j) * Dp);
+        }
+        if (i < k.Nr && j < k.Nth) {
+            const double Br = avg_r(k, B.a[0], 0, 1, i, j);
+            const double Dt = avg_r(k, D.a[1], 0, 1, i, j);
+            H.p[2][o] = fma(k.T.at(3, 0, i, j), fma(k.T.at(3, 4, i, j), Br, k.T.at(3, 6, i, j) * B.a[2][o]),
+                            -k.T.at(3, 2, i, j) * k.T.at(3, 1, i, j) * Dt);
+        }
+    }
+}
+
+// Eq. (m4) + (abs0): B_out = (B_in - dt curl E / sqrtg) exp(-chi dt).
+__global__ void k_update_B(FK k, F3 Bin, O3 E, O3 Bout)
+{
+    const int i = blockIdx.y;
+    const GridDev& G = k.G;
+    for (int j = threadIdx.x; j <= k.Nth; j += blockDim.x) {
+        const size_t o = (size_t)i * k.ld + j;
+        if (j < k.Nth) {   // B^r (i, j+1/2)
+            const double curl = (E.p[2][o + 1] - E.p[2][o]) / (G.tn[j + 1] - G.tn[j]);
+            Bout.p[0][o] = (Bin.v(0, o) - k.dt * curl / k.T.at(2, 2, i, j)) * damp(k, G.rn[i]);
+        }
+        if (i < k.Nr) {    // B^th (i+1/2, j)
+            const double curl = -(E.p[2][o + k.ld] - E.p[2][o]) / (G.rn[i + 1] - G.rn[i]);
+            Bout.p[1][o] = (Bin.v(1, o) - k.dt * curl / k.T.at(1, 2, i, j)) * damp(k, G.rh[i]);
+        }
+        if (i < k.Nr && j < k.Nth) {   // B^ph (i+1/2, j+1/2)
+            const double dEt = (E.p[1][o + k.ld] - E.p[1][o]) / (G.rn[i + 1] - G.rn[i]);
+            const double dEr = (E.p[0][o + 1] - E.p[0][o]) / (G.tn[j + 1] - G.tn[j]);
+            Bout.p[2][o] = (Bin.v(2, o) - k.dt * (dEt - dEr) / k.T.at(3, 2, i, j)) * damp(k, G.rh[i]);
+        }
+    }
+}
+
+struct Src {
+    const double *j[3], *rho;
+    double w;
+};
+
+// J = alpha j - rho beta at the J^k point (rho averaged to J^r's point)
+__device__ __forceinline__ double jsrc(const FK& k, const Src& S, int comp, int i, int j)
+{
+    if (S.w == 0.0) return 0.0;
+    const size_t o = (size_t)i * k.ld + j;
+    if (comp == 0) {
+        const double rb = avg_r(k, S.rho, 0, 0, i, j);
+        return S.w * fma(k.T.at(1, 0, i, j), S.j[0][o], -rb * k.T.at(1, 1, i, j));
+    }
+    if (comp == 1) return S.w * (k.T.at(2, 0, i, j) * S.j[1][o]);
+    return S.w * (k.T.at(0, 0, i, j) * S.j[2][o]);
+}
+
+// Eq. (m3) + (abs1): D_out = (D_in + dt [curl H / sqrtg - 4 pi J]) exp(-chi dt),
+// interior points only (boundaries: k_bc_D).
+__global__ void k_update_D(FK k, F3 Din, O3 H, Src S0, Src S1, O3 Dout)
+{
+    const int i = blockIdx.y;
+    const GridDev& G = k.G;
+    const double fpi = 4.0 * M_PI;
+    for (int j = threadIdx.x; j <= k.Nth; j += blockDim.x) {
+        const size_t o = (size_t)i * k.ld + j;
+        if (i < k.Nr && j >= 1 && j < k.Nth) {    // D^r (i+1/2, j)
+            const double curl = (H.p[2][o] - H.p[2][o - 1]) / (G.th[j] - G.th[j - 1]);
+            const double J = jsrc(k, S0, 0, i, j) + jsrc(k, S1, 0, i, j);
+            Dout.p[0][o] = (Din.v(0, o) + k.dt * (curl / k.T.at(1, 2, i, j) - fpi * J)) * damp(k, G.rh[i]);
+        }
+        if (i >= 1 && i < k.Nr && j < k.Nth) {    // D^th (i, j+1/2)
+            const double curl = -(H.p[2][o] - H.p[2][o - k.ld]) / (G.rh[i] - G.rh[i - 1]);
+            const double J = jsrc(k, S0, 1, i, j) + jsrc(k, S1, 1, i, j);
+            Dout.p[1][o] = (Din.v(1, o) + k.dt * (curl / k.T.at(2, 2, i, j) - fpi * J)) * damp(k, G.rn[i]);
+        }
+        if (i >= 1 && i < k.Nr && j >= 1 && j < k.Nth) {   // D^ph (i, j)
+            const double dHt = (H.p[1][o] - H.p[1][o - k.ld]) / (G.rh[i] - G.rh[i - 1]);
+            const double dHr = (H.p[0][o] - H.p[0][o - 1]) / (G.th[j] - G.th[j - 1]);
+            const double J = jsrc(k, S0, 2, i, j) + jsrc(k, S1, 2, i, j);
+            Dout.p[2][o] = (Din.v(2, o) + k.dt * ((dHt - dHr) / k.T.at(0, 2, i, j) - fpi * J)) * damp(k, G.rn[i]);
+        }
+    }
+}
+
+// Sec. 2.5 (reading): zero gradient where a stencil is one-sided, D^ph = 0 on
+// the axis rows.
+__global__ void k_bc_D(FK k, O3 D)
+{
+    const int i = blockIdx.y;
+    const int Nr = k.Nr, Nth = k.Nth, ld = k.ld;
+    if (threadIdx.x == 0) {
+        if (i < Nr) {
+            D.p[0][(size_t)i * ld + 0] = D.p[0][(size_t)i * ld + 1];
+            D.p[0][(size_t)i * ld + Nth] = D.p[0][(size_t)i * ld + Nth - 1];
+        }
+    }
+    for (int j = threadIdx.x; j <= Nth; j += blockDim.x) {
+        if (i == 0 && j < Nth) D.p[1][j] = D.p[1][(size_t)ld + j];
+        if (i == Nr && j < Nth) D.p[1][(size_t)Nr * ld + j] = D.p[1][(size_t)(Nr - 1) * ld + j];
+        if (i == 0 && j >= 1 && j < Nth) D.p[2][j] = D.p[2][(size_t)ld + j];
+        if (i == Nr && j >= 1 && j < Nth) D.p[2][(size_t)Nr * ld + j] = D.p[2][(size_t)(Nr - 1) * ld + j];
+    }
+}
+
+__global__ void k_axis_D(FK k, O3 D)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i <= k.Nr) {
+        D.p[2][(size_t)i * k.ld + 0] = 0.0;
+        D.p[2][(size_t)i * k.ld + k.Nth] = 0.0;
+    }
+}
+
 }  // namespace fpic
+
+using namespace fpic;
+
+static Tabs tabs_of(const fpic_ctx* c)
+{
+    return Tabs{c->d_metric, c->metric_stride, c->ld};
+}
+
+extern "C" int fpic_sort(fpic_ctx* c, fpic_particles* p, void* stream)
+{
+    if (!c || !p) return set_error(FPIC_EINVAL, "fpic_sort: NULL argument");
+    if (!c->has_grid) return set_error(FPIC_EINVAL, "fpic_sort: no grid set");
+    if (p->n < 0 || p->n >= (1LL << 31)) return set_error(FPIC_EINVAL, "fpic_sort: n out of range");
+    if (p->n == 0) return FPIC_OK;
+    if (!particles_ok(p, true) || !p->w) return set_error(FPIC_EINVAL, "fpic_sort: NULL particle array");
+    FPIC_CUDA(cudaSetDevice(c->device));
+    Work w;
+    int rc = work_layout(c, p->n, false, w);
+    if (rc) return rc;
+    return sort_impl(c, p, w, (cudaStream_t)stream);
+}
+
+extern "C" int fpic_deposit(fpic_ctx* c, fpic_particles* p, double* rho, double* jr, double* jth, double* jph,
+                            void* stream)
+{
+    if (!c || !p || !rho || !jr || !jth || !jph) return set_error(FPIC_EINVAL, "fpic_deposit: NULL argument");
+    if (!c->has_grid) return set_error(FPIC_EINVAL, "fpic_deposit: no grid set");
+    if (p->n < 0 || p->n >= (1LL << 31)) return set_error(FPIC_EINVAL, "fpic_deposit: n out of range");
+    if (p->n > 0 && (!particles_ok(p, true) || !p->w)) return set_error(FPIC_EINVAL, "fpic_deposit: NULL particle array");
+    FPIC_CUDA(cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long n = p->n;
+    const uint32_t C = (uint32_t)c->Nr * (uint32_t)c->Nth;
+    Work w;
+    int rc = work_layout(c, n > 0 ? n : 1, true, w);
+    if (rc) return rc;
+    if (n > 0) {
+        rc = sort_impl(c, p, w, s);
+        if (rc) return rc;
+    } else {
+        FPIC_CUDA(cudaMemsetAsync(w.off, 0, 4 * ((size_t)C + 2), s));
+    }
+    // alive particles occupy [0, off[C]) after the sort; the count is read on the device
+    DepK k{c->bh, c->G, p->r, p->th, p->ur, p->uth, p->uph, p->qm, p->w, n, w.rec, w.code};
+    if (n > 0) {
+        // rec/code for all n slots; removed particles (past off[C]) are never summed
+        k_dep_particle<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(k);
+    }
+    k_dep_cell<<<(unsigned)(((long long)C * 32 + 255) / 256), 256, 0, s>>>(w.rec, w.code, w.off, w.part, n > 0 ? n : 1, C);
+    NodeK nk{c->Nr, c->Nth, c->ld, w.part, C, tabs_of(c), rho, jr, jth, jph};
+    k_dep_node<<<dim3(1, c->Nr + 1), 256, 0, s>>>(nk);
+    FPIC_CUDA(cudaGetLastError());
+    return FPIC_OK;
+}
+
+extern "C" int fpic_fdtd_step(fpic_ctx* c, fpic_fields* f, const fpic_fdtd_params* prm, int stage, void* stream)
+{
+    if (!c || !f || !prm) return set_error(FPIC_EINVAL, "fpic_fdtd_step: NULL argument");
+    if (!c->has_grid) return set_error(FPIC_EINVAL, "fpic_fdtd_step: no grid set");
+    if (stage != 1 && stage != 2) return set_error(FPIC_EINVAL, "fpic_fdtd_step: stage must be 1 or 2");
+    if (!std::isfinite(prm->dt) || !std::isfinite(prm->chi0) || prm->chi0 < 0.0 ||
+        (prm->chi0 > 0.0 && !(prm->r_max > prm->r_abs)))
+        return set_error(FPIC_EINVAL, "fpic_fdtd_step: bad dt or absorbing-layer parameters");
+    for (int k = 0; k < 3; ++k) {
+        const void* need[] = {f->B0[k], f->B1[k], f->D0[k], f->D1[k], f->j0[k], f->j1[k], f->E[k], f->H[k],
+                              f->Bh[k], f->Dw[k]};
+        for (const void* q : need)
+            if (!q) return set_error(FPIC_EINVAL, "fpic_fdtd_step: NULL field array");
+    }
+    if (!f->rho0 || !f->rho1) return set_error(FPIC_EINVAL, "fpic_fdtd_step: NULL rho array");
+    FPIC_CUDA(cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    FK k{c->Nr, c->Nth, c->ld, c->G, tabs_of(c), prm->dt, prm->chi0, prm->lambda, prm->r_abs, prm->r_max};
+    const size_t sz = (size_t)(c->Nr + 1) * c->ld;
+    const dim3 g2(1, c->Nr + 1);
+    const int TB = 256;
+    auto f3 = [](double* const a[3], double* const b[3]) {
+        F3 r;
+        for (int q = 0; q < 3; ++q) { r.a[q] = a[q]; r.b[q] = b ? b[q] : nullptr; }
+        return r;
+    };
+    auto o3 = [](double* const a[3]) { O3 r; for (int q = 0; q < 3; ++q) r.p[q] = a[q]; return r; };
+    if (stage == 1) {
+        // [1] E^{n+1} = alpha <D>^{n+1} + beta x B^{n+1}, <D> materialised in Dw
+        k_avg3<<<1024, TB, 0, s>>>(f3(f->D0, f->D1), o3(f->Dw), sz);
+        k_make_E<<<g2, TB, 0, s>>>(k, f3(f->Dw, nullptr), f3(f->B1, nullptr), o3(f->E));
+        // [2] B^{n+3/2} = <B>^{n+1/2} - dt curl E^{n+1}
+        k_update_B<<<g2, TB, 0, s>>>(k, f3(f->B0, f->B1), o3(f->E), o3(f->Bh));
+        // [3] E^{n+3/2}
+        k_make_E<<<g2, TB, 0, s>>>(k, f3(f->D1, nullptr), f3(f->Bh, nullptr), o3(f->E));
+        // [4] B^{n+2} = B^{n+1} - dt curl E^{n+3/2}  (into B0)
+        k_update_B<<<g2, TB, 0, s>>>(k, f3(f->B1, nullptr), o3(f->E), o3(f->B0));
+    } else {
+        // [7] H^{n+3/2} = alpha B^{n+3/2} - beta x D^{n+3/2}
+        k_make_H<<<g2, TB, 0, s>>>(k, f3(f->D1, nullptr), f3(f->Bh, nullptr), o3(f->H));
+        // [8] D^{n+2} = <D>^{n+1} + dt [curl H - 4 pi <J>^{n+3/2}]  (into Dw)
+        Src S0{{f->j0[0], f->j0[1], f->j0[2]}, f->rho0, 0.5}, S1{{f->j1[0], f->j1[1], f->j1[2]}, f->rho1, 0.5};
+        k_update_D<<<g2, TB, 0, s>>>(k, f3(f->D0, f->D1), o3(f->H), S0, S1, o3(f->Dw));
+        k_bc_D<<<g2, TB, 0, s>>>(k, o3(f->Dw));
+        k_axis_D<<<(c->Nr + 1 + 255) / 256, 256, 0, s>>>(k, o3(f->Dw));
+        // [9] H^{n+2} = alpha B^{n+2} - beta x D^{n+2}
+        k_make_H<<<g2, TB, 0, s>>>(k, f3(f->Dw, nullptr), f3(f->B0, nullptr), o3(f->H));
+        // [10] D^{n+5/2} = D^{n+3/2} + dt [curl H - 4 pi J^{n+2}]  (into D0)
+        S0.w = 0.0;
+        S1.w = 1.0;
+        k_update_D<<<g2, TB, 0, s>>>(k, f3(f->D1, nullptr), o3(f->H), S0, S1, o3(f->D0));
+        k_bc_D<<<g2, TB, 0, s>>>(k, o3(f->D0));
+        k_axis_D<<<(c->Nr + 1 + 255) / 256, 256, 0, s>>>(k, o3(f->D0));
+    }
+    FPIC_CUDA(cudaGetLastError());
+    return FPIC_OK;
+}

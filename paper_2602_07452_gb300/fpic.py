@@ -58,8 +58,25 @@ class fpic_push_stats(C.Structure):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
+_P3 = _D * 3
+
+
+class fpic_fields(C.Structure):
+    _fields_ = [("B0", _P3), ("B1", _P3), ("D0", _P3), ("D1", _P3), ("j0", _P3), ("rho0", _D),
+                ("j1", _P3), ("rho1", _D), ("E", _P3), ("H", _P3), ("Bh", _P3), ("Dw", _P3)]
+
+
+class fpic_fdtd_params(C.Structure):
+    _fields_ = [("dt", C.c_double), ("chi0", C.c_double), ("lam", C.c_double), ("r_abs", C.c_double),
+                ("r_max", C.c_double)]
+
+
 # name -> (restype, argtypes)
 _SIGS = {
+    "fpic_sort": (C.c_int, [C.c_void_p, C.POINTER(fpic_particles), C.c_void_p]),
+    "fpic_deposit": (C.c_int, [C.c_void_p, C.POINTER(fpic_particles), _D, _D, _D, _D, C.c_void_p]),
+    "fpic_fdtd_step": (C.c_int, [C.c_void_p, C.POINTER(fpic_fields), C.POINTER(fpic_fdtd_params), C.c_int,
+                                 C.c_void_p]),
     "fpic_init_metric": (C.c_int, [C.POINTER(C.c_void_p), C.c_double, C.c_double]),
     "fpic_destroy": (None, [C.c_void_p]),
     "fpic_last_error": (C.c_char_p, []),
@@ -298,3 +315,54 @@ def fpic_push_noalloc(M: float, a: float, p: Particles, prm: fpic_push_params, s
                                  _stream(stream))
     _check(rc)
     return st.as_dict() if st is not None else None
+
+
+def fpic_sort(ctx: Ctx, p: Particles, stream=None) -> None:
+    s = p.struct()
+    _check(lib().fpic_sort(ctx.handle, C.byref(s), _stream(stream)))
+
+
+def fpic_deposit(ctx: Ctx, p: Particles, size: int, out=None, stream=None):
+    """Returns (rho, j^r, j^th, j^ph) device arrays of the grid size."""
+    if out is None:
+        out = tuple(torch.zeros(size, dtype=torch.float64, device=p.r.device) for _ in range(4))
+    s = p.struct()
+    _check(lib().fpic_deposit(ctx.handle, C.byref(s), *[_dp(t) for t in out], _stream(stream)))
+    return out
+
+
+class Fields:
+    """Leapfrog field storage (device tensors) mirroring fpic_fields."""
+
+    NAMES3 = ("B0", "B1", "D0", "D1", "j0", "j1", "E", "H", "Bh", "Dw")
+
+    def __init__(self, size, device="cuda"):
+        z = lambda: [torch.zeros(size, dtype=torch.float64, device=device) for _ in range(3)]
+        for nm in self.NAMES3:
+            setattr(self, nm, z())
+        self.rho0 = torch.zeros(size, dtype=torch.float64, device=device)
+        self.rho1 = torch.zeros(size, dtype=torch.float64, device=device)
+
+    def struct(self):
+        p3 = lambda arrs: _P3(*[_dp(t) for t in arrs])
+        return fpic_fields(p3(self.B0), p3(self.B1), p3(self.D0), p3(self.D1), p3(self.j0), _dp(self.rho0),
+                           p3(self.j1), _dp(self.rho1), p3(self.E), p3(self.H), p3(self.Bh), p3(self.Dw))
+
+    def swap(self):
+        self.B0, self.B1 = self.B1, self.B0
+        self.D0, self.D1 = self.D1, self.D0
+        self.j0, self.j1 = self.j1, self.j0
+        self.rho0, self.rho1 = self.rho1, self.rho0
+
+    def push_fields(self):
+        """D^{n+3/2}, B^{n+3/2}: the fields of the push after stage 1."""
+        return [self.D1[0], self.D1[1], self.D1[2], self.Bh[0], self.Bh[1], self.Bh[2]]
+
+
+def fdtd_params(dt, chi0=0.0, lam=5.0, r_abs=0.0, r_max=1.0):
+    return fpic_fdtd_params(dt, chi0, lam, r_abs, r_max)
+
+
+def fpic_fdtd_step(ctx: Ctx, f: Fields, prm: fpic_fdtd_params, stage: int, stream=None) -> None:
+    s = f.struct()
+    _check(lib().fpic_fdtd_step(ctx.handle, C.byref(s), C.byref(prm), stage, _stream(stream)))

@@ -1,0 +1,187 @@
+"""GPU parity of the grid side (sort, deposit, FDTD) against the oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import pic as P
+from paper_2602_07452_gb300 import inputs as I
+from helpers import cuda_or_skip, dev, fpic, make_particles, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    cuda_or_skip()
+    return fpic()
+
+
+def _plasma(g, n, a, seed, dead_frac=0.1):
+    d, q, w = I.thermal_draws(n, g, g.rn[0], g.rn[-1], 0.5, seed=seed)
+    z = O.seed_fido(1.0, a, d)
+    rng = np.random.default_rng(seed)
+    w = rng.uniform(0.5, 2.0, n)
+    alive = (rng.random(n) > dead_frac).astype(np.uint8)
+    return z, q, w, alive
+
+
+def test_sort_is_the_stable_argsort(F):
+    """fpic_sort = stable sort by cell (removed particles last, in order),
+    applied to every array; bit-exact."""
+    a = 0.9
+    g = I.log_grid(37, 29, 1.5, 30.0)
+    ctx = F.fpic_init_metric(1.0, a)
+    F.fpic_set_grid(ctx, g)
+    n = 20011
+    z, q, w, alive = _plasma(g, n, a, 3, dead_frac=0.2)
+    p = make_particles(z, q, w=w, alive=alive)
+    p.Hn.copy_(dev(np.arange(n, dtype=float)))
+    F.fpic_sort(ctx, p)
+    cell = O.cell_index(g, z[:, 0], z[:, 1]).astype(np.int64)
+    key = np.where(alive == 1, cell, g.Nr * g.Nth)
+    perm = np.argsort(key, kind="stable")
+    zg = p.state().cpu().numpy()
+    assert np.array_equal(zg, z[perm])
+    assert np.array_equal(p.Hn.cpu().numpy(), perm.astype(float))
+    assert np.array_equal(p.alive.cpu().numpy(), alive[perm])
+    assert np.array_equal(p.cell.cpu().numpy().view(np.uint32), cell[perm].astype(np.uint32))
+
+
+@pytest.mark.parametrize("a", [0.0, 0.9])
+def test_deposit_matches_oracle(F, a):
+    """Sec. 2.3 deposit on a 48 x 40 grid, 30011 e-/e+ with random weights
+    and 10 % removed: every node of rho, j^r, j^th, j^ph within 1e-10 of the
+    oracle (relative to the node's sum of |Q W| scale), and bitwise
+    reproducible."""
+    g = I.log_grid(48, 40, 1.2 * I.horizon(1.0, a), 25.0)
+    ctx = F.fpic_init_metric(1.0, a)
+    F.fpic_set_grid(ctx, g)
+    n = 30011
+    z, q, w, alive = _plasma(g, n, a, 5)
+    ro = P.deposit(1.0, a, g, z, q, w, alive)
+    scale = P.deposit(1.0, a, g, z, np.abs(q), w, alive)[0]     # sum |Q| W / V per node
+    p = make_particles(z, q, w=w, alive=alive)
+    out = F.fpic_deposit(ctx, p, g.size)
+    got = [t.cpu().numpy() for t in out]
+    # rho, j^r, j^th, j^ph; |v| <= 1 so |Q v W| <= |Q| W
+    sc = np.maximum(scale, scale.max() * 1e-6)
+    for k in range(4):
+        mask = np.zeros((g.Nr + 1, g.ld), bool)
+        mask[: g.Nr + (0 if k == 1 else 1), : g.Nth + (0 if k == 2 else 1)] = True
+        m = mask.ravel()
+        err = np.abs(got[k] - ro[k])[m]
+        assert err.max() <= 1e-10 * sc.max(), (k, err.max())
+    # determinism: the same particles deposited again give identical bits
+    p2 = make_particles(z, q, w=w, alive=alive)
+    out2 = F.fpic_deposit(ctx, p2, g.size)
+    for x, y in zip(out, out2):
+        assert np.array_equal(x.cpu().numpy(), y.cpu().numpy())
+
+
+# (r, th) staggering of the components of each field family
+STAG = {"B": [(0, 1), (1, 0), (1, 1)], "D": [(1, 0), (0, 1), (0, 0)]}
+FAMILY = {"B0": "B", "B1": "B", "Bh": "B", "H": "B", "D0": "D", "D1": "D", "Dw": "D", "E": "D"}
+
+
+def valid(g, name, k):
+    """Mask of the entries a component actually uses (the rest is padding)."""
+    ro, to = STAG[FAMILY[name]][k]
+    m = np.zeros((g.Nr + 1, g.ld), bool)
+    m[: g.Nr + 1 - ro, : g.Nth + 1 - to] = True
+    return m.ravel()
+
+
+def _fill_random(state, fields, g, seed, sources=True):
+    rng = np.random.default_rng(seed)
+    names = ["B0", "B1", "D0", "D1"] + (["j0", "j1"] if sources else [])
+    for nm in names:
+        for k in range(3):
+            x = rng.normal(size=g.size)
+            getattr(state, nm)[k][:] = x
+            getattr(fields, nm)[k].copy_(dev(x))
+    if sources:
+        for nm in ("rho0", "rho1"):
+            x = rng.normal(size=g.size)
+            setattr(state, nm, x)
+            getattr(fields, nm).copy_(dev(x))
+
+
+@pytest.mark.parametrize("chi0", [0.0, 1e4])
+def test_fdtd_step_matches_oracle(F, chi0):
+    """Sub-steps 1-4 and 7-10 of Sec. 2.1 on a 40 x 32 grid with random fields
+    and sources (absorbing layer on/off): every array within 1e-12 of the
+    oracle relative to its magnitude."""
+    a = 0.9
+    g = I.log_grid(40, 32, 1.5, 30.0)
+    ctx = F.fpic_init_metric(1.0, a)
+    F.fpic_set_grid(ctx, g)
+    st = P.FdtdState(g)
+    fl = F.Fields(g.size)
+    _fill_random(st, fl, g, 9)
+    dt = 0.003
+    po = P.FdtdParams(1.0, a, dt, chi0, 5.0, 0.9 * g.rn[-1], g.rn[-1])
+    pg = F.fdtd_params(dt, chi0, 5.0, 0.9 * g.rn[-1], g.rn[-1])
+    for stage in (1, 2):
+        P.fdtd(po, st, stage)
+        F.fpic_fdtd_step(ctx, fl, pg, stage)
+        for nm in ("B0", "B1", "D0", "D1", "Bh", "Dw", "E", "H"):
+            if stage == 1 and nm in ("Dw",):
+                continue
+            for k in range(3):
+                m = valid(g, nm, k)
+                exp = getattr(st, nm)[k][m]
+                got = getattr(fl, nm)[k].cpu().numpy()[m]
+                sc = np.abs(exp).max() + 1e-300
+                assert np.abs(got - exp).max() <= 1e-12 * sc, (stage, nm, k, np.abs(got - exp).max() / sc)
+
+
+def test_full_pic_step_matches_oracle(F):
+    """One full GRPIC step in the paper's order (Sec. 2.1): FDTD stage 1,
+    RK4 push with D^{n+3/2}, B^{n+3/2}, deposit at n+2, FDTD stage 2 --
+    particles within 1e-12, fields within 1e-10 of the oracle."""
+    a = 0.9
+    g = I.log_grid(32, 28, 1.2 * I.horizon(1.0, a), 20.0)
+    ctx = F.fpic_init_metric(1.0, a)
+    F.fpic_set_grid(ctx, g)
+    Fw = O.wald_on_grid(a, 1.0, g)
+    st = P.FdtdState(g)
+    fl = F.Fields(g.size)
+    for k in range(3):
+        for nm, src in (("D0", Fw[k]), ("D1", Fw[k]), ("B0", Fw[3 + k]), ("B1", Fw[3 + k])):
+            getattr(st, nm)[k][:] = src
+            getattr(fl, nm)[k].copy_(dev(src))
+    n = 8009
+    z, q, w, alive = _plasma(g, n, a, 12, dead_frac=0.0)
+    dt = 1e-3
+    po = P.FdtdParams(1.0, a, dt, 1e4, 5.0, 0.9 * g.rn[-1], g.rn[-1])
+    pg = F.fdtd_params(dt, 1e4, 5.0, 0.9 * g.rn[-1], g.rn[-1])
+    # oracle
+    P.fdtd(po, st, 1)
+    Fpush = [st.D1[0], st.D1[1], st.D1[2], st.Bh[0], st.Bh[1], st.Bh[2]]
+    pp = O.push_params(a=a, dt=dt, scheme=O.RK4, field_kind=O.FIELD_GRID, r_max=g.rn[-1])
+    zo = np.ascontiguousarray(z.copy()); H0, _, D0 = O.hamiltonian(1.0, a, 0.0, z, q); Hn = H0.copy()
+    ao = np.ones(n, np.uint8)
+    O.push(pp, zo, q, H0, D0, Hn, ao, g, [np.ascontiguousarray(x) for x in Fpush])
+    rho, jr, jt, jp = P.deposit(1.0, a, g, zo, q, w, ao)
+    st.j1 = [jr, jt, jp]; st.rho1 = rho
+    P.fdtd(po, st, 2)
+    # GPU
+    p = make_particles(z, q, H0, D0, H0.copy(), w=w)
+    F.fpic_fdtd_step(ctx, fl, pg, 1)
+    F.fpic_push(ctx, p, fl.push_fields(), F.push_params(dt, scheme=F.FPIC_RK4, r_max=float(g.rn[-1])))
+    F.fpic_deposit(ctx, p, g.size, out=(fl.rho1, fl.j1[0], fl.j1[1], fl.j1[2]))
+    F.fpic_fdtd_step(ctx, fl, pg, 2)
+    # the deposit sorted the GPU particles: compare after sorting the oracle's the same way
+    cell = O.cell_index(g, zo[:, 0], zo[:, 1]).astype(np.int64)
+    key = np.where(ao == 1, cell, g.Nr * g.Nth)
+    perm = np.argsort(key, kind="stable")
+    zg = p.state().cpu().numpy()
+    err = (np.abs(zg - zo[perm]) / (np.abs(zo[perm]) + 1)).max()
+    assert err <= 1e-12, err
+    for nm in ("D0", "Dw", "B0", "Bh"):
+        for k in range(3):
+            m = valid(g, nm, k)
+            exp = getattr(st, nm)[k][m]; got = getattr(fl, nm)[k].cpu().numpy()[m]
+            assert np.abs(got - exp).max() <= 1e-10 * (np.abs(exp).max() + 1e-300), (nm, k)
