@@ -273,6 +273,42 @@ int fpic_deposit(fpic_ctx *ctx, fpic_particles *p, double *rho, double *jr, doub
  * 2, NULL array, dt not finite). */
 int fpic_fdtd_step(fpic_ctx *ctx, fpic_fields *f, const fpic_fdtd_params *prm, int stage, void *stream);
 
+/* ---- Learned implicit guess: MLP 14 -> 128 -> 128 -> 128 -> 9 --------------
+ * No counterpart in the paper (its method has no learned component): a
+ * network trained on the plain pusher's own steps predicts, per particle,
+ * the implicit step and whether the hybrid test would reject the RK4 trial;
+ * the push still accepts a step only by its own convergence and H tests.
+ * BF16 operands, FP32 accumulation in tensor memory (tcgen05).
+ * Parameter vector (FP32, device, fpic_mlp_nparams() entries):
+ *   W1 [128][14] b1 [128] W2 [128][128] b2 [128] W3 [128][128] b3 [128]
+ *   W4 [9][128] b4 [9]   (row-major [out][in], ReLU after layers 1-3). */
+typedef struct fpic_mlp fpic_mlp;
+
+/* Generic tensor-core GEMM C (+)= A B^T: A [M][lda] and B [N][ldb] bf16
+ * row-major (K contiguous, 16-byte aligned), C [M][ldc] FP32; N a multiple
+ * of 16 in [16, 256], K a multiple of 16.  accumulate != 0 adds into C.
+ * *err (device int) is set to 1 if a bounded tensor-core wait ran out.
+ * Errors: FPIC_EINVAL. */
+int fpic_mma_bf16(const uint16_t *A, int lda, const uint16_t *B, int ldb, float *C, int ldc, int M, int N, int K,
+                  int accumulate, int *err, void *stream);
+
+/* Create / destroy a network handle (library-owned bf16 weight buffers). */
+int fpic_mlp_create(fpic_mlp **m);
+void fpic_mlp_destroy(fpic_mlp *m);
+long long fpic_mlp_nparams(void);
+
+/* Load FP32 parameters P (device) into the handle's bf16 tensor-core layouts. */
+int fpic_mlp_set_params(fpic_mlp *m, const float *P, void *stream);
+
+/* Forward pass of B samples: X (device, B x 16 FP32: 14 standardised
+ * features then two zeros) -> Y (device, B x 16 FP32: 9 outputs then
+ * padding).  Errors: FPIC_EINVAL. */
+int fpic_mlp_forward(fpic_mlp *m, const float *X, float *Y, long long B, void *stream);
+
+/* Reads the handle's error word (synchronous): FPIC_ETIMEOUT if a bounded
+ * tensor-core wait of an earlier launch ran out, else FPIC_OK. */
+int fpic_mlp_status(fpic_mlp *m, int *status);
+
 #ifdef __cplusplus
 }
 #endif

@@ -73,6 +73,14 @@ class fpic_fdtd_params(C.Structure):
 
 # name -> (restype, argtypes)
 _SIGS = {
+    "fpic_mma_bf16": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_int,
+                                C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
+    "fpic_mlp_create": (C.c_int, [C.POINTER(C.c_void_p)]),
+    "fpic_mlp_destroy": (None, [C.c_void_p]),
+    "fpic_mlp_nparams": (C.c_longlong, []),
+    "fpic_mlp_set_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "fpic_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p]),
+    "fpic_mlp_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "fpic_sort": (C.c_int, [C.c_void_p, C.POINTER(fpic_particles), C.c_void_p]),
     "fpic_deposit": (C.c_int, [C.c_void_p, C.POINTER(fpic_particles), _D, _D, _D, _D, C.c_void_p]),
     "fpic_fdtd_step": (C.c_int, [C.c_void_p, C.POINTER(fpic_fields), C.POINTER(fpic_fdtd_params), C.c_int,
@@ -366,3 +374,53 @@ def fdtd_params(dt, chi0=0.0, lam=5.0, r_abs=0.0, r_max=1.0):
 def fpic_fdtd_step(ctx: Ctx, f: Fields, prm: fpic_fdtd_params, stage: int, stream=None) -> None:
     s = f.struct()
     _check(lib().fpic_fdtd_step(ctx.handle, C.byref(s), C.byref(prm), stage, _stream(stream)))
+
+
+def fpic_mma_bf16(A, B, C=None, accumulate=False, stream=None):
+    """C (+)= A @ B.T on the tensor cores; A [M,K], B [N,K] bf16 (cuda)."""
+    M, K = A.shape
+    N = B.shape[0]
+    if C is None:
+        C = torch.zeros(M, N, dtype=torch.float32, device=A.device)
+    err = torch.zeros(1, dtype=torch.int32, device=A.device)
+    _check(lib().fpic_mma_bf16(A.data_ptr(), A.stride(0), B.data_ptr(),
+                               B.stride(0), C.data_ptr(), C.stride(0), M, N, K, int(accumulate), err.data_ptr(),
+                               _stream(stream)))
+    return C, err
+
+
+class MLP:
+    """Handle of the learned-guess network (fpic_mlp)."""
+
+    def __init__(self):
+        h = C.c_void_p()
+        _check(lib().fpic_mlp_create(C.byref(h)))
+        self.handle = h
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            _lib.fpic_mlp_destroy(h)
+
+    @staticmethod
+    def nparams():
+        return int(lib().fpic_mlp_nparams())
+
+    def set_params(self, P, stream=None):
+        assert P.dtype == torch.float32 and P.is_cuda and P.numel() == self.nparams()
+        _check(lib().fpic_mlp_set_params(self.handle, P.data_ptr(), _stream(stream)))
+
+    def forward(self, X, Y=None, stream=None):
+        B = X.shape[0]
+        assert X.dtype == torch.float32 and X.shape[1] == 16 and X.is_contiguous()
+        if Y is None:
+            Y = torch.empty(B, 16, dtype=torch.float32, device=X.device)
+        _check(lib().fpic_mlp_forward(self.handle, X.data_ptr(), Y.data_ptr(), B, _stream(stream)))
+        return Y
+
+    def status(self):
+        st = C.c_int()
+        rc = lib().fpic_mlp_status(self.handle, C.byref(st))
+        if rc != 0:
+            raise FpicError(rc, lib().fpic_last_error().decode())
+        return st.value

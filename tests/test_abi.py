@@ -14,7 +14,7 @@ def _declared():
     for fn in os.listdir(os.path.join(ROOT, "include")):
         if fn.endswith(".h"):
             src = open(os.path.join(ROOT, "include", fn)).read()
-            names |= set(re.findall(r"^\s*(?:const\s+)?\w+\s*\**\s*(fpic_\w+)\s*\(", src, re.M))
+            names |= set(re.findall(r"^\s*(?:\w+\s+)+\**\s*(fpic_\w+)\s*\(", src, re.M))
     return sorted(names)
 
 
