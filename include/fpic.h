@@ -305,6 +305,26 @@ int fpic_mlp_set_params(fpic_mlp *m, const float *P, void *stream);
  * padding).  Errors: FPIC_EINVAL. */
 int fpic_mlp_forward(fpic_mlp *m, const float *X, float *Y, long long B, void *stream);
 
+/* Gradient of the training loss over a batch of B samples (B a power of two
+ * in [256, 2^24]): X (B x 16 features), T (B x 16 targets: outputs 0-5, 7,
+ * 8 regressed, 6 unused), S (B labels in {0, 1} for the scheme logit,
+ * output 6), lossw (9 host floats: weight of each regression output).
+ * Loss per sample = sum_k lossw_k (y_k - T_k)^2 + log(1 + e^{y_6}) - S y_6,
+ * averaged over the batch.  grad (device, fpic_mlp_nparams() FP32, the
+ * parameter layout); loss (host, nullable; synchronises when given).
+ * All GEMMs (forward and backward) run on the tensor cores.
+ * Errors: FPIC_EINVAL, FPIC_ENOMEM. */
+int fpic_mlp_grad(fpic_mlp *m, const float *X, const float *T, const float *S, const float *lossw, long long B,
+                  float *grad, float *loss, void *stream);
+
+/* One training step: gradient as fpic_mlp_grad, then Adam (Kingma & Ba)
+ * on the FP32 master parameters P with moments mom, vel (device, updated in
+ * place; step = 1, 2, ... is the Adam time step), then the handle's bf16
+ * weights are refreshed from P.  Errors: as fpic_mlp_grad. */
+int fpic_mlp_train_step(fpic_mlp *m, float *P, float *mom, float *vel, const float *X, const float *T,
+                        const float *S, const float *lossw, long long B, int step, float lr, float beta1,
+                        float beta2, float eps, float *loss, void *stream);
+
 /* Reads the handle's error word (synchronous): FPIC_ETIMEOUT if a bounded
  * tensor-core wait of an earlier launch ran out, else FPIC_OK. */
 int fpic_mlp_status(fpic_mlp *m, int *status);

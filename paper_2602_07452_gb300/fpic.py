@@ -81,6 +81,11 @@ _SIGS = {
     "fpic_mlp_set_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "fpic_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p]),
     "fpic_mlp_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    "fpic_mlp_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_float), C.c_longlong,
+                                C.c_void_p, C.POINTER(C.c_float), C.c_void_p]),
+    "fpic_mlp_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.POINTER(C.c_float), C.c_longlong, C.c_int, C.c_float, C.c_float,
+                                      C.c_float, C.c_float, C.POINTER(C.c_float), C.c_void_p]),
     "fpic_sort": (C.c_int, [C.c_void_p, C.POINTER(fpic_particles), C.c_void_p]),
     "fpic_deposit": (C.c_int, [C.c_void_p, C.POINTER(fpic_particles), _D, _D, _D, _D, C.c_void_p]),
     "fpic_fdtd_step": (C.c_int, [C.c_void_p, C.POINTER(fpic_fields), C.POINTER(fpic_fdtd_params), C.c_int,
@@ -417,6 +422,26 @@ class MLP:
             Y = torch.empty(B, 16, dtype=torch.float32, device=X.device)
         _check(lib().fpic_mlp_forward(self.handle, X.data_ptr(), Y.data_ptr(), B, _stream(stream)))
         return Y
+
+    def grad(self, X, T, S, lossw, stream=None):
+        """(loss, grad) of a batch; all tensors float32 cuda."""
+        B = X.shape[0]
+        g = torch.empty(self.nparams(), dtype=torch.float32, device=X.device)
+        lw = (C.c_float * 9)(*[float(v) for v in lossw])
+        L = C.c_float()
+        _check(lib().fpic_mlp_grad(self.handle, X.data_ptr(), T.data_ptr(), S.data_ptr(), lw, B, g.data_ptr(),
+                                   C.byref(L), _stream(stream)))
+        return L.value, g
+
+    def train_step(self, P, mom, vel, X, T, S, lossw, step, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, want_loss=False,
+                   stream=None):
+        B = X.shape[0]
+        lw = (C.c_float * 9)(*[float(v) for v in lossw])
+        L = C.c_float()
+        _check(lib().fpic_mlp_train_step(self.handle, P.data_ptr(), mom.data_ptr(), vel.data_ptr(), X.data_ptr(),
+                                         T.data_ptr(), S.data_ptr(), lw, B, step, lr, b1, b2, eps,
+                                         C.byref(L) if want_loss else None, _stream(stream)))
+        return L.value if want_loss else None
 
     def status(self):
         st = C.c_int()

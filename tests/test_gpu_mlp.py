@@ -63,3 +63,61 @@ def test_fused_forward_matches_oracle(F):
     err = np.abs(y - y_or)
     assert err.max() <= 2e-2 * scale, err.max() / scale
     assert err.mean() <= 2e-3 * scale
+
+
+def _batch(B, seed):
+    rng = np.random.default_rng(seed)
+    x = rng.normal(size=(B, 14))
+    t = np.zeros((B, 9)); t[:] = rng.normal(size=(B, 9)) * 0.5
+    s = (rng.random(B) < 0.3).astype(float)
+    lw = np.array([1, 1, 1, 1, 1, 1, 0, 0.1, 0.1])
+    return x, t, s, lw
+
+
+def _dev_batch(x, t, s):
+    B = x.shape[0]
+    X = torch.zeros(B, 16, dtype=torch.float32, device="cuda"); X[:, :14] = torch.tensor(x, dtype=torch.float32)
+    T = torch.zeros(B, 16, dtype=torch.float32, device="cuda"); T[:, :9] = torch.tensor(t, dtype=torch.float32)
+    S = torch.tensor(s, dtype=torch.float32, device="cuda")
+    return X, T, S
+
+
+def test_gradient_matches_oracle(F):
+    """Backward on the tensor cores (split-K weight gradients, ReLU masks,
+    bias column sums) against the oracle's bf16-operand / FP32-accumulate
+    backpropagation, batch 1024."""
+    P = M.init_params(11)
+    x, t, s, lw = _batch(1024, 12)
+    L_or, g_or = M.loss_grad(P, x, t, s, lw, mode=0)
+    net = F.MLP()
+    net.set_params(torch.tensor(P, dtype=torch.float32, device="cuda"))
+    X, T, S = _dev_batch(x, t, s)
+    L, g = net.grad(X, T, S, lw)
+    torch.cuda.synchronize()
+    assert net.status() == 0
+    g = g.double().cpu().numpy()
+    assert abs(L - L_or) <= 1e-3 * abs(L_or)
+    rel = np.linalg.norm(g - g_or) / np.linalg.norm(g_or)
+    assert rel <= 1e-2, rel
+    assert np.abs(g - g_or).max() <= 5e-2 * np.abs(g_or).max()
+
+
+def test_train_step_adam_and_learning(F):
+    """fpic_mlp_train_step = the tensor-core gradient followed by the oracle's
+    Adam step (same gradient), and repeated steps lower the loss."""
+    P = M.init_params(5).astype(np.float32)
+    x, t, s, lw = _batch(2048, 6)
+    net = F.MLP()
+    Pd = torch.tensor(P, device="cuda")
+    net.set_params(Pd)
+    X, T, S = _dev_batch(x, t, s)
+    L0, g = net.grad(X, T, S, lw)
+    mom = torch.zeros_like(Pd); vel = torch.zeros_like(Pd)
+    net.train_step(Pd, mom, vel, X, T, S, lw, step=1, lr=1e-3)
+    Pc = P.copy(); mc = np.zeros_like(P); vc = np.zeros_like(P)
+    M.adam(Pc, mc, vc, g.cpu().numpy().astype(np.float32), 1, 1e-3)
+    assert np.allclose(Pd.cpu().numpy(), Pc, rtol=1e-5, atol=1e-6)
+    for step in range(2, 60):
+        L = net.train_step(Pd, mom, vel, X, T, S, lw, step=step, lr=3e-3, want_loss=True)
+    assert L < 0.7 * L0, (L0, L)
+    assert net.status() == 0
