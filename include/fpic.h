@@ -167,6 +167,30 @@ int fpic_init_particles(fpic_ctx *ctx, fpic_particles *p, int kind, const double
 int fpic_push(fpic_ctx *ctx, fpic_particles *p, const double *const fields[6],
               const fpic_push_params *prm, fpic_push_stats *stats, void *stream);
 
+/* One run of a batched push: an independent spacetime (ctx: M, a and grid),
+ * its fields (device, or all NULL), its particle range [begin, end) in the
+ * batch's particle arrays, its outer removal radius and Wald potential B0. */
+typedef struct {
+    fpic_ctx *ctx;
+    const double *fields[6];
+    int64_t begin, end;
+    double r_max, B0pot;
+} fpic_run;
+
+/* Batched hybrid push (no counterpart in the paper): one explicit launch and
+ * one persistent implicit launch advance every run of the batch -- different
+ * spins, grids, fields and particle counts -- by one step, each particle
+ * with its own run's spacetime and fields, exactly as fpic_push would.
+ * runs[0..nruns) must tile [0, p->n) in order (runs[0].begin = 0,
+ * runs[i].begin = runs[i-1].end, runs[nruns-1].end = p->n); all contexts on
+ * the current device; prm is shared (its r_max and B0pot are ignored in
+ * favour of each run's).  The run table is staged through pinned memory
+ * owned by runs[0].ctx, so after one call outside capture the call can be
+ * captured in a CUDA graph and replayed.  Errors: FPIC_EINVAL, FPIC_ENOMEM,
+ * FPIC_ECUDA; FPIC_ENOTCONVERGED as fpic_push. */
+int fpic_push_batched(const fpic_run *runs, int nruns, fpic_particles *p, const fpic_push_params *prm,
+                      fpic_push_stats *stats, void *stream);
+
 /* fpic_push on a particle set held in HOST memory (pinned or pageable):
  * the arrays of *host_p are copied to library-owned device buffers, pushed
  * exactly as fpic_push does, and the state, Hn, alive, scheme, iters and
@@ -324,6 +348,50 @@ int fpic_mlp_grad(fpic_mlp *m, const float *X, const float *T, const float *S, c
 int fpic_mlp_train_step(fpic_mlp *m, float *P, float *mom, float *vel, const float *X, const float *T,
                         const float *S, const float *lossw, long long B, int step, float lr, float beta1,
                         float beta2, float eps, float *loss, void *stream);
+
+/* Configuration of the learned guess in the push.
+ *   feat_mean, feat_std : standardisation of the 14 features (x - mean)/std,
+ *     features = (ln r, th, u_r, u_th, u_ph, D^r, D^th, D^ph, B^r, B^th, B^ph
+ *     gathered at the particle, the current energy error (H^n - H_0)/D_0, the
+ *     fractional position of r in its cell, (q/m) dt), computed in FP32;
+ *   inc_scale : scale of the six implicit-step increments z^{n+1} - z^n
+ *     (network outputs 0-5 are increments / inc_scale);
+ *   p_skip : a particle whose predicted rejection probability sigmoid(y_6)
+ *     exceeds p_skip skips the RK4 trial and goes straight to the implicit
+ *     solve, started from z^n + inc_scale * y[0..5]. */
+typedef struct {
+    float feat_mean[16], feat_std[16];
+    double inc_scale[6];
+    float p_skip;
+} fpic_learned_cfg;
+
+/* Network inputs of every particle: X (device, n x 16 FP32, standardised
+ * with cfg; cfg NULL = raw features; removed particles get zeros).
+ * Errors: FPIC_EINVAL. */
+int fpic_features(fpic_ctx *ctx, const fpic_particles *p, const double *const fields[6], double dt,
+                  const fpic_learned_cfg *cfg, float *X, void *stream);
+
+/* Training samples from the plain method itself, leaving the particles
+ * unchanged: features X (as fpic_features), targets T (n x 16: outputs 0-5 =
+ * (z_implicit - z^n) / inc_scale with z_implicit the converged implicit step
+ * from the RK4 trial, output 7 = (iterations - 8)/4), labels S (n: 1 if the
+ * plain hybrid test (prm) rejects the RK4 trial).  Removed particles get
+ * zero rows.  prm->scheme must be FPIC_HYB1 or FPIC_HYB2 with the IMR
+ * partner.  Errors: FPIC_EINVAL, FPIC_ENOMEM. */
+int fpic_learn_sample(fpic_ctx *ctx, fpic_particles *p, const double *const fields[6], const fpic_push_params *prm,
+                      const fpic_learned_cfg *cfg, float *X, float *T, float *S, void *stream);
+
+/* Hybrid push with the learned guess: features -> network (tensor cores) ->
+ * particles predicted to be rejected go straight to the IMR (started from
+ * the predicted step), the others take the RK4 trial and the plain test
+ * (rejected ones -> IMR from the trial).  Every step is accepted only by the
+ * plain method's own tests: the H test for RK4 steps, convergence for
+ * implicit ones.  prm as fpic_push (scheme FPIC_HYB1/HYB2, implicit
+ * FPIC_IMR).  stats: as fpic_push; n_implicit includes the skipped ones.
+ * Errors: FPIC_EINVAL, FPIC_ENOMEM, FPIC_ECUDA. */
+int fpic_push_learned(fpic_ctx *ctx, fpic_mlp *m, fpic_particles *p, const double *const fields[6],
+                      const fpic_push_params *prm, const fpic_learned_cfg *cfg, fpic_push_stats *stats,
+                      void *stream);
 
 /* Reads the handle's error word (synchronous): FPIC_ETIMEOUT if a bounded
  * tensor-core wait of an earlier launch ran out, else FPIC_OK. */

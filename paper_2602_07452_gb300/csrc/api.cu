@@ -276,6 +276,8 @@ extern "C" void fpic_destroy(fpic_ctx* c)
     if (c->h_cnt) cudaFreeHost(c->h_cnt);
     if (c->d_scratch) cudaFree(c->d_scratch);
     if (c->d_scratch2) cudaFree(c->d_scratch2);
+    if (c->d_runs) cudaFree(c->d_runs);
+    if (c->h_runs) cudaFreeHost(c->h_runs);
     delete c;
 }
 

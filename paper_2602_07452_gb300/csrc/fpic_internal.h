@@ -30,6 +30,10 @@ struct fpic_ctx {
     // scratch grown on demand
     void* d_scratch = nullptr;
     size_t scratch_bytes = 0;
+    // batched push: run descriptors (pinned host staging + device copy)
+    void* h_runs = nullptr;
+    void* d_runs = nullptr;
+    int runs_cap = 0;
     // second scratch (sort / deposit)
     void* d_scratch2 = nullptr;
     size_t scratch2_bytes = 0;
@@ -38,13 +42,14 @@ struct fpic_ctx {
 namespace fpic {
 
 enum { CNT_QUEUE = 0, CNT_HEAD = 1, CNT_ITERS = 2, CNT_NOTCONV = 3, CNT_REMOVED = 4,
-       CNT_ALIVE = 5, CNT_EVALS = 6, CNT_ERR = 7, CNT_N = 8 };
+       CNT_ALIVE = 5, CNT_EVALS = 6, CNT_ERR = 7, CNT_WORK = 8, CNT_SKIP = 9, CNT_N = 10 };
 
 int set_error(int code, const char* fmt, ...);
 int check_cuda(cudaError_t e, const char* what);
 int ensure_scratch(fpic_ctx* c, size_t bytes);
 int ensure_scratch2(fpic_ctx* c, size_t bytes);
 bool particles_ok(const fpic_particles* p, bool need_state);
+int mlp_forward_dev(fpic_mlp* m, const float* X, float* Y, long long B, cudaStream_t s);
 
 }  // namespace fpic
 

@@ -512,11 +512,21 @@ static int mlp_forward_impl(fpic_mlp* m, const float* X, float* Y, uint16_t* H, 
     if (B == 0) return FPIC_OK;
     FwdK k{m->d, X, Y, H, B, m->err};
     const long long ntiles = (B + 127) / 128;
-    const unsigned grid = (unsigned)(ntiles < (long long)m->sm_count ? ntiles : m->sm_count);
+    // two CTAs per SM (108 KB of shared memory and 128 TMEM columns each) so
+    // one CTA's epilogue overlaps the other's MMAs
+    const long long cap = 2LL * m->sm_count;
+    const unsigned grid = (unsigned)(ntiles < cap ? ntiles : cap);
     k_mlp_fwd<<<grid, 128, FW_SMEM, s>>>(k);
     FPIC_CUDA(cudaGetLastError());
     return FPIC_OK;
 }
+
+namespace fpic {
+int mlp_forward_dev(fpic_mlp* m, const float* X, float* Y, long long B, cudaStream_t s)
+{
+    return mlp_forward_impl(m, X, Y, nullptr, B, s);
+}
+}  // namespace fpic
 
 extern "C" int fpic_mlp_forward(fpic_mlp* m, const float* X, float* Y, long long B, void* stream)
 {

@@ -13,6 +13,9 @@
 //   k_dg        discrete-gradient Hamiltonian scheme (geodesics), one thread
 //               per queued particle.
 #include <math.h>
+#include <string.h>
+
+#include <vector>
 
 #include "fpic_internal.h"
 
@@ -24,20 +27,33 @@ struct PartDev {
     uint32_t* cell;
 };
 
-struct PushK {
+// Parameters of one spacetime / grid / field set (one run of a batch).
+struct RunK {
     BH bh;
     GridDev G;
     Fields F;
     int has_fields;
     int has_grid;
-    double dt, thr, tol, dg_eps, B0pot, r_h, r_max;
+    double B0pot, r_h, r_max;
+    long long begin, end;     // particle range of the run (batched push)
+};
+
+struct PushK {
+    RunK run;
+    double dt, thr, tol, dg_eps;
     int scheme, max_iter;
     long long n;
     PartDev P;
     double* guess;          // 6 x n (SoA) implicit initial guesses
     uint32_t* queue;        // indices of particles for the implicit solver
     long long* cnt;
-    const float* learned;   // n x 8 learned guess (nullable)
+    const float* learned;   // n x 16 MLP outputs (nullable)
+    // learned / sampling extensions
+    uint32_t* work;         // explicit-pass work list (nullable: all particles)
+    int record;             // sampling mode: write targets, leave the particles unchanged
+    float* recT;            // n x 16 targets (sampling)
+    float* recS;            // n labels (sampling)
+    double inc_scale[6];    // scale of the implicit-step increments
 };
 
 __device__ __forceinline__ void load_state(const PartDev& P, long long p, double z[6])
@@ -63,16 +79,16 @@ __device__ __forceinline__ uint32_t cell_of(const GridDev& G, double r, double t
 }
 
 // Right-hand side at y: gathers the fields when the particle is charged.
-__device__ __forceinline__ void F_at(const PushK& k, const double y[6], double qm, bool em,
+__device__ __forceinline__ void F_at(const RunK& R, const double y[6], double qm, bool em,
                                      double f[6], double& H)
 {
     double D[3] = {0, 0, 0}, B[3] = {0, 0, 0};
-    if (em) gather(k.G, k.F, y[0], y[1], D, B);
-    eval_rhs(k.bh, y, qm, em, D, B, k.B0pot, f, H);
+    if (em) gather(R.G, R.F, y[0], y[1], D, B);
+    eval_rhs(R.bh, y, qm, em, D, B, R.B0pot, f, H);
 }
 
 // Particle boundaries (Sec. 2.5) and write-back of a finished step.
-__device__ __forceinline__ bool finish(const PushK& k, long long p, double z[6], double H,
+__device__ __forceinline__ bool finish(const RunK& R, const PartDev& P, long long p, double z[6], double H,
                                        int implicit, int iters)
 {
     if (z[1] < 0.0) {
@@ -84,13 +100,13 @@ __device__ __forceinline__ bool finish(const PushK& k, long long p, double z[6],
         z[4] = -z[4];
         z[2] += M_PI;
     }
-    const bool alive = (z[0] >= k.r_h) && (z[0] <= k.r_max);
-    store_state(k.P, p, z);
-    k.P.Hn[p] = H;
-    k.P.scheme[p] = (uint8_t)implicit;
-    k.P.iters[p] = (uint8_t)min(iters, 255);
-    k.P.alive[p] = alive ? 1 : 0;
-    if (k.P.cell) k.P.cell[p] = k.has_grid ? cell_of(k.G, z[0], z[1]) : 0u;
+    const bool alive = (z[0] >= R.r_h) && (z[0] <= R.r_max);
+    store_state(P, p, z);
+    P.Hn[p] = H;
+    P.scheme[p] = (uint8_t)implicit;
+    P.iters[p] = (uint8_t)min(iters, 255);
+    P.alive[p] = alive ? 1 : 0;
+    if (P.cell) P.cell[p] = R.has_grid ? cell_of(R.G, z[0], z[1]) : 0u;
     return alive;
 }
 
@@ -112,8 +128,14 @@ __device__ __forceinline__ void warp_add(long long* c, long long v, unsigned mas
 template <int MODE>
 __global__ void __launch_bounds__(128) k_explicit(PushK k)
 {
-    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (p >= k.n) return;
+    const long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long p = w;
+    if (k.work) {
+        if (w >= k.cnt[CNT_WORK]) return;
+        p = k.work[w];
+    } else if (p >= k.n) {
+        return;
+    }
     if (!k.P.alive[p]) {
         k.P.scheme[p] = 0;
         k.P.iters[p] = 0;
@@ -122,23 +144,23 @@ __global__ void __launch_bounds__(128) k_explicit(PushK k)
     double z0[6], kk[6], acc[6], y[6];
     load_state(k.P, p, z0);
     const double qm = k.P.qm[p];
-    const bool em = k.has_fields && qm != 0.0;
+    const bool em = k.run.has_fields && qm != 0.0;
     const double dt = k.dt, hdt = 0.5 * k.dt;
     double Hd;
-    F_at(k, z0, qm, em, kk, Hd);
+    F_at(k.run, z0, qm, em, kk, Hd);
 #pragma unroll
     for (int i = 0; i < 6; ++i) { acc[i] = kk[i]; y[i] = fma(hdt, kk[i], z0[i]); }
-    F_at(k, y, qm, em, kk, Hd);
+    F_at(k.run, y, qm, em, kk, Hd);
 #pragma unroll
     for (int i = 0; i < 6; ++i) { acc[i] = fma(2.0, kk[i], acc[i]); y[i] = fma(hdt, kk[i], z0[i]); }
-    F_at(k, y, qm, em, kk, Hd);
+    F_at(k.run, y, qm, em, kk, Hd);
 #pragma unroll
     for (int i = 0; i < 6; ++i) { acc[i] = fma(2.0, kk[i], acc[i]); y[i] = fma(dt, kk[i], z0[i]); }
-    F_at(k, y, qm, em, kk, Hd);
+    F_at(k.run, y, qm, em, kk, Hd);
     const double d6 = dt / 6.0;
 #pragma unroll
     for (int i = 0; i < 6; ++i) y[i] = fma(d6, acc[i] + kk[i], z0[i]);
-    const double H1 = eval_H(k.bh, y, qm, k.B0pot);
+    const double H1 = eval_H(k.run.bh, y, qm, k.run.B0pot);
     bool accept = true;
     if (MODE == 1) {
         const double H0 = k.P.H0[p], D0 = k.P.D0[p];
@@ -150,9 +172,13 @@ __global__ void __launch_bounds__(128) k_explicit(PushK k)
             accept = (Ht1 - Htn) / dt < k.thr;
         }
     }
+    if (k.record) {                 // sampling: label, then every particle goes implicit
+        k.recS[p] = accept ? 0.f : 1.f;
+        accept = false;
+    }
     const unsigned act = __activemask();
     const unsigned rej = __ballot_sync(act, !accept);
-    if (accept && !finish(k, p, y, H1, 0, 0))
+    if (accept && !finish(k.run, k.P, p, y, H1, 0, 0))
         atomicAdd((unsigned long long*)&k.cnt[CNT_REMOVED], 1ull);
     if (rej) {
         const int leader = __ffs(act) - 1;
@@ -220,7 +246,7 @@ __global__ void __launch_bounds__(128) k_imr(PushK k, int all_mode)
                             for (int i = 0; i < 6; ++i) zk[i] = k.guess[(size_t)i * k.n + p];
                         }
                         qm = k.P.qm[p];
-                        em = k.has_fields && qm != 0.0;
+                        em = k.run.has_fields && qm != 0.0;
                         it = 0;
                         fin = false;
                     }
@@ -243,7 +269,7 @@ __global__ void __launch_bounds__(128) k_imr(PushK k, int all_mode)
 #pragma unroll
                 for (int i = 0; i < 6; ++i) y[i] = 0.5 * (z0[i] + zk[i]);
             }
-            F_at(k, y, qm, em, f, H);
+            F_at(k.run, y, qm, em, f, H);
             ++n_ev;
             if (!fin) {
                 double zn[6];
@@ -258,7 +284,16 @@ __global__ void __launch_bounds__(128) k_imr(PushK k, int all_mode)
                     if (!ok) ++n_nc;
                 }
             } else {
-                if (!finish(k, p, zk, H, 1, it)) ++n_rm;
+                if (k.record) {
+                    float* t = k.recT + 16 * p;
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) t[i] = (float)((zk[i] - z0[i]) / k.inc_scale[i]);
+                    t[6] = 0.f;
+                    t[7] = (float)(it - 8) * 0.25f;
+                    t[8] = 0.f;
+                } else if (!finish(k.run, k.P, p, zk, H, 1, it)) {
+                    ++n_rm;
+                }
                 n_it += it;
                 p = -1;
             }
@@ -349,7 +384,7 @@ __global__ void __launch_bounds__(128) k_dg(PushK k, int all_mode)
             for (int i = 0; i < 6; ++i) zk[i] = k.guess[(size_t)i * k.n + p];
         }
         const double R0 = z0[0], T0 = z0[1], U0 = z0[3], V0 = z0[4], P = z0[5];
-        const GH m00 = gh_at(k.bh, R0, T0);
+        const GH m00 = gh_at(k.run.bh, R0, T0);
         const double Hz0 = gh_H(m00, U0, V0, P);
         const double f00 = gh_dHdup(m00, U0, V0, P);
         const double eps = k.dg_eps;
@@ -357,7 +392,7 @@ __global__ void __launch_bounds__(128) k_dg(PushK k, int all_mode)
         bool ok = false;
         while (it < k.max_iter) {
             const double R1 = zk[0], T1 = zk[1], U1 = zk[3], V1 = zk[4];
-            const GH m10 = gh_at(k.bh, R1, T0), m01 = gh_at(k.bh, R0, T1), m11 = gh_at(k.bh, R1, T1);
+            const GH m10 = gh_at(k.run.bh, R1, T0), m01 = gh_at(k.run.bh, R0, T1), m11 = gh_at(k.run.bh, R1, T1);
             const double dR = R1 - R0, dT = T1 - T0, dU = U1 - U0, dV = V1 - V0;
             const double Rm = 0.5 * (R0 + R1), Tm = 0.5 * (T0 + T1);
             const double Um = 0.5 * (U0 + U1), Vm = 0.5 * (V0 + V1);
@@ -366,7 +401,7 @@ __global__ void __launch_bounds__(128) k_dg(PushK k, int all_mode)
             const double B1 = gh_H(m00, U1, V0, P), B3 = gh_H(m10, U1, V1, P);
             const double C1 = gh_H(m01, U0, V0, P), C2 = gh_H(m01, U0, V1, P), C3 = gh_H(m11, U0, V1, P);
             const double D1 = gh_H(m00, U0, V1, P), D3 = gh_H(m01, U1, V1, P);
-            const BH& bh = k.bh;
+            const BH& bh = k.run.bh;
             // order A: r, u_r, th, u_th
             const double rA = dgq(bh, A1, Hz0, dR, eps, Rm, T0, U0, V0, P, 0);
             const double uA = dgq(bh, A2, A1, dU, eps, R1, T0, Um, V0, P, 3);
@@ -407,8 +442,8 @@ __global__ void __launch_bounds__(128) k_dg(PushK k, int all_mode)
         }
         if (!ok) ++n_nc;
         n_it += it;
-        const double H1 = eval_H(k.bh, zk, 0.0, 0.0);
-        if (!finish(k, p, zk, H1, 1, it)) ++n_rm;
+        const double H1 = eval_H(k.run.bh, zk, 0.0, 0.0);
+        if (!finish(k.run, k.P, p, zk, H1, 1, it)) ++n_rm;
     }
     const unsigned m = __activemask();
     warp_add(&k.cnt[CNT_ITERS], n_it, m);
@@ -456,18 +491,18 @@ extern "C" int fpic_push(fpic_ctx* c, fpic_particles* p, const double* const fie
     int rc = ensure_scratch(c, need);
     if (rc) return rc;
     PushK k{};
-    k.bh = c->bh;
-    k.G = c->G;
-    k.has_grid = c->has_grid;
-    k.has_fields = has_fields;
-    for (int i = 0; i < 6; ++i) k.F.f[i] = has_fields ? fields[i] : nullptr;
+    k.run.bh = c->bh;
+    k.run.G = c->G;
+    k.run.has_grid = c->has_grid;
+    k.run.has_fields = has_fields;
+    for (int i = 0; i < 6; ++i) k.run.F.f[i] = has_fields ? fields[i] : nullptr;
     k.dt = prm->dt;
     k.thr = prm->thr;
     k.tol = prm->tol;
     k.dg_eps = prm->dg_eps;
-    k.B0pot = prm->B0pot;
-    k.r_h = c->r_h;
-    k.r_max = prm->r_max;
+    k.run.B0pot = prm->B0pot;
+    k.run.r_h = c->r_h;
+    k.run.r_max = prm->r_max;
     k.scheme = prm->scheme;
     k.max_iter = prm->max_iter;
     k.n = n;
@@ -630,16 +665,16 @@ extern "C" int fpic_push_noalloc(double M, double a, fpic_particles* p, const fp
     const long long n = p->n;
     unsigned char* base = (unsigned char*)g_noalloc_dev_ptr[dev];
     PushK k{};
-    k.bh = BH{M, a, a * a, 2.0 * M};
-    k.has_grid = 0;
-    k.has_fields = 0;
+    k.run.bh = BH{M, a, a * a, 2.0 * M};
+    k.run.has_grid = 0;
+    k.run.has_fields = 0;
     k.dt = prm->dt;
     k.thr = prm->thr;
     k.tol = prm->tol;
     k.dg_eps = prm->dg_eps;
-    k.B0pot = prm->B0pot;
-    k.r_h = M + sqrt(M * M - a * a);
-    k.r_max = prm->r_max;
+    k.run.B0pot = prm->B0pot;
+    k.run.r_h = M + sqrt(M * M - a * a);
+    k.run.r_max = prm->r_max;
     k.scheme = prm->scheme;
     k.max_iter = prm->max_iter;
     k.n = n;
@@ -684,6 +719,595 @@ extern "C" int fpic_push_noalloc(double M, double a, fpic_particles* p, const fp
         stats->n_notconv = h[CNT_NOTCONV];
         stats->n_removed = h[CNT_REMOVED];
         stats->n_rhs_evals = h[CNT_EVALS] + (explicit_pass ? 4 * h[CNT_ALIVE] : 0);
+        if (h[CNT_NOTCONV] > 0) return FPIC_ENOTCONVERGED;
+    }
+    return FPIC_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Learned guess: features, sampling from the plain method, learned push.
+// ---------------------------------------------------------------------------
+namespace fpic {
+
+struct FeatK {
+    BH bh;
+    GridDev G;
+    Fields F;
+    int has_fields;
+    const double *r, *th, *ur, *uth, *uph, *qm, *H0, *D0, *Hn;
+    const uint8_t* alive;
+    long long n;
+    float dt;
+    float mean[16], istd[16];
+    float* X;
+    float* T;   // nullable: zero rows of removed particles
+    float* S;
+};
+
+__device__ __forceinline__ float lerp_f(const double* f, int ld, int i, int j, float wr, float wt)
+{
+    const double* q = f + (size_t)i * ld + j;
+    const float f00 = (float)__ldg(q), f01 = (float)__ldg(q + 1), f10 = (float)__ldg(q + ld), f11 = (float)__ldg(q + ld + 1);
+    const float lo = fmaf(wt, f01 - f00, f00), hi = fmaf(wt, f11 - f10, f10);
+    return fmaf(wr, hi - lo, lo);
+}
+
+__global__ void k_features(FeatK k)
+{
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= k.n) return;
+    float f[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) f[i] = 0.f;
+    if (!k.alive[p]) {
+        for (int i = 0; i < 16; ++i) k.X[p * 16 + i] = 0.f;
+        if (k.T) for (int i = 0; i < 16; ++i) k.T[p * 16 + i] = 0.f;
+        if (k.S) k.S[p] = 0.f;
+        return;
+    }
+    const double r = k.r[p], th = k.th[p];
+    const float rf = (float)r, tf = (float)th;
+    f[0] = __logf(rf);
+    f[1] = tf;
+    f[2] = (float)k.ur[p];
+    f[3] = (float)k.uth[p];
+    f[4] = (float)k.uph[p];
+    float wr_cell = 0.f;
+    if (k.has_fields) {
+        const GridDev& G = k.G;
+        int i0, i1, j0, j1;
+        double w0, w1, v0, v1;
+        const float lr = f[0];
+        locate(G.rn, G.irn, G.Nr + 1, r, (lr - G.lr0) * G.ilr, i0, w0);
+        locate(G.rh, G.irh, G.Nr, r, (lr - G.lrh0) * G.ilr, i1, w1);
+        locate(G.tn, G.itn, G.Nth + 1, th, (tf - G.t0) * G.it, j0, v0);
+        locate(G.th, G.ith, G.Nth, th, (tf - G.th0) * G.it, j1, v1);
+        const float a0 = (float)w0, a1 = (float)w1, b0 = (float)v0, b1 = (float)v1;
+        wr_cell = a0;
+        f[5] = lerp_f(k.F.f[0], G.ld, i1, j0, a1, b0);    // D^r  (i+1/2, j)
+        f[6] = lerp_f(k.F.f[1], G.ld, i0, j1, a0, b1);    // D^th (i, j+1/2)
+        f[7] = lerp_f(k.F.f[2], G.ld, i0, j0, a0, b0);    // D^ph (i, j)
+        f[8] = lerp_f(k.F.f[3], G.ld, i0, j1, a0, b1);    // B^r  (i, j+1/2)
+        f[9] = lerp_f(k.F.f[4], G.ld, i1, j0, a1, b0);    // B^th (i+1/2, j)
+        f[10] = lerp_f(k.F.f[5], G.ld, i1, j1, a1, b1);   // B^ph (i+1/2, j+1/2)
+    }
+    // the hybrid test depends on the current energy error and on where the
+    // particle sits in its cell (the interpolation error pattern)
+    f[11] = (float)((k.Hn[p] - k.H0[p]) / k.D0[p]);
+    f[12] = wr_cell;
+    f[13] = (float)k.qm[p] * k.dt;
+#pragma unroll
+    for (int i = 0; i < 14; ++i) k.X[p * 16 + i] = (f[i] - k.mean[i]) * k.istd[i];
+    k.X[p * 16 + 14] = 0.f;
+    k.X[p * 16 + 15] = 0.f;
+}
+
+// Route each alive particle: predicted rejected -> implicit queue (guess
+// z^n + scale * y), else -> explicit work list.
+__global__ void k_split(PushK k, float skip_logit)
+{
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= k.n) return;
+    if (!k.P.alive[p]) {
+        k.P.scheme[p] = 0;
+        k.P.iters[p] = 0;
+        return;
+    }
+    const float* y = k.learned + 16 * p;
+    const bool skip = y[6] > skip_logit;
+    const unsigned act = __activemask();
+    const unsigned sk = __ballot_sync(act, skip);
+    const int leader = __ffs(act) - 1;
+    const int lane = threadIdx.x & 31;
+    unsigned long long bq = 0, bw = 0;
+    if (lane == leader) {
+        if (sk) bq = atomicAdd((unsigned long long*)&k.cnt[CNT_QUEUE], (unsigned long long)__popc(sk));
+        const unsigned nw = __popc(act & ~sk);
+        if (nw) bw = atomicAdd((unsigned long long*)&k.cnt[CNT_WORK], (unsigned long long)nw);
+    }
+    bq = __shfl_sync(act, bq, leader);
+    bw = __shfl_sync(act, bw, leader);
+    if (skip) {
+        k.queue[bq + __popc(sk & lanemask_lt())] = (uint32_t)p;
+        const double z0[6] = {k.P.r[p], k.P.th[p], k.P.ph[p], k.P.ur[p], k.P.uth[p], k.P.uph[p]};
+#pragma unroll
+        for (int i = 0; i < 6; ++i) k.guess[(size_t)i * k.n + p] = fma(k.inc_scale[i], (double)y[i], z0[i]);
+    } else {
+        k.work[bw + __popc(act & ~sk & lanemask_lt())] = (uint32_t)p;
+    }
+}
+
+static bool push_prm_ok(const fpic_push_params* prm)
+{
+    return std::isfinite(prm->dt) && prm->dt != 0.0 && prm->scheme >= FPIC_HYB1 && prm->scheme <= FPIC_HYB2 &&
+           prm->implicit == FPIC_IMR && prm->max_iter >= 1 && prm->max_iter <= 255 && prm->tol >= 0.0;
+}
+
+static void fill_pushk(PushK& k, fpic_ctx* c, fpic_particles* p, const double* const fields[6],
+                       const fpic_push_params* prm)
+{
+    k.run.bh = c->bh;
+    k.run.G = c->G;
+    k.run.has_grid = c->has_grid;
+    k.run.has_fields = fields != nullptr;
+    for (int i = 0; i < 6; ++i) k.run.F.f[i] = fields ? fields[i] : nullptr;
+    k.dt = prm->dt;
+    k.thr = prm->thr;
+    k.tol = prm->tol;
+    k.dg_eps = prm->dg_eps;
+    k.run.B0pot = prm->B0pot;
+    k.run.r_h = c->r_h;
+    k.run.r_max = prm->r_max;
+    k.scheme = prm->scheme;
+    k.max_iter = prm->max_iter;
+    k.n = p->n;
+    k.P = PartDev{p->r, p->th, p->ph, p->ur, p->uth, p->uph, p->qm, p->H0, p->D0, p->Hn,
+                  p->alive, p->scheme, p->iters, p->cell};
+    k.cnt = c->d_cnt;
+}
+
+// scratch: guess 6n doubles | queue n | work n | X 16n floats | Y 16n floats
+static int learned_scratch(fpic_ctx* c, long long n, PushK& k, float** X, float** Y)
+{
+    const size_t need = (size_t)n * (6 * sizeof(double) + 2 * sizeof(uint32_t) + 32 * sizeof(float)) + 1024;
+    int rc = ensure_scratch(c, need);
+    if (rc) return rc;
+    char* b = (char*)c->d_scratch;
+    k.guess = (double*)b;
+    b += (size_t)n * 6 * sizeof(double);
+    k.queue = (uint32_t*)b;
+    b += (size_t)n * sizeof(uint32_t);
+    k.work = (uint32_t*)b;
+    b += (size_t)n * sizeof(uint32_t);
+    b = (char*)(((uintptr_t)b + 255) & ~(uintptr_t)255);
+    *X = (float*)b;
+    b += (size_t)n * 16 * sizeof(float);
+    *Y = (float*)b;
+    return 0;
+}
+
+static FeatK make_featk(fpic_ctx* c, const fpic_particles* p, const double* const fields[6], double dt,
+                        const fpic_learned_cfg* cfg, float* X)
+{
+    FeatK f{};
+    f.bh = c->bh;
+    f.G = c->G;
+    f.has_fields = fields != nullptr;
+    for (int i = 0; i < 6; ++i) f.F.f[i] = fields ? fields[i] : nullptr;
+    f.r = p->r; f.th = p->th; f.ur = p->ur; f.uth = p->uth; f.uph = p->uph; f.qm = p->qm;
+    f.H0 = p->H0; f.D0 = p->D0; f.Hn = p->Hn;
+    f.alive = p->alive;
+    f.n = p->n;
+    f.dt = (float)dt;
+    for (int i = 0; i < 16; ++i) {
+        f.mean[i] = cfg ? cfg->feat_mean[i] : 0.f;
+        const float sd = cfg ? cfg->feat_std[i] : 1.f;
+        f.istd[i] = sd > 0.f ? 1.f / sd : 1.f;
+    }
+    f.X = X;
+    return f;
+}
+
+}  // namespace fpic
+
+extern "C" int fpic_features(fpic_ctx* c, const fpic_particles* p, const double* const fields[6], double dt,
+                             const fpic_learned_cfg* cfg, float* X, void* stream)
+{
+    if (!c || !p || !X) return set_error(FPIC_EINVAL, "fpic_features: NULL argument");
+    if (p->n < 0) return set_error(FPIC_EINVAL, "fpic_features: n < 0");
+    if (fields && !c->has_grid) return set_error(FPIC_EINVAL, "fpic_features: fields given but no grid set");
+    if (p->n == 0) return FPIC_OK;
+    FPIC_CUDA(cudaSetDevice(c->device));
+    FeatK f = make_featk(c, p, fields, dt, cfg, X);
+    k_features<<<(unsigned)((p->n + 127) / 128), 128, 0, (cudaStream_t)stream>>>(f);
+    FPIC_CUDA(cudaGetLastError());
+    return FPIC_OK;
+}
+
+extern "C" int fpic_learn_sample(fpic_ctx* c, fpic_particles* p, const double* const fields[6],
+                                 const fpic_push_params* prm, const fpic_learned_cfg* cfg, float* X, float* T,
+                                 float* S, void* stream)
+{
+    if (!c || !p || !prm || !X || !T || !S) return set_error(FPIC_EINVAL, "fpic_learn_sample: NULL argument");
+    if (!push_prm_ok(prm)) return set_error(FPIC_EINVAL, "fpic_learn_sample: need a Hyb1/Hyb2 scheme with the IMR partner");
+    if (p->n < 0 || p->n >= (1LL << 31)) return set_error(FPIC_EINVAL, "fpic_learn_sample: n out of range");
+    if (!particles_ok(p, true)) return set_error(FPIC_EINVAL, "fpic_learn_sample: NULL particle array");
+    if (fields && !c->has_grid) return set_error(FPIC_EINVAL, "fpic_learn_sample: fields given but no grid set");
+    if (p->n == 0) return FPIC_OK;
+    FPIC_CUDA(cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long n = p->n;
+    PushK k{};
+    fill_pushk(k, c, p, fields, prm);
+    float *Xs, *Ys;
+    int rc = learned_scratch(c, n, k, &Xs, &Ys);
+    if (rc) return rc;
+    k.work = nullptr;
+    k.record = 1;
+    k.recT = T;
+    k.recS = S;
+    for (int i = 0; i < 6; ++i) k.inc_scale[i] = cfg ? cfg->inc_scale[i] : 1.0;
+    FPIC_CUDA(cudaMemsetAsync(c->d_cnt, 0, CNT_N * sizeof(long long), s));
+    FeatK f = make_featk(c, p, fields, prm->dt, cfg, X);
+    f.T = T;
+    f.S = S;
+    const unsigned nb = (unsigned)((n + 127) / 128);
+    k_features<<<nb, 128, 0, s>>>(f);
+    k_explicit<1><<<nb, 128, 0, s>>>(k);
+    k_imr<<<(unsigned)c->sm_count * 8u, 128, 0, s>>>(k, 0);
+    FPIC_CUDA(cudaGetLastError());
+    return FPIC_OK;
+}
+
+extern "C" int fpic_push_learned(fpic_ctx* c, fpic_mlp* m, fpic_particles* p, const double* const fields[6],
+                                 const fpic_push_params* prm, const fpic_learned_cfg* cfg, fpic_push_stats* stats,
+                                 void* stream)
+{
+    if (!c || !m || !p || !prm || !cfg) return set_error(FPIC_EINVAL, "fpic_push_learned: NULL argument");
+    if (!push_prm_ok(prm)) return set_error(FPIC_EINVAL, "fpic_push_learned: need a Hyb1/Hyb2 scheme with the IMR partner");
+    if (p->n < 0 || p->n >= (1LL << 31)) return set_error(FPIC_EINVAL, "fpic_push_learned: n out of range");
+    if (!particles_ok(p, true)) return set_error(FPIC_EINVAL, "fpic_push_learned: NULL particle array");
+    if (fields && !c->has_grid) return set_error(FPIC_EINVAL, "fpic_push_learned: fields given but no grid set");
+    if (!(cfg->p_skip > 0.f && cfg->p_skip < 1.f)) return set_error(FPIC_EINVAL, "fpic_push_learned: p_skip must be in (0, 1)");
+    FPIC_CUDA(cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long n = p->n;
+    PushK k{};
+    fill_pushk(k, c, p, fields, prm);
+    float *X, *Y;
+    int rc = learned_scratch(c, n > 0 ? n : 1, k, &X, &Y);
+    if (rc) return rc;
+    for (int i = 0; i < 6; ++i) k.inc_scale[i] = cfg->inc_scale[i];
+    k.learned = Y;
+    FPIC_CUDA(cudaMemsetAsync(c->d_cnt, 0, CNT_N * sizeof(long long), s));
+    if (n == 0) {
+        if (stats) *stats = fpic_push_stats{};
+        return FPIC_OK;
+    }
+    const unsigned nb = (unsigned)((n + 127) / 128);
+    const unsigned persist = (unsigned)c->sm_count * 8u;
+    cudaEvent_t* ev = prm->events ? (cudaEvent_t*)prm->events : nullptr;
+    if (stats) k_count_alive<<<persist, 256, 0, s>>>(k.P, n, c->d_cnt);
+    if (ev) FPIC_CUDA(cudaEventRecord(ev[0], s));
+    FeatK f = make_featk(c, p, fields, prm->dt, cfg, X);
+    k_features<<<nb, 128, 0, s>>>(f);
+    rc = mlp_forward_dev(m, X, Y, n, s);
+    if (rc) return rc;
+    const float skip_logit = logf(cfg->p_skip / (1.f - cfg->p_skip));
+    k_split<<<nb, 128, 0, s>>>(k, skip_logit);
+    k_explicit<1><<<nb, 128, 0, s>>>(k);
+    if (ev) {
+        FPIC_CUDA(cudaEventRecord(ev[1], s));
+        FPIC_CUDA(cudaEventRecord(ev[2], s));
+    }
+    k.work = nullptr;
+    k_imr<<<persist, 128, 0, s>>>(k, 0);
+    if (ev) FPIC_CUDA(cudaEventRecord(ev[3], s));
+    FPIC_CUDA(cudaGetLastError());
+    if (stats) {
+        FPIC_CUDA(cudaMemcpyAsync(c->h_cnt, c->d_cnt, CNT_N * sizeof(long long), cudaMemcpyDeviceToHost, s));
+        FPIC_CUDA(cudaStreamSynchronize(s));
+        const long long* h = c->h_cnt;
+        stats->n_alive_before = h[CNT_ALIVE];
+        stats->n_implicit = h[CNT_QUEUE];
+        stats->n_iter_total = h[CNT_ITERS];
+        stats->n_notconv = h[CNT_NOTCONV];
+        stats->n_removed = h[CNT_REMOVED];
+        stats->n_rhs_evals = h[CNT_EVALS] + 4 * h[CNT_WORK];
+        if (h[CNT_NOTCONV] > 0) return FPIC_ENOTCONVERGED;
+    }
+    return FPIC_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Batched push: many independent runs (spacetime, grid, fields, particle
+// range) in one explicit launch and one persistent implicit launch.
+// ---------------------------------------------------------------------------
+namespace fpic {
+
+struct BatchK {
+    const RunK* runs;
+    int nruns;
+    PushK k;        // shared step parameters (its run member is unused)
+};
+
+__device__ __forceinline__ int run_of(const RunK* __restrict__ runs, int nruns, long long p)
+{
+    int lo = 0, hi = nruns - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (runs[mid].begin <= p) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(128) k_explicit_batched(const __grid_constant__ BatchK B)
+{
+    const PushK& k = B.k;
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= k.n) return;
+    if (!k.P.alive[p]) {
+        k.P.scheme[p] = 0;
+        k.P.iters[p] = 0;
+        return;
+    }
+    const RunK& R = B.runs[run_of(B.runs, B.nruns, p)];
+    double z0[6], kk[6], acc[6], y[6];
+    load_state(k.P, p, z0);
+    const double qm = k.P.qm[p];
+    const bool em = R.has_fields && qm != 0.0;
+    const double dt = k.dt, hdt = 0.5 * k.dt;
+    double Hd;
+    F_at(R, z0, qm, em, kk, Hd);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) { acc[i] = kk[i]; y[i] = fma(hdt, kk[i], z0[i]); }
+    F_at(R, y, qm, em, kk, Hd);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) { acc[i] = fma(2.0, kk[i], acc[i]); y[i] = fma(hdt, kk[i], z0[i]); }
+    F_at(R, y, qm, em, kk, Hd);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) { acc[i] = fma(2.0, kk[i], acc[i]); y[i] = fma(dt, kk[i], z0[i]); }
+    F_at(R, y, qm, em, kk, Hd);
+    const double d6 = dt / 6.0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) y[i] = fma(d6, acc[i] + kk[i], z0[i]);
+    const double H1 = eval_H(R.bh, y, qm, R.B0pot);
+    bool accept = true;
+    if (k.scheme >= FPIC_HYB1) {
+        const double H0 = k.P.H0[p], D0 = k.P.D0[p];
+        const double Ht1 = fabs(H1 - H0) / D0;
+        if (k.scheme == FPIC_HYB2) {
+            accept = Ht1 < k.thr;
+        } else {
+            const double Htn = fabs(k.P.Hn[p] - H0) / D0;
+            accept = (Ht1 - Htn) / dt < k.thr;
+        }
+    }
+    const unsigned act = __activemask();
+    const unsigned rej = __ballot_sync(act, !accept);
+    if (accept && !finish(R, k.P, p, y, H1, 0, 0))
+        atomicAdd((unsigned long long*)&k.cnt[CNT_REMOVED], 1ull);
+    if (rej) {
+        const int leader = __ffs(act) - 1;
+        unsigned long long base = 0;
+        if ((int)(threadIdx.x & 31) == leader)
+            base = atomicAdd((unsigned long long*)&k.cnt[CNT_QUEUE], (unsigned long long)__popc(rej));
+        base = __shfl_sync(act, base, leader);
+        if (!accept) {
+            const unsigned long long idx = base + __popc(rej & lanemask_lt());
+            k.queue[idx] = (uint32_t)p;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) k.guess[(size_t)i * k.n + p] = y[i];
+        }
+    }
+}
+
+// Persistent lane-refilling IMR over the batch's queue; each lane carries
+// the run of its current particle.
+__global__ void __launch_bounds__(128) k_imr_batched(const __grid_constant__ BatchK B, int all_mode)
+{
+    const PushK& k = B.k;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const long long qn = all_mode ? k.n : k.cnt[CNT_QUEUE];
+    long long p = -1;
+    const RunK* R = B.runs;
+    bool exhausted = false, fin = false;
+    double z0[6], zk[6];
+    double qm = 0.0;
+    bool em = false;
+    int it = 0;
+    long long n_it = 0, n_nc = 0, n_ev = 0, n_rm = 0;
+    for (;;) {
+        const bool need = (p < 0) && !exhausted;
+        const unsigned nm = __ballot_sync(FULL, need);
+        if (nm) {
+            const int leader = __ffs(nm) - 1;
+            unsigned long long base = 0;
+            if (lane == leader)
+                base = atomicAdd((unsigned long long*)&k.cnt[CNT_HEAD], (unsigned long long)__popc(nm));
+            base = __shfl_sync(FULL, base, leader);
+            if (need) {
+                const long long idx = (long long)(base + __popc(nm & lanemask_lt()));
+                if (idx < qn) {
+                    const long long q = all_mode ? idx : (long long)k.queue[idx];
+                    if (all_mode && !k.P.alive[q]) {
+                        k.P.scheme[q] = 0;
+                        k.P.iters[q] = 0;
+                    } else {
+                        p = q;
+                        R = B.runs + run_of(B.runs, B.nruns, p);
+                        load_state(k.P, p, z0);
+#pragma unroll
+                        for (int i = 0; i < 6; ++i) zk[i] = all_mode ? z0[i] : k.guess[(size_t)i * k.n + p];
+                        qm = k.P.qm[p];
+                        em = R->has_fields && qm != 0.0;
+                        it = 0;
+                        fin = false;
+                    }
+                } else {
+                    exhausted = true;
+                }
+            }
+        }
+        const unsigned busy = __ballot_sync(FULL, p >= 0);
+        if (!busy) {
+            if (!__ballot_sync(FULL, !exhausted)) break;
+            continue;
+        }
+        if (p >= 0) {
+            double y[6], f[6], H;
+            if (fin) {
+#pragma unroll
+                for (int i = 0; i < 6; ++i) y[i] = zk[i];
+            } else {
+#pragma unroll
+                for (int i = 0; i < 6; ++i) y[i] = 0.5 * (z0[i] + zk[i]);
+            }
+            F_at(*R, y, qm, em, f, H);
+            ++n_ev;
+            if (!fin) {
+                double zn[6];
+#pragma unroll
+                for (int i = 0; i < 6; ++i) zn[i] = fma(k.dt, f[i], z0[i]);
+                const bool ok = conv6(zn, zk, k.tol);
+#pragma unroll
+                for (int i = 0; i < 6; ++i) zk[i] = zn[i];
+                ++it;
+                if (ok || it >= k.max_iter) {
+                    fin = true;
+                    if (!ok) ++n_nc;
+                }
+            } else {
+                if (!finish(*R, k.P, p, zk, H, 1, it)) ++n_rm;
+                n_it += it;
+                p = -1;
+            }
+        }
+    }
+    warp_add(&k.cnt[CNT_ITERS], n_it, FULL);
+    warp_add(&k.cnt[CNT_NOTCONV], n_nc, FULL);
+    warp_add(&k.cnt[CNT_EVALS], n_ev, FULL);
+    warp_add(&k.cnt[CNT_REMOVED], n_rm, FULL);
+}
+
+}  // namespace fpic
+
+extern "C" int fpic_push_batched(const fpic_run* runs, int nruns, fpic_particles* p, const fpic_push_params* prm,
+                                 fpic_push_stats* stats, void* stream)
+{
+    if (!runs || nruns < 1 || !p || !prm) return set_error(FPIC_EINVAL, "fpic_push_batched: NULL argument or nruns < 1");
+    if (p->n < 0 || p->n >= (1LL << 31)) return set_error(FPIC_EINVAL, "fpic_push_batched: n out of range");
+    if (!particles_ok(p, true)) return set_error(FPIC_EINVAL, "fpic_push_batched: NULL particle array");
+    if (!(std::isfinite(prm->dt)) || prm->dt == 0.0) return set_error(FPIC_EINVAL, "fpic_push_batched: bad dt");
+    if (prm->scheme != FPIC_RK4 && prm->scheme != FPIC_IMR && prm->scheme != FPIC_HYB1 && prm->scheme != FPIC_HYB2)
+        return set_error(FPIC_EINVAL, "fpic_push_batched: scheme must be RK4, IMR, Hyb1 or Hyb2");
+    if (prm->scheme >= FPIC_HYB1 && prm->implicit != FPIC_IMR)
+        return set_error(FPIC_EINVAL, "fpic_push_batched: the implicit partner must be FPIC_IMR");
+    if (prm->max_iter < 1 || prm->max_iter > 255 || !(prm->tol >= 0.0))
+        return set_error(FPIC_EINVAL, "fpic_push_batched: bad max_iter or tol");
+    fpic_ctx* c = runs[0].ctx;
+    if (!c) return set_error(FPIC_EINVAL, "fpic_push_batched: runs[0].ctx is NULL");
+    for (int i = 0; i < nruns; ++i) {
+        const fpic_run& r = runs[i];
+        if (!r.ctx || r.ctx->device != c->device) return set_error(FPIC_EINVAL, "fpic_push_batched: run %d: bad ctx", i);
+        if (r.begin != (i == 0 ? 0 : runs[i - 1].end) || r.end < r.begin)
+            return set_error(FPIC_EINVAL, "fpic_push_batched: runs must tile [0, n) in order (run %d)", i);
+        const int nf = (r.fields[0] != nullptr) + (r.fields[1] != nullptr) + (r.fields[2] != nullptr) +
+                       (r.fields[3] != nullptr) + (r.fields[4] != nullptr) + (r.fields[5] != nullptr);
+        if (nf != 0 && nf != 6) return set_error(FPIC_EINVAL, "fpic_push_batched: run %d: give all six fields or none", i);
+        if (nf == 6 && !r.ctx->has_grid) return set_error(FPIC_EINVAL, "fpic_push_batched: run %d: fields but no grid", i);
+    }
+    if (runs[nruns - 1].end != p->n) return set_error(FPIC_EINVAL, "fpic_push_batched: the runs must end at n");
+    FPIC_CUDA(cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long n = p->n;
+    if (c->runs_cap < nruns) {
+        if (c->d_runs) FPIC_CUDA(cudaFree(c->d_runs));
+        if (c->h_runs) FPIC_CUDA(cudaFreeHost(c->h_runs));
+        c->d_runs = nullptr;
+        c->h_runs = nullptr;
+        c->runs_cap = 0;
+        FPIC_CUDA(cudaMalloc(&c->d_runs, sizeof(RunK) * nruns));
+        FPIC_CUDA(cudaMallocHost(&c->h_runs, sizeof(RunK) * nruns));
+        c->runs_cap = nruns;
+    }
+    int rc = ensure_scratch(c, (size_t)(n > 0 ? n : 1) * (6 * sizeof(double) + sizeof(uint32_t)) + 256);
+    if (rc) return rc;
+    std::vector<RunK> tab(nruns);
+    for (int i = 0; i < nruns; ++i) {
+        const fpic_run& r = runs[i];
+        RunK R{};
+        R.bh = r.ctx->bh;
+        R.G = r.ctx->G;
+        R.has_grid = r.ctx->has_grid;
+        R.has_fields = r.fields[0] != nullptr;
+        for (int q = 0; q < 6; ++q) R.F.f[q] = r.fields[q];
+        R.B0pot = r.B0pot;
+        R.r_h = r.ctx->r_h;
+        R.r_max = r.r_max;
+        R.begin = r.begin;
+        R.end = r.end;
+        tab[i] = R;
+    }
+    // The pinned staging table is rewritten only when it changes; outside a
+    // stream capture the previous asynchronous copy out of it is waited for
+    // first.  (A captured graph reads the table at replay time.)
+    if (memcmp(c->h_runs, tab.data(), sizeof(RunK) * nruns) != 0) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        FPIC_CUDA(cudaStreamIsCapturing(s, &cs));
+        if (cs == cudaStreamCaptureStatusNone) FPIC_CUDA(cudaStreamSynchronize(s));
+        memcpy(c->h_runs, tab.data(), sizeof(RunK) * nruns);
+    }
+    FPIC_CUDA(cudaMemcpyAsync(c->d_runs, c->h_runs, sizeof(RunK) * nruns, cudaMemcpyHostToDevice, s));
+    BatchK B{};
+    B.runs = (const RunK*)c->d_runs;
+    B.nruns = nruns;
+    PushK& k = B.k;
+    k.dt = prm->dt;
+    k.thr = prm->thr;
+    k.tol = prm->tol;
+    k.dg_eps = prm->dg_eps;
+    k.scheme = prm->scheme;
+    k.max_iter = prm->max_iter;
+    k.n = n;
+    k.P = PartDev{p->r, p->th, p->ph, p->ur, p->uth, p->uph, p->qm, p->H0, p->D0, p->Hn,
+                  p->alive, p->scheme, p->iters, p->cell};
+    k.guess = (double*)c->d_scratch;
+    k.queue = (uint32_t*)((char*)c->d_scratch + (size_t)(n > 0 ? n : 1) * 6 * sizeof(double));
+    k.cnt = c->d_cnt;
+    FPIC_CUDA(cudaMemsetAsync(c->d_cnt, 0, CNT_N * sizeof(long long), s));
+    if (n == 0) {
+        if (stats) *stats = fpic_push_stats{};
+        return FPIC_OK;
+    }
+    const unsigned nb = (unsigned)((n + 127) / 128);
+    const unsigned persist = (unsigned)c->sm_count * 8u;
+    cudaEvent_t* ev = prm->events ? (cudaEvent_t*)prm->events : nullptr;
+    if (stats) k_count_alive<<<persist, 256, 0, s>>>(k.P, n, c->d_cnt);
+    if (ev) FPIC_CUDA(cudaEventRecord(ev[0], s));
+    if (prm->scheme != FPIC_IMR) k_explicit_batched<<<nb, 128, 0, s>>>(B);
+    if (ev) {
+        FPIC_CUDA(cudaEventRecord(ev[1], s));
+        FPIC_CUDA(cudaEventRecord(ev[2], s));
+    }
+    if (prm->scheme == FPIC_IMR) k_imr_batched<<<persist, 128, 0, s>>>(B, 1);
+    else if (prm->scheme >= FPIC_HYB1) k_imr_batched<<<persist, 128, 0, s>>>(B, 0);
+    if (ev) FPIC_CUDA(cudaEventRecord(ev[3], s));
+    FPIC_CUDA(cudaGetLastError());
+    if (stats) {
+        FPIC_CUDA(cudaMemcpyAsync(c->h_cnt, c->d_cnt, CNT_N * sizeof(long long), cudaMemcpyDeviceToHost, s));
+        FPIC_CUDA(cudaStreamSynchronize(s));
+        const long long* h = c->h_cnt;
+        stats->n_alive_before = h[CNT_ALIVE];
+        stats->n_implicit = prm->scheme == FPIC_RK4 ? 0 : (prm->scheme >= FPIC_HYB1 ? h[CNT_QUEUE] : h[CNT_ALIVE]);
+        stats->n_iter_total = h[CNT_ITERS];
+        stats->n_notconv = h[CNT_NOTCONV];
+        stats->n_removed = h[CNT_REMOVED];
+        stats->n_rhs_evals = h[CNT_EVALS] + (prm->scheme != FPIC_IMR ? 4 * h[CNT_ALIVE] : 0);
         if (h[CNT_NOTCONV] > 0) return FPIC_ENOTCONVERGED;
     }
     return FPIC_OK;

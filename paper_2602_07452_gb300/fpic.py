@@ -71,8 +71,27 @@ class fpic_fdtd_params(C.Structure):
                 ("r_max", C.c_double)]
 
 
+class fpic_run(C.Structure):
+    _fields_ = [("ctx", C.c_void_p), ("fields", _D * 6), ("begin", C.c_int64), ("end", C.c_int64),
+                ("r_max", C.c_double), ("B0pot", C.c_double)]
+
+
+class fpic_learned_cfg(C.Structure):
+    _fields_ = [("feat_mean", C.c_float * 16), ("feat_std", C.c_float * 16), ("inc_scale", C.c_double * 6),
+                ("p_skip", C.c_float)]
+
+
 # name -> (restype, argtypes)
 _SIGS = {
+    "fpic_push_batched": (C.c_int, [C.POINTER(fpic_run), C.c_int, C.POINTER(fpic_particles),
+                                    C.POINTER(fpic_push_params), C.POINTER(fpic_push_stats), C.c_void_p]),
+    "fpic_features": (C.c_int, [C.c_void_p, C.POINTER(fpic_particles), C.POINTER(_D), C.c_double,
+                                C.POINTER(fpic_learned_cfg), C.c_void_p, C.c_void_p]),
+    "fpic_learn_sample": (C.c_int, [C.c_void_p, C.POINTER(fpic_particles), C.POINTER(_D), C.POINTER(fpic_push_params),
+                                    C.POINTER(fpic_learned_cfg), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "fpic_push_learned": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(fpic_particles), C.POINTER(_D),
+                                    C.POINTER(fpic_push_params), C.POINTER(fpic_learned_cfg),
+                                    C.POINTER(fpic_push_stats), C.c_void_p]),
     "fpic_mma_bf16": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_int,
                                 C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "fpic_mlp_create": (C.c_int, [C.POINTER(C.c_void_p)]),
@@ -449,3 +468,64 @@ class MLP:
         if rc != 0:
             raise FpicError(rc, lib().fpic_last_error().decode())
         return st.value
+
+
+def learned_cfg(feat_mean=None, feat_std=None, inc_scale=None, p_skip=0.5):
+    cfg = fpic_learned_cfg()
+    for i in range(16):
+        cfg.feat_mean[i] = 0.0 if feat_mean is None or i >= len(feat_mean) else float(feat_mean[i])
+        cfg.feat_std[i] = 1.0 if feat_std is None or i >= len(feat_std) else float(feat_std[i])
+    for i in range(6):
+        cfg.inc_scale[i] = 1.0 if inc_scale is None else float(inc_scale[i])
+    cfg.p_skip = p_skip
+    return cfg
+
+
+def fpic_features(ctx: Ctx, p: Particles, fields, dt, cfg=None, stream=None):
+    X = torch.empty(p.n, 16, dtype=torch.float32, device=p.r.device)
+    s = p.struct()
+    _check(lib().fpic_features(ctx.handle, C.byref(s), _fields_arg(fields), dt,
+                               C.byref(cfg) if cfg is not None else None, X.data_ptr(), _stream(stream)))
+    return X
+
+
+def fpic_learn_sample(ctx: Ctx, p: Particles, fields, prm, cfg=None, stream=None):
+    """(X, T, S) training samples from the plain method; particles unchanged."""
+    X = torch.empty(p.n, 16, dtype=torch.float32, device=p.r.device)
+    T = torch.zeros(p.n, 16, dtype=torch.float32, device=p.r.device)
+    S = torch.empty(p.n, dtype=torch.float32, device=p.r.device)
+    s = p.struct()
+    _check(lib().fpic_learn_sample(ctx.handle, C.byref(s), _fields_arg(fields), C.byref(prm),
+                                   C.byref(cfg) if cfg is not None else None, X.data_ptr(), T.data_ptr(),
+                                   S.data_ptr(), _stream(stream)))
+    return X, T, S
+
+
+def fpic_push_learned(ctx: Ctx, net: "MLP", p: Particles, fields, prm, cfg, stats=False, stream=None):
+    s = p.struct()
+    st = fpic_push_stats() if stats else None
+    rc = lib().fpic_push_learned(ctx.handle, net.handle, C.byref(s), _fields_arg(fields), C.byref(prm),
+                                 C.byref(cfg), C.byref(st) if st is not None else None, _stream(stream))
+    _check(rc)
+    return st.as_dict() if st is not None else None
+
+
+def make_runs(specs):
+    """specs: list of (ctx, fields or None, begin, end, r_max, B0pot) -> ctypes array."""
+    arr = (fpic_run * len(specs))()
+    for i, (ctx, fields, b, e, r_max, B0pot) in enumerate(specs):
+        arr[i].ctx = ctx.handle
+        for k in range(6):
+            arr[i].fields[k] = _dp(fields[k]) if fields is not None else None
+        arr[i].begin, arr[i].end, arr[i].r_max, arr[i].B0pot = b, e, r_max, B0pot
+    return arr
+
+
+def fpic_push_batched(runs, p: Particles, prm, stats=False, stream=None):
+    """runs: result of make_runs (keep the field tensors alive)."""
+    s = p.struct()
+    st = fpic_push_stats() if stats else None
+    rc = lib().fpic_push_batched(runs, len(runs), C.byref(s), C.byref(prm),
+                                 C.byref(st) if st is not None else None, _stream(stream))
+    _check(rc)
+    return st.as_dict() if st is not None else None
