@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--n", type=int, default=1 << 20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=4)
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--train-steps", type=int, default=3000)
     return ap.parse_args()
 
 
@@ -176,6 +178,51 @@ def setup(n, rank, device):
     return F, g, ctx, fields, p
 
 
+def _snapshot(p):
+    return {k: getattr(p, k).clone() for k in ("r", "th", "ph", "ur", "uth", "uph", "H0", "D0", "Hn", "alive")}
+
+
+def _restore(p, snap):
+    for k, v in snap.items():
+        getattr(p, k).copy_(v)
+
+
+def _timed(F, ctx, p, fields, prm, ev, steps, flush, learned=None):
+    """K steps, each bracketed by CUDA events on the launch stream; returns a
+    dict of device times, work and algorithmic flops."""
+    import torch
+    out = dict(t_step=0.0, t_ex=0.0, t_im=0.0, psteps=0, impl=0, iters=0, evals=0, fl_ex=0.0, fl_im=0.0,
+               launches=0)
+    for k in range(steps):
+        flush.fill_(k & 255)
+        ev[0].record()
+        if learned is None:
+            st = F.fpic_push(ctx, p, fields, prm, stats=True)
+        else:
+            net, cfg = learned
+            st = F.fpic_push_learned(ctx, net, p, fields, prm, cfg, stats=True)
+        ev[5].record()
+        torch.cuda.synchronize()
+        out["t_step"] += ev[0].elapsed_time(ev[5]) * 1e-3
+        out["t_ex"] += ev[1].elapsed_time(ev[2]) * 1e-3
+        out["t_im"] += ev[3].elapsed_time(ev[4]) * 1e-3
+        out["psteps"] += st["n_alive_before"]
+        out["impl"] += st["n_implicit"]
+        out["iters"] += st["n_iter_total"]
+        out["evals"] += st["n_rhs_evals"]
+        out["fl_ex"] += st["n_alive_before"] * FLOP_RK4_TRIAL
+        out["fl_im"] += st["n_iter_total"] * FLOP_IMR_ITER + st["n_implicit"] * FLOP_IMR_FINAL
+        out["launches"] += 3 if learned is None else 7
+    return out
+
+
+def _max_dH(F, ctx, p):
+    H, _ = F.fpic_hamiltonian(ctx, p, B0pot=B0)
+    alive = p.alive.bool()
+    dH = ((H - p.H0).abs() / p.D0)[alive]
+    return float(dH.max().item()) if dH.numel() else 0.0
+
+
 def run_gpu(args, ws, rank, local):
     import torch
     import torch.distributed as dist
@@ -190,49 +237,55 @@ def run_gpu(args, ws, rank, local):
                         B0pot=B0, events=ev[1:5])
     for _ in range(args.warmup):
         F.fpic_push(ctx, p, fields, prm, stats=True)
+    learned = None
+    train_info = None
+    if not args.no_learned:
+        # the network learns from the plain pusher's own steps (untimed)
+        from paper_2602_07452_gb300 import learned as L
+        prm_plain = F.push_params(DT, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=HYB1_THR,
+                                  r_max=float(g.rn[-1]), B0pot=B0)
+        t0 = time.perf_counter()
+        cfg = L.fit_cfg(ctx, p, fields, prm_plain, p_skip=0.7)
+        X, T, S = L.generate(ctx, p, fields, prm_plain, cfg, steps=8)
+        net, P, hist = L.train(X, T, S, steps=args.train_steps, batch=8192, lr=3e-3, log_every=500)
+        torch.cuda.synchronize()
+        train_info = {"samples": int(X.shape[0]), "train_steps": args.train_steps, "batch": 8192,
+                      "loss_first_last": [hist[0][1], hist[-1][1]], "seconds": round(time.perf_counter() - t0, 1)}
+        del X, T, S
+        learned = (net, cfg)
+        for _ in range(2):
+            snap0 = _snapshot(p)
+            F.fpic_push_learned(ctx, net, p, fields, prm, cfg)
+            _restore(p, snap0)
     fp64_gflops = F.fpic_probe_fp64(3000)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)   # > 129 MB L2
-    t_step = t_ex = t_im = 0.0
-    psteps = 0
-    flops_ex = flops_im = 0.0
-    n_impl = n_iter = 0
-    launches = 0
+    snap = _snapshot(p)
     clocks = Clocks(local)
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    for k in range(args.steps):
-        flush.fill_(k & 255)
-        ev[0].record()
-        st = F.fpic_push(ctx, p, fields, prm, stats=True)
-        ev[5].record()
-        torch.cuda.synchronize()
-        t_step += ev[0].elapsed_time(ev[5]) * 1e-3
-        t_ex += ev[1].elapsed_time(ev[2]) * 1e-3
-        t_im += ev[3].elapsed_time(ev[4]) * 1e-3
-        psteps += st["n_alive_before"]
-        n_impl += st["n_implicit"]
-        n_iter += st["n_iter_total"]
-        flops_ex += st["n_alive_before"] * FLOP_RK4_TRIAL
-        flops_im += st["n_iter_total"] * FLOP_IMR_ITER + st["n_implicit"] * FLOP_IMR_FINAL
-        launches += 3
+    plain = _timed(F, ctx, p, fields, prm, ev, args.steps, flush)
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
     clk = clocks.stop()
+    max_dH = _max_dH(F, ctx, p)
+    lrn = None
+    if learned is not None:
+        after_plain = _snapshot(p)
+        _restore(p, snap)
+        torch.cuda.synchronize()
+        lrn = _timed(F, ctx, p, fields, prm, ev, args.steps, flush, learned)
+        lrn["max_dH"] = _max_dH(F, ctx, p)
+        _restore(p, after_plain)
     # max over ranks of the device time, sum of the work
-    tot = torch.tensor([t_step], dtype=torch.float64, device=device)
-    work = torch.tensor([float(psteps)], dtype=torch.float64, device=device)
+    tot = torch.tensor([plain["t_step"]], dtype=torch.float64, device=device)
+    work = torch.tensor([float(plain["psteps"])], dtype=torch.float64, device=device)
     if ws > 1:
         dist.all_reduce(tot, op=dist.ReduceOp.MAX)
         dist.all_reduce(work, op=dist.ReduceOp.SUM)
     T, W = float(tot.item()), float(work.item())
-    # energy error at the end of the timed region
-    H, _ = F.fpic_hamiltonian(ctx, p, B0pot=B0)
-    alive = p.alive.bool()
-    dH = ((H - p.H0).abs() / p.D0)[alive]
-    max_dH = float(dH.max().item()) if dH.numel() else 0.0
     # end to end through the host-buffer C ABI: H2D inputs + push + D2H result, every step
     hp = F.HostParticles(p.n)
     for f in F.HostParticles.FIELDS_D:
@@ -254,8 +307,10 @@ def run_gpu(args, ws, rank, local):
     if ws > 1:
         dist.all_reduce(e2e, op=dist.ReduceOp.MAX)
         dist.all_reduce(e2e_w, op=dist.ReduceOp.SUM)
+    t_ex, t_im = plain["t_ex"], plain["t_im"]
     dom = "k_explicit" if t_ex >= t_im else "k_imr"
-    ach = (flops_ex / t_ex if dom == "k_explicit" else flops_im / max(t_im, 1e-30)) / 1e9
+    ach = (plain["fl_ex"] / t_ex if dom == "k_explicit" else plain["fl_im"] / max(t_im, 1e-30)) / 1e9
+    psteps = max(plain["psteps"], 1)
     line = {
         "metric": METRIC, "value": W / T, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True,
@@ -264,9 +319,10 @@ def run_gpu(args, ws, rank, local):
         "config": {"workload": "wald-charged-test-particles (push only)", "a": A_SPIN, "B0": B0,
                    "grid": f"{NGRID}x{NGRID} (ln r, theta), r in [0.9 r_+, 50 M]",
                    "particles_per_gpu": args.n, "theta_T": THETA_T, "q_over_m": QM, "dt": DT,
-                   "scheme": "Hyb1 RK4<->IMR", "hyb1_thr": HYB1_THR, "tol": 1e-14,
-                   "implicit_fraction": n_impl / max(psteps, 1),
-                   "mean_imr_iterations": n_iter / max(n_impl, 1),
+                   "scheme": "Hyb1 RK4<->IMR (plain)", "hyb1_thr": HYB1_THR, "tol": 1e-14,
+                   "implicit_fraction": plain["impl"] / psteps,
+                   "mean_imr_iterations": plain["iters"] / max(plain["impl"], 1),
+                   "rhs_evals_per_particle_step": plain["evals"] / psteps,
                    "max_dH_over_D0": max_dH, "parallelism": f"dp{ws} (independent particle sets)",
                    "l2": "256 MB buffer written between timed steps (outside the events)"},
         "e2e": {"value": float(e2e_w.item()) / float(e2e.item()), "unit": UNIT,
@@ -277,8 +333,19 @@ def run_gpu(args, ws, rank, local):
                      "unit": "GFLOP/s", "frac": ach / fp64_gflops, "traffic": None,
                      "share_explicit": t_ex / max(t_ex + t_im, 1e-30)},
         "clocks": clk,
-        "gpu_launches": launches,
+        "gpu_launches": plain["launches"],
     }
+    if lrn is not None:
+        lp = max(lrn["psteps"], 1)
+        line["learned"] = {
+            "value": lrn["psteps"] / lrn["t_step"], "unit": UNIT,
+            "ratio_vs_plain": (lrn["psteps"] / lrn["t_step"]) / (W / T if ws == 1 else plain["psteps"] / plain["t_step"]),
+            "ms_per_step": 1e3 * lrn["t_step"] / args.steps, "implicit_fraction": lrn["impl"] / lp,
+            "mean_imr_iterations": lrn["iters"] / max(lrn["impl"], 1),
+            "rhs_evals_per_particle_step": lrn["evals"] / lp, "max_dH_over_D0": lrn["max_dH"],
+            "same_start_state_as_plain": True, "p_skip": 0.7, "training": train_info,
+            "gpu_launches": lrn["launches"],
+        }
     return line
 
 

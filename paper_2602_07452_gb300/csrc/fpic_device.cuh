@@ -17,6 +17,36 @@ struct BH {
     double M, a, a2, twoM;
 };
 
+// 1/x from the hardware approximation refined by two Newton steps
+// (y <- y + y (1 - x y)); each step doubles the correct bits, so the result
+// is within an ulp or two of the correctly rounded reciprocal for normal x.
+__device__ __forceinline__ double rcp_nr(double x)
+{
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    double e = fma(-x, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-x, y, 1.0);
+    return fma(y, e, y);
+}
+
+// sin and cos of t from those of a nearby t0 by the angle-addition formula,
+// with sin d and cos d - 1 of d = t - t0 by their Taylor series (the first
+// omitted terms are below 1e-23 for |d| < 2^-7); farther away, sincos.
+__device__ __forceinline__ void sincos_near(double t0, double s0, double c0, double t, double& s, double& c)
+{
+    const double d = t - t0;
+    if (fabs(d) < 0.0078125) {
+        const double d2 = d * d;
+        const double sd = d * fma(d2, fma(d2, fma(d2, -1.0 / 5040.0, 1.0 / 120.0), -1.0 / 6.0), 1.0);
+        const double cm = d2 * fma(d2, fma(d2, fma(d2, 1.0 / 40320.0, -1.0 / 720.0), 1.0 / 24.0), -0.5);
+        s = fma(s0, cm, fma(c0, sd, s0));
+        c = fma(c0, cm, fma(-s0, sd, c0));
+    } else {
+        sincos(t, &s, &c);
+    }
+}
+
 // Metric at a point (r, th) given sin/cos th.
 struct Geo {
     double s, c, rho2, irho2, t;      // t = 1/(rho^2 sin^2 th)
@@ -31,7 +61,7 @@ __device__ __forceinline__ void geo_eval(const BH& bh, double r, double s, doubl
     g.s = s;
     g.c = c;
     g.rho2 = fma(bh.a2, c2, r * r);
-    g.t = 1.0 / (g.rho2 * s2);
+    g.t = rcp_nr(g.rho2 * s2);
     g.irho2 = g.t * s2;
     g.xi = fma(bh.twoM * r, g.irho2, 1.0);
     g.alpha = rsqrt(g.xi);
@@ -160,12 +190,10 @@ __device__ __forceinline__ void gather(const GridDev& G, const Fields& F, double
 // Equations of motion at y (Eqs. p1, p2, O1, O2) and, as a by-product, the
 // Hamiltonian H(y) = alpha Gamma - beta u_r - (q/m) A_0 (Eq. Ham with the
 // Wald A_0 when B0pot != 0).  D, B: FIDO fields at y (ignored if !em).
-__device__ __forceinline__ void eval_rhs(const BH& bh, const double y[6], double qm, bool em,
-                                         const double D[3], const double B[3], double B0pot,
-                                         double f[6], double& H)
+__device__ __forceinline__ void eval_rhs_sc(const BH& bh, const double y[6], double s, double c, double qm,
+                                            bool em, const double D[3], const double B[3], double B0pot,
+                                            double f[6], double& H)
 {
-    double s, c;
-    sincos(y[1], &s, &c);
     Geo g;
     geo_eval(bh, y[0], s, c, g);
     GeoD d;
@@ -206,11 +234,19 @@ __device__ __forceinline__ void eval_rhs(const BH& bh, const double y[6], double
     }
 }
 
-// Hamiltonian only (no derivatives, no force).
-__device__ __forceinline__ double eval_H(const BH& bh, const double y[6], double qm, double B0pot)
+__device__ __forceinline__ void eval_rhs(const BH& bh, const double y[6], double qm, bool em,
+                                         const double D[3], const double B[3], double B0pot,
+                                         double f[6], double& H)
 {
     double s, c;
     sincos(y[1], &s, &c);
+    eval_rhs_sc(bh, y, s, c, qm, em, D, B, B0pot, f, H);
+}
+
+// Hamiltonian only (no derivatives, no force), given sin/cos of y[1].
+__device__ __forceinline__ double eval_H_sc(const BH& bh, const double y[6], double s, double c, double qm,
+                                            double B0pot)
+{
     Geo g;
     geo_eval(bh, y[0], s, c, g);
     const double ur = y[3], ut = y[4], up = y[5];
@@ -221,6 +257,13 @@ __device__ __forceinline__ double eval_H(const BH& bh, const double y[6], double
     double H = fma(g.alpha, G, -g.beta * ur);
     if (B0pot != 0.0 && qm != 0.0) H = fma(-qm * B0pot * bh.a * y[0], (1.0 + c * c) * g.irho2, H);
     return H;
+}
+
+__device__ __forceinline__ double eval_H(const BH& bh, const double y[6], double qm, double B0pot)
+{
+    double s, c;
+    sincos(y[1], &s, &c);
+    return eval_H_sc(bh, y, s, c, qm, B0pot);
 }
 
 }  // namespace fpic

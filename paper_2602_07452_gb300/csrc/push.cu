@@ -87,6 +87,15 @@ __device__ __forceinline__ void F_at(const RunK& R, const double y[6], double qm
     eval_rhs(R.bh, y, qm, em, D, B, R.B0pot, f, H);
 }
 
+// Same, with sin/cos of y[1] supplied (from sincos_near).
+__device__ __forceinline__ void F_at_sc(const RunK& R, const double y[6], double s, double c, double qm, bool em,
+                                        double f[6], double& H)
+{
+    double D[3] = {0, 0, 0}, B[3] = {0, 0, 0};
+    if (em) gather(R.G, R.F, y[0], y[1], D, B);
+    eval_rhs_sc(R.bh, y, s, c, qm, em, D, B, R.B0pot, f, H);
+}
+
 // Particle boundaries (Sec. 2.5) and write-back of a finished step.
 __device__ __forceinline__ bool finish(const RunK& R, const PartDev& P, long long p, double z[6], double H,
                                        int implicit, int iters)
@@ -146,21 +155,26 @@ __global__ void __launch_bounds__(128) k_explicit(PushK k)
     const double qm = k.P.qm[p];
     const bool em = k.run.has_fields && qm != 0.0;
     const double dt = k.dt, hdt = 0.5 * k.dt;
-    double Hd;
-    F_at(k.run, z0, qm, em, kk, Hd);
+    double Hd, s0, c0, sn, cn;
+    sincos(z0[1], &s0, &c0);
+    F_at_sc(k.run, z0, s0, c0, qm, em, kk, Hd);
 #pragma unroll
     for (int i = 0; i < 6; ++i) { acc[i] = kk[i]; y[i] = fma(hdt, kk[i], z0[i]); }
-    F_at(k.run, y, qm, em, kk, Hd);
+    sincos_near(z0[1], s0, c0, y[1], sn, cn);
+    F_at_sc(k.run, y, sn, cn, qm, em, kk, Hd);
 #pragma unroll
     for (int i = 0; i < 6; ++i) { acc[i] = fma(2.0, kk[i], acc[i]); y[i] = fma(hdt, kk[i], z0[i]); }
-    F_at(k.run, y, qm, em, kk, Hd);
+    sincos_near(z0[1], s0, c0, y[1], sn, cn);
+    F_at_sc(k.run, y, sn, cn, qm, em, kk, Hd);
 #pragma unroll
     for (int i = 0; i < 6; ++i) { acc[i] = fma(2.0, kk[i], acc[i]); y[i] = fma(dt, kk[i], z0[i]); }
-    F_at(k.run, y, qm, em, kk, Hd);
+    sincos_near(z0[1], s0, c0, y[1], sn, cn);
+    F_at_sc(k.run, y, sn, cn, qm, em, kk, Hd);
     const double d6 = dt / 6.0;
 #pragma unroll
     for (int i = 0; i < 6; ++i) y[i] = fma(d6, acc[i] + kk[i], z0[i]);
-    const double H1 = eval_H(k.run.bh, y, qm, k.run.B0pot);
+    sincos_near(z0[1], s0, c0, y[1], sn, cn);
+    const double H1 = eval_H_sc(k.run.bh, y, sn, cn, qm, k.run.B0pot);
     bool accept = true;
     if (MODE == 1) {
         const double H0 = k.P.H0[p], D0 = k.P.D0[p];
@@ -215,7 +229,7 @@ __global__ void __launch_bounds__(128) k_imr(PushK k, int all_mode)
     long long p = -1;
     bool exhausted = false, fin = false;
     double z0[6], zk[6];
-    double qm = 0.0;
+    double qm = 0.0, s0 = 0.0, c0 = 1.0;
     bool em = false;
     int it = 0;
     long long n_it = 0, n_nc = 0, n_ev = 0, n_rm = 0;
@@ -247,6 +261,7 @@ __global__ void __launch_bounds__(128) k_imr(PushK k, int all_mode)
                         }
                         qm = k.P.qm[p];
                         em = k.run.has_fields && qm != 0.0;
+                        sincos(z0[1], &s0, &c0);
                         it = 0;
                         fin = false;
                     }
@@ -269,7 +284,9 @@ __global__ void __launch_bounds__(128) k_imr(PushK k, int all_mode)
 #pragma unroll
                 for (int i = 0; i < 6; ++i) y[i] = 0.5 * (z0[i] + zk[i]);
             }
-            F_at(k.run, y, qm, em, f, H);
+            double sy, cy;
+            sincos_near(z0[1], s0, c0, y[1], sy, cy);
+            F_at_sc(k.run, y, sy, cy, qm, em, f, H);
             ++n_ev;
             if (!fin) {
                 double zn[6];
@@ -1060,21 +1077,26 @@ __global__ void __launch_bounds__(128) k_explicit_batched(const __grid_constant_
     const double qm = k.P.qm[p];
     const bool em = R.has_fields && qm != 0.0;
     const double dt = k.dt, hdt = 0.5 * k.dt;
-    double Hd;
-    F_at(R, z0, qm, em, kk, Hd);
+    double Hd, s0, c0, sn, cn;
+    sincos(z0[1], &s0, &c0);
+    F_at_sc(R, z0, s0, c0, qm, em, kk, Hd);
 #pragma unroll
     for (int i = 0; i < 6; ++i) { acc[i] = kk[i]; y[i] = fma(hdt, kk[i], z0[i]); }
-    F_at(R, y, qm, em, kk, Hd);
+    sincos_near(z0[1], s0, c0, y[1], sn, cn);
+    F_at_sc(R, y, sn, cn, qm, em, kk, Hd);
 #pragma unroll
     for (int i = 0; i < 6; ++i) { acc[i] = fma(2.0, kk[i], acc[i]); y[i] = fma(hdt, kk[i], z0[i]); }
-    F_at(R, y, qm, em, kk, Hd);
+    sincos_near(z0[1], s0, c0, y[1], sn, cn);
+    F_at_sc(R, y, sn, cn, qm, em, kk, Hd);
 #pragma unroll
     for (int i = 0; i < 6; ++i) { acc[i] = fma(2.0, kk[i], acc[i]); y[i] = fma(dt, kk[i], z0[i]); }
-    F_at(R, y, qm, em, kk, Hd);
+    sincos_near(z0[1], s0, c0, y[1], sn, cn);
+    F_at_sc(R, y, sn, cn, qm, em, kk, Hd);
     const double d6 = dt / 6.0;
 #pragma unroll
     for (int i = 0; i < 6; ++i) y[i] = fma(d6, acc[i] + kk[i], z0[i]);
-    const double H1 = eval_H(R.bh, y, qm, R.B0pot);
+    sincos_near(z0[1], s0, c0, y[1], sn, cn);
+    const double H1 = eval_H_sc(R.bh, y, sn, cn, qm, R.B0pot);
     bool accept = true;
     if (k.scheme >= FPIC_HYB1) {
         const double H0 = k.P.H0[p], D0 = k.P.D0[p];
@@ -1117,7 +1139,7 @@ __global__ void __launch_bounds__(128) k_imr_batched(const __grid_constant__ Bat
     const RunK* R = B.runs;
     bool exhausted = false, fin = false;
     double z0[6], zk[6];
-    double qm = 0.0;
+    double qm = 0.0, s0 = 0.0, c0 = 1.0;
     bool em = false;
     int it = 0;
     long long n_it = 0, n_nc = 0, n_ev = 0, n_rm = 0;
@@ -1145,6 +1167,7 @@ __global__ void __launch_bounds__(128) k_imr_batched(const __grid_constant__ Bat
                         for (int i = 0; i < 6; ++i) zk[i] = all_mode ? z0[i] : k.guess[(size_t)i * k.n + p];
                         qm = k.P.qm[p];
                         em = R->has_fields && qm != 0.0;
+                        sincos(z0[1], &s0, &c0);
                         it = 0;
                         fin = false;
                     }
@@ -1167,7 +1190,9 @@ __global__ void __launch_bounds__(128) k_imr_batched(const __grid_constant__ Bat
 #pragma unroll
                 for (int i = 0; i < 6; ++i) y[i] = 0.5 * (z0[i] + zk[i]);
             }
-            F_at(*R, y, qm, em, f, H);
+            double sy, cy;
+            sincos_near(z0[1], s0, c0, y[1], sy, cy);
+            F_at_sc(*R, y, sy, cy, qm, em, f, H);
             ++n_ev;
             if (!fin) {
                 double zn[6];
