@@ -38,6 +38,10 @@ FLOP_RK4_TRIAL = 4 * FLOP_EVAL + 79 + 56 + 5
 FLOP_IMR_ITER = FLOP_EVAL + 48
 FLOP_IMR_FINAL = FLOP_EVAL
 NOMINAL_FP64_GFLOPS = 1250.0
+# deposit: FIDO velocity (41) + 3 sub-grids x (49 sqrt(gamma) points x 9 +
+# lattice 14 + four 16-point sums 128 + weights 16) + 2 th lattices (56) + shares (30)
+FLOP_DEPOSIT = 41 + 3 * (49 * 9 + 14 + 128 + 16) + 56 + 30
+PIC_A, PIC_DT, PIC_W = 0.99, 5e-4, 1e-6
 
 
 def parse():
@@ -50,8 +54,26 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--workload", default="push", choices=["push", "pic"])
+    ap.add_argument("--pic-grid", type=int, default=1024)
+    ap.add_argument("--pic-ppc", type=int, default=64)
+    ap.add_argument("--pic-steps", type=int, default=3)
+    ap.add_argument("--no-pic", action="store_true")
     ap.add_argument("--train-steps", type=int, default=3000)
     return ap.parse_args()
+
+
+def aggregate(t_local, work_local, device=None):
+    """Whole-job figures across ranks: the slowest rank's time (max) and the
+    total work (sum); a single process returns its own values."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(t_local)], dtype=torch.float64, device=device)
+    w = torch.tensor([float(work_local)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(w.item())
 
 
 def dist_env():
@@ -280,12 +302,7 @@ def run_gpu(args, ws, rank, local):
         lrn["max_dH"] = _max_dH(F, ctx, p)
         _restore(p, after_plain)
     # max over ranks of the device time, sum of the work
-    tot = torch.tensor([plain["t_step"]], dtype=torch.float64, device=device)
-    work = torch.tensor([float(plain["psteps"])], dtype=torch.float64, device=device)
-    if ws > 1:
-        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
-        dist.all_reduce(work, op=dist.ReduceOp.SUM)
-    T, W = float(tot.item()), float(work.item())
+    T, W = aggregate(plain["t_step"], plain["psteps"], device)
     # end to end through the host-buffer C ABI: H2D inputs + push + D2H result, every step
     hp = F.HostParticles(p.n)
     for f in F.HostParticles.FIELDS_D:
@@ -302,11 +319,7 @@ def run_gpu(args, ws, rank, local):
         e2e_ps += int(hp.alive.sum().item())
         F.fpic_push_host(ctx, hp, fields, prm_h)
     e2e_t = time.perf_counter() - t0
-    e2e = torch.tensor([e2e_t], dtype=torch.float64, device=device)
-    e2e_w = torch.tensor([float(e2e_ps)], dtype=torch.float64, device=device)
-    if ws > 1:
-        dist.all_reduce(e2e, op=dist.ReduceOp.MAX)
-        dist.all_reduce(e2e_w, op=dist.ReduceOp.SUM)
+    e2e_T, e2e_W = aggregate(e2e_t, e2e_ps, device)
     t_ex, t_im = plain["t_ex"], plain["t_im"]
     dom = "k_explicit" if t_ex >= t_im else "k_imr"
     ach = (plain["fl_ex"] / t_ex if dom == "k_explicit" else plain["fl_im"] / max(t_im, 1e-30)) / 1e9
@@ -325,7 +338,7 @@ def run_gpu(args, ws, rank, local):
                    "rhs_evals_per_particle_step": plain["evals"] / psteps,
                    "max_dH_over_D0": max_dH, "parallelism": f"dp{ws} (independent particle sets)",
                    "l2": "256 MB buffer written between timed steps (outside the events)"},
-        "e2e": {"value": float(e2e_w.item()) / float(e2e.item()), "unit": UNIT,
+        "e2e": {"value": e2e_W / e2e_T, "unit": UNIT,
                 "h2d_bytes_per_step": hp.bytes_in(), "d2h_bytes_per_step": hp.bytes_out(),
                 "api": "fpic_push_host (pinned host SoA in, result out, every step)"},
         "roofline": {"bound": "alu", "kernel": dom, "achieved": ach, "peak": fp64_gflops,
@@ -347,6 +360,76 @@ def run_gpu(args, ws, rank, local):
             "gpu_launches": lrn["launches"],
         }
     return line
+
+
+def run_pic(args, device, grid_n, ppc, steps, rank=0):
+    """Full GRPIC step (Sec. 2.1 order): FDTD sub-steps 1-4, RK4 push with
+    D^{n+3/2}, B^{n+3/2}, sort + deposit at n+2, FDTD sub-steps 7-10.
+    Plasma-filled Wald magnetosphere, a = 0.99, ppc particles in every cell."""
+    import numpy as np
+    import torch
+    from paper_2602_07452_gb300 import fpic as F
+    from paper_2602_07452_gb300 import inputs as I
+    g = I.wald_grid(grid_n, PIC_A)
+    ctx = F.fpic_init_metric(1.0, PIC_A)
+    F.fpic_set_grid(ctx, g)
+    fl = F.Fields(g.size, device)
+    wald = [torch.zeros(g.size, dtype=torch.float64, device=device) for _ in range(6)]
+    F.fpic_init_wald(ctx, wald, B0)
+    for k in range(3):
+        for nm, src in (("D0", wald[k]), ("D1", wald[k]), ("B0", wald[3 + k]), ("B1", wald[3 + k])):
+            getattr(fl, nm)[k].copy_(src)
+    d, q, w = I.cell_fill_draws(g, ppc, 0.5, seed=3 + rank, qm=QM, r_lo=1.02 * I.horizon(1.0, PIC_A))
+    n = d.shape[0]
+    p = F.Particles.empty(n, device)
+    p.qm.copy_(torch.as_tensor(q, device=device))
+    p.w.fill_(PIC_W)
+    F.fpic_init_particles(ctx, p, F.FPIC_SEED_FIDO, torch.as_tensor(d, device=device))
+    del d, q, w
+    r_max = float(g.rn[-1])
+    fprm = F.fdtd_params(PIC_DT, 1e4, 5.0, 0.9 * r_max, r_max)
+    pprm = F.push_params(PIC_DT, scheme=F.FPIC_RK4, r_max=r_max)
+    out4 = (fl.rho1, fl.j1[0], fl.j1[1], fl.j1[2])
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+
+    def step(timed):
+        if timed:
+            ev[0].record()
+        F.fpic_fdtd_step(ctx, fl, fprm, 1)
+        if timed:
+            ev[1].record()
+        F.fpic_push(ctx, p, fl.push_fields(), pprm)
+        if timed:
+            ev[2].record()
+        F.fpic_deposit(ctx, p, g.size, out=(fl.rho1, fl.j1[0], fl.j1[1], fl.j1[2]))
+        if timed:
+            ev[3].record()
+        F.fpic_fdtd_step(ctx, fl, fprm, 2)
+        if timed:
+            ev[4].record()
+        fl.swap()
+
+    step(False)
+    torch.cuda.synchronize()
+    ph = [0.0] * 4
+    ps = 0
+    for _ in range(steps):
+        ps += int(p.alive.sum().item())
+        step(True)
+        torch.cuda.synchronize()
+        for i in range(4):
+            ph[i] += ev[i].elapsed_time(ev[i + 1]) * 1e-3
+    T = sum(ph)
+    t_dep = ph[2]
+    return {
+        "workload": f"plasma-filled Wald GRPIC step, a={PIC_A}, {grid_n}x{grid_n} (ln r, theta), "
+                    f"{ppc} particles/cell ({ppc // 2} e-/e+ pairs)",
+        "particles": n, "steps": steps, "value": ps / T, "unit": UNIT, "ms_per_step": 1e3 * T / steps,
+        "phase_ms": {"fdtd_1_4": 1e3 * ph[0] / steps, "push_rk4": 1e3 * ph[1] / steps,
+                     "sort_and_deposit": 1e3 * ph[2] / steps, "fdtd_7_10": 1e3 * ph[3] / steps},
+        "dt": PIC_DT, "absorbing": {"chi0": 1e4, "lambda": 5, "r_abs": 0.9 * r_max},
+        "deposit_achieved_gflops": ps * FLOP_DEPOSIT / t_dep / 1e9,
+    }
 
 
 def main():
@@ -393,7 +476,20 @@ def main():
     import torch.distributed as dist
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if args.workload == "pic":
+        import torch
+        torch.cuda.set_device(local)
+        res = run_pic(args, torch.device("cuda", local), args.pic_grid, args.pic_ppc, args.pic_steps, rank)
+        if rank == 0:
+            line = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": ws, "steps": res["steps"],
+                    "warmup": 1, "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+                    "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": res}
+            print(json.dumps(line))
+        return 0
     line = run_gpu(args, ws, rank, local)
+    if not args.no_pic and rank == 0:
+        import torch
+        line["pic_step"] = run_pic(args, torch.device("cuda", local), 512, 16, 3, rank)
     if rank == 0:
         if pool is not None:
             try:

@@ -750,7 +750,7 @@ namespace fpic {
 struct FeatK {
     BH bh;
     GridDev G;
-    Fields F;
+    const float* f32[6];    // FP32 copies of the six field arrays (inputs only)
     int has_fields;
     const double *r, *th, *ur, *uth, *uph, *qm, *H0, *D0, *Hn;
     const uint8_t* alive;
@@ -762,10 +762,10 @@ struct FeatK {
     float* S;
 };
 
-__device__ __forceinline__ float lerp_f(const double* f, int ld, int i, int j, float wr, float wt)
+__device__ __forceinline__ float lerp_f(const float* f, int ld, int i, int j, float wr, float wt)
 {
-    const double* q = f + (size_t)i * ld + j;
-    const float f00 = (float)__ldg(q), f01 = (float)__ldg(q + 1), f10 = (float)__ldg(q + ld), f11 = (float)__ldg(q + ld + 1);
+    const float* q = f + (size_t)i * ld + j;
+    const float f00 = __ldg(q), f01 = __ldg(q + 1), f10 = __ldg(q + ld), f11 = __ldg(q + ld + 1);
     const float lo = fmaf(wt, f01 - f00, f00), hi = fmaf(wt, f11 - f10, f10);
     return fmaf(wr, hi - lo, lo);
 }
@@ -802,12 +802,12 @@ __global__ void k_features(FeatK k)
         locate(G.th, G.ith, G.Nth, th, (tf - G.th0) * G.it, j1, v1);
         const float a0 = (float)w0, a1 = (float)w1, b0 = (float)v0, b1 = (float)v1;
         wr_cell = a0;
-        f[5] = lerp_f(k.F.f[0], G.ld, i1, j0, a1, b0);    // D^r  (i+1/2, j)
-        f[6] = lerp_f(k.F.f[1], G.ld, i0, j1, a0, b1);    // D^th (i, j+1/2)
-        f[7] = lerp_f(k.F.f[2], G.ld, i0, j0, a0, b0);    // D^ph (i, j)
-        f[8] = lerp_f(k.F.f[3], G.ld, i0, j1, a0, b1);    // B^r  (i, j+1/2)
-        f[9] = lerp_f(k.F.f[4], G.ld, i1, j0, a1, b0);    // B^th (i+1/2, j)
-        f[10] = lerp_f(k.F.f[5], G.ld, i1, j1, a1, b1);   // B^ph (i+1/2, j+1/2)
+        f[5] = lerp_f(k.f32[0], G.ld, i1, j0, a1, b0);    // D^r  (i+1/2, j)
+        f[6] = lerp_f(k.f32[1], G.ld, i0, j1, a0, b1);    // D^th (i, j+1/2)
+        f[7] = lerp_f(k.f32[2], G.ld, i0, j0, a0, b0);    // D^ph (i, j)
+        f[8] = lerp_f(k.f32[3], G.ld, i0, j1, a0, b1);    // B^r  (i, j+1/2)
+        f[9] = lerp_f(k.f32[4], G.ld, i1, j0, a1, b0);    // B^th (i+1/2, j)
+        f[10] = lerp_f(k.f32[5], G.ld, i1, j1, a1, b1);   // B^ph (i+1/2, j+1/2)
     }
     // the hybrid test depends on the current energy error and on where the
     // particle sits in its cell (the interpolation error pattern)
@@ -884,10 +884,12 @@ static void fill_pushk(PushK& k, fpic_ctx* c, fpic_particles* p, const double* c
     k.cnt = c->d_cnt;
 }
 
-// scratch: guess 6n doubles | queue n | work n | X 16n floats | Y 16n floats
-static int learned_scratch(fpic_ctx* c, long long n, PushK& k, float** X, float** Y)
+// scratch: guess 6n doubles | queue n | work n | X 16n floats | Y 16n floats | 6 FP32 field copies
+static int learned_scratch(fpic_ctx* c, long long n, PushK& k, float** X, float** Y, float** f32)
 {
-    const size_t need = (size_t)n * (6 * sizeof(double) + 2 * sizeof(uint32_t) + 32 * sizeof(float)) + 1024;
+    const size_t fsz = c->has_grid ? 6 * (size_t)(c->Nr + 1) * c->ld : 0;
+    const size_t need = (size_t)n * (6 * sizeof(double) + 2 * sizeof(uint32_t) + 32 * sizeof(float)) +
+                        fsz * sizeof(float) + 2048;
     int rc = ensure_scratch(c, need);
     if (rc) return rc;
     char* b = (char*)c->d_scratch;
@@ -901,17 +903,35 @@ static int learned_scratch(fpic_ctx* c, long long n, PushK& k, float** X, float*
     *X = (float*)b;
     b += (size_t)n * 16 * sizeof(float);
     *Y = (float*)b;
+    b += (size_t)n * 16 * sizeof(float);
+    *f32 = (float*)b;
     return 0;
 }
 
+// FP32 copies of the field arrays (network inputs are rounded to bf16 anyway;
+// converting the grid once is cheaper than converting 24 gathered values per
+// particle on the FP64 pipe).
+__global__ void k_fields_f32(Fields F, float* out, size_t sz)
+{
+    for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < sz; o += (size_t)gridDim.x * blockDim.x)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) out[k * sz + o] = (float)F.f[k][o];
+}
+
 static FeatK make_featk(fpic_ctx* c, const fpic_particles* p, const double* const fields[6], double dt,
-                        const fpic_learned_cfg* cfg, float* X)
+                        const fpic_learned_cfg* cfg, float* X, float* f32, cudaStream_t s)
 {
     FeatK f{};
     f.bh = c->bh;
     f.G = c->G;
     f.has_fields = fields != nullptr;
-    for (int i = 0; i < 6; ++i) f.F.f[i] = fields ? fields[i] : nullptr;
+    if (fields) {
+        const size_t sz = (size_t)(c->Nr + 1) * c->ld;
+        Fields F;
+        for (int i = 0; i < 6; ++i) F.f[i] = fields[i];
+        k_fields_f32<<<256, 256, 0, s>>>(F, f32, sz);
+        for (int i = 0; i < 6; ++i) f.f32[i] = f32 + i * sz;
+    }
     f.r = p->r; f.th = p->th; f.ur = p->ur; f.uth = p->uth; f.uph = p->uph; f.qm = p->qm;
     f.H0 = p->H0; f.D0 = p->D0; f.Hn = p->Hn;
     f.alive = p->alive;
@@ -936,7 +956,11 @@ extern "C" int fpic_features(fpic_ctx* c, const fpic_particles* p, const double*
     if (fields && !c->has_grid) return set_error(FPIC_EINVAL, "fpic_features: fields given but no grid set");
     if (p->n == 0) return FPIC_OK;
     FPIC_CUDA(cudaSetDevice(c->device));
-    FeatK f = make_featk(c, p, fields, dt, cfg, X);
+    PushK k{};
+    float *Xs, *Ys, *f32;
+    int rc = learned_scratch(c, p->n, k, &Xs, &Ys, &f32);
+    if (rc) return rc;
+    FeatK f = make_featk(c, p, fields, dt, cfg, X, f32, (cudaStream_t)stream);
     k_features<<<(unsigned)((p->n + 127) / 128), 128, 0, (cudaStream_t)stream>>>(f);
     FPIC_CUDA(cudaGetLastError());
     return FPIC_OK;
@@ -957,8 +981,8 @@ extern "C" int fpic_learn_sample(fpic_ctx* c, fpic_particles* p, const double* c
     const long long n = p->n;
     PushK k{};
     fill_pushk(k, c, p, fields, prm);
-    float *Xs, *Ys;
-    int rc = learned_scratch(c, n, k, &Xs, &Ys);
+    float *Xs, *Ys, *f32;
+    int rc = learned_scratch(c, n, k, &Xs, &Ys, &f32);
     if (rc) return rc;
     k.work = nullptr;
     k.record = 1;
@@ -966,7 +990,7 @@ extern "C" int fpic_learn_sample(fpic_ctx* c, fpic_particles* p, const double* c
     k.recS = S;
     for (int i = 0; i < 6; ++i) k.inc_scale[i] = cfg ? cfg->inc_scale[i] : 1.0;
     FPIC_CUDA(cudaMemsetAsync(c->d_cnt, 0, CNT_N * sizeof(long long), s));
-    FeatK f = make_featk(c, p, fields, prm->dt, cfg, X);
+    FeatK f = make_featk(c, p, fields, prm->dt, cfg, X, f32, s);
     f.T = T;
     f.S = S;
     const unsigned nb = (unsigned)((n + 127) / 128);
@@ -992,8 +1016,8 @@ extern "C" int fpic_push_learned(fpic_ctx* c, fpic_mlp* m, fpic_particles* p, co
     const long long n = p->n;
     PushK k{};
     fill_pushk(k, c, p, fields, prm);
-    float *X, *Y;
-    int rc = learned_scratch(c, n > 0 ? n : 1, k, &X, &Y);
+    float *X, *Y, *f32;
+    int rc = learned_scratch(c, n > 0 ? n : 1, k, &X, &Y, &f32);
     if (rc) return rc;
     for (int i = 0; i < 6; ++i) k.inc_scale[i] = cfg->inc_scale[i];
     k.learned = Y;
@@ -1007,7 +1031,7 @@ extern "C" int fpic_push_learned(fpic_ctx* c, fpic_mlp* m, fpic_particles* p, co
     cudaEvent_t* ev = prm->events ? (cudaEvent_t*)prm->events : nullptr;
     if (stats) k_count_alive<<<persist, 256, 0, s>>>(k.P, n, c->d_cnt);
     if (ev) FPIC_CUDA(cudaEventRecord(ev[0], s));
-    FeatK f = make_featk(c, p, fields, prm->dt, cfg, X);
+    FeatK f = make_featk(c, p, fields, prm->dt, cfg, X, f32, s);
     k_features<<<nb, 128, 0, s>>>(f);
     rc = mlp_forward_dev(m, X, Y, n, s);
     if (rc) return rc;
