@@ -54,6 +54,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--learned-form", choices=("correct", "skip"), default="correct",
+                    help="learned guess: corrector of the rejected trials (default) or pre-step skip")
+    ap.add_argument("--train-gen-steps", type=int, default=10,
+                    help="plain steps sampled for the training set")
     ap.add_argument("--workload", default="push", choices=["push", "pic"])
     ap.add_argument("--pic-grid", type=int, default=1024)
     ap.add_argument("--pic-ppc", type=int, default=64)
@@ -213,7 +217,7 @@ def _timed(F, ctx, p, fields, prm, ev, steps, flush, learned=None):
     """K steps, each bracketed by CUDA events on the launch stream; returns a
     dict of device times, work and algorithmic flops."""
     import torch
-    out = dict(t_step=0.0, t_ex=0.0, t_im=0.0, psteps=0, impl=0, iters=0, evals=0, fl_ex=0.0, fl_im=0.0,
+    out = dict(t_step=0.0, t_ex=0.0, t_inf=0.0, t_im=0.0, psteps=0, notconv=0, impl=0, iters=0, evals=0, fl_ex=0.0, fl_im=0.0,
                launches=0)
     for k in range(steps):
         flush.fill_(k & 255)
@@ -227,14 +231,16 @@ def _timed(F, ctx, p, fields, prm, ev, steps, flush, learned=None):
         torch.cuda.synchronize()
         out["t_step"] += ev[0].elapsed_time(ev[5]) * 1e-3
         out["t_ex"] += ev[1].elapsed_time(ev[2]) * 1e-3
+        out["t_inf"] += ev[2].elapsed_time(ev[3]) * 1e-3
         out["t_im"] += ev[3].elapsed_time(ev[4]) * 1e-3
         out["psteps"] += st["n_alive_before"]
         out["impl"] += st["n_implicit"]
         out["iters"] += st["n_iter_total"]
         out["evals"] += st["n_rhs_evals"]
+        out["notconv"] += st["n_notconv"]
         out["fl_ex"] += st["n_alive_before"] * FLOP_RK4_TRIAL
         out["fl_im"] += st["n_iter_total"] * FLOP_IMR_ITER + st["n_implicit"] * FLOP_IMR_FINAL
-        out["launches"] += 3 if learned is None else 7
+        out["launches"] += 3 if learned is None else (7 if learned[1].mode == F.FPIC_LEARN_SKIP else 5)
     return out
 
 
@@ -267,8 +273,9 @@ def run_gpu(args, ws, rank, local):
         prm_plain = F.push_params(DT, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=HYB1_THR,
                                   r_max=float(g.rn[-1]), B0pot=B0)
         t0 = time.perf_counter()
-        cfg = L.fit_cfg(ctx, p, fields, prm_plain, p_skip=0.7)
-        X, T, S = L.generate(ctx, p, fields, prm_plain, cfg, steps=8)
+        mode = F.FPIC_LEARN_CORRECT if args.learned_form == "correct" else F.FPIC_LEARN_SKIP
+        cfg = L.fit_cfg(ctx, p, fields, prm_plain, p_skip=0.7, mode=mode)
+        X, T, S = L.generate(ctx, p, fields, prm_plain, cfg, steps=args.train_gen_steps)
         net, P, hist = L.train(X, T, S, steps=args.train_steps, batch=8192, lr=3e-3, log_every=500)
         torch.cuda.synchronize()
         train_info = {"samples": int(X.shape[0]), "train_steps": args.train_steps, "batch": 8192,
@@ -293,13 +300,21 @@ def run_gpu(args, ws, rank, local):
         dist.barrier()
     clk = clocks.stop()
     max_dH = _max_dH(F, ctx, p)
-    lrn = None
+    lrn = lead = None
     if learned is not None:
         after_plain = _snapshot(p)
         _restore(p, snap)
         torch.cuda.synchronize()
         lrn = _timed(F, ctx, p, fields, prm, ev, args.steps, flush, learned)
         lrn["max_dH"] = _max_dH(F, ctx, p)
+        if learned[1].mode == F.FPIC_LEARN_CORRECT:
+            # ablation: the same corrector with a zero network (leading-order gap only)
+            net0 = F.MLP()
+            net0.set_params(torch.zeros(F.MLP.nparams(), dtype=torch.float32, device=device))
+            _restore(p, snap)
+            torch.cuda.synchronize()
+            lead = _timed(F, ctx, p, fields, prm, ev, args.steps, flush, (net0, learned[1]))
+            lead["max_dH"] = _max_dH(F, ctx, p)
         _restore(p, after_plain)
     # max over ranks of the device time, sum of the work
     T, W = aggregate(plain["t_step"], plain["psteps"], device)
@@ -356,9 +371,24 @@ def run_gpu(args, ws, rank, local):
             "ms_per_step": 1e3 * lrn["t_step"] / args.steps, "implicit_fraction": lrn["impl"] / lp,
             "mean_imr_iterations": lrn["iters"] / max(lrn["impl"], 1),
             "rhs_evals_per_particle_step": lrn["evals"] / lp, "max_dH_over_D0": lrn["max_dH"],
-            "same_start_state_as_plain": True, "p_skip": 0.7, "training": train_info,
+            "same_start_state_as_plain": True, "form": args.learned_form,
+            "inference_ms_per_step": 1e3 * lrn["t_inf"] / args.steps,
+            **({"p_skip": 0.7} if args.learned_form == "skip" else {}), "training": train_info,
             "gpu_launches": lrn["launches"],
+            "explicit_ms_per_step": 1e3 * lrn["t_ex"] / args.steps,
+            "implicit_ms_per_step": 1e3 * lrn["t_im"] / args.steps,
+            "imr_not_converged": lrn["notconv"],
         }
+        line["config"]["explicit_ms_per_step"] = 1e3 * plain["t_ex"] / args.steps
+        line["config"]["implicit_ms_per_step"] = 1e3 * plain["t_im"] / args.steps
+        line["config"]["imr_not_converged"] = plain["notconv"]
+        if lead is not None:
+            lp0 = max(lead["psteps"], 1)
+            line["learned"]["leading_order_only"] = {
+                "value": lead["psteps"] / lead["t_step"], "ms_per_step": 1e3 * lead["t_step"] / args.steps,
+                "mean_imr_iterations": lead["iters"] / max(lead["impl"], 1),
+                "rhs_evals_per_particle_step": lead["evals"] / lp0, "max_dH_over_D0": lead["max_dH"],
+                "note": "same corrector with a zero network: guess = trial + (2/3) A - (1/6) B"}
     return line
 
 

@@ -234,6 +234,16 @@ int fpic_push_noalloc(double M, double a, fpic_particles *p, const fpic_push_par
  * FPIC_ECUDA. */
 int fpic_probe_fp64(double *gflops_out, int reps);
 
+/* Test helper for the library's own FP64 elementary routines, one thread
+ * per element of x (device, n values) into y (device):
+ *   fn 0: 1/x by the hardware estimate and two Newton steps (push metric);
+ *   fn 1: sqrt(x) by the hardware reciprocal-square-root estimate and one
+ *         Goldschmidt step (deposit trapezoid sums), x > 0 normal;
+ *   fn 2: y[2i] = sin x, y[2i+1] = cos x - 1 for a small step x (series
+ *         below 2^-7, libm above), as used by the angle-addition updates.
+ * Errors: FPIC_EINVAL (fn out of range, n < 0, NULL with n > 0). */
+int fpic_probe_math(int fn, const double *x, double *y, long long n, void *stream);
+
 /* H (Eq. Ham with the Wald A_0 of Sec. 3.1.3 when B0pot != 0) and
  * L = u_ph + (q/m) A_ph for every particle.  H_out, L_out: device arrays of
  * length n, either may be NULL.  Errors: FPIC_EINVAL. */
@@ -349,20 +359,37 @@ int fpic_mlp_train_step(fpic_mlp *m, float *P, float *mom, float *vel, const flo
                         const float *S, const float *lossw, long long B, int step, float lr, float beta1,
                         float beta2, float eps, float *loss, void *stream);
 
-/* Configuration of the learned guess in the push.
- *   feat_mean, feat_std : standardisation of the 14 features (x - mean)/std,
- *     features = (ln r, th, u_r, u_th, u_ph, D^r, D^th, D^ph, B^r, B^th, B^ph
- *     gathered at the particle, the current energy error (H^n - H_0)/D_0, the
+/* Configuration of the learned guess in the push.  Two forms:
+ *
+ * FPIC_LEARN_SKIP (0), decided before the step: the 14 features are
+ *     (ln r, th, u_r, u_th, u_ph, D^r, D^th, D^ph, B^r, B^th, B^ph gathered
+ *     at the particle, the current energy error (H^n - H_0)/D_0, the
  *     fractional position of r in its cell, (q/m) dt), computed in FP32;
- *   inc_scale : scale of the six implicit-step increments z^{n+1} - z^n
- *     (network outputs 0-5 are increments / inc_scale);
- *   p_skip : a particle whose predicted rejection probability sigmoid(y_6)
- *     exceeds p_skip skips the RK4 trial and goes straight to the implicit
- *     solve, started from z^n + inc_scale * y[0..5]. */
+ *     outputs 0-5 are (z^{n+1} - z^n) / inc_scale; a particle whose
+ *     predicted rejection probability sigmoid(y_6) exceeds p_skip skips the
+ *     RK4 trial and starts the implicit solve from z^n + inc_scale y[0..5].
+ *
+ * FPIC_LEARN_CORRECT (1), decided after the trial: for each particle whose
+ *     RK4 trial the plain test rejects, the features are the RK4 stage
+ *     differences A = dt (k3 - k2) and B = dt (k4 - 2 k2 + k1) (k1..k4 the
+ *     stage slopes of Sec. 2.2.1), each component i divided by its own scale
+ *     s_i = |A_i| + |B_i| (features 0-5: A_i / s_i, 6-11: B_i / s_i), then
+ *     ln r and th (12, 13).  The gap between the converged implicit step and
+ *     the trial is, to leading order in dt, dt^3 (f'f'f / 12 - f''(f,f) / 24)
+ *     = g + O(dt^4) with g = (2/3) A - (1/6) B; outputs 0-5 are the rest of
+ *     the gap, (z_IMR - z_RK4 - g)_i / s_i, and the implicit solve starts
+ *     from z_RK4 + g + s y[0..5] instead of z_RK4 (a network with zero
+ *     output gives the leading-order guess alone).  inc_scale and p_skip
+ *     are unused.
+ *
+ *   feat_mean, feat_std : standardisation (x - mean)/std of the 14 features;
+ *   mode : FPIC_LEARN_SKIP or FPIC_LEARN_CORRECT. */
+enum { FPIC_LEARN_SKIP = 0, FPIC_LEARN_CORRECT = 1 };
 typedef struct {
     float feat_mean[16], feat_std[16];
     double inc_scale[6];
     float p_skip;
+    int mode;
 } fpic_learned_cfg;
 
 /* Network inputs of every particle: X (device, n x 16 FP32, standardised
@@ -372,23 +399,35 @@ int fpic_features(fpic_ctx *ctx, const fpic_particles *p, const double *const fi
                   const fpic_learned_cfg *cfg, float *X, void *stream);
 
 /* Training samples from the plain method itself, leaving the particles
- * unchanged: features X (as fpic_features), targets T (n x 16: outputs 0-5 =
- * (z_implicit - z^n) / inc_scale with z_implicit the converged implicit step
- * from the RK4 trial, output 7 = (iterations - 8)/4), labels S (n: 1 if the
- * plain hybrid test (prm) rejects the RK4 trial).  Removed particles get
- * zero rows.  prm->scheme must be FPIC_HYB1 or FPIC_HYB2 with the IMR
- * partner.  Errors: FPIC_EINVAL, FPIC_ENOMEM. */
+ * unchanged; every alive particle takes the RK4 trial, the plain test and
+ * then the implicit solve from the trial.  Labels S (1 if the plain hybrid
+ * test (prm) rejects the trial) and targets T (16 floats per sample: outputs
+ * 0-5 as the form's outputs, output 7 = (iterations - 8)/4).
+ *   cfg->mode FPIC_LEARN_SKIP: row p = particle p; X as fpic_features;
+ *     targets (z_IMR - z^n) / inc_scale; removed particles get zero rows.
+ *   cfg->mode FPIC_LEARN_CORRECT: row = the particle's slot in the implicit
+ *     queue (rows 0 .. n_alive - 1, the order is not deterministic; X, T
+ *     and S rows match); X = the trial features; targets
+ *     (z_IMR - z_RK4 - g)_i / s_i clamped to [-16, 16].
+ * cfg NULL = FPIC_LEARN_SKIP with raw features.  prm->scheme must be
+ * FPIC_HYB1 or FPIC_HYB2 with the IMR partner.
+ * Errors: FPIC_EINVAL, FPIC_ENOMEM. */
 int fpic_learn_sample(fpic_ctx *ctx, fpic_particles *p, const double *const fields[6], const fpic_push_params *prm,
                       const fpic_learned_cfg *cfg, float *X, float *T, float *S, void *stream);
 
-/* Hybrid push with the learned guess: features -> network (tensor cores) ->
- * particles predicted to be rejected go straight to the IMR (started from
- * the predicted step), the others take the RK4 trial and the plain test
- * (rejected ones -> IMR from the trial).  Every step is accepted only by the
- * plain method's own tests: the H test for RK4 steps, convergence for
- * implicit ones.  prm as fpic_push (scheme FPIC_HYB1/HYB2, implicit
- * FPIC_IMR).  stats: as fpic_push; n_implicit includes the skipped ones.
- * Errors: FPIC_EINVAL, FPIC_ENOMEM, FPIC_ECUDA. */
+/* Hybrid push with the learned guess (cfg->mode):
+ *   FPIC_LEARN_SKIP: features -> network -> particles predicted to be
+ *     rejected go straight to the IMR (started from the predicted step), the
+ *     others take the RK4 trial and the plain test (rejected ones -> IMR from
+ *     the trial);
+ *   FPIC_LEARN_CORRECT: RK4 trial and plain test for every particle; the
+ *     rejected ones' trial features -> network (tensor cores, rows = implicit
+ *     queue, count read on the device) -> IMR from the corrected trial.
+ * Every step is accepted only by the plain method's own tests: the H test for
+ * RK4 steps, convergence for implicit ones (so in FPIC_LEARN_CORRECT the
+ * scheme choices are exactly the plain ones).  prm as fpic_push (scheme
+ * FPIC_HYB1/HYB2, implicit FPIC_IMR).  stats: as fpic_push; n_implicit
+ * includes the skipped ones.  Errors: FPIC_EINVAL, FPIC_ENOMEM, FPIC_ECUDA. */
 int fpic_push_learned(fpic_ctx *ctx, fpic_mlp *m, fpic_particles *p, const double *const fields[6],
                       const fpic_push_params *prm, const fpic_learned_cfg *cfg, fpic_push_stats *stats,
                       void *stream);

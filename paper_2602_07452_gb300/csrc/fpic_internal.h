@@ -50,6 +50,9 @@ int ensure_scratch(fpic_ctx* c, size_t bytes);
 int ensure_scratch2(fpic_ctx* c, size_t bytes);
 bool particles_ok(const fpic_particles* p, bool need_state);
 int mlp_forward_dev(fpic_mlp* m, const float* X, float* Y, long long B, cudaStream_t s);
+// Forward pass of min(B, *count) rows, count read on the device (B bounds the launch).
+int mlp_forward_dev_count(fpic_mlp* m, const float* X, float* Y, long long B, const long long* count,
+                          cudaStream_t s);
 
 }  // namespace fpic
 

@@ -144,8 +144,9 @@ __global__ void k_mlp_pack(const float* __restrict__ P, MlpDev d)
 // ---------------------------------------------------------------------------
 // shared memory map (bytes)
 constexpr int FW_W1 = 0, FW_W2 = FW_W1 + 128 * 16 * 2, FW_W3 = FW_W2 + 128 * 128 * 2, FW_W4 = FW_W3 + 128 * 128 * 2,
-              FW_X = FW_W4 + 16 * 128 * 2, FW_H = FW_X + 128 * 16 * 2, FW_BAR = FW_H + 128 * 128 * 2,
-              FW_SMEM = FW_BAR + 64;
+              FW_X = FW_W4 + 16 * 128 * 2, FW_H = FW_X + 128 * 16 * 2, FW_B = FW_H + 128 * 128 * 2,
+              FW_BAR = FW_B + (3 * 128 + 16) * 4, FW_SMEM = FW_BAR + 64;
+constexpr int FW_THREADS = 256;
 
 __device__ __forceinline__ void load_tile_kmajor(uint8_t* dst, const uint16_t* __restrict__ src, int R, int Kd)
 {
@@ -181,13 +182,14 @@ __device__ __forceinline__ int layer_mma(uint32_t tbase, const uint8_t* sA, cons
     return ok;
 }
 
-// Epilogue of a hidden layer: z = acc + b; a = bf16(relu(z)) into sH (row r
-// = thread), optionally to global H (bf16 [B][128]).
-__device__ __forceinline__ void hidden_epilogue(uint32_t tbase, const float* __restrict__ b, uint8_t* sH,
-                                                uint16_t* Hg, long long row, long long B)
+// Epilogue of a hidden layer: z = acc + b; a = bf16(relu(z)) into sH.  Row
+// r = thread % 128 (its TMEM lane); the two halves of the block take
+// columns [0, 64) and [64, 128).  Optionally to global H (bf16 [B][128]).
+__device__ __forceinline__ void hidden_epilogue(uint32_t tbase, const float* b, uint8_t* sH, uint16_t* Hg,
+                                                long long row, long long B)
 {
-    const int r = threadIdx.x, warp = r >> 5;
-    for (int c0 = 0; c0 < 128; c0 += 32) {
+    const int r = threadIdx.x & 127, warp = (threadIdx.x >> 5) & 3, half = threadIdx.x >> 7;
+    for (int c0 = 64 * half; c0 < 64 * half + 64; c0 += 32) {
         float v[32];
         tc::tmem_ld32(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
 #pragma unroll
@@ -211,20 +213,35 @@ struct FwdK {
     const float* X;      // B x 16 FP32 features (standardised, padded with zeros)
     float* Y;            // B x 16 FP32 outputs (9 used)
     uint16_t* H;         // nullable: 3 x B x 128 bf16 hidden activations
-    long long B;
+    long long B;         // rows (bound of the launch)
+    const long long* count;   // nullable: rows = min(B, *count), read on the device
     int* err;
 };
 
-__global__ void __launch_bounds__(128) k_mlp_fwd(FwdK k)
+// Fused persistent forward, 256 threads: thread t owns row t % 128 of each
+// 128-row tile and half t / 128 of its 16 inputs and of the hidden columns.
+// The next tile's inputs are loaded into registers while the current tile
+// runs through the four layers.
+__global__ void __launch_bounds__(FW_THREADS) k_mlp_fwd(FwdK k)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
+    long long B = k.B;
+    if (k.count) {
+        const long long c = *k.count;
+        B = c < 0 ? 0 : (c < B ? c : B);
+    }
+    const long long ntiles = (B + 127) / 128;
+    if ((long long)blockIdx.x >= ntiles) return;     // whole block, before any allocation
     uint64_t* mbar = (uint64_t*)(smem + FW_BAR);
     uint32_t* tslot = (uint32_t*)(smem + FW_BAR + 16);
-    const int tid = threadIdx.x, warp = tid >> 5;
+    float* sb = (float*)(smem + FW_B);
+    const int tid = threadIdx.x, warp = tid >> 5, r = tid & 127, half = tid >> 7;
     load_tile_kmajor(smem + FW_W1, k.w.W1, 128, 16);
     load_tile_kmajor(smem + FW_W2, k.w.W2, 128, 128);
     load_tile_kmajor(smem + FW_W3, k.w.W3, 128, 128);
     load_tile_kmajor(smem + FW_W4, k.w.W4, 16, 128);
+    for (int i = tid; i < 3 * 128 + 16; i += FW_THREADS)
+        sb[i] = i < 128 ? k.w.b1[i] : i < 256 ? k.w.b2[i - 128] : i < 384 ? k.w.b3[i - 256] : k.w.b4[i - 384];
     if (warp == 0) tc::tmem_alloc(tslot, 128);
     if (tid == 0) tc::mbar_init(mbar, 1);
     tc::fence_before();
@@ -233,40 +250,50 @@ __global__ void __launch_bounds__(128) k_mlp_fwd(FwdK k)
     const uint32_t tbase = *tslot;
     uint32_t phase = 0;
     int ok = 1;
-    const long long ntiles = (k.B + 127) / 128;
+    // this thread's 8 inputs of the first tile
+    float4 xa = make_float4(0.f, 0.f, 0.f, 0.f), xb = xa;
+    {
+        const long long row = (long long)blockIdx.x * 128 + r;
+        if (row < B) {
+            xa = *(const float4*)(k.X + row * 16 + 8 * half);
+            xb = *(const float4*)(k.X + row * 16 + 8 * half + 4);
+        }
+    }
     for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        const long long row = tile * 128 + tid;
-        // input tile: one row per thread, 16 features -> bf16
+        const long long row = tile * 128 + r;
+        *(uint4*)(smem + FW_X + tc::kmajor_off(r, 8 * half, 128)) =
+            make_uint4(tc::pack_bf2(xa.x, xa.y), tc::pack_bf2(xa.z, xa.w), tc::pack_bf2(xb.x, xb.y),
+                       tc::pack_bf2(xb.z, xb.w));
         {
-            uint32_t pk[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                float a = 0.f, b = 0.f;
-                if (row < k.B) {
-                    a = k.X[row * 16 + 2 * q];
-                    b = k.X[row * 16 + 2 * q + 1];
-                }
-                pk[q] = tc::pack_bf2(a, b);
+            const long long nrow = (tile + gridDim.x) * 128 + r;
+            xa = make_float4(0.f, 0.f, 0.f, 0.f);
+            xb = xa;
+            if (nrow < B) {
+                xa = *(const float4*)(k.X + nrow * 16 + 8 * half);
+                xb = *(const float4*)(k.X + nrow * 16 + 8 * half + 4);
             }
-            *(uint4*)(smem + FW_X + tc::kmajor_off(tid, 0, 128)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-            *(uint4*)(smem + FW_X + tc::kmajor_off(tid, 8, 128)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
         }
         ok = layer_mma(tbase, smem + FW_X, smem + FW_W1, 128, 16, mbar, phase);
         if (!ok) break;
-        hidden_epilogue(tbase, k.w.b1, smem + FW_H, k.H ? k.H : nullptr, row, k.B);
+        hidden_epilogue(tbase, sb, smem + FW_H, k.H ? k.H : nullptr, row, B);
         ok = layer_mma(tbase, smem + FW_H, smem + FW_W2, 128, 128, mbar, phase);
         if (!ok) break;
-        hidden_epilogue(tbase, k.w.b2, smem + FW_H, k.H ? k.H + (size_t)k.B * 128 : nullptr, row, k.B);
+        hidden_epilogue(tbase, sb + 128, smem + FW_H, k.H ? k.H + (size_t)B * 128 : nullptr, row, B);
         ok = layer_mma(tbase, smem + FW_H, smem + FW_W3, 128, 128, mbar, phase);
         if (!ok) break;
-        hidden_epilogue(tbase, k.w.b3, smem + FW_H, k.H ? k.H + (size_t)2 * k.B * 128 : nullptr, row, k.B);
+        hidden_epilogue(tbase, sb + 256, smem + FW_H, k.H ? k.H + (size_t)2 * B * 128 : nullptr, row, B);
         ok = layer_mma(tbase, smem + FW_H, smem + FW_W4, 16, 128, mbar, phase);
         if (!ok) break;
-        float v[16];
-        tc::tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16), v);
-        if (row < k.B) {
+        if (half == 0) {
+            float v[16];
+            tc::tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16), v);
+            if (row < B) {
+                float4* y = (float4*)(k.Y + row * 16);
 #pragma unroll
-            for (int c = 0; c < 16; ++c) k.Y[row * 16 + c] = v[c] + k.w.b4[c];
+                for (int q = 0; q < 4; ++q)
+                    y[q] = make_float4(v[4 * q] + sb[384 + 4 * q], v[4 * q + 1] + sb[385 + 4 * q],
+                                       v[4 * q + 2] + sb[386 + 4 * q], v[4 * q + 3] + sb[387 + 4 * q]);
+            }
         }
     }
     if (!ok && tid == 0) atomicExch(k.err, 1);
@@ -503,20 +530,21 @@ extern "C" int fpic_mlp_set_params(fpic_mlp* m, const float* P, void* stream)
     return FPIC_OK;
 }
 
-static int mlp_forward_impl(fpic_mlp* m, const float* X, float* Y, uint16_t* H, long long B, cudaStream_t s)
+static int mlp_forward_impl(fpic_mlp* m, const float* X, float* Y, uint16_t* H, long long B,
+                            const long long* count, cudaStream_t s)
 {
     if (!g_fwd_attr_set) {
         FPIC_CUDA(cudaFuncSetAttribute(k_mlp_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, FW_SMEM));
         g_fwd_attr_set = true;
     }
     if (B == 0) return FPIC_OK;
-    FwdK k{m->d, X, Y, H, B, m->err};
+    FwdK k{m->d, X, Y, H, B, count, m->err};
     const long long ntiles = (B + 127) / 128;
-    // two CTAs per SM (108 KB of shared memory and 128 TMEM columns each) so
+    // two CTAs per SM (~110 KB of shared memory and 128 TMEM columns each) so
     // one CTA's epilogue overlaps the other's MMAs
     const long long cap = 2LL * m->sm_count;
     const unsigned grid = (unsigned)(ntiles < cap ? ntiles : cap);
-    k_mlp_fwd<<<grid, 128, FW_SMEM, s>>>(k);
+    k_mlp_fwd<<<grid, FW_THREADS, FW_SMEM, s>>>(k);
     FPIC_CUDA(cudaGetLastError());
     return FPIC_OK;
 }
@@ -524,7 +552,13 @@ static int mlp_forward_impl(fpic_mlp* m, const float* X, float* Y, uint16_t* H, 
 namespace fpic {
 int mlp_forward_dev(fpic_mlp* m, const float* X, float* Y, long long B, cudaStream_t s)
 {
-    return mlp_forward_impl(m, X, Y, nullptr, B, s);
+    return mlp_forward_impl(m, X, Y, nullptr, B, nullptr, s);
+}
+
+int mlp_forward_dev_count(fpic_mlp* m, const float* X, float* Y, long long B, const long long* count,
+                          cudaStream_t s)
+{
+    return mlp_forward_impl(m, X, Y, nullptr, B, count, s);
 }
 }  // namespace fpic
 
@@ -533,7 +567,7 @@ extern "C" int fpic_mlp_forward(fpic_mlp* m, const float* X, float* Y, long long
     if (!m || (B > 0 && (!X || !Y))) return set_error(FPIC_EINVAL, "fpic_mlp_forward: NULL argument");
     if (B < 0) return set_error(FPIC_EINVAL, "fpic_mlp_forward: B < 0");
     FPIC_CUDA(cudaSetDevice(m->device));
-    return mlp_forward_impl(m, X, Y, nullptr, B, (cudaStream_t)stream);
+    return mlp_forward_impl(m, X, Y, nullptr, B, nullptr, (cudaStream_t)stream);
 }
 
 extern "C" int fpic_mlp_status(fpic_mlp* m, int* status)
@@ -623,7 +657,7 @@ static int mlp_grad_impl(fpic_mlp* m, const float* X, const float* T, const floa
     if (rc) return rc;
     TrainBufs& t = g_tb;
     const long long BH = B * 128;
-    rc = mlp_forward_impl(m, X, t.Y, t.H, B, s);
+    rc = mlp_forward_impl(m, X, t.Y, t.H, B, nullptr, s);
     if (rc) return rc;
     LossW lw;
     for (int k = 0; k < 16; ++k) lw.m[k] = k < 9 ? lossw[k] : 0.f;

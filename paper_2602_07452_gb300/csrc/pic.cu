@@ -6,8 +6,8 @@
 //   k_dep_particle  one thread per particle (in cell order): the 4x4
 //                   trapezoidal subvolumes of sqrt(gamma) on each sub-grid
 //                   -> 16 node shares (rho, j^ph, j^r, j^th);
-//   k_dep_cell      one warp per cell: fixed-order tree sum of its particles'
-//                   shares into 20 stencil slots;
+//   k_dep_cell      one warp per cell, one lane per stencil slot (20):
+//                   fixed-order sum of the cell's particles' shares;
 //   k_dep_node      one thread per node: fixed-order sum of the slots of the
 //                   (up to six) cells touching it, / (2 pi V_dual).
 // The FDTD is HBM-bound; its metric factors come from tables built once.
@@ -337,33 +337,67 @@ static int sort_impl(fpic_ctx* c, fpic_particles* p, Work& w, cudaStream_t s)
 // Deposit (Sec. 2.3)
 // ---------------------------------------------------------------------------
 
+// (s, c) of angle x + h from (s, c) of x and (sin h, cos h - 1).
+__device__ __forceinline__ void rotate(double s, double c, double sh, double cm, double& so, double& co)
+{
+    so = fma(s, cm, fma(c, sh, s));
+    co = fma(c, cm, fma(-s, sh, c));
+}
+
+// sin/cos at the 7 lattice th values of the th cell [y0, y1] split at t:
+// y0 + l hc (l = 0..3, y0 + 3 hc = t), t + l hd (l = 1..3, t + 3 hd = y1).
+// The end points come in (node tables, the particle's own sin/cos); the
+// interior points are angle-addition rotations by hc, 2 hc, hd, 2 hd.
+__device__ __forceinline__ void theta_lattice(double hc, double hd, double s0, double c0, double st, double ct,
+                                              double s1, double c1, double sy[7], double cy[7])
+{
+    double sh, cm;
+    sy[0] = s0; cy[0] = c0;
+    sy[3] = st; cy[3] = ct;
+    sy[6] = s1; cy[6] = c1;
+    sincos_step(hc, sh, cm);
+    rotate(s0, c0, sh, cm, sy[1], cy[1]);
+    // double angle: sin 2h = 2 sin h cos h, cos 2h - 1 = 2 (cos h - 1)(cos h + 1)
+    rotate(s0, c0, 2.0 * fma(sh, cm, sh), 2.0 * cm * (cm + 2.0), sy[2], cy[2]);
+    sincos_step(hd, sh, cm);
+    rotate(st, ct, sh, cm, sy[4], cy[4]);
+    rotate(st, ct, 2.0 * fma(sh, cm, sh), 2.0 * cm * (cm + 2.0), sy[5], cy[5]);
+}
+
 // 4x4 trapezoid lattice of a sub-grid cell [x0, x1] x [y0, y1] split at
 // (r, t): the four subvolumes V00 = [x0,r]x[y0,t], V10 = [r,x1]x[y0,t],
 // V01 = [x0,r]x[t,y1], V11 = [r,x1]x[t,y1], each by its own 4 x 4 rule; the
-// points of the 7 x 7 lattice are evaluated once.
-__device__ __forceinline__ void subvolumes(const BH& bh, double x0, double x1, double r, double y0, double y1,
-                                           double t, const double sy[7], const double cy[7], double V[4])
+// points of the 7 x 7 lattice are evaluated once.  With X = x^2,
+// B = X + 2 M x and A = a^2 cos^2 th, sqrt(gamma) = sin th sqrt((X + A)(B + A))
+// and the radicand is X B + A (X + B + A): two operations per point.  The
+// sin th factor is applied once per lattice row.
+__device__ __forceinline__ void subvolumes(const BH& bh, double x0, double x1, double r, double hc, double hd,
+                                           const double sy[7], const double cy[7], double V[4])
 {
-    double xs[7];
-    const double ha = (r - x0) / 3.0, hb = (x1 - r) / 3.0;
+    const double third = 1.0 / 3.0;
+    const double ha = (r - x0) * third, hb = (x1 - r) * third;
+    double P[7], Q[7];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) xs[k] = x0 + k * ha;
-#pragma unroll
-    for (int k = 1; k < 4; ++k) xs[3 + k] = r + k * hb;
-    const double hc = (t - y0) / 3.0, hd = (y1 - t) / 3.0;
-    const double wt[4] = {0.5, 1.0, 1.0, 0.5};
+    for (int k = 0; k < 7; ++k) {
+        const double x = k < 3 ? fma((double)k, ha, x0) : (k == 3 ? r : fma((double)(k - 3), hb, r));
+        const double X = x * x, B = fma(bh.twoM, x, X);
+        P[k] = X * B;
+        Q[k] = X + B;
+    }
     double S00 = 0, S10 = 0, S01 = 0, S11 = 0;
 #pragma unroll
     for (int l = 0; l < 7; ++l) {
-        double ra = 0.0, rb = 0.0;    // rows over the lower (a) and upper (b) r halves
+        const double A = bh.a2 * (cy[l] * cy[l]);
+        double f[7];
 #pragma unroll
-        for (int k = 0; k < 7; ++k) {
-            const double f = sqrtg_sc(bh, xs[k], sy[l], cy[l]);
-            if (k <= 3) ra = fma(wt[k], f, ra);
-            if (k >= 3) rb = fma(wt[k - 3], f, rb);
-        }
-        if (l <= 3) { S00 = fma(wt[l], ra, S00); S10 = fma(wt[l], rb, S10); }
-        if (l >= 3) { S01 = fma(wt[l - 3], ra, S01); S11 = fma(wt[l - 3], rb, S11); }
+        for (int k = 0; k < 7; ++k) f[k] = sqrt_dep(fma(A, Q[k] + A, P[k]));
+        // trapezoid weights 1/2, 1, 1, 1/2 along r on each half
+        const double ra = sy[l] * fma(0.5, f[0] + f[3], f[1] + f[2]);
+        const double rb = sy[l] * fma(0.5, f[3] + f[6], f[4] + f[5]);
+        const double wl = (l == 0 || l == 6) ? 0.5 : 1.0;
+        if (l < 3) { S00 = fma(wl, ra, S00); S10 = fma(wl, rb, S10); }
+        if (l == 3) { S00 = fma(0.5, ra, S00); S10 = fma(0.5, rb, S10); S01 = fma(0.5, ra, S01); S11 = fma(0.5, rb, S11); }
+        if (l > 3) { S01 = fma(wl, ra, S01); S11 = fma(wl, rb, S11); }
     }
     V[0] = S00 * (ha * hc);
     V[1] = S10 * (hb * hc);
@@ -371,19 +405,10 @@ __device__ __forceinline__ void subvolumes(const BH& bh, double x0, double x1, d
     V[3] = S11 * (hb * hd);
 }
 
-// sin/cos at the 7 lattice th values of the th cell [y0, y1] split at t.
-__device__ __forceinline__ void theta_lattice(double y0, double y1, double t, double sy[7], double cy[7])
-{
-    const double hc = (t - y0) / 3.0, hd = (y1 - t) / 3.0;
-#pragma unroll
-    for (int l = 0; l < 4; ++l) sincos(y0 + l * hc, &sy[l], &cy[l]);
-#pragma unroll
-    for (int l = 1; l < 4; ++l) sincos(t + l * hd, &sy[3 + l], &cy[3 + l]);
-}
-
 struct DepK {
     BH bh;
     GridDev G;
+    const double* trig;  // sin tn[0..Nth], cos tn[0..Nth], sin th[0..Nth-1], cos th[0..Nth-1]
     const double *r, *th, *ur, *uth, *uph, *qm, *w;
     long long n_alive;
     double* rec;     // 16 x n
@@ -421,27 +446,41 @@ __global__ void __launch_bounds__(128) k_dep_particle(DepK k)
     locate(G.rh, G.irh, G.Nr, rh_c, (lr - G.lrh0) * G.ilr, i1, wd);
     locate(G.tn, G.itn, G.Nth + 1, tn_c, ((float)t - G.t0) * G.it, j0, wd);
     locate(G.th, G.ith, G.Nth, th_c, ((float)t - G.th0) * G.it, j1, wd);
+    // sin/cos at the clamped th (the particle's own unless clamped at an edge)
+    double stn = s, ctn = c, sth = s, cth = c;
+    if (tn_c != t) sincos(tn_c, &stn, &ctn);
+    if (th_c != t) sincos(th_c, &sth, &cth);
+    const double* sn = k.trig;
+    const double* cn = k.trig + (G.Nth + 1);
+    const double* sh = k.trig + 2 * (G.Nth + 1);
+    const double* ch = sh + G.Nth;
+    const double third = 1.0 / 3.0;
     double sy[7], cy[7], V[4];
     const long long n = k.n_alive;
     // (i, j): rho and j^ph
-    theta_lattice(G.tn[j0], G.tn[j0 + 1], tn_c, sy, cy);
-    subvolumes(k.bh, G.rn[i0], G.rn[i0 + 1], rn_c, G.tn[j0], G.tn[j0 + 1], tn_c, sy, cy, V);
-    double iV = 1.0 / (V[0] + V[1] + V[2] + V[3]);
+    const double y0 = G.tn[j0], y1 = G.tn[j0 + 1];
+    double hc = (tn_c - y0) * third, hd = (y1 - tn_c) * third;
+    theta_lattice(hc, hd, sn[j0], cn[j0], stn, ctn, sn[j0 + 1], cn[j0 + 1], sy, cy);
+    subvolumes(k.bh, G.rn[i0], G.rn[i0 + 1], rn_c, hc, hd, sy, cy, V);
+    double iV = rcp_nr(V[0] + V[1] + V[2] + V[3]);
     // share of node (i+a, j+b) = V(opposite corner) / V
     const double w00 = V[3] * iV, w10 = V[2] * iV, w01 = V[1] * iV, w11 = V[0] * iV;
     k.rec[0 * n + p] = Q * w00; k.rec[1 * n + p] = Q * w10; k.rec[2 * n + p] = Q * w01; k.rec[3 * n + p] = Q * w11;
     const double Qp = Q * vp;
     k.rec[4 * n + p] = Qp * w00; k.rec[5 * n + p] = Qp * w10; k.rec[6 * n + p] = Qp * w01; k.rec[7 * n + p] = Qp * w11;
     // (i+1/2, j): j^r  (same th lattice)
-    subvolumes(k.bh, G.rh[i1], G.rh[i1 + 1], rh_c, G.tn[j0], G.tn[j0 + 1], tn_c, sy, cy, V);
-    iV = 1.0 / (V[0] + V[1] + V[2] + V[3]);
+    subvolumes(k.bh, G.rh[i1], G.rh[i1 + 1], rh_c, hc, hd, sy, cy, V);
+    iV = rcp_nr(V[0] + V[1] + V[2] + V[3]);
     const double Qr = Q * vr;
     k.rec[8 * n + p] = Qr * (V[3] * iV); k.rec[9 * n + p] = Qr * (V[2] * iV);
     k.rec[10 * n + p] = Qr * (V[1] * iV); k.rec[11 * n + p] = Qr * (V[0] * iV);
     // (i, j+1/2): j^th
-    theta_lattice(G.th[j1], G.th[j1 + 1], th_c, sy, cy);
-    subvolumes(k.bh, G.rn[i0], G.rn[i0 + 1], rn_c, G.th[j1], G.th[j1 + 1], th_c, sy, cy, V);
-    iV = 1.0 / (V[0] + V[1] + V[2] + V[3]);
+    const double z0 = G.th[j1], z1 = G.th[j1 + 1];
+    hc = (th_c - z0) * third;
+    hd = (z1 - th_c) * third;
+    theta_lattice(hc, hd, sh[j1], ch[j1], sth, cth, sh[j1 + 1], ch[j1 + 1], sy, cy);
+    subvolumes(k.bh, G.rn[i0], G.rn[i0 + 1], rn_c, hc, hd, sy, cy, V);
+    iV = rcp_nr(V[0] + V[1] + V[2] + V[3]);
     const double Qt = Q * vt;
     k.rec[12 * n + p] = Qt * (V[3] * iV); k.rec[13 * n + p] = Qt * (V[2] * iV);
     k.rec[14 * n + p] = Qt * (V[1] * iV); k.rec[15 * n + p] = Qt * (V[0] * iV);
@@ -450,44 +489,47 @@ __global__ void __launch_bounds__(128) k_dep_particle(DepK k)
 
 // Slots of a cell (i0, j0): rho[a + 2b] (0..3), j^ph[a + 2b] (4..7),
 // j^r[k + 3b] at half-r node i0 - 1 + k (8..13), j^th[a + 2k] at half-th
-// node j0 - 1 + k (14..19).
+// node j0 - 1 + k (14..19).  Record row feeding slot q of a particle with
+// offsets (ko, kt), or -1 when the particle does not touch that slot.
+__device__ __forceinline__ int slot_row(int q, uint32_t cd)
+{
+    if (q < 8) return q;
+    if (q < 14) {
+        const int kk = (q - 8) % 3, b = (q - 8) / 3, ko = cd & 3;
+        return kk == ko ? 8 + 2 * b : (kk == ko + 1 ? 9 + 2 * b : -1);
+    }
+    const int a = (q - 14) & 1, kk = (q - 14) >> 1, kt = (cd >> 2) & 3;
+    return kk == kt ? 12 + a : (kk == kt + 1 ? 14 + a : -1);
+}
+
+// One warp per cell; lane q < 20 owns slot q and adds the cell's particles
+// in their sorted order (fixed order: bitwise reproducible).  Four
+// particles' records are loaded ahead of the additions.
 __global__ void __launch_bounds__(256) k_dep_cell(const double* __restrict__ rec, const uint32_t* __restrict__ code,
                                                    const uint32_t* __restrict__ off, double* __restrict__ part,
                                                    long long n, uint32_t C)
 {
     const long long cell = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (cell >= C) return;
+    const int q = threadIdx.x & 31;
+    if (cell >= C || q >= 20) return;
     const uint32_t b0 = off[cell], b1 = off[cell + 1];
-    double acc[20];
+    double acc = 0.0;
+    uint32_t a = b0;
+    for (; a + 4 <= b1; a += 4) {
+        double v[4];
 #pragma unroll
-    for (int q = 0; q < 20; ++q) acc[q] = 0.0;
-    for (uint32_t a = b0 + lane; a < b1; a += 32) {
-        const uint32_t cd = code[a];
-        const int ko = cd & 3, kt = (cd >> 2) & 3;     // half-r / half-th slot offsets (0 or 1)
-#pragma unroll
-        for (int q = 0; q < 8; ++q) acc[q] += rec[(size_t)q * n + a];
-        const double r0 = rec[8 * n + a], r1 = rec[9 * n + a], r2 = rec[10 * n + a], r3 = rec[11 * n + a];
-        // j^r shares: (node i1, j0), (i1+1, j0), (i1, j0+1), (i1+1, j0+1); i1 = i0 - 1 + ko
-#pragma unroll
-        for (int kk = 0; kk < 3; ++kk) {
-            acc[8 + kk] += (kk == ko ? r0 : 0.0) + (kk == ko + 1 ? r1 : 0.0);
-            acc[11 + kk] += (kk == ko ? r2 : 0.0) + (kk == ko + 1 ? r3 : 0.0);
+        for (int u = 0; u < 4; ++u) {
+            const int row = slot_row(q, __ldg(code + a + u));
+            v[u] = row >= 0 ? __ldg(rec + (size_t)row * n + a + u) : 0.0;
         }
-        const double t0 = rec[12 * n + a], t1 = rec[13 * n + a], t2 = rec[14 * n + a], t3 = rec[15 * n + a];
-        // j^th shares: (i0, j1), (i0+1, j1), (i0, j1+1), (i0+1, j1+1); j1 = j0 - 1 + kt
 #pragma unroll
-        for (int kk = 0; kk < 3; ++kk) {
-            acc[14 + 2 * kk] += (kk == kt ? t0 : 0.0) + (kk == kt + 1 ? t2 : 0.0);
-            acc[15 + 2 * kk] += (kk == kt ? t1 : 0.0) + (kk == kt + 1 ? t3 : 0.0);
-        }
+        for (int u = 0; u < 4; ++u) acc += v[u];
     }
-#pragma unroll
-    for (int q = 0; q < 20; ++q) {
-        double v = acc[q];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) part[(size_t)q * C + cell] = v;
+    for (; a < b1; ++a) {
+        const int row = slot_row(q, __ldg(code + a));
+        if (row >= 0) acc += __ldg(rec + (size_t)row * n + a);
     }
+    part[(size_t)q * C + cell] = acc;
 }
 
 struct NodeK {
@@ -783,7 +825,7 @@ extern "C" int fpic_deposit(fpic_ctx* c, fpic_particles* p, double* rho, double*
         FPIC_CUDA(cudaMemsetAsync(w.off, 0, 4 * ((size_t)C + 2), s));
     }
     // alive particles occupy [0, off[C]) after the sort; the count is read on the device
-    DepK k{c->bh, c->G, p->r, p->th, p->ur, p->uth, p->uph, p->qm, p->w, n, w.rec, w.code};
+    DepK k{c->bh, c->G, c->d_metric + (size_t)MT_N * c->metric_stride, p->r, p->th, p->ur, p->uth, p->uph, p->qm, p->w, n, w.rec, w.code};
     if (n > 0) {
         // rec/code for all n slots; removed particles (past off[C]) are never summed
         k_dep_particle<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(k);

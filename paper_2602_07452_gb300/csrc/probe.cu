@@ -20,7 +20,34 @@ __global__ void __launch_bounds__(256) k_fma64(double* out, int reps, double x)
     out[blockIdx.x * blockDim.x + threadIdx.x] = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
 }
 
+__global__ void k_math(int fn, const double* __restrict__ x, double* __restrict__ y, long long n)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double v = x[i];
+    if (fn == 0) {
+        y[i] = rcp_nr(v);
+    } else if (fn == 1) {
+        y[i] = sqrt_dep(v);
+    } else {
+        double sh, cm;
+        sincos_step(v, sh, cm);
+        y[2 * i] = sh;
+        y[2 * i + 1] = cm;
+    }
+}
+
 }  // namespace fpic
+
+extern "C" int fpic_probe_math(int fn, const double* x, double* y, long long n, void* stream)
+{
+    using namespace fpic;
+    if (fn < 0 || fn > 2 || n < 0 || (n > 0 && (!x || !y))) return set_error(FPIC_EINVAL, "fpic_probe_math: bad argument");
+    if (n == 0) return FPIC_OK;
+    k_math<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(fn, x, y, n);
+    FPIC_CUDA(cudaGetLastError());
+    return FPIC_OK;
+}
 
 extern "C" int fpic_probe_fp64(double* gflops_out, int reps)
 {

@@ -54,6 +54,11 @@ struct PushK {
     float* recT;            // n x 16 targets (sampling)
     float* recS;            // n labels (sampling)
     double inc_scale[6];    // scale of the implicit-step increments
+    // corrector form of the learned guess (per implicit-queue slot)
+    float* featX;           // 16 floats: trial features (network input)
+    float* featS;           // 16 floats: scales s_i (0-5), leading-order gaps g_i (8-13)
+    double* stg;            // 12 x n: RK4 slopes k1, k2 of the trial, then A, B, then the trial
+    float fmean[14], fistd[14];
 };
 
 __device__ __forceinline__ void load_state(const PartDev& P, long long p, double z[6])
@@ -133,7 +138,26 @@ __device__ __forceinline__ void warp_add(long long* c, long long v, unsigned mas
     if ((threadIdx.x & 31) == __ffs(mask) - 1 && v) atomicAdd((unsigned long long*)c, (unsigned long long)v);
 }
 
-// MODE 0: RK4 only.  MODE 1: hybrid (RK4 trial + test + enqueue).
+// Corrector form, rejected particle p: from the slopes k1, k2 in the stg
+// scratch, acc = k1 + 2 k2 + 2 k3 and k4, the stage differences
+// A = dt (k3 - k2) and B = dt (k4 - 2 k2 + k1) overwrite k1, k2 in stg.
+__device__ __forceinline__ void trial_diffs(const PushK& k, long long p, const double acc[6], const double k4[6])
+{
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        double* a = k.stg + (size_t)i * k.n + p;
+        double* b = k.stg + (size_t)(6 + i) * k.n + p;
+        const double k1 = *a, k2 = *b;
+        *a = k.dt * fma(0.5, acc[i] - k1, -2.0 * k2);
+        *b = k.dt * ((k4[i] - k2) - (k2 - k1));
+    }
+}
+
+// MODE 0: RK4 only.  MODE 1: hybrid (RK4 trial + test + enqueue).  MODE 2:
+// hybrid that also writes the trial features of each rejected particle
+// (corrector form of the learned guess); its slopes k1, k2 go through the
+// stg scratch (12 doubles of HBM traffic per particle) rather than staying
+// live in registers across the later stages.
 template <int MODE>
 __global__ void __launch_bounds__(128) k_explicit(PushK k)
 {
@@ -159,11 +183,19 @@ __global__ void __launch_bounds__(128) k_explicit(PushK k)
     sincos(z0[1], &s0, &c0);
     F_at_sc(k.run, z0, s0, c0, qm, em, kk, Hd);
 #pragma unroll
-    for (int i = 0; i < 6; ++i) { acc[i] = kk[i]; y[i] = fma(hdt, kk[i], z0[i]); }
+    for (int i = 0; i < 6; ++i) {
+        acc[i] = kk[i];
+        y[i] = fma(hdt, kk[i], z0[i]);
+        if (MODE == 2) k.stg[(size_t)i * k.n + p] = kk[i];
+    }
     sincos_near(z0[1], s0, c0, y[1], sn, cn);
     F_at_sc(k.run, y, sn, cn, qm, em, kk, Hd);
 #pragma unroll
-    for (int i = 0; i < 6; ++i) { acc[i] = fma(2.0, kk[i], acc[i]); y[i] = fma(hdt, kk[i], z0[i]); }
+    for (int i = 0; i < 6; ++i) {
+        acc[i] = fma(2.0, kk[i], acc[i]);
+        y[i] = fma(hdt, kk[i], z0[i]);
+        if (MODE == 2) k.stg[(size_t)(6 + i) * k.n + p] = kk[i];
+    }
     sincos_near(z0[1], s0, c0, y[1], sn, cn);
     F_at_sc(k.run, y, sn, cn, qm, em, kk, Hd);
 #pragma unroll
@@ -176,7 +208,7 @@ __global__ void __launch_bounds__(128) k_explicit(PushK k)
     sincos_near(z0[1], s0, c0, y[1], sn, cn);
     const double H1 = eval_H_sc(k.run.bh, y, sn, cn, qm, k.run.B0pot);
     bool accept = true;
-    if (MODE == 1) {
+    if (MODE >= 1) {
         const double H0 = k.P.H0[p], D0 = k.P.D0[p];
         const double Ht1 = fabs(H1 - H0) / D0;
         if (k.scheme == FPIC_HYB2) {
@@ -186,8 +218,9 @@ __global__ void __launch_bounds__(128) k_explicit(PushK k)
             accept = (Ht1 - Htn) / dt < k.thr;
         }
     }
+    const float label = accept ? 0.f : 1.f;
     if (k.record) {                 // sampling: label, then every particle goes implicit
-        k.recS[p] = accept ? 0.f : 1.f;
+        if (MODE != 2) k.recS[p] = label;
         accept = false;
     }
     const unsigned act = __activemask();
@@ -205,6 +238,10 @@ __global__ void __launch_bounds__(128) k_explicit(PushK k)
             k.queue[idx] = (uint32_t)p;
 #pragma unroll
             for (int i = 0; i < 6; ++i) k.guess[(size_t)i * k.n + p] = y[i];
+            if (MODE == 2) {
+                trial_diffs(k, p, acc, kk);
+                if (k.record) k.recS[idx] = label;
+            }
         }
     }
 }
@@ -221,13 +258,16 @@ __device__ __forceinline__ bool conv6(const double a[6], const double b[6], doub
 // z^[k] = z^n + dt F((z^n + z^[k-1]) / 2), then one evaluation at the
 // converged point for H.  all_mode: the queue is every particle (pure IMR,
 // guess z^n); otherwise entries come from k_explicit with their trial.
-__global__ void __launch_bounds__(128) k_imr(PushK k, int all_mode)
+// RESTART 1: a solve that does not converge restarts once from the trial in
+// stg (corrector form of the learned guess).
+template <int RESTART>
+__global__ void __launch_bounds__(128, 4) k_imr(PushK k, int all_mode)
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const long long qn = all_mode ? k.n : k.cnt[CNT_QUEUE];
-    long long p = -1;
-    bool exhausted = false, fin = false;
+    long long p = -1, qi = 0;
+    bool exhausted = false, fin = false, again = false;
     double z0[6], zk[6];
     double qm = 0.0, s0 = 0.0, c0 = 1.0;
     bool em = false;
@@ -251,6 +291,8 @@ __global__ void __launch_bounds__(128) k_imr(PushK k, int all_mode)
                         k.P.iters[q] = 0;
                     } else {
                         p = q;
+                        qi = idx;
+                        again = RESTART != 0;
                         load_state(k.P, p, z0);
                         if (all_mode) {
 #pragma unroll
@@ -296,12 +338,31 @@ __global__ void __launch_bounds__(128) k_imr(PushK k, int all_mode)
 #pragma unroll
                 for (int i = 0; i < 6; ++i) zk[i] = zn[i];
                 ++it;
-                if (ok || it >= k.max_iter) {
+                if (RESTART && !ok && it >= k.max_iter && again) {
+                    // the corrected start did not converge: the plain trial is the fallback
+                    again = false;
+                    n_it += it;
+                    it = 0;
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) zk[i] = k.stg[(size_t)i * k.n + p];
+                } else if (ok || it >= k.max_iter) {
                     fin = true;
                     if (!ok) ++n_nc;
                 }
             } else {
-                if (k.record) {
+                if (k.record && k.featS) {
+                    // corrector form: row = queue slot, (gap to the trial - leading-order gap) / s_i
+                    float* t = k.recT + 16 * qi;
+                    const float* sc = k.featS + 16 * qi;
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) {
+                        const double g = (zk[i] - k.guess[(size_t)i * k.n + p] - (double)sc[8 + i]) / (double)sc[i];
+                        t[i] = sc[i] > 0.f ? (float)fmin(16.0, fmax(-16.0, g)) : 0.f;
+                    }
+                    t[6] = 0.f;
+                    t[7] = (float)(it - 8) * 0.25f;
+                    t[8] = 0.f;
+                } else if (k.record) {
                     float* t = k.recT + 16 * p;
 #pragma unroll
                     for (int i = 0; i < 6; ++i) t[i] = (float)((zk[i] - z0[i]) / k.inc_scale[i]);
@@ -546,9 +607,9 @@ extern "C" int fpic_push(fpic_ctx* c, fpic_particles* p, const double* const fie
         FPIC_CUDA(cudaEventRecord(ev[1], s));
         FPIC_CUDA(cudaEventRecord(ev[2], s));
     }
-    if (prm->scheme == FPIC_IMR) k_imr<<<persist, TB, 0, s>>>(k, 1);
+    if (prm->scheme == FPIC_IMR) k_imr<0><<<persist, TB, 0, s>>>(k, 1);
     else if (prm->scheme == FPIC_HAM) k_dg<<<nb, TB, 0, s>>>(k, 1);
-    else if (prm->scheme >= FPIC_HYB1 && prm->implicit == FPIC_IMR) k_imr<<<persist, TB, 0, s>>>(k, 0);
+    else if (prm->scheme >= FPIC_HYB1 && prm->implicit == FPIC_IMR) k_imr<0><<<persist, TB, 0, s>>>(k, 0);
     else if (prm->scheme >= FPIC_HYB1) k_dg<<<nb, TB, 0, s>>>(k, 0);
     if (ev) FPIC_CUDA(cudaEventRecord(ev[3], s));
     FPIC_CUDA(cudaGetLastError());
@@ -719,9 +780,9 @@ extern "C" int fpic_push_noalloc(double M, double a, fpic_particles* p, const fp
         FPIC_CUDA(cudaEventRecord(ev[1], s));
         FPIC_CUDA(cudaEventRecord(ev[2], s));
     }
-    if (prm->scheme == FPIC_IMR) k_imr<<<persist, TB, 0, s>>>(k, 1);
+    if (prm->scheme == FPIC_IMR) k_imr<0><<<persist, TB, 0, s>>>(k, 1);
     else if (prm->scheme == FPIC_HAM) k_dg<<<nb, TB, 0, s>>>(k, 1);
-    else if (prm->scheme >= FPIC_HYB1 && prm->implicit == FPIC_IMR) k_imr<<<persist, TB, 0, s>>>(k, 0);
+    else if (prm->scheme >= FPIC_HYB1 && prm->implicit == FPIC_IMR) k_imr<0><<<persist, TB, 0, s>>>(k, 0);
     else if (prm->scheme >= FPIC_HYB1) k_dg<<<nb, TB, 0, s>>>(k, 0);
     if (ev) FPIC_CUDA(cudaEventRecord(ev[3], s));
     FPIC_CUDA(cudaGetLastError());
@@ -884,17 +945,20 @@ static void fill_pushk(PushK& k, fpic_ctx* c, fpic_particles* p, const double* c
     k.cnt = c->d_cnt;
 }
 
-// scratch: guess 6n doubles | queue n | work n | X 16n floats | Y 16n floats | 6 FP32 field copies
+// scratch: guess 6n doubles | stg 12n doubles | queue n | work n | X 16n floats |
+// Y 16n floats | featS 16n floats | 6 FP32 field copies
 static int learned_scratch(fpic_ctx* c, long long n, PushK& k, float** X, float** Y, float** f32)
 {
     const size_t fsz = c->has_grid ? 6 * (size_t)(c->Nr + 1) * c->ld : 0;
-    const size_t need = (size_t)n * (6 * sizeof(double) + 2 * sizeof(uint32_t) + 32 * sizeof(float)) +
+    const size_t need = (size_t)n * (18 * sizeof(double) + 2 * sizeof(uint32_t) + 48 * sizeof(float)) +
                         fsz * sizeof(float) + 2048;
     int rc = ensure_scratch(c, need);
     if (rc) return rc;
     char* b = (char*)c->d_scratch;
     k.guess = (double*)b;
     b += (size_t)n * 6 * sizeof(double);
+    k.stg = (double*)b;
+    b += (size_t)n * 12 * sizeof(double);
     k.queue = (uint32_t*)b;
     b += (size_t)n * sizeof(uint32_t);
     k.work = (uint32_t*)b;
@@ -904,8 +968,97 @@ static int learned_scratch(fpic_ctx* c, long long n, PushK& k, float** X, float*
     b += (size_t)n * 16 * sizeof(float);
     *Y = (float*)b;
     b += (size_t)n * 16 * sizeof(float);
+    k.featS = (float*)b;
+    b += (size_t)n * 16 * sizeof(float);
     *f32 = (float*)b;
     return 0;
+}
+
+static void set_corrector(PushK& k, const fpic_learned_cfg* cfg, float* X)
+{
+    k.featX = X;
+    for (int i = 0; i < 14; ++i) {
+        k.fmean[i] = cfg->feat_mean[i];
+        k.fistd[i] = cfg->feat_std[i] > 0.f ? 1.f / cfg->feat_std[i] : 1.f;
+    }
+}
+
+// Corrector form, one thread per implicit-queue slot (the count is read on
+// the device): trial features from the stage differences A, B in stg
+// (per component i: A_i / s_i, B_i / s_i with s_i = |A_i| + |B_i|, zero when
+// both vanish; then ln r, th; standardised) and, next to the scales s_i, the
+// leading-order gap between the implicit midpoint step and the RK4 trial,
+// g = (2/3) A - (1/6) B: expanding both steps in dt, IMR - RK4 =
+// dt^3 (f'f'f / 12 - f''(f,f) / 24) + O(dt^4), while k3 - k2 =
+// dt^2 f'f'f / 4 + O(dt^3) and k4 - 2 k2 + k1 = dt^2 (f'f'f / 2 +
+// f''(f,f) / 4) + O(dt^3).
+__global__ void k_trial_feat(PushK k)
+{
+    const long long qn = k.cnt[CNT_QUEUE];
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < qn;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long p = k.queue[idx];
+        float f[16], sc[16];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            const double a = k.stg[(size_t)i * k.n + p], b = k.stg[(size_t)(6 + i) * k.n + p];
+            const double sm = fabs(a) + fabs(b);
+            sc[8 + i] = (float)fma(2.0 / 3.0, a, -b / 6.0);
+            if (sm > 0.0) {
+                f[i] = (float)(a / sm);
+                f[6 + i] = (float)(b / sm);
+                sc[i] = (float)sm;
+            } else {
+                f[i] = 0.f;
+                f[6 + i] = 0.f;
+                sc[i] = 0.f;
+            }
+        }
+        f[12] = __logf((float)k.P.r[p]);
+        f[13] = (float)k.P.th[p];
+#pragma unroll
+        for (int i = 0; i < 14; ++i) f[i] = (f[i] - k.fmean[i]) * k.fistd[i];
+        f[14] = f[15] = 0.f;
+        sc[6] = sc[7] = sc[14] = sc[15] = 0.f;
+        float4* x = (float4*)(k.featX + 16 * idx);
+        float4* o = (float4*)(k.featS + 16 * idx);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            x[q] = make_float4(f[4 * q], f[4 * q + 1], f[4 * q + 2], f[4 * q + 3]);
+            o[q] = make_float4(sc[4 * q], sc[4 * q + 1], sc[4 * q + 2], sc[4 * q + 3]);
+        }
+    }
+}
+
+// Corrector form: the trial z_RK4 of queue slot idx is kept in stg (for the
+// restart), and the implicit guess becomes z_RK4 + g_i + s_i y_i (g the
+// leading-order gap).  Guard: the IMR - RK4 gap is O(dt^3) against the
+// O(dt) step, so a correction larger than CORR_MAX times the trial's own
+// increment in a component (or a prediction outside [-16, 16] or not
+// finite) leaves that component of the trial unchanged.
+constexpr double CORR_MAX = 0.05;
+__global__ void k_correct(PushK k, const float* __restrict__ Y)
+{
+    const long long qn = k.cnt[CNT_QUEUE];
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < qn;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long p = k.queue[idx];
+        const float4 y0 = *(const float4*)(Y + 16 * idx), y1 = *(const float4*)(Y + 16 * idx + 4);
+        const float4* fs = (const float4*)(k.featS + 16 * idx);
+        const float4 s0 = fs[0], s1 = fs[1], g0 = fs[2], g1 = fs[3];
+        const float y[6] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y};
+        const float sc[6] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y};
+        const float gl[6] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y};
+        double z0[6];
+        load_state(k.P, p, z0);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            const double zt = k.guess[(size_t)i * k.n + p];
+            const double d = (double)gl[i] + (double)sc[i] * (double)y[i];
+            k.stg[(size_t)i * k.n + p] = zt;
+            if (fabsf(y[i]) <= 16.f && fabs(d) <= CORR_MAX * fabs(zt - z0[i])) k.guess[(size_t)i * k.n + p] = zt + d;
+        }
+    }
 }
 
 // FP32 copies of the field arrays (network inputs are rounded to bf16 anyway;
@@ -990,13 +1143,26 @@ extern "C" int fpic_learn_sample(fpic_ctx* c, fpic_particles* p, const double* c
     k.recS = S;
     for (int i = 0; i < 6; ++i) k.inc_scale[i] = cfg ? cfg->inc_scale[i] : 1.0;
     FPIC_CUDA(cudaMemsetAsync(c->d_cnt, 0, CNT_N * sizeof(long long), s));
+    const unsigned nb = (unsigned)((n + 127) / 128);
+    if (cfg && cfg->mode == FPIC_LEARN_CORRECT) {
+        // rows = implicit-queue slots (every alive particle is queued)
+        FPIC_CUDA(cudaMemsetAsync(X, 0, (size_t)n * 16 * sizeof(float), s));
+        FPIC_CUDA(cudaMemsetAsync(T, 0, (size_t)n * 16 * sizeof(float), s));
+        FPIC_CUDA(cudaMemsetAsync(S, 0, (size_t)n * sizeof(float), s));
+        set_corrector(k, cfg, X);
+        k_explicit<2><<<nb, 128, 0, s>>>(k);
+        k_trial_feat<<<(unsigned)c->sm_count * 8u, 256, 0, s>>>(k);
+        k_imr<0><<<(unsigned)c->sm_count * 8u, 128, 0, s>>>(k, 0);
+        FPIC_CUDA(cudaGetLastError());
+        return FPIC_OK;
+    }
+    k.featS = nullptr;
     FeatK f = make_featk(c, p, fields, prm->dt, cfg, X, f32, s);
     f.T = T;
     f.S = S;
-    const unsigned nb = (unsigned)((n + 127) / 128);
     k_features<<<nb, 128, 0, s>>>(f);
     k_explicit<1><<<nb, 128, 0, s>>>(k);
-    k_imr<<<(unsigned)c->sm_count * 8u, 128, 0, s>>>(k, 0);
+    k_imr<0><<<(unsigned)c->sm_count * 8u, 128, 0, s>>>(k, 0);
     FPIC_CUDA(cudaGetLastError());
     return FPIC_OK;
 }
@@ -1010,7 +1176,10 @@ extern "C" int fpic_push_learned(fpic_ctx* c, fpic_mlp* m, fpic_particles* p, co
     if (p->n < 0 || p->n >= (1LL << 31)) return set_error(FPIC_EINVAL, "fpic_push_learned: n out of range");
     if (!particles_ok(p, true)) return set_error(FPIC_EINVAL, "fpic_push_learned: NULL particle array");
     if (fields && !c->has_grid) return set_error(FPIC_EINVAL, "fpic_push_learned: fields given but no grid set");
-    if (!(cfg->p_skip > 0.f && cfg->p_skip < 1.f)) return set_error(FPIC_EINVAL, "fpic_push_learned: p_skip must be in (0, 1)");
+    if (cfg->mode != FPIC_LEARN_SKIP && cfg->mode != FPIC_LEARN_CORRECT)
+        return set_error(FPIC_EINVAL, "fpic_push_learned: unknown cfg->mode");
+    if (cfg->mode == FPIC_LEARN_SKIP && !(cfg->p_skip > 0.f && cfg->p_skip < 1.f))
+        return set_error(FPIC_EINVAL, "fpic_push_learned: p_skip must be in (0, 1)");
     FPIC_CUDA(cudaSetDevice(c->device));
     cudaStream_t s = (cudaStream_t)stream;
     const long long n = p->n;
@@ -1031,19 +1200,36 @@ extern "C" int fpic_push_learned(fpic_ctx* c, fpic_mlp* m, fpic_particles* p, co
     cudaEvent_t* ev = prm->events ? (cudaEvent_t*)prm->events : nullptr;
     if (stats) k_count_alive<<<persist, 256, 0, s>>>(k.P, n, c->d_cnt);
     if (ev) FPIC_CUDA(cudaEventRecord(ev[0], s));
-    FeatK f = make_featk(c, p, fields, prm->dt, cfg, X, f32, s);
-    k_features<<<nb, 128, 0, s>>>(f);
-    rc = mlp_forward_dev(m, X, Y, n, s);
-    if (rc) return rc;
-    const float skip_logit = logf(cfg->p_skip / (1.f - cfg->p_skip));
-    k_split<<<nb, 128, 0, s>>>(k, skip_logit);
-    k_explicit<1><<<nb, 128, 0, s>>>(k);
-    if (ev) {
-        FPIC_CUDA(cudaEventRecord(ev[1], s));
-        FPIC_CUDA(cudaEventRecord(ev[2], s));
+    const bool correct = cfg->mode == FPIC_LEARN_CORRECT;
+    if (correct) {
+        // RK4 trial + plain test for all; network on the rejected ones only
+        k.work = nullptr;
+        set_corrector(k, cfg, X);
+        k_explicit<2><<<nb, 128, 0, s>>>(k);
+        if (ev) FPIC_CUDA(cudaEventRecord(ev[1], s));
+        k_trial_feat<<<persist, 256, 0, s>>>(k);
+        rc = mlp_forward_dev_count(m, X, Y, n, &c->d_cnt[CNT_QUEUE], s);
+        if (rc) return rc;
+        k_correct<<<persist, 256, 0, s>>>(k, Y);
+        if (ev) FPIC_CUDA(cudaEventRecord(ev[2], s));
+    } else {
+        // network on every particle first; predicted rejections skip the trial
+        k.featS = nullptr;
+        FeatK f = make_featk(c, p, fields, prm->dt, cfg, X, f32, s);
+        k_features<<<nb, 128, 0, s>>>(f);
+        rc = mlp_forward_dev(m, X, Y, n, s);
+        if (rc) return rc;
+        const float skip_logit = logf(cfg->p_skip / (1.f - cfg->p_skip));
+        k_split<<<nb, 128, 0, s>>>(k, skip_logit);
+        k_explicit<1><<<nb, 128, 0, s>>>(k);
+        if (ev) {
+            FPIC_CUDA(cudaEventRecord(ev[1], s));
+            FPIC_CUDA(cudaEventRecord(ev[2], s));
+        }
+        k.work = nullptr;
     }
-    k.work = nullptr;
-    k_imr<<<persist, 128, 0, s>>>(k, 0);
+    if (correct) k_imr<1><<<persist, 128, 0, s>>>(k, 0);
+    else k_imr<0><<<persist, 128, 0, s>>>(k, 0);
     if (ev) FPIC_CUDA(cudaEventRecord(ev[3], s));
     FPIC_CUDA(cudaGetLastError());
     if (stats) {
@@ -1055,7 +1241,7 @@ extern "C" int fpic_push_learned(fpic_ctx* c, fpic_mlp* m, fpic_particles* p, co
         stats->n_iter_total = h[CNT_ITERS];
         stats->n_notconv = h[CNT_NOTCONV];
         stats->n_removed = h[CNT_REMOVED];
-        stats->n_rhs_evals = h[CNT_EVALS] + 4 * h[CNT_WORK];
+        stats->n_rhs_evals = h[CNT_EVALS] + 4 * (correct ? h[CNT_ALIVE] : h[CNT_WORK]);
         if (h[CNT_NOTCONV] > 0) return FPIC_ENOTCONVERGED;
     }
     return FPIC_OK;

@@ -78,7 +78,11 @@ class fpic_run(C.Structure):
 
 class fpic_learned_cfg(C.Structure):
     _fields_ = [("feat_mean", C.c_float * 16), ("feat_std", C.c_float * 16), ("inc_scale", C.c_double * 6),
-                ("p_skip", C.c_float)]
+                ("p_skip", C.c_float),
+                ("mode", C.c_int)]
+
+
+FPIC_LEARN_SKIP, FPIC_LEARN_CORRECT = 0, 1
 
 
 # name -> (restype, argtypes)
@@ -121,6 +125,7 @@ _SIGS = {
     "fpic_push_host": (C.c_int, [C.c_void_p, C.POINTER(fpic_particles), C.POINTER(_D),
                                  C.POINTER(fpic_push_params), C.POINTER(fpic_push_stats), C.c_void_p]),
     "fpic_probe_fp64": (C.c_int, [C.POINTER(C.c_double), C.c_int]),
+    "fpic_probe_math": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p]),
     "fpic_push_noalloc": (C.c_int, [C.c_double, C.c_double, C.POINTER(fpic_particles),
                                     C.POINTER(fpic_push_params), C.POINTER(fpic_push_stats), C.c_void_p]),
     "fpic_hamiltonian": (C.c_int, [C.c_void_p, C.POINTER(fpic_particles), C.c_double, _D, _D, C.c_void_p]),
@@ -329,6 +334,15 @@ def fpic_push_host(ctx: Ctx, hp: HostParticles, fields, prm: fpic_push_params, s
     return st.as_dict() if st is not None else None
 
 
+def fpic_probe_math(fn: int, x: torch.Tensor) -> torch.Tensor:
+    """The library's FP64 elementary routine `fn` (0 reciprocal, 1 square
+    root, 2 small-step sin / cos - 1) applied to the device tensor x."""
+    x = x.contiguous()
+    y = torch.empty((x.numel(), 2) if fn == 2 else (x.numel(),), dtype=torch.float64, device=x.device)
+    _check(lib().fpic_probe_math(fn, x.data_ptr(), y.data_ptr(), x.numel(), _stream(None)))
+    return y
+
+
 def fpic_probe_fp64(reps: int = 2000) -> float:
     out = C.c_double()
     _check(lib().fpic_probe_fp64(C.byref(out), reps))
@@ -470,7 +484,7 @@ class MLP:
         return st.value
 
 
-def learned_cfg(feat_mean=None, feat_std=None, inc_scale=None, p_skip=0.5):
+def learned_cfg(feat_mean=None, feat_std=None, inc_scale=None, p_skip=0.5, mode=FPIC_LEARN_SKIP):
     cfg = fpic_learned_cfg()
     for i in range(16):
         cfg.feat_mean[i] = 0.0 if feat_mean is None or i >= len(feat_mean) else float(feat_mean[i])
@@ -478,6 +492,7 @@ def learned_cfg(feat_mean=None, feat_std=None, inc_scale=None, p_skip=0.5):
     for i in range(6):
         cfg.inc_scale[i] = 1.0 if inc_scale is None else float(inc_scale[i])
     cfg.p_skip = p_skip
+    cfg.mode = mode
     return cfg
 
 

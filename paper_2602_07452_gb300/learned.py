@@ -4,7 +4,9 @@ Generates samples from the plain hybrid pusher itself (fpic_learn_sample:
 features, the converged implicit step and the plain test's verdict for
 every particle, without moving them), advances the particles with the plain
 push, and trains the network with the tensor-core training step
-(fpic_mlp_train_step).  Dataset statistics and minibatch selection are host
+(fpic_mlp_train_step).  Two forms (see fpic_learned_cfg): the skip form
+learns from every alive particle, the corrector form from the particles the
+plain test rejects (the rows it is applied to).  Dataset statistics and minibatch selection are host
 plumbing; every network evaluation and gradient runs in the library.
 """
 from __future__ import annotations
@@ -21,17 +23,29 @@ def _alive_rows(p):
     return p.alive.bool()
 
 
-def fit_cfg(ctx, p, fields, prm, p_skip=0.5):
-    """Standardisation of features and increments from one raw sample."""
-    X, T, S = F.fpic_learn_sample(ctx, p, fields, prm, None)
-    a = _alive_rows(p)
+def _rows(p, cfg, S):
+    """Valid sample rows: particle rows of alive particles (skip form), or
+    the queue slots of the particles the plain test rejected (corrector form:
+    the only rows the network sees in the push)."""
+    if cfg is not None and cfg.mode == F.FPIC_LEARN_CORRECT:
+        m = torch.zeros_like(S, dtype=torch.bool)
+        m[: int(p.alive.sum().item())] = True
+        return m & (S > 0.5)
+    return _alive_rows(p)
+
+
+def fit_cfg(ctx, p, fields, prm, p_skip=0.5, mode=F.FPIC_LEARN_SKIP):
+    """Standardisation of features (and, skip form, increments) from one raw sample."""
+    raw = F.learned_cfg(mode=mode) if mode == F.FPIC_LEARN_CORRECT else None
+    X, T, S = F.fpic_learn_sample(ctx, p, fields, prm, raw)
+    a = _rows(p, raw, S)
     Xa, Ta = X[a][:, :14].double(), T[a][:, :6].double()
     mean = Xa.mean(0).cpu().numpy()
     std = Xa.std(0).cpu().numpy()
     std[std < 1e-30] = 1.0
     inc = Ta.std(0).cpu().numpy()
     inc[inc < 1e-300] = 1.0
-    return F.learned_cfg(mean, std, inc, p_skip)
+    return F.learned_cfg(mean, std, inc, p_skip, mode)
 
 
 def generate(ctx, p, fields, prm, cfg, steps):
@@ -39,7 +53,7 @@ def generate(ctx, p, fields, prm, cfg, steps):
     xs, ts, ss = [], [], []
     for _ in range(steps):
         X, T, S = F.fpic_learn_sample(ctx, p, fields, prm, cfg)
-        a = _alive_rows(p)
+        a = _rows(p, cfg, S)
         xs.append(X[a]); ts.append(T[a]); ss.append(S[a])
         F.fpic_push(ctx, p, fields, prm)
     return torch.cat(xs), torch.cat(ts), torch.cat(ss)

@@ -117,3 +117,119 @@ def test_learned_push_parity_and_gain(setup):
     ev_p = st_p["n_rhs_evals"] / st_p["n_alive_before"]
     ev_l = st_l["n_rhs_evals"] / st_l["n_alive_before"]
     assert ev_l < ev_p, (ev_l, ev_p, st_p, st_l)
+
+
+# ---------------------------------------------------------------------------
+# Corrector form: the network corrects the implicit guess of rejected trials
+# ---------------------------------------------------------------------------
+def _slope(g, Fo, z, q):
+    DB = O.gather(g, Fo, z[:, 0], z[:, 1])
+    return O.rhs(1.0, A, z, q, DB[:, :3], DB[:, 3:])
+
+
+def _match_rows(X, z):
+    """Row -> particle, by the (ln r, th) features (FP32) nearest to the
+    particles' own values; must be a permutation."""
+    key = np.stack([np.log(z[:, 0]), z[:, 1]], 1)
+    idx = np.empty(X.shape[0], np.int64)
+    for b in range(0, X.shape[0], 512):
+        d = np.abs(X[b:b + 512, None, 12] - key[None, :, 0]) + np.abs(X[b:b + 512, None, 13] - key[None, :, 1])
+        idx[b:b + 512] = d.argmin(1)
+    assert np.unique(idx).size == X.shape[0]
+    return idx
+
+
+def test_corrector_samples_are_the_plain_method(setup):
+    """Corrector form: one row per implicit-queue slot (every alive particle
+    in sampling); features = per-component dt (k3 - k2) and dt (k4 - 2 k2 +
+    k1) over s = |.| + |.|, then ln r, th; targets = (z_IMR - z_RK4 -
+    (2/3 A - 1/6 B)) / s, the gap left by the leading-order term; labels =
+    the plain Hyb1 verdict.  Row by row against the oracle's
+    right-hand side (RK4 stages of Sec. 2.2.1) and IMR; the particles are
+    left unchanged."""
+    F, g, Fo, ctx = setup
+    n = 2048
+    z, q, H0, D0 = _parts(n, g, 7)
+    fd = fields_dev(Fo)
+    p = make_particles(z, q, H0, D0, H0.copy())
+    prm = F.push_params(DT, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=THR, r_max=float(g.rn[-1]), B0pot=1.0)
+    X, T, S = F.fpic_learn_sample(ctx, p, fd, prm, F.learned_cfg(mode=F.FPIC_LEARN_CORRECT))
+    assert np.array_equal(p.state().cpu().numpy(), z)
+    X, T, S = (t.double().cpu().numpy() for t in (X, T, S))
+    idx = _match_rows(X, z)
+    zz, qq = z[idx], q[idx]
+    k1 = _slope(g, Fo, zz, qq)
+    k2 = _slope(g, Fo, zz + 0.5 * DT * k1, qq)
+    k3 = _slope(g, Fo, zz + 0.5 * DT * k2, qq)
+    k4 = _slope(g, Fo, zz + DT * k3, qq)
+    zr = zz + DT / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
+    Av, Bv = DT * (k3 - k2), DT * (k4 - 2 * k2 + k1)
+    s = np.abs(Av) + np.abs(Bv)
+    safe = np.where(s > 0, s, 1.0)
+    assert np.abs(X[:, :6] - np.where(s > 0, Av / safe, 0)).max() < 1e-5
+    assert np.abs(X[:, 6:12] - np.where(s > 0, Bv / safe, 0)).max() < 1e-5
+    assert np.all(X[:, 14:] == 0)
+    po = O.push_params(a=A, dt=DT, scheme=O.IMR, field_kind=O.FIELD_GRID, r_max=g.rn[-1], B0pot=1.0)
+    zi = np.ascontiguousarray(zz.copy()); Hx = H0[idx].copy()
+    O.push(po, zi, qq, H0[idx], D0[idx], Hx, np.ones(n, np.uint8), g, Fo)
+    lead = 2.0 / 3.0 * Av - Bv / 6.0            # leading-order IMR - RK4 gap
+    gap = (zi - zr - lead) / safe
+    ok = (s > 1e-12 * (np.abs(zz) + 1)) & (np.abs(gap) < 15)
+    assert ok.mean() > 0.8
+    assert np.abs(T[:, :6] - gap)[ok].max() <= 1e-4 * np.abs(gap[ok]).max() + 1e-6
+    # labels: the plain verdict of each row's particle
+    stat = (np.abs(_rk4_H(g, Fo, zr, qq) - H0[idx]) / D0[idx]) / DT
+    near = np.abs(stat - THR) < 1e-9 * THR
+    assert np.array_equal(S[~near], (stat >= THR).astype(float)[~near])
+
+
+def _rk4_H(g, Fo, zr, q):
+    H, _, _ = O.hamiltonian(1.0, A, 1.0, zr, q)
+    return H
+
+
+def test_corrector_push_parity_and_gain(setup):
+    """Train the corrector briefly on the plain pusher's rejected trials, then
+    one step from the same state with the plain and the learned push: the
+    scheme choices are identical (the trial and the test are the plain
+    ones), every particle matches the plain push and the oracle to 1e-12,
+    and the implicit solves need fewer iterations."""
+    from paper_2602_07452_gb300 import learned as L
+    F, g, Fo, ctx = setup
+    n = 1 << 16
+    z, q, H0, D0 = _parts(n, g, 8)
+    fd = fields_dev(Fo)
+    prm = F.push_params(DT, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=THR, r_max=float(g.rn[-1]), B0pot=1.0)
+    p = make_particles(z, q, H0, D0, H0.copy())
+    cfg = L.fit_cfg(ctx, p, fd, prm, mode=F.FPIC_LEARN_CORRECT)
+    X, T, S = L.generate(ctx, p, fd, prm, cfg, steps=10)
+    assert X.shape[0] > 10000 and float(S.min()) == 1.0
+    net, P, hist = L.train(X, T, S, steps=2500, batch=8192, lr=3e-3, log_every=500)
+    assert hist[-1][1] < hist[0][1]
+    zs = p.state().cpu().numpy(); Hn = p.Hn.cpu().numpy(); al = p.alive.cpu().numpy()
+    pp = make_particles(zs, q, H0, D0, Hn.copy(), al.copy())
+    pl = make_particles(zs, q, H0, D0, Hn.copy(), al.copy())
+    st_p = F.fpic_push(ctx, pp, fd, prm, stats=True)
+    st_l = F.fpic_push_learned(ctx, net, pl, fd, prm, cfg, stats=True)
+    zp, _, alp, sp, ip, _ = to_np(pp)
+    zl, Hl, alv, sl, il, _ = to_np(pl)
+    assert np.array_equal(sp, sl) and np.array_equal(alp, alv)
+    assert st_l["n_implicit"] == st_p["n_implicit"]
+    live = al == 1
+    assert (np.abs(zl - zp) / (np.abs(zp) + 1))[live].max() <= 1e-12
+    imp = (sl == 1) & live
+    po = O.push_params(a=A, dt=DT, scheme=O.IMR, field_kind=O.FIELD_GRID, r_max=g.rn[-1], B0pot=1.0)
+    zi = np.ascontiguousarray(zs[imp]); Hi = Hn[imp].copy()
+    O.push(po, zi, q[imp], H0[imp], D0[imp], Hi, np.ones(imp.sum(), np.uint8), g, Fo)
+    assert (np.abs(zl[imp] - zi) / (np.abs(zi) + 1)).max() <= 1e-12
+    # the leading-order term alone (network output zero) as the reference
+    net0 = F.MLP()
+    net0.set_params(torch.zeros_like(P))
+    p0 = make_particles(zs, q, H0, D0, Hn.copy(), al.copy())
+    st_0 = F.fpic_push_learned(ctx, net0, p0, fd, prm, cfg, stats=True)
+    assert np.array_equal(to_np(p0)[3], sp)
+    it_p = st_p["n_iter_total"] / st_p["n_implicit"]
+    it_0 = st_0["n_iter_total"] / st_0["n_implicit"]
+    it_l = st_l["n_iter_total"] / st_l["n_implicit"]
+    print("IMR iterations per implicit step: plain %.3f leading-order %.3f learned %.3f" % (it_p, it_0, it_l))
+    assert it_l < it_p and it_0 < it_p, (it_l, it_0, it_p)

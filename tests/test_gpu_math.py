@@ -1,0 +1,62 @@
+"""The library's own FP64 elementary routines against correctly rounded
+references (numpy's reciprocal and square root are IEEE correctly rounded;
+sin / cos - 1 are checked against libm in extended form)."""
+import numpy as np
+import pytest
+
+from helpers import cuda_or_skip, dev, fpic
+
+pytestmark = pytest.mark.gpu
+
+ULP = 2.0 ** -52
+
+
+@pytest.fixture(scope="module")
+def F():
+    cuda_or_skip()
+    return fpic()
+
+
+def _samples(lo, hi, n, seed):
+    rng = np.random.default_rng(seed)
+    return np.exp(rng.uniform(np.log(lo), np.log(hi), n))
+
+
+def test_reciprocal_within_two_ulp(F):
+    x = _samples(1e-30, 1e30, 1 << 20, 1)
+    x[: 1 << 19] *= -1.0
+    got = F.fpic_probe_math(0, dev(x)).cpu().numpy()
+    rel = np.abs(got * x - 1.0)
+    assert rel.max() <= 2 * ULP, rel.max()
+
+
+def test_deposit_sqrt_error_bound(F):
+    """One Goldschmidt step on the hardware estimate: relative error far
+    below the deposit's 1e-10 tolerance (bound 2^-38; 2^-39.6 measured) over the radicands of
+    sqrt(gamma) on a grid r in [1, 1e4] (x ~ r^4)."""
+    x = _samples(0.5, 1e17, 1 << 20, 2)
+    got = F.fpic_probe_math(1, dev(x)).cpu().numpy()
+    ref = np.sqrt(x)
+    rel = np.abs(got - ref) / ref
+    print("sqrt_dep max rel err", rel.max(), "= 2^%.1f" % np.log2(rel.max() + 1e-300))
+    assert rel.max() <= 2.0 ** -38, rel.max()
+
+
+def test_small_step_sin_cos(F):
+    """Series branch (|h| < 2^-7): sin h and cos h - 1 to a few ulp of their
+    own magnitude, against cos h - 1 = -2 sin^2(h/2); libm branch (larger
+    steps): to a few ulp of 1."""
+    rng = np.random.default_rng(3)
+    hs = np.concatenate([rng.uniform(-0.0078, 0.0078, 1 << 18), [0.0, 1e-300, -1e-9]])
+    hl = rng.uniform(-0.5, 0.5, 1 << 12)
+    hl = hl[np.abs(hl) >= 0.0078125]
+    for h, series in ((hs, True), (hl, False)):
+        got = F.fpic_probe_math(2, dev(h)).cpu().numpy()
+        s_ref = np.sin(h)
+        cm_ref = -2.0 * np.sin(0.5 * h) ** 2
+        if series:
+            assert np.all(np.abs(got[:, 0] - s_ref) <= 8 * ULP * np.abs(s_ref))
+            assert np.all(np.abs(got[:, 1] - cm_ref) <= 8 * ULP * np.abs(cm_ref))
+        else:
+            assert np.abs(got[:, 0] - s_ref).max() <= 4 * ULP
+            assert np.abs(got[:, 1] - cm_ref).max() <= 4 * ULP

@@ -49,13 +49,14 @@ def test_sort_is_the_stable_argsort(F):
     assert np.array_equal(p.cell.cpu().numpy().view(np.uint32), cell[perm].astype(np.uint32))
 
 
-@pytest.mark.parametrize("a", [0.0, 0.9])
-def test_deposit_matches_oracle(F, a):
-    """Sec. 2.3 deposit on a 48 x 40 grid, 30011 e-/e+ with random weights
-    and 10 % removed: every node of rho, j^r, j^th, j^ph within 1e-10 of the
-    oracle (relative to the node's sum of |Q W| scale), and bitwise
-    reproducible."""
-    g = I.log_grid(48, 40, 1.2 * I.horizon(1.0, a), 25.0)
+@pytest.mark.parametrize("a,nr,nth", [(0.0, 48, 40), (0.9, 48, 40), (0.99, 64, 700)])
+def test_deposit_matches_oracle(F, a, nr, nth):
+    """Sec. 2.3 deposit on a coarse 48 x 40 grid (th steps beyond the
+    series range of the lattice rotations) and a fine 64 x 700 grid (series
+    range), 30011 e-/e+ with random weights and 10 % removed: every node of
+    rho, j^r, j^th, j^ph within 1e-10 of the oracle (relative to the node's
+    sum of |Q W| scale), and bitwise reproducible."""
+    g = I.log_grid(nr, nth, 1.2 * I.horizon(1.0, a), 25.0)
     ctx = F.fpic_init_metric(1.0, a)
     F.fpic_set_grid(ctx, g)
     n = 30011
