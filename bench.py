@@ -32,11 +32,11 @@ UNIT = "particle-steps/s"
 A_SPIN, B0, THETA_T, QM, DT, NGRID = 0.9, 1.0, 0.1, 100.0, 1e-3, 512
 HYB1_THR = 3.5e-6          # (d Htilde/dt)_max of the Hyb1 test
 # Algorithmic FP64 flops (FMA = 2, add/mul/div/sqrt/rsqrt = 1, sin+cos = 2),
-# counted from the formulas of the push ("Roofline").
+# counted from the formulas of the push.
 FLOP_EVAL = 230            # metric + derivatives + gather + RHS + H at one point
 FLOP_RK4_TRIAL = 4 * FLOP_EVAL + 79 + 56 + 5
 FLOP_IMR_ITER = FLOP_EVAL + 48
-FLOP_IMR_FINAL = FLOP_EVAL
+FLOP_IMR_FINAL = 56         # H at the converged point (metric + Gamma + H)
 NOMINAL_FP64_GFLOPS = 1250.0
 # deposit: FIDO velocity (41) + 3 sub-grids x (49 sqrt(gamma) points x 9 +
 # lattice 14 + four 16-point sums 128 + weights 16) + 2 th lattices (56) + shares (30)
@@ -240,7 +240,7 @@ def _timed(F, ctx, p, fields, prm, ev, steps, flush, learned=None):
         out["notconv"] += st["n_notconv"]
         out["fl_ex"] += st["n_alive_before"] * FLOP_RK4_TRIAL
         out["fl_im"] += st["n_iter_total"] * FLOP_IMR_ITER + st["n_implicit"] * FLOP_IMR_FINAL
-        out["launches"] += 3 if learned is None else (7 if learned[1].mode == F.FPIC_LEARN_SKIP else 5)
+        out["launches"] += 4 if learned is None else (8 if learned[1].mode == F.FPIC_LEARN_SKIP else 5)
     return out
 
 
@@ -265,6 +265,11 @@ def run_gpu(args, ws, rank, local):
                         B0pot=B0, events=ev[1:5])
     for _ in range(args.warmup):
         F.fpic_push(ctx, p, fields, prm, stats=True)
+    # launch shape of the implicit solver, timed on these particles (untimed here)
+    from paper_2602_07452_gb300 import autotune
+    prm_t = F.push_params(DT, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=HYB1_THR, r_max=float(g.rn[-1]),
+                          B0pot=B0)
+    tune_ms = autotune.tune_imr_blocks(ctx, p, fields, prm_t)
     learned = None
     train_info = None
     if not args.no_learned:
@@ -352,7 +357,9 @@ def run_gpu(args, ws, rank, local):
                    "mean_imr_iterations": plain["iters"] / max(plain["impl"], 1),
                    "rhs_evals_per_particle_step": plain["evals"] / psteps,
                    "max_dH_over_D0": max_dH, "parallelism": f"dp{ws} (independent particle sets)",
-                   "l2": "256 MB buffer written between timed steps (outside the events)"},
+                   "l2": "256 MB buffer written between timed steps (outside the events)",
+                   "imr_blocks_per_sm": F.fpic_get_tuning(ctx, F.FPIC_TUNE_IMR_BLOCKS_PER_SM),
+                   "autotune_ms_per_push": {str(k): round(v, 4) for k, v in tune_ms.items()}},
         "e2e": {"value": e2e_W / e2e_T, "unit": UNIT,
                 "h2d_bytes_per_step": hp.bytes_in(), "d2h_bytes_per_step": hp.bytes_out(),
                 "api": "fpic_push_host (pinned host SoA in, result out, every step)"},

@@ -234,6 +234,18 @@ int fpic_push_noalloc(double M, double a, fpic_particles *p, const fpic_push_par
  * FPIC_ECUDA. */
 int fpic_probe_fp64(double *gflops_out, int reps);
 
+/* Launch-shape tuning of a context (read by every later push on it).
+ *   FPIC_TUNE_IMR_BLOCKS_PER_SM: resident blocks of 128 threads per SM of
+ *     the persistent implicit solver, 1..4 (default 4, the register-limited
+ *     maximum).  Fewer lanes process more queued particles each, which
+ *     evens out the uneven iteration counts at the end of the queue; more
+ *     lanes hide more memory latency.  The autotuner in the Python package
+ *     (autotune.py) times the candidates on the caller's own particles.
+ * Errors: FPIC_EINVAL (NULL, unknown key, value out of range). */
+enum { FPIC_TUNE_IMR_BLOCKS_PER_SM = 0 };
+int fpic_set_tuning(fpic_ctx *ctx, int key, int value);
+int fpic_get_tuning(const fpic_ctx *ctx, int key, int *value);
+
 /* Test helper for the library's own FP64 elementary routines, one thread
  * per element of x (device, n values) into y (device):
  *   fn 0: 1/x by the hardware estimate and two Newton steps (push metric);
@@ -374,13 +386,17 @@ int fpic_mlp_train_step(fpic_mlp *m, float *P, float *mom, float *vel, const flo
  *     differences A = dt (k3 - k2) and B = dt (k4 - 2 k2 + k1) (k1..k4 the
  *     stage slopes of Sec. 2.2.1), each component i divided by its own scale
  *     s_i = |A_i| + |B_i| (features 0-5: A_i / s_i, 6-11: B_i / s_i), then
- *     ln r and th (12, 13).  The gap between the converged implicit step and
+ *     ln r (12) and ln(sum |A_i| / sum |(z_RK4 - z^n)_i|) over the momenta
+ *     u_r, u_th (13, a measure of the step's expansion parameter
+ *     (omega dt)^2).  The
+ *     gap between the converged implicit step and
  *     the trial is, to leading order in dt, dt^3 (f'f'f / 12 - f''(f,f) / 24)
  *     = g + O(dt^4) with g = (2/3) A - (1/6) B; outputs 0-5 are the rest of
- *     the gap, (z_IMR - z_RK4 - g)_i / s_i, and the implicit solve starts
- *     from z_RK4 + g + s y[0..5] instead of z_RK4 (a network with zero
- *     output gives the leading-order guess alone).  inc_scale and p_skip
- *     are unused.
+ *     the gap, (z_IMR - z_RK4 - g)_i / (s_i inc_scale_i), and the implicit
+ *     solve starts from z_RK4 + g + s inc_scale y[0..5] instead of z_RK4
+ *     (a network with zero output gives the leading-order guess alone; a
+ *     component whose correction exceeds 5 % of the trial's own increment
+ *     keeps the trial value).  p_skip is unused.
  *
  *   feat_mean, feat_std : standardisation (x - mean)/std of the 14 features;
  *   mode : FPIC_LEARN_SKIP or FPIC_LEARN_CORRECT. */
@@ -408,7 +424,7 @@ int fpic_features(fpic_ctx *ctx, const fpic_particles *p, const double *const fi
  *   cfg->mode FPIC_LEARN_CORRECT: row = the particle's slot in the implicit
  *     queue (rows 0 .. n_alive - 1, the order is not deterministic; X, T
  *     and S rows match); X = the trial features; targets
- *     (z_IMR - z_RK4 - g)_i / s_i clamped to [-16, 16].
+ *     (z_IMR - z_RK4 - g)_i / (s_i inc_scale_i) clamped to [-4, 4].
  * cfg NULL = FPIC_LEARN_SKIP with raw features.  prm->scheme must be
  * FPIC_HYB1 or FPIC_HYB2 with the IMR partner.
  * Errors: FPIC_EINVAL, FPIC_ENOMEM. */

@@ -1,0 +1,51 @@
+"""Autotuner of the launch shapes the library leaves open (fpic_set_tuning).
+
+Each candidate is timed on the caller's own particles and fields with CUDA
+events around the push, starting every trial from the same saved state, and
+the fastest is kept in the context.  The particles are restored afterwards.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import fpic as F
+
+_STATE = ("r", "th", "ph", "ur", "uth", "uph", "H0", "D0", "Hn", "alive", "scheme", "iters")
+
+
+def _save(p):
+    return {k: getattr(p, k).clone() for k in _STATE if getattr(p, k, None) is not None}
+
+
+def _load(p, snap):
+    for k, v in snap.items():
+        getattr(p, k).copy_(v)
+
+
+def tune_imr_blocks(ctx, p, fields, prm, candidates=(1, 2, 3, 4), reps=3, push=None):
+    """Pick FPIC_TUNE_IMR_BLOCKS_PER_SM by timing `reps` pushes per candidate
+    (push(ctx, p, fields, prm) defaults to fpic_push).  Returns
+    {candidate: mean ms} and leaves the best value set in ctx."""
+    push = push or (lambda c, q, f, m: F.fpic_push(c, q, f, m))
+    snap = _save(p)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times = {}
+    for v in candidates:
+        F.fpic_set_tuning(ctx, F.FPIC_TUNE_IMR_BLOCKS_PER_SM, v)
+        _load(p, snap)
+        push(ctx, p, fields, prm)          # warm-up at this shape
+        tot = 0.0
+        for _ in range(reps):
+            _load(p, snap)
+            torch.cuda.synchronize()
+            e0.record()
+            push(ctx, p, fields, prm)
+            e1.record()
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        times[v] = tot / reps
+    best = min(times, key=times.get)
+    F.fpic_set_tuning(ctx, F.FPIC_TUNE_IMR_BLOCKS_PER_SM, best)
+    _load(p, snap)
+    torch.cuda.synchronize()
+    return times

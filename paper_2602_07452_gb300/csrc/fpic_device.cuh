@@ -80,25 +80,32 @@ __device__ __forceinline__ void sincos_near(double t0, double s0, double c0, dou
 
 // Metric at a point (r, th) given sin/cos th.
 struct Geo {
-    double s, c, rho2, irho2, t;      // t = 1/(rho^2 sin^2 th)
+    double s, c, s2, rho2, irho2, t;  // t = 1/(rho^2 sin^2 th)
+    double twoMr, a2s2;               // 2 M r, a^2 sin^2 th
     double xi, alpha, ixi, beta;
     double gurr, gurp, gutt, gupp;
     double grr, grp, gtt, gpp, sqrtg;
 };
 
+// With xi = 1 + 2 M r / rho^2: alpha = xi^(-1/2), beta^r = 2 M r / (rho^2 xi)
+// = 1 - 1/xi, g^rr = a^2 s^2 / rho^2 + 1/xi, g^rp = a / rho^2,
+// g^tt = 1 / rho^2, g^pp = 1 / (rho^2 s^2) (App. A).
 __device__ __forceinline__ void geo_eval(const BH& bh, double r, double s, double c, Geo& g)
 {
     const double s2 = s * s, c2 = c * c;
     g.s = s;
     g.c = c;
+    g.s2 = s2;
     g.rho2 = fma(bh.a2, c2, r * r);
     g.t = rcp_nr(g.rho2 * s2);
     g.irho2 = g.t * s2;
-    g.xi = fma(bh.twoM * r, g.irho2, 1.0);
+    g.twoMr = bh.twoM * r;
+    g.a2s2 = bh.a2 * s2;
+    g.xi = fma(g.twoMr, g.irho2, 1.0);
     g.alpha = rsqrt(g.xi);
     g.ixi = g.alpha * g.alpha;
-    g.beta = (bh.twoM * r) * g.irho2 * g.ixi;
-    g.gurr = fma(bh.a2 * s2, g.irho2, g.ixi);
+    g.beta = 1.0 - g.ixi;
+    g.gurr = fma(g.a2s2, g.irho2, g.ixi);
     g.gurp = bh.a * g.irho2;
     g.gutt = g.irho2;
     g.gupp = g.t;
@@ -114,33 +121,33 @@ struct GeoD {
     double al[2], be[2], rr[2], rp[2], tt[2], pp[2];
 };
 
+// With P = rho^2 (d_r P = 2 r, d_th P = -q, q = 2 a^2 s c) and u = 1/P^2:
+// d g^tt = -dP u, d g^rp = a d g^tt, d_r xi = 2M (P - 2 r^2) u,
+// d_th xi = 2 M r q u, d alpha = -alpha^3 d xi / 2, d beta = d xi / xi^2,
+// d g^rr = a^2 s^2 d g^tt - d beta (+ q / P in th),
+// d_r g^pp = -2 r t / P, d_th g^pp = -2 s c t^2 (P - a^2 s^2).
 __device__ __forceinline__ void geo_deriv(const BH& bh, double r, const Geo& g, GeoD& d)
 {
-    const double s = g.s, c = g.c, s2 = s * s;
-    const double iP = g.irho2, iP2 = iP * iP;
-    const double sc = s * c;
-    const double dPr = 2.0 * r;
-    const double dPt = -2.0 * bh.a2 * sc;
-    // d xi = 2M d(r / rho^2)
-    const double dxir = bh.twoM * fma(-r, dPr, g.rho2) * iP2;
-    const double dxit = -bh.twoM * r * dPt * iP2;
-    const double a3h = -0.5 * g.alpha * g.ixi;      // -alpha^3 / 2
+    const double sc = g.s * g.c;
+    const double q = 2.0 * bh.a2 * sc;
+    const double u = g.irho2 * g.irho2;
+    const double mr2 = -2.0 * r;
+    d.tt[0] = mr2 * u;
+    d.tt[1] = q * u;
+    d.rp[0] = bh.a * d.tt[0];
+    d.rp[1] = bh.a * d.tt[1];
+    const double dxir = fma(mr2, r, g.rho2) * (bh.twoM * u);
+    const double dxit = g.twoMr * d.tt[1];
+    const double a3h = (-0.5 * g.alpha) * g.ixi;      // -alpha^3 / 2
     const double ixi2 = g.ixi * g.ixi;
     d.al[0] = a3h * dxir;
     d.al[1] = a3h * dxit;
     d.be[0] = dxir * ixi2;
     d.be[1] = dxit * ixi2;
-    const double a2s2 = bh.a2 * s2;
-    d.rr[0] = -a2s2 * dPr * iP2 - dxir * ixi2;
-    d.rr[1] = fma(2.0 * bh.a2 * sc, iP, -a2s2 * dPt * iP2) - dxit * ixi2;
-    d.rp[0] = -bh.a * dPr * iP2;
-    d.rp[1] = -bh.a * dPt * iP2;
-    d.tt[0] = -dPr * iP2;
-    d.tt[1] = -dPt * iP2;
-    // g^pp = t = 1/(rho^2 s^2):  d t = -t^2 d(rho^2 s^2)
-    const double t2 = g.t * g.t;
-    d.pp[0] = -t2 * dPr * s2;
-    d.pp[1] = -t2 * fma(dPt, s2, 2.0 * g.rho2 * sc);
+    d.rr[0] = fma(g.a2s2, d.tt[0], -d.be[0]);
+    d.rr[1] = fma(q, g.irho2, fma(g.a2s2, d.tt[1], -d.be[1]));
+    d.pp[0] = mr2 * (g.t * g.irho2);
+    d.pp[1] = (-2.0 * sc) * (g.t * g.t) * (g.rho2 - g.a2s2);
 }
 
 // Order-preserving integer key of a double (monotone for all non-NaN values).
@@ -250,7 +257,7 @@ __device__ __forceinline__ void eval_rhs_sc(const BH& bh, const double y[6], dou
     f[5] = 0.0;
     if (em) {
         const double k = qm * g.alpha;
-        const double ks = k * g.sqrtg * iG;
+        const double ks = (qm * g.rho2) * (g.s * iG);    // k sqrt(gamma) / Gamma, alpha^2 xi = 1
         const double cr = fma(Ut, B[2], -Up * B[1]);
         const double ct = fma(Up, B[0], -Ur * B[2]);
         const double cp = fma(Ur, B[1], -Ut * B[0]);

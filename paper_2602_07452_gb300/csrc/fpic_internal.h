@@ -37,6 +37,8 @@ struct fpic_ctx {
     // second scratch (sort / deposit)
     void* d_scratch2 = nullptr;
     size_t scratch2_bytes = 0;
+    // launch-shape tuning (fpic_set_tuning)
+    int imr_blocks_per_sm = 4;
 };
 
 namespace fpic {
@@ -50,6 +52,10 @@ int ensure_scratch(fpic_ctx* c, size_t bytes);
 int ensure_scratch2(fpic_ctx* c, size_t bytes);
 bool particles_ok(const fpic_particles* p, bool need_state);
 int mlp_forward_dev(fpic_mlp* m, const float* X, float* Y, long long B, cudaStream_t s);
+struct MlpDev;
+const MlpDev& mlp_weights(const fpic_mlp* m);
+int* mlp_err(const fpic_mlp* m);
+int mlp_sm_count(const fpic_mlp* m);
 // Forward pass of min(B, *count) rows, count read on the device (B bounds the launch).
 int mlp_forward_dev_count(fpic_mlp* m, const float* X, float* Y, long long B, const long long* count,
                           cudaStream_t s);

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "fpic_internal.h"
+#include "mlp_dev.cuh"
 #include "tc.cuh"
 
 namespace fpic {
@@ -105,13 +106,6 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(const uint16_t* __restrict__ 
 // ---------------------------------------------------------------------------
 // Parameter packing: FP32 master -> padded bf16 matrices (and transposes)
 // ---------------------------------------------------------------------------
-struct MlpDev {
-    // bf16 weights, row-major [out][in] padded: W1 [128][16], W2, W3 [128][128], W4 [16][128]
-    uint16_t *W1, *W2, *W3, *W4;
-    // transposes for the backward: W2t, W3t [128][128] (= [in][out]), W4t [128][16]
-    uint16_t *W2t, *W3t, *W4t;
-    float *b1, *b2, *b3, *b4;    // b4 padded to 16
-};
 
 __global__ void k_mlp_pack(const float* __restrict__ P, MlpDev d)
 {
@@ -140,74 +134,8 @@ __global__ void k_mlp_pack(const float* __restrict__ P, MlpDev d)
 }
 
 // ---------------------------------------------------------------------------
-// Fused forward
+// Fused forward (building blocks in mlp_dev.cuh)
 // ---------------------------------------------------------------------------
-// shared memory map (bytes)
-constexpr int FW_W1 = 0, FW_W2 = FW_W1 + 128 * 16 * 2, FW_W3 = FW_W2 + 128 * 128 * 2, FW_W4 = FW_W3 + 128 * 128 * 2,
-              FW_X = FW_W4 + 16 * 128 * 2, FW_H = FW_X + 128 * 16 * 2, FW_B = FW_H + 128 * 128 * 2,
-              FW_BAR = FW_B + (3 * 128 + 16) * 4, FW_SMEM = FW_BAR + 64;
-constexpr int FW_THREADS = 256;
-
-__device__ __forceinline__ void load_tile_kmajor(uint8_t* dst, const uint16_t* __restrict__ src, int R, int Kd)
-{
-    const int nv = Kd / 8;
-    for (int v = threadIdx.x; v < R * nv; v += blockDim.x) {
-        const int r = v / nv, g = v % nv;
-        *(uint4*)(dst + tc::kmajor_off(r, g * 8, R)) = *(const uint4*)(src + (size_t)r * Kd + g * 8);
-    }
-}
-
-// Run one layer's MMAs (A: 128 x K in sA, B: N x K in sB) into TMEM and wait.
-__device__ __forceinline__ int layer_mma(uint32_t tbase, const uint8_t* sA, const uint8_t* sB, int N, int K,
-                                         uint64_t* mbar, uint32_t& phase)
-{
-    tc::fence_async_smem();
-    tc::fence_before();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        tc::fence_after();
-        const uint32_t idesc = tc::idesc_bf16(128, N);
-        const uint32_t a0 = tc::smem_addr(sA), b0 = tc::smem_addr(sB);
-        for (int kk = 0; kk < K / 16; ++kk) {
-            const uint64_t ad = tc::smem_desc(a0 + kk * 2 * (128 * 16), 128 * 16, 128);
-            const uint64_t bd = tc::smem_desc(b0 + kk * 2 * (N * 16), N * 16, 128);
-            tc::mma_bf16(tbase, ad, bd, idesc, kk > 0 ? 1u : 0u);
-        }
-        tc::mma_commit(mbar);
-    }
-    const int done = tc::mbar_wait(mbar, phase) ? 1 : 0;
-    phase ^= 1u;
-    const int ok = __syncthreads_and(done);
-    tc::fence_after();
-    return ok;
-}
-
-// Epilogue of a hidden layer: z = acc + b; a = bf16(relu(z)) into sH.  Row
-// r = thread % 128 (its TMEM lane); the two halves of the block take
-// columns [0, 64) and [64, 128).  Optionally to global H (bf16 [B][128]).
-__device__ __forceinline__ void hidden_epilogue(uint32_t tbase, const float* b, uint8_t* sH, uint16_t* Hg,
-                                                long long row, long long B)
-{
-    const int r = threadIdx.x & 127, warp = (threadIdx.x >> 5) & 3, half = threadIdx.x >> 7;
-    for (int c0 = 64 * half; c0 < 64 * half + 64; c0 += 32) {
-        float v[32];
-        tc::tmem_ld32(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-#pragma unroll
-        for (int g = 0; g < 4; ++g) {
-            uint32_t pk[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int c = c0 + g * 8 + 2 * q;
-                const float z0 = v[g * 8 + 2 * q] + b[c], z1 = v[g * 8 + 2 * q + 1] + b[c + 1];
-                pk[q] = tc::pack_bf2(z0 > 0.f ? z0 : 0.f, z1 > 0.f ? z1 : 0.f);
-            }
-            const uint4 u = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-            *(uint4*)(sH + tc::kmajor_off(r, c0 + g * 8, 128)) = u;
-            if (Hg && row < B) *(uint4*)(Hg + (size_t)row * 128 + c0 + g * 8) = u;
-        }
-    }
-}
-
 struct FwdK {
     MlpDev w;
     const float* X;      // B x 16 FP32 features (standardised, padded with zeros)
@@ -232,22 +160,10 @@ __global__ void __launch_bounds__(FW_THREADS) k_mlp_fwd(FwdK k)
     }
     const long long ntiles = (B + 127) / 128;
     if ((long long)blockIdx.x >= ntiles) return;     // whole block, before any allocation
-    uint64_t* mbar = (uint64_t*)(smem + FW_BAR);
-    uint32_t* tslot = (uint32_t*)(smem + FW_BAR + 16);
     float* sb = (float*)(smem + FW_B);
     const int tid = threadIdx.x, warp = tid >> 5, r = tid & 127, half = tid >> 7;
-    load_tile_kmajor(smem + FW_W1, k.w.W1, 128, 16);
-    load_tile_kmajor(smem + FW_W2, k.w.W2, 128, 128);
-    load_tile_kmajor(smem + FW_W3, k.w.W3, 128, 128);
-    load_tile_kmajor(smem + FW_W4, k.w.W4, 16, 128);
-    for (int i = tid; i < 3 * 128 + 16; i += FW_THREADS)
-        sb[i] = i < 128 ? k.w.b1[i] : i < 256 ? k.w.b2[i - 128] : i < 384 ? k.w.b3[i - 256] : k.w.b4[i - 384];
-    if (warp == 0) tc::tmem_alloc(tslot, 128);
-    if (tid == 0) tc::mbar_init(mbar, 1);
-    tc::fence_before();
-    __syncthreads();
-    tc::fence_after();
-    const uint32_t tbase = *tslot;
+    uint64_t* mbar;
+    const uint32_t tbase = mlp_cta_setup(k.w, smem, &mbar);
     uint32_t phase = 0;
     int ok = 1;
     // this thread's 8 inputs of the first tile
@@ -273,16 +189,7 @@ __global__ void __launch_bounds__(FW_THREADS) k_mlp_fwd(FwdK k)
                 xb = *(const float4*)(k.X + nrow * 16 + 8 * half + 4);
             }
         }
-        ok = layer_mma(tbase, smem + FW_X, smem + FW_W1, 128, 16, mbar, phase);
-        if (!ok) break;
-        hidden_epilogue(tbase, sb, smem + FW_H, k.H ? k.H : nullptr, row, B);
-        ok = layer_mma(tbase, smem + FW_H, smem + FW_W2, 128, 128, mbar, phase);
-        if (!ok) break;
-        hidden_epilogue(tbase, sb + 128, smem + FW_H, k.H ? k.H + (size_t)B * 128 : nullptr, row, B);
-        ok = layer_mma(tbase, smem + FW_H, smem + FW_W3, 128, 128, mbar, phase);
-        if (!ok) break;
-        hidden_epilogue(tbase, sb + 256, smem + FW_H, k.H ? k.H + (size_t)2 * B * 128 : nullptr, row, B);
-        ok = layer_mma(tbase, smem + FW_H, smem + FW_W4, 16, 128, mbar, phase);
+        ok = mlp_tile_layers(tbase, smem, mbar, phase, k.H, row, B);
         if (!ok) break;
         if (half == 0) {
             float v[16];
@@ -296,10 +203,7 @@ __global__ void __launch_bounds__(FW_THREADS) k_mlp_fwd(FwdK k)
             }
         }
     }
-    if (!ok && tid == 0) atomicExch(k.err, 1);
-    tc::fence_before();
-    __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tbase, 128);
+    mlp_cta_teardown(tbase, ok, k.err);
 }
 
 
@@ -453,6 +357,12 @@ struct fpic_mlp {
     MlpDev d{};
     int* err = nullptr;
 };
+
+namespace fpic {
+const MlpDev& mlp_weights(const fpic_mlp* m) { return m->d; }
+int* mlp_err(const fpic_mlp* m) { return m->err; }
+int mlp_sm_count(const fpic_mlp* m) { return m->sm_count; }
+}  // namespace fpic
 
 static bool g_fwd_attr_set = false;
 

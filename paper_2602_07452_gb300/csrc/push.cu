@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "fpic_internal.h"
+#include "mlp_dev.cuh"
 
 namespace fpic {
 
@@ -44,7 +45,8 @@ struct PushK {
     int scheme, max_iter;
     long long n;
     PartDev P;
-    double* guess;          // 6 x n (SoA) implicit initial guesses
+    double* guess;          // 6 x n (SoA) implicit initial guesses, then the implicit results
+    double* sc0;            // 2 x n: sin, cos of th^n of the implicit particles
     uint32_t* queue;        // indices of particles for the implicit solver
     long long* cnt;
     const float* learned;   // n x 16 MLP outputs (nullable)
@@ -57,8 +59,9 @@ struct PushK {
     // corrector form of the learned guess (per implicit-queue slot)
     float* featX;           // 16 floats: trial features (network input)
     float* featS;           // 16 floats: scales s_i (0-5), leading-order gaps g_i (8-13)
-    double* stg;            // 12 x n: RK4 slopes k1, k2 of the trial, then A, B, then the trial
+    double* stg;            // 24 x n: slopes k1, k2, acc, k4 (by queue slot), then the trial (by particle)
     float fmean[14], fistd[14];
+    float oscale[6];        // corrector outputs 0-5 are residual / (s_i oscale_i)
 };
 
 __device__ __forceinline__ void load_state(const PartDev& P, long long p, double z[6])
@@ -138,29 +141,33 @@ __device__ __forceinline__ void warp_add(long long* c, long long v, unsigned mas
     if ((threadIdx.x & 31) == __ffs(mask) - 1 && v) atomicAdd((unsigned long long*)c, (unsigned long long)v);
 }
 
-// Corrector form, rejected particle p: from the slopes k1, k2 in the stg
-// scratch, acc = k1 + 2 k2 + 2 k3 and k4, the stage differences
-// A = dt (k3 - k2) and B = dt (k4 - 2 k2 + k1) overwrite k1, k2 in stg.
-__device__ __forceinline__ void trial_diffs(const PushK& k, long long p, const double acc[6], const double k4[6])
+// Corrector form, rejected particle in queue slot idx: its slopes k1, k2
+// (kept in shared memory, column threadIdx.x), acc = k1 + 2 k2 + 2 k3 and
+// k4 go to stg rows 0-5, 6-11, 12-17, 18-23 at column idx (a warp's
+// rejected lanes hold consecutive slots, so the stores coalesce).  Plain
+// copies: the arithmetic on them runs in k_trial_feat, where every lane of
+// a warp has a queue entry.
+__device__ __forceinline__ void trial_store(const PushK& k, unsigned long long idx, const double (*sk)[128],
+                                            const double acc[6], const double k4[6])
 {
+    const int t = threadIdx.x;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-        double* a = k.stg + (size_t)i * k.n + p;
-        double* b = k.stg + (size_t)(6 + i) * k.n + p;
-        const double k1 = *a, k2 = *b;
-        *a = k.dt * fma(0.5, acc[i] - k1, -2.0 * k2);
-        *b = k.dt * ((k4[i] - k2) - (k2 - k1));
+        k.stg[(size_t)i * k.n + idx] = sk[i][t];
+        k.stg[(size_t)(6 + i) * k.n + idx] = sk[6 + i][t];
+        k.stg[(size_t)(12 + i) * k.n + idx] = acc[i];
+        k.stg[(size_t)(18 + i) * k.n + idx] = k4[i];
     }
 }
 
 // MODE 0: RK4 only.  MODE 1: hybrid (RK4 trial + test + enqueue).  MODE 2:
-// hybrid that also writes the trial features of each rejected particle
-// (corrector form of the learned guess); its slopes k1, k2 go through the
-// stg scratch (12 doubles of HBM traffic per particle) rather than staying
-// live in registers across the later stages.
+// hybrid that also parks the RK4 slopes of each rejected particle
+// (corrector form of the learned guess); k1, k2 wait in shared memory
+// (12 KB per block) rather than in registers across the later stages.
 template <int MODE>
 __global__ void __launch_bounds__(128) k_explicit(PushK k)
 {
+    __shared__ double sk[MODE == 2 ? 12 : 1][128];
     const long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     long long p = w;
     if (k.work) {
@@ -186,7 +193,7 @@ __global__ void __launch_bounds__(128) k_explicit(PushK k)
     for (int i = 0; i < 6; ++i) {
         acc[i] = kk[i];
         y[i] = fma(hdt, kk[i], z0[i]);
-        if (MODE == 2) k.stg[(size_t)i * k.n + p] = kk[i];
+        if (MODE == 2) sk[i][threadIdx.x] = kk[i];
     }
     sincos_near(z0[1], s0, c0, y[1], sn, cn);
     F_at_sc(k.run, y, sn, cn, qm, em, kk, Hd);
@@ -194,7 +201,7 @@ __global__ void __launch_bounds__(128) k_explicit(PushK k)
     for (int i = 0; i < 6; ++i) {
         acc[i] = fma(2.0, kk[i], acc[i]);
         y[i] = fma(hdt, kk[i], z0[i]);
-        if (MODE == 2) k.stg[(size_t)(6 + i) * k.n + p] = kk[i];
+        if (MODE == 2) sk[6 + i][threadIdx.x] = kk[i];
     }
     sincos_near(z0[1], s0, c0, y[1], sn, cn);
     F_at_sc(k.run, y, sn, cn, qm, em, kk, Hd);
@@ -238,8 +245,10 @@ __global__ void __launch_bounds__(128) k_explicit(PushK k)
             k.queue[idx] = (uint32_t)p;
 #pragma unroll
             for (int i = 0; i < 6; ++i) k.guess[(size_t)i * k.n + p] = y[i];
+            k.sc0[p] = s0;
+            k.sc0[k.n + p] = c0;
             if (MODE == 2) {
-                trial_diffs(k, p, acc, kk);
+                trial_store(k, idx, sk, acc, kk);
                 if (k.record) k.recS[idx] = label;
             }
         }
@@ -255,11 +264,18 @@ __device__ __forceinline__ bool conv6(const double a[6], const double b[6], doub
 }
 
 // Persistent lane-refilling implicit-midpoint solver (Sec. 2.2.2):
-// z^[k] = z^n + dt F((z^n + z^[k-1]) / 2), then one evaluation at the
-// converged point for H.  all_mode: the queue is every particle (pure IMR,
-// guess z^n); otherwise entries come from k_explicit with their trial.
-// RESTART 1: a solve that does not converge restarts once from the trial in
-// stg (corrector form of the learned guess).
+// z^[k] = z^n + dt F((z^n + z^[k-1]) / 2) until two iterates agree to tol.
+// all_mode: the queue is every particle (pure IMR, guess z^n); otherwise
+// entries come from k_explicit with their trial and sin/cos of th^n (sc0).
+// Each loop trip is one right-hand side per lane; a lane whose solve ends
+// parks the result in the guess slot and takes the next particle at once.
+// H at the converged point and the write-back run afterwards in
+// k_imr_finish (one thread per particle, no lane waits on them here).
+// RESTART 1: a solve that has not converged after IMR_RESTART_AFTER
+// iterations from the corrected start restarts once, with the full
+// max_iter budget, from the trial in stg (corrector form of the learned
+// guess; a corrected start that helps converges well before that).
+constexpr int IMR_RESTART_AFTER = 25;
 template <int RESTART>
 __global__ void __launch_bounds__(128, 4) k_imr(PushK k, int all_mode)
 {
@@ -267,12 +283,12 @@ __global__ void __launch_bounds__(128, 4) k_imr(PushK k, int all_mode)
     const int lane = threadIdx.x & 31;
     const long long qn = all_mode ? k.n : k.cnt[CNT_QUEUE];
     long long p = -1, qi = 0;
-    bool exhausted = false, fin = false, again = false;
+    bool exhausted = false, again = false;
     double z0[6], zk[6];
     double qm = 0.0, s0 = 0.0, c0 = 1.0;
     bool em = false;
     int it = 0;
-    long long n_it = 0, n_nc = 0, n_ev = 0, n_rm = 0;
+    long long n_it = 0, n_nc = 0, n_ev = 0;
     for (;;) {
         const bool need = (p < 0) && !exhausted;
         const unsigned nm = __ballot_sync(FULL, need);
@@ -295,17 +311,20 @@ __global__ void __launch_bounds__(128, 4) k_imr(PushK k, int all_mode)
                         again = RESTART != 0;
                         load_state(k.P, p, z0);
                         if (all_mode) {
+                            sincos(z0[1], &s0, &c0);
+                            k.sc0[p] = s0;
+                            k.sc0[k.n + p] = c0;
 #pragma unroll
                             for (int i = 0; i < 6; ++i) zk[i] = z0[i];
                         } else {
+                            s0 = k.sc0[p];
+                            c0 = k.sc0[k.n + p];
 #pragma unroll
                             for (int i = 0; i < 6; ++i) zk[i] = k.guess[(size_t)i * k.n + p];
                         }
                         qm = k.P.qm[p];
                         em = k.run.has_fields && qm != 0.0;
-                        sincos(z0[1], &s0, &c0);
                         it = 0;
-                        fin = false;
                     }
                 } else {
                     exhausted = true;
@@ -319,45 +338,37 @@ __global__ void __launch_bounds__(128, 4) k_imr(PushK k, int all_mode)
         }
         if (p >= 0) {
             double y[6], f[6], H;
-            if (fin) {
 #pragma unroll
-                for (int i = 0; i < 6; ++i) y[i] = zk[i];
-            } else {
-#pragma unroll
-                for (int i = 0; i < 6; ++i) y[i] = 0.5 * (z0[i] + zk[i]);
-            }
+            for (int i = 0; i < 6; ++i) y[i] = 0.5 * (z0[i] + zk[i]);
             double sy, cy;
             sincos_near(z0[1], s0, c0, y[1], sy, cy);
             F_at_sc(k.run, y, sy, cy, qm, em, f, H);
             ++n_ev;
-            if (!fin) {
-                double zn[6];
+            double zn[6];
 #pragma unroll
-                for (int i = 0; i < 6; ++i) zn[i] = fma(k.dt, f[i], z0[i]);
-                const bool ok = conv6(zn, zk, k.tol);
+            for (int i = 0; i < 6; ++i) zn[i] = fma(k.dt, f[i], z0[i]);
+            const bool ok = conv6(zn, zk, k.tol);
 #pragma unroll
-                for (int i = 0; i < 6; ++i) zk[i] = zn[i];
-                ++it;
-                if (RESTART && !ok && it >= k.max_iter && again) {
-                    // the corrected start did not converge: the plain trial is the fallback
-                    again = false;
-                    n_it += it;
-                    it = 0;
+            for (int i = 0; i < 6; ++i) zk[i] = zn[i];
+            ++it;
+            if (RESTART && !ok && it >= min(k.max_iter, IMR_RESTART_AFTER) && again) {
+                // the corrected start did not converge: the plain trial is the fallback
+                again = false;
+                n_it += it;
+                it = 0;
 #pragma unroll
-                    for (int i = 0; i < 6; ++i) zk[i] = k.stg[(size_t)i * k.n + p];
-                } else if (ok || it >= k.max_iter) {
-                    fin = true;
-                    if (!ok) ++n_nc;
-                }
-            } else {
+                for (int i = 0; i < 6; ++i) zk[i] = k.stg[(size_t)i * k.n + p];
+            } else if (ok || it >= k.max_iter) {
+                if (!ok) ++n_nc;
                 if (k.record && k.featS) {
-                    // corrector form: row = queue slot, (gap to the trial - leading-order gap) / s_i
+                    // corrector form: row = queue slot, (gap to the trial - leading-order gap) / (s_i oscale_i)
                     float* t = k.recT + 16 * qi;
                     const float* sc = k.featS + 16 * qi;
 #pragma unroll
                     for (int i = 0; i < 6; ++i) {
-                        const double g = (zk[i] - k.guess[(size_t)i * k.n + p] - (double)sc[8 + i]) / (double)sc[i];
-                        t[i] = sc[i] > 0.f ? (float)fmin(16.0, fmax(-16.0, g)) : 0.f;
+                        const double g = (zk[i] - k.guess[(size_t)i * k.n + p] - (double)sc[8 + i]) /
+                                         ((double)sc[i] * (double)k.oscale[i]);
+                        t[i] = sc[i] > 0.f ? (float)fmin(4.0, fmax(-4.0, g)) : 0.f;
                     }
                     t[6] = 0.f;
                     t[7] = (float)(it - 8) * 0.25f;
@@ -369,8 +380,10 @@ __global__ void __launch_bounds__(128, 4) k_imr(PushK k, int all_mode)
                     t[6] = 0.f;
                     t[7] = (float)(it - 8) * 0.25f;
                     t[8] = 0.f;
-                } else if (!finish(k.run, k.P, p, zk, H, 1, it)) {
-                    ++n_rm;
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) k.guess[(size_t)i * k.n + p] = zk[i];
+                    k.P.iters[p] = (uint8_t)min(it, 255);
                 }
                 n_it += it;
                 p = -1;
@@ -380,7 +393,28 @@ __global__ void __launch_bounds__(128, 4) k_imr(PushK k, int all_mode)
     warp_add(&k.cnt[CNT_ITERS], n_it, FULL);
     warp_add(&k.cnt[CNT_NOTCONV], n_nc, FULL);
     warp_add(&k.cnt[CNT_EVALS], n_ev, FULL);
-    warp_add(&k.cnt[CNT_REMOVED], n_rm, FULL);
+}
+
+// After k_imr: H at each converged implicit step (sin/cos of th^{n+1} by
+// angle addition from th^n) and the write-back with the particle
+// boundaries of Sec. 2.5.
+__global__ void __launch_bounds__(256) k_imr_finish(PushK k, int all_mode)
+{
+    const long long qn = all_mode ? k.n : k.cnt[CNT_QUEUE];
+    long long n_rm = 0;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < qn;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long p = all_mode ? idx : (long long)k.queue[idx];
+        if (all_mode && !k.P.alive[p]) continue;
+        double z[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) z[i] = k.guess[(size_t)i * k.n + p];
+        double sn, cn;
+        sincos_near(k.P.th[p], k.sc0[p], k.sc0[k.n + p], z[1], sn, cn);
+        const double H = eval_H_sc(k.run.bh, z, sn, cn, k.P.qm[p], k.run.B0pot);
+        if (!finish(k.run, k.P, p, z, H, 1, k.P.iters[p])) ++n_rm;
+    }
+    warp_add(&k.cnt[CNT_REMOVED], n_rm, 0xffffffffu);
 }
 
 // ---------------------------------------------------------------------------
@@ -565,7 +599,7 @@ extern "C" int fpic_push(fpic_ctx* c, fpic_particles* p, const double* const fie
     cudaStream_t s = (cudaStream_t)stream;
     const long long n = p->n;
     FPIC_CUDA(cudaSetDevice(c->device));
-    const size_t need = (size_t)n * (6 * sizeof(double) + sizeof(uint32_t)) + 256;
+    const size_t need = (size_t)n * (8 * sizeof(double) + sizeof(uint32_t)) + 256;
     int rc = ensure_scratch(c, need);
     if (rc) return rc;
     PushK k{};
@@ -587,7 +621,8 @@ extern "C" int fpic_push(fpic_ctx* c, fpic_particles* p, const double* const fie
     k.P = PartDev{p->r, p->th, p->ph, p->ur, p->uth, p->uph, p->qm, p->H0, p->D0, p->Hn,
                   p->alive, p->scheme, p->iters, p->cell};
     k.guess = (double*)c->d_scratch;
-    k.queue = (uint32_t*)((char*)c->d_scratch + (size_t)n * 6 * sizeof(double));
+    k.sc0 = k.guess + (size_t)n * 6;
+    k.queue = (uint32_t*)((char*)c->d_scratch + (size_t)n * 8 * sizeof(double));
     k.cnt = c->d_cnt;
     k.learned = nullptr;
     FPIC_CUDA(cudaMemsetAsync(c->d_cnt, 0, CNT_N * sizeof(long long), s));
@@ -598,6 +633,7 @@ extern "C" int fpic_push(fpic_ctx* c, fpic_particles* p, const double* const fie
     const int TB = 128;
     const unsigned nb = (unsigned)((n + TB - 1) / TB);
     const unsigned persist = (unsigned)c->sm_count * 8u;
+    const unsigned imr_grid = (unsigned)c->sm_count * (unsigned)c->imr_blocks_per_sm;
     cudaEvent_t* ev = prm->events ? (cudaEvent_t*)prm->events : nullptr;
     if (stats) k_count_alive<<<persist, 256, 0, s>>>(k.P, n, c->d_cnt);
     if (ev) FPIC_CUDA(cudaEventRecord(ev[0], s));
@@ -607,10 +643,17 @@ extern "C" int fpic_push(fpic_ctx* c, fpic_particles* p, const double* const fie
         FPIC_CUDA(cudaEventRecord(ev[1], s));
         FPIC_CUDA(cudaEventRecord(ev[2], s));
     }
-    if (prm->scheme == FPIC_IMR) k_imr<0><<<persist, TB, 0, s>>>(k, 1);
-    else if (prm->scheme == FPIC_HAM) k_dg<<<nb, TB, 0, s>>>(k, 1);
-    else if (prm->scheme >= FPIC_HYB1 && prm->implicit == FPIC_IMR) k_imr<0><<<persist, TB, 0, s>>>(k, 0);
-    else if (prm->scheme >= FPIC_HYB1) k_dg<<<nb, TB, 0, s>>>(k, 0);
+    if (prm->scheme == FPIC_IMR) {
+        k_imr<0><<<imr_grid, TB, 0, s>>>(k, 1);
+        k_imr_finish<<<persist, 256, 0, s>>>(k, 1);
+    } else if (prm->scheme == FPIC_HAM) {
+        k_dg<<<nb, TB, 0, s>>>(k, 1);
+    } else if (prm->scheme >= FPIC_HYB1 && prm->implicit == FPIC_IMR) {
+        k_imr<0><<<imr_grid, TB, 0, s>>>(k, 0);
+        k_imr_finish<<<persist, 256, 0, s>>>(k, 0);
+    } else if (prm->scheme >= FPIC_HYB1) {
+        k_dg<<<nb, TB, 0, s>>>(k, 0);
+    }
     if (ev) FPIC_CUDA(cudaEventRecord(ev[3], s));
     FPIC_CUDA(cudaGetLastError());
     if (stats) {
@@ -688,7 +731,7 @@ namespace fpic {
 
 constexpr long long kNoAllocMax = FPIC_NOALLOC_MAX_PARTICLES;
 constexpr size_t kNoAllocCountersBytes = 256;   // CNT_N counters, padded for alignment
-constexpr size_t kNoAllocBytes = kNoAllocCountersBytes + (size_t)kNoAllocMax * (6 * sizeof(double) + sizeof(uint32_t));
+constexpr size_t kNoAllocBytes = kNoAllocCountersBytes + (size_t)kNoAllocMax * (8 * sizeof(double) + sizeof(uint32_t));
 
 // Shared by every call on a device and held until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
@@ -760,7 +803,8 @@ extern "C" int fpic_push_noalloc(double M, double a, fpic_particles* p, const fp
                   p->alive, p->scheme, p->iters, p->cell};
     k.cnt = (long long*)base;
     k.guess = (double*)(base + kNoAllocCountersBytes);
-    k.queue = (uint32_t*)(base + kNoAllocCountersBytes + (size_t)n * 6 * sizeof(double));
+    k.sc0 = k.guess + (size_t)n * 6;
+    k.queue = (uint32_t*)(base + kNoAllocCountersBytes + (size_t)n * 8 * sizeof(double));
     k.learned = nullptr;
     // the counters (queue length and head among them) must start at zero
     FPIC_CUDA(cudaMemsetAsync(k.cnt, 0, CNT_N * sizeof(long long), s));
@@ -780,10 +824,17 @@ extern "C" int fpic_push_noalloc(double M, double a, fpic_particles* p, const fp
         FPIC_CUDA(cudaEventRecord(ev[1], s));
         FPIC_CUDA(cudaEventRecord(ev[2], s));
     }
-    if (prm->scheme == FPIC_IMR) k_imr<0><<<persist, TB, 0, s>>>(k, 1);
-    else if (prm->scheme == FPIC_HAM) k_dg<<<nb, TB, 0, s>>>(k, 1);
-    else if (prm->scheme >= FPIC_HYB1 && prm->implicit == FPIC_IMR) k_imr<0><<<persist, TB, 0, s>>>(k, 0);
-    else if (prm->scheme >= FPIC_HYB1) k_dg<<<nb, TB, 0, s>>>(k, 0);
+    if (prm->scheme == FPIC_IMR) {
+        k_imr<0><<<persist / 2, TB, 0, s>>>(k, 1);
+        k_imr_finish<<<persist, 256, 0, s>>>(k, 1);
+    } else if (prm->scheme == FPIC_HAM) {
+        k_dg<<<nb, TB, 0, s>>>(k, 1);
+    } else if (prm->scheme >= FPIC_HYB1 && prm->implicit == FPIC_IMR) {
+        k_imr<0><<<persist / 2, TB, 0, s>>>(k, 0);
+        k_imr_finish<<<persist, 256, 0, s>>>(k, 0);
+    } else if (prm->scheme >= FPIC_HYB1) {
+        k_dg<<<nb, TB, 0, s>>>(k, 0);
+    }
     if (ev) FPIC_CUDA(cudaEventRecord(ev[3], s));
     FPIC_CUDA(cudaGetLastError());
     if (stats) {
@@ -911,6 +962,10 @@ __global__ void k_split(PushK k, float skip_logit)
         const double z0[6] = {k.P.r[p], k.P.th[p], k.P.ph[p], k.P.ur[p], k.P.uth[p], k.P.uph[p]};
 #pragma unroll
         for (int i = 0; i < 6; ++i) k.guess[(size_t)i * k.n + p] = fma(k.inc_scale[i], (double)y[i], z0[i]);
+        double s0, c0;
+        sincos(z0[1], &s0, &c0);
+        k.sc0[p] = s0;
+        k.sc0[k.n + p] = c0;
     } else {
         k.work[bw + __popc(act & ~sk & lanemask_lt())] = (uint32_t)p;
     }
@@ -945,20 +1000,22 @@ static void fill_pushk(PushK& k, fpic_ctx* c, fpic_particles* p, const double* c
     k.cnt = c->d_cnt;
 }
 
-// scratch: guess 6n doubles | stg 12n doubles | queue n | work n | X 16n floats |
+// scratch: guess 6n doubles | sc0 2n doubles | stg 24n doubles | queue n | work n | X 16n floats |
 // Y 16n floats | featS 16n floats | 6 FP32 field copies
 static int learned_scratch(fpic_ctx* c, long long n, PushK& k, float** X, float** Y, float** f32)
 {
     const size_t fsz = c->has_grid ? 6 * (size_t)(c->Nr + 1) * c->ld : 0;
-    const size_t need = (size_t)n * (18 * sizeof(double) + 2 * sizeof(uint32_t) + 48 * sizeof(float)) +
+    const size_t need = (size_t)n * (32 * sizeof(double) + 2 * sizeof(uint32_t) + 48 * sizeof(float)) +
                         fsz * sizeof(float) + 2048;
     int rc = ensure_scratch(c, need);
     if (rc) return rc;
     char* b = (char*)c->d_scratch;
     k.guess = (double*)b;
     b += (size_t)n * 6 * sizeof(double);
+    k.sc0 = (double*)b;
+    b += (size_t)n * 2 * sizeof(double);
     k.stg = (double*)b;
-    b += (size_t)n * 12 * sizeof(double);
+    b += (size_t)n * 24 * sizeof(double);
     k.queue = (uint32_t*)b;
     b += (size_t)n * sizeof(uint32_t);
     k.work = (uint32_t*)b;
@@ -977,88 +1034,140 @@ static int learned_scratch(fpic_ctx* c, long long n, PushK& k, float** X, float*
 static void set_corrector(PushK& k, const fpic_learned_cfg* cfg, float* X)
 {
     k.featX = X;
+    for (int i = 0; i < 6; ++i) k.oscale[i] = cfg->inc_scale[i] > 0.0 ? (float)cfg->inc_scale[i] : 1.f;
     for (int i = 0; i < 14; ++i) {
         k.fmean[i] = cfg->feat_mean[i];
         k.fistd[i] = cfg->feat_std[i] > 0.f ? 1.f / cfg->feat_std[i] : 1.f;
     }
 }
 
-// Corrector form, one thread per implicit-queue slot (the count is read on
-// the device): trial features from the stage differences A, B in stg
-// (per component i: A_i / s_i, B_i / s_i with s_i = |A_i| + |B_i|, zero when
-// both vanish; then ln r, th; standardised) and, next to the scales s_i, the
-// leading-order gap between the implicit midpoint step and the RK4 trial,
-// g = (2/3) A - (1/6) B: expanding both steps in dt, IMR - RK4 =
-// dt^3 (f'f'f / 12 - f''(f,f) / 24) + O(dt^4), while k3 - k2 =
+// Corrector form, implicit-queue slot idx (particle p = queue[idx]): the 14
+// trial features f and, per component, the scale s_i and the leading-order
+// gap g_i between the implicit midpoint step and the RK4 trial.  From the
+// slopes parked in stg: A = dt (k3 - k2), B = dt (k4 - 2 k2 + k1) with
+// k3 = (acc - k1) / 2 - k2; features A_i / s_i, B_i / s_i (s_i = |A_i| +
+// |B_i|, zero when both vanish), ln r and ln(|A| / |z_RK4 - z^n|) over u_r,
+// u_th (a measure of the step's expansion parameter (omega dt)^2), then
+// standardised.  g = (2/3) A - (1/6) B: expanding both steps in dt,
+// IMR - RK4 = dt^3 (f'f'f / 12 - f''(f,f) / 24) + O(dt^4), while k3 - k2 =
 // dt^2 f'f'f / 4 + O(dt^3) and k4 - 2 k2 + k1 = dt^2 (f'f'f / 2 +
-// f''(f,f) / 4) + O(dt^3).
+// f''(f,f) / 4) + O(dt^3).  FP32 after the differences: the features feed
+// a bf16 network and the gap only has to be a good start for the solve.
+__device__ __forceinline__ void trial_row(const PushK& k, long long idx, long long p, float f[16], float sc[6],
+                                          float gl[6])
+{
+    double z0[6];
+    load_state(k.P, p, z0);
+    float num = 0.f, den = 0.f;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const double k1 = k.stg[(size_t)i * k.n + idx], k2 = k.stg[(size_t)(6 + i) * k.n + idx];
+        const double acc = k.stg[(size_t)(12 + i) * k.n + idx], k4 = k.stg[(size_t)(18 + i) * k.n + idx];
+        const float a = (float)(k.dt * fma(0.5, acc - k1, -2.0 * k2));
+        const float b = (float)(k.dt * ((k4 - k2) - (k2 - k1)));
+        const float sm = fabsf(a) + fabsf(b);
+        gl[i] = fmaf(2.f / 3.f, a, -b * (1.f / 6.f));
+        const float is = sm > 0.f ? 1.f / sm : 0.f;
+        f[i] = a * is;
+        f[6 + i] = b * is;
+        sc[i] = sm;
+        if (i == 3 || i == 4) {
+            num += fabsf(a);
+            den += fabsf((float)(k.guess[(size_t)i * k.n + p] - z0[i]));
+        }
+    }
+    f[12] = __logf((float)z0[0]);
+    f[13] = (num > 0.f && den > 0.f) ? __logf(num / den) : 0.f;
+#pragma unroll
+    for (int i = 0; i < 14; ++i) f[i] = (f[i] - k.fmean[i]) * k.fistd[i];
+    f[14] = f[15] = 0.f;
+}
+
+// Sampling (corrector form): features of every queue slot to featX, the
+// scales s_i and gaps g_i to featS (0-5, 8-13).
 __global__ void k_trial_feat(PushK k)
 {
     const long long qn = k.cnt[CNT_QUEUE];
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < qn;
          idx += (long long)gridDim.x * blockDim.x) {
-        const long long p = k.queue[idx];
-        float f[16], sc[16];
-#pragma unroll
-        for (int i = 0; i < 6; ++i) {
-            const double a = k.stg[(size_t)i * k.n + p], b = k.stg[(size_t)(6 + i) * k.n + p];
-            const double sm = fabs(a) + fabs(b);
-            sc[8 + i] = (float)fma(2.0 / 3.0, a, -b / 6.0);
-            if (sm > 0.0) {
-                f[i] = (float)(a / sm);
-                f[6 + i] = (float)(b / sm);
-                sc[i] = (float)sm;
-            } else {
-                f[i] = 0.f;
-                f[6 + i] = 0.f;
-                sc[i] = 0.f;
-            }
-        }
-        f[12] = __logf((float)k.P.r[p]);
-        f[13] = (float)k.P.th[p];
-#pragma unroll
-        for (int i = 0; i < 14; ++i) f[i] = (f[i] - k.fmean[i]) * k.fistd[i];
-        f[14] = f[15] = 0.f;
-        sc[6] = sc[7] = sc[14] = sc[15] = 0.f;
+        float f[16], sc[6], gl[6];
+        trial_row(k, idx, (long long)k.queue[idx], f, sc, gl);
         float4* x = (float4*)(k.featX + 16 * idx);
         float4* o = (float4*)(k.featS + 16 * idx);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            x[q] = make_float4(f[4 * q], f[4 * q + 1], f[4 * q + 2], f[4 * q + 3]);
-            o[q] = make_float4(sc[4 * q], sc[4 * q + 1], sc[4 * q + 2], sc[4 * q + 3]);
-        }
+        for (int q = 0; q < 4; ++q) x[q] = make_float4(f[4 * q], f[4 * q + 1], f[4 * q + 2], f[4 * q + 3]);
+        o[0] = make_float4(sc[0], sc[1], sc[2], sc[3]);
+        o[1] = make_float4(sc[4], sc[5], 0.f, 0.f);
+        o[2] = make_float4(gl[0], gl[1], gl[2], gl[3]);
+        o[3] = make_float4(gl[4], gl[5], 0.f, 0.f);
     }
 }
 
-// Corrector form: the trial z_RK4 of queue slot idx is kept in stg (for the
-// restart), and the implicit guess becomes z_RK4 + g_i + s_i y_i (g the
-// leading-order gap).  Guard: the IMR - RK4 gap is O(dt^3) against the
-// O(dt) step, so a correction larger than CORR_MAX times the trial's own
-// increment in a component (or a prediction outside [-16, 16] or not
-// finite) leaves that component of the trial unchanged.
-constexpr double CORR_MAX = 0.05;
-__global__ void k_correct(PushK k, const float* __restrict__ Y)
+// Corrector form in the push, one fused persistent kernel per step: per
+// 128-slot tile of the implicit queue (count read on the device), thread
+// t < 128 builds the features of slot tile*128 + t straight into the
+// network's bf16 input tile, the four layers run on the tensor cores
+// (mlp_dev.cuh), and the same thread applies its row's output: the trial
+// z_RK4 is kept in stg (for the restart) and the implicit guess becomes
+// z_RK4 + g_i + s_i oscale_i y_i.  Guard: the IMR - RK4 gap is O(dt^3)
+// against the O(dt) step, so a component whose correction exceeds CORR_MAX
+// times the trial's own increment (or whose output is outside [-16, 16] or
+// not finite) keeps the trial value.
+constexpr float CORR_MAX = 0.05f;
+__global__ void __launch_bounds__(FW_THREADS) k_mlp_correct(PushK k, MlpDev w, int* err)
 {
+    extern __shared__ __align__(1024) uint8_t smem[];
     const long long qn = k.cnt[CNT_QUEUE];
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < qn;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const long long p = k.queue[idx];
-        const float4 y0 = *(const float4*)(Y + 16 * idx), y1 = *(const float4*)(Y + 16 * idx + 4);
-        const float4* fs = (const float4*)(k.featS + 16 * idx);
-        const float4 s0 = fs[0], s1 = fs[1], g0 = fs[2], g1 = fs[3];
-        const float y[6] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y};
-        const float sc[6] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y};
-        const float gl[6] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y};
-        double z0[6];
-        load_state(k.P, p, z0);
+    const long long ntiles = (qn + 127) / 128;
+    if ((long long)blockIdx.x >= ntiles) return;     // whole block, before any allocation
+    const float* sb = (const float*)(smem + FW_B);
+    const int warp = threadIdx.x >> 5, r = threadIdx.x & 127, half = threadIdx.x >> 7;
+    uint64_t* mbar;
+    const uint32_t tbase = mlp_cta_setup(w, smem, &mbar);
+    uint32_t phase = 0;
+    int ok = 1;
+    for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const long long idx = tile * 128 + r;
+        const bool valid = idx < qn;
+        long long p = 0;
+        float sc[6], gl[6];
+        if (half == 0) {
+            float f[16];
+            if (valid) {
+                p = k.queue[idx];
+                trial_row(k, idx, p, f, sc, gl);
+            } else {
 #pragma unroll
-        for (int i = 0; i < 6; ++i) {
-            const double zt = k.guess[(size_t)i * k.n + p];
-            const double d = (double)gl[i] + (double)sc[i] * (double)y[i];
-            k.stg[(size_t)i * k.n + p] = zt;
-            if (fabsf(y[i]) <= 16.f && fabs(d) <= CORR_MAX * fabs(zt - z0[i])) k.guess[(size_t)i * k.n + p] = zt + d;
+                for (int i = 0; i < 16; ++i) f[i] = 0.f;
+            }
+            *(uint4*)(smem + FW_X + tc::kmajor_off(r, 0, 128)) =
+                make_uint4(tc::pack_bf2(f[0], f[1]), tc::pack_bf2(f[2], f[3]), tc::pack_bf2(f[4], f[5]),
+                           tc::pack_bf2(f[6], f[7]));
+            *(uint4*)(smem + FW_X + tc::kmajor_off(r, 8, 128)) =
+                make_uint4(tc::pack_bf2(f[8], f[9]), tc::pack_bf2(f[10], f[11]), tc::pack_bf2(f[12], f[13]),
+                           tc::pack_bf2(f[14], f[15]));
+        }
+        ok = mlp_tile_layers(tbase, smem, mbar, phase, nullptr, idx, qn);
+        if (!ok) break;
+        if (half == 0) {
+            float v[16];
+            tc::tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16), v);
+            if (valid) {
+                double z0[6];
+                load_state(k.P, p, z0);
+#pragma unroll
+                for (int i = 0; i < 6; ++i) {
+                    const float y = v[i] + sb[384 + i];
+                    const double zt = k.guess[(size_t)i * k.n + p];
+                    const float d = fmaf(sc[i] * k.oscale[i], y, gl[i]);
+                    k.stg[(size_t)i * k.n + p] = zt;
+                    if (fabsf(y) <= 16.f && fabsf(d) <= CORR_MAX * (float)fabs(zt - z0[i]))
+                        k.guess[(size_t)i * k.n + p] = zt + (double)d;
+                }
+            }
         }
     }
+    mlp_cta_teardown(tbase, ok, err);
 }
 
 // FP32 copies of the field arrays (network inputs are rounded to bf16 anyway;
@@ -1152,7 +1261,7 @@ extern "C" int fpic_learn_sample(fpic_ctx* c, fpic_particles* p, const double* c
         set_corrector(k, cfg, X);
         k_explicit<2><<<nb, 128, 0, s>>>(k);
         k_trial_feat<<<(unsigned)c->sm_count * 8u, 256, 0, s>>>(k);
-        k_imr<0><<<(unsigned)c->sm_count * 8u, 128, 0, s>>>(k, 0);
+        k_imr<0><<<(unsigned)c->sm_count * (unsigned)c->imr_blocks_per_sm, 128, 0, s>>>(k, 0);
         FPIC_CUDA(cudaGetLastError());
         return FPIC_OK;
     }
@@ -1162,7 +1271,7 @@ extern "C" int fpic_learn_sample(fpic_ctx* c, fpic_particles* p, const double* c
     f.S = S;
     k_features<<<nb, 128, 0, s>>>(f);
     k_explicit<1><<<nb, 128, 0, s>>>(k);
-    k_imr<0><<<(unsigned)c->sm_count * 8u, 128, 0, s>>>(k, 0);
+    k_imr<0><<<(unsigned)c->sm_count * (unsigned)c->imr_blocks_per_sm, 128, 0, s>>>(k, 0);
     FPIC_CUDA(cudaGetLastError());
     return FPIC_OK;
 }
@@ -1207,10 +1316,16 @@ extern "C" int fpic_push_learned(fpic_ctx* c, fpic_mlp* m, fpic_particles* p, co
         set_corrector(k, cfg, X);
         k_explicit<2><<<nb, 128, 0, s>>>(k);
         if (ev) FPIC_CUDA(cudaEventRecord(ev[1], s));
-        k_trial_feat<<<persist, 256, 0, s>>>(k);
-        rc = mlp_forward_dev_count(m, X, Y, n, &c->d_cnt[CNT_QUEUE], s);
-        if (rc) return rc;
-        k_correct<<<persist, 256, 0, s>>>(k, Y);
+        static bool attr_set = false;
+        if (!attr_set) {
+            FPIC_CUDA(cudaFuncSetAttribute(k_mlp_correct, cudaFuncAttributeMaxDynamicSharedMemorySize, FW_SMEM));
+            attr_set = true;
+        }
+        // two CTAs per SM (shared memory and TMEM allow two); the kernel reads
+        // the queue length itself and idle CTAs leave at once
+        const long long ntiles = (n + 127) / 128, cap = 2LL * mlp_sm_count(m);
+        k_mlp_correct<<<(unsigned)(ntiles < cap ? ntiles : cap), FW_THREADS, FW_SMEM, s>>>(k, mlp_weights(m),
+                                                                                           mlp_err(m));
         if (ev) FPIC_CUDA(cudaEventRecord(ev[2], s));
     } else {
         // network on every particle first; predicted rejections skip the trial
@@ -1228,8 +1343,10 @@ extern "C" int fpic_push_learned(fpic_ctx* c, fpic_mlp* m, fpic_particles* p, co
         }
         k.work = nullptr;
     }
-    if (correct) k_imr<1><<<persist, 128, 0, s>>>(k, 0);
-    else k_imr<0><<<persist, 128, 0, s>>>(k, 0);
+    const unsigned imr_grid = (unsigned)c->sm_count * (unsigned)c->imr_blocks_per_sm;
+    if (correct) k_imr<1><<<imr_grid, 128, 0, s>>>(k, 0);
+    else k_imr<0><<<imr_grid, 128, 0, s>>>(k, 0);
+    k_imr_finish<<<persist, 256, 0, s>>>(k, 0);
     if (ev) FPIC_CUDA(cudaEventRecord(ev[3], s));
     FPIC_CUDA(cudaGetLastError());
     if (stats) {
@@ -1546,4 +1663,30 @@ extern "C" int fpic_push_batched(const fpic_run* runs, int nruns, fpic_particles
         if (h[CNT_NOTCONV] > 0) return FPIC_ENOTCONVERGED;
     }
     return FPIC_OK;
+}
+
+extern "C" int fpic_set_tuning(fpic_ctx* c, int key, int value)
+{
+    if (!c) return set_error(FPIC_EINVAL, "fpic_set_tuning: NULL ctx");
+    switch (key) {
+    case FPIC_TUNE_IMR_BLOCKS_PER_SM:
+        if (value < 1 || value > 4)
+            return set_error(FPIC_EINVAL, "fpic_set_tuning: IMR blocks per SM must be in [1, 4], got %d", value);
+        c->imr_blocks_per_sm = value;
+        return FPIC_OK;
+    default:
+        return set_error(FPIC_EINVAL, "fpic_set_tuning: unknown key %d", key);
+    }
+}
+
+extern "C" int fpic_get_tuning(const fpic_ctx* c, int key, int* value)
+{
+    if (!c || !value) return set_error(FPIC_EINVAL, "fpic_get_tuning: NULL argument");
+    switch (key) {
+    case FPIC_TUNE_IMR_BLOCKS_PER_SM:
+        *value = c->imr_blocks_per_sm;
+        return FPIC_OK;
+    default:
+        return set_error(FPIC_EINVAL, "fpic_get_tuning: unknown key %d", key);
+    }
 }

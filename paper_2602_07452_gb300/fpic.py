@@ -83,6 +83,7 @@ class fpic_learned_cfg(C.Structure):
 
 
 FPIC_LEARN_SKIP, FPIC_LEARN_CORRECT = 0, 1
+FPIC_TUNE_IMR_BLOCKS_PER_SM = 0
 
 
 # name -> (restype, argtypes)
@@ -126,6 +127,8 @@ _SIGS = {
                                  C.POINTER(fpic_push_params), C.POINTER(fpic_push_stats), C.c_void_p]),
     "fpic_probe_fp64": (C.c_int, [C.POINTER(C.c_double), C.c_int]),
     "fpic_probe_math": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p]),
+    "fpic_set_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "fpic_get_tuning": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
     "fpic_push_noalloc": (C.c_int, [C.c_double, C.c_double, C.POINTER(fpic_particles),
                                     C.POINTER(fpic_push_params), C.POINTER(fpic_push_stats), C.c_void_p]),
     "fpic_hamiltonian": (C.c_int, [C.c_void_p, C.POINTER(fpic_particles), C.c_double, _D, _D, C.c_void_p]),
@@ -332,6 +335,16 @@ def fpic_push_host(ctx: Ctx, hp: HostParticles, fields, prm: fpic_push_params, s
                               C.byref(st) if st is not None else None, _stream(stream))
     _check(rc)
     return st.as_dict() if st is not None else None
+
+
+def fpic_set_tuning(ctx: Ctx, key: int, value: int) -> None:
+    _check(lib().fpic_set_tuning(ctx.handle, key, value))
+
+
+def fpic_get_tuning(ctx: Ctx, key: int) -> int:
+    v = C.c_int()
+    _check(lib().fpic_get_tuning(ctx.handle, key, C.byref(v)))
+    return v.value
 
 
 def fpic_probe_math(fn: int, x: torch.Tensor) -> torch.Tensor:

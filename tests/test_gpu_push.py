@@ -298,3 +298,33 @@ def test_full_size_charged_workload_sampled(F):
     O.push(po, zo, q[idx], H0, D0, Ho, ao, g, Fo)
     assert_state_close(zg[idx], zo, TOL)
     assert st["n_alive_before"] == n
+
+
+def test_imr_launch_shape_changes_no_result():
+    """FPIC_TUNE_IMR_BLOCKS_PER_SM only reshapes the persistent implicit
+    launch: every particle's step is bitwise the same for 1 and 4 resident
+    blocks per SM; out-of-range values are rejected."""
+    cuda_or_skip()
+    F = fpic()
+    a = 0.9
+    g = I.wald_grid(96, a)
+    Fo = O.wald_on_grid(a, 1.0, g)
+    ctx = F.fpic_init_metric(1.0, a)
+    F.fpic_set_grid(ctx, g)
+    d, z, q = thermal_state(20000, g, a, theta=0.1, seed=12)
+    H0, _, D0 = O.hamiltonian(1.0, a, 1.0, z, q)
+    prm = F.push_params(1e-3, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=8e-5, r_max=float(g.rn[-1]),
+                        B0pot=1.0)
+    outs = []
+    for v in (1, 4):
+        F.fpic_set_tuning(ctx, F.FPIC_TUNE_IMR_BLOCKS_PER_SM, v)
+        assert F.fpic_get_tuning(ctx, F.FPIC_TUNE_IMR_BLOCKS_PER_SM) == v
+        p = make_particles(z, q, H0, D0, H0.copy())
+        st = F.fpic_push(ctx, p, fields_dev(Fo), prm, stats=True)
+        assert st["n_implicit"] > 100
+        outs.append(to_np(p))
+    for x, y in zip(*outs):
+        assert np.array_equal(x, y)
+    for bad in (0, 5):
+        with pytest.raises(F.FpicError):
+            F.fpic_set_tuning(ctx, F.FPIC_TUNE_IMR_BLOCKS_PER_SM, bad)
