@@ -191,11 +191,15 @@ typedef struct {
 int fpic_push_batched(const fpic_run *runs, int nruns, fpic_particles *p, const fpic_push_params *prm,
                       fpic_push_stats *stats, void *stream);
 
-/* fpic_push on a particle set held in HOST memory (pinned or pageable):
- * the arrays of *host_p are copied to library-owned device buffers, pushed
- * exactly as fpic_push does, and the state, Hn, alive, scheme, iters and
- * cell arrays are copied back; synchronises the stream before returning.
- * fields stay device arrays.  Errors: as fpic_push. */
+/* fpic_push on a particle set held in HOST memory (pinned for overlap):
+ * the input arrays of *host_p (state, q/m, H_0, D_0, H^n, alive; w is not
+ * read by the push and not copied) go to library-owned device buffers in
+ * four particle chunks on a library-owned copy stream, the explicit pass of
+ * each chunk starting as soon as its copies land (the implicit pass then
+ * runs over all queued particles); the push is exactly fpic_push's, and the
+ * state, Hn, alive, scheme, iters and cell arrays are copied back on
+ * `stream`, which is synchronised before returning.  fields stay device
+ * arrays.  Errors: as fpic_push. */
 int fpic_push_host(fpic_ctx *ctx, fpic_particles *host_p, const double *const fields[6],
                    const fpic_push_params *prm, fpic_push_stats *stats, void *stream);
 
@@ -211,7 +215,7 @@ int fpic_push_host(fpic_ctx *ctx, fpic_particles *host_p, const double *const fi
  * no context (M, a given directly), calls no cudaMalloc, cudaFree or other
  * allocating routine, and keeps its scratch (implicit guesses, queue of
  * rejected particles, counters) in one file-scope device array of fixed
- * size, FPIC_NOALLOC_MAX_PARTICLES * 52 + 256 bytes (about 3.4 MB), that
+ * size, FPIC_NOALLOC_MAX_PARTICLES * 68 + 256 bytes (about 4.5 MB), that
  * every device which loads the library holds until the process exits.
  *   p, prm, stats, stream : as fpic_push (no fields; prm->guess must be
  *     NULL).  Neutral and charged particles move on geodesics of the Kerr

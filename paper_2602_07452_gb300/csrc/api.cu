@@ -56,6 +56,14 @@ int ensure_scratch2(fpic_ctx* c, size_t bytes)
     return 0;
 }
 
+int ensure_copy_stream(fpic_ctx* c)
+{
+    if (c->copy_stream) return 0;
+    FPIC_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+    for (cudaEvent_t& e : c->copy_ev) FPIC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    return 0;
+}
+
 bool particles_ok(const fpic_particles* p, bool need_state)
 {
     if (p->n == 0) return true;
@@ -278,6 +286,9 @@ extern "C" void fpic_destroy(fpic_ctx* c)
     if (c->d_scratch2) cudaFree(c->d_scratch2);
     if (c->d_runs) cudaFree(c->d_runs);
     if (c->h_runs) cudaFreeHost(c->h_runs);
+    for (cudaEvent_t e : c->copy_ev)
+        if (e) cudaEventDestroy(e);
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     delete c;
 }
 

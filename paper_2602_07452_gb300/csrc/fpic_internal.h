@@ -8,6 +8,10 @@
 #include "../../include/fpic.h"
 #include "fpic_device.cuh"
 
+// fpic_push_host: particle chunks whose host-to-device copies overlap the
+// explicit pass of the earlier chunks.
+#define FPIC_HOST_CHUNKS 4
+
 struct fpic_ctx {
     int device = 0;
     int sm_count = 0;
@@ -39,6 +43,9 @@ struct fpic_ctx {
     size_t scratch2_bytes = 0;
     // launch-shape tuning (fpic_set_tuning)
     int imr_blocks_per_sm = 4;
+    // fpic_push_host: copy stream and per-chunk events (created on first use)
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t copy_ev[FPIC_HOST_CHUNKS + 1] = {};
 };
 
 namespace fpic {
@@ -50,6 +57,7 @@ int set_error(int code, const char* fmt, ...);
 int check_cuda(cudaError_t e, const char* what);
 int ensure_scratch(fpic_ctx* c, size_t bytes);
 int ensure_scratch2(fpic_ctx* c, size_t bytes);
+int ensure_copy_stream(fpic_ctx* c);
 bool particles_ok(const fpic_particles* p, bool need_state);
 int mlp_forward_dev(fpic_mlp* m, const float* X, float* Y, long long B, cudaStream_t s);
 struct MlpDev;

@@ -44,6 +44,7 @@ struct PushK {
     double dt, thr, tol, dg_eps;
     int scheme, max_iter;
     long long n;
+    long long p_begin, p_end;   // explicit pass over [p_begin, p_end) (p_end 0: all n)
     PartDev P;
     double* guess;          // 6 x n (SoA) implicit initial guesses, then the implicit results
     double* sc0;            // 2 x n: sin, cos of th^n of the implicit particles
@@ -169,11 +170,11 @@ __global__ void __launch_bounds__(128) k_explicit(PushK k)
 {
     __shared__ double sk[MODE == 2 ? 12 : 1][128];
     const long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    long long p = w;
+    long long p = k.p_begin + w;
     if (k.work) {
         if (w >= k.cnt[CNT_WORK]) return;
         p = k.work[w];
-    } else if (p >= k.n) {
+    } else if (p >= (k.p_end ? k.p_end : k.n)) {
         return;
     }
     if (!k.P.alive[p]) {
@@ -577,6 +578,19 @@ __global__ void k_count_alive(PartDev P, long long n, long long* cnt)
 
 using namespace fpic;
 
+namespace fpic {
+// Explicit pass split into chunks whose launches wait for per-chunk events
+// (set by the caller after each chunk's host-to-device copies).
+struct PushChunks {
+    int k;
+    const long long* bounds;    // k + 1 particle offsets
+    const cudaEvent_t* ready;   // k events
+};
+}  // namespace fpic
+
+static int push_core(fpic_ctx* c, fpic_particles* p, const double* const fields[6], const fpic_push_params* prm,
+                     fpic_push_stats* stats, cudaStream_t s, const PushChunks* ch);
+
 extern "C" int fpic_push(fpic_ctx* c, fpic_particles* p, const double* const fields[6],
                          const fpic_push_params* prm, fpic_push_stats* stats, void* stream)
 {
@@ -596,7 +610,13 @@ extern "C" int fpic_push(fpic_ctx* c, fpic_particles* p, const double* const fie
         if (!c->has_grid) return set_error(FPIC_EINVAL, "fpic_push: fields given but no grid set");
     }
     if (prm->guess) return set_error(FPIC_EINVAL, "fpic_push: learned guesses need fpic_push_learned");
-    cudaStream_t s = (cudaStream_t)stream;
+    return push_core(c, p, fields, prm, stats, (cudaStream_t)stream, nullptr);
+}
+
+static int push_core(fpic_ctx* c, fpic_particles* p, const double* const fields[6], const fpic_push_params* prm,
+                     fpic_push_stats* stats, cudaStream_t s, const PushChunks* ch)
+{
+    const bool has_fields = fields != nullptr;
     const long long n = p->n;
     FPIC_CUDA(cudaSetDevice(c->device));
     const size_t need = (size_t)n * (8 * sizeof(double) + sizeof(uint32_t)) + 256;
@@ -637,8 +657,24 @@ extern "C" int fpic_push(fpic_ctx* c, fpic_particles* p, const double* const fie
     cudaEvent_t* ev = prm->events ? (cudaEvent_t*)prm->events : nullptr;
     if (stats) k_count_alive<<<persist, 256, 0, s>>>(k.P, n, c->d_cnt);
     if (ev) FPIC_CUDA(cudaEventRecord(ev[0], s));
-    if (prm->scheme == FPIC_RK4) k_explicit<0><<<nb, TB, 0, s>>>(k);
-    else if (prm->scheme >= FPIC_HYB1) k_explicit<1><<<nb, TB, 0, s>>>(k);
+    const bool explicit_pass = prm->scheme == FPIC_RK4 || prm->scheme >= FPIC_HYB1;
+    if (ch && !explicit_pass)
+        for (int j = 0; j < ch->k; ++j) FPIC_CUDA(cudaStreamWaitEvent(s, ch->ready[j], 0));
+    if (explicit_pass) {
+        const int nck = ch ? ch->k : 1;
+        for (int j = 0; j < nck; ++j) {
+            k.p_begin = ch ? ch->bounds[j] : 0;
+            k.p_end = ch ? ch->bounds[j + 1] : n;
+            const long long len = k.p_end - k.p_begin;
+            if (ch) FPIC_CUDA(cudaStreamWaitEvent(s, ch->ready[j], 0));
+            if (len <= 0) continue;
+            const unsigned nbj = (unsigned)((len + TB - 1) / TB);
+            if (prm->scheme == FPIC_RK4) k_explicit<0><<<nbj, TB, 0, s>>>(k);
+            else k_explicit<1><<<nbj, TB, 0, s>>>(k);
+        }
+        k.p_begin = 0;
+        k.p_end = 0;
+    }
     if (ev) {
         FPIC_CUDA(cudaEventRecord(ev[1], s));
         FPIC_CUDA(cudaEventRecord(ev[2], s));
@@ -660,7 +696,6 @@ extern "C" int fpic_push(fpic_ctx* c, fpic_particles* p, const double* const fie
         FPIC_CUDA(cudaMemcpyAsync(c->h_cnt, c->d_cnt, CNT_N * sizeof(long long), cudaMemcpyDeviceToHost, s));
         FPIC_CUDA(cudaStreamSynchronize(s));
         const long long* h = c->h_cnt;
-        const bool explicit_pass = prm->scheme == FPIC_RK4 || prm->scheme >= FPIC_HYB1;
         stats->n_alive_before = h[CNT_ALIVE];
         stats->n_implicit = prm->scheme == FPIC_RK4 ? 0 : (prm->scheme >= FPIC_HYB1 ? h[CNT_QUEUE] : h[CNT_ALIVE]);
         stats->n_iter_total = h[CNT_ITERS];
@@ -685,6 +720,8 @@ extern "C" int fpic_push_host(fpic_ctx* c, fpic_particles* hp, const double* con
     const size_t nd = (size_t)n * sizeof(double), nb = (size_t)n, n4 = (size_t)n * 4;
     int rc = ensure_scratch2(c, 11 * nd + 3 * nb + n4 + 64);
     if (rc) return rc;
+    rc = ensure_copy_stream(c);
+    if (rc) return rc;
     char* base = (char*)c->d_scratch2;
     fpic_particles d{};
     d.n = n;
@@ -695,10 +732,27 @@ extern "C" int fpic_push_host(fpic_ctx* c, fpic_particles* hp, const double* con
     d.scheme = d.alive + nb;
     d.iters = d.scheme + nb;
     d.cell = (uint32_t*)(((uintptr_t)(d.iters + nb) + 15) & ~(uintptr_t)15);
-    for (int i = 0; i < 11; ++i)
-        if (hd[i] && n) FPIC_CUDA(cudaMemcpyAsync(*dd[i], hd[i], nd, cudaMemcpyHostToDevice, s));
-    if (n) FPIC_CUDA(cudaMemcpyAsync(d.alive, hp->alive, nb, cudaMemcpyHostToDevice, s));
-    rc = fpic_push(c, &d, fields, prm, stats, stream);
+    // Host-to-device copies in FPIC_HOST_CHUNKS particle chunks on the
+    // context's copy stream; the explicit pass of chunk j starts as soon as
+    // its inputs have landed, overlapping the copies of the later chunks.
+    // w is not read by the push and is not copied.
+    long long bounds[FPIC_HOST_CHUNKS + 1];
+    for (int j = 0; j <= FPIC_HOST_CHUNKS; ++j) bounds[j] = n * j / FPIC_HOST_CHUNKS;
+    FPIC_CUDA(cudaEventRecord(c->copy_ev[FPIC_HOST_CHUNKS], s));
+    FPIC_CUDA(cudaStreamWaitEvent(c->copy_stream, c->copy_ev[FPIC_HOST_CHUNKS], 0));
+    for (int j = 0; j < FPIC_HOST_CHUNKS; ++j) {
+        const size_t o = (size_t)bounds[j], len = (size_t)(bounds[j + 1] - bounds[j]);
+        if (len) {
+            for (int i = 0; i < 11; ++i)
+                if (i != 7 && hd[i])
+                    FPIC_CUDA(cudaMemcpyAsync(*dd[i] + o, hd[i] + o, len * sizeof(double), cudaMemcpyHostToDevice,
+                                              c->copy_stream));
+            FPIC_CUDA(cudaMemcpyAsync(d.alive + o, hp->alive + o, len, cudaMemcpyHostToDevice, c->copy_stream));
+        }
+        FPIC_CUDA(cudaEventRecord(c->copy_ev[j], c->copy_stream));
+    }
+    const PushChunks ch{FPIC_HOST_CHUNKS, bounds, c->copy_ev};
+    rc = push_core(c, &d, fields, prm, stats, s, &ch);
     if (rc < 0) return rc;
     const int back[] = {0, 1, 2, 3, 4, 5, 10};
     for (int i : back)

@@ -321,7 +321,8 @@ class HostParticles:
                               *[hp(getattr(self, f), _U8) for f in self.FIELDS_B], hp(self.cell, _U32))
 
     def bytes_in(self):
-        return self.n * (8 * len(self.FIELDS_D) + 1)
+        # every double array but w (not read by the push), plus alive
+        return self.n * (8 * (len(self.FIELDS_D) - 1) + 1)
 
     def bytes_out(self):
         return self.n * (8 * 7 + 3 + 4)

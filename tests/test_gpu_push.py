@@ -328,3 +328,46 @@ def test_imr_launch_shape_changes_no_result():
     for bad in (0, 5):
         with pytest.raises(F.FpicError):
             F.fpic_set_tuning(ctx, F.FPIC_TUNE_IMR_BLOCKS_PER_SM, bad)
+
+
+@pytest.mark.parametrize("n", [0, 3, 20011])
+def test_host_buffer_push_equals_device_push(n):
+    """fpic_push_host (chunked copies overlapping the explicit pass) gives
+    bitwise the device push's results, for ragged chunk sizes and removed
+    particles; the host arrays hold the result afterwards."""
+    cuda_or_skip()
+    F = fpic()
+    a = 0.9
+    g = I.wald_grid(96, a)
+    Fo = O.wald_on_grid(a, 1.0, g)
+    ctx = F.fpic_init_metric(1.0, a)
+    F.fpic_set_grid(ctx, g)
+    prm = F.push_params(1e-3, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=8e-5, r_max=float(g.rn[-1]),
+                        B0pot=1.0)
+    if n:
+        d, z, q = thermal_state(n, g, a, theta=0.1, seed=13)
+        H0, _, D0 = O.hamiltonian(1.0, a, 1.0, z, q)
+    else:
+        z, q, H0, D0 = np.zeros((0, 6)), np.zeros(0), np.zeros(0), np.zeros(0)
+    alive = (np.arange(n) % 7 != 3).astype(np.uint8)
+    p = make_particles(z, q, H0, D0, H0.copy(), alive.copy())
+    F.fpic_push(ctx, p, fields_dev(Fo), prm)
+    hp = F.HostParticles(n)
+    for k, col in zip(("r", "th", "ph", "ur", "uth", "uph"), range(6)):
+        getattr(hp, k).copy_(torch_from(z[:, col]))
+    hp.qm.copy_(torch_from(q)); hp.H0.copy_(torch_from(H0)); hp.D0.copy_(torch_from(D0))
+    hp.Hn.copy_(torch_from(H0)); hp.alive.copy_(torch_from(alive))
+    F.fpic_push_host(ctx, hp, fields_dev(Fo), prm)
+    zs, Hn, al, sc, it, cell = to_np(p)
+    zh = np.stack([getattr(hp, k).numpy() for k in ("r", "th", "ph", "ur", "uth", "uph")], 1)
+    assert np.array_equal(zh, zs)
+    assert np.array_equal(hp.Hn.numpy(), Hn)
+    assert np.array_equal(hp.alive.numpy(), al)
+    assert np.array_equal(hp.scheme.numpy(), sc)
+    assert np.array_equal(hp.iters.numpy(), it)
+    assert np.array_equal(hp.cell.numpy().view(np.uint32), cell)
+
+
+def torch_from(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x))
