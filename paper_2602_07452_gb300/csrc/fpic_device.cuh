@@ -116,36 +116,27 @@ __device__ __forceinline__ void geo_eval(const BH& bh, double r, double s, doubl
     g.sqrtg = g.rho2 * g.xi * g.alpha * s;
 }
 
-// d_r and d_th of alpha, beta^r, g^rr, g^rp, g^tt, g^pp.
+// d_r and d_th of the three functions the momentum equations need: xi,
+// g^tt = 1/rho^2 (g^rp = a g^tt, and g^rr, alpha, beta^r follow from xi and
+// g^tt, see eval_rhs_sc) and g^pp; plus q = 2 a^2 sin cos = -d_th rho^2.
 struct GeoD {
-    double al[2], be[2], rr[2], rp[2], tt[2], pp[2];
+    double xi[2], tt[2], pp[2];
+    double q;
 };
 
-// With P = rho^2 (d_r P = 2 r, d_th P = -q, q = 2 a^2 s c) and u = 1/P^2:
-// d g^tt = -dP u, d g^rp = a d g^tt, d_r xi = 2M (P - 2 r^2) u,
-// d_th xi = 2 M r q u, d alpha = -alpha^3 d xi / 2, d beta = d xi / xi^2,
-// d g^rr = a^2 s^2 d g^tt - d beta (+ q / P in th),
-// d_r g^pp = -2 r t / P, d_th g^pp = -2 s c t^2 (P - a^2 s^2).
+// With P = rho^2 (d_r P = 2 r, d_th P = -q) and u = 1/P^2: d g^tt = -dP u,
+// d_r xi = 2M (P - 2 r^2) u, d_th xi = 2 M r q u, d_r g^pp = -2 r t / P,
+// d_th g^pp = -2 s c t^2 (P - a^2 s^2)  (t = g^pp = 1 / (P s^2)).
 __device__ __forceinline__ void geo_deriv(const BH& bh, double r, const Geo& g, GeoD& d)
 {
     const double sc = g.s * g.c;
-    const double q = 2.0 * bh.a2 * sc;
+    d.q = 2.0 * bh.a2 * sc;
     const double u = g.irho2 * g.irho2;
     const double mr2 = -2.0 * r;
     d.tt[0] = mr2 * u;
-    d.tt[1] = q * u;
-    d.rp[0] = bh.a * d.tt[0];
-    d.rp[1] = bh.a * d.tt[1];
-    const double dxir = fma(mr2, r, g.rho2) * (bh.twoM * u);
-    const double dxit = g.twoMr * d.tt[1];
-    const double a3h = (-0.5 * g.alpha) * g.ixi;      // -alpha^3 / 2
-    const double ixi2 = g.ixi * g.ixi;
-    d.al[0] = a3h * dxir;
-    d.al[1] = a3h * dxit;
-    d.be[0] = dxir * ixi2;
-    d.be[1] = dxit * ixi2;
-    d.rr[0] = fma(g.a2s2, d.tt[0], -d.be[0]);
-    d.rr[1] = fma(q, g.irho2, fma(g.a2s2, d.tt[1], -d.be[1]));
+    d.tt[1] = d.q * u;
+    d.xi[0] = fma(mr2, r, g.rho2) * (bh.twoM * u);
+    d.xi[1] = g.twoMr * d.tt[1];
     d.pp[0] = mr2 * (g.t * g.irho2);
     d.pp[1] = (-2.0 * sc) * (g.t * g.t) * (g.rho2 - g.a2s2);
 }
@@ -247,13 +238,20 @@ __device__ __forceinline__ void eval_rhs_sc(const BH& bh, const double y[6], dou
     f[0] = fma(aiG, Ur, -g.beta);
     f[1] = aiG * Ut;
     f[2] = aiG * Up;
-    const double h = -0.5 * aiG;   // -alpha / (2 Gamma)
-    const double urur = ur * ur, urup2 = 2.0 * ur * up, utut = ut * ut, upup = up * up;
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const double quad = fma(urur, d.rr[i], fma(urup2, d.rp[i], fma(utut, d.tt[i], upup * d.pp[i])));
-        f[3 + i] = fma(h, quad, fma(-G, d.al[i], ur * d.be[i]));
-    }
+    // du_i/dt = -Gamma d_i alpha + u_r d_i beta^r - (alpha / 2 Gamma) u_j u_k d_i g^jk
+    // (Eq. p2).  With d alpha = -(alpha^3 / 2) d xi, d beta^r = d xi / xi^2,
+    // d g^rr = a^2 s^2 d g^tt - d xi / xi^2 (+ q / rho^2 in th), d g^rp = a d g^tt:
+    //   u_j u_k d_i g^jk = W d_i g^tt + u_ph^2 d_i g^pp - u_r^2 d_i xi / xi^2 (+ u_r^2 q / rho^2)
+    //   with W = a^2 s^2 u_r^2 + 2 a u_r u_ph + u_th^2, so
+    //   du_i/dt = h (W d_i g^tt + u_ph^2 d_i g^pp [+ u_r^2 q / rho^2])
+    //             + d_i xi (u_r (1 - h u_r) / xi^2 + Gamma alpha^3 / 2),  h = -alpha / (2 Gamma).
+    const double h = -0.5 * aiG;
+    const double urur = ur * ur, upup = up * up;
+    const double W = fma(urur, g.a2s2, fma(2.0 * bh.a * ur, up, ut * ut));
+    const double a3h = (-0.5 * g.alpha) * g.ixi;      // -alpha^3 / 2
+    const double kap = fma(g.ixi * g.ixi * ur, fma(-h, ur, 1.0), -G * a3h);
+    f[3] = fma(h, fma(W, d.tt[0], upup * d.pp[0]), d.xi[0] * kap);
+    f[4] = fma(h, fma(W, d.tt[1], fma(upup, d.pp[1], urur * d.q * g.irho2)), d.xi[1] * kap);
     f[5] = 0.0;
     if (em) {
         const double k = qm * g.alpha;

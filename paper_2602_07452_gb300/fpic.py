@@ -213,12 +213,16 @@ class Particles:
             getattr(self, name).copy_(z[:, k])
 
     def struct(self):
-        return fpic_particles(self.n, _dp(self.r), _dp(self.th), _dp(self.ph), _dp(self.ur), _dp(self.uth),
-                              _dp(self.uph), _dp(self.qm), _dp(self.w), _dp(self.H0), _dp(self.D0), _dp(self.Hn),
-                              C.cast(C.c_void_p(self.alive.data_ptr()), _U8),
-                              C.cast(C.c_void_p(self.scheme.data_ptr()), _U8),
-                              C.cast(C.c_void_p(self.iters.data_ptr()), _U8),
-                              C.cast(C.c_void_p(self.cell.data_ptr()), _U32))
+        # the ctypes struct is rebuilt only when an array was replaced
+        arrs = (self.r, self.th, self.ph, self.ur, self.uth, self.uph, self.qm, self.w, self.H0, self.D0, self.Hn,
+                self.alive, self.scheme, self.iters, self.cell)
+        key = (self.n,) + tuple(t.data_ptr() for t in arrs)
+        if getattr(self, "_skey", None) != key:
+            self._s = fpic_particles(self.n, *[_dp(t) for t in arrs[:11]],
+                                     *[C.cast(C.c_void_p(t.data_ptr()), _U8) for t in arrs[11:14]],
+                                     C.cast(C.c_void_p(arrs[14].data_ptr()), _U32))
+            self._skey = key
+        return self._s
 
 
 class Ctx:
@@ -245,13 +249,22 @@ def fpic_set_grid(ctx: Ctx, grid) -> None:
     _check(lib().fpic_set_grid(ctx.handle, grid.Nr, grid.Nth, *[a.ctypes.data_as(_D) for a in arrs]))
 
 
+_FIELDS_CACHE = {}
+
+
 def _fields_arg(fields):
     if fields is None:
         return None
     assert len(fields) == 6
     for f in fields:
         assert f.dtype == torch.float64 and f.is_cuda and f.is_contiguous()
-    return (_D * 6)(*[_dp(f) for f in fields])
+    key = tuple(f.data_ptr() for f in fields)
+    arg = _FIELDS_CACHE.get(key)
+    if arg is None:
+        if len(_FIELDS_CACHE) > 64:
+            _FIELDS_CACHE.clear()
+        arg = _FIELDS_CACHE[key] = (_D * 6)(*[_dp(f) for f in fields])
+    return arg
 
 
 def fpic_init_wald(ctx: Ctx, fields, B0: float, stream=None) -> None:
@@ -316,9 +329,15 @@ class HostParticles:
         self.cell = torch.zeros(n, dtype=torch.int32).pin_memory()
 
     def struct(self):
-        hp = lambda t, ty: C.cast(C.c_void_p(t.data_ptr()), ty)
-        return fpic_particles(self.n, *[hp(getattr(self, f), _D) for f in self.FIELDS_D],
-                              *[hp(getattr(self, f), _U8) for f in self.FIELDS_B], hp(self.cell, _U32))
+        # the ctypes struct is rebuilt only when an array was replaced
+        arrs = [getattr(self, f) for f in self.FIELDS_D + self.FIELDS_B] + [self.cell]
+        key = (self.n,) + tuple(t.data_ptr() for t in arrs)
+        if getattr(self, "_skey", None) != key:
+            hp = lambda t, ty: C.cast(C.c_void_p(t.data_ptr()), ty)
+            self._s = fpic_particles(self.n, *[hp(t, _D) for t in arrs[:11]],
+                                     *[hp(t, _U8) for t in arrs[11:14]], hp(arrs[14], _U32))
+            self._skey = key
+        return self._s
 
     def bytes_in(self):
         # every double array but w (not read by the push), plus alive
