@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--learned-form", choices=("correct", "skip"), default="correct",
                     help="learned guess: corrector of the rejected trials (default) or pre-step skip")
+    ap.add_argument("--learned-restart", type=int, default=0,
+                    help="corrector: restart a solve from the plain trial after this many iterations (0: never)")
     ap.add_argument("--train-gen-steps", type=int, default=10,
                     help="plain steps sampled for the training set")
     ap.add_argument("--workload", default="push", choices=["push", "pic"])
@@ -279,7 +281,7 @@ def run_gpu(args, ws, rank, local):
                                   r_max=float(g.rn[-1]), B0pot=B0)
         t0 = time.perf_counter()
         mode = F.FPIC_LEARN_CORRECT if args.learned_form == "correct" else F.FPIC_LEARN_SKIP
-        cfg = L.fit_cfg(ctx, p, fields, prm_plain, p_skip=0.7, mode=mode)
+        cfg = L.fit_cfg(ctx, p, fields, prm_plain, p_skip=0.7, mode=mode, restart_after=args.learned_restart)
         X, T, S = L.generate(ctx, p, fields, prm_plain, cfg, steps=args.train_gen_steps)
         net, P, hist = L.train(X, T, S, steps=args.train_steps, batch=8192, lr=3e-3, log_every=500)
         torch.cuda.synchronize()
@@ -379,6 +381,7 @@ def run_gpu(args, ws, rank, local):
             "mean_imr_iterations": lrn["iters"] / max(lrn["impl"], 1),
             "rhs_evals_per_particle_step": lrn["evals"] / lp, "max_dH_over_D0": lrn["max_dH"],
             "same_start_state_as_plain": True, "form": args.learned_form,
+            "restart_after": args.learned_restart,
             "inference_ms_per_step": 1e3 * lrn["t_inf"] / args.steps,
             **({"p_skip": 0.7} if args.learned_form == "skip" else {}), "training": train_info,
             "gpu_launches": lrn["launches"],

@@ -398,18 +398,25 @@ int fpic_mlp_train_step(fpic_mlp *m, float *P, float *mom, float *vel, const flo
  *     = g + O(dt^4) with g = (2/3) A - (1/6) B; outputs 0-5 are the rest of
  *     the gap, (z_IMR - z_RK4 - g)_i / (s_i inc_scale_i), and the implicit
  *     solve starts from z_RK4 + g + s inc_scale y[0..5] instead of z_RK4
- *     (a network with zero output gives the leading-order guess alone; a
- *     component whose correction exceeds 5 % of the trial's own increment
- *     keeps the trial value).  p_skip is unused.
+ *     (a network with zero output gives the leading-order guess alone).
+ *     The plain guess is the fallback: a component whose correction
+ *     exceeds 5 % of the trial's own increment, or whose output is not
+ *     finite, keeps the trial value; with restart_after > 0 a solve not
+ *     converged after that many iterations from the corrected start
+ *     restarts from the trial with the full max_iter budget (0: the solve
+ *     runs to convergence or max_iter like the plain one).  p_skip is
+ *     unused.
  *
  *   feat_mean, feat_std : standardisation (x - mean)/std of the 14 features;
- *   mode : FPIC_LEARN_SKIP or FPIC_LEARN_CORRECT. */
+ *   mode : FPIC_LEARN_SKIP or FPIC_LEARN_CORRECT;
+ *   restart_after : see FPIC_LEARN_CORRECT (ignored by FPIC_LEARN_SKIP). */
 enum { FPIC_LEARN_SKIP = 0, FPIC_LEARN_CORRECT = 1 };
 typedef struct {
     float feat_mean[16], feat_std[16];
     double inc_scale[6];
     float p_skip;
     int mode;
+    int restart_after;
 } fpic_learned_cfg;
 
 /* Network inputs of every particle: X (device, n x 16 FP32, standardised

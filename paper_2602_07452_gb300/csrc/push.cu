@@ -60,9 +60,10 @@ struct PushK {
     // corrector form of the learned guess (per implicit-queue slot)
     float* featX;           // 16 floats: trial features (network input)
     float* featS;           // 16 floats: scales s_i (0-5), leading-order gaps g_i (8-13)
-    double* stg;            // 24 x n: slopes k1, k2, acc, k4 (by queue slot), then the trial (by particle)
+    double* stg;            // STG_ROWS x n, by queue slot: see STG_* (corrector form)
     float fmean[14], fistd[14];
     float oscale[6];        // corrector outputs 0-5 are residual / (s_i oscale_i)
+    int restart_after;      // corrector: restart from the trial after this many iterations (0: never)
 };
 
 __device__ __forceinline__ void load_state(const PartDev& P, long long p, double z[6])
@@ -142,22 +143,31 @@ __device__ __forceinline__ void warp_add(long long* c, long long v, unsigned mas
     if ((threadIdx.x & 31) == __ffs(mask) - 1 && v) atomicAdd((unsigned long long*)c, (unsigned long long)v);
 }
 
+// Rows of the corrector form's slot-indexed scratch stg (6 each): the RK4
+// slopes k1, k2, acc = k1 + 2 k2 + 2 k3, k4, the state z^n, the trial
+// z_RK4, and the corrected implicit guess.
+enum { STG_K1 = 0, STG_K2 = 6, STG_ACC = 12, STG_K4 = 18, STG_Z0 = 24, STG_TRIAL = 30, STG_GUESS = 36,
+       STG_ROWS = 42 };
+
 // Corrector form, rejected particle in queue slot idx: its slopes k1, k2
-// (kept in shared memory, column threadIdx.x), acc = k1 + 2 k2 + 2 k3 and
-// k4 go to stg rows 0-5, 6-11, 12-17, 18-23 at column idx (a warp's
-// rejected lanes hold consecutive slots, so the stores coalesce).  Plain
-// copies: the arithmetic on them runs in k_trial_feat, where every lane of
-// a warp has a queue entry.
+// (kept in shared memory, column threadIdx.x), acc, k4, z^n and the trial go
+// to stg at column idx (a warp's rejected lanes hold consecutive slots, so
+// the stores coalesce).  Plain copies: the arithmetic on them runs where
+// every lane of a warp has a queue entry, and every later read is
+// slot-ordered.
 __device__ __forceinline__ void trial_store(const PushK& k, unsigned long long idx, const double (*sk)[128],
-                                            const double acc[6], const double k4[6])
+                                            const double acc[6], const double k4[6], const double z0[6],
+                                            const double zt[6])
 {
     const int t = threadIdx.x;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-        k.stg[(size_t)i * k.n + idx] = sk[i][t];
-        k.stg[(size_t)(6 + i) * k.n + idx] = sk[6 + i][t];
-        k.stg[(size_t)(12 + i) * k.n + idx] = acc[i];
-        k.stg[(size_t)(18 + i) * k.n + idx] = k4[i];
+        k.stg[(size_t)(STG_K1 + i) * k.n + idx] = sk[i][t];
+        k.stg[(size_t)(STG_K2 + i) * k.n + idx] = sk[6 + i][t];
+        k.stg[(size_t)(STG_ACC + i) * k.n + idx] = acc[i];
+        k.stg[(size_t)(STG_K4 + i) * k.n + idx] = k4[i];
+        k.stg[(size_t)(STG_Z0 + i) * k.n + idx] = z0[i];
+        k.stg[(size_t)(STG_TRIAL + i) * k.n + idx] = zt[i];
     }
 }
 
@@ -249,7 +259,7 @@ __global__ void __launch_bounds__(128) k_explicit(PushK k)
             k.sc0[p] = s0;
             k.sc0[k.n + p] = c0;
             if (MODE == 2) {
-                trial_store(k, idx, sk, acc, kk);
+                trial_store(k, idx, sk, acc, kk, z0, y);
                 if (k.record) k.recS[idx] = label;
             }
         }
@@ -272,11 +282,10 @@ __device__ __forceinline__ bool conv6(const double a[6], const double b[6], doub
 // parks the result in the guess slot and takes the next particle at once.
 // H at the converged point and the write-back run afterwards in
 // k_imr_finish (one thread per particle, no lane waits on them here).
-// RESTART 1: a solve that has not converged after IMR_RESTART_AFTER
-// iterations from the corrected start restarts once, with the full
-// max_iter budget, from the trial in stg (corrector form of the learned
-// guess; a corrected start that helps converges well before that).
-constexpr int IMR_RESTART_AFTER = 25;
+// RESTART 1 (corrector form of the learned guess): the start is the
+// corrected guess of the queue slot (stg); with k.restart_after > 0, a solve
+// that has not converged after that many iterations from it restarts once,
+// with the full max_iter budget, from the trial in stg.
 template <int RESTART>
 __global__ void __launch_bounds__(128, 4) k_imr(PushK k, int all_mode)
 {
@@ -321,7 +330,9 @@ __global__ void __launch_bounds__(128, 4) k_imr(PushK k, int all_mode)
                             s0 = k.sc0[p];
                             c0 = k.sc0[k.n + p];
 #pragma unroll
-                            for (int i = 0; i < 6; ++i) zk[i] = k.guess[(size_t)i * k.n + p];
+                            for (int i = 0; i < 6; ++i)
+                                zk[i] = RESTART ? k.stg[(size_t)(STG_GUESS + i) * k.n + idx]
+                                                : k.guess[(size_t)i * k.n + p];
                         }
                         qm = k.P.qm[p];
                         em = k.run.has_fields && qm != 0.0;
@@ -352,13 +363,13 @@ __global__ void __launch_bounds__(128, 4) k_imr(PushK k, int all_mode)
 #pragma unroll
             for (int i = 0; i < 6; ++i) zk[i] = zn[i];
             ++it;
-            if (RESTART && !ok && it >= min(k.max_iter, IMR_RESTART_AFTER) && again) {
+            if (RESTART && !ok && k.restart_after > 0 && it >= min(k.max_iter, k.restart_after) && again) {
                 // the corrected start did not converge: the plain trial is the fallback
                 again = false;
                 n_it += it;
                 it = 0;
 #pragma unroll
-                for (int i = 0; i < 6; ++i) zk[i] = k.stg[(size_t)i * k.n + p];
+                for (int i = 0; i < 6; ++i) zk[i] = k.stg[(size_t)(STG_TRIAL + i) * k.n + qi];
             } else if (ok || it >= k.max_iter) {
                 if (!ok) ++n_nc;
                 if (k.record && k.featS) {
@@ -1054,12 +1065,12 @@ static void fill_pushk(PushK& k, fpic_ctx* c, fpic_particles* p, const double* c
     k.cnt = c->d_cnt;
 }
 
-// scratch: guess 6n doubles | sc0 2n doubles | stg 24n doubles | queue n | work n | X 16n floats |
+// scratch: guess 6n doubles | sc0 2n doubles | stg STG_ROWS n doubles | queue n | work n | X 16n floats |
 // Y 16n floats | featS 16n floats | 6 FP32 field copies
 static int learned_scratch(fpic_ctx* c, long long n, PushK& k, float** X, float** Y, float** f32)
 {
     const size_t fsz = c->has_grid ? 6 * (size_t)(c->Nr + 1) * c->ld : 0;
-    const size_t need = (size_t)n * (32 * sizeof(double) + 2 * sizeof(uint32_t) + 48 * sizeof(float)) +
+    const size_t need = (size_t)n * ((8 + STG_ROWS) * sizeof(double) + 2 * sizeof(uint32_t) + 48 * sizeof(float)) +
                         fsz * sizeof(float) + 2048;
     int rc = ensure_scratch(c, need);
     if (rc) return rc;
@@ -1069,7 +1080,7 @@ static int learned_scratch(fpic_ctx* c, long long n, PushK& k, float** X, float*
     k.sc0 = (double*)b;
     b += (size_t)n * 2 * sizeof(double);
     k.stg = (double*)b;
-    b += (size_t)n * 24 * sizeof(double);
+    b += (size_t)n * STG_ROWS * sizeof(double);
     k.queue = (uint32_t*)b;
     b += (size_t)n * sizeof(uint32_t);
     k.work = (uint32_t*)b;
@@ -1088,6 +1099,7 @@ static int learned_scratch(fpic_ctx* c, long long n, PushK& k, float** X, float*
 static void set_corrector(PushK& k, const fpic_learned_cfg* cfg, float* X)
 {
     k.featX = X;
+    k.restart_after = cfg->restart_after;
     for (int i = 0; i < 6; ++i) k.oscale[i] = cfg->inc_scale[i] > 0.0 ? (float)cfg->inc_scale[i] : 1.f;
     for (int i = 0; i < 14; ++i) {
         k.fmean[i] = cfg->feat_mean[i];
@@ -1107,16 +1119,16 @@ static void set_corrector(PushK& k, const fpic_learned_cfg* cfg, float* X)
 // dt^2 f'f'f / 4 + O(dt^3) and k4 - 2 k2 + k1 = dt^2 (f'f'f / 2 +
 // f''(f,f) / 4) + O(dt^3).  FP32 after the differences: the features feed
 // a bf16 network and the gap only has to be a good start for the solve.
-__device__ __forceinline__ void trial_row(const PushK& k, long long idx, long long p, float f[16], float sc[6],
-                                          float gl[6])
+__device__ __forceinline__ void trial_row(const PushK& k, long long idx, float f[16], float sc[6], float gl[6])
 {
-    double z0[6];
-    load_state(k.P, p, z0);
     float num = 0.f, den = 0.f;
+    double r0 = 0.0;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-        const double k1 = k.stg[(size_t)i * k.n + idx], k2 = k.stg[(size_t)(6 + i) * k.n + idx];
-        const double acc = k.stg[(size_t)(12 + i) * k.n + idx], k4 = k.stg[(size_t)(18 + i) * k.n + idx];
+        const double k1 = k.stg[(size_t)(STG_K1 + i) * k.n + idx], k2 = k.stg[(size_t)(STG_K2 + i) * k.n + idx];
+        const double acc = k.stg[(size_t)(STG_ACC + i) * k.n + idx], k4 = k.stg[(size_t)(STG_K4 + i) * k.n + idx];
+        const double z0 = k.stg[(size_t)(STG_Z0 + i) * k.n + idx];
+        if (i == 0) r0 = z0;
         const float a = (float)(k.dt * fma(0.5, acc - k1, -2.0 * k2));
         const float b = (float)(k.dt * ((k4 - k2) - (k2 - k1)));
         const float sm = fabsf(a) + fabsf(b);
@@ -1127,10 +1139,10 @@ __device__ __forceinline__ void trial_row(const PushK& k, long long idx, long lo
         sc[i] = sm;
         if (i == 3 || i == 4) {
             num += fabsf(a);
-            den += fabsf((float)(k.guess[(size_t)i * k.n + p] - z0[i]));
+            den += fabsf((float)(k.stg[(size_t)(STG_TRIAL + i) * k.n + idx] - z0));
         }
     }
-    f[12] = __logf((float)z0[0]);
+    f[12] = __logf((float)r0);
     f[13] = (num > 0.f && den > 0.f) ? __logf(num / den) : 0.f;
 #pragma unroll
     for (int i = 0; i < 14; ++i) f[i] = (f[i] - k.fmean[i]) * k.fistd[i];
@@ -1145,7 +1157,7 @@ __global__ void k_trial_feat(PushK k)
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < qn;
          idx += (long long)gridDim.x * blockDim.x) {
         float f[16], sc[6], gl[6];
-        trial_row(k, idx, (long long)k.queue[idx], f, sc, gl);
+        trial_row(k, idx, f, sc, gl);
         float4* x = (float4*)(k.featX + 16 * idx);
         float4* o = (float4*)(k.featS + 16 * idx);
 #pragma unroll
@@ -1161,9 +1173,9 @@ __global__ void k_trial_feat(PushK k)
 // 128-slot tile of the implicit queue (count read on the device), thread
 // t < 128 builds the features of slot tile*128 + t straight into the
 // network's bf16 input tile, the four layers run on the tensor cores
-// (mlp_dev.cuh), and the same thread applies its row's output: the trial
-// z_RK4 is kept in stg (for the restart) and the implicit guess becomes
-// z_RK4 + g_i + s_i oscale_i y_i.  Guard: the IMR - RK4 gap is O(dt^3)
+// (mlp_dev.cuh), and the same thread applies its row's output: the implicit
+// guess of the slot (stg, read by k_imr<1>) becomes z_RK4 + g_i + s_i
+// oscale_i y_i.  Guard: the IMR - RK4 gap is O(dt^3)
 // against the O(dt) step, so a component whose correction exceeds CORR_MAX
 // times the trial's own increment (or whose output is outside [-16, 16] or
 // not finite) keeps the trial value.
@@ -1183,13 +1195,11 @@ __global__ void __launch_bounds__(FW_THREADS) k_mlp_correct(PushK k, MlpDev w, i
     for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         const long long idx = tile * 128 + r;
         const bool valid = idx < qn;
-        long long p = 0;
         float sc[6], gl[6];
         if (half == 0) {
             float f[16];
             if (valid) {
-                p = k.queue[idx];
-                trial_row(k, idx, p, f, sc, gl);
+                trial_row(k, idx, f, sc, gl);
             } else {
 #pragma unroll
                 for (int i = 0; i < 16; ++i) f[i] = 0.f;
@@ -1207,16 +1217,14 @@ __global__ void __launch_bounds__(FW_THREADS) k_mlp_correct(PushK k, MlpDev w, i
             float v[16];
             tc::tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16), v);
             if (valid) {
-                double z0[6];
-                load_state(k.P, p, z0);
 #pragma unroll
                 for (int i = 0; i < 6; ++i) {
                     const float y = v[i] + sb[384 + i];
-                    const double zt = k.guess[(size_t)i * k.n + p];
+                    const double zt = k.stg[(size_t)(STG_TRIAL + i) * k.n + idx];
+                    const double z0 = k.stg[(size_t)(STG_Z0 + i) * k.n + idx];
                     const float d = fmaf(sc[i] * k.oscale[i], y, gl[i]);
-                    k.stg[(size_t)i * k.n + p] = zt;
-                    if (fabsf(y) <= 16.f && fabsf(d) <= CORR_MAX * (float)fabs(zt - z0[i]))
-                        k.guess[(size_t)i * k.n + p] = zt + (double)d;
+                    const bool use = fabsf(y) <= 16.f && fabsf(d) <= CORR_MAX * (float)fabs(zt - z0);
+                    k.stg[(size_t)(STG_GUESS + i) * k.n + idx] = use ? zt + (double)d : zt;
                 }
             }
         }

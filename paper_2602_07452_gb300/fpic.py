@@ -79,7 +79,8 @@ class fpic_run(C.Structure):
 class fpic_learned_cfg(C.Structure):
     _fields_ = [("feat_mean", C.c_float * 16), ("feat_std", C.c_float * 16), ("inc_scale", C.c_double * 6),
                 ("p_skip", C.c_float),
-                ("mode", C.c_int)]
+                ("mode", C.c_int),
+                ("restart_after", C.c_int)]
 
 
 FPIC_LEARN_SKIP, FPIC_LEARN_CORRECT = 0, 1
@@ -517,7 +518,8 @@ class MLP:
         return st.value
 
 
-def learned_cfg(feat_mean=None, feat_std=None, inc_scale=None, p_skip=0.5, mode=FPIC_LEARN_SKIP):
+def learned_cfg(feat_mean=None, feat_std=None, inc_scale=None, p_skip=0.5, mode=FPIC_LEARN_SKIP,
+                restart_after=0):
     cfg = fpic_learned_cfg()
     for i in range(16):
         cfg.feat_mean[i] = 0.0 if feat_mean is None or i >= len(feat_mean) else float(feat_mean[i])
@@ -526,6 +528,7 @@ def learned_cfg(feat_mean=None, feat_std=None, inc_scale=None, p_skip=0.5, mode=
         cfg.inc_scale[i] = 1.0 if inc_scale is None else float(inc_scale[i])
     cfg.p_skip = p_skip
     cfg.mode = mode
+    cfg.restart_after = restart_after
     return cfg
 
 

@@ -34,7 +34,7 @@ def _rows(p, cfg, S):
     return _alive_rows(p)
 
 
-def fit_cfg(ctx, p, fields, prm, p_skip=0.5, mode=F.FPIC_LEARN_SKIP):
+def fit_cfg(ctx, p, fields, prm, p_skip=0.5, mode=F.FPIC_LEARN_SKIP, restart_after=0):
     """Standardisation of features (and, skip form, increments) from one raw sample."""
     raw = F.learned_cfg(mode=mode) if mode == F.FPIC_LEARN_CORRECT else None
     X, T, S = F.fpic_learn_sample(ctx, p, fields, prm, raw)
@@ -45,7 +45,7 @@ def fit_cfg(ctx, p, fields, prm, p_skip=0.5, mode=F.FPIC_LEARN_SKIP):
     std[std < 1e-30] = 1.0
     inc = Ta.std(0).cpu().numpy()
     inc[inc < 1e-300] = 1.0
-    return F.learned_cfg(mean, std, inc, p_skip, mode)
+    return F.learned_cfg(mean, std, inc, p_skip, mode, restart_after)
 
 
 def generate(ctx, p, fields, prm, cfg, steps):
