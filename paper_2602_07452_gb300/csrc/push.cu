@@ -1119,8 +1119,10 @@ static void set_corrector(PushK& k, const fpic_learned_cfg* cfg, float* X)
 // dt^2 f'f'f / 4 + O(dt^3) and k4 - 2 k2 + k1 = dt^2 (f'f'f / 2 +
 // f''(f,f) / 4) + O(dt^3).  FP32 after the differences: the features feed
 // a bf16 network and the gap only has to be a good start for the solve.
-__device__ __forceinline__ void trial_row(const PushK& k, long long idx, float f[16], float sc[6], float gl[6])
+__device__ __forceinline__ void trial_row(const PushK& k, long long idx, float f[16], float sc[6], float gl[6],
+                                          float dz[6])
 {
+    const float dt = (float)k.dt;
     float num = 0.f, den = 0.f;
     double r0 = 0.0;
 #pragma unroll
@@ -1129,8 +1131,10 @@ __device__ __forceinline__ void trial_row(const PushK& k, long long idx, float f
         const double acc = k.stg[(size_t)(STG_ACC + i) * k.n + idx], k4 = k.stg[(size_t)(STG_K4 + i) * k.n + idx];
         const double z0 = k.stg[(size_t)(STG_Z0 + i) * k.n + idx];
         if (i == 0) r0 = z0;
-        const float a = (float)(k.dt * fma(0.5, acc - k1, -2.0 * k2));
-        const float b = (float)(k.dt * ((k4 - k2) - (k2 - k1)));
+        // the differences in FP64 (they cancel), the rest in FP32
+        const float a = dt * (float)fma(0.5, acc - k1, -2.0 * k2);
+        const float b = dt * (float)((k4 - k2) - (k2 - k1));
+        dz[i] = fabsf((float)(k.stg[(size_t)(STG_TRIAL + i) * k.n + idx] - z0));
         const float sm = fabsf(a) + fabsf(b);
         gl[i] = fmaf(2.f / 3.f, a, -b * (1.f / 6.f));
         const float is = sm > 0.f ? 1.f / sm : 0.f;
@@ -1139,7 +1143,7 @@ __device__ __forceinline__ void trial_row(const PushK& k, long long idx, float f
         sc[i] = sm;
         if (i == 3 || i == 4) {
             num += fabsf(a);
-            den += fabsf((float)(k.stg[(size_t)(STG_TRIAL + i) * k.n + idx] - z0));
+            den += dz[i];
         }
     }
     f[12] = __logf((float)r0);
@@ -1156,8 +1160,8 @@ __global__ void k_trial_feat(PushK k)
     const long long qn = k.cnt[CNT_QUEUE];
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < qn;
          idx += (long long)gridDim.x * blockDim.x) {
-        float f[16], sc[6], gl[6];
-        trial_row(k, idx, f, sc, gl);
+        float f[16], sc[6], gl[6], dz[6];
+        trial_row(k, idx, f, sc, gl, dz);
         float4* x = (float4*)(k.featX + 16 * idx);
         float4* o = (float4*)(k.featS + 16 * idx);
 #pragma unroll
@@ -1169,68 +1173,70 @@ __global__ void k_trial_feat(PushK k)
     }
 }
 
-// Corrector form in the push, one fused persistent kernel per step: per
-// 128-slot tile of the implicit queue (count read on the device), thread
-// t < 128 builds the features of slot tile*128 + t straight into the
-// network's bf16 input tile, the four layers run on the tensor cores
-// (mlp_dev.cuh), and the same thread applies its row's output: the implicit
-// guess of the slot (stg, read by k_imr<1>) becomes z_RK4 + g_i + s_i
-// oscale_i y_i.  Guard: the IMR - RK4 gap is O(dt^3)
-// against the O(dt) step, so a component whose correction exceeds CORR_MAX
-// times the trial's own increment (or whose output is outside [-16, 16] or
-// not finite) keeps the trial value.
+// Guard of the corrector: the IMR - RK4 gap is O(dt^3) against the O(dt)
+// step, so a component whose correction exceeds CORR_MAX times the trial's
+// own increment (or whose output is outside [-16, 16] or not finite) keeps
+// the trial value.
 constexpr float CORR_MAX = 0.05f;
-__global__ void __launch_bounds__(FW_THREADS) k_mlp_correct(PushK k, MlpDev w, int* err)
+
+// Corrector form in the push, one fused persistent kernel per step
+// (mlp_dev.cuh): one CTA of 512 threads per SM runs four independent
+// 128-slot tile pipelines of the implicit queue (its length read on the
+// device) over the shared resident weights.  Thread t % 128 of group t / 128
+// builds its slot's features straight into the group's bf16 input tile,
+// the four layers run on the tensor cores, and the same thread applies its
+// row's output: the slot's implicit guess (stg, read by k_imr<1>) becomes
+// z_RK4 + g_i + s_i oscale_i y_i.
+__global__ void __launch_bounds__(G4_THREADS, 1) k_mlp_correct4(PushK k, MlpDev w, int* err)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     const long long qn = k.cnt[CNT_QUEUE];
     const long long ntiles = (qn + 127) / 128;
-    if ((long long)blockIdx.x >= ntiles) return;     // whole block, before any allocation
-    const float* sb = (const float*)(smem + FW_B);
-    const int warp = threadIdx.x >> 5, r = threadIdx.x & 127, half = threadIdx.x >> 7;
-    uint64_t* mbar;
-    const uint32_t tbase = mlp_cta_setup(w, smem, &mbar);
+    if ((long long)blockIdx.x * G4_GROUPS >= ntiles) return;     // whole block, before any allocation
+    const float* sb = (const float*)(smem + G4_B);
+    const int g = threadIdx.x >> 7, r = threadIdx.x & 127, wq = (threadIdx.x >> 5) & 3;
+    const uint32_t tbase0 = mlp_cta_setup4(w, smem);
+    const uint32_t tbase = tbase0 + (uint32_t)(128 * g);
+    uint64_t* mbar = (uint64_t*)(smem + G4_BAR) + g;
+    uint8_t* sX = smem + G4_TILE0 + g * G4_TILE_BYTES;
     uint32_t phase = 0;
     int ok = 1;
-    for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    for (long long tile = (long long)blockIdx.x * G4_GROUPS + g; tile < ntiles && ok;
+         tile += (long long)gridDim.x * G4_GROUPS) {
         const long long idx = tile * 128 + r;
         const bool valid = idx < qn;
-        float sc[6], gl[6];
-        if (half == 0) {
-            float f[16];
-            if (valid) {
-                trial_row(k, idx, f, sc, gl);
-            } else {
+        float f[16], sc[6], gl[6], dz[6];
+        if (valid) {
+            trial_row(k, idx, f, sc, gl, dz);
+        } else {
 #pragma unroll
-                for (int i = 0; i < 16; ++i) f[i] = 0.f;
-            }
-            *(uint4*)(smem + FW_X + tc::kmajor_off(r, 0, 128)) =
-                make_uint4(tc::pack_bf2(f[0], f[1]), tc::pack_bf2(f[2], f[3]), tc::pack_bf2(f[4], f[5]),
-                           tc::pack_bf2(f[6], f[7]));
-            *(uint4*)(smem + FW_X + tc::kmajor_off(r, 8, 128)) =
-                make_uint4(tc::pack_bf2(f[8], f[9]), tc::pack_bf2(f[10], f[11]), tc::pack_bf2(f[12], f[13]),
-                           tc::pack_bf2(f[14], f[15]));
+            for (int i = 0; i < 16; ++i) f[i] = 0.f;
         }
-        ok = mlp_tile_layers(tbase, smem, mbar, phase, nullptr, idx, qn);
+        *(uint4*)(sX + tc::kmajor_off(r, 0, 128)) =
+            make_uint4(tc::pack_bf2(f[0], f[1]), tc::pack_bf2(f[2], f[3]), tc::pack_bf2(f[4], f[5]),
+                       tc::pack_bf2(f[6], f[7]));
+        *(uint4*)(sX + tc::kmajor_off(r, 8, 128)) =
+            make_uint4(tc::pack_bf2(f[8], f[9]), tc::pack_bf2(f[10], f[11]), tc::pack_bf2(f[12], f[13]),
+                       tc::pack_bf2(f[14], f[15]));
+        ok = mlp_tile_layers_g(g, tbase, smem, mbar, phase);
         if (!ok) break;
-        if (half == 0) {
-            float v[16];
-            tc::tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16), v);
-            if (valid) {
+        float v[16];
+        tc::tmem_ld16(tbase + ((uint32_t)(wq * 32) << 16), v);
+        if (valid) {
 #pragma unroll
-                for (int i = 0; i < 6; ++i) {
-                    const float y = v[i] + sb[384 + i];
-                    const double zt = k.stg[(size_t)(STG_TRIAL + i) * k.n + idx];
-                    const double z0 = k.stg[(size_t)(STG_Z0 + i) * k.n + idx];
-                    const float d = fmaf(sc[i] * k.oscale[i], y, gl[i]);
-                    const bool use = fabsf(y) <= 16.f && fabsf(d) <= CORR_MAX * (float)fabs(zt - z0);
-                    k.stg[(size_t)(STG_GUESS + i) * k.n + idx] = use ? zt + (double)d : zt;
-                }
+            for (int i = 0; i < 6; ++i) {
+                const float y = v[i] + sb[384 + i];
+                const double zt = k.stg[(size_t)(STG_TRIAL + i) * k.n + idx];
+                const double z0 = k.stg[(size_t)(STG_Z0 + i) * k.n + idx];
+                const float d = fmaf(sc[i] * k.oscale[i], y, gl[i]);
+                const bool use = fabsf(y) <= 16.f && fabsf(d) <= CORR_MAX * (float)fabs(zt - z0);
+                k.stg[(size_t)(STG_GUESS + i) * k.n + idx] = use ? zt + (double)d : zt;
             }
         }
     }
-    mlp_cta_teardown(tbase, ok, err);
+    mlp_cta_teardown4(tbase0, ok, err);
 }
+
 
 // FP32 copies of the field arrays (network inputs are rounded to bf16 anyway;
 // converting the grid once is cheaper than converting 24 gathered values per
@@ -1380,14 +1386,14 @@ extern "C" int fpic_push_learned(fpic_ctx* c, fpic_mlp* m, fpic_particles* p, co
         if (ev) FPIC_CUDA(cudaEventRecord(ev[1], s));
         static bool attr_set = false;
         if (!attr_set) {
-            FPIC_CUDA(cudaFuncSetAttribute(k_mlp_correct, cudaFuncAttributeMaxDynamicSharedMemorySize, FW_SMEM));
+            FPIC_CUDA(cudaFuncSetAttribute(k_mlp_correct4, cudaFuncAttributeMaxDynamicSharedMemorySize, G4_SMEM));
             attr_set = true;
         }
-        // two CTAs per SM (shared memory and TMEM allow two); the kernel reads
-        // the queue length itself and idle CTAs leave at once
-        const long long ntiles = (n + 127) / 128, cap = 2LL * mlp_sm_count(m);
-        k_mlp_correct<<<(unsigned)(ntiles < cap ? ntiles : cap), FW_THREADS, FW_SMEM, s>>>(k, mlp_weights(m),
-                                                                                           mlp_err(m));
+        // one CTA of four tile pipelines per SM; the kernel reads the queue
+        // length itself and idle CTAs leave at once
+        const long long nct = (n + 127) / 128 / G4_GROUPS + 1, cap = mlp_sm_count(m);
+        k_mlp_correct4<<<(unsigned)(nct < cap ? nct : cap), G4_THREADS, G4_SMEM, s>>>(k, mlp_weights(m),
+                                                                                      mlp_err(m));
         if (ev) FPIC_CUDA(cudaEventRecord(ev[2], s));
     } else {
         // network on every particle first; predicted rejections skip the trial
