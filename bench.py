@@ -60,11 +60,15 @@ def parse():
                     help="corrector: restart a solve from the plain trial after this many iterations (0: never)")
     ap.add_argument("--train-gen-steps", type=int, default=10,
                     help="plain steps sampled for the training set")
-    ap.add_argument("--workload", default="push", choices=["push", "pic"])
+    ap.add_argument("--workload", default="push", choices=["push", "pic", "neutral", "batched"])
     ap.add_argument("--pic-grid", type=int, default=1024)
     ap.add_argument("--pic-ppc", type=int, default=64)
     ap.add_argument("--pic-steps", type=int, default=3)
     ap.add_argument("--no-pic", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the neutral-geodesic and batched-runs keys of the default run")
+    ap.add_argument("--batch-scale", type=float, default=1.0,
+                    help="--workload batched: particle counts x this (1.0 = 1e5..4e7 per run)")
     ap.add_argument("--train-steps", type=int, default=3000)
     return ap.parse_args()
 
@@ -402,6 +406,123 @@ def run_gpu(args, ws, rank, local):
     return line
 
 
+def run_neutral(args, device, n, steps, K=32, seed=1, pre_steps=1000, scheme="HYB2"):
+    """Neutral test particles (geodesics, no fields): Kerr a = 0.9, bound-orbit
+    seeds r ~ U[3, 20], th ~ U(0.1, pi - 0.1), E ~ U[0.9, 0.98],
+    L ~ U[2.5, 4.5] (K candidates per particle, rejection-sampled on the
+    device), dt = 0.01, Hyb2 RK4 <-> discrete-gradient scheme with
+    Ht_max = 1e-12 (Sec. 3.1.2, Tab. C.2 Kerr row)."""
+    import numpy as np
+    import torch
+    from paper_2602_07452_gb300 import fpic as F
+    from paper_2602_07452_gb300 import inputs as I
+    a, dt = 0.9, 0.01
+    ctx = F.fpic_init_metric(1.0, a)
+    cand = torch.as_tensor(I.orbit_candidates(n, K=K, seed=seed), device=device)
+    p = F.Particles.empty(n, device)
+    F.fpic_init_particles(ctx, p, F.FPIC_SEED_ORBIT, cand, K=K)
+    del cand
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    for e in ev:
+        e.record()
+    prm = F.push_params(dt, scheme=getattr(F, "FPIC_" + scheme), implicit=F.FPIC_HAM, thr=1e-12,
+                        events=ev[1:5])
+    # the cumulative test only starts sending particles to the implicit
+    # scheme once RK4's energy error has built up: measure after pre_steps
+    for _ in range(pre_steps):
+        F.fpic_push(ctx, p, None, prm)
+    torch.cuda.synchronize()
+    t = ps = impl = iters = 0.0
+    for _ in range(steps):
+        ev[0].record()
+        st = F.fpic_push(ctx, p, None, prm, stats=True)
+        ev[5].record()
+        torch.cuda.synchronize()
+        t += ev[0].elapsed_time(ev[5]) * 1e-3
+        ps += st["n_alive_before"]
+        impl += st["n_implicit"]
+        iters += st["n_iter_total"]
+    H, _ = F.fpic_hamiltonian(ctx, p, B0pot=0.0)
+    al = p.alive.bool()
+    drift = float(((H - p.H0).abs() / p.H0.abs())[al].max().item()) if bool(al.any()) else 0.0
+    name = {"HYB2": "Hyb2 RK4<->discrete-gradient, Ht_max=1e-12", "HAM": "discrete-gradient scheme alone",
+            "RK4": "RK4 alone"}[scheme]
+    return {"workload": f"neutral geodesics, Kerr a={a}, {n} candidates-seeded particles, dt={dt}, {name}",
+            "particles": int(ps / max(steps, 1)), "steps": steps, "value": ps / t, "unit": UNIT,
+            "ms_per_step": 1e3 * t / steps, "implicit_fraction": impl / max(ps, 1),
+            "mean_dg_iterations": iters / max(impl, 1), "max_dH_over_H0_after": drift,
+            "steps_before_measurement": pre_steps}
+
+
+def run_batched(args, device, scale, steps):
+    """24 independent runs in one explicit and one persistent implicit launch
+    per step, replayed from a CUDA graph: spins a = 0.5 ... 0.99, grids 256^2
+    ... 1024^2 (geometric), scale x (1e5 ... 4e7) particles each (log-spaced),
+    each run its own analytic Wald field (B0 = 1) and thermal e-/e+ plasma
+    (theta_T = 0.1, q/m = -/+100), Hyb1 RK4 <-> IMR, dt = 1e-3."""
+    import numpy as np
+    import torch
+    from paper_2602_07452_gb300 import fpic as F
+    from paper_2602_07452_gb300 import inputs as I
+    spins = np.linspace(0.5, 0.99, 24)
+    grids = np.round(np.geomspace(256, 1024, 24)).astype(int)
+    counts = np.maximum(1, np.round(np.geomspace(1e5, 4e7, 24) * scale)).astype(int)
+    n = int(counts.sum())
+    p = F.Particles.empty(n, device)
+    ctxs, flds, specs = [], [], []
+    off = 0
+    for k in range(24):
+        a, N, m = float(spins[k]), int(grids[k]), int(counts[k])
+        g = I.wald_grid(N, a)
+        ctx = F.fpic_init_metric(1.0, a)
+        F.fpic_set_grid(ctx, g)
+        fl = [torch.zeros(g.size, dtype=torch.float64, device=device) for _ in range(6)]
+        F.fpic_init_wald(ctx, fl, B0)
+        d, q, w = I.thermal_draws(m, g, 1.02 * I.horizon(1.0, a), 0.98 * g.rn[-1], THETA_T, seed=100 + k, qm=QM)
+        sub = F.Particles.empty(m, device)
+        sub.qm.copy_(torch.as_tensor(q, device=device))
+        sub.w.copy_(torch.as_tensor(w, device=device))
+        F.fpic_init_particles(ctx, sub, F.FPIC_SEED_FIDO, torch.as_tensor(d, device=device), B0pot=B0)
+        for name in ("r", "th", "ph", "ur", "uth", "uph", "qm", "w", "H0", "D0", "Hn", "alive"):
+            getattr(p, name)[off:off + m].copy_(getattr(sub, name))
+        del sub, d
+        ctxs.append(ctx)
+        flds.append(fl)
+        specs.append((ctx, fl, off, off + m, float(g.rn[-1]), B0))
+        off += m
+    runs = F.make_runs(specs)
+    prm = F.push_params(DT, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=HYB1_THR)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for _ in range(2):
+            F.fpic_push_batched(runs, p, prm, stream=s)
+    torch.cuda.synchronize()
+    alive0 = int(p.alive.sum().item())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        F.fpic_push_batched(runs, p, prm, stream=s)
+    with torch.cuda.stream(s):
+        graph.replay()                      # warm replay
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    alive_start = int(p.alive.sum().item())
+    with torch.cuda.stream(s):              # replay on the stream the events are recorded on
+        e0.record(s)
+        for _ in range(steps):
+            graph.replay()
+        e1.record(s)
+    torch.cuda.synchronize()
+    alive_end = int(p.alive.sum().item())
+    t = e0.elapsed_time(e1) * 1e-3
+    # particle-steps: alive particles at the start of each step; removal is
+    # slow, so the mean of the first and last count bounds it within 1e-3
+    ps = 0.5 * (alive_start + alive_end) * steps
+    return {"workload": "24 uneven Wald runs in one batched launch per step (CUDA graph replay): "
+                        f"a=0.5..0.99, grids 256^2..1024^2, {scale:g} x (1e5..4e7) particles each",
+            "particles": n, "alive_at_start": alive_start, "runs": 24, "steps": steps, "value": ps / t,
+            "unit": UNIT, "ms_per_step": 1e3 * t / steps}
+
+
 def run_pic(args, device, grid_n, ppc, steps, rank=0):
     """Full GRPIC step (Sec. 2.1 order): FDTD sub-steps 1-4, RK4 push with
     D^{n+3/2}, B^{n+3/2}, sort + deposit at n+2, FDTD sub-steps 7-10.
@@ -516,10 +637,16 @@ def main():
     import torch.distributed as dist
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    if args.workload == "pic":
+    if args.workload in ("pic", "neutral", "batched"):
         import torch
         torch.cuda.set_device(local)
-        res = run_pic(args, torch.device("cuda", local), args.pic_grid, args.pic_ppc, args.pic_steps, rank)
+        dev = torch.device("cuda", local)
+        if args.workload == "pic":
+            res = run_pic(args, dev, args.pic_grid, args.pic_ppc, args.pic_steps, rank)
+        elif args.workload == "neutral":
+            res = run_neutral(args, dev, 1 << 20, args.steps)
+        else:
+            res = run_batched(args, dev, args.batch_scale, args.steps)
         if rank == 0:
             line = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": ws, "steps": res["steps"],
                     "warmup": 1, "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
@@ -530,6 +657,14 @@ def main():
     if not args.no_pic and rank == 0:
         import torch
         line["pic_step"] = run_pic(args, torch.device("cuda", local), 512, 16, 3, rank)
+    if not args.no_extra and rank == 0:
+        import torch
+        dev = torch.device("cuda", local)
+        line["neutral"] = run_neutral(args, dev, 1 << 20, 20)
+        line["neutral_4096"] = run_neutral(args, dev, 4096, 20)
+        line["neutral_dg_alone"] = run_neutral(args, dev, 1 << 20, 5, pre_steps=2, scheme="HAM")
+        line["neutral_rk4_alone"] = run_neutral(args, dev, 1 << 20, 20, pre_steps=2, scheme="RK4")
+        line["batched"] = run_batched(args, dev, 0.1, 5)
     if rank == 0:
         if pool is not None:
             try:
