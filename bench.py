@@ -38,6 +38,10 @@ FLOP_RK4_TRIAL = 4 * FLOP_EVAL + 79 + 56 + 5
 FLOP_IMR_ITER = FLOP_EVAL + 48
 FLOP_IMR_FINAL = 56         # H at the converged point (metric + Gamma + H)
 NOMINAL_FP64_GFLOPS = 1250.0
+# DRAM bytes (read + write) of one k_explicit<1> launch on this workload,
+# from one ncu capture of the current kernel (117.8 MB + 51.6 MB); the
+# algorithmic bytes are ~180 B per particle (189 MB for 2^20).
+TRAFFIC_K_EXPLICIT = 169.4e6
 # deposit: FIDO velocity (41) + 3 sub-grids x (49 sqrt(gamma) points x 9 +
 # lattice 14 + four 16-point sums 128 + weights 16) + 2 th lattices (56) + shares (30)
 FLOP_DEPOSIT = 41 + 3 * (49 * 9 + 14 + 128 + 16) + 56 + 30
@@ -371,7 +375,9 @@ def run_gpu(args, ws, rank, local):
                 "api": "fpic_push_host (pinned host SoA in, result out, every step)"},
         "roofline": {"bound": "alu", "kernel": dom, "achieved": ach, "peak": fp64_gflops,
                      "peak_source": "FP64 FMA probe (fpic_probe_fp64) in this run; nominal 1250",
-                     "unit": "GFLOP/s", "frac": ach / fp64_gflops, "traffic": None,
+                     "unit": "GFLOP/s", "frac": ach / fp64_gflops,
+                     "traffic": TRAFFIC_K_EXPLICIT if dom == "k_explicit" else None,
+                     "traffic_unit": "bytes per launch (ncu dram__bytes_read + dram__bytes_write)",
                      "share_explicit": t_ex / max(t_ex + t_im, 1e-30)},
         "clocks": clk,
         "gpu_launches": plain["launches"],
