@@ -1,0 +1,101 @@
+"""Parity at the benchmark's full sizes, in the launch configuration the
+benchmark times, on sampled outputs the oracle computes one by one:
+
+* the charged Wald push (2^20 particles, 512 x 512 grid, a = 0.9, Hyb1
+  RK4 <-> IMR, dt = 1e-3, the autotuned implicit launch shape): every
+  sampled particle's step against the oracle's;
+* the deposit of the plasma-filled Wald step (1024 x 1024 grid, 64
+  particles per cell, a = 0.99): sampled interior nodes of rho, j^r, j^th,
+  j^ph against the oracle's deposit of the particles that can reach them.
+
+Inputs are the seeded draws of the benchmark, turned into states by the
+oracle's own seeding (no input comes from the CUDA path)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import pic as P
+from paper_2602_07452_gb300 import inputs as I
+from helpers import cuda_or_skip, fields_dev, fpic, make_particles, to_np
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+A, B0, THETA_T, QM, DT, NGRID, THR = 0.9, 1.0, 0.1, 100.0, 1e-3, 512, 3.5e-6
+
+
+def test_fullsize_charged_push_sampled():
+    cuda_or_skip()
+    F = fpic()
+    n = 1 << 20
+    g = I.wald_grid(NGRID, A)
+    Fo = O.wald_on_grid(A, B0, g)
+    ctx = F.fpic_init_metric(1.0, A)
+    F.fpic_set_grid(ctx, g)
+    d, q, w = I.thermal_draws(n, g, 1.02 * I.horizon(1.0, A), 49.0, THETA_T, seed=2, qm=QM)
+    z = O.seed_fido(1.0, A, d)
+    H0, _, D0 = O.hamiltonian(1.0, A, B0, z, q)
+    fd = fields_dev(Fo)
+    prm = F.push_params(DT, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=THR, r_max=float(g.rn[-1]), B0pot=B0)
+    p = make_particles(z, q, H0, D0, H0.copy())
+    from paper_2602_07452_gb300 import autotune
+    autotune.tune_imr_blocks(ctx, p, fd, prm, reps=1)
+    st = F.fpic_push(ctx, p, fd, prm, stats=True)
+    assert 0.05 < st["n_implicit"] / st["n_alive_before"] < 0.6
+    zg, Hg, ag, sg, ig, cg = to_np(p)
+    rng = np.random.default_rng(7)
+    idx = np.sort(rng.choice(n, 4000, replace=False))
+    po = O.push_params(a=A, dt=DT, scheme=O.HYB1, implicit_kind=O.IMR, thr=THR, r_max=g.rn[-1], B0pot=B0,
+                       field_kind=O.FIELD_GRID)
+    zo = np.ascontiguousarray(z[idx]); Ho = H0[idx].copy(); ao = np.ones(len(idx), np.uint8)
+    O.push(po, zo, q[idx], H0[idx], D0[idx], Ho, ao, g, Fo)
+    # scheme choice: the oracle's Hyb1 statistic of each sampled particle
+    pr = O.push_params(a=A, dt=DT, scheme=O.RK4, r_max=g.rn[-1], B0pot=B0, field_kind=O.FIELD_GRID)
+    zr = np.ascontiguousarray(z[idx]); Hr = H0[idx].copy()
+    O.push(pr, zr, q[idx], H0[idx], D0[idx], Hr, np.ones(len(idx), np.uint8), g, Fo)
+    stat = np.abs(Hr - H0[idx]) / D0[idx] / DT
+    near = np.abs(stat - THR) < 1e-9 * THR
+    imp = stat >= THR
+    assert np.array_equal(sg[idx][~near], imp[~near].astype(np.uint8))
+    ok = ~near & (ao == ag[idx])
+    assert ok.mean() > 0.99
+    live = ok & (ao == 1)
+    err = (np.abs(zg[idx] - zo) / (np.abs(zo) + 1.0)).max(axis=1)
+    assert err[live].max() <= 1e-12, err[live].max()
+    assert np.array_equal(cg[idx][live], O.cell_index(g, zo[live, 0], zo[live, 1]).astype(np.uint32))
+
+
+def test_fullsize_deposit_sampled_nodes():
+    cuda_or_skip()
+    F = fpic()
+    a, N, ppc = 0.99, 1024, 64
+    g = I.wald_grid(N, a)
+    ctx = F.fpic_init_metric(1.0, a)
+    F.fpic_set_grid(ctx, g)
+    d, q, w = I.cell_fill_draws(g, ppc, 0.5, seed=3, qm=QM, r_lo=1.02 * I.horizon(1.0, a))
+    z = O.seed_fido(1.0, a, d)
+    del d
+    n = len(q)
+    w = np.full(n, 1e-6)
+    p = make_particles(z, q, w=w)
+    out = [t.cpu().numpy() for t in F.fpic_deposit(ctx, p, g.size)]
+    del p
+    # integer cell of every particle (the oracle's), bucketed once, to pick
+    # the particles of each sampled node's 4 x 4-cell neighbourhood
+    key = (np.searchsorted(g.rn, z[:, 0], side="right") - 1) * g.Nth + \
+          (np.searchsorted(g.tn, z[:, 1], side="right") - 1)
+    order = np.argsort(key, kind="stable")
+    start = np.searchsorted(key[order], np.arange(g.Nr * g.Nth + 1))
+    rng = np.random.default_rng(11)
+    i_lo = int(np.searchsorted(g.rn, 1.02 * I.horizon(1.0, a))) + 3
+    nodes = [(int(rng.integers(i_lo, g.Nr - 3)), int(rng.integers(3, g.Nth - 3))) for _ in range(40)]
+    for (i, j) in nodes:
+        sel = np.concatenate([order[start[ci * g.Nth + j - 2]:start[ci * g.Nth + j + 2]]
+                              for ci in range(i - 2, i + 2)])
+        ro = P.deposit(1.0, a, g, z[sel], q[sel], w[sel])
+        sc = P.deposit(1.0, a, g, z[sel], np.abs(q[sel]), w[sel])[0]
+        o = i * g.ld + j
+        scale = sc[o]
+        assert scale > 0
+        for k in range(4):
+            assert abs(out[k][o] - ro[k][o]) <= 1e-10 * scale, (i, j, k, out[k][o], ro[k][o], scale)
