@@ -282,6 +282,7 @@ def run_gpu(args, ws, rank, local):
     tune_ms = autotune.tune_imr_blocks(ctx, p, fields, prm_t)
     learned = None
     train_info = None
+    learned_bps, tune_lrn = None, {}
     if not args.no_learned:
         # the network learns from the plain pusher's own steps (untimed)
         from paper_2602_07452_gb300 import learned as L
@@ -297,6 +298,12 @@ def run_gpu(args, ws, rank, local):
                       "loss_first_last": [hist[0][1], hist[-1][1]], "seconds": round(time.perf_counter() - t0, 1)}
         del X, T, S
         learned = (net, cfg)
+        # the learned push's own launch shape of the implicit solver
+        plain_bps = F.fpic_get_tuning(ctx, F.FPIC_TUNE_IMR_BLOCKS_PER_SM)
+        tune_lrn = autotune.tune_imr_blocks(ctx, p, fields, prm_t,
+                                            push=lambda c, q, f, m: F.fpic_push_learned(c, net, q, f, m, cfg))
+        learned_bps = F.fpic_get_tuning(ctx, F.FPIC_TUNE_IMR_BLOCKS_PER_SM)
+        F.fpic_set_tuning(ctx, F.FPIC_TUNE_IMR_BLOCKS_PER_SM, plain_bps)
         for _ in range(2):
             snap0 = _snapshot(p)
             F.fpic_push_learned(ctx, net, p, fields, prm, cfg)
@@ -320,6 +327,7 @@ def run_gpu(args, ws, rank, local):
         after_plain = _snapshot(p)
         _restore(p, snap)
         torch.cuda.synchronize()
+        F.fpic_set_tuning(ctx, F.FPIC_TUNE_IMR_BLOCKS_PER_SM, learned_bps)
         lrn = _timed(F, ctx, p, fields, prm, ev, args.steps, flush, learned)
         lrn["max_dH"] = _max_dH(F, ctx, p)
         if learned[1].mode == F.FPIC_LEARN_CORRECT:
@@ -330,6 +338,7 @@ def run_gpu(args, ws, rank, local):
             torch.cuda.synchronize()
             lead = _timed(F, ctx, p, fields, prm, ev, args.steps, flush, (net0, learned[1]))
             lead["max_dH"] = _max_dH(F, ctx, p)
+        F.fpic_set_tuning(ctx, F.FPIC_TUNE_IMR_BLOCKS_PER_SM, plain_bps)
         _restore(p, after_plain)
     # max over ranks of the device time, sum of the work
     T, W = aggregate(plain["t_step"], plain["psteps"], device)
@@ -392,6 +401,8 @@ def run_gpu(args, ws, rank, local):
             "rhs_evals_per_particle_step": lrn["evals"] / lp, "max_dH_over_D0": lrn["max_dH"],
             "same_start_state_as_plain": True, "form": args.learned_form,
             "restart_after": args.learned_restart,
+            "imr_blocks_per_sm": learned_bps,
+            "autotune_ms_per_push": {str(k): round(v, 4) for k, v in tune_lrn.items()},
             "inference_ms_per_step": 1e3 * lrn["t_inf"] / args.steps,
             **({"p_skip": 0.7} if args.learned_form == "skip" else {}), "training": train_info,
             "gpu_launches": lrn["launches"],
