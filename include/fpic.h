@@ -215,7 +215,7 @@ int fpic_push_host(fpic_ctx *ctx, fpic_particles *host_p, const double *const fi
  * no context (M, a given directly), calls no cudaMalloc, cudaFree or other
  * allocating routine, and keeps its scratch (implicit guesses, queue of
  * rejected particles, counters) in one file-scope device array of fixed
- * size, FPIC_NOALLOC_MAX_PARTICLES * 68 + 256 bytes (about 4.5 MB), that
+ * size, FPIC_NOALLOC_MAX_PARTICLES * 72 + 256 bytes (about 4.7 MB), that
  * every device which loads the library holds until the process exits.
  *   p, prm, stats, stream : as fpic_push (no fields; prm->guess must be
  *     NULL).  Neutral and charged particles move on geodesics of the Kerr

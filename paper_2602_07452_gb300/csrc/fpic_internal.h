@@ -51,7 +51,8 @@ struct fpic_ctx {
 namespace fpic {
 
 enum { CNT_QUEUE = 0, CNT_HEAD = 1, CNT_ITERS = 2, CNT_NOTCONV = 3, CNT_REMOVED = 4,
-       CNT_ALIVE = 5, CNT_EVALS = 6, CNT_ERR = 7, CNT_WORK = 8, CNT_SKIP = 9, CNT_N = 10 };
+       CNT_ALIVE = 5, CNT_EVALS = 6, CNT_ERR = 7, CNT_WORK = 8, CNT_SKIP = 9, CNT_PRIO = 10,
+       CNT_NORM = 11, CNT_N = 12 };
 
 int set_error(int code, const char* fmt, ...);
 int check_cuda(cudaError_t e, const char* what);

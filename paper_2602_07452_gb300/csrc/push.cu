@@ -49,6 +49,7 @@ struct PushK {
     double* guess;          // 6 x n (SoA) implicit initial guesses, then the implicit results
     double* sc0;            // 2 x n: sin, cos of th^n of the implicit particles
     uint32_t* queue;        // indices of particles for the implicit solver
+    uint32_t* order;        // nullable: processing order of the queue slots (k_order)
     long long* cnt;
     const float* learned;   // n x 16 MLP outputs (nullable)
     // learned / sampling extensions
@@ -274,6 +275,40 @@ __device__ __forceinline__ bool conv6(const double a[6], const double b[6], doub
     return ok;
 }
 
+// Processing order of the implicit queue: slots of particles within
+// AXIS_PRIORITY_TH of the polar axis first.  Near the axis the u_ph^2 /
+// sin^3 th terms make the Picard iteration contract slowly or cycle (the
+// solves that run to max_iter are found there), so starting them first lets
+// their long solves overlap the bulk instead of trailing it.  The order only
+// decides which lane takes which particle; every particle's arithmetic, and
+// hence its result, is the same.
+constexpr double AXIS_PRIORITY_TH = 0.01;
+__global__ void k_order(PushK k)
+{
+    const long long qn = k.cnt[CNT_QUEUE];
+    for (long long slot = blockIdx.x * (long long)blockDim.x + threadIdx.x; slot < qn;
+         slot += (long long)gridDim.x * blockDim.x) {
+        const double th = k.P.th[k.queue[slot]];
+        const bool prio = th < AXIS_PRIORITY_TH || th > M_PI - AXIS_PRIORITY_TH;
+        const unsigned act = __activemask();
+        const unsigned pm = __ballot_sync(act, prio);
+        const int leader = __ffs(act) - 1;
+        unsigned long long bp = 0, bn = 0;
+        if ((int)(threadIdx.x & 31) == leader) {
+            if (pm) bp = atomicAdd((unsigned long long*)&k.cnt[CNT_PRIO], (unsigned long long)__popc(pm));
+            const unsigned nn = __popc(act & ~pm);
+            if (nn) bn = atomicAdd((unsigned long long*)&k.cnt[CNT_NORM], (unsigned long long)nn);
+        }
+        bp = __shfl_sync(act, bp, leader);
+        bn = __shfl_sync(act, bn, leader);
+        const unsigned below = lanemask_lt();
+        // priority slots fill the order from the front, the others from the back
+        const long long pos = prio ? (long long)(bp + __popc(pm & below))
+                                   : qn - 1 - (long long)(bn + __popc(act & ~pm & below));
+        k.order[pos] = (uint32_t)slot;
+    }
+}
+
 // Persistent lane-refilling implicit-midpoint solver (Sec. 2.2.2):
 // z^[k] = z^n + dt F((z^n + z^[k-1]) / 2) until two iterates agree to tol.
 // all_mode: the queue is every particle (pure IMR, guess z^n); otherwise
@@ -311,13 +346,14 @@ __global__ void __launch_bounds__(128, 4) k_imr(PushK k, int all_mode)
             if (need) {
                 const long long idx = (long long)(base + __popc(nm & lanemask_lt()));
                 if (idx < qn) {
-                    const long long q = all_mode ? idx : (long long)k.queue[idx];
+                    const long long slot = (!all_mode && k.order) ? (long long)k.order[idx] : idx;
+                    const long long q = all_mode ? idx : (long long)k.queue[slot];
                     if (all_mode && !k.P.alive[q]) {
                         k.P.scheme[q] = 0;
                         k.P.iters[q] = 0;
                     } else {
                         p = q;
-                        qi = idx;
+                        qi = slot;
                         again = RESTART != 0;
                         load_state(k.P, p, z0);
                         if (all_mode) {
@@ -331,7 +367,7 @@ __global__ void __launch_bounds__(128, 4) k_imr(PushK k, int all_mode)
                             c0 = k.sc0[k.n + p];
 #pragma unroll
                             for (int i = 0; i < 6; ++i)
-                                zk[i] = RESTART ? k.stg[(size_t)(STG_GUESS + i) * k.n + idx]
+                                zk[i] = RESTART ? k.stg[(size_t)(STG_GUESS + i) * k.n + slot]
                                                 : k.guess[(size_t)i * k.n + p];
                         }
                         qm = k.P.qm[p];
@@ -630,7 +666,7 @@ static int push_core(fpic_ctx* c, fpic_particles* p, const double* const fields[
     const bool has_fields = fields != nullptr;
     const long long n = p->n;
     FPIC_CUDA(cudaSetDevice(c->device));
-    const size_t need = (size_t)n * (8 * sizeof(double) + sizeof(uint32_t)) + 256;
+    const size_t need = (size_t)n * (8 * sizeof(double) + 2 * sizeof(uint32_t)) + 256;
     int rc = ensure_scratch(c, need);
     if (rc) return rc;
     PushK k{};
@@ -654,6 +690,7 @@ static int push_core(fpic_ctx* c, fpic_particles* p, const double* const fields[
     k.guess = (double*)c->d_scratch;
     k.sc0 = k.guess + (size_t)n * 6;
     k.queue = (uint32_t*)((char*)c->d_scratch + (size_t)n * 8 * sizeof(double));
+    k.order = k.queue + n;
     k.cnt = c->d_cnt;
     k.learned = nullptr;
     FPIC_CUDA(cudaMemsetAsync(c->d_cnt, 0, CNT_N * sizeof(long long), s));
@@ -696,6 +733,7 @@ static int push_core(fpic_ctx* c, fpic_particles* p, const double* const fields[
     } else if (prm->scheme == FPIC_HAM) {
         k_dg<<<nb, TB, 0, s>>>(k, 1);
     } else if (prm->scheme >= FPIC_HYB1 && prm->implicit == FPIC_IMR) {
+        k_order<<<persist, 256, 0, s>>>(k);
         k_imr<0><<<imr_grid, TB, 0, s>>>(k, 0);
         k_imr_finish<<<persist, 256, 0, s>>>(k, 0);
     } else if (prm->scheme >= FPIC_HYB1) {
@@ -796,7 +834,7 @@ namespace fpic {
 
 constexpr long long kNoAllocMax = FPIC_NOALLOC_MAX_PARTICLES;
 constexpr size_t kNoAllocCountersBytes = 256;   // CNT_N counters, padded for alignment
-constexpr size_t kNoAllocBytes = kNoAllocCountersBytes + (size_t)kNoAllocMax * (8 * sizeof(double) + sizeof(uint32_t));
+constexpr size_t kNoAllocBytes = kNoAllocCountersBytes + (size_t)kNoAllocMax * (8 * sizeof(double) + 2 * sizeof(uint32_t));
 
 // Shared by every call on a device and held until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
@@ -870,6 +908,7 @@ extern "C" int fpic_push_noalloc(double M, double a, fpic_particles* p, const fp
     k.guess = (double*)(base + kNoAllocCountersBytes);
     k.sc0 = k.guess + (size_t)n * 6;
     k.queue = (uint32_t*)(base + kNoAllocCountersBytes + (size_t)n * 8 * sizeof(double));
+    k.order = k.queue + n;
     k.learned = nullptr;
     // the counters (queue length and head among them) must start at zero
     FPIC_CUDA(cudaMemsetAsync(k.cnt, 0, CNT_N * sizeof(long long), s));
@@ -895,6 +934,7 @@ extern "C" int fpic_push_noalloc(double M, double a, fpic_particles* p, const fp
     } else if (prm->scheme == FPIC_HAM) {
         k_dg<<<nb, TB, 0, s>>>(k, 1);
     } else if (prm->scheme >= FPIC_HYB1 && prm->implicit == FPIC_IMR) {
+        k_order<<<persist, 256, 0, s>>>(k);
         k_imr<0><<<persist / 2, TB, 0, s>>>(k, 0);
         k_imr_finish<<<persist, 256, 0, s>>>(k, 0);
     } else if (prm->scheme >= FPIC_HYB1) {
@@ -1065,12 +1105,12 @@ static void fill_pushk(PushK& k, fpic_ctx* c, fpic_particles* p, const double* c
     k.cnt = c->d_cnt;
 }
 
-// scratch: guess 6n doubles | sc0 2n doubles | stg STG_ROWS n doubles | queue n | work n | X 16n floats |
+// scratch: guess 6n doubles | sc0 2n doubles | stg STG_ROWS n doubles | queue n | work n | order n | X 16n floats |
 // Y 16n floats | featS 16n floats | 6 FP32 field copies
 static int learned_scratch(fpic_ctx* c, long long n, PushK& k, float** X, float** Y, float** f32)
 {
     const size_t fsz = c->has_grid ? 6 * (size_t)(c->Nr + 1) * c->ld : 0;
-    const size_t need = (size_t)n * ((8 + STG_ROWS) * sizeof(double) + 2 * sizeof(uint32_t) + 48 * sizeof(float)) +
+    const size_t need = (size_t)n * ((8 + STG_ROWS) * sizeof(double) + 3 * sizeof(uint32_t) + 48 * sizeof(float)) +
                         fsz * sizeof(float) + 2048;
     int rc = ensure_scratch(c, need);
     if (rc) return rc;
@@ -1084,6 +1124,8 @@ static int learned_scratch(fpic_ctx* c, long long n, PushK& k, float** X, float*
     k.queue = (uint32_t*)b;
     b += (size_t)n * sizeof(uint32_t);
     k.work = (uint32_t*)b;
+    b += (size_t)n * sizeof(uint32_t);
+    k.order = (uint32_t*)b;
     b += (size_t)n * sizeof(uint32_t);
     b = (char*)(((uintptr_t)b + 255) & ~(uintptr_t)255);
     *X = (float*)b;
@@ -1327,6 +1369,7 @@ extern "C" int fpic_learn_sample(fpic_ctx* c, fpic_particles* p, const double* c
         FPIC_CUDA(cudaMemsetAsync(T, 0, (size_t)n * 16 * sizeof(float), s));
         FPIC_CUDA(cudaMemsetAsync(S, 0, (size_t)n * sizeof(float), s));
         set_corrector(k, cfg, X);
+        k.order = nullptr;
         k_explicit<2><<<nb, 128, 0, s>>>(k);
         k_trial_feat<<<(unsigned)c->sm_count * 8u, 256, 0, s>>>(k);
         k_imr<0><<<(unsigned)c->sm_count * (unsigned)c->imr_blocks_per_sm, 128, 0, s>>>(k, 0);
@@ -1334,6 +1377,7 @@ extern "C" int fpic_learn_sample(fpic_ctx* c, fpic_particles* p, const double* c
         return FPIC_OK;
     }
     k.featS = nullptr;
+    k.order = nullptr;
     FeatK f = make_featk(c, p, fields, prm->dt, cfg, X, f32, s);
     f.T = T;
     f.S = S;
@@ -1412,6 +1456,7 @@ extern "C" int fpic_push_learned(fpic_ctx* c, fpic_mlp* m, fpic_particles* p, co
         k.work = nullptr;
     }
     const unsigned imr_grid = (unsigned)c->sm_count * (unsigned)c->imr_blocks_per_sm;
+    k_order<<<persist, 256, 0, s>>>(k);
     if (correct) k_imr<1><<<imr_grid, 128, 0, s>>>(k, 0);
     else k_imr<0><<<imr_grid, 128, 0, s>>>(k, 0);
     k_imr_finish<<<persist, 256, 0, s>>>(k, 0);
