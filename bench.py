@@ -250,7 +250,7 @@ def _timed(F, ctx, p, fields, prm, ev, steps, flush, learned=None):
         out["notconv"] += st["n_notconv"]
         out["fl_ex"] += st["n_alive_before"] * FLOP_RK4_TRIAL
         out["fl_im"] += st["n_iter_total"] * FLOP_IMR_ITER + st["n_implicit"] * FLOP_IMR_FINAL
-        out["launches"] += 4 if learned is None else (8 if learned[1].mode == F.FPIC_LEARN_SKIP else 5)
+        out["launches"] += 5 if learned is None else (9 if learned[1].mode == F.FPIC_LEARN_SKIP else 6)
     return out
 
 
@@ -391,6 +391,9 @@ def run_gpu(args, ws, rank, local):
         "clocks": clk,
         "gpu_launches": plain["launches"],
     }
+    line["config"]["explicit_ms_per_step"] = 1e3 * plain["t_ex"] / args.steps
+    line["config"]["implicit_ms_per_step"] = 1e3 * plain["t_im"] / args.steps
+    line["config"]["imr_not_converged"] = plain["notconv"]
     if lrn is not None:
         lp = max(lrn["psteps"], 1)
         line["learned"] = {
@@ -410,9 +413,6 @@ def run_gpu(args, ws, rank, local):
             "implicit_ms_per_step": 1e3 * lrn["t_im"] / args.steps,
             "imr_not_converged": lrn["notconv"],
         }
-        line["config"]["explicit_ms_per_step"] = 1e3 * plain["t_ex"] / args.steps
-        line["config"]["implicit_ms_per_step"] = 1e3 * plain["t_im"] / args.steps
-        line["config"]["imr_not_converged"] = plain["notconv"]
         if lead is not None:
             lp0 = max(lead["psteps"], 1)
             line["learned"]["leading_order_only"] = {

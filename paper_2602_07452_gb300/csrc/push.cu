@@ -41,6 +41,8 @@ struct RunK {
 
 struct PushK {
     RunK run;
+    const RunK* runs;       // batched push: run table (nruns > 0), particle ranges [begin, end)
+    int nruns;
     double dt, thr, tol, dg_eps;
     int scheme, max_iter;
     long long n;
@@ -66,6 +68,18 @@ struct PushK {
     float oscale[6];        // corrector outputs 0-5 are residual / (s_i oscale_i)
     int restart_after;      // corrector: restart from the trial after this many iterations (0: never)
 };
+
+// Run of particle p in a batched push (runs sorted by begin).
+__device__ __forceinline__ int run_of(const RunK* __restrict__ runs, int nruns, long long p)
+{
+    int lo = 0, hi = nruns - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (runs[mid].begin <= p) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
 
 __device__ __forceinline__ void load_state(const PartDev& P, long long p, double z[6])
 {
@@ -176,8 +190,8 @@ __device__ __forceinline__ void trial_store(const PushK& k, unsigned long long i
 // hybrid that also parks the RK4 slopes of each rejected particle
 // (corrector form of the learned guess); k1, k2 wait in shared memory
 // (12 KB per block) rather than in registers across the later stages.
-template <int MODE>
-__global__ void __launch_bounds__(128) k_explicit(PushK k)
+template <int MODE, bool BATCHED = false>
+__global__ void __launch_bounds__(128) k_explicit(const __grid_constant__ PushK k)
 {
     __shared__ double sk[MODE == 2 ? 12 : 1][128];
     const long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -193,14 +207,15 @@ __global__ void __launch_bounds__(128) k_explicit(PushK k)
         k.P.iters[p] = 0;
         return;
     }
+    const RunK& R = BATCHED ? k.runs[run_of(k.runs, k.nruns, p)] : k.run;
     double z0[6], kk[6], acc[6], y[6];
     load_state(k.P, p, z0);
     const double qm = k.P.qm[p];
-    const bool em = k.run.has_fields && qm != 0.0;
+    const bool em = R.has_fields && qm != 0.0;
     const double dt = k.dt, hdt = 0.5 * k.dt;
     double Hd, s0, c0, sn, cn;
     sincos(z0[1], &s0, &c0);
-    F_at_sc(k.run, z0, s0, c0, qm, em, kk, Hd);
+    F_at_sc(R, z0, s0, c0, qm, em, kk, Hd);
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
         acc[i] = kk[i];
@@ -208,7 +223,7 @@ __global__ void __launch_bounds__(128) k_explicit(PushK k)
         if (MODE == 2) sk[i][threadIdx.x] = kk[i];
     }
     sincos_near(z0[1], s0, c0, y[1], sn, cn);
-    F_at_sc(k.run, y, sn, cn, qm, em, kk, Hd);
+    F_at_sc(R, y, sn, cn, qm, em, kk, Hd);
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
         acc[i] = fma(2.0, kk[i], acc[i]);
@@ -216,16 +231,16 @@ __global__ void __launch_bounds__(128) k_explicit(PushK k)
         if (MODE == 2) sk[6 + i][threadIdx.x] = kk[i];
     }
     sincos_near(z0[1], s0, c0, y[1], sn, cn);
-    F_at_sc(k.run, y, sn, cn, qm, em, kk, Hd);
+    F_at_sc(R, y, sn, cn, qm, em, kk, Hd);
 #pragma unroll
     for (int i = 0; i < 6; ++i) { acc[i] = fma(2.0, kk[i], acc[i]); y[i] = fma(dt, kk[i], z0[i]); }
     sincos_near(z0[1], s0, c0, y[1], sn, cn);
-    F_at_sc(k.run, y, sn, cn, qm, em, kk, Hd);
+    F_at_sc(R, y, sn, cn, qm, em, kk, Hd);
     const double d6 = dt / 6.0;
 #pragma unroll
     for (int i = 0; i < 6; ++i) y[i] = fma(d6, acc[i] + kk[i], z0[i]);
     sincos_near(z0[1], s0, c0, y[1], sn, cn);
-    const double H1 = eval_H_sc(k.run.bh, y, sn, cn, qm, k.run.B0pot);
+    const double H1 = eval_H_sc(R.bh, y, sn, cn, qm, R.B0pot);
     bool accept = true;
     if (MODE >= 1) {
         const double H0 = k.P.H0[p], D0 = k.P.D0[p];
@@ -244,7 +259,7 @@ __global__ void __launch_bounds__(128) k_explicit(PushK k)
     }
     const unsigned act = __activemask();
     const unsigned rej = __ballot_sync(act, !accept);
-    if (accept && !finish(k.run, k.P, p, y, H1, 0, 0))
+    if (accept && !finish(R, k.P, p, y, H1, 0, 0))
         atomicAdd((unsigned long long*)&k.cnt[CNT_REMOVED], 1ull);
     if (rej) {
         const int leader = __ffs(act) - 1;
@@ -321,12 +336,13 @@ __global__ void k_order(PushK k)
 // corrected guess of the queue slot (stg); with k.restart_after > 0, a solve
 // that has not converged after that many iterations from it restarts once,
 // with the full max_iter budget, from the trial in stg.
-template <int RESTART>
-__global__ void __launch_bounds__(128, 4) k_imr(PushK k, int all_mode)
+template <int RESTART, bool BATCHED = false>
+__global__ void __launch_bounds__(128, 4) k_imr(const __grid_constant__ PushK k, int all_mode)
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const long long qn = all_mode ? k.n : k.cnt[CNT_QUEUE];
+    const RunK* R = &k.run;
     long long p = -1, qi = 0;
     bool exhausted = false, again = false;
     double z0[6], zk[6];
@@ -354,6 +370,7 @@ __global__ void __launch_bounds__(128, 4) k_imr(PushK k, int all_mode)
                     } else {
                         p = q;
                         qi = slot;
+                        if (BATCHED) R = k.runs + run_of(k.runs, k.nruns, p);
                         again = RESTART != 0;
                         load_state(k.P, p, z0);
                         if (all_mode) {
@@ -371,7 +388,7 @@ __global__ void __launch_bounds__(128, 4) k_imr(PushK k, int all_mode)
                                                 : k.guess[(size_t)i * k.n + p];
                         }
                         qm = k.P.qm[p];
-                        em = k.run.has_fields && qm != 0.0;
+                        em = R->has_fields && qm != 0.0;
                         it = 0;
                     }
                 } else {
@@ -390,7 +407,7 @@ __global__ void __launch_bounds__(128, 4) k_imr(PushK k, int all_mode)
             for (int i = 0; i < 6; ++i) y[i] = 0.5 * (z0[i] + zk[i]);
             double sy, cy;
             sincos_near(z0[1], s0, c0, y[1], sy, cy);
-            F_at_sc(k.run, y, sy, cy, qm, em, f, H);
+            F_at_sc(*R, y, sy, cy, qm, em, f, H);
             ++n_ev;
             double zn[6];
 #pragma unroll
@@ -446,7 +463,8 @@ __global__ void __launch_bounds__(128, 4) k_imr(PushK k, int all_mode)
 // After k_imr: H at each converged implicit step (sin/cos of th^{n+1} by
 // angle addition from th^n) and the write-back with the particle
 // boundaries of Sec. 2.5.
-__global__ void __launch_bounds__(256) k_imr_finish(PushK k, int all_mode)
+template <bool BATCHED = false>
+__global__ void __launch_bounds__(256) k_imr_finish(const __grid_constant__ PushK k, int all_mode)
 {
     const long long qn = all_mode ? k.n : k.cnt[CNT_QUEUE];
     long long n_rm = 0;
@@ -459,8 +477,9 @@ __global__ void __launch_bounds__(256) k_imr_finish(PushK k, int all_mode)
         for (int i = 0; i < 6; ++i) z[i] = k.guess[(size_t)i * k.n + p];
         double sn, cn;
         sincos_near(k.P.th[p], k.sc0[p], k.sc0[k.n + p], z[1], sn, cn);
-        const double H = eval_H_sc(k.run.bh, z, sn, cn, k.P.qm[p], k.run.B0pot);
-        if (!finish(k.run, k.P, p, z, H, 1, k.P.iters[p])) ++n_rm;
+        const RunK& R = BATCHED ? k.runs[run_of(k.runs, k.nruns, p)] : k.run;
+        const double H = eval_H_sc(R.bh, z, sn, cn, k.P.qm[p], R.B0pot);
+        if (!finish(R, k.P, p, z, H, 1, k.P.iters[p])) ++n_rm;
     }
     warp_add(&k.cnt[CNT_REMOVED], n_rm, 0xffffffffu);
 }
@@ -729,13 +748,13 @@ static int push_core(fpic_ctx* c, fpic_particles* p, const double* const fields[
     }
     if (prm->scheme == FPIC_IMR) {
         k_imr<0><<<imr_grid, TB, 0, s>>>(k, 1);
-        k_imr_finish<<<persist, 256, 0, s>>>(k, 1);
+        k_imr_finish<><<<persist, 256, 0, s>>>(k, 1);
     } else if (prm->scheme == FPIC_HAM) {
         k_dg<<<nb, TB, 0, s>>>(k, 1);
     } else if (prm->scheme >= FPIC_HYB1 && prm->implicit == FPIC_IMR) {
         k_order<<<persist, 256, 0, s>>>(k);
         k_imr<0><<<imr_grid, TB, 0, s>>>(k, 0);
-        k_imr_finish<<<persist, 256, 0, s>>>(k, 0);
+        k_imr_finish<><<<persist, 256, 0, s>>>(k, 0);
     } else if (prm->scheme >= FPIC_HYB1) {
         k_dg<<<nb, TB, 0, s>>>(k, 0);
     }
@@ -930,13 +949,13 @@ extern "C" int fpic_push_noalloc(double M, double a, fpic_particles* p, const fp
     }
     if (prm->scheme == FPIC_IMR) {
         k_imr<0><<<persist / 2, TB, 0, s>>>(k, 1);
-        k_imr_finish<<<persist, 256, 0, s>>>(k, 1);
+        k_imr_finish<><<<persist, 256, 0, s>>>(k, 1);
     } else if (prm->scheme == FPIC_HAM) {
         k_dg<<<nb, TB, 0, s>>>(k, 1);
     } else if (prm->scheme >= FPIC_HYB1 && prm->implicit == FPIC_IMR) {
         k_order<<<persist, 256, 0, s>>>(k);
         k_imr<0><<<persist / 2, TB, 0, s>>>(k, 0);
-        k_imr_finish<<<persist, 256, 0, s>>>(k, 0);
+        k_imr_finish<><<<persist, 256, 0, s>>>(k, 0);
     } else if (prm->scheme >= FPIC_HYB1) {
         k_dg<<<nb, TB, 0, s>>>(k, 0);
     }
@@ -1459,7 +1478,7 @@ extern "C" int fpic_push_learned(fpic_ctx* c, fpic_mlp* m, fpic_particles* p, co
     k_order<<<persist, 256, 0, s>>>(k);
     if (correct) k_imr<1><<<imr_grid, 128, 0, s>>>(k, 0);
     else k_imr<0><<<imr_grid, 128, 0, s>>>(k, 0);
-    k_imr_finish<<<persist, 256, 0, s>>>(k, 0);
+    k_imr_finish<><<<persist, 256, 0, s>>>(k, 0);
     if (ev) FPIC_CUDA(cudaEventRecord(ev[3], s));
     FPIC_CUDA(cudaGetLastError());
     if (stats) {
@@ -1483,181 +1502,6 @@ extern "C" int fpic_push_learned(fpic_ctx* c, fpic_mlp* m, fpic_particles* p, co
 // range) in one explicit launch and one persistent implicit launch.
 // ---------------------------------------------------------------------------
 namespace fpic {
-
-struct BatchK {
-    const RunK* runs;
-    int nruns;
-    PushK k;        // shared step parameters (its run member is unused)
-};
-
-__device__ __forceinline__ int run_of(const RunK* __restrict__ runs, int nruns, long long p)
-{
-    int lo = 0, hi = nruns - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (runs[mid].begin <= p) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
-__global__ void __launch_bounds__(128) k_explicit_batched(const __grid_constant__ BatchK B)
-{
-    const PushK& k = B.k;
-    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (p >= k.n) return;
-    if (!k.P.alive[p]) {
-        k.P.scheme[p] = 0;
-        k.P.iters[p] = 0;
-        return;
-    }
-    const RunK& R = B.runs[run_of(B.runs, B.nruns, p)];
-    double z0[6], kk[6], acc[6], y[6];
-    load_state(k.P, p, z0);
-    const double qm = k.P.qm[p];
-    const bool em = R.has_fields && qm != 0.0;
-    const double dt = k.dt, hdt = 0.5 * k.dt;
-    double Hd, s0, c0, sn, cn;
-    sincos(z0[1], &s0, &c0);
-    F_at_sc(R, z0, s0, c0, qm, em, kk, Hd);
-#pragma unroll
-    for (int i = 0; i < 6; ++i) { acc[i] = kk[i]; y[i] = fma(hdt, kk[i], z0[i]); }
-    sincos_near(z0[1], s0, c0, y[1], sn, cn);
-    F_at_sc(R, y, sn, cn, qm, em, kk, Hd);
-#pragma unroll
-    for (int i = 0; i < 6; ++i) { acc[i] = fma(2.0, kk[i], acc[i]); y[i] = fma(hdt, kk[i], z0[i]); }
-    sincos_near(z0[1], s0, c0, y[1], sn, cn);
-    F_at_sc(R, y, sn, cn, qm, em, kk, Hd);
-#pragma unroll
-    for (int i = 0; i < 6; ++i) { acc[i] = fma(2.0, kk[i], acc[i]); y[i] = fma(dt, kk[i], z0[i]); }
-    sincos_near(z0[1], s0, c0, y[1], sn, cn);
-    F_at_sc(R, y, sn, cn, qm, em, kk, Hd);
-    const double d6 = dt / 6.0;
-#pragma unroll
-    for (int i = 0; i < 6; ++i) y[i] = fma(d6, acc[i] + kk[i], z0[i]);
-    sincos_near(z0[1], s0, c0, y[1], sn, cn);
-    const double H1 = eval_H_sc(R.bh, y, sn, cn, qm, R.B0pot);
-    bool accept = true;
-    if (k.scheme >= FPIC_HYB1) {
-        const double H0 = k.P.H0[p], D0 = k.P.D0[p];
-        const double Ht1 = fabs(H1 - H0) / D0;
-        if (k.scheme == FPIC_HYB2) {
-            accept = Ht1 < k.thr;
-        } else {
-            const double Htn = fabs(k.P.Hn[p] - H0) / D0;
-            accept = (Ht1 - Htn) / dt < k.thr;
-        }
-    }
-    const unsigned act = __activemask();
-    const unsigned rej = __ballot_sync(act, !accept);
-    if (accept && !finish(R, k.P, p, y, H1, 0, 0))
-        atomicAdd((unsigned long long*)&k.cnt[CNT_REMOVED], 1ull);
-    if (rej) {
-        const int leader = __ffs(act) - 1;
-        unsigned long long base = 0;
-        if ((int)(threadIdx.x & 31) == leader)
-            base = atomicAdd((unsigned long long*)&k.cnt[CNT_QUEUE], (unsigned long long)__popc(rej));
-        base = __shfl_sync(act, base, leader);
-        if (!accept) {
-            const unsigned long long idx = base + __popc(rej & lanemask_lt());
-            k.queue[idx] = (uint32_t)p;
-#pragma unroll
-            for (int i = 0; i < 6; ++i) k.guess[(size_t)i * k.n + p] = y[i];
-        }
-    }
-}
-
-// Persistent lane-refilling IMR over the batch's queue; each lane carries
-// the run of its current particle.
-__global__ void __launch_bounds__(128) k_imr_batched(const __grid_constant__ BatchK B, int all_mode)
-{
-    const PushK& k = B.k;
-    const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const long long qn = all_mode ? k.n : k.cnt[CNT_QUEUE];
-    long long p = -1;
-    const RunK* R = B.runs;
-    bool exhausted = false, fin = false;
-    double z0[6], zk[6];
-    double qm = 0.0, s0 = 0.0, c0 = 1.0;
-    bool em = false;
-    int it = 0;
-    long long n_it = 0, n_nc = 0, n_ev = 0, n_rm = 0;
-    for (;;) {
-        const bool need = (p < 0) && !exhausted;
-        const unsigned nm = __ballot_sync(FULL, need);
-        if (nm) {
-            const int leader = __ffs(nm) - 1;
-            unsigned long long base = 0;
-            if (lane == leader)
-                base = atomicAdd((unsigned long long*)&k.cnt[CNT_HEAD], (unsigned long long)__popc(nm));
-            base = __shfl_sync(FULL, base, leader);
-            if (need) {
-                const long long idx = (long long)(base + __popc(nm & lanemask_lt()));
-                if (idx < qn) {
-                    const long long q = all_mode ? idx : (long long)k.queue[idx];
-                    if (all_mode && !k.P.alive[q]) {
-                        k.P.scheme[q] = 0;
-                        k.P.iters[q] = 0;
-                    } else {
-                        p = q;
-                        R = B.runs + run_of(B.runs, B.nruns, p);
-                        load_state(k.P, p, z0);
-#pragma unroll
-                        for (int i = 0; i < 6; ++i) zk[i] = all_mode ? z0[i] : k.guess[(size_t)i * k.n + p];
-                        qm = k.P.qm[p];
-                        em = R->has_fields && qm != 0.0;
-                        sincos(z0[1], &s0, &c0);
-                        it = 0;
-                        fin = false;
-                    }
-                } else {
-                    exhausted = true;
-                }
-            }
-        }
-        const unsigned busy = __ballot_sync(FULL, p >= 0);
-        if (!busy) {
-            if (!__ballot_sync(FULL, !exhausted)) break;
-            continue;
-        }
-        if (p >= 0) {
-            double y[6], f[6], H;
-            if (fin) {
-#pragma unroll
-                for (int i = 0; i < 6; ++i) y[i] = zk[i];
-            } else {
-#pragma unroll
-                for (int i = 0; i < 6; ++i) y[i] = 0.5 * (z0[i] + zk[i]);
-            }
-            double sy, cy;
-            sincos_near(z0[1], s0, c0, y[1], sy, cy);
-            F_at_sc(*R, y, sy, cy, qm, em, f, H);
-            ++n_ev;
-            if (!fin) {
-                double zn[6];
-#pragma unroll
-                for (int i = 0; i < 6; ++i) zn[i] = fma(k.dt, f[i], z0[i]);
-                const bool ok = conv6(zn, zk, k.tol);
-#pragma unroll
-                for (int i = 0; i < 6; ++i) zk[i] = zn[i];
-                ++it;
-                if (ok || it >= k.max_iter) {
-                    fin = true;
-                    if (!ok) ++n_nc;
-                }
-            } else {
-                if (!finish(*R, k.P, p, zk, H, 1, it)) ++n_rm;
-                n_it += it;
-                p = -1;
-            }
-        }
-    }
-    warp_add(&k.cnt[CNT_ITERS], n_it, FULL);
-    warp_add(&k.cnt[CNT_NOTCONV], n_nc, FULL);
-    warp_add(&k.cnt[CNT_EVALS], n_ev, FULL);
-    warp_add(&k.cnt[CNT_REMOVED], n_rm, FULL);
-}
 
 }  // namespace fpic
 
@@ -1700,7 +1544,8 @@ extern "C" int fpic_push_batched(const fpic_run* runs, int nruns, fpic_particles
         FPIC_CUDA(cudaMallocHost(&c->h_runs, sizeof(RunK) * nruns));
         c->runs_cap = nruns;
     }
-    int rc = ensure_scratch(c, (size_t)(n > 0 ? n : 1) * (6 * sizeof(double) + sizeof(uint32_t)) + 256);
+    const long long nn = n > 0 ? n : 1;
+    int rc = ensure_scratch(c, (size_t)nn * (8 * sizeof(double) + 2 * sizeof(uint32_t)) + 256);
     if (rc) return rc;
     std::vector<RunK> tab(nruns);
     for (int i = 0; i < nruns; ++i) {
@@ -1728,10 +1573,10 @@ extern "C" int fpic_push_batched(const fpic_run* runs, int nruns, fpic_particles
         memcpy(c->h_runs, tab.data(), sizeof(RunK) * nruns);
     }
     FPIC_CUDA(cudaMemcpyAsync(c->d_runs, c->h_runs, sizeof(RunK) * nruns, cudaMemcpyHostToDevice, s));
-    BatchK B{};
-    B.runs = (const RunK*)c->d_runs;
-    B.nruns = nruns;
-    PushK& k = B.k;
+    // the single-run kernels with a per-particle run lookup (BATCHED)
+    PushK k{};
+    k.runs = (const RunK*)c->d_runs;
+    k.nruns = nruns;
     k.dt = prm->dt;
     k.thr = prm->thr;
     k.tol = prm->tol;
@@ -1742,7 +1587,9 @@ extern "C" int fpic_push_batched(const fpic_run* runs, int nruns, fpic_particles
     k.P = PartDev{p->r, p->th, p->ph, p->ur, p->uth, p->uph, p->qm, p->H0, p->D0, p->Hn,
                   p->alive, p->scheme, p->iters, p->cell};
     k.guess = (double*)c->d_scratch;
-    k.queue = (uint32_t*)((char*)c->d_scratch + (size_t)(n > 0 ? n : 1) * 6 * sizeof(double));
+    k.sc0 = k.guess + (size_t)nn * 6;
+    k.queue = (uint32_t*)((char*)c->d_scratch + (size_t)nn * 8 * sizeof(double));
+    k.order = k.queue + nn;
     k.cnt = c->d_cnt;
     FPIC_CUDA(cudaMemsetAsync(c->d_cnt, 0, CNT_N * sizeof(long long), s));
     if (n == 0) {
@@ -1751,16 +1598,24 @@ extern "C" int fpic_push_batched(const fpic_run* runs, int nruns, fpic_particles
     }
     const unsigned nb = (unsigned)((n + 127) / 128);
     const unsigned persist = (unsigned)c->sm_count * 8u;
+    const unsigned imr_grid = (unsigned)c->sm_count * (unsigned)c->imr_blocks_per_sm;
     cudaEvent_t* ev = prm->events ? (cudaEvent_t*)prm->events : nullptr;
     if (stats) k_count_alive<<<persist, 256, 0, s>>>(k.P, n, c->d_cnt);
     if (ev) FPIC_CUDA(cudaEventRecord(ev[0], s));
-    if (prm->scheme != FPIC_IMR) k_explicit_batched<<<nb, 128, 0, s>>>(B);
+    if (prm->scheme == FPIC_RK4) k_explicit<0, true><<<nb, 128, 0, s>>>(k);
+    else if (prm->scheme >= FPIC_HYB1) k_explicit<1, true><<<nb, 128, 0, s>>>(k);
     if (ev) {
         FPIC_CUDA(cudaEventRecord(ev[1], s));
         FPIC_CUDA(cudaEventRecord(ev[2], s));
     }
-    if (prm->scheme == FPIC_IMR) k_imr_batched<<<persist, 128, 0, s>>>(B, 1);
-    else if (prm->scheme >= FPIC_HYB1) k_imr_batched<<<persist, 128, 0, s>>>(B, 0);
+    if (prm->scheme == FPIC_IMR) {
+        k_imr<0, true><<<imr_grid, 128, 0, s>>>(k, 1);
+        k_imr_finish<true><<<persist, 256, 0, s>>>(k, 1);
+    } else if (prm->scheme >= FPIC_HYB1) {
+        k_order<<<persist, 256, 0, s>>>(k);
+        k_imr<0, true><<<imr_grid, 128, 0, s>>>(k, 0);
+        k_imr_finish<true><<<persist, 256, 0, s>>>(k, 0);
+    }
     if (ev) FPIC_CUDA(cudaEventRecord(ev[3], s));
     FPIC_CUDA(cudaGetLastError());
     if (stats) {
