@@ -507,3 +507,52 @@ void or_div(double M, double a, int Nr, int Nth, int ld, const double *rn, const
             divD[i * ld + j] = (fr1 - fr0) / (rh[i] - rh[i - 1]) + (ft1 - ft0) / (th[j] - th[j - 1]);
         }
 }
+
+/* Split-monopole initial field (Sec. 3.4; App. B.2): B^r = d_th Psi / sqrtg
+ * with the flux function Psi = 4 M^2 B0 zeta(th) (1 - cos th) and the
+ * smoothed equatorial step zeta = (2/pi) arctan[zeta0 (th - pi/2)], at the
+ * B^r Yee points (r_i, th_{j+1/2}); every other component is zero (the
+ * paper starts from this vacuum field).
+ *   d_th Psi = 4 M^2 B0 [zeta'(th) (1 - cos th) + zeta(th) sin th],
+ *   zeta' = (2/pi) zeta0 / (1 + zeta0^2 (th - pi/2)^2).
+ * F[0..5] = D^r, D^th, D^ph, B^r, B^th, B^ph (size (Nr + 1) ld each). */
+void or_split_monopole_on_grid(double M, double a, double B0, double zeta0, int Nr, int Nth, int ld,
+                               const double *rn, const double *rh, const double *tn, const double *th,
+                               double *const F[6])
+{
+    (void)rh;
+    (void)tn;
+    const size_t sz = (size_t)(Nr + 1) * ld;
+    for (int k = 0; k < 6; ++k)
+        for (size_t o = 0; o < sz; ++o) F[k][o] = 0.0;
+    for (int i = 0; i <= Nr; ++i)
+        for (int j = 0; j < Nth; ++j) {
+            const double t = th[j], x = t - M_PI / 2.0;
+            const double zeta = 2.0 / M_PI * atan(zeta0 * x);
+            const double dzeta = 2.0 / M_PI * zeta0 / (1.0 + zeta0 * zeta0 * x * x);
+            const double dpsi = 4.0 * M * M * B0 * (dzeta * (1.0 - cos(t)) + zeta * sin(t));
+            F[3][i * ld + j] = dpsi / sqrtg_at(M, a, rn[i], t);
+        }
+}
+
+/* Eq. (Pbz): P_BZ = 2 pi int S^r sqrtg dth with S^r = (E_th H_ph - E_ph
+ * H_th) / (4 pi sqrtg), i.e. (1/2) int (E_th H_ph - E_ph H_th) dth, on the
+ * sphere r = rh[i] (half-r index i).  Each product is formed at the cell
+ * centres (rh[i], th_{j+1/2}): H_ph lives there; E_th (i, j+1/2) and
+ * (i+1, j+1/2) are averaged in r; H_th (i+1/2, j), (i+1/2, j+1) in th; E_ph
+ * at the four surrounding nodes.  Midpoint rule over the th cells. */
+double or_bz_power(int Nr, int Nth, int ld, const double *tn, const double *const E[3],
+                   const double *const H[3], int i)
+{
+    double P = 0.0;
+    if (i < 0 || i >= Nr) return 0.0;
+    for (int j = 0; j < Nth; ++j) {
+        const double Eth = 0.5 * (E[1][i * ld + j] + E[1][(i + 1) * ld + j]);
+        const double Hph = H[2][i * ld + j];
+        const double Eph = 0.25 * (E[2][i * ld + j] + E[2][i * ld + j + 1] + E[2][(i + 1) * ld + j] +
+                                   E[2][(i + 1) * ld + j + 1]);
+        const double Hth = 0.5 * (H[1][i * ld + j] + H[1][i * ld + j + 1]);
+        P += (Eth * Hph - Eph * Hth) * (tn[j + 1] - tn[j]);
+    }
+    return 0.5 * P;
+}

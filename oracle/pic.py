@@ -24,6 +24,9 @@ def _declare(L):
     P3 = _D * 3
     L.or_fdtd.argtypes = [C.POINTER(FdtdParams)] + g + [C.c_int, P3, P3, P3, P3, P3, _D, P3, _D, P3, P3, P3, P3]
     L.or_div.argtypes = [C.c_double, C.c_double] + g + [P3, P3, _D, _D]
+    L.or_split_monopole_on_grid.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double] + g + [_D * 6]
+    L.or_bz_power.argtypes = [C.c_int, C.c_int, C.c_int, _D, P3, P3, C.c_int]
+    L.or_bz_power.restype = C.c_double
 
 
 def _g(g):
@@ -82,3 +85,15 @@ def div(M, a, g, B, D):
     dB, dD = np.zeros(g.size), np.zeros(g.size)
     lib().or_div(M, a, *_g(g), _p3([f64(x) for x in B]), _p3([f64(x) for x in D]), ptr(dB), ptr(dD))
     return dB, dD
+
+
+def split_monopole_on_grid(M, a, B0, zeta0, g):
+    """Sec. 3.4 / App. B.2 vacuum split monopole: (D^r, D^th, D^ph, B^r, B^th, B^ph)."""
+    F = [np.zeros(g.size) for _ in range(6)]
+    lib().or_split_monopole_on_grid(M, a, B0, zeta0, *_g(g), (_D * 6)(*[ptr(x) for x in F]))
+    return F
+
+
+def bz_power(g, E, H, i):
+    """Eq. (Pbz) on the sphere r = rh[i] from the auxiliary fields E_i, H_i."""
+    return lib().or_bz_power(g.Nr, g.Nth, g.ld, ptr(g.tn), _p3([f64(x) for x in E]), _p3([f64(x) for x in H]), i)

@@ -180,3 +180,68 @@ def test_fdtd_static_wald_schwarzschild_stays_static():
         Br0 = F[3].reshape(g.Nr + 1, g.ld)[ri][:, :g.Nth][:, tj]
         errs.append(np.abs(Br - Br0).max() / np.abs(Br0).max())
     assert errs[0] < 2e-2 and errs[1] < 0.6 * errs[0], errs
+
+
+# ---------------------------------------------------------------------------
+# Split monopole (Sec. 3.4, App. B.2) and the BZ power diagnostic (Eq. Pbz)
+# ---------------------------------------------------------------------------
+def _psi(M, B0, zeta0, th):
+    return 4.0 * M * M * B0 * (2.0 / np.pi) * np.arctan(zeta0 * (th - np.pi / 2)) * (1.0 - np.cos(th))
+
+
+def test_split_monopole_flux_function_identity():
+    """sqrt(gamma) B^r integrated over th from the pole gives back Psi(th)
+    (Schwarzschild sqrt(gamma) = r^2 sin th sqrt(1 + 2M/r), written out here):
+    pins the derivative of the flux function, both terms and the sign."""
+    M, B0, z0 = 1.0, 1.7, 40.0
+    g = I.log_grid(8, 4000, 2.0, 20.0)
+    F = P.split_monopole_on_grid(M, 0.0, B0, z0, g)
+    Br = F[3].reshape(g.Nr + 1, g.ld)
+    for i in (0, 3, 8):
+        r = g.rn[i]
+        sg = r * r * np.sin(g.th) * np.sqrt(1.0 + 2.0 * M / r)
+        f = Br[i, : g.Nth] * sg                       # d_th Psi at the cell centres th_{j+1/2}
+        cum = np.concatenate([[0.0], np.cumsum(f * np.diff(g.tn))])   # int from tn[0]
+        expect = _psi(M, B0, z0, g.tn) - _psi(M, B0, z0, g.tn[0])
+        assert np.abs(cum - expect).max() <= 1e-5 * np.abs(expect).max()
+    for k in (0, 1, 2, 4, 5):
+        assert not F[k].any()
+
+
+def test_split_monopole_is_divergence_free():
+    """sqrt(gamma) B^r = d_th Psi does not depend on r, so the Yee divergence
+    of the field vanishes to rounding (a = 0.9)."""
+    a = 0.9
+    g = I.log_grid(40, 64, 1.5, 30.0)
+    F = P.split_monopole_on_grid(1.0, a, 1.0, 1e3, g)
+    dB, _ = P.div(1.0, a, g, F[3:], F[:3])
+    scale = (np.abs(F[3]).max() * 30.0 ** 2) / np.diff(g.rn).min()
+    assert np.abs(dB).max() <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("N", [64, 128, 256])
+def test_bz_power_quadrature(N):
+    """Eq. (Pbz) for E_th = r sin th, H_ph = sin th, E_ph = sin th cos th,
+    H_th = cos th on their Yee points: P = (1/2)[r pi/2 - 2/3] on the sphere,
+    to the second order of the staggered averages and the midpoint rule."""
+    g = I.log_grid(16, N, 2.0, 20.0)
+    R = lambda ro: (g.rh if ro else g.rn)
+    T = lambda to: (g.th if to else g.tn)
+    def field(ro, to, f):
+        x = np.zeros((g.Nr + 1, g.ld))
+        rr, tt = R(ro), T(to)
+        x[: len(rr), : len(tt)] = f(rr[:, None], tt[None, :])
+        return x.ravel()
+    z = np.zeros(g.size)
+    E = [z, field(0, 1, lambda r, t: r * np.sin(t)), field(0, 0, lambda r, t: np.sin(t) * np.cos(t))]
+    H = [z, field(1, 0, lambda r, t: np.cos(t) + 0 * r), field(1, 1, lambda r, t: np.sin(t) + 0 * r)]
+    i = 7
+    got = P.bz_power(g, E, H, i)
+    exact = 0.5 * (g.rh[i] * np.pi / 2 - 2.0 / 3.0)
+    err = abs(got - exact)
+    # staggering in r: E_th is averaged between rn[i] and rn[i+1] (mean
+    # cosh(d/2) rh[i] on the log grid, d = ln(rn[i+1] / rn[i])); in th the
+    # averages and the midpoint rule are second order
+    d = np.log(g.rn[i + 1] / g.rn[i])
+    tol_r = 1.5 * g.rh[i] * (np.cosh(d / 2) - 1.0) * np.pi / 4
+    assert err < 8.0 / N ** 2 + tol_r, (N, err, tol_r)
