@@ -141,6 +141,15 @@ int fpic_set_grid(fpic_ctx *ctx, int Nr, int Nth, const double *rn, const double
  * appendix's units).  Errors: FPIC_EINVAL. */
 int fpic_init_wald(fpic_ctx *ctx, double *const fields[6], double B0, void *stream);
 
+/* Sample the vacuum split-monopole field (Sec. 3.4, App. B.2): B^r =
+ * d_th Psi / sqrt(gamma) at the B^r Yee points with the flux function
+ * Psi = 4 M^2 B0 zeta(th) (1 - cos th) and the smoothed equatorial current
+ * sheet zeta = (2/pi) arctan[zeta0 (th - pi/2)]; fields[0..5] = D^r, D^th,
+ * D^ph, B^r, B^th, B^ph as for fpic_init_wald, every component but B^r set
+ * to zero.  Requires fpic_set_grid.  Errors: FPIC_EINVAL (NULL, no grid,
+ * B0 not finite, zeta0 <= 0). */
+int fpic_init_split_monopole(fpic_ctx *ctx, double *const fields[6], double B0, double zeta0, void *stream);
+
 /* Initialise particles from caller-supplied random draws (device arrays):
  *   FPIC_SEED_ORBIT: draws is n x K x 5 (r, th, E, L, root sign); the first
  *     candidate for which H(r, th, u_r, 0, L) = E has a root with
@@ -322,6 +331,16 @@ int fpic_deposit(fpic_ctx *ctx, fpic_particles *p, double *rho, double *jr, doub
  * and (j0, rho0)/(j1, rho1).  Errors: FPIC_EINVAL (no grid, stage not 1 or
  * 2, NULL array, dt not finite). */
 int fpic_fdtd_step(fpic_ctx *ctx, fpic_fields *f, const fpic_fdtd_params *prm, int stage, void *stream);
+
+/* Blandford-Znajek power through the sphere r = rh[i] (half-r index i in
+ * [0, Nr)), Eq. (Pbz): P = 2 pi int S^r sqrt(gamma) dth with S^r = (E_th H_ph
+ * - E_ph H_th) / (4 pi sqrt(gamma)), i.e. (1/2) int (E_th H_ph - E_ph H_th)
+ * dth, from the auxiliary fields f->E, f->H of the last fpic_fdtd_step
+ * (sub-step 9 leaves H^{n+2}; sub-step 3 leaves E^{n+3/2}).  Each product is
+ * formed at the cell centres (rh[i], th_{j+1/2}) from its staggered
+ * neighbours averaged; midpoint rule over the th cells; fixed-order
+ * reduction.  out: one device double.  Errors: FPIC_EINVAL. */
+int fpic_bz_power(fpic_ctx *ctx, const fpic_fields *f, int i, double *out, void *stream);
 
 /* ---- Learned implicit guess: MLP 14 -> 128 -> 128 -> 128 -> 9 --------------
  * No counterpart in the paper (its method has no learned component): a

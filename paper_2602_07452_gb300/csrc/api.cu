@@ -127,6 +127,34 @@ __global__ void k_wald(BH bh, GridDev G, double B0, double* F0, double* F1, doub
     }
 }
 
+// Split-monopole initial field (Sec. 3.4, App. B.2): B^r = d_th Psi / sqrt(gamma)
+// at the B^r Yee points, Psi = 4 M^2 B0 zeta(th) (1 - cos th), zeta =
+// (2/pi) arctan[zeta0 (th - pi/2)]; every other component zero.
+__global__ void k_split_monopole(BH bh, GridDev G, double B0, double zeta0, double* F0, double* F1, double* F2,
+                                 double* F3, double* F4, double* F5)
+{
+    double* F[6] = {F0, F1, F2, F3, F4, F5};
+    const int i = blockIdx.y;
+    for (int j = threadIdx.x; j <= G.Nth; j += blockDim.x) {
+        const size_t o = (size_t)i * G.ld + j;
+        for (int k = 0; k < 6; ++k)
+            if (k != 3) F[k][o] = 0.0;
+        if (j >= G.Nth) {
+            F[3][o] = 0.0;
+            continue;
+        }
+        const double t = G.th[j], x = t - 0.5 * M_PI;
+        double s, c;
+        sincos(t, &s, &c);
+        const double zeta = (2.0 / M_PI) * atan(zeta0 * x);
+        const double dzeta = (2.0 / M_PI) * zeta0 / fma(zeta0 * zeta0, x * x, 1.0);
+        const double dpsi = 4.0 * bh.M * bh.M * B0 * fma(dzeta, 1.0 - c, zeta * s);
+        Geo g;
+        geo_eval(bh, G.rn[i], s, c, g);
+        F[3][o] = dpsi / g.sqrtg;
+    }
+}
+
 struct PInit {
     double *r, *th, *ph, *ur, *uth, *uph, *qm, *H0, *D0, *Hn;
     uint8_t *alive, *scheme, *iters;
@@ -355,6 +383,23 @@ extern "C" int fpic_set_grid(fpic_ctx* c, int Nr, int Nth, const double* rn, con
     int rc = build_metric_tables(c);
     if (rc) return rc;
     FPIC_CUDA(cudaDeviceSynchronize());
+    return FPIC_OK;
+}
+
+extern "C" int fpic_init_split_monopole(fpic_ctx* c, double* const fields[6], double B0, double zeta0,
+                                        void* stream)
+{
+    if (!c || !fields) return set_error(FPIC_EINVAL, "fpic_init_split_monopole: NULL argument");
+    for (int i = 0; i < 6; ++i)
+        if (!fields[i]) return set_error(FPIC_EINVAL, "fpic_init_split_monopole: fields[%d] is NULL", i);
+    if (!c->has_grid) return set_error(FPIC_EINVAL, "fpic_init_split_monopole: no grid set");
+    if (!std::isfinite(B0) || !std::isfinite(zeta0) || !(zeta0 > 0.0))
+        return set_error(FPIC_EINVAL, "fpic_init_split_monopole: need finite B0 and zeta0 > 0");
+    FPIC_CUDA(cudaSetDevice(c->device));
+    dim3 grid(1, c->Nr + 1);
+    k_split_monopole<<<grid, 256, 0, (cudaStream_t)stream>>>(c->bh, c->G, B0, zeta0, fields[0], fields[1],
+                                                             fields[2], fields[3], fields[4], fields[5]);
+    FPIC_CUDA(cudaGetLastError());
     return FPIC_OK;
 }
 

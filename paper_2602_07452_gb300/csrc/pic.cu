@@ -837,6 +837,48 @@ extern "C" int fpic_deposit(fpic_ctx* c, fpic_particles* p, double* rho, double*
     return FPIC_OK;
 }
 
+namespace fpic {
+// Eq. (Pbz) on the sphere r = rh[i]: P = (1/2) sum_j (E_th H_ph - E_ph H_th)
+// dth_j with each product at the cell centre (rh[i], th_{j+1/2}) from its
+// staggered neighbours (E_th averaged in r, H_th in th, E_ph over the four
+// nodes).  One block; each thread sums a fixed stride of cells and the block
+// sums in a fixed tree, so the result is bitwise reproducible.
+__global__ void __launch_bounds__(256) k_bz_power(int Nth, int ld, const double* __restrict__ tn, const double* Eth,
+                                                  const double* Eph, const double* Hth, const double* Hph, int i,
+                                                  double* out)
+{
+    __shared__ double part[256];
+    double acc = 0.0;
+    for (int j = threadIdx.x; j < Nth; j += 256) {
+        const size_t o = (size_t)i * ld + j, o1 = o + ld;
+        const double et = 0.5 * (Eth[o] + Eth[o1]);
+        const double ep = 0.25 * ((Eph[o] + Eph[o + 1]) + (Eph[o1] + Eph[o1 + 1]));
+        const double ht = 0.5 * (Hth[o] + Hth[o + 1]);
+        acc = fma(fma(et, Hph[o], -ep * ht), tn[j + 1] - tn[j], acc);
+    }
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = 0.5 * part[0];
+}
+}  // namespace fpic
+
+extern "C" int fpic_bz_power(fpic_ctx* c, const fpic_fields* f, int i, double* out, void* stream)
+{
+    if (!c || !f || !out) return set_error(FPIC_EINVAL, "fpic_bz_power: NULL argument");
+    if (!c->has_grid) return set_error(FPIC_EINVAL, "fpic_bz_power: no grid set");
+    if (i < 0 || i >= c->Nr) return set_error(FPIC_EINVAL, "fpic_bz_power: half-r index %d outside [0, %d)", i, c->Nr);
+    if (!f->E[1] || !f->E[2] || !f->H[1] || !f->H[2]) return set_error(FPIC_EINVAL, "fpic_bz_power: NULL E or H array");
+    FPIC_CUDA(cudaSetDevice(c->device));
+    k_bz_power<<<1, 256, 0, (cudaStream_t)stream>>>(c->Nth, c->ld, c->G.tn, f->E[1], f->E[2], f->H[1], f->H[2], i,
+                                                    out);
+    FPIC_CUDA(cudaGetLastError());
+    return FPIC_OK;
+}
+
 extern "C" int fpic_fdtd_step(fpic_ctx* c, fpic_fields* f, const fpic_fdtd_params* prm, int stage, void* stream)
 {
     if (!c || !f || !prm) return set_error(FPIC_EINVAL, "fpic_fdtd_step: NULL argument");

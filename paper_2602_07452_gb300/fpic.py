@@ -129,6 +129,8 @@ _SIGS = {
     "fpic_probe_fp64": (C.c_int, [C.POINTER(C.c_double), C.c_int]),
     "fpic_probe_math": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p]),
     "fpic_set_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "fpic_init_split_monopole": (C.c_int, [C.c_void_p, C.POINTER(_D), C.c_double, C.c_double, C.c_void_p]),
+    "fpic_bz_power": (C.c_int, [C.c_void_p, C.POINTER(fpic_fields), C.c_int, C.c_void_p, C.c_void_p]),
     "fpic_get_tuning": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
     "fpic_push_noalloc": (C.c_int, [C.c_double, C.c_double, C.POINTER(fpic_particles),
                                     C.POINTER(fpic_push_params), C.POINTER(fpic_push_stats), C.c_void_p]),
@@ -356,6 +358,18 @@ def fpic_push_host(ctx: Ctx, hp: HostParticles, fields, prm: fpic_push_params, s
                               C.byref(st) if st is not None else None, _stream(stream))
     _check(rc)
     return st.as_dict() if st is not None else None
+
+
+def fpic_init_split_monopole(ctx: Ctx, fields, B0: float, zeta0: float = 1e3, stream=None) -> None:
+    _check(lib().fpic_init_split_monopole(ctx.handle, _fields_arg(fields), B0, zeta0, _stream(stream)))
+
+
+def fpic_bz_power(ctx: Ctx, f: "Fields", i: int, stream=None) -> torch.Tensor:
+    """Eq. (Pbz) through the sphere r = rh[i]; a one-element device tensor."""
+    out = torch.empty(1, dtype=torch.float64, device=f.E[0].device)
+    s = f.struct()
+    _check(lib().fpic_bz_power(ctx.handle, C.byref(s), i, out.data_ptr(), _stream(stream)))
+    return out
 
 
 def fpic_set_tuning(ctx: Ctx, key: int, value: int) -> None:

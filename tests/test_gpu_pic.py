@@ -186,3 +186,35 @@ def test_full_pic_step_matches_oracle(F):
             m = valid(g, nm, k)
             exp = getattr(st, nm)[k][m]; got = getattr(fl, nm)[k].cpu().numpy()[m]
             assert np.abs(got - exp).max() <= 1e-10 * (np.abs(exp).max() + 1e-300), (nm, k)
+
+
+def test_split_monopole_field_and_bz_power_match_oracle(F):
+    """Sec. 3.4 / App. B.2 field sampled by the library vs the oracle (1e-12
+    relative), and Eq. (Pbz) from the auxiliary fields of one FDTD stage vs
+    the oracle's quadrature of the same arrays (1e-12 relative)."""
+    import torch
+    a = 0.9
+    g = I.log_grid(48, 64, 1.5, 30.0)
+    ctx = F.fpic_init_metric(1.0, a)
+    F.fpic_set_grid(ctx, g)
+    fo = P.split_monopole_on_grid(1.0, a, 2.0, 1e3, g)
+    fd = [torch.zeros(g.size, dtype=torch.float64, device="cuda") for _ in range(6)]
+    F.fpic_init_split_monopole(ctx, fd, 2.0, 1e3)
+    for k in range(6):
+        got = fd[k].cpu().numpy()
+        sc = np.abs(fo[k]).max() + 1e-300
+        assert np.abs(got - fo[k]).max() <= 1e-12 * sc, k
+    # BZ power of random auxiliary fields (the arrays the FDTD leaves in E, H)
+    fl = F.Fields(g.size)
+    rng = np.random.default_rng(21)
+    E = [rng.normal(size=g.size) for _ in range(3)]
+    H = [rng.normal(size=g.size) for _ in range(3)]
+    for k in range(3):
+        fl.E[k].copy_(dev(E[k]))
+        fl.H[k].copy_(dev(H[k]))
+    for i in (0, 17, g.Nr - 1):
+        got = float(F.fpic_bz_power(ctx, fl, i).item())
+        ref = P.bz_power(g, E, H, i)
+        assert abs(got - ref) <= 1e-12 * (np.pi * 4), (i, got, ref)
+    with pytest.raises(F.FpicError):
+        F.fpic_bz_power(ctx, fl, g.Nr)
