@@ -556,3 +556,93 @@ double or_bz_power(int Nr, int Nth, int ld, const double *tn, const double *cons
     }
     return 0.5 * P;
 }
+
+/* Divergence cleaning (Sec. 2.4, Eq. phi).  Solve
+ *   (1/sqrtg) d_k (sqrtg gamma^kl d_l phi) = (1/sqrtg) d_j (sqrtg D^j) - 4 pi rho
+ * at the integer nodes (rn[i], tn[j]), i = 1 .. Nr-1, j = 0 .. Nth, by
+ * n_iter Jacobi sweeps from phi = 0, then correct D^i -= gamma^ij d_j phi.
+ * Discretisation: d_r phi at the D^r points (i+1/2, j), d_th phi at the D^th
+ * points (i, j+1/2); both sides are multiplied by sqrtg at the node, so the
+ * left side is the sum over the four faces of (sqrtg gamma^kk d_k phi)
+ * differences over the dual widths rh[i] - rh[i-1] and th[j] - th[j-1] —
+ * the same fluxes as the Yee divergence of D, so at convergence the
+ * corrected field satisfies the discrete Gauss law exactly.  Boundaries:
+ * phi = 0 on the radial end rows; the faces at the poles (th = 0, pi) carry
+ * no flux (sqrtg = 0 there), the end dual widths reaching the pole.
+ * (d_ph = 0; gamma^{r th} = 0.)  The correction of D^ph uses gamma^{ph r}
+ * times d_r phi at the node, the mean of the two adjacent half-point
+ * derivatives (one-sided on the end rows).  phi_out: nullable, size
+ * (Nr + 1) ld. */
+void or_div_clean(double M, double a, int Nr, int Nth, int ld, const double *rn, const double *rh,
+                  const double *tn, const double *th, double *const D[3], const double *rho, int n_iter,
+                  double *phi_out)
+{
+    const size_t sz = (size_t)(Nr + 1) * ld;
+    double *phi = calloc(sz, sizeof(double)), *nxt = calloc(sz, sizeof(double));
+    double *rhs = calloc(sz, sizeof(double));
+    double *c_r1 = calloc(sz, sizeof(double)), *c_r0 = calloc(sz, sizeof(double));
+    double *c_t1 = calloc(sz, sizeof(double)), *c_t0 = calloc(sz, sizeof(double));
+    pm_t m;
+    for (int i = 1; i < Nr; ++i)
+        for (int j = 0; j <= Nth; ++j) {
+            const size_t o = (size_t)i * ld + j;
+            const double dr = rh[i] - rh[i - 1];
+            const double dth = (j < Nth ? th[j] : M_PI) - (j > 0 ? th[j - 1] : 0.0);
+            /* right side: sqrtg-weighted divergence of D minus 4 pi sqrtg rho */
+            const double fr1 = sqrtg_at(M, a, rh[i], tn[j]) * D[0][o];
+            const double fr0 = sqrtg_at(M, a, rh[i - 1], tn[j]) * D[0][o - ld];
+            const double ft1 = j < Nth ? sqrtg_at(M, a, rn[i], th[j]) * D[1][o] : 0.0;
+            const double ft0 = j > 0 ? sqrtg_at(M, a, rn[i], th[j - 1]) * D[1][o - 1] : 0.0;
+            rhs[o] = (fr1 - fr0) / dr + (ft1 - ft0) / dth - 4.0 * M_PI * sqrtg_at(M, a, rn[i], tn[j]) * rho[o];
+            /* face coefficients sqrtg gamma^kk / (spacing x dual width) */
+            pm_eval(M, a, rh[i], tn[j], &m);
+            c_r1[o] = m.sqrtg * m.gu_rr / ((rn[i + 1] - rn[i]) * dr);
+            pm_eval(M, a, rh[i - 1], tn[j], &m);
+            c_r0[o] = m.sqrtg * m.gu_rr / ((rn[i] - rn[i - 1]) * dr);
+            if (j < Nth) {
+                pm_eval(M, a, rn[i], th[j], &m);
+                c_t1[o] = m.sqrtg * m.gu_tt / ((tn[j + 1] - tn[j]) * dth);
+            }
+            if (j > 0) {
+                pm_eval(M, a, rn[i], th[j - 1], &m);
+                c_t0[o] = m.sqrtg * m.gu_tt / ((tn[j] - tn[j - 1]) * dth);
+            }
+        }
+    for (int it = 0; it < n_iter; ++it) {
+        for (int i = 1; i < Nr; ++i)
+            for (int j = 0; j <= Nth; ++j) {
+                const size_t o = (size_t)i * ld + j;
+                double s = c_r1[o] * phi[o + ld] + c_r0[o] * phi[o - ld];
+                if (j < Nth) s += c_t1[o] * phi[o + 1];
+                if (j > 0) s += c_t0[o] * phi[o - 1];
+                nxt[o] = (s - rhs[o]) / (c_r1[o] + c_r0[o] + c_t1[o] + c_t0[o]);
+            }
+        double *t = phi;
+        phi = nxt;
+        nxt = t;
+    }
+    /* D^i -= gamma^ij d_j phi */
+    for (int i = 0; i < Nr; ++i)
+        for (int j = 0; j <= Nth; ++j) {
+            pm_eval(M, a, rh[i], tn[j], &m);
+            D[0][(size_t)i * ld + j] -= m.gu_rr * (phi[(size_t)(i + 1) * ld + j] - phi[(size_t)i * ld + j]) /
+                                        (rn[i + 1] - rn[i]);
+        }
+    for (int i = 0; i <= Nr; ++i)
+        for (int j = 0; j < Nth; ++j) {
+            pm_eval(M, a, rn[i], th[j], &m);
+            D[1][(size_t)i * ld + j] -= m.gu_tt * (phi[(size_t)i * ld + j + 1] - phi[(size_t)i * ld + j]) /
+                                        (tn[j + 1] - tn[j]);
+        }
+    for (int i = 0; i <= Nr; ++i)
+        for (int j = 0; j <= Nth; ++j) {
+            double dr_up = 0.0, dr_dn = 0.0;
+            int k = 0;
+            if (i < Nr) { dr_up = (phi[(size_t)(i + 1) * ld + j] - phi[(size_t)i * ld + j]) / (rn[i + 1] - rn[i]); ++k; }
+            if (i > 0) { dr_dn = (phi[(size_t)i * ld + j] - phi[(size_t)(i - 1) * ld + j]) / (rn[i] - rn[i - 1]); ++k; }
+            pm_eval(M, a, rn[i], tn[j], &m);
+            D[2][(size_t)i * ld + j] -= m.gu_rp * (dr_up + dr_dn) / k;
+        }
+    if (phi_out) memcpy(phi_out, phi, sz * sizeof(double));
+    free(phi); free(nxt); free(rhs); free(c_r1); free(c_r0); free(c_t1); free(c_t0);
+}

@@ -27,6 +27,7 @@ def _declare(L):
     L.or_split_monopole_on_grid.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double] + g + [_D * 6]
     L.or_bz_power.argtypes = [C.c_int, C.c_int, C.c_int, _D, P3, P3, C.c_int]
     L.or_bz_power.restype = C.c_double
+    L.or_div_clean.argtypes = [C.c_double, C.c_double] + g + [P3, _D, C.c_int, _D]
 
 
 def _g(g):
@@ -97,3 +98,12 @@ def split_monopole_on_grid(M, a, B0, zeta0, g):
 def bz_power(g, E, H, i):
     """Eq. (Pbz) on the sphere r = rh[i] from the auxiliary fields E_i, H_i."""
     return lib().or_bz_power(g.Nr, g.Nth, g.ld, ptr(g.tn), _p3([f64(x) for x in E]), _p3([f64(x) for x in H]), i)
+
+
+def div_clean(M, a, g, D, rho, n_iter):
+    """Sec. 2.4 divergence cleaning of D (list of 3 arrays, returned corrected
+    copies) against rho with n_iter Jacobi sweeps; also returns phi."""
+    Dc = [f64(x).copy() for x in D]
+    phi = np.zeros(g.size)
+    lib().or_div_clean(M, a, *_g(g), _p3(Dc), ptr(f64(rho)), int(n_iter), ptr(phi))
+    return Dc, phi
