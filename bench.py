@@ -64,7 +64,8 @@ def parse():
                     help="corrector: restart a solve from the plain trial after this many iterations (0: never)")
     ap.add_argument("--train-gen-steps", type=int, default=10,
                     help="plain steps sampled for the training set")
-    ap.add_argument("--workload", default="push", choices=["push", "pic", "neutral", "batched"])
+    ap.add_argument("--workload", default="push", choices=["push", "pic", "neutral", "batched", "clean"])
+    ap.add_argument("--clean-sweeps", type=int, default=500, help="Jacobi sweeps of --workload clean")
     ap.add_argument("--pic-grid", type=int, default=1024)
     ap.add_argument("--pic-ppc", type=int, default=64)
     ap.add_argument("--pic-steps", type=int, default=3)
@@ -611,6 +612,50 @@ def run_pic(args, device, grid_n, ppc, steps, rank=0):
     }
 
 
+def run_div_clean(device, grid_n=1024, n_iter=500, reps=3):
+    """Sec. 2.4 divergence cleaning (Eq. phi, n_iter Jacobi sweeps and the
+    correction) of a Wald D perturbed by noise against a random rho on the
+    grid_n x grid_n plasma grid, a = 0.99.  The paper cleans every 25 steps
+    with 500 sweeps; the amortised cost per step is reported beside it."""
+    import numpy as np
+    import torch
+    from paper_2602_07452_gb300 import fpic as F
+    from paper_2602_07452_gb300 import inputs as I
+    g = I.wald_grid(grid_n, PIC_A)
+    ctx = F.fpic_init_metric(1.0, PIC_A)
+    F.fpic_set_grid(ctx, g)
+    wald = [torch.zeros(g.size, dtype=torch.float64, device=device) for _ in range(6)]
+    F.fpic_init_wald(ctx, wald, B0)
+    gen = torch.Generator(device=device).manual_seed(5)
+    D0 = [wald[k] + 1e-3 * torch.randn(g.size, generator=gen, dtype=torch.float64, device=device)
+          for k in range(3)]
+    rho = 1e-3 * torch.randn(g.size, generator=gen, dtype=torch.float64, device=device)
+    D = [x.clone() for x in D0]
+    s = torch.cuda.current_stream(device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    F.fpic_div_clean(ctx, D, rho, n_iter)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        for k in range(3):
+            D[k].copy_(D0[k])
+        e0.record(s)
+        F.fpic_div_clean(ctx, D, rho, n_iter)
+        e1.record(s)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) * 1e-3)
+    t = float(np.median(ts))
+    nodes = (g.Nr - 1) * (g.Nth + 1)
+    # per node and sweep: 4 coefficients, the scaled right side, phi read
+    # once (neighbours from cache), phi written
+    bytes_sweep = nodes * 7 * 8
+    return {"workload": f"divergence cleaning, {grid_n}x{grid_n} (ln r, theta), a={PIC_A}, {n_iter} Jacobi sweeps",
+            "ms_per_clean": 1e3 * t, "us_per_sweep": 1e6 * t / max(n_iter, 1),
+            "amortised_ms_per_step_every_25": 1e3 * t / 25,
+            "sweep_working_set_mb": 7 * g.size * 8 / 1e6,
+            "sweep_achieved_gbs": bytes_sweep * n_iter / t / 1e9 if n_iter else None}
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -655,6 +700,15 @@ def main():
     import torch.distributed as dist
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if args.workload == "clean":
+        torch.cuda.set_device(local)
+        res = run_div_clean(torch.device("cuda", local), args.pic_grid, args.clean_sweeps, reps=max(args.steps, 1))
+        if rank == 0:
+            print(json.dumps({"metric": "divergence cleaning time", "value": res["ms_per_clean"], "unit": "ms",
+                              "n_gpus": ws, "steps": max(args.steps, 1), "warmup": 1,
+                              "ms_per_step": res["ms_per_clean"], "higher_is_better": False, "scaling": "weak",
+                              "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": res}))
+        return 0
     if args.workload in ("pic", "neutral", "batched"):
         import torch
         torch.cuda.set_device(local)
@@ -683,6 +737,7 @@ def main():
         line["neutral_dg_alone"] = run_neutral(args, dev, 1 << 20, 5, pre_steps=2, scheme="HAM")
         line["neutral_rk4_alone"] = run_neutral(args, dev, 1 << 20, 20, pre_steps=2, scheme="RK4")
         line["batched"] = run_batched(args, dev, 0.1, 5)
+        line["div_clean"] = run_div_clean(dev)
     if rank == 0:
         if pool is not None:
             try:

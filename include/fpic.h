@@ -332,6 +332,19 @@ int fpic_deposit(fpic_ctx *ctx, fpic_particles *p, double *rho, double *jr, doub
  * 2, NULL array, dt not finite). */
 int fpic_fdtd_step(fpic_ctx *ctx, fpic_fields *f, const fpic_fdtd_params *prm, int stage, void *stream);
 
+/* Divergence cleaning (Sec. 2.4, Eq. phi): solve
+ *   (1/sqrtg) d_k (sqrtg gamma^kl d_l phi) = (1/sqrtg) d_j (sqrtg D^j) - 4 pi rho
+ * at the integer nodes (i = 1 .. Nr-1, all j) by n_iter Jacobi sweeps from
+ * phi = 0, then D^i -= gamma^ij d_j phi in place.  D[0..2] = D^r, D^th,
+ * D^ph (device, grid layout), rho at the nodes.  The discrete operator uses
+ * the Yee divergence's own sqrtg-weighted fluxes, so a converged solve
+ * leaves the discrete Gauss law satisfied to rounding at every interior
+ * node; phi = 0 on the radial end rows, no flux through the poles.  phi:
+ * nullable device array (grid layout) receiving the potential.  Uses the
+ * context's second scratch (7 grid arrays).  The paper cleans every 25 steps
+ * with 500 sweeps.  Errors: FPIC_EINVAL, FPIC_ENOMEM. */
+int fpic_div_clean(fpic_ctx *ctx, double *const D[3], const double *rho, int n_iter, double *phi, void *stream);
+
 /* Blandford-Znajek power through the sphere r = rh[i] (half-r index i in
  * [0, Nr)), Eq. (Pbz): P = 2 pi int S^r sqrt(gamma) dth with S^r = (E_th H_ph
  * - E_ph H_th) / (4 pi sqrt(gamma)), i.e. (1/2) int (E_th H_ph - E_ph H_th)

@@ -317,6 +317,7 @@ extern "C" void fpic_destroy(fpic_ctx* c)
     for (cudaEvent_t e : c->copy_ev)
         if (e) cudaEventDestroy(e);
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    if (c->clean_exec) cudaGraphExecDestroy(c->clean_exec);
     delete c;
 }
 

@@ -46,6 +46,11 @@ struct fpic_ctx {
     // fpic_push_host: copy stream and per-chunk events (created on first use)
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t copy_ev[FPIC_HOST_CHUNKS + 1] = {};
+    // fpic_div_clean: the chain of Jacobi sweeps as an instantiated graph,
+    // rebuilt when its key (scratch base, grid shape, sweep count) changes
+    cudaGraphExec_t clean_exec = nullptr;
+    const void* clean_key_base = nullptr;
+    int clean_key_Nr = 0, clean_key_Nth = 0, clean_key_iter = -1;
 };
 
 namespace fpic {

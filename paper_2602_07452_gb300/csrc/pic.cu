@@ -838,6 +838,116 @@ extern "C" int fpic_deposit(fpic_ctx* c, fpic_particles* p, double* rho, double*
 }
 
 namespace fpic {
+// ---------------------------------------------------------------------------
+// Divergence cleaning (Sec. 2.4, Eq. phi)
+// ---------------------------------------------------------------------------
+// (1/sqrtg) d_k (sqrtg gamma^kl d_l phi) = (1/sqrtg) d_j (sqrtg D^j) - 4 pi rho at
+// the integer nodes i = 1 .. Nr-1, j = 0 .. Nth, multiplied by sqrtg at the
+// node: the left side is the sum over the four faces of sqrtg gamma^kk d_k phi
+// differences over the dual widths (the Yee divergence's own fluxes), the
+// pole faces carry no flux, phi = 0 on the radial end rows.  Jacobi form
+// phi <- sum_f c_f phi_f - b with c_f = face coefficient / sum of the face
+// coefficients and b = right side / the same sum, both built once.
+struct CleanK {
+    int Nr, Nth, ld;
+    GridDev G;
+    Tabs T;                                  // metric tables at the Yee points
+    double *c_r1, *c_r0, *c_t1, *c_t0, *b;   // per node (library scratch)
+};
+
+// Inverse spatial metric from the tabulated lower one: the th block is
+// diagonal, the (r, ph) block a 2 x 2 inverse.
+__device__ __forceinline__ double tab_gu_rr(const Tabs& T, int t, int i, int j)
+{
+    const double grr = T.at(t, 3, i, j), grp = T.at(t, 4, i, j), gpp = T.at(t, 6, i, j);
+    return gpp / fma(grr, gpp, -grp * grp);
+}
+
+__device__ __forceinline__ double tab_gu_rp(const Tabs& T, int t, int i, int j)
+{
+    const double grr = T.at(t, 3, i, j), grp = T.at(t, 4, i, j), gpp = T.at(t, 6, i, j);
+    return -grp / fma(grr, gpp, -grp * grp);
+}
+
+__global__ void k_clean_setup(CleanK k, const double* __restrict__ Dr, const double* __restrict__ Dt,
+                              const double* __restrict__ rho)
+{
+    const int i = blockIdx.y + 1;                   // 1 .. Nr-1
+    const GridDev& G = k.G;
+    const Tabs& T = k.T;
+    const double dr = G.rh[i] - G.rh[i - 1];
+    const double ir1 = 1.0 / ((G.rn[i + 1] - G.rn[i]) * dr), ir0 = 1.0 / ((G.rn[i] - G.rn[i - 1]) * dr);
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j <= k.Nth; j += gridDim.x * blockDim.x) {
+        const size_t o = (size_t)i * k.ld + j;
+        const double dth = (j < k.Nth ? G.th[j] : M_PI) - (j > 0 ? G.th[j - 1] : 0.0);
+        const double sr1 = T.at(1, 2, i, j), sr0 = T.at(1, 2, i - 1, j);
+        const double st1 = j < k.Nth ? T.at(2, 2, i, j) : 0.0, st0 = j > 0 ? T.at(2, 2, i, j - 1) : 0.0;
+        const double rhs = (sr1 * Dr[o] - sr0 * Dr[o - k.ld]) / dr +
+                           ((j < k.Nth ? st1 * Dt[o] : 0.0) - (j > 0 ? st0 * Dt[o - 1] : 0.0)) / dth -
+                           4.0 * M_PI * T.at(0, 2, i, j) * rho[o];
+        const double cr1 = sr1 * tab_gu_rr(T, 1, i, j) * ir1;
+        const double cr0 = sr0 * tab_gu_rr(T, 1, i - 1, j) * ir0;
+        const double ct1 = j < k.Nth ? st1 / (T.at(2, 5, i, j) * (G.tn[j + 1] - G.tn[j]) * dth) : 0.0;
+        const double ct0 = j > 0 ? st0 / (T.at(2, 5, i, j - 1) * (G.tn[j] - G.tn[j - 1]) * dth) : 0.0;
+        const double inv = 1.0 / (cr1 + cr0 + ct1 + ct0);
+        k.c_r1[o] = cr1 * inv;
+        k.c_r0[o] = cr0 * inv;
+        k.c_t1[o] = ct1 * inv;
+        k.c_t0[o] = ct0 * inv;
+        k.b[o] = rhs * inv;
+    }
+}
+
+// One Jacobi sweep over the interior nodes (phi_in -> phi_out); the radial
+// end rows stay zero in both buffers.  A thread walks JAC_ROWS rows of one
+// theta column keeping the column's three radial neighbours in registers,
+// so each phi value comes from L2 about once per sweep; the theta
+// neighbours are the same row's loads of the adjacent threads (L1).
+constexpr int JAC_ROWS = 8, JAC_THREADS = 128;
+__global__ void __launch_bounds__(JAC_THREADS) k_jacobi(CleanK k, const double* __restrict__ phi_in,
+                                                        double* __restrict__ phi_out)
+{
+    const int j = blockIdx.x * JAC_THREADS + threadIdx.x;
+    if (j > k.Nth) return;
+    const int i0 = 1 + blockIdx.y * JAC_ROWS;
+    const int i1 = min(i0 + JAC_ROWS, k.Nr);        // exclusive
+    size_t o = (size_t)i0 * k.ld + j;
+    double dn = phi_in[o - k.ld], mid = phi_in[o];
+    for (int i = i0; i < i1; ++i, o += k.ld) {
+        const double up = phi_in[o + k.ld];
+        double s = fma(k.c_r1[o], up, k.c_r0[o] * dn);
+        if (j < k.Nth) s = fma(k.c_t1[o], phi_in[o + 1], s);
+        if (j > 0) s = fma(k.c_t0[o], phi_in[o - 1], s);
+        phi_out[o] = s - k.b[o];
+        dn = mid;
+        mid = up;
+    }
+}
+
+// D^i -= gamma^ij d_j phi: D^r at (i+1/2, j), D^th at (i, j+1/2), D^ph at
+// (i, j) with d_r phi the mean of the two adjacent half-point differences
+// (one-sided on the end rows).
+__global__ void k_clean_correct(CleanK k, const double* __restrict__ phi, double* Dr, double* Dt, double* Dp)
+{
+    const int i = blockIdx.y;                       // 0 .. Nr
+    const GridDev& G = k.G;
+    const Tabs& T = k.T;
+    const double iu = i < k.Nr ? 1.0 / (G.rn[i + 1] - G.rn[i]) : 0.0;
+    const double id = i > 0 ? 1.0 / (G.rn[i] - G.rn[i - 1]) : 0.0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j <= k.Nth; j += gridDim.x * blockDim.x) {
+        const size_t o = (size_t)i * k.ld + j;
+        const double up = i < k.Nr ? (phi[o + k.ld] - phi[o]) * iu : 0.0;
+        const double dn = i > 0 ? (phi[o] - phi[o - k.ld]) * id : 0.0;
+        const double mean = (i > 0 && i < k.Nr) ? 0.5 * (up + dn) : up + dn;
+        if (i < k.Nr) Dr[o] -= tab_gu_rr(T, 1, i, j) * up;
+        if (j < k.Nth) Dt[o] -= (phi[o + 1] - phi[o]) / (T.at(2, 5, i, j) * (G.tn[j + 1] - G.tn[j]));
+        Dp[o] -= tab_gu_rp(T, 0, i, j) * mean;
+    }
+}
+
+}  // namespace fpic
+
+namespace fpic {
 // Eq. (Pbz) on the sphere r = rh[i]: P = (1/2) sum_j (E_th H_ph - E_ph H_th)
 // dth_j with each product at the cell centre (rh[i], th_{j+1/2}) from its
 // staggered neighbours (E_th averaged in r, H_th in th, E_ph over the four
@@ -875,6 +985,75 @@ extern "C" int fpic_bz_power(fpic_ctx* c, const fpic_fields* f, int i, double* o
     FPIC_CUDA(cudaSetDevice(c->device));
     k_bz_power<<<1, 256, 0, (cudaStream_t)stream>>>(c->Nth, c->ld, c->G.tn, f->E[1], f->E[2], f->H[1], f->H[2], i,
                                                     out);
+    FPIC_CUDA(cudaGetLastError());
+    return FPIC_OK;
+}
+
+extern "C" int fpic_div_clean(fpic_ctx* c, double* const D[3], const double* rho, int n_iter, double* phi,
+                              void* stream)
+{
+    if (!c || !D || !D[0] || !D[1] || !D[2] || !rho) return set_error(FPIC_EINVAL, "fpic_div_clean: NULL argument");
+    if (!c->has_grid) return set_error(FPIC_EINVAL, "fpic_div_clean: no grid set");
+    if (n_iter < 0) return set_error(FPIC_EINVAL, "fpic_div_clean: n_iter < 0");
+    FPIC_CUDA(cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t sz = (size_t)(c->Nr + 1) * c->ld;
+    // scratch: 5 coefficient arrays and two phi buffers
+    int rc = ensure_scratch2(c, 7 * sz * sizeof(double) + 256);
+    if (rc) return rc;
+    double* base = (double*)c->d_scratch2;
+    CleanK k{c->Nr, c->Nth, c->ld, c->G, tabs_of(c), base, base + sz, base + 2 * sz, base + 3 * sz, base + 4 * sz};
+    double* pa = base + 5 * sz;
+    double* pb = base + 6 * sz;
+    FPIC_CUDA(cudaMemsetAsync(pa, 0, 2 * sz * sizeof(double), s));
+    if (c->Nr >= 2) {
+        const unsigned gx = (unsigned)((c->Nth + 1 + 255) / 256);
+        k_clean_setup<<<dim3(gx, c->Nr - 1), 256, 0, s>>>(k, D[0], D[1], rho);
+        const dim3 jg((unsigned)((c->Nth + 1 + JAC_THREADS - 1) / JAC_THREADS),
+                      (unsigned)((c->Nr - 1 + JAC_ROWS - 1) / JAC_ROWS));
+        auto sweeps = [&](cudaStream_t st) {
+            double *x = base + 5 * sz, *y = base + 6 * sz;
+            for (int it = 0; it < n_iter; ++it) {
+                k_jacobi<<<jg, JAC_THREADS, 0, st>>>(k, x, y);
+                double* t = x;
+                x = y;
+                y = t;
+            }
+        };
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        FPIC_CUDA(cudaStreamIsCapturing(s, &cap));
+        if (n_iter < 8 || cap != cudaStreamCaptureStatusNone) {
+            sweeps(s);       // short chains, or the caller is recording a graph itself
+        } else {
+            // hundreds of short launches: replay them as one graph
+            if (!c->clean_exec || c->clean_key_base != base || c->clean_key_Nr != c->Nr ||
+                c->clean_key_Nth != c->Nth || c->clean_key_iter != n_iter) {
+                if (c->clean_exec) FPIC_CUDA(cudaGraphExecDestroy(c->clean_exec));
+                c->clean_exec = nullptr;
+                int rc2 = ensure_copy_stream(c);
+                if (rc2) return rc2;
+                cudaGraph_t g = nullptr;
+                FPIC_CUDA(cudaStreamBeginCapture(c->copy_stream, cudaStreamCaptureModeThreadLocal));
+                sweeps(c->copy_stream);
+                FPIC_CUDA(cudaStreamEndCapture(c->copy_stream, &g));
+                cudaError_t e = cudaGraphInstantiate(&c->clean_exec, g, 0);
+                cudaGraphDestroy(g);
+                FPIC_CUDA(e);
+                c->clean_key_base = base;
+                c->clean_key_Nr = c->Nr;
+                c->clean_key_Nth = c->Nth;
+                c->clean_key_iter = n_iter;
+            }
+            FPIC_CUDA(cudaGraphLaunch(c->clean_exec, s));
+        }
+        if (n_iter & 1) {
+            double* t = pa;
+            pa = pb;
+            pb = t;
+        }
+    }
+    k_clean_correct<<<dim3((unsigned)((c->Nth + 1 + 255) / 256), c->Nr + 1), 256, 0, s>>>(k, pa, D[0], D[1], D[2]);
+    if (phi) FPIC_CUDA(cudaMemcpyAsync(phi, pa, sz * sizeof(double), cudaMemcpyDeviceToDevice, s));
     FPIC_CUDA(cudaGetLastError());
     return FPIC_OK;
 }

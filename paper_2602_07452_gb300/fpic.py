@@ -131,6 +131,7 @@ _SIGS = {
     "fpic_set_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "fpic_init_split_monopole": (C.c_int, [C.c_void_p, C.POINTER(_D), C.c_double, C.c_double, C.c_void_p]),
     "fpic_bz_power": (C.c_int, [C.c_void_p, C.POINTER(fpic_fields), C.c_int, C.c_void_p, C.c_void_p]),
+    "fpic_div_clean": (C.c_int, [C.c_void_p, C.POINTER(_D), C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "fpic_get_tuning": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
     "fpic_push_noalloc": (C.c_int, [C.c_double, C.c_double, C.POINTER(fpic_particles),
                                     C.POINTER(fpic_push_params), C.POINTER(fpic_push_stats), C.c_void_p]),
@@ -370,6 +371,15 @@ def fpic_bz_power(ctx: Ctx, f: "Fields", i: int, stream=None) -> torch.Tensor:
     s = f.struct()
     _check(lib().fpic_bz_power(ctx.handle, C.byref(s), i, out.data_ptr(), _stream(stream)))
     return out
+
+
+def fpic_div_clean(ctx: Ctx, D, rho: torch.Tensor, n_iter: int = 500, want_phi: bool = False, stream=None):
+    """Sec. 2.4 divergence cleaning of D (3 device tensors, corrected in place)."""
+    arr = (_D * 3)(*[_dp(d) for d in D])
+    phi = torch.zeros_like(rho) if want_phi else None
+    _check(lib().fpic_div_clean(ctx.handle, arr, rho.data_ptr(), n_iter,
+                                phi.data_ptr() if phi is not None else None, _stream(stream)))
+    return phi
 
 
 def fpic_set_tuning(ctx: Ctx, key: int, value: int) -> None:
