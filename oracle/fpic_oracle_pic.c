@@ -646,3 +646,91 @@ void or_div_clean(double M, double a, int Nr, int Nth, int ld, const double *rn,
     if (phi_out) memcpy(phi_out, phi, sz * sizeof(double));
     free(phi); free(nxt); free(rhs); free(c_r1); free(c_r0); free(c_t1); free(c_t0);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Pair injection (Sec. 3.3 and Sec. 3.4).                                   */
+/* ------------------------------------------------------------------------ */
+
+/* In every cell whose centre radius rh[i] lies in [r_lo, r_hi], an e-/e+
+ * pair is added when the plasma density is below the multiplicity times
+ * the Goldreich-Julian density, n < mult n_GJ, n_GJ = |Omega . B| / (4 pi e)
+ * with Omega the horizon's angular velocity a / (2 M r_h) along the spin
+ * axis.  Readings (the paper is silent on them):
+ *   - densities are charge-number densities: e n = sum of w |q/m| over the
+ *     cell's alive particles (in particle-index order) / V, V = 2 pi x the
+ *     4 x 4 trapezoid of sqrt(gamma) over the cell (the Sec. 2.3 volume);
+ *   - Omega . B = Omega (B^r cos th - r sin th B^th) at the cell centre,
+ *     B^r averaged over the cell's two r faces, B^th over its two th faces
+ *     (the flat-space z component of B with the coordinate r, th);
+ *   - the pair is placed at one point, drawn uniformly in the cell's
+ *     coordinate box, ph uniform in [0, 2 pi), each particle with its own
+ *     FIDO-frame momentum (Maxwell-Juttner draws supplied by the caller),
+ *     mapped to u_i as in the FIDO seeding (gamma = L L^T);
+ *   - both particles get the weight that makes the pair's density n0 n_GJ
+ *     (the "effective density" conferred by one injection), w |q/m| / V =
+ *     n0 e n_GJ / 2;
+ *   - pairs are appended in cell order (c = i Nth + j), e- then e+, while
+ *     they fit in the capacity.
+ * draws: 9 numbers per cell c (u_r, u_th, u_ph uniform in [0,1), e- FIDO
+ * momentum, e+ FIDO momentum).  z (cap x 6), qm, w, alive hold n particles.
+ * flags (nullable, Nr Nth bytes) receives the decisions.  Returns the
+ * number of pairs wanted; *n_out = the new particle count. */
+int64_t or_inject_pairs(double M, double a, int Nr, int Nth, int ld, const double *rn, const double *rh,
+                        const double *tn, const double *th, const double *Br, const double *Bth, double r_lo,
+                        double r_hi, double mult, double n0, double qm_e, const double *draws, int64_t n,
+                        int64_t cap, double *z, double *qm, double *w, uint8_t *alive, uint8_t *flags,
+                        int64_t *n_out)
+{
+    const int64_t C = (int64_t)Nr * Nth;
+    double *S = calloc((size_t)C, sizeof(double));
+    for (int64_t p = 0; p < n; ++p) {
+        if (!alive[p]) continue;
+        int i = loc(rn, Nr + 1, z[6 * p]), j = loc(tn, Nth + 1, z[6 * p + 1]);
+        S[(int64_t)i * Nth + j] += w[p] * fabs(qm[p]);
+    }
+    const double r_h = M + sqrt(M * M - a * a);
+    const double Om = a / (2.0 * M * r_h);
+    int64_t K = 0, m = n;
+    for (int i = 0; i < Nr; ++i)
+        for (int j = 0; j < Nth; ++j) {
+            const int64_t c = (int64_t)i * Nth + j;
+            int inj = 0;
+            double V = 0.0, gj = 0.0;
+            if (rh[i] >= r_lo && rh[i] <= r_hi) {
+                V = 2.0 * M_PI * trap16(M, a, rn[i], rn[i + 1], tn[j], tn[j + 1], 0);
+                double br = 0.5 * (Br[(size_t)i * ld + j] + Br[(size_t)(i + 1) * ld + j]);
+                double bt = 0.5 * (Bth[(size_t)i * ld + j] + Bth[(size_t)i * ld + j + 1]);
+                double Bz = br * cos(th[j]) - rh[i] * sin(th[j]) * bt;
+                gj = fabs(Om * Bz) / (4.0 * M_PI);
+                inj = S[c] / V < mult * gj;
+            }
+            if (flags) flags[c] = (uint8_t)inj;
+            if (!inj) continue;
+            ++K;
+            if (m + 2 > cap) continue;
+            const double *d = draws + 9 * c;
+            const double r = rn[i] + d[0] * (rn[i + 1] - rn[i]);
+            const double t = tn[j] + d[1] * (tn[j + 1] - tn[j]);
+            const double ph = 2.0 * M_PI * d[2];
+            pm_t g;
+            pm_eval(M, a, r, t, &g);
+            const double L11 = sqrt(g.g_rr), L31 = g.g_rp / L11, L22 = sqrt(g.g_tt);
+            const double L33 = sqrt(g.g_pp - L31 * L31);
+            const double wp = n0 * gj * V / (2.0 * qm_e);
+            for (int s = 0; s < 2; ++s) {
+                const double *u = d + 3 + 3 * s;
+                double *o = z + 6 * m;
+                o[0] = r; o[1] = t; o[2] = ph;
+                o[3] = L11 * u[0];
+                o[4] = L22 * u[1];
+                o[5] = L31 * u[0] + L33 * u[2];
+                qm[m] = s == 0 ? -qm_e : qm_e;
+                w[m] = wp;
+                alive[m] = 1;
+                ++m;
+            }
+        }
+    free(S);
+    *n_out = m;
+    return K;
+}

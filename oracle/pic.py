@@ -28,6 +28,9 @@ def _declare(L):
     L.or_bz_power.argtypes = [C.c_int, C.c_int, C.c_int, _D, P3, P3, C.c_int]
     L.or_bz_power.restype = C.c_double
     L.or_div_clean.argtypes = [C.c_double, C.c_double] + g + [P3, _D, C.c_int, _D]
+    L.or_inject_pairs.argtypes = [C.c_double, C.c_double] + g + [_D, _D] + [C.c_double] * 5 + [
+        _D, _I64, _I64, _D, _D, _D, _U8, _U8, C.POINTER(_I64)]
+    L.or_inject_pairs.restype = _I64
 
 
 def _g(g):
@@ -107,3 +110,21 @@ def div_clean(M, a, g, D, rho, n_iter):
     phi = np.zeros(g.size)
     lib().or_div_clean(M, a, *_g(g), _p3(Dc), ptr(f64(rho)), int(n_iter), ptr(phi))
     return Dc, phi
+
+
+def inject_pairs(M, a, g, z, qm, w, alive, n, cap, Br, Bth, r_lo, r_hi, mult, n0, qm_e, draws):
+    """Sec. 3.3 / 3.4 pair injection on copies of capacity-sized arrays
+    (z: cap x 6, the first n in use).  Returns (z, qm, w, alive, n_new,
+    pairs wanted, per-cell flags)."""
+    z = np.ascontiguousarray(f64(z).copy()).reshape(-1, 6)
+    qm, w = f64(qm).copy(), f64(w).copy()
+    alive = np.ascontiguousarray(alive, dtype=np.uint8).copy()
+    assert z.shape[0] >= cap and qm.size >= cap and w.size >= cap and alive.size >= cap
+    flags = np.zeros(g.Nr * g.Nth, np.uint8)
+    d = np.ascontiguousarray(f64(draws))
+    assert d.size >= 9 * g.Nr * g.Nth
+    n_out = C.c_int64(0)
+    K = lib().or_inject_pairs(M, a, *_g(g), ptr(f64(Br)), ptr(f64(Bth)), r_lo, r_hi, mult, n0, qm_e, ptr(d),
+                              int(n), int(cap), ptr(z), ptr(qm), ptr(w),
+                              ptr(alive, _U8), ptr(flags, _U8), C.byref(n_out))
+    return z, qm, w, alive, int(n_out.value), int(K), flags

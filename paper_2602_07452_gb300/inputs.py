@@ -144,3 +144,16 @@ def cell_fill_draws(g: Grid, ppc: int, theta_T: float, seed: int = 3, qm: float 
     d[:, 3:] = maxwell_juettner(rng, n, theta_T)
     q = np.where(np.arange(n) % 2 == 0, -qm, qm).astype(np.float64)
     return d, q, np.ones(n)
+
+
+def injection_draws(g: Grid, theta_T: float, seed: int = 4) -> np.ndarray:
+    """Random numbers of one pair injection: (Nr Nth, 9) per cell c = i Nth + j
+    = (u_r, u_th, u_ph) uniform in [0, 1), then the FIDO-frame momenta of the
+    electron and of the positron, each Maxwell-Juttner(theta_T)."""
+    rng = np.random.default_rng(seed)
+    C = g.Nr * g.Nth
+    d = np.empty((C, 9))
+    d[:, :3] = rng.random((C, 3))
+    d[:, 3:6] = maxwell_juettner(rng, C, theta_T)
+    d[:, 6:9] = maxwell_juettner(rng, C, theta_T)
+    return d

@@ -343,3 +343,147 @@ def test_div_clean_leaves_solenoidal_field_alone():
     assert np.abs(phi).max() < 1e-12 * scale
     for k in range(3):
         assert np.abs(Dc[k] - D[k]).max() < 1e-12 * scale
+
+
+# ---- pair injection (Sec. 3.3, 3.4) -------------------------------------------
+
+def _radial_field(g, B0=1.0):
+    """B^r = B0 on every B^r point, B^th = 0: at a cell centre the spin-axis
+    component is exactly B0 cos th (no averaging error)."""
+    return np.full(g.size, B0), np.zeros(g.size)
+
+
+def _empty_store(cap):
+    return np.zeros((cap, 6)), np.zeros(cap), np.zeros(cap), np.zeros(cap, np.uint8)
+
+
+def _omega_h(a, M=1.0):
+    """Horizon angular velocity a / (r_h^2 + a^2)."""
+    rh = M + math.sqrt(M * M - a * a)
+    return a / (rh * rh + a * a)
+
+
+def test_inject_weights_follow_the_gj_density():
+    """Into an empty region every cell with centre radius in [r_lo, r_hi] gets
+    one pair whose two weights give n = n0 n_GJ with n_GJ = |Omega_h B0
+    cos th - r B1 sin th| / (4 pi e) for the uniform coordinate components
+    B^r = B0, B^th = B1 (exact at the cell centre): w |q/m| x 2 / (n0 e n_GJ)
+    equals the proper cell volume, checked against an independent adaptive
+    quadrature of sqrt(gamma) (within the 4 x 4 trapezoid's error)."""
+    from scipy import integrate
+    a = 0.9
+    g = I.log_grid(10, 8, 1.5, 12.0)
+    Br, Bt = np.full(g.size, 2.0), np.full(g.size, 0.3)
+    d = I.injection_draws(g, 0.5, seed=1)
+    z, qm, w, al = _empty_store(4 * g.Nr * g.Nth)
+    r_lo, r_hi = 2.0, 6.0
+    z, qm, w, al, n1, K, fl = P.inject_pairs(1.0, a, g, z, qm, w, al, 0, z.shape[0], Br, Bt, r_lo, r_hi,
+                                             3.0, 5.0, 100.0, d)
+    F = fl.reshape(g.Nr, g.Nth)
+    rows = (g.rh >= r_lo) & (g.rh <= r_hi)
+    assert np.array_equal(F.any(axis=1), rows) and np.all(F[rows])
+    assert K == F.sum() and n1 == 2 * K
+    Om = _omega_h(a)
+    sg = lambda t, r: O.metric(1.0, a, [r], [t])[0, 12]
+    k = 0
+    for i in range(g.Nr):
+        for j in range(g.Nth):
+            if not F[i, j]:
+                continue
+            egj = abs(Om * (2.0 * math.cos(g.th[j]) - g.rh[i] * 0.3 * math.sin(g.th[j]))) / (4 * math.pi)
+            V = 2 * math.pi * integrate.dblquad(sg, g.rn[i], g.rn[i + 1], g.tn[j], g.tn[j + 1],
+                                                epsabs=0, epsrel=1e-11)[0]
+            for s in (0, 1):
+                Vw = w[k + s] * 100.0 * 2 / (5.0 * egj)
+                assert abs(Vw / V - 1) < 2e-3, (i, j, Vw / V)
+            assert qm[k] == -100.0 and qm[k + 1] == 100.0 and w[k] == w[k + 1]
+            k += 2
+
+
+def test_inject_stops_at_the_multiplicity():
+    """Re-injecting with no particle loss: with n0 = 1.25 and multiplicity 3
+    the density climbs 1.25, 2.5, 3.75 n_GJ, so exactly three calls inject
+    into each eligible cell and the fourth none; without spin (Omega_h = 0,
+    n_GJ = 0) nothing is injected."""
+    g = I.log_grid(8, 6, 1.5, 10.0)
+    Br, Bt = _radial_field(g)
+    d = I.injection_draws(g, 0.5, seed=2)
+    cap = 10 * g.Nr * g.Nth
+    z, qm, w, al = _empty_store(cap)
+    n = 0
+    counts = []
+    for call in range(4):
+        z, qm, w, al, n, K, fl = P.inject_pairs(1.0, 0.7, g, z, qm, w, al, n, cap, Br, Bt, 1.0, 20.0, 3.0, 1.25,
+                                                50.0, d)
+        counts.append(K)
+    C = g.Nr * g.Nth
+    assert counts == [C, C, C, 0]
+    z0, qm0, w0, al0 = _empty_store(cap)
+    _, _, _, _, n0_, K0, _ = P.inject_pairs(1.0, 0.0, g, z0, qm0, w0, al0, 0, cap, Br, Bt, 1.0, 20.0, 3.0, 1.25,
+                                            50.0, d)
+    assert K0 == 0 and n0_ == 0
+
+
+def test_inject_pair_kinematics():
+    """The two particles of a pair sit at one point inside their cell, carry
+    opposite q/m and equal weights, and their covariant momenta have the
+    drawn FIDO-frame magnitudes: gamma^ij u_i u_j = |uhat|^2 (Appendix A
+    inverse metric)."""
+    a = 0.99
+    g = I.log_grid(9, 7, 1.3, 8.0)
+    Br, Bt = _radial_field(g)
+    d = I.injection_draws(g, 0.5, seed=3)
+    cap = 2 * g.Nr * g.Nth
+    z, qm, w, al, n, K, fl = P.inject_pairs(1.0, a, g, *_empty_store(cap), 0, cap, Br, Bt, 0.0, 1e9, 3.0, 5.0,
+                                            100.0, d)
+    cells = np.flatnonzero(fl)
+    assert n == 2 * cells.size > 0
+    for k, c in enumerate(cells):
+        i, j = divmod(int(c), g.Nth)
+        e, p = z[2 * k], z[2 * k + 1]
+        assert np.array_equal(e[:3], p[:3])
+        assert g.rn[i] <= e[0] <= g.rn[i + 1] and g.tn[j] <= e[1] <= g.tn[j + 1] and 0 <= e[2] < 2 * math.pi
+        m = O.metric(1.0, a, [e[0]], [e[1]])[0]
+        for s, zz in ((0, e), (1, p)):
+            u = zz[3:]
+            norm = m[8] * u[0] ** 2 + 2 * m[9] * u[0] * u[2] + m[10] * u[1] ** 2 + m[11] * u[2] ** 2
+            uh = d[c, 3 + 3 * s: 6 + 3 * s]
+            assert abs(norm - uh @ uh) < 1e-12 * (1 + uh @ uh)
+        assert qm[2 * k] == -qm[2 * k + 1] and w[2 * k] == w[2 * k + 1] and al[2 * k] == al[2 * k + 1] == 1
+
+
+def test_inject_counts_alive_particles_of_the_cell_only():
+    """Existing alive particles fill (saturate) their cell; removed particles
+    count for nothing; cells outside [r_lo, r_hi] are never flagged."""
+    a = 0.9
+    g = I.log_grid(8, 6, 1.5, 10.0)
+    Br, Bt = _radial_field(g)
+    d = I.injection_draws(g, 0.5, seed=5)
+    cap = 4 * g.Nr * g.Nth + 10
+    z, qm, w, al = _empty_store(cap)
+    # particle 0 alive, huge weight, in cell (3, 2); particle 1 removed, huge weight, in cell (4, 1)
+    for p, (i, j), alive in ((0, (3, 2), 1), (1, (4, 1), 0)):
+        z[p, 0] = 0.5 * (g.rn[i] + g.rn[i + 1])
+        z[p, 1] = 0.5 * (g.tn[j] + g.tn[j + 1])
+        qm[p], w[p], al[p] = -10.0, 1e9, alive
+    r_lo, r_hi = g.rh[2], g.rh[5]
+    _, _, _, _, n, K, fl = P.inject_pairs(1.0, a, g, z, qm, w, al, 2, cap, Br, Bt, r_lo, r_hi, 3.0, 5.0, 100.0, d)
+    F = fl.reshape(g.Nr, g.Nth)
+    assert not F[3, 2] and F[4, 1]
+    assert not F[:2].any() and not F[6:].any()
+    assert F[2:6].sum() == 4 * g.Nth - 1 and K == F.sum() and n == 2 + 2 * K
+
+
+def test_inject_capacity_keeps_cell_order():
+    """With room for three pairs only, the pairs of the first three flagged
+    cells (cell order) are written, identical to the first three of an
+    unlimited call; the return value still counts every wanted pair."""
+    a = 0.9
+    g = I.log_grid(8, 6, 1.5, 10.0)
+    Br, Bt = _radial_field(g)
+    d = I.injection_draws(g, 0.5, seed=6)
+    big = P.inject_pairs(1.0, a, g, *_empty_store(200), 0, 200, Br, Bt, 0.0, 1e9, 3.0, 5.0, 100.0, d)
+    small = P.inject_pairs(1.0, a, g, *_empty_store(200), 0, 7, Br, Bt, 0.0, 1e9, 3.0, 5.0, 100.0, d)
+    assert small[4] == 6 and small[5] == big[5] > 3
+    assert np.array_equal(small[0][:6], big[0][:6]) and np.array_equal(small[2][:6], big[2][:6])
+    assert not small[0][6:].any()
