@@ -64,7 +64,7 @@ def parse():
                     help="corrector: restart a solve from the plain trial after this many iterations (0: never)")
     ap.add_argument("--train-gen-steps", type=int, default=10,
                     help="plain steps sampled for the training set")
-    ap.add_argument("--workload", default="push", choices=["push", "pic", "neutral", "batched", "clean"])
+    ap.add_argument("--workload", default="push", choices=["push", "pic", "neutral", "batched", "clean", "inject"])
     ap.add_argument("--clean-sweeps", type=int, default=500, help="Jacobi sweeps of --workload clean")
     ap.add_argument("--pic-grid", type=int, default=1024)
     ap.add_argument("--pic-ppc", type=int, default=64)
@@ -656,6 +656,50 @@ def run_div_clean(device, grid_n=1024, n_iter=500, reps=3):
             "sweep_achieved_gbs": bytes_sweep * n_iter / t / 1e9 if n_iter else None}
 
 
+def run_inject(device, grid_n=1024, ppc=64, reps=5):
+    """Sec. 3.3 pair injection on the plasma-filled Wald workload (a = 0.99,
+    grid_n^2 cells, ppc particles per cell): region r_h .. 6 M,
+    multiplicity 3, n0 = 5 (the paper's Wald-test values), into a store with
+    room for a pair in every cell; each timed call starts from the same
+    particle count.  The paper injects every 0.01 M (every 20 steps at
+    dt = 5e-4), so the amortised cost per step is reported beside it."""
+    import numpy as np
+    import torch
+    from paper_2602_07452_gb300 import fpic as F
+    from paper_2602_07452_gb300 import inputs as I
+    g = I.wald_grid(grid_n, PIC_A)
+    ctx = F.fpic_init_metric(1.0, PIC_A)
+    F.fpic_set_grid(ctx, g)
+    wald = [torch.zeros(g.size, dtype=torch.float64, device=device) for _ in range(6)]
+    F.fpic_init_wald(ctx, wald, B0)
+    d, q, w = I.cell_fill_draws(g, ppc, 0.5, seed=3, qm=QM, r_lo=1.02 * I.horizon(1.0, PIC_A))
+    n = d.shape[0]
+    C = g.Nr * g.Nth
+    st = F.Particles.empty(n + 2 * C, device)
+    head = st.head(n)
+    head.qm.copy_(torch.as_tensor(q, device=device))
+    head.w.fill_(PIC_W)
+    F.fpic_init_particles(ctx, head, F.FPIC_SEED_FIDO, torch.as_tensor(d, device=device))
+    del d, q, w
+    draws = torch.as_tensor(I.injection_draws(g, 0.5, seed=9).ravel(), device=device)
+    prm = F.fpic_inject_params(I.horizon(1.0, PIC_A), 6.0, 3.0, 5.0, QM, 0.0)
+    s = torch.cuda.current_stream(device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    F.fpic_inject_pairs(ctx, st, n, wald[3], wald[4], prm, draws)
+    ts = []
+    for _ in range(reps):
+        e0.record(s)
+        n_new, K, _ = F.fpic_inject_pairs(ctx, st, n, wald[3], wald[4], prm, draws)
+        e1.record(s)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) * 1e-3)
+    t = float(np.median(ts))
+    return {"workload": f"pair injection (multiplicity 3, n0 = 5, r_h..6M), plasma-filled Wald a={PIC_A}, "
+                        f"{grid_n}x{grid_n}, {ppc} particles/cell",
+            "particles": n, "pairs_injected": K, "ms_per_injection": 1e3 * t,
+            "amortised_ms_per_step_every_20": 1e3 * t / 20, "particles_per_s": n / t}
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -700,6 +744,16 @@ def main():
     import torch.distributed as dist
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if args.workload == "inject":
+        torch.cuda.set_device(local)
+        res = run_inject(torch.device("cuda", local), args.pic_grid, args.pic_ppc, reps=max(args.steps, 1))
+        if rank == 0:
+            print(json.dumps({"metric": "pair injection time", "value": res["ms_per_injection"], "unit": "ms",
+                              "n_gpus": ws, "steps": max(args.steps, 1), "warmup": 1,
+                              "ms_per_step": res["ms_per_injection"], "higher_is_better": False,
+                              "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                              "config": res}))
+        return 0
     if args.workload == "clean":
         torch.cuda.set_device(local)
         res = run_div_clean(torch.device("cuda", local), args.pic_grid, args.clean_sweeps, reps=max(args.steps, 1))
@@ -738,6 +792,7 @@ def main():
         line["neutral_rk4_alone"] = run_neutral(args, dev, 1 << 20, 20, pre_steps=2, scheme="RK4")
         line["batched"] = run_batched(args, dev, 0.1, 5)
         line["div_clean"] = run_div_clean(dev)
+        line["inject"] = run_inject(dev, 1024, 16)
     if rank == 0:
         if pool is not None:
             try:

@@ -332,6 +332,43 @@ int fpic_deposit(fpic_ctx *ctx, fpic_particles *p, double *rho, double *jr, doub
  * 2, NULL array, dt not finite). */
 int fpic_fdtd_step(fpic_ctx *ctx, fpic_fields *f, const fpic_fdtd_params *prm, int stage, void *stream);
 
+/* Pair injection parameters (Sec. 3.3, 3.4). */
+typedef struct {
+    double r_lo, r_hi;     /* cells whose centre radius rh[i] lies in [r_lo, r_hi] */
+    double multiplicity;   /* inject where n < multiplicity x n_GJ (the paper: 3, 10) */
+    double n0;             /* density of one injected pair in units of n_GJ (the paper: 5) */
+    double qm_e;           /* |q/m| of the pair particles (> 0): e- gets -qm_e, e+ +qm_e */
+    double B0pot;          /* Wald potential strength for H0 / D0 of the new particles
+                              (as in fpic_push_params; 0 on a PIC grid) */
+} fpic_inject_params;
+
+/* Pair injection (Sec. 3.3, 3.4): every cell whose centre radius lies in
+ * [r_lo, r_hi] receives one e-/e+ pair when its plasma density is below
+ * multiplicity x n_GJ, with e n = sum of w |q/m| over the cell's alive
+ * particles / the cell's proper volume V (2 pi x the 4 x 4 trapezoid of
+ * sqrt(gamma), Sec. 2.3) and e n_GJ = |Omega_h B^z| / 4 pi, Omega_h =
+ * a / (2 M r_h), B^z = B^r cos th - r sin th B^th at the cell centre (B^r
+ * averaged over the cell's r faces, B^th over its th faces).  The pair is
+ * placed at one point (r, th) = cell corner + (u_r, u_th) x cell size,
+ * ph = 2 pi u_ph, each particle with weight n0 (e n_GJ) V / (2 qm_e) and its
+ * FIDO-frame momentum mapped to u_i as in FPIC_SEED_FIDO; H0 = Hn, D0 set,
+ * alive = 1, cell written when p->cell is set.  Pairs are appended at
+ * p->n, p->n + 1, ... in cell order (c = i Nth + j), e- first, while they
+ * fit in capacity (the arrays of p must hold capacity entries).
+ *   Br, Bth : B^r, B^th (device, Yee layout) — the magnetic field of the step
+ *   draws   : device, 9 per cell c (u_r, u_th, u_ph in [0,1), e- FIDO
+ *             momentum, e+ FIDO momentum): the caller's random numbers
+ *   flags   : nullable device array of Nr Nth bytes, receives the decisions
+ *   wanted  : nullable host out, pairs wanted (including those that did not fit)
+ *   n_new   : host out, the new particle count (p->n itself is not changed)
+ * The injection is called every Delta t_inj by the caller (the paper:
+ * 0.01 M).  Synchronises the stream (the count is returned on the host).
+ * Errors: FPIC_EINVAL (NULL, no grid, capacity < n, bad parameters, more
+ * than 2^32 particles), FPIC_ECUDA. */
+int fpic_inject_pairs(fpic_ctx *ctx, fpic_particles *p, long long capacity, const double *Br, const double *Bth,
+                      const fpic_inject_params *prm, const double *draws, unsigned char *flags,
+                      long long *wanted, long long *n_new, void *stream);
+
 /* Divergence cleaning (Sec. 2.4, Eq. phi): solve
  *   (1/sqrtg) d_k (sqrtg gamma^kl d_l phi) = (1/sqrtg) d_j (sqrtg D^j) - 4 pi rho
  * at the integer nodes (i = 1 .. Nr-1, all j) by n_iter Jacobi sweeps from

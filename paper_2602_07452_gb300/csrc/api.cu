@@ -162,16 +162,8 @@ struct PInit {
 
 __device__ void set_energy(const BH& bh, const PInit& P, long long p, const double z[6], double B0pot)
 {
-    double s, c;
-    sincos(z[1], &s, &c);
-    Geo g;
-    geo_eval(bh, z[0], s, c, g);
-    const double ur = z[3], ut = z[4], up = z[5];
-    const double G2 = fma(ur, fma(g.gurr, ur, g.gurp * up), fma(ut, g.gutt * ut, fma(up, fma(g.gurp, ur, g.gupp * up), 1.0)));
-    const double kin = fma(g.alpha, sqrt(G2), -g.beta * ur);
-    const double qm = P.qm[p];
-    double pot = 0.0;
-    if (B0pot != 0.0 && qm != 0.0) pot = qm * B0pot * bh.a * z[0] * (1.0 + c * c) * g.irho2;
+    double kin, pot;
+    h_parts(bh, z, P.qm[p], B0pot, kin, pot);
     P.H0[p] = kin - pot;
     P.Hn[p] = kin - pot;
     P.D0[p] = fabs(kin) + fabs(pot);

@@ -295,6 +295,24 @@ __device__ __forceinline__ double eval_H_sc(const BH& bh, const double y[6], dou
     return H;
 }
 
+// The two parts of H at z (Sec. 3.1.2): kin = alpha Gamma - beta^r u_r and
+// pot = (q/m) A_0 of the Wald potential (B0pot = 0: none); H = kin - pot and
+// the error normaliser D0 = |kin| + |pot|.
+__device__ __forceinline__ void h_parts(const BH& bh, const double z[6], double qm, double B0pot, double& kin,
+                                        double& pot)
+{
+    double s, c;
+    sincos(z[1], &s, &c);
+    Geo g;
+    geo_eval(bh, z[0], s, c, g);
+    const double ur = z[3], ut = z[4], up = z[5];
+    const double G2 = fma(ur, fma(g.gurr, ur, g.gurp * up),
+                          fma(ut, g.gutt * ut, fma(up, fma(g.gurp, ur, g.gupp * up), 1.0)));
+    kin = fma(g.alpha, sqrt(G2), -g.beta * ur);
+    pot = 0.0;
+    if (B0pot != 0.0 && qm != 0.0) pot = qm * B0pot * bh.a * z[0] * (1.0 + c * c) * g.irho2;
+}
+
 __device__ __forceinline__ double eval_H(const BH& bh, const double y[6], double qm, double B0pot)
 {
     double s, c;

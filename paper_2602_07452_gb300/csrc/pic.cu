@@ -948,6 +948,146 @@ __global__ void k_clean_correct(CleanK k, const double* __restrict__ phi, double
 }  // namespace fpic
 
 namespace fpic {
+// ---------------------------------------------------------------------------
+// Pair injection (Sec. 3.3, 3.4)
+// ---------------------------------------------------------------------------
+// Every cell whose centre radius lies in [r_lo, r_hi] gets an e-/e+ pair
+// when e n < mult e n_GJ: e n = sum of w |q/m| over the cell's alive
+// particles (taken in particle-index order from the stable bucket order, so
+// the sum is the same on every run) over the cell's proper volume V,
+// e n_GJ = |Omega_h B^z| / 4 pi with B^z = B^r cos th - r sin th B^th at the
+// centre.  The pair sits at one point of the cell, each particle with the
+// weight that makes the pair's density n0 n_GJ; pairs are appended in cell
+// order, e- then e+, while they fit.
+struct InjK {
+    int Nr, Nth, ld;
+    GridDev G;
+    BH bh;
+    double Om, r_lo, r_hi, mult, n0, qm_e, B0pot;
+    const double *Br, *Bth, *draws;
+    const double *w, *qm;                    // existing particles
+    const uint32_t *off, *perm;              // cell buckets, particle-index order
+    uint32_t* flag;                          // per cell 0 / 1
+    uint8_t* flags8;                         // optional copy for the caller
+    double* wpair;                           // per cell: weight of each new particle
+};
+
+__global__ void k_inject_flag(InjK k)
+{
+    const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= (long long)k.Nr * k.Nth) return;
+    const int i = (int)(c / k.Nth), j = (int)(c - (long long)i * k.Nth);
+    uint32_t inj = 0;
+    double wp = 0.0;
+    const double rc = k.G.rh[i];
+    if (rc >= k.r_lo && rc <= k.r_hi) {
+        double S = 0.0;
+        for (uint32_t q = k.off[c]; q < k.off[c + 1]; ++q) {
+            const uint32_t p = k.perm[q];
+            S = __dadd_rn(S, __dmul_rn(k.w[p], fabs(k.qm[p])));   // product rounded, then added
+        }
+        const double V = 2.0 * M_PI * trap16_dev(k.bh, k.G.rn[i], k.G.rn[i + 1], k.G.tn[j], k.G.tn[j + 1]);
+        const size_t o = (size_t)i * k.ld + j;
+        const double br = 0.5 * (k.Br[o] + k.Br[o + k.ld]);
+        const double bt = 0.5 * (k.Bth[o] + k.Bth[o + 1]);
+        double sn, cs;
+        sincos(k.G.th[j], &sn, &cs);
+        const double Bz = br * cs - rc * sn * bt;
+        const double gj = fabs(k.Om * Bz) / (4.0 * M_PI);
+        inj = S / V < k.mult * gj ? 1u : 0u;
+        wp = k.n0 * gj * V / (2.0 * k.qm_e);
+    }
+    k.flag[c] = inj;
+    if (k.flags8) k.flags8[c] = (uint8_t)inj;
+    k.wpair[c] = wp;
+}
+
+__global__ void k_inject_write(InjK k, fpic_particles P, const uint32_t* __restrict__ pos, long long cap)
+{
+    const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= (long long)k.Nr * k.Nth || !k.flag[c]) return;
+    const long long m = P.n + 2LL * pos[c];
+    if (m + 2 > cap) return;
+    const int i = (int)(c / k.Nth), j = (int)(c - (long long)i * k.Nth);
+    const double* d = k.draws + 9 * c;
+    const double r = k.G.rn[i] + d[0] * (k.G.rn[i + 1] - k.G.rn[i]);
+    const double t = k.G.tn[j] + d[1] * (k.G.tn[j + 1] - k.G.tn[j]);
+    const double ph = 2.0 * M_PI * d[2];
+    double sn, cs;
+    sincos(t, &sn, &cs);
+    Geo g;
+    geo_eval(k.bh, r, sn, cs, g);
+    const double L11 = sqrt(g.grr), L31 = g.grp / L11, L22 = sqrt(g.gtt);
+    const double L33 = sqrt(fma(-L31, L31, g.gpp));
+    const double wp = k.wpair[c];
+    for (int s = 0; s < 2; ++s) {
+        const double* u = d + 3 + 3 * s;
+        const double z[6] = {r, t, ph, L11 * u[0], L22 * u[1], fma(L31, u[0], L33 * u[2])};
+        const long long q = m + s;
+        const double qm = s == 0 ? -k.qm_e : k.qm_e;
+        P.r[q] = z[0]; P.th[q] = z[1]; P.ph[q] = z[2];
+        P.ur[q] = z[3]; P.uth[q] = z[4]; P.uph[q] = z[5];
+        P.qm[q] = qm;
+        P.w[q] = wp;
+        P.alive[q] = 1;
+        P.scheme[q] = 0;
+        P.iters[q] = 0;
+        if (P.cell) P.cell[q] = (uint32_t)c;
+        double kin, pot;
+        h_parts(k.bh, z, qm, k.B0pot, kin, pot);
+        P.H0[q] = kin - pot;
+        P.Hn[q] = kin - pot;
+        P.D0[q] = fabs(kin) + fabs(pot);
+    }
+}
+}  // namespace fpic
+
+extern "C" int fpic_inject_pairs(fpic_ctx* c, fpic_particles* p, long long capacity, const double* Br,
+                                 const double* Bth, const fpic_inject_params* prm, const double* draws,
+                                 unsigned char* flags, long long* wanted, long long* n_new, void* stream)
+{
+    if (!c || !p || !Br || !Bth || !prm || !draws || !n_new)
+        return set_error(FPIC_EINVAL, "fpic_inject_pairs: NULL argument");
+    if (!c->has_grid) return set_error(FPIC_EINVAL, "fpic_inject_pairs: no grid set");
+    if (p->n < 0 || capacity < p->n) return set_error(FPIC_EINVAL, "fpic_inject_pairs: need 0 <= n <= capacity");
+    if (!particles_ok(p, true) || !p->w) return set_error(FPIC_EINVAL, "fpic_inject_pairs: NULL particle array");
+    if (!(prm->qm_e > 0.0) || !(prm->n0 > 0.0) || !(prm->multiplicity >= 0.0) || !(prm->r_lo <= prm->r_hi))
+        return set_error(FPIC_EINVAL, "fpic_inject_pairs: need qm_e > 0, n0 > 0, multiplicity >= 0, r_lo <= r_hi");
+    const long long n = p->n;
+    const long long C = (long long)c->Nr * c->Nth;
+    if (n + 2 * C > 0xffffffffLL) return set_error(FPIC_EINVAL, "fpic_inject_pairs: more than 2^32 particles");
+    FPIC_CUDA(cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    Work w;
+    int rc = work_layout(c, n > C + 2 ? n : C + 2, false, w);
+    if (rc) return rc;
+    FPIC_CUDA(cudaMemsetAsync(w.count, 0, 4 * ((size_t)C + 2), s));
+    FPIC_CUDA(cudaMemsetAsync(w.cursor, 0, 4 * ((size_t)C + 2), s));
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    if (n > 0) k_keys<<<nb, 256, 0, s>>>(c->G, p->r, p->th, p->alive, w.key, nullptr, w.count, n, (uint32_t)C);
+    rc = scan_u32(w.count, w.off, w.bsum, C + 1, s);
+    if (rc) return rc;
+    if (n > 0) k_scatter<<<nb, 256, 0, s>>>(w.key, w.off, w.cursor, w.perm, n);
+    k_bucket_rank<<<(unsigned)((C * 32 + 255) / 256), 256, 0, s>>>(w.off, w.perm, w.perm2, (uint32_t)C);
+    const double r_h = c->r_h;
+    InjK k{c->Nr, c->Nth, c->ld, c->G, c->bh, c->a / (2.0 * c->M * r_h), prm->r_lo, prm->r_hi, prm->multiplicity,
+           prm->n0, prm->qm_e, prm->B0pot, Br, Bth, draws, p->w, p->qm, w.off, w.perm2, w.flag, flags, w.tmp};
+    const unsigned cb = (unsigned)((C + 255) / 256);
+    k_inject_flag<<<cb, 256, 0, s>>>(k);
+    rc = scan_u32(w.flag, w.pos, w.bsum, C, s);
+    if (rc) return rc;
+    k_inject_write<<<cb, 256, 0, s>>>(k, *p, w.pos, capacity);
+    FPIC_CUDA(cudaGetLastError());
+    uint32_t K = 0;
+    FPIC_CUDA(cudaMemcpyAsync(&K, w.pos + C, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    FPIC_CUDA(cudaStreamSynchronize(s));
+    const long long room = (capacity - n) / 2;
+    if (wanted) *wanted = (long long)K;
+    *n_new = n + 2 * ((long long)K < room ? (long long)K : room);
+    return FPIC_OK;
+}
+
+namespace fpic {
 // Eq. (Pbz) on the sphere r = rh[i]: P = (1/2) sum_j (E_th H_ph - E_ph H_th)
 // dth_j with each product at the cell centre (rh[i], th_{j+1/2}) from its
 // staggered neighbours (E_th averaged in r, H_th in th, E_ph over the four

@@ -61,6 +61,11 @@ class fpic_push_stats(C.Structure):
 _P3 = _D * 3
 
 
+class fpic_inject_params(C.Structure):
+    _fields_ = [("r_lo", C.c_double), ("r_hi", C.c_double), ("multiplicity", C.c_double), ("n0", C.c_double),
+                ("qm_e", C.c_double), ("B0pot", C.c_double)]
+
+
 class fpic_fields(C.Structure):
     _fields_ = [("B0", _P3), ("B1", _P3), ("D0", _P3), ("D1", _P3), ("j0", _P3), ("rho0", _D),
                 ("j1", _P3), ("rho1", _D), ("E", _P3), ("H", _P3), ("Bh", _P3), ("Dw", _P3)]
@@ -132,6 +137,9 @@ _SIGS = {
     "fpic_init_split_monopole": (C.c_int, [C.c_void_p, C.POINTER(_D), C.c_double, C.c_double, C.c_void_p]),
     "fpic_bz_power": (C.c_int, [C.c_void_p, C.POINTER(fpic_fields), C.c_int, C.c_void_p, C.c_void_p]),
     "fpic_div_clean": (C.c_int, [C.c_void_p, C.POINTER(_D), C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "fpic_inject_pairs": (C.c_int, [C.c_void_p, C.POINTER(fpic_particles), C.c_longlong, C.c_void_p, C.c_void_p,
+                                    C.POINTER(fpic_inject_params), C.c_void_p, C.c_void_p,
+                                    C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.c_void_p]),
     "fpic_get_tuning": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
     "fpic_push_noalloc": (C.c_int, [C.c_double, C.c_double, C.POINTER(fpic_particles),
                                     C.POINTER(fpic_push_params), C.POINTER(fpic_push_stats), C.c_void_p]),
@@ -209,6 +217,10 @@ class Particles:
     def n(self):
         return self.r.numel()
 
+    def head(self, n):
+        """The first n particles (views of the same storage)."""
+        return Particles(*[getattr(self, f)[:n] for f in self.__dataclass_fields__])
+
     def state(self):
         return torch.stack([self.r, self.th, self.ph, self.ur, self.uth, self.uph], dim=1)
 
@@ -251,6 +263,7 @@ def fpic_set_grid(ctx: Ctx, grid) -> None:
     import numpy as np
     arrs = [np.ascontiguousarray(x, dtype=np.float64) for x in (grid.rn, grid.rh, grid.tn, grid.th)]
     _check(lib().fpic_set_grid(ctx.handle, grid.Nr, grid.Nth, *[a.ctypes.data_as(_D) for a in arrs]))
+    ctx.cells = grid.Nr * grid.Nth
 
 
 _FIELDS_CACHE = {}
@@ -371,6 +384,21 @@ def fpic_bz_power(ctx: Ctx, f: "Fields", i: int, stream=None) -> torch.Tensor:
     s = f.struct()
     _check(lib().fpic_bz_power(ctx.handle, C.byref(s), i, out.data_ptr(), _stream(stream)))
     return out
+
+
+def fpic_inject_pairs(ctx: Ctx, store: "Particles", n: int, Br: torch.Tensor, Bth: torch.Tensor,
+                      prm: fpic_inject_params, draws: torch.Tensor, want_flags: bool = False, stream=None):
+    """Sec. 3.3 / 3.4 pair injection into a capacity-sized particle store whose
+    first n entries are in use.  Returns (n_new, pairs wanted, flags or None);
+    store.head(n_new) is the particle set afterwards."""
+    st = fpic_particles.from_buffer_copy(store.struct())
+    st.n = int(n)
+    flags = torch.zeros(ctx.cells, dtype=torch.uint8, device=Br.device) if want_flags else None
+    wanted, n_new = C.c_longlong(0), C.c_longlong(0)
+    _check(lib().fpic_inject_pairs(ctx.handle, C.byref(st), store.n, Br.data_ptr(), Bth.data_ptr(), C.byref(prm),
+                                   draws.data_ptr(), flags.data_ptr() if flags is not None else None,
+                                   C.byref(wanted), C.byref(n_new), _stream(stream)))
+    return int(n_new.value), int(wanted.value), flags
 
 
 def fpic_div_clean(ctx: Ctx, D, rho: torch.Tensor, n_iter: int = 500, want_phi: bool = False, stream=None):

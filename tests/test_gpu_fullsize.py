@@ -125,3 +125,51 @@ def test_fullsize_div_clean():
         assert np.abs(got - Dc[k]).max() <= 1e-10 * sc, k
     got = phi.cpu().numpy()
     assert np.abs(got - phio).max() <= 1e-10 * np.abs(phio).max()
+
+
+def test_fullsize_pair_injection():
+    """Sec. 3.3 injection on the 1024 x 1024 plasma grid (a = 0.99, 16
+    particles per cell, 1.7e7 particles; the benchmark times 64 per cell),
+    region r_h .. 6 M, multiplicity 3, n0 = 5, in the benchmark's launch
+    configuration: every cell's decision against the oracle's (bit-exact),
+    the counts, and a sample of 4096 appended pairs (1e-12)."""
+    cuda_or_skip()
+    F = fpic()
+    a = 0.99
+    g = I.wald_grid(1024, a)
+    d, q, w = I.cell_fill_draws(g, 16, 0.5, seed=3, qm=QM, r_lo=1.02 * I.horizon(1.0, a))
+    z = O.seed_fido(1.0, a, d)
+    n = z.shape[0]
+    w = np.full(n, 1e-6)
+    alive = np.ones(n, np.uint8)
+    Fw = O.wald_on_grid(a, 1.0, g)
+    dr = I.injection_draws(g, 0.5, seed=9)
+    C = g.Nr * g.Nth
+    cap = n + 2 * C
+    r_lo, r_hi = I.horizon(1.0, a), 6.0
+    ctx = F.fpic_init_metric(1.0, a)
+    F.fpic_set_grid(ctx, g)
+    st = F.Particles.empty(cap)
+    st.head(n).set_state(torch.as_tensor(z, device="cuda"))
+    st.qm[:n].copy_(torch.as_tensor(q, device="cuda"))
+    st.w[:n].fill_(1e-6)
+    st.alive[:n].fill_(1)
+    prm = F.fpic_inject_params(r_lo, r_hi, 3.0, 5.0, QM, 0.0)
+    n_g, K_g, f_g = F.fpic_inject_pairs(ctx, st, n, torch.as_tensor(Fw[3], device="cuda"),
+                                        torch.as_tensor(Fw[4], device="cuda"), prm,
+                                        torch.as_tensor(dr.ravel(), device="cuda"), want_flags=True)
+    zo = np.zeros((cap, 6)); zo[:n] = z
+    qo = np.zeros(cap); qo[:n] = q
+    wo = np.zeros(cap); wo[:n] = w
+    ao = np.zeros(cap, np.uint8); ao[:n] = 1
+    zo, qo, wo, ao, n_o, K_o, f_o = P.inject_pairs(1.0, a, g, zo, qo, wo, ao, n, cap, Fw[3], Fw[4], r_lo, r_hi,
+                                                   3.0, 5.0, QM, dr)
+    assert K_g == K_o > 0 and n_g == n_o
+    assert np.array_equal(f_g.cpu().numpy(), f_o)
+    rng = np.random.default_rng(0)
+    ks = rng.choice(K_o, size=min(4096, K_o), replace=False)
+    idx = np.sort(np.r_[n + 2 * ks, n + 2 * ks + 1])
+    zg = st.state()[torch.as_tensor(idx, device="cuda")].cpu().numpy()
+    assert (np.abs(zg - zo[idx]) / (np.abs(zo[idx]) + 1)).max() <= 1e-12
+    wg = st.w[torch.as_tensor(idx, device="cuda")].cpu().numpy()
+    assert np.allclose(wg, wo[idx], rtol=1e-12, atol=0)

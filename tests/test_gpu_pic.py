@@ -251,3 +251,93 @@ def test_div_clean_matches_oracle(F, a, Nr, Nth, n_iter):
         assert torch.equal(Dd[k], Dd2[k])
     with pytest.raises(F.FpicError):
         F.fpic_div_clean(ctx, Dd, dev(rho), -1)
+
+
+def _inject_case(g, a, n, seed, dead_frac=0.1):
+    """Plasma particles (unit weights, some removed), the Wald B^r, B^th, the
+    injection draws, and a multiplicity placing about half of the eligible
+    cells below it (calibrated from the particle counts, not from the
+    library)."""
+    z, q, w, alive = _plasma(g, n, a, seed, dead_frac)
+    w = np.ones(n)
+    Fw = O.wald_on_grid(a, 1.0, g)
+    d = I.injection_draws(g, 0.5, seed=seed + 1)
+    return z, q, w, alive, Fw[3], Fw[4], d
+
+
+def _gpu_store(F, z, q, w, alive, cap):
+    import torch
+    n = z.shape[0]
+    st = F.Particles.empty(cap)
+    zz = np.zeros((cap, 6)); zz[:n] = z
+    st.set_state(dev(zz))
+    for name, x in (("qm", q), ("w", w)):
+        v = np.zeros(cap); v[:n] = x
+        getattr(st, name).copy_(dev(v))
+    al = np.zeros(cap, np.uint8); al[:n] = alive
+    st.alive.copy_(torch.as_tensor(al, device="cuda"))
+    return st
+
+
+@pytest.mark.parametrize("a,Nr,Nth,n,extra", [(0.9, 40, 48, 20011, None), (0.99, 33, 70, 5003, 5),
+                                              (0.9, 24, 20, 0, None)])
+def test_inject_pairs_matches_oracle(F, a, Nr, Nth, n, extra):
+    """Sec. 3.3 / 3.4 injection: the per-cell decisions bit-exact (cells
+    within 1e-9 of the threshold excluded), the wanted count and the new
+    particle count equal, every appended particle's state, q/m, weight,
+    H0, D0 within 1e-12 of the oracle (cell order, e- then e+), the cell
+    index written, the existing particles untouched; `extra` limits the
+    capacity to that many pairs (cell-order truncation)."""
+    import torch
+    g = I.log_grid(Nr, Nth, 1.2 * I.horizon(1.0, a), 20.0)
+    ctx = F.fpic_init_metric(1.0, a)
+    F.fpic_set_grid(ctx, g)
+    z, q, w, alive, Br, Bt, d = _inject_case(g, a, max(n, 1), 40 + Nr)
+    z, q, w, alive = z[:n], q[:n], w[:n], alive[:n]
+    r_lo, r_hi, n0, qm_e = I.horizon(1.0, a), 6.0, 5.0, 100.0
+    C = g.Nr * g.Nth
+    # calibration: weight per new particle at n0 = 1 -> per-cell threshold on sum w |q/m|
+    zc, qc, wc, ac, nc, Kc, fc = P.inject_pairs(1.0, a, g, np.zeros((2 * C, 6)), np.zeros(2 * C), np.zeros(2 * C),
+                                                np.zeros(2 * C, np.uint8), 0, 2 * C, Br, Bt, r_lo, r_hi, 1e300,
+                                                1.0, qm_e, d)
+    S = np.zeros(C)
+    if n:
+        cell = O.cell_index(g, z[:, 0], z[:, 1]).astype(np.int64)
+        np.add.at(S, cell[alive == 1], (w * np.abs(q))[alive == 1])
+    thr1 = np.zeros(C)
+    thr1[np.flatnonzero(fc)] = 2 * qm_e * wc[0:2 * Kc:2]            # = V e n_GJ per cell
+    el = thr1 > 0
+    ratio = S[el] / thr1[el]
+    mult = float(np.median(ratio)) * (1 + 1e-6) if n else 3.0
+    cap = n + (2 * C if extra is None else 2 * extra + 1)
+    zo, qo, wo, ao, n_o, K_o, f_o = P.inject_pairs(1.0, a, g, np.vstack([z, np.zeros((cap - n, 6))]),
+                                                   np.r_[q, np.zeros(cap - n)], np.r_[w, np.zeros(cap - n)],
+                                                   np.r_[alive, np.zeros(cap - n, np.uint8)], n, cap, Br, Bt,
+                                                   r_lo, r_hi, mult, n0, qm_e, d)
+    st = _gpu_store(F, z, q, w, alive, cap)
+    prm = F.fpic_inject_params(r_lo, r_hi, mult, n0, qm_e, 0.0)
+    n_g, K_g, f_g = F.fpic_inject_pairs(ctx, st, n, dev(Br), dev(Bt), prm, dev(d.ravel()), want_flags=True)
+    f_g = f_g.cpu().numpy()
+    tie = np.zeros(C, bool)
+    tie[el] = np.abs(S[el] / (mult * thr1[el]) - 1) < 1e-9
+    assert tie.sum() <= 1
+    assert np.array_equal(f_g[~tie], f_o[~tie])
+    assert K_g == K_o and n_g == n_o
+    if n:
+        assert 0 < f_o[el].sum() < el.sum()
+    h = st.head(n_g)
+    zg = h.state().cpu().numpy()
+    assert np.array_equal(zg[:n], z)
+    new = slice(n, n_g)
+    err = (np.abs(zg[new] - zo[new]) / (np.abs(zo[new]) + 1)).max() if n_g > n else 0.0
+    assert err <= 1e-12
+    assert np.array_equal(h.qm.cpu().numpy()[new], qo[new])
+    assert np.allclose(h.w.cpu().numpy()[new], wo[new], rtol=1e-12, atol=0)
+    assert np.all(h.alive.cpu().numpy()[new] == 1)
+    H, _, D0 = O.hamiltonian(1.0, a, 0.0, zo[new], qo[new])
+    assert np.allclose(h.H0.cpu().numpy()[new], H, rtol=1e-12, atol=1e-14)
+    assert np.allclose(h.D0.cpu().numpy()[new], D0, rtol=1e-12, atol=1e-14)
+    cells = np.repeat(np.flatnonzero(f_o)[:(n_g - n) // 2], 2)
+    assert np.array_equal(h.cell.cpu().numpy()[new].view(np.uint32), cells.astype(np.uint32))
+    with pytest.raises(F.FpicError):
+        F.fpic_inject_pairs(ctx, st, cap + 1, dev(Br), dev(Bt), prm, dev(d.ravel()))
