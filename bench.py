@@ -64,7 +64,7 @@ def parse():
                     help="corrector: restart a solve from the plain trial after this many iterations (0: never)")
     ap.add_argument("--train-gen-steps", type=int, default=10,
                     help="plain steps sampled for the training set")
-    ap.add_argument("--workload", default="push", choices=["push", "pic", "neutral", "batched", "clean", "inject"])
+    ap.add_argument("--workload", default="push", choices=["push", "pic", "neutral", "batched", "clean", "inject", "adaptive"])
     ap.add_argument("--clean-sweeps", type=int, default=500, help="Jacobi sweeps of --workload clean")
     ap.add_argument("--pic-grid", type=int, default=1024)
     ap.add_argument("--pic-ppc", type=int, default=64)
@@ -612,6 +612,91 @@ def run_pic(args, device, grid_n, ppc, steps, rank=0):
     }
 
 
+def run_adaptive(device, n=1 << 20, steps=20, ratios=(1, 2, 4)):
+    """Adaptive per-scheme steps (Sec. 3.1.2, Tab. C.2) on the charged Wald
+    workload: Hyb1 with dt = 1e-3 for the RK4 trials and dt_implicit =
+    ratio x dt for the IMR steps, from the same start state.  Reports the
+    step time, the implicit share, the particle time advanced per second
+    (sum of every particle's step over the wall time) and max |dH| / D0."""
+    import torch
+    F, g, ctx, fields, p = setup(n, 0, device)
+    snap = _snapshot(p)
+    s = torch.cuda.current_stream(device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"workload": f"charged Wald test particles, a={A_SPIN}, {n} particles, Hyb1 RK4 dt={DT} <-> IMR dt_implicit",
+           "steps": steps, "runs": []}
+    for ratio in ratios:
+        _restore(p, snap)
+        t = torch.zeros(n, dtype=torch.float64, device=device)
+        prm = F.push_params(DT, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=HYB1_THR, r_max=float(g.rn[-1]),
+                            B0pot=B0, dt_implicit=ratio * DT, t=t)
+        for _ in range(3):
+            F.fpic_push(ctx, p, fields, prm)
+        torch.cuda.synchronize()
+        t.zero_()
+        tot, impl, alive = 0.0, 0, 0
+        for _ in range(steps):
+            e0.record(s)
+            st = F.fpic_push(ctx, p, fields, prm, stats=True)
+            e1.record(s)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1) * 1e-3
+            impl += st["n_implicit"]
+            alive += st["n_alive_before"]
+        out["runs"].append({"dt_implicit": ratio * DT, "ms_per_step": 1e3 * tot / steps,
+                            "implicit_fraction": impl / max(alive, 1),
+                            "particle_time_per_s": float(t.sum().item()) / tot,
+                            "max_dH": _max_dH(F, ctx, p)})
+    return out
+
+
+def run_adaptive_neutral(device, n=1 << 18, steps=20, pre_steps=20, K=32):
+    """Tab. C.2's a = 0.995 parameters on candidate-seeded bound geodesics:
+    RK4 alone (dt 0.05), the discrete-gradient scheme alone (dt 0.1), and
+    Hyb2 (Ht_max = 1e-12) with the discrete-gradient partner at its own
+    step 0.05 and at the adaptive step 0.1.  Reports particle time advanced
+    per second and the energy drift max |H - H0| / |H0| after the run."""
+    import torch
+    from paper_2602_07452_gb300 import fpic as F
+    from paper_2602_07452_gb300 import inputs as I
+    a = 0.995
+    ctx = F.fpic_init_metric(1.0, a)
+    cand = torch.as_tensor(I.orbit_candidates(n, K=K, seed=5), device=device)
+    p = F.Particles.empty(n, device)
+    F.fpic_init_particles(ctx, p, F.FPIC_SEED_ORBIT, cand, K=K)
+    del cand
+    snap = _snapshot(p)
+    s = torch.cuda.current_stream(device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    runs = []
+    for name, sch, dt, dti in (("RK4", F.FPIC_RK4, 0.05, 0.0), ("Ham", F.FPIC_HAM, 0.1, 0.0),
+                               ("Hyb2", F.FPIC_HYB2, 0.05, 0.05), ("Hyb2 adaptive", F.FPIC_HYB2, 0.05, 0.1)):
+        _restore(p, snap)
+        t = torch.zeros(n, dtype=torch.float64, device=device)
+        prm = F.push_params(dt, scheme=sch, implicit=F.FPIC_HAM, thr=1e-12, dt_implicit=dti, t=t)
+        for _ in range(pre_steps):
+            F.fpic_push(ctx, p, None, prm)
+        torch.cuda.synchronize()
+        t.zero_()
+        tot, impl, alive = 0.0, 0, 0
+        for _ in range(steps):
+            e0.record(s)
+            st = F.fpic_push(ctx, p, None, prm, stats=True)
+            e1.record(s)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1) * 1e-3
+            impl += st["n_implicit"]
+            alive += st["n_alive_before"]
+        H, _ = F.fpic_hamiltonian(ctx, p, B0pot=0.0)
+        al = p.alive.bool()
+        drift = float(((H - p.H0).abs() / p.H0.abs())[al].max().item()) if bool(al.any()) else 0.0
+        runs.append({"scheme": name, "dt": dt, "dt_implicit": dti or None, "ms_per_step": 1e3 * tot / steps,
+                     "implicit_fraction": impl / max(alive, 1),
+                     "particle_time_per_s": float(t.sum().item()) / tot, "max_dH_over_H0": drift})
+    return {"workload": f"neutral geodesics, Kerr a={a}, {n} candidate-seeded particles, Tab. C.2 a.995 steps",
+            "steps": steps, "steps_before_measurement": pre_steps, "runs": runs}
+
+
 def run_div_clean(device, grid_n=1024, n_iter=500, reps=3):
     """Sec. 2.4 divergence cleaning (Eq. phi, n_iter Jacobi sweeps and the
     correction) of a Wald D perturbed by noise against a random rho on the
@@ -744,6 +829,17 @@ def main():
     import torch.distributed as dist
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if args.workload == "adaptive":
+        torch.cuda.set_device(local)
+        res = run_adaptive(torch.device("cuda", local), args.n, max(args.steps, 1))
+        res["neutral"] = run_adaptive_neutral(torch.device("cuda", local))
+        if rank == 0:
+            r0 = res["runs"][0]
+            print(json.dumps({"metric": "particle time advanced per second", "value": r0["particle_time_per_s"],
+                              "unit": "particle-M/s", "n_gpus": ws, "steps": res["steps"], "warmup": 3,
+                              "ms_per_step": r0["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+                              "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": res}))
+        return 0
     if args.workload == "inject":
         torch.cuda.set_device(local)
         res = run_inject(torch.device("cuda", local), args.pic_grid, args.pic_ppc, reps=max(args.steps, 1))
@@ -792,6 +888,8 @@ def main():
         line["neutral_rk4_alone"] = run_neutral(args, dev, 1 << 20, 20, pre_steps=2, scheme="RK4")
         line["batched"] = run_batched(args, dev, 0.1, 5)
         line["div_clean"] = run_div_clean(dev)
+        line["adaptive_dt"] = run_adaptive(dev)
+        line["adaptive_dt_neutral"] = run_adaptive_neutral(dev)
         line["inject"] = run_inject(dev, 1024, 16)
     if rank == 0:
         if pool is not None:

@@ -87,7 +87,15 @@ typedef struct {
  *               guesses and scheme logits (see fpic_mlp_infer); NULL = plain
  *   events    : nullable array of 4 cudaEvent_t recorded on the stream
  *               around the explicit kernel ([0], [1]) and the implicit
- *               kernel ([2], [3]) for per-kernel timing; NULL = none */
+ *               kernel ([2], [3]) for per-kernel timing; NULL = none
+ *   dt_implicit: step of the hybrid's implicit partner (adaptive steps,
+ *               Sec. 3.1.2 and Tab. C.2: Delta t_Ham != Delta t_RK4); a
+ *               rejected particle is advanced from z^n by dt_implicit, its
+ *               solve starting from z^n + (z_RK4 - z^n) dt_implicit / dt.
+ *               0 = dt.  Same sign as dt.  Pure schemes ignore it; the
+ *               learned guess needs 0 or dt.
+ *   t         : nullable device array (n doubles): each alive particle's
+ *               time, advanced by the step it took (dt or dt_implicit) */
 typedef struct {
     double dt;
     int scheme;
@@ -100,6 +108,8 @@ typedef struct {
     double B0pot;
     const float *guess;
     void *const *events;
+    double dt_implicit;
+    double *t;
 } fpic_push_params;
 
 /* Host-side counters of one push (filled only when a pointer is passed;

@@ -61,7 +61,7 @@ class PushParams(C.Structure):
                 ("field_kind", C.c_int), ("B0field", C.c_double), ("dt", C.c_double),
                 ("scheme", C.c_int), ("implicit_kind", C.c_int), ("thr", C.c_double),
                 ("tol", C.c_double), ("max_iter", C.c_int), ("r_h", C.c_double),
-                ("r_max", C.c_double), ("dg_eps", C.c_double)]
+                ("r_max", C.c_double), ("dg_eps", C.c_double), ("dt_imp", C.c_double)]
 
 
 _D = C.POINTER(C.c_double)
@@ -205,11 +205,11 @@ def wald_on_grid(a, B0, g):
 
 def push_params(M=1.0, a=0.9, B0pot=0.0, field_kind=FIELD_NONE, B0field=0.0, dt=0.01,
                 scheme=RK4, implicit_kind=IMR, thr=1e-12, tol=1e-14, max_iter=50,
-                r_h=None, r_max=1e300, dg_eps=1e-10):
+                r_h=None, r_max=1e300, dg_eps=1e-10, dt_imp=0.0):
     if r_h is None:
         r_h = M + np.sqrt(M * M - a * a)
     return PushParams(M, a, B0pot, field_kind, B0field, dt, scheme, implicit_kind, thr, tol,
-                      max_iter, r_h, r_max, dg_eps)
+                      max_iter, r_h, r_max, dg_eps, dt_imp)
 
 
 def push(p: PushParams, z, qm, H0, D0, Hn, alive, g=None, F=None):

@@ -341,6 +341,7 @@ typedef struct {
     int max_iter;          /* implicit iteration cap */
     double r_h, r_max;     /* particle removal radii */
     double dg_eps;         /* discrete-gradient increment threshold */
+    double dt_imp;         /* step of the implicit partner of a hybrid (0: dt) */
 } or_push_params;
 
 typedef struct {
@@ -402,14 +403,14 @@ static int converged(const double *a, const double *b, double tol)
  * the midpoint (Eq. imr1), and the "Newton" of the text as this fixed-point
  * update (the one the equation shows).  Returns the iteration count, or
  * -max_iter if the cap was reached. */
-static int step_imr(const or_ctx *c, const double *z0, const double *guess, double *z1)
+static int step_imr(const or_ctx *c, double h, const double *z0, const double *guess, double *z1)
 {
     double zk[6], y[6], f[6], zn[6];
     memcpy(zk, guess, sizeof zk);
     for (int k = 1; k <= c->p->max_iter; ++k) {
         for (int i = 0; i < 6; ++i) y[i] = 0.5 * (z0[i] + zk[i]);
         F_eval(c, y, f);
-        for (int i = 0; i < 6; ++i) zn[i] = z0[i] + c->p->dt * f[i];
+        for (int i = 0; i < 6; ++i) zn[i] = z0[i] + h * f[i];
         int ok = converged(zn, zk, c->p->tol);
         memcpy(zk, zn, sizeof zk);
         if (ok) { memcpy(z1, zk, sizeof zk); return k; }
@@ -496,15 +497,15 @@ static void dg_grad(double M, double a, const double *z0, const double *z1, doub
 /* Sec. 2.2.3: discrete-gradient Hamiltonian step for geodesics,
  * dx/dt = D_u H, du/dt = -D_x H, solved by fixed-point iteration on z^{n+1}
  * (same stop rule as the IMR). */
-static int step_ham(const or_ctx *c, const double *z0, const double *guess, double *z1)
+static int step_ham(const or_ctx *c, double h, const double *z0, const double *guess, double *z1)
 {
     double zk[6], G[6], zn[6];
     memcpy(zk, guess, sizeof zk);
     for (int k = 1; k <= c->p->max_iter; ++k) {
         dg_grad(c->p->M, c->p->a, z0, zk, c->p->dg_eps, G);
         for (int i = 0; i < 3; ++i) {
-            zn[i] = z0[i] + c->p->dt * G[3 + i];
-            zn[3 + i] = z0[3 + i] - c->p->dt * G[i];
+            zn[i] = z0[i] + h * G[3 + i];
+            zn[3 + i] = z0[3 + i] - h * G[i];
         }
         int ok = converged(zn, zk, c->p->tol);
         memcpy(zk, zn, sizeof zk);
@@ -552,10 +553,10 @@ static int push_one(const or_ctx *c, double *z, double H0, double D0, double *Hn
     if (p->scheme == OR_RK4) {
         step_rk4(c, z0, z1);
     } else if (p->scheme == OR_IMR) {
-        it = step_imr(c, z0, z0, z1);
+        it = step_imr(c, p->dt, z0, z0, z1);
         implicit = 1;
     } else if (p->scheme == OR_HAM) {
-        it = step_ham(c, z0, z0, z1);
+        it = step_ham(c, p->dt, z0, z0, z1);
         implicit = 1;
     } else {
         step_rk4(c, z0, trial);
@@ -571,9 +572,22 @@ static int push_one(const or_ctx *c, double *z, double H0, double D0, double *Hn
         if (accept) {
             memcpy(z1, trial, sizeof z1);
         } else {
+            /* Adaptive step (Sec. 3.1.2, Tab. C.2): the implicit partner
+             * takes its own step dt_imp.  Reading: its iteration starts from
+             * the trial's increment scaled to that step,
+             * z^n + (z_RK4 - z^n) dt_imp / dt (the trial itself when the
+             * steps are equal). */
             implicit = 1;
-            if (p->implicit_kind == OR_HAM) it = step_ham(c, z0, trial, z1);
-            else it = step_imr(c, z0, trial, z1);
+            const double hi = p->dt_imp > 0.0 ? p->dt_imp : p->dt;
+            double guess[6];
+            if (hi == p->dt) {
+                memcpy(guess, trial, sizeof guess);
+            } else {
+                const double ratio = hi / p->dt;
+                for (int i = 0; i < 6; ++i) guess[i] = z0[i] + (trial[i] - z0[i]) * ratio;
+            }
+            if (p->implicit_kind == OR_HAM) it = step_ham(c, hi, z0, guess, z1);
+            else it = step_imr(c, hi, z0, guess, z1);
         }
     }
     *Hn = ham(&bh, c->qm, z1);

@@ -44,6 +44,8 @@ struct PushK {
     const RunK* runs;       // batched push: run table (nruns > 0), particle ranges [begin, end)
     int nruns;
     double dt, thr, tol, dg_eps;
+    double dt_imp;          // step of the implicit solves (the hybrid's partner: fpic_push_params.dt_implicit)
+    double* t;              // nullable per-particle time, advanced by the step each particle took
     int scheme, max_iter;
     long long n;
     long long p_begin, p_end;   // explicit pass over [p_begin, p_end) (p_end 0: all n)
@@ -259,8 +261,10 @@ __global__ void __launch_bounds__(128) k_explicit(const __grid_constant__ PushK 
     }
     const unsigned act = __activemask();
     const unsigned rej = __ballot_sync(act, !accept);
-    if (accept && !finish(R, k.P, p, y, H1, 0, 0))
-        atomicAdd((unsigned long long*)&k.cnt[CNT_REMOVED], 1ull);
+    if (accept) {
+        if (!finish(R, k.P, p, y, H1, 0, 0)) atomicAdd((unsigned long long*)&k.cnt[CNT_REMOVED], 1ull);
+        if (k.t) k.t[p] += dt;
+    }
     if (rej) {
         const int leader = __ffs(act) - 1;
         unsigned long long base = 0;
@@ -270,8 +274,17 @@ __global__ void __launch_bounds__(128) k_explicit(const __grid_constant__ PushK 
         if (!accept) {
             const unsigned long long idx = base + __popc(rej & lanemask_lt());
             k.queue[idx] = (uint32_t)p;
+            if (k.dt_imp == dt) {
 #pragma unroll
-            for (int i = 0; i < 6; ++i) k.guess[(size_t)i * k.n + p] = y[i];
+                for (int i = 0; i < 6; ++i) k.guess[(size_t)i * k.n + p] = y[i];
+            } else {
+                // adaptive step: the trial's increment scaled to the implicit step
+                // (rounded product, then sum: the same value as the plain C form)
+                const double ratio = k.dt_imp / dt;
+#pragma unroll
+                for (int i = 0; i < 6; ++i)
+                    k.guess[(size_t)i * k.n + p] = __dadd_rn(z0[i], __dmul_rn(__dsub_rn(y[i], z0[i]), ratio));
+            }
             k.sc0[p] = s0;
             k.sc0[k.n + p] = c0;
             if (MODE == 2) {
@@ -411,7 +424,7 @@ __global__ void __launch_bounds__(128, 4) k_imr(const __grid_constant__ PushK k,
             ++n_ev;
             double zn[6];
 #pragma unroll
-            for (int i = 0; i < 6; ++i) zn[i] = fma(k.dt, f[i], z0[i]);
+            for (int i = 0; i < 6; ++i) zn[i] = fma(k.dt_imp, f[i], z0[i]);
             const bool ok = conv6(zn, zk, k.tol);
 #pragma unroll
             for (int i = 0; i < 6; ++i) zk[i] = zn[i];
@@ -480,6 +493,7 @@ __global__ void __launch_bounds__(256) k_imr_finish(const __grid_constant__ Push
         const RunK& R = BATCHED ? k.runs[run_of(k.runs, k.nruns, p)] : k.run;
         const double H = eval_H_sc(R.bh, z, sn, cn, k.P.qm[p], R.B0pot);
         if (!finish(R, k.P, p, z, H, 1, k.P.iters[p])) ++n_rm;
+        if (k.t) k.t[p] += k.dt_imp;
     }
     warp_add(&k.cnt[CNT_REMOVED], n_rm, 0xffffffffu);
 }
@@ -608,11 +622,11 @@ __global__ void __launch_bounds__(128) k_dg(PushK k, int all_mode)
             const double Gp = (2.0 * f00 + gh_dHdup(m10, U1, V0, P) + gh_dHdup(m01, U0, V1, P) +
                                2.0 * gh_dHdup(m11, U1, V1, P)) / 6.0;
             double zn[6];
-            zn[0] = fma(k.dt, Gu, z0[0]);
-            zn[1] = fma(k.dt, Gv, z0[1]);
-            zn[2] = fma(k.dt, Gp, z0[2]);
-            zn[3] = fma(-k.dt, Gr, z0[3]);
-            zn[4] = fma(-k.dt, Gt, z0[4]);
+            zn[0] = fma(k.dt_imp, Gu, z0[0]);
+            zn[1] = fma(k.dt_imp, Gv, z0[1]);
+            zn[2] = fma(k.dt_imp, Gp, z0[2]);
+            zn[3] = fma(-k.dt_imp, Gr, z0[3]);
+            zn[4] = fma(-k.dt_imp, Gt, z0[4]);
             zn[5] = z0[5];
             ok = conv6(zn, zk, k.tol);
             for (int i = 0; i < 6; ++i) zk[i] = zn[i];
@@ -623,6 +637,7 @@ __global__ void __launch_bounds__(128) k_dg(PushK k, int all_mode)
         n_it += it;
         const double H1 = eval_H(k.run.bh, zk, 0.0, 0.0);
         if (!finish(k.run, k.P, p, zk, H1, 1, it)) ++n_rm;
+        if (k.t) k.t[p] += k.dt_imp;
     }
     const unsigned m = __activemask();
     warp_add(&k.cnt[CNT_ITERS], n_it, m);
@@ -654,6 +669,19 @@ struct PushChunks {
 };
 }  // namespace fpic
 
+// Step of the implicit solves: the hybrid's partner takes dt_implicit when
+// set (adaptive steps, Sec. 3.1.2); pure schemes take dt.
+static double implicit_step(const fpic_push_params* prm)
+{
+    const bool hyb = prm->scheme == FPIC_HYB1 || prm->scheme == FPIC_HYB2;
+    return (hyb && prm->dt_implicit != 0.0) ? prm->dt_implicit : prm->dt;
+}
+
+static bool dt_implicit_ok(const fpic_push_params* prm)
+{
+    return prm->dt_implicit == 0.0 || (std::isfinite(prm->dt_implicit) && (prm->dt_implicit > 0.0) == (prm->dt > 0.0));
+}
+
 static int push_core(fpic_ctx* c, fpic_particles* p, const double* const fields[6], const fpic_push_params* prm,
                      fpic_push_stats* stats, cudaStream_t s, const PushChunks* ch);
 
@@ -664,6 +692,7 @@ extern "C" int fpic_push(fpic_ctx* c, fpic_particles* p, const double* const fie
     if (p->n < 0 || p->n >= (1LL << 31)) return set_error(FPIC_EINVAL, "fpic_push: n out of range [0, 2^31)");
     if (!particles_ok(p, true)) return set_error(FPIC_EINVAL, "fpic_push: a particle array is NULL");
     if (!(std::isfinite(prm->dt)) || prm->dt == 0.0) return set_error(FPIC_EINVAL, "fpic_push: dt must be finite and nonzero");
+    if (!dt_implicit_ok(prm)) return set_error(FPIC_EINVAL, "fpic_push: dt_implicit must be 0 or finite with the sign of dt");
     if (prm->scheme < FPIC_RK4 || prm->scheme > FPIC_HYB2) return set_error(FPIC_EINVAL, "fpic_push: unknown scheme %d", prm->scheme);
     if (prm->scheme >= FPIC_HYB1 && prm->implicit != FPIC_IMR && prm->implicit != FPIC_HAM)
         return set_error(FPIC_EINVAL, "fpic_push: implicit partner must be FPIC_IMR or FPIC_HAM");
@@ -695,6 +724,8 @@ static int push_core(fpic_ctx* c, fpic_particles* p, const double* const fields[
     k.run.has_fields = has_fields;
     for (int i = 0; i < 6; ++i) k.run.F.f[i] = has_fields ? fields[i] : nullptr;
     k.dt = prm->dt;
+    k.dt_imp = implicit_step(prm);
+    k.t = prm->t;
     k.thr = prm->thr;
     k.tol = prm->tol;
     k.dg_eps = prm->dg_eps;
@@ -894,6 +925,7 @@ extern "C" int fpic_push_noalloc(double M, double a, fpic_particles* p, const fp
                          (long long)p->n, (long long)kNoAllocMax);
     if (!particles_ok(p, true)) return set_error(FPIC_EINVAL, "fpic_push_noalloc: a particle array is NULL");
     if (!(std::isfinite(prm->dt)) || prm->dt == 0.0) return set_error(FPIC_EINVAL, "fpic_push_noalloc: dt must be finite and nonzero");
+    if (!dt_implicit_ok(prm)) return set_error(FPIC_EINVAL, "fpic_push_noalloc: bad dt_implicit");
     if (prm->scheme < FPIC_RK4 || prm->scheme > FPIC_HYB2) return set_error(FPIC_EINVAL, "fpic_push_noalloc: unknown scheme %d", prm->scheme);
     if (prm->scheme >= FPIC_HYB1 && prm->implicit != FPIC_IMR && prm->implicit != FPIC_HAM)
         return set_error(FPIC_EINVAL, "fpic_push_noalloc: implicit partner must be FPIC_IMR or FPIC_HAM");
@@ -912,6 +944,8 @@ extern "C" int fpic_push_noalloc(double M, double a, fpic_particles* p, const fp
     k.run.has_grid = 0;
     k.run.has_fields = 0;
     k.dt = prm->dt;
+    k.dt_imp = implicit_step(prm);
+    k.t = prm->t;
     k.thr = prm->thr;
     k.tol = prm->tol;
     k.dg_eps = prm->dg_eps;
@@ -1110,6 +1144,8 @@ static void fill_pushk(PushK& k, fpic_ctx* c, fpic_particles* p, const double* c
     k.run.has_fields = fields != nullptr;
     for (int i = 0; i < 6; ++i) k.run.F.f[i] = fields ? fields[i] : nullptr;
     k.dt = prm->dt;
+    k.dt_imp = prm->dt;
+    k.t = nullptr;
     k.thr = prm->thr;
     k.tol = prm->tol;
     k.dg_eps = prm->dg_eps;
@@ -1413,6 +1449,8 @@ extern "C" int fpic_push_learned(fpic_ctx* c, fpic_mlp* m, fpic_particles* p, co
 {
     if (!c || !m || !p || !prm || !cfg) return set_error(FPIC_EINVAL, "fpic_push_learned: NULL argument");
     if (!push_prm_ok(prm)) return set_error(FPIC_EINVAL, "fpic_push_learned: need a Hyb1/Hyb2 scheme with the IMR partner");
+    if (prm->dt_implicit != 0.0 && prm->dt_implicit != prm->dt)
+        return set_error(FPIC_EINVAL, "fpic_push_learned: the learned guess is trained for dt_implicit = dt");
     if (p->n < 0 || p->n >= (1LL << 31)) return set_error(FPIC_EINVAL, "fpic_push_learned: n out of range");
     if (!particles_ok(p, true)) return set_error(FPIC_EINVAL, "fpic_push_learned: NULL particle array");
     if (fields && !c->has_grid) return set_error(FPIC_EINVAL, "fpic_push_learned: fields given but no grid set");
@@ -1512,6 +1550,7 @@ extern "C" int fpic_push_batched(const fpic_run* runs, int nruns, fpic_particles
     if (p->n < 0 || p->n >= (1LL << 31)) return set_error(FPIC_EINVAL, "fpic_push_batched: n out of range");
     if (!particles_ok(p, true)) return set_error(FPIC_EINVAL, "fpic_push_batched: NULL particle array");
     if (!(std::isfinite(prm->dt)) || prm->dt == 0.0) return set_error(FPIC_EINVAL, "fpic_push_batched: bad dt");
+    if (!dt_implicit_ok(prm)) return set_error(FPIC_EINVAL, "fpic_push_batched: bad dt_implicit");
     if (prm->scheme != FPIC_RK4 && prm->scheme != FPIC_IMR && prm->scheme != FPIC_HYB1 && prm->scheme != FPIC_HYB2)
         return set_error(FPIC_EINVAL, "fpic_push_batched: scheme must be RK4, IMR, Hyb1 or Hyb2");
     if (prm->scheme >= FPIC_HYB1 && prm->implicit != FPIC_IMR)
@@ -1578,6 +1617,8 @@ extern "C" int fpic_push_batched(const fpic_run* runs, int nruns, fpic_particles
     k.runs = (const RunK*)c->d_runs;
     k.nruns = nruns;
     k.dt = prm->dt;
+    k.dt_imp = implicit_step(prm);
+    k.t = prm->t;
     k.thr = prm->thr;
     k.tol = prm->tol;
     k.dg_eps = prm->dg_eps;

@@ -97,7 +97,7 @@ def test_seeding_matches_oracle(F):
 
 
 def _one_step(F, ctx, g, Fo, z, q, scheme, dt, thr=1e-12, implicit=None, B0pot=1.0, r_max=None,
-              max_iter=50, alive=None, tol=1e-14):
+              max_iter=50, alive=None, tol=1e-14, dt_imp=0.0, t=None):
     n = z.shape[0]
     H0, _, D0 = O.hamiltonian(1.0, _A[id(ctx)], B0pot, z, q)
     Hn = H0 * (1.0 + 1e-9 * np.cos(np.arange(n)))
@@ -106,10 +106,10 @@ def _one_step(F, ctx, g, Fo, z, q, scheme, dt, thr=1e-12, implicit=None, B0pot=1
     alive = np.ones(n, np.uint8) if alive is None else alive
     p = make_particles(z, q, H0, D0, Hn, alive)
     prm = F.push_params(dt, scheme=scheme, implicit=implicit, thr=thr, tol=tol, max_iter=max_iter,
-                        r_max=r_max, B0pot=B0pot)
+                        r_max=r_max, B0pot=B0pot, dt_implicit=dt_imp, t=t)
     st = F.fpic_push(ctx, p, fields_dev(Fo) if Fo is not None else None, prm, stats=True)
     po = O.push_params(a=_A[id(ctx)], dt=dt, scheme=scheme, implicit_kind=implicit, thr=thr, tol=tol,
-                       max_iter=max_iter, r_max=r_max, B0pot=B0pot,
+                       max_iter=max_iter, r_max=r_max, B0pot=B0pot, dt_imp=dt_imp,
                        field_kind=O.FIELD_GRID if Fo is not None else O.FIELD_NONE)
     zo = np.ascontiguousarray(z.copy()); Ho = Hn.copy(); ao = alive.copy()
     nc, so, io = O.push(po, zo, q, H0, D0, Ho, ao, g, Fo)
@@ -371,3 +371,68 @@ def test_host_buffer_push_equals_device_push(n):
 def torch_from(x):
     import torch
     return torch.from_numpy(np.ascontiguousarray(x))
+
+
+@pytest.mark.parametrize("scheme", ["HYB1", "HYB2"])
+def test_adaptive_implicit_step_matches_oracle(F, scheme):
+    """Sec. 3.1.2 / Tab. C.2 adaptive steps on the charged Wald workload
+    (4741 particles, dt = 1e-3, the IMR partner with dt_implicit = 3e-3):
+    states 1e-12, choices bit-exact (threshold ties excluded), and the
+    per-particle time advanced by dt or dt_implicit as each particle's
+    scheme says (removed-at-start particles keep their time)."""
+    import torch
+    a = 0.9
+    g = I.wald_grid(128, a)
+    Fo = O.wald_on_grid(a, 1.0, g)
+    ctx = _mk(F, a, g)
+    d, z, q = thermal_state(4741, g, a, theta=0.1, seed=13)
+    n = len(q)
+    alive = (np.arange(n) % 97 != 5).astype(np.uint8)
+    t0 = np.linspace(0.0, 1.0, n)
+    tg = torch.as_tensor(t0.copy(), device="cuda")
+    thr = {"HYB1": 8e-5, "HYB2": 8e-8}[scheme]
+    sch = getattr(F, "FPIC_" + scheme)
+    p, st, (zo, Ho, ao, so, io, nc), (H0, D0, Hn) = _one_step(F, ctx, g, Fo, z, q, sch, 1e-3, thr=thr,
+                                                              alive=alive, dt_imp=3e-3, t=tg)
+    zg, Hg, ag, sg, ig, cg = to_np(p)
+    assert np.array_equal(ag, ao)
+    pr = O.push_params(a=a, dt=1e-3, scheme=O.RK4, B0pot=1.0, field_kind=O.FIELD_GRID, r_max=g.rn[-1])
+    zr = np.ascontiguousarray(z.copy()); Hr = Hn.copy()
+    O.push(pr, zr, q, H0, D0, Hr, np.ones(n, np.uint8), g, Fo)
+    Ht1 = np.abs(Hr - H0) / D0
+    stat = Ht1 if scheme == "HYB2" else (Ht1 - np.abs(Hn - H0) / D0) / 1e-3
+    near = np.abs(stat - thr) <= 1e-12 * abs(thr) + 1e-12 * np.abs(stat)
+    ok = ~near & (alive == 1)
+    assert near.sum() <= 2
+    assert np.array_equal(sg[ok], so[ok]) and 0 < so[alive == 1].sum() < alive.sum()
+    assert_state_close(zg, zo, TOL, ok)
+    t_exp = t0 + np.where(alive == 1, np.where(so == 1, 3e-3, 1e-3), 0.0)
+    assert np.array_equal(tg.cpu().numpy()[ok | (alive == 0)], t_exp[ok | (alive == 0)])
+
+
+def test_adaptive_step_dg_partner_matches_oracle(F):
+    """Neutral geodesics with the discrete-gradient partner at dt = 0.5,
+    dt_implicit = 1.0 (the a.0 column of Tab. C.2 takes 1.0 for the
+    Hamiltonian steps): states within 1e-12 plus the quotient conditioning
+    bound, choices bit-exact, H conserved by the implicit steps."""
+    a = 0.9
+    ctx = _mk(F, a)
+    z, bad = O.seed_orbits(1.0, a, I.orbit_candidates(1000, seed=4))
+    q = np.zeros(len(z))
+    H0 = O.hamiltonian(1.0, a, 0.0, z, q)[0]
+    dt, dti = 0.5, 1.0
+    pr = O.push_params(a=a, dt=dt, scheme=O.RK4)
+    zr = np.ascontiguousarray(z.copy()); Hr = H0.copy()
+    O.push(pr, zr, q, H0, H0, Hr, np.ones(len(q), np.uint8))
+    stat = np.abs(Hr - H0) / H0
+    thr = float(np.median(stat))
+    p, st, (zo, Ho, ao, so, io, nc), _ = _one_step(F, ctx, None, None, z, q, F.FPIC_HYB2, dt, thr=thr,
+                                                  implicit=F.FPIC_HAM, B0pot=0.0, tol=1e-15, dt_imp=dti)
+    zg, Hg, ag, sg, ig, cg = to_np(p)
+    near = np.abs(stat - thr) <= 1e-10 * thr + 1e-15
+    assert near.sum() <= 10 and np.array_equal(sg[~near], so[~near]) and 0 < so.sum() < len(q)
+    bound = TOL + np.where(so == 1, dg_conditioning(z, zo, H0, dti), 0.0)
+    err = (np.abs(zg - zo) / (np.abs(zo) + 1.0)).max(axis=1)
+    assert np.all(err[~near] <= bound[~near]), (err / bound).max()
+    imp = (so == 1) & ~near & (ag == 1)
+    assert np.abs(Hg[imp] - H0[imp]).max() < 2e-14

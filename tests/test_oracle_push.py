@@ -322,3 +322,46 @@ def test_particle_boundaries():
     z1, _, _, alive = _run(p, z, 3)
     assert alive.tolist() == [0, 1, 0]
     assert z1[1, 1] > 0 and z1[1, 4] > 0 and abs(z1[1, 2] - math.pi) < 1e-3
+
+
+@pytest.mark.parametrize("partner,charged", [(O.IMR, False), (O.HAM, False), (O.IMR, True)])
+def test_adaptive_implicit_step_is_the_standalone_step(partner, charged):
+    """Sec. 3.1.2 / Tab. C.2 adaptive steps: a hybrid whose test rejects every
+    trial returns, for every particle, the standalone implicit step of size
+    dt_imp from z^n (independently started at z^n), to the iteration
+    tolerance; a test that accepts everything returns the RK4 step of size
+    dt, whatever dt_imp; dt_imp = dt is bit-identical to dt_imp = 0."""
+    a, dt, dti = 0.9, 0.05, 0.15
+    if charged:
+        d, q, _ = I.thermal_draws(48, I.log_grid(8, 8, 1.5, 30.0), 3.0, 12.0, 0.1, seed=4, qm=1.0)
+        z0 = O.seed_fido(1.0, a, d)
+        kw = dict(field_kind=O.FIELD_WALD, B0field=1.0, B0pot=1.0)
+    else:
+        # generic bound states away from turning points (u_th != 0), where
+        # the discrete-gradient iteration reaches 1e-14
+        rng = np.random.default_rng(12)
+        m_ = 48
+        z0 = np.stack([rng.uniform(6, 12, m_), rng.uniform(0.8, 2.3, m_), np.zeros(m_), rng.uniform(-0.1, 0.1, m_),
+                       rng.choice([-1, 1], m_) * rng.uniform(0.1, 0.4, m_), rng.uniform(2.5, 3.5, m_)], 1)
+        q = np.zeros(m_)
+        kw = {}
+    n = z0.shape[0]
+    H0, _, D0 = O.hamiltonian(1.0, a, kw.get("B0pot", 0.0), z0, q)
+
+    def run(**p):
+        z = z0.copy(); Hn = H0.copy(); al = np.ones(n, np.uint8)
+        _, sch, its = O.push(O.push_params(a=a, tol=1e-14, **kw, **p), z, q, H0, D0, Hn, al)
+        return z, sch, al
+
+    z_rej, sch, al = run(dt=dt, scheme=O.HYB2, implicit_kind=partner, thr=-1.0, dt_imp=dti)
+    z_ref, _, al2 = run(dt=dti, scheme=partner)
+    assert np.all(sch == 1) and np.array_equal(al, al2) and al.sum() > 0.8 * n
+    m = al == 1
+    assert (np.abs(z_rej[m] - z_ref[m]) / (np.abs(z_ref[m]) + 1)).max() < 1e-12
+    z_acc, sch, _ = run(dt=dt, scheme=O.HYB2, implicit_kind=partner, thr=1e300, dt_imp=dti)
+    z_rk4, _, _ = run(dt=dt, scheme=O.RK4)
+    assert np.all(sch == 0) and np.array_equal(z_acc, z_rk4)
+    thr = 1e-13
+    za, _, _ = run(dt=dt, scheme=O.HYB2, implicit_kind=partner, thr=thr, dt_imp=dt)
+    zb, _, _ = run(dt=dt, scheme=O.HYB2, implicit_kind=partner, thr=thr, dt_imp=0.0)
+    assert np.array_equal(za, zb)
