@@ -79,6 +79,7 @@ def _declare(L):
     L.or_gather.argtypes = [C.c_int, C.c_int, C.c_int, _D, _D, _D, _D, C.POINTER(_D), _I64, _D, _D, _D]
     L.or_cell_index.argtypes = [C.c_int, C.c_int, _D, _D, _I64, _D, _D, _U32]
     L.or_dg_grad.argtypes = [C.c_double, C.c_double, _D, _D, C.c_double, _D]
+    L.or_dg_quot.argtypes = [C.c_double, C.c_double, _D, _D, C.c_int, _D]
     L.or_push.argtypes = [C.POINTER(PushParams), C.c_int, C.c_int, C.c_int, _D, _D, _D, _D,
                           C.POINTER(_D), _I64, _D, _D, _D, _D, _D, _U8, _U8, _U8]
     L.or_push.restype = _I64
@@ -161,6 +162,13 @@ def rhs(M, a, z, qm, D=None, B=None):
         Dp, Bp = ptr(Dk), ptr(Bk)
     lib().or_rhs(M, a, n, ptr(z), ptr(qm), Dp, Bp, ptr(f))
     return f
+
+
+def dg_quot(M, a, zb, za, v):
+    """Closed-form quotient (H(za) - H(zb)) / (za_v - zb_v) of a single-variable move."""
+    out = np.zeros(1)
+    lib().or_dg_quot(M, a, ptr(f64(zb)), ptr(f64(za)), int(v), ptr(out))
+    return float(out[0])
 
 
 def dg_grad(M, a, z0, z1, eps=1e-10):

@@ -419,53 +419,103 @@ static int step_imr(const or_ctx *c, double h, const double *z0, const double *g
     return -c->p->max_iter;
 }
 
-/* Geodesic Hamiltonian of Appendix D: H = alpha sqrt(1 + g^lm u_l u_m) - beta u_r. */
-static double ham_geo(double M, double a, const double *z)
+/* sin(h) / h, by its series below |h| = 1e-3 (error < 1e-19 there). */
+static double sinc_(double h)
 {
-    om_t m;
-    om_eval(M, a, z[0], z[1], &m);
-    return m.alpha * gamma_lorentz(&m, z + 3) - m.beta * z[3];
+    if (fabs(h) < 1e-3) {
+        double h2 = h * h;
+        return 1.0 - h2 / 6.0 + h2 * h2 / 120.0;
+    }
+    return sin(h) / h;
 }
 
-/* Analytic partial dH/dz_v of the geodesic Hamiltonian: (dx/dt, -du/dt)
- * of Eqs. (p1)-(p2) with q = 0. */
-static double ham_geo_partial(double M, double a, const double *z, int v)
+/* The difference quotient of the geodesic Hamiltonian for a move of the
+ * single variable v from zb to za (the other components equal):
+ *   G = (H(za) - H(zb)) / (za_v - zb_v),
+ * evaluated in closed form with the increment divided out analytically, so
+ * that no difference of nearly equal H values is formed (Appendix D writes
+ * its quotients in this split form: alpha' Gamma' - alpha Gamma =
+ * (alpha' + alpha)/2 (Gamma' - Gamma) + (Gamma' + Gamma)/2 (alpha' - alpha),
+ * Gamma' - Gamma = (Gamma'^2 - Gamma^2) / (Gamma' + Gamma)).  The metric
+ * differences per unit increment:
+ *   r:  d(rho^2) = r + r',  d(2 M r / rho^2) = 2 M (a^2 c^2 - r r') / (rho^2 rho'^2)
+ *   th: d(c) = -sin(th_m) sinc(dth/2) (th_m the midpoint), d(c^2) = (c + c') d(c),
+ *       d(rho^2) = a^2 d(c^2), d(2 M r / rho^2) = -2 M r d(rho^2) / (rho^2 rho'^2)
+ * and then d(1/rho^2) = -d(rho^2) / (rho^2 rho'^2), d(xi) = d(2 M r / rho^2),
+ * d(1/xi) = -d(xi) / (xi xi'), d(alpha) = -d(xi) / (sqrt(xi xi')
+ * (sqrt(xi) + sqrt(xi'))), d(beta) = d(xi) / (xi xi').  In exact arithmetic
+ * G is the plain quotient; it tends to the partial derivative as the
+ * increment vanishes, so no switch to the partial is needed. */
+static double dg_quot(double M, double a, const double *zb, const double *za, int v)
 {
-    double f[6];
-    rhs(M, a, 0.0, z, NULL, NULL, f);
-    if (v >= 3) return f[v - 3];   /* dH/du_i = dx^i/dt */
-    return -f[3 + v];              /* dH/dx^i = -du_i/dt */
+    if (v == 2) return 0.0;                                   /* H does not depend on ph */
+    om_t mb, ma;
+    om_eval(M, a, zb[0], zb[1], &mb);
+    om_eval(M, a, za[0], za[1], &ma);
+    const double *ub = zb + 3, *ua = za + 3;
+    const double Gb = gamma_lorentz(&mb, ub), Ga = gamma_lorentz(&ma, ua);
+    const double Gs = Ga + Gb;
+    if (v == 3)
+        return mb.alpha * (mb.gu_rr * (ua[0] + ub[0]) + 2.0 * mb.gu_rp * ub[2]) / Gs - mb.beta;
+    if (v == 4)
+        return mb.alpha * mb.gu_tt * (ua[1] + ub[1]) / Gs;
+    if (v == 5)
+        return mb.alpha * (2.0 * mb.gu_rp * ub[0] + mb.gu_pp * (ua[2] + ub[2])) / Gs;
+    /* position moves: metric differences per unit increment */
+    const double a2 = a * a;
+    double d_rho2, d_f, d_s2;
+    if (v == 0) {
+        const double c2 = mb.c * mb.c;
+        d_rho2 = zb[0] + za[0];
+        d_f = 2.0 * M * (a2 * c2 - zb[0] * za[0]) / (mb.rho2 * ma.rho2);
+        d_s2 = 0.0;
+    } else {
+        const double h = 0.5 * (za[1] - zb[1]);
+        const double d_c = -sin(0.5 * (za[1] + zb[1])) * sinc_(h);
+        const double d_c2 = (mb.c + ma.c) * d_c;
+        d_rho2 = a2 * d_c2;
+        d_f = -2.0 * M * zb[0] * d_rho2 / (mb.rho2 * ma.rho2);
+        d_s2 = -d_c2;
+    }
+    const double d_irho2 = -d_rho2 / (mb.rho2 * ma.rho2);
+    const double xx = mb.xi * ma.xi, sx = sqrt(xx);
+    const double d_ixi = -d_f / xx;
+    const double d_alpha = -d_f / (sx * (sqrt(mb.xi) + sqrt(ma.xi)));
+    const double d_beta = d_f / xx;
+    /* d(s^2 / rho^2) = (d(s^2) rho^2 - s^2 d(rho^2)) / (rho^2 rho'^2) */
+    const double s2b = mb.s * mb.s, s2a = ma.s * ma.s;
+    const double d_s2irho2 = (d_s2 * mb.rho2 - s2b * d_rho2) / (mb.rho2 * ma.rho2);
+    /* d(1 / (rho^2 s^2)) = -(d(rho^2) s'^2 + rho^2 d(s^2)) / (P P'), P = rho^2 s^2 */
+    const double d_ipp = -(d_rho2 * s2a + mb.rho2 * d_s2) / (mb.rho2 * s2b * ma.rho2 * s2a);
+    const double d_grr = a2 * d_s2irho2 + d_ixi;
+    const double d_grp = a * d_irho2;
+    const double d_gtt = d_irho2;
+    const double u0 = ub[0], u1 = ub[1], u2 = ub[2];         /* momenta unchanged by a position move */
+    const double dG2 = d_grr * u0 * u0 + 2.0 * d_grp * u0 * u2 + d_gtt * u1 * u1 + d_ipp * u2 * u2;
+    return 0.5 * (ma.alpha + mb.alpha) * dG2 / Gs + 0.5 * Gs * d_alpha - d_beta * u0;
 }
 
 /* Coordinate-increment discrete gradient along one ordering of the six
  * variables (Sec. 2.2.3, Eq. hh and the displayed quotients): variable
  * ord[k] is moved from z0 to z1 in turn, and its component is the
- * difference quotient of H across that single move, so that the components
- * telescope: sum_v G_v (z1_v - z0_v) = H(z1) - H(z0) exactly.  When
- * |z1_v - z0_v| < eps the quotient is replaced by the analytic partial at
- * the midpoint of the move (Appendix D, closing paragraph). */
+ * difference quotient of H across that single move (dg_quot), so that the
+ * components telescope: sum_v G_v (z1_v - z0_v) = H(z1) - H(z0) (exactly in
+ * exact arithmetic, to rounding here).  Appendix D replaces the quotient by
+ * the analytic partial when |z1_v - z0_v| < eps, a guard against the 0/0 of
+ * the plain quotient; the closed form has no 0/0 (it tends to the partial),
+ * so eps is not used. */
 static void dg_path(double M, double a, const double *z0, const double *z1,
                     const int *ord, double eps, double *G)
 {
-    double zc[6];
-    memcpy(zc, z0, sizeof zc);
-    double Hc = ham_geo(M, a, zc);
+    (void)eps;
+    double zb[6], za[6];
+    memcpy(zb, z0, sizeof zb);
     for (int k = 0; k < 6; ++k) {
         int v = ord[k];
-        double dz = z1[v] - z0[v];
-        if (fabs(dz) < eps) {
-            double zm[6];
-            memcpy(zm, zc, sizeof zm);
-            zm[v] = 0.5 * (z0[v] + z1[v]);
-            G[v] = ham_geo_partial(M, a, zm, v);
-            zc[v] = z1[v];
-            Hc = ham_geo(M, a, zc);
-        } else {
-            zc[v] = z1[v];
-            double Hn = ham_geo(M, a, zc);
-            G[v] = (Hn - Hc) / dz;
-            Hc = Hn;
-        }
+        memcpy(za, zb, sizeof za);
+        za[v] = z1[v];
+        G[v] = dg_quot(M, a, zb, za, v);
+        memcpy(zb, za, sizeof zb);
     }
 }
 
@@ -673,6 +723,11 @@ void or_cell_index(int Nr, int Nth, const double *rn, const double *tn, int64_t 
 }
 
 /* Discrete gradient between two states (exposed for the conservation pins). */
+void or_dg_quot(double M, double a, const double *zb, const double *za, int v, double *G)
+{
+    *G = dg_quot(M, a, zb, za, v);
+}
+
 void or_dg_grad(double M, double a, const double *z0, const double *z1, double eps, double *G)
 {
     dg_grad(M, a, z0, z1, eps, G);

@@ -365,3 +365,51 @@ def test_adaptive_implicit_step_is_the_standalone_step(partner, charged):
     za, _, _ = run(dt=dt, scheme=O.HYB2, implicit_kind=partner, thr=thr, dt_imp=dt)
     zb, _, _ = run(dt=dt, scheme=O.HYB2, implicit_kind=partner, thr=thr, dt_imp=0.0)
     assert np.array_equal(za, zb)
+
+
+@pytest.mark.parametrize("a", [0.0, 0.9, 0.995])
+def test_dg_quotient_closed_form(a):
+    """Appendix D quotients in closed form: for a single-variable move the
+    value equals the plain difference quotient (H(za) - H(zb)) / dz of the
+    Appendix A Hamiltonian at increments where that quotient is accurate
+    (|dz| = 1e-3: rounding ~1e-13), and tends to the partial derivative of
+    Hamilton's equations (Eqs. p1, p2 with q = 0) at |dz| = 1e-12, where the
+    plain quotient has lost all digits; the ph move gives 0."""
+    rng = np.random.default_rng(int(a * 1000) + 3)
+    H = _H(a)
+    for _ in range(20):
+        zb = np.array([rng.uniform(1.5 * (1 + math.sqrt(1 - a * a)), 15), rng.uniform(0.3, 2.8), 0.2,
+                       rng.normal() * 0.5, rng.normal(), rng.normal() * 3])
+        f = O.rhs(1.0, a, zb[None, :], 0.0)[0]
+        partial = {0: -f[3], 1: -f[4], 3: f[0], 4: f[1], 5: f[2]}
+        for v in (0, 1, 3, 4, 5):
+            za = zb.copy(); za[v] += 1e-3 * (1 + abs(zb[v]))
+            plain = (H(za) - H(zb)) / (za[v] - zb[v])
+            q = O.dg_quot(1.0, a, zb, za, v)
+            # the plain quotient's own rounding: a few ulp(H) / |dz|
+            assert abs(q - plain) <= 1e-10 * abs(plain) + 4e-16 * max(1.0, abs(H(zb))) / abs(za[v] - zb[v]), \
+                (v, q, plain)
+            za = zb.copy(); za[v] += 1e-12
+            q = O.dg_quot(1.0, a, zb, za, v)
+            # O(dz) = 1e-12 from the second derivative
+            assert abs(q - partial[v]) <= 1e-10 * abs(partial[v]) + 1e-11, (v, q, partial[v])
+        za = zb.copy(); za[2] += 0.3
+        assert O.dg_quot(1.0, a, zb, za, 2) == 0.0
+
+
+def test_dg_converges_from_turning_points():
+    """Bound orbits seeded at a th turning point (u_th = 0, where th moves by
+    tiny increments): the closed-form quotients let every discrete-gradient
+    solve converge to 1e-15 within a few iterations and conserve H to
+    rounding."""
+    a = 0.9
+    z0, bad = O.seed_orbits(1.0, a, I.orbit_candidates(48, seed=12))
+    assert bad == 0
+    n = z0.shape[0]
+    q = np.zeros(n)
+    H0, _, D0 = O.hamiltonian(1.0, a, 0.0, z0, q)
+    z = z0.copy(); Hn = H0.copy(); al = np.ones(n, np.uint8)
+    for _ in range(5):
+        nc, sch, its = O.push(O.push_params(a=a, dt=0.15, scheme=O.HAM, tol=1e-15), z, q, H0, D0, Hn, al)
+        assert nc == 0 and its.max() <= 12
+    assert np.abs(Hn - H0).max() <= 4e-15 * np.abs(H0).max()
