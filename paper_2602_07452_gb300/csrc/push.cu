@@ -504,63 +504,102 @@ __global__ void __launch_bounds__(256) k_imr_finish(const __grid_constant__ Push
 // the 12 update orders (3! pair orders x {coordinate-first, momentum-first});
 // since H does not depend on ph and u_ph never changes, they reduce to four
 // distinct orders over (r, u_r, th, u_th), each of weight 1/4, and the
-// u_ph component to the analytic dH/du_ph averaged over the states where
-// u_ph is visited (weights 2,1,1,2 / 6).  H needs the metric at only four
-// (r, th) combinations per iteration.
+// u_ph component to dH/du_ph averaged over the states where u_ph is visited
+// (weights 2,1,1,2 / 6).  Every quotient (H(z') - H(z)) / dz is taken in
+// the closed form of App. D: alpha' G' - alpha G = (alpha' + alpha)/2 (G' - G)
+// + (G' + G)/2 (alpha' - alpha), G'^2 - G^2 and the metric differences with
+// the increment divided out, so no digits are lost to cancellation and no
+// switch to the partial derivative is needed.  The metric is needed at the
+// four (r, th) combinations of z^n and the iterate.
 // ---------------------------------------------------------------------------
-struct GH {
-    double alpha, beta, gurr, gurp, gutt, gupp;
-};
-
-__device__ __forceinline__ GH gh_at(const BH& bh, double r, double th)
+__device__ __forceinline__ Geo geo_at(const BH& bh, double r, double s, double c)
 {
-    double s, c;
-    sincos(th, &s, &c);
     Geo g;
     geo_eval(bh, r, s, c, g);
-    return GH{g.alpha, g.beta, g.gurr, g.gurp, g.gutt, g.gupp};
+    return g;
 }
 
-__device__ __forceinline__ double gh_G(const GH& g, double ur, double ut, double up)
+// Gamma = sqrt(1 + g^ij u_i u_j) at a metric point
+__device__ __forceinline__ double dg_gam(const Geo& g, double ur, double ut, double up)
 {
     return sqrt(fma(g.gurr * ur, ur, fma(2.0 * g.gurp * ur, up, fma(g.gutt * ut, ut, fma(g.gupp * up, up, 1.0)))));
 }
 
-__device__ __forceinline__ double gh_H(const GH& g, double ur, double ut, double up)
+// Metric differences per unit increment of a position move b -> a.
+struct PD {
+    double dgrr, dgrp, dgtt, dgpp, dal, dbe, asum;
+};
+
+__device__ __forceinline__ PD pd_common(const BH& bh, const Geo& b, const Geo& a, double d_rho2, double d_f,
+                                        double d_s2)
 {
-    return fma(g.alpha, gh_G(g, ur, ut, up), -g.beta * ur);
+    PD d;
+    const double irr = b.irho2 * a.irho2;            // 1 / (rho^2 rho'^2)
+    const double d_irho2 = -d_rho2 * irr;
+    const double ixx = b.ixi * a.ixi;                // 1 / (xi xi')
+    const double sb = b.xi * b.alpha, sa = a.xi * a.alpha;   // sqrt(xi), sqrt(xi')
+    d.dbe = d_f * ixx;
+    d.dal = -d_f * (b.alpha * a.alpha) / (sb + sa);
+    const double d_s2irho2 = fma(d_s2, b.rho2, -b.s2 * d_rho2) * irr;
+    d.dgrr = fma(bh.a2, d_s2irho2, -d.dbe);          // d(1/xi) = -d(beta)
+    d.dgrp = bh.a * d_irho2;
+    d.dgtt = d_irho2;
+    d.dgpp = -fma(d_rho2, a.s2, b.rho2 * d_s2) * (b.t * a.t);
+    d.asum = b.alpha + a.alpha;
+    return d;
 }
 
-__device__ __forceinline__ double gh_dHdup(const GH& g, double ur, double ut, double up)
+// r move (th fixed): d(rho^2) = r + r', d(2 M r / rho^2) = 2 M (a^2 c^2 - r r') / (rho^2 rho'^2)
+__device__ __forceinline__ PD pd_r(const BH& bh, const Geo& b, const Geo& a, double r0, double r1)
 {
-    return g.alpha * fma(g.gurp, ur, g.gupp * up) / gh_G(g, ur, ut, up);
+    const double d_f = bh.twoM * fma(bh.a2, b.c * b.c, -r0 * r1) * (b.irho2 * a.irho2);
+    return pd_common(bh, b, a, r0 + r1, d_f, 0.0);
 }
 
-// Analytic partial dH/dz_v (v: 0 r, 1 th, 3 u_r, 4 u_th) at a state.
-__device__ double dg_partial(const BH& bh, double r, double th, double ur, double ut, double up, int v)
+// th move (r fixed) with d(cos th) per unit increment dc: d(c^2) = (c + c') dc,
+// d(rho^2) = a^2 d(c^2), d(2 M r / rho^2) = -2 M r d(rho^2) / (rho^2 rho'^2), d(s^2) = -d(c^2)
+__device__ __forceinline__ PD pd_th(const BH& bh, const Geo& b, const Geo& a, double r, double dc)
 {
-    double y[6] = {r, th, 0.0, ur, ut, up}, f[6], H;
-    const double D[3] = {0, 0, 0};
-    eval_rhs(bh, y, 0.0, false, D, D, 0.0, f, H);
-    switch (v) {
-        case 0: return -f[3];
-        case 1: return -f[4];
-        case 3: return f[0];
-        default: return f[1];
+    const double d_c2 = (b.c + a.c) * dc;
+    const double d_rho2 = bh.a2 * d_c2;
+    const double d_f = -bh.twoM * r * d_rho2 * (b.irho2 * a.irho2);
+    return pd_common(bh, b, a, d_rho2, d_f, -d_c2);
+}
+
+// Quotient of a position move at momenta (ur, ut, up), Gamma at both ends given.
+__device__ __forceinline__ double dq_pos(const PD& d, double gb, double ga, double ur, double ut, double up)
+{
+    const double dG2 = fma(d.dgrr * ur, ur, fma(2.0 * d.dgrp * ur, up, fma(d.dgtt * ut, ut, d.dgpp * up * up)));
+    const double gs = ga + gb;
+    return fma(0.5 * d.asum, dG2 / gs, fma(0.5 * gs, d.dal, -d.dbe * ur));
+}
+
+// Quotients of the momentum moves at a metric point (u_r: u0 -> u1 at u_th = ut; u_th: v0 -> v1 at u_r = ur).
+__device__ __forceinline__ double dq_ur(const Geo& g, double gb, double ga, double u0, double u1, double up)
+{
+    return g.alpha * fma(g.gurr, u0 + u1, 2.0 * g.gurp * up) / (ga + gb) - g.beta;
+}
+
+__device__ __forceinline__ double dq_ut(const Geo& g, double gb, double ga, double v0, double v1)
+{
+    return g.alpha * g.gutt * (v0 + v1) / (ga + gb);
+}
+
+// sin(h) / h, by its series below |h| = 1e-3
+__device__ __forceinline__ double sinc_dev(double h)
+{
+    if (fabs(h) < 1e-3) {
+        const double h2 = h * h;
+        return fma(h2, fma(h2, 1.0 / 120.0, -1.0 / 6.0), 1.0);
     }
-}
-
-__device__ __forceinline__ double dgq(const BH& bh, double Hn, double Ho, double dz, double eps,
-                                      double r, double th, double ur, double ut, double up, int v)
-{
-    if (fabs(dz) < eps) return dg_partial(bh, r, th, ur, ut, up, v);
-    return (Hn - Ho) / dz;
+    return sin(h) / h;
 }
 
 __global__ void __launch_bounds__(128) k_dg(PushK k, int all_mode)
 {
     const long long qn = all_mode ? k.n : k.cnt[CNT_QUEUE];
     long long n_it = 0, n_nc = 0, n_rm = 0;
+    const BH& bh = k.run.bh;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < qn;
          idx += (long long)gridDim.x * blockDim.x) {
         const long long p = all_mode ? idx : (long long)k.queue[idx];
@@ -577,50 +616,56 @@ __global__ void __launch_bounds__(128) k_dg(PushK k, int all_mode)
             for (int i = 0; i < 6; ++i) zk[i] = k.guess[(size_t)i * k.n + p];
         }
         const double R0 = z0[0], T0 = z0[1], U0 = z0[3], V0 = z0[4], P = z0[5];
-        const GH m00 = gh_at(k.run.bh, R0, T0);
-        const double Hz0 = gh_H(m00, U0, V0, P);
-        const double f00 = gh_dHdup(m00, U0, V0, P);
-        const double eps = k.dg_eps;
+        double s0, c0;
+        sincos(T0, &s0, &c0);
+        const Geo m00 = geo_at(bh, R0, s0, c0);
+        const double g00 = dg_gam(m00, U0, V0, P);
+        const double f00 = m00.alpha * fma(m00.gurp, U0, m00.gupp * P) / g00;
         int it = 0;
         bool ok = false;
         while (it < k.max_iter) {
             const double R1 = zk[0], T1 = zk[1], U1 = zk[3], V1 = zk[4];
-            const GH m10 = gh_at(k.run.bh, R1, T0), m01 = gh_at(k.run.bh, R0, T1), m11 = gh_at(k.run.bh, R1, T1);
+            double s1, c1;
+            sincos(T1, &s1, &c1);
+            const Geo m10 = geo_at(bh, R1, s0, c0), m01 = geo_at(bh, R0, s1, c1), m11 = geo_at(bh, R1, s1, c1);
             const double dR = R1 - R0, dT = T1 - T0, dU = U1 - U0, dV = V1 - V0;
-            const double Rm = 0.5 * (R0 + R1), Tm = 0.5 * (T0 + T1);
-            const double Um = 0.5 * (U0 + U1), Vm = 0.5 * (V0 + V1);
-            const double Hz1 = gh_H(m11, U1, V1, P);
-            const double A1 = gh_H(m10, U0, V0, P), A2 = gh_H(m10, U1, V0, P), A3 = gh_H(m11, U1, V0, P);
-            const double B1 = gh_H(m00, U1, V0, P), B3 = gh_H(m10, U1, V1, P);
-            const double C1 = gh_H(m01, U0, V0, P), C2 = gh_H(m01, U0, V1, P), C3 = gh_H(m11, U0, V1, P);
-            const double D1 = gh_H(m00, U0, V1, P), D3 = gh_H(m01, U1, V1, P);
-            const BH& bh = k.run.bh;
+            // d(cos th) / d th across the th move, without cancellation
+            const double dc = -sin(0.5 * (T0 + T1)) * sinc_dev(0.5 * dT);
+            const PD r_T0 = pd_r(bh, m00, m10, R0, R1), r_T1 = pd_r(bh, m01, m11, R0, R1);
+            const PD t_R0 = pd_th(bh, m00, m01, R0, dc), t_R1 = pd_th(bh, m10, m11, R1, dc);
+            // Gamma at the visited states
+            const double g00_u1 = dg_gam(m00, U1, V0, P), g00_v1 = dg_gam(m00, U0, V1, P);
+            const double g10 = dg_gam(m10, U0, V0, P), g10_u1 = dg_gam(m10, U1, V0, P), g10_uv = dg_gam(m10, U1, V1, P);
+            const double g01 = dg_gam(m01, U0, V0, P), g01_v1 = dg_gam(m01, U0, V1, P), g01_uv = dg_gam(m01, U1, V1, P);
+            const double g11_u1 = dg_gam(m11, U1, V0, P), g11_uv = dg_gam(m11, U1, V1, P), g11_v1 = dg_gam(m11, U0, V1, P);
             // order A: r, u_r, th, u_th
-            const double rA = dgq(bh, A1, Hz0, dR, eps, Rm, T0, U0, V0, P, 0);
-            const double uA = dgq(bh, A2, A1, dU, eps, R1, T0, Um, V0, P, 3);
-            const double tA = dgq(bh, A3, A2, dT, eps, R1, Tm, U1, V0, P, 1);
-            const double vA = dgq(bh, Hz1, A3, dV, eps, R1, T1, U1, Vm, P, 4);
+            const double rA = dq_pos(r_T0, g00, g10, U0, V0, P);
+            const double uA = dq_ur(m10, g10, g10_u1, U0, U1, P);
+            const double tA = dq_pos(t_R1, g10_u1, g11_u1, U1, V0, P);
+            const double vA = dq_ut(m11, g11_u1, g11_uv, V0, V1);
             // order B: u_r, r, u_th, th
-            const double uB = dgq(bh, B1, Hz0, dU, eps, R0, T0, Um, V0, P, 3);
-            const double rB = dgq(bh, A2, B1, dR, eps, Rm, T0, U1, V0, P, 0);
-            const double vB = dgq(bh, B3, A2, dV, eps, R1, T0, U1, Vm, P, 4);
-            const double tB = dgq(bh, Hz1, B3, dT, eps, R1, Tm, U1, V1, P, 1);
+            const double uB = dq_ur(m00, g00, g00_u1, U0, U1, P);
+            const double rB = dq_pos(r_T0, g00_u1, g10_u1, U1, V0, P);
+            const double vB = dq_ut(m10, g10_u1, g10_uv, V0, V1);
+            const double tB = dq_pos(t_R1, g10_uv, g11_uv, U1, V1, P);
             // order C: th, u_th, r, u_r
-            const double tC = dgq(bh, C1, Hz0, dT, eps, R0, Tm, U0, V0, P, 1);
-            const double vC = dgq(bh, C2, C1, dV, eps, R0, T1, U0, Vm, P, 4);
-            const double rC = dgq(bh, C3, C2, dR, eps, Rm, T1, U0, V1, P, 0);
-            const double uC = dgq(bh, Hz1, C3, dU, eps, R1, T1, Um, V1, P, 3);
+            const double tC = dq_pos(t_R0, g00, g01, U0, V0, P);
+            const double vC = dq_ut(m01, g01, g01_v1, V0, V1);
+            const double rC = dq_pos(r_T1, g01_v1, g11_v1, U0, V1, P);
+            const double uC = dq_ur(m11, g11_v1, g11_uv, U0, U1, P);
             // order D: u_th, th, u_r, r
-            const double vD = dgq(bh, D1, Hz0, dV, eps, R0, T0, U0, Vm, P, 4);
-            const double tD = dgq(bh, C2, D1, dT, eps, R0, Tm, U0, V1, P, 1);
-            const double uD = dgq(bh, D3, C2, dU, eps, R0, T1, Um, V1, P, 3);
-            const double rD = dgq(bh, Hz1, D3, dR, eps, Rm, T1, U1, V1, P, 0);
+            const double vD = dq_ut(m00, g00, g00_v1, V0, V1);
+            const double tD = dq_pos(t_R0, g00_v1, g01_v1, U0, V1, P);
+            const double uD = dq_ur(m01, g01_v1, g01_uv, U0, U1, P);
+            const double rD = dq_pos(r_T1, g01_uv, g11_uv, U1, V1, P);
             const double Gr = 0.25 * (rA + rB + rC + rD);
             const double Gt = 0.25 * (tA + tB + tC + tD);
             const double Gu = 0.25 * (uA + uB + uC + uD);
             const double Gv = 0.25 * (vA + vB + vC + vD);
-            const double Gp = (2.0 * f00 + gh_dHdup(m10, U1, V0, P) + gh_dHdup(m01, U0, V1, P) +
-                               2.0 * gh_dHdup(m11, U1, V1, P)) / 6.0;
+            const double Gp = (2.0 * f00 + m10.alpha * fma(m10.gurp, U1, m10.gupp * P) / g10_u1 +
+                               m01.alpha * fma(m01.gurp, U0, m01.gupp * P) / g01_v1 +
+                               2.0 * m11.alpha * fma(m11.gurp, U1, m11.gupp * P) / g11_uv) / 6.0;
+            (void)dR; (void)dU; (void)dV;
             double zn[6];
             zn[0] = fma(k.dt_imp, Gu, z0[0]);
             zn[1] = fma(k.dt_imp, Gv, z0[1]);
@@ -635,7 +680,7 @@ __global__ void __launch_bounds__(128) k_dg(PushK k, int all_mode)
         }
         if (!ok) ++n_nc;
         n_it += it;
-        const double H1 = eval_H(k.run.bh, zk, 0.0, 0.0);
+        const double H1 = eval_H(bh, zk, 0.0, 0.0);
         if (!finish(k.run, k.P, p, zk, H1, 1, it)) ++n_rm;
         if (k.t) k.t[p] += k.dt_imp;
     }
