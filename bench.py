@@ -66,6 +66,9 @@ def parse():
                     help="plain steps sampled for the training set")
     ap.add_argument("--workload", default="push", choices=["push", "pic", "neutral", "batched", "clean", "inject", "adaptive"])
     ap.add_argument("--clean-sweeps", type=int, default=500, help="Jacobi sweeps of --workload clean")
+    ap.add_argument("--neutral-scheme", default="HYB2", choices=["HYB2", "HAM", "RK4"],
+                    help="scheme of --workload neutral")
+    ap.add_argument("--neutral-pre", type=int, default=1000, help="untimed steps before --workload neutral")
     ap.add_argument("--pic-grid", type=int, default=1024)
     ap.add_argument("--pic-ppc", type=int, default=64)
     ap.add_argument("--pic-steps", type=int, default=3)
@@ -866,7 +869,7 @@ def main():
         if args.workload == "pic":
             res = run_pic(args, dev, args.pic_grid, args.pic_ppc, args.pic_steps, rank)
         elif args.workload == "neutral":
-            res = run_neutral(args, dev, 1 << 20, args.steps)
+            res = run_neutral(args, dev, args.n, args.steps, pre_steps=args.neutral_pre, scheme=args.neutral_scheme)
         else:
             res = run_batched(args, dev, args.batch_scale, args.steps)
         if rank == 0:
