@@ -80,6 +80,8 @@ def _declare(L):
     L.or_cell_index.argtypes = [C.c_int, C.c_int, _D, _D, _I64, _D, _D, _U32]
     L.or_dg_grad.argtypes = [C.c_double, C.c_double, _D, _D, C.c_double, _D]
     L.or_dg_quot.argtypes = [C.c_double, C.c_double, _D, _D, C.c_int, _D]
+    L.or_dg_quot_em.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, _D, _D, C.c_int, _D]
+    L.or_wald_A.argtypes = [C.c_double, C.c_double, _I64, _D, _D, _D, _D]
     L.or_push.argtypes = [C.POINTER(PushParams), C.c_int, C.c_int, C.c_int, _D, _D, _D, _D,
                           C.POINTER(_D), _I64, _D, _D, _D, _D, _D, _U8, _U8, _U8]
     L.or_push.restype = _I64
@@ -169,6 +171,21 @@ def dg_quot(M, a, zb, za, v):
     out = np.zeros(1)
     lib().or_dg_quot(M, a, ptr(f64(zb)), ptr(f64(za)), int(v), ptr(out))
     return float(out[0])
+
+
+def dg_quot_em(M, a, B0, qm, wb, wa, v):
+    """Charged closed-form quotient in canonical variables (Wald field)."""
+    out = np.zeros(1)
+    lib().or_dg_quot_em(M, a, B0, qm, ptr(f64(wb)), ptr(f64(wa)), int(v), ptr(out))
+    return float(out[0])
+
+
+def wald_A(a, B0, r, th):
+    """A_r and A_ph of Eq. (Amu) (M = 1)."""
+    r, th = f64(np.atleast_1d(r)), f64(np.atleast_1d(th))
+    Ar, Aph = np.empty(r.size), np.empty(r.size)
+    lib().or_wald_A(a, B0, r.size, ptr(r), ptr(th), ptr(Ar), ptr(Aph))
+    return Ar, Aph
 
 
 def dg_grad(M, a, z0, z1, eps=1e-10):

@@ -123,6 +123,17 @@ static double wald_Aph(double a, double B0, double r, double th)
     return 0.5 * B0 * s * s * (r * r + a * a - 2.0 * a * a * r * (1.0 + c * c) / rho2);
 }
 
+/* A_r of Eq. (Amu): (B0/2)(g_rph + 2 a g_0r) = (B0/2)(2 a r (1 + c^2)/rho^2 - a s^2)
+ * (M = 1).  Sec. 3.1.3's H and L need only A_0 and A_ph; the canonical
+ * momentum pi_r = u_r + (q/m) A_r of the discrete-gradient scheme for
+ * charged particles needs it too. */
+static double wald_Ar(double a, double B0, double r, double th)
+{
+    double s = sin(th), c = cos(th);
+    double rho2 = r * r + a * a * c * c;
+    return 0.5 * B0 * (2.0 * a * r * (1.0 + c * c) / rho2 - a * s * s);
+}
+
 /* Appendix B.1, Eqs. (wald1)-(wald6): contravariant B^i and covariant E_i.
  * Reading: the printed E_theta carries an extra factor a; the value used,
  * E_theta = 2 B0 a r (a^2 - r^2) sin th cos th / rho^4, is the one that
@@ -495,6 +506,87 @@ static double dg_quot(double M, double a, const double *zb, const double *za, in
     return 0.5 * (ma.alpha + mb.alpha) * dG2 / Gs + 0.5 * Gs * d_alpha - d_beta * u0;
 }
 
+/* The same quotient for a charged particle in the static Wald field, in
+ * canonical variables w = (r, th, ph, pi_r, pi_th, pi_ph), pi_i = u_i +
+ * (q/m) A_i (Eq. Amu, M = 1), of
+ *   H_c(x, pi) = alpha Gamma(u) - beta^r u_r - (q/m) A_0,  u = pi - (q/m) A(x)
+ * (Sec. 3.1.3's H written in pi).  Momentum moves change u by the same
+ * increment, so their quotients are the geodesic ones at u.  A position
+ * move changes the metric and u together; with P = r / rho^2 and
+ * K = 1 + c^2 (A_0 = a B0 K P, A_ph = (B0/2) s^2 (r^2 + a^2 - 2 a^2 K P),
+ * A_r = (B0/2)(2 a K P - a s^2)), the potential differences per unit
+ * increment are
+ *   r:  dP = (a^2 c^2 - r r') / (rho^2 rho'^2), d(KP) = K dP,
+ *       dA_ph = (B0/2) s^2 (r + r' - 2 a^2 d(KP))
+ *   th: dP = -r d(rho^2) / (rho^2 rho'^2), d(KP) = d(c^2) P' + K dP,
+ *       dA_ph = (B0/2) (d(s^2) (r^2 + a^2 - 2 a^2 K' P') - 2 a^2 s^2 d(KP))
+ *   both: dA_0 = a B0 d(KP), dA_r = (B0/2)(2 a d(KP) - a d(s^2)),
+ * du_r = -(q/m) dA_r, du_ph = -(q/m) dA_ph, and
+ *   Gamma'^2 - Gamma^2 = dg^ij u'_i u'_j + g^ij (du_i u'_j + u_i du_j),
+ *   dH = (alpha' + alpha)/2 dGamma + (Gamma' + Gamma)/2 d(alpha)
+ *        - (d(beta) u'_r + beta du_r) - (q/m) dA_0. */
+static double dg_quot_em(double M, double a, double B0, double qm, const double *wb, const double *wa, int v)
+{
+    if (v == 2) return 0.0;
+    const double rb = wb[0], ra = wa[0], tb = wb[1], ta = wa[1];
+    om_t mb, ma;
+    om_eval(M, a, rb, tb, &mb);
+    om_eval(M, a, ra, ta, &ma);
+    double ub[3] = {wb[3] - qm * wald_Ar(a, B0, rb, tb), wb[4], wb[5] - qm * wald_Aph(a, B0, rb, tb)};
+    double ua[3] = {wa[3] - qm * wald_Ar(a, B0, ra, ta), wa[4], wa[5] - qm * wald_Aph(a, B0, ra, ta)};
+    const double Gb = gamma_lorentz(&mb, ub), Ga = gamma_lorentz(&ma, ua);
+    const double Gs = Ga + Gb;
+    if (v == 3)
+        return mb.alpha * (mb.gu_rr * (ua[0] + ub[0]) + 2.0 * mb.gu_rp * ub[2]) / Gs - mb.beta;
+    if (v == 4)
+        return mb.alpha * mb.gu_tt * (ua[1] + ub[1]) / Gs;
+    if (v == 5)
+        return mb.alpha * (2.0 * mb.gu_rp * ub[0] + mb.gu_pp * (ua[2] + ub[2])) / Gs;
+    const double a2 = a * a;
+    const double s2b = mb.s * mb.s, s2a = ma.s * ma.s, c2b = mb.c * mb.c, c2a = ma.c * ma.c;
+    const double Pb = rb / mb.rho2, Pa = ra / ma.rho2, Kb = 1.0 + c2b, Ka = 1.0 + c2a;
+    double d_rho2, d_f, d_s2, dP, dKP, dAph;
+    if (v == 0) {
+        d_rho2 = rb + ra;
+        dP = (a2 * c2b - rb * ra) / (mb.rho2 * ma.rho2);
+        d_f = 2.0 * M * dP;
+        d_s2 = 0.0;
+        dKP = Kb * dP;
+        dAph = 0.5 * B0 * s2b * (rb + ra - 2.0 * a2 * dKP);
+    } else {
+        const double h = 0.5 * (ta - tb);
+        const double d_c = -sin(0.5 * (ta + tb)) * sinc_(h);
+        const double d_c2 = (mb.c + ma.c) * d_c;
+        d_rho2 = a2 * d_c2;
+        dP = -rb * d_rho2 / (mb.rho2 * ma.rho2);
+        d_f = 2.0 * M * dP;
+        d_s2 = -d_c2;
+        dKP = d_c2 * Pa + Kb * dP;
+        dAph = 0.5 * B0 * (d_s2 * (rb * rb + a2 - 2.0 * a2 * Ka * Pa) - 2.0 * a2 * s2b * dKP);
+    }
+    const double dA0 = a * B0 * dKP;
+    const double dAr = 0.5 * B0 * (2.0 * a * dKP - a * d_s2);
+    const double dur = -qm * dAr, dup = -qm * dAph;
+    const double d_irho2 = -d_rho2 / (mb.rho2 * ma.rho2);
+    const double xx = mb.xi * ma.xi, sx = sqrt(xx);
+    const double d_ixi = -d_f / xx;
+    const double d_alpha = -d_f / (sx * (sqrt(mb.xi) + sqrt(ma.xi)));
+    const double d_beta = d_f / xx;
+    const double d_s2irho2 = (d_s2 * mb.rho2 - s2b * d_rho2) / (mb.rho2 * ma.rho2);
+    const double d_ipp = -(d_rho2 * s2a + mb.rho2 * d_s2) / (mb.rho2 * s2b * ma.rho2 * s2a);
+    const double d_grr = a2 * d_s2irho2 + d_ixi;
+    const double d_grp = a * d_irho2;
+    const double d_gtt = d_irho2;
+    const double dG2 = d_grr * ua[0] * ua[0] + 2.0 * d_grp * ua[0] * ua[2] + d_gtt * ua[1] * ua[1]
+                     + d_ipp * ua[2] * ua[2]
+                     + mb.gu_rr * (dur * ua[0] + ub[0] * dur)
+                     + 2.0 * mb.gu_rp * (dur * ua[2] + ub[0] * dup)
+                     + mb.gu_pp * (dup * ua[2] + ub[2] * dup);
+    (void)Pb;
+    return 0.5 * (ma.alpha + mb.alpha) * dG2 / Gs + 0.5 * Gs * d_alpha - (d_beta * ua[0] + mb.beta * dur)
+           - qm * dA0;
+}
+
 /* Coordinate-increment discrete gradient along one ordering of the six
  * variables (Sec. 2.2.3, Eq. hh and the displayed quotients): variable
  * ord[k] is moved from z0 to z1 in turn, and its component is the
@@ -504,7 +596,7 @@ static double dg_quot(double M, double a, const double *zb, const double *za, in
  * the analytic partial when |z1_v - z0_v| < eps, a guard against the 0/0 of
  * the plain quotient; the closed form has no 0/0 (it tends to the partial),
  * so eps is not used. */
-static void dg_path(double M, double a, const double *z0, const double *z1,
+static void dg_path(double M, double a, double B0, double qm, const double *z0, const double *z1,
                     const int *ord, double eps, double *G)
 {
     (void)eps;
@@ -514,7 +606,7 @@ static void dg_path(double M, double a, const double *z0, const double *z1,
         int v = ord[k];
         memcpy(za, zb, sizeof za);
         za[v] = z1[v];
-        G[v] = dg_quot(M, a, zb, za, v);
+        G[v] = (qm != 0.0 && B0 != 0.0) ? dg_quot_em(M, a, B0, qm, zb, za, v) : dg_quot(M, a, zb, za, v);
         memcpy(zb, za, sizeof zb);
     }
 }
@@ -526,7 +618,8 @@ static void dg_path(double M, double a, const double *z0, const double *z1,
  * within-pair orders (coordinate first, or momentum first, for every pair).
  * Each ordering telescopes exactly, so their average conserves H exactly;
  * the set is closed under reversal, which makes the scheme time-symmetric. */
-static void dg_grad(double M, double a, const double *z0, const double *z1, double eps, double *G)
+static void dg_grad(double M, double a, double B0, double qm, const double *z0, const double *z1, double eps,
+                    double *G)
 {
     static const int pairs[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
     double acc[6] = {0, 0, 0, 0, 0, 0}, g[6];
@@ -538,7 +631,7 @@ static void dg_grad(double M, double a, const double *z0, const double *z1, doub
                 ord[2 * q] = xf ? x : u;
                 ord[2 * q + 1] = xf ? u : x;
             }
-            dg_path(M, a, z0, z1, ord, eps, g);
+            dg_path(M, a, B0, qm, z0, z1, ord, eps, g);
             for (int i = 0; i < 6; ++i) acc[i] += g[i];
         }
     for (int i = 0; i < 6; ++i) G[i] = acc[i] / 12.0;
@@ -547,22 +640,41 @@ static void dg_grad(double M, double a, const double *z0, const double *z1, doub
 /* Sec. 2.2.3: discrete-gradient Hamiltonian step for geodesics,
  * dx/dt = D_u H, du/dt = -D_x H, solved by fixed-point iteration on z^{n+1}
  * (same stop rule as the IMR). */
+/* Kinetic <-> canonical momenta of a charged particle in the Wald field:
+ * pi_i = u_i + (q/m) A_i (A_th = 0); sgn = +1 maps u -> pi, -1 pi -> u. */
+static void canonical(double a, double B0, double qm, double *z, double sgn)
+{
+    z[3] += sgn * qm * wald_Ar(a, B0, z[0], z[1]);
+    z[5] += sgn * qm * wald_Aph(a, B0, z[0], z[1]);
+}
+
 static int step_ham(const or_ctx *c, double h, const double *z0, const double *guess, double *z1)
 {
-    double zk[6], G[6], zn[6];
+    /* Charged particles in the analytic Wald field (an extension, not in the
+     * paper): the same scheme on H_c(x, pi) with the potentials of Eq. (Amu),
+     * iterated in canonical variables, which conserves H and L exactly. */
+    const double B0 = (c->qm != 0.0 && c->p->field_kind == OR_FIELD_WALD) ? c->p->B0field : 0.0;
+    double w0[6], zk[6], G[6], zn[6];
+    memcpy(w0, z0, sizeof w0);
     memcpy(zk, guess, sizeof zk);
-    for (int k = 1; k <= c->p->max_iter; ++k) {
-        dg_grad(c->p->M, c->p->a, z0, zk, c->p->dg_eps, G);
-        for (int i = 0; i < 3; ++i) {
-            zn[i] = z0[i] + h * G[3 + i];
-            zn[3 + i] = z0[3 + i] - h * G[i];
-        }
-        int ok = converged(zn, zk, c->p->tol);
-        memcpy(zk, zn, sizeof zk);
-        if (ok) { memcpy(z1, zk, sizeof zk); return k; }
+    if (B0 != 0.0) {
+        canonical(c->p->a, B0, c->qm, w0, 1.0);
+        canonical(c->p->a, B0, c->qm, zk, 1.0);
     }
+    int k, ok = 0;
+    for (k = 1; k <= c->p->max_iter; ++k) {
+        dg_grad(c->p->M, c->p->a, B0, c->qm, w0, zk, c->p->dg_eps, G);
+        for (int i = 0; i < 3; ++i) {
+            zn[i] = w0[i] + h * G[3 + i];
+            zn[3 + i] = w0[3 + i] - h * G[i];
+        }
+        ok = converged(zn, zk, c->p->tol);
+        memcpy(zk, zn, sizeof zk);
+        if (ok) break;
+    }
+    if (B0 != 0.0) canonical(c->p->a, B0, c->qm, zk, -1.0);
     memcpy(z1, zk, sizeof zk);
-    return -c->p->max_iter;
+    return ok ? k : -c->p->max_iter;
 }
 
 /* Particle boundary conditions (Sec. 2.5, closing paragraph), half-th
@@ -728,9 +840,23 @@ void or_dg_quot(double M, double a, const double *zb, const double *za, int v, d
     *G = dg_quot(M, a, zb, za, v);
 }
 
+/* Charged quotient in canonical variables (Wald field B0, q/m = qm). */
+void or_dg_quot_em(double M, double a, double B0, double qm, const double *wb, const double *wa, int v, double *G)
+{
+    *G = dg_quot_em(M, a, B0, qm, wb, wa, v);
+}
+
+void or_wald_A(double a, double B0, int64_t n, const double *r, const double *th, double *Ar, double *Aph)
+{
+    for (int64_t p = 0; p < n; ++p) {
+        Ar[p] = wald_Ar(a, B0, r[p], th[p]);
+        Aph[p] = wald_Aph(a, B0, r[p], th[p]);
+    }
+}
+
 void or_dg_grad(double M, double a, const double *z0, const double *z1, double eps, double *G)
 {
-    dg_grad(M, a, z0, z1, eps, G);
+    dg_grad(M, a, 0.0, 0.0, z0, z1, eps, G);
 }
 
 /* One step of n particles.  F: six field arrays (Yee layout) when

@@ -413,3 +413,93 @@ def test_dg_converges_from_turning_points():
         nc, sch, its = O.push(O.push_params(a=a, dt=0.15, scheme=O.HAM, tol=1e-15), z, q, H0, D0, Hn, al)
         assert nc == 0 and its.max() <= 12
     assert np.abs(Hn - H0).max() <= 4e-15 * np.abs(H0).max()
+
+
+# ---- discrete-gradient scheme for charged particles in the Wald field (extension) ----
+
+def _Hc(a, B0, qm):
+    """H_c(x, pi) = H(x, u) with u = pi - (q/m) A (Eq. Amu), via the oracle's H."""
+    def f(w):
+        Ar, Aph = O.wald_A(a, B0, [w[0]], [w[1]])
+        z = w.copy(); z[3] -= qm * Ar[0]; z[5] -= qm * Aph[0]
+        return O.hamiltonian(1.0, a, B0, z[None, :], np.array([qm]))[0][0]
+    return f
+
+
+@pytest.mark.parametrize("a", [0.0, 0.7, 0.9])
+def test_charged_dg_quotient_closed_form(a):
+    """Canonical-variable quotients for a charged particle in the Wald field:
+    equal to the plain difference quotient of H_c at dz = 1e-3, and at
+    dz = 1e-12 to the partial derivatives that the Lorentz-force equations
+    (Eqs. p1, p2, O1, O2 with the App. B field) imply, d pi_i / dt = du_i/dt +
+    (q/m) dA_i/dt, with the potential derivatives by central differences: this
+    ties A_r, A_ph, A_0 of Eq. (Amu) to the field the RHS uses."""
+    B0, qm = 1.0, 1.5
+    rng = np.random.default_rng(int(a * 100) + 7)
+    Hc = _Hc(a, B0, qm)
+    for _ in range(12):
+        w = np.array([rng.uniform(2.5, 10), rng.uniform(0.4, 2.7), 0.3,
+                      rng.normal() * 0.5, rng.normal(), rng.normal() * 3])
+        Ar, Aph = O.wald_A(a, B0, [w[0]], [w[1]])
+        z = w.copy(); z[3] -= qm * Ar[0]; z[5] -= qm * Aph[0]
+        _, _, D, _, _ = O.wald(a, B0, [z[0]], [z[1]])
+        Bw = O.wald(a, B0, [z[0]], [z[1]])[0]
+        f = O.rhs(1.0, a, z[None, :], qm, D, Bw)[0]
+        h = 1e-6
+        dA = {}
+        for k in (0, 1):
+            e = np.zeros(2); e[k] = h
+            p1 = O.wald_A(a, B0, [w[0] + e[0]], [w[1] + e[1]])
+            m1 = O.wald_A(a, B0, [w[0] - e[0]], [w[1] - e[1]])
+            dA[k] = ((p1[0][0] - m1[0][0]) / (2 * h), (p1[1][0] - m1[1][0]) / (2 * h))
+        dpir = f[3] + qm * (dA[0][0] * f[0] + dA[1][0] * f[1])
+        dpit = f[4]
+        partial = {0: None, 1: None, 3: f[0], 4: f[1], 5: f[2]}
+        # dH/dr|pi = -dpi_r/dt, dH/dth|pi = -dpi_th/dt
+        partial[0] = -dpir
+        partial[1] = -dpit
+        for v in (0, 1, 3, 4, 5):
+            wa = w.copy(); wa[v] += 1e-3 * (1 + abs(w[v]))
+            plain = (Hc(wa) - Hc(w)) / (wa[v] - w[v])
+            q = O.dg_quot_em(1.0, a, B0, qm, w, wa, v)
+            assert abs(q - plain) <= 1e-10 * abs(plain) + 4e-16 * max(1.0, abs(Hc(w))) / abs(wa[v] - w[v]), (v, q, plain)
+            wa = w.copy(); wa[v] += 1e-12
+            q = O.dg_quot_em(1.0, a, B0, qm, w, wa, v)
+            assert abs(q - partial[v]) <= 1e-7 * (abs(partial[v]) + 1.0), (v, q, partial[v])
+
+
+def _wald_charged_states(a, n, seed):
+    rng = np.random.default_rng(seed)
+    return np.stack([rng.uniform(4, 9, n), rng.uniform(0.7, 2.4, n), np.zeros(n),
+                     rng.normal(size=n) * 0.3, rng.normal(size=n) * 0.5, rng.normal(size=n) * 2], 1)
+
+
+def test_charged_dg_conserves_H_and_L_and_converges_to_the_lorentz_force():
+    """In the exact Wald field the canonical discrete-gradient scheme keeps
+    H (Sec. 3.1.3) to rounding and L = u_ph + (q/m) A_ph exactly for any dt,
+    and its trajectory converges at second order to the RK4 solution of the
+    Lorentz-force equations (Eqs. p1, p2, O1, O2) in the same field."""
+    a, B0, qm = 0.9, 1.0, 2.0
+    z0 = _wald_charged_states(a, 16, 3)
+    n = z0.shape[0]
+    q = np.full(n, qm)
+    kw = dict(a=a, field_kind=O.FIELD_WALD, B0field=B0, B0pot=B0, tol=1e-15, max_iter=100)
+    H0, L0, D0 = O.hamiltonian(1.0, a, B0, z0, q)
+
+    def run(scheme, dt, steps):
+        z = z0.copy(); Hn = H0.copy(); al = np.ones(n, np.uint8)
+        nc = 0
+        for _ in range(steps):
+            nc += O.push(O.push_params(dt=dt, scheme=scheme, **kw), z, q, H0, D0, Hn, al)[0]
+        return z, Hn, al, nc
+
+    z, Hn, al, nc = run(O.HAM, 0.1, 20)
+    assert al.all() and nc == 0
+    H1, L1, _ = O.hamiltonian(1.0, a, B0, z, q)
+    assert np.abs(H1 - H0).max() <= 1e-14 * np.abs(H0).max()
+    assert np.abs(L1 - L0).max() <= 1e-13 * np.abs(L0).max()
+    T = 0.8
+    ref = run(O.RK4, T / 400, 400)[0]
+    errs = [np.abs(run(O.HAM, T / m, m)[0] - ref).max() for m in (20, 40, 80)]
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(abs(r_ - 2) < 0.35 for r_ in rates), (errs, rates)
