@@ -700,6 +700,44 @@ def run_adaptive_neutral(device, n=1 << 18, steps=20, pre_steps=20, K=32):
             "steps": steps, "steps_before_measurement": pre_steps, "runs": runs}
 
 
+def run_charged_dg(device, n=1 << 20, steps=20):
+    """Charged test particles in the analytic Wald field (no grid: the
+    Lorentz force from App. B.1 at each point), the headline's draws and
+    dt = 1e-3: RK4 alone, the IMR alone and the discrete-gradient scheme in
+    canonical momenta (an extension, not in the paper).  Reports throughput
+    and max |H - H0| / D0 and max |L - L0| / |L0| after the run."""
+    import torch
+    F, g, ctx, fields, p = setup(n, 0, device)
+    snap = _snapshot(p)
+    s = torch.cuda.current_stream(device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    H0, L0 = F.fpic_hamiltonian(ctx, p, B0pot=B0)
+    runs = []
+    for name, sch in (("RK4", F.FPIC_RK4), ("IMR", F.FPIC_IMR), ("discrete gradient", F.FPIC_HAM)):
+        _restore(p, snap)
+        prm = F.push_params(DT, scheme=sch, implicit=F.FPIC_HAM, tol=1e-14, max_iter=50, r_max=float(g.rn[-1]),
+                            B0pot=B0, B0field=B0)
+        F.fpic_push(ctx, p, None, prm)
+        torch.cuda.synchronize()
+        tot, ps, it = 0.0, 0, 0
+        for _ in range(steps):
+            e0.record(s)
+            st = F.fpic_push(ctx, p, None, prm, stats=True)
+            e1.record(s)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1) * 1e-3
+            ps += st["n_alive_before"]
+            it += st["n_iter_total"]
+        H, L = F.fpic_hamiltonian(ctx, p, B0pot=B0)
+        al = p.alive.bool()
+        dH = float(((H - p.H0).abs() / p.D0)[al].max().item())
+        dL = float(((L - L0).abs() / L0.abs().clamp_min(1e-300))[al].max().item())
+        runs.append({"scheme": name, "value": ps / tot, "unit": UNIT, "ms_per_step": 1e3 * tot / steps,
+                     "mean_iterations": it / max(ps, 1), "max_dH_over_D0": dH, "max_dL_over_L0": dL})
+    return {"workload": f"charged test particles in the analytic Wald field, a={A_SPIN}, {n} particles, dt={DT}",
+            "steps": steps + 1, "runs": runs}
+
+
 def run_div_clean(device, grid_n=1024, n_iter=500, reps=3):
     """Sec. 2.4 divergence cleaning (Eq. phi, n_iter Jacobi sweeps and the
     correction) of a Wald D perturbed by noise against a random rho on the
@@ -894,6 +932,7 @@ def main():
         line["adaptive_dt"] = run_adaptive(dev)
         line["adaptive_dt_neutral"] = run_adaptive_neutral(dev)
         line["inject"] = run_inject(dev, 1024, 16)
+        line["charged_dg"] = run_charged_dg(dev)
     if rank == 0:
         if pool is not None:
             try:

@@ -95,7 +95,15 @@ typedef struct {
  *               0 = dt.  Same sign as dt.  Pure schemes ignore it; the
  *               learned guess needs 0 or dt.
  *   t         : nullable device array (n doubles): each alive particle's
- *               time, advanced by the step it took (dt or dt_implicit) */
+ *               time, advanced by the step it took (dt or dt_implicit)
+ *   B0field   : with fields == NULL, the analytic Wald field of this B0
+ *               (App. B.1, M = 1) supplies the Lorentz force instead of a
+ *               grid, and the discrete-gradient scheme (FPIC_HAM, alone or as
+ *               the hybrid's partner) also takes charged particles: it runs
+ *               in canonical momenta pi_i = u_i + (q/m) A_i with the
+ *               potentials of Eq. (Amu) and conserves H (with B0pot =
+ *               B0field) and L exactly (an extension, not in the paper).
+ *               0 = none.  Not with fields, the batched or the learned push. */
 typedef struct {
     double dt;
     int scheme;
@@ -110,6 +118,7 @@ typedef struct {
     void *const *events;
     double dt_implicit;
     double *t;
+    double B0field;
 } fpic_push_params;
 
 /* Host-side counters of one push (filled only when a pointer is passed;

@@ -320,4 +320,34 @@ __device__ __forceinline__ double eval_H(const BH& bh, const double y[6], double
     return eval_H_sc(bh, y, s, c, qm, B0pot);
 }
 
+// The Wald field (App. B.1) at (r, th) with sin/cos of th given: B^i =
+// eta^ijk d_j A_k / sqrt(gamma) from the potentials of Eq. (Amu), E_i =
+// d_i A_0, D^i raised from Eq. (Ei) with beta = (beta^r, 0, 0).
+__device__ __forceinline__ void wald_point_sc(const BH& bh, double B0, double r, double s, double c, double D[3],
+                                              double B[3])
+{
+    Geo g;
+    geo_eval(bh, r, s, c, g);
+    const double M = bh.M, a = bh.a, a2 = bh.a2;
+    const double P = g.rho2, iP = g.irho2, iP2 = iP * iP;
+    const double sc = s * c, s2 = s * s, c2p1 = 1.0 + c * c;
+    const double q = a2 * c2p1 - P;                 // enters d_th[(1+c^2)/rho^2]
+    const double isg = 1.0 / g.sqrtg;
+    const double dAph_t = B0 * sc * (r * r + a2 - 2.0 * M * a2 * r * c2p1 * iP - 2.0 * M * a2 * r * s2 * q * iP2);
+    const double dAph_r = 0.5 * B0 * s2 * (2.0 * r - 2.0 * M * a2 * c2p1 * (P - 2.0 * r * r) * iP2);
+    const double dAr_t = B0 * a * sc * (-1.0 + 2.0 * M * r * q * iP2);
+    B[0] = dAph_t * isg;
+    B[1] = -dAph_r * isg;
+    B[2] = -dAr_t * isg;
+    const double Er = B0 * a * M * c2p1 * (P - 2.0 * r * r) * iP2;
+    const double Et = 2.0 * B0 * a * M * r * sc * q * iP2;
+    // D_i from Eq. (Ei) with beta = (beta^r, 0, 0), then raised
+    const double Dr_ = Er / g.alpha;
+    const double Dt_ = (Et + g.sqrtg * g.beta * B[2]) / g.alpha;
+    const double Dp_ = -g.sqrtg * g.beta * B[1] / g.alpha;
+    D[0] = fma(g.gurr, Dr_, g.gurp * Dp_);
+    D[1] = g.gutt * Dt_;
+    D[2] = fma(g.gurp, Dr_, g.gupp * Dp_);
+}
+
 }  // namespace fpic

@@ -36,6 +36,7 @@ struct RunK {
     int has_fields;
     int has_grid;
     double B0pot, r_h, r_max;
+    double B0field;           // analytic Wald field (no grid fields): its B0, else 0
     long long begin, end;     // particle range of the run (batched push)
 };
 
@@ -119,7 +120,10 @@ __device__ __forceinline__ void F_at_sc(const RunK& R, const double y[6], double
                                         double f[6], double& H)
 {
     double D[3] = {0, 0, 0}, B[3] = {0, 0, 0};
-    if (em) gather(R.G, R.F, y[0], y[1], D, B);
+    if (em) {
+        if (R.B0field != 0.0) wald_point_sc(R.bh, R.B0field, y[0], s, c, D, B);
+        else gather(R.G, R.F, y[0], y[1], D, B);
+    }
     eval_rhs_sc(R.bh, y, s, c, qm, em, D, B, R.B0pot, f, H);
 }
 
@@ -213,7 +217,7 @@ __global__ void __launch_bounds__(128) k_explicit(const __grid_constant__ PushK 
     double z0[6], kk[6], acc[6], y[6];
     load_state(k.P, p, z0);
     const double qm = k.P.qm[p];
-    const bool em = R.has_fields && qm != 0.0;
+    const bool em = (R.has_fields || R.B0field != 0.0) && qm != 0.0;
     const double dt = k.dt, hdt = 0.5 * k.dt;
     double Hd, s0, c0, sn, cn;
     sincos(z0[1], &s0, &c0);
@@ -401,7 +405,7 @@ __global__ void __launch_bounds__(128, 4) k_imr(const __grid_constant__ PushK k,
                                                 : k.guess[(size_t)i * k.n + p];
                         }
                         qm = k.P.qm[p];
-                        em = R->has_fields && qm != 0.0;
+                        em = (R->has_fields || R->B0field != 0.0) && qm != 0.0;
                         it = 0;
                     }
                 } else {
@@ -691,6 +695,209 @@ __global__ void __launch_bounds__(128) k_dg(PushK k, int all_mode)
     warp_add(&k.cnt[CNT_REMOVED], n_rm, m);
 }
 
+// ---------------------------------------------------------------------------
+// Discrete-gradient scheme for charged particles in the analytic Wald field
+// (an extension, not in the paper): the same scheme on
+//   H_c(x, pi) = alpha Gamma(u) - beta^r u_r - (q/m) A_0,  u = pi - (q/m) A(x),
+// in canonical momenta pi_i = u_i + (q/m) A_i with the potentials of Eq. (Amu)
+// (A_th = 0); pi_ph is conserved.  Quotients in closed form as above, the
+// position moves also carrying the potential differences (P = r / rho^2,
+// K = 1 + c^2: A_0 = a B0 M K P, A_r = (B0/2)(2 a M K P - a s^2),
+// A_ph = (B0/2) s^2 (r^2 + a^2 - 2 M a^2 K P)).  Neutral particles take the
+// same path with q = 0.
+// ---------------------------------------------------------------------------
+struct PotP {
+    double Ar, Aph, K, P;      // potentials and K, P at a metric point
+};
+
+__device__ __forceinline__ PotP pot_at(const BH& bh, double B0, double r, const Geo& g)
+{
+    PotP o;
+    o.K = fma(g.c, g.c, 1.0);
+    o.P = r * g.irho2;
+    const double KP = o.K * o.P;
+    o.Ar = 0.5 * B0 * bh.a * fma(2.0 * bh.M, KP, -g.s2);
+    o.Aph = 0.5 * B0 * g.s2 * fma(-2.0 * bh.M * bh.a2, KP, fma(r, r, bh.a2));
+    return o;
+}
+
+struct PDem {
+    PD m;                      // metric differences per unit increment
+    double dAr, dAph, dA0;     // potential differences per unit increment
+};
+
+__device__ __forceinline__ PDem pdem_r(const BH& bh, double B0, const Geo& b, const Geo& a, const PotP& pb,
+                                       double r0, double r1)
+{
+    PDem d;
+    d.m = pd_r(bh, b, a, r0, r1);
+    const double dP = fma(bh.a2, b.c * b.c, -r0 * r1) * (b.irho2 * a.irho2);
+    const double dKP = pb.K * dP;
+    d.dA0 = bh.a * B0 * bh.M * dKP;
+    d.dAr = d.dA0;
+    d.dAph = 0.5 * B0 * b.s2 * fma(-2.0 * bh.M * bh.a2, dKP, r0 + r1);
+    return d;
+}
+
+__device__ __forceinline__ PDem pdem_th(const BH& bh, double B0, const Geo& b, const Geo& a, const PotP& pb,
+                                        const PotP& pa, double r, double dc)
+{
+    PDem d;
+    d.m = pd_th(bh, b, a, r, dc);
+    const double dc2 = (b.c + a.c) * dc;
+    const double dP = -r * bh.a2 * dc2 * (b.irho2 * a.irho2);
+    const double dKP = fma(dc2, pa.P, pb.K * dP);
+    d.dA0 = bh.a * B0 * bh.M * dKP;
+    d.dAr = 0.5 * B0 * bh.a * fma(2.0 * bh.M, dKP, dc2);
+    const double Ya = fma(-2.0 * bh.M * bh.a2, pa.K * pa.P, fma(r, r, bh.a2));
+    d.dAph = 0.5 * B0 * fma(-dc2, Ya, -2.0 * bh.M * bh.a2 * b.s2 * dKP);
+    return d;
+}
+
+// Quotient of a position move; (ub_r, ub_p) and (ua_r, ua_p) the kinetic
+// momenta at the two ends (same pi), ut the th momentum.
+__device__ __forceinline__ double dq_pos_em(const PDem& d, const Geo& b, double qm, double gb, double ga,
+                                            double ub_r, double ub_p, double ua_r, double ua_p, double ut)
+{
+    const double dur = -qm * d.dAr, dup = -qm * d.dAph;
+    double dG2 = fma(d.m.dgrr * ua_r, ua_r, fma(2.0 * d.m.dgrp * ua_r, ua_p, fma(d.m.dgtt * ut, ut, d.m.dgpp * ua_p * ua_p)));
+    dG2 = fma(b.gurr * dur, ua_r + ub_r, dG2);
+    dG2 = fma(2.0 * b.gurp, fma(dur, ua_p, ub_r * dup), dG2);
+    dG2 = fma(b.gupp * dup, ua_p + ub_p, dG2);
+    const double gs = ga + gb;
+    return fma(0.5 * d.m.asum, dG2 / gs, fma(0.5 * gs, d.m.dal, -fma(d.m.dbe, ua_r, fma(b.beta, dur, qm * d.dA0))));
+}
+
+__global__ void __launch_bounds__(128) k_dg_em(PushK k, int all_mode)
+{
+    const long long qn = all_mode ? k.n : k.cnt[CNT_QUEUE];
+    long long n_it = 0, n_nc = 0, n_rm = 0;
+    const BH& bh = k.run.bh;
+    const double B0 = k.run.B0field;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < qn;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long p = all_mode ? idx : (long long)k.queue[idx];
+        if (all_mode && !k.P.alive[p]) {
+            k.P.scheme[p] = 0;
+            k.P.iters[p] = 0;
+            continue;
+        }
+        const double qm = k.P.qm[p];
+        double z0[6], zk[6];
+        load_state(k.P, p, z0);
+        if (all_mode) {
+            for (int i = 0; i < 6; ++i) zk[i] = z0[i];
+        } else {
+            for (int i = 0; i < 6; ++i) zk[i] = k.guess[(size_t)i * k.n + p];
+        }
+        const double R0 = z0[0], T0 = z0[1];
+        double s0, c0;
+        sincos(T0, &s0, &c0);
+        const Geo m00 = geo_at(bh, R0, s0, c0);
+        const PotP p00 = pot_at(bh, B0, R0, m00);
+        // canonical momenta of z^n and of the start
+        const double U0 = fma(qm, p00.Ar, z0[3]), V0 = z0[4], P = fma(qm, p00.Aph, z0[5]);
+        {
+            double sk, ck;
+            sincos(zk[1], &sk, &ck);
+            const Geo gk = geo_at(bh, zk[0], sk, ck);
+            const PotP pk = pot_at(bh, B0, zk[0], gk);
+            zk[3] = fma(qm, pk.Ar, zk[3]);
+            zk[5] = fma(qm, pk.Aph, zk[5]);
+        }
+        zk[5] = P;
+        // kinetic momenta at m00
+        const double u00r = fma(-qm, p00.Ar, U0), u00p = fma(-qm, p00.Aph, P);
+        const double g00 = dg_gam(m00, u00r, V0, u00p);
+        const double f00 = m00.alpha * fma(m00.gurp, u00r, m00.gupp * u00p) / g00;
+        int it = 0;
+        bool ok = false;
+        double wn[6];
+        while (it < k.max_iter) {
+            const double R1 = zk[0], T1 = zk[1], U1 = zk[3], V1 = zk[4];
+            double s1, c1;
+            sincos(T1, &s1, &c1);
+            const Geo m10 = geo_at(bh, R1, s0, c0), m01 = geo_at(bh, R0, s1, c1), m11 = geo_at(bh, R1, s1, c1);
+            const PotP p10 = pot_at(bh, B0, R1, m10), p01 = pot_at(bh, B0, R0, m01), p11 = pot_at(bh, B0, R1, m11);
+            const double dT = T1 - T0;
+            const double dc = -sin(0.5 * (T0 + T1)) * sinc_dev(0.5 * dT);
+            const PDem r_T0 = pdem_r(bh, B0, m00, m10, p00, R0, R1), r_T1 = pdem_r(bh, B0, m01, m11, p01, R0, R1);
+            const PDem t_R0 = pdem_th(bh, B0, m00, m01, p00, p01, R0, dc);
+            const PDem t_R1 = pdem_th(bh, B0, m10, m11, p10, p11, R1, dc);
+            // kinetic u_r, u_ph at each metric point for pi_r = U0 / U1 (pi_ph = P)
+            const double a00 = qm * p00.Ar, a10 = qm * p10.Ar, a01 = qm * p01.Ar, a11 = qm * p11.Ar;
+            const double up00 = u00p, up10 = fma(-qm, p10.Aph, P), up01 = fma(-qm, p01.Aph, P),
+                         up11 = fma(-qm, p11.Aph, P);
+            const double r00_0 = U0 - a00, r00_1 = U1 - a00, r10_0 = U0 - a10, r10_1 = U1 - a10;
+            const double r01_0 = U0 - a01, r01_1 = U1 - a01, r11_0 = U0 - a11, r11_1 = U1 - a11;
+            // Gamma at the visited states
+            const double g00_u1 = dg_gam(m00, r00_1, V0, up00), g00_v1 = dg_gam(m00, r00_0, V1, up00);
+            const double g10 = dg_gam(m10, r10_0, V0, up10), g10_u1 = dg_gam(m10, r10_1, V0, up10),
+                         g10_uv = dg_gam(m10, r10_1, V1, up10);
+            const double g01 = dg_gam(m01, r01_0, V0, up01), g01_v1 = dg_gam(m01, r01_0, V1, up01),
+                         g01_uv = dg_gam(m01, r01_1, V1, up01);
+            const double g11_u1 = dg_gam(m11, r11_1, V0, up11), g11_uv = dg_gam(m11, r11_1, V1, up11),
+                         g11_v1 = dg_gam(m11, r11_0, V1, up11);
+            // order A: r, u_r, th, u_th
+            const double rA = dq_pos_em(r_T0, m00, qm, g00, g10, r00_0, up00, r10_0, up10, V0);
+            const double uA = dq_ur(m10, g10, g10_u1, r10_0, r10_1, up10);
+            const double tA = dq_pos_em(t_R1, m10, qm, g10_u1, g11_u1, r10_1, up10, r11_1, up11, V0);
+            const double vA = dq_ut(m11, g11_u1, g11_uv, V0, V1);
+            // order B: u_r, r, u_th, th
+            const double uB = dq_ur(m00, g00, g00_u1, r00_0, r00_1, up00);
+            const double rB = dq_pos_em(r_T0, m00, qm, g00_u1, g10_u1, r00_1, up00, r10_1, up10, V0);
+            const double vB = dq_ut(m10, g10_u1, g10_uv, V0, V1);
+            const double tB = dq_pos_em(t_R1, m10, qm, g10_uv, g11_uv, r10_1, up10, r11_1, up11, V1);
+            // order C: th, u_th, r, u_r
+            const double tC = dq_pos_em(t_R0, m00, qm, g00, g01, r00_0, up00, r01_0, up01, V0);
+            const double vC = dq_ut(m01, g01, g01_v1, V0, V1);
+            const double rC = dq_pos_em(r_T1, m01, qm, g01_v1, g11_v1, r01_0, up01, r11_0, up11, V1);
+            const double uC = dq_ur(m11, g11_v1, g11_uv, r11_0, r11_1, up11);
+            // order D: u_th, th, u_r, r
+            const double vD = dq_ut(m00, g00, g00_v1, V0, V1);
+            const double tD = dq_pos_em(t_R0, m00, qm, g00_v1, g01_v1, r00_0, up00, r01_0, up01, V1);
+            const double uD = dq_ur(m01, g01_v1, g01_uv, r01_0, r01_1, up01);
+            const double rD = dq_pos_em(r_T1, m01, qm, g01_uv, g11_uv, r01_1, up01, r11_1, up11, V1);
+            const double Gr = 0.25 * (rA + rB + rC + rD);
+            const double Gt = 0.25 * (tA + tB + tC + tD);
+            const double Gu = 0.25 * (uA + uB + uC + uD);
+            const double Gv = 0.25 * (vA + vB + vC + vD);
+            const double Gp = (2.0 * f00 + m10.alpha * fma(m10.gurp, r10_1, m10.gupp * up10) / g10_u1 +
+                               m01.alpha * fma(m01.gurp, r01_0, m01.gupp * up01) / g01_v1 +
+                               2.0 * m11.alpha * fma(m11.gurp, r11_1, m11.gupp * up11) / g11_uv) / 6.0;
+            wn[0] = fma(k.dt_imp, Gu, z0[0]);
+            wn[1] = fma(k.dt_imp, Gv, z0[1]);
+            wn[2] = fma(k.dt_imp, Gp, z0[2]);
+            wn[3] = fma(-k.dt_imp, Gr, U0);
+            wn[4] = fma(-k.dt_imp, Gt, V0);
+            wn[5] = P;
+            ok = conv6(wn, zk, k.tol);
+            for (int i = 0; i < 6; ++i) zk[i] = wn[i];
+            ++it;
+            if (ok) break;
+        }
+        if (!ok) ++n_nc;
+        n_it += it;
+        // back to kinetic momenta at x^{n+1}
+        {
+            double sk, ck;
+            sincos(zk[1], &sk, &ck);
+            const Geo gk = geo_at(bh, zk[0], sk, ck);
+            const PotP pk = pot_at(bh, B0, zk[0], gk);
+            zk[3] = fma(-qm, pk.Ar, zk[3]);
+            zk[5] = fma(-qm, pk.Aph, zk[5]);
+        }
+        const double H1 = eval_H(bh, zk, qm, k.run.B0pot);
+        if (!finish(k.run, k.P, p, zk, H1, 1, it)) ++n_rm;
+        if (k.t) k.t[p] += k.dt_imp;
+    }
+    const unsigned m = __activemask();
+    warp_add(&k.cnt[CNT_ITERS], n_it, m);
+    warp_add(&k.cnt[CNT_NOTCONV], n_nc, m);
+    warp_add(&k.cnt[CNT_EVALS], n_it, m);
+    warp_add(&k.cnt[CNT_REMOVED], n_rm, m);
+}
+
 __global__ void k_count_alive(PartDev P, long long n, long long* cnt)
 {
     long long v = 0;
@@ -738,6 +945,8 @@ extern "C" int fpic_push(fpic_ctx* c, fpic_particles* p, const double* const fie
     if (!particles_ok(p, true)) return set_error(FPIC_EINVAL, "fpic_push: a particle array is NULL");
     if (!(std::isfinite(prm->dt)) || prm->dt == 0.0) return set_error(FPIC_EINVAL, "fpic_push: dt must be finite and nonzero");
     if (!dt_implicit_ok(prm)) return set_error(FPIC_EINVAL, "fpic_push: dt_implicit must be 0 or finite with the sign of dt");
+    if (prm->B0field != 0.0 && (fields || !std::isfinite(prm->B0field) || c->M != 1.0))
+        return set_error(FPIC_EINVAL, "fpic_push: B0field needs fields == NULL, a finite value and M = 1");
     if (prm->scheme < FPIC_RK4 || prm->scheme > FPIC_HYB2) return set_error(FPIC_EINVAL, "fpic_push: unknown scheme %d", prm->scheme);
     if (prm->scheme >= FPIC_HYB1 && prm->implicit != FPIC_IMR && prm->implicit != FPIC_HAM)
         return set_error(FPIC_EINVAL, "fpic_push: implicit partner must be FPIC_IMR or FPIC_HAM");
@@ -775,6 +984,7 @@ static int push_core(fpic_ctx* c, fpic_particles* p, const double* const fields[
     k.tol = prm->tol;
     k.dg_eps = prm->dg_eps;
     k.run.B0pot = prm->B0pot;
+    k.run.B0field = has_fields ? 0.0 : prm->B0field;
     k.run.r_h = c->r_h;
     k.run.r_max = prm->r_max;
     k.scheme = prm->scheme;
@@ -826,13 +1036,15 @@ static int push_core(fpic_ctx* c, fpic_particles* p, const double* const fields[
         k_imr<0><<<imr_grid, TB, 0, s>>>(k, 1);
         k_imr_finish<><<<persist, 256, 0, s>>>(k, 1);
     } else if (prm->scheme == FPIC_HAM) {
-        k_dg<<<nb, TB, 0, s>>>(k, 1);
+        if (k.run.B0field != 0.0) k_dg_em<<<nb, TB, 0, s>>>(k, 1);
+        else k_dg<<<nb, TB, 0, s>>>(k, 1);
     } else if (prm->scheme >= FPIC_HYB1 && prm->implicit == FPIC_IMR) {
         k_order<<<persist, 256, 0, s>>>(k);
         k_imr<0><<<imr_grid, TB, 0, s>>>(k, 0);
         k_imr_finish<><<<persist, 256, 0, s>>>(k, 0);
     } else if (prm->scheme >= FPIC_HYB1) {
-        k_dg<<<nb, TB, 0, s>>>(k, 0);
+        if (k.run.B0field != 0.0) k_dg_em<<<nb, TB, 0, s>>>(k, 0);
+        else k_dg<<<nb, TB, 0, s>>>(k, 0);
     }
     if (ev) FPIC_CUDA(cudaEventRecord(ev[3], s));
     FPIC_CUDA(cudaGetLastError());
@@ -971,6 +1183,8 @@ extern "C" int fpic_push_noalloc(double M, double a, fpic_particles* p, const fp
     if (!particles_ok(p, true)) return set_error(FPIC_EINVAL, "fpic_push_noalloc: a particle array is NULL");
     if (!(std::isfinite(prm->dt)) || prm->dt == 0.0) return set_error(FPIC_EINVAL, "fpic_push_noalloc: dt must be finite and nonzero");
     if (!dt_implicit_ok(prm)) return set_error(FPIC_EINVAL, "fpic_push_noalloc: bad dt_implicit");
+    if (prm->B0field != 0.0 && (!std::isfinite(prm->B0field) || M != 1.0))
+        return set_error(FPIC_EINVAL, "fpic_push_noalloc: B0field needs a finite value and M = 1");
     if (prm->scheme < FPIC_RK4 || prm->scheme > FPIC_HYB2) return set_error(FPIC_EINVAL, "fpic_push_noalloc: unknown scheme %d", prm->scheme);
     if (prm->scheme >= FPIC_HYB1 && prm->implicit != FPIC_IMR && prm->implicit != FPIC_HAM)
         return set_error(FPIC_EINVAL, "fpic_push_noalloc: implicit partner must be FPIC_IMR or FPIC_HAM");
@@ -995,6 +1209,7 @@ extern "C" int fpic_push_noalloc(double M, double a, fpic_particles* p, const fp
     k.tol = prm->tol;
     k.dg_eps = prm->dg_eps;
     k.run.B0pot = prm->B0pot;
+    k.run.B0field = prm->B0field;
     k.run.r_h = M + sqrt(M * M - a * a);
     k.run.r_max = prm->r_max;
     k.scheme = prm->scheme;
@@ -1030,13 +1245,15 @@ extern "C" int fpic_push_noalloc(double M, double a, fpic_particles* p, const fp
         k_imr<0><<<persist / 2, TB, 0, s>>>(k, 1);
         k_imr_finish<><<<persist, 256, 0, s>>>(k, 1);
     } else if (prm->scheme == FPIC_HAM) {
-        k_dg<<<nb, TB, 0, s>>>(k, 1);
+        if (k.run.B0field != 0.0) k_dg_em<<<nb, TB, 0, s>>>(k, 1);
+        else k_dg<<<nb, TB, 0, s>>>(k, 1);
     } else if (prm->scheme >= FPIC_HYB1 && prm->implicit == FPIC_IMR) {
         k_order<<<persist, 256, 0, s>>>(k);
         k_imr<0><<<persist / 2, TB, 0, s>>>(k, 0);
         k_imr_finish<><<<persist, 256, 0, s>>>(k, 0);
     } else if (prm->scheme >= FPIC_HYB1) {
-        k_dg<<<nb, TB, 0, s>>>(k, 0);
+        if (k.run.B0field != 0.0) k_dg_em<<<nb, TB, 0, s>>>(k, 0);
+        else k_dg<<<nb, TB, 0, s>>>(k, 0);
     }
     if (ev) FPIC_CUDA(cudaEventRecord(ev[3], s));
     FPIC_CUDA(cudaGetLastError());
@@ -1195,6 +1412,7 @@ static void fill_pushk(PushK& k, fpic_ctx* c, fpic_particles* p, const double* c
     k.tol = prm->tol;
     k.dg_eps = prm->dg_eps;
     k.run.B0pot = prm->B0pot;
+    k.run.B0field = 0.0;
     k.run.r_h = c->r_h;
     k.run.r_max = prm->r_max;
     k.scheme = prm->scheme;
@@ -1496,6 +1714,7 @@ extern "C" int fpic_push_learned(fpic_ctx* c, fpic_mlp* m, fpic_particles* p, co
     if (!push_prm_ok(prm)) return set_error(FPIC_EINVAL, "fpic_push_learned: need a Hyb1/Hyb2 scheme with the IMR partner");
     if (prm->dt_implicit != 0.0 && prm->dt_implicit != prm->dt)
         return set_error(FPIC_EINVAL, "fpic_push_learned: the learned guess is trained for dt_implicit = dt");
+    if (prm->B0field != 0.0) return set_error(FPIC_EINVAL, "fpic_push_learned: B0field is not supported");
     if (p->n < 0 || p->n >= (1LL << 31)) return set_error(FPIC_EINVAL, "fpic_push_learned: n out of range");
     if (!particles_ok(p, true)) return set_error(FPIC_EINVAL, "fpic_push_learned: NULL particle array");
     if (fields && !c->has_grid) return set_error(FPIC_EINVAL, "fpic_push_learned: fields given but no grid set");
@@ -1596,6 +1815,7 @@ extern "C" int fpic_push_batched(const fpic_run* runs, int nruns, fpic_particles
     if (!particles_ok(p, true)) return set_error(FPIC_EINVAL, "fpic_push_batched: NULL particle array");
     if (!(std::isfinite(prm->dt)) || prm->dt == 0.0) return set_error(FPIC_EINVAL, "fpic_push_batched: bad dt");
     if (!dt_implicit_ok(prm)) return set_error(FPIC_EINVAL, "fpic_push_batched: bad dt_implicit");
+    if (prm->B0field != 0.0) return set_error(FPIC_EINVAL, "fpic_push_batched: B0field is not supported");
     if (prm->scheme != FPIC_RK4 && prm->scheme != FPIC_IMR && prm->scheme != FPIC_HYB1 && prm->scheme != FPIC_HYB2)
         return set_error(FPIC_EINVAL, "fpic_push_batched: scheme must be RK4, IMR, Hyb1 or Hyb2");
     if (prm->scheme >= FPIC_HYB1 && prm->implicit != FPIC_IMR)

@@ -426,3 +426,49 @@ def test_adaptive_step_dg_partner_matches_oracle(F):
     assert np.all(err[~near] <= bound[~near]), (err / bound).max()
     imp = (so == 1) & ~near & (ag == 1)
     assert np.abs(Hg[imp] - H0[imp]).max() < 2e-14
+
+
+@pytest.mark.parametrize("scheme", ["RK4", "IMR", "HAM", "HYB2"])
+def test_analytic_wald_push_matches_oracle(F, scheme):
+    """Charged particles in the analytic Wald field (fields = NULL, B0field):
+    RK4 / IMR / the discrete-gradient scheme in canonical momenta (an
+    extension) / Hyb2 with the discrete-gradient partner, one step of 3001
+    e-/e+ and neutral particles, a = 0.9, dt = 0.05: states within 1e-12 of
+    the oracle (choices bit-exact away from threshold ties); the
+    discrete-gradient steps keep H to 1e-14."""
+    a, B0, dt = 0.9, 1.0, 0.05
+    ctx = _mk(F, a)
+    rng = np.random.default_rng(21)
+    n = 3001
+    z = np.stack([rng.uniform(4, 9, n), rng.uniform(0.7, 2.4, n), rng.uniform(0, 6, n),
+                  rng.normal(size=n) * 0.3, rng.normal(size=n) * 0.5, rng.normal(size=n) * 2], 1)
+    q = np.choose(np.arange(n) % 3, [np.full(n, -2.0), np.full(n, 2.0), np.zeros(n)])
+    H0, _, D0 = O.hamiltonian(1.0, a, B0, z, q)
+    Hn = H0.copy()
+    sch = getattr(F, "FPIC_" + scheme)
+    thr = 1e-12
+    if scheme == "HYB2":
+        pr = O.push_params(a=a, dt=dt, scheme=O.RK4, field_kind=O.FIELD_WALD, B0field=B0, B0pot=B0)
+        zr = np.ascontiguousarray(z.copy()); Hr = Hn.copy()
+        O.push(pr, zr, q, H0, D0, Hr, np.ones(n, np.uint8))
+        stat = np.abs(Hr - H0) / D0
+        thr = float(np.median(stat))
+    p = make_particles(z, q, H0, D0, Hn)
+    prm = F.push_params(dt, scheme=sch, implicit=F.FPIC_HAM, thr=thr, tol=1e-15, max_iter=100, B0pot=B0,
+                        B0field=B0)
+    F.fpic_push(ctx, p, None, prm)
+    po = O.push_params(a=a, dt=dt, scheme=sch, implicit_kind=O.HAM, thr=thr, tol=1e-15, max_iter=100, B0pot=B0,
+                       field_kind=O.FIELD_WALD, B0field=B0)
+    zo = np.ascontiguousarray(z.copy()); Ho = Hn.copy(); ao = np.ones(n, np.uint8)
+    nc, so, io = O.push(po, zo, q, H0, D0, Ho, ao)
+    zg, Hg, ag, sg, ig, cg = to_np(p)
+    assert np.array_equal(ag, ao)
+    ok = np.ones(n, bool)
+    if scheme == "HYB2":
+        ok = np.abs(stat - thr) > 1e-10 * thr
+        assert (~ok).sum() <= 2 and np.array_equal(sg[ok], so[ok]) and 0 < so.sum() < n
+    assert_state_close(zg, zo, TOL, ok)
+    if scheme in ("HAM", "HYB2"):
+        imp = (so == 1) & ok
+        Hnew = O.hamiltonian(1.0, a, B0, zg[imp], q[imp])[0]
+        assert np.abs(Hnew - H0[imp]).max() <= 1e-14 * np.abs(H0).max()
