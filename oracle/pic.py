@@ -13,7 +13,7 @@ _I64 = C.c_int64
 
 class FdtdParams(C.Structure):
     _fields_ = [("M", C.c_double), ("a", C.c_double), ("dt", C.c_double), ("chi0", C.c_double),
-                ("lam", C.c_double), ("r_abs", C.c_double), ("r_max", C.c_double)]
+                ("lam", C.c_double), ("r_abs", C.c_double), ("r_max", C.c_double), ("conserving", C.c_int)]
 
 
 def _declare(L):
@@ -31,6 +31,9 @@ def _declare(L):
     L.or_inject_pairs.argtypes = [C.c_double, C.c_double] + g + [_D, _D] + [C.c_double] * 5 + [
         _D, _I64, _I64, _D, _D, _D, _U8, _U8, C.POINTER(_I64)]
     L.or_inject_pairs.restype = _I64
+    L.or_deposit_conserving.argtypes = [C.c_double, C.c_double] + g + [_I64, _D, _D, _D, _D, _U8, C.c_double,
+                                                                       _D, _D, _D, _D]
+    L.or_deposit_conserving.restype = _I64
 
 
 def _g(g):
@@ -128,3 +131,16 @@ def inject_pairs(M, a, g, z, qm, w, alive, n, cap, Br, Bth, r_lo, r_hi, mult, n0
                               int(n), int(cap), ptr(z), ptr(qm), ptr(w),
                               ptr(alive, _U8), ptr(flags, _U8), C.byref(n_out))
     return z, qm, w, alive, int(n_out.value), int(K), flags
+
+
+def deposit_conserving(M, a, g, z0, z1, qm, w, alive, dt):
+    """Charge-conserving deposit of the moves z0 -> z1: (rho at z1 in the Yee
+    node volume, coordinate currents J^r, J^th, J^ph, moves skipped)."""
+    z0 = np.ascontiguousarray(f64(z0)).reshape(-1, 6)
+    z1 = np.ascontiguousarray(f64(z1)).reshape(-1, 6)
+    n = z0.shape[0]
+    alive = np.ascontiguousarray(alive, np.uint8)
+    out = [np.zeros(g.size) for _ in range(4)]
+    sk = lib().or_deposit_conserving(M, a, *_g(g), n, ptr(z0), ptr(z1), ptr(f64(qm)), ptr(f64(w)),
+                                     ptr(alive, _U8), float(dt), *[ptr(x) for x in out])
+    return out[0], out[1], out[2], out[3], int(sk)

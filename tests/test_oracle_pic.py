@@ -487,3 +487,133 @@ def test_inject_capacity_keeps_cell_order():
     assert small[4] == 6 and small[5] == big[5] > 3
     assert np.array_equal(small[0][:6], big[0][:6]) and np.array_equal(small[2][:6], big[2][:6])
     assert not small[0][6:].any()
+
+
+# ---- charge-conserving deposit (extension) -----------------------------------
+
+def _yee_dual(g):
+    dr = np.array([(g.rh[i] if i < g.Nr else g.rn[-1]) - (g.rh[i - 1] if i > 0 else g.rn[0])
+                   for i in range(g.Nr + 1)])
+    dt_ = np.array([(g.th[j] if j < g.Nth else math.pi) - (g.th[j - 1] if j > 0 else 0.0)
+                    for j in range(g.Nth + 1)])
+    return dr, dt_
+
+
+def _moves(g, a, n, seed, frac=0.4):
+    """States inside the grid and moves of up to frac of a cell (some cross a node)."""
+    rng = np.random.default_rng(seed)
+    i = rng.integers(1, g.Nr - 1, n); j = rng.integers(1, g.Nth - 1, n)
+    r = g.rn[i] + rng.random(n) * (g.rn[i + 1] - g.rn[i])
+    t = g.tn[j] + rng.random(n) * (g.tn[j + 1] - g.tn[j])
+    z0 = np.stack([r, t, rng.uniform(0, 6, n), rng.normal(size=n), rng.normal(size=n), rng.normal(size=n)], 1)
+    z1 = z0.copy()
+    z1[:, 0] += frac * rng.uniform(-1, 1, n) * (g.rn[i + 1] - g.rn[i])
+    z1[:, 1] += frac * rng.uniform(-1, 1, n) * (g.tn[j + 1] - g.tn[j])
+    z1[:, 3:] += 0.1 * rng.normal(size=(n, 3))
+    q = np.where(rng.random(n) < 0.5, -1.0, 1.0) * rng.uniform(0.5, 2, n)
+    return z0, z1, q, rng.uniform(0.5, 2, n)
+
+
+@pytest.mark.parametrize("a", [0.0, 0.9])
+def test_conserving_deposit_continuity_at_every_node(a):
+    """The deposit of a move satisfies the discrete continuity equation
+    sqrtg (rho^{n+1} - rho^n) + dt Yee-div(sqrtg J) = 0 at every node (the
+    Yee divergence with the Appendix A sqrt(gamma), written here
+    independently), and conserves the total charge."""
+    g = I.log_grid(12, 10, 1.5, 20.0)
+    z0, z1, q, w = _moves(g, a, 400, 3)
+    al = np.ones(len(q), np.uint8)
+    dt = 0.05
+    rho0 = P.deposit_conserving(1.0, a, g, z0, z0, q, w, al, dt)[0]
+    rho1, Jr, Jt, Jp, sk = P.deposit_conserving(1.0, a, g, z0, z1, q, w, al, dt)
+    assert sk == 0
+    L = g.ld
+    sg = lambda r, t: O.metric(1.0, a, [r], [t])[0, 12]
+    dr, dth = _yee_dual(g)
+    worst, scale = 0.0, 0.0
+    Qtot = 0.0
+    for i in range(g.Nr + 1):
+        for j in range(g.Nth + 1):
+            o = i * L + j
+            fr1 = sg(g.rh[i], g.tn[j]) * Jr[o] if i < g.Nr else 0.0
+            fr0 = sg(g.rh[i - 1], g.tn[j]) * Jr[o - L] if i > 0 else 0.0
+            ft1 = sg(g.rn[i], g.th[j]) * Jt[o] if j < g.Nth else 0.0
+            ft0 = sg(g.rn[i], g.th[j - 1]) * Jt[o - 1] if j > 0 else 0.0
+            div = (fr1 - fr0) / dr[i] + (ft1 - ft0) / dth[j]
+            lhs = sg(g.rn[i], g.tn[j]) * (rho1[o] - rho0[o])
+            worst = max(worst, abs(lhs + dt * div))
+            scale = max(scale, abs(lhs))
+            Qtot += 2 * math.pi * sg(g.rn[i], g.tn[j]) * dr[i] * dth[j] * rho1[o]
+    assert scale > 0 and worst <= 1e-13 * scale
+    assert abs(Qtot - (q * w).sum()) <= 1e-12 * np.abs(q * w).sum()
+
+
+def test_conserving_deposit_particle_on_a_node_and_at_rest():
+    """A particle resting on a node puts all its charge there and no
+    current; a pure r move makes no th current (and vice versa)."""
+    a = 0.9
+    g = I.log_grid(8, 8, 1.5, 10.0)
+    z = np.array([[g.rn[3], g.tn[4], 0.0, 0.0, 0.0, 0.0]])
+    rho, Jr, Jt, Jp, _ = P.deposit_conserving(1.0, a, g, z, z, [2.0], [1.5], [1], 0.1)
+    dr, dth = _yee_dual(g)
+    o = 3 * g.ld + 4
+    V = 2 * math.pi * O.metric(1.0, a, [g.rn[3]], [g.tn[4]])[0, 12] * dr[3] * dth[4]
+    assert np.count_nonzero(rho) == 1 and abs(rho[o] * V - 3.0) < 1e-13
+    assert not Jr.any() and not Jt.any() and not Jp.any()
+    z1 = z.copy(); z1[0, 0] += 0.3 * (g.rn[4] - g.rn[3])
+    _, Jr, Jt, _, _ = P.deposit_conserving(1.0, a, g, z, z1, [2.0], [1.5], [1], 0.1)
+    assert Jr.any() and not Jt.any()
+    z1 = z.copy(); z1[0, 1] -= 0.3 * (g.tn[4] - g.tn[3])
+    _, Jr, Jt, _, _ = P.deposit_conserving(1.0, a, g, z, z1, [2.0], [1.5], [1], 0.1)
+    assert Jt.any() and not Jr.any()
+
+
+def test_conserving_pic_loop_keeps_gauss_residual():
+    """Sec. 2.1's step with the conserving deposit and the FDTD in its
+    conserving mode (no absorbing layer): Yee-div(sqrtg D^{n+1/2}) -
+    4 pi sqrtg rho^n stays what it was at the start, at the interior nodes,
+    to rounding over 6 steps of a charged plasma (the paper's deposit
+    changes it at O(1))."""
+    a = 0.9
+    g = I.log_grid(24, 20, 1.5, 20.0)
+    n = 3000
+    rng = np.random.default_rng(4)
+    d, q, w = I.thermal_draws(n, g, 3.0, 12.0, 0.3, seed=5, qm=50.0)
+    d[:, 1] = rng.uniform(0.5, math.pi - 0.5, n)
+    z = O.seed_fido(1.0, a, d)
+    Fw = O.wald_on_grid(a, 1.0, g)
+    st = P.FdtdState(g)
+    for k in range(3):
+        st.D0[k][:] = Fw[k]; st.D1[k][:] = Fw[k]; st.B0[k][:] = Fw[3 + k]; st.B1[k][:] = Fw[3 + k]
+    dt = 2e-3
+    po = P.FdtdParams(1.0, a, dt, 0.0, 5.0, g.rn[-1], g.rn[-1], 1)
+    w = np.full(n, 1e-3)
+    al = np.ones(n, np.uint8)
+    rho, _, _, _, _ = P.deposit_conserving(1.0, a, g, z, z, q, w, al, dt)
+    st.rho1 = rho.copy()
+    sel = np.zeros((g.Nr + 1, g.ld), bool)
+    sel[2:g.Nr - 1, 2:g.Nth - 1] = True
+    sg = O.metric(1.0, a, np.repeat(g.rn, g.ld), np.tile(g.tn, g.Nr + 1))[:, 12]
+
+    def resid(D, rho_):
+        _, dD = P.div(1.0, a, g, st.B1, D)
+        return (dD - 4 * math.pi * sg * rho_).reshape(g.Nr + 1, g.ld)[sel]
+
+    R0 = resid(st.D1, st.rho1)
+    H0, _, D0 = O.hamiltonian(1.0, a, 0.0, z, q)
+    pp = O.push_params(a=a, dt=dt, scheme=O.RK4, field_kind=O.FIELD_GRID, r_max=g.rn[-1])
+    drift = 0.0
+    for step in range(6):
+        P.fdtd(po, st, 1)
+        zold = z.copy()
+        O.push(pp, z, q, H0, D0, H0.copy(), al, g, [st.D1[0], st.D1[1], st.D1[2], st.Bh[0], st.Bh[1], st.Bh[2]])
+        assert al.all()
+        rho, Jr, Jt, Jp, sk = P.deposit_conserving(1.0, a, g, zold, z, q, w, np.ones(n, np.uint8), dt)
+        assert sk == 0
+        st.j1 = [Jr, Jt, Jp]; st.rho1 = rho
+        P.fdtd(po, st, 2)
+        st.swap()
+        R = resid(st.D1, st.rho0)          # D^{n+5/2} with rho^{n+2} (swapped into slot 0)
+        drift = max(drift, np.abs(R - R0).max())
+    scale = np.abs(4 * math.pi * sg.reshape(g.Nr + 1, g.ld)[sel] * st.rho0.reshape(g.Nr + 1, g.ld)[sel]).max()
+    assert scale > 0 and drift <= 1e-11 * scale, (drift, scale)
