@@ -66,6 +66,7 @@ def parse():
                     help="plain steps sampled for the training set")
     ap.add_argument("--workload", default="push", choices=["push", "pic", "neutral", "batched", "clean", "inject", "adaptive"])
     ap.add_argument("--clean-sweeps", type=int, default=500, help="Jacobi sweeps of --workload clean")
+    ap.add_argument("--conserving", action="store_true", help="--workload pic with the charge-conserving deposit")
     ap.add_argument("--neutral-scheme", default="HYB2", choices=["HYB2", "HAM", "RK4"],
                     help="scheme of --workload neutral")
     ap.add_argument("--neutral-pre", type=int, default=1000, help="untimed steps before --workload neutral")
@@ -545,10 +546,13 @@ def run_batched(args, device, scale, steps):
             "unit": UNIT, "ms_per_step": 1e3 * t / steps}
 
 
-def run_pic(args, device, grid_n, ppc, steps, rank=0):
+def run_pic(args, device, grid_n, ppc, steps, rank=0, conserving=False):
     """Full GRPIC step (Sec. 2.1 order): FDTD sub-steps 1-4, RK4 push with
     D^{n+3/2}, B^{n+3/2}, sort + deposit at n+2, FDTD sub-steps 7-10.
-    Plasma-filled Wald magnetosphere, a = 0.99, ppc particles in every cell."""
+    Plasma-filled Wald magnetosphere, a = 0.99, ppc particles in every cell.
+    conserving: the charge-conserving variant (the move's coordinate
+    currents from a copy of the state before the push, no sort; the FDTD in
+    its conserving mode)."""
     import numpy as np
     import torch
     from paper_2602_07452_gb300 import fpic as F
@@ -570,21 +574,31 @@ def run_pic(args, device, grid_n, ppc, steps, rank=0):
     F.fpic_init_particles(ctx, p, F.FPIC_SEED_FIDO, torch.as_tensor(d, device=device))
     del d, q, w
     r_max = float(g.rn[-1])
-    fprm = F.fdtd_params(PIC_DT, 1e4, 5.0, 0.9 * r_max, r_max)
+    fprm = F.fdtd_params(PIC_DT, 1e4, 5.0, 0.9 * r_max, r_max, conserving=conserving)
     pprm = F.push_params(PIC_DT, scheme=F.FPIC_RK4, r_max=r_max)
     out4 = (fl.rho1, fl.j1[0], fl.j1[1], fl.j1[2])
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    prev = None
+    if conserving:
+        prev = F.Particles(*[getattr(p, f).clone() for f in p.__dataclass_fields__])
+        F.fpic_deposit_conserving(ctx, prev, p, PIC_DT, out=out4)
 
     def step(timed):
         if timed:
             ev[0].record()
         F.fpic_fdtd_step(ctx, fl, fprm, 1)
+        if conserving:
+            for nm in ("r", "th", "ur", "uth", "uph", "alive"):
+                getattr(prev, nm).copy_(getattr(p, nm))
         if timed:
             ev[1].record()
         F.fpic_push(ctx, p, fl.push_fields(), pprm)
         if timed:
             ev[2].record()
-        F.fpic_deposit(ctx, p, g.size, out=(fl.rho1, fl.j1[0], fl.j1[1], fl.j1[2]))
+        if conserving:
+            F.fpic_deposit_conserving(ctx, prev, p, PIC_DT, out=out4)
+        else:
+            F.fpic_deposit(ctx, p, g.size, out=(fl.rho1, fl.j1[0], fl.j1[1], fl.j1[2]))
         if timed:
             ev[3].record()
         F.fpic_fdtd_step(ctx, fl, fprm, 2)
@@ -608,10 +622,14 @@ def run_pic(args, device, grid_n, ppc, steps, rank=0):
         "workload": f"plasma-filled Wald GRPIC step, a={PIC_A}, {grid_n}x{grid_n} (ln r, theta), "
                     f"{ppc} particles/cell ({ppc // 2} e-/e+ pairs)",
         "particles": n, "steps": steps, "value": ps / T, "unit": UNIT, "ms_per_step": 1e3 * T / steps,
-        "phase_ms": {"fdtd_1_4": 1e3 * ph[0] / steps, "push_rk4": 1e3 * ph[1] / steps,
-                     "sort_and_deposit": 1e3 * ph[2] / steps, "fdtd_7_10": 1e3 * ph[3] / steps},
+        "phase_ms": {"fdtd_1_4" + ("_and_state_copy" if conserving else ""): 1e3 * ph[0] / steps,
+                     "push_rk4": 1e3 * ph[1] / steps,
+                     ("conserving_deposit" if conserving else "sort_and_deposit"): 1e3 * ph[2] / steps,
+                     "fdtd_7_10": 1e3 * ph[3] / steps},
+        "deposit": "charge-conserving variant (linear weights, Esirkepov split)" if conserving
+                   else "Sec. 2.3 volume-weighted",
         "dt": PIC_DT, "absorbing": {"chi0": 1e4, "lambda": 5, "r_abs": 0.9 * r_max},
-        "deposit_achieved_gflops": ps * FLOP_DEPOSIT / t_dep / 1e9,
+        "deposit_achieved_gflops": None if conserving else ps * FLOP_DEPOSIT / t_dep / 1e9,
     }
 
 
@@ -905,7 +923,7 @@ def main():
         torch.cuda.set_device(local)
         dev = torch.device("cuda", local)
         if args.workload == "pic":
-            res = run_pic(args, dev, args.pic_grid, args.pic_ppc, args.pic_steps, rank)
+            res = run_pic(args, dev, args.pic_grid, args.pic_ppc, args.pic_steps, rank, conserving=args.conserving)
         elif args.workload == "neutral":
             res = run_neutral(args, dev, args.n, args.steps, pre_steps=args.neutral_pre, scheme=args.neutral_scheme)
         else:
@@ -920,6 +938,7 @@ def main():
     if not args.no_pic and rank == 0:
         import torch
         line["pic_step"] = run_pic(args, torch.device("cuda", local), 512, 16, 3, rank)
+        line["pic_step_conserving"] = run_pic(args, torch.device("cuda", local), 512, 16, 3, rank, conserving=True)
     if not args.no_extra and rank == 0:
         import torch
         dev = torch.device("cuda", local)

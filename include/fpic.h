@@ -315,9 +315,13 @@ typedef struct {
 
 /* FDTD parameters: time step dt and the absorbing layer of Eqs. (abs0)-(abs2):
  * chi(r) = chi0 ((r - r_abs)/(r_max - r_abs))^lambda for r > r_abs (chi0 = 0
- * switches it off); the damping is applied as a factor exp(-chi dt). */
+ * switches it off); the damping is applied as a factor exp(-chi dt).
+ * conserving = 1: the j arrays hold coordinate currents J = alpha j - rho beta
+ * (fpic_deposit_conserving), used as they are in sub-steps 8 and 10;
+ * 0: FIDO currents j, turned into J with rho (Sec. 2.1). */
 typedef struct {
     double dt, chi0, lambda, r_abs, r_max;
+    int conserving;
 } fpic_fdtd_params;
 
 /* Stable sort of the particles by cell index ir * Nth + ith (removed
@@ -350,6 +354,29 @@ int fpic_deposit(fpic_ctx *ctx, fpic_particles *p, double *rho, double *jr, doub
  * and (j0, rho0)/(j1, rho1).  Errors: FPIC_EINVAL (no grid, stage not 1 or
  * 2, NULL array, dt not finite). */
 int fpic_fdtd_step(fpic_ctx *ctx, fpic_fields *f, const fpic_fdtd_params *prm, int stage, void *stream);
+
+/* Charge-conserving deposit of one step's moves (an extension: the paper's
+ * deposit is not charge-conserving and relies on the cleaning of Sec. 2.4).
+ * Each particle alive in *before moves from its state in *before to its
+ * state in *after (same n, same order; only r, th, u and alive of *before are
+ * read, r, th, u, qm, w of *after).  Node weights are linear (area) weights
+ * in r and th; the move is split Esirkepov's way, W_r = dS_r <S_th>,
+ * W_th = <S_r> dS_th, over the 3 x 3 nodes of both stencils, and the charge
+ * crossing each dual face gives the coordinate currents.  Outputs (device,
+ * grid layout):
+ *   rho (i, j)      = Q S(x^{n+1}) / (2 pi sqrtg dr_dual dth_dual)
+ *   jr  (i+1/2, j)  = J^r,  jth (i, j+1/2) = J^th: charge crossing per unit time
+ *                     / (2 pi sqrtg x the dual face's width)
+ *   jph (i, j)      = Q <S> (dph/dt) / (2 pi sqrtg dr_dual dth_dual)
+ * so that sqrtg (rho^{n+1} - rho^n) + dt Yee-div(sqrtg J) = 0 at every node;
+ * with fpic_fdtd_params.conserving = 1 the field update then keeps
+ * Yee-div(sqrtg D) - 4 pi sqrtg rho constant.  Moves longer than one cell
+ * are skipped and counted in *n_skipped (nullable; reading it synchronises
+ * the stream).  Deterministic (per-cell warp sums in particle-index order).
+ * Errors: FPIC_EINVAL, FPIC_ENOMEM, FPIC_ECUDA. */
+int fpic_deposit_conserving(fpic_ctx *ctx, const fpic_particles *before, const fpic_particles *after, double dt,
+                            double *rho, double *jr, double *jth, double *jph, long long *n_skipped,
+                            void *stream);
 
 /* Pair injection parameters (Sec. 3.3, 3.4). */
 typedef struct {

@@ -593,6 +593,7 @@ struct FK {
     GridDev G;
     Tabs T;
     double dt, chi0, lam, r_abs, r_max;
+    int conserving;     // sources are coordinate currents J (fpic_deposit_conserving)
 };
 
 __device__ __forceinline__ double damp(const FK& k, double r)
@@ -716,6 +717,7 @@ __device__ __forceinline__ double jsrc(const FK& k, const Src& S, int comp, int 
 {
     if (S.w == 0.0) return 0.0;
     const size_t o = (size_t)i * k.ld + j;
+    if (k.conserving) return S.w * S.j[comp][o];
     if (comp == 0) {
         const double rb = avg_r(k, S.rho, 0, 0, i, j);
         return S.w * fma(k.T.at(1, 0, i, j), S.j[0][o], -rb * k.T.at(1, 1, i, j));
@@ -834,6 +836,242 @@ extern "C" int fpic_deposit(fpic_ctx* c, fpic_particles* p, double* rho, double*
     NodeK nk{c->Nr, c->Nth, c->ld, w.part, C, tabs_of(c), rho, jr, jth, jph};
     k_dep_node<<<dim3(1, c->Nr + 1), 256, 0, s>>>(nk);
     FPIC_CUDA(cudaGetLastError());
+    return FPIC_OK;
+}
+
+namespace fpic {
+// ---------------------------------------------------------------------------
+// Charge-conserving deposit (an extension; the paper's deposit is not and
+// relies on the cleaning of Sec. 2.4)
+// ---------------------------------------------------------------------------
+// A move from x^n to x^{n+1} with linear (area) node weights S = S_r S_th,
+// split Esirkepov's way on the 3 x 3 window of integer nodes spanned by the
+// two stencils: W_r = dS_r <S_th>, W_th = <S_r> dS_th (<.> the mean of old
+// and new), charge crossing the dual face between window nodes x and x+1 in
+// +r: -Q sum_{x' <= x} W_r(x', y) (alike in th).  Window partials (30 per
+// particle: Q S^new and Q <S> (dph/dt)_mid on 3 x 3 nodes, 2 x 3 r faces,
+// 3 x 2 th faces) are summed per window-base cell by one warp over the cell's
+// particles in index order (fixed shuffle tree), then gathered per node /
+// face in a fixed order: bitwise reproducible.  Normalised by the Yee cell
+// (2 pi sqrtg dr_dual dth_dual) so that sqrtg (rho^{n+1} - rho^n) + dt
+// Yee-div(sqrtg J) = 0 at every node.
+enum { CD_Q = 0, CD_P = 9, CD_R = 18, CD_T = 24, CD_SLOTS = 30 };
+
+struct CDepK {
+    int Nr, Nth, ld;
+    GridDev G;
+    BH bh;
+    long long n;
+    const double *r0, *t0, *ur0, *ut0, *up0;
+    const uint8_t* alive0;
+    const double *r1, *t1, *ur1, *ut1, *up1, *qm, *w;
+};
+
+__device__ __forceinline__ void cd_lin(const GridDev& G, double r, double t, int& i, double& fr, int& j, double& ft)
+{
+    const float lr = __logf((float)r);
+    locate(G.rn, G.irn, G.Nr + 1, r, (lr - G.lr0) * G.ilr, i, fr);
+    locate(G.tn, G.itn, G.Nth + 1, t, ((float)t - G.t0) * G.it, j, ft);
+}
+
+// window base cell of each particle alive before the move (C: skipped / removed)
+__global__ void k_cdep_keys(CDepK k, uint32_t* key, uint32_t* count, uint32_t C, long long* n_skip)
+{
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= k.n) return;
+    uint32_t kk = C;
+    if (k.alive0[p]) {
+        int ia, ja, ib, jb;
+        double f;
+        cd_lin(k.G, k.r0[p], k.t0[p], ia, f, ja, f);
+        cd_lin(k.G, k.r1[p], k.t1[p], ib, f, jb, f);
+        if (abs(ia - ib) > 1 || abs(ja - jb) > 1) atomicAdd((unsigned long long*)n_skip, 1ull);
+        else kk = (uint32_t)min(ia, ib) * (uint32_t)k.Nth + (uint32_t)min(ja, jb);
+    }
+    key[p] = kk;
+    atomicAdd(&count[kk], 1u);
+}
+
+// coordinate dph/dt = alpha gamma^{ph j} u_j / Gamma
+__device__ __forceinline__ double cd_phdot(const BH& bh, double r, double t, double ur, double ut, double up)
+{
+    double s, c;
+    sincos(t, &s, &c);
+    Geo g;
+    geo_eval(bh, r, s, c, g);
+    const double G = sqrt(fma(g.gurr * ur, ur, fma(2.0 * g.gurp * ur, up, fma(g.gutt * ut, ut, fma(g.gupp * up, up, 1.0)))));
+    return g.alpha * fma(g.gurp, ur, g.gupp * up) / G;
+}
+
+// one warp per window-base cell: its particles' 30 window partials, summed
+__global__ void k_cdep_cell(CDepK k, const uint32_t* __restrict__ off, const uint32_t* __restrict__ perm,
+                            double* __restrict__ part, uint32_t C)
+{
+    const long long cell = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (cell >= C) return;
+    const uint32_t b0 = off[cell], b1 = off[cell + 1];
+    const int i0 = (int)(cell / k.Nth), j0 = (int)(cell - (long long)i0 * k.Nth);
+    double acc[CD_SLOTS];
+#pragma unroll
+    for (int q = 0; q < CD_SLOTS; ++q) acc[q] = 0.0;
+    for (uint32_t base = b0; base < b1; base += 32) {
+        double v[CD_SLOTS];
+#pragma unroll
+        for (int q = 0; q < CD_SLOTS; ++q) v[q] = 0.0;
+        const uint32_t a = base + lane;
+        if (a < b1) {
+            const uint32_t p = perm[a];
+            int ia, ja, ib, jb;
+            double fra, fta, frb, ftb;
+            cd_lin(k.G, k.r0[p], k.t0[p], ia, fra, ja, fta);
+            cd_lin(k.G, k.r1[p], k.t1[p], ib, frb, jb, ftb);
+            double Sra[3] = {0, 0, 0}, Srb[3] = {0, 0, 0}, Sta[3] = {0, 0, 0}, Stb[3] = {0, 0, 0};
+            Sra[ia - i0] = 1.0 - fra; Sra[ia - i0 + 1] = fra;
+            Srb[ib - i0] = 1.0 - frb; Srb[ib - i0 + 1] = frb;
+            Sta[ja - j0] = 1.0 - fta; Sta[ja - j0 + 1] = fta;
+            Stb[jb - j0] = 1.0 - ftb; Stb[jb - j0 + 1] = ftb;
+            const double Q = k.w[p] * k.qm[p];
+            const double phd = 0.5 * (cd_phdot(k.bh, k.r0[p], k.t0[p], k.ur0[p], k.ut0[p], k.up0[p]) +
+                                      cd_phdot(k.bh, k.r1[p], k.t1[p], k.ur1[p], k.ut1[p], k.up1[p]));
+#pragma unroll
+            for (int x = 0; x < 3; ++x)
+#pragma unroll
+                for (int y = 0; y < 3; ++y) {
+                    v[CD_Q + 3 * x + y] = Q * (Srb[x] * Stb[y]);
+                    v[CD_P + 3 * x + y] = Q * (0.5 * (Sra[x] * Sta[y] + Srb[x] * Stb[y])) * phd;
+                }
+#pragma unroll
+            for (int y = 0; y < 3; ++y) {
+                double s_ = 0.0;
+#pragma unroll
+                for (int x = 0; x < 2; ++x) {
+                    s_ += 0.5 * (Srb[x] - Sra[x]) * (Sta[y] + Stb[y]);
+                    v[CD_R + 3 * x + y] = -Q * s_;
+                }
+            }
+#pragma unroll
+            for (int x = 0; x < 3; ++x) {
+                double s_ = 0.0;
+#pragma unroll
+                for (int y = 0; y < 2; ++y) {
+                    s_ += 0.5 * (Sra[x] + Srb[x]) * (Stb[y] - Sta[y]);
+                    v[CD_T + 2 * x + y] = -Q * s_;
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < CD_SLOTS; ++q) {
+            double t = v[q];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+            acc[q] += t;
+        }
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < CD_SLOTS; ++q) part[(size_t)q * C + cell] = acc[q];
+    }
+}
+
+__device__ __forceinline__ double cd_dual_r(const GridDev& G, int i)
+{
+    return (i == G.Nr ? G.rn[G.Nr] : G.rh[i]) - (i == 0 ? G.rn[0] : G.rh[i - 1]);
+}
+
+__device__ __forceinline__ double cd_dual_t(const GridDev& G, int j)
+{
+    return (j == G.Nth ? M_PI : G.th[j]) - (j == 0 ? 0.0 : G.th[j - 1]);
+}
+
+// per node / face: the partials of the window cells covering it, fixed order
+__global__ void k_cdep_node(CDepK k, Tabs T, const double* __restrict__ part, uint32_t C, double dt, double* rho,
+                            double* Jr, double* Jt, double* Jp)
+{
+    const int i = blockIdx.y;
+    const GridDev& G = k.G;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j <= k.Nth; j += gridDim.x * blockDim.x) {
+        const size_t o = (size_t)i * k.ld + j;
+        double Q = 0.0, Pp = 0.0, Fr = 0.0, Ft = 0.0;
+        for (int x = 0; x < 3; ++x)
+            for (int y = 0; y < 3; ++y) {
+                const int ci = i - x, cj = j - y;
+                if (ci < 0 || ci >= k.Nr || cj < 0 || cj >= k.Nth) continue;
+                const size_t cell = (size_t)ci * k.Nth + cj;
+                Q += part[(size_t)(CD_Q + 3 * x + y) * C + cell];
+                Pp += part[(size_t)(CD_P + 3 * x + y) * C + cell];
+                if (x < 2) Fr += part[(size_t)(CD_R + 3 * x + y) * C + cell];
+                if (y < 2) Ft += part[(size_t)(CD_T + 2 * x + y) * C + cell];
+            }
+        const double drd = cd_dual_r(G, i), dtd = cd_dual_t(G, j);
+        const double vol = 2.0 * M_PI * T.at(0, 2, i, j) * drd * dtd;
+        rho[o] = vol > 0.0 ? Q / vol : 0.0;
+        Jp[o] = vol > 0.0 ? Pp / vol : 0.0;
+        if (i < k.Nr) Jr[o] = Fr / (dt * 2.0 * M_PI * T.at(1, 2, i, j) * dtd);
+        else Jr[o] = 0.0;
+        if (j < k.Nth) Jt[o] = Ft / (dt * 2.0 * M_PI * T.at(2, 2, i, j) * drd);
+        else Jt[o] = 0.0;
+    }
+}
+}  // namespace fpic
+
+extern "C" int fpic_deposit_conserving(fpic_ctx* c, const fpic_particles* before, const fpic_particles* after,
+                                       double dt, double* rho, double* jr, double* jth, double* jph,
+                                       long long* n_skipped, void* stream)
+{
+    if (!c || !before || !after || !rho || !jr || !jth || !jph)
+        return set_error(FPIC_EINVAL, "fpic_deposit_conserving: NULL argument");
+    if (!c->has_grid) return set_error(FPIC_EINVAL, "fpic_deposit_conserving: no grid set");
+    if (before->n != after->n || after->n < 0) return set_error(FPIC_EINVAL, "fpic_deposit_conserving: n mismatch");
+    if (!(std::isfinite(dt)) || dt == 0.0) return set_error(FPIC_EINVAL, "fpic_deposit_conserving: dt must be finite and nonzero");
+    const long long n = after->n;
+    if (n > 0 && (!before->r || !before->th || !before->ur || !before->uth || !before->uph || !before->alive ||
+                  !after->r || !after->th || !after->ur || !after->uth || !after->uph || !after->qm || !after->w))
+        return set_error(FPIC_EINVAL, "fpic_deposit_conserving: NULL particle array");
+    if (n >= (1LL << 32)) return set_error(FPIC_EINVAL, "fpic_deposit_conserving: more than 2^32 particles");
+    FPIC_CUDA(cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long C = (long long)c->Nr * c->Nth;
+    Work w;
+    int rc = work_layout(c, n > 0 ? n : 1, false, w);
+    if (rc) return rc;
+    // per-cell partials after the Work block (CD_SLOTS x C doubles)
+    {
+        const size_t need_extra = (size_t)CD_SLOTS * C * sizeof(double) + 256;
+        size_t used = (size_t)((char*)w.tmp - (char*)c->d_scratch2) + 8 * (size_t)(n > 0 ? n : 1);
+        used = (used + 255) & ~(size_t)255;
+        if (used + need_extra > c->scratch2_bytes) {
+            rc = ensure_scratch2(c, used + need_extra);
+            if (rc) return rc;
+            rc = work_layout(c, n > 0 ? n : 1, false, w);
+            if (rc) return rc;
+        }
+    }
+    size_t used = (size_t)((char*)w.tmp - (char*)c->d_scratch2) + 8 * (size_t)(n > 0 ? n : 1);
+    used = (used + 255) & ~(size_t)255;
+    double* part = (double*)((char*)c->d_scratch2 + used);
+    CDepK k{c->Nr, c->Nth, c->ld, c->G, c->bh, n, before->r, before->th, before->ur, before->uth, before->uph,
+            before->alive, after->r, after->th, after->ur, after->uth, after->uph, after->qm, after->w};
+    FPIC_CUDA(cudaMemsetAsync(w.count, 0, 4 * ((size_t)C + 2), s));
+    FPIC_CUDA(cudaMemsetAsync(w.cursor, 0, 4 * ((size_t)C + 2), s));
+    FPIC_CUDA(cudaMemsetAsync(c->d_cnt + CNT_ERR, 0, sizeof(long long), s));
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    if (n > 0) k_cdep_keys<<<nb, 256, 0, s>>>(k, w.key, w.count, (uint32_t)C, c->d_cnt + CNT_ERR);
+    rc = scan_u32(w.count, w.off, w.bsum, C + 1, s);
+    if (rc) return rc;
+    if (n > 0) k_scatter<<<nb, 256, 0, s>>>(w.key, w.off, w.cursor, w.perm, n);
+    k_bucket_rank<<<(unsigned)((C * 32 + 255) / 256), 256, 0, s>>>(w.off, w.perm, w.perm2, (uint32_t)C);
+    k_cdep_cell<<<(unsigned)((C * 32 + 255) / 256), 256, 0, s>>>(k, w.off, w.perm2, part, (uint32_t)C);
+    k_cdep_node<<<dim3((unsigned)((c->Nth + 1 + 255) / 256), c->Nr + 1), 256, 0, s>>>(k, tabs_of(c), part,
+                                                                                     (uint32_t)C, dt, rho, jr,
+                                                                                     jth, jph);
+    FPIC_CUDA(cudaGetLastError());
+    if (n_skipped) {
+        long long v = 0;
+        FPIC_CUDA(cudaMemcpyAsync(&v, c->d_cnt + CNT_ERR, sizeof(long long), cudaMemcpyDeviceToHost, s));
+        FPIC_CUDA(cudaStreamSynchronize(s));
+        *n_skipped = v;
+    }
     return FPIC_OK;
 }
 
@@ -1215,7 +1453,8 @@ extern "C" int fpic_fdtd_step(fpic_ctx* c, fpic_fields* f, const fpic_fdtd_param
     if (!f->rho0 || !f->rho1) return set_error(FPIC_EINVAL, "fpic_fdtd_step: NULL rho array");
     FPIC_CUDA(cudaSetDevice(c->device));
     cudaStream_t s = (cudaStream_t)stream;
-    FK k{c->Nr, c->Nth, c->ld, c->G, tabs_of(c), prm->dt, prm->chi0, prm->lambda, prm->r_abs, prm->r_max};
+    FK k{c->Nr, c->Nth, c->ld, c->G, tabs_of(c), prm->dt, prm->chi0, prm->lambda, prm->r_abs, prm->r_max,
+         prm->conserving};
     const size_t sz = (size_t)(c->Nr + 1) * c->ld;
     const dim3 g2(1, c->Nr + 1);
     const int TB = 256;

@@ -73,7 +73,7 @@ class fpic_fields(C.Structure):
 
 class fpic_fdtd_params(C.Structure):
     _fields_ = [("dt", C.c_double), ("chi0", C.c_double), ("lam", C.c_double), ("r_abs", C.c_double),
-                ("r_max", C.c_double)]
+                ("r_max", C.c_double), ("conserving", C.c_int)]
 
 
 class fpic_run(C.Structure):
@@ -137,6 +137,9 @@ _SIGS = {
     "fpic_init_split_monopole": (C.c_int, [C.c_void_p, C.POINTER(_D), C.c_double, C.c_double, C.c_void_p]),
     "fpic_bz_power": (C.c_int, [C.c_void_p, C.POINTER(fpic_fields), C.c_int, C.c_void_p, C.c_void_p]),
     "fpic_div_clean": (C.c_int, [C.c_void_p, C.POINTER(_D), C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "fpic_deposit_conserving": (C.c_int, [C.c_void_p, C.POINTER(fpic_particles), C.POINTER(fpic_particles),
+                                          C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                          C.POINTER(C.c_longlong), C.c_void_p]),
     "fpic_inject_pairs": (C.c_int, [C.c_void_p, C.POINTER(fpic_particles), C.c_longlong, C.c_void_p, C.c_void_p,
                                     C.POINTER(fpic_inject_params), C.c_void_p, C.c_void_p,
                                     C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.c_void_p]),
@@ -264,6 +267,7 @@ def fpic_set_grid(ctx: Ctx, grid) -> None:
     arrs = [np.ascontiguousarray(x, dtype=np.float64) for x in (grid.rn, grid.rh, grid.tn, grid.th)]
     _check(lib().fpic_set_grid(ctx.handle, grid.Nr, grid.Nth, *[a.ctypes.data_as(_D) for a in arrs]))
     ctx.cells = grid.Nr * grid.Nth
+    ctx.cells_size = (grid.Nr + 1) * (grid.Nth + 1)
 
 
 _FIELDS_CACHE = {}
@@ -468,6 +472,19 @@ def fpic_deposit(ctx: Ctx, p: Particles, size: int, out=None, stream=None):
     return out
 
 
+def fpic_deposit_conserving(ctx: Ctx, before: Particles, after: Particles, dt: float, out=None,
+                            want_skipped: bool = False, stream=None):
+    """Charge-conserving deposit of the moves before -> after; returns
+    (rho, J^r, J^th, J^ph) (and the number of skipped moves if asked)."""
+    if out is None:
+        out = tuple(torch.zeros(ctx.cells_size, dtype=torch.float64, device=after.r.device) for _ in range(4))
+    sk = C.c_longlong(0)
+    _check(lib().fpic_deposit_conserving(ctx.handle, C.byref(before.struct()), C.byref(after.struct()), float(dt),
+                                         *[_dp(t) for t in out], C.byref(sk) if want_skipped else None,
+                                         _stream(stream)))
+    return (out, int(sk.value)) if want_skipped else out
+
+
 class Fields:
     """Leapfrog field storage (device tensors) mirroring fpic_fields."""
 
@@ -496,8 +513,8 @@ class Fields:
         return [self.D1[0], self.D1[1], self.D1[2], self.Bh[0], self.Bh[1], self.Bh[2]]
 
 
-def fdtd_params(dt, chi0=0.0, lam=5.0, r_abs=0.0, r_max=1.0):
-    return fpic_fdtd_params(dt, chi0, lam, r_abs, r_max)
+def fdtd_params(dt, chi0=0.0, lam=5.0, r_abs=0.0, r_max=1.0, conserving=False):
+    return fpic_fdtd_params(dt, chi0, lam, r_abs, r_max, int(bool(conserving)))
 
 
 def fpic_fdtd_step(ctx: Ctx, f: Fields, prm: fpic_fdtd_params, stage: int, stream=None) -> None:
