@@ -912,13 +912,11 @@ __global__ void k_cdep_cell(CDepK k, const uint32_t* __restrict__ off, const uin
     if (cell >= C) return;
     const uint32_t b0 = off[cell], b1 = off[cell + 1];
     const int i0 = (int)(cell / k.Nth), j0 = (int)(cell - (long long)i0 * k.Nth);
-    double acc[CD_SLOTS];
-#pragma unroll
-    for (int q = 0; q < CD_SLOTS; ++q) acc[q] = 0.0;
+    double acc = 0.0;           // lane q: slot q of the cell (q < CD_SLOTS)
     for (uint32_t base = b0; base < b1; base += 32) {
-        double v[CD_SLOTS];
+        double v[32];
 #pragma unroll
-        for (int q = 0; q < CD_SLOTS; ++q) v[q] = 0.0;
+        for (int q = 0; q < 32; ++q) v[q] = 0.0;
         const uint32_t a = base + lane;
         if (a < b1) {
             const uint32_t p = perm[a];
@@ -926,11 +924,16 @@ __global__ void k_cdep_cell(CDepK k, const uint32_t* __restrict__ off, const uin
             double fra, fta, frb, ftb;
             cd_lin(k.G, k.r0[p], k.t0[p], ia, fra, ja, fta);
             cd_lin(k.G, k.r1[p], k.t1[p], ib, frb, jb, ftb);
-            double Sra[3] = {0, 0, 0}, Srb[3] = {0, 0, 0}, Sta[3] = {0, 0, 0}, Stb[3] = {0, 0, 0};
-            Sra[ia - i0] = 1.0 - fra; Sra[ia - i0 + 1] = fra;
-            Srb[ib - i0] = 1.0 - frb; Srb[ib - i0 + 1] = frb;
-            Sta[ja - j0] = 1.0 - fta; Sta[ja - j0 + 1] = fta;
-            Stb[jb - j0] = 1.0 - ftb; Stb[jb - j0 + 1] = ftb;
+            // window weights by selects (registers, no indexed local arrays)
+            const int da = ia - i0, db = ib - i0, ea = ja - j0, eb = jb - j0;
+            double Sra[3], Srb[3], Sta[3], Stb[3];
+#pragma unroll
+            for (int x = 0; x < 3; ++x) {
+                Sra[x] = x == da ? 1.0 - fra : (x == da + 1 ? fra : 0.0);
+                Srb[x] = x == db ? 1.0 - frb : (x == db + 1 ? frb : 0.0);
+                Sta[x] = x == ea ? 1.0 - fta : (x == ea + 1 ? fta : 0.0);
+                Stb[x] = x == eb ? 1.0 - ftb : (x == eb + 1 ? ftb : 0.0);
+            }
             const double Q = k.w[p] * k.qm[p];
             const double phd = 0.5 * (cd_phdot(k.bh, k.r0[p], k.t0[p], k.ur0[p], k.ut0[p], k.up0[p]) +
                                       cd_phdot(k.bh, k.r1[p], k.t1[p], k.ur1[p], k.ut1[p], k.up1[p]));
@@ -960,18 +963,22 @@ __global__ void k_cdep_cell(CDepK k, const uint32_t* __restrict__ off, const uin
                 }
             }
         }
+        // reduce-scatter across the warp (recursive halving): each step a lane
+        // keeps half of its slots and adds its partner's copy of them; after
+        // five steps lane q holds the warp's sum of slot q (31 adds per lane)
 #pragma unroll
-        for (int q = 0; q < CD_SLOTS; ++q) {
-            double t = v[q];
+        for (int o = 16; o >= 1; o >>= 1) {
+            const bool upper = (lane & o) != 0;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-            acc[q] += t;
+            for (int q = 0; q < o; ++q) {
+                const double send = upper ? v[q] : v[q + o];
+                const double keep = upper ? v[q + o] : v[q];
+                v[q] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
         }
+        acc += v[0];
     }
-    if (lane == 0) {
-#pragma unroll
-        for (int q = 0; q < CD_SLOTS; ++q) part[(size_t)q * C + cell] = acc[q];
-    }
+    if (lane < CD_SLOTS) part[(size_t)lane * C + cell] = acc;
 }
 
 __device__ __forceinline__ double cd_dual_r(const GridDev& G, int i)
