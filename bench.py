@@ -579,9 +579,14 @@ def run_pic(args, device, grid_n, ppc, steps, rank=0, conserving=False):
     out4 = (fl.rho1, fl.j1[0], fl.j1[1], fl.j1[2])
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
     prev = None
+    dep_tune = None
     if conserving:
         prev = F.Particles(*[getattr(p, f).clone() for f in p.__dataclass_fields__])
         F.fpic_deposit_conserving(ctx, prev, p, PIC_DT, out=out4)
+    else:
+        from paper_2602_07452_gb300 import autotune
+        dep_tune = autotune.tune_deposit_threads(ctx, p, g.size)
+        F.fpic_deposit(ctx, p, g.size, out=out4)
 
     def step(timed):
         if timed:
@@ -630,6 +635,7 @@ def run_pic(args, device, grid_n, ppc, steps, rank=0, conserving=False):
                    else "Sec. 2.3 volume-weighted",
         "dt": PIC_DT, "absorbing": {"chi0": 1e4, "lambda": 5, "r_abs": 0.9 * r_max},
         "deposit_achieved_gflops": None if conserving else ps * FLOP_DEPOSIT / t_dep / 1e9,
+        "deposit_threads_autotuned_ms": dep_tune,
     }
 
 

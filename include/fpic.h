@@ -273,8 +273,11 @@ int fpic_probe_fp64(double *gflops_out, int reps);
  *     evens out the uneven iteration counts at the end of the queue; more
  *     lanes hide more memory latency.  The autotuner in the Python package
  *     (autotune.py) times the candidates on the caller's own particles.
+ *   FPIC_TUNE_DEP_THREADS: threads per block of the deposit's per-particle
+ *     kernel (the trapezoid lattices), 64, 128 or 256 (default 128); the
+ *     deposit's result does not depend on it.
  * Errors: FPIC_EINVAL (NULL, unknown key, value out of range). */
-enum { FPIC_TUNE_IMR_BLOCKS_PER_SM = 0 };
+enum { FPIC_TUNE_IMR_BLOCKS_PER_SM = 0, FPIC_TUNE_DEP_THREADS = 1 };
 int fpic_set_tuning(fpic_ctx *ctx, int key, int value);
 int fpic_get_tuning(const fpic_ctx *ctx, int key, int *value);
 

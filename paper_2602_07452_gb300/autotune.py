@@ -49,3 +49,28 @@ def tune_imr_blocks(ctx, p, fields, prm, candidates=(1, 2, 3, 4), reps=3, push=N
     _load(p, snap)
     torch.cuda.synchronize()
     return times
+
+
+def tune_deposit_threads(ctx, p, size, candidates=(64, 128, 256), reps=3):
+    """Pick FPIC_TUNE_DEP_THREADS by timing `reps` deposits (sort included)
+    per candidate on the caller's particles.  The deposit's output does not
+    depend on the choice; the particles end up sorted by cell either way.
+    Returns {candidate: mean ms} and leaves the best value set in ctx."""
+    out = tuple(torch.zeros(size, dtype=torch.float64, device=p.r.device) for _ in range(4))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times = {}
+    for v in candidates:
+        F.fpic_set_tuning(ctx, F.FPIC_TUNE_DEP_THREADS, v)
+        F.fpic_deposit(ctx, p, size, out=out)      # warm-up at this shape
+        tot = 0.0
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            e0.record()
+            F.fpic_deposit(ctx, p, size, out=out)
+            e1.record()
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        times[v] = tot / reps
+    best = min(times, key=times.get)
+    F.fpic_set_tuning(ctx, F.FPIC_TUNE_DEP_THREADS, best)
+    return times

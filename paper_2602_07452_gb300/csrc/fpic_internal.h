@@ -43,6 +43,7 @@ struct fpic_ctx {
     size_t scratch2_bytes = 0;
     // launch-shape tuning (fpic_set_tuning)
     int imr_blocks_per_sm = 4;
+    int dep_threads = 128;           // threads per block of the deposit's particle kernel
     // fpic_push_host: copy stream and per-chunk events (created on first use)
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t copy_ev[FPIC_HOST_CHUNKS + 1] = {};

@@ -420,7 +420,7 @@ __device__ __forceinline__ double clampd(double x, double lo, double hi)
     return x < lo ? lo : (x > hi ? hi : x);
 }
 
-__global__ void __launch_bounds__(128) k_dep_particle(DepK k)
+__global__ void __launch_bounds__(256) k_dep_particle(DepK k)
 {
     const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= k.n_alive) return;
@@ -830,7 +830,8 @@ extern "C" int fpic_deposit(fpic_ctx* c, fpic_particles* p, double* rho, double*
     DepK k{c->bh, c->G, c->d_metric + (size_t)MT_N * c->metric_stride, p->r, p->th, p->ur, p->uth, p->uph, p->qm, p->w, n, w.rec, w.code};
     if (n > 0) {
         // rec/code for all n slots; removed particles (past off[C]) are never summed
-        k_dep_particle<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(k);
+        const int dt_ = c->dep_threads;
+        k_dep_particle<<<(unsigned)((n + dt_ - 1) / dt_), dt_, 0, s>>>(k);
     }
     k_dep_cell<<<(unsigned)(((long long)C * 32 + 255) / 256), 256, 0, s>>>(w.rec, w.code, w.off, w.part, n > 0 ? n : 1, C);
     NodeK nk{c->Nr, c->Nth, c->ld, w.part, C, tabs_of(c), rho, jr, jth, jph};

@@ -1948,6 +1948,11 @@ extern "C" int fpic_set_tuning(fpic_ctx* c, int key, int value)
             return set_error(FPIC_EINVAL, "fpic_set_tuning: IMR blocks per SM must be in [1, 4], got %d", value);
         c->imr_blocks_per_sm = value;
         return FPIC_OK;
+    case FPIC_TUNE_DEP_THREADS:
+        if (value != 64 && value != 128 && value != 256)
+            return set_error(FPIC_EINVAL, "fpic_set_tuning: deposit threads must be 64, 128 or 256, got %d", value);
+        c->dep_threads = value;
+        return FPIC_OK;
     default:
         return set_error(FPIC_EINVAL, "fpic_set_tuning: unknown key %d", key);
     }
@@ -1959,6 +1964,9 @@ extern "C" int fpic_get_tuning(const fpic_ctx* c, int key, int* value)
     switch (key) {
     case FPIC_TUNE_IMR_BLOCKS_PER_SM:
         *value = c->imr_blocks_per_sm;
+        return FPIC_OK;
+    case FPIC_TUNE_DEP_THREADS:
+        *value = c->dep_threads;
         return FPIC_OK;
     default:
         return set_error(FPIC_EINVAL, "fpic_get_tuning: unknown key %d", key);

@@ -89,7 +89,7 @@ class fpic_learned_cfg(C.Structure):
 
 
 FPIC_LEARN_SKIP, FPIC_LEARN_CORRECT = 0, 1
-FPIC_TUNE_IMR_BLOCKS_PER_SM = 0
+FPIC_TUNE_IMR_BLOCKS_PER_SM, FPIC_TUNE_DEP_THREADS = 0, 1
 
 
 # name -> (restype, argtypes)

@@ -469,3 +469,30 @@ def test_conserving_pic_loop_matches_oracle(F):
     R = resid(Dg, fl.rho0.cpu().numpy())
     scale = np.abs(4 * math.pi * sg.reshape(g.Nr + 1, g.ld)[sel] * fl.rho0.cpu().numpy().reshape(g.Nr + 1, g.ld)[sel]).max()
     assert np.abs(R - R0).max() <= 1e-11 * scale
+
+
+def test_deposit_thread_tuning_changes_no_result(F):
+    """FPIC_TUNE_DEP_THREADS only reshapes the deposit's per-particle launch:
+    rho and the currents are bitwise the same for 64, 128 and 256 threads per
+    block; other values are rejected; the autotuner leaves a valid choice."""
+    import torch
+    from paper_2602_07452_gb300 import autotune
+    a = 0.9
+    g = I.log_grid(40, 32, 1.2 * I.horizon(1.0, a), 25.0)
+    ctx = F.fpic_init_metric(1.0, a)
+    F.fpic_set_grid(ctx, g)
+    z, q, w, alive = _plasma(g, 30011, a, 8)
+    outs = []
+    for v in (64, 128, 256):
+        F.fpic_set_tuning(ctx, F.FPIC_TUNE_DEP_THREADS, v)
+        p = make_particles(z, q, w=w, alive=alive)
+        outs.append([t.cpu().numpy() for t in F.fpic_deposit(ctx, p, g.size)])
+    for o in outs[1:]:
+        for x, y in zip(outs[0], o):
+            assert np.array_equal(x, y)
+    with pytest.raises(F.FpicError):
+        F.fpic_set_tuning(ctx, F.FPIC_TUNE_DEP_THREADS, 96)
+    p = make_particles(z, q, w=w, alive=alive)
+    times = autotune.tune_deposit_threads(ctx, p, g.size, reps=1)
+    assert set(times) == {64, 128, 256}
+    assert F.fpic_get_tuning(ctx, F.FPIC_TUNE_DEP_THREADS) == min(times, key=times.get)
