@@ -219,15 +219,18 @@ typedef struct {
 int fpic_push_batched(const fpic_run *runs, int nruns, fpic_particles *p, const fpic_push_params *prm,
                       fpic_push_stats *stats, void *stream);
 
-/* fpic_push on a particle set held in HOST memory (pinned for overlap):
- * the input arrays of *host_p (state, q/m, H_0, D_0, H^n, alive; w is not
- * read by the push and not copied) go to library-owned device buffers in
- * four particle chunks on a library-owned copy stream, the explicit pass of
- * each chunk starting as soon as its copies land (the implicit pass then
- * runs over all queued particles); the push is exactly fpic_push's, and the
- * state, Hn, alive, scheme, iters and cell arrays are copied back on
- * `stream`, which is synchronised before returning.  fields stay device
- * arrays.  Errors: as fpic_push. */
+/* fpic_push on a particle set held in HOST memory.  When every array of
+ * *host_p is page-locked, mapped host memory (cudaHostAlloc, cudaHostRegister,
+ * torch pin_memory), the kernels read and write it in place over the
+ * CPU-GPU link (NVLink-C2C on Grace): no staging copies, each byte crosses
+ * once per direction.  Otherwise the input arrays (state, q/m, H_0, D_0,
+ * H^n, alive; w is not read by the push and not copied) go to library-owned
+ * device buffers in four particle chunks on a library-owned copy stream, the
+ * explicit pass of each chunk starting as soon as its copies land (the
+ * implicit pass then runs over all queued particles), and the state, Hn,
+ * alive, scheme, iters and cell arrays are copied back on `stream`.  Either
+ * way the push is exactly fpic_push's and `stream` is synchronised before
+ * returning.  fields stay device arrays.  Errors: as fpic_push. */
 int fpic_push_host(fpic_ctx *ctx, fpic_particles *host_p, const double *const fields[6],
                    const fpic_push_params *prm, fpic_push_stats *stats, void *stream);
 

@@ -47,6 +47,11 @@ struct PushK {
     double dt, thr, tol, dg_eps;
     double dt_imp;          // step of the implicit solves (the hybrid's partner: fpic_push_params.dt_implicit)
     double* t;              // nullable per-particle time, advanced by the step each particle took
+    // particle arrays in host memory (read over the link): the implicit pass
+    // works from device copies by queue slot of z^n and q/m (7 x n) and of
+    // the iteration counts (n bytes); both null for device-resident particles
+    double* z0s;
+    uint8_t* its;
     int scheme, max_iter;
     long long n;
     long long p_begin, p_end;   // explicit pass over [p_begin, p_end) (p_end 0: all n)
@@ -291,6 +296,11 @@ __global__ void __launch_bounds__(128) k_explicit(const __grid_constant__ PushK 
             }
             k.sc0[p] = s0;
             k.sc0[k.n + p] = c0;
+            if (k.z0s) {
+#pragma unroll
+                for (int i = 0; i < 6; ++i) k.z0s[(size_t)i * k.n + idx] = z0[i];
+                k.z0s[(size_t)6 * k.n + idx] = qm;
+            }
             if (MODE == 2) {
                 trial_store(k, idx, sk, acc, kk, z0, y);
                 if (k.record) k.recS[idx] = label;
@@ -389,7 +399,12 @@ __global__ void __launch_bounds__(128, 4) k_imr(const __grid_constant__ PushK k,
                         qi = slot;
                         if (BATCHED) R = k.runs + run_of(k.runs, k.nruns, p);
                         again = RESTART != 0;
-                        load_state(k.P, p, z0);
+                        if (!all_mode && k.z0s) {
+#pragma unroll
+                            for (int i = 0; i < 6; ++i) z0[i] = k.z0s[(size_t)i * k.n + slot];
+                        } else {
+                            load_state(k.P, p, z0);
+                        }
                         if (all_mode) {
                             sincos(z0[1], &s0, &c0);
                             k.sc0[p] = s0;
@@ -404,7 +419,7 @@ __global__ void __launch_bounds__(128, 4) k_imr(const __grid_constant__ PushK k,
                                 zk[i] = RESTART ? k.stg[(size_t)(STG_GUESS + i) * k.n + slot]
                                                 : k.guess[(size_t)i * k.n + p];
                         }
-                        qm = k.P.qm[p];
+                        qm = (!all_mode && k.z0s) ? k.z0s[(size_t)6 * k.n + slot] : k.P.qm[p];
                         em = (R->has_fields || R->B0field != 0.0) && qm != 0.0;
                         it = 0;
                     }
@@ -465,7 +480,8 @@ __global__ void __launch_bounds__(128, 4) k_imr(const __grid_constant__ PushK k,
                 } else {
 #pragma unroll
                     for (int i = 0; i < 6; ++i) k.guess[(size_t)i * k.n + p] = zk[i];
-                    k.P.iters[p] = (uint8_t)min(it, 255);
+                    if (k.its && !all_mode) k.its[qi] = (uint8_t)min(it, 255);
+                    else k.P.iters[p] = (uint8_t)min(it, 255);
                 }
                 n_it += it;
                 p = -1;
@@ -493,10 +509,13 @@ __global__ void __launch_bounds__(256) k_imr_finish(const __grid_constant__ Push
 #pragma unroll
         for (int i = 0; i < 6; ++i) z[i] = k.guess[(size_t)i * k.n + p];
         double sn, cn;
-        sincos_near(k.P.th[p], k.sc0[p], k.sc0[k.n + p], z[1], sn, cn);
+        const bool st = k.z0s && !all_mode;
+        const double th0 = st ? k.z0s[(size_t)1 * k.n + idx] : k.P.th[p];
+        sincos_near(th0, k.sc0[p], k.sc0[k.n + p], z[1], sn, cn);
         const RunK& R = BATCHED ? k.runs[run_of(k.runs, k.nruns, p)] : k.run;
-        const double H = eval_H_sc(R.bh, z, sn, cn, k.P.qm[p], R.B0pot);
-        if (!finish(R, k.P, p, z, H, 1, k.P.iters[p])) ++n_rm;
+        const double qm = st ? k.z0s[(size_t)6 * k.n + idx] : k.P.qm[p];
+        const double H = eval_H_sc(R.bh, z, sn, cn, qm, R.B0pot);
+        if (!finish(R, k.P, p, z, H, 1, (k.its && !all_mode) ? k.its[idx] : k.P.iters[p])) ++n_rm;
         if (k.t) k.t[p] += k.dt_imp;
     }
     warp_add(&k.cnt[CNT_REMOVED], n_rm, 0xffffffffu);
@@ -935,7 +954,7 @@ static bool dt_implicit_ok(const fpic_push_params* prm)
 }
 
 static int push_core(fpic_ctx* c, fpic_particles* p, const double* const fields[6], const fpic_push_params* prm,
-                     fpic_push_stats* stats, cudaStream_t s, const PushChunks* ch);
+                     fpic_push_stats* stats, cudaStream_t s, const PushChunks* ch, bool host_state = false);
 
 extern "C" int fpic_push(fpic_ctx* c, fpic_particles* p, const double* const fields[6],
                          const fpic_push_params* prm, fpic_push_stats* stats, void* stream)
@@ -963,12 +982,13 @@ extern "C" int fpic_push(fpic_ctx* c, fpic_particles* p, const double* const fie
 }
 
 static int push_core(fpic_ctx* c, fpic_particles* p, const double* const fields[6], const fpic_push_params* prm,
-                     fpic_push_stats* stats, cudaStream_t s, const PushChunks* ch)
+                     fpic_push_stats* stats, cudaStream_t s, const PushChunks* ch, bool host_state)
 {
     const bool has_fields = fields != nullptr;
     const long long n = p->n;
     FPIC_CUDA(cudaSetDevice(c->device));
-    const size_t need = (size_t)n * (8 * sizeof(double) + 2 * sizeof(uint32_t)) + 256;
+    const size_t base_need = (size_t)n * (8 * sizeof(double) + 2 * sizeof(uint32_t));
+    const size_t need = base_need + (host_state ? (size_t)n * (7 * sizeof(double) + 1) : 0) + 256;
     int rc = ensure_scratch(c, need);
     if (rc) return rc;
     PushK k{};
@@ -996,6 +1016,10 @@ static int push_core(fpic_ctx* c, fpic_particles* p, const double* const fields[
     k.sc0 = k.guess + (size_t)n * 6;
     k.queue = (uint32_t*)((char*)c->d_scratch + (size_t)n * 8 * sizeof(double));
     k.order = k.queue + n;
+    if (host_state) {
+        k.z0s = (double*)((char*)c->d_scratch + base_need);
+        k.its = (uint8_t*)(k.z0s + (size_t)n * 7);
+    }
     k.cnt = c->d_cnt;
     k.learned = nullptr;
     FPIC_CUDA(cudaMemsetAsync(c->d_cnt, 0, CNT_N * sizeof(long long), s));
@@ -1072,6 +1096,34 @@ extern "C" int fpic_push_host(fpic_ctx* c, fpic_particles* hp, const double* con
     const long long n = hp->n;
     cudaStream_t s = (cudaStream_t)stream;
     FPIC_CUDA(cudaSetDevice(c->device));
+    // Pinned (page-locked, mapped) host arrays are reachable from the GPU over
+    // NVLink-C2C: the push then reads and writes them in place, with no
+    // staging copies (each byte still crosses the link once per direction).
+    if (n > 0) {
+        fpic_particles z = *hp;
+        bool mapped = true;
+        void** fields_h[] = {(void**)&z.r, (void**)&z.th, (void**)&z.ph, (void**)&z.ur, (void**)&z.uth,
+                             (void**)&z.uph, (void**)&z.qm, (void**)&z.w, (void**)&z.H0, (void**)&z.D0,
+                             (void**)&z.Hn, (void**)&z.alive, (void**)&z.scheme, (void**)&z.iters,
+                             (void**)&z.cell};
+        for (void** f : fields_h) {
+            if (!*f) continue;
+            cudaPointerAttributes at{};
+            if (cudaPointerGetAttributes(&at, *f) != cudaSuccess || at.type != cudaMemoryTypeHost ||
+                !at.devicePointer) {
+                cudaGetLastError();
+                mapped = false;
+                break;
+            }
+            *f = at.devicePointer;
+        }
+        if (mapped) {
+            int rc0 = push_core(c, &z, fields, prm, stats, s, nullptr, true);
+            if (rc0 < 0) return rc0;
+            FPIC_CUDA(cudaStreamSynchronize(s));
+            return rc0;
+        }
+    }
     // device mirror: 11 double arrays, 3 byte arrays, 1 u32 array
     const size_t nd = (size_t)n * sizeof(double), nb = (size_t)n, n4 = (size_t)n * 4;
     int rc = ensure_scratch2(c, 11 * nd + 3 * nb + n4 + 64);

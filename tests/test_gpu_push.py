@@ -321,10 +321,13 @@ def test_imr_launch_shape_changes_no_result():
 
 
 @pytest.mark.parametrize("n", [0, 3, 20011])
-def test_host_buffer_push_equals_device_push(n):
-    """fpic_push_host (chunked copies overlapping the explicit pass) gives
-    bitwise the device push's results, for ragged chunk sizes and removed
-    particles; the host arrays hold the result afterwards."""
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_buffer_push_equals_device_push(n, pinned):
+    """fpic_push_host gives bitwise the device push's results, for ragged
+    chunk sizes and removed particles, both on pinned host arrays (read and
+    written in place by the kernels) and on pageable ones (chunked copies
+    overlapping the explicit pass); the host arrays hold the result
+    afterwards."""
     cuda_or_skip()
     F = fpic()
     a = 0.9
@@ -343,6 +346,11 @@ def test_host_buffer_push_equals_device_push(n):
     p = make_particles(z, q, H0, D0, H0.copy(), alive.copy())
     F.fpic_push(ctx, p, fields_dev(Fo), prm)
     hp = F.HostParticles(n)
+    if not pinned:
+        import torch
+        for f in F.HostParticles.FIELDS_D + F.HostParticles.FIELDS_B + ("cell",):
+            t = getattr(hp, f)
+            setattr(hp, f, torch.zeros(t.shape, dtype=t.dtype))
     for k, col in zip(("r", "th", "ph", "ur", "uth", "uph"), range(6)):
         getattr(hp, k).copy_(torch_from(z[:, col]))
     hp.qm.copy_(torch_from(q)); hp.H0.copy_(torch_from(H0)); hp.D0.copy_(torch_from(D0))
