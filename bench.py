@@ -574,6 +574,7 @@ def run_pic(args, device, grid_n, ppc, steps, rank=0, conserving=False):
     import torch
     from paper_2602_07452_gb300 import fpic as F
     from paper_2602_07452_gb300 import inputs as I
+    from paper_2602_07452_gb300 import parallel as par
     g = I.wald_grid(grid_n, PIC_A)
     ctx = F.fpic_init_metric(1.0, PIC_A)
     F.fpic_set_grid(ctx, g)
@@ -621,6 +622,7 @@ def run_pic(args, device, grid_n, ppc, steps, rank=0, conserving=False):
             F.fpic_deposit_conserving(ctx, prev, p, PIC_DT, out=out4)
         else:
             F.fpic_deposit(ctx, p, g.size, out=(fl.rho1, fl.j1[0], fl.j1[1], fl.j1[2]))
+        par.allreduce_sources(out4)          # sharded particles: sum the sources over the ranks
         if timed:
             ev[3].record()
         F.fpic_fdtd_step(ctx, fl, fprm, 2)
