@@ -266,6 +266,21 @@ def _max_dH(F, ctx, p):
     return float(dH.max().item()) if dH.numel() else 0.0
 
 
+def _hbm_roofline(traffic, t_launch):
+    """DRAM bytes per launch / launch time against the measured copy bandwidth
+    (MEASURED_PEAKS.json beside this file, else the 6.8 TB/s fallback)."""
+    peak, src = 6800.0, "fallback"
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            peak, src = float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        pass
+    if not traffic or t_launch <= 0:
+        return {"achieved": None, "peak": peak, "unit": "GB/s", "frac": None, "peak_source": src}
+    a = traffic / t_launch / 1e9
+    return {"achieved": a, "peak": peak, "unit": "GB/s", "frac": a / peak, "peak_source": src}
+
+
 def run_gpu(args, ws, rank, local):
     import torch
     import torch.distributed as dist
@@ -409,7 +424,11 @@ def run_gpu(args, ws, rank, local):
                      "unit": "GFLOP/s", "frac": ach / fp64_gflops,
                      "traffic": TRAFFIC_K_EXPLICIT if dom == "k_explicit" else None,
                      "traffic_unit": "bytes per launch (ncu dram__bytes_read + dram__bytes_write)",
-                     "share_explicit": t_ex / max(t_ex + t_im, 1e-30)},
+                     "share_explicit": t_ex / max(t_ex + t_im, 1e-30),
+                     # the same kernel against the HBM roofline: its measured DRAM traffic per
+                     # launch over its event time, against the measured copy bandwidth
+                     "hbm": _hbm_roofline(TRAFFIC_K_EXPLICIT if dom == "k_explicit" else None,
+                                          (t_ex if dom == "k_explicit" else t_im) / max(args.steps, 1))},
         "clocks": clk,
         "gpu_launches": plain["launches"],
     }
