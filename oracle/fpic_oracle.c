@@ -544,7 +544,7 @@ static double dg_quot_em(double M, double a, double B0, double qm, const double 
         return mb.alpha * (2.0 * mb.gu_rp * ub[0] + mb.gu_pp * (ua[2] + ub[2])) / Gs;
     const double a2 = a * a;
     const double s2b = mb.s * mb.s, s2a = ma.s * ma.s, c2b = mb.c * mb.c, c2a = ma.c * ma.c;
-    const double Pb = rb / mb.rho2, Pa = ra / ma.rho2, Kb = 1.0 + c2b, Ka = 1.0 + c2a;
+    const double Pa = ra / ma.rho2, Kb = 1.0 + c2b, Ka = 1.0 + c2a;
     double d_rho2, d_f, d_s2, dP, dKP, dAph;
     if (v == 0) {
         d_rho2 = rb + ra;
@@ -582,7 +582,6 @@ static double dg_quot_em(double M, double a, double B0, double qm, const double 
                      + mb.gu_rr * (dur * ua[0] + ub[0] * dur)
                      + 2.0 * mb.gu_rp * (dur * ua[2] + ub[0] * dup)
                      + mb.gu_pp * (dup * ua[2] + ub[2] * dup);
-    (void)Pb;
     return 0.5 * (ma.alpha + mb.alpha) * dG2 / Gs + 0.5 * Gs * d_alpha - (d_beta * ua[0] + mb.beta * dur)
            - qm * dA0;
 }

@@ -262,7 +262,8 @@ struct Work {
     double* part;       // 20 x C cell partials
 };
 
-static int work_layout(fpic_ctx* c, long long n, bool deposit, Work& w)
+static int work_layout(fpic_ctx* c, long long n, bool deposit, Work& w, size_t extra_bytes = 0,
+                       void** extra = nullptr)
 {
     const long long C = (long long)c->Nr * c->Nth;
     const long long nbs = (n > C + 2 ? n : C + 2) / (SCAN_B * SCAN_PER) + 2;
@@ -277,9 +278,11 @@ static int work_layout(fpic_ctx* c, long long n, bool deposit, Work& w)
         o_code = take(4 * n);
         o_part = take(20 * 8 * (size_t)C);
     }
+    const size_t o_extra = extra_bytes ? take(extra_bytes) : 0;
     int rc = ensure_scratch2(c, bytes);
     if (rc) return rc;
     char* b = (char*)c->d_scratch2;
+    if (extra) *extra = extra_bytes ? (void*)(b + o_extra) : nullptr;
     w.key = (uint32_t*)(b + o_key);
     w.perm = (uint32_t*)(b + o_perm);
     w.perm2 = (uint32_t*)(b + o_perm2);
@@ -1041,23 +1044,10 @@ extern "C" int fpic_deposit_conserving(fpic_ctx* c, const fpic_particles* before
     cudaStream_t s = (cudaStream_t)stream;
     const long long C = (long long)c->Nr * c->Nth;
     Work w;
-    int rc = work_layout(c, n > 0 ? n : 1, false, w);
+    void* part_v = nullptr;     // per-cell window partials, CD_SLOTS x C doubles
+    int rc = work_layout(c, n > 0 ? n : 1, false, w, (size_t)CD_SLOTS * C * sizeof(double), &part_v);
     if (rc) return rc;
-    // per-cell partials after the Work block (CD_SLOTS x C doubles)
-    {
-        const size_t need_extra = (size_t)CD_SLOTS * C * sizeof(double) + 256;
-        size_t used = (size_t)((char*)w.tmp - (char*)c->d_scratch2) + 8 * (size_t)(n > 0 ? n : 1);
-        used = (used + 255) & ~(size_t)255;
-        if (used + need_extra > c->scratch2_bytes) {
-            rc = ensure_scratch2(c, used + need_extra);
-            if (rc) return rc;
-            rc = work_layout(c, n > 0 ? n : 1, false, w);
-            if (rc) return rc;
-        }
-    }
-    size_t used = (size_t)((char*)w.tmp - (char*)c->d_scratch2) + 8 * (size_t)(n > 0 ? n : 1);
-    used = (used + 255) & ~(size_t)255;
-    double* part = (double*)((char*)c->d_scratch2 + used);
+    double* part = (double*)part_v;
     CDepK k{c->Nr, c->Nth, c->ld, c->G, c->bh, n, before->r, before->th, before->ur, before->uth, before->uph,
             before->alive, after->r, after->th, after->ur, after->uth, after->uph, after->qm, after->w};
     FPIC_CUDA(cudaMemsetAsync(w.count, 0, 4 * ((size_t)C + 2), s));

@@ -651,7 +651,7 @@ __global__ void __launch_bounds__(128) k_dg(PushK k, int all_mode)
             double s1, c1;
             sincos(T1, &s1, &c1);
             const Geo m10 = geo_at(bh, R1, s0, c0), m01 = geo_at(bh, R0, s1, c1), m11 = geo_at(bh, R1, s1, c1);
-            const double dR = R1 - R0, dT = T1 - T0, dU = U1 - U0, dV = V1 - V0;
+            const double dT = T1 - T0;
             // d(cos th) / d th across the th move, without cancellation
             const double dc = -sin(0.5 * (T0 + T1)) * sinc_dev(0.5 * dT);
             const PD r_T0 = pd_r(bh, m00, m10, R0, R1), r_T1 = pd_r(bh, m01, m11, R0, R1);
@@ -688,7 +688,6 @@ __global__ void __launch_bounds__(128) k_dg(PushK k, int all_mode)
             const double Gp = (2.0 * f00 + m10.alpha * fma(m10.gurp, U1, m10.gupp * P) / g10_u1 +
                                m01.alpha * fma(m01.gurp, U0, m01.gupp * P) / g01_v1 +
                                2.0 * m11.alpha * fma(m11.gurp, U1, m11.gupp * P) / g11_uv) / 6.0;
-            (void)dR; (void)dU; (void)dV;
             double zn[6];
             zn[0] = fma(k.dt_imp, Gu, z0[0]);
             zn[1] = fma(k.dt_imp, Gv, z0[1]);
