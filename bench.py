@@ -67,6 +67,7 @@ def parse():
     ap.add_argument("--workload", default="push", choices=["push", "pic", "neutral", "batched", "clean", "inject", "adaptive"])
     ap.add_argument("--clean-sweeps", type=int, default=500, help="Jacobi sweeps of --workload clean")
     ap.add_argument("--conserving", action="store_true", help="--workload pic with the charge-conserving deposit")
+    ap.add_argument("--inject-every", type=int, default=0, help="--workload pic: pair injection every K steps")
     ap.add_argument("--neutral-scheme", default="HYB2", choices=["HYB2", "HAM", "RK4"],
                     help="scheme of --workload neutral")
     ap.add_argument("--neutral-pre", type=int, default=1000, help="untimed steps before --workload neutral")
@@ -582,13 +583,15 @@ def run_batched(args, device, scale, steps):
             "unit": UNIT, "ms_per_step": 1e3 * t / steps}
 
 
-def run_pic(args, device, grid_n, ppc, steps, rank=0, conserving=False):
+def run_pic(args, device, grid_n, ppc, steps, rank=0, conserving=False, inject_every=0):
     """Full GRPIC step (Sec. 2.1 order): FDTD sub-steps 1-4, RK4 push with
     D^{n+3/2}, B^{n+3/2}, sort + deposit at n+2, FDTD sub-steps 7-10.
     Plasma-filled Wald magnetosphere, a = 0.99, ppc particles in every cell.
     conserving: the charge-conserving variant (the move's coordinate
     currents from a copy of the state before the push, no sort; the FDTD in
-    its conserving mode)."""
+    its conserving mode).  inject_every: pair injection (Sec. 3.3: r_h..6 M,
+    multiplicity 3, n0 = 5) every that many steps, after sub-steps 1-4 and
+    before the push, into a store with room for it."""
     import numpy as np
     import torch
     from paper_2602_07452_gb300 import fpic as F
@@ -605,30 +608,52 @@ def run_pic(args, device, grid_n, ppc, steps, rank=0, conserving=False):
             getattr(fl, nm)[k].copy_(src)
     d, q, w = I.cell_fill_draws(g, ppc, 0.5, seed=3 + rank, qm=QM, r_lo=1.02 * I.horizon(1.0, PIC_A))
     n = d.shape[0]
-    p = F.Particles.empty(n, device)
+    C = g.Nr * g.Nth
+    cap = n + (4 * C if inject_every > 0 else 0)
+    store = F.Particles.empty(cap, device)
+    p = store.head(n)
     p.qm.copy_(torch.as_tensor(q, device=device))
     p.w.fill_(PIC_W)
     F.fpic_init_particles(ctx, p, F.FPIC_SEED_FIDO, torch.as_tensor(d, device=device))
     del d, q, w
+    n0 = n
+    inj = None
+    if inject_every > 0:
+        inj = {"prm": F.fpic_inject_params(I.horizon(1.0, PIC_A), 6.0, 3.0, 5.0, QM, 0.0),
+               "draws": torch.as_tensor(I.injection_draws(g, 0.5, seed=11 + rank).ravel(), device=device),
+               "pairs": 0, "calls": 0}
     r_max = float(g.rn[-1])
     fprm = F.fdtd_params(PIC_DT, 1e4, 5.0, 0.9 * r_max, r_max, conserving=conserving)
     pprm = F.push_params(PIC_DT, scheme=F.FPIC_RK4, r_max=r_max)
     out4 = (fl.rho1, fl.j1[0], fl.j1[1], fl.j1[2])
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
-    prev = None
+    prev = prev_store = None
     dep_tune = None
     if conserving:
-        prev = F.Particles(*[getattr(p, f).clone() for f in p.__dataclass_fields__])
+        prev_store = F.Particles(*[getattr(store, f).clone() for f in store.__dataclass_fields__])
+        prev = prev_store.head(n)
         F.fpic_deposit_conserving(ctx, prev, p, PIC_DT, out=out4)
     else:
         from paper_2602_07452_gb300 import autotune
         dep_tune = autotune.tune_deposit_threads(ctx, p, g.size)
         F.fpic_deposit(ctx, p, g.size, out=out4)
 
+    state = {"k": 0}
+
     def step(timed):
+        nonlocal p, prev, n
         if timed:
             ev[0].record()
         F.fpic_fdtd_step(ctx, fl, fprm, 1)
+        if inj is not None and state["k"] % inject_every == 0:
+            n_new, K, _ = F.fpic_inject_pairs(ctx, store, n, fl.B1[0], fl.B1[1], inj["prm"], inj["draws"])
+            inj["pairs"] += K
+            inj["calls"] += 1
+            n = n_new
+            p = store.head(n)
+            if conserving:
+                prev = prev_store.head(n)
+        state["k"] += 1
         if conserving:
             for nm in ("r", "th", "ur", "uth", "uph", "alive"):
                 getattr(prev, nm).copy_(getattr(p, nm))
@@ -664,8 +689,12 @@ def run_pic(args, device, grid_n, ppc, steps, rank=0, conserving=False):
     return {
         "workload": f"plasma-filled Wald GRPIC step, a={PIC_A}, {grid_n}x{grid_n} (ln r, theta), "
                     f"{ppc} particles/cell ({ppc // 2} e-/e+ pairs)",
-        "particles": n, "steps": steps, "value": ps / T, "unit": UNIT, "ms_per_step": 1e3 * T / steps,
-        "phase_ms": {"fdtd_1_4" + ("_and_state_copy" if conserving else ""): 1e3 * ph[0] / steps,
+        "particles": n0, "particles_at_end": n, "steps": steps, "value": ps / T, "unit": UNIT,
+        "ms_per_step": 1e3 * T / steps,
+        "injection": None if inj is None else {"every": inject_every, "calls": inj["calls"],
+                                               "pairs_wanted": inj["pairs"]},
+        "phase_ms": {"fdtd_1_4" + ("_and_injection" if inj is not None else "")
+                     + ("_and_state_copy" if conserving else ""): 1e3 * ph[0] / steps,
                      "push_rk4": 1e3 * ph[1] / steps,
                      ("conserving_deposit" if conserving else "sort_and_deposit"): 1e3 * ph[2] / steps,
                      "fdtd_7_10": 1e3 * ph[3] / steps},
@@ -967,7 +996,8 @@ def main():
         torch.cuda.set_device(local)
         dev = torch.device("cuda", local)
         if args.workload == "pic":
-            res = run_pic(args, dev, args.pic_grid, args.pic_ppc, args.pic_steps, rank, conserving=args.conserving)
+            res = run_pic(args, dev, args.pic_grid, args.pic_ppc, args.pic_steps, rank, conserving=args.conserving,
+                          inject_every=args.inject_every)
         elif args.workload == "neutral":
             res = run_neutral(args, dev, args.n, args.steps, pre_steps=args.neutral_pre, scheme=args.neutral_scheme)
         else:
@@ -983,6 +1013,8 @@ def main():
         import torch
         line["pic_step"] = run_pic(args, torch.device("cuda", local), 512, 16, 3, rank)
         line["pic_step_conserving"] = run_pic(args, torch.device("cuda", local), 512, 16, 3, rank, conserving=True)
+        line["pic_step_conserving_injecting"] = run_pic(args, torch.device("cuda", local), 512, 16, 4, rank,
+                                                        conserving=True, inject_every=2)
     if not args.no_extra and rank == 0:
         import torch
         dev = torch.device("cuda", local)
