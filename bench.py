@@ -68,6 +68,7 @@ def parse():
     ap.add_argument("--clean-sweeps", type=int, default=500, help="Jacobi sweeps of --workload clean")
     ap.add_argument("--conserving", action="store_true", help="--workload pic with the charge-conserving deposit")
     ap.add_argument("--inject-every", type=int, default=0, help="--workload pic: pair injection every K steps")
+    ap.add_argument("--clean-every", type=int, default=0, help="--workload pic: divergence cleaning every K steps")
     ap.add_argument("--neutral-scheme", default="HYB2", choices=["HYB2", "HAM", "RK4"],
                     help="scheme of --workload neutral")
     ap.add_argument("--neutral-pre", type=int, default=1000, help="untimed steps before --workload neutral")
@@ -583,7 +584,8 @@ def run_batched(args, device, scale, steps):
             "unit": UNIT, "ms_per_step": 1e3 * t / steps}
 
 
-def run_pic(args, device, grid_n, ppc, steps, rank=0, conserving=False, inject_every=0):
+def run_pic(args, device, grid_n, ppc, steps, rank=0, conserving=False, inject_every=0, clean_every=0,
+            clean_sweeps=500):
     """Full GRPIC step (Sec. 2.1 order): FDTD sub-steps 1-4, RK4 push with
     D^{n+3/2}, B^{n+3/2}, sort + deposit at n+2, FDTD sub-steps 7-10.
     Plasma-filled Wald magnetosphere, a = 0.99, ppc particles in every cell.
@@ -591,7 +593,9 @@ def run_pic(args, device, grid_n, ppc, steps, rank=0, conserving=False, inject_e
     currents from a copy of the state before the push, no sort; the FDTD in
     its conserving mode).  inject_every: pair injection (Sec. 3.3: r_h..6 M,
     multiplicity 3, n0 = 5) every that many steps, after sub-steps 1-4 and
-    before the push, into a store with room for it."""
+    before the push, into a store with room for it.  clean_every: divergence
+    cleaning (Sec. 2.4, clean_sweeps Jacobi sweeps) of D^{n+3/2} against
+    rho^{n+1} every that many steps, at the start of the step."""
     import numpy as np
     import torch
     from paper_2602_07452_gb300 import fpic as F
@@ -644,6 +648,9 @@ def run_pic(args, device, grid_n, ppc, steps, rank=0, conserving=False, inject_e
         nonlocal p, prev, n
         if timed:
             ev[0].record()
+        if clean_every > 0 and state["k"] % clean_every == 0:
+            F.fpic_div_clean(ctx, fl.D1, fl.rho0, clean_sweeps)
+            state["cleanings"] = state.get("cleanings", 0) + 1
         F.fpic_fdtd_step(ctx, fl, fprm, 1)
         if inj is not None and state["k"] % inject_every == 0:
             n_new, K, _ = F.fpic_inject_pairs(ctx, store, n, fl.B1[0], fl.B1[1], inj["prm"], inj["draws"])
@@ -693,6 +700,8 @@ def run_pic(args, device, grid_n, ppc, steps, rank=0, conserving=False, inject_e
         "ms_per_step": 1e3 * T / steps,
         "injection": None if inj is None else {"every": inject_every, "calls": inj["calls"],
                                                "pairs_wanted": inj["pairs"]},
+        "cleaning": None if clean_every <= 0 else {"every": clean_every, "sweeps": clean_sweeps,
+                                                   "calls": state.get("cleanings", 0)},
         "phase_ms": {"fdtd_1_4" + ("_and_injection" if inj is not None else "")
                      + ("_and_state_copy" if conserving else ""): 1e3 * ph[0] / steps,
                      "push_rk4": 1e3 * ph[1] / steps,
@@ -997,7 +1006,8 @@ def main():
         dev = torch.device("cuda", local)
         if args.workload == "pic":
             res = run_pic(args, dev, args.pic_grid, args.pic_ppc, args.pic_steps, rank, conserving=args.conserving,
-                          inject_every=args.inject_every)
+                          inject_every=args.inject_every, clean_every=args.clean_every,
+                          clean_sweeps=args.clean_sweeps)
         elif args.workload == "neutral":
             res = run_neutral(args, dev, args.n, args.steps, pre_steps=args.neutral_pre, scheme=args.neutral_scheme)
         else:
