@@ -33,7 +33,9 @@ A_SPIN, B0, THETA_T, QM, DT, NGRID = 0.9, 1.0, 0.1, 100.0, 1e-3, 512
 HYB1_THR = 3.5e-6          # (d Htilde/dt)_max of the Hyb1 test
 # Algorithmic FP64 flops (FMA = 2, add/mul/div/sqrt/rsqrt = 1, sin+cos = 2),
 # counted from the formulas of the push.
-FLOP_EVAL = 230            # metric + derivatives + gather + RHS + H at one point
+# metric (31) + derivatives (46) + gather (4 cell weights x 2 + 6 components x
+# 3 FMA of the per-cell bilinear form = 44) + RHS + H (91) at one point
+FLOP_EVAL = 212
 FLOP_RK4_TRIAL = 4 * FLOP_EVAL + 79 + 56 + 5
 FLOP_IMR_ITER = FLOP_EVAL + 48
 FLOP_IMR_FINAL = 56         # H at the converged point (metric + Gamma + H)
@@ -41,7 +43,7 @@ NOMINAL_FP64_GFLOPS = 1250.0
 # DRAM bytes (read + write) of one k_explicit<1> launch on this workload,
 # from one ncu capture of the current kernel (117.8 MB + 51.6 MB); the
 # algorithmic bytes are ~180 B per particle (189 MB for 2^20).
-TRAFFIC_K_EXPLICIT = 169.4e6
+TRAFFIC_K_EXPLICIT = 255.8e6   # ncu dram__bytes_read.sum + dram__bytes_write.sum, one 2^20 launch
 # deposit: FIDO velocity (41) + 3 sub-grids x (49 sqrt(gamma) points x 9 +
 # lattice 14 + four 16-point sums 128 + weights 16) + 2 th lattices (56) + shares (30)
 FLOP_DEPOSIT = 41 + 3 * (49 * 9 + 14 + 128 + 16) + 56 + 30

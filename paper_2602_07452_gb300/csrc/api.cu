@@ -289,6 +289,7 @@ extern "C" void fpic_destroy(fpic_ctx* c)
         if (e) cudaEventDestroy(e);
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     if (c->clean_exec) cudaGraphExecDestroy(c->clean_exec);
+    if (c->d_fcoef) cudaFree(c->d_fcoef);
     delete c;
 }
 

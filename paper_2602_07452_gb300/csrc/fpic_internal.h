@@ -44,6 +44,9 @@ struct fpic_ctx {
     // launch-shape tuning (fpic_set_tuning)
     int imr_blocks_per_sm = 4;
     int dep_threads = 128;           // threads per block of the deposit's particle kernel
+    // per-cell field interpolation coefficients (rebuilt by every push with fields)
+    void* d_fcoef = nullptr;
+    size_t fcoef_bytes = 0;
     // fpic_push_host: copy stream and per-chunk events (created on first use)
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t copy_ev[FPIC_HOST_CHUNKS + 1] = {};

@@ -37,6 +37,8 @@ struct RunK {
     int has_grid;
     double B0pot, r_h, r_max;
     double B0field;           // analytic Wald field (no grid fields): its B0, else 0
+    FieldsC FC;               // per-cell interpolation coefficients of F (has_coef)
+    int has_coef;
     long long begin, end;     // particle range of the run (batched push)
 };
 
@@ -116,7 +118,10 @@ __device__ __forceinline__ void F_at(const RunK& R, const double y[6], double qm
                                      double f[6], double& H)
 {
     double D[3] = {0, 0, 0}, B[3] = {0, 0, 0};
-    if (em) gather(R.G, R.F, y[0], y[1], D, B);
+    if (em) {
+        if (R.has_coef) gather_c(R.G, R.FC, y[0], y[1], D, B);
+        else gather(R.G, R.F, y[0], y[1], D, B);
+    }
     eval_rhs(R.bh, y, qm, em, D, B, R.B0pot, f, H);
 }
 
@@ -127,6 +132,7 @@ __device__ __forceinline__ void F_at_sc(const RunK& R, const double y[6], double
     double D[3] = {0, 0, 0}, B[3] = {0, 0, 0};
     if (em) {
         if (R.B0field != 0.0) wald_point_sc(R.bh, R.B0field, y[0], s, c, D, B);
+        else if (R.has_coef) gather_c(R.G, R.FC, y[0], y[1], D, B);
         else gather(R.G, R.F, y[0], y[1], D, B);
     }
     eval_rhs_sc(R.bh, y, s, c, qm, em, D, B, R.B0pot, f, H);
@@ -939,6 +945,55 @@ struct PushChunks {
 };
 }  // namespace fpic
 
+namespace fpic {
+// Per-cell bilinear coefficients of the six field components (see gather_c),
+// one thread per (node row, column); cells past a sub-grid's last node pair
+// are never read (the cell search clamps to the last cell).
+__global__ void k_field_coef(GridDev G, Fields F, double* out, size_t sz)
+{
+    const int i = blockIdx.y;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j <= G.Nth; j += gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const bool ro = (k == 0 || k == 4 || k == 5);
+            const bool to = (k == 1 || k == 3 || k == 5);
+            const int NRk = ro ? G.Nr : G.Nr + 1, NTk = to ? G.Nth : G.Nth + 1;
+            if (i >= NRk - 1 || j >= NTk - 1) continue;
+            const size_t o = (size_t)i * G.ld + j;
+            const double* f = F.f[k];
+            const double f00 = f[o], f01 = f[o + 1], f10 = f[o + G.ld], f11 = f[o + G.ld + 1];
+            const double b = f10 - f00, c = f01 - f00;
+            double2* q = reinterpret_cast<double2*>(out + (size_t)k * 4 * sz + 4 * o);
+            q[0] = make_double2(f00, b);
+            q[1] = make_double2(c, (f11 - f10) - c);
+        }
+    }
+}
+}  // namespace fpic
+
+// Builds the context's coefficient copy of the fields on stream s and points
+// R at it.
+static int field_coefs(fpic_ctx* c, const double* const fields[6], RunK& R, cudaStream_t s)
+{
+    const size_t sz = (size_t)(c->Nr + 1) * c->ld;
+    const size_t bytes = 6 * 4 * sz * sizeof(double);
+    if (c->fcoef_bytes < bytes) {
+        if (c->d_fcoef) FPIC_CUDA(cudaFree(c->d_fcoef));
+        c->d_fcoef = nullptr;
+        c->fcoef_bytes = 0;
+        FPIC_CUDA(cudaMalloc(&c->d_fcoef, bytes));
+        c->fcoef_bytes = bytes;
+    }
+    Fields F;
+    for (int i = 0; i < 6; ++i) F.f[i] = fields[i];
+    double* out = (double*)c->d_fcoef;
+    k_field_coef<<<dim3((unsigned)((c->Nth + 1 + 127) / 128), c->Nr + 1), 128, 0, s>>>(c->G, F, out, sz);
+    FPIC_CUDA(cudaGetLastError());
+    for (int i = 0; i < 6; ++i) R.FC.c[i] = out + (size_t)i * 4 * sz;
+    R.has_coef = 1;
+    return 0;
+}
+
 // Step of the implicit solves: the hybrid's partner takes dt_implicit when
 // set (adaptive steps, Sec. 3.1.2); pure schemes take dt.
 static double implicit_step(const fpic_push_params* prm)
@@ -1011,6 +1066,10 @@ static int push_core(fpic_ctx* c, fpic_particles* p, const double* const fields[
     k.n = n;
     k.P = PartDev{p->r, p->th, p->ph, p->ur, p->uth, p->uph, p->qm, p->H0, p->D0, p->Hn,
                   p->alive, p->scheme, p->iters, p->cell};
+    if (has_fields && n > 0) {
+        rc = field_coefs(c, fields, k.run, s);
+        if (rc) return rc;
+    }
     k.guess = (double*)c->d_scratch;
     k.sc0 = k.guess + (size_t)n * 6;
     k.queue = (uint32_t*)((char*)c->d_scratch + (size_t)n * 8 * sizeof(double));
@@ -1725,6 +1784,10 @@ extern "C" int fpic_learn_sample(fpic_ctx* c, fpic_particles* p, const double* c
     float *Xs, *Ys, *f32;
     int rc = learned_scratch(c, n, k, &Xs, &Ys, &f32);
     if (rc) return rc;
+    if (fields) {
+        rc = field_coefs(c, fields, k.run, s);
+        if (rc) return rc;
+    }
     k.work = nullptr;
     k.record = 1;
     k.recT = T;
@@ -1781,6 +1844,10 @@ extern "C" int fpic_push_learned(fpic_ctx* c, fpic_mlp* m, fpic_particles* p, co
     float *X, *Y, *f32;
     int rc = learned_scratch(c, n > 0 ? n : 1, k, &X, &Y, &f32);
     if (rc) return rc;
+    if (fields && n > 0) {
+        rc = field_coefs(c, fields, k.run, s);
+        if (rc) return rc;
+    }
     for (int i = 0; i < 6; ++i) k.inc_scale[i] = cfg->inc_scale[i];
     k.learned = Y;
     FPIC_CUDA(cudaMemsetAsync(c->d_cnt, 0, CNT_N * sizeof(long long), s));
@@ -1916,6 +1983,13 @@ extern "C" int fpic_push_batched(const fpic_run* runs, int nruns, fpic_particles
         R.r_max = r.r_max;
         R.begin = r.begin;
         R.end = r.end;
+        // interpolation coefficients in the run's context (when no other run shares it)
+        int uses = 0;
+        for (int j = 0; j < nruns; ++j) uses += runs[j].ctx == r.ctx ? 1 : 0;
+        if (R.has_fields && uses == 1 && r.end > r.begin) {
+            int rc0 = field_coefs(r.ctx, r.fields, R, s);
+            if (rc0) return rc0;
+        }
         tab[i] = R;
     }
     // The pinned staging table is rewritten only when it changes; outside a
