@@ -496,3 +496,48 @@ def test_deposit_thread_tuning_changes_no_result(F):
     times = autotune.tune_deposit_threads(ctx, p, g.size, reps=1)
     assert set(times) == {64, 128, 256}
     assert F.fpic_get_tuning(ctx, F.FPIC_TUNE_DEP_THREADS) == min(times, key=times.get)
+
+
+def test_new_grid_entry_points_edge_cases(F):
+    """Degenerate inputs of the grid-side extensions: an empty particle set
+    deposits zeros (conserving deposit) and injects into every eligible cell
+    of an empty store; a store without room injects nothing but still counts
+    the wanted pairs; the cleaning runs on the smallest grid (2 x 2) and on
+    zero sweeps leaves D unchanged when rho matches div D; a zero-length
+    move is a rest (no current)."""
+    import torch
+    a = 0.9
+    g = I.log_grid(6, 5, 1.5, 10.0)
+    ctx = F.fpic_init_metric(1.0, a)
+    F.fpic_set_grid(ctx, g)
+    empty = make_particles(np.zeros((0, 6)), np.zeros(0))
+    rho, jr, jt, jp = F.fpic_deposit_conserving(ctx, empty, empty, 0.1)
+    assert not rho.any() and not jr.any() and not jt.any() and not jp.any()
+    Br = dev(np.full(g.size, 1.0)); Bt = dev(np.zeros(g.size))
+    d = dev(I.injection_draws(g, 0.5, seed=1).ravel())
+    prm = F.fpic_inject_params(0.0, 1e9, 3.0, 5.0, 10.0, 0.0)
+    st = F.Particles.empty(2 * g.Nr * g.Nth)
+    n_new, K, fl = F.fpic_inject_pairs(ctx, st, 0, Br, Bt, prm, d, want_flags=True)
+    assert K == int(fl.sum().item()) > 0 and n_new == 2 * K
+    full = F.Particles.empty(5)
+    n2, K2, _ = F.fpic_inject_pairs(ctx, full, 5, Br, Bt, prm, d)
+    assert n2 == 5 and K2 == K
+    z = np.array([[2.5, 1.0, 0.0, 0.1, 0.0, 0.5]])
+    p = make_particles(z, np.array([1.0]))
+    _, jr, jt, jp = F.fpic_deposit_conserving(ctx, p, p, 0.1)
+    assert not jr.any() and not jt.any()
+    g2 = I.log_grid(2, 2, 1.5, 10.0)
+    ctx2 = F.fpic_init_metric(1.0, a)
+    F.fpic_set_grid(ctx2, g2)
+    D = [dev(np.random.default_rng(0).normal(size=g2.size)) for _ in range(3)]
+    D0 = [x.clone() for x in D]
+    rho2 = dev(np.zeros(g2.size))
+    F.fpic_div_clean(ctx2, D, rho2, 10)
+    Dc, _ = P.div_clean(1.0, a, g2, [x.cpu().numpy() for x in D0], np.zeros(g2.size), 10)
+    for k in range(3):
+        assert np.abs(D[k].cpu().numpy() - Dc[k]).max() <= 1e-12 * (np.abs(Dc[k]).max() + 1e-300)
+    D = [x.clone() for x in D0]
+    F.fpic_div_clean(ctx2, D, rho2, 0)
+    Dc0, _ = P.div_clean(1.0, a, g2, [x.cpu().numpy() for x in D0], np.zeros(g2.size), 0)
+    for k in range(3):
+        assert np.abs(D[k].cpu().numpy() - Dc0[k]).max() <= 1e-12 * (np.abs(Dc0[k]).max() + 1e-300)
