@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--impl", default="fpic", choices=["fpic", "reference"])
     ap.add_argument("--n", type=int, default=1 << 20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-steps", type=int, default=4)
+    ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--learned-form", choices=("correct", "skip"), default="correct",
                     help="learned guess: corrector of the rejected trials (default) or pre-step skip")
@@ -151,9 +151,14 @@ def cpu_baseline(n, steps, pool=None, cores=None):
             pool.close()
             pool.join()
     ps = sum(r[0] for r in res)
-    return {"value": ps / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{n} particles x {steps} steps of the same workload (serial C oracle, "
-                      f"one spawn process per core)", "wall_s": round(wall, 3)}
+    out = {"value": ps / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{n} particles x {steps} steps of the same workload (serial C oracle, "
+                     f"one spawn process per core)", "wall_s": round(wall, 3),
+           "cpu_seconds": round(sum(r[1] for r in res), 1)}
+    # the oracle as specified, on one core (a 1/cores share of the sample)
+    one = _oracle_chunk((0, n // cores, n, steps, 2))
+    out["serial_one_core"] = {"value": one[0] / one[1], "unit": UNIT, "particles": n // cores}
+    return out
 
 
 # ---------------------------------------------------------------------------
