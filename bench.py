@@ -66,7 +66,7 @@ def parse():
                     help="corrector: restart a solve from the plain trial after this many iterations (0: never)")
     ap.add_argument("--train-gen-steps", type=int, default=10,
                     help="plain steps sampled for the training set")
-    ap.add_argument("--workload", default="push", choices=["push", "pic", "neutral", "batched", "clean", "inject", "adaptive"])
+    ap.add_argument("--workload", default="push", choices=["push", "pic", "neutral", "batched", "clean", "inject", "adaptive", "charged_dg"])
     ap.add_argument("--clean-sweeps", type=int, default=500, help="Jacobi sweeps of --workload clean")
     ap.add_argument("--conserving", action="store_true", help="--workload pic with the charge-conserving deposit")
     ap.add_argument("--inject-every", type=int, default=0, help="--workload pic: pair injection every K steps")
@@ -977,6 +977,16 @@ def main():
     import torch.distributed as dist
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if args.workload == "charged_dg":
+        torch.cuda.set_device(local)
+        res = run_charged_dg(torch.device("cuda", local), args.n, max(args.steps, 1))
+        if rank == 0:
+            r0 = res["runs"][-1]
+            print(json.dumps({"metric": METRIC, "value": r0["value"], "unit": UNIT, "n_gpus": ws,
+                              "steps": res["steps"], "warmup": 1, "ms_per_step": r0["ms_per_step"],
+                              "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                              "data": "synthetic", "config": res}))
+        return 0
     if args.workload == "adaptive":
         torch.cuda.set_device(local)
         res = run_adaptive(torch.device("cuda", local), args.n, max(args.steps, 1))
