@@ -54,6 +54,7 @@ struct PushK {
     // the iteration counts (n bytes); both null for device-resident particles
     double* z0s;
     uint8_t* its;
+    int count_alive;        // the explicit pass also counts the alive particles (stats)
     int scheme, max_iter;
     long long n;
     long long p_begin, p_end;   // explicit pass over [p_begin, p_end) (p_end 0: all n)
@@ -218,6 +219,12 @@ __global__ void __launch_bounds__(128) k_explicit(const __grid_constant__ PushK 
         p = k.work[w];
     } else if (p >= (k.p_end ? k.p_end : k.n)) {
         return;
+    }
+    if (k.count_alive) {
+        const unsigned act = __activemask();
+        const unsigned al = __ballot_sync(act, k.P.alive[p] != 0);
+        if ((int)(threadIdx.x & 31) == __ffs(act) - 1)
+            atomicAdd((unsigned long long*)&k.cnt[CNT_ALIVE], (unsigned long long)__popc(al));
     }
     if (!k.P.alive[p]) {
         k.P.scheme[p] = 0;
@@ -1090,9 +1097,16 @@ static int push_core(fpic_ctx* c, fpic_particles* p, const double* const fields[
     const unsigned persist = (unsigned)c->sm_count * 8u;
     const unsigned imr_grid = (unsigned)c->sm_count * (unsigned)c->imr_blocks_per_sm;
     cudaEvent_t* ev = prm->events ? (cudaEvent_t*)prm->events : nullptr;
-    if (stats) k_count_alive<<<persist, 256, 0, s>>>(k.P, n, c->d_cnt);
-    if (ev) FPIC_CUDA(cudaEventRecord(ev[0], s));
     const bool explicit_pass = prm->scheme == FPIC_RK4 || prm->scheme >= FPIC_HYB1;
+    // with an explicit pass the alive count rides along in it (after each
+    // chunk's copies have landed); otherwise a separate pass counts
+    if (stats && !explicit_pass) {
+        if (ch)
+            for (int j = 0; j < ch->k; ++j) FPIC_CUDA(cudaStreamWaitEvent(s, ch->ready[j], 0));
+        k_count_alive<<<persist, 256, 0, s>>>(k.P, n, c->d_cnt);
+    }
+    k.count_alive = stats && explicit_pass ? 1 : 0;
+    if (ev) FPIC_CUDA(cudaEventRecord(ev[0], s));
     if (ch && !explicit_pass)
         for (int j = 0; j < ch->k; ++j) FPIC_CUDA(cudaStreamWaitEvent(s, ch->ready[j], 0));
     if (explicit_pass) {
