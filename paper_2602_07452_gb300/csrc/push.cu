@@ -1098,6 +1098,10 @@ static int push_core(fpic_ctx* c, fpic_particles* p, const double* const fields[
     const unsigned imr_grid = (unsigned)c->sm_count * (unsigned)c->imr_blocks_per_sm;
     cudaEvent_t* ev = prm->events ? (cudaEvent_t*)prm->events : nullptr;
     const bool explicit_pass = prm->scheme == FPIC_RK4 || prm->scheme >= FPIC_HYB1;
+    // few particles (under 4 blocks of 128 per SM): one-warp blocks, so the
+    // latency-bound steps spread over every SM instead of a few
+    const int TBx = n <= (long long)c->sm_count * 4 * 128 ? 32 : TB;
+    const unsigned nbx = (unsigned)((n + TBx - 1) / TBx);
     // with an explicit pass the alive count rides along in it (after each
     // chunk's copies have landed); otherwise a separate pass counts
     if (stats && !explicit_pass) {
@@ -1117,9 +1121,9 @@ static int push_core(fpic_ctx* c, fpic_particles* p, const double* const fields[
             const long long len = k.p_end - k.p_begin;
             if (ch) FPIC_CUDA(cudaStreamWaitEvent(s, ch->ready[j], 0));
             if (len <= 0) continue;
-            const unsigned nbj = (unsigned)((len + TB - 1) / TB);
-            if (prm->scheme == FPIC_RK4) k_explicit<0><<<nbj, TB, 0, s>>>(k);
-            else k_explicit<1><<<nbj, TB, 0, s>>>(k);
+            const unsigned nbj = (unsigned)((len + TBx - 1) / TBx);
+            if (prm->scheme == FPIC_RK4) k_explicit<0><<<nbj, TBx, 0, s>>>(k);
+            else k_explicit<1><<<nbj, TBx, 0, s>>>(k);
         }
         k.p_begin = 0;
         k.p_end = 0;
@@ -1132,15 +1136,15 @@ static int push_core(fpic_ctx* c, fpic_particles* p, const double* const fields[
         k_imr<0><<<imr_grid, TB, 0, s>>>(k, 1);
         k_imr_finish<><<<persist, 256, 0, s>>>(k, 1);
     } else if (prm->scheme == FPIC_HAM) {
-        if (k.run.B0field != 0.0) k_dg_em<<<nb, TB, 0, s>>>(k, 1);
-        else k_dg<<<nb, TB, 0, s>>>(k, 1);
+        if (k.run.B0field != 0.0) k_dg_em<<<nbx, TBx, 0, s>>>(k, 1);
+        else k_dg<<<nbx, TBx, 0, s>>>(k, 1);
     } else if (prm->scheme >= FPIC_HYB1 && prm->implicit == FPIC_IMR) {
         k_order<<<persist, 256, 0, s>>>(k);
         k_imr<0><<<imr_grid, TB, 0, s>>>(k, 0);
         k_imr_finish<><<<persist, 256, 0, s>>>(k, 0);
     } else if (prm->scheme >= FPIC_HYB1) {
-        if (k.run.B0field != 0.0) k_dg_em<<<nb, TB, 0, s>>>(k, 0);
-        else k_dg<<<nb, TB, 0, s>>>(k, 0);
+        if (k.run.B0field != 0.0) k_dg_em<<<nbx, TBx, 0, s>>>(k, 0);
+        else k_dg<<<nbx, TBx, 0, s>>>(k, 0);
     }
     if (ev) FPIC_CUDA(cudaEventRecord(ev[3], s));
     FPIC_CUDA(cudaGetLastError());
