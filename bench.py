@@ -607,7 +607,6 @@ def run_pic(args, device, grid_n, ppc, steps, rank=0, conserving=False, inject_e
     import torch
     from paper_2602_07452_gb300 import fpic as F
     from paper_2602_07452_gb300 import inputs as I
-    from paper_2602_07452_gb300 import parallel as par
     g = I.wald_grid(grid_n, PIC_A)
     ctx = F.fpic_init_metric(1.0, PIC_A)
     F.fpic_set_grid(ctx, g)
@@ -636,68 +635,30 @@ def run_pic(args, device, grid_n, ppc, steps, rank=0, conserving=False, inject_e
     r_max = float(g.rn[-1])
     fprm = F.fdtd_params(PIC_DT, 1e4, 5.0, 0.9 * r_max, r_max, conserving=conserving)
     pprm = F.push_params(PIC_DT, scheme=F.FPIC_RK4, r_max=r_max)
-    out4 = (fl.rho1, fl.j1[0], fl.j1[1], fl.j1[2])
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
-    prev = prev_store = None
     dep_tune = None
-    if conserving:
-        prev_store = F.Particles(*[getattr(store, f).clone() for f in store.__dataclass_fields__])
-        prev = prev_store.head(n)
-        F.fpic_deposit_conserving(ctx, prev, p, PIC_DT, out=out4)
-    else:
+    if not conserving:
         from paper_2602_07452_gb300 import autotune
         dep_tune = autotune.tune_deposit_threads(ctx, p, g.size)
-        F.fpic_deposit(ctx, p, g.size, out=out4)
-
-    state = {"k": 0}
-
-    def step(timed):
-        nonlocal p, prev, n
-        if timed:
-            ev[0].record()
-        if clean_every > 0 and state["k"] % clean_every == 0:
-            F.fpic_div_clean(ctx, fl.D1, fl.rho0, clean_sweeps)
-            state["cleanings"] = state.get("cleanings", 0) + 1
-        F.fpic_fdtd_step(ctx, fl, fprm, 1)
-        if inj is not None and state["k"] % inject_every == 0:
-            n_new, K, _ = F.fpic_inject_pairs(ctx, store, n, fl.B1[0], fl.B1[1], inj["prm"], inj["draws"])
-            inj["pairs"] += K
-            inj["calls"] += 1
-            n = n_new
-            p = store.head(n)
-            if conserving:
-                prev = prev_store.head(n)
-        state["k"] += 1
-        if conserving:
-            for nm in ("r", "th", "ur", "uth", "uph", "alive"):
-                getattr(prev, nm).copy_(getattr(p, nm))
-        if timed:
-            ev[1].record()
-        F.fpic_push(ctx, p, fl.push_fields(), pprm)
-        if timed:
-            ev[2].record()
-        if conserving:
-            F.fpic_deposit_conserving(ctx, prev, p, PIC_DT, out=out4)
-        else:
-            F.fpic_deposit(ctx, p, g.size, out=(fl.rho1, fl.j1[0], fl.j1[1], fl.j1[2]))
-        par.allreduce_sources(out4)          # sharded particles: sum the sources over the ranks
-        if timed:
-            ev[3].record()
-        F.fpic_fdtd_step(ctx, fl, fprm, 2)
-        if timed:
-            ev[4].record()
-        fl.swap()
-
-    step(False)
+    from paper_2602_07452_gb300.grpic import GRPIC
+    sim = GRPIC(ctx, g, fl, store, n, pprm, fprm, conserving=conserving,
+                clean=(clean_every, clean_sweeps) if clean_every > 0 else None,
+                inject=(inject_every, inj["prm"], inj["draws"]) if inj is not None else None)
+    sim.deposit_initial()
+    sim.step()
     torch.cuda.synchronize()
     ph = [0.0] * 4
     ps = 0
     for _ in range(steps):
-        ps += int(p.alive.sum().item())
-        step(True)
+        ps += int(sim.particles.alive.sum().item())
+        sim.step(events=ev)
         torch.cuda.synchronize()
         for i in range(4):
             ph[i] += ev[i].elapsed_time(ev[i + 1]) * 1e-3
+    n = sim.n
+    if inj is not None:
+        inj["pairs"], inj["calls"] = sim.pairs, (sim.k + inject_every - 1) // inject_every
+    state = {"cleanings": sim.cleanings}
     T = sum(ph)
     t_dep = ph[2]
     return {
@@ -709,7 +670,8 @@ def run_pic(args, device, grid_n, ppc, steps, rank=0, conserving=False, inject_e
                                                "pairs_wanted": inj["pairs"]},
         "cleaning": None if clean_every <= 0 else {"every": clean_every, "sweeps": clean_sweeps,
                                                    "calls": state.get("cleanings", 0)},
-        "phase_ms": {"fdtd_1_4" + ("_and_injection" if inj is not None else "")
+        "phase_ms": {("cleaning_and_" if clean_every > 0 else "") + "fdtd_1_4"
+                     + ("_and_injection" if inj is not None else "")
                      + ("_and_state_copy" if conserving else ""): 1e3 * ph[0] / steps,
                      "push_rk4": 1e3 * ph[1] / steps,
                      ("conserving_deposit" if conserving else "sort_and_deposit"): 1e3 * ph[2] / steps,

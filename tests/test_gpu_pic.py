@@ -541,3 +541,52 @@ def test_new_grid_entry_points_edge_cases(F):
     Dc0, _ = P.div_clean(1.0, a, g2, [x.cpu().numpy() for x in D0], np.zeros(g2.size), 0)
     for k in range(3):
         assert np.abs(D[k].cpu().numpy() - Dc0[k]).max() <= 1e-12 * (np.abs(Dc0[k]).max() + 1e-300)
+
+
+def test_grpic_conserving_loop_with_injection_keeps_gauss(F):
+    """The GRPIC sequencer (grpic.py) with the conserving deposit, the FDTD in
+    its conserving mode and pair injection every other step: the injected
+    pairs are neutral at one point, so Yee-div(sqrtg D) - 4 pi sqrtg rho at
+    the interior nodes stays what it was, over 6 steps, while the particle
+    count grows."""
+    from paper_2602_07452_gb300.grpic import GRPIC
+    a = 0.9
+    g = I.log_grid(24, 20, 1.5, 20.0)
+    ctx = F.fpic_init_metric(1.0, a)
+    F.fpic_set_grid(ctx, g)
+    n = 3000
+    rng = np.random.default_rng(4)
+    d, q, _ = I.thermal_draws(n, g, 3.0, 12.0, 0.3, seed=5, qm=50.0)
+    d[:, 1] = rng.uniform(0.5, math.pi - 0.5, n)
+    z = O.seed_fido(1.0, a, d)
+    Fw = O.wald_on_grid(a, 1.0, g)
+    fl = F.Fields(g.size)
+    for k in range(3):
+        for nm, src in (("D0", Fw[k]), ("D1", Fw[k]), ("B0", Fw[3 + k]), ("B1", Fw[3 + k])):
+            getattr(fl, nm)[k].copy_(dev(src))
+    cap = n + 4 * g.Nr * g.Nth
+    store = F.Particles.empty(cap)
+    head = store.head(n)
+    head.set_state(dev(z)); head.qm.copy_(dev(q)); head.w.fill_(1e-3); head.alive.fill_(1)
+    dt = 2e-3
+    inj = (2, F.fpic_inject_params(3.5, 8.0, 1e30, 0.05, 50.0, 0.0), dev(I.injection_draws(g, 0.3, seed=7).ravel()))
+    sim = GRPIC(ctx, g, fl, store, n, F.push_params(dt, scheme=F.FPIC_RK4, r_max=float(g.rn[-1])),
+                F.fdtd_params(dt, 0.0, 5.0, g.rn[-1], g.rn[-1]), conserving=True, inject=inj)
+    sim.deposit_initial()
+    sel = np.zeros((g.Nr + 1, g.ld), bool)
+    sel[2:g.Nr - 1, 2:g.Nth - 1] = True
+    sg = O.metric(1.0, a, np.repeat(g.rn, g.ld), np.tile(g.tn, g.Nr + 1))[:, 12]
+
+    def resid():
+        _, dD = P.div(1.0, a, g, [np.zeros(g.size)] * 3, [x.cpu().numpy() for x in fl.D1])
+        return (dD - 4 * math.pi * sg * fl.rho1.cpu().numpy()).reshape(g.Nr + 1, g.ld)[sel]
+
+    R0 = resid()
+    scale = np.abs(4 * math.pi * sg.reshape(g.Nr + 1, g.ld)[sel] * fl.rho1.cpu().numpy().reshape(g.Nr + 1, g.ld)[sel]).max()
+    for _ in range(6):
+        sim.step()
+        # after the swap the step's sources sit in the "0" slot: pair D1 with rho0
+        _, dD = P.div(1.0, a, g, [np.zeros(g.size)] * 3, [x.cpu().numpy() for x in fl.D1])
+        R = (dD - 4 * math.pi * sg * fl.rho0.cpu().numpy()).reshape(g.Nr + 1, g.ld)[sel]
+        assert np.abs(R - R0).max() <= 1e-11 * scale
+    assert sim.n > n and sim.pairs > 0
