@@ -279,8 +279,13 @@ int fpic_probe_fp64(double *gflops_out, int reps);
  *   FPIC_TUNE_DEP_THREADS: threads per block of the deposit's per-particle
  *     kernel (the trapezoid lattices), 64, 128 or 256 (default 128); the
  *     deposit's result does not depend on it.
+ *   FPIC_TUNE_STATIC_FIELDS: 1 = the caller does not change the contents of
+ *     the field arrays it passes (test particles in a fixed field), so the
+ *     per-cell interpolation coefficients each push builds are reused while
+ *     the six field pointers stay the same; 0 (default) = rebuilt every push.
+ *     Setting it discards the current coefficients.
  * Errors: FPIC_EINVAL (NULL, unknown key, value out of range). */
-enum { FPIC_TUNE_IMR_BLOCKS_PER_SM = 0, FPIC_TUNE_DEP_THREADS = 1 };
+enum { FPIC_TUNE_IMR_BLOCKS_PER_SM = 0, FPIC_TUNE_DEP_THREADS = 1, FPIC_TUNE_STATIC_FIELDS = 2 };
 int fpic_set_tuning(fpic_ctx *ctx, int key, int value);
 int fpic_get_tuning(const fpic_ctx *ctx, int key, int *value);
 

@@ -353,6 +353,7 @@ extern "C" int fpic_set_grid(fpic_ctx* c, int Nr, int Nth, const double* rn, con
     c->Nth = Nth;
     c->ld = Nth + 1;
     c->has_grid = true;
+    for (int i = 0; i < 6; ++i) c->fcoef_src[i] = nullptr;   // coefficients belong to the old grid
     int rc = build_metric_tables(c);
     if (rc) return rc;
     FPIC_CUDA(cudaDeviceSynchronize());

@@ -47,6 +47,8 @@ struct fpic_ctx {
     // per-cell field interpolation coefficients (rebuilt by every push with fields)
     void* d_fcoef = nullptr;
     size_t fcoef_bytes = 0;
+    int static_fields = 0;           // FPIC_TUNE_STATIC_FIELDS: reuse the coefficients of unchanged pointers
+    const double* fcoef_src[6] = {};  // the field arrays the coefficients were built from
     // fpic_push_host: copy stream and per-chunk events (created on first use)
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t copy_ev[FPIC_HOST_CHUNKS + 1] = {};

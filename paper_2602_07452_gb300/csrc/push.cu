@@ -988,14 +988,20 @@ static int field_coefs(fpic_ctx* c, const double* const fields[6], RunK& R, cuda
         if (c->d_fcoef) FPIC_CUDA(cudaFree(c->d_fcoef));
         c->d_fcoef = nullptr;
         c->fcoef_bytes = 0;
+        for (int i = 0; i < 6; ++i) c->fcoef_src[i] = nullptr;
         FPIC_CUDA(cudaMalloc(&c->d_fcoef, bytes));
         c->fcoef_bytes = bytes;
     }
     Fields F;
     for (int i = 0; i < 6; ++i) F.f[i] = fields[i];
     double* out = (double*)c->d_fcoef;
-    k_field_coef<<<dim3((unsigned)((c->Nth + 1 + 127) / 128), c->Nr + 1), 128, 0, s>>>(c->G, F, out, sz);
-    FPIC_CUDA(cudaGetLastError());
+    bool same = c->static_fields != 0;
+    for (int i = 0; i < 6; ++i) same = same && c->fcoef_src[i] == fields[i];
+    if (!same) {
+        k_field_coef<<<dim3((unsigned)((c->Nth + 1 + 127) / 128), c->Nr + 1), 128, 0, s>>>(c->G, F, out, sz);
+        FPIC_CUDA(cudaGetLastError());
+        for (int i = 0; i < 6; ++i) c->fcoef_src[i] = fields[i];
+    }
     for (int i = 0; i < 6; ++i) R.FC.c[i] = out + (size_t)i * 4 * sz;
     R.has_coef = 1;
     return 0;
@@ -2096,6 +2102,12 @@ extern "C" int fpic_set_tuning(fpic_ctx* c, int key, int value)
             return set_error(FPIC_EINVAL, "fpic_set_tuning: deposit threads must be 64, 128 or 256, got %d", value);
         c->dep_threads = value;
         return FPIC_OK;
+    case FPIC_TUNE_STATIC_FIELDS:
+        if (value != 0 && value != 1)
+            return set_error(FPIC_EINVAL, "fpic_set_tuning: static fields must be 0 or 1, got %d", value);
+        c->static_fields = value;
+        for (int i = 0; i < 6; ++i) c->fcoef_src[i] = nullptr;   // rebuilt at the next push
+        return FPIC_OK;
     default:
         return set_error(FPIC_EINVAL, "fpic_set_tuning: unknown key %d", key);
     }
@@ -2110,6 +2122,9 @@ extern "C" int fpic_get_tuning(const fpic_ctx* c, int key, int* value)
         return FPIC_OK;
     case FPIC_TUNE_DEP_THREADS:
         *value = c->dep_threads;
+        return FPIC_OK;
+    case FPIC_TUNE_STATIC_FIELDS:
+        *value = c->static_fields;
         return FPIC_OK;
     default:
         return set_error(FPIC_EINVAL, "fpic_get_tuning: unknown key %d", key);

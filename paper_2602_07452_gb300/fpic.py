@@ -89,7 +89,7 @@ class fpic_learned_cfg(C.Structure):
 
 
 FPIC_LEARN_SKIP, FPIC_LEARN_CORRECT = 0, 1
-FPIC_TUNE_IMR_BLOCKS_PER_SM, FPIC_TUNE_DEP_THREADS = 0, 1
+FPIC_TUNE_IMR_BLOCKS_PER_SM, FPIC_TUNE_DEP_THREADS, FPIC_TUNE_STATIC_FIELDS = 0, 1, 2
 
 
 # name -> (restype, argtypes)

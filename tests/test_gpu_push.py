@@ -480,3 +480,41 @@ def test_analytic_wald_push_matches_oracle(F, scheme):
         imp = (so == 1) & ok
         Hnew = O.hamiltonian(1.0, a, B0, zg[imp], q[imp])[0]
         assert np.abs(Hnew - H0[imp]).max() <= 1e-14 * np.abs(H0).max()
+
+
+def test_static_fields_reuse_changes_no_result():
+    """FPIC_TUNE_STATIC_FIELDS reuses the interpolation coefficients while the
+    field pointers stay the same: two pushes with it on give bitwise the
+    results of two pushes with it off; new field arrays are picked up; the
+    flag only takes 0 or 1."""
+    cuda_or_skip()
+    F = fpic()
+    a = 0.9
+    g = I.wald_grid(96, a)
+    Fo = O.wald_on_grid(a, 1.0, g)
+    ctx = F.fpic_init_metric(1.0, a)
+    F.fpic_set_grid(ctx, g)
+    d, z, q = thermal_state(3001, g, a, theta=0.1, seed=17)
+    H0, _, D0 = O.hamiltonian(1.0, a, 1.0, z, q)
+    prm = F.push_params(1e-3, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=8e-5, r_max=float(g.rn[-1]),
+                        B0pot=1.0)
+    fd = fields_dev(Fo)
+    res = []
+    for flag in (0, 1):
+        F.fpic_set_tuning(ctx, F.FPIC_TUNE_STATIC_FIELDS, flag)
+        assert F.fpic_get_tuning(ctx, F.FPIC_TUNE_STATIC_FIELDS) == flag
+        p = make_particles(z, q, H0, D0, H0.copy())
+        F.fpic_push(ctx, p, fd, prm)
+        F.fpic_push(ctx, p, fd, prm)
+        res.append(to_np(p)[0])
+    assert np.array_equal(res[0], res[1])
+    # a second, scaled field set through new arrays is used at once
+    fd2 = fields_dev([2.0 * f for f in Fo])
+    pa = make_particles(z, q, H0, D0, H0.copy())
+    F.fpic_push(ctx, pa, fd2, prm)
+    F.fpic_set_tuning(ctx, F.FPIC_TUNE_STATIC_FIELDS, 0)
+    pb = make_particles(z, q, H0, D0, H0.copy())
+    F.fpic_push(ctx, pb, fd2, prm)
+    assert np.array_equal(to_np(pa)[0], to_np(pb)[0])
+    with pytest.raises(F.FpicError):
+        F.fpic_set_tuning(ctx, F.FPIC_TUNE_STATIC_FIELDS, 2)
