@@ -61,7 +61,8 @@ class PushParams(C.Structure):
                 ("field_kind", C.c_int), ("B0field", C.c_double), ("dt", C.c_double),
                 ("scheme", C.c_int), ("implicit_kind", C.c_int), ("thr", C.c_double),
                 ("tol", C.c_double), ("max_iter", C.c_int), ("r_h", C.c_double),
-                ("r_max", C.c_double), ("dg_eps", C.c_double), ("dt_imp", C.c_double)]
+                ("r_max", C.c_double), ("dg_eps", C.c_double), ("dt_imp", C.c_double),
+                ("imr_newton", C.c_int)]
 
 
 _D = C.POINTER(C.c_double)
@@ -76,6 +77,7 @@ def _declare(L):
     L.or_wald.argtypes = [C.c_double, C.c_double, _I64, _D, _D, _D, _D, _D, _D, _D]
     L.or_hamiltonian.argtypes = [C.c_double, C.c_double, C.c_double, _I64, _D, _D, _D, _D, _D]
     L.or_rhs.argtypes = [C.c_double, C.c_double, _I64, _D, _D, _D, _D, _D]
+    L.or_imr_blocks.argtypes = [C.c_double, C.c_double, _I64, _D, _D, _D, _D, _D]
     L.or_gather.argtypes = [C.c_int, C.c_int, C.c_int, _D, _D, _D, _D, C.POINTER(_D), _I64, _D, _D, _D]
     L.or_cell_index.argtypes = [C.c_int, C.c_int, _D, _D, _I64, _D, _D, _U32]
     L.or_dg_grad.argtypes = [C.c_double, C.c_double, _D, _D, C.c_double, _D]
@@ -166,6 +168,17 @@ def rhs(M, a, z, qm, D=None, B=None):
     return f
 
 
+def imr_blocks(M, a, z, qm, B=None):
+    """Momentum blocks (A, J), each (n, 3, 3), of the IMR Newton matrix (Sec. 2.2.2)."""
+    z = f64(z).reshape(-1, 6)
+    n = z.shape[0]
+    qm = f64(np.broadcast_to(qm, (n,)))
+    A, J = np.empty((n, 3, 3)), np.empty((n, 3, 3))
+    Bp = None if B is None else ptr(f64(B).reshape(n, 3))
+    lib().or_imr_blocks(M, a, n, ptr(z), ptr(qm), Bp, ptr(A), ptr(J))
+    return A, J
+
+
 def dg_quot(M, a, zb, za, v):
     """Closed-form quotient (H(za) - H(zb)) / (za_v - zb_v) of a single-variable move."""
     out = np.zeros(1)
@@ -230,11 +243,11 @@ def wald_on_grid(a, B0, g):
 
 def push_params(M=1.0, a=0.9, B0pot=0.0, field_kind=FIELD_NONE, B0field=0.0, dt=0.01,
                 scheme=RK4, implicit_kind=IMR, thr=1e-12, tol=1e-14, max_iter=50,
-                r_h=None, r_max=1e300, dg_eps=1e-10, dt_imp=0.0):
+                r_h=None, r_max=1e300, dg_eps=1e-10, dt_imp=0.0, imr_newton=False):
     if r_h is None:
         r_h = M + np.sqrt(M * M - a * a)
     return PushParams(M, a, B0pot, field_kind, B0field, dt, scheme, implicit_kind, thr, tol,
-                      max_iter, r_h, r_max, dg_eps, dt_imp)
+                      max_iter, r_h, r_max, dg_eps, dt_imp, int(bool(imr_newton)))
 
 
 def push(p: PushParams, z, qm, H0, D0, Hn, alive, g=None, F=None):

@@ -353,6 +353,7 @@ typedef struct {
     double r_h, r_max;     /* particle removal radii */
     double dg_eps;         /* discrete-gradient increment threshold */
     double dt_imp;         /* step of the implicit partner of a hybrid (0: dt) */
+    int imr_newton;        /* IMR solver: 0 the fixed-point map of Eq. (imr2), 1 Newton */
 } or_push_params;
 
 typedef struct {
@@ -408,12 +409,94 @@ static int converged(const double *a, const double *b, double tol)
     return 1;
 }
 
-/* Sec. 2.2.2, Eqs. (imr1)-(imr2): implicit midpoint rule, solved by the
- * fixed-point iteration z^[k] = z^n + dt F((z^n + z^[k-1])/2).
+/* Momentum derivatives of the right-hand side at z (Eqs. p1, p2), the
+ * blocks kept in the Newton matrix of the IMR solve:
+ *   A_il = d(dx^i/dt)/du_l = alpha (g^il / Gamma - u^i u^l / Gamma^3),
+ *   J_il = d(du_i/dt)/du_l of the magnetic force qm alpha sqrt(gamma) (u x B)_i / Gamma
+ *        = qm alpha sqrt(gamma) ((g^{.l} x B)_i / Gamma - (u x B)_i u^l / Gamma^3),
+ * with u^i = g^ij u_j and g^{.l} the l-th column of g^ij (d u^i / du_l).
+ * The gravitational part of du/dt depends on u only through Gamma and is
+ * left out of J, as are all position derivatives. */
+static void cross3(const double *x, const double *y, double *o)
+{
+    o[0] = x[1] * y[2] - x[2] * y[1];
+    o[1] = x[2] * y[0] - x[0] * y[2];
+    o[2] = x[0] * y[1] - x[1] * y[0];
+}
+
+static void imr_blocks_at(double M, double a, double qm, const double *z, const double *B,
+                          double A[3][3], double J[3][3])
+{
+    om_t m;
+    om_eval(M, a, z[0], z[1], &m);
+    const double gi[3][3] = {{m.gu_rr, 0.0, m.gu_rp}, {0.0, m.gu_tt, 0.0}, {m.gu_rp, 0.0, m.gu_pp}};
+    double U[3];
+    for (int i = 0; i < 3; ++i) U[i] = gi[i][0] * z[3] + gi[i][1] * z[4] + gi[i][2] * z[5];
+    const double G = sqrt(1.0 + U[0] * z[3] + U[1] * z[4] + U[2] * z[5]);
+    for (int i = 0; i < 3; ++i)
+        for (int l = 0; l < 3; ++l) {
+            A[i][l] = m.alpha * (gi[i][l] / G - U[i] * U[l] / (G * G * G));
+            J[i][l] = 0.0;
+        }
+    if (!B || qm == 0.0) return;
+    const double k = qm * m.alpha * m.sqrtg;
+    double cr[3];
+    cross3(U, B, cr);
+    for (int l = 0; l < 3; ++l) {
+        const double col[3] = {gi[0][l], gi[1][l], gi[2][l]};
+        double x[3];
+        cross3(col, B, x);
+        for (int i = 0; i < 3; ++i) J[i][l] = k * (x[i] / G - cr[i] * U[l] / (G * G * G));
+    }
+}
+
+static void imr_blocks(const or_ctx *c, const double *z, double A[3][3], double J[3][3])
+{
+    double D[3], B[3];
+    int have;
+    field_at(c, z, D, B, &have);
+    imr_blocks_at(c->p->M, c->p->a, c->qm, z, have ? B : NULL, A, J);
+}
+
+/* Solve the 3 x 3 system M x = b by Gaussian elimination with partial
+ * pivoting (M is overwritten). */
+static void solve3(double M[3][3], double b[3], double x[3])
+{
+    for (int k = 0; k < 3; ++k) {
+        int piv = k;
+        for (int i = k + 1; i < 3; ++i)
+            if (fabs(M[i][k]) > fabs(M[piv][k])) piv = i;
+        if (piv != k) {
+            for (int j = 0; j < 3; ++j) { double t = M[k][j]; M[k][j] = M[piv][j]; M[piv][j] = t; }
+            double t = b[k]; b[k] = b[piv]; b[piv] = t;
+        }
+        for (int i = k + 1; i < 3; ++i) {
+            const double f = M[i][k] / M[k][k];
+            for (int j = k; j < 3; ++j) M[i][j] -= f * M[k][j];
+            b[i] -= f * b[k];
+        }
+    }
+    for (int i = 2; i >= 0; --i) {
+        double s = b[i];
+        for (int j = i + 1; j < 3; ++j) s -= M[i][j] * x[j];
+        x[i] = s / M[i][i];
+    }
+}
+
+/* Sec. 2.2.2, Eqs. (imr1)-(imr2): implicit midpoint rule z1 = z^n + h F((z^n + z1)/2).
  * Reading: Eq. (imr2) prints dt/2 F(z^n + z^[k-1]); the argument is read as
- * the midpoint (Eq. imr1), and the "Newton" of the text as this fixed-point
- * update (the one the equation shows).  Returns the iteration count, or
- * -max_iter if the cap was reached. */
+ * the midpoint (Eq. imr1).  Two solvers of the same equation:
+ *  - imr_newton = 0: the fixed-point update the equation shows,
+ *    z^[k] = z^n + h F((z^n + z^[k-1])/2);
+ *  - imr_newton = 1: the Newton iteration the text names, on the residual
+ *    R(z) = z - z^n - h F((z^n + z)/2) with the Jacobian dR/dz = 1 - (h/2) dF
+ *    in which dF keeps its momentum columns (imr_blocks: A for the
+ *    positions, J for the momenta) and drops the position columns.  With
+ *    z^p = z^n + h F(y), y = (z^n + z^[k-1])/2, the step solves
+ *    (1 - (h/2) J) du = u^[k-1] - u^p, then u^[k] = u^[k-1] - du and
+ *    x^[k] = x^p - (h/2) A du.  Only the convergence rate differs: both
+ *    stop at the same fixed point.
+ * Returns the iteration count, or -max_iter if the cap was reached. */
 static int step_imr(const or_ctx *c, double h, const double *z0, const double *guess, double *z1)
 {
     double zk[6], y[6], f[6], zn[6];
@@ -422,6 +505,19 @@ static int step_imr(const or_ctx *c, double h, const double *z0, const double *g
         for (int i = 0; i < 6; ++i) y[i] = 0.5 * (z0[i] + zk[i]);
         F_eval(c, y, f);
         for (int i = 0; i < 6; ++i) zn[i] = z0[i] + h * f[i];
+        if (c->p->imr_newton) {
+            double A[3][3], J[3][3], Mx[3][3], b[3], du[3];
+            imr_blocks(c, y, A, J);
+            for (int i = 0; i < 3; ++i) {
+                for (int l = 0; l < 3; ++l) Mx[i][l] = (i == l ? 1.0 : 0.0) - 0.5 * h * J[i][l];
+                b[i] = zk[3 + i] - zn[3 + i];
+            }
+            solve3(Mx, b, du);
+            for (int i = 0; i < 3; ++i) {
+                zn[3 + i] = zk[3 + i] - du[i];
+                zn[i] -= 0.5 * h * (A[i][0] * du[0] + A[i][1] * du[1] + A[i][2] * du[2]);
+            }
+        }
         int ok = converged(zn, zk, c->p->tol);
         memcpy(zk, zn, sizeof zk);
         if (ok) { memcpy(z1, zk, sizeof zk); return k; }
@@ -802,6 +898,19 @@ void or_hamiltonian(double M, double a, double B0pot, int64_t n, const double *z
         if (H) H[p] = ham(&bh, qm[p], z + 6 * p);
         if (L) L[p] = angmom(&bh, qm[p], z + 6 * p);
         if (Dn) Dn[p] = ham_norm(&bh, qm[p], z + 6 * p);
+    }
+}
+
+/* Momentum blocks A, J of the IMR Newton matrix (row-major 3 x 3 each) at
+ * n states, B per state (n x 3; NULL = no field). */
+void or_imr_blocks(double M, double a, int64_t n, const double *z, const double *qm, const double *B,
+                   double *A, double *J)
+{
+    for (int64_t p = 0; p < n; ++p) {
+        double a3[3][3], j3[3][3];
+        imr_blocks_at(M, a, qm[p], z + 6 * p, B ? B + 3 * p : NULL, a3, j3);
+        memcpy(A + 9 * p, a3, sizeof a3);
+        memcpy(J + 9 * p, j3, sizeof j3);
     }
 }
 

@@ -503,3 +503,128 @@ def test_charged_dg_conserves_H_and_L_and_converges_to_the_lorentz_force():
     errs = [np.abs(run(O.HAM, T / m, m)[0] - ref).max() for m in (20, 40, 80)]
     rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
     assert all(abs(r_ - 2) < 0.35 for r_ in rates), (errs, rates)
+
+
+def _wald_plasma(n, a=0.9, seed=5):
+    g = I.wald_grid(64, a)
+    d, qm, _ = I.thermal_draws(n, g, 1.02 * I.horizon(1.0, a), 49.0, 0.1, seed=seed, qm=100.0)
+    return O.seed_fido(1.0, a, d), qm
+
+
+def test_imr_newton_blocks_match_finite_differences():
+    """The momentum blocks of the IMR Newton matrix (Sec. 2.2.2) are the
+    derivatives of the right-hand side (Eqs. p1, p2, O1, O2) with respect
+    to u: A = d(dx/dt)/du against central differences of the position rows,
+    J against central differences of the momentum rows' field part (the
+    right-hand side with the Wald field minus the one without)."""
+    a, B0 = 0.9, 1.0
+    z, qm = _wald_plasma(64, a)
+    B, _, D, _, _ = O.wald(a, B0, z[:, 0], z[:, 1])
+    A, J = O.imr_blocks(1.0, a, z, qm, B)
+    fdA, fdJ = np.zeros_like(A), np.zeros_like(J)
+    for l in range(3):
+        h = 1e-5 * (np.abs(z[:, 3 + l]) + 1.0)
+        zp, zm = z.copy(), z.copy()
+        zp[:, 3 + l] += h
+        zm[:, 3 + l] -= h
+        fe = O.rhs(1.0, a, zp, qm, D, B) - O.rhs(1.0, a, zm, qm, D, B)
+        fg = O.rhs(1.0, a, zp, qm) - O.rhs(1.0, a, zm, qm)
+        fdA[:, :, l] = fe[:, :3] / (2 * h)[:, None]
+        fdJ[:, :, l] = (fe - fg)[:, 3:] / (2 * h)[:, None]
+    assert np.abs(A - fdA).max() < 1e-8 * np.abs(A).max()
+    assert np.abs(J - fdJ).max() < 1e-8 * np.abs(J).max()
+    # no field: J vanishes, A does not depend on the charge
+    A0, J0 = O.imr_blocks(1.0, a, z, qm)
+    assert np.array_equal(A0, A) and not J0.any()
+
+
+@pytest.mark.parametrize("field", ["wald", "grid"])
+def test_imr_newton_reaches_the_fixed_point_solution(field):
+    """The Newton iteration and the fixed-point update of Eq. (imr2) solve
+    the same implicit-midpoint equation: from the same start they stop at
+    the same state (to the iteration tolerance), the Newton form in fewer
+    iterations for charged particles gyrating in the Wald field."""
+    a, B0 = 0.9, 1.0
+    z0, qm = _wald_plasma(600, a)
+    H0, _, D0 = O.hamiltonian(1.0, a, B0, z0, qm)
+    if field == "wald":
+        kw, gf = dict(field_kind=O.FIELD_WALD, B0field=B0), {}
+    else:
+        g = I.wald_grid(64, a)
+        kw, gf = dict(field_kind=O.FIELD_GRID), dict(g=g, F=O.wald_on_grid(a, B0, g))
+    out = {}
+    for newton in (False, True):
+        p = O.push_params(a=a, dt=1e-3, scheme=O.IMR, B0pot=B0, tol=1e-14, imr_newton=newton, **kw)
+        z = z0.copy()
+        Hn, alive = np.zeros(len(z)), np.ones(len(z), np.uint8)
+        nc, sch, its = O.push(p, z, qm, H0, D0, Hn, alive, **gf)
+        assert nc == 0
+        out[newton] = (z, its.astype(float))
+    (zf, itf), (zn, itn) = out[False], out[True]
+    assert np.abs(zn - zf).max(axis=1).max() < 1e-12 * (np.abs(zf).max() + 1)
+    assert itn.mean() < 0.6 * itf.mean() and itn.max() <= 8, (itn.mean(), itf.mean())
+
+
+def test_imr_newton_keeps_order_and_symmetry():
+    """The Newton-solved IMR is the same scheme: second order (global error
+    at fixed T with dt halved) and time symmetric (+dt then -dt returns to
+    the start) on a Kerr geodesic."""
+    a, T = 0.9, 4.0
+    z0 = _kerr_orbit_state()
+    ref = _ref(a, z0, T)
+    errs = []
+    for nsteps in (20, 40, 80):
+        p = O.push_params(a=a, dt=T / nsteps, scheme=O.IMR, imr_newton=True)
+        errs.append(np.abs(_run(p, z0, nsteps)[0][0] - ref).max())
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(abs(q - 2) < 0.35 for q in rates), rates
+    p = O.push_params(a=a, dt=0.3, scheme=O.IMR, tol=1e-15, imr_newton=True)
+    z1 = _run(p, z0, 1)[0]
+    p2 = O.push_params(a=a, dt=-0.3, scheme=O.IMR, tol=1e-15, r_max=1e300, imr_newton=True)
+    assert np.abs(_run(p2, z1[0], 1)[0][0] - z0).max() < 1e-12
+
+
+def test_imr_newton_first_iterates_are_newton_steps():
+    """Each Newton iterate of the IMR solve is z - P^-1 R(z) for the residual
+    R(z) = z - z^n - dt F((z^n + z)/2) and P = 1 - (dt/2) dF restricted to
+    its momentum columns, here built from central differences of the
+    right-hand side and solved by numpy: the first two iterates of the
+    oracle's solve (max_iter = 1, 2; start z^n) agree with that
+    construction far inside the size of the momentum coupling terms."""
+    a, B0, dt = 0.9, 1.0, 1e-3
+    z0, qm = _wald_plasma(40, a, seed=9)
+    H0, _, D0 = O.hamiltonian(1.0, a, B0, z0, qm)
+
+    def F(z):
+        B, _, D, _, _ = O.wald(a, B0, z[:, 0], z[:, 1])
+        return O.rhs(1.0, a, z, qm, D, B)
+
+    def newton_np(zk):
+        y = 0.5 * (z0 + zk)
+        R = zk - (z0 + dt * F(y))
+        dF = np.zeros((len(y), 6, 3))
+        for l in range(3):
+            h = 1e-5 * (np.abs(y[:, 3 + l]) + 1.0)
+            yp, ym = y.copy(), y.copy()
+            yp[:, 3 + l] += h
+            ym[:, 3 + l] -= h
+            B, _, D, _, _ = O.wald(a, B0, y[:, 0], y[:, 1])   # fields at the midpoint
+            fe = O.rhs(1.0, a, yp, qm, D, B) - O.rhs(1.0, a, ym, qm, D, B)
+            fg = O.rhs(1.0, a, yp, qm) - O.rhs(1.0, a, ym, qm)
+            dF[:, :3, l] = fe[:, :3] / (2 * h)[:, None]
+            dF[:, 3:, l] = (fe - fg)[:, 3:] / (2 * h)[:, None]
+        P = np.tile(np.eye(6), (len(y), 1, 1))
+        P[:, :, 3:] -= 0.5 * dt * dF
+        d = np.linalg.solve(P, R[:, :, None])[:, :, 0]
+        coup = np.abs(0.5 * dt * np.einsum("nij,nj->ni", dF[:, :3], d[:, 3:]))
+        return zk - d, coup, np.abs(d[:, 3:])
+
+    zk = z0.copy()
+    for it in (1, 2):
+        p = O.push_params(a=a, dt=dt, scheme=O.IMR, B0pot=B0, max_iter=it, imr_newton=True,
+                          field_kind=O.FIELD_WALD, B0field=B0)
+        z = z0.copy()
+        O.push(p, z, qm, H0, D0, np.zeros(len(z)), np.ones(len(z), np.uint8))
+        zk, coup, du = newton_np(zk)
+        assert (np.abs(z[:, :3] - zk[:, :3]) <= 1e-3 * coup + 1e-15 * (np.abs(zk[:, :3]) + 1)).all(), it
+        assert (np.abs(z[:, 3:] - zk[:, 3:]) <= 1e-6 * du + 1e-15 * (np.abs(zk[:, 3:]) + 1)).all(), it
