@@ -38,6 +38,7 @@ HYB1_THR = 3.5e-6          # (d Htilde/dt)_max of the Hyb1 test
 FLOP_EVAL = 212
 FLOP_RK4_TRIAL = 4 * FLOP_EVAL + 79 + 56 + 5
 FLOP_IMR_ITER = FLOP_EVAL + 48
+FLOP_IMR_NEWTON = 125       # Newton form: the 3 x 3 momentum system and the position coupling per iteration
 FLOP_IMR_FINAL = 56         # H at the converged point (metric + Gamma + H)
 NOMINAL_FP64_GFLOPS = 1250.0
 # DRAM bytes (read + write) of one k_explicit<1> launch on this workload,
@@ -66,6 +67,8 @@ def parse():
                     help="corrector: restart a solve from the plain trial after this many iterations (0: never)")
     ap.add_argument("--train-gen-steps", type=int, default=10,
                     help="plain steps sampled for the training set")
+    ap.add_argument("--imr", choices=("fixed", "newton"), default="newton",
+                    help="IMR iteration of the headline push: the fixed-point update or the Newton form")
     ap.add_argument("--workload", default="push", choices=["push", "pic", "neutral", "batched", "clean", "inject", "adaptive", "charged_dg"])
     ap.add_argument("--clean-sweeps", type=int, default=500, help="Jacobi sweeps of --workload clean")
     ap.add_argument("--conserving", action="store_true", help="--workload pic with the charge-conserving deposit")
@@ -111,7 +114,7 @@ def dist_env():
 # ---------------------------------------------------------------------------
 
 def _oracle_chunk(args):
-    lo, hi, n_total, steps, seed = args
+    lo, hi, n_total, steps, seed, newton = args
     sys.path.insert(0, ROOT)
     import numpy as np
     import oracle as O
@@ -125,7 +128,7 @@ def _oracle_chunk(args):
     Hn = H0.copy()
     alive = np.ones(len(q), np.uint8)
     p = O.push_params(a=A_SPIN, dt=DT, scheme=O.HYB1, implicit_kind=O.IMR, thr=HYB1_THR, r_max=g.rn[-1],
-                      B0pot=B0, field_kind=O.FIELD_GRID)
+                      B0pot=B0, field_kind=O.FIELD_GRID, imr_newton=newton)
     t0 = time.perf_counter()
     ps = 0
     for _ in range(steps):
@@ -134,16 +137,17 @@ def _oracle_chunk(args):
     return ps, time.perf_counter() - t0
 
 
-def cpu_baseline(n, steps, pool=None, cores=None):
-    """Time the oracle on n particles x steps over all host cores."""
+def cpu_baseline(n, steps, pool=None, cores=None, newton=True):
+    """Time the oracle on n particles x steps over all host cores (the IMR
+    by the Newton or the fixed-point iteration, as the GPU arm)."""
     import multiprocessing as mp
     cores = cores or os.cpu_count() or 1
-    chunks = [(i * n // cores, (i + 1) * n // cores, n, steps, 2) for i in range(cores)]
+    chunks = [(i * n // cores, (i + 1) * n // cores, n, steps, 2, newton) for i in range(cores)]
     own = pool is None
     if own:
         pool = mp.get_context("spawn").Pool(cores)
     try:
-        pool.map(_oracle_chunk, [(0, 64, 64, 1, 2)] * cores)   # import + build in every worker
+        pool.map(_oracle_chunk, [(0, 64, 64, 1, 2, newton)] * cores)   # import + build in every worker
         res = pool.map(_oracle_chunk, chunks)
         wall = max(r[1] for r in res)      # the workers push concurrently; set-up is not timed
     finally:
@@ -156,7 +160,7 @@ def cpu_baseline(n, steps, pool=None, cores=None):
                      f"one spawn process per core)", "wall_s": round(wall, 3),
            "cpu_seconds": round(sum(r[1] for r in res), 1)}
     # the oracle as specified, on one core (a 1/cores share of the sample)
-    one = _oracle_chunk((0, n // cores, n, steps, 2))
+    one = _oracle_chunk((0, n // cores, n, steps, 2, newton))
     out["serial_one_core"] = {"value": one[0] / one[1], "unit": UNIT, "particles": n // cores}
     return out
 
@@ -263,7 +267,8 @@ def _timed(F, ctx, p, fields, prm, ev, steps, flush, learned=None):
         out["evals"] += st["n_rhs_evals"]
         out["notconv"] += st["n_notconv"]
         out["fl_ex"] += st["n_alive_before"] * FLOP_RK4_TRIAL
-        out["fl_im"] += st["n_iter_total"] * FLOP_IMR_ITER + st["n_implicit"] * FLOP_IMR_FINAL
+        it_fl = FLOP_IMR_ITER + (FLOP_IMR_NEWTON if prm.imr_newton else 0)
+        out["fl_im"] += st["n_iter_total"] * it_fl + st["n_implicit"] * FLOP_IMR_FINAL
         # the library's launches per step (static fields: no coefficient rebuild):
         # plain k_explicit (+ alive count), k_order, k_imr, k_imr_finish;
         # corrector + k_count_alive, k_mlp_correct4; skip form 9
@@ -304,14 +309,15 @@ def run_gpu(args, ws, rank, local):
     for e in ev:            # torch creates the CUDA event on its first record
         e.record()
     torch.cuda.synchronize()
+    newton = args.imr == "newton"
     prm = F.push_params(DT, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=HYB1_THR, r_max=float(g.rn[-1]),
-                        B0pot=B0, events=ev[1:5])
+                        B0pot=B0, events=ev[1:5], imr_newton=newton)
     for _ in range(args.warmup):
         F.fpic_push(ctx, p, fields, prm, stats=True)
     # launch shape of the implicit solver, timed on these particles (untimed here)
     from paper_2602_07452_gb300 import autotune
     prm_t = F.push_params(DT, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=HYB1_THR, r_max=float(g.rn[-1]),
-                          B0pot=B0)
+                          B0pot=B0, imr_newton=newton)
     tune_ms = autotune.tune_imr_blocks(ctx, p, fields, prm_t)
     learned = None
     train_info = None
@@ -320,7 +326,7 @@ def run_gpu(args, ws, rank, local):
         # the network learns from the plain pusher's own steps (untimed)
         from paper_2602_07452_gb300 import learned as L
         prm_plain = F.push_params(DT, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=HYB1_THR,
-                                  r_max=float(g.rn[-1]), B0pot=B0)
+                                  r_max=float(g.rn[-1]), B0pot=B0, imr_newton=newton)
         t0 = time.perf_counter()
         mode = F.FPIC_LEARN_CORRECT if args.learned_form == "correct" else F.FPIC_LEARN_SKIP
         cfg = L.fit_cfg(ctx, p, fields, prm_plain, p_skip=0.7, mode=mode, restart_after=args.learned_restart)
@@ -373,6 +379,17 @@ def run_gpu(args, ws, rank, local):
             lead["max_dH"] = _max_dH(F, ctx, p)
         F.fpic_set_tuning(ctx, F.FPIC_TUNE_IMR_BLOCKS_PER_SM, plain_bps)
         _restore(p, after_plain)
+    # the other IMR iteration from the same start state (same launch shape)
+    after_plain = _snapshot(p)
+    _restore(p, snap)
+    prm_o = F.push_params(DT, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=HYB1_THR, r_max=float(g.rn[-1]),
+                          B0pot=B0, events=ev[1:5], imr_newton=not newton)
+    F.fpic_push(ctx, p, fields, prm_o)
+    _restore(p, snap)
+    torch.cuda.synchronize()
+    other = _timed(F, ctx, p, fields, prm_o, ev, args.steps, flush)
+    other["max_dH"] = _max_dH(F, ctx, p)
+    _restore(p, after_plain)
     # max over ranks of the device time, sum of the work
     T, W = aggregate(plain["t_step"], plain["psteps"], device)
     # end to end through the host-buffer C ABI: H2D inputs + push + D2H result, every step
@@ -381,7 +398,7 @@ def run_gpu(args, ws, rank, local):
         getattr(hp, f).copy_(getattr(p, f).cpu())
     hp.alive.copy_(p.alive.cpu())
     prm_h = F.push_params(DT, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=HYB1_THR, r_max=float(g.rn[-1]),
-                          B0pot=B0)
+                          B0pot=B0, imr_newton=newton)
     e2e_steps = max(1, min(args.steps, 20))
     for _ in range(2):
         F.fpic_push_host(ctx, hp, fields, prm_h)
@@ -418,6 +435,7 @@ def run_gpu(args, ws, rank, local):
                    "grid": f"{NGRID}x{NGRID} (ln r, theta), r in [0.9 r_+, 50 M]",
                    "particles_per_gpu": args.n, "theta_T": THETA_T, "q_over_m": QM, "dt": DT,
                    "scheme": "Hyb1 RK4<->IMR (plain)", "hyb1_thr": HYB1_THR, "tol": 1e-14,
+                   "imr_iteration": "Newton (momentum columns of dF)" if newton else "fixed point (Eq. imr2)",
                    "implicit_fraction": plain["impl"] / psteps,
                    "mean_imr_iterations": plain["iters"] / max(plain["impl"], 1),
                    "rhs_evals_per_particle_step": plain["evals"] / psteps,
@@ -448,6 +466,15 @@ def run_gpu(args, ws, rank, local):
     line["config"]["explicit_ms_per_step"] = 1e3 * plain["t_ex"] / args.steps
     line["config"]["implicit_ms_per_step"] = 1e3 * plain["t_im"] / args.steps
     line["config"]["imr_not_converged"] = plain["notconv"]
+    po_ = max(other["psteps"], 1)
+    line["imr_other_iteration"] = {
+        "imr_iteration": "fixed point (Eq. imr2)" if newton else "Newton (momentum columns of dF)",
+        "value": other["psteps"] / other["t_step"], "unit": UNIT,
+        "ms_per_step": 1e3 * other["t_step"] / args.steps,
+        "implicit_ms_per_step": 1e3 * other["t_im"] / args.steps,
+        "mean_imr_iterations": other["iters"] / max(other["impl"], 1),
+        "rhs_evals_per_particle_step": other["evals"] / po_, "max_dH_over_D0": other["max_dH"],
+        "imr_not_converged": other["notconv"], "same_start_state_as_plain": True}
     if lrn is not None:
         lp = max(lrn["psteps"], 1)
         line["learned"] = {
@@ -911,11 +938,11 @@ def main():
         pool = mp.get_context("spawn").Pool(cores)
         try:
             for _ in range(args.warmup):
-                cpu_baseline(n, 1, pool, cores)
+                cpu_baseline(n, 1, pool, cores, args.imr == "newton")
             vals, walls = [], 0.0
             tot_ps = 0.0
             for _ in range(args.steps):
-                r = cpu_baseline(n, 1, pool, cores)
+                r = cpu_baseline(n, 1, pool, cores, args.imr == "newton")
                 vals.append(r["value"])
                 walls += r["wall_s"]
                 tot_ps += r["value"] * r["wall_s"]
@@ -1024,7 +1051,7 @@ def main():
     if rank == 0:
         if pool is not None:
             try:
-                line["cpu_baseline"] = cpu_baseline(1 << 20, args.cpu_steps, pool)
+                line["cpu_baseline"] = cpu_baseline(1 << 20, args.cpu_steps, pool, newton=args.imr == "newton")
             finally:
                 pool.close()
                 pool.join()

@@ -103,7 +103,14 @@ typedef struct {
  *               in canonical momenta pi_i = u_i + (q/m) A_i with the
  *               potentials of Eq. (Amu) and conserves H (with B0pot =
  *               B0field) and L exactly (an extension, not in the paper).
- *               0 = none.  Not with fields, the batched or the learned push. */
+ *               0 = none.  Not with fields, the batched or the learned push.
+ *   imr_newton: iteration of the IMR solve (Sec. 2.2.2).  0: the fixed-point
+ *               update of Eq. (imr2), z^[k] = z^n + dt F((z^n + z^[k-1])/2).
+ *               1: the Newton iteration the section names, with the Newton
+ *               matrix 1 - (dt/2) dF reduced to the momentum columns of dF
+ *               (d(dx/dt)/du and the magnetic force's d(du/dt)/du, both in
+ *               closed form); same fixed point and stop test, about half
+ *               the iterations for charged particles.  Any nonzero = 1. */
 typedef struct {
     double dt;
     int scheme;
@@ -119,6 +126,7 @@ typedef struct {
     double dt_implicit;
     double *t;
     double B0field;
+    int imr_newton;
 } fpic_push_params;
 
 /* Host-side counters of one push (filled only when a pointer is passed;

@@ -252,12 +252,25 @@ __device__ __forceinline__ void gather_c(const GridDev& G, const FieldsC& F, dou
     B[0] = v[3]; B[1] = v[4]; B[2] = v[5];
 }
 
+// What the Newton form of the implicit-midpoint solve needs from one
+// right-hand side: u^i = g^ij u_j, 1 / Gamma, alpha / Gamma, g^ij, the
+// magnetic-force factor qm alpha sqrt(gamma) / Gamma (0 without a field),
+// B^i and u x B.
+struct RhsJ {
+    double U[3], iG, aiG;
+    double gurr, gurp, gutt, gupp;
+    double ks;
+    double B[3], cx[3];
+};
+
 // Equations of motion at y (Eqs. p1, p2, O1, O2) and, as a by-product, the
 // Hamiltonian H(y) = alpha Gamma - beta u_r - (q/m) A_0 (Eq. Ham with the
 // Wald A_0 when B0pot != 0).  D, B: FIDO fields at y (ignored if !em).
-__device__ __forceinline__ void eval_rhs_sc(const BH& bh, const double y[6], double s, double c, double qm,
-                                            bool em, const double D[3], const double B[3], double B0pot,
-                                            double f[6], double& H)
+// JAC: also fill *J (RhsJ) for the Newton iteration.
+template <bool JAC>
+__device__ __forceinline__ void eval_rhs_sc_t(const BH& bh, const double y[6], double s, double c, double qm,
+                                              bool em, const double D[3], const double B[3], double B0pot,
+                                              double f[6], double& H, RhsJ* J)
 {
     Geo g;
     geo_eval(bh, y[0], s, c, g);
@@ -289,6 +302,12 @@ __device__ __forceinline__ void eval_rhs_sc(const BH& bh, const double y[6], dou
     f[3] = fma(h, fma(W, d.tt[0], upup * d.pp[0]), d.xi[0] * kap);
     f[4] = fma(h, fma(W, d.tt[1], fma(upup, d.pp[1], urur * d.q * g.irho2)), d.xi[1] * kap);
     f[5] = 0.0;
+    if (JAC) {
+        J->U[0] = Ur; J->U[1] = Ut; J->U[2] = Up;
+        J->iG = iG; J->aiG = aiG;
+        J->gurr = g.gurr; J->gurp = g.gurp; J->gutt = g.gutt; J->gupp = g.gupp;
+        J->ks = 0.0;
+    }
     if (em) {
         const double k = qm * g.alpha;
         const double ks = (qm * g.rho2) * (g.s * iG);    // k sqrt(gamma) / Gamma, alpha^2 xi = 1
@@ -298,12 +317,24 @@ __device__ __forceinline__ void eval_rhs_sc(const BH& bh, const double y[6], dou
         f[3] = fma(k, fma(g.grr, D[0], g.grp * D[2]), fma(ks, cr, f[3]));
         f[4] = fma(k, g.gtt * D[1], fma(ks, ct, f[4]));
         f[5] = fma(k, fma(g.grp, D[0], g.gpp * D[2]), ks * cp);
+        if (JAC) {
+            J->ks = ks;
+            J->B[0] = B[0]; J->B[1] = B[1]; J->B[2] = B[2];
+            J->cx[0] = cr; J->cx[1] = ct; J->cx[2] = cp;
+        }
     }
     H = fma(g.alpha, G, -g.beta * ur);
     if (B0pot != 0.0 && qm != 0.0) {
         // A_0 = B0 a r (1 + cos^2 th) / rho^2   (Sec. 3.1.3)
         H = fma(-qm * B0pot * bh.a * y[0], (1.0 + c * c) * g.irho2, H);
     }
+}
+
+__device__ __forceinline__ void eval_rhs_sc(const BH& bh, const double y[6], double s, double c, double qm,
+                                            bool em, const double D[3], const double B[3], double B0pot,
+                                            double f[6], double& H)
+{
+    eval_rhs_sc_t<false>(bh, y, s, c, qm, em, D, B, B0pot, f, H, nullptr);
 }
 
 __device__ __forceinline__ void eval_rhs(const BH& bh, const double y[6], double qm, bool em,

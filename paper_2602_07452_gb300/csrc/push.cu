@@ -48,6 +48,7 @@ struct PushK {
     int nruns;
     double dt, thr, tol, dg_eps;
     double dt_imp;          // step of the implicit solves (the hybrid's partner: fpic_push_params.dt_implicit)
+    int imr_newton;         // IMR iteration: Newton form (fpic_push_params.imr_newton)
     double* t;              // nullable per-particle time, advanced by the step each particle took
     // particle arrays in host memory (read over the link): the implicit pass
     // works from device copies by queue slot of z^n and q/m (7 x n) and of
@@ -127,8 +128,9 @@ __device__ __forceinline__ void F_at(const RunK& R, const double y[6], double qm
 }
 
 // Same, with sin/cos of y[1] supplied (from sincos_near).
+template <bool JAC = false>
 __device__ __forceinline__ void F_at_sc(const RunK& R, const double y[6], double s, double c, double qm, bool em,
-                                        double f[6], double& H)
+                                        double f[6], double& H, RhsJ* J = nullptr)
 {
     double D[3] = {0, 0, 0}, B[3] = {0, 0, 0};
     if (em) {
@@ -136,7 +138,52 @@ __device__ __forceinline__ void F_at_sc(const RunK& R, const double y[6], double
         else if (R.has_coef) gather_c(R.G, R.FC, y[0], y[1], D, B);
         else gather(R.G, R.F, y[0], y[1], D, B);
     }
-    eval_rhs_sc(R.bh, y, s, c, qm, em, D, B, R.B0pot, f, H);
+    eval_rhs_sc_t<JAC>(R.bh, y, s, c, qm, em, D, B, R.B0pot, f, H, J);
+}
+
+// Newton form of the implicit-midpoint iteration (Sec. 2.2.2 names a Newton
+// scheme): with zp = z^n + h F(y) the fixed-point update at the midpoint y
+// of z^n and the current iterate zk, the Newton matrix 1 - (h/2) dF keeps
+// the momentum columns of dF,
+//   A_il = d(dx^i/dt)/du_l = (alpha / Gamma) (g^il - u^i u^l / Gamma^2),
+//   J_il = d(du_i/dt)/du_l = ks ((g^{.l} x B)_i - (u x B)_i u^l / Gamma^2)
+// (the magnetic force; ks = qm alpha sqrt(gamma) / Gamma), and the step is
+//   (1 - (h/2) J) du = u_k - u_p,  u_new = u_k - du,  x_new = x_p - (h/2) A du.
+// The 3 x 3 system is solved by Cramer's rule.  Same fixed point as the
+// plain update, fewer iterations where the gyration dominates.
+__device__ __forceinline__ void newton_update(const RhsJ& J, double hh, const double zk[6], double zn[6])
+{
+    const double w = hh * J.ks;
+    const double wB0 = w * J.B[0], wB1 = w * J.B[1], wB2 = w * J.B[2];
+    const double w2 = w * (J.iG * J.iG);
+    const double c0 = w2 * J.cx[0], c1 = w2 * J.cx[1], c2 = w2 * J.cx[2];
+    // M = 1 - w X + w2 (u x B) u^T, X's columns g^{.l} x B
+    const double m00 = fma(c0, J.U[0], fma(J.gurp, wB1, 1.0));
+    const double m01 = fma(c0, J.U[1], -J.gutt * wB2);
+    const double m02 = fma(c0, J.U[2], J.gupp * wB1);
+    const double m10 = fma(c1, J.U[0], fma(J.gurr, wB2, -J.gurp * wB0));
+    const double m11 = fma(c1, J.U[1], 1.0);
+    const double m12 = fma(c1, J.U[2], fma(J.gurp, wB2, -J.gupp * wB0));
+    const double m20 = fma(c2, J.U[0], -J.gurr * wB1);
+    const double m21 = fma(c2, J.U[1], J.gutt * wB0);
+    const double m22 = fma(c2, J.U[2], fma(-J.gurp, wB1, 1.0));
+    const double b0 = zk[3] - zn[3], b1 = zk[4] - zn[4], b2 = zk[5] - zn[5];
+    const double a00 = fma(m11, m22, -m12 * m21), a01 = fma(m02, m21, -m01 * m22), a02 = fma(m01, m12, -m02 * m11);
+    const double a10 = fma(m12, m20, -m10 * m22), a11 = fma(m00, m22, -m02 * m20), a12 = fma(m02, m10, -m00 * m12);
+    const double a20 = fma(m10, m21, -m11 * m20), a21 = fma(m01, m20, -m00 * m21), a22 = fma(m00, m11, -m01 * m10);
+    const double idet = rcp_nr(fma(m00, a00, fma(m01, a10, m02 * a20)));
+    const double d0 = idet * fma(a00, b0, fma(a01, b1, a02 * b2));
+    const double d1 = idet * fma(a10, b0, fma(a11, b1, a12 * b2));
+    const double d2 = idet * fma(a20, b0, fma(a21, b1, a22 * b2));
+    zn[3] = zk[3] - d0;
+    zn[4] = zk[4] - d1;
+    zn[5] = zk[5] - d2;
+    // A du = (alpha / Gamma) (g^-1 du - u (u . du) / Gamma^2)
+    const double ud = fma(J.U[0], d0, fma(J.U[1], d1, J.U[2] * d2)) * (J.iG * J.iG);
+    const double ha = hh * J.aiG;
+    zn[0] = fma(-ha, fma(J.gurr, d0, fma(J.gurp, d2, -J.U[0] * ud)), zn[0]);
+    zn[1] = fma(-ha, fma(J.gutt, d1, -J.U[1] * ud), zn[1]);
+    zn[2] = fma(-ha, fma(J.gurp, d0, fma(J.gupp, d2, -J.U[2] * ud)), zn[2]);
 }
 
 // Particle boundaries (Sec. 2.5) and write-back of a finished step.
@@ -365,7 +412,8 @@ __global__ void k_order(PushK k)
 }
 
 // Persistent lane-refilling implicit-midpoint solver (Sec. 2.2.2):
-// z^[k] = z^n + dt F((z^n + z^[k-1]) / 2) until two iterates agree to tol.
+// z^[k] = z^n + dt F((z^n + z^[k-1]) / 2) until two iterates agree to tol;
+// NEWTON: the Newton form of the same iteration (newton_update).
 // all_mode: the queue is every particle (pure IMR, guess z^n); otherwise
 // entries come from k_explicit with their trial and sin/cos of th^n (sc0).
 // Each loop trip is one right-hand side per lane; a lane whose solve ends
@@ -376,8 +424,8 @@ __global__ void k_order(PushK k)
 // corrected guess of the queue slot (stg); with k.restart_after > 0, a solve
 // that has not converged after that many iterations from it restarts once,
 // with the full max_iter budget, from the trial in stg.
-template <int RESTART, bool BATCHED = false>
-__global__ void __launch_bounds__(128, 4) k_imr(const __grid_constant__ PushK k, int all_mode)
+template <int RESTART, bool BATCHED = false, bool NEWTON = false>
+__global__ void __launch_bounds__(128, NEWTON ? 3 : 4) k_imr(const __grid_constant__ PushK k, int all_mode)
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -452,11 +500,13 @@ __global__ void __launch_bounds__(128, 4) k_imr(const __grid_constant__ PushK k,
             for (int i = 0; i < 6; ++i) y[i] = 0.5 * (z0[i] + zk[i]);
             double sy, cy;
             sincos_near(z0[1], s0, c0, y[1], sy, cy);
-            F_at_sc(*R, y, sy, cy, qm, em, f, H);
+            RhsJ J;
+            F_at_sc<NEWTON>(*R, y, sy, cy, qm, em, f, H, &J);
             ++n_ev;
             double zn[6];
 #pragma unroll
             for (int i = 0; i < 6; ++i) zn[i] = fma(k.dt_imp, f[i], z0[i]);
+            if (NEWTON) newton_update(J, 0.5 * k.dt_imp, zk, zn);
             const bool ok = conv6(zn, zk, k.tol);
 #pragma unroll
             for (int i = 0; i < 6; ++i) zk[i] = zn[i];
@@ -504,6 +554,14 @@ __global__ void __launch_bounds__(128, 4) k_imr(const __grid_constant__ PushK k,
     warp_add(&k.cnt[CNT_ITERS], n_it, FULL);
     warp_add(&k.cnt[CNT_NOTCONV], n_nc, FULL);
     warp_add(&k.cnt[CNT_EVALS], n_ev, FULL);
+}
+
+// Launch k_imr in the iteration form the push asked for (k.imr_newton).
+template <int RESTART, bool BATCHED = false>
+static void launch_imr(unsigned grid, unsigned block, cudaStream_t s, const PushK& k, int all_mode)
+{
+    if (k.imr_newton) k_imr<RESTART, BATCHED, true><<<grid, block, 0, s>>>(k, all_mode);
+    else k_imr<RESTART, BATCHED, false><<<grid, block, 0, s>>>(k, all_mode);
 }
 
 // After k_imr: H at each converged implicit step (sin/cos of th^{n+1} by
@@ -1066,6 +1124,7 @@ static int push_core(fpic_ctx* c, fpic_particles* p, const double* const fields[
     for (int i = 0; i < 6; ++i) k.run.F.f[i] = has_fields ? fields[i] : nullptr;
     k.dt = prm->dt;
     k.dt_imp = implicit_step(prm);
+    k.imr_newton = prm->imr_newton ? 1 : 0;
     k.t = prm->t;
     k.thr = prm->thr;
     k.tol = prm->tol;
@@ -1139,14 +1198,14 @@ static int push_core(fpic_ctx* c, fpic_particles* p, const double* const fields[
         FPIC_CUDA(cudaEventRecord(ev[2], s));
     }
     if (prm->scheme == FPIC_IMR) {
-        k_imr<0><<<imr_grid, TB, 0, s>>>(k, 1);
+        launch_imr<0>(imr_grid, TB, s, k, 1);
         k_imr_finish<><<<persist, 256, 0, s>>>(k, 1);
     } else if (prm->scheme == FPIC_HAM) {
         if (k.run.B0field != 0.0) k_dg_em<<<nbx, TBx, 0, s>>>(k, 1);
         else k_dg<<<nbx, TBx, 0, s>>>(k, 1);
     } else if (prm->scheme >= FPIC_HYB1 && prm->implicit == FPIC_IMR) {
         k_order<<<persist, 256, 0, s>>>(k);
-        k_imr<0><<<imr_grid, TB, 0, s>>>(k, 0);
+        launch_imr<0>(imr_grid, TB, s, k, 0);
         k_imr_finish<><<<persist, 256, 0, s>>>(k, 0);
     } else if (prm->scheme >= FPIC_HYB1) {
         if (k.run.B0field != 0.0) k_dg_em<<<nbx, TBx, 0, s>>>(k, 0);
@@ -1338,6 +1397,7 @@ extern "C" int fpic_push_noalloc(double M, double a, fpic_particles* p, const fp
     k.run.has_fields = 0;
     k.dt = prm->dt;
     k.dt_imp = implicit_step(prm);
+    k.imr_newton = prm->imr_newton ? 1 : 0;
     k.t = prm->t;
     k.thr = prm->thr;
     k.tol = prm->tol;
@@ -1376,14 +1436,14 @@ extern "C" int fpic_push_noalloc(double M, double a, fpic_particles* p, const fp
         FPIC_CUDA(cudaEventRecord(ev[2], s));
     }
     if (prm->scheme == FPIC_IMR) {
-        k_imr<0><<<persist / 2, TB, 0, s>>>(k, 1);
+        launch_imr<0>(persist / 2, TB, s, k, 1);
         k_imr_finish<><<<persist, 256, 0, s>>>(k, 1);
     } else if (prm->scheme == FPIC_HAM) {
         if (k.run.B0field != 0.0) k_dg_em<<<nb, TB, 0, s>>>(k, 1);
         else k_dg<<<nb, TB, 0, s>>>(k, 1);
     } else if (prm->scheme >= FPIC_HYB1 && prm->implicit == FPIC_IMR) {
         k_order<<<persist, 256, 0, s>>>(k);
-        k_imr<0><<<persist / 2, TB, 0, s>>>(k, 0);
+        launch_imr<0>(persist / 2, TB, s, k, 0);
         k_imr_finish<><<<persist, 256, 0, s>>>(k, 0);
     } else if (prm->scheme >= FPIC_HYB1) {
         if (k.run.B0field != 0.0) k_dg_em<<<nb, TB, 0, s>>>(k, 0);
@@ -1541,6 +1601,7 @@ static void fill_pushk(PushK& k, fpic_ctx* c, fpic_particles* p, const double* c
     for (int i = 0; i < 6; ++i) k.run.F.f[i] = fields ? fields[i] : nullptr;
     k.dt = prm->dt;
     k.dt_imp = prm->dt;
+    k.imr_newton = prm->imr_newton ? 1 : 0;
     k.t = nullptr;
     k.thr = prm->thr;
     k.tol = prm->tol;
@@ -1828,7 +1889,7 @@ extern "C" int fpic_learn_sample(fpic_ctx* c, fpic_particles* p, const double* c
         k.order = nullptr;
         k_explicit<2><<<nb, 128, 0, s>>>(k);
         k_trial_feat<<<(unsigned)c->sm_count * 8u, 256, 0, s>>>(k);
-        k_imr<0><<<(unsigned)c->sm_count * (unsigned)c->imr_blocks_per_sm, 128, 0, s>>>(k, 0);
+        launch_imr<0>((unsigned)c->sm_count * (unsigned)c->imr_blocks_per_sm, 128, s, k, 0);
         FPIC_CUDA(cudaGetLastError());
         return FPIC_OK;
     }
@@ -1839,7 +1900,7 @@ extern "C" int fpic_learn_sample(fpic_ctx* c, fpic_particles* p, const double* c
     f.S = S;
     k_features<<<nb, 128, 0, s>>>(f);
     k_explicit<1><<<nb, 128, 0, s>>>(k);
-    k_imr<0><<<(unsigned)c->sm_count * (unsigned)c->imr_blocks_per_sm, 128, 0, s>>>(k, 0);
+    launch_imr<0>((unsigned)c->sm_count * (unsigned)c->imr_blocks_per_sm, 128, s, k, 0);
     FPIC_CUDA(cudaGetLastError());
     return FPIC_OK;
 }
@@ -1920,8 +1981,8 @@ extern "C" int fpic_push_learned(fpic_ctx* c, fpic_mlp* m, fpic_particles* p, co
     }
     const unsigned imr_grid = (unsigned)c->sm_count * (unsigned)c->imr_blocks_per_sm;
     k_order<<<persist, 256, 0, s>>>(k);
-    if (correct) k_imr<1><<<imr_grid, 128, 0, s>>>(k, 0);
-    else k_imr<0><<<imr_grid, 128, 0, s>>>(k, 0);
+    if (correct) launch_imr<1>(imr_grid, 128, s, k, 0);
+    else launch_imr<0>(imr_grid, 128, s, k, 0);
     k_imr_finish<><<<persist, 256, 0, s>>>(k, 0);
     if (ev) FPIC_CUDA(cudaEventRecord(ev[3], s));
     FPIC_CUDA(cudaGetLastError());
@@ -2032,6 +2093,7 @@ extern "C" int fpic_push_batched(const fpic_run* runs, int nruns, fpic_particles
     k.nruns = nruns;
     k.dt = prm->dt;
     k.dt_imp = implicit_step(prm);
+    k.imr_newton = prm->imr_newton ? 1 : 0;
     k.t = prm->t;
     k.thr = prm->thr;
     k.tol = prm->tol;
@@ -2064,11 +2126,11 @@ extern "C" int fpic_push_batched(const fpic_run* runs, int nruns, fpic_particles
         FPIC_CUDA(cudaEventRecord(ev[2], s));
     }
     if (prm->scheme == FPIC_IMR) {
-        k_imr<0, true><<<imr_grid, 128, 0, s>>>(k, 1);
+        launch_imr<0, true>(imr_grid, 128, s, k, 1);
         k_imr_finish<true><<<persist, 256, 0, s>>>(k, 1);
     } else if (prm->scheme >= FPIC_HYB1) {
         k_order<<<persist, 256, 0, s>>>(k);
-        k_imr<0, true><<<imr_grid, 128, 0, s>>>(k, 0);
+        launch_imr<0, true>(imr_grid, 128, s, k, 0);
         k_imr_finish<true><<<persist, 256, 0, s>>>(k, 0);
     }
     if (ev) FPIC_CUDA(cudaEventRecord(ev[3], s));

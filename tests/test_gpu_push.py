@@ -97,7 +97,7 @@ def test_seeding_matches_oracle(F):
 
 
 def _one_step(F, ctx, g, Fo, z, q, scheme, dt, thr=1e-12, implicit=None, B0pot=1.0, r_max=None,
-              max_iter=50, alive=None, tol=1e-14, dt_imp=0.0, t=None):
+              max_iter=50, alive=None, tol=1e-14, dt_imp=0.0, t=None, newton=False):
     n = z.shape[0]
     H0, _, D0 = O.hamiltonian(1.0, _A[id(ctx)], B0pot, z, q)
     Hn = H0 * (1.0 + 1e-9 * np.cos(np.arange(n)))
@@ -106,10 +106,10 @@ def _one_step(F, ctx, g, Fo, z, q, scheme, dt, thr=1e-12, implicit=None, B0pot=1
     alive = np.ones(n, np.uint8) if alive is None else alive
     p = make_particles(z, q, H0, D0, Hn, alive)
     prm = F.push_params(dt, scheme=scheme, implicit=implicit, thr=thr, tol=tol, max_iter=max_iter,
-                        r_max=r_max, B0pot=B0pot, dt_implicit=dt_imp, t=t)
+                        r_max=r_max, B0pot=B0pot, dt_implicit=dt_imp, t=t, imr_newton=newton)
     st = F.fpic_push(ctx, p, fields_dev(Fo) if Fo is not None else None, prm, stats=True)
     po = O.push_params(a=_A[id(ctx)], dt=dt, scheme=scheme, implicit_kind=implicit, thr=thr, tol=tol,
-                       max_iter=max_iter, r_max=r_max, B0pot=B0pot, dt_imp=dt_imp,
+                       max_iter=max_iter, r_max=r_max, B0pot=B0pot, dt_imp=dt_imp, imr_newton=newton,
                        field_kind=O.FIELD_GRID if Fo is not None else O.FIELD_NONE)
     zo = np.ascontiguousarray(z.copy()); Ho = Hn.copy(); ao = alive.copy()
     nc, so, io = O.push(po, zo, q, H0, D0, Ho, ao, g, Fo)
@@ -125,10 +125,13 @@ def _mk(F, a, g=None):
     return ctx
 
 
-@pytest.mark.parametrize("scheme", ["RK4", "IMR", "HYB1", "HYB2"])
-def test_charged_push_one_step_matches_oracle(F, scheme):
+@pytest.mark.parametrize("scheme,newton", [("RK4", False), ("IMR", False), ("HYB1", False), ("HYB2", False),
+                                           ("IMR", True), ("HYB1", True), ("HYB2", True)])
+def test_charged_push_one_step_matches_oracle(F, scheme, newton):
     """Wald field on a 128 x 128 (ln r, th) grid, e-/e+ q/m = -/+100,
-    4741 particles (37 blocks of 128 plus a ragged tail), dt = 1e-3."""
+    4741 particles (37 blocks of 128 plus a ragged tail), dt = 1e-3; the
+    IMR solved by the fixed-point update or by the Newton iteration
+    (imr_newton) on both sides."""
     a = 0.9
     g = I.wald_grid(128, a)
     Fo = O.wald_on_grid(a, 1.0, g)
@@ -136,9 +139,12 @@ def test_charged_push_one_step_matches_oracle(F, scheme):
     d, z, q = thermal_state(4741, g, a, theta=0.1, seed=11)
     sch = getattr(F, "FPIC_" + scheme)
     thr = {"HYB1": 8e-5, "HYB2": 8e-8}.get(scheme, 1e-12)
-    p, st, (zo, Ho, ao, so, io, nc), (H0, D0, Hn) = _one_step(F, ctx, g, Fo, z, q, sch, 1e-3, thr=thr)
+    p, st, (zo, Ho, ao, so, io, nc), (H0, D0, Hn) = _one_step(F, ctx, g, Fo, z, q, sch, 1e-3, thr=thr,
+                                                             newton=newton)
     zg, Hg, ag, sg, ig, cg = to_np(p)
     assert np.array_equal(ag, ao)
+    if newton:
+        assert io[so == 1].mean() < 6.0
     if scheme.startswith("HYB"):
         # exclude particles whose test statistic lies within 1e-12 of the threshold
         pr = O.push_params(a=a, dt=1e-3, scheme=O.RK4, B0pot=1.0, field_kind=O.FIELD_GRID, r_max=g.rn[-1])
@@ -260,10 +266,12 @@ def test_invalid_arguments_raise(F):
         F.fpic_cell_index(ctx, p)   # no grid
 
 
-def test_full_size_charged_workload_sampled(F):
+@pytest.mark.parametrize("newton", [False, True])
+def test_full_size_charged_workload_sampled(F, newton):
     """Charged Wald workload at full size (512 x 512 grid, 2^20 particles,
     hybrid RK4 <-> IMR, dt = 1e-3) in the launch configuration the benchmark
-    times; 3000 sampled particles are recomputed by the oracle."""
+    times (IMR by the fixed-point update and by the Newton iteration); 3000
+    sampled particles are recomputed by the oracle."""
     a = 0.9
     n = 1 << 20
     g = I.wald_grid(512, a)
@@ -278,22 +286,24 @@ def test_full_size_charged_workload_sampled(F):
     z0 = p.state().cpu().numpy()[idx]
     H0 = p.H0.cpu().numpy()[idx]; D0 = p.D0.cpu().numpy()[idx]; Hn = p.Hn.cpu().numpy()[idx]
     thr = 5e-6
-    prm = F.push_params(1e-3, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=thr, r_max=g.rn[-1], B0pot=1.0)
+    prm = F.push_params(1e-3, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=thr, r_max=g.rn[-1], B0pot=1.0,
+                        imr_newton=newton)
     st = F.fpic_push(ctx, p, Fg, prm, stats=True)
     zg, Hg, ag, sg, ig, cg = to_np(p)
     Fo = [f.cpu().numpy() for f in Fg]
     po = O.push_params(a=a, dt=1e-3, scheme=O.HYB1, implicit_kind=O.IMR, thr=thr, r_max=g.rn[-1],
-                       B0pot=1.0, field_kind=O.FIELD_GRID)
+                       B0pot=1.0, field_kind=O.FIELD_GRID, imr_newton=newton)
     zo = np.ascontiguousarray(z0.copy()); Ho = Hn.copy(); ao = np.ones(len(idx), np.uint8)
     O.push(po, zo, q[idx], H0, D0, Ho, ao, g, Fo)
     assert_state_close(zg[idx], zo, TOL)
     assert st["n_alive_before"] == n
 
 
-def test_imr_launch_shape_changes_no_result():
+@pytest.mark.parametrize("newton", [False, True])
+def test_imr_launch_shape_changes_no_result(newton):
     """FPIC_TUNE_IMR_BLOCKS_PER_SM only reshapes the persistent implicit
     launch: every particle's step is bitwise the same for 1 and 4 resident
-    blocks per SM; out-of-range values are rejected."""
+    blocks per SM (either IMR iteration); out-of-range values are rejected."""
     cuda_or_skip()
     F = fpic()
     a = 0.9
@@ -304,7 +314,7 @@ def test_imr_launch_shape_changes_no_result():
     d, z, q = thermal_state(20000, g, a, theta=0.1, seed=12)
     H0, _, D0 = O.hamiltonian(1.0, a, 1.0, z, q)
     prm = F.push_params(1e-3, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=8e-5, r_max=float(g.rn[-1]),
-                        B0pot=1.0)
+                        B0pot=1.0, imr_newton=newton)
     outs = []
     for v in (1, 4):
         F.fpic_set_tuning(ctx, F.FPIC_TUNE_IMR_BLOCKS_PER_SM, v)
@@ -436,7 +446,7 @@ def test_adaptive_step_dg_partner_matches_oracle(F):
     assert np.abs(Hg[imp] - H0[imp]).max() < 2e-14
 
 
-@pytest.mark.parametrize("scheme", ["RK4", "IMR", "HAM", "HYB2"])
+@pytest.mark.parametrize("scheme", ["RK4", "IMR", "IMR_NEWTON", "HAM", "HYB2"])
 def test_analytic_wald_push_matches_oracle(F, scheme):
     """Charged particles in the analytic Wald field (fields = NULL, B0field):
     RK4 / IMR / the discrete-gradient scheme in canonical momenta (an
@@ -453,6 +463,8 @@ def test_analytic_wald_push_matches_oracle(F, scheme):
     q = np.choose(np.arange(n) % 3, [np.full(n, -2.0), np.full(n, 2.0), np.zeros(n)])
     H0, _, D0 = O.hamiltonian(1.0, a, B0, z, q)
     Hn = H0.copy()
+    newton = scheme == "IMR_NEWTON"
+    scheme = "IMR" if newton else scheme
     sch = getattr(F, "FPIC_" + scheme)
     thr = 1e-12
     if scheme == "HYB2":
@@ -463,10 +475,10 @@ def test_analytic_wald_push_matches_oracle(F, scheme):
         thr = float(np.median(stat))
     p = make_particles(z, q, H0, D0, Hn)
     prm = F.push_params(dt, scheme=sch, implicit=F.FPIC_HAM, thr=thr, tol=1e-15, max_iter=100, B0pot=B0,
-                        B0field=B0)
+                        B0field=B0, imr_newton=newton)
     F.fpic_push(ctx, p, None, prm)
     po = O.push_params(a=a, dt=dt, scheme=sch, implicit_kind=O.HAM, thr=thr, tol=1e-15, max_iter=100, B0pot=B0,
-                       field_kind=O.FIELD_WALD, B0field=B0)
+                       field_kind=O.FIELD_WALD, B0field=B0, imr_newton=newton)
     zo = np.ascontiguousarray(z.copy()); Ho = Hn.copy(); ao = np.ones(n, np.uint8)
     nc, so, io = O.push(po, zo, q, H0, D0, Ho, ao)
     zg, Hg, ag, sg, ig, cg = to_np(p)
