@@ -306,7 +306,10 @@ __device__ __forceinline__ void eval_rhs_sc_t(const BH& bh, const double y[6], d
         J->U[0] = Ur; J->U[1] = Ut; J->U[2] = Up;
         J->iG = iG; J->aiG = aiG;
         J->gurr = g.gurr; J->gurp = g.gurp; J->gutt = g.gutt; J->gupp = g.gupp;
+        // no field: the force terms of the Newton matrix vanish (set, not left undefined)
         J->ks = 0.0;
+        J->B[0] = J->B[1] = J->B[2] = 0.0;
+        J->cx[0] = J->cx[1] = J->cx[2] = 0.0;
     }
     if (em) {
         const double k = qm * g.alpha;
