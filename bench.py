@@ -243,10 +243,11 @@ def _restore(p, snap):
 
 def _timed(F, ctx, p, fields, prm, ev, steps, flush, learned=None):
     """K steps, each bracketed by CUDA events on the launch stream; returns a
-    dict of device times, work and algorithmic flops."""
+    dict of device times, work and algorithmic flops, and (untimed) the mask
+    of particles with an implicit solve that reached max_iter."""
     import torch
     out = dict(t_step=0.0, t_ex=0.0, t_inf=0.0, t_im=0.0, psteps=0, notconv=0, impl=0, iters=0, evals=0, fl_ex=0.0, fl_im=0.0,
-               launches=0)
+               launches=0, ncmask=torch.zeros(p.n, dtype=torch.bool, device=p.r.device))
     for k in range(steps):
         flush.fill_(k & 255)
         ev[0].record()
@@ -258,6 +259,7 @@ def _timed(F, ctx, p, fields, prm, ev, steps, flush, learned=None):
         ev[5].record()
         torch.cuda.synchronize()
         out["t_step"] += ev[0].elapsed_time(ev[5]) * 1e-3
+        out["ncmask"] |= (p.scheme == 1) & (p.iters >= prm.max_iter)
         out["t_ex"] += ev[1].elapsed_time(ev[2]) * 1e-3
         out["t_inf"] += ev[2].elapsed_time(ev[3]) * 1e-3
         out["t_im"] += ev[3].elapsed_time(ev[4]) * 1e-3
@@ -276,10 +278,11 @@ def _timed(F, ctx, p, fields, prm, ev, steps, flush, learned=None):
     return out
 
 
-def _max_dH(F, ctx, p):
+def _max_dH(F, ctx, p, exclude=None):
+    """max |H - H0| / D0 over the alive particles (without those in exclude)."""
     H, _ = F.fpic_hamiltonian(ctx, p, B0pot=B0)
-    alive = p.alive.bool()
-    dH = ((H - p.H0).abs() / p.D0)[alive]
+    keep = p.alive.bool() if exclude is None else p.alive.bool() & ~exclude
+    dH = ((H - p.H0).abs() / p.D0)[keep]
     return float(dH.max().item()) if dH.numel() else 0.0
 
 
@@ -361,6 +364,7 @@ def run_gpu(args, ws, rank, local):
         dist.barrier()
     clk = clocks.stop()
     max_dH = _max_dH(F, ctx, p)
+    max_dH_conv = _max_dH(F, ctx, p, plain["ncmask"])
     lrn = lead = None
     if learned is not None:
         after_plain = _snapshot(p)
@@ -369,6 +373,7 @@ def run_gpu(args, ws, rank, local):
         F.fpic_set_tuning(ctx, F.FPIC_TUNE_IMR_BLOCKS_PER_SM, learned_bps)
         lrn = _timed(F, ctx, p, fields, prm, ev, args.steps, flush, learned)
         lrn["max_dH"] = _max_dH(F, ctx, p)
+        lrn["max_dH_conv"] = _max_dH(F, ctx, p, lrn["ncmask"])
         if learned[1].mode == F.FPIC_LEARN_CORRECT:
             # ablation: the same corrector with a zero network (leading-order gap only)
             net0 = F.MLP()
@@ -389,6 +394,7 @@ def run_gpu(args, ws, rank, local):
     torch.cuda.synchronize()
     other = _timed(F, ctx, p, fields, prm_o, ev, args.steps, flush)
     other["max_dH"] = _max_dH(F, ctx, p)
+    other["max_dH_conv"] = _max_dH(F, ctx, p, other["ncmask"])
     _restore(p, after_plain)
     # max over ranks of the device time, sum of the work
     T, W = aggregate(plain["t_step"], plain["psteps"], device)
@@ -439,7 +445,10 @@ def run_gpu(args, ws, rank, local):
                    "implicit_fraction": plain["impl"] / psteps,
                    "mean_imr_iterations": plain["iters"] / max(plain["impl"], 1),
                    "rhs_evals_per_particle_step": plain["evals"] / psteps,
-                   "max_dH_over_D0": max_dH, "parallelism": f"dp{ws} (independent particle sets)",
+                   "max_dH_over_D0": max_dH,
+                   "max_dH_over_D0_converged": max_dH_conv,
+                   "particles_with_unconverged_solve": int(plain["ncmask"].sum().item()),
+                   "parallelism": f"dp{ws} (independent particle sets)",
                    "l2": "256 MB buffer written between timed steps (outside the events)",
                    "imr_blocks_per_sm": F.fpic_get_tuning(ctx, F.FPIC_TUNE_IMR_BLOCKS_PER_SM),
                    "autotune_ms_per_push": {str(k): round(v, 4) for k, v in tune_ms.items()}},
@@ -474,6 +483,8 @@ def run_gpu(args, ws, rank, local):
         "implicit_ms_per_step": 1e3 * other["t_im"] / args.steps,
         "mean_imr_iterations": other["iters"] / max(other["impl"], 1),
         "rhs_evals_per_particle_step": other["evals"] / po_, "max_dH_over_D0": other["max_dH"],
+        "max_dH_over_D0_converged": other["max_dH_conv"],
+        "particles_with_unconverged_solve": int(other["ncmask"].sum().item()),
         "imr_not_converged": other["notconv"], "same_start_state_as_plain": True}
     if lrn is not None:
         lp = max(lrn["psteps"], 1)
@@ -483,6 +494,7 @@ def run_gpu(args, ws, rank, local):
             "ms_per_step": 1e3 * lrn["t_step"] / args.steps, "implicit_fraction": lrn["impl"] / lp,
             "mean_imr_iterations": lrn["iters"] / max(lrn["impl"], 1),
             "rhs_evals_per_particle_step": lrn["evals"] / lp, "max_dH_over_D0": lrn["max_dH"],
+            "max_dH_over_D0_converged": lrn["max_dH_conv"],
             "same_start_state_as_plain": True, "form": args.learned_form,
             "restart_after": args.learned_restart,
             "imr_blocks_per_sm": learned_bps,
