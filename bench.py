@@ -45,9 +45,10 @@ NOMINAL_FP64_GFLOPS = 1250.0
 # from one ncu capture of the current kernel (117.8 MB + 51.6 MB); the
 # algorithmic bytes are ~180 B per particle (189 MB for 2^20).
 TRAFFIC_K_EXPLICIT = 255.8e6   # ncu dram__bytes_read.sum + dram__bytes_write.sum, one 2^20 launch
-# deposit: FIDO velocity (41) + 3 sub-grids x (49 sqrt(gamma) points x 9 +
-# lattice 14 + four 16-point sums 128 + weights 16) + 2 th lattices (56) + shares (30)
-FLOP_DEPOSIT = 41 + 3 * (49 * 9 + 14 + 128 + 16) + 56 + 30
+# deposit: FIDO velocity (41) + 133 distinct sqrt(gamma) lattice points x 9
+# (3 sub-grids x 49, less the split column and row they share) + 3 sub-grids x
+# (lattice 14 + four 16-point sums 128 + weights 16) + 2 th lattices (56) + shares (30)
+FLOP_DEPOSIT = 41 + 133 * 9 + 3 * (14 + 128 + 16) + 56 + 30
 PIC_A, PIC_DT, PIC_W = 0.99, 5e-4, 1e-6
 
 

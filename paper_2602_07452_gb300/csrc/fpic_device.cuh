@@ -38,12 +38,20 @@ __device__ __forceinline__ double rcp_nr(double x)
 // (2^-39.6) against correctly rounded square roots, far inside the deposit's
 // 1e-10 bound.  Each particle's shares still sum to its charge to rounding:
 // they are ratios of the same subvolumes.
-__device__ __forceinline__ double sqrt_dep(double x)
+// sqrt2_dep returns 2 sqrt(x) in the same step written as g (3 - g y) with
+// g = x y: three FP64 operations after the estimate; the deposit only uses
+// ratios of sums of these values, so the factor 2 cancels.
+__device__ __forceinline__ double sqrt2_dep(double x)
 {
     double y;
     asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-    const double g = x * y, h = 0.5 * y;
-    return fma(g, fma(-g, h, 0.5), g);
+    const double g = x * y;
+    return g * fma(-g, y, 3.0);
+}
+
+__device__ __forceinline__ double sqrt_dep(double x)
+{
+    return 0.5 * sqrt2_dep(x);
 }
 
 // sin h and cos h - 1 for a step h inside one cell: Maclaurin series through

@@ -374,8 +374,15 @@ __device__ __forceinline__ void theta_lattice(double hc, double hd, double s0, d
 // B = X + 2 M x and A = a^2 cos^2 th, sqrt(gamma) = sin th sqrt((X + A)(B + A))
 // and the radicand is X B + A (X + B + A): two operations per point.  The
 // sin th factor is applied once per lattice row.
+// The three sub-grids of a particle share lattice lines: the split column
+// x = r of the (i, j) and (i+1/2, j) lattices (same th rows) and the split
+// row th = t of the (i, j) and (i, j+1/2) lattices (same r columns), when
+// neither split point was clamped.  col / row carry those 7 values: written
+// by every call, read instead of evaluated with COL_IN / ROW_IN.
+template <bool COL_IN = false, bool ROW_IN = false>
 __device__ __forceinline__ void subvolumes(const BH& bh, double x0, double x1, double r, double hc, double hd,
-                                           const double sy[7], const double cy[7], double V[4])
+                                           const double sy[7], const double cy[7], double V[4], double col[7],
+                                           double row[7])
 {
     const double third = 1.0 / 3.0;
     const double ha = (r - x0) * third, hb = (x1 - r) * third;
@@ -387,20 +394,31 @@ __device__ __forceinline__ void subvolumes(const BH& bh, double x0, double x1, d
         P[k] = X * B;
         Q[k] = X + B;
     }
+    // the lattice values are 2 sqrt(...) (sqrt2_dep): a common factor of the
+    // four subvolumes, which only enter as ratios
     double S00 = 0, S10 = 0, S01 = 0, S11 = 0;
 #pragma unroll
     for (int l = 0; l < 7; ++l) {
         const double A = bh.a2 * (cy[l] * cy[l]);
         double f[7];
 #pragma unroll
-        for (int k = 0; k < 7; ++k) f[k] = sqrt_dep(fma(A, Q[k] + A, P[k]));
-        // trapezoid weights 1/2, 1, 1, 1/2 along r on each half
-        const double ra = sy[l] * fma(0.5, f[0] + f[3], f[1] + f[2]);
-        const double rb = sy[l] * fma(0.5, f[3] + f[6], f[4] + f[5]);
-        const double wl = (l == 0 || l == 6) ? 0.5 : 1.0;
-        if (l < 3) { S00 = fma(wl, ra, S00); S10 = fma(wl, rb, S10); }
-        if (l == 3) { S00 = fma(0.5, ra, S00); S10 = fma(0.5, rb, S10); S01 = fma(0.5, ra, S01); S11 = fma(0.5, rb, S11); }
-        if (l > 3) { S01 = fma(wl, ra, S01); S11 = fma(wl, rb, S11); }
+        for (int k = 0; k < 7; ++k) {
+            if (ROW_IN && l == 3) f[k] = row[k];
+            else if (COL_IN && k == 3) f[k] = col[l];
+            else f[k] = sqrt2_dep(fma(A, Q[k] + A, P[k]));
+        }
+        if (!COL_IN) col[l] = f[3];
+        if (!ROW_IN && l == 3) {
+#pragma unroll
+            for (int k = 0; k < 7; ++k) row[k] = f[k];
+        }
+        // trapezoid weights 1/2, 1, 1, 1/2 along r on each half; the row's
+        // th weight (1/2 at the ends and the split row) times sin th
+        const double ra = fma(0.5, f[0] + f[3], f[1] + f[2]);
+        const double rb = fma(0.5, f[3] + f[6], f[4] + f[5]);
+        const double ws = (l == 0 || l == 3 || l == 6) ? 0.5 * sy[l] : sy[l];
+        if (l <= 3) { S00 = fma(ws, ra, S00); S10 = fma(ws, rb, S10); }
+        if (l >= 3) { S01 = fma(ws, ra, S01); S11 = fma(ws, rb, S11); }
     }
     V[0] = S00 * (ha * hc);
     V[1] = S10 * (hb * hc);
@@ -458,13 +476,15 @@ __global__ void __launch_bounds__(256) k_dep_particle(DepK k)
     const double* sh = k.trig + 2 * (G.Nth + 1);
     const double* ch = sh + G.Nth;
     const double third = 1.0 / 3.0;
-    double sy[7], cy[7], V[4];
+    double sy[7], cy[7], V[4], col[7], row[7];
     const long long n = k.n_alive;
+    // the split column / row are shared between the sub-grids unless clamped
+    const bool share = (rn_c == rh_c) && (tn_c == th_c);
     // (i, j): rho and j^ph
     const double y0 = G.tn[j0], y1 = G.tn[j0 + 1];
     double hc = (tn_c - y0) * third, hd = (y1 - tn_c) * third;
     theta_lattice(hc, hd, sn[j0], cn[j0], stn, ctn, sn[j0 + 1], cn[j0 + 1], sy, cy);
-    subvolumes(k.bh, G.rn[i0], G.rn[i0 + 1], rn_c, hc, hd, sy, cy, V);
+    subvolumes(k.bh, G.rn[i0], G.rn[i0 + 1], rn_c, hc, hd, sy, cy, V, col, row);
     double iV = rcp_nr(V[0] + V[1] + V[2] + V[3]);
     // share of node (i+a, j+b) = V(opposite corner) / V
     const double w00 = V[3] * iV, w10 = V[2] * iV, w01 = V[1] * iV, w11 = V[0] * iV;
@@ -472,7 +492,11 @@ __global__ void __launch_bounds__(256) k_dep_particle(DepK k)
     const double Qp = Q * vp;
     k.rec[4 * n + p] = Qp * w00; k.rec[5 * n + p] = Qp * w10; k.rec[6 * n + p] = Qp * w01; k.rec[7 * n + p] = Qp * w11;
     // (i+1/2, j): j^r  (same th lattice)
-    subvolumes(k.bh, G.rh[i1], G.rh[i1 + 1], rh_c, hc, hd, sy, cy, V);
+    {
+        double row_rh[7];   // this lattice's split row (r columns of the half grid): not shared
+        if (share) subvolumes<true, false>(k.bh, G.rh[i1], G.rh[i1 + 1], rh_c, hc, hd, sy, cy, V, col, row_rh);
+        else subvolumes(k.bh, G.rh[i1], G.rh[i1 + 1], rh_c, hc, hd, sy, cy, V, col, row_rh);
+    }
     iV = rcp_nr(V[0] + V[1] + V[2] + V[3]);
     const double Qr = Q * vr;
     k.rec[8 * n + p] = Qr * (V[3] * iV); k.rec[9 * n + p] = Qr * (V[2] * iV);
@@ -482,7 +506,8 @@ __global__ void __launch_bounds__(256) k_dep_particle(DepK k)
     hc = (th_c - z0) * third;
     hd = (z1 - th_c) * third;
     theta_lattice(hc, hd, sh[j1], ch[j1], sth, cth, sh[j1 + 1], ch[j1 + 1], sy, cy);
-    subvolumes(k.bh, G.rn[i0], G.rn[i0 + 1], rn_c, hc, hd, sy, cy, V);
+    if (share) subvolumes<false, true>(k.bh, G.rn[i0], G.rn[i0 + 1], rn_c, hc, hd, sy, cy, V, col, row);
+    else subvolumes(k.bh, G.rn[i0], G.rn[i0 + 1], rn_c, hc, hd, sy, cy, V, col, row);
     iV = rcp_nr(V[0] + V[1] + V[2] + V[3]);
     const double Qt = Q * vt;
     k.rec[12 * n + p] = Qt * (V[3] * iV); k.rec[13 * n + p] = Qt * (V[2] * iV);
