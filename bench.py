@@ -1052,7 +1052,7 @@ def main():
         import torch
         dev = torch.device("cuda", local)
         line["neutral"] = run_neutral(args, dev, 1 << 20, 20)
-        line["neutral_4096"] = run_neutral(args, dev, 4096, 20)
+        line["neutral_4096"] = run_neutral(args, dev, 4096, 2000, pre_steps=0)   # the 2000-step run, all timed
         line["neutral_dg_alone"] = run_neutral(args, dev, 1 << 20, 5, pre_steps=2, scheme="HAM")
         line["neutral_rk4_alone"] = run_neutral(args, dev, 1 << 20, 20, pre_steps=2, scheme="RK4")
         line["batched"] = run_batched(args, dev, 0.1, 5)
