@@ -603,7 +603,8 @@ def run_batched(args, device, scale, steps):
         specs.append((ctx, fl, off, off + m, float(g.rn[-1]), 0.0))
         off += m
     runs = F.make_runs(specs)
-    prm = F.push_params(DT, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=HYB1_THR)
+    prm = F.push_params(DT, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=HYB1_THR,
+                        imr_newton=args.imr == "newton")
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
         for _ in range(2):
@@ -728,7 +729,7 @@ def run_pic(args, device, grid_n, ppc, steps, rank=0, conserving=False, inject_e
     }
 
 
-def run_adaptive(device, n=1 << 20, steps=20, ratios=(1, 2, 4)):
+def run_adaptive(device, n=1 << 20, steps=20, ratios=(1, 2, 4), newton=True):
     """Adaptive per-scheme steps (Sec. 3.1.2, Tab. C.2) on the charged Wald
     workload: Hyb1 with dt = 1e-3 for the RK4 trials and dt_implicit =
     ratio x dt for the IMR steps, from the same start state.  Reports the
@@ -739,13 +740,13 @@ def run_adaptive(device, n=1 << 20, steps=20, ratios=(1, 2, 4)):
     snap = _snapshot(p)
     s = torch.cuda.current_stream(device)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    out = {"workload": f"charged Wald test particles, a={A_SPIN}, {n} particles, Hyb1 RK4 dt={DT} <-> IMR dt_implicit",
+    out = {"workload": f"charged Wald test particles, a={A_SPIN}, {n} particles, Hyb1 RK4 dt={DT} <-> IMR dt_implicit" + (" (Newton iteration)" if newton else ""),
            "steps": steps, "runs": []}
     for ratio in ratios:
         _restore(p, snap)
         t = torch.zeros(n, dtype=torch.float64, device=device)
         prm = F.push_params(DT, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=HYB1_THR, r_max=float(g.rn[-1]),
-                            B0pot=B0, dt_implicit=ratio * DT, t=t)
+                            B0pot=B0, dt_implicit=ratio * DT, t=t, imr_newton=newton)
         for _ in range(3):
             F.fpic_push(ctx, p, fields, prm)
         torch.cuda.synchronize()
@@ -826,10 +827,11 @@ def run_charged_dg(device, n=1 << 20, steps=20):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     H0, L0 = F.fpic_hamiltonian(ctx, p, B0pot=B0)
     runs = []
-    for name, sch in (("RK4", F.FPIC_RK4), ("IMR", F.FPIC_IMR), ("discrete gradient", F.FPIC_HAM)):
+    for name, sch, newton in (("RK4", F.FPIC_RK4, False), ("IMR", F.FPIC_IMR, False),
+                              ("IMR (Newton iteration)", F.FPIC_IMR, True), ("discrete gradient", F.FPIC_HAM, False)):
         _restore(p, snap)
         prm = F.push_params(DT, scheme=sch, implicit=F.FPIC_HAM, tol=1e-14, max_iter=50, r_max=float(g.rn[-1]),
-                            B0pot=B0, B0field=B0)
+                            B0pot=B0, B0field=B0, imr_newton=newton)
         F.fpic_push(ctx, p, None, prm)
         torch.cuda.synchronize()
         tot, ps, it = 0.0, 0, 0
@@ -995,7 +997,7 @@ def main():
         return 0
     if args.workload == "adaptive":
         torch.cuda.set_device(local)
-        res = run_adaptive(torch.device("cuda", local), args.n, max(args.steps, 1))
+        res = run_adaptive(torch.device("cuda", local), args.n, max(args.steps, 1), newton=args.imr == "newton")
         res["neutral"] = run_adaptive_neutral(torch.device("cuda", local))
         if rank == 0:
             r0 = res["runs"][0]
@@ -1057,7 +1059,7 @@ def main():
         line["neutral_rk4_alone"] = run_neutral(args, dev, 1 << 20, 20, pre_steps=2, scheme="RK4")
         line["batched"] = run_batched(args, dev, 0.1, 5)
         line["div_clean"] = run_div_clean(dev)
-        line["adaptive_dt"] = run_adaptive(dev)
+        line["adaptive_dt"] = run_adaptive(dev, newton=args.imr == "newton")
         line["adaptive_dt_neutral"] = run_adaptive_neutral(dev)
         line["inject"] = run_inject(dev, 1024, 16)
         line["charged_dg"] = run_charged_dg(dev)
