@@ -31,7 +31,10 @@ def _build(F):
     return ctxs, flds, zs, qs, H0s, D0s, grids, Fos
 
 
-def test_batched_equals_separate_and_oracle():
+@pytest.mark.parametrize("newton", [False, True])
+def test_batched_equals_separate_and_oracle(newton):
+    """Bitwise equal to the runs pushed one by one, within 1e-12 of the
+    oracle, with the IMR in its fixed-point or its Newton form."""
     cuda_or_skip()
     F = fpic()
     ctxs, flds, zs, qs, H0s, D0s, grids, Fos = _build(F)
@@ -40,7 +43,7 @@ def test_batched_equals_separate_and_oracle():
     off = np.concatenate([[0], np.cumsum([r[2] for r in RUNS])])
     specs = [(ctxs[k], flds[k], int(off[k]), int(off[k + 1]), float(grids[k].rn[-1]), 1.0) for k in range(len(RUNS))]
     runs = F.make_runs(specs)
-    prm = F.push_params(DT, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=THR)
+    prm = F.push_params(DT, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=THR, imr_newton=newton)
     st = F.fpic_push_batched(runs, pb, prm, stats=True)
     zb, Hb, ab, sb, ib, cb = to_np(pb)
     tot_impl = 0
@@ -48,7 +51,7 @@ def test_batched_equals_separate_and_oracle():
         sl = slice(off[k], off[k + 1])
         p1 = make_particles(zs[k], qs[k], H0s[k], D0s[k], H0s[k].copy())
         prm1 = F.push_params(DT, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=THR,
-                             r_max=float(grids[k].rn[-1]), B0pot=1.0)
+                             r_max=float(grids[k].rn[-1]), B0pot=1.0, imr_newton=newton)
         F.fpic_push(ctxs[k], p1, flds[k], prm1)
         z1, H1, a1, s1, i1, c1 = to_np(p1)
         assert np.array_equal(zb[sl], z1) and np.array_equal(sb[sl], s1) and np.array_equal(cb[sl], c1)
@@ -58,7 +61,7 @@ def test_batched_equals_separate_and_oracle():
     k = 3
     sl = slice(off[k], off[k + 1])
     po = O.push_params(a=RUNS[k][0], dt=DT, scheme=O.HYB1, implicit_kind=O.IMR, thr=THR, r_max=grids[k].rn[-1],
-                       B0pot=1.0, field_kind=O.FIELD_GRID)
+                       B0pot=1.0, field_kind=O.FIELD_GRID, imr_newton=newton)
     zo = np.ascontiguousarray(zs[k].copy()); Ho = H0s[k].copy()
     O.push(po, zo, qs[k], H0s[k], D0s[k], Ho, np.ones(RUNS[k][2], np.uint8), grids[k], Fos[k])
     err = (np.abs(zb[sl] - zo) / (np.abs(zo) + 1)).max()

@@ -190,18 +190,21 @@ def _rk4_H(g, Fo, zr, q):
     return H
 
 
-def test_corrector_push_parity_and_gain(setup):
+@pytest.mark.parametrize("newton", [False, True])
+def test_corrector_push_parity_and_gain(setup, newton):
     """Train the corrector briefly on the plain pusher's rejected trials, then
     one step from the same state with the plain and the learned push: the
     scheme choices are identical (the trial and the test are the plain
-    ones), every particle matches the plain push and the oracle to 1e-12,
+    ones), every particle matches the plain push and the oracle to 1e-12
+    (the IMR in its fixed-point or Newton form on both sides),
     and the implicit solves need fewer iterations."""
     from paper_2602_07452_gb300 import learned as L
     F, g, Fo, ctx = setup
     n = 1 << 16
     z, q, H0, D0 = _parts(n, g, 8)
     fd = fields_dev(Fo)
-    prm = F.push_params(DT, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=THR, r_max=float(g.rn[-1]), B0pot=1.0)
+    prm = F.push_params(DT, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=THR, r_max=float(g.rn[-1]), B0pot=1.0,
+                        imr_newton=newton)
     p = make_particles(z, q, H0, D0, H0.copy())
     cfg = L.fit_cfg(ctx, p, fd, prm, mode=F.FPIC_LEARN_CORRECT)
     X, T, S = L.generate(ctx, p, fd, prm, cfg, steps=10)
@@ -220,7 +223,8 @@ def test_corrector_push_parity_and_gain(setup):
     live = al == 1
     assert (np.abs(zl - zp) / (np.abs(zp) + 1))[live].max() <= 1e-12
     imp = (sl == 1) & live
-    po = O.push_params(a=A, dt=DT, scheme=O.IMR, field_kind=O.FIELD_GRID, r_max=g.rn[-1], B0pot=1.0)
+    po = O.push_params(a=A, dt=DT, scheme=O.IMR, field_kind=O.FIELD_GRID, r_max=g.rn[-1], B0pot=1.0,
+                       imr_newton=newton)
     zi = np.ascontiguousarray(zs[imp]); Hi = Hn[imp].copy()
     O.push(po, zi, q[imp], H0[imp], D0[imp], Hi, np.ones(imp.sum(), np.uint8), g, Fo)
     assert (np.abs(zl[imp] - zi) / (np.abs(zi) + 1)).max() <= 1e-12
