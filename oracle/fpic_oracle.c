@@ -496,10 +496,14 @@ static void solve3(double M[3][3], double b[3], double x[3])
  *    (1 - (h/2) J) du = u^[k-1] - u^p, then u^[k] = u^[k-1] - du and
  *    x^[k] = x^p - (h/2) A du.  Only the convergence rate differs: both
  *    stop at the same fixed point.
+ * A solve that reaches max_iter without converging (reading: the paper
+ * gives no policy) returns the iterate whose update max_i |z^[k]_i - z^[k-1]_i|
+ * was the smallest, the earliest on ties: for a locally contracting map
+ * that update bounds the iterate's distance to the solution.
  * Returns the iteration count, or -max_iter if the cap was reached. */
 static int step_imr(const or_ctx *c, double h, const double *z0, const double *guess, double *z1)
 {
-    double zk[6], y[6], f[6], zn[6];
+    double zk[6], y[6], f[6], zn[6], best[6], best_dz = INFINITY;
     memcpy(zk, guess, sizeof zk);
     for (int k = 1; k <= c->p->max_iter; ++k) {
         for (int i = 0; i < 6; ++i) y[i] = 0.5 * (z0[i] + zk[i]);
@@ -519,10 +523,13 @@ static int step_imr(const or_ctx *c, double h, const double *z0, const double *g
             }
         }
         int ok = converged(zn, zk, c->p->tol);
+        double dz = 0.0;
+        for (int i = 0; i < 6; ++i) dz = fmax(dz, fabs(zn[i] - zk[i]));
+        if (dz < best_dz) { best_dz = dz; memcpy(best, zn, sizeof best); }
         memcpy(zk, zn, sizeof zk);
         if (ok) { memcpy(z1, zk, sizeof zk); return k; }
     }
-    memcpy(z1, zk, sizeof zk);
+    memcpy(z1, best, sizeof best);
     return -c->p->max_iter;
 }
 

@@ -628,3 +628,52 @@ def test_imr_newton_first_iterates_are_newton_steps():
         zk, coup, du = newton_np(zk)
         assert (np.abs(z[:, :3] - zk[:, :3]) <= 1e-3 * coup + 1e-15 * (np.abs(zk[:, :3]) + 1)).all(), it
         assert (np.abs(z[:, 3:] - zk[:, 3:]) <= 1e-6 * du + 1e-15 * (np.abs(zk[:, 3:]) + 1)).all(), it
+
+
+@pytest.mark.parametrize("newton", [False, True])
+def test_imr_unconverged_solve_returns_smallest_update_iterate(newton):
+    """Reading for a solve stopped by max_iter (the paper gives no policy):
+    the result is the iterate whose update max_i |z^[k]_i - z^[k-1]_i| was
+    the smallest.  The iterates are rebuilt here from the right-hand side
+    and the grid gather (the fixed-point map; for the Newton form only the
+    first iterate, which max_iter = 1 returns as is), at a step far too long
+    for the map to contract (dt = 0.05, q/m = 100), where the updates grow
+    and the first iterate wins over the last."""
+    a, B0 = 0.9, 1.0
+    g = I.wald_grid(64, a)
+    Fo = O.wald_on_grid(a, B0, g)
+    z0, qm = _wald_plasma(200, a, seed=13)
+    H0, _, D0 = O.hamiltonian(1.0, a, B0, z0, qm)
+    dt, m = 0.05, 6
+
+    def push(max_iter):
+        p = O.push_params(a=a, dt=dt, scheme=O.IMR, B0pot=B0, max_iter=max_iter, imr_newton=newton,
+                          field_kind=O.FIELD_GRID, r_max=1e300)
+        z = z0.copy()
+        nc, sch, its = O.push(p, z, qm, H0, D0, np.zeros(len(z)), np.ones(len(z), np.uint8), g, Fo)
+        return z, nc
+
+    if not newton:
+        zk, its, ups = z0.copy(), [], []
+        for k in range(m):
+            y = 0.5 * (z0 + zk)
+            DB = O.gather(g, Fo, y[:, 0], y[:, 1])
+            zn = z0 + dt * O.rhs(1.0, a, y, qm, DB[:, :3], DB[:, 3:])
+            ups.append(np.abs(zn - zk).max(axis=1))
+            its.append(zn)
+            zk = zn
+        ups, its = np.array(ups), np.array(its)
+        pick = np.argmin(ups, axis=0)                 # first minimum on ties
+        exp = its[pick, np.arange(len(z0))]
+        z, nc = push(m)
+        assert nc == len(z0)
+        ok = (exp[:, 1] > 0) & (exp[:, 1] < np.pi) & (exp[:, 0] > 1.5)   # no boundary handling applied
+        assert ok.mean() > 0.5 and (pick < m - 1).mean() > 0.5
+        assert np.abs(z[ok] - exp[ok]).max() <= 1e-12 * (np.abs(exp[ok]).max() + 1)
+    # the returned state is one of the iterates, and never one with a larger
+    # update than the first: max_iter = 1 (the first iterate) bounds it
+    z1, _ = push(1)
+    zm, _ = push(m)
+    d1 = np.abs(z1 - z0).max(axis=1)
+    dm = np.abs(zm - z0).max(axis=1)
+    assert np.isfinite(zm).all() and (dm <= 10 * d1 + 1e-12).mean() > 0.9
