@@ -434,6 +434,10 @@ __global__ void __launch_bounds__(128, NEWTON ? 3 : 4) k_imr(const __grid_consta
     long long p = -1, qi = 0;
     bool exhausted = false, again = false;
     double z0[6], zk[6];
+    // the iterate with the smallest update so far (returned by a solve that
+    // reaches max_iter), one column per thread (blockDim.x <= 128)
+    __shared__ double s_best[6 * 128];
+    double best_dz = INFINITY;
     double qm = 0.0, s0 = 0.0, c0 = 1.0;
     bool em = false;
     int it = 0;
@@ -483,6 +487,7 @@ __global__ void __launch_bounds__(128, NEWTON ? 3 : 4) k_imr(const __grid_consta
                         qm = (!all_mode && k.z0s) ? k.z0s[(size_t)6 * k.n + slot] : k.P.qm[p];
                         em = (R->has_fields || R->B0field != 0.0) && qm != 0.0;
                         it = 0;
+                        best_dz = INFINITY;
                     }
                 } else {
                     exhausted = true;
@@ -508,6 +513,14 @@ __global__ void __launch_bounds__(128, NEWTON ? 3 : 4) k_imr(const __grid_consta
             for (int i = 0; i < 6; ++i) zn[i] = fma(k.dt_imp, f[i], z0[i]);
             if (NEWTON) newton_update(J, 0.5 * k.dt_imp, zk, zn);
             const bool ok = conv6(zn, zk, k.tol);
+            double dz = 0.0;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) dz = fmax(dz, fabs(zn[i] - zk[i]));
+            if (dz < best_dz) {
+                best_dz = dz;
+#pragma unroll
+                for (int i = 0; i < 6; ++i) s_best[i * blockDim.x + threadIdx.x] = zn[i];
+            }
 #pragma unroll
             for (int i = 0; i < 6; ++i) zk[i] = zn[i];
             ++it;
@@ -519,7 +532,12 @@ __global__ void __launch_bounds__(128, NEWTON ? 3 : 4) k_imr(const __grid_consta
 #pragma unroll
                 for (int i = 0; i < 6; ++i) zk[i] = k.stg[(size_t)(STG_TRIAL + i) * k.n + qi];
             } else if (ok || it >= k.max_iter) {
-                if (!ok) ++n_nc;
+                if (!ok) {
+                    // not converged: the iterate with the smallest update (Sec. 2.2.2 gives no policy)
+                    ++n_nc;
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) zk[i] = s_best[i * blockDim.x + threadIdx.x];
+                }
                 if (k.record && k.featS) {
                     // corrector form: row = queue slot, (gap to the trial - leading-order gap) / (s_i oscale_i)
                     float* t = k.recT + 16 * qi;
