@@ -26,8 +26,9 @@ def _pair(n, a, seed):
     return mk(), mk()
 
 
-@pytest.mark.parametrize("scheme,implicit", [("HYB2", "IMR"), ("HYB1", "HAM"), ("RK4", "IMR")])
-def test_noalloc_matches_regular_push_two_calls(scheme, implicit):
+@pytest.mark.parametrize("scheme,implicit,newton", [("HYB2", "IMR", False), ("HYB2", "IMR", True),
+                                                   ("HYB1", "HAM", False), ("RK4", "IMR", False)])
+def test_noalloc_matches_regular_push_two_calls(scheme, implicit, newton):
     cuda_or_skip()
     F = fpic()
     a, dt, n = 0.9, 0.5, 3001
@@ -35,7 +36,7 @@ def test_noalloc_matches_regular_push_two_calls(scheme, implicit):
     ctx = F.fpic_init_metric(1.0, a)
     thr = 1e-10 if scheme == "HYB2" else 1e-11
     prm = F.push_params(dt, scheme=getattr(F, "FPIC_" + scheme), implicit=getattr(F, "FPIC_" + implicit),
-                        thr=thr, tol=1e-14)
+                        thr=thr, tol=1e-14, imr_newton=newton)
     for _ in range(2):                     # two calls in a row
         st_ref = F.fpic_push(ctx, p_ref, None, prm, stats=True)
         st_na = F.fpic_push_noalloc(1.0, a, p_na, prm, stats=True)
