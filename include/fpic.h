@@ -593,6 +593,19 @@ int fpic_push_learned(fpic_ctx *ctx, fpic_mlp *m, fpic_particles *p, const doubl
                       const fpic_push_params *prm, const fpic_learned_cfg *cfg, fpic_push_stats *stats,
                       void *stream);
 
+/* fpic_push_batched with the learned guess: the corrector form of
+ * fpic_push_learned (cfg->mode = FPIC_LEARN_CORRECT, dt_implicit 0 or dt,
+ * scheme FPIC_HYB1/HYB2) on every run of the batch in the same launches:
+ * RK4 trial + plain test for all particles, the network on the rejected ones
+ * of every run, the implicit solves from the corrected trials.  One network
+ * serves all runs (its features are run independent).  runs, p, prm, stats
+ * as fpic_push_batched; the scratch is runs[0].ctx's.  Scheme choices are
+ * exactly fpic_push_batched's.  Errors: FPIC_EINVAL, FPIC_ENOMEM, FPIC_ECUDA,
+ * FPIC_ENOTCONVERGED (stats only). */
+int fpic_push_batched_learned(const fpic_run *runs, int nruns, fpic_mlp *m, fpic_particles *p,
+                              const fpic_push_params *prm, const fpic_learned_cfg *cfg, fpic_push_stats *stats,
+                              void *stream);
+
 /* Reads the handle's error word (synchronous): FPIC_ETIMEOUT if a bounded
  * tensor-core wait of an earlier launch ran out, else FPIC_OK. */
 int fpic_mlp_status(fpic_mlp *m, int *status);

@@ -2028,10 +2028,20 @@ namespace fpic {
 
 }  // namespace fpic
 
-extern "C" int fpic_push_batched(const fpic_run* runs, int nruns, fpic_particles* p, const fpic_push_params* prm,
-                                 fpic_push_stats* stats, void* stream)
+// The batched push, plain (m == nullptr) or with the learned corrector (m,
+// cfg: the corrector form of fpic_push_learned on the batched kernels).
+static int push_batched(const fpic_run* runs, int nruns, fpic_mlp* m, fpic_particles* p, const fpic_push_params* prm,
+                        const fpic_learned_cfg* cfg, fpic_push_stats* stats, void* stream)
 {
     if (!runs || nruns < 1 || !p || !prm) return set_error(FPIC_EINVAL, "fpic_push_batched: NULL argument or nruns < 1");
+    if (m) {
+        if (!cfg || cfg->mode != FPIC_LEARN_CORRECT)
+            return set_error(FPIC_EINVAL, "fpic_push_batched_learned: need a corrector-form cfg (FPIC_LEARN_CORRECT)");
+        if (prm->scheme != FPIC_HYB1 && prm->scheme != FPIC_HYB2)
+            return set_error(FPIC_EINVAL, "fpic_push_batched_learned: need a Hyb1/Hyb2 scheme with the IMR partner");
+        if (prm->dt_implicit != 0.0 && prm->dt_implicit != prm->dt)
+            return set_error(FPIC_EINVAL, "fpic_push_batched_learned: the learned guess is trained for dt_implicit = dt");
+    }
     if (p->n < 0 || p->n >= (1LL << 31)) return set_error(FPIC_EINVAL, "fpic_push_batched: n out of range");
     if (!particles_ok(p, true)) return set_error(FPIC_EINVAL, "fpic_push_batched: NULL particle array");
     if (!(std::isfinite(prm->dt)) || prm->dt == 0.0) return set_error(FPIC_EINVAL, "fpic_push_batched: bad dt");
@@ -2070,7 +2080,10 @@ extern "C" int fpic_push_batched(const fpic_run* runs, int nruns, fpic_particles
         c->runs_cap = nruns;
     }
     const long long nn = n > 0 ? n : 1;
-    int rc = ensure_scratch(c, (size_t)nn * (8 * sizeof(double) + 2 * sizeof(uint32_t)) + 256);
+    PushK k{};
+    float *X = nullptr, *Y = nullptr, *f32 = nullptr;
+    int rc = m ? learned_scratch(c, nn, k, &X, &Y, &f32)
+               : ensure_scratch(c, (size_t)nn * (8 * sizeof(double) + 2 * sizeof(uint32_t)) + 256);
     if (rc) return rc;
     std::vector<RunK> tab(nruns);
     for (int i = 0; i < nruns; ++i) {
@@ -2106,7 +2119,6 @@ extern "C" int fpic_push_batched(const fpic_run* runs, int nruns, fpic_particles
     }
     FPIC_CUDA(cudaMemcpyAsync(c->d_runs, c->h_runs, sizeof(RunK) * nruns, cudaMemcpyHostToDevice, s));
     // the single-run kernels with a per-particle run lookup (BATCHED)
-    PushK k{};
     k.runs = (const RunK*)c->d_runs;
     k.nruns = nruns;
     k.dt = prm->dt;
@@ -2121,10 +2133,18 @@ extern "C" int fpic_push_batched(const fpic_run* runs, int nruns, fpic_particles
     k.n = n;
     k.P = PartDev{p->r, p->th, p->ph, p->ur, p->uth, p->uph, p->qm, p->H0, p->D0, p->Hn,
                   p->alive, p->scheme, p->iters, p->cell};
-    k.guess = (double*)c->d_scratch;
-    k.sc0 = k.guess + (size_t)nn * 6;
-    k.queue = (uint32_t*)((char*)c->d_scratch + (size_t)nn * 8 * sizeof(double));
-    k.order = k.queue + nn;
+    if (m) {
+        // buffers laid out by learned_scratch; the corrector's parameters
+        set_corrector(k, cfg, X);
+        for (int i = 0; i < 6; ++i) k.inc_scale[i] = cfg->inc_scale[i];
+        k.learned = Y;
+        k.work = nullptr;
+    } else {
+        k.guess = (double*)c->d_scratch;
+        k.sc0 = k.guess + (size_t)nn * 6;
+        k.queue = (uint32_t*)((char*)c->d_scratch + (size_t)nn * 8 * sizeof(double));
+        k.order = k.queue + nn;
+    }
     k.cnt = c->d_cnt;
     FPIC_CUDA(cudaMemsetAsync(c->d_cnt, 0, CNT_N * sizeof(long long), s));
     if (n == 0) {
@@ -2137,6 +2157,18 @@ extern "C" int fpic_push_batched(const fpic_run* runs, int nruns, fpic_particles
     cudaEvent_t* ev = prm->events ? (cudaEvent_t*)prm->events : nullptr;
     if (stats) k_count_alive<<<persist, 256, 0, s>>>(k.P, n, c->d_cnt);
     if (ev) FPIC_CUDA(cudaEventRecord(ev[0], s));
+    if (m) {
+        // RK4 trial + plain test for all; the network on the rejected ones
+        k_explicit<2, true><<<nb, 128, 0, s>>>(k);
+        if (ev) FPIC_CUDA(cudaEventRecord(ev[1], s));
+        FPIC_CUDA(cudaFuncSetAttribute(k_mlp_correct4, cudaFuncAttributeMaxDynamicSharedMemorySize, G4_SMEM));
+        const long long nct = (n + 127) / 128 / G4_GROUPS + 1, cap = mlp_sm_count(m);
+        k_mlp_correct4<<<(unsigned)(nct < cap ? nct : cap), G4_THREADS, G4_SMEM, s>>>(k, mlp_weights(m), mlp_err(m));
+        if (ev) FPIC_CUDA(cudaEventRecord(ev[2], s));
+        k_order<<<persist, 256, 0, s>>>(k);
+        launch_imr<1, true>(imr_grid, 128, s, k, 0);
+        k_imr_finish<true><<<persist, 256, 0, s>>>(k, 0);
+    } else {
     if (prm->scheme == FPIC_RK4) k_explicit<0, true><<<nb, 128, 0, s>>>(k);
     else if (prm->scheme >= FPIC_HYB1) k_explicit<1, true><<<nb, 128, 0, s>>>(k);
     if (ev) {
@@ -2150,6 +2182,7 @@ extern "C" int fpic_push_batched(const fpic_run* runs, int nruns, fpic_particles
         k_order<<<persist, 256, 0, s>>>(k);
         launch_imr<0, true>(imr_grid, 128, s, k, 0);
         k_imr_finish<true><<<persist, 256, 0, s>>>(k, 0);
+    }
     }
     if (ev) FPIC_CUDA(cudaEventRecord(ev[3], s));
     FPIC_CUDA(cudaGetLastError());
@@ -2166,6 +2199,20 @@ extern "C" int fpic_push_batched(const fpic_run* runs, int nruns, fpic_particles
         if (h[CNT_NOTCONV] > 0) return FPIC_ENOTCONVERGED;
     }
     return FPIC_OK;
+}
+
+extern "C" int fpic_push_batched(const fpic_run* runs, int nruns, fpic_particles* p, const fpic_push_params* prm,
+                                 fpic_push_stats* stats, void* stream)
+{
+    return push_batched(runs, nruns, nullptr, p, prm, nullptr, stats, stream);
+}
+
+extern "C" int fpic_push_batched_learned(const fpic_run* runs, int nruns, fpic_mlp* m, fpic_particles* p,
+                                         const fpic_push_params* prm, const fpic_learned_cfg* cfg,
+                                         fpic_push_stats* stats, void* stream)
+{
+    if (!m) return set_error(FPIC_EINVAL, "fpic_push_batched_learned: NULL network");
+    return push_batched(runs, nruns, m, p, prm, cfg, stats, stream);
 }
 
 extern "C" int fpic_set_tuning(fpic_ctx* c, int key, int value)

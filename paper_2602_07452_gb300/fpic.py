@@ -97,6 +97,9 @@ FPIC_TUNE_IMR_BLOCKS_PER_SM, FPIC_TUNE_DEP_THREADS, FPIC_TUNE_STATIC_FIELDS = 0,
 _SIGS = {
     "fpic_push_batched": (C.c_int, [C.POINTER(fpic_run), C.c_int, C.POINTER(fpic_particles),
                                     C.POINTER(fpic_push_params), C.POINTER(fpic_push_stats), C.c_void_p]),
+    "fpic_push_batched_learned": (C.c_int, [C.POINTER(fpic_run), C.c_int, C.c_void_p, C.POINTER(fpic_particles),
+                                            C.POINTER(fpic_push_params), C.POINTER(fpic_learned_cfg),
+                                            C.POINTER(fpic_push_stats), C.c_void_p]),
     "fpic_features": (C.c_int, [C.c_void_p, C.POINTER(fpic_particles), C.POINTER(_D), C.c_double,
                                 C.POINTER(fpic_learned_cfg), C.c_void_p, C.c_void_p]),
     "fpic_learn_sample": (C.c_int, [C.c_void_p, C.POINTER(fpic_particles), C.POINTER(_D), C.POINTER(fpic_push_params),
@@ -633,6 +636,16 @@ def fpic_push_learned(ctx: Ctx, net: "MLP", p: Particles, fields, prm, cfg, stat
     st = fpic_push_stats() if stats else None
     rc = lib().fpic_push_learned(ctx.handle, net.handle, C.byref(s), _fields_arg(fields), C.byref(prm),
                                  C.byref(cfg), C.byref(st) if st is not None else None, _stream(stream))
+    _check(rc)
+    return st.as_dict() if st is not None else None
+
+
+def fpic_push_batched_learned(runs, net: "MLP", p: Particles, prm, cfg, stats=False, stream=None):
+    """fpic_push_batched with the learned corrector (cfg.mode = FPIC_LEARN_CORRECT)."""
+    s = p.struct()
+    st = fpic_push_stats() if stats else None
+    rc = lib().fpic_push_batched_learned(runs, len(runs), net.handle, C.byref(s), C.byref(prm), C.byref(cfg),
+                                         C.byref(st) if st is not None else None, _stream(stream))
     _check(rc)
     return st.as_dict() if st is not None else None
 

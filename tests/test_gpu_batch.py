@@ -98,3 +98,48 @@ def test_batched_step_in_cuda_graph():
     torch.cuda.synchronize()
     assert np.array_equal(pg.state().cpu().numpy(), pe.state().cpu().numpy())
     assert np.array_equal(pg.Hn.cpu().numpy(), pe.Hn.cpu().numpy())
+
+
+@pytest.mark.parametrize("newton", [False, True])
+def test_batched_learned_corrector_equals_separate(newton):
+    """fpic_push_batched_learned (the corrector form on the batched kernels)
+    gives bitwise the particles of fpic_push_learned on each run alone, with
+    the same network and configuration (here the zero network: the
+    leading-order gap alone), and the scheme choices of the plain batched
+    push; the sampled run stays within 1e-12 of the oracle."""
+    cuda_or_skip()
+    F = fpic()
+    ctxs, flds, zs, qs, H0s, D0s, grids, Fos = _build(F)
+    z = np.concatenate(zs); q = np.concatenate(qs); H0 = np.concatenate(H0s); D0 = np.concatenate(D0s)
+    off = np.concatenate([[0], np.cumsum([r[2] for r in RUNS])])
+    specs = [(ctxs[k], flds[k], int(off[k]), int(off[k + 1]), float(grids[k].rn[-1]), 1.0) for k in range(len(RUNS))]
+    runs = F.make_runs(specs)
+    net0 = F.MLP()
+    net0.set_params(torch.zeros(F.MLP.nparams(), dtype=torch.float32, device="cuda"))
+    cfg = F.learned_cfg(mode=F.FPIC_LEARN_CORRECT)
+    prm = F.push_params(DT, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=THR, imr_newton=newton)
+    pb = make_particles(z, q, H0, D0, H0.copy())
+    st = F.fpic_push_batched_learned(runs, net0, pb, prm, cfg, stats=True)
+    zb, Hb, ab, sb, ib, cb = to_np(pb)
+    pp = make_particles(z, q, H0, D0, H0.copy())
+    F.fpic_push_batched(runs, pp, prm)
+    assert np.array_equal(to_np(pp)[3], sb)
+    tot_impl = 0
+    for k in range(len(RUNS)):
+        sl = slice(off[k], off[k + 1])
+        p1 = make_particles(zs[k], qs[k], H0s[k], D0s[k], H0s[k].copy())
+        prm1 = F.push_params(DT, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=THR,
+                             r_max=float(grids[k].rn[-1]), B0pot=1.0, imr_newton=newton)
+        F.fpic_push_learned(ctxs[k], net0, p1, flds[k], prm1, cfg)
+        z1, H1, a1, s1, i1, c1 = to_np(p1)
+        assert np.array_equal(zb[sl], z1) and np.array_equal(sb[sl], s1) and np.array_equal(ib[sl], i1)
+        tot_impl += int(s1.sum())
+    assert st["n_implicit"] == tot_impl > 0
+    k = 1
+    sl = slice(off[k], off[k + 1])
+    po = O.push_params(a=RUNS[k][0], dt=DT, scheme=O.HYB1, implicit_kind=O.IMR, thr=THR, r_max=grids[k].rn[-1],
+                       B0pot=1.0, field_kind=O.FIELD_GRID, imr_newton=newton)
+    zo = np.ascontiguousarray(zs[k].copy()); Ho = H0s[k].copy()
+    O.push(po, zo, qs[k], H0s[k], D0s[k], Ho, np.ones(RUNS[k][2], np.uint8), grids[k], Fos[k])
+    err = (np.abs(zb[sl] - zo) / (np.abs(zo) + 1)).max()
+    assert err <= 1e-12, err
