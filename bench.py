@@ -630,10 +630,60 @@ def run_batched(args, device, scale, steps):
     # particle-steps: alive particles at the start of each step; removal is
     # slow, so the mean of the first and last count bounds it within 1e-3
     ps = 0.5 * (alive_start + alive_end) * steps
-    return {"workload": "24 uneven split-monopole runs in one batched launch per step (CUDA graph replay): "
-                        f"a=0.5..0.99, grids 256^2..1024^2, {scale:g} x (1e5..4e7) particles each",
-            "particles": n, "alive_at_start": alive_start, "runs": 24, "steps": steps, "value": ps / t,
-            "unit": UNIT, "ms_per_step": 1e3 * t / steps}
+    out = {"workload": "24 uneven split-monopole runs in one batched launch per step (CUDA graph replay): "
+                       f"a=0.5..0.99, grids 256^2..1024^2, {scale:g} x (1e5..4e7) particles each",
+           "particles": n, "alive_at_start": alive_start, "runs": 24, "steps": steps, "value": ps / t,
+           "unit": UNIT, "ms_per_step": 1e3 * t / steps,
+           "imr_iteration": "Newton" if args.imr == "newton" else "fixed point"}
+    if not args.no_learned:
+        # the learned corrector on the same batch: one network, trained on the
+        # plain steps of the largest run with at most 2e6 particles (untimed)
+        from paper_2602_07452_gb300 import learned as L
+        after = _snapshot(p)
+        kk = max((k for k in range(24) if counts[k] <= 2_000_000), key=lambda k: counts[k])
+        b0, b1 = specs[kk][2], specs[kk][3]
+        sub = p.head(n)                                  # views; copy the run's slice out
+        tr = F.Particles(*[getattr(sub, f)[b0:b1].clone() for f in sub.__dataclass_fields__])
+        prm_k = F.push_params(DT, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=HYB1_THR, r_max=specs[kk][4],
+                              imr_newton=args.imr == "newton")
+        t0 = time.perf_counter()
+        cfg = L.fit_cfg(ctxs[kk], tr, flds[kk], prm_k, mode=F.FPIC_LEARN_CORRECT)
+        X, T, S = L.generate(ctxs[kk], tr, flds[kk], prm_k, cfg, steps=args.train_gen_steps)
+        net, P, hist = L.train(X, T, S, steps=args.train_steps, batch=8192, lr=3e-3, log_every=500)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
+        del X, T, S, tr
+        _restore(p, after)
+        with torch.cuda.stream(s):
+            for _ in range(2):
+                F.fpic_push_batched_learned(runs, net, p, prm, cfg, stream=s)
+        torch.cuda.synchronize()
+        _restore(p, after)
+        g2 = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g2, stream=s):
+            F.fpic_push_batched_learned(runs, net, p, prm, cfg, stream=s)
+        _restore(p, after)
+        # the plain graph once more from the same state, then the learned one
+        res = {}
+        for name, gr in (("plain", graph), ("learned", g2)):
+            _restore(p, after)
+            torch.cuda.synchronize()
+            a0 = int(p.alive.sum().item())
+            with torch.cuda.stream(s):
+                e0.record(s)
+                for _ in range(steps):
+                    gr.replay()
+                e1.record(s)
+            torch.cuda.synchronize()
+            a1 = int(p.alive.sum().item())
+            tt = e0.elapsed_time(e1) * 1e-3
+            res[name] = (0.5 * (a0 + a1) * steps / tt, 1e3 * tt / steps)
+        out["learned"] = {"value": res["learned"][0], "ms_per_step": res["learned"][1],
+                          "plain_same_state": res["plain"][0], "ratio_vs_plain": res["learned"][0] / res["plain"][0],
+                          "training": {"run": int(kk), "particles": int(counts[kk]), "train_steps": args.train_steps,
+                                       "loss_first_last": [hist[0][1], hist[-1][1]], "seconds": round(train_s, 1)},
+                          "api": "fpic_push_batched_learned (corrector form), CUDA graph replay"}
+    return out
 
 
 def run_pic(args, device, grid_n, ppc, steps, rank=0, conserving=False, inject_every=0, clean_every=0,
