@@ -659,9 +659,15 @@ def run_batched(args, device, scale, steps):
                 F.fpic_push_batched_learned(runs, net, p, prm, cfg, stream=s)
         torch.cuda.synchronize()
         _restore(p, after)
+        # the learned push needs more scratch than the plain one: the context
+        # reallocated it, so the plain graph captured above is stale and both
+        # graphs are captured now, against the grown scratch
         g2 = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g2, stream=s):
             F.fpic_push_batched_learned(runs, net, p, prm, cfg, stream=s)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=s):
+            F.fpic_push_batched(runs, p, prm, stream=s)
         _restore(p, after)
         # the plain graph once more from the same state, then the learned one
         res = {}

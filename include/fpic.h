@@ -222,8 +222,12 @@ typedef struct {
  * the current device; prm is shared (its r_max and B0pot are ignored in
  * favour of each run's).  The run table is staged through pinned memory
  * owned by runs[0].ctx, so after one call outside capture the call can be
- * captured in a CUDA graph and replayed.  Errors: FPIC_EINVAL, FPIC_ENOMEM,
- * FPIC_ECUDA; FPIC_ENOTCONVERGED as fpic_push. */
+ * captured in a CUDA graph and replayed.  A captured graph holds the
+ * addresses of the context's scratch: a later call on the same context that
+ * needs more scratch (more particles, or the learned push) reallocates it and
+ * leaves graphs captured before pointing at freed memory -- capture after the
+ * largest call, and capture again after any larger one.  Errors: FPIC_EINVAL,
+ * FPIC_ENOMEM, FPIC_ECUDA; FPIC_ENOTCONVERGED as fpic_push. */
 int fpic_push_batched(const fpic_run *runs, int nruns, fpic_particles *p, const fpic_push_params *prm,
                       fpic_push_stats *stats, void *stream);
 
