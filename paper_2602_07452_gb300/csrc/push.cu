@@ -2024,10 +2024,6 @@ extern "C" int fpic_push_learned(fpic_ctx* c, fpic_mlp* m, fpic_particles* p, co
 // Batched push: many independent runs (spacetime, grid, fields, particle
 // range) in one explicit launch and one persistent implicit launch.
 // ---------------------------------------------------------------------------
-namespace fpic {
-
-}  // namespace fpic
-
 // The batched push, plain (m == nullptr) or with the learned corrector (m,
 // cfg: the corrector form of fpic_push_learned on the batched kernels).
 static int push_batched(const fpic_run* runs, int nruns, fpic_mlp* m, fpic_particles* p, const fpic_push_params* prm,
@@ -2169,20 +2165,20 @@ static int push_batched(const fpic_run* runs, int nruns, fpic_mlp* m, fpic_parti
         launch_imr<1, true>(imr_grid, 128, s, k, 0);
         k_imr_finish<true><<<persist, 256, 0, s>>>(k, 0);
     } else {
-    if (prm->scheme == FPIC_RK4) k_explicit<0, true><<<nb, 128, 0, s>>>(k);
-    else if (prm->scheme >= FPIC_HYB1) k_explicit<1, true><<<nb, 128, 0, s>>>(k);
-    if (ev) {
-        FPIC_CUDA(cudaEventRecord(ev[1], s));
-        FPIC_CUDA(cudaEventRecord(ev[2], s));
-    }
-    if (prm->scheme == FPIC_IMR) {
-        launch_imr<0, true>(imr_grid, 128, s, k, 1);
-        k_imr_finish<true><<<persist, 256, 0, s>>>(k, 1);
-    } else if (prm->scheme >= FPIC_HYB1) {
-        k_order<<<persist, 256, 0, s>>>(k);
-        launch_imr<0, true>(imr_grid, 128, s, k, 0);
-        k_imr_finish<true><<<persist, 256, 0, s>>>(k, 0);
-    }
+        if (prm->scheme == FPIC_RK4) k_explicit<0, true><<<nb, 128, 0, s>>>(k);
+        else if (prm->scheme >= FPIC_HYB1) k_explicit<1, true><<<nb, 128, 0, s>>>(k);
+        if (ev) {
+            FPIC_CUDA(cudaEventRecord(ev[1], s));
+            FPIC_CUDA(cudaEventRecord(ev[2], s));
+        }
+        if (prm->scheme == FPIC_IMR) {
+            launch_imr<0, true>(imr_grid, 128, s, k, 1);
+            k_imr_finish<true><<<persist, 256, 0, s>>>(k, 1);
+        } else if (prm->scheme >= FPIC_HYB1) {
+            k_order<<<persist, 256, 0, s>>>(k);
+            launch_imr<0, true>(imr_grid, 128, s, k, 0);
+            k_imr_finish<true><<<persist, 256, 0, s>>>(k, 0);
+        }
     }
     if (ev) FPIC_CUDA(cudaEventRecord(ev[3], s));
     FPIC_CUDA(cudaGetLastError());
