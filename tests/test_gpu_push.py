@@ -555,3 +555,26 @@ def test_newton_imr_mixed_charges_is_deterministic_and_matches_oracle(F):
     assert_state_close(zg, zo, TOL)
     assert np.abs(ig.astype(int) - io.astype(int)).max() <= 1
     assert io[q == 0].mean() < io[q != 0].mean()
+
+
+@pytest.mark.parametrize("newton", [False, True])
+def test_unconverged_solve_returns_smallest_update_iterate(F, newton):
+    """At a step far too long for the IMR map to contract (dt = 0.05,
+    q/m = 100), every solve stops at max_iter = 4 and returns the iterate
+    with the smallest update, as the oracle does: states within 1e-12 of the
+    oracle, every particle counted as not converged (fixed-point form).  The
+    Newton form converges for some of them; either way GPU and oracle agree."""
+    a = 0.9
+    g = I.wald_grid(64, a)
+    Fo = O.wald_on_grid(a, 1.0, g)
+    ctx = _mk(F, a, g)
+    d, z, q = thermal_state(1001, g, a, theta=0.1, seed=17)
+    p, st, (zo, Ho, ao, so, io, nc), _ = _one_step(F, ctx, g, Fo, z, q, F.FPIC_IMR, 0.05, max_iter=4,
+                                                   newton=newton, r_max=1e300)
+    zg, Hg, ag, sg, ig, cg = to_np(p)
+    if not newton:
+        assert nc == len(q)
+    assert st["n_notconv"] == nc
+    ok = (ao == 1) & (ag == 1)
+    assert ok.mean() > 0.9
+    assert_state_close(zg, zo, TOL, ok)
