@@ -677,3 +677,29 @@ def test_imr_unconverged_solve_returns_smallest_update_iterate(newton):
     d1 = np.abs(z1 - z0).max(axis=1)
     dm = np.abs(zm - z0).max(axis=1)
     assert np.isfinite(zm).all() and (dm <= 10 * d1 + 1e-12).mean() > 0.9
+
+
+@pytest.mark.parametrize("newton", [False, True])
+def test_imr_a_posteriori_stop_is_within_tolerance(newton):
+    """The IMR's stop from the observed contraction accepts an iterate only
+    when theta / (1 - theta) times its update passes the tolerance: the
+    accepted states lie within a few tol (|z| + 1) of the solution iterated
+    to the end (tol = 0: every iteration until max_iter, the smallest-update
+    iterate returned), and the Newton form needs fewer than 3.7 on average."""
+    a, B0 = 0.9, 1.0
+    z0, qm = _wald_plasma(500, a, seed=19)
+    H0, _, D0 = O.hamiltonian(1.0, a, B0, z0, qm)
+
+    def solve(tol, max_iter):
+        p = O.push_params(a=a, dt=1e-3, scheme=O.IMR, B0pot=B0, tol=tol, max_iter=max_iter, imr_newton=newton,
+                          field_kind=O.FIELD_WALD, B0field=B0)
+        z = z0.copy()
+        nc, sch, its = O.push(p, z, qm, H0, D0, np.zeros(len(z)), np.ones(len(z), np.uint8))
+        return z, its.astype(float), nc
+
+    z, its, nc = solve(1e-14, 50)
+    zr, _, _ = solve(0.0, 60)
+    assert nc == 0
+    assert (np.abs(z - zr) / (np.abs(zr) + 1)).max() <= 5e-14
+    if newton:
+        assert its.mean() < 3.7 and its.max() <= 6, (its.mean(), its.max())
