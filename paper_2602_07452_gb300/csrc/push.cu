@@ -412,8 +412,11 @@ __global__ void k_order(PushK k)
 }
 
 // Persistent lane-refilling implicit-midpoint solver (Sec. 2.2.2):
-// z^[k] = z^n + dt F((z^n + z^[k-1]) / 2) until two iterates agree to tol;
-// NEWTON: the Newton form of the same iteration (newton_update).
+// z^[k] = z^n + dt F((z^n + z^[k-1]) / 2) until two iterates agree to tol,
+// or, from the second iteration on, each component's a-posteriori error
+// bound theta_i / (1 - theta_i) |dz_i| (theta_i the ratio of its last two
+// updates) does; NEWTON: the Newton form of the same iteration
+// (newton_update).
 // all_mode: the queue is every particle (pure IMR, guess z^n); otherwise
 // entries come from k_explicit with their trial and sin/cos of th^n (sc0).
 // Each loop trip is one right-hand side per lane; a lane whose solve ends
@@ -425,7 +428,7 @@ __global__ void k_order(PushK k)
 // that has not converged after that many iterations from it restarts once,
 // with the full max_iter budget, from the trial in stg.
 template <int RESTART, bool BATCHED = false, bool NEWTON = false>
-__global__ void __launch_bounds__(128, NEWTON ? 3 : 4) k_imr(const __grid_constant__ PushK k, int all_mode)
+__global__ void __launch_bounds__(128, 3) k_imr(const __grid_constant__ PushK k, int all_mode)
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -438,6 +441,7 @@ __global__ void __launch_bounds__(128, NEWTON ? 3 : 4) k_imr(const __grid_consta
     // reaches max_iter), one column per thread (blockDim.x <= 128)
     __shared__ double s_best[6 * 128];
     double best_dz = INFINITY;
+    double dprev[6];        // the previous iteration's |update| per component (a-posteriori stop)
     double qm = 0.0, s0 = 0.0, c0 = 1.0;
     bool em = false;
     int it = 0;
@@ -512,10 +516,26 @@ __global__ void __launch_bounds__(128, NEWTON ? 3 : 4) k_imr(const __grid_consta
 #pragma unroll
             for (int i = 0; i < 6; ++i) zn[i] = fma(k.dt_imp, f[i], z0[i]);
             if (NEWTON) newton_update(J, 0.5 * k.dt_imp, zk, zn);
-            const bool ok = conv6(zn, zk, k.tol);
+            double di[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) di[i] = fabs(zn[i] - zk[i]);
+            bool ok = true;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) ok = ok && (di[i] <= k.tol * (fabs(zn[i]) + 1.0));
+            if (!ok && it >= 1) {
+                // a-posteriori stop: theta_i / (1 - theta_i) d_i <= tol (|z_i| + 1),
+                // theta_i = d_i / p_i, written without division
+                ok = true;
+#pragma unroll
+                for (int i = 0; i < 6; ++i)
+                    ok = ok && (di[i] < dprev[i]) && (di[i] * di[i] <= k.tol * (fabs(zn[i]) + 1.0) * (dprev[i] - di[i]));
+            }
             double dz = 0.0;
 #pragma unroll
-            for (int i = 0; i < 6; ++i) dz = fmax(dz, fabs(zn[i] - zk[i]));
+            for (int i = 0; i < 6; ++i) {
+                dz = fmax(dz, di[i]);
+                dprev[i] = di[i];
+            }
             if (dz < best_dz) {
                 best_dz = dz;
 #pragma unroll
