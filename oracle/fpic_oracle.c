@@ -496,9 +496,11 @@ static void solve3(double M[3][3], double b[3], double x[3])
  *    (1 - (h/2) J) du = u^[k-1] - u^p, then u^[k] = u^[k-1] - du and
  *    x^[k] = x^p - (h/2) A du.  Only the convergence rate differs: both
  *    stop at the same fixed point.
- * Stop (both forms): the update passes the test of `converged`, or, from
- * the second iteration on, the distance of the new iterate to the solution
- * estimated from the observed contraction does, component by component:
+ * Stop: the update passes the test of `converged`; in the Newton form also
+ * when, from the second iteration on, the distance of the new iterate to the
+ * solution estimated from the observed contraction does, component by
+ * component (the fixed-point form contracts too slowly for that estimate to
+ * save an iteration often):
  * with d_i = |z^[k]_i - z^[k-1]_i|, its previous value p_i and
  * theta_i = d_i / p_i < 1, the a-posteriori bound of a contraction
  * theta_i / (1 - theta_i) d_i (the stopping rule of simplified Newton
@@ -534,7 +536,7 @@ static int step_imr(const or_ctx *c, double h, const double *z0, const double *g
         int ok = converged(zn, zk, c->p->tol);
         double dz = 0.0;
         for (int i = 0; i < 6; ++i) dz = fmax(dz, fabs(zn[i] - zk[i]));
-        if (!ok && k >= 2) {
+        if (c->p->imr_newton && !ok && k >= 2) {
             ok = 1;
             for (int i = 0; i < 6; ++i) {
                 const double di = fabs(zn[i] - zk[i]);

@@ -412,11 +412,11 @@ __global__ void k_order(PushK k)
 }
 
 // Persistent lane-refilling implicit-midpoint solver (Sec. 2.2.2):
-// z^[k] = z^n + dt F((z^n + z^[k-1]) / 2) until two iterates agree to tol,
-// or, from the second iteration on, each component's a-posteriori error
-// bound theta_i / (1 - theta_i) |dz_i| (theta_i the ratio of its last two
-// updates) does; NEWTON: the Newton form of the same iteration
-// (newton_update).
+// z^[k] = z^n + dt F((z^n + z^[k-1]) / 2) until two iterates agree to tol.
+// NEWTON: the Newton form of the same iteration (newton_update), which also
+// stops, from the second iteration on, when each component's a-posteriori
+// error bound theta_i / (1 - theta_i) |dz_i| (theta_i the ratio of its last
+// two updates) passes the tolerance.
 // all_mode: the queue is every particle (pure IMR, guess z^n); otherwise
 // entries come from k_explicit with their trial and sin/cos of th^n (sc0).
 // Each loop trip is one right-hand side per lane; a lane whose solve ends
@@ -428,7 +428,7 @@ __global__ void k_order(PushK k)
 // that has not converged after that many iterations from it restarts once,
 // with the full max_iter budget, from the trial in stg.
 template <int RESTART, bool BATCHED = false, bool NEWTON = false>
-__global__ void __launch_bounds__(128, 3) k_imr(const __grid_constant__ PushK k, int all_mode)
+__global__ void __launch_bounds__(128, NEWTON ? 3 : 4) k_imr(const __grid_constant__ PushK k, int all_mode)
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -522,7 +522,7 @@ __global__ void __launch_bounds__(128, 3) k_imr(const __grid_constant__ PushK k,
             bool ok = true;
 #pragma unroll
             for (int i = 0; i < 6; ++i) ok = ok && (di[i] <= k.tol * (fabs(zn[i]) + 1.0));
-            if (!ok && it >= 1) {
+            if (NEWTON && !ok && it >= 1) {
                 // a-posteriori stop: theta_i / (1 - theta_i) d_i <= tol (|z_i| + 1),
                 // theta_i = d_i / p_i, written without division
                 ok = true;
