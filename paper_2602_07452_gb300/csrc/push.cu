@@ -437,10 +437,11 @@ __global__ void __launch_bounds__(128, NEWTON ? 3 : 4) k_imr(const __grid_consta
     long long p = -1, qi = 0;
     bool exhausted = false, again = false;
     double z0[6], zk[6];
-    // the iterate with the smallest update so far (returned by a solve that
-    // reaches max_iter), one column per thread (blockDim.x <= 128)
-    __shared__ double s_best[6 * 128];
+    // the smallest update so far and its iteration: a solve that reaches
+    // max_iter replays its iterations from the start up to that one (the
+    // sequence is deterministic) and returns that iterate
     double best_dz = INFINITY;
+    int best_it = 0, replay_to = 0;
     double dprev[6];        // the previous iteration's |update| per component (a-posteriori stop)
     double qm = 0.0, s0 = 0.0, c0 = 1.0;
     bool em = false;
@@ -492,6 +493,8 @@ __global__ void __launch_bounds__(128, NEWTON ? 3 : 4) k_imr(const __grid_consta
                         em = (R->has_fields || R->B0field != 0.0) && qm != 0.0;
                         it = 0;
                         best_dz = INFINITY;
+                        best_it = 0;
+                        replay_to = 0;
                     }
                 } else {
                     exhausted = true;
@@ -516,6 +519,14 @@ __global__ void __launch_bounds__(128, NEWTON ? 3 : 4) k_imr(const __grid_consta
 #pragma unroll
             for (int i = 0; i < 6; ++i) zn[i] = fma(k.dt_imp, f[i], z0[i]);
             if (NEWTON) newton_update(J, 0.5 * k.dt_imp, zk, zn);
+            bool done = false, conv = false;
+            if (replay_to) {
+                // replaying an unconverged solve up to its smallest-update iterate
+#pragma unroll
+                for (int i = 0; i < 6; ++i) zk[i] = zn[i];
+                if (++it < replay_to) continue;
+                done = true;
+            } else {
             double di[6];
 #pragma unroll
             for (int i = 0; i < 6; ++i) di[i] = fabs(zn[i] - zk[i]);
@@ -538,8 +549,7 @@ __global__ void __launch_bounds__(128, NEWTON ? 3 : 4) k_imr(const __grid_consta
             }
             if (dz < best_dz) {
                 best_dz = dz;
-#pragma unroll
-                for (int i = 0; i < 6; ++i) s_best[i * blockDim.x + threadIdx.x] = zn[i];
+                best_it = it + 1;
             }
 #pragma unroll
             for (int i = 0; i < 6; ++i) zk[i] = zn[i];
@@ -549,15 +559,33 @@ __global__ void __launch_bounds__(128, NEWTON ? 3 : 4) k_imr(const __grid_consta
                 again = false;
                 n_it += it;
                 it = 0;
+                best_dz = INFINITY;
+                best_it = 0;
 #pragma unroll
                 for (int i = 0; i < 6; ++i) zk[i] = k.stg[(size_t)(STG_TRIAL + i) * k.n + qi];
-            } else if (ok || it >= k.max_iter) {
-                if (!ok) {
-                    // not converged: the iterate with the smallest update (Sec. 2.2.2 gives no policy)
-                    ++n_nc;
+            } else if (ok) {
+                done = conv = true;
+            } else if (it >= k.max_iter) {
+                // not converged (Sec. 2.2.2 gives no policy): the iterate with
+                // the smallest update, the last one or one replayed from the start
+                n_it += it;
+                if (best_it == it) {
+                    done = true;
+                } else {
+                    replay_to = best_it;
+                    it = 0;
 #pragma unroll
-                    for (int i = 0; i < 6; ++i) zk[i] = s_best[i * blockDim.x + threadIdx.x];
+                    for (int i = 0; i < 6; ++i)
+                        zk[i] = all_mode ? z0[i]
+                              : RESTART ? k.stg[(size_t)((again ? STG_GUESS : STG_TRIAL) + i) * k.n + qi]
+                                        : k.guess[(size_t)i * k.n + p];
                 }
+            }
+            }
+            if (done) {
+                const int its_done = conv ? it : k.max_iter;
+                if (conv) n_it += it;
+                else ++n_nc;
                 if (k.record && k.featS) {
                     // corrector form: row = queue slot, (gap to the trial - leading-order gap) / (s_i oscale_i)
                     float* t = k.recT + 16 * qi;
@@ -569,22 +597,21 @@ __global__ void __launch_bounds__(128, NEWTON ? 3 : 4) k_imr(const __grid_consta
                         t[i] = sc[i] > 0.f ? (float)fmin(4.0, fmax(-4.0, g)) : 0.f;
                     }
                     t[6] = 0.f;
-                    t[7] = (float)(it - 8) * 0.25f;
+                    t[7] = (float)(its_done - 8) * 0.25f;
                     t[8] = 0.f;
                 } else if (k.record) {
                     float* t = k.recT + 16 * p;
 #pragma unroll
                     for (int i = 0; i < 6; ++i) t[i] = (float)((zk[i] - z0[i]) / k.inc_scale[i]);
                     t[6] = 0.f;
-                    t[7] = (float)(it - 8) * 0.25f;
+                    t[7] = (float)(its_done - 8) * 0.25f;
                     t[8] = 0.f;
                 } else {
 #pragma unroll
                     for (int i = 0; i < 6; ++i) k.guess[(size_t)i * k.n + p] = zk[i];
-                    if (k.its && !all_mode) k.its[qi] = (uint8_t)min(it, 255);
-                    else k.P.iters[p] = (uint8_t)min(it, 255);
+                    if (k.its && !all_mode) k.its[qi] = (uint8_t)min(its_done, 255);
+                    else k.P.iters[p] = (uint8_t)min(its_done, 255);
                 }
-                n_it += it;
                 p = -1;
             }
         }
