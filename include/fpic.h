@@ -78,7 +78,9 @@ typedef struct {
  *   implicit  : FPIC_IMR or FPIC_HAM, the implicit partner of the hybrid
  *   thr       : Hyb2: Htilde_max; Hyb1: (d Htilde / dt)_max   (Sec. 3.1.2)
  *   tol       : implicit stop: max_i |dz_i| / (|z_i| + 1) <= tol
- *   max_iter  : implicit iteration cap (1..255)
+ *   max_iter  : implicit iteration cap (1..255); an IMR solve that reaches
+ *               it returns the iterate whose update max_i |dz_i| was the
+ *               smallest (the earliest on ties) and counts in n_notconv
  *   r_max     : outer removal radius; the inner one is the horizon r_+
  *   dg_eps    : increment below which the discrete gradient takes the
  *               analytic partial (App. D uses 1e-10)
@@ -109,8 +111,12 @@ typedef struct {
  *               1: the Newton iteration the section names, with the Newton
  *               matrix 1 - (dt/2) dF reduced to the momentum columns of dF
  *               (d(dx/dt)/du and the magnetic force's d(du/dt)/du, both in
- *               closed form); same fixed point and stop test, about half
- *               the iterations for charged particles.  Any nonzero = 1. */
+ *               closed form); same fixed point.  It also stops, from its
+ *               second iteration on, when every component's a-posteriori
+ *               error bound theta_i / (1 - theta_i) |dz_i| (theta_i the
+ *               ratio of its last two updates) is within tol (|z_i| + 1):
+ *               about a third of the iterations of the fixed-point update
+ *               for charged particles.  Any nonzero = 1. */
 typedef struct {
     double dt;
     int scheme;
