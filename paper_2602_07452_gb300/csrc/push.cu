@@ -527,60 +527,60 @@ __global__ void __launch_bounds__(128, NEWTON ? 3 : 4) k_imr(const __grid_consta
                 if (++it < replay_to) continue;
                 done = true;
             } else {
-            double di[6];
+                double di[6];
 #pragma unroll
-            for (int i = 0; i < 6; ++i) di[i] = fabs(zn[i] - zk[i]);
-            bool ok = true;
+                for (int i = 0; i < 6; ++i) di[i] = fabs(zn[i] - zk[i]);
+                bool ok = true;
 #pragma unroll
-            for (int i = 0; i < 6; ++i) ok = ok && (di[i] <= k.tol * (fabs(zn[i]) + 1.0));
-            if (NEWTON && !ok && it >= 1) {
-                // a-posteriori stop: theta_i / (1 - theta_i) d_i <= tol (|z_i| + 1),
-                // theta_i = d_i / p_i, written without division
-                ok = true;
-#pragma unroll
-                for (int i = 0; i < 6; ++i)
-                    ok = ok && (di[i] < dprev[i]) && (di[i] * di[i] <= k.tol * (fabs(zn[i]) + 1.0) * (dprev[i] - di[i]));
-            }
-            double dz = 0.0;
-#pragma unroll
-            for (int i = 0; i < 6; ++i) {
-                dz = fmax(dz, di[i]);
-                dprev[i] = di[i];
-            }
-            if (dz < best_dz) {
-                best_dz = dz;
-                best_it = it + 1;
-            }
-#pragma unroll
-            for (int i = 0; i < 6; ++i) zk[i] = zn[i];
-            ++it;
-            if (RESTART && !ok && k.restart_after > 0 && it >= min(k.max_iter, k.restart_after) && again) {
-                // the corrected start did not converge: the plain trial is the fallback
-                again = false;
-                n_it += it;
-                it = 0;
-                best_dz = INFINITY;
-                best_it = 0;
-#pragma unroll
-                for (int i = 0; i < 6; ++i) zk[i] = k.stg[(size_t)(STG_TRIAL + i) * k.n + qi];
-            } else if (ok) {
-                done = conv = true;
-            } else if (it >= k.max_iter) {
-                // not converged (Sec. 2.2.2 gives no policy): the iterate with
-                // the smallest update, the last one or one replayed from the start
-                n_it += it;
-                if (best_it == it) {
-                    done = true;
-                } else {
-                    replay_to = best_it;
-                    it = 0;
+                for (int i = 0; i < 6; ++i) ok = ok && (di[i] <= k.tol * (fabs(zn[i]) + 1.0));
+                if (NEWTON && !ok && it >= 1) {
+                    // a-posteriori stop: theta_i / (1 - theta_i) d_i <= tol (|z_i| + 1),
+                    // theta_i = d_i / p_i, written without division
+                    ok = true;
 #pragma unroll
                     for (int i = 0; i < 6; ++i)
-                        zk[i] = all_mode ? z0[i]
-                              : RESTART ? k.stg[(size_t)((again ? STG_GUESS : STG_TRIAL) + i) * k.n + qi]
-                                        : k.guess[(size_t)i * k.n + p];
+                        ok = ok && (di[i] < dprev[i]) && (di[i] * di[i] <= k.tol * (fabs(zn[i]) + 1.0) * (dprev[i] - di[i]));
                 }
-            }
+                double dz = 0.0;
+#pragma unroll
+                for (int i = 0; i < 6; ++i) {
+                    dz = fmax(dz, di[i]);
+                    dprev[i] = di[i];
+                }
+                if (dz < best_dz) {
+                    best_dz = dz;
+                    best_it = it + 1;
+                }
+#pragma unroll
+                for (int i = 0; i < 6; ++i) zk[i] = zn[i];
+                ++it;
+                if (RESTART && !ok && k.restart_after > 0 && it >= min(k.max_iter, k.restart_after) && again) {
+                    // the corrected start did not converge: the plain trial is the fallback
+                    again = false;
+                    n_it += it;
+                    it = 0;
+                    best_dz = INFINITY;
+                    best_it = 0;
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) zk[i] = k.stg[(size_t)(STG_TRIAL + i) * k.n + qi];
+                } else if (ok) {
+                    done = conv = true;
+                } else if (it >= k.max_iter) {
+                    // not converged (Sec. 2.2.2 gives no policy): the iterate with
+                    // the smallest update, the last one or one replayed from the start
+                    n_it += it;
+                    if (best_it == it) {
+                        done = true;
+                    } else {
+                        replay_to = best_it;
+                        it = 0;
+#pragma unroll
+                        for (int i = 0; i < 6; ++i)
+                            zk[i] = all_mode ? z0[i]
+                                  : RESTART ? k.stg[(size_t)((again ? STG_GUESS : STG_TRIAL) + i) * k.n + qi]
+                                            : k.guess[(size_t)i * k.n + p];
+                    }
+                }
             }
             if (done) {
                 const int its_done = conv ? it : k.max_iter;
