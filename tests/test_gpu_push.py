@@ -119,6 +119,22 @@ def _one_step(F, ctx, g, Fo, z, q, scheme, dt, thr=1e-12, implicit=None, B0pot=1
 _A = {}
 
 
+def _check_iterations(ig, io, newton):
+    """Implicit iteration counts, GPU against oracle.  Fixed-point form: the
+    same successive-update stop on both sides, so the counts agree except
+    where the last update sits at the tolerance within rounding (at most
+    1 % of the solves, by one iteration).  Newton form: the kernel also
+    stops when its a-posteriori bound passes the tolerance, which the
+    oracle does not use; it stops no later than the oracle (up to the same
+    rounding) and usually one iteration earlier."""
+    d = io.astype(int) - ig.astype(int)
+    if not newton:
+        assert np.abs(d).max() <= 1 and (d != 0).mean() <= 0.01, (np.abs(d).max(), (d != 0).mean())
+    else:
+        assert d.min() >= -1 and d.max() <= 2 and (d < 0).mean() <= 0.01, (d.min(), d.max(), (d < 0).mean())
+        assert d.mean() > 0.3, d.mean()
+
+
 def _mk(F, a, g=None):
     ctx = _ctx(F, a, g)
     _A[id(ctx)] = a
@@ -171,8 +187,7 @@ def test_charged_push_one_step_matches_oracle(F, scheme, newton):
     far = rel > 1e-11
     assert np.array_equal(cg[far & (ao == 1)], cell_o[far & (ao == 1)])
     if scheme in ("IMR",) or scheme.startswith("HYB"):
-        imp = so == 1
-        assert np.abs(ig[imp].astype(int) - io[imp].astype(int)).max() <= 1
+        _check_iterations(ig[so == 1], io[so == 1], newton)
 
 
 @pytest.mark.parametrize("scheme", ["RK4", "HAM", "HYB2"])
@@ -553,7 +568,7 @@ def test_newton_imr_mixed_charges_is_deterministic_and_matches_oracle(F):
     zg, Hg, ag, sg, ig, cg = outs[0]
     assert np.array_equal(ag, ao) and nc == 0
     assert_state_close(zg, zo, TOL)
-    assert np.abs(ig.astype(int) - io.astype(int)).max() <= 1
+    _check_iterations(ig, io, True)
     assert io[q == 0].mean() < io[q != 0].mean()
 
 
@@ -563,7 +578,9 @@ def test_unconverged_solve_returns_smallest_update_iterate(F, newton):
     q/m = 100), every solve stops at max_iter = 4 and returns the iterate
     with the smallest update, as the oracle does: states within 1e-12 of the
     oracle, every particle counted as not converged (fixed-point form).  The
-    Newton form converges for some of them; either way GPU and oracle agree."""
+    Newton form converges for some of them (the kernel, with its a-posteriori
+    stop, for at least as many as the oracle); either way GPU and oracle
+    agree."""
     a = 0.9
     g = I.wald_grid(64, a)
     Fo = O.wald_on_grid(a, 1.0, g)
@@ -574,7 +591,11 @@ def test_unconverged_solve_returns_smallest_update_iterate(F, newton):
     zg, Hg, ag, sg, ig, cg = to_np(p)
     if not newton:
         assert nc == len(q)
-    assert st["n_notconv"] == nc
+        assert st["n_notconv"] == nc
+    else:
+        # the kernel's a-posteriori stop accepts some solves the oracle's
+        # successive-update test runs to the cap: those states still agree
+        assert 0 < st["n_notconv"] <= nc
     ok = (ao == 1) & (ag == 1)
     assert ok.mean() > 0.9
     assert_state_close(zg, zo, TOL, ok)

@@ -680,12 +680,13 @@ def test_imr_unconverged_solve_returns_smallest_update_iterate(newton):
 
 
 @pytest.mark.parametrize("newton", [False, True])
-def test_imr_a_posteriori_stop_is_within_tolerance(newton):
-    """The IMR's stop from the observed contraction accepts an iterate only
-    when theta / (1 - theta) times its update passes the tolerance: the
-    accepted states lie within a few tol (|z| + 1) of the solution iterated
-    to the end (tol = 0: every iteration until max_iter, the smallest-update
-    iterate returned), and the Newton form needs fewer than 3.7 on average."""
+def test_imr_successive_update_stop_is_within_tolerance(newton):
+    """The IMR iterates to round-off (Sec. 2.2.2): a solve stops when its
+    last update is within tol (|z| + 1), in both forms, and the state it
+    returns lies within a few tol (|z| + 1) of the solution iterated to the
+    end (tol = 0: every iteration until max_iter, the smallest-update
+    iterate returned); from z^n the Newton form needs under half the
+    iterations of the fixed-point form (4.4 against 10)."""
     a, B0 = 0.9, 1.0
     z0, qm = _wald_plasma(500, a, seed=19)
     H0, _, D0 = O.hamiltonian(1.0, a, B0, z0, qm)
@@ -701,5 +702,11 @@ def test_imr_a_posteriori_stop_is_within_tolerance(newton):
     zr, _, _ = solve(0.0, 60)
     assert nc == 0
     assert (np.abs(z - zr) / (np.abs(zr) + 1)).max() <= 5e-14
+    # the stop is the first iterate whose update passes the test: capped one
+    # iteration earlier, every solve is reported unconverged
+    _, _, nc1 = solve(1e-14, int(its.min()) - 1)
+    assert nc1 == len(z0)
     if newton:
-        assert its.mean() < 3.7 and its.max() <= 6, (its.mean(), its.max())
+        assert its.mean() < 5.0 and its.max() <= 6, (its.mean(), its.max())
+    else:
+        assert its.mean() > 8.0
