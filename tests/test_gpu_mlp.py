@@ -43,9 +43,10 @@ def test_tensor_core_gemm_matches_torch(F, M_, N, K):
 
 
 def test_fused_forward_matches_oracle(F):
-    """Fused tcgen05 forward of 5000 samples (39 tiles + a ragged tail) equals
-    the oracle's bf16-operand / FP32-accumulate network within bf16
-    accuracy."""
+    """Fused tcgen05 forward of 5000 samples (39 tiles + a ragged tail) of a
+    random network equals the oracle's bf16-operand / FP32-accumulate
+    network to FP32 rounding, except for samples where a different
+    summation order flips one bf16 activation rounding."""
     P = M.init_params(3)
     rng = np.random.default_rng(4)
     B = 5000
@@ -59,10 +60,44 @@ def test_fused_forward_matches_oracle(F):
     torch.cuda.synchronize()
     assert net.status() == 0
     y = Y[:, :9].double().cpu().numpy()
-    scale = np.abs(y_or).max()
-    err = np.abs(y - y_or)
-    assert err.max() <= 2e-2 * scale, err.max() / scale
-    assert err.mean() <= 2e-3 * scale
+    err = np.abs(y - y_or) / np.abs(y_or).max()
+    q = np.quantile(err, [0.5, 0.99])
+    print("fused forward vs oracle, relative to scale: median %.2e, 99%% %.2e, max %.2e" % (q[0], q[1], err.max()))
+    # FP32 sums in another order: most outputs agree to FP32 rounding; a
+    # sample whose bf16 activation rounding flipped moves by ~1e-4 of scale
+    assert q[0] <= 1e-6 and q[1] <= 1e-3 and err.max() <= 5e-3, (q, err.max())
+
+
+def test_fused_forward_bit_exact_on_integer_network(F):
+    """Small-integer weights, biases and inputs (sparse rows of +-1, +-2):
+    every product and partial sum is an integer below 2^24, so the
+    tensor-core forward has exactly one correct answer whatever its
+    summation order, and it equals the oracle's bit for bit (bf16 rounding
+    of activations above 256 included): 3000 samples, 23 tiles and a
+    ragged tail."""
+    rng = np.random.default_rng(23)
+    parts = []
+    for l in range(4):
+        ni, no = M.DIMS[l], M.DIMS[l + 1]
+        W = np.zeros((no, ni))
+        for o in range(no):
+            cols = rng.choice(ni, min(ni, 6), replace=False)
+            W[o, cols] = rng.choice([-2, -1, 1, 2], len(cols))
+        parts += [W.ravel(), rng.integers(-3, 4, no).astype(float)]
+    P = np.concatenate(parts)
+    B = 3000
+    X = rng.integers(-8, 9, (B, 14)).astype(float)
+    y_or = M.forward(P, X, mode=0)
+    net = F.MLP()
+    net.set_params(torch.tensor(P, dtype=torch.float32, device="cuda"))
+    Xg = torch.zeros(B, 16, dtype=torch.float32, device="cuda")
+    Xg[:, :14] = torch.tensor(X, dtype=torch.float32)
+    Y = net.forward(Xg)
+    torch.cuda.synchronize()
+    assert net.status() == 0
+    y = Y[:, :9].double().cpu().numpy()
+    assert np.abs(y_or).max() > 256
+    assert np.array_equal(y, y_or), np.abs(y - y_or).max()
 
 
 def _batch(B, seed):

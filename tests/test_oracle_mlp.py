@@ -65,3 +65,66 @@ def test_bf16_model_close_to_exact_model():
     y0 = M.forward(P, x, 0)
     y1 = M.forward(P, x, 1)
     assert np.abs(y0 - y1).max() < 3e-2 * np.abs(y1).max()
+
+
+def _torch_forward(P, x, bf16):
+    """The 14-128-128-128-9 ReLU network written with torch.nn.functional:
+    y = W4 relu(W3 relu(W2 relu(W1 x + b1) + b2) + b3) + b4, weights
+    [out][in].  bf16: the tensor-core precision model (every GEMM operand
+    rounded to bfloat16 by torch's own conversion, FP32 products and sums,
+    FP32 biases); else FP64 throughout."""
+    F = torch.nn.functional
+    dt = torch.float32 if bf16 else torch.float64
+    rnd = (lambda t: t.to(torch.bfloat16).to(dt)) if bf16 else (lambda t: t)
+    h = rnd(torch.tensor(x, dtype=dt))
+    for l, (W, b) in enumerate(M.unpack(np.asarray(P, np.float64))):
+        z = F.linear(h, rnd(torch.tensor(W, dtype=dt)), torch.tensor(b, dtype=dt))
+        h = z if l == 3 else rnd(F.relu(z))
+    return h.double().numpy()
+
+
+def test_forward_fp64_equals_torch_network():
+    """The oracle forward pass in its exact mode is the network evaluated
+    layer by layer by torch (FP64): any dropped bias, transposed weight,
+    wrong layer order or misplaced ReLU fails this at rounding level."""
+    P = M.init_params(21)
+    x, _, _, _ = _batch(257, 22)
+    y = M.forward(P, x, 1)
+    ref = _torch_forward(P, x, bf16=False)
+    assert np.abs(y - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_forward_bf16_exact_on_integer_network():
+    """With small-integer weights, biases and inputs (sparse rows of +-1 and
+    +-2) every product and partial sum is an integer below 2^24, so the
+    bf16-operand / FP32-accumulate forward has one correct answer whatever
+    the summation order; the oracle's mode 0 equals torch's bf16-rounded
+    FP32 network bit for bit, activations above 256 rounded to bf16
+    included."""
+    rng = np.random.default_rng(23)
+    parts = []
+    for l in range(4):
+        ni, no = M.DIMS[l], M.DIMS[l + 1]
+        W = np.zeros((no, ni))
+        for o in range(no):
+            cols = rng.choice(ni, min(ni, 6), replace=False)
+            W[o, cols] = rng.choice([-2, -1, 1, 2], len(cols))
+        parts += [W.ravel(), rng.integers(-3, 4, no).astype(float)]
+    P = np.concatenate(parts)
+    x = rng.integers(-8, 9, (300, 14)).astype(float)
+    y = M.forward(P, x, 0)
+    ref = _torch_forward(P, x, bf16=True)
+    assert np.abs(y).max() > 256 and np.array_equal(y, ref)
+
+
+def test_forward_bf16_equals_torch_network():
+    """Random network and inputs in the bf16 model: the oracle's sequential
+    FP32 sums against torch's own FP32 linear layers agree elementwise to
+    1e-6 of the output scale (an order-of-summation difference could flip
+    a bf16 activation rounding; none does here)."""
+    P = M.init_params(25)
+    x, _, _, _ = _batch(512, 26)
+    y = M.forward(P, x, 0)
+    ref = _torch_forward(P, x, bf16=True)
+    err = np.abs(y - ref) / np.abs(ref).max()
+    assert err.max() <= 1e-6, err.max()
