@@ -229,10 +229,12 @@ typedef struct {
  * favour of each run's).  The run table is staged through pinned memory
  * owned by runs[0].ctx, so after one call outside capture the call can be
  * captured in a CUDA graph and replayed.  A captured graph holds the
- * addresses of the context's scratch: a later call on the same context that
- * needs more scratch (more particles, or the learned push) reallocates it and
- * leaves graphs captured before pointing at freed memory -- capture after the
- * largest call, and capture again after any larger one.  Errors: FPIC_EINVAL,
+ * addresses of the context's scratch; a later call that needs more scratch
+ * (more particles, or the learned push) allocates a larger buffer and keeps
+ * the superseded one until fpic_destroy, so graphs captured earlier stay
+ * valid for the context's lifetime (the same holds for every library-owned
+ * buffer that grows: coefficients, run table, node and metric tables).
+ * Errors: FPIC_EINVAL,
  * FPIC_ENOMEM, FPIC_ECUDA; FPIC_ENOTCONVERGED as fpic_push. */
 int fpic_push_batched(const fpic_run *runs, int nruns, fpic_particles *p, const fpic_push_params *prm,
                       fpic_push_stats *stats, void *stream);
@@ -255,7 +257,7 @@ int fpic_push_host(fpic_ctx *ctx, fpic_particles *host_p, const double *const fi
 /* Fixed capacity of fpic_push_noalloc's scratch, in particles. */
 #define FPIC_NOALLOC_MAX_PARTICLES 65536
 
-/* Allocation-free variant of fpic_push for geodesic (field-free) pushes.
+/* Allocation-free variant of fpic_push for pushes without grid fields.
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate device memory -- code whose device memory belongs to a
  * host framework or custom allocator that forbids direct cudaMalloc,
@@ -264,19 +266,23 @@ int fpic_push_host(fpic_ctx *ctx, fpic_particles *host_p, const double *const fi
  * no context (M, a given directly), calls no cudaMalloc, cudaFree or other
  * allocating routine, and keeps its scratch (implicit guesses, queue of
  * rejected particles, counters) in one file-scope device array of fixed
- * size, FPIC_NOALLOC_MAX_PARTICLES * 72 + 256 bytes (about 4.7 MB), that
- * every device which loads the library holds until the process exits.
- *   p, prm, stats, stream : as fpic_push (no fields; prm->guess must be
- *     NULL).  Neutral and charged particles move on geodesics of the Kerr
- *     metric (M, a).
+ * size, FPIC_NOALLOC_MAX_PARTICLES * 72 + 256 = 4718848 bytes, that every
+ * device which loads the library holds until the process exits.
+ *   p, prm, stats, stream : as fpic_push without fields (prm->guess must be
+ *     NULL).  Neutral particles move on geodesics of the Kerr metric
+ *     (M, a); with prm->B0field != 0 (M = 1) charged particles feel the
+ *     analytic Wald field as in fpic_push (the discrete-gradient partner
+ *     then works in canonical momenta).
  *   Errors: FPIC_EINVAL if p->n > FPIC_NOALLOC_MAX_PARTICLES (nothing is
  *     launched) or for the argument errors of fpic_push; FPIC_ECUDA.
- * The first call on each device looks up the device address of the
- * scratch array (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.  Every call on a device shares the
- * one array and the counters are cleared at the start of each call, so
- * calls whose work overlaps on the GPU (other streams, other threads)
- * race: serialise them on one stream.  Results equal fpic_push's. */
+ * The first call on each device (and the first under a new CUDA context,
+ * e.g. after cudaDeviceReset) looks up the device address of the scratch
+ * array (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  The look-up is guarded by a mutex, so
+ * host threads may make their first calls concurrently.  Every call on a
+ * device shares the one array and the counters are cleared at the start of
+ * each call, so calls whose work overlaps on the GPU (other streams, other
+ * threads) race: serialise them on one stream.  Results equal fpic_push's. */
 int fpic_push_noalloc(double M, double a, fpic_particles *p, const fpic_push_params *prm,
                       fpic_push_stats *stats, void *stream);
 

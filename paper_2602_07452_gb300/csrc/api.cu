@@ -32,11 +32,18 @@ int check_cuda(cudaError_t e, const char* what)
     return set_error(FPIC_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+void retire(fpic_ctx* c, void** p, bool host)
+{
+    if (*p) (host ? c->retired_host : c->retired_dev).push_back(*p);
+    *p = nullptr;
+}
+
+// Scratch grows and never shrinks; the superseded buffer is retired, not
+// freed, so a graph captured over it stays valid until fpic_destroy.
 int ensure_scratch(fpic_ctx* c, size_t bytes)
 {
     if (bytes <= c->scratch_bytes) return 0;
-    if (c->d_scratch) FPIC_CUDA(cudaFree(c->d_scratch));
-    c->d_scratch = nullptr;
+    retire(c, &c->d_scratch);
     c->scratch_bytes = 0;
     size_t b = bytes + bytes / 8;
     FPIC_CUDA(cudaMalloc(&c->d_scratch, b));
@@ -47,8 +54,7 @@ int ensure_scratch(fpic_ctx* c, size_t bytes)
 int ensure_scratch2(fpic_ctx* c, size_t bytes)
 {
     if (bytes <= c->scratch2_bytes) return 0;
-    if (c->d_scratch2) FPIC_CUDA(cudaFree(c->d_scratch2));
-    c->d_scratch2 = nullptr;
+    retire(c, &c->d_scratch2);
     c->scratch2_bytes = 0;
     size_t b = bytes + bytes / 8;
     FPIC_CUDA(cudaMalloc(&c->d_scratch2, b));
@@ -290,6 +296,8 @@ extern "C" void fpic_destroy(fpic_ctx* c)
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     if (c->clean_exec) cudaGraphExecDestroy(c->clean_exec);
     if (c->d_fcoef) cudaFree(c->d_fcoef);
+    for (void* q : c->retired_dev) cudaFree(q);
+    for (void* q : c->retired_host) cudaFreeHost(q);
     delete c;
 }
 
@@ -329,8 +337,7 @@ extern "C" int fpic_set_grid(fpic_ctx* c, int Nr, int Nth, const double* rn, con
     inv(rh, Nr, p + o_irh);
     inv(tn, Nth + 1, p + o_itn);
     inv(th, Nth, p + o_ith);
-    if (c->d_nodes) FPIC_CUDA(cudaFree(c->d_nodes));
-    c->d_nodes = nullptr;
+    retire(c, (void**)&c->d_nodes);
     FPIC_CUDA(cudaMalloc(&c->d_nodes, tot * sizeof(double)));
     FPIC_CUDA(cudaMemcpy(c->d_nodes, p, tot * sizeof(double), cudaMemcpyHostToDevice));
     c->h_nodes.assign((const char*)p, (o_irn) * sizeof(double));

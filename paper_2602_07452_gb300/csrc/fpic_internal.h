@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/fpic.h"
 #include "fpic_device.cuh"
@@ -57,6 +58,11 @@ struct fpic_ctx {
     cudaGraphExec_t clean_exec = nullptr;
     const void* clean_key_base = nullptr;
     int clean_key_Nr = 0, clean_key_Nth = 0, clean_key_iter = -1;
+    // buffers superseded by a larger one (scratch, coefficients, run table,
+    // node and metric tables): a CUDA graph captured earlier may still
+    // address them, so they are freed only by fpic_destroy
+    std::vector<void*> retired_dev;
+    std::vector<void*> retired_host;
 };
 
 namespace fpic {
@@ -70,6 +76,9 @@ int check_cuda(cudaError_t e, const char* what);
 int ensure_scratch(fpic_ctx* c, size_t bytes);
 int ensure_scratch2(fpic_ctx* c, size_t bytes);
 int ensure_copy_stream(fpic_ctx* c);
+// Moves a superseded buffer to the context's retired list (nothing is freed
+// before fpic_destroy) and clears the pointer.
+void retire(fpic_ctx* c, void** p, bool host = false);
 bool particles_ok(const fpic_particles* p, bool need_state);
 int mlp_forward_dev(fpic_mlp* m, const float* X, float* Y, long long B, cudaStream_t s);
 struct MlpDev;

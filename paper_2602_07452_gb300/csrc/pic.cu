@@ -110,8 +110,7 @@ int build_metric_tables(fpic_ctx* c)
 {
     const size_t sz = (size_t)(c->Nr + 1) * c->ld;
     const size_t tot = (size_t)MT_N * sz + 2 * (size_t)(c->Nth + 1) + 2 * (size_t)c->Nth;
-    if (c->d_metric) FPIC_CUDA(cudaFree(c->d_metric));
-    c->d_metric = nullptr;
+    retire(c, (void**)&c->d_metric);
     FPIC_CUDA(cudaMalloc(&c->d_metric, tot * sizeof(double)));
     c->metric_stride = sz;
     dim3 grid(1, c->Nr + 1);

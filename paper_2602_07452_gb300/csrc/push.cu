@@ -12,9 +12,11 @@
 //               counts does not idle the FP64 pipe.
 //   k_dg        discrete-gradient Hamiltonian scheme (geodesics), one thread
 //               per queued particle.
+#include <cuda.h>
 #include <math.h>
 #include <string.h>
 
+#include <mutex>
 #include <vector>
 
 #include "fpic_internal.h"
@@ -1108,8 +1110,7 @@ static int field_coefs(fpic_ctx* c, const double* const fields[6], RunK& R, cuda
     const size_t sz = (size_t)(c->Nr + 1) * c->ld;
     const size_t bytes = 6 * 4 * sz * sizeof(double);
     if (c->fcoef_bytes < bytes) {
-        if (c->d_fcoef) FPIC_CUDA(cudaFree(c->d_fcoef));
-        c->d_fcoef = nullptr;
+        retire(c, &c->d_fcoef);
         c->fcoef_bytes = 0;
         for (int i = 0; i < 6; ++i) c->fcoef_src[i] = nullptr;
         FPIC_CUDA(cudaMalloc(&c->d_fcoef, bytes));
@@ -1406,23 +1407,71 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 // Per-device set-up cache: the device address of g_noalloc_scratch (the host
 // symbol is only a stand-in and must never be passed to a kernel) and the
-// SM count.  Filled by the first call on each device.
+// SM count, filled by the first call on each device and tagged with the ID of
+// the CUDA context it was looked up in.  A later call under another context
+// (after cudaDeviceReset, or from a driver-API context of its own) repeats
+// the look-up, since the module and its array may then sit at another
+// address.  One mutex guards the cache: host threads making their first calls
+// at the same time see either no entry or a complete one.
 constexpr int kNoAllocMaxDevices = 64;
-static void* g_noalloc_dev_ptr[kNoAllocMaxDevices];
-static int g_noalloc_sms[kNoAllocMaxDevices];
+struct NoAllocSlot {
+    unsigned long long ctx_id;
+    void* ptr;
+    int sms;
+};
+static NoAllocSlot g_noalloc_slot[kNoAllocMaxDevices];
+static std::mutex g_noalloc_mu;
 
-static int noalloc_setup(int dev)
+// cuCtxGetCurrent / cuCtxGetId through the runtime's driver entry points (the
+// library does not link the driver library directly).
+typedef CUresult (*PfnCtxGetCurrent)(CUcontext*);
+typedef CUresult (*PfnCtxGetId)(CUcontext, unsigned long long*);
+
+static int current_ctx_id(int dev, unsigned long long* id)
+{
+    static PfnCtxGetCurrent get_cur = nullptr;
+    static PfnCtxGetId get_id = nullptr;
+    if (!get_cur || !get_id) {
+        void *f0 = nullptr, *f1 = nullptr;
+        cudaDriverEntryPointQueryResult q0, q1;
+        FPIC_CUDA(cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000, cudaEnableDefault, &q0));
+        FPIC_CUDA(cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault, &q1));
+        if (q0 != cudaDriverEntryPointSuccess || q1 != cudaDriverEntryPointSuccess || !f0 || !f1)
+            return set_error(FPIC_ECUDA, "fpic_push_noalloc: driver entry points cuCtxGetCurrent/cuCtxGetId not found");
+        get_cur = (PfnCtxGetCurrent)f0;
+        get_id = (PfnCtxGetId)f1;
+    }
+    CUcontext ctx = nullptr;
+    if (get_cur(&ctx) != CUDA_SUCCESS || !ctx) {
+        // no context bound to this thread yet: bind the device's primary one
+        FPIC_CUDA(cudaSetDevice(dev));
+        if (get_cur(&ctx) != CUDA_SUCCESS || !ctx)
+            return set_error(FPIC_ECUDA, "fpic_push_noalloc: no current CUDA context on device %d", dev);
+    }
+    if (get_id(ctx, id) != CUDA_SUCCESS) return set_error(FPIC_ECUDA, "fpic_push_noalloc: cuCtxGetId failed");
+    return 0;
+}
+
+static int noalloc_setup(int dev, void** ptr_out, int* sms_out)
 {
     if (dev < 0 || dev >= kNoAllocMaxDevices) return set_error(FPIC_EINVAL, "fpic_push_noalloc: device id %d out of range", dev);
-    if (g_noalloc_dev_ptr[dev]) return 0;
-    void* ptr = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (e != cudaSuccess || !ptr)
-        return set_error(FPIC_ECUDA, "fpic_push_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-    int sms = 0;
-    FPIC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    g_noalloc_sms[dev] = sms;
-    g_noalloc_dev_ptr[dev] = ptr;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    unsigned long long id = 0;
+    int rc = current_ctx_id(dev, &id);
+    if (rc) return rc;
+    NoAllocSlot& sl = g_noalloc_slot[dev];
+    if (!sl.ptr || sl.ctx_id != id) {
+        void* ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr)
+            return set_error(FPIC_ECUDA, "fpic_push_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        int sms = 0;
+        FPIC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        if (sms < 1) return set_error(FPIC_ECUDA, "fpic_push_noalloc: device %d reports %d SMs", dev, sms);
+        sl = NoAllocSlot{id, ptr, sms};
+    }
+    *ptr_out = sl.ptr;
+    *sms_out = sl.sms;
     return 0;
 }
 
@@ -1449,13 +1498,14 @@ extern "C" int fpic_push_noalloc(double M, double a, fpic_particles* p, const fp
     if (prm->max_iter < 1 || prm->max_iter > 255) return set_error(FPIC_EINVAL, "fpic_push_noalloc: max_iter must be in [1, 255]");
     if (!(prm->tol >= 0.0)) return set_error(FPIC_EINVAL, "fpic_push_noalloc: tol must be >= 0");
     if (prm->guess) return set_error(FPIC_EINVAL, "fpic_push_noalloc: learned guesses are not supported here");
-    int dev = 0;
+    int dev = 0, sms = 0;
+    void* scratch = nullptr;
     FPIC_CUDA(cudaGetDevice(&dev));
-    int rc = noalloc_setup(dev);
+    int rc = noalloc_setup(dev, &scratch, &sms);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     const long long n = p->n;
-    unsigned char* base = (unsigned char*)g_noalloc_dev_ptr[dev];
+    unsigned char* base = (unsigned char*)scratch;
     PushK k{};
     k.run.bh = BH{M, a, a * a, 2.0 * M};
     k.run.has_grid = 0;
@@ -1490,7 +1540,7 @@ extern "C" int fpic_push_noalloc(double M, double a, fpic_particles* p, const fp
     }
     const int TB = 128;
     const unsigned nb = (unsigned)((n + TB - 1) / TB);
-    const unsigned persist = (unsigned)g_noalloc_sms[dev] * 8u;
+    const unsigned persist = (unsigned)sms * 8u;
     cudaEvent_t* ev = prm->events ? (cudaEvent_t*)prm->events : nullptr;
     if (stats) k_count_alive<<<persist, 256, 0, s>>>(k.P, n, k.cnt);
     if (ev) FPIC_CUDA(cudaEventRecord(ev[0], s));
@@ -2113,10 +2163,8 @@ static int push_batched(const fpic_run* runs, int nruns, fpic_mlp* m, fpic_parti
     cudaStream_t s = (cudaStream_t)stream;
     const long long n = p->n;
     if (c->runs_cap < nruns) {
-        if (c->d_runs) FPIC_CUDA(cudaFree(c->d_runs));
-        if (c->h_runs) FPIC_CUDA(cudaFreeHost(c->h_runs));
-        c->d_runs = nullptr;
-        c->h_runs = nullptr;
+        retire(c, &c->d_runs);
+        retire(c, &c->h_runs, true);
         c->runs_cap = 0;
         FPIC_CUDA(cudaMalloc(&c->d_runs, sizeof(RunK) * nruns));
         FPIC_CUDA(cudaMallocHost(&c->h_runs, sizeof(RunK) * nruns));

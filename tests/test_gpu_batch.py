@@ -143,3 +143,48 @@ def test_batched_learned_corrector_equals_separate(newton):
     O.push(po, zo, qs[k], H0s[k], D0s[k], Ho, np.ones(RUNS[k][2], np.uint8), grids[k], Fos[k])
     err = (np.abs(zb[sl] - zo) / (np.abs(zo) + 1)).max()
     assert err <= 1e-12, err
+
+
+def test_graph_survives_a_larger_call_on_the_same_context():
+    """A plain batched step is captured in a CUDA graph; then a learned
+    batched call on the same contexts needs more scratch, and the library
+    allocates a larger buffer (device free memory drops) while keeping the
+    superseded one alive until fpic_destroy; replaying the first graph
+    afterwards gives bitwise the particles of an uncaptured plain step from
+    the same state."""
+    cuda_or_skip()
+    F = fpic()
+    ctxs, flds, zs, qs, H0s, D0s, grids, Fos = _build(F)
+    z = np.concatenate(zs); q = np.concatenate(qs); H0 = np.concatenate(H0s); D0 = np.concatenate(D0s)
+    off = np.concatenate([[0], np.cumsum([r[2] for r in RUNS])])
+    specs = [(ctxs[k], flds[k], int(off[k]), int(off[k + 1]), float(grids[k].rn[-1]), 1.0) for k in range(len(RUNS))]
+    runs = F.make_runs(specs)
+    prm = F.push_params(DT, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=THR)
+    s = torch.cuda.Stream()
+    pg = make_particles(z, q, H0, D0, H0.copy())
+    with torch.cuda.stream(s):
+        F.fpic_push_batched(runs, pg, prm, stream=s)      # warm-up outside capture (scratch, tables)
+    torch.cuda.synchronize()
+    p0 = make_particles(z, q, H0, D0, H0.copy())
+    for name in ("r", "th", "ph", "ur", "uth", "uph", "Hn", "alive"):
+        getattr(pg, name).copy_(getattr(p0, name))
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        F.fpic_push_batched(runs, pg, prm, stream=s)
+    torch.cuda.synchronize()
+    # a larger call on the same context grows its scratch
+    net0 = F.MLP()
+    net0.set_params(torch.zeros(F.MLP.nparams(), dtype=torch.float32, device="cuda"))
+    cfg = F.learned_cfg(mode=F.FPIC_LEARN_CORRECT)
+    pl = make_particles(z, q, H0, D0, H0.copy())
+    free0 = torch.cuda.mem_get_info()[0]
+    F.fpic_push_batched_learned(runs, net0, pl, prm, cfg)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] < free0 - len(q) * 64      # the learned scratch is new memory
+    graph.replay()
+    torch.cuda.synchronize()
+    pe = make_particles(z, q, H0, D0, H0.copy())
+    F.fpic_push_batched(runs, pe, prm)
+    torch.cuda.synchronize()
+    for x, y in zip(to_np(pg), to_np(pe)):
+        assert np.array_equal(x, y)
