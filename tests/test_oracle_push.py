@@ -182,6 +182,111 @@ def test_circular_orbit_closed_form(a, r):
     assert abs(z[0, 1] - math.pi / 2) < 1e-12
 
 
+def _kappa_r(a, r):
+    """Radial epicyclic frequency of a prograde circular equatorial Kerr orbit
+    in coordinate time (M = 1; e.g. Okazaki, Kato & Fukue 1987):
+    kappa_r^2 = Omega^2 (1 - 6/r + 8 a / r^1.5 - 3 a^2 / r^2)."""
+    Om = 1.0 / (r ** 1.5 + a)
+    return Om * math.sqrt(1 - 6 / r + 8 * a / r ** 1.5 - 3 * a * a / (r * r))
+
+
+def _isco(a):
+    """Bardeen, Press & Teukolsky (1972): prograde ISCO radius (M = 1)."""
+    z1 = 1 + (1 - a * a) ** (1 / 3) * ((1 + a) ** (1 / 3) + (1 - a) ** (1 / 3))
+    z2 = math.sqrt(3 * a * a + z1 * z1)
+    return 3 + z2 - math.sqrt((3 - z1) * (3 + z1 + 2 * z2))
+
+
+def _circular_state(a, r):
+    E, L, Om = _circular(a, r)
+    m = O.metric(1.0, a, [r], [math.pi / 2])[0]
+    al2, be, grr, grp = m[2] ** 2, m[3], m[8], m[9]
+    ur = (be * E - al2 * grp * L) / (al2 * grr - be * be)      # dr/dt = 0
+    return np.array([r, math.pi / 2, 0.0, ur, 0.0, L])
+
+
+def _radial_jacobian(a, r):
+    """Linearisation of the oracle's right-hand side (Eqs. p1, p2) in the
+    (r, u_r) plane about the circular orbit (th = pi/2, u_th = 0, u_ph = L
+    fixed; ph does not enter): central differences of dr/dt and du_r/dt."""
+    z0 = _circular_state(a, r)
+    J = np.zeros((2, 2))
+    for col, k in enumerate((0, 3)):
+        h = 1e-5 * (abs(z0[k]) + 1.0)
+        zp, zm = z0.copy(), z0.copy()
+        zp[k] += h
+        zm[k] -= h
+        d = (O.rhs(1.0, a, zp, 0.0)[0] - O.rhs(1.0, a, zm, 0.0)[0]) / (2 * h)
+        J[:, col] = d[[0, 3]]
+    return z0, J
+
+
+@pytest.mark.parametrize("a,r", [(0.9, 6.0), (0.9, 3.0), (0.0, 8.0), (0.5, 5.0)])
+def test_radial_epicyclic_frequency(a, r):
+    """App. A metric through Eqs. (p1)-(p2) at second order: the circular
+    orbit is a fixed point of the (r, u_r) flow, and the linearised flow
+    about it oscillates at the closed-form radial epicyclic frequency
+    (eigenvalues +-i kappa_r: zero trace, determinant kappa_r^2).  Printed
+    values (a = 0.9): kappa_r = 0.041669812 at r = 6, 0.055782688 at r = 3."""
+    if (a, r) == (0.9, 6.0):
+        assert abs(_kappa_r(a, r) - 0.041669812) < 1e-9
+    if (a, r) == (0.9, 3.0):
+        assert abs(_kappa_r(a, r) - 0.055782688) < 1e-9
+    z0, J = _radial_jacobian(a, r)
+    f0 = O.rhs(1.0, a, z0, 0.0)[0]
+    assert abs(f0[0]) < 1e-14 and abs(f0[3]) < 1e-14
+    k = _kappa_r(a, r)
+    assert abs(np.trace(J)) < 1e-8 * k
+    assert abs(math.sqrt(np.linalg.det(J)) - k) < 1e-7 * k, (math.sqrt(np.linalg.det(J)), k)
+
+
+def test_radial_oscillation_period_of_a_perturbed_circular_orbit():
+    """A circular orbit (a = 0.9, r = 6) kicked radially (u_r + 1e-4) and
+    pushed with RK4 (dt = 0.1) oscillates in r with period 2 pi / kappa_r
+    (upward crossings of its mean radius over two periods, 1e-4 relative)."""
+    a, r, dt = 0.9, 6.0, 0.1
+    z = np.ascontiguousarray(_circular_state(a, r)[None, :])
+    z[0, 3] += 1e-4
+    p = O.push_params(a=a, dt=dt, scheme=O.RK4)
+    qm = np.zeros(1)
+    H0, _, D0 = O.hamiltonian(1.0, a, 0.0, z, qm)
+    Hn, alive = H0.copy(), np.ones(1, np.uint8)
+    T = 2.0 * math.pi / _kappa_r(a, r)
+    rs = [z[0, 0]]
+    for _ in range(int(2.3 * T / dt)):
+        O.push(p, z, qm, H0, D0, Hn, alive)
+        rs.append(z[0, 0])
+    rs = np.array(rs)
+    x = rs - 0.5 * (rs.max() + rs.min())
+    up = np.nonzero((x[:-1] < 0) & (x[1:] >= 0))[0]
+    tc = (up + x[up] / (x[up] - x[up + 1])) * dt
+    assert len(tc) >= 2
+    period = (tc[-1] - tc[0]) / (len(tc) - 1)
+    assert abs(period - T) < 1e-4 * T, (period, T)
+
+
+@pytest.mark.parametrize("a", [0.0, 0.5, 0.9])
+def test_isco_is_where_the_radial_restoring_force_vanishes(a):
+    """The innermost stable circular orbit is where the oracle's linearised
+    radial flow stops oscillating (det J = kappa_r^2 changes sign): found by
+    bisection on the oracle's right-hand side, it equals the Bardeen-Press-
+    Teukolsky radius (printed: 2.320883 for a = 0.9; 6 for a = 0)."""
+    rI = _isco(a)
+    if a == 0.9:
+        assert abs(rI - 2.320883) < 1e-6
+    if a == 0.0:
+        assert abs(rI - 6.0) < 1e-12
+    lo, hi = rI - 0.3, rI + 0.3
+    assert np.linalg.det(_radial_jacobian(a, lo)[1]) < 0 < np.linalg.det(_radial_jacobian(a, hi)[1])
+    for _ in range(40):
+        mid = 0.5 * (lo + hi)
+        if np.linalg.det(_radial_jacobian(a, mid)[1]) < 0:
+            lo = mid
+        else:
+            hi = mid
+    assert abs(0.5 * (lo + hi) - rI) < 1e-6, (0.5 * (lo + hi), rI)
+
+
 def test_charged_orbit_exact_wald_conserves_H_L():
     """Sec. 3.1.3: charged orbits (Table C.1 RKA initial states) in the exact
     Wald field conserve H and L; RK4 at dt = 1e-3 keeps both to ~1e-10."""
