@@ -53,7 +53,8 @@ class fpic_push_params(C.Structure):
 
 class fpic_push_stats(C.Structure):
     _fields_ = [("n_alive_before", C.c_int64), ("n_implicit", C.c_int64), ("n_iter_total", C.c_int64),
-                ("n_notconv", C.c_int64), ("n_removed", C.c_int64), ("n_rhs_evals", C.c_int64)]
+                ("n_notconv", C.c_int64), ("n_removed", C.c_int64), ("n_rhs_evals", C.c_int64),
+                ("n_slope_reused", C.c_int64)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -90,7 +91,7 @@ class fpic_learned_cfg(C.Structure):
 
 
 FPIC_LEARN_SKIP, FPIC_LEARN_CORRECT = 0, 1
-FPIC_TUNE_IMR_BLOCKS_PER_SM, FPIC_TUNE_DEP_THREADS, FPIC_TUNE_STATIC_FIELDS = 0, 1, 2
+FPIC_TUNE_IMR_BLOCKS_PER_SM, FPIC_TUNE_DEP_THREADS, FPIC_TUNE_STATIC_FIELDS, FPIC_TUNE_REUSE_SLOPE = 0, 1, 2, 3
 
 
 # name -> (restype, argtypes)
@@ -495,12 +496,21 @@ class Fields:
 
     NAMES3 = ("B0", "B1", "D0", "D1", "j0", "j1", "E", "H", "Bh", "Dw")
 
+    # the four source arrays of one level (rho, J^r, J^th, J^ph) are
+    # consecutive slices of one buffer, each starting on a 256-byte boundary,
+    # so a multi-rank step sums them with a single collective
+    SRC_ALIGN = 32
+
     def __init__(self, size, device="cuda"):
         z = lambda: [torch.zeros(size, dtype=torch.float64, device=device) for _ in range(3)]
         for nm in self.NAMES3:
-            setattr(self, nm, z())
-        self.rho0 = torch.zeros(size, dtype=torch.float64, device=device)
-        self.rho1 = torch.zeros(size, dtype=torch.float64, device=device)
+            if nm not in ("j0", "j1"):
+                setattr(self, nm, z())
+        slot = -(-size // self.SRC_ALIGN) * self.SRC_ALIGN
+        for lvl in (0, 1):
+            buf = torch.zeros(4 * slot, dtype=torch.float64, device=device)
+            setattr(self, "rho%d" % lvl, buf[:size])
+            setattr(self, "j%d" % lvl, [buf[(k + 1) * slot:(k + 1) * slot + size] for k in range(3)])
 
     def struct(self):
         p3 = lambda arrs: _P3(*[_dp(t) for t in arrs])
