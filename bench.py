@@ -40,6 +40,12 @@ FLOP_RK4_TRIAL = 4 * FLOP_EVAL + 79 + 56 + 5
 FLOP_IMR_ITER = FLOP_EVAL + 48
 FLOP_IMR_NEWTON = 125       # Newton form: the 3 x 3 momentum system and the position coupling per iteration
 FLOP_IMR_FINAL = 56         # H at the converged point (metric + Gamma + H)
+# slope reuse (FPIC_TUNE_REUSE_SLOPE): the trial's end point gets the full
+# right-hand side (H included) instead of H alone, k1 is evaluated only for
+# particles without a cached slope, and the IMR's converged point gets the
+# full right-hand side too
+FLOP_RK4_TRIAL_REUSED = 4 * FLOP_EVAL + 79 + 5
+FLOP_IMR_FINAL_REUSE = FLOP_EVAL
 NOMINAL_FP64_GFLOPS = 1250.0
 # DRAM bytes (read + write) of one k_explicit<1> launch on this workload,
 # from one ncu capture of the current kernel (117.8 MB + 51.6 MB); the
@@ -62,6 +68,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-reuse-slope", action="store_true",
+                    help="evaluate k1 = F(z^n) every step instead of keeping it from the previous step")
     ap.add_argument("--learned-form", choices=("correct", "skip"), default="correct",
                     help="learned guess: corrector of the rejected trials (default) or pre-step skip")
     ap.add_argument("--learned-restart", type=int, default=0,
@@ -248,7 +256,8 @@ def _timed(F, ctx, p, fields, prm, ev, steps, flush, learned=None):
     of particles with an implicit solve that reached max_iter."""
     import torch
     out = dict(t_step=0.0, t_ex=0.0, t_inf=0.0, t_im=0.0, psteps=0, notconv=0, impl=0, iters=0, evals=0, fl_ex=0.0, fl_im=0.0,
-               launches=0, ncmask=torch.zeros(p.n, dtype=torch.bool, device=p.r.device))
+               launches=0, reused=0, ncmask=torch.zeros(p.n, dtype=torch.bool, device=p.r.device))
+    reuse = F.fpic_get_tuning(ctx, F.FPIC_TUNE_REUSE_SLOPE) == 1
     for k in range(steps):
         flush.fill_(k & 255)
         ev[0].record()
@@ -269,9 +278,15 @@ def _timed(F, ctx, p, fields, prm, ev, steps, flush, learned=None):
         out["iters"] += st["n_iter_total"]
         out["evals"] += st["n_rhs_evals"]
         out["notconv"] += st["n_notconv"]
-        out["fl_ex"] += st["n_alive_before"] * FLOP_RK4_TRIAL
         it_fl = FLOP_IMR_ITER + (FLOP_IMR_NEWTON if prm.imr_newton else 0)
-        out["fl_im"] += st["n_iter_total"] * it_fl + st["n_implicit"] * FLOP_IMR_FINAL
+        if reuse:
+            out["fl_ex"] += st["n_alive_before"] * FLOP_RK4_TRIAL_REUSED + \
+                (st["n_alive_before"] - st["n_slope_reused"]) * FLOP_EVAL
+            out["fl_im"] += st["n_iter_total"] * it_fl + st["n_implicit"] * FLOP_IMR_FINAL_REUSE
+        else:
+            out["fl_ex"] += st["n_alive_before"] * FLOP_RK4_TRIAL
+            out["fl_im"] += st["n_iter_total"] * it_fl + st["n_implicit"] * FLOP_IMR_FINAL
+        out["reused"] += st["n_slope_reused"]
         # the library's launches per step (static fields: no coefficient rebuild):
         # plain k_explicit (+ alive count), k_order, k_imr, k_imr_finish;
         # corrector + k_count_alive, k_mlp_correct4; skip form 9
@@ -309,6 +324,8 @@ def run_gpu(args, ws, rank, local):
     torch.cuda.set_device(device)
     F, g, ctx, fields, p = setup(args.n, rank, device)
     F.fpic_set_tuning(ctx, F.FPIC_TUNE_STATIC_FIELDS, 1)     # the Wald field does not change
+    if not args.no_reuse_slope:
+        F.fpic_set_tuning(ctx, F.FPIC_TUNE_REUSE_SLOPE, 1)   # k1 from the previous step's end point
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
     for e in ev:            # torch creates the CUDA event on its first record
         e.record()
@@ -446,6 +463,10 @@ def run_gpu(args, ws, rank, local):
                    "implicit_fraction": plain["impl"] / psteps,
                    "mean_imr_iterations": plain["iters"] / max(plain["impl"], 1),
                    "rhs_evals_per_particle_step": plain["evals"] / psteps,
+                   "slope_reuse": {"on": not args.no_reuse_slope,
+                                   "fraction_of_particle_steps": plain["reused"] / psteps,
+                                   "note": "k1 = F(z^n) kept from the previous step's end point; the "
+                                           "first timed step starts from a restored state (k1 evaluated)"},
                    "max_dH_over_D0": max_dH,
                    "max_dH_over_D0_converged": max_dH_conv,
                    "particles_with_unconverged_solve": int(plain["ncmask"].sum().item()),

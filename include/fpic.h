@@ -144,6 +144,8 @@ typedef struct {
     int64_t n_notconv;        /* implicit solves stopped by max_iter */
     int64_t n_removed;        /* particles removed by the boundaries */
     int64_t n_rhs_evals;      /* right-hand-side evaluations performed */
+    int64_t n_slope_reused;   /* particles whose first RK4 stage came from the
+                                 slope cache (FPIC_TUNE_REUSE_SLOPE) */
 } fpic_push_stats;
 
 /* Create a context for the Kerr spacetime of mass M > 0 and spin |a| <= M
@@ -308,8 +310,23 @@ int fpic_probe_fp64(double *gflops_out, int reps);
  *     per-cell interpolation coefficients each push builds are reused while
  *     the six field pointers stay the same; 0 (default) = rebuilt every push.
  *     Setting it discards the current coefficients.
+ *   FPIC_TUNE_REUSE_SLOPE: 1 = fpic_push, fpic_push_host and the corrector
+ *     form of fpic_push_learned keep, per particle, the right-hand side
+ *     F(z^{n+1}) and sin/cos th^{n+1} at the end of its step (the RK4 trial
+ *     evaluates the full right-hand side at its end point instead of H
+ *     alone; the IMR solves at their converged point) in a library-owned
+ *     array of 15 doubles per particle, and the next push takes its first
+ *     RK4 stage k1 = F(z^n) from there for every particle whose state and
+ *     q/m are bitwise those the library stored.  The cache applies only
+ *     while the right-hand side cannot have changed: no grid fields, or
+ *     FPIC_TUNE_STATIC_FIELDS = 1; it is dropped when the particle arrays,
+ *     n, the six field pointers, B0field or the grid change.  Results equal
+ *     those without it up to rounding (sin/cos of th^{n+1} by angle
+ *     addition instead of libm, H of the trial through 1/sqrt instead of
+ *     sqrt).  0 (default) = every push evaluates k1.
  * Errors: FPIC_EINVAL (NULL, unknown key, value out of range). */
-enum { FPIC_TUNE_IMR_BLOCKS_PER_SM = 0, FPIC_TUNE_DEP_THREADS = 1, FPIC_TUNE_STATIC_FIELDS = 2 };
+enum { FPIC_TUNE_IMR_BLOCKS_PER_SM = 0, FPIC_TUNE_DEP_THREADS = 1, FPIC_TUNE_STATIC_FIELDS = 2,
+       FPIC_TUNE_REUSE_SLOPE = 3 };
 int fpic_set_tuning(fpic_ctx *ctx, int key, int value);
 int fpic_get_tuning(const fpic_ctx *ctx, int key, int *value);
 

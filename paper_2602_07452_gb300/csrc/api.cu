@@ -296,6 +296,7 @@ extern "C" void fpic_destroy(fpic_ctx* c)
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     if (c->clean_exec) cudaGraphExecDestroy(c->clean_exec);
     if (c->d_fcoef) cudaFree(c->d_fcoef);
+    if (c->d_slope) cudaFree(c->d_slope);
     for (void* q : c->retired_dev) cudaFree(q);
     for (void* q : c->retired_host) cudaFreeHost(q);
     delete c;
@@ -361,6 +362,7 @@ extern "C" int fpic_set_grid(fpic_ctx* c, int Nr, int Nth, const double* rn, con
     c->ld = Nth + 1;
     c->has_grid = true;
     for (int i = 0; i < 6; ++i) c->fcoef_src[i] = nullptr;   // coefficients belong to the old grid
+    ++c->grid_gen;                                            // and so do cached slopes
     int rc = build_metric_tables(c);
     if (rc) return rc;
     FPIC_CUDA(cudaDeviceSynchronize());

@@ -49,6 +49,18 @@ struct fpic_ctx {
     void* d_fcoef = nullptr;
     size_t fcoef_bytes = 0;
     int static_fields = 0;           // FPIC_TUNE_STATIC_FIELDS: reuse the coefficients of unchanged pointers
+    // FPIC_TUNE_REUSE_SLOPE: the right-hand side at the end of each particle's
+    // step, kept for the first RK4 stage of the next (see push.cu); the
+    // cache is cold whenever its key (particle arrays, n, fields, grid) changes
+    int reuse_slope = 0;
+    void* d_slope = nullptr;
+    size_t slope_bytes = 0;
+    const void* slope_key_r = nullptr;
+    long long slope_key_n = -1;
+    const double* slope_key_f[6] = {};
+    double slope_key_B0field = 0.0;
+    unsigned long long slope_key_grid = 0;
+    unsigned long long grid_gen = 0;    // incremented by every fpic_set_grid
     const double* fcoef_src[6] = {};  // the field arrays the coefficients were built from
     // fpic_push_host: copy stream and per-chunk events (created on first use)
     cudaStream_t copy_stream = nullptr;
@@ -69,7 +81,7 @@ namespace fpic {
 
 enum { CNT_QUEUE = 0, CNT_HEAD = 1, CNT_ITERS = 2, CNT_NOTCONV = 3, CNT_REMOVED = 4,
        CNT_ALIVE = 5, CNT_EVALS = 6, CNT_ERR = 7, CNT_WORK = 8, CNT_SKIP = 9, CNT_PRIO = 10,
-       CNT_NORM = 11, CNT_N = 12 };
+       CNT_NORM = 11, CNT_SLOPE = 12, CNT_N = 13 };
 
 int set_error(int code, const char* fmt, ...);
 int check_cuda(cudaError_t e, const char* what);

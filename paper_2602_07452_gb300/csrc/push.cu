@@ -81,7 +81,42 @@ struct PushK {
     float fmean[14], fistd[14];
     float oscale[6];        // corrector outputs 0-5 are residual / (s_i oscale_i)
     int restart_after;      // corrector: restart from the trial after this many iterations (0: never)
+    // slope reuse (FPIC_TUNE_REUSE_SLOPE): SLOPE_ROWS x n, see SLOPE_*; null = off
+    double* slope;
+    int slope_cold;         // the cache holds nothing for these particles: do not look
 };
+
+// Rows of the slope cache: the state z^{n+1} and q/m it was computed for
+// (the validity tag, compared bit for bit), F(z^{n+1}), sin and cos th^{n+1}.
+enum { SLOPE_Z = 0, SLOPE_QM = 6, SLOPE_F = 7, SLOPE_S = 13, SLOPE_C = 14, SLOPE_ROWS = 15 };
+
+__device__ __forceinline__ bool slope_valid(const PushK& k, long long p, const double z[6], double qm)
+{
+    bool ok = true;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        ok = ok && __double_as_longlong(__ldcs(k.slope + (size_t)(SLOPE_Z + i) * k.n + p)) == __double_as_longlong(z[i]);
+    return ok && __double_as_longlong(__ldcs(k.slope + (size_t)SLOPE_QM * k.n + p)) == __double_as_longlong(qm);
+}
+
+__device__ __forceinline__ void slope_store(const PushK& k, long long p, const double z[6], double qm,
+                                            const double f[6], double s, double c)
+{
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        __stcs(k.slope + (size_t)(SLOPE_Z + i) * k.n + p, z[i]);
+        __stcs(k.slope + (size_t)(SLOPE_F + i) * k.n + p, f[i]);
+    }
+    __stcs(k.slope + (size_t)SLOPE_QM * k.n + p, qm);
+    __stcs(k.slope + (size_t)SLOPE_S * k.n + p, s);
+    __stcs(k.slope + (size_t)SLOPE_C * k.n + p, c);
+}
+
+// Invalidates a particle's cache entry (its tag can no longer match a state).
+__device__ __forceinline__ void slope_drop(const PushK& k, long long p)
+{
+    __stcs(k.slope + (size_t)SLOPE_Z * k.n + p, __longlong_as_double(0x7ff8dead0000dead));
+}
 
 // Run of particle p in a batched push (runs sorted by begin).
 __device__ __forceinline__ int run_of(const RunK* __restrict__ runs, int nruns, long long p)
@@ -287,8 +322,24 @@ __global__ void __launch_bounds__(128) k_explicit(const __grid_constant__ PushK 
     const bool em = (R.has_fields || R.B0field != 0.0) && qm != 0.0;
     const double dt = k.dt, hdt = 0.5 * k.dt;
     double Hd, s0, c0, sn, cn;
-    sincos(z0[1], &s0, &c0);
-    F_at_sc(R, z0, s0, c0, qm, em, kk, Hd);
+    // k1 = F(z^n): from the slope cache when this particle's state is the
+    // one stored there, else evaluated
+    const bool reuse = !BATCHED && k.slope && !k.slope_cold && slope_valid(k, p, z0, qm);
+    if (!BATCHED && k.slope) {
+        const unsigned act = __activemask();
+        const unsigned rm = __ballot_sync(act, reuse);
+        if ((int)(threadIdx.x & 31) == __ffs(act) - 1 && rm)
+            atomicAdd((unsigned long long*)&k.cnt[CNT_SLOPE], (unsigned long long)__popc(rm));
+    }
+    if (reuse) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) kk[i] = __ldcs(k.slope + (size_t)(SLOPE_F + i) * k.n + p);
+        s0 = __ldcs(k.slope + (size_t)SLOPE_S * k.n + p);
+        c0 = __ldcs(k.slope + (size_t)SLOPE_C * k.n + p);
+    } else {
+        sincos(z0[1], &s0, &c0);
+        F_at_sc(R, z0, s0, c0, qm, em, kk, Hd);
+    }
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
         acc[i] = kk[i];
@@ -313,7 +364,12 @@ __global__ void __launch_bounds__(128) k_explicit(const __grid_constant__ PushK 
 #pragma unroll
     for (int i = 0; i < 6; ++i) y[i] = fma(d6, acc[i] + kk[i], z0[i]);
     sincos_near(z0[1], s0, c0, y[1], sn, cn);
-    const double H1 = eval_H_sc(R.bh, y, sn, cn, qm, R.B0pot);
+    // H of the trial; with the slope cache the whole right-hand side at the
+    // trial point, kept for the next step if the trial is accepted
+    double H1, fy[6];
+    const bool keep = !BATCHED && k.slope && !k.record;
+    if (keep) F_at_sc(R, y, sn, cn, qm, em, fy, H1);
+    else H1 = eval_H_sc(R.bh, y, sn, cn, qm, R.B0pot);
     bool accept = true;
     if (MODE >= 1) {
         const double H0 = k.P.H0[p], D0 = k.P.D0[p];
@@ -333,8 +389,19 @@ __global__ void __launch_bounds__(128) k_explicit(const __grid_constant__ PushK 
     const unsigned act = __activemask();
     const unsigned rej = __ballot_sync(act, !accept);
     if (accept) {
-        if (!finish(R, k.P, p, y, H1, 0, 0)) atomicAdd((unsigned long long*)&k.cnt[CNT_REMOVED], 1ull);
+        const double th_trial = y[1];
+        const bool alive = finish(R, k.P, p, y, H1, 0, 0);
+        if (!alive) atomicAdd((unsigned long long*)&k.cnt[CNT_REMOVED], 1ull);
         if (k.t) k.t[p] += dt;
+        if (keep && alive) {
+            if (y[1] != th_trial) {       // reflected at a pole: the slope of the stored state
+                sn = -sn;
+                F_at_sc(R, y, sn, cn, qm, em, fy, Hd);
+            }
+            slope_store(k, p, y, qm, fy, sn, cn);
+        }
+    } else if (keep) {
+        slope_drop(k, p);                 // the implicit partner sets its own entry, if any
     }
     if (rej) {
         const int leader = __ffs(act) - 1;
@@ -652,9 +719,23 @@ __global__ void __launch_bounds__(256) k_imr_finish(const __grid_constant__ Push
         sincos_near(th0, k.sc0[p], k.sc0[k.n + p], z[1], sn, cn);
         const RunK& R = BATCHED ? k.runs[run_of(k.runs, k.nruns, p)] : k.run;
         const double qm = st ? k.z0s[(size_t)6 * k.n + idx] : k.P.qm[p];
-        const double H = eval_H_sc(R.bh, z, sn, cn, qm, R.B0pot);
-        if (!finish(R, k.P, p, z, H, 1, (k.its && !all_mode) ? k.its[idx] : k.P.iters[p])) ++n_rm;
+        const bool keep = !BATCHED && k.slope && !all_mode && !k.record;
+        double H, f[6];
+        const bool em = (R.has_fields || R.B0field != 0.0) && qm != 0.0;
+        if (keep) F_at_sc(R, z, sn, cn, qm, em, f, H);
+        else H = eval_H_sc(R.bh, z, sn, cn, qm, R.B0pot);
+        const double th_new = z[1];
+        const bool alive = finish(R, k.P, p, z, H, 1, (k.its && !all_mode) ? k.its[idx] : k.P.iters[p]);
+        if (!alive) ++n_rm;
         if (k.t) k.t[p] += k.dt_imp;
+        if (keep && alive) {
+            if (z[1] != th_new) {
+                double Hd;
+                sn = -sn;
+                F_at_sc(R, z, sn, cn, qm, em, f, Hd);
+            }
+            slope_store(k, p, z, qm, f, sn, cn);
+        }
     }
     warp_add(&k.cnt[CNT_REMOVED], n_rm, 0xffffffffu);
 }
@@ -1131,6 +1212,41 @@ static int field_coefs(fpic_ctx* c, const double* const fields[6], RunK& R, cuda
     return 0;
 }
 
+// Slope cache of a push (FPIC_TUNE_REUSE_SLOPE): points k at the context's
+// cache and marks it cold when the push's key differs from the previous
+// one's (another particle set or size, other fields, another grid) or the
+// cache was just (re)allocated.  Off when grid fields may change between
+// pushes (FPIC_TUNE_STATIC_FIELDS = 0).
+static int slope_setup(fpic_ctx* c, const fpic_particles* p, const double* const fields[6], double B0field, PushK& k)
+{
+    k.slope = nullptr;
+    k.slope_cold = 1;
+    if (!c->reuse_slope || (fields && !c->static_fields) || p->n <= 0) return 0;
+    const size_t need = (size_t)SLOPE_ROWS * (size_t)p->n * sizeof(double);
+    bool cold = false;
+    if (c->slope_bytes < need) {
+        retire(c, &c->d_slope);
+        c->slope_bytes = 0;
+        FPIC_CUDA(cudaMalloc(&c->d_slope, need));
+        c->slope_bytes = need;
+        cold = true;
+    }
+    cold = cold || c->slope_key_r != (const void*)p->r || c->slope_key_n != p->n ||
+           c->slope_key_B0field != B0field || c->slope_key_grid != c->grid_gen;
+    for (int i = 0; i < 6; ++i) {
+        const double* f = fields ? fields[i] : nullptr;
+        cold = cold || c->slope_key_f[i] != f;
+        c->slope_key_f[i] = f;
+    }
+    c->slope_key_r = p->r;
+    c->slope_key_n = p->n;
+    c->slope_key_B0field = B0field;
+    c->slope_key_grid = c->grid_gen;
+    k.slope = (double*)c->d_slope;
+    k.slope_cold = cold ? 1 : 0;
+    return 0;
+}
+
 // Step of the implicit solves: the hybrid's partner takes dt_implicit when
 // set (adaptive steps, Sec. 3.1.2); pure schemes take dt.
 static double implicit_step(const fpic_push_params* prm)
@@ -1206,6 +1322,10 @@ static int push_core(fpic_ctx* c, fpic_particles* p, const double* const fields[
                   p->alive, p->scheme, p->iters, p->cell};
     if (has_fields && n > 0) {
         rc = field_coefs(c, fields, k.run, s);
+        if (rc) return rc;
+    }
+    if (prm->scheme == FPIC_RK4 || prm->scheme >= FPIC_HYB1) {
+        rc = slope_setup(c, p, fields, k.run.B0field, k);
         if (rc) return rc;
     }
     k.guess = (double*)c->d_scratch;
@@ -1289,6 +1409,13 @@ static int push_core(fpic_ctx* c, fpic_particles* p, const double* const fields[
         stats->n_notconv = h[CNT_NOTCONV];
         stats->n_removed = h[CNT_REMOVED];
         stats->n_rhs_evals = h[CNT_EVALS] + (explicit_pass ? 4 * h[CNT_ALIVE] : 0);
+        stats->n_slope_reused = h[CNT_SLOPE];
+        if (k.slope) {
+            // slope reuse: k1 only where not reused, the full right-hand side
+            // at every trial's end point and at every converged IMR solve
+            stats->n_rhs_evals += h[CNT_ALIVE] - h[CNT_SLOPE];
+            if (prm->scheme >= FPIC_HYB1 && prm->implicit == FPIC_IMR) stats->n_rhs_evals += h[CNT_QUEUE];
+        }
         if (h[CNT_NOTCONV] > 0) return FPIC_ENOTCONVERGED;
     }
     return FPIC_OK;
@@ -1577,6 +1704,7 @@ extern "C" int fpic_push_noalloc(double M, double a, fpic_particles* p, const fp
         stats->n_notconv = h[CNT_NOTCONV];
         stats->n_removed = h[CNT_REMOVED];
         stats->n_rhs_evals = h[CNT_EVALS] + (explicit_pass ? 4 * h[CNT_ALIVE] : 0);
+        stats->n_slope_reused = 0;
         if (h[CNT_NOTCONV] > 0) return FPIC_ENOTCONVERGED;
     }
     return FPIC_OK;
@@ -2050,6 +2178,8 @@ extern "C" int fpic_push_learned(fpic_ctx* c, fpic_mlp* m, fpic_particles* p, co
     }
     for (int i = 0; i < 6; ++i) k.inc_scale[i] = cfg->inc_scale[i];
     k.learned = Y;
+    rc = slope_setup(c, p, fields, 0.0, k);
+    if (rc) return rc;
     FPIC_CUDA(cudaMemsetAsync(c->d_cnt, 0, CNT_N * sizeof(long long), s));
     if (n == 0) {
         if (stats) *stats = fpic_push_stats{};
@@ -2111,6 +2241,8 @@ extern "C" int fpic_push_learned(fpic_ctx* c, fpic_mlp* m, fpic_particles* p, co
         stats->n_notconv = h[CNT_NOTCONV];
         stats->n_removed = h[CNT_REMOVED];
         stats->n_rhs_evals = h[CNT_EVALS] + 4 * (correct ? h[CNT_ALIVE] : h[CNT_WORK]);
+        stats->n_slope_reused = h[CNT_SLOPE];
+        if (k.slope) stats->n_rhs_evals += (correct ? h[CNT_ALIVE] : h[CNT_WORK]) - h[CNT_SLOPE] + h[CNT_QUEUE];
         if (h[CNT_NOTCONV] > 0) return FPIC_ENOTCONVERGED;
     }
     return FPIC_OK;
@@ -2287,6 +2419,7 @@ static int push_batched(const fpic_run* runs, int nruns, fpic_mlp* m, fpic_parti
         stats->n_notconv = h[CNT_NOTCONV];
         stats->n_removed = h[CNT_REMOVED];
         stats->n_rhs_evals = h[CNT_EVALS] + (prm->scheme != FPIC_IMR ? 4 * h[CNT_ALIVE] : 0);
+        stats->n_slope_reused = 0;
         if (h[CNT_NOTCONV] > 0) return FPIC_ENOTCONVERGED;
     }
     return FPIC_OK;
@@ -2325,6 +2458,13 @@ extern "C" int fpic_set_tuning(fpic_ctx* c, int key, int value)
             return set_error(FPIC_EINVAL, "fpic_set_tuning: static fields must be 0 or 1, got %d", value);
         c->static_fields = value;
         for (int i = 0; i < 6; ++i) c->fcoef_src[i] = nullptr;   // rebuilt at the next push
+        c->slope_key_n = -1;                                      // cached slopes dropped
+        return FPIC_OK;
+    case FPIC_TUNE_REUSE_SLOPE:
+        if (value != 0 && value != 1)
+            return set_error(FPIC_EINVAL, "fpic_set_tuning: slope reuse must be 0 or 1, got %d", value);
+        c->reuse_slope = value;
+        c->slope_key_n = -1;
         return FPIC_OK;
     default:
         return set_error(FPIC_EINVAL, "fpic_set_tuning: unknown key %d", key);
@@ -2343,6 +2483,9 @@ extern "C" int fpic_get_tuning(const fpic_ctx* c, int key, int* value)
         return FPIC_OK;
     case FPIC_TUNE_STATIC_FIELDS:
         *value = c->static_fields;
+        return FPIC_OK;
+    case FPIC_TUNE_REUSE_SLOPE:
+        *value = c->reuse_slope;
         return FPIC_OK;
     default:
         return set_error(FPIC_EINVAL, "fpic_get_tuning: unknown key %d", key);
