@@ -17,17 +17,17 @@ struct BH {
     double M, a, a2, twoM;
 };
 
-// 1/x from the hardware approximation refined by two Newton steps
-// (y <- y + y (1 - x y)); each step doubles the correct bits, so the result
-// is within an ulp or two of the correctly rounded reciprocal for normal x.
+// 1/x from the hardware approximation y refined by one third-order step:
+// with e = 1 - x y, 1/x = y / (1 - e) = y (1 + e + e^2 + ...), so
+// y (1 + e + e^2) triples the correct bits of the estimate (its relative
+// error e^3); fpic_probe_math measures the result against correctly
+// rounded reciprocals.
 __device__ __forceinline__ double rcp_nr(double x)
 {
     double y;
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-    double e = fma(-x, y, 1.0);
-    y = fma(y, e, y);
-    e = fma(-x, y, 1.0);
-    return fma(y, e, y);
+    const double e = fma(-x, y, 1.0);
+    return fma(y, fma(e, e, e), y);
 }
 
 // Square root of a positive normal x (the deposit's trapezoid sums): the
@@ -55,10 +55,16 @@ __device__ __forceinline__ double sqrt_dep(double x)
 }
 
 // sin h and cos h - 1 for a step h inside one cell: Maclaurin series through
-// h^7 / h^8 when |h| < 1/128 (truncation below 1e-22 relative), else libm.
+// h^5 / h^6 when |h| < 2^-10 (the first omitted terms are below 2^-62 of
+// sin h and 2^-63 of cos h - 1), through h^7 / h^8 when |h| < 2^-7 (below
+// 1e-22 relative), else libm.
 __device__ __forceinline__ void sincos_step(double h, double& sh, double& cm)
 {
-    if (fabs(h) < 0.0078125) {
+    if (fabs(h) < 0.0009765625) {
+        const double h2 = h * h;
+        sh = h * fma(h2, fma(h2, 1.0 / 120.0, -1.0 / 6.0), 1.0);
+        cm = h2 * fma(h2, fma(h2, -1.0 / 720.0, 1.0 / 24.0), -0.5);
+    } else if (fabs(h) < 0.0078125) {
         const double h2 = h * h;
         sh = h * fma(h2, fma(h2, fma(h2, -1.0 / 5040.0, 1.0 / 120.0), -1.0 / 6.0), 1.0);
         cm = h2 * fma(h2, fma(h2, fma(h2, 1.0 / 40320.0, -1.0 / 720.0), 1.0 / 24.0), -0.5);
@@ -302,12 +308,16 @@ __device__ __forceinline__ void eval_rhs_sc_t(const BH& bh, const double y[6], d
     //   with W = a^2 s^2 u_r^2 + 2 a u_r u_ph + u_th^2, so
     //   du_i/dt = h (W d_i g^tt + u_ph^2 d_i g^pp [+ u_r^2 q / rho^2])
     //             + d_i xi (u_r (1 - h u_r) / xi^2 + Gamma alpha^3 / 2),  h = -alpha / (2 Gamma).
+    //   In r: W d_r g^tt + u_ph^2 d_r g^pp = -2 r (W / rho^4 + u_ph^2 / (rho^4 s^2))
+    //   = -2 r / rho^2 (W / rho^2 + u_ph^2 t), t = 1 / (rho^2 s^2), so that
+    //   h (...) = (alpha / Gamma) m0 with m0 = (r / rho^2) (W / rho^2 + u_ph^2 t).
     const double h = -0.5 * aiG;
     const double urur = ur * ur, upup = up * up;
     const double W = fma(urur, g.a2s2, fma(2.0 * bh.a * ur, up, ut * ut));
     const double a3h = (-0.5 * g.alpha) * g.ixi;      // -alpha^3 / 2
     const double kap = fma(g.ixi * g.ixi * ur, fma(-h, ur, 1.0), -G * a3h);
-    f[3] = fma(h, fma(W, d.tt[0], upup * d.pp[0]), d.xi[0] * kap);
+    const double m0 = (y[0] * g.irho2) * fma(W, g.irho2, upup * g.t);
+    f[3] = fma(aiG, m0, d.xi[0] * kap);
     f[4] = fma(h, fma(W, d.tt[1], fma(upup, d.pp[1], urur * d.q * g.irho2)), d.xi[1] * kap);
     f[5] = 0.0;
     if (JAC) {
@@ -320,14 +330,19 @@ __device__ __forceinline__ void eval_rhs_sc_t(const BH& bh, const double y[6], d
         J->cx[0] = J->cx[1] = J->cx[2] = 0.0;
     }
     if (em) {
+        // (q/m) alpha gamma_ij D^j with gamma_rr = xi, gamma_rph = -a xi s^2,
+        // gamma_thth = rho^2, gamma_phph = s^2 (rho^2 + a^2 xi s^2):
+        //   r:  k xi X,  X = D^r - a s^2 D^ph
+        //   ph: k s^2 (rho^2 D^ph - a xi X)
         const double k = qm * g.alpha;
         const double ks = (qm * g.rho2) * (g.s * iG);    // k sqrt(gamma) / Gamma, alpha^2 xi = 1
         const double cr = fma(Ut, B[2], -Up * B[1]);
         const double ct = fma(Up, B[0], -Ur * B[2]);
         const double cp = fma(Ur, B[1], -Ut * B[0]);
-        f[3] = fma(k, fma(g.grr, D[0], g.grp * D[2]), fma(ks, cr, f[3]));
-        f[4] = fma(k, g.gtt * D[1], fma(ks, ct, f[4]));
-        f[5] = fma(k, fma(g.grp, D[0], g.gpp * D[2]), ks * cp);
+        const double X = fma(-bh.a * g.s2, D[2], D[0]);
+        f[3] = fma(k * g.xi, X, fma(ks, cr, f[3]));
+        f[4] = fma(k, g.rho2 * D[1], fma(ks, ct, f[4]));
+        f[5] = fma(k * g.s2, fma(-bh.a * g.xi, X, g.rho2 * D[2]), ks * cp);
         if (JAC) {
             J->ks = ks;
             J->B[0] = B[0]; J->B[1] = B[1]; J->B[2] = B[2];
