@@ -155,6 +155,18 @@ __device__ __forceinline__ void geo_deriv(const BH& bh, double r, const Geo& g, 
     d.pp[1] = (-2.0 * sc) * (g.t * g.t) * (g.rho2 - g.a2s2);
 }
 
+// FP32 value of a double from its high word (20 of its 52 mantissa bits,
+// truncated), by integer operations only, for the index estimates of
+// locate: no FP64 conversion instruction.  Exact enough for normal floats;
+// any other input still ends in the right cell, since the walk in locate
+// corrects any start.
+__device__ __forceinline__ float f32_est(double x)
+{
+    const int hi = __double2hiint(x);
+    const int e = ((hi >> 20) & 0x7ff) - 896;
+    return __int_as_float((hi & (int)0x80000000) | (e << 23) | ((hi & 0xfffff) << 3));
+}
+
 // Order-preserving integer key of a double (monotone for all non-NaN values).
 __device__ __forceinline__ long long okey(double x)
 {
@@ -201,8 +213,8 @@ struct Fields {
 __device__ __forceinline__ void gather(const GridDev& G, const Fields& F, double r, double th,
                                        double D[3], double B[3])
 {
-    const float lr = __logf((float)r);
-    const float tf = (float)th;
+    const float lr = __logf(f32_est(r));
+    const float tf = f32_est(th);
     int i0, i1, j0, j1;
     double wr0, wr1, wt0, wt1;
     locate(G.rn, G.irn, G.Nr + 1, r, (lr - G.lr0) * G.ilr, i0, wr0);
@@ -242,8 +254,8 @@ struct FieldsC {
 __device__ __forceinline__ void gather_c(const GridDev& G, const FieldsC& F, double r, double th, double D[3],
                                          double B[3])
 {
-    const float lr = __logf((float)r);
-    const float tf = (float)th;
+    const float lr = __logf(f32_est(r));
+    const float tf = f32_est(th);
     int i0, i1, j0, j1;
     double wr0, wr1, wt0, wt1;
     locate(G.rn, G.irn, G.Nr + 1, r, (lr - G.lr0) * G.ilr, i0, wr0);

@@ -146,9 +146,9 @@ __device__ __forceinline__ uint32_t cell_of(const GridDev& G, double r, double t
 {
     int i, j;
     double w;
-    const float lr = __logf((float)r);
+    const float lr = __logf(f32_est(r));
     locate(G.rn, G.irn, G.Nr + 1, r, (lr - G.lr0) * G.ilr, i, w);
-    locate(G.tn, G.itn, G.Nth + 1, th, ((float)th - G.t0) * G.it, j, w);
+    locate(G.tn, G.itn, G.Nth + 1, th, (f32_est(th) - G.t0) * G.it, j, w);
     return (uint32_t)i * (uint32_t)G.Nth + (uint32_t)j;
 }
 
