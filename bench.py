@@ -759,9 +759,11 @@ def run_pic(args, device, grid_n, ppc, steps, rank=0, conserving=False, inject_e
     pprm = F.push_params(PIC_DT, scheme=F.FPIC_RK4, r_max=r_max)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
     dep_tune = None
+    from paper_2602_07452_gb300 import autotune
     if not conserving:
-        from paper_2602_07452_gb300 import autotune
-        dep_tune = autotune.tune_deposit_threads(ctx, p, g.size)
+        dep_tune = autotune.tune_deposit_threads(ctx, p, g.size)     # also leaves p sorted by cell
+    else:
+        F.fpic_sort(ctx, p)
     from paper_2602_07452_gb300.grpic import GRPIC
     sim = GRPIC(ctx, g, fl, store, n, pprm, fprm, conserving=conserving,
                 clean=(clean_every, clean_sweeps) if clean_every > 0 else None,
@@ -769,6 +771,10 @@ def run_pic(args, device, grid_n, ppc, steps, rank=0, conserving=False, inject_e
     sim.deposit_initial()
     sim.step()
     torch.cuda.synchronize()
+    # TMA staging of the push's field tiles, on or off: timed on these
+    # (cell-sorted) particles with the step's push fields
+    stage_tune = autotune.tune_stage_fields(ctx, sim.particles, fl.push_fields(), pprm)
+    stage_frac = autotune.staged_fraction(ctx, sim.particles, fl.push_fields(), pprm)
     ph = [0.0] * 4
     ps = 0
     for _ in range(steps):
@@ -803,6 +809,9 @@ def run_pic(args, device, grid_n, ppc, steps, rank=0, conserving=False, inject_e
         "dt": PIC_DT, "absorbing": {"chi0": 1e4, "lambda": 5, "r_abs": 0.9 * r_max},
         "deposit_achieved_gflops": None if conserving else ps * FLOP_DEPOSIT / t_dep / 1e9,
         "deposit_threads_autotuned_ms": dep_tune,
+        "field_tile_staging_autotuned_ms": {("on" if k else "off"): round(v, 3) for k, v in stage_tune.items()},
+        "field_tile_staging": "on" if F.fpic_get_tuning(ctx, F.FPIC_TUNE_STAGE_FIELDS) else "off",
+        "field_tile_staged_block_fraction": stage_frac,
     }
 
 
@@ -1123,8 +1132,10 @@ def main():
     line = run_gpu(args, ws, rank, local)
     if not args.no_pic and rank == 0:
         import torch
-        line["pic_step"] = run_pic(args, torch.device("cuda", local), 512, 16, 3, rank)
-        line["pic_step_conserving"] = run_pic(args, torch.device("cuda", local), 512, 16, 3, rank, conserving=True)
+        # the full PIC step at its configuration: 1024^2, a = 0.99, 32 e-/e+ pairs per cell
+        line["pic_step"] = run_pic(args, torch.device("cuda", local), 1024, 64, 3, rank)
+        line["pic_step_conserving"] = run_pic(args, torch.device("cuda", local), 1024, 64, 3, rank, conserving=True)
+        line["pic_step_512"] = run_pic(args, torch.device("cuda", local), 512, 16, 3, rank)
         line["pic_step_conserving_injecting"] = run_pic(args, torch.device("cuda", local), 512, 16, 4, rank,
                                                         conserving=True, inject_every=2)
     if not args.no_extra and rank == 0:

@@ -146,6 +146,8 @@ typedef struct {
     int64_t n_rhs_evals;      /* right-hand-side evaluations performed */
     int64_t n_slope_reused;   /* particles whose first RK4 stage came from the
                                  slope cache (FPIC_TUNE_REUSE_SLOPE) */
+    int64_t n_tiles_staged;   /* blocks of the explicit pass that staged their
+                                 field tile (FPIC_TUNE_STAGE_FIELDS) */
 } fpic_push_stats;
 
 /* Create a context for the Kerr spacetime of mass M > 0 and spin |a| <= M
@@ -324,9 +326,20 @@ int fpic_probe_fp64(double *gflops_out, int reps);
  *     those without it up to rounding (sin/cos of th^{n+1} by angle
  *     addition instead of libm, H of the trial through 1/sqrt instead of
  *     sqrt).  0 (default) = every push evaluates k1.
+ *   FPIC_TUNE_STAGE_FIELDS: 1 = the explicit pass of fpic_push with grid
+ *     fields stages, per block of 128 particles, the interpolation
+ *     coefficients of the cells the block's particles occupy (from p->cell,
+ *     as the last push or fpic_sort left it; the block's cells plus two
+ *     cells of margin, up to 5 x 8 coefficient cells per component) in
+ *     shared memory with TMA tensor loads; gathers outside the tile read
+ *     global memory, so results are bitwise those without staging.  Pays
+ *     only for particles sorted by cell (the PIC step sorts them in its
+ *     deposit).  A tile load whose bounded wait runs out is counted and
+ *     reported as FPIC_ETIMEOUT when stats are requested.  0 (default) =
+ *     no staging.
  * Errors: FPIC_EINVAL (NULL, unknown key, value out of range). */
 enum { FPIC_TUNE_IMR_BLOCKS_PER_SM = 0, FPIC_TUNE_DEP_THREADS = 1, FPIC_TUNE_STATIC_FIELDS = 2,
-       FPIC_TUNE_REUSE_SLOPE = 3 };
+       FPIC_TUNE_REUSE_SLOPE = 3, FPIC_TUNE_STAGE_FIELDS = 4 };
 int fpic_set_tuning(fpic_ctx *ctx, int key, int value);
 int fpic_get_tuning(const fpic_ctx *ctx, int key, int *value);
 

@@ -297,6 +297,7 @@ extern "C" void fpic_destroy(fpic_ctx* c)
     if (c->clean_exec) cudaGraphExecDestroy(c->clean_exec);
     if (c->d_fcoef) cudaFree(c->d_fcoef);
     if (c->d_slope) cudaFree(c->d_slope);
+    if (c->d_stage_maps) cudaFree(c->d_stage_maps);
     for (void* q : c->retired_dev) cudaFree(q);
     for (void* q : c->retired_host) cudaFreeHost(q);
     delete c;

@@ -278,6 +278,53 @@ __device__ __forceinline__ void gather_c(const GridDev& G, const FieldsC& F, dou
     B[0] = v[3]; B[1] = v[4]; B[2] = v[5];
 }
 
+// Field tile staged in shared memory for a block of cell-sorted particles:
+// STAGE_TI coefficient rows (r cells) x STAGE_TJ coefficient cells (th) of
+// each of the six components, starting at coefficient cell (i0, j0).  A
+// gather whose cell lies in the tile reads shared memory, any other the
+// global coefficients (so staging never changes a result).
+constexpr int STAGE_TI = 5, STAGE_TJ = 8;
+struct StageTile {
+    const double* s;    // shared: [6][STAGE_TI][4 * STAGE_TJ]; nullptr = nothing staged
+    int i0, j0;
+};
+
+__device__ __forceinline__ void gather_c(const GridDev& G, const FieldsC& F, double r, double th, double D[3],
+                                         double B[3], const StageTile& T)
+{
+    const float lr = __logf(f32_est(r));
+    const float tf = f32_est(th);
+    int i0, i1, j0, j1;
+    double wr0, wr1, wt0, wt1;
+    locate(G.rn, G.irn, G.Nr + 1, r, (lr - G.lr0) * G.ilr, i0, wr0);
+    locate(G.rh, G.irh, G.Nr, r, (lr - G.lrh0) * G.ilr, i1, wr1);
+    locate(G.tn, G.itn, G.Nth + 1, th, (tf - G.t0) * G.it, j0, wt0);
+    locate(G.th, G.ith, G.Nth, th, (tf - G.th0) * G.it, j1, wt1);
+    const int ld = G.ld;
+    double v[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const bool ro = (k == 0 || k == 4 || k == 5);
+        const bool to = (k == 1 || k == 3 || k == 5);
+        const int i = ro ? i1 : i0, j = to ? j1 : j0;
+        const double wr = ro ? wr1 : wr0, wt = to ? wt1 : wt0;
+        const unsigned ti = (unsigned)(i - T.i0), tj = (unsigned)(j - T.j0);
+        double2 ab, cd;
+        if (T.s && ti < (unsigned)STAGE_TI && tj < (unsigned)STAGE_TJ) {
+            const double2* q = reinterpret_cast<const double2*>(T.s + ((k * STAGE_TI + ti) * STAGE_TJ + tj) * 4);
+            ab = q[0];
+            cd = q[1];
+        } else {
+            const double2* q = reinterpret_cast<const double2*>(F.c[k] + 4 * ((size_t)i * ld + j));
+            ab = __ldg(q);
+            cd = __ldg(q + 1);
+        }
+        v[k] = fma(wt, fma(cd.y, wr, cd.x), fma(ab.y, wr, ab.x));
+    }
+    D[0] = v[0]; D[1] = v[1]; D[2] = v[2];
+    B[0] = v[3]; B[1] = v[4]; B[2] = v[5];
+}
+
 // What the Newton form of the implicit-midpoint solve needs from one
 // right-hand side: u^i = g^ij u_j, 1 / Gamma, alpha / Gamma, g^ij, the
 // magnetic-force factor qm alpha sqrt(gamma) / Gamma (0 without a field),

@@ -61,6 +61,12 @@ struct fpic_ctx {
     double slope_key_B0field = 0.0;
     unsigned long long slope_key_grid = 0;
     unsigned long long grid_gen = 0;    // incremented by every fpic_set_grid
+    // FPIC_TUNE_STAGE_FIELDS: TMA staging of the coefficient tiles a block of
+    // cell-sorted particles touches (tensor maps of d_fcoef, see push.cu)
+    int stage_fields = 0;
+    void* d_stage_maps = nullptr;
+    const void* stage_key = nullptr;
+    int stage_key_Nr = 0, stage_key_ld = 0;
     const double* fcoef_src[6] = {};  // the field arrays the coefficients were built from
     // fpic_push_host: copy stream and per-chunk events (created on first use)
     cudaStream_t copy_stream = nullptr;
@@ -81,7 +87,7 @@ namespace fpic {
 
 enum { CNT_QUEUE = 0, CNT_HEAD = 1, CNT_ITERS = 2, CNT_NOTCONV = 3, CNT_REMOVED = 4,
        CNT_ALIVE = 5, CNT_EVALS = 6, CNT_ERR = 7, CNT_WORK = 8, CNT_SKIP = 9, CNT_PRIO = 10,
-       CNT_NORM = 11, CNT_SLOPE = 12, CNT_N = 13 };
+       CNT_NORM = 11, CNT_SLOPE = 12, CNT_STAGED = 13, CNT_N = 14 };
 
 int set_error(int code, const char* fmt, ...);
 int check_cuda(cudaError_t e, const char* what);

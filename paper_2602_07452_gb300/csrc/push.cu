@@ -13,6 +13,7 @@
 //   k_dg        discrete-gradient Hamiltonian scheme (geodesics), one thread
 //               per queued particle.
 #include <cuda.h>
+#include <limits.h>
 #include <math.h>
 #include <string.h>
 
@@ -81,6 +82,9 @@ struct PushK {
     float fmean[14], fistd[14];
     float oscale[6];        // corrector outputs 0-5 are residual / (s_i oscale_i)
     int restart_after;      // corrector: restart from the trial after this many iterations (0: never)
+    // field-tile staging (FPIC_TUNE_STAGE_FIELDS): six 2-D tensor maps of the
+    // coefficient arrays (device memory, 64-byte aligned); null = off
+    const uint8_t* stage_maps;
     // slope reuse (FPIC_TUNE_REUSE_SLOPE): SLOPE_ROWS x n, see SLOPE_*; null = off
     double* slope;
     int slope_cold;         // the cache holds nothing for these particles: do not look
@@ -164,18 +168,92 @@ __device__ __forceinline__ void F_at(const RunK& R, const double y[6], double qm
     eval_rhs(R.bh, y, qm, em, D, B, R.B0pot, f, H);
 }
 
-// Same, with sin/cos of y[1] supplied (from sincos_near).
-template <bool JAC = false>
+// Same, with sin/cos of y[1] supplied (from sincos_near).  STAGED: the
+// coefficient gather looks in the block's staged field tile T first.
+template <bool JAC = false, bool STAGED = false>
 __device__ __forceinline__ void F_at_sc(const RunK& R, const double y[6], double s, double c, double qm, bool em,
-                                        double f[6], double& H, RhsJ* J = nullptr)
+                                        double f[6], double& H, RhsJ* J = nullptr, const StageTile* T = nullptr)
 {
     double D[3] = {0, 0, 0}, B[3] = {0, 0, 0};
     if (em) {
         if (R.B0field != 0.0) wald_point_sc(R.bh, R.B0field, y[0], s, c, D, B);
+        else if (STAGED && R.has_coef) gather_c(R.G, R.FC, y[0], y[1], D, B, *T);
         else if (R.has_coef) gather_c(R.G, R.FC, y[0], y[1], D, B);
         else gather(R.G, R.F, y[0], y[1], D, B);
     }
     eval_rhs_sc_t<JAC>(R.bh, y, s, c, qm, em, D, B, R.B0pot, f, H, J);
+}
+
+// Bounded waits of the field-tile staging (polls of the mbarrier).
+constexpr uint32_t STAGE_WAIT_POLLS = 1u << 22;
+
+// Block prologue of a staged push (every thread of the block calls it).
+// The block's alive particles are sorted by cell; the cells their last push
+// or sort left in P.cell give the block's range of coefficient cells, and
+// if the tile around it (one cell of margin for the RK4 stages' motion, one
+// more for the half-node sub-grids) fits STAGE_TI x STAGE_TJ, one thread
+// loads the six components' tiles into shared memory with TMA.  P.cell only
+// steers the choice of tile: a gather outside the tile reads global memory.
+__device__ __forceinline__ StageTile stage_fields(const PushK& k, long long p, bool valid, double* s_coef,
+                                                  uint64_t* mbar, int* s_red)
+{
+    const uint32_t Nth = (uint32_t)k.run.G.Nth;
+    int imin = INT_MAX, imax = INT_MIN, jmin = INT_MAX, jmax = INT_MIN;
+    if (valid && k.P.alive[p]) {
+        const uint32_t cell = k.P.cell[p];
+        imin = imax = (int)(cell / Nth);
+        jmin = jmax = (int)(cell % Nth);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        imin = min(imin, __shfl_xor_sync(0xffffffffu, imin, o));
+        imax = max(imax, __shfl_xor_sync(0xffffffffu, imax, o));
+        jmin = min(jmin, __shfl_xor_sync(0xffffffffu, jmin, o));
+        jmax = max(jmax, __shfl_xor_sync(0xffffffffu, jmax, o));
+    }
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        s_red[4 * warp + 0] = imin;
+        s_red[4 * warp + 1] = imax;
+        s_red[4 * warp + 2] = jmin;
+        s_red[4 * warp + 3] = jmax;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < nw; ++w) {
+            imin = min(imin, s_red[4 * w + 0]);
+            imax = max(imax, s_red[4 * w + 1]);
+            jmin = min(jmin, s_red[4 * w + 2]);
+            jmax = max(jmax, s_red[4 * w + 3]);
+        }
+        const int ok = imax >= imin && imax - imin + 4 <= STAGE_TI && jmax - jmin + 4 <= STAGE_TJ;
+        const int i0 = imin - 2, j0 = jmin - 2;
+        if (ok) {
+            tc::mbar_init(mbar, 1);
+            tc::mbar_arrive_expect_tx(mbar, 6u * STAGE_TI * STAGE_TJ * 4u * 8u);
+#pragma unroll
+            for (int c = 0; c < 6; ++c)
+                tc::tma_load_2d(s_coef + c * STAGE_TI * STAGE_TJ * 4, k.stage_maps + 128 * c, 4 * j0, i0, mbar);
+        }
+        s_red[4 * nw + 0] = ok;
+        s_red[4 * nw + 1] = i0;
+        s_red[4 * nw + 2] = j0;
+        if (ok) atomicAdd((unsigned long long*)&k.cnt[CNT_STAGED], 1ull);
+    }
+    __syncthreads();
+    StageTile T{nullptr, s_red[4 * nw + 1], s_red[4 * nw + 2]};
+    if (s_red[4 * nw + 0]) {
+        if (tc::mbar_wait(mbar, 0, STAGE_WAIT_POLLS)) {
+            T.s = s_coef;
+        } else {
+            // the copies did not land in time: count it, give them one more
+            // bounded wait (the shared memory must not be left to a later
+            // block while they are in flight) and read global memory
+            atomicAdd((unsigned long long*)&k.cnt[CNT_ERR], 1ull);
+            tc::mbar_wait(mbar, 0, STAGE_WAIT_POLLS);
+        }
+    }
+    return T;
 }
 
 // Newton form of the implicit-midpoint iteration (Sec. 2.2.2 names a Newton
@@ -292,12 +370,17 @@ __device__ __forceinline__ void trial_store(const PushK& k, unsigned long long i
 // hybrid that also parks the RK4 slopes of each rejected particle
 // (corrector form of the learned guess); k1, k2 wait in shared memory
 // (12 KB per block) rather than in registers across the later stages.
-template <int MODE, bool BATCHED = false>
+template <int MODE, bool BATCHED = false, bool STAGED = false>
 __global__ void __launch_bounds__(128) k_explicit(const __grid_constant__ PushK k)
 {
     __shared__ double sk[MODE == 2 ? 12 : 1][128];
+    __shared__ __align__(128) double s_coef[STAGED ? 6 * STAGE_TI * STAGE_TJ * 4 : 2];
+    __shared__ __align__(8) uint64_t s_mbar;
+    __shared__ int s_red[4 * 4 + 4];
     const long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     long long p = k.p_begin + w;
+    StageTile tile{nullptr, 0, 0};
+    if (STAGED) tile = stage_fields(k, p, p < (k.p_end ? k.p_end : k.n), s_coef, &s_mbar, s_red);
     if (k.work) {
         if (w >= k.cnt[CNT_WORK]) return;
         p = k.work[w];
@@ -338,7 +421,7 @@ __global__ void __launch_bounds__(128) k_explicit(const __grid_constant__ PushK 
         c0 = __ldcs(k.slope + (size_t)SLOPE_C * k.n + p);
     } else {
         sincos(z0[1], &s0, &c0);
-        F_at_sc(R, z0, s0, c0, qm, em, kk, Hd);
+        F_at_sc<false, STAGED>(R, z0, s0, c0, qm, em, kk, Hd, nullptr, &tile);
     }
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
@@ -347,7 +430,7 @@ __global__ void __launch_bounds__(128) k_explicit(const __grid_constant__ PushK 
         if (MODE == 2) sk[i][threadIdx.x] = kk[i];
     }
     sincos_near(z0[1], s0, c0, y[1], sn, cn);
-    F_at_sc(R, y, sn, cn, qm, em, kk, Hd);
+    F_at_sc<false, STAGED>(R, y, sn, cn, qm, em, kk, Hd, nullptr, &tile);
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
         acc[i] = fma(2.0, kk[i], acc[i]);
@@ -355,11 +438,11 @@ __global__ void __launch_bounds__(128) k_explicit(const __grid_constant__ PushK 
         if (MODE == 2) sk[6 + i][threadIdx.x] = kk[i];
     }
     sincos_near(z0[1], s0, c0, y[1], sn, cn);
-    F_at_sc(R, y, sn, cn, qm, em, kk, Hd);
+    F_at_sc<false, STAGED>(R, y, sn, cn, qm, em, kk, Hd, nullptr, &tile);
 #pragma unroll
     for (int i = 0; i < 6; ++i) { acc[i] = fma(2.0, kk[i], acc[i]); y[i] = fma(dt, kk[i], z0[i]); }
     sincos_near(z0[1], s0, c0, y[1], sn, cn);
-    F_at_sc(R, y, sn, cn, qm, em, kk, Hd);
+    F_at_sc<false, STAGED>(R, y, sn, cn, qm, em, kk, Hd, nullptr, &tile);
     const double d6 = dt / 6.0;
 #pragma unroll
     for (int i = 0; i < 6; ++i) y[i] = fma(d6, acc[i] + kk[i], z0[i]);
@@ -368,7 +451,7 @@ __global__ void __launch_bounds__(128) k_explicit(const __grid_constant__ PushK 
     // trial point, kept for the next step if the trial is accepted
     double H1, fy[6];
     const bool keep = !BATCHED && k.slope && !k.record;
-    if (keep) F_at_sc(R, y, sn, cn, qm, em, fy, H1);
+    if (keep) F_at_sc<false, STAGED>(R, y, sn, cn, qm, em, fy, H1, nullptr, &tile);
     else H1 = eval_H_sc(R.bh, y, sn, cn, qm, R.B0pot);
     bool accept = true;
     if (MODE >= 1) {
@@ -396,7 +479,7 @@ __global__ void __launch_bounds__(128) k_explicit(const __grid_constant__ PushK 
         if (keep && alive) {
             if (y[1] != th_trial) {       // reflected at a pole: the slope of the stored state
                 sn = -sn;
-                F_at_sc(R, y, sn, cn, qm, em, fy, Hd);
+                F_at_sc<false, STAGED>(R, y, sn, cn, qm, em, fy, Hd, nullptr, &tile);
             }
             slope_store(k, p, y, qm, fy, sn, cn);
         }
@@ -1212,6 +1295,51 @@ static int field_coefs(fpic_ctx* c, const double* const fields[6], RunK& R, cuda
     return 0;
 }
 
+// Tensor maps of the six coefficient arrays for the field-tile staging
+// (FPIC_TUNE_STAGE_FIELDS): each component is a 2-D FP64 tensor of Nr + 1
+// rows of 4 ld values (a cell's four coefficients side by side), read in
+// boxes of STAGE_TI rows x 4 STAGE_TJ values.  Encoded on the host through
+// the driver's cuTensorMapEncodeTiled and copied to a library-owned device
+// buffer (a fresh one per coefficient buffer; the old one is retired).
+typedef CUresult (*PfnEncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static int stage_maps(fpic_ctx* c, PushK& k)
+{
+    if (!(c->d_stage_maps && c->stage_key == c->d_fcoef && c->stage_key_Nr == c->Nr && c->stage_key_ld == c->ld)) {
+        static PfnEncodeTiled enc = nullptr;
+        if (!enc) {
+            void* f = nullptr;
+            cudaDriverEntryPointQueryResult q;
+            FPIC_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q));
+            if (q != cudaDriverEntryPointSuccess || !f)
+                return set_error(FPIC_ECUDA, "field staging: cuTensorMapEncodeTiled not found");
+            enc = (PfnEncodeTiled)f;
+        }
+        alignas(64) CUtensorMap maps[6];
+        const size_t sz = (size_t)(c->Nr + 1) * c->ld;
+        const cuuint64_t dims[2] = {(cuuint64_t)4 * c->ld, (cuuint64_t)c->Nr + 1};
+        const cuuint64_t strides[1] = {(cuuint64_t)4 * c->ld * sizeof(double)};
+        const cuuint32_t box[2] = {4u * STAGE_TJ, (cuuint32_t)STAGE_TI};
+        const cuuint32_t es[2] = {1u, 1u};
+        for (int i = 0; i < 6; ++i) {
+            CUresult r = enc(&maps[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, (double*)c->d_fcoef + (size_t)i * 4 * sz, dims,
+                             strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return set_error(FPIC_ECUDA, "field staging: cuTensorMapEncodeTiled failed (%d)", (int)r);
+        }
+        retire(c, &c->d_stage_maps);
+        FPIC_CUDA(cudaMalloc(&c->d_stage_maps, sizeof maps));
+        FPIC_CUDA(cudaMemcpy(c->d_stage_maps, maps, sizeof maps, cudaMemcpyHostToDevice));
+        c->stage_key = c->d_fcoef;
+        c->stage_key_Nr = c->Nr;
+        c->stage_key_ld = c->ld;
+    }
+    k.stage_maps = (const uint8_t*)c->d_stage_maps;
+    return 0;
+}
+
 // Slope cache of a push (FPIC_TUNE_REUSE_SLOPE): points k at the context's
 // cache and marks it cold when the push's key differs from the previous
 // one's (another particle set or size, other fields, another grid) or the
@@ -1323,6 +1451,10 @@ static int push_core(fpic_ctx* c, fpic_particles* p, const double* const fields[
     if (has_fields && n > 0) {
         rc = field_coefs(c, fields, k.run, s);
         if (rc) return rc;
+        if (c->stage_fields && !ch && !host_state && p->cell) {
+            rc = stage_maps(c, k);
+            if (rc) return rc;
+        }
     }
     if (prm->scheme == FPIC_RK4 || prm->scheme >= FPIC_HYB1) {
         rc = slope_setup(c, p, fields, k.run.B0field, k);
@@ -1373,8 +1505,14 @@ static int push_core(fpic_ctx* c, fpic_particles* p, const double* const fields[
             if (ch) FPIC_CUDA(cudaStreamWaitEvent(s, ch->ready[j], 0));
             if (len <= 0) continue;
             const unsigned nbj = (unsigned)((len + TBx - 1) / TBx);
-            if (prm->scheme == FPIC_RK4) k_explicit<0><<<nbj, TBx, 0, s>>>(k);
-            else k_explicit<1><<<nbj, TBx, 0, s>>>(k);
+            if (k.stage_maps) {
+                if (prm->scheme == FPIC_RK4) k_explicit<0, false, true><<<nbj, TBx, 0, s>>>(k);
+                else k_explicit<1, false, true><<<nbj, TBx, 0, s>>>(k);
+            } else if (prm->scheme == FPIC_RK4) {
+                k_explicit<0><<<nbj, TBx, 0, s>>>(k);
+            } else {
+                k_explicit<1><<<nbj, TBx, 0, s>>>(k);
+            }
         }
         k.p_begin = 0;
         k.p_end = 0;
@@ -1410,6 +1548,8 @@ static int push_core(fpic_ctx* c, fpic_particles* p, const double* const fields[
         stats->n_removed = h[CNT_REMOVED];
         stats->n_rhs_evals = h[CNT_EVALS] + (explicit_pass ? 4 * h[CNT_ALIVE] : 0);
         stats->n_slope_reused = h[CNT_SLOPE];
+        stats->n_tiles_staged = h[CNT_STAGED];
+        if (h[CNT_ERR] > 0) return set_error(FPIC_ETIMEOUT, "fpic_push: %lld field-tile loads timed out", h[CNT_ERR]);
         if (k.slope) {
             // slope reuse: k1 only where not reused, the full right-hand side
             // at every trial's end point and at every converged IMR solve
@@ -1705,6 +1845,7 @@ extern "C" int fpic_push_noalloc(double M, double a, fpic_particles* p, const fp
         stats->n_removed = h[CNT_REMOVED];
         stats->n_rhs_evals = h[CNT_EVALS] + (explicit_pass ? 4 * h[CNT_ALIVE] : 0);
         stats->n_slope_reused = 0;
+        stats->n_tiles_staged = 0;
         if (h[CNT_NOTCONV] > 0) return FPIC_ENOTCONVERGED;
     }
     return FPIC_OK;
@@ -2242,6 +2383,7 @@ extern "C" int fpic_push_learned(fpic_ctx* c, fpic_mlp* m, fpic_particles* p, co
         stats->n_removed = h[CNT_REMOVED];
         stats->n_rhs_evals = h[CNT_EVALS] + 4 * (correct ? h[CNT_ALIVE] : h[CNT_WORK]);
         stats->n_slope_reused = h[CNT_SLOPE];
+        stats->n_tiles_staged = 0;
         if (k.slope) stats->n_rhs_evals += (correct ? h[CNT_ALIVE] : h[CNT_WORK]) - h[CNT_SLOPE] + h[CNT_QUEUE];
         if (h[CNT_NOTCONV] > 0) return FPIC_ENOTCONVERGED;
     }
@@ -2420,6 +2562,7 @@ static int push_batched(const fpic_run* runs, int nruns, fpic_mlp* m, fpic_parti
         stats->n_removed = h[CNT_REMOVED];
         stats->n_rhs_evals = h[CNT_EVALS] + (prm->scheme != FPIC_IMR ? 4 * h[CNT_ALIVE] : 0);
         stats->n_slope_reused = 0;
+        stats->n_tiles_staged = 0;
         if (h[CNT_NOTCONV] > 0) return FPIC_ENOTCONVERGED;
     }
     return FPIC_OK;
@@ -2466,6 +2609,11 @@ extern "C" int fpic_set_tuning(fpic_ctx* c, int key, int value)
         c->reuse_slope = value;
         c->slope_key_n = -1;
         return FPIC_OK;
+    case FPIC_TUNE_STAGE_FIELDS:
+        if (value != 0 && value != 1)
+            return set_error(FPIC_EINVAL, "fpic_set_tuning: field staging must be 0 or 1, got %d", value);
+        c->stage_fields = value;
+        return FPIC_OK;
     default:
         return set_error(FPIC_EINVAL, "fpic_set_tuning: unknown key %d", key);
     }
@@ -2486,6 +2634,9 @@ extern "C" int fpic_get_tuning(const fpic_ctx* c, int key, int* value)
         return FPIC_OK;
     case FPIC_TUNE_REUSE_SLOPE:
         *value = c->reuse_slope;
+        return FPIC_OK;
+    case FPIC_TUNE_STAGE_FIELDS:
+        *value = c->stage_fields;
         return FPIC_OK;
     default:
         return set_error(FPIC_EINVAL, "fpic_get_tuning: unknown key %d", key);

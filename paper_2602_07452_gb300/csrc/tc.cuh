@@ -100,6 +100,26 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint3
     return false;
 }
 
+// Tensor-memory-accelerator (TMA) tile load: the box of the 2-D tensor map
+// at element coordinates (x inner, y outer) into shared memory, completing
+// on mbar as transaction bytes.  map: a CUtensorMap in global, constant or
+// parameter memory; x times the element size must be a multiple of 16 bytes
+// (negative or out-of-range coordinates read zeros).
+__device__ __forceinline__ void tma_load_2d(void* smem, const void* map, int x, int y, uint64_t* mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
+        ::"r"(smem_addr(smem)), "l"(map), "r"(x), "r"(y), "r"(smem_addr(mbar))
+        : "memory");
+}
+
+// One arrival on mbar that also announces `bytes` of transactions to come.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(mbar)), "r"(bytes)
+                 : "memory");
+}
+
 // 32 consecutive FP32 columns of this thread's TMEM lane (warp w reads lanes
 // 32 (w % 4) .. +31).
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v)

@@ -54,7 +54,7 @@ class fpic_push_params(C.Structure):
 class fpic_push_stats(C.Structure):
     _fields_ = [("n_alive_before", C.c_int64), ("n_implicit", C.c_int64), ("n_iter_total", C.c_int64),
                 ("n_notconv", C.c_int64), ("n_removed", C.c_int64), ("n_rhs_evals", C.c_int64),
-                ("n_slope_reused", C.c_int64)]
+                ("n_slope_reused", C.c_int64), ("n_tiles_staged", C.c_int64)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -92,6 +92,7 @@ class fpic_learned_cfg(C.Structure):
 
 FPIC_LEARN_SKIP, FPIC_LEARN_CORRECT = 0, 1
 FPIC_TUNE_IMR_BLOCKS_PER_SM, FPIC_TUNE_DEP_THREADS, FPIC_TUNE_STATIC_FIELDS, FPIC_TUNE_REUSE_SLOPE = 0, 1, 2, 3
+FPIC_TUNE_STAGE_FIELDS = 4
 
 
 # name -> (restype, argtypes)
