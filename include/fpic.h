@@ -330,7 +330,7 @@ int fpic_probe_fp64(double *gflops_out, int reps);
  *     fields stages, per block of 128 particles, the interpolation
  *     coefficients of the cells the block's particles occupy (from p->cell,
  *     as the last push or fpic_sort left it; the block's cells plus two
- *     cells of margin, up to 5 x 8 coefficient cells per component) in
+ *     cells of margin, up to 5 x 16 coefficient cells per component) in
  *     shared memory with TMA tensor loads; gathers outside the tile read
  *     global memory, so results are bitwise those without staging.  Pays
  *     only for particles sorted by cell (the PIC step sorts them in its

@@ -283,7 +283,7 @@ __device__ __forceinline__ void gather_c(const GridDev& G, const FieldsC& F, dou
 // each of the six components, starting at coefficient cell (i0, j0).  A
 // gather whose cell lies in the tile reads shared memory, any other the
 // global coefficients (so staging never changes a result).
-constexpr int STAGE_TI = 5, STAGE_TJ = 8;
+constexpr int STAGE_TI = 5, STAGE_TJ = 16;
 struct StageTile {
     const double* s;    // shared: [6][STAGE_TI][4 * STAGE_TJ]; nullptr = nothing staged
     int i0, j0;
