@@ -78,7 +78,8 @@ def parse():
                     help="plain steps sampled for the training set")
     ap.add_argument("--imr", choices=("fixed", "newton"), default="newton",
                     help="IMR iteration of the headline push: the fixed-point update or the Newton form")
-    ap.add_argument("--workload", default="push", choices=["push", "pic", "neutral", "batched", "clean", "inject", "adaptive", "charged_dg"])
+    ap.add_argument("--workload", default="push", choices=["push", "pic", "neutral", "batched", "clean", "inject", "adaptive",
+                                                          "charged_dg", "learned_analysis"])
     ap.add_argument("--clean-sweeps", type=int, default=500, help="Jacobi sweeps of --workload clean")
     ap.add_argument("--conserving", action="store_true", help="--workload pic with the charge-conserving deposit")
     ap.add_argument("--inject-every", type=int, default=0, help="--workload pic: pair injection every K steps")
@@ -536,6 +537,115 @@ def run_gpu(args, ws, rank, local):
                 "rhs_evals_per_particle_step": lead["evals"] / lp0, "max_dH_over_D0": lead["max_dH"],
                 "note": "same corrector with a zero network: guess = trial + (2/3) A - (1/6) B"}
     return line
+
+
+def run_skip_analysis(device, n=1 << 20, gen_steps=10, eval_steps=10, time_steps=10, train_steps=3000,
+                      thresholds=(0.5, 0.6, 0.7, 0.8, 0.9, 0.95, 0.99)):
+    """The scheme verdict as a learned classifier (skip form): how well the
+    network's rejection probability predicts the plain Hyb1 test on held-out
+    steps, what the skip push gains at each cut, and what a perfect
+    classifier with free inference could gain at most.
+
+    Charged Wald workload (Newton IMR, slope reuse).  The network is trained
+    on `gen_steps` plain steps, then evaluated on the next `eval_steps` steps
+    (features before each step, the plain push's own verdict after it).
+    Timing: `time_steps` steps from one saved state for the plain push and
+    for the skip push at each cut.  Bound: the plain step minus the RK4
+    trials of the rejected particles plus their extra IMR iterations when
+    started from z^n instead of the trial (pure IMR from the same state),
+    inference free."""
+    import torch
+    from paper_2602_07452_gb300 import learned as L
+    F, g, ctx, fields, p = setup(n, 0, device)
+    F.fpic_set_tuning(ctx, F.FPIC_TUNE_STATIC_FIELDS, 1)
+    F.fpic_set_tuning(ctx, F.FPIC_TUNE_REUSE_SLOPE, 1)
+    F.fpic_set_tuning(ctx, F.FPIC_TUNE_IMR_BLOCKS_PER_SM, 2)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    for e in ev:
+        e.record()
+    prm = F.push_params(DT, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=HYB1_THR, r_max=float(g.rn[-1]),
+                        B0pot=B0, events=ev[1:5], imr_newton=True)
+    for _ in range(3):
+        F.fpic_push(ctx, p, fields, prm)
+    cfg = L.fit_cfg(ctx, p, fields, prm, p_skip=0.5, mode=F.FPIC_LEARN_SKIP)
+    X, T, S = L.generate(ctx, p, fields, prm, cfg, steps=gen_steps)
+    net, P, hist = L.train(X, T, S, steps=train_steps, batch=8192, lr=3e-3, log_every=1000)
+    del X, T, S
+    # held-out steps: predicted rejection probability against the plain verdict
+    probs, labels = [], []
+    for _ in range(eval_steps):
+        alive = p.alive.bool().clone()
+        Xh = F.fpic_features(ctx, p, fields, DT, cfg)
+        y = net.forward(Xh)
+        F.fpic_push(ctx, p, fields, prm)
+        probs.append(torch.sigmoid(y[:, 6])[alive])
+        labels.append((p.scheme == 1)[alive])
+    prob, lab = torch.cat(probs), torch.cat(labels)
+    pos = int(lab.sum().item())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, steps):
+        t = ps = it = impl = 0.0
+        for _ in range(steps):
+            torch.cuda.synchronize()
+            e0.record()
+            st = fn()
+            e1.record()
+            torch.cuda.synchronize()
+            t += e0.elapsed_time(e1)
+            ps += st["n_alive_before"]; it += st["n_iter_total"]; impl += st["n_implicit"]
+        return t / steps, ps, it, impl
+
+    F.fpic_push(ctx, p, fields, prm)                   # the cache holds the state after this push
+    snap = _snapshot(p)
+    t_plain, ps_plain, it_plain, impl_plain = timed(lambda: F.fpic_push(ctx, p, fields, prm, stats=True), time_steps)
+    t_ex = ev[1].elapsed_time(ev[2])
+    dH_plain = _max_dH(F, ctx, p)
+    rows = []
+    for thr in thresholds:
+        pred = prob > thr
+        tp = int((pred & lab).sum().item()); fp = int((pred & ~lab).sum().item())
+        _restore(p, snap)
+        cfg.p_skip = thr
+        t_l, ps_l, it_l, impl_l = timed(lambda: F.fpic_push_learned(ctx, net, p, fields, prm, cfg, stats=True),
+                                        time_steps)
+        rows.append({"p_skip": thr, "precision": tp / max(tp + fp, 1), "recall": tp / max(pos, 1),
+                     "skipped_fraction": (tp + fp) / max(lab.numel(), 1),
+                     "ms_per_step": t_l, "ratio_vs_plain": (ps_l / t_l) / (ps_plain / t_plain),
+                     "implicit_fraction": impl_l / max(ps_l, 1), "mean_imr_iterations": it_l / max(impl_l, 1),
+                     "max_dH_over_D0": _max_dH(F, ctx, p)})
+    # pure IMR from z^n on the same state: iterations per solve without the trial as guess
+    _restore(p, snap)
+    prm_i = F.push_params(DT, scheme=F.FPIC_IMR, r_max=float(g.rn[-1]), B0pot=B0, imr_newton=True)
+    torch.cuda.synchronize()
+    e0.record()
+    st_i = F.fpic_push(ctx, p, fields, prm_i, stats=True)
+    e1.record()
+    torch.cuda.synchronize()
+    t_imr_all = e0.elapsed_time(e1)
+    it_zn = st_i["n_iter_total"] / max(st_i["n_implicit"], 1)
+    t_iter = t_imr_all / max(st_i["n_iter_total"], 1)               # ms per IMR iteration, all particles busy
+    it_trial = it_plain / max(impl_plain, 1)
+    n_rej = impl_plain / time_steps
+    n_alive = ps_plain / time_steps
+    t_trial = t_ex / max(n_alive, 1)
+    bound = t_plain - n_rej * t_trial + n_rej * max(it_zn - it_trial, 0.0) * t_iter
+    _restore(p, snap)
+    return {"workload": f"charged Wald test particles, a={A_SPIN}, {n} particles, Hyb1 RK4 <-> IMR (Newton)",
+            "training": {"samples_steps": gen_steps, "train_steps": train_steps, "loss_first_last": [hist[0][1], hist[-1][1]]},
+            "held_out": {"steps": eval_steps, "particle_steps": int(lab.numel()), "rejected_fraction": pos / max(lab.numel(), 1)},
+            "plain": {"ms_per_step": t_plain, "explicit_ms": t_ex, "implicit_fraction": impl_plain / max(ps_plain, 1),
+                      "mean_imr_iterations_from_trial": it_trial, "max_dH_over_D0": dH_plain},
+            "skip_cuts": rows,
+            "imr_from_zn": {"mean_iterations": it_zn, "ms_per_iteration_all_busy": t_iter},
+            "bound_perfect_classifier_free_inference": {
+                "ms_per_step": bound, "ratio_vs_plain": t_plain / bound,
+                "note": "rejected particles skip their RK4 trial (t_explicit / n each) and pay "
+                        "(IMR iterations from z^n - from the trial) x the IMR iteration cost"},
+            "bound_corrector_floor_2_iterations": {
+                "ratio_vs_plain": t_plain / max(t_plain - n_rej * max(it_trial - 2.0, 0.0) * t_iter, 1e-9),
+                "note": "every corrected solve in 2 iterations (a guess within bf16 precision of the "
+                        "solution still needs one update and one confirming iteration), inference free"}}
 
 
 def run_neutral(args, device, n, steps, K=32, seed=1, pre_steps=1000, scheme="HYB2"):
@@ -1071,6 +1181,17 @@ def main():
     import torch.distributed as dist
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if args.workload == "learned_analysis":
+        import torch
+        torch.cuda.set_device(local)
+        if rank == 0:
+            res = run_skip_analysis(torch.device("cuda", local))
+            print(json.dumps({"metric": "learned skip form: precision / recall and step time vs plain", "value":
+                              max(r["ratio_vs_plain"] for r in res["skip_cuts"]), "unit": "ratio", "n_gpus": 1,
+                              "steps": 10, "warmup": 3, "ms_per_step": res["plain"]["ms_per_step"],
+                              "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                              "data": "synthetic", "config": res}))
+        return 0
     if args.workload == "charged_dg":
         torch.cuda.set_device(local)
         res = run_charged_dg(torch.device("cuda", local), args.n, max(args.steps, 1))
@@ -1151,6 +1272,7 @@ def main():
         line["adaptive_dt_neutral"] = run_adaptive_neutral(dev)
         line["inject"] = run_inject(dev, 1024, 16)
         line["charged_dg"] = run_charged_dg(dev)
+        line["learned_skip_analysis"] = run_skip_analysis(dev)
     if rank == 0:
         if pool is not None:
             try:
