@@ -31,6 +31,10 @@ METRIC = "particle-steps/s at fixed max |ΔH|/H; learned-guess vs plain hybrid, 
 UNIT = "particle-steps/s"
 A_SPIN, B0, THETA_T, QM, DT, NGRID = 0.9, 1.0, 0.1, 100.0, 1e-3, 512
 HYB1_THR = 3.5e-6          # (d Htilde/dt)_max of the Hyb1 test
+# an IMR step whose solve does not converge, or whose end point changes H by
+# more than 1e-4 D_0 (both found near the polar axis), is redone in up to 2^8
+# substeps
+IMR_SUBSTEPS, SUBSTEP_TOL = 8, 1e-4
 # Algorithmic FP64 flops (FMA = 2, add/mul/div/sqrt/rsqrt = 1, sin+cos = 2),
 # counted from the formulas of the push.
 # metric (31) + derivatives (46) + gather (4 cell weights x 2 + 6 components x
@@ -78,6 +82,10 @@ def parse():
                     help="plain steps sampled for the training set")
     ap.add_argument("--imr", choices=("fixed", "newton"), default="newton",
                     help="IMR iteration of the headline push: the fixed-point update or the Newton form")
+    ap.add_argument("--imr-substeps", type=int, default=IMR_SUBSTEPS,
+                    help="levels of substeps for unconverged or inaccurate IMR steps (0: off)")
+    ap.add_argument("--substep-tol", type=float, default=SUBSTEP_TOL,
+                    help="|dH|/D0 of an IMR step above which it is redone in substeps (0: unconverged only)")
     ap.add_argument("--workload", default="push", choices=["push", "pic", "neutral", "batched", "clean", "inject", "adaptive",
                                                           "charged_dg", "learned_analysis"])
     ap.add_argument("--clean-sweeps", type=int, default=500, help="Jacobi sweeps of --workload clean")
@@ -332,14 +340,15 @@ def run_gpu(args, ws, rank, local):
         e.record()
     torch.cuda.synchronize()
     newton = args.imr == "newton"
+    sub = dict(imr_substeps=args.imr_substeps, substep_tol=args.substep_tol)
     prm = F.push_params(DT, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=HYB1_THR, r_max=float(g.rn[-1]),
-                        B0pot=B0, events=ev[1:5], imr_newton=newton)
+                        B0pot=B0, events=ev[1:5], imr_newton=newton, **sub)
     for _ in range(args.warmup):
         F.fpic_push(ctx, p, fields, prm, stats=True)
     # launch shape of the implicit solver, timed on these particles (untimed here)
     from paper_2602_07452_gb300 import autotune
     prm_t = F.push_params(DT, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=HYB1_THR, r_max=float(g.rn[-1]),
-                          B0pot=B0, imr_newton=newton)
+                          B0pot=B0, imr_newton=newton, **sub)
     tune_ms = autotune.tune_imr_blocks(ctx, p, fields, prm_t)
     learned = None
     train_info = None
@@ -348,7 +357,7 @@ def run_gpu(args, ws, rank, local):
         # the network learns from the plain pusher's own steps (untimed)
         from paper_2602_07452_gb300 import learned as L
         prm_plain = F.push_params(DT, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=HYB1_THR,
-                                  r_max=float(g.rn[-1]), B0pot=B0, imr_newton=newton)
+                                  r_max=float(g.rn[-1]), B0pot=B0, imr_newton=newton, **sub)
         t0 = time.perf_counter()
         mode = F.FPIC_LEARN_CORRECT if args.learned_form == "correct" else F.FPIC_LEARN_SKIP
         cfg = L.fit_cfg(ctx, p, fields, prm_plain, p_skip=0.7, mode=mode, restart_after=args.learned_restart)
@@ -407,7 +416,7 @@ def run_gpu(args, ws, rank, local):
     after_plain = _snapshot(p)
     _restore(p, snap)
     prm_o = F.push_params(DT, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=HYB1_THR, r_max=float(g.rn[-1]),
-                          B0pot=B0, events=ev[1:5], imr_newton=not newton)
+                          B0pot=B0, events=ev[1:5], imr_newton=not newton, **sub)
     F.fpic_push(ctx, p, fields, prm_o)
     _restore(p, snap)
     torch.cuda.synchronize()
@@ -423,7 +432,7 @@ def run_gpu(args, ws, rank, local):
         getattr(hp, f).copy_(getattr(p, f).cpu())
     hp.alive.copy_(p.alive.cpu())
     prm_h = F.push_params(DT, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=HYB1_THR, r_max=float(g.rn[-1]),
-                          B0pot=B0, imr_newton=newton)
+                          B0pot=B0, imr_newton=newton, **sub)
     e2e_steps = max(1, min(args.steps, 20))
     for _ in range(2):
         F.fpic_push_host(ctx, hp, fields, prm_h)
@@ -461,6 +470,8 @@ def run_gpu(args, ws, rank, local):
                    "particles_per_gpu": args.n, "theta_T": THETA_T, "q_over_m": QM, "dt": DT,
                    "scheme": "Hyb1 RK4<->IMR (plain)", "hyb1_thr": HYB1_THR, "tol": 1e-14,
                    "imr_iteration": "Newton (momentum columns of dF)" if newton else "fixed point (Eq. imr2)",
+                   "imr_substeps": {"levels": args.imr_substeps, "H_tol": args.substep_tol,
+                                    "rule": "an unconverged solve is redone in 2, 4, ... substeps"},
                    "implicit_fraction": plain["impl"] / psteps,
                    "mean_imr_iterations": plain["iters"] / max(plain["impl"], 1),
                    "rhs_evals_per_particle_step": plain["evals"] / psteps,

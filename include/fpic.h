@@ -116,7 +116,20 @@ typedef struct {
  *               error bound theta_i / (1 - theta_i) |dz_i| (theta_i the
  *               ratio of its last two updates) is within tol (|z_i| + 1):
  *               about a third of the iterations of the fixed-point update
- *               for charged particles.  Any nonzero = 1. */
+ *               for charged particles.  Any nonzero = 1.
+ *   imr_substeps: K > 0: an IMR solve that reaches max_iter without
+ *               converging (found within a few 1e-4 rad of the polar axis,
+ *               where the step under-resolves the turn) is redone from z^n
+ *               as m = 2, 4, ..., 2^K substeps of the implicit step / m,
+ *               each an IMR solve of the same form from its own start
+ *               state, the pole reflection applied after each; the first
+ *               level whose solves all converge and whose end point has
+ *               |H - H(z^n)| / D_0 <= substep_tol (0: no H condition) is
+ *               kept, else the finest level whose solves all converged,
+ *               else the smallest-update iterate of the full step (counted
+ *               in n_notconv).  Iterations of every attempt count in
+ *               n_iter_total.  0 = off (0..12).
+ *   substep_tol: see imr_substeps. */
 typedef struct {
     double dt;
     int scheme;
@@ -133,6 +146,8 @@ typedef struct {
     double *t;
     double B0field;
     int imr_newton;
+    int imr_substeps;
+    double substep_tol;
 } fpic_push_params;
 
 /* Host-side counters of one push (filled only when a pointer is passed;

@@ -62,7 +62,7 @@ class PushParams(C.Structure):
                 ("scheme", C.c_int), ("implicit_kind", C.c_int), ("thr", C.c_double),
                 ("tol", C.c_double), ("max_iter", C.c_int), ("r_h", C.c_double),
                 ("r_max", C.c_double), ("dg_eps", C.c_double), ("dt_imp", C.c_double),
-                ("imr_newton", C.c_int)]
+                ("imr_newton", C.c_int), ("imr_substeps", C.c_int), ("substep_tol", C.c_double)]
 
 
 _D = C.POINTER(C.c_double)
@@ -85,7 +85,7 @@ def _declare(L):
     L.or_dg_quot_em.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, _D, _D, C.c_int, _D]
     L.or_wald_A.argtypes = [C.c_double, C.c_double, _I64, _D, _D, _D, _D]
     L.or_push.argtypes = [C.POINTER(PushParams), C.c_int, C.c_int, C.c_int, _D, _D, _D, _D,
-                          C.POINTER(_D), _I64, _D, _D, _D, _D, _D, _U8, _U8, _U8]
+                          C.POINTER(_D), _I64, _D, _D, _D, _D, _D, _U8, _U8, _U8, _U8]
     L.or_push.restype = _I64
     L.or_wald_on_grid.argtypes = [C.c_double, C.c_double, C.c_int, C.c_int, C.c_int, _D, _D, _D, _D,
                                   C.POINTER(_D)]
@@ -243,16 +243,19 @@ def wald_on_grid(a, B0, g):
 
 def push_params(M=1.0, a=0.9, B0pot=0.0, field_kind=FIELD_NONE, B0field=0.0, dt=0.01,
                 scheme=RK4, implicit_kind=IMR, thr=1e-12, tol=1e-14, max_iter=50,
-                r_h=None, r_max=1e300, dg_eps=1e-10, dt_imp=0.0, imr_newton=False):
+                r_h=None, r_max=1e300, dg_eps=1e-10, dt_imp=0.0, imr_newton=False, imr_substeps=0,
+                substep_tol=0.0):
     if r_h is None:
         r_h = M + np.sqrt(M * M - a * a)
     return PushParams(M, a, B0pot, field_kind, B0field, dt, scheme, implicit_kind, thr, tol,
-                      max_iter, r_h, r_max, dg_eps, dt_imp, int(bool(imr_newton)))
+                      max_iter, r_h, r_max, dg_eps, dt_imp, int(bool(imr_newton)), int(imr_substeps),
+                      float(substep_tol))
 
 
-def push(p: PushParams, z, qm, H0, D0, Hn, alive, g=None, F=None):
+def push(p: PushParams, z, qm, H0, D0, Hn, alive, g=None, F=None, flags=False):
     """One step of all particles, in place on z (n x 6), Hn and alive.
-    Returns (n_not_converged, scheme[n], iters[n])."""
+    Returns (n_not_converged, scheme[n], iters[n]), and with flags=True also
+    the per-particle not-converged flags."""
     n = z.shape[0]
     assert z.dtype == np.float64 and z.flags.c_contiguous
     sch = np.zeros(n, np.uint8)
@@ -265,9 +268,10 @@ def push(p: PushParams, z, qm, H0, D0, Hn, alive, g=None, F=None):
         e = np.zeros(2)
         gargs = (1, 1, 2, ptr(e), ptr(e), ptr(e), ptr(e))
         Fp = None
+    ncf = np.zeros(n, np.uint8)
     nc = lib().or_push(C.byref(p), *gargs, Fp, n, ptr(z), ptr(f64(qm)), ptr(f64(H0)),
-                       ptr(f64(D0)), ptr(Hn), ptr(alive, _U8), ptr(sch, _U8), ptr(its, _U8))
-    return nc, sch, its
+                       ptr(f64(D0)), ptr(Hn), ptr(alive, _U8), ptr(sch, _U8), ptr(its, _U8), ptr(ncf, _U8))
+    return (nc, sch, its, ncf) if flags else (nc, sch, its)
 
 
 def seed_orbits(M, a, cand):

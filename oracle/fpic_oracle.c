@@ -354,6 +354,8 @@ typedef struct {
     double dg_eps;         /* discrete-gradient increment threshold */
     double dt_imp;         /* step of the implicit partner of a hybrid (0: dt) */
     int imr_newton;        /* IMR solver: 0 the fixed-point map of Eq. (imr2), 1 Newton */
+    int imr_substeps;      /* an unconverged IMR solve is redone in up to 2^this substeps (0: never) */
+    double substep_tol;    /* |H(end) - H(z^n)| / D_0 a substepped step must meet (0: none) */
 } or_push_params;
 
 typedef struct {
@@ -802,6 +804,66 @@ static int particle_bc(const or_push_params *p, double *z)
     return 1;
 }
 
+/* An IMR step whose solve did not converge, or whose end point has
+ * |H - H^n| / D_0 > substep_tol (reading: the paper gives no policy; such
+ * steps are found within a few 1e-4 rad of the polar axis, where the
+ * u_ph^2 / sin^3 th terms change faster than the step resolves and a
+ * solve either fails or converges to an inaccurate end point):
+ * the step is redone from z^n as m = 2, 4, ..., 2^K substeps of h/m, each
+ * an IMR solve of the same form (capped at min(max_iter, 16) iterations: a
+ * level whose substeps need more is too coarse) started from the substep's
+ * own start state,
+ * with the pole reflection of the particle boundaries applied after each
+ * substep.  The first level whose solves all converge and whose end state
+ * has |H - H(z^n)| / D_0 <= substep_tol (0: no H condition) is taken;
+ * failing that, the finest level whose solves all converged; failing that,
+ * nothing (the full-step solve's own result stands).  *its accumulates the
+ * iterations of every attempt.  Returns 1 if a level was taken. */
+static int imr_substeps(const or_ctx *c, double h, const double *z0, double H0ref, double D0, double *z1, int *its);
+
+/* The full-step IMR solve's outcome it (iterations, negative if it did not
+ * converge) and end point z1, revised by the substeps when they apply. */
+static int imr_revise(const or_ctx *c, double h, const double *z0, double Hn, double D0, double *z1, int it)
+{
+    const or_push_params *p = c->p;
+    or_bh bh = {p->M, p->a, p->B0pot};
+    if (p->imr_substeps <= 0) return it;
+    if (!(it < 0 || (p->substep_tol > 0.0 && fabs(ham(&bh, c->qm, z1) - Hn) / D0 > p->substep_tol))) return it;
+    int sit = 0;
+    const int ok = imr_substeps(c, h, z0, ham(&bh, c->qm, z0), D0, z1, &sit);
+    const int mag = (it < 0 ? -it : it) + sit;
+    return (it >= 0 || ok) ? mag : -mag;
+}
+static int imr_substeps(const or_ctx *c, double h, const double *z0, double H0ref, double D0, double *z1, int *its)
+{
+    const or_push_params *p = c->p;
+    or_bh bh = {p->M, p->a, p->B0pot};
+    or_push_params ps = *p;
+    ps.max_iter = p->max_iter < 16 ? p->max_iter : 16;
+    const or_ctx cs = {&ps, c->g, c->F, c->qm};
+    double best[6];
+    int have = 0;
+    for (int k = 1; k <= p->imr_substeps; ++k) {
+        const int m = 1 << k;
+        double zs[6], zn[6];
+        memcpy(zs, z0, sizeof zs);
+        int ok = 1;
+        for (int s = 0; s < m && ok; ++s) {
+            const int it = step_imr(&cs, h / m, zs, zs, zn);
+            *its += it < 0 ? -it : it;
+            if (it < 0) ok = 0;
+            particle_bc(p, zn);
+            memcpy(zs, zn, sizeof zs);
+        }
+        if (!ok) continue;
+        memcpy(best, zs, sizeof best);
+        have = 1;
+        if (p->substep_tol <= 0.0 || fabs(ham(&bh, c->qm, zs) - H0ref) / D0 <= p->substep_tol) break;
+    }
+    if (have) memcpy(z1, best, sizeof best);
+    return have;
+}
+
 /* One step of one particle.  Hybrid (Sec. 3.1.2): RK4 trial, then
  *   Hyb2: accept iff Ht^{n+1} < Ht_max,
  *   Hyb1: accept iff (Ht^{n+1} - Ht^n)/dt < (dHt/dt)_max,
@@ -823,6 +885,7 @@ static int push_one(const or_ctx *c, double *z, double H0, double D0, double *Hn
     } else if (p->scheme == OR_IMR) {
         it = step_imr(c, p->dt, z0, z0, z1);
         implicit = 1;
+        it = imr_revise(c, p->dt, z0, *Hn, D0, z1, it);
     } else if (p->scheme == OR_HAM) {
         it = step_ham(c, p->dt, z0, z0, z1);
         implicit = 1;
@@ -854,8 +917,12 @@ static int push_one(const or_ctx *c, double *z, double H0, double D0, double *Hn
                 const double ratio = hi / p->dt;
                 for (int i = 0; i < 6; ++i) guess[i] = z0[i] + (trial[i] - z0[i]) * ratio;
             }
-            if (p->implicit_kind == OR_HAM) it = step_ham(c, hi, z0, guess, z1);
-            else it = step_imr(c, hi, z0, guess, z1);
+            if (p->implicit_kind == OR_HAM) {
+                it = step_ham(c, hi, z0, guess, z1);
+            } else {
+                it = step_imr(c, hi, z0, guess, z1);
+                it = imr_revise(c, hi, z0, *Hn, D0, z1, it);
+            }
         }
     }
     *Hn = ham(&bh, c->qm, z1);
@@ -985,16 +1052,19 @@ int64_t or_push(const or_push_params *p, int Nr, int Nth, int ld, const double *
                 const double *rh, const double *tn, const double *th,
                 const double *const *F, int64_t n, double *z, const double *qm,
                 const double *H0, const double *D0, double *Hn, uint8_t *alive,
-                uint8_t *scheme_out, uint8_t *iters_out)
+                uint8_t *scheme_out, uint8_t *iters_out, uint8_t *notconv_out)
 {
     or_grid g = {Nr, Nth, ld, rn, rh, tn, th};
     int64_t notconv = 0;
     for (int64_t k = 0; k < n; ++k) {
         scheme_out[k] = 0;
         iters_out[k] = 0;
+        if (notconv_out) notconv_out[k] = 0;
         if (!alive[k]) continue;
         or_ctx c = {p, &g, F, qm[k]};
-        notconv += push_one(&c, z + 6 * k, H0[k], D0[k], Hn + k, scheme_out + k, iters_out + k);
+        const int nc = push_one(&c, z + 6 * k, H0[k], D0[k], Hn + k, scheme_out + k, iters_out + k);
+        notconv += nc;
+        if (notconv_out) notconv_out[k] = (uint8_t)nc;
         if (!particle_bc(p, z + 6 * k)) alive[k] = 0;
     }
     return notconv;

@@ -87,7 +87,7 @@ namespace fpic {
 
 enum { CNT_QUEUE = 0, CNT_HEAD = 1, CNT_ITERS = 2, CNT_NOTCONV = 3, CNT_REMOVED = 4,
        CNT_ALIVE = 5, CNT_EVALS = 6, CNT_ERR = 7, CNT_WORK = 8, CNT_SKIP = 9, CNT_PRIO = 10,
-       CNT_NORM = 11, CNT_SLOPE = 12, CNT_STAGED = 13, CNT_N = 14 };
+       CNT_NORM = 11, CNT_SLOPE = 12, CNT_STAGED = 13, CNT_STRAG = 14, CNT_N = 15 };
 
 int set_error(int code, const char* fmt, ...);
 int check_cuda(cudaError_t e, const char* what);

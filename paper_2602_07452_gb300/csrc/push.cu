@@ -85,6 +85,13 @@ struct PushK {
     // field-tile staging (FPIC_TUNE_STAGE_FIELDS): six 2-D tensor maps of the
     // coefficient arrays (device memory, 64-byte aligned); null = off
     const uint8_t* stage_maps;
+    // substeps of unconverged IMR solves (fpic_push_params.imr_substeps):
+    // levels K (0 = off), H condition, and the list of the solves' queue
+    // slots (particle indices in all_mode), CNT_STRAG entries
+    int substeps;
+    double substep_tol;
+    uint32_t* strag;
+    uint8_t* strag_flag;    // by queue slot: k_imr's solve did not converge
     // slope reuse (FPIC_TUNE_REUSE_SLOPE): SLOPE_ROWS x n, see SLOPE_*; null = off
     double* slope;
     int slope_cold;         // the cache holds nothing for these particles: do not look
@@ -738,6 +745,7 @@ __global__ void __launch_bounds__(128, NEWTON ? 3 : 4) k_imr(const __grid_consta
                 const int its_done = conv ? it : k.max_iter;
                 if (conv) n_it += it;
                 else ++n_nc;
+                if (!conv && k.substeps > 0 && !k.record) k.strag_flag[qi] = 1;
                 if (k.record && k.featS) {
                     // corrector form: row = queue slot, (gap to the trial - leading-order gap) / (s_i oscale_i)
                     float* t = k.recT + 16 * qi;
@@ -773,6 +781,72 @@ __global__ void __launch_bounds__(128, NEWTON ? 3 : 4) k_imr(const __grid_consta
     warp_add(&k.cnt[CNT_EVALS], n_ev, FULL);
 }
 
+// Pole reflection of the particle boundaries (Sec. 2.5, reading: th -> -th
+// or 2 pi - th, u_th -> -u_th, ph -> ph + pi), as in finish.
+__device__ __forceinline__ void reflect_pole(double z[6])
+{
+    if (z[1] < 0.0) {
+        z[1] = -z[1];
+        z[4] = -z[4];
+        z[2] += M_PI;
+    } else if (z[1] > M_PI) {
+        z[1] = 2.0 * M_PI - z[1];
+        z[4] = -z[4];
+        z[2] += M_PI;
+    }
+}
+
+// One implicit-midpoint solve of step h from zs (guess zs) by one thread,
+// with k_imr's iteration and stop rule; true if it converged within
+// max_iter (result in out), iterations added to its.
+template <bool NEWTON>
+__device__ bool imr_solve_serial(const PushK& k, const RunK& R, const double zs[6], double h, double qm, bool em,
+                                 int max_iter, double out[6], long long& its, long long& evals)
+{
+    double ss, cs, zk[6], dprev[6];
+    sincos(zs[1], &ss, &cs);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) zk[i] = zs[i];
+    for (int it = 0; it < max_iter; ++it) {
+        double y[6], f[6], H, zn[6], sy, cy;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) y[i] = 0.5 * (zs[i] + zk[i]);
+        sincos_near(zs[1], ss, cs, y[1], sy, cy);
+        RhsJ J;
+        F_at_sc<NEWTON>(R, y, sy, cy, qm, em, f, H, &J);
+        ++evals;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) zn[i] = fma(h, f[i], zs[i]);
+        if (NEWTON) newton_update(J, 0.5 * h, zk, zn);
+        double di[6];
+        bool ok = true;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            di[i] = fabs(zn[i] - zk[i]);
+            ok = ok && (di[i] <= k.tol * (fabs(zn[i]) + 1.0));
+        }
+        if (NEWTON && !ok && it >= 1) {
+            ok = true;
+#pragma unroll
+            for (int i = 0; i < 6; ++i)
+                ok = ok && (di[i] < dprev[i]) && (di[i] * di[i] <= k.tol * (fabs(zn[i]) + 1.0) * (dprev[i] - di[i]));
+        }
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            dprev[i] = di[i];
+            zk[i] = zn[i];
+        }
+        if (ok) {
+            its += it + 1;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) out[i] = zk[i];
+            return true;
+        }
+    }
+    its += max_iter;
+    return false;
+}
+
 // Launch k_imr in the iteration form the push asked for (k.imr_newton).
 template <int RESTART, bool BATCHED = false>
 static void launch_imr(unsigned grid, unsigned block, cudaStream_t s, const PushK& k, int all_mode)
@@ -781,9 +855,32 @@ static void launch_imr(unsigned grid, unsigned block, cudaStream_t s, const Push
     else k_imr<RESTART, BATCHED, false><<<grid, block, 0, s>>>(k, all_mode);
 }
 
-// After k_imr: H at each converged implicit step (sin/cos of th^{n+1} by
+// The end of an implicit step of particle p (queue slot idx) at z: the
+// particle boundaries and write-back (finish), the particle's time and, with
+// the slope cache, F at the stored state.  f, H: the right-hand side (keep)
+// and H at z.  Returns whether the particle stays in the domain.
+__device__ __forceinline__ bool implicit_end(const PushK& k, const RunK& R, long long p, double z[6], double sn,
+                                             double cn, double qm, bool em, double H, double f[6], bool keep, int its)
+{
+    const double th_new = z[1];
+    const bool alive = finish(R, k.P, p, z, H, 1, its);
+    if (k.t) k.t[p] += k.dt_imp;
+    if (keep && alive) {
+        if (z[1] != th_new) {
+            double Hd;
+            sn = -sn;
+            F_at_sc(R, z, sn, cn, qm, em, f, Hd);
+        }
+        slope_store(k, p, z, qm, f, sn, cn);
+    }
+    return alive;
+}
+
+// After k_imr: H at each implicit step's end point (sin/cos of th^{n+1} by
 // angle addition from th^n) and the write-back with the particle
-// boundaries of Sec. 2.5.
+// boundaries of Sec. 2.5.  With substeps (k.substeps > 0) a step whose solve
+// did not converge, or whose |H - H^n| / D_0 exceeds substep_tol, is listed
+// for k_imr_substep instead (the top bit of the entry marks the former).
 template <bool BATCHED = false>
 __global__ void __launch_bounds__(256) k_imr_finish(const __grid_constant__ PushK k, int all_mode)
 {
@@ -807,20 +904,109 @@ __global__ void __launch_bounds__(256) k_imr_finish(const __grid_constant__ Push
         const bool em = (R.has_fields || R.B0field != 0.0) && qm != 0.0;
         if (keep) F_at_sc(R, z, sn, cn, qm, em, f, H);
         else H = eval_H_sc(R.bh, z, sn, cn, qm, R.B0pot);
-        const double th_new = z[1];
-        const bool alive = finish(R, k.P, p, z, H, 1, (k.its && !all_mode) ? k.its[idx] : k.P.iters[p]);
-        if (!alive) ++n_rm;
-        if (k.t) k.t[p] += k.dt_imp;
-        if (keep && alive) {
-            if (z[1] != th_new) {
-                double Hd;
-                sn = -sn;
-                F_at_sc(R, z, sn, cn, qm, em, f, Hd);
+        if (k.substeps > 0 && !k.record) {
+            const bool flagged = k.strag_flag[idx] != 0;
+            if (flagged || (k.substep_tol > 0.0 && fabs(H - k.P.Hn[p]) / k.P.D0[p] > k.substep_tol)) {
+                if (flagged) k.strag_flag[idx] = 0;
+                const unsigned long long e = atomicAdd((unsigned long long*)&k.cnt[CNT_STRAG], 1ull);
+                k.strag[e] = (uint32_t)idx | (flagged ? 0x80000000u : 0u);
+                continue;
             }
-            slope_store(k, p, z, qm, f, sn, cn);
         }
+        const int its = (k.its && !all_mode) ? k.its[idx] : k.P.iters[p];
+        if (!implicit_end(k, R, p, z, sn, cn, qm, em, H, f, keep, its)) ++n_rm;
     }
     warp_add(&k.cnt[CNT_REMOVED], n_rm, 0xffffffffu);
+}
+
+// Iteration cap of each substep's solve: a level whose substeps need more
+// is too coarse, and the next level is tried.
+constexpr int SUBSTEP_MAX_ITER = 16;
+
+// Implicit steps listed by k_imr_finish (a solve that did not converge, or
+// an end point off by more than substep_tol in H): the step redone from z^n
+// as m = 2, 4, ..., 2^K substeps of dt_imp / m, each a solve (capped at
+// SUBSTEP_MAX_ITER iterations) from its own start state with the pole
+// reflection after it.  The first level whose
+// solves all converge and whose end point has |H - H(z^n)| / D_0 <=
+// substep_tol (0: no H condition) is taken, else the finest level whose
+// solves all converged, else the full step's own result; then the step
+// ends as in k_imr_finish.  One thread per listed step: they are rare.
+template <bool BATCHED, bool NEWTON>
+__global__ void __launch_bounds__(128) k_imr_substep(const __grid_constant__ PushK k, int all_mode)
+{
+    const long long ns = k.cnt[CNT_STRAG];
+    long long n_it = 0, n_ev = 0, n_fix = 0, n_rm = 0;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ns;
+         e += (long long)gridDim.x * blockDim.x) {
+        const uint32_t ent = k.strag[e];
+        const bool unconv = (ent & 0x80000000u) != 0;
+        const long long qi = ent & 0x7fffffffu;
+        const long long p = all_mode ? qi : (long long)k.queue[qi];
+        const RunK& R = BATCHED ? k.runs[run_of(k.runs, k.nruns, p)] : k.run;
+        const bool st = !all_mode && k.z0s;
+        double z0[6];
+        if (st) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) z0[i] = k.z0s[(size_t)i * k.n + qi];
+        } else {
+            load_state(k.P, p, z0);
+        }
+        const double qm = st ? k.z0s[(size_t)6 * k.n + qi] : k.P.qm[p];
+        const bool em = (R.has_fields || R.B0field != 0.0) && qm != 0.0;
+        const double Href = eval_H(R.bh, z0, qm, R.B0pot), D0 = k.P.D0[p];
+        double z[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) z[i] = k.guess[(size_t)i * k.n + p];     // the full step's result
+        bool have = false;
+        long long its = 0;
+        const int sub_iter = min(k.max_iter, SUBSTEP_MAX_ITER);
+        for (int lev = 1; lev <= k.substeps; ++lev) {
+            const int m = 1 << lev;
+            const double h = k.dt_imp / m;
+            double zs[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) zs[i] = z0[i];
+            bool ok = true;
+            for (int sub = 0; sub < m && ok; ++sub) {
+                double zn[6];
+                ok = imr_solve_serial<NEWTON>(k, R, zs, h, qm, em, sub_iter, zn, its, n_ev);
+                reflect_pole(zn);
+#pragma unroll
+                for (int i = 0; i < 6; ++i) zs[i] = zn[i];
+            }
+            if (!ok) continue;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) z[i] = zs[i];
+            have = true;
+            if (k.substep_tol <= 0.0 || fabs(eval_H(R.bh, zs, qm, R.B0pot) - Href) / D0 <= k.substep_tol) break;
+        }
+        n_it += its;
+        if (have && unconv) ++n_fix;
+        const int its0 = (k.its && !all_mode) ? k.its[qi] : k.P.iters[p];
+        const int its_out = (int)min((long long)its0 + its, 255LL);
+        double sn, cn, H, f[6];
+        sincos(z[1], &sn, &cn);
+        const bool keep = !BATCHED && k.slope && !all_mode;
+        if (keep) F_at_sc(R, z, sn, cn, qm, em, f, H);
+        else H = eval_H_sc(R.bh, z, sn, cn, qm, R.B0pot);
+        if (!implicit_end(k, R, p, z, sn, cn, qm, em, H, f, keep, its_out)) ++n_rm;
+    }
+    warp_add(&k.cnt[CNT_ITERS], n_it, 0xffffffffu);
+    warp_add(&k.cnt[CNT_EVALS], n_ev, 0xffffffffu);
+    warp_add(&k.cnt[CNT_NOTCONV], -n_fix, 0xffffffffu);
+    warp_add(&k.cnt[CNT_REMOVED], n_rm, 0xffffffffu);
+}
+
+// k_imr_finish and, with substeps, the substep kernel over what it listed.
+template <bool BATCHED = false>
+static void finish_implicit(unsigned grid, cudaStream_t s, const PushK& k, int all_mode)
+{
+    k_imr_finish<BATCHED><<<grid, 256, 0, s>>>(k, all_mode);
+    if (k.substeps > 0 && !k.record) {
+        if (k.imr_newton) k_imr_substep<BATCHED, true><<<grid, 128, 0, s>>>(k, all_mode);
+        else k_imr_substep<BATCHED, false><<<grid, 128, 0, s>>>(k, all_mode);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1391,28 +1577,39 @@ static bool dt_implicit_ok(const fpic_push_params* prm)
 static int push_core(fpic_ctx* c, fpic_particles* p, const double* const fields[6], const fpic_push_params* prm,
                      fpic_push_stats* stats, cudaStream_t s, const PushChunks* ch, bool host_state = false);
 
+// Argument checks shared by fpic_push and fpic_push_host (who: the caller's
+// name in the message).
+static int check_push_args(const fpic_ctx* c, const fpic_particles* p, const double* const fields[6],
+                           const fpic_push_params* prm, const char* who)
+{
+    if (!c || !p || !prm) return set_error(FPIC_EINVAL, "%s: NULL ctx/particles/params", who);
+    if (p->n < 0 || p->n >= (1LL << 31)) return set_error(FPIC_EINVAL, "%s: n out of range [0, 2^31)", who);
+    if (!particles_ok(p, true)) return set_error(FPIC_EINVAL, "%s: a particle array is NULL", who);
+    if (!(std::isfinite(prm->dt)) || prm->dt == 0.0) return set_error(FPIC_EINVAL, "%s: dt must be finite and nonzero", who);
+    if (!dt_implicit_ok(prm)) return set_error(FPIC_EINVAL, "%s: dt_implicit must be 0 or finite with the sign of dt", who);
+    if (prm->B0field != 0.0 && (fields || !std::isfinite(prm->B0field) || c->M != 1.0))
+        return set_error(FPIC_EINVAL, "%s: B0field needs fields == NULL, a finite value and M = 1", who);
+    if (prm->scheme < FPIC_RK4 || prm->scheme > FPIC_HYB2) return set_error(FPIC_EINVAL, "%s: unknown scheme %d", who, prm->scheme);
+    if (prm->scheme >= FPIC_HYB1 && prm->implicit != FPIC_IMR && prm->implicit != FPIC_HAM)
+        return set_error(FPIC_EINVAL, "%s: implicit partner must be FPIC_IMR or FPIC_HAM", who);
+    if (prm->max_iter < 1 || prm->max_iter > 255) return set_error(FPIC_EINVAL, "%s: max_iter must be in [1, 255]", who);
+    if (!(prm->tol >= 0.0)) return set_error(FPIC_EINVAL, "%s: tol must be >= 0", who);
+    if (prm->imr_substeps < 0 || prm->imr_substeps > 12 || !(prm->substep_tol >= 0.0) || !std::isfinite(prm->substep_tol))
+        return set_error(FPIC_EINVAL, "%s: imr_substeps must be in [0, 12] and substep_tol finite and >= 0", who);
+    if (fields) {
+        for (int i = 0; i < 6; ++i)
+            if (!fields[i]) return set_error(FPIC_EINVAL, "%s: fields[%d] is NULL", who, i);
+        if (!c->has_grid) return set_error(FPIC_EINVAL, "%s: fields given but no grid set", who);
+    }
+    if (prm->guess) return set_error(FPIC_EINVAL, "%s: learned guesses need fpic_push_learned", who);
+    return 0;
+}
+
 extern "C" int fpic_push(fpic_ctx* c, fpic_particles* p, const double* const fields[6],
                          const fpic_push_params* prm, fpic_push_stats* stats, void* stream)
 {
-    if (!c || !p || !prm) return set_error(FPIC_EINVAL, "fpic_push: NULL ctx/particles/params");
-    if (p->n < 0 || p->n >= (1LL << 31)) return set_error(FPIC_EINVAL, "fpic_push: n out of range [0, 2^31)");
-    if (!particles_ok(p, true)) return set_error(FPIC_EINVAL, "fpic_push: a particle array is NULL");
-    if (!(std::isfinite(prm->dt)) || prm->dt == 0.0) return set_error(FPIC_EINVAL, "fpic_push: dt must be finite and nonzero");
-    if (!dt_implicit_ok(prm)) return set_error(FPIC_EINVAL, "fpic_push: dt_implicit must be 0 or finite with the sign of dt");
-    if (prm->B0field != 0.0 && (fields || !std::isfinite(prm->B0field) || c->M != 1.0))
-        return set_error(FPIC_EINVAL, "fpic_push: B0field needs fields == NULL, a finite value and M = 1");
-    if (prm->scheme < FPIC_RK4 || prm->scheme > FPIC_HYB2) return set_error(FPIC_EINVAL, "fpic_push: unknown scheme %d", prm->scheme);
-    if (prm->scheme >= FPIC_HYB1 && prm->implicit != FPIC_IMR && prm->implicit != FPIC_HAM)
-        return set_error(FPIC_EINVAL, "fpic_push: implicit partner must be FPIC_IMR or FPIC_HAM");
-    if (prm->max_iter < 1 || prm->max_iter > 255) return set_error(FPIC_EINVAL, "fpic_push: max_iter must be in [1, 255]");
-    if (!(prm->tol >= 0.0)) return set_error(FPIC_EINVAL, "fpic_push: tol must be >= 0");
-    bool has_fields = fields != nullptr;
-    if (has_fields) {
-        for (int i = 0; i < 6; ++i)
-            if (!fields[i]) return set_error(FPIC_EINVAL, "fpic_push: fields[%d] is NULL", i);
-        if (!c->has_grid) return set_error(FPIC_EINVAL, "fpic_push: fields given but no grid set");
-    }
-    if (prm->guess) return set_error(FPIC_EINVAL, "fpic_push: learned guesses need fpic_push_learned");
+    const int rc = check_push_args(c, p, fields, prm, "fpic_push");
+    if (rc) return rc;
     return push_core(c, p, fields, prm, stats, (cudaStream_t)stream, nullptr);
 }
 
@@ -1422,8 +1619,12 @@ static int push_core(fpic_ctx* c, fpic_particles* p, const double* const fields[
     const bool has_fields = fields != nullptr;
     const long long n = p->n;
     FPIC_CUDA(cudaSetDevice(c->device));
-    const size_t base_need = (size_t)n * (8 * sizeof(double) + 2 * sizeof(uint32_t));
-    const size_t need = base_need + (host_state ? (size_t)n * (7 * sizeof(double) + 1) : 0) + 256;
+    // guess 6n, sin/cos 2n (doubles) | queue, order, straggler list (u32) |
+    // host state: z^n and q/m by slot 7n (doubles, 16-byte aligned), iteration
+    // counts n (bytes) | straggler flags n (bytes, 16-byte aligned)
+    const size_t base_need = ((size_t)n * (8 * sizeof(double) + 3 * sizeof(uint32_t)) + 15) & ~(size_t)15;
+    const size_t flag_off = (base_need + (host_state ? (size_t)n * (7 * sizeof(double) + 1) : 0) + 15) & ~(size_t)15;
+    const size_t need = flag_off + (size_t)n + 256;
     int rc = ensure_scratch(c, need);
     if (rc) return rc;
     PushK k{};
@@ -1464,6 +1665,10 @@ static int push_core(fpic_ctx* c, fpic_particles* p, const double* const fields[
     k.sc0 = k.guess + (size_t)n * 6;
     k.queue = (uint32_t*)((char*)c->d_scratch + (size_t)n * 8 * sizeof(double));
     k.order = k.queue + n;
+    k.strag = k.order + n;
+    k.strag_flag = (uint8_t*)c->d_scratch + flag_off;
+    k.substeps = prm->imr_substeps;
+    k.substep_tol = prm->substep_tol;
     if (host_state) {
         k.z0s = (double*)((char*)c->d_scratch + base_need);
         k.its = (uint8_t*)(k.z0s + (size_t)n * 7);
@@ -1475,6 +1680,7 @@ static int push_core(fpic_ctx* c, fpic_particles* p, const double* const fields[
         if (stats) *stats = fpic_push_stats{};
         return FPIC_OK;
     }
+    if (k.substeps > 0) FPIC_CUDA(cudaMemsetAsync(k.strag_flag, 0, (size_t)n, s));
     const int TB = 128;
     const unsigned nb = (unsigned)((n + TB - 1) / TB);
     const unsigned persist = (unsigned)c->sm_count * 8u;
@@ -1523,14 +1729,14 @@ static int push_core(fpic_ctx* c, fpic_particles* p, const double* const fields[
     }
     if (prm->scheme == FPIC_IMR) {
         launch_imr<0>(imr_grid, TB, s, k, 1);
-        k_imr_finish<><<<persist, 256, 0, s>>>(k, 1);
+        finish_implicit<>(persist, s, k, 1);
     } else if (prm->scheme == FPIC_HAM) {
         if (k.run.B0field != 0.0) k_dg_em<<<nbx, TBx, 0, s>>>(k, 1);
         else k_dg<<<nbx, TBx, 0, s>>>(k, 1);
     } else if (prm->scheme >= FPIC_HYB1 && prm->implicit == FPIC_IMR) {
         k_order<<<persist, 256, 0, s>>>(k);
         launch_imr<0>(imr_grid, TB, s, k, 0);
-        k_imr_finish<><<<persist, 256, 0, s>>>(k, 0);
+        finish_implicit<>(persist, s, k, 0);
     } else if (prm->scheme >= FPIC_HYB1) {
         if (k.run.B0field != 0.0) k_dg_em<<<nbx, TBx, 0, s>>>(k, 0);
         else k_dg<<<nbx, TBx, 0, s>>>(k, 0);
@@ -1564,9 +1770,8 @@ static int push_core(fpic_ctx* c, fpic_particles* p, const double* const fields[
 extern "C" int fpic_push_host(fpic_ctx* c, fpic_particles* hp, const double* const fields[6],
                               const fpic_push_params* prm, fpic_push_stats* stats, void* stream)
 {
-    if (!c || !hp || !prm) return set_error(FPIC_EINVAL, "fpic_push_host: NULL ctx/particles/params");
-    if (hp->n < 0 || hp->n >= (1LL << 31)) return set_error(FPIC_EINVAL, "fpic_push_host: n out of range");
-    if (!particles_ok(hp, true)) return set_error(FPIC_EINVAL, "fpic_push_host: a particle array is NULL");
+    const int rc_args = check_push_args(c, hp, fields, prm, "fpic_push_host");
+    if (rc_args) return rc_args;
     const long long n = hp->n;
     cudaStream_t s = (cudaStream_t)stream;
     FPIC_CUDA(cudaSetDevice(c->device));
@@ -1765,6 +1970,7 @@ extern "C" int fpic_push_noalloc(double M, double a, fpic_particles* p, const fp
     if (prm->max_iter < 1 || prm->max_iter > 255) return set_error(FPIC_EINVAL, "fpic_push_noalloc: max_iter must be in [1, 255]");
     if (!(prm->tol >= 0.0)) return set_error(FPIC_EINVAL, "fpic_push_noalloc: tol must be >= 0");
     if (prm->guess) return set_error(FPIC_EINVAL, "fpic_push_noalloc: learned guesses are not supported here");
+    if (prm->imr_substeps != 0) return set_error(FPIC_EINVAL, "fpic_push_noalloc: imr_substeps is not supported here");
     int dev = 0, sms = 0;
     void* scratch = nullptr;
     FPIC_CUDA(cudaGetDevice(&dev));
@@ -1819,14 +2025,14 @@ extern "C" int fpic_push_noalloc(double M, double a, fpic_particles* p, const fp
     }
     if (prm->scheme == FPIC_IMR) {
         launch_imr<0>(persist / 2, TB, s, k, 1);
-        k_imr_finish<><<<persist, 256, 0, s>>>(k, 1);
+        finish_implicit<>(persist, s, k, 1);
     } else if (prm->scheme == FPIC_HAM) {
         if (k.run.B0field != 0.0) k_dg_em<<<nb, TB, 0, s>>>(k, 1);
         else k_dg<<<nb, TB, 0, s>>>(k, 1);
     } else if (prm->scheme >= FPIC_HYB1 && prm->implicit == FPIC_IMR) {
         k_order<<<persist, 256, 0, s>>>(k);
         launch_imr<0>(persist / 2, TB, s, k, 0);
-        k_imr_finish<><<<persist, 256, 0, s>>>(k, 0);
+        finish_implicit<>(persist, s, k, 0);
     } else if (prm->scheme >= FPIC_HYB1) {
         if (k.run.B0field != 0.0) k_dg_em<<<nb, TB, 0, s>>>(k, 0);
         else k_dg<<<nb, TB, 0, s>>>(k, 0);
@@ -1972,7 +2178,9 @@ __global__ void k_split(PushK k, float skip_logit)
 static bool push_prm_ok(const fpic_push_params* prm)
 {
     return std::isfinite(prm->dt) && prm->dt != 0.0 && prm->scheme >= FPIC_HYB1 && prm->scheme <= FPIC_HYB2 &&
-           prm->implicit == FPIC_IMR && prm->max_iter >= 1 && prm->max_iter <= 255 && prm->tol >= 0.0;
+           prm->implicit == FPIC_IMR && prm->max_iter >= 1 && prm->max_iter <= 255 && prm->tol >= 0.0 &&
+           prm->imr_substeps >= 0 && prm->imr_substeps <= 12 && prm->substep_tol >= 0.0 &&
+           std::isfinite(prm->substep_tol);
 }
 
 static void fill_pushk(PushK& k, fpic_ctx* c, fpic_particles* p, const double* const fields[6],
@@ -1996,18 +2204,20 @@ static void fill_pushk(PushK& k, fpic_ctx* c, fpic_particles* p, const double* c
     k.run.r_max = prm->r_max;
     k.scheme = prm->scheme;
     k.max_iter = prm->max_iter;
+    k.substeps = prm->imr_substeps;
+    k.substep_tol = prm->substep_tol;
     k.n = p->n;
     k.P = PartDev{p->r, p->th, p->ph, p->ur, p->uth, p->uph, p->qm, p->H0, p->D0, p->Hn,
                   p->alive, p->scheme, p->iters, p->cell};
     k.cnt = c->d_cnt;
 }
 
-// scratch: guess 6n doubles | sc0 2n doubles | stg STG_ROWS n doubles | queue n | work n | order n | X 16n floats |
+// scratch: guess 6n doubles | sc0 2n doubles | stg STG_ROWS n doubles | queue n | work n | order n | strag n | X 16n floats |
 // Y 16n floats | featS 16n floats | 6 FP32 field copies
 static int learned_scratch(fpic_ctx* c, long long n, PushK& k, float** X, float** Y, float** f32)
 {
     const size_t fsz = c->has_grid ? 6 * (size_t)(c->Nr + 1) * c->ld : 0;
-    const size_t need = (size_t)n * ((8 + STG_ROWS) * sizeof(double) + 3 * sizeof(uint32_t) + 48 * sizeof(float)) +
+    const size_t need = (size_t)n * ((8 + STG_ROWS) * sizeof(double) + 4 * sizeof(uint32_t) + 48 * sizeof(float) + 1) +
                         fsz * sizeof(float) + 2048;
     int rc = ensure_scratch(c, need);
     if (rc) return rc;
@@ -2024,6 +2234,8 @@ static int learned_scratch(fpic_ctx* c, long long n, PushK& k, float** X, float*
     b += (size_t)n * sizeof(uint32_t);
     k.order = (uint32_t*)b;
     b += (size_t)n * sizeof(uint32_t);
+    k.strag = (uint32_t*)b;
+    b += (size_t)n * sizeof(uint32_t);
     b = (char*)(((uintptr_t)b + 255) & ~(uintptr_t)255);
     *X = (float*)b;
     b += (size_t)n * 16 * sizeof(float);
@@ -2032,6 +2244,8 @@ static int learned_scratch(fpic_ctx* c, long long n, PushK& k, float** X, float*
     k.featS = (float*)b;
     b += (size_t)n * 16 * sizeof(float);
     *f32 = (float*)b;
+    b += fsz * sizeof(float);
+    k.strag_flag = (uint8_t*)b;
     return 0;
 }
 
@@ -2326,6 +2540,7 @@ extern "C" int fpic_push_learned(fpic_ctx* c, fpic_mlp* m, fpic_particles* p, co
         if (stats) *stats = fpic_push_stats{};
         return FPIC_OK;
     }
+    if (k.substeps > 0) FPIC_CUDA(cudaMemsetAsync(k.strag_flag, 0, (size_t)n, s));
     const unsigned nb = (unsigned)((n + 127) / 128);
     const unsigned persist = (unsigned)c->sm_count * 8u;
     cudaEvent_t* ev = prm->events ? (cudaEvent_t*)prm->events : nullptr;
@@ -2369,7 +2584,7 @@ extern "C" int fpic_push_learned(fpic_ctx* c, fpic_mlp* m, fpic_particles* p, co
     k_order<<<persist, 256, 0, s>>>(k);
     if (correct) launch_imr<1>(imr_grid, 128, s, k, 0);
     else launch_imr<0>(imr_grid, 128, s, k, 0);
-    k_imr_finish<><<<persist, 256, 0, s>>>(k, 0);
+    finish_implicit<>(persist, s, k, 0);
     if (ev) FPIC_CUDA(cudaEventRecord(ev[3], s));
     FPIC_CUDA(cudaGetLastError());
     if (stats) {
@@ -2420,6 +2635,8 @@ static int push_batched(const fpic_run* runs, int nruns, fpic_mlp* m, fpic_parti
         return set_error(FPIC_EINVAL, "fpic_push_batched: the implicit partner must be FPIC_IMR");
     if (prm->max_iter < 1 || prm->max_iter > 255 || !(prm->tol >= 0.0))
         return set_error(FPIC_EINVAL, "fpic_push_batched: bad max_iter or tol");
+    if (prm->imr_substeps < 0 || prm->imr_substeps > 12 || !(prm->substep_tol >= 0.0) || !std::isfinite(prm->substep_tol))
+        return set_error(FPIC_EINVAL, "fpic_push_batched: imr_substeps must be in [0, 12] and substep_tol finite and >= 0");
     fpic_ctx* c = runs[0].ctx;
     if (!c) return set_error(FPIC_EINVAL, "fpic_push_batched: runs[0].ctx is NULL");
     for (int i = 0; i < nruns; ++i) {
@@ -2448,7 +2665,7 @@ static int push_batched(const fpic_run* runs, int nruns, fpic_mlp* m, fpic_parti
     PushK k{};
     float *X = nullptr, *Y = nullptr, *f32 = nullptr;
     int rc = m ? learned_scratch(c, nn, k, &X, &Y, &f32)
-               : ensure_scratch(c, (size_t)nn * (8 * sizeof(double) + 2 * sizeof(uint32_t)) + 256);
+               : ensure_scratch(c, (size_t)nn * (8 * sizeof(double) + 3 * sizeof(uint32_t) + 1) + 256);
     if (rc) return rc;
     std::vector<RunK> tab(nruns);
     for (int i = 0; i < nruns; ++i) {
@@ -2509,13 +2726,18 @@ static int push_batched(const fpic_run* runs, int nruns, fpic_mlp* m, fpic_parti
         k.sc0 = k.guess + (size_t)nn * 6;
         k.queue = (uint32_t*)((char*)c->d_scratch + (size_t)nn * 8 * sizeof(double));
         k.order = k.queue + nn;
+        k.strag = k.order + nn;
+        k.strag_flag = (uint8_t*)(k.strag + nn);
     }
+    k.substeps = prm->imr_substeps;
+    k.substep_tol = prm->substep_tol;
     k.cnt = c->d_cnt;
     FPIC_CUDA(cudaMemsetAsync(c->d_cnt, 0, CNT_N * sizeof(long long), s));
     if (n == 0) {
         if (stats) *stats = fpic_push_stats{};
         return FPIC_OK;
     }
+    if (k.substeps > 0) FPIC_CUDA(cudaMemsetAsync(k.strag_flag, 0, (size_t)n, s));
     const unsigned nb = (unsigned)((n + 127) / 128);
     const unsigned persist = (unsigned)c->sm_count * 8u;
     const unsigned imr_grid = (unsigned)c->sm_count * (unsigned)c->imr_blocks_per_sm;
@@ -2532,7 +2754,7 @@ static int push_batched(const fpic_run* runs, int nruns, fpic_mlp* m, fpic_parti
         if (ev) FPIC_CUDA(cudaEventRecord(ev[2], s));
         k_order<<<persist, 256, 0, s>>>(k);
         launch_imr<1, true>(imr_grid, 128, s, k, 0);
-        k_imr_finish<true><<<persist, 256, 0, s>>>(k, 0);
+        finish_implicit<true>(persist, s, k, 0);
     } else {
         if (prm->scheme == FPIC_RK4) k_explicit<0, true><<<nb, 128, 0, s>>>(k);
         else if (prm->scheme >= FPIC_HYB1) k_explicit<1, true><<<nb, 128, 0, s>>>(k);
@@ -2542,11 +2764,11 @@ static int push_batched(const fpic_run* runs, int nruns, fpic_mlp* m, fpic_parti
         }
         if (prm->scheme == FPIC_IMR) {
             launch_imr<0, true>(imr_grid, 128, s, k, 1);
-            k_imr_finish<true><<<persist, 256, 0, s>>>(k, 1);
+            finish_implicit<true>(persist, s, k, 1);
         } else if (prm->scheme >= FPIC_HYB1) {
             k_order<<<persist, 256, 0, s>>>(k);
             launch_imr<0, true>(imr_grid, 128, s, k, 0);
-            k_imr_finish<true><<<persist, 256, 0, s>>>(k, 0);
+            finish_implicit<true>(persist, s, k, 0);
         }
     }
     if (ev) FPIC_CUDA(cudaEventRecord(ev[3], s));

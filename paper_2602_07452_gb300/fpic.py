@@ -48,7 +48,7 @@ class fpic_push_params(C.Structure):
                 ("tol", C.c_double), ("max_iter", C.c_int), ("r_max", C.c_double),
                 ("dg_eps", C.c_double), ("B0pot", C.c_double), ("guess", C.c_void_p),
                 ("events", C.c_void_p), ("dt_implicit", C.c_double), ("t", C.c_void_p), ("B0field", C.c_double),
-                ("imr_newton", C.c_int)]
+                ("imr_newton", C.c_int), ("imr_substeps", C.c_int), ("substep_tol", C.c_double)]
 
 
 class fpic_push_stats(C.Structure):
@@ -307,15 +307,18 @@ def fpic_init_particles(ctx: Ctx, p: Particles, kind: int, draws: torch.Tensor, 
 
 def push_params(dt, scheme=FPIC_RK4, implicit=FPIC_IMR, thr=1e-12, tol=1e-14, max_iter=50,
                 r_max=1e300, dg_eps=1e-10, B0pot=0.0, guess=None, events=None, dt_implicit=0.0, t=None,
-                B0field=0.0, imr_newton=False):
+                B0field=0.0, imr_newton=False, imr_substeps=0, substep_tol=0.0):
     """events: optional list of 4 torch.cuda.Event(enable_timing=True);
     dt_implicit: step of the hybrid's implicit partner (0 = dt); t: optional
     per-particle time tensor (float64, device) advanced by each step;
     B0field: analytic Wald field (fields must be None); imr_newton: solve
-    the IMR by the Newton iteration instead of the fixed-point update."""
+    the IMR by the Newton iteration instead of the fixed-point update;
+    imr_substeps, substep_tol: unconverged IMR solves redone in up to
+    2^imr_substeps substeps (see fpic.h)."""
     prm = fpic_push_params(dt, scheme, implicit, thr, tol, max_iter, r_max, dg_eps, B0pot,
                            None if guess is None else guess.data_ptr(), None, dt_implicit,
-                           None if t is None else t.data_ptr(), B0field, int(bool(imr_newton)))
+                           None if t is None else t.data_ptr(), B0field, int(bool(imr_newton)),
+                           int(imr_substeps), float(substep_tol))
     if events is not None:
         arr = (C.c_void_p * 4)(*[C.c_void_p(e.cuda_event) for e in events])
         prm._events_keepalive = arr

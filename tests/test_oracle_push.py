@@ -815,3 +815,89 @@ def test_imr_successive_update_stop_is_within_tolerance(newton):
         assert its.mean() < 5.0 and its.max() <= 6, (its.mean(), its.max())
     else:
         assert its.mean() > 8.0
+
+
+def _axis_particles(n=600, a=0.9, seed=41):
+    """Charged particles within 3e-4 rad of a pole moving towards it
+    (|u_th| 0.3..3, small u_ph): steps of dt = 1e-3 under-resolve their
+    turn at the axis, the IMR solve of many of them does not converge."""
+    rng = np.random.default_rng(seed)
+    th = np.exp(rng.uniform(np.log(1e-5), np.log(3e-4), n))
+    north = rng.random(n) < 0.5
+    th = np.where(north, th, np.pi - th)
+    uth = rng.uniform(0.3, 3.0, n) * np.where(north, -1.0, 1.0)
+    z = np.stack([rng.uniform(1.5, 5.0, n), th, rng.uniform(0, 6, n), rng.normal(size=n) * 0.5, uth,
+                  rng.normal(size=n) * 2e-4], 1)
+    q = np.where(np.arange(n) % 2 == 0, -100.0, 100.0)
+    return np.ascontiguousarray(z), q
+
+
+@pytest.mark.parametrize("newton", [False, True])
+def test_unconverged_imr_step_is_redone_in_substeps(newton):
+    """Reading for unconverged IMR solves near the axis: the step is redone
+    as 2, 4, ..., 2^K substeps.  Pins, in the analytic Wald field (where the
+    exact flow conserves H): (i) with no H condition the result is bitwise
+    the composition of m plain IMR steps of dt/m (each a separate oracle
+    push with max_iter 16, pole reflection included), m the first level at
+    which every substep solve converges; (ii) solves that converge on their own are
+    untouched; (iii) the substepped steps keep H far better than the
+    smallest-update fallback; (iv) with an H condition of 1e-6 the steps
+    redone are the unconverged ones and the converged ones whose end point
+    misses it, each taking the first level that meets it (else the finest
+    converged one), bitwise as the composition predicts."""
+    a, B0, dt, K = 0.9, 1.0, 1e-3, 8
+    z, q = _axis_particles(a=a)
+    H0, _, D0 = O.hamiltonian(1.0, a, B0, z, q)
+    kw = dict(a=a, scheme=O.IMR, B0pot=B0, field_kind=O.FIELD_WALD, B0field=B0, imr_newton=newton)
+
+    def push(dt_, zz, max_iter=50, **extra):
+        p = O.push_params(dt=dt_, max_iter=max_iter, **kw, **extra)
+        zz = np.ascontiguousarray(zz.copy()); Hn = H0.copy(); al = np.ones(len(zz), np.uint8)
+        nc, s, its, ncf = O.push(p, zz, q, H0, D0, Hn, al, flags=True)
+        return zz, its, nc, ncf
+
+    z_off, its_off, nc_off, fl_off = push(dt, z)
+    fail = fl_off == 1
+    assert 50 < fail.sum() < len(q) - 50, fail.sum()
+    z_on, its_on, nc_on, _ = push(dt, z, imr_substeps=K)
+    assert np.array_equal(z_on[~fail], z_off[~fail]) and np.array_equal(its_on[~fail], its_off[~fail])
+    # (i) the composition of m plain pushes of dt/m, level by level
+    dH = lambda zz: np.abs(O.hamiltonian(1.0, a, B0, zz, q)[0] - H0) / D0
+    levels = []
+    for k in range(1, K + 1):
+        m = 2 ** k
+        zz, ok = z.copy(), np.ones(len(q), bool)
+        for _ in range(m):
+            zz, it, _, f = push(dt / m, zz, max_iter=16)     # a substep's solve is capped at 16
+            ok &= f == 0
+        levels.append((zz, ok))
+
+    def expected(tol):
+        # the steps redone: unconverged ones, and with an H condition those
+        # whose end point is off by more than it (H^n = H0 here)
+        trig = fail | ((dH(z_off) > tol) if tol > 0 else False)
+        out, left = z_off.copy(), trig.copy()
+        finest = z_off.copy()
+        for zz, ok in levels:
+            finest[trig & ok] = zz[trig & ok]
+            take = left & ok & ((dH(zz) <= tol) if tol > 0 else True)
+            out[take] = zz[take]
+            left &= ~take
+        conv = trig & np.any([ok for _, ok in levels], axis=0)
+        out[left & conv] = finest[left & conv]
+        return out, fail & ~conv
+
+    exp0, never = expected(0.0)
+    assert np.array_equal(z_on, exp0)
+    assert nc_on == never.sum() < 0.1 * fail.sum()
+    # (iii) H of the rescued steps against the fallback's; the H condition
+    # takes the first level that meets it, else the finest converged one
+    resc = fail & ~never
+    assert np.median(dH(z_on)[resc]) < 0.1 * np.median(dH(z_off)[resc])
+    z_t, _, _, _ = push(dt, z, imr_substeps=K, substep_tol=1e-6)
+    exp_t, _ = expected(1e-6)
+    assert np.array_equal(z_t, exp_t)
+    assert np.median(dH(z_t)[resc]) <= np.median(dH(z_on)[resc])
+    # the H condition also redoes converged steps that miss it: the largest
+    # step error over all particles falls
+    assert dH(z_t).max() < dH(z_on).max()
