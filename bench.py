@@ -298,8 +298,10 @@ def _timed(F, ctx, p, fields, prm, ev, steps, flush, learned=None):
         out["reused"] += st["n_slope_reused"]
         # the library's launches per step (static fields: no coefficient rebuild):
         # plain k_explicit (+ alive count), k_order, k_imr, k_imr_finish;
-        # corrector + k_count_alive, k_mlp_correct4; skip form 9
-        out["launches"] += 4 if learned is None else (9 if learned[1].mode == F.FPIC_LEARN_SKIP else 6)
+        # corrector + k_count_alive, k_mlp_correct4; skip form 9; with
+        # substeps one more (k_imr_substep)
+        sub = 1 if prm.imr_substeps > 0 else 0     # k_imr_substep after k_imr_finish
+        out["launches"] += (4 if learned is None else (9 if learned[1].mode == F.FPIC_LEARN_SKIP else 6)) + sub
     return out
 
 
@@ -575,7 +577,8 @@ def run_skip_analysis(device, n=1 << 20, gen_steps=10, eval_steps=10, time_steps
     for e in ev:
         e.record()
     prm = F.push_params(DT, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=HYB1_THR, r_max=float(g.rn[-1]),
-                        B0pot=B0, events=ev[1:5], imr_newton=True)
+                        B0pot=B0, events=ev[1:5], imr_newton=True, imr_substeps=IMR_SUBSTEPS,
+                        substep_tol=SUBSTEP_TOL)
     for _ in range(3):
         F.fpic_push(ctx, p, fields, prm)
     cfg = L.fit_cfg(ctx, p, fields, prm, p_skip=0.5, mode=F.FPIC_LEARN_SKIP)
@@ -627,7 +630,8 @@ def run_skip_analysis(device, n=1 << 20, gen_steps=10, eval_steps=10, time_steps
                      "max_dH_over_D0": _max_dH(F, ctx, p)})
     # pure IMR from z^n on the same state: iterations per solve without the trial as guess
     _restore(p, snap)
-    prm_i = F.push_params(DT, scheme=F.FPIC_IMR, r_max=float(g.rn[-1]), B0pot=B0, imr_newton=True)
+    prm_i = F.push_params(DT, scheme=F.FPIC_IMR, r_max=float(g.rn[-1]), B0pot=B0, imr_newton=True,
+                          imr_substeps=IMR_SUBSTEPS, substep_tol=SUBSTEP_TOL)
     torch.cuda.synchronize()
     e0.record()
     st_i = F.fpic_push(ctx, p, fields, prm_i, stats=True)
