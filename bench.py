@@ -54,7 +54,7 @@ NOMINAL_FP64_GFLOPS = 1250.0
 # DRAM bytes (read + write) of one k_explicit<1> launch on this workload,
 # from one ncu capture of the current kernel (117.8 MB + 51.6 MB); the
 # algorithmic bytes are ~180 B per particle (189 MB for 2^20).
-TRAFFIC_K_EXPLICIT = 255.8e6   # ncu dram__bytes_read.sum + dram__bytes_write.sum, one 2^20 launch
+TRAFFIC_K_EXPLICIT = 590.1e6   # ncu dram__bytes_read.sum + dram__bytes_write.sum, one warm 2^20 launch (slope cache on)
 # deposit: FIDO velocity (41) + 133 distinct sqrt(gamma) lattice points x 9
 # (3 sub-grids x 49, less the split column and row they share) + 3 sub-grids x
 # (lattice 14 + four 16-point sums 128 + weights 16) + 2 th lattices (56) + shares (30)
