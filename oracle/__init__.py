@@ -62,7 +62,8 @@ class PushParams(C.Structure):
                 ("scheme", C.c_int), ("implicit_kind", C.c_int), ("thr", C.c_double),
                 ("tol", C.c_double), ("max_iter", C.c_int), ("r_h", C.c_double),
                 ("r_max", C.c_double), ("dg_eps", C.c_double), ("dt_imp", C.c_double),
-                ("imr_newton", C.c_int), ("imr_substeps", C.c_int), ("substep_tol", C.c_double)]
+                ("imr_newton", C.c_int), ("imr_substeps", C.c_int), ("substep_tol", C.c_double),
+                ("theta_full", C.c_int), ("theta_lo", C.c_double), ("theta_period", C.c_double)]
 
 
 _D = C.POINTER(C.c_double)
@@ -78,7 +79,7 @@ def _declare(L):
     L.or_hamiltonian.argtypes = [C.c_double, C.c_double, C.c_double, _I64, _D, _D, _D, _D, _D]
     L.or_rhs.argtypes = [C.c_double, C.c_double, _I64, _D, _D, _D, _D, _D]
     L.or_imr_blocks.argtypes = [C.c_double, C.c_double, _I64, _D, _D, _D, _D, _D]
-    L.or_gather.argtypes = [C.c_int, C.c_int, C.c_int, _D, _D, _D, _D, C.POINTER(_D), _I64, _D, _D, _D]
+    L.or_gather.argtypes = [C.c_int, C.c_int, C.c_int, _D, _D, _D, _D, C.POINTER(_D), _I64, _D, _D, _D, C.c_int]
     L.or_cell_index.argtypes = [C.c_int, C.c_int, _D, _D, _I64, _D, _D, _U32]
     L.or_dg_grad.argtypes = [C.c_double, C.c_double, _D, _D, C.c_double, _D]
     L.or_dg_quot.argtypes = [C.c_double, C.c_double, _D, _D, C.c_int, _D]
@@ -222,7 +223,8 @@ def gather(g, F, r, t):
     r, t = f64(np.atleast_1d(r)), f64(np.atleast_1d(t))
     F = [f64(f) for f in F]
     out = np.empty((r.size, 6))
-    lib().or_gather(*_grid_args(g), _fields_ptrs(F), r.size, ptr(r), ptr(t), ptr(out))
+    lib().or_gather(*_grid_args(g), _fields_ptrs(F), r.size, ptr(r), ptr(t), ptr(out),
+                    int(getattr(g, "full_theta", False)))
     return out
 
 
@@ -234,22 +236,33 @@ def cell_index(g, r, t):
 
 
 def wald_on_grid(a, B0, g):
-    """Appendix B.1 sampled at every Yee point; returns [D^r, D^th, D^ph, B^r, B^th, B^ph]."""
+    """Appendix B.1 sampled at every Yee point; returns [D^r, D^th, D^ph, B^r, B^th, B^ph].
+    Full-theta grid: column Nth of every component is the periodic image of
+    column 0 (copied, so the two are equal bit for bit)."""
     F = [np.zeros((g.Nr + 1) * g.ld) for _ in range(6)]
     arr = (_D * 6)(*[ptr(f) for f in F])
     lib().or_wald_on_grid(a, B0, *_grid_args(g), arr)
+    if getattr(g, "full_theta", False):
+        for f in F:
+            v = f.reshape(g.Nr + 1, g.ld)
+            v[:, g.Nth] = v[:, 0]
     return F
 
 
 def push_params(M=1.0, a=0.9, B0pot=0.0, field_kind=FIELD_NONE, B0field=0.0, dt=0.01,
                 scheme=RK4, implicit_kind=IMR, thr=1e-12, tol=1e-14, max_iter=50,
                 r_h=None, r_max=1e300, dg_eps=1e-10, dt_imp=0.0, imr_newton=False, imr_substeps=0,
-                substep_tol=0.0):
+                substep_tol=0.0, grid=None):
+    """grid: with a full-theta grid (inputs.full_theta_grid) the particles'
+    th boundary is periodic over its period; otherwise the half-theta
+    reflection at the poles."""
     if r_h is None:
         r_h = M + np.sqrt(M * M - a * a)
+    full = grid is not None and getattr(grid, "full_theta", False)
+    lo, per = (float(grid.tn[0]), float(grid.tn[-1] - grid.tn[0])) if full else (0.0, 0.0)
     return PushParams(M, a, B0pot, field_kind, B0field, dt, scheme, implicit_kind, thr, tol,
                       max_iter, r_h, r_max, dg_eps, dt_imp, int(bool(imr_newton)), int(imr_substeps),
-                      float(substep_tol))
+                      float(substep_tol), int(full), lo, per)
 
 
 def push(p: PushParams, z, qm, H0, D0, Hn, alive, g=None, F=None, flags=False):

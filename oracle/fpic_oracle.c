@@ -277,6 +277,7 @@ typedef struct {
     const double *rh;   /* r_{i+1/2},  i = 0..Nr-1 */
     const double *tn;   /* th_j,       j = 0..Nth  */
     const double *th;   /* th_{j+1/2}, j = 0..Nth-1 */
+    int full;           /* full-theta domain: th periodic with period tn[Nth] - tn[0] */
 } or_grid;
 
 static const int yee_roff[6] = {1, 0, 0, 0, 1, 1};
@@ -308,20 +309,52 @@ static double lin_w(const double *X, int i, double x)
     return w;
 }
 
+/* th reduced to one period [tn[0], tn[0] + P) of the full-theta domain
+ * (Sec. 2.5: periodic boundaries at th_max = 2 pi + eps). */
+static double wrap_theta(const or_grid *g, double t)
+{
+    const double t0 = g->tn[0], P = g->tn[g->Nth] - g->tn[0];
+    while (t < t0) t += P;
+    while (t >= t0 + P) t -= P;
+    return t;
+}
+
 /* Field gather (grid -> particle).  Reading: the paper does not state its
  * gather; each component is interpolated bilinearly in (r, th) on its own
- * staggered sub-grid. */
+ * staggered sub-grid.  Full-theta domain: th is taken modulo the period;
+ * column Nth of every array is the image of column 0, so the node sub-grid
+ * interpolates between tn[Nth-1] and tn[Nth] as usual, and the half-node
+ * sub-grid's nodes are extended by th[Nth] = th[0] + P: a point below th[0]
+ * is taken at th + P, in the cell [th[Nth-1], th[Nth]]. */
 static void gather(const or_grid *g, const double *const F[6], double r, double t,
                    double D[3], double B[3])
 {
-    double v[6];
+    double v[6], th_ext[2] = {0.0, 0.0};
+    if (g->full) t = wrap_theta(g, t);
     for (int k = 0; k < 6; ++k) {
         const double *X = yee_roff[k] ? g->rh : g->rn;
         const double *Y = yee_toff[k] ? g->th : g->tn;
         int mx = yee_roff[k] ? g->Nr : g->Nr + 1;
         int my = yee_toff[k] ? g->Nth : g->Nth + 1;
-        int i = locate(X, mx, r), j = locate(Y, my, t);
-        double wr = lin_w(X, i, r), wt = lin_w(Y, j, t);
+        int i = locate(X, mx, r), j;
+        double wr = lin_w(X, i, r), wt;
+        if (g->full && yee_toff[k]) {
+            const double P = g->tn[g->Nth] - g->tn[0];
+            const double th_top = g->th[0] + P;
+            const double tt = t < g->th[0] ? t + P : t;
+            if (tt >= g->th[g->Nth - 1]) {
+                j = g->Nth - 1;
+                th_ext[0] = g->th[g->Nth - 1];
+                th_ext[1] = th_top;
+                wt = lin_w(th_ext, 0, tt);
+            } else {
+                j = locate(Y, my, tt);
+                wt = lin_w(Y, j, tt);
+            }
+        } else {
+            j = locate(Y, my, t);
+            wt = lin_w(Y, j, t);
+        }
         const double *f = F[k];
         v[k] = (1.0 - wr) * (1.0 - wt) * f[i * g->ld + j]
              + wr * (1.0 - wt) * f[(i + 1) * g->ld + j]
@@ -356,6 +389,8 @@ typedef struct {
     int imr_newton;        /* IMR solver: 0 the fixed-point map of Eq. (imr2), 1 Newton */
     int imr_substeps;      /* an unconverged IMR solve is redone in up to 2^this substeps (0: never) */
     double substep_tol;    /* |H(end) - H(z^n)| / D_0 a substepped step must meet (0: none) */
+    int theta_full;        /* full-theta domain: th periodic on [theta_lo, theta_lo + theta_period) */
+    double theta_lo, theta_period;   /* tn[0] and tn[Nth] - tn[0] of the grid (period 2 pi) */
 } or_push_params;
 
 typedef struct {
@@ -791,7 +826,12 @@ static int step_ham(const or_ctx *c, double h, const double *z0, const double *g
  * Returns 0 if the particle is removed (r < r_h or r > r_max). */
 static int particle_bc(const or_push_params *p, double *z)
 {
-    if (z[1] < 0.0) {
+    if (p->theta_full) {
+        /* full-theta domain (Sec. 2.5): periodic in th, no reflection */
+        const double P = p->theta_period;
+        while (z[1] < p->theta_lo) z[1] += P;
+        while (z[1] >= p->theta_lo + P) z[1] -= P;
+    } else if (z[1] < 0.0) {
         z[1] = -z[1];
         z[4] = -z[4];
         z[2] += M_PI;
@@ -1003,9 +1043,9 @@ void or_rhs(double M, double a, int64_t n, const double *z, const double *qm,
 
 void or_gather(int Nr, int Nth, int ld, const double *rn, const double *rh,
                const double *tn, const double *th, const double *const *F,
-               int64_t n, const double *r, const double *t, double *DB)
+               int64_t n, const double *r, const double *t, double *DB, int full)
 {
-    or_grid g = {Nr, Nth, ld, rn, rh, tn, th};
+    or_grid g = {Nr, Nth, ld, rn, rh, tn, th, full};
     for (int64_t p = 0; p < n; ++p) gather(&g, F, r[p], t[p], DB + 6 * p, DB + 6 * p + 3);
 }
 
@@ -1054,7 +1094,7 @@ int64_t or_push(const or_push_params *p, int Nr, int Nth, int ld, const double *
                 const double *H0, const double *D0, double *Hn, uint8_t *alive,
                 uint8_t *scheme_out, uint8_t *iters_out, uint8_t *notconv_out)
 {
-    or_grid g = {Nr, Nth, ld, rn, rh, tn, th};
+    or_grid g = {Nr, Nth, ld, rn, rh, tn, th, p->theta_full};
     int64_t notconv = 0;
     for (int64_t k = 0; k < n; ++k) {
         scheme_out[k] = 0;

@@ -29,6 +29,10 @@ class Grid:
     rn, rh   : integer r nodes (Nr + 1) and half nodes r_{i+1/2} (Nr)
     tn, th   : integer th nodes (Nth + 1) and half nodes (Nth)
     ld       : leading dimension of every field array ([i * ld + j])
+    full_theta : th spans one full period [tn[0], tn[0] + 2 pi) with
+               periodic boundaries (tn[Nth] = tn[0] + 2 pi is the image of
+               tn[0]; column Nth of every field array holds the image of
+               column 0); False: the half-theta domain between the poles
     """
     Nr: int
     Nth: int
@@ -37,6 +41,7 @@ class Grid:
     tn: np.ndarray
     th: np.ndarray
     ld: int
+    full_theta: bool = False
 
     @property
     def size(self) -> int:
@@ -61,6 +66,22 @@ def log_grid(Nr: int, Nth: int, r_min: float, r_max: float,
     tn = np.linspace(th_min, th_max, Nth + 1)
     th = 0.5 * (tn[:-1] + tn[1:])
     return Grid(Nr, Nth, rn, rh, tn, th, Nth + 1)
+
+
+def full_theta_grid(Nr: int, Nth: int, r_min: float, r_max: float) -> Grid:
+    """Full-theta domain (Sec. 2.5): th nodes eps + j dth, j = 0..Nth, with
+    dth = 2 pi / Nth and eps = pi / (2 Nth) = dth / 4, half nodes midway;
+    both poles (th = pi and th = 0 = 2 pi) then lie midway between a half
+    node and a node.  Nth must be even.  Uniform in ln r as log_grid."""
+    if Nth % 2:
+        raise ValueError("full_theta_grid: Nth must be even")
+    lr = np.linspace(math.log(r_min), math.log(r_max), Nr + 1)
+    rn = np.exp(lr)
+    rh = np.exp(0.5 * (lr[:-1] + lr[1:]))
+    dth = 2.0 * math.pi / Nth
+    tn = 0.25 * dth + dth * np.arange(Nth + 1)
+    th = tn[:-1] + 0.5 * dth
+    return Grid(Nr, Nth, rn, rh, tn, th, Nth + 1, True)
 
 
 def wald_grid(N: int, a: float, M: float = 1.0, r_max: float = 50.0) -> Grid:

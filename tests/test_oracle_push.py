@@ -901,3 +901,144 @@ def test_unconverged_imr_step_is_redone_in_substeps(newton):
     # the H condition also redoes converged steps that miss it: the largest
     # step error over all particles falls
     assert dH(z_t).max() < dH(z_on).max()
+
+
+def _meridional(a, n, seed):
+    """Geodesics with u_ph = 0 (L = 0) heading for a pole: th near 0 or pi,
+    u_th towards it."""
+    rng = np.random.default_rng(seed)
+    north = rng.random(n) < 0.5
+    th = rng.uniform(0.02, 0.2, n)
+    th = np.where(north, th, np.pi - th)
+    uth = rng.uniform(1.0, 3.0, n) * np.where(north, -1.0, 1.0)
+    z = np.stack([rng.uniform(6.0, 12.0, n), th, rng.uniform(0, 6, n), rng.normal(size=n) * 0.2, uth,
+                  np.zeros(n)], 1)
+    return np.ascontiguousarray(z)
+
+
+def _to_half(zf):
+    """A full-theta state in the half-theta coordinates: th taken modulo
+    2 pi; th in (pi, 2 pi) is the half plane ph + pi at polar angle
+    2 pi - th, with u_th reversed."""
+    zh = zf.copy()
+    zh[:, 1] = np.mod(zf[:, 1], 2 * np.pi)
+    zf = zh.copy()
+    low = zf[:, 1] > np.pi
+    zh[low, 1] = 2 * np.pi - zf[low, 1]
+    zh[low, 4] = -zf[low, 4]
+    zh[low, 2] = zf[low, 2] + np.pi
+    return zh
+
+
+def test_full_theta_geodesics_cross_the_poles_as_the_reflection_maps_them():
+    """Sec. 2.5: in the full-theta domain particles cross the poles without
+    reflection (th continues past pi into the other half plane, and past 0 to
+    2 pi, periodically).  Geodesics with u_ph = 0 (regular on the axis) over
+    60 RK4 steps that take them over a pole equal, mapped back into the
+    half-theta coordinates, the half-theta run with its reflections (1e-12:
+    the reflection's ph + pi and 2 pi - th round differently)."""
+    a, dt, steps = 0.9, 0.05, 60
+    z0 = _meridional(a, 200, 47)
+    gf = I.full_theta_grid(16, 32, 1.5, 40.0)
+    pf = O.push_params(a=a, dt=dt, scheme=O.RK4, grid=gf)
+    ph = O.push_params(a=a, dt=dt, scheme=O.RK4)
+    zf, _, _, af = _run(pf, z0, steps)
+    zh, _, _, ah = _run(ph, z0, steps)
+    assert (af == 1).all() and (ah == 1).all()
+    assert ((zf[:, 1] > np.pi) | (zf[:, 1] < z0[:, 1].min())).mean() > 0.3       # crossed
+    assert ((zf[:, 1] >= gf.tn[0]) & (zf[:, 1] < gf.tn[0] + 2 * np.pi)).all()
+    zm = _to_half(zf)
+    dph = np.angle(np.exp(1j * (zm[:, 2] - zh[:, 2])))
+    zm[:, 2] = zh[:, 2] + dph
+    assert np.abs(zm - zh).max() / (np.abs(zh).max() + 1) < 1e-12
+
+
+def test_full_theta_particle_boundary_wraps():
+    """Particles stepping below tn[0] reappear at th + 2 pi, above tn[0] +
+    2 pi at th - 2 pi, with u_th and ph unchanged (no reflection)."""
+    a = 0.9
+    gf = I.full_theta_grid(8, 16, 1.5, 40.0)
+    t0 = gf.tn[0]
+    z = np.ascontiguousarray(np.array([[8.0, t0 + 1e-6, 1.0, 0.0, -2.0, 0.0],
+                                       [8.0, t0 + 2 * np.pi - 1e-6, 1.0, 0.0, 2.0, 0.0]]))
+    pf = O.push_params(a=a, dt=0.01, scheme=O.RK4, grid=gf)
+    zf, _, _, af = _run(pf, z, 1)
+    assert af.all()
+    assert t0 + np.pi < zf[0, 1] < t0 + 2 * np.pi and zf[0, 4] < 0 and zf[0, 2] == pytest.approx(1.0, abs=1e-3)
+    assert t0 <= zf[1, 1] < t0 + np.pi and zf[1, 4] > 0 and zf[1, 2] == pytest.approx(1.0, abs=1e-3)
+
+
+def test_full_theta_gather_is_periodic():
+    """The gather on a full-theta grid: a component sampled from a smooth
+    2 pi-periodic function (column Nth = column 0) is interpolated at th and
+    at th +- 2 pi identically; in the half-node wrap cell (th below th[0])
+    it is the linear interpolation between th[Nth-1] - 2 pi and th[0]."""
+    gf = I.full_theta_grid(6, 12, 2.0, 20.0)
+    ld = gf.ld
+    F = []
+    for k in range(6):
+        roff = k in (0, 4, 5); toff = k in (1, 3, 5)
+        X = gf.rh if roff else gf.rn
+        Y = gf.th if toff else gf.tn
+        f = np.zeros((gf.Nr + 1, ld))
+        for i, r in enumerate(X):
+            f[i, :len(Y)] = np.log(r) * (1.5 + np.cos(Y + k)) + np.sin(2 * Y)
+        if toff:
+            f[:, gf.Nth] = f[:, 0]
+        else:
+            f[:, gf.Nth] = f[:, 0]
+        F.append(np.ascontiguousarray(f.ravel()))
+    rng = np.random.default_rng(3)
+    r = rng.uniform(3.0, 15.0, 400)
+    t = rng.uniform(gf.tn[0], gf.tn[0] + 2 * np.pi, 400)
+    v0 = O.gather(gf, F, r, t)
+    for shift in (2 * np.pi, -2 * np.pi):
+        v1 = O.gather(gf, F, r, t + shift)
+        assert np.abs(v1 - v0).max() < 1e-13
+    # the half-node wrap cell for B^r (k = 3, at (i, j+1/2))
+    tw = gf.tn[0] + 0.3 * (gf.th[0] - gf.tn[0])
+    rr = np.array([7.0])
+    got = O.gather(gf, F, rr, np.array([tw]))[0, 3]
+    i = np.searchsorted(gf.rn, 7.0) - 1
+    wr = (7.0 - gf.rn[i]) / (gf.rn[i + 1] - gf.rn[i])
+    f3 = F[3].reshape(gf.Nr + 1, ld)
+    lo, hi = gf.th[-1] - 2 * np.pi, gf.th[0]
+    wt = (tw - lo) / (hi - lo)
+    col = lambda j: (1 - wr) * f3[i, j] + wr * f3[i + 1, j]
+    assert got == pytest.approx((1 - wt) * col(gf.Nth - 1) + wt * col(0), rel=1e-13)
+
+
+def test_full_theta_continued_lorentz_force_is_the_mirror_half_plane():
+    """In the full-theta domain th in (pi, 2 pi) is the other half of the
+    meridional plane, described by the same closed forms continued to
+    sin th < 0 (a signed sqrt(gamma) in the Lorentz force, the Wald field of
+    App. B continued likewise).  Charged particles (q/m = -1, +1) started
+    there in the analytic Wald field move exactly as their mirrors
+    (2 pi - th, ph + pi, -u_th) in the half-theta domain: 200 RK4 steps,
+    1e-10 (the mirror's ph + pi and 2 pi - th round differently)."""
+    a, B0, dt, steps, n = 0.9, 1.0, 0.01, 200, 100
+    rng = np.random.default_rng(53)
+    z = np.stack([rng.uniform(4.0, 9.0, n), rng.uniform(np.pi + 0.4, 2 * np.pi - 0.4, n), rng.uniform(0, 6, n),
+                  rng.normal(size=n) * 0.3, rng.normal(size=n) * 0.5, rng.normal(size=n) * 1.5], 1)
+    z = np.ascontiguousarray(z)
+    q = np.where(np.arange(n) % 2 == 0, -1.0, 1.0)
+    gf = I.full_theta_grid(8, 16, 1.5, 40.0)
+    zmirror = _to_half(z)
+    kw = dict(a=a, dt=dt, scheme=O.RK4, B0pot=B0, field_kind=O.FIELD_WALD, B0field=B0)
+    pf = O.push_params(grid=gf, **kw)
+    ph = O.push_params(**kw)
+    qf = np.ascontiguousarray(q)
+    zf = np.ascontiguousarray(z.copy())
+    zh = np.ascontiguousarray(zmirror.copy())
+    Hf, _, Df = O.hamiltonian(1.0, a, B0, zf, qf)
+    Hh, _, Dh = O.hamiltonian(1.0, a, B0, zh, qf)
+    assert np.abs(Hf - Hh).max() < 1e-12 * np.abs(Hh).max()       # H is even in the mirror
+    af, ah = np.ones(n, np.uint8), np.ones(n, np.uint8)
+    Hnf, Hnh = Hf.copy(), Hh.copy()
+    for _ in range(steps):
+        O.push(pf, zf, qf, Hf, Df, Hnf, af)
+        O.push(ph, zh, qf, Hh, Dh, Hnh, ah)
+    assert af.all() and ah.all()
+    zm = _to_half(zf)
+    zm[:, 2] = zh[:, 2] + np.angle(np.exp(1j * (zm[:, 2] - zh[:, 2])))
+    assert np.abs(zm - zh).max() / (np.abs(zh).max() + 1) < 1e-10
