@@ -187,6 +187,27 @@ const char *fpic_last_error(void);
 int fpic_set_grid(fpic_ctx *ctx, int Nr, int Nth, const double *rn, const double *rh,
                   const double *tn, const double *th);
 
+/* Geometry of the th direction (Sec. 2.5).  FPIC_THETA_HALF (the default
+ * after fpic_set_grid): th between the poles, particles reflected at them.
+ * FPIC_THETA_FULL: th covers one period, tn[Nth] - tn[0] = 2 pi (e.g.
+ * tn[j] = eps + j dth, dth = 2 pi / Nth, eps = pi / (2 Nth), so both poles
+ * lie midway between a node and a half node); th in (pi, 2 pi) is the other
+ * half of the meridional plane, described by the same closed forms with
+ * sin th < 0.  Particles cross the poles and wrap around periodically (no
+ * reflection); gathers wrap too: column Nth of every field array must hold
+ * the image of column 0 (fpic_init_wald writes it), and the half-node
+ * sub-grid's wrap cell runs from th[Nth-1] to th[0] + 2 pi.  Supported in
+ * the full-theta domain: the pushes (fpic_push, fpic_push_host,
+ * fpic_push_batched, the corrector form of the learned push),
+ * fpic_cell_index, fpic_sort, fpic_init_wald, fpic_hamiltonian,
+ * fpic_init_particles; the grid-side solvers (deposits, FDTD, cleaning,
+ * injection, BZ power, split-monopole initial field) and the skip form's
+ * features return FPIC_EINVAL.  Setting the mode drops cached slopes and
+ * coefficients.  Errors: FPIC_EINVAL (no grid, unknown mode, a full-theta
+ * grid whose period is not 2 pi to 1e-12). */
+enum { FPIC_THETA_HALF = 0, FPIC_THETA_FULL = 1 };
+int fpic_set_theta_mode(fpic_ctx *ctx, int mode);
+
 /* Sample the Wald electro-vacuum field of strength B0 (Appendix B.1) at
  * every Yee point: fields[0..5] = D^r, D^th, D^ph, B^r, B^th, B^ph, device
  * arrays in the grid layout.  Requires fpic_set_grid and M = 1 (the

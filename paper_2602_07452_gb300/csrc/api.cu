@@ -239,7 +239,10 @@ __global__ void k_cell(GridDev G, const double* r, const double* th, uint32_t* c
     if (p >= n) return;
     int i, j;
     double w;
-    const double rr = r[p], tt = th[p];
+    const double rr = r[p];
+    double tt, thv;
+    int mh;
+    theta_views(G, th[p], tt, thv, mh);
     const float lr = __logf((float)rr);
     locate(G.rn, G.irn, G.Nr + 1, rr, (lr - G.lr0) * G.ilr, i, w);
     locate(G.tn, G.itn, G.Nth + 1, tt, ((float)tt - G.t0) * G.it, j, w);
@@ -322,15 +325,18 @@ extern "C" int fpic_set_grid(fpic_ctx* c, int Nr, int Nth, const double* rn, con
         return set_error(FPIC_EINVAL, "fpic_set_grid: node tables must be finite and strictly increasing");
     if (!(rn[0] > 0.0)) return set_error(FPIC_EINVAL, "fpic_set_grid: r nodes must be positive");
     FPIC_CUDA(cudaSetDevice(c->device));
-    const size_t tot = 2 * ((size_t)(Nr + 1) + Nr + (Nth + 1) + Nth);
+    // the half-th list carries one more node, th[Nth] = th[0] + (tn[Nth] - tn[0]):
+    // the upper end of the full-theta wrap cell (unused in the half-theta domain)
+    const size_t tot = 2 * ((size_t)(Nr + 1) + Nr + (Nth + 1) + (Nth + 1));
     std::vector<double> h(tot);
     double* p = h.data();
     size_t o_rn = 0, o_rh = o_rn + Nr + 1, o_tn = o_rh + Nr, o_th = o_tn + Nth + 1;
-    size_t o_irn = o_th + Nth, o_irh = o_irn + Nr + 1, o_itn = o_irh + Nr, o_ith = o_itn + Nth + 1;
+    size_t o_irn = o_th + Nth + 1, o_irh = o_irn + Nr + 1, o_itn = o_irh + Nr, o_ith = o_itn + Nth + 1;
     memcpy(p + o_rn, rn, (Nr + 1) * sizeof(double));
     memcpy(p + o_rh, rh, Nr * sizeof(double));
     memcpy(p + o_tn, tn, (Nth + 1) * sizeof(double));
     memcpy(p + o_th, th, Nth * sizeof(double));
+    p[o_th + Nth] = th[0] + (tn[Nth] - tn[0]);
     auto inv = [](const double* X, int m, double* out) {
         for (int i = 0; i < m - 1; ++i) out[i] = 1.0 / (X[i + 1] - X[i]);
         out[m - 1] = 0.0;
@@ -338,7 +344,7 @@ extern "C" int fpic_set_grid(fpic_ctx* c, int Nr, int Nth, const double* rn, con
     inv(rn, Nr + 1, p + o_irn);
     inv(rh, Nr, p + o_irh);
     inv(tn, Nth + 1, p + o_itn);
-    inv(th, Nth, p + o_ith);
+    inv(p + o_th, Nth + 1, p + o_ith);
     retire(c, (void**)&c->d_nodes);
     FPIC_CUDA(cudaMalloc(&c->d_nodes, tot * sizeof(double)));
     FPIC_CUDA(cudaMemcpy(c->d_nodes, p, tot * sizeof(double), cudaMemcpyHostToDevice));
@@ -358,6 +364,10 @@ extern "C" int fpic_set_grid(fpic_ctx* c, int Nr, int Nth, const double* rn, con
     G.t0 = (float)tn[0];
     G.th0 = (float)th[0];
     G.it = (float)(Nth / (tn[Nth] - tn[0]));
+    G.full = 0;                      // half-theta until fpic_set_theta_mode says otherwise
+    G.tlo = tn[0];
+    G.tper = tn[Nth] - tn[0];
+    G.thlo = th[0];
     c->Nr = Nr;
     c->Nth = Nth;
     c->ld = Nth + 1;
@@ -370,6 +380,34 @@ extern "C" int fpic_set_grid(fpic_ctx* c, int Nr, int Nth, const double* rn, con
     return FPIC_OK;
 }
 
+extern "C" int fpic_set_theta_mode(fpic_ctx* c, int mode)
+{
+    if (!c) return set_error(FPIC_EINVAL, "fpic_set_theta_mode: NULL ctx");
+    if (!c->has_grid) return set_error(FPIC_EINVAL, "fpic_set_theta_mode: no grid set");
+    if (mode != FPIC_THETA_HALF && mode != FPIC_THETA_FULL)
+        return set_error(FPIC_EINVAL, "fpic_set_theta_mode: mode must be FPIC_THETA_HALF or FPIC_THETA_FULL");
+    if (mode == FPIC_THETA_FULL && !(fabs(c->G.tper - 2.0 * M_PI) <= 1e-12 * 2.0 * M_PI))
+        return set_error(FPIC_EINVAL, "fpic_set_theta_mode: a full-theta grid needs tn[Nth] - tn[0] = 2 pi (got %.17g)",
+                         c->G.tper);
+    c->G.full = mode == FPIC_THETA_FULL ? 1 : 0;
+    for (int i = 0; i < 6; ++i) c->fcoef_src[i] = nullptr;   // the wrap cell's coefficients
+    ++c->grid_gen;                                            // cached slopes belong to the old mode
+    return FPIC_OK;
+}
+
+// Full-theta domain: column Nth of each component array is the image of
+// column 0 (copied, so the two are equal bit for bit).
+__global__ void k_theta_image(GridDev G, double* F0, double* F1, double* F2, double* F3, double* F4, double* F5)
+{
+    double* F[6] = {F0, F1, F2, F3, F4, F5};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= G.Nr; i += gridDim.x * blockDim.x)
+        for (int k = 0; k < 6; ++k) {
+            const bool ro = (k == 0 || k == 4 || k == 5);
+            if (ro && i >= G.Nr) continue;
+            F[k][(size_t)i * G.ld + G.Nth] = F[k][(size_t)i * G.ld];
+        }
+}
+
 extern "C" int fpic_init_split_monopole(fpic_ctx* c, double* const fields[6], double B0, double zeta0,
                                         void* stream)
 {
@@ -377,6 +415,7 @@ extern "C" int fpic_init_split_monopole(fpic_ctx* c, double* const fields[6], do
     for (int i = 0; i < 6; ++i)
         if (!fields[i]) return set_error(FPIC_EINVAL, "fpic_init_split_monopole: fields[%d] is NULL", i);
     if (!c->has_grid) return set_error(FPIC_EINVAL, "fpic_init_split_monopole: no grid set");
+    if (c->G.full) return set_error(FPIC_EINVAL, "fpic_init_split_monopole: not in the full-theta domain");
     if (!std::isfinite(B0) || !std::isfinite(zeta0) || !(zeta0 > 0.0))
         return set_error(FPIC_EINVAL, "fpic_init_split_monopole: need finite B0 and zeta0 > 0");
     FPIC_CUDA(cudaSetDevice(c->device));
@@ -398,6 +437,9 @@ extern "C" int fpic_init_wald(fpic_ctx* c, double* const fields[6], double B0, v
     dim3 grid(1, c->Nr + 1);
     k_wald<<<grid, 256, 0, (cudaStream_t)stream>>>(c->bh, c->G, B0, fields[0], fields[1], fields[2], fields[3],
                                                    fields[4], fields[5]);
+    if (c->G.full)
+        k_theta_image<<<(unsigned)((c->Nr + 1 + 127) / 128), 128, 0, (cudaStream_t)stream>>>(
+            c->G, fields[0], fields[1], fields[2], fields[3], fields[4], fields[5]);
     FPIC_CUDA(cudaGetLastError());
     return FPIC_OK;
 }

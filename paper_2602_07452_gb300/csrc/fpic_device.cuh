@@ -178,11 +178,35 @@ __device__ __forceinline__ long long okey(double x)
 // 1/(X[i+1]-X[i]) live in library-owned device memory.
 struct GridDev {
     int Nr, Nth, ld;
-    const double *rn, *rh, *tn, *th;
+    const double *rn, *rh, *tn, *th;   // th: Nth half nodes + th[Nth] = th[0] + (tn[Nth] - tn[0])
     const double *irn, *irh, *itn, *ith;
     float lr0, lrh0, ilr;        // FP32 index estimate in ln r
     float t0, th0, it;           // FP32 index estimate in th
+    int full;                    // full-theta domain (periodic th), else half-theta
+    double tlo, tper, thlo;      // tn[0], the period tn[Nth] - tn[0], th[0]
 };
+
+// The th a gather sees.  Half-theta domain: th itself on both sub-grids,
+// Nth half nodes.  Full-theta domain (Sec. 2.5: periodic boundaries): th
+// wrapped into [tn[0], tn[0] + P) on the node sub-grid; on the half-node
+// sub-grid a point below th[0] is taken at th + P, in the wrap cell
+// [th[Nth-1], th[Nth] = th[0] + P] whose upper column (Nth) holds the image
+// of column 0, so that sub-grid has Nth + 1 nodes.  One wrap suffices:
+// particle states stay in the period and the RK4 stages and IMR midpoints
+// stay within a step of it.
+__device__ __forceinline__ void theta_views(const GridDev& G, double th, double& tn_view, double& th_view, int& mh)
+{
+    if (G.full) {
+        double t = th < G.tlo ? th + G.tper : th;
+        t = t >= G.tlo + G.tper ? t - G.tper : t;
+        tn_view = t;
+        th_view = t < G.thlo ? t + G.tper : t;
+        mh = G.Nth + 1;
+    } else {
+        tn_view = th_view = th;
+        mh = G.Nth;
+    }
+}
 
 // Locate x in node list X[0..m-1]: X[i] <= x < X[i+1], clamped to
 // [0, m-2]; w is the clamped linear weight.  est: FP32 index estimate.
@@ -214,13 +238,15 @@ __device__ __forceinline__ void gather(const GridDev& G, const Fields& F, double
                                        double D[3], double B[3])
 {
     const float lr = __logf(f32_est(r));
-    const float tf = f32_est(th);
     int i0, i1, j0, j1;
     double wr0, wr1, wt0, wt1;
     locate(G.rn, G.irn, G.Nr + 1, r, (lr - G.lr0) * G.ilr, i0, wr0);
     locate(G.rh, G.irh, G.Nr, r, (lr - G.lrh0) * G.ilr, i1, wr1);
-    locate(G.tn, G.itn, G.Nth + 1, th, (tf - G.t0) * G.it, j0, wt0);
-    locate(G.th, G.ith, G.Nth, th, (tf - G.th0) * G.it, j1, wt1);
+    double tnv, thv;
+    int mh;
+    theta_views(G, th, tnv, thv, mh);
+    locate(G.tn, G.itn, G.Nth + 1, tnv, (f32_est(tnv) - G.t0) * G.it, j0, wt0);
+    locate(G.th, G.ith, mh, thv, (f32_est(thv) - G.th0) * G.it, j1, wt1);
     const int ld = G.ld;
     // component k sits at (roff, toff): D^r (1,0) D^th (0,1) D^ph (0,0)
     //                                    B^r (0,1) B^th (1,0) B^ph (1,1)
@@ -255,13 +281,15 @@ __device__ __forceinline__ void gather_c(const GridDev& G, const FieldsC& F, dou
                                          double B[3])
 {
     const float lr = __logf(f32_est(r));
-    const float tf = f32_est(th);
     int i0, i1, j0, j1;
     double wr0, wr1, wt0, wt1;
     locate(G.rn, G.irn, G.Nr + 1, r, (lr - G.lr0) * G.ilr, i0, wr0);
     locate(G.rh, G.irh, G.Nr, r, (lr - G.lrh0) * G.ilr, i1, wr1);
-    locate(G.tn, G.itn, G.Nth + 1, th, (tf - G.t0) * G.it, j0, wt0);
-    locate(G.th, G.ith, G.Nth, th, (tf - G.th0) * G.it, j1, wt1);
+    double tnv, thv;
+    int mh;
+    theta_views(G, th, tnv, thv, mh);
+    locate(G.tn, G.itn, G.Nth + 1, tnv, (f32_est(tnv) - G.t0) * G.it, j0, wt0);
+    locate(G.th, G.ith, mh, thv, (f32_est(thv) - G.th0) * G.it, j1, wt1);
     const int ld = G.ld;
     double v[6];
 #pragma unroll
@@ -293,13 +321,15 @@ __device__ __forceinline__ void gather_c(const GridDev& G, const FieldsC& F, dou
                                          double B[3], const StageTile& T)
 {
     const float lr = __logf(f32_est(r));
-    const float tf = f32_est(th);
     int i0, i1, j0, j1;
     double wr0, wr1, wt0, wt1;
     locate(G.rn, G.irn, G.Nr + 1, r, (lr - G.lr0) * G.ilr, i0, wr0);
     locate(G.rh, G.irh, G.Nr, r, (lr - G.lrh0) * G.ilr, i1, wr1);
-    locate(G.tn, G.itn, G.Nth + 1, th, (tf - G.t0) * G.it, j0, wt0);
-    locate(G.th, G.ith, G.Nth, th, (tf - G.th0) * G.it, j1, wt1);
+    double tnv, thv;
+    int mh;
+    theta_views(G, th, tnv, thv, mh);
+    locate(G.tn, G.itn, G.Nth + 1, tnv, (f32_est(tnv) - G.t0) * G.it, j0, wt0);
+    locate(G.th, G.ith, mh, thv, (f32_est(thv) - G.th0) * G.it, j1, wt1);
     const int ld = G.ld;
     double v[6];
 #pragma unroll

@@ -134,7 +134,10 @@ __global__ void k_keys(GridDev G, const double* r, const double* th, const uint8
     if (p >= n) return;
     int i, j;
     double w;
-    const double rr = r[p], tt = th[p];
+    const double rr = r[p];
+    double tt, thv;
+    int mh;
+    theta_views(G, th[p], tt, thv, mh);
     const float lr = __logf((float)rr);
     locate(G.rn, G.irn, G.Nr + 1, rr, (lr - G.lr0) * G.ilr, i, w);
     locate(G.tn, G.itn, G.Nth + 1, tt, ((float)tt - G.t0) * G.it, j, w);
@@ -836,6 +839,7 @@ extern "C" int fpic_sort(fpic_ctx* c, fpic_particles* p, void* stream)
 extern "C" int fpic_deposit(fpic_ctx* c, fpic_particles* p, double* rho, double* jr, double* jth, double* jph,
                             void* stream)
 {
+    if (c && c->G.full) return set_error(FPIC_EINVAL, "fpic_deposit: not built for the full-theta domain");
     if (!c || !p || !rho || !jr || !jth || !jph) return set_error(FPIC_EINVAL, "fpic_deposit: NULL argument");
     if (!c->has_grid) return set_error(FPIC_EINVAL, "fpic_deposit: no grid set");
     if (p->n < 0 || p->n >= (1LL << 31)) return set_error(FPIC_EINVAL, "fpic_deposit: n out of range");
@@ -1054,6 +1058,7 @@ extern "C" int fpic_deposit_conserving(fpic_ctx* c, const fpic_particles* before
                                        double dt, double* rho, double* jr, double* jth, double* jph,
                                        long long* n_skipped, void* stream)
 {
+    if (c && c->G.full) return set_error(FPIC_EINVAL, "fpic_deposit_conserving: not built for the full-theta domain");
     if (!c || !before || !after || !rho || !jr || !jth || !jph)
         return set_error(FPIC_EINVAL, "fpic_deposit_conserving: NULL argument");
     if (!c->has_grid) return set_error(FPIC_EINVAL, "fpic_deposit_conserving: no grid set");
@@ -1306,6 +1311,7 @@ extern "C" int fpic_inject_pairs(fpic_ctx* c, fpic_particles* p, long long capac
                                  const double* Bth, const fpic_inject_params* prm, const double* draws,
                                  unsigned char* flags, long long* wanted, long long* n_new, void* stream)
 {
+    if (c && c->G.full) return set_error(FPIC_EINVAL, "fpic_inject_pairs: not built for the full-theta domain");
     if (!c || !p || !Br || !Bth || !prm || !draws || !n_new)
         return set_error(FPIC_EINVAL, "fpic_inject_pairs: NULL argument");
     if (!c->has_grid) return set_error(FPIC_EINVAL, "fpic_inject_pairs: no grid set");
@@ -1378,6 +1384,7 @@ __global__ void __launch_bounds__(256) k_bz_power(int Nth, int ld, const double*
 
 extern "C" int fpic_bz_power(fpic_ctx* c, const fpic_fields* f, int i, double* out, void* stream)
 {
+    if (c && c->G.full) return set_error(FPIC_EINVAL, "fpic_bz_power: not built for the full-theta domain");
     if (!c || !f || !out) return set_error(FPIC_EINVAL, "fpic_bz_power: NULL argument");
     if (!c->has_grid) return set_error(FPIC_EINVAL, "fpic_bz_power: no grid set");
     if (i < 0 || i >= c->Nr) return set_error(FPIC_EINVAL, "fpic_bz_power: half-r index %d outside [0, %d)", i, c->Nr);
@@ -1392,6 +1399,7 @@ extern "C" int fpic_bz_power(fpic_ctx* c, const fpic_fields* f, int i, double* o
 extern "C" int fpic_div_clean(fpic_ctx* c, double* const D[3], const double* rho, int n_iter, double* phi,
                               void* stream)
 {
+    if (c && c->G.full) return set_error(FPIC_EINVAL, "fpic_div_clean: not built for the full-theta domain");
     if (!c || !D || !D[0] || !D[1] || !D[2] || !rho) return set_error(FPIC_EINVAL, "fpic_div_clean: NULL argument");
     if (!c->has_grid) return set_error(FPIC_EINVAL, "fpic_div_clean: no grid set");
     if (n_iter < 0) return set_error(FPIC_EINVAL, "fpic_div_clean: n_iter < 0");
@@ -1460,6 +1468,7 @@ extern "C" int fpic_div_clean(fpic_ctx* c, double* const D[3], const double* rho
 
 extern "C" int fpic_fdtd_step(fpic_ctx* c, fpic_fields* f, const fpic_fdtd_params* prm, int stage, void* stream)
 {
+    if (c && c->G.full) return set_error(FPIC_EINVAL, "fpic_fdtd_step: not built for the full-theta domain");
     if (!c || !f || !prm) return set_error(FPIC_EINVAL, "fpic_fdtd_step: NULL argument");
     if (!c->has_grid) return set_error(FPIC_EINVAL, "fpic_fdtd_step: no grid set");
     if (stage != 1 && stage != 2) return set_error(FPIC_EINVAL, "fpic_fdtd_step: stage must be 1 or 2");

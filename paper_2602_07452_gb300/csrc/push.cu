@@ -158,8 +158,11 @@ __device__ __forceinline__ uint32_t cell_of(const GridDev& G, double r, double t
     int i, j;
     double w;
     const float lr = __logf(f32_est(r));
+    double tnv, thv;
+    int mh;
+    theta_views(G, th, tnv, thv, mh);
     locate(G.rn, G.irn, G.Nr + 1, r, (lr - G.lr0) * G.ilr, i, w);
-    locate(G.tn, G.itn, G.Nth + 1, th, (f32_est(th) - G.t0) * G.it, j, w);
+    locate(G.tn, G.itn, G.Nth + 1, tnv, (f32_est(tnv) - G.t0) * G.it, j, w);
     return (uint32_t)i * (uint32_t)G.Nth + (uint32_t)j;
 }
 
@@ -309,10 +312,16 @@ __device__ __forceinline__ void newton_update(const RhsJ& J, double hh, const do
 }
 
 // Particle boundaries (Sec. 2.5) and write-back of a finished step.
-__device__ __forceinline__ bool finish(const RunK& R, const PartDev& P, long long p, double z[6], double H,
-                                       int implicit, int iters)
+// Particle boundary in th (Sec. 2.5): half-theta domain, reflection at the
+// poles (reading: th -> -th or 2 pi - th, u_th -> -u_th, ph -> ph + pi);
+// full-theta domain, periodic (th wrapped into [tn[0], tn[0] + P), nothing
+// else changes).
+__device__ __forceinline__ void theta_boundary(const GridDev& G, double z[6])
 {
-    if (z[1] < 0.0) {
+    if (G.full) {
+        z[1] = z[1] < G.tlo ? z[1] + G.tper : z[1];
+        z[1] = z[1] >= G.tlo + G.tper ? z[1] - G.tper : z[1];
+    } else if (z[1] < 0.0) {
         z[1] = -z[1];
         z[4] = -z[4];
         z[2] += M_PI;
@@ -321,6 +330,12 @@ __device__ __forceinline__ bool finish(const RunK& R, const PartDev& P, long lon
         z[4] = -z[4];
         z[2] += M_PI;
     }
+}
+
+__device__ __forceinline__ bool finish(const RunK& R, const PartDev& P, long long p, double z[6], double H,
+                                       int implicit, int iters)
+{
+    theta_boundary(R.G, z);
     const bool alive = (z[0] >= R.r_h) && (z[0] <= R.r_max);
     store_state(P, p, z);
     P.Hn[p] = H;
@@ -484,8 +499,8 @@ __global__ void __launch_bounds__(128) k_explicit(const __grid_constant__ PushK 
         if (!alive) atomicAdd((unsigned long long*)&k.cnt[CNT_REMOVED], 1ull);
         if (k.t) k.t[p] += dt;
         if (keep && alive) {
-            if (y[1] != th_trial) {       // reflected at a pole: the slope of the stored state
-                sn = -sn;
+            if (y[1] != th_trial && !R.G.full) {   // reflected at a pole: the slope of the stored state
+                sn = -sn;                              // (a full-theta wrap changes neither F nor sin/cos)
                 F_at_sc<false, STAGED>(R, y, sn, cn, qm, em, fy, Hd, nullptr, &tile);
             }
             slope_store(k, p, y, qm, fy, sn, cn);
@@ -781,21 +796,6 @@ __global__ void __launch_bounds__(128, NEWTON ? 3 : 4) k_imr(const __grid_consta
     warp_add(&k.cnt[CNT_EVALS], n_ev, FULL);
 }
 
-// Pole reflection of the particle boundaries (Sec. 2.5, reading: th -> -th
-// or 2 pi - th, u_th -> -u_th, ph -> ph + pi), as in finish.
-__device__ __forceinline__ void reflect_pole(double z[6])
-{
-    if (z[1] < 0.0) {
-        z[1] = -z[1];
-        z[4] = -z[4];
-        z[2] += M_PI;
-    } else if (z[1] > M_PI) {
-        z[1] = 2.0 * M_PI - z[1];
-        z[4] = -z[4];
-        z[2] += M_PI;
-    }
-}
-
 // One implicit-midpoint solve of step h from zs (guess zs) by one thread,
 // with k_imr's iteration and stop rule; true if it converged within
 // max_iter (result in out), iterations added to its.
@@ -866,7 +866,7 @@ __device__ __forceinline__ bool implicit_end(const PushK& k, const RunK& R, long
     const bool alive = finish(R, k.P, p, z, H, 1, its);
     if (k.t) k.t[p] += k.dt_imp;
     if (keep && alive) {
-        if (z[1] != th_new) {
+        if (z[1] != th_new && !R.G.full) {     // reflected at a pole (a full-theta wrap changes nothing)
             double Hd;
             sn = -sn;
             F_at_sc(R, z, sn, cn, qm, em, f, Hd);
@@ -971,7 +971,7 @@ __global__ void __launch_bounds__(128) k_imr_substep(const __grid_constant__ Pus
             for (int sub = 0; sub < m && ok; ++sub) {
                 double zn[6];
                 ok = imr_solve_serial<NEWTON>(k, R, zs, h, qm, em, sub_iter, zn, its, n_ev);
-                reflect_pole(zn);
+                theta_boundary(R.G, zn);
 #pragma unroll
                 for (int i = 0; i < 6; ++i) zs[i] = zn[i];
             }
@@ -1439,7 +1439,9 @@ __global__ void k_field_coef(GridDev G, Fields F, double* out, size_t sz)
         for (int k = 0; k < 6; ++k) {
             const bool ro = (k == 0 || k == 4 || k == 5);
             const bool to = (k == 1 || k == 3 || k == 5);
-            const int NRk = ro ? G.Nr : G.Nr + 1, NTk = to ? G.Nth : G.Nth + 1;
+            // full-theta domain: the half-node wrap cell (Nth - 1) also has
+            // coefficients (its upper column Nth is the image of column 0)
+            const int NRk = ro ? G.Nr : G.Nr + 1, NTk = to ? G.Nth + G.full : G.Nth + 1;
             if (i >= NRk - 1 || j >= NTk - 1) continue;
             const size_t o = (size_t)i * G.ld + j;
             const double* f = F.f[k];
@@ -2434,6 +2436,7 @@ static FeatK make_featk(fpic_ctx* c, const fpic_particles* p, const double* cons
 extern "C" int fpic_features(fpic_ctx* c, const fpic_particles* p, const double* const fields[6], double dt,
                              const fpic_learned_cfg* cfg, float* X, void* stream)
 {
+    if (c && c->G.full) return set_error(FPIC_EINVAL, "fpic_features: not built for the full-theta domain");
     if (!c || !p || !X) return set_error(FPIC_EINVAL, "fpic_features: NULL argument");
     if (p->n < 0) return set_error(FPIC_EINVAL, "fpic_features: n < 0");
     if (fields && !c->has_grid) return set_error(FPIC_EINVAL, "fpic_features: fields given but no grid set");
@@ -2454,6 +2457,8 @@ extern "C" int fpic_learn_sample(fpic_ctx* c, fpic_particles* p, const double* c
                                  float* S, void* stream)
 {
     if (!c || !p || !prm || !X || !T || !S) return set_error(FPIC_EINVAL, "fpic_learn_sample: NULL argument");
+    if ((!cfg || cfg->mode == FPIC_LEARN_SKIP) && c->G.full)
+        return set_error(FPIC_EINVAL, "fpic_learn_sample: the skip form is not built for the full-theta domain");
     if (!push_prm_ok(prm)) return set_error(FPIC_EINVAL, "fpic_learn_sample: need a Hyb1/Hyb2 scheme with the IMR partner");
     if (p->n < 0 || p->n >= (1LL << 31)) return set_error(FPIC_EINVAL, "fpic_learn_sample: n out of range");
     if (!particles_ok(p, true)) return set_error(FPIC_EINVAL, "fpic_learn_sample: NULL particle array");
@@ -2519,6 +2524,8 @@ extern "C" int fpic_push_learned(fpic_ctx* c, fpic_mlp* m, fpic_particles* p, co
         return set_error(FPIC_EINVAL, "fpic_push_learned: unknown cfg->mode");
     if (cfg->mode == FPIC_LEARN_SKIP && !(cfg->p_skip > 0.f && cfg->p_skip < 1.f))
         return set_error(FPIC_EINVAL, "fpic_push_learned: p_skip must be in (0, 1)");
+    if (cfg->mode == FPIC_LEARN_SKIP && c->G.full)
+        return set_error(FPIC_EINVAL, "fpic_push_learned: the skip form is not built for the full-theta domain");
     FPIC_CUDA(cudaSetDevice(c->device));
     cudaStream_t s = (cudaStream_t)stream;
     const long long n = p->n;

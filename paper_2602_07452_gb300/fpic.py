@@ -93,6 +93,7 @@ class fpic_learned_cfg(C.Structure):
 FPIC_LEARN_SKIP, FPIC_LEARN_CORRECT = 0, 1
 FPIC_TUNE_IMR_BLOCKS_PER_SM, FPIC_TUNE_DEP_THREADS, FPIC_TUNE_STATIC_FIELDS, FPIC_TUNE_REUSE_SLOPE = 0, 1, 2, 3
 FPIC_TUNE_STAGE_FIELDS = 4
+FPIC_THETA_HALF, FPIC_THETA_FULL = 0, 1
 
 
 # name -> (restype, argtypes)
@@ -130,6 +131,7 @@ _SIGS = {
     "fpic_destroy": (None, [C.c_void_p]),
     "fpic_last_error": (C.c_char_p, []),
     "fpic_set_grid": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _D, _D, _D, _D]),
+    "fpic_set_theta_mode": (C.c_int, [C.c_void_p, C.c_int]),
     "fpic_init_wald": (C.c_int, [C.c_void_p, C.POINTER(_D), C.c_double, C.c_void_p]),
     "fpic_init_particles": (C.c_int, [C.c_void_p, C.POINTER(fpic_particles), C.c_int, _D, C.c_int,
                                       C.c_double, C.c_void_p]),
@@ -269,11 +271,19 @@ def fpic_init_metric(M: float, a: float) -> Ctx:
 
 
 def fpic_set_grid(ctx: Ctx, grid) -> None:
+    """The grid's node tables; a full-theta grid (inputs.full_theta_grid)
+    also switches the context to FPIC_THETA_FULL."""
     import numpy as np
     arrs = [np.ascontiguousarray(x, dtype=np.float64) for x in (grid.rn, grid.rh, grid.tn, grid.th)]
     _check(lib().fpic_set_grid(ctx.handle, grid.Nr, grid.Nth, *[a.ctypes.data_as(_D) for a in arrs]))
     ctx.cells = grid.Nr * grid.Nth
     ctx.cells_size = (grid.Nr + 1) * (grid.Nth + 1)
+    if getattr(grid, "full_theta", False):
+        fpic_set_theta_mode(ctx, FPIC_THETA_FULL)
+
+
+def fpic_set_theta_mode(ctx: Ctx, mode: int) -> None:
+    _check(lib().fpic_set_theta_mode(ctx.handle, int(mode)))
 
 
 _FIELDS_CACHE = {}

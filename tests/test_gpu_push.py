@@ -798,3 +798,104 @@ def test_unconverged_solves_redone_in_substeps_match_oracle(F, field, newton):
         assert bad.mean() <= 0.02, (bad.sum(), trig.sum())
         assert abs(st["n_notconv"] - nc) <= max(2, 0.02 * fail.sum())
         assert nc < 0.1 * fail.sum()
+
+
+def test_full_theta_wald_field_matches_oracle(F):
+    """fpic_init_wald on a full-theta grid (fpic_set_theta_mode FULL): every
+    Yee component at th in (pi, 2 pi) from the continued closed forms, and
+    column Nth the exact image of column 0, as the oracle samples it."""
+    a = 0.9
+    g = I.full_theta_grid(64, 96, 0.9 * I.horizon(1.0, a), 40.0)
+    ctx = _mk(F, a, g)
+    Fo = O.wald_on_grid(a, 1.0, g)
+    Fg = [dev(np.zeros_like(f)) for f in Fo]
+    F.fpic_init_wald(ctx, Fg, 1.0)
+    for k in range(6):
+        got = Fg[k].cpu().numpy().reshape(g.Nr + 1, g.ld)
+        exp = Fo[k].reshape(g.Nr + 1, g.ld)
+        rows = g.Nr if k in (0, 4, 5) else g.Nr + 1
+        assert np.array_equal(got[:rows, g.Nth], got[:rows, 0])
+        assert np.abs(got[:rows] - exp[:rows]).max() <= 1e-13 * np.abs(exp).max(), k
+
+
+@pytest.mark.parametrize("scheme", ["RK4", "HYB1"])
+def test_full_theta_push_matches_oracle(F, scheme):
+    """Charged particles (q/m = -/+100) over the whole period of a
+    full-theta grid (96 x 128, a = 0.9 Wald field on it), some next to the
+    wrap at tn[0] and tn[0] + 2 pi and next to th = pi, plus meridional
+    geodesics crossing the poles: three steps, each within 1e-12 of the
+    oracle's full-theta step from the same state (periodic gather with the
+    half-node wrap cell, periodic particle boundary), cells and alive flags
+    bit-exact, scheme choices bit-exact away from threshold ties; slope
+    reuse on from the second step."""
+    a = 0.9
+    g = I.full_theta_grid(96, 128, 0.9 * I.horizon(1.0, a), 40.0)
+    Fo = O.wald_on_grid(a, 1.0, g)
+    ctx = _mk(F, a, g)
+    F.fpic_set_tuning(ctx, F.FPIC_TUNE_STATIC_FIELDS, 1)
+    F.fpic_set_tuning(ctx, F.FPIC_TUNE_REUSE_SLOPE, 1)
+    d, z, q = thermal_state(3000, g, a, theta=0.1, seed=61)
+    rng = np.random.default_rng(62)
+    t0 = g.tn[0]
+    edge = np.concatenate([t0 + rng.uniform(1e-6, 2e-3, 150), t0 + 2 * np.pi - rng.uniform(1e-6, 2e-3, 150),
+                           np.pi + rng.choice([-1.0, 1.0], 150) * rng.uniform(1e-3, 4e-3, 150)])
+    z[:450, 1] = edge
+    north = rng.random(200) < 0.5
+    zm = np.stack([rng.uniform(6.0, 12.0, 200),
+                   np.where(north, t0 + rng.uniform(0, 3e-5, 200), np.pi - rng.uniform(0, 3e-5, 200)),
+                   rng.uniform(0, 6, 200), rng.normal(size=200) * 0.2, np.where(north, -2.0, 2.0),
+                   np.zeros(200)], 1)
+    z = np.ascontiguousarray(np.concatenate([z, zm]))
+    q = np.concatenate([q, np.zeros(200)])
+    n = len(q)
+    H0, _, D0 = O.hamiltonian(1.0, a, 1.0, z, q)
+    p = make_particles(z, q, H0, D0, H0.copy())
+    fd = fields_dev(Fo)
+    sch = getattr(F, "FPIC_" + scheme)
+    thr = 8e-5
+    prm = F.push_params(1e-3, scheme=sch, implicit=F.FPIC_IMR, thr=thr, r_max=g.rn[-1], B0pot=1.0, imr_newton=True)
+    po = O.push_params(a=a, dt=1e-3, scheme=getattr(O, scheme), implicit_kind=O.IMR, thr=thr, r_max=g.rn[-1],
+                       B0pot=1.0, field_kind=O.FIELD_GRID, imr_newton=True, grid=g)
+    pr = O.push_params(a=a, dt=1e-3, scheme=O.RK4, r_max=g.rn[-1], B0pot=1.0, field_kind=O.FIELD_GRID, grid=g)
+    wrapped = 0
+    for step in range(3):
+        zs, Hs, als, _, _, _ = to_np(p)
+        F.fpic_push(ctx, p, fd, prm)
+        zg, Hg, ag, sg, ig, cg = to_np(p)
+        zo = np.ascontiguousarray(zs.copy()); Ho = Hs.copy(); ao = als.copy()
+        nc, so, io = O.push(po, zo, q, H0, D0, Ho, ao, g, Fo)
+        ok = als == 1
+        if scheme == "HYB1":
+            zr = np.ascontiguousarray(zs.copy()); Hr = Hs.copy()
+            O.push(pr, zr, q, H0, D0, Hr, als.copy(), g, Fo)
+            stat = (np.abs(Hr - H0) - np.abs(Hs - H0)) / D0 / 1e-3
+            near = np.abs(stat - thr) <= 1e-12 * abs(thr) + 1e-12 * np.abs(stat)
+            assert near.sum() <= 2
+            ok &= ~near
+            assert np.array_equal(sg[ok], so[ok])
+        assert np.array_equal(ag[ok], ao[ok])
+        live = ok & (ao == 1)
+        assert_state_close(zg, zo, TOL, live)
+        rel = np.minimum(np.abs(zo[:, 0, None] / g.rn[None, :] - 1).min(1), np.abs(zo[:, 1, None] - g.tn[None, :]).min(1))
+        far = live & (rel > 1e-11)
+        assert np.array_equal(cg[far], O.cell_index(g, zo[far, 0], zo[far, 1]))
+        assert ((zg[live, 1] >= t0) & (zg[live, 1] < t0 + 2 * np.pi)).all()
+        wrapped += int((np.abs(zg[live, 1] - zs[live, 1]) > np.pi).sum())
+    assert wrapped > 0
+
+
+def test_full_theta_rejects_the_grid_side_solvers(F):
+    """In the full-theta domain the deposits, FDTD, cleaning and injection
+    are not built: they refuse with FPIC_EINVAL instead of running."""
+    a = 0.9
+    g = I.full_theta_grid(16, 32, 0.9 * I.horizon(1.0, a), 40.0)
+    ctx = _mk(F, a, g)
+    z = np.ascontiguousarray(np.tile([[8.0, 1.0, 0.0, 0.0, 0.0, 3.0]], (10, 1)))
+    p = make_particles(z, np.ones(10))
+    with pytest.raises(F.FpicError, match="full-theta"):
+        F.fpic_deposit(ctx, p, g.size)
+    fl = F.Fields(g.size)
+    with pytest.raises(F.FpicError, match="full-theta"):
+        F.fpic_fdtd_step(ctx, fl, F.fdtd_params(1e-3), 1)
+    F.fpic_set_theta_mode(ctx, F.FPIC_THETA_HALF)
+    F.fpic_deposit(ctx, p, g.size)          # the half-theta reading of the same tables
