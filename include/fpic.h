@@ -373,19 +373,30 @@ int fpic_probe_fp64(double *gflops_out, int reps);
  *     deposit).  A tile load whose bounded wait runs out is counted and
  *     reported as FPIC_ETIMEOUT when stats are requested.  0 (default) =
  *     no staging.
+ *   FPIC_TUNE_DEP_LATTICE: arithmetic of fpic_deposit's trapezoid lattices
+ *     of sqrt(gamma) (Sec. 2.3).  1 (default) = paired FP32 (each value the
+ *     sum of two floats, about 48 bits; the square root to about 2^-44
+ *     relative), run on the FP32 pipe; 0 = FP64 with the square root from
+ *     the hardware estimate and one Goldschmidt step (2^-39.6 measured).
+ *     Lattice points, weights and node shares are the same; results differ
+ *     by rounding only (1e-13 relative and below on the deposited sources).
  * Errors: FPIC_EINVAL (NULL, unknown key, value out of range). */
 enum { FPIC_TUNE_IMR_BLOCKS_PER_SM = 0, FPIC_TUNE_DEP_THREADS = 1, FPIC_TUNE_STATIC_FIELDS = 2,
-       FPIC_TUNE_REUSE_SLOPE = 3, FPIC_TUNE_STAGE_FIELDS = 4 };
+       FPIC_TUNE_REUSE_SLOPE = 3, FPIC_TUNE_STAGE_FIELDS = 4, FPIC_TUNE_DEP_LATTICE = 5 };
 int fpic_set_tuning(fpic_ctx *ctx, int key, int value);
 int fpic_get_tuning(const fpic_ctx *ctx, int key, int *value);
 
 /* Test helper for the library's own FP64 elementary routines, one thread
  * per element of x (device, n values) into y (device):
- *   fn 0: 1/x by the hardware estimate and two Newton steps (push metric);
+ *   fn 0: 1/x by the hardware estimate and one third-order refinement
+ *         (push metric);
  *   fn 1: sqrt(x) by the hardware reciprocal-square-root estimate and one
  *         Goldschmidt step (deposit trapezoid sums), x > 0 normal;
  *   fn 2: y[2i] = sin x, y[2i+1] = cos x - 1 for a small step x (series
- *         below 2^-7, libm above), as used by the angle-addition updates.
+ *         below 2^-7, libm above), as used by the angle-addition updates;
+ *   fn 3: y = sqrt(x) in the deposit's paired-FP32 form (x split into two
+ *         floats, the result's two floats summed in FP64);
+ *   fn 4: as fn 2, in the deposit's paired-FP32 form.
  * Errors: FPIC_EINVAL (fn out of range, n < 0, NULL with n > 0). */
 int fpic_probe_math(int fn, const double *x, double *y, long long n, void *stream);
 

@@ -45,6 +45,7 @@ struct fpic_ctx {
     // launch-shape tuning (fpic_set_tuning)
     int imr_blocks_per_sm = 4;
     int dep_threads = 128;           // threads per block of the deposit's particle kernel
+    int dep_lattice = 1;             // FPIC_TUNE_DEP_LATTICE: 1 paired-FP32 trapezoid lattices, 0 FP64
     // per-cell field interpolation coefficients (rebuilt by every push with fields)
     void* d_fcoef = nullptr;
     size_t fcoef_bytes = 0;

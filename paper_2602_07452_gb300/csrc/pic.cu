@@ -13,6 +13,7 @@
 // The FDTD is HBM-bound; its metric factors come from tables built once.
 #include <math.h>
 
+#include "ff.cuh"
 #include "fpic_internal.h"
 
 namespace fpic {
@@ -428,8 +429,104 @@ __device__ __forceinline__ void subvolumes(const BH& bh, double x0, double x1, d
     V[3] = S11 * (hb * hd);
 }
 
+// The same lattices in paired-FP32 arithmetic (ff.cuh): the lattice
+// coordinates, the sin/cos rotations of the th lattice, the radicand, its
+// square root and the trapezoid sums run on the FP32 pipe (about 48 bits;
+// the square root to about 2^-44, against 2^-39.6 for the FP64 form above),
+// which issues 64 times the FP64 rate; the step sizes and the final
+// products stay in FP64, and the conversions between the two are integer
+// operations on the bits.  The values are sqrt(...) itself (no factor 2).
+struct BHff {
+    ff twoM, a2;
+};
+
+__device__ __forceinline__ void rotate_ff(ff s, ff c, ff sh, ff cm, ff& so, ff& co)
+{
+    so = ff_add(s, ff_add(ff_mul(c, sh), ff_mul(s, cm)));
+    co = ff_add(c, ff_add(ff_neg(ff_mul(s, sh)), ff_mul(c, cm)));
+}
+
+__device__ __forceinline__ void theta_lattice_ff(double hc, double hd, double s0, double c0, double st, double ct,
+                                                 double s1, double c1, ff sy[7], ff cy[7])
+{
+    sy[0] = ff_from(s0); cy[0] = ff_from(c0);
+    sy[3] = ff_from(st); cy[3] = ff_from(ct);
+    sy[6] = ff_from(s1); cy[6] = ff_from(c1);
+#pragma unroll 1
+    for (int half = 0; half < 2; ++half) {
+        const int b = 3 * half;
+        ff sh, cm;
+        sincos_step_ff(half ? hd : hc, sh, cm);
+        rotate_ff(sy[b], cy[b], sh, cm, sy[b + 1], cy[b + 1]);
+        // double angle: sin 2h = 2 sin h (1 + (cos h - 1)), cos 2h - 1 = 2 (cos h - 1)(cos h - 1 + 2)
+        const ff sh2 = ff_scale(ff_add(sh, ff_mul(sh, cm)), 2.f);
+        const ff cm2 = ff_scale(ff_mul(cm, ff_add(cm, ff_of(2.f))), 2.f);
+        rotate_ff(sy[b], cy[b], sh2, cm2, sy[b + 2], cy[b + 2]);
+    }
+}
+
+// One sub-grid lattice in paired FP32, row by row (the row loop is not
+// unrolled: one copy of the code serves every row and, through
+// k_dep_particle_ff's loop, every sub-grid).  col_in / row_in: take the
+// split column / row from col / row instead of evaluating them; put_shared:
+// store this lattice's split column and row there.
+__device__ __forceinline__ void subvolumes_ff(const BHff& bh, double x0, double x1, double r, double hc, double hd,
+                                              const ff* sy, const ff* cy, double V[4], ff* col, ff row[7],
+                                              bool col_in, bool row_in, bool put_shared)
+{
+    const double third = 1.0 / 3.0;
+    const double ha = (r - x0) * third, hb = (x1 - r) * third;
+    const ff x0f = ff_from(x0), rf = ff_from(r), haf = ff_from(ha), hbf = ff_from(hb);
+    ff P[7], Q[7];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        ff x;
+        if (k == 0) x = x0f;
+        else if (k < 3) x = ff_add(x0f, k == 1 ? haf : ff_scale(haf, 2.f));
+        else if (k == 3) x = rf;
+        else x = ff_add(rf, k == 4 ? hbf : (k == 5 ? ff_scale(hbf, 2.f) : ff_mulf(hbf, 3.f)));
+        const ff X = ff_sqr(x), B = ff_add(X, ff_mul(bh.twoM, x));
+        P[k] = ff_mul(X, B);
+        Q[k] = ff_add(X, B);
+    }
+    ff S00 = ff_of(0.f), S10 = ff_of(0.f), S01 = ff_of(0.f), S11 = ff_of(0.f);
+#pragma unroll 1
+    for (int l = 0; l < 7; ++l) {
+        ff f[7];
+        if (row_in && l == 3) {
+#pragma unroll
+            for (int k = 0; k < 7; ++k) f[k] = row[k];
+        } else {
+            const ff A = ff_mul(bh.a2, ff_sqr(cy[l]));
+#pragma unroll
+            for (int k = 0; k < 7; ++k)
+                if (k != 3 || !col_in) f[k] = ff_sqrt(ff_add(P[k], ff_mul(A, ff_add(Q[k], A))));
+            if (col_in) f[3] = col[l];
+        }
+        if (put_shared) {
+            col[l] = f[3];
+            if (l == 3) {
+#pragma unroll
+                for (int k = 0; k < 7; ++k) row[k] = f[k];
+            }
+        }
+        // trapezoid weights 1/2, 1, 1, 1/2 along r on each half; the row's
+        // th weight (1/2 at the ends and the split row) times sin th
+        const ff ra = ff_add(ff_scale(ff_add(f[0], f[3]), 0.5f), ff_add(f[1], f[2]));
+        const ff rb = ff_add(ff_scale(ff_add(f[3], f[6]), 0.5f), ff_add(f[4], f[5]));
+        const ff ws = ff_scale(sy[l], (l == 0 || l == 3 || l == 6) ? 0.5f : 1.f);
+        if (l <= 3) { S00 = ff_add(S00, ff_mul(ws, ra)); S10 = ff_add(S10, ff_mul(ws, rb)); }
+        if (l >= 3) { S01 = ff_add(S01, ff_mul(ws, ra)); S11 = ff_add(S11, ff_mul(ws, rb)); }
+    }
+    V[0] = ff_to(S00) * (ha * hc);
+    V[1] = ff_to(S10) * (hb * hc);
+    V[2] = ff_to(S01) * (ha * hd);
+    V[3] = ff_to(S11) * (hb * hd);
+}
+
 struct DepK {
     BH bh;
+    BHff bhf;        // 2M and a^2 as paired floats
     GridDev G;
     const double* trig;  // sin tn[0..Nth], cos tn[0..Nth], sin th[0..Nth-1], cos th[0..Nth-1]
     const double *r, *th, *ur, *uth, *uph, *qm, *w;
@@ -514,6 +611,81 @@ __global__ void __launch_bounds__(256) k_dep_particle(DepK k)
     const double Qt = Q * vt;
     k.rec[12 * n + p] = Qt * (V[3] * iV); k.rec[13 * n + p] = Qt * (V[2] * iV);
     k.rec[14 * n + p] = Qt * (V[1] * iV); k.rec[15 * n + p] = Qt * (V[0] * iV);
+    k.code[p] = (uint32_t)(i1 - i0 + 1) | ((uint32_t)(j1 - j0 + 1) << 2);
+}
+
+__global__ void __launch_bounds__(256) k_dep_particle_ff(DepK k)
+{
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= k.n_alive) return;
+    const GridDev& G = k.G;
+    const double r = k.r[p], t = k.th[p];
+    // FIDO three-velocity v^i = gamma^ij u_j / Gamma at the particle
+    double s, c;
+    sincos(t, &s, &c);
+    Geo g;
+    geo_eval(k.bh, r, s, c, g);
+    const double ur = k.ur[p], ut = k.uth[p], up = k.uph[p];
+    const double Ur = fma(g.gurr, ur, g.gurp * up), Ut = g.gutt * ut, Up = fma(g.gurp, ur, g.gupp * up);
+    const double iG = rsqrt(fma(ur, Ur, fma(ut, Ut, fma(up, Up, 1.0))));
+    const double Q = k.w[p] * k.qm[p];
+    const double vr = Ur * iG, vt = Ut * iG, vp = Up * iG;
+    // clamped positions and cells on the integer and half node lists
+    const double rn_c = clampd(r, G.rn[0], G.rn[G.Nr]), rh_c = clampd(r, G.rh[0], G.rh[G.Nr - 1]);
+    const double tn_c = clampd(t, G.tn[0], G.tn[G.Nth]), th_c = clampd(t, G.th[0], G.th[G.Nth - 1]);
+    int i0, i1, j0, j1;
+    double wd;
+    const float lr = __logf((float)r);
+    locate(G.rn, G.irn, G.Nr + 1, rn_c, (lr - G.lr0) * G.ilr, i0, wd);
+    locate(G.rh, G.irh, G.Nr, rh_c, (lr - G.lrh0) * G.ilr, i1, wd);
+    locate(G.tn, G.itn, G.Nth + 1, tn_c, ((float)t - G.t0) * G.it, j0, wd);
+    locate(G.th, G.ith, G.Nth, th_c, ((float)t - G.th0) * G.it, j1, wd);
+    // sin/cos at the clamped th (the particle's own unless clamped at an edge)
+    double stn = s, ctn = c, sth = s, cth = c;
+    if (tn_c != t) sincos(tn_c, &stn, &ctn);
+    if (th_c != t) sincos(th_c, &sth, &cth);
+    const double* sn = k.trig;
+    const double* cn = k.trig + (G.Nth + 1);
+    const double* sh = k.trig + 2 * (G.Nth + 1);
+    const double* ch = sh + G.Nth;
+    const double third = 1.0 / 3.0;
+    const long long n = k.n_alive;
+    // the split column / row are shared between the sub-grids unless clamped
+    const bool share = (rn_c == rh_c) && (tn_c == th_c);
+    ff sy[7], cy[7], col[7], row[7];
+    double hc = 0.0, hd = 0.0;
+    // sub-grid 0: (i, j), rho and j^ph; 1: (i+1/2, j), j^r (the th lattice of
+    // 0); 2: (i, j+1/2), j^th.  One copy of the lattice code serves all three.
+#pragma unroll 1
+    for (int sg = 0; sg < 3; ++sg) {
+        if (sg != 1) {
+            const bool hth = sg == 2;
+            const int jj = hth ? j1 : j0;
+            const double* Y = hth ? G.th : G.tn;
+            const double* sY = hth ? sh : sn;
+            const double* cY = hth ? ch : cn;
+            const double tc = hth ? th_c : tn_c;
+            hc = (tc - Y[jj]) * third;
+            hd = (Y[jj + 1] - tc) * third;
+            theta_lattice_ff(hc, hd, sY[jj], cY[jj], hth ? sth : stn, hth ? cth : ctn, sY[jj + 1], cY[jj + 1], sy, cy);
+        }
+        const bool hr = sg == 1;
+        const double x0 = hr ? G.rh[i1] : G.rn[i0], x1 = hr ? G.rh[i1 + 1] : G.rn[i0 + 1];
+        double V[4];
+        subvolumes_ff(k.bhf, x0, x1, hr ? rh_c : rn_c, hc, hd, sy, cy, V, col, row, share && sg == 1, share && sg == 2,
+                      sg == 0);
+        const double iV = rcp_nr(V[0] + V[1] + V[2] + V[3]);
+        // share of node (i+a, j+b) = V(opposite corner) / V
+        const double w00 = V[3] * iV, w10 = V[2] * iV, w01 = V[1] * iV, w11 = V[0] * iV;
+        const int b = sg == 0 ? 0 : 4 + 4 * sg;
+        const double Qs = sg == 0 ? Q : (sg == 1 ? Q * vr : Q * vt);
+        k.rec[(b + 0) * n + p] = Qs * w00; k.rec[(b + 1) * n + p] = Qs * w10;
+        k.rec[(b + 2) * n + p] = Qs * w01; k.rec[(b + 3) * n + p] = Qs * w11;
+        if (sg == 0) {
+            const double Qp = Q * vp;
+            k.rec[4 * n + p] = Qp * w00; k.rec[5 * n + p] = Qp * w10; k.rec[6 * n + p] = Qp * w01; k.rec[7 * n + p] = Qp * w11;
+        }
+    }
     k.code[p] = (uint32_t)(i1 - i0 + 1) | ((uint32_t)(j1 - j0 + 1) << 2);
 }
 
@@ -836,6 +1008,19 @@ extern "C" int fpic_sort(fpic_ctx* c, fpic_particles* p, void* stream)
     return sort_impl(c, p, w, (cudaStream_t)stream);
 }
 
+namespace fpic {
+static ff ff_host(double x)
+{
+    const float h = (float)x;
+    return {h, (float)(x - (double)h)};
+}
+
+static BHff bh_ff(const BH& bh)
+{
+    return {ff_host(bh.twoM), ff_host(bh.a2)};
+}
+}  // namespace fpic
+
 extern "C" int fpic_deposit(fpic_ctx* c, fpic_particles* p, double* rho, double* jr, double* jth, double* jph,
                             void* stream)
 {
@@ -858,11 +1043,13 @@ extern "C" int fpic_deposit(fpic_ctx* c, fpic_particles* p, double* rho, double*
         FPIC_CUDA(cudaMemsetAsync(w.off, 0, 4 * ((size_t)C + 2), s));
     }
     // alive particles occupy [0, off[C]) after the sort; the count is read on the device
-    DepK k{c->bh, c->G, c->d_metric + (size_t)MT_N * c->metric_stride, p->r, p->th, p->ur, p->uth, p->uph, p->qm, p->w, n, w.rec, w.code};
+    DepK k{c->bh, bh_ff(c->bh), c->G, c->d_metric + (size_t)MT_N * c->metric_stride, p->r, p->th, p->ur, p->uth, p->uph, p->qm, p->w, n, w.rec, w.code};
     if (n > 0) {
         // rec/code for all n slots; removed particles (past off[C]) are never summed
         const int dt_ = c->dep_threads;
-        k_dep_particle<<<(unsigned)((n + dt_ - 1) / dt_), dt_, 0, s>>>(k);
+        const unsigned nb = (unsigned)((n + dt_ - 1) / dt_);
+        if (c->dep_lattice) k_dep_particle_ff<<<nb, dt_, 0, s>>>(k);
+        else k_dep_particle<<<nb, dt_, 0, s>>>(k);
     }
     k_dep_cell<<<(unsigned)(((long long)C * 32 + 255) / 256), 256, 0, s>>>(w.rec, w.code, w.off, w.part, n > 0 ? n : 1, C);
     NodeK nk{c->Nr, c->Nth, c->ld, w.part, C, tabs_of(c), rho, jr, jth, jph};

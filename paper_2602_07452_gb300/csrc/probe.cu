@@ -1,6 +1,7 @@
 // Measurement helper: sustained FP64 FMA throughput of the device.  Eight
 // independent FMA chains per thread keep the FP64 pipe fed; the result is
 // stored so the chains cannot be removed.
+#include "ff.cuh"
 #include "fpic_internal.h"
 
 namespace fpic {
@@ -29,6 +30,13 @@ __global__ void k_math(int fn, const double* __restrict__ x, double* __restrict_
         y[i] = rcp_nr(v);
     } else if (fn == 1) {
         y[i] = sqrt_dep(v);
+    } else if (fn == 3) {
+        y[i] = ff_to(ff_sqrt(ff_from(v)));
+    } else if (fn == 4) {
+        ff sh, cm;
+        sincos_step_ff(v, sh, cm);
+        y[2 * i] = ff_to(sh);
+        y[2 * i + 1] = ff_to(cm);
     } else {
         double sh, cm;
         sincos_step(v, sh, cm);
@@ -42,7 +50,7 @@ __global__ void k_math(int fn, const double* __restrict__ x, double* __restrict_
 extern "C" int fpic_probe_math(int fn, const double* x, double* y, long long n, void* stream)
 {
     using namespace fpic;
-    if (fn < 0 || fn > 2 || n < 0 || (n > 0 && (!x || !y))) return set_error(FPIC_EINVAL, "fpic_probe_math: bad argument");
+    if (fn < 0 || fn > 4 || n < 0 || (n > 0 && (!x || !y))) return set_error(FPIC_EINVAL, "fpic_probe_math: bad argument");
     if (n == 0) return FPIC_OK;
     k_math<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(fn, x, y, n);
     FPIC_CUDA(cudaGetLastError());

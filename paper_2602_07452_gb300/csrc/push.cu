@@ -2843,6 +2843,11 @@ extern "C" int fpic_set_tuning(fpic_ctx* c, int key, int value)
             return set_error(FPIC_EINVAL, "fpic_set_tuning: field staging must be 0 or 1, got %d", value);
         c->stage_fields = value;
         return FPIC_OK;
+    case FPIC_TUNE_DEP_LATTICE:
+        if (value != 0 && value != 1)
+            return set_error(FPIC_EINVAL, "fpic_set_tuning: deposit lattice must be 0 or 1, got %d", value);
+        c->dep_lattice = value;
+        return FPIC_OK;
     default:
         return set_error(FPIC_EINVAL, "fpic_set_tuning: unknown key %d", key);
     }
@@ -2866,6 +2871,9 @@ extern "C" int fpic_get_tuning(const fpic_ctx* c, int key, int* value)
         return FPIC_OK;
     case FPIC_TUNE_STAGE_FIELDS:
         *value = c->stage_fields;
+        return FPIC_OK;
+    case FPIC_TUNE_DEP_LATTICE:
+        *value = c->dep_lattice;
         return FPIC_OK;
     default:
         return set_error(FPIC_EINVAL, "fpic_get_tuning: unknown key %d", key);

@@ -93,6 +93,7 @@ class fpic_learned_cfg(C.Structure):
 FPIC_LEARN_SKIP, FPIC_LEARN_CORRECT = 0, 1
 FPIC_TUNE_IMR_BLOCKS_PER_SM, FPIC_TUNE_DEP_THREADS, FPIC_TUNE_STATIC_FIELDS, FPIC_TUNE_REUSE_SLOPE = 0, 1, 2, 3
 FPIC_TUNE_STAGE_FIELDS = 4
+FPIC_TUNE_DEP_LATTICE = 5
 FPIC_THETA_HALF, FPIC_THETA_FULL = 0, 1
 
 
@@ -450,10 +451,11 @@ def fpic_get_tuning(ctx: Ctx, key: int) -> int:
 
 
 def fpic_probe_math(fn: int, x: torch.Tensor) -> torch.Tensor:
-    """The library's FP64 elementary routine `fn` (0 reciprocal, 1 square
-    root, 2 small-step sin / cos - 1) applied to the device tensor x."""
+    """The library's elementary routine `fn` (0 reciprocal, 1 square root,
+    2 small-step sin / cos - 1, 3 paired-FP32 square root, 4 paired-FP32
+    small-step sin / cos - 1) applied to the device tensor x."""
     x = x.contiguous()
-    y = torch.empty((x.numel(), 2) if fn == 2 else (x.numel(),), dtype=torch.float64, device=x.device)
+    y = torch.empty((x.numel(), 2) if fn in (2, 4) else (x.numel(),), dtype=torch.float64, device=x.device)
     _check(lib().fpic_probe_math(fn, x.data_ptr(), y.data_ptr(), x.numel(), _stream(None)))
     return y
 

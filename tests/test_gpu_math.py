@@ -44,6 +44,40 @@ def test_deposit_sqrt_error_bound(F):
     assert rel.max() <= 2.0 ** -38, rel.max()
 
 
+def test_paired_sqrt_error_bound(F):
+    """The deposit's paired-FP32 square root (the FP32 estimate, one FP32
+    Newton step on it, one Newton step for the root with the exact square
+    error): relative error below 2^-43 over the same radicands, an order of
+    magnitude inside the FP64 form's."""
+    x = _samples(0.5, 1e17, 1 << 20, 4)
+    got = F.fpic_probe_math(3, dev(x)).cpu().numpy()
+    ref = np.sqrt(x)
+    rel = np.abs(got - ref) / ref
+    print("paired sqrt max rel err", rel.max(), "= 2^%.1f" % np.log2(rel.max() + 1e-300))
+    assert rel.max() <= 2.0 ** -43, rel.max()
+
+
+def test_paired_small_step_sin_cos(F):
+    """The deposit's paired-FP32 sin h, cos h - 1 of a lattice step: the
+    series branch (|h| < 2^-7) to 2^-45 of sin h and 2^-54 absolute on
+    cos h - 1 (2^-38 of itself), the FP64 branch above within the same
+    relative bounds (the split into two floats); against sin h and
+    -2 sin^2(h/2)."""
+    rng = np.random.default_rng(5)
+    h = np.concatenate([rng.uniform(0.0, 0.0078, 1 << 18), rng.uniform(0.0, 1e-4, 1 << 14),
+                        [0.0, 1e-12, 0.0078124], rng.uniform(0.0079, 0.3, 1 << 12)])
+    got = F.fpic_probe_math(4, dev(h)).cpu().numpy()
+    s_ref = np.sin(h)
+    cm_ref = -2.0 * np.sin(0.5 * h) ** 2
+    es = np.abs(got[:, 0] - s_ref) / np.maximum(s_ref, 1e-300)
+    ec = np.abs(got[:, 1] - cm_ref)
+    print("paired sin rel %.3e, cos-1 abs %.3e, cos-1 rel %.3e" % (es.max(), ec.max(),
+          (ec / np.maximum(np.abs(cm_ref), 1e-300)).max()))
+    assert es.max() <= 2.0 ** -45
+    assert ec[h < 0.0078125].max() <= 2.0 ** -54
+    assert np.all(ec <= 2.0 ** -38 * np.abs(cm_ref) + 1e-300)
+
+
 def test_small_step_sin_cos(F):
     """Series branches (|h| < 2^-10: through h^5 / h^6; |h| < 2^-7: through
     h^7 / h^8): sin h and cos h - 1 to a few ulp of their own magnitude,

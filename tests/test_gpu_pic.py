@@ -49,16 +49,20 @@ def test_sort_is_the_stable_argsort(F):
     assert np.array_equal(p.cell.cpu().numpy().view(np.uint32), cell[perm].astype(np.uint32))
 
 
+@pytest.mark.parametrize("lattice", [1, 0])
 @pytest.mark.parametrize("a,nr,nth", [(0.0, 48, 40), (0.9, 48, 40), (0.99, 64, 700)])
-def test_deposit_matches_oracle(F, a, nr, nth):
+def test_deposit_matches_oracle(F, a, nr, nth, lattice):
     """Sec. 2.3 deposit on a coarse 48 x 40 grid (th steps beyond the
     series range of the lattice rotations) and a fine 64 x 700 grid (series
     range), 30011 e-/e+ with random weights and 10 % removed: every node of
     rho, j^r, j^th, j^ph within 1e-10 of the oracle (relative to the node's
-    sum of |Q W| scale), and bitwise reproducible."""
+    sum of |Q W| scale), and bitwise reproducible; with the trapezoid
+    lattices in paired FP32 (1, the default) and in FP64 (0)."""
     g = I.log_grid(nr, nth, 1.2 * I.horizon(1.0, a), 25.0)
     ctx = F.fpic_init_metric(1.0, a)
     F.fpic_set_grid(ctx, g)
+    assert F.fpic_get_tuning(ctx, F.FPIC_TUNE_DEP_LATTICE) == 1
+    F.fpic_set_tuning(ctx, F.FPIC_TUNE_DEP_LATTICE, lattice)
     n = 30011
     z, q, w, alive = _plasma(g, n, a, 5)
     ro = P.deposit(1.0, a, g, z, q, w, alive)
@@ -73,12 +77,44 @@ def test_deposit_matches_oracle(F, a, nr, nth):
         mask[: g.Nr + (0 if k == 1 else 1), : g.Nth + (0 if k == 2 else 1)] = True
         m = mask.ravel()
         err = np.abs(got[k] - ro[k])[m]
+        print("lattice", lattice, "component", k, "max err / scale %.3e" % (err.max() / sc.max()))
         assert err.max() <= 1e-10 * sc.max(), (k, err.max())
     # determinism: the same particles deposited again give identical bits
     p2 = make_particles(z, q, w=w, alive=alive)
     out2 = F.fpic_deposit(ctx, p2, g.size)
     for x, y in zip(out, out2):
         assert np.array_equal(x.cpu().numpy(), y.cpu().numpy())
+
+
+def test_deposit_lattice_arithmetic_changes_only_rounding(F):
+    """The paired-FP32 and FP64 trapezoid lattices (FPIC_TUNE_DEP_LATTICE)
+    evaluate the same points with the same weights: on the 1024^2 grid's
+    spacing near the horizon and far out (a = 0.99, 40000 particles) the
+    two deposits agree to 5e-12 of the largest node's |Q W| scale (the
+    scale the oracle test uses) -- set by the FP64 form's square root
+    (2^-39.6 relative; the paired one is 2^-44) -- while the oracle bound is
+    1e-10."""
+    a = 0.99
+    g = I.wald_grid(1024, a)
+    ctx = F.fpic_init_metric(1.0, a)
+    F.fpic_set_grid(ctx, g)
+    rng = np.random.default_rng(17)
+    n = 40000
+    lo = 1.02 * I.horizon(1.0, a)
+    d, q, w = I.thermal_draws(n, g, lo, 49.0, 0.5, seed=17)
+    z = O.seed_fido(1.0, a, d)
+    w = rng.uniform(0.5, 2.0, n)
+    outs = []
+    for lattice in (1, 0):
+        F.fpic_set_tuning(ctx, F.FPIC_TUNE_DEP_LATTICE, lattice)
+        p = make_particles(z, q, w=w)
+        outs.append([t.cpu().numpy() for t in F.fpic_deposit(ctx, p, g.size)])
+    p = make_particles(z, np.abs(q), w=w)
+    sc = F.fpic_deposit(ctx, p, g.size)[0].cpu().numpy().max()
+    for k in range(4):
+        rel = np.abs(outs[0][k] - outs[1][k]).max() / sc
+        print("component", k, "max |paired - FP64| / scale %.3e" % rel)
+        assert rel <= 5e-12, (k, rel)
 
 
 # (r, th) staggering of the components of each field family
