@@ -52,12 +52,14 @@ FLOP_RK4_TRIAL_REUSED = 4 * FLOP_EVAL + 79 + 5
 FLOP_IMR_FINAL_REUSE = FLOP_EVAL
 NOMINAL_FP64_GFLOPS = 1250.0
 # DRAM bytes (read + write) of one k_explicit<1> launch on this workload,
-# from one ncu capture of the current kernel (117.8 MB + 51.6 MB); the
-# algorithmic bytes are ~180 B per particle (189 MB for 2^20).
+# from one ncu capture of the current kernel (401.6 MB + 188.5 MB); the
+# algorithmic bytes are ~420 B per particle with the slope cache (440 MB
+# for 2^20).
 TRAFFIC_K_EXPLICIT = 590.1e6   # ncu dram__bytes_read.sum + dram__bytes_write.sum, one warm 2^20 launch (slope cache on)
 # deposit: FIDO velocity (41) + 133 distinct sqrt(gamma) lattice points x 9
 # (3 sub-grids x 49, less the split column and row they share) + 3 sub-grids x
-# (lattice 14 + four 16-point sums 128 + weights 16) + 2 th lattices (56) + shares (30)
+# (lattice 14 + four 16-point sums 128 + weights 16) + 2 th lattices (56) + shares (30),
+# counted as the FP64 operations of the quadrature however the lattice is evaluated
 FLOP_DEPOSIT = 41 + 133 * 9 + 3 * (14 + 128 + 16) + 56 + 30
 PIC_A, PIC_DT, PIC_W = 0.99, 5e-4, 1e-6
 
@@ -891,8 +893,10 @@ def run_pic(args, device, grid_n, ppc, steps, rank=0, conserving=False, inject_e
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
     dep_tune = None
     from paper_2602_07452_gb300 import autotune
+    lat_ms = None
     if not conserving:
         dep_tune = autotune.tune_deposit_threads(ctx, p, g.size)     # also leaves p sorted by cell
+        lat_ms = _time_deposit_lattices(F, ctx, p, g.size)
     else:
         F.fpic_sort(ctx, p)
     from paper_2602_07452_gb300.grpic import GRPIC
@@ -938,12 +942,37 @@ def run_pic(args, device, grid_n, ppc, steps, rank=0, conserving=False, inject_e
         "deposit": "charge-conserving variant (linear weights, Esirkepov split)" if conserving
                    else "Sec. 2.3 volume-weighted",
         "dt": PIC_DT, "absorbing": {"chi0": 1e4, "lambda": 5, "r_abs": 0.9 * r_max},
-        "deposit_achieved_gflops": None if conserving else ps * FLOP_DEPOSIT / t_dep / 1e9,
+        "deposit_lattice": None if conserving else
+        ("paired FP32" if F.fpic_get_tuning(ctx, F.FPIC_TUNE_DEP_LATTICE) else "FP64"),
+        "deposit_lattice_ms": lat_ms,
+        "deposit_algorithmic_gflops": None if conserving else ps * FLOP_DEPOSIT / t_dep / 1e9,
         "deposit_threads_autotuned_ms": dep_tune,
         "field_tile_staging_autotuned_ms": {("on" if k else "off"): round(v, 3) for k, v in stage_tune.items()},
         "field_tile_staging": "on" if F.fpic_get_tuning(ctx, F.FPIC_TUNE_STAGE_FIELDS) else "off",
         "field_tile_staged_block_fraction": stage_frac,
     }
+
+
+def _time_deposit_lattices(F, ctx, p, size, reps=2):
+    """fpic_deposit (sort included) with the trapezoid lattices in paired
+    FP32 (FPIC_TUNE_DEP_LATTICE 1, the default) and in FP64 (0), on the same
+    particles; the default is set again afterwards.  {"paired_fp32": ms,
+    "fp64": ms}."""
+    import torch
+    out = tuple(torch.zeros(size, dtype=torch.float64, device=p.r.device) for _ in range(4))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = {}
+    for name, v in (("fp64", 0), ("paired_fp32", 1)):
+        F.fpic_set_tuning(ctx, F.FPIC_TUNE_DEP_LATTICE, v)
+        F.fpic_deposit(ctx, p, size, out=out)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            F.fpic_deposit(ctx, p, size, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        res[name] = round(e0.elapsed_time(e1) / reps, 3)
+    return res
 
 
 def run_adaptive(device, n=1 << 20, steps=20, ratios=(1, 2, 4), newton=True):

@@ -194,13 +194,22 @@ struct GridDev {
 // of column 0, so that sub-grid has Nth + 1 nodes.  One wrap suffices:
 // particle states stay in the period and the RK4 stages and IMR midpoints
 // stay within a step of it.
+// The full-theta wrap is kept out of line behind a warp-uniform branch: if
+// it were if-converted, its FP64 compares and adds would be issued in the
+// half-theta domain too, on an FP64-bound push.
+static __device__ __noinline__ double2 theta_wrap_full(double th, double tlo, double tper, double thlo)
+{
+    double t = th < tlo ? th + tper : th;
+    t = t >= tlo + tper ? t - tper : t;
+    return make_double2(t, t < thlo ? t + tper : t);
+}
+
 __device__ __forceinline__ void theta_views(const GridDev& G, double th, double& tn_view, double& th_view, int& mh)
 {
     if (G.full) {
-        double t = th < G.tlo ? th + G.tper : th;
-        t = t >= G.tlo + G.tper ? t - G.tper : t;
-        tn_view = t;
-        th_view = t < G.thlo ? t + G.tper : t;
+        const double2 v = theta_wrap_full(th, G.tlo, G.tper, G.thlo);
+        tn_view = v.x;
+        th_view = v.y;
         mh = G.Nth + 1;
     } else {
         tn_view = th_view = th;
@@ -245,8 +254,9 @@ __device__ __forceinline__ void gather(const GridDev& G, const Fields& F, double
     double tnv, thv;
     int mh;
     theta_views(G, th, tnv, thv, mh);
-    locate(G.tn, G.itn, G.Nth + 1, tnv, (f32_est(tnv) - G.t0) * G.it, j0, wt0);
-    locate(G.th, G.ith, mh, thv, (f32_est(thv) - G.th0) * G.it, j1, wt1);
+    const float tfn = f32_est(tnv), tfh = G.full ? f32_est(thv) : tfn;
+    locate(G.tn, G.itn, G.Nth + 1, tnv, (tfn - G.t0) * G.it, j0, wt0);
+    locate(G.th, G.ith, mh, thv, (tfh - G.th0) * G.it, j1, wt1);
     const int ld = G.ld;
     // component k sits at (roff, toff): D^r (1,0) D^th (0,1) D^ph (0,0)
     //                                    B^r (0,1) B^th (1,0) B^ph (1,1)
@@ -288,8 +298,9 @@ __device__ __forceinline__ void gather_c(const GridDev& G, const FieldsC& F, dou
     double tnv, thv;
     int mh;
     theta_views(G, th, tnv, thv, mh);
-    locate(G.tn, G.itn, G.Nth + 1, tnv, (f32_est(tnv) - G.t0) * G.it, j0, wt0);
-    locate(G.th, G.ith, mh, thv, (f32_est(thv) - G.th0) * G.it, j1, wt1);
+    const float tfn = f32_est(tnv), tfh = G.full ? f32_est(thv) : tfn;
+    locate(G.tn, G.itn, G.Nth + 1, tnv, (tfn - G.t0) * G.it, j0, wt0);
+    locate(G.th, G.ith, mh, thv, (tfh - G.th0) * G.it, j1, wt1);
     const int ld = G.ld;
     double v[6];
 #pragma unroll
@@ -328,8 +339,9 @@ __device__ __forceinline__ void gather_c(const GridDev& G, const FieldsC& F, dou
     double tnv, thv;
     int mh;
     theta_views(G, th, tnv, thv, mh);
-    locate(G.tn, G.itn, G.Nth + 1, tnv, (f32_est(tnv) - G.t0) * G.it, j0, wt0);
-    locate(G.th, G.ith, mh, thv, (f32_est(thv) - G.th0) * G.it, j1, wt1);
+    const float tfn = f32_est(tnv), tfh = G.full ? f32_est(thv) : tfn;
+    locate(G.tn, G.itn, G.Nth + 1, tnv, (tfn - G.t0) * G.it, j0, wt0);
+    locate(G.th, G.ith, mh, thv, (tfh - G.th0) * G.it, j1, wt1);
     const int ld = G.ld;
     double v[6];
 #pragma unroll

@@ -316,11 +316,16 @@ __device__ __forceinline__ void newton_update(const RhsJ& J, double hh, const do
 // poles (reading: th -> -th or 2 pi - th, u_th -> -u_th, ph -> ph + pi);
 // full-theta domain, periodic (th wrapped into [tn[0], tn[0] + P), nothing
 // else changes).
+static __device__ __noinline__ double theta_period_wrap(double th, double tlo, double tper)
+{
+    th = th < tlo ? th + tper : th;
+    return th >= tlo + tper ? th - tper : th;
+}
+
 __device__ __forceinline__ void theta_boundary(const GridDev& G, double z[6])
 {
     if (G.full) {
-        z[1] = z[1] < G.tlo ? z[1] + G.tper : z[1];
-        z[1] = z[1] >= G.tlo + G.tper ? z[1] - G.tper : z[1];
+        z[1] = theta_period_wrap(z[1], G.tlo, G.tper);
     } else if (z[1] < 0.0) {
         z[1] = -z[1];
         z[4] = -z[4];
