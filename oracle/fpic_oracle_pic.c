@@ -215,6 +215,7 @@ typedef struct {
     double M, a, dt;
     double chi0, lam, r_abs, r_max;   /* absorbing layer, Eqs. (abs0)-(abs2) */
     int conserving;                   /* j arrays hold coordinate currents J (or_deposit_conserving) */
+    int full;                         /* full-theta domain: periodic in th (Sec. 2.5) */
 } or_fdtd_params;
 
 typedef struct {
@@ -227,6 +228,24 @@ static double R(const fctx *c, int ro, int i) { return ro ? c->g.rh[i] : c->g.rn
 static double T(const fctx *c, int to, int j) { return to ? c->g.th[j] : c->g.tn[j]; }
 static int NR(const fctx *c, int ro) { return ro ? c->g.Nr : c->g.Nr + 1; }
 static int NT(const fctx *c, int to) { return to ? c->g.Nth : c->g.Nth + 1; }
+
+/* Full-theta domain (Sec. 2.5: periodic boundaries at th_max = th_0 + 2 pi;
+ * reading: the node range is [tn_0, tn_0 + P), P = tn[Nth] - tn[0] = 2 pi,
+ * with Nth distinct nodes and Nth distinct half nodes; column Nth of every
+ * array holds the image of column 0, the way the gather reads it).  The
+ * backward th difference at j = 0 reaches the half node below th_0, i.e.
+ * th[Nth-1] - P: its spacing is th_ext - th[Nth-1] with th_ext = th[0] + P. */
+static double th_ext(const fctx *c)
+{
+    return c->g.th[0] + (c->g.tn[c->g.Nth] - c->g.tn[0]);
+}
+
+static void theta_images(const fctx *c, double *const F[3])
+{
+    if (!c->p->full) return;
+    for (int k = 0; k < 3; ++k)
+        for (int i = 0; i <= c->g.Nr; ++i) F[k][i * c->g.ld + c->g.Nth] = F[k][i * c->g.ld];
+}
 
 /* Eq. (abs2): chi(r) = chi0 ((r - r_abs)/(r_max - r_abs))^lambda beyond r_abs.
  * Reading: the damping term -chi F is integrated exactly over the step, i.e.
@@ -290,6 +309,7 @@ static void make_E(const fctx *c, const double *const D[3], const double *const 
             double Bt = avg_r(c, B[1], 1, 0, i, j);
             E[2][i * ld + j] = m.alpha * (m.g_rp * Dr + m.g_pp * D[2][i * ld + j]) + m.sqrtg * m.beta * Bt;
         }
+    theta_images(c, E);
 }
 
 /* H_i = alpha B_i - sqrtg eta_ijk beta^j D^k:
@@ -322,6 +342,7 @@ static void make_H(const fctx *c, const double *const D[3], const double *const 
             double Dt = avg_r(c, D[1], 0, 1, i, j);
             H[2][i * ld + j] = m.alpha * (m.g_rp * Br + m.g_pp * B[2][i * ld + j]) - m.sqrtg * m.beta * Dt;
         }
+    theta_images(c, H);
 }
 
 /* Eq. (m4) with Eq. (abs0): B_out = (B_in - dt curl E / sqrtg) exp(-chi dt),
@@ -353,6 +374,7 @@ static void update_B(const fctx *c, const double *const Bin[3], const double *co
             double dEr = (E[0][i * ld + j + 1] - E[0][i * ld + j]) / (c->g.tn[j + 1] - c->g.tn[j]);
             Bout[2][i * ld + j] = (Bin[2][i * ld + j] - p->dt * (dEt - dEr) / sg) * damp(c, r);
         }
+    theta_images(c, Bout);
 }
 
 /* Source J = alpha j - rho beta (Sec. 2.1, below Eq. m4) at the J^i points;
@@ -382,18 +404,23 @@ static double Jsrc(const fctx *c, int k, int i, int j, const double *const jv[3]
  * J = w0 J(j0, rho0) + w1 J(j1, rho1).  Boundaries (Sec. 2.5, reading):
  * components without a two-sided stencil copy their neighbour (zero
  * gradient) -- D^th, D^ph at i = 0 and i = Nr, D^r at j = 0 and j = Nth --
- * and D^ph = 0 on the axis rows j = 0, Nth. */
+ * and D^ph = 0 on the axis rows j = 0, Nth.  In the full-theta domain there
+ * are no axis rows: D^r and D^ph at j = 0 take their th difference across
+ * the seam (half node Nth-1, one period below), and column Nth is the image
+ * of column 0. */
 static void update_D(const fctx *c, const double *const Din[3], const double *const H[3],
                      const double *const j0[3], const double *rho0, double w0,
                      const double *const j1[3], const double *rho1, double w1, double *const Dout[3])
 {
     const or_fdtd_params *p = c->p;
-    int ld = c->g.ld, Nr = c->g.Nr, Nth = c->g.Nth;
+    int ld = c->g.ld, Nr = c->g.Nr, Nth = c->g.Nth, j_lo = p->full ? 0 : 1;
     for (int i = 0; i < Nr; ++i)                    /* D^r (i+1/2, j) */
-        for (int j = 1; j < Nth; ++j) {
+        for (int j = j_lo; j < Nth; ++j) {
             double r = c->g.rh[i], t = c->g.tn[j];
             double sg = sqrtg_at(p->M, p->a, r, t);
-            double curl = (H[2][i * ld + j] - H[2][i * ld + j - 1]) / (c->g.th[j] - c->g.th[j - 1]);
+            int jm = j > 0 ? j - 1 : Nth - 1;
+            double dth = j > 0 ? c->g.th[j] - c->g.th[j - 1] : th_ext(c) - c->g.th[Nth - 1];
+            double curl = (H[2][i * ld + j] - H[2][i * ld + jm]) / dth;
             double J = 0.0;
             if (w0 != 0.0) J += w0 * Jsrc(c, 0, i, j, j0, rho0);
             if (w1 != 0.0) J += w1 * Jsrc(c, 0, i, j, j1, rho1);
@@ -410,33 +437,38 @@ static void update_D(const fctx *c, const double *const Din[3], const double *co
             Dout[1][i * ld + j] = (Din[1][i * ld + j] + p->dt * (curl / sg - 4.0 * M_PI * J)) * damp(c, r);
         }
     for (int i = 1; i < Nr; ++i)                    /* D^ph (i, j) */
-        for (int j = 1; j < Nth; ++j) {
+        for (int j = j_lo; j < Nth; ++j) {
             double r = c->g.rn[i], t = c->g.tn[j];
             double sg = sqrtg_at(p->M, p->a, r, t);
+            int jm = j > 0 ? j - 1 : Nth - 1;
+            double dth = j > 0 ? c->g.th[j] - c->g.th[j - 1] : th_ext(c) - c->g.th[Nth - 1];
             double dHt = (H[1][i * ld + j] - H[1][(i - 1) * ld + j]) / (c->g.rh[i] - c->g.rh[i - 1]);
-            double dHr = (H[0][i * ld + j] - H[0][i * ld + j - 1]) / (c->g.th[j] - c->g.th[j - 1]);
+            double dHr = (H[0][i * ld + j] - H[0][i * ld + jm]) / dth;
             double J = 0.0;
             if (w0 != 0.0) J += w0 * Jsrc(c, 2, i, j, j0, rho0);
             if (w1 != 0.0) J += w1 * Jsrc(c, 2, i, j, j1, rho1);
             Dout[2][i * ld + j] = (Din[2][i * ld + j] + p->dt * ((dHt - dHr) / sg - 4.0 * M_PI * J)) * damp(c, r);
         }
     /* boundaries */
-    for (int i = 0; i < Nr; ++i) {
-        Dout[0][i * ld + 0] = Dout[0][i * ld + 1];
-        Dout[0][i * ld + Nth] = Dout[0][i * ld + Nth - 1];
-    }
+    if (!p->full)
+        for (int i = 0; i < Nr; ++i) {
+            Dout[0][i * ld + 0] = Dout[0][i * ld + 1];
+            Dout[0][i * ld + Nth] = Dout[0][i * ld + Nth - 1];
+        }
     for (int j = 0; j < Nth; ++j) {
         Dout[1][0 * ld + j] = Dout[1][1 * ld + j];
         Dout[1][Nr * ld + j] = Dout[1][(Nr - 1) * ld + j];
     }
-    for (int j = 1; j < Nth; ++j) {
+    for (int j = j_lo; j < Nth; ++j) {
         Dout[2][0 * ld + j] = Dout[2][1 * ld + j];
         Dout[2][Nr * ld + j] = Dout[2][(Nr - 1) * ld + j];
     }
-    for (int i = 0; i <= Nr; ++i) {
-        Dout[2][i * ld + 0] = 0.0;
-        Dout[2][i * ld + Nth] = 0.0;
-    }
+    if (!p->full)
+        for (int i = 0; i <= Nr; ++i) {
+            Dout[2][i * ld + 0] = 0.0;
+            Dout[2][i * ld + Nth] = 0.0;
+        }
+    theta_images(c, Dout);
 }
 
 /* The ten sub-steps of Sec. 2.1, split around the particle push:
@@ -490,7 +522,7 @@ void or_fdtd(const or_fdtd_params *p, int Nr, int Nth, int ld, const double *rn,
  * differences (the Yee forms of Eqs. m1-m2), times sqrtg at the point. */
 void or_div(double M, double a, int Nr, int Nth, int ld, const double *rn, const double *rh,
             const double *tn, const double *th, const double *const B[3], const double *const D[3],
-            double *divB, double *divD)
+            double *divB, double *divD, int full)
 {
     for (int i = 0; i < Nr; ++i)
         for (int j = 0; j < Nth; ++j) {
@@ -500,13 +532,17 @@ void or_div(double M, double a, int Nr, int Nth, int ld, const double *rn, const
             double ft0 = sqrtg_at(M, a, rh[i], tn[j]) * B[1][i * ld + j];
             divB[i * ld + j] = (fr1 - fr0) / (rn[i + 1] - rn[i]) + (ft1 - ft0) / (tn[j + 1] - tn[j]);
         }
+    /* full-theta domain: div D at j = 0 too, across the seam (half node
+     * Nth-1 one period below; spacing th[0] + P - th[Nth-1]) */
     for (int i = 1; i < Nr; ++i)
-        for (int j = 1; j < Nth; ++j) {
+        for (int j = full ? 0 : 1; j < Nth; ++j) {
+            int jm = j > 0 ? j - 1 : Nth - 1;
+            double dth = j > 0 ? th[j] - th[j - 1] : (th[0] + (tn[Nth] - tn[0])) - th[Nth - 1];
             double fr1 = sqrtg_at(M, a, rh[i], tn[j]) * D[0][i * ld + j];
             double fr0 = sqrtg_at(M, a, rh[i - 1], tn[j]) * D[0][(i - 1) * ld + j];
             double ft1 = sqrtg_at(M, a, rn[i], th[j]) * D[1][i * ld + j];
-            double ft0 = sqrtg_at(M, a, rn[i], th[j - 1]) * D[1][i * ld + j - 1];
-            divD[i * ld + j] = (fr1 - fr0) / (rh[i] - rh[i - 1]) + (ft1 - ft0) / (th[j] - th[j - 1]);
+            double ft0 = sqrtg_at(M, a, rn[i], th[jm]) * D[1][i * ld + jm];
+            divD[i * ld + j] = (fr1 - fr0) / (rh[i] - rh[i - 1]) + (ft1 - ft0) / dth;
         }
 }
 

@@ -13,7 +13,8 @@ _I64 = C.c_int64
 
 class FdtdParams(C.Structure):
     _fields_ = [("M", C.c_double), ("a", C.c_double), ("dt", C.c_double), ("chi0", C.c_double),
-                ("lam", C.c_double), ("r_abs", C.c_double), ("r_max", C.c_double), ("conserving", C.c_int)]
+                ("lam", C.c_double), ("r_abs", C.c_double), ("r_max", C.c_double), ("conserving", C.c_int),
+                ("full", C.c_int)]
 
 
 def _declare(L):
@@ -23,7 +24,7 @@ def _declare(L):
     L.or_dual_volumes.argtypes = [C.c_double, C.c_double] + g + [_D, _D, _D]
     P3 = _D * 3
     L.or_fdtd.argtypes = [C.POINTER(FdtdParams)] + g + [C.c_int, P3, P3, P3, P3, P3, _D, P3, _D, P3, P3, P3, P3]
-    L.or_div.argtypes = [C.c_double, C.c_double] + g + [P3, P3, _D, _D]
+    L.or_div.argtypes = [C.c_double, C.c_double] + g + [P3, P3, _D, _D, C.c_int]
     L.or_split_monopole_on_grid.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double] + g + [_D * 6]
     L.or_bz_power.argtypes = [C.c_int, C.c_int, C.c_int, _D, P3, P3, C.c_int]
     L.or_bz_power.restype = C.c_double
@@ -88,9 +89,11 @@ def fdtd(p: FdtdParams, s: FdtdState, stage: int):
 
 
 def div(M, a, g, B, D):
-    """sqrtg-weighted Yee divergences: div B at cell centres, div D at nodes."""
+    """sqrtg-weighted Yee divergences: div B at cell centres, div D at nodes
+    (at j = 0 too, across the seam, on a full-theta grid)."""
     dB, dD = np.zeros(g.size), np.zeros(g.size)
-    lib().or_div(M, a, *_g(g), _p3([f64(x) for x in B]), _p3([f64(x) for x in D]), ptr(dB), ptr(dD))
+    lib().or_div(M, a, *_g(g), _p3([f64(x) for x in B]), _p3([f64(x) for x in D]), ptr(dB), ptr(dD),
+                 int(getattr(g, "full_theta", False)))
     return dB, dD
 
 

@@ -617,3 +617,125 @@ def test_conserving_pic_loop_keeps_gauss_residual():
         drift = max(drift, np.abs(R - R0).max())
     scale = np.abs(4 * math.pi * sg.reshape(g.Nr + 1, g.ld)[sel] * st.rho0.reshape(g.Nr + 1, g.ld)[sel]).max()
     assert scale > 0 and drift <= 1e-11 * scale, (drift, scale)
+
+
+# ---------------------------------------------------------------------------
+# Full-theta domain (Sec. 2.5: periodic in th), FDTD
+# ---------------------------------------------------------------------------
+def _images(g, arrs):
+    for x in arrs:
+        X = x.reshape(g.Nr + 1, g.ld)
+        X[:, g.Nth] = X[:, 0]
+
+
+def _rand_fields_full(g, seed):
+    s = _rand_fields(g, seed)
+    for arrs in (s.B0, s.B1, s.D0, s.D1):
+        _images(g, arrs)
+    return s
+
+
+def _uneven_full_theta_grid(Nr, Nth, r_min, r_max):
+    """A full-theta grid whose th spacing varies (nodes displaced by up to
+    15 % of a cell, half nodes between them, the period kept): the spacing
+    across the seam then differs from its neighbours'."""
+    g = I.full_theta_grid(Nr, Nth, r_min, r_max)
+    dth = 2.0 * math.pi / Nth
+    u = np.arange(Nth + 1) / Nth
+    tn = g.tn + 0.15 * dth * np.sin(2.0 * math.pi * u) * np.cos(6.0 * math.pi * u)
+    th = 0.5 * (tn[:-1] + tn[1:]) + 0.1 * dth * np.sin(4.0 * math.pi * (u[:-1] + 0.5 / Nth))
+    return I.Grid(g.Nr, g.Nth, g.rn, g.rh, tn, th, g.ld, True)
+
+
+@pytest.mark.parametrize("uneven", [False, True])
+@pytest.mark.parametrize("a", [0.0, 0.9])
+def test_full_theta_fdtd_preserves_divergences_across_the_seam(a, uneven):
+    """Sec. 2.1 / 2.5: on a full-theta grid the curl updates leave div B
+    unchanged to round-off in every cell, the one across the seam (j = Nth-1,
+    whose upper face is the image column) included, and div D in vacuum at
+    every node, j = 0 (whose lower face is half node Nth-1, one period below)
+    included; column Nth stays the bitwise image of column 0.  A wrong wrap
+    index at the seam breaks these on any grid, a wrong spacing across it on
+    the uneven one."""
+    g = (_uneven_full_theta_grid if uneven else I.full_theta_grid)(24, 20, 1.9, 30.0)
+    s = _rand_fields_full(g, 5)
+    p = P.FdtdParams(1.0, a, 0.002, 1e4, 5.0, 0.9 * g.rn[-1], g.rn[-1], 0, 1)
+    dB0, dD0 = P.div(1.0, a, g, s.B1, s.D1)
+    for _ in range(3):
+        P.fdtd(p, s, 1)
+        P.fdtd(p, s, 2)
+        s.swap()
+    dB1, dD1 = P.div(1.0, a, g, s.B1, s.D1)
+    for arrs in (s.B0, s.B1, s.D0, s.D1):
+        for x in arrs:
+            X = x.reshape(g.Nr + 1, g.ld)
+            assert np.array_equal(X[:, g.Nth], X[:, 0])
+    rm = g.rh < 0.9 * g.rn[-1] * 0.999
+    ii = np.arange(g.Nr)[rm[:g.Nr]]
+    ii = ii[ii < g.Nr - 2]
+    sel = np.zeros((g.Nr + 1, g.ld), bool)
+    sel[ii, :g.Nth] = True
+    scale = np.abs(dB0).max()
+    dB = np.abs((dB1 - dB0).reshape(g.Nr + 1, g.ld))
+    assert dB[sel].max() < 1e-12 * scale
+    assert dB[ii, g.Nth - 1].max() < 1e-12 * scale
+    seld = np.zeros((g.Nr + 1, g.ld), bool)
+    seld[2:ii.max(), :g.Nth] = True
+    scale = np.abs(dD0).max()
+    dD = np.abs((dD1 - dD0).reshape(g.Nr + 1, g.ld))
+    assert dD[seld].max() < 1e-12 * scale
+    assert dD[2:ii.max(), 0].max() < 1e-12 * scale
+    # the seam column carries a divergence of its own (small: sqrt(gamma) ~ sin(dth / 4) there)
+    assert np.abs(dD0.reshape(g.Nr + 1, g.ld)[2:ii.max(), 0]).max() > 1e-3 * scale
+
+
+def test_full_theta_static_wald_stays_static_through_the_axes():
+    """The a = 0 Wald field continued to th in (pi, 2 pi) with the signed
+    sin th (reading 25) is a static vacuum solution on the full-theta grid:
+    the leapfrog keeps it static up to the grid's truncation error, which
+    falls at second order, alike in both half planes and in the bands
+    around both axes (no axis boundary rows here); a wrong sign of
+    sqrt(gamma) beyond th = pi would not be static there."""
+    errs = {"north": [], "south": [], "axes": []}
+    for N in (32, 64):
+        g = I.full_theta_grid(N, 2 * N, 2.2, 12.0)
+        F = O.wald_on_grid(0.0, 1.0, g)
+        s = P.FdtdState(g)
+        for k in range(3):
+            s.D0[k][:] = F[k]; s.D1[k][:] = F[k]
+            s.B0[k][:] = F[3 + k]; s.B1[k][:] = F[3 + k]
+        p = P.FdtdParams(1.0, 0.0, 0.2 * (g.rn[1] - g.rn[0]), 0.0, 5.0, 1e9, 2e9, 0, 1)
+        for _ in range(int(round(0.5 / p.dt))):
+            P.fdtd(p, s, 1); P.fdtd(p, s, 2); s.swap()
+        ri = (g.rn >= 4.0) & (g.rn <= 8.0)
+        Br = s.B1[0].reshape(g.Nr + 1, g.ld)[ri][:, :g.Nth]
+        Br0 = F[3].reshape(g.Nr + 1, g.ld)[ri][:, :g.Nth]
+        for name, tj in (("north", (g.th >= 0.5) & (g.th <= math.pi - 0.5)),
+                         ("south", (g.th >= math.pi + 0.5) & (g.th <= 2 * math.pi - 0.5)),
+                         ("axes", np.abs(np.sin(g.th)) < 0.3)):
+            errs[name].append(np.abs(Br[:, tj] - Br0[:, tj]).max() / np.abs(Br0).max())
+    for name, e in errs.items():
+        assert e[0] < 1e-4 and e[1] < 0.35 * e[0], (name, e)
+
+
+def test_full_theta_fdtd_equals_the_half_theta_update_away_from_the_seam():
+    """The full-theta mode changes the leapfrog only at the seam: on the same
+    node tables, one full step (both stages) of the full and the half mode
+    from the same random fields agree bit for bit on every column at least
+    six cells from the seam and from the half mode's boundary rows."""
+    a = 0.9
+    g = I.full_theta_grid(16, 40, 1.9, 30.0)
+    outs = []
+    for full in (1, 0):
+        s = _rand_fields_full(g, 8)
+        rng = np.random.default_rng(9)
+        for x in s.j0 + s.j1 + [s.rho0, s.rho1]:
+            x[:] = rng.normal(size=g.size)
+        p = P.FdtdParams(1.0, a, 0.002, 0.0, 5.0, g.rn[-1], g.rn[-1], 0, full)
+        P.fdtd(p, s, 1)
+        P.fdtd(p, s, 2)
+        outs.append([x.reshape(g.Nr + 1, g.ld).copy() for x in s.B0 + s.D0 + s.Bh + s.Dw])
+    for X, Y in zip(*outs):
+        assert np.array_equal(X[:, 6:g.Nth - 6], Y[:, 6:g.Nth - 6])
+    # and they do differ at the seam
+    assert any(not np.array_equal(X[:, :2], Y[:, :2]) for X, Y in zip(*outs))
