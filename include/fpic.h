@@ -200,9 +200,12 @@ int fpic_set_grid(fpic_ctx *ctx, int Nr, int Nth, const double *rn, const double
  * the full-theta domain: the pushes (fpic_push, fpic_push_host,
  * fpic_push_batched, the corrector form of the learned push),
  * fpic_cell_index, fpic_sort, fpic_init_wald, fpic_hamiltonian,
- * fpic_init_particles; the grid-side solvers (deposits, FDTD, cleaning,
- * injection, BZ power, split-monopole initial field) and the skip form's
- * features return FPIC_EINVAL.  Setting the mode drops cached slopes and
+ * fpic_init_particles, and fpic_fdtd_step with periodic field boundaries
+ * (the th differences at the seam wrap around, no axis rows; it keeps
+ * column Nth of what it writes equal to column 0, as the paper's vacuum
+ * Wald run in the full domain needs); the other grid-side solvers
+ * (deposits, cleaning, injection, BZ power, split-monopole initial field)
+ * and the skip form's features return FPIC_EINVAL.  Setting the mode drops cached slopes and
  * coefficients.  Errors: FPIC_EINVAL (no grid, unknown mode, a full-theta
  * grid whose period is not 2 pi to 1e-12). */
 enum { FPIC_THETA_HALF = 0, FPIC_THETA_FULL = 1 };
@@ -463,8 +466,12 @@ int fpic_deposit(fpic_ctx *ctx, fpic_particles *p, double *rho, double *jr, doub
  *            H^{n+3/2} -> D^{n+2} (into Dw, with <J>^{n+3/2}) -> H^{n+2} ->
  *            D^{n+5/2} (into D0, with J^{n+2}),
  * with J = alpha j - rho beta.  After stage 2 the caller swaps B0/B1, D0/D1
- * and (j0, rho0)/(j1, rho1).  Errors: FPIC_EINVAL (no grid, stage not 1 or
- * 2, NULL array, dt not finite). */
+ * and (j0, rho0)/(j1, rho1).  Boundaries: in the half-theta domain zero
+ * gradient where a stencil is one-sided and D^ph = 0 on the axis rows; in
+ * the full-theta domain (fpic_set_theta_mode) periodic in th, with column Nth
+ * of every array it writes set to column 0 (the caller's input arrays must
+ * hold that image too).  Errors: FPIC_EINVAL (no grid, stage not 1 or 2,
+ * NULL array, dt not finite). */
 int fpic_fdtd_step(fpic_ctx *ctx, fpic_fields *f, const fpic_fdtd_params *prm, int stage, void *stream);
 
 /* Charge-conserving deposit of one step's moves (an extension: the paper's

@@ -839,24 +839,34 @@ __global__ void k_avg3(F3 in, O3 out, size_t sz)
 // Eq. (Ei): E_r (i+1/2,j) = alpha (g_rr D^r + g_rp <D^ph>);
 // E_th (i,j+1/2) = alpha g_tt D^th - sqrtg beta <B^ph>;
 // E_ph (i,j) = alpha (g_rp <D^r> + g_pp D^ph) + sqrtg beta <B^th>.
+// Full-theta domain (Sec. 2.5, periodic in th): columns 0..Nth-1 are the
+// distinct points; the thread of column 0 also stores its values in column
+// Nth, the image the seam's stencils and the push's gather read.
+__device__ __forceinline__ void put(double* F, size_t o, int j, const FK& k, double v)
+{
+    F[o] = v;
+    if (k.G.full && j == 0) F[o + k.Nth] = v;
+}
+
 __global__ void k_make_E(FK k, F3 D, F3 B, O3 E)
 {
     const int i = blockIdx.y;
-    for (int j = threadIdx.x; j <= k.Nth; j += blockDim.x) {
+    const int jend = k.G.full ? k.Nth - 1 : k.Nth;
+    for (int j = threadIdx.x; j <= jend; j += blockDim.x) {
         const size_t o = (size_t)i * k.ld + j;
         if (i < k.Nr) {
             const double Dp = avg_r(k, D.a[2], 0, 0, i, j);
-            E.p[0][o] = k.T.at(1, 0, i, j) * fma(k.T.at(1, 3, i, j), D.a[0][o], k.T.at(1, 4, i, j) * Dp);
+            put(E.p[0], o, j, k, k.T.at(1, 0, i, j) * fma(k.T.at(1, 3, i, j), D.a[0][o], k.T.at(1, 4, i, j) * Dp));
         }
         if (j < k.Nth) {
             const double Bp = avg_r(k, B.a[2], 1, 1, i, j);
-            E.p[1][o] = fma(k.T.at(2, 0, i, j) * k.T.at(2, 5, i, j), D.a[1][o],
-                            -k.T.at(2, 2, i, j) * k.T.at(2, 1, i, j) * Bp);
+            put(E.p[1], o, j, k, fma(k.T.at(2, 0, i, j) * k.T.at(2, 5, i, j), D.a[1][o],
+                                     -k.T.at(2, 2, i, j) * k.T.at(2, 1, i, j) * Bp));
         }
         const double Dr = avg_r(k, D.a[0], 1, 0, i, j);
         const double Bt = avg_r(k, B.a[1], 1, 0, i, j);
-        E.p[2][o] = fma(k.T.at(0, 0, i, j), fma(k.T.at(0, 4, i, j), Dr, k.T.at(0, 6, i, j) * D.a[2][o]),
-                        k.T.at(0, 2, i, j) * k.T.at(0, 1, i, j) * Bt);
+        put(E.p[2], o, j, k, fma(k.T.at(0, 0, i, j), fma(k.T.at(0, 4, i, j), Dr, k.T.at(0, 6, i, j) * D.a[2][o]),
+                                 k.T.at(0, 2, i, j) * k.T.at(0, 1, i, j) * Bt));
     }
 }
 
@@ -866,45 +876,49 @@ __global__ void k_make_E(FK k, F3 D, F3 B, O3 E)
 __global__ void k_make_H(FK k, F3 D, F3 B, O3 H)
 {
     const int i = blockIdx.y;
-    for (int j = threadIdx.x; j <= k.Nth; j += blockDim.x) {
+    const int jend = k.G.full ? k.Nth - 1 : k.Nth;
+    for (int j = threadIdx.x; j <= jend; j += blockDim.x) {
         const size_t o = (size_t)i * k.ld + j;
         if (j < k.Nth) {
             const double Bp = avg_r(k, B.a[2], 1, 1, i, j);
-            H.p[0][o] = k.T.at(2, 0, i, j) * fma(k.T.at(2, 3, i, j), B.a[0][o], k.T.at(2, 4, i, j) * Bp);
+            put(H.p[0], o, j, k, k.T.at(2, 0, i, j) * fma(k.T.at(2, 3, i, j), B.a[0][o], k.T.at(2, 4, i, j) * Bp));
         }
         if (i < k.Nr) {
             const double Dp = avg_r(k, D.a[2], 0, 0, i, j);
-            H.p[1][o] = fma(k.T.at(1, 0, i, j) * k.T.at(1, 5, i, j), B.a[1][o],
-                            k.T.at(1, 2, i, j) * k.T.at(1, 1, i, j) * Dp);
+            put(H.p[1], o, j, k, fma(k.T.at(1, 0, i, j) * k.T.at(1, 5, i, j), B.a[1][o],
+                                     k.T.at(1, 2, i, j) * k.T.at(1, 1, i, j) * Dp));
         }
         if (i < k.Nr && j < k.Nth) {
             const double Br = avg_r(k, B.a[0], 0, 1, i, j);
             const double Dt = avg_r(k, D.a[1], 0, 1, i, j);
-            H.p[2][o] = fma(k.T.at(3, 0, i, j), fma(k.T.at(3, 4, i, j), Br, k.T.at(3, 6, i, j) * B.a[2][o]),
-                            -k.T.at(3, 2, i, j) * k.T.at(3, 1, i, j) * Dt);
+            put(H.p[2], o, j, k, fma(k.T.at(3, 0, i, j), fma(k.T.at(3, 4, i, j), Br, k.T.at(3, 6, i, j) * B.a[2][o]),
+                                     -k.T.at(3, 2, i, j) * k.T.at(3, 1, i, j) * Dt));
         }
     }
 }
 
 // Eq. (m4) + (abs0): B_out = (B_in - dt curl E / sqrtg) exp(-chi dt).
+// The forward th differences at j = Nth-1 read column Nth: the image of
+// column 0 in the full-theta domain.
 __global__ void k_update_B(FK k, F3 Bin, O3 E, O3 Bout)
 {
     const int i = blockIdx.y;
     const GridDev& G = k.G;
-    for (int j = threadIdx.x; j <= k.Nth; j += blockDim.x) {
+    const int jend = G.full ? k.Nth - 1 : k.Nth;
+    for (int j = threadIdx.x; j <= jend; j += blockDim.x) {
         const size_t o = (size_t)i * k.ld + j;
         if (j < k.Nth) {   // B^r (i, j+1/2)
             const double curl = (E.p[2][o + 1] - E.p[2][o]) / (G.tn[j + 1] - G.tn[j]);
-            Bout.p[0][o] = (Bin.v(0, o) - k.dt * curl / k.T.at(2, 2, i, j)) * damp(k, G.rn[i]);
+            put(Bout.p[0], o, j, k, (Bin.v(0, o) - k.dt * curl / k.T.at(2, 2, i, j)) * damp(k, G.rn[i]));
         }
         if (i < k.Nr) {    // B^th (i+1/2, j)
             const double curl = -(E.p[2][o + k.ld] - E.p[2][o]) / (G.rn[i + 1] - G.rn[i]);
-            Bout.p[1][o] = (Bin.v(1, o) - k.dt * curl / k.T.at(1, 2, i, j)) * damp(k, G.rh[i]);
+            put(Bout.p[1], o, j, k, (Bin.v(1, o) - k.dt * curl / k.T.at(1, 2, i, j)) * damp(k, G.rh[i]));
         }
         if (i < k.Nr && j < k.Nth) {   // B^ph (i+1/2, j+1/2)
             const double dEt = (E.p[1][o + k.ld] - E.p[1][o]) / (G.rn[i + 1] - G.rn[i]);
             const double dEr = (E.p[0][o + 1] - E.p[0][o]) / (G.tn[j + 1] - G.tn[j]);
-            Bout.p[2][o] = (Bin.v(2, o) - k.dt * (dEt - dEr) / k.T.at(3, 2, i, j)) * damp(k, G.rh[i]);
+            put(Bout.p[2], o, j, k, (Bin.v(2, o) - k.dt * (dEt - dEr) / k.T.at(3, 2, i, j)) * damp(k, G.rh[i]));
         }
     }
 }
@@ -929,50 +943,59 @@ __device__ __forceinline__ double jsrc(const FK& k, const Src& S, int comp, int 
 }
 
 // Eq. (m3) + (abs1): D_out = (D_in + dt [curl H / sqrtg - 4 pi J]) exp(-chi dt),
-// interior points only (boundaries: k_bc_D).
+// interior points only (boundaries: k_bc_D).  Full-theta domain: D^r and D^ph
+// at j = 0 too, their backward th difference across the seam (half node
+// Nth-1, one period below: spacing th[Nth] - th[Nth-1], th[Nth] = th[0] + P).
 __global__ void k_update_D(FK k, F3 Din, O3 H, Src S0, Src S1, O3 Dout)
 {
     const int i = blockIdx.y;
     const GridDev& G = k.G;
     const double fpi = 4.0 * M_PI;
-    for (int j = threadIdx.x; j <= k.Nth; j += blockDim.x) {
+    const int jlo = G.full ? 0 : 1;
+    for (int j = threadIdx.x; j < k.Nth; j += blockDim.x) {
         const size_t o = (size_t)i * k.ld + j;
-        if (i < k.Nr && j >= 1 && j < k.Nth) {    // D^r (i+1/2, j)
-            const double curl = (H.p[2][o] - H.p[2][o - 1]) / (G.th[j] - G.th[j - 1]);
+        const size_t om = j > 0 ? o - 1 : o + (k.Nth - 1);
+        const double dth = j > 0 ? G.th[j] - G.th[j - 1] : G.th[k.Nth] - G.th[k.Nth - 1];
+        if (i < k.Nr && j >= jlo) {    // D^r (i+1/2, j)
+            const double curl = (H.p[2][o] - H.p[2][om]) / dth;
             const double J = jsrc(k, S0, 0, i, j) + jsrc(k, S1, 0, i, j);
-            Dout.p[0][o] = (Din.v(0, o) + k.dt * (curl / k.T.at(1, 2, i, j) - fpi * J)) * damp(k, G.rh[i]);
+            put(Dout.p[0], o, j, k, (Din.v(0, o) + k.dt * (curl / k.T.at(1, 2, i, j) - fpi * J)) * damp(k, G.rh[i]));
         }
-        if (i >= 1 && i < k.Nr && j < k.Nth) {    // D^th (i, j+1/2)
+        if (i >= 1 && i < k.Nr) {    // D^th (i, j+1/2)
             const double curl = -(H.p[2][o] - H.p[2][o - k.ld]) / (G.rh[i] - G.rh[i - 1]);
             const double J = jsrc(k, S0, 1, i, j) + jsrc(k, S1, 1, i, j);
-            Dout.p[1][o] = (Din.v(1, o) + k.dt * (curl / k.T.at(2, 2, i, j) - fpi * J)) * damp(k, G.rn[i]);
+            put(Dout.p[1], o, j, k, (Din.v(1, o) + k.dt * (curl / k.T.at(2, 2, i, j) - fpi * J)) * damp(k, G.rn[i]));
         }
-        if (i >= 1 && i < k.Nr && j >= 1 && j < k.Nth) {   // D^ph (i, j)
+        if (i >= 1 && i < k.Nr && j >= jlo) {   // D^ph (i, j)
             const double dHt = (H.p[1][o] - H.p[1][o - k.ld]) / (G.rh[i] - G.rh[i - 1]);
-            const double dHr = (H.p[0][o] - H.p[0][o - 1]) / (G.th[j] - G.th[j - 1]);
+            const double dHr = (H.p[0][o] - H.p[0][om]) / dth;
             const double J = jsrc(k, S0, 2, i, j) + jsrc(k, S1, 2, i, j);
-            Dout.p[2][o] = (Din.v(2, o) + k.dt * ((dHt - dHr) / k.T.at(0, 2, i, j) - fpi * J)) * damp(k, G.rn[i]);
+            put(Dout.p[2], o, j, k,
+                (Din.v(2, o) + k.dt * ((dHt - dHr) / k.T.at(0, 2, i, j) - fpi * J)) * damp(k, G.rn[i]));
         }
     }
 }
 
 // Sec. 2.5 (reading): zero gradient where a stencil is one-sided, D^ph = 0 on
-// the axis rows.
+// the axis rows (k_axis_D).  Full-theta domain: no th boundary; the radial
+// boundary rows copy every column, the image column Nth included.
 __global__ void k_bc_D(FK k, O3 D)
 {
     const int i = blockIdx.y;
     const int Nr = k.Nr, Nth = k.Nth, ld = k.ld;
-    if (threadIdx.x == 0) {
+    const bool full = k.G.full;
+    if (threadIdx.x == 0 && !full) {
         if (i < Nr) {
             D.p[0][(size_t)i * ld + 0] = D.p[0][(size_t)i * ld + 1];
             D.p[0][(size_t)i * ld + Nth] = D.p[0][(size_t)i * ld + Nth - 1];
         }
     }
+    const int jt = full ? Nth : Nth - 1, jp0 = full ? 0 : 1, jp1 = full ? Nth : Nth - 1;
     for (int j = threadIdx.x; j <= Nth; j += blockDim.x) {
-        if (i == 0 && j < Nth) D.p[1][j] = D.p[1][(size_t)ld + j];
-        if (i == Nr && j < Nth) D.p[1][(size_t)Nr * ld + j] = D.p[1][(size_t)(Nr - 1) * ld + j];
-        if (i == 0 && j >= 1 && j < Nth) D.p[2][j] = D.p[2][(size_t)ld + j];
-        if (i == Nr && j >= 1 && j < Nth) D.p[2][(size_t)Nr * ld + j] = D.p[2][(size_t)(Nr - 1) * ld + j];
+        if (i == 0 && j <= jt) D.p[1][j] = D.p[1][(size_t)ld + j];
+        if (i == Nr && j <= jt) D.p[1][(size_t)Nr * ld + j] = D.p[1][(size_t)(Nr - 1) * ld + j];
+        if (i == 0 && j >= jp0 && j <= jp1) D.p[2][j] = D.p[2][(size_t)ld + j];
+        if (i == Nr && j >= jp0 && j <= jp1) D.p[2][(size_t)Nr * ld + j] = D.p[2][(size_t)(Nr - 1) * ld + j];
     }
 }
 
@@ -1655,7 +1678,6 @@ extern "C" int fpic_div_clean(fpic_ctx* c, double* const D[3], const double* rho
 
 extern "C" int fpic_fdtd_step(fpic_ctx* c, fpic_fields* f, const fpic_fdtd_params* prm, int stage, void* stream)
 {
-    if (c && c->G.full) return set_error(FPIC_EINVAL, "fpic_fdtd_step: not built for the full-theta domain");
     if (!c || !f || !prm) return set_error(FPIC_EINVAL, "fpic_fdtd_step: NULL argument");
     if (!c->has_grid) return set_error(FPIC_EINVAL, "fpic_fdtd_step: no grid set");
     if (stage != 1 && stage != 2) return set_error(FPIC_EINVAL, "fpic_fdtd_step: stage must be 1 or 2");
@@ -1699,7 +1721,7 @@ extern "C" int fpic_fdtd_step(fpic_ctx* c, fpic_fields* f, const fpic_fdtd_param
         Src S0{{f->j0[0], f->j0[1], f->j0[2]}, f->rho0, 0.5}, S1{{f->j1[0], f->j1[1], f->j1[2]}, f->rho1, 0.5};
         k_update_D<<<g2, TB, 0, s>>>(k, f3(f->D0, f->D1), o3(f->H), S0, S1, o3(f->Dw));
         k_bc_D<<<g2, TB, 0, s>>>(k, o3(f->Dw));
-        k_axis_D<<<(c->Nr + 1 + 255) / 256, 256, 0, s>>>(k, o3(f->Dw));
+        if (!c->G.full) k_axis_D<<<(c->Nr + 1 + 255) / 256, 256, 0, s>>>(k, o3(f->Dw));
         // [9] H^{n+2} = alpha B^{n+2} - beta x D^{n+2}
         k_make_H<<<g2, TB, 0, s>>>(k, f3(f->Dw, nullptr), f3(f->B0, nullptr), o3(f->H));
         // [10] D^{n+5/2} = D^{n+3/2} + dt [curl H - 4 pi J^{n+2}]  (into D0)
@@ -1707,7 +1729,7 @@ extern "C" int fpic_fdtd_step(fpic_ctx* c, fpic_fields* f, const fpic_fdtd_param
         S1.w = 1.0;
         k_update_D<<<g2, TB, 0, s>>>(k, f3(f->D1, nullptr), o3(f->H), S0, S1, o3(f->D0));
         k_bc_D<<<g2, TB, 0, s>>>(k, o3(f->D0));
-        k_axis_D<<<(c->Nr + 1 + 255) / 256, 256, 0, s>>>(k, o3(f->D0));
+        if (!c->G.full) k_axis_D<<<(c->Nr + 1 + 255) / 256, 256, 0, s>>>(k, o3(f->D0));
     }
     FPIC_CUDA(cudaGetLastError());
     return FPIC_OK;

@@ -174,6 +174,58 @@ def test_fdtd_step_matches_oracle(F, chi0):
                 assert np.abs(got - exp).max() <= 1e-12 * sc, (stage, nm, k, np.abs(got - exp).max() / sc)
 
 
+@pytest.mark.parametrize("uneven", [False, True])
+def test_full_theta_fdtd_step_matches_oracle(F, uneven):
+    """The leapfrog in the full-theta domain (fpic_set_theta_mode FULL,
+    periodic in th, Sec. 2.5) on a 40 x 64 grid (and on the oracle pins'
+    uneven th table) with random fields and sources, two steps: every
+    array within 1e-12 of the oracle's full-theta update relative to its
+    magnitude, every column Nth the bitwise image of column 0, and the
+    seam columns themselves within the bound."""
+    import test_oracle_pic as TO
+    a = 0.9
+    g = (TO._uneven_full_theta_grid if uneven else I.full_theta_grid)(40, 64, 1.5, 30.0)
+    ctx = F.fpic_init_metric(1.0, a)
+    F.fpic_set_grid(ctx, g)
+    st = P.FdtdState(g)
+    fl = F.Fields(g.size)
+    rng = np.random.default_rng(19)
+    for nm in ("B0", "B1", "D0", "D1", "j0", "j1"):
+        for k in range(3):
+            x = rng.normal(size=(g.Nr + 1, g.ld))
+            x[:, g.Nth] = x[:, 0]
+            x = x.ravel()
+            getattr(st, nm)[k][:] = x
+            getattr(fl, nm)[k].copy_(dev(x))
+    for nm in ("rho0", "rho1"):
+        x = rng.normal(size=(g.Nr + 1, g.ld))
+        x[:, g.Nth] = x[:, 0]
+        x = x.ravel()
+        setattr(st, nm, x)
+        getattr(fl, nm).copy_(dev(x))
+    dt = 0.002
+    po = P.FdtdParams(1.0, a, dt, 1e4, 5.0, 0.9 * g.rn[-1], g.rn[-1], 0, 1)
+    pg = F.fdtd_params(dt, 1e4, 5.0, 0.9 * g.rn[-1], g.rn[-1])
+    for step in range(2):
+        for stage in (1, 2):
+            P.fdtd(po, st, stage)
+            F.fpic_fdtd_step(ctx, fl, pg, stage)
+            for nm in ("B0", "B1", "D0", "D1", "Bh", "Dw", "E", "H"):
+                if stage == 1 and nm == "Dw":
+                    continue
+                for k in range(3):
+                    ro, _ = STAG[FAMILY[nm]][k]
+                    exp = getattr(st, nm)[k].reshape(g.Nr + 1, g.ld)[: g.Nr + 1 - ro]
+                    got = getattr(fl, nm)[k].cpu().numpy().reshape(g.Nr + 1, g.ld)[: g.Nr + 1 - ro]
+                    sc = np.abs(exp).max() + 1e-300
+                    err = np.abs(got - exp)
+                    assert err.max() <= 1e-12 * sc, (step, stage, nm, k, err.max() / sc)
+                    assert err[:, [0, g.Nth - 1]].max() <= 1e-12 * sc
+                    assert np.array_equal(got[:, g.Nth], got[:, 0]), (step, stage, nm, k)
+        st.swap()
+        fl.swap()
+
+
 def test_full_pic_step_matches_oracle(F):
     """One full GRPIC step in the paper's order (Sec. 2.1): FDTD stage 1,
     RK4 push with D^{n+3/2}, B^{n+3/2}, deposit at n+2, FDTD stage 2 --

@@ -885,8 +885,8 @@ def test_full_theta_push_matches_oracle(F, scheme):
 
 
 def test_full_theta_rejects_the_grid_side_solvers(F):
-    """In the full-theta domain the deposits, FDTD, cleaning and injection
-    are not built: they refuse with FPIC_EINVAL instead of running."""
+    """In the full-theta domain the deposits, cleaning and injection are not
+    built: they refuse with FPIC_EINVAL instead of running."""
     a = 0.9
     g = I.full_theta_grid(16, 32, 0.9 * I.horizon(1.0, a), 40.0)
     ctx = _mk(F, a, g)
@@ -894,8 +894,10 @@ def test_full_theta_rejects_the_grid_side_solvers(F):
     p = make_particles(z, np.ones(10))
     with pytest.raises(F.FpicError, match="full-theta"):
         F.fpic_deposit(ctx, p, g.size)
+    with pytest.raises(F.FpicError, match="full-theta"):
+        F.fpic_deposit_conserving(ctx, p, make_particles(z, np.ones(10)), 1e-3)
     fl = F.Fields(g.size)
     with pytest.raises(F.FpicError, match="full-theta"):
-        F.fpic_fdtd_step(ctx, fl, F.fdtd_params(1e-3), 1)
+        F.fpic_div_clean(ctx, fl.D1, fl.rho1, 5)
     F.fpic_set_theta_mode(ctx, F.FPIC_THETA_HALF)
     F.fpic_deposit(ctx, p, g.size)          # the half-theta reading of the same tables
