@@ -88,7 +88,7 @@ def parse():
                     help="levels of substeps for unconverged or inaccurate IMR steps (0: off)")
     ap.add_argument("--substep-tol", type=float, default=SUBSTEP_TOL,
                     help="|dH|/D0 of an IMR step above which it is redone in substeps (0: unconverged only)")
-    ap.add_argument("--workload", default="push", choices=["push", "pic", "neutral", "batched", "clean", "inject", "adaptive",
+    ap.add_argument("--workload", default="push", choices=["push", "pic", "neutral", "batched", "clean", "inject", "adaptive", "vacuum_wald",
                                                           "charged_dg", "learned_analysis"])
     ap.add_argument("--clean-sweeps", type=int, default=500, help="Jacobi sweeps of --workload clean")
     ap.add_argument("--conserving", action="store_true", help="--workload pic with the charge-conserving deposit")
@@ -1143,6 +1143,64 @@ def run_div_clean(device, grid_n=1024, n_iter=500, reps=3):
             "sweep_achieved_gbs": bytes_sweep * n_iter / t / 1e9 if n_iter else None}
 
 
+# Per full FDTD step (stages 1 and 2, no particles), the grid arrays each
+# kernel reads or writes once, counted per component: the level averages
+# (9), E twice (2 x 24 with the metric tables), B^{n+3/2} and B^{n+2} (15,
+# 12), H twice (2 x 24), D^{n+2} and D^{n+5/2} with the sources (26, 19).
+FDTD_ARRAY_PASSES = 9 + 24 + 15 + 24 + 12 + 24 + 26 + 24 + 19
+
+
+def run_vacuum_wald(device, Nr=4196, Nth=1024, steps=20, warmup=3):
+    """The geometry of the paper's vacuum Wald run (Sec. 3.3): the full-theta
+    domain 0 <= th <= 2 pi (periodic, Sec. 2.5) on Nr x Nth cells, r in
+    [0.99 r_h, 20 M], a = 0.999, absorbing layer from 0.9 r_max; the exact
+    Kerr Wald field of App. B.1 as the start (the paper starts from the
+    Schwarzschild one), FDTD only.  Reports the leapfrog's time per step,
+    cells per second, the array traffic it implies against the measured
+    HBM copy bandwidth, and how far B^r has moved from the static solution."""
+    import torch
+    from paper_2602_07452_gb300 import fpic as F
+    from paper_2602_07452_gb300 import inputs as I
+    a = 0.999
+    g = I.full_theta_grid(Nr, Nth, 0.99 * I.horizon(1.0, a), 20.0)
+    ctx = F.fpic_init_metric(1.0, a)
+    F.fpic_set_grid(ctx, g)               # full-theta grid: the binding sets FPIC_THETA_FULL
+    fl = F.Fields(g.size, device)
+    wald = [torch.zeros(g.size, dtype=torch.float64, device=device) for _ in range(6)]
+    F.fpic_init_wald(ctx, wald, 1.0)
+    for k in range(3):
+        for nm, src in (("D0", wald[k]), ("D1", wald[k]), ("B0", wald[3 + k]), ("B1", wald[3 + k])):
+            getattr(fl, nm)[k].copy_(src)
+    r_max = float(g.rn[-1])
+    dt = 0.25 * float(g.rn[1] - g.rn[0])
+    prm = F.fdtd_params(dt, 1e4, 5.0, 0.9 * r_max, r_max)
+    s = torch.cuda.current_stream(device)
+
+    def step():
+        F.fpic_fdtd_step(ctx, fl, prm, 1)
+        F.fpic_fdtd_step(ctx, fl, prm, 2)
+        fl.swap()
+    for _ in range(warmup):
+        step()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(steps):
+        step()
+    e1.record(s)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) * 1e-3 / steps
+    cells = g.Nr * g.Nth
+    inner = (torch.as_tensor(g.rn, device=device) < 0.8 * r_max)[:, None].expand(g.Nr + 1, g.ld).reshape(-1)
+    dBr = ((fl.B1[0] - wald[3]).abs() * inner).max().item() / (wald[3].abs() * inner).max().item()
+    bytes_step = FDTD_ARRAY_PASSES * g.size * 8
+    return {"workload": f"vacuum Wald magnetosphere, full-theta domain (periodic th), {Nr}x{Nth} (ln r, theta), "
+                        f"r in [0.99 r_h, 20 M], a={a}, absorbing layer from 0.9 r_max, FDTD only",
+            "steps": steps, "dt": dt, "ms_per_step": 1e3 * t, "cells_per_s": cells / t,
+            "array_traffic_gb_per_step": bytes_step / 1e9, "achieved_gbs": bytes_step / t / 1e9,
+            "max_rel_change_Br_inside_0.8_rmax": dBr}
+
+
 def run_inject(device, grid_n=1024, ppc=64, reps=5):
     """Sec. 3.3 pair injection on the plasma-filled Wald workload (a = 0.99,
     grid_n^2 cells, ppc particles per cell): region r_h .. 6 M,
@@ -1273,6 +1331,15 @@ def main():
                               "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                               "config": res}))
         return 0
+    if args.workload == "vacuum_wald":
+        torch.cuda.set_device(local)
+        if rank == 0:
+            res = run_vacuum_wald(torch.device("cuda", local), steps=max(args.steps, 1), warmup=max(args.warmup, 1))
+            print(json.dumps({"metric": "FDTD cells per second (full-theta vacuum Wald)", "value": res["cells_per_s"],
+                              "unit": "cells/s", "n_gpus": 1, "steps": res["steps"], "warmup": max(args.warmup, 1),
+                              "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+                              "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": res}))
+        return 0
     if args.workload == "clean":
         torch.cuda.set_device(local)
         res = run_div_clean(torch.device("cuda", local), args.pic_grid, args.clean_sweeps, reps=max(args.steps, 1))
@@ -1318,6 +1385,7 @@ def main():
         line["neutral_rk4_alone"] = run_neutral(args, dev, 1 << 20, 20, pre_steps=2, scheme="RK4")
         line["batched"] = run_batched(args, dev, 0.1, 5)
         line["div_clean"] = run_div_clean(dev)
+        line["vacuum_wald_full_theta"] = run_vacuum_wald(dev)
         line["adaptive_dt"] = run_adaptive(dev, newton=args.imr == "newton")
         line["adaptive_dt_neutral"] = run_adaptive_neutral(dev)
         line["inject"] = run_inject(dev, 1024, 16)

@@ -22,10 +22,11 @@ namespace fpic {
 // Metric tables
 // ---------------------------------------------------------------------------
 // type t: 0 (i, j), 1 (i+1/2, j), 2 (i, j+1/2), 3 (i+1/2, j+1/2)
-// quantity q: 0 alpha, 1 beta, 2 sqrt(gamma), 3 g_rr, 4 g_rp, 5 g_tt, 6 g_pp
-// tables 28..30: 2 pi x dual-cell volume of the (i,j), (i+1/2,j), (i,j+1/2) grids
+// quantity q: 0 alpha, 1 beta, 2 sqrt(gamma), 3 g_rr, 4 g_rp, 5 g_tt, 6 g_pp,
+// 7 1/sqrt(gamma) (the FDTD multiplies by it instead of dividing)
+// tables 32..34: 2 pi x dual-cell volume of the (i,j), (i+1/2,j), (i,j+1/2) grids
 // then sin/cos of the integer and half th nodes.
-enum { MT_Q = 7, MT_DUAL = 28, MT_N = 31 };
+enum { MT_Q = 8, MT_DUAL = 32, MT_N = 35 };
 
 struct Tabs {
     const double* m;   // MT_N tables of size sz, then 2 (Nth+1) + 2 Nth trig values
@@ -76,7 +77,7 @@ __global__ void k_metric_tables(BH bh, GridDev G, double* m, size_t sz)
             sincos(th, &s, &c);
             Geo g;
             geo_eval(bh, r, s, c, g);
-            const double v[MT_Q] = {g.alpha, g.beta, g.sqrtg, g.grr, g.grp, g.gtt, g.gpp};
+            const double v[MT_Q] = {g.alpha, g.beta, g.sqrtg, g.grr, g.grp, g.gtt, g.gpp, 1.0 / g.sqrtg};
             for (int q = 0; q < MT_Q; ++q) m[(size_t)(t * MT_Q + q) * sz + (size_t)i * G.ld + j] = v[q];
         }
         // dual-cell volumes of the (i,j), (i+1/2,j), (i,j+1/2) sub-grids
@@ -814,8 +815,8 @@ __device__ __forceinline__ double avg_r(const FK& k, const double* F, int ro, in
     if (ia < 0) ia = ib;
     if (ib > m - 1) ib = ia;
     const int tF = (ro ? 1 : 0) | (to ? 2 : 0), tT = (ro ? 0 : 1) | (to ? 2 : 0);
-    const double sa = k.T.at(tF, 2, ia, j), sb = k.T.at(tF, 2, ib, j), st = k.T.at(tT, 2, i2, j);
-    return fma(sa, F[(size_t)ia * k.ld + j], sb * F[(size_t)ib * k.ld + j]) / (2.0 * st);
+    const double sa = k.T.at(tF, 2, ia, j), sb = k.T.at(tF, 2, ib, j), ist = k.T.at(tT, 7, i2, j);
+    return fma(sa, F[(size_t)ia * k.ld + j], sb * F[(size_t)ib * k.ld + j]) * (0.5 * ist);
 }
 
 struct F3 {
@@ -905,20 +906,23 @@ __global__ void k_update_B(FK k, F3 Bin, O3 E, O3 Bout)
     const int i = blockIdx.y;
     const GridDev& G = k.G;
     const int jend = G.full ? k.Nth - 1 : k.Nth;
+    // the damping factor depends on the row only; 1/dr of the row
+    const double dn = damp(k, G.rn[i]), dh = i < k.Nr ? damp(k, G.rh[i]) : 1.0;
+    const double idr = i < k.Nr ? G.irn[i] : 0.0;
     for (int j = threadIdx.x; j <= jend; j += blockDim.x) {
         const size_t o = (size_t)i * k.ld + j;
         if (j < k.Nth) {   // B^r (i, j+1/2)
-            const double curl = (E.p[2][o + 1] - E.p[2][o]) / (G.tn[j + 1] - G.tn[j]);
-            put(Bout.p[0], o, j, k, (Bin.v(0, o) - k.dt * curl / k.T.at(2, 2, i, j)) * damp(k, G.rn[i]));
+            const double curl = (E.p[2][o + 1] - E.p[2][o]) * G.itn[j];
+            put(Bout.p[0], o, j, k, (Bin.v(0, o) - k.dt * curl * k.T.at(2, 7, i, j)) * dn);
         }
         if (i < k.Nr) {    // B^th (i+1/2, j)
-            const double curl = -(E.p[2][o + k.ld] - E.p[2][o]) / (G.rn[i + 1] - G.rn[i]);
-            put(Bout.p[1], o, j, k, (Bin.v(1, o) - k.dt * curl / k.T.at(1, 2, i, j)) * damp(k, G.rh[i]));
+            const double curl = -(E.p[2][o + k.ld] - E.p[2][o]) * idr;
+            put(Bout.p[1], o, j, k, (Bin.v(1, o) - k.dt * curl * k.T.at(1, 7, i, j)) * dh);
         }
         if (i < k.Nr && j < k.Nth) {   // B^ph (i+1/2, j+1/2)
-            const double dEt = (E.p[1][o + k.ld] - E.p[1][o]) / (G.rn[i + 1] - G.rn[i]);
-            const double dEr = (E.p[0][o + 1] - E.p[0][o]) / (G.tn[j + 1] - G.tn[j]);
-            put(Bout.p[2], o, j, k, (Bin.v(2, o) - k.dt * (dEt - dEr) / k.T.at(3, 2, i, j)) * damp(k, G.rh[i]));
+            const double dEt = (E.p[1][o + k.ld] - E.p[1][o]) * idr;
+            const double dEr = (E.p[0][o + 1] - E.p[0][o]) * G.itn[j];
+            put(Bout.p[2], o, j, k, (Bin.v(2, o) - k.dt * (dEt - dEr) * k.T.at(3, 7, i, j)) * dh);
         }
     }
 }
@@ -952,26 +956,28 @@ __global__ void k_update_D(FK k, F3 Din, O3 H, Src S0, Src S1, O3 Dout)
     const GridDev& G = k.G;
     const double fpi = 4.0 * M_PI;
     const int jlo = G.full ? 0 : 1;
+    // the damping factor depends on the row only; 1/dr of the row
+    const double dn = damp(k, G.rn[i]), dh = i < k.Nr ? damp(k, G.rh[i]) : 1.0;
+    const double idr = (i >= 1 && i < k.Nr) ? G.irh[i - 1] : 0.0;
     for (int j = threadIdx.x; j < k.Nth; j += blockDim.x) {
         const size_t o = (size_t)i * k.ld + j;
         const size_t om = j > 0 ? o - 1 : o + (k.Nth - 1);
-        const double dth = j > 0 ? G.th[j] - G.th[j - 1] : G.th[k.Nth] - G.th[k.Nth - 1];
+        const double idth = G.ith[j > 0 ? j - 1 : k.Nth - 1];     // 1/(th[j] - th[j-1]), across the seam at j = 0
         if (i < k.Nr && j >= jlo) {    // D^r (i+1/2, j)
-            const double curl = (H.p[2][o] - H.p[2][om]) / dth;
+            const double curl = (H.p[2][o] - H.p[2][om]) * idth;
             const double J = jsrc(k, S0, 0, i, j) + jsrc(k, S1, 0, i, j);
-            put(Dout.p[0], o, j, k, (Din.v(0, o) + k.dt * (curl / k.T.at(1, 2, i, j) - fpi * J)) * damp(k, G.rh[i]));
+            put(Dout.p[0], o, j, k, (Din.v(0, o) + k.dt * fma(curl, k.T.at(1, 7, i, j), -fpi * J)) * dh);
         }
         if (i >= 1 && i < k.Nr) {    // D^th (i, j+1/2)
-            const double curl = -(H.p[2][o] - H.p[2][o - k.ld]) / (G.rh[i] - G.rh[i - 1]);
+            const double curl = -(H.p[2][o] - H.p[2][o - k.ld]) * idr;
             const double J = jsrc(k, S0, 1, i, j) + jsrc(k, S1, 1, i, j);
-            put(Dout.p[1], o, j, k, (Din.v(1, o) + k.dt * (curl / k.T.at(2, 2, i, j) - fpi * J)) * damp(k, G.rn[i]));
+            put(Dout.p[1], o, j, k, (Din.v(1, o) + k.dt * fma(curl, k.T.at(2, 7, i, j), -fpi * J)) * dn);
         }
         if (i >= 1 && i < k.Nr && j >= jlo) {   // D^ph (i, j)
-            const double dHt = (H.p[1][o] - H.p[1][o - k.ld]) / (G.rh[i] - G.rh[i - 1]);
-            const double dHr = (H.p[0][o] - H.p[0][om]) / dth;
+            const double dHt = (H.p[1][o] - H.p[1][o - k.ld]) * idr;
+            const double dHr = (H.p[0][o] - H.p[0][om]) * idth;
             const double J = jsrc(k, S0, 2, i, j) + jsrc(k, S1, 2, i, j);
-            put(Dout.p[2], o, j, k,
-                (Din.v(2, o) + k.dt * ((dHt - dHr) / k.T.at(0, 2, i, j) - fpi * J)) * damp(k, G.rn[i]));
+            put(Dout.p[2], o, j, k, (Din.v(2, o) + k.dt * fma(dHt - dHr, k.T.at(0, 7, i, j), -fpi * J)) * dn);
         }
     }
 }
