@@ -934,8 +934,7 @@ def run_pic(args, device, grid_n, ppc, steps, rank=0, conserving=False, inject_e
         "cleaning": None if clean_every <= 0 else {"every": clean_every, "sweeps": clean_sweeps,
                                                    "calls": state.get("cleanings", 0)},
         "phase_ms": {("cleaning_and_" if clean_every > 0 else "") + "fdtd_1_4"
-                     + ("_and_injection" if inj is not None else "")
-                     + ("_and_state_copy" if conserving else ""): 1e3 * ph[0] / steps,
+                     + ("_and_injection" if inj is not None else ""): 1e3 * ph[0] / steps,
                      "push_rk4": 1e3 * ph[1] / steps,
                      ("conserving_deposit" if conserving else "sort_and_deposit"): 1e3 * ph[2] / steps,
                      "fdtd_7_10": 1e3 * ph[3] / steps},

@@ -129,7 +129,14 @@ typedef struct {
  *               else the smallest-update iterate of the full step (counted
  *               in n_notconv).  Iterations of every attempt count in
  *               n_iter_total.  0 = off (0..12).
- *   substep_tol: see imr_substeps. */
+ *   substep_tol: see imr_substeps.
+ *   before    : nullable; the state of every particle at the start of the
+ *               step -- r, th, ur, uth, uph and alive (n entries) -- is
+ *               written into these arrays of *before (device, before->n >=
+ *               n; its other arrays are not touched) by the explicit pass as
+ *               it reads the state: what fpic_deposit_conserving needs as
+ *               its `before`, without a separate copy.  fpic_push with RK4 or
+ *               a hybrid scheme only (FPIC_EINVAL elsewhere). */
 typedef struct {
     double dt;
     int scheme;
@@ -148,6 +155,7 @@ typedef struct {
     int imr_newton;
     int imr_substeps;
     double substep_tol;
+    fpic_particles *before;
 } fpic_push_params;
 
 /* Host-side counters of one push (filled only when a pointer is passed;

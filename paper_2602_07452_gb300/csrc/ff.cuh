@@ -1,14 +1,18 @@
 // Paired-FP32 ("double-float") arithmetic for FP64-pipe-bound inner loops.
 //
 // A value is the unevaluated sum hi + lo of two floats with |lo| at most
-// about one unit in the last place of hi: some 48 significant bits.  Every
+// a few units in the last place of hi: some 48 significant bits.  Every
 // operation is built from the error-free transformations of FP32 sums and
 // products -- Knuth's TwoSum (TAOCP vol. 2, Sec. 4.2.2), Dekker's fast
 // two-sum (1971) and the exact product error fmaf(a, b, -a b) -- so it runs on
 // the FP32 pipe, which on this GPU issues 64 times the FP64 rate.  Sums use
 // the short form (exact error of the high parts, plain sum of the low
 // parts): a few units of 2^-48 relative when both operands have the same
-// sign, and a few units of 2^-48 of |a| + |b| absolute in general.  The
+// sign, and a few units of 2^-48 of |a| + |b| absolute in general.  Sums and
+// products leave the pair unnormalized (no closing two-sum: |lo| stays within
+// a few ulp of hi, which every operation here accepts, and the error of the
+// short chains the deposit forms stays near 2^-45); the square root and the
+// conversion from a double return normalized pairs.  The
 // explicit __f*_rn intrinsics keep the compiler from contracting or
 // reordering the transformations.
 #pragma once
@@ -80,9 +84,8 @@ __device__ __forceinline__ ff ff_add(ff a, ff b)
 {
     const float s = __fadd_rn(a.hi, b.hi);
     const float v = __fsub_rn(s, a.hi);
-    float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fsub_rn(b.hi, v));
-    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
-    return ff_fast2(s, e);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fsub_rn(b.hi, v));
+    return {s, __fadd_rn(e, __fadd_rn(a.lo, b.lo))};
 }
 
 __device__ __forceinline__ ff ff_neg(ff a)
@@ -95,24 +98,21 @@ __device__ __forceinline__ ff ff_mul(ff a, ff b)
     const float p = __fmul_rn(a.hi, b.hi);
     float e = __fmaf_rn(a.hi, b.hi, -p);
     e = __fmaf_rn(a.hi, b.lo, e);
-    e = __fmaf_rn(a.lo, b.hi, e);
-    return ff_fast2(p, e);
+    return {p, __fmaf_rn(a.lo, b.hi, e)};
 }
 
 __device__ __forceinline__ ff ff_sqr(ff a)
 {
     const float p = __fmul_rn(a.hi, a.hi);
-    float e = __fmaf_rn(a.hi, a.hi, -p);
-    e = __fmaf_rn(__fadd_rn(a.hi, a.hi), a.lo, e);
-    return ff_fast2(p, e);
+    const float e = __fmaf_rn(a.hi, a.hi, -p);
+    return {p, __fmaf_rn(__fadd_rn(a.hi, a.hi), a.lo, e)};
 }
 
 // a times a float b
 __device__ __forceinline__ ff ff_mulf(ff a, float b)
 {
     const float p = __fmul_rn(a.hi, b);
-    const float e = __fmaf_rn(a.lo, b, __fmaf_rn(a.hi, b, -p));
-    return ff_fast2(p, e);
+    return {p, __fmaf_rn(a.lo, b, __fmaf_rn(a.hi, b, -p))};
 }
 
 // a times a power of two (exact)

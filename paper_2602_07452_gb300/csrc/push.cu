@@ -63,6 +63,7 @@ struct PushK {
     long long n;
     long long p_begin, p_end;   // explicit pass over [p_begin, p_end) (p_end 0: all n)
     PartDev P;
+    PartDev before;         // fpic_push_params.before: r, th, ur, uth, uph, alive at the step's start (r null: off)
     double* guess;          // 6 x n (SoA) implicit initial guesses, then the implicit results
     double* sc0;            // 2 x n: sin, cos of th^n of the implicit particles
     uint32_t* queue;        // indices of particles for the implicit solver
@@ -420,7 +421,9 @@ __global__ void __launch_bounds__(128) k_explicit(const __grid_constant__ PushK 
         if ((int)(threadIdx.x & 31) == __ffs(act) - 1)
             atomicAdd((unsigned long long*)&k.cnt[CNT_ALIVE], (unsigned long long)__popc(al));
     }
-    if (!k.P.alive[p]) {
+    const uint8_t alive0 = k.P.alive[p];
+    if (k.before.r) k.before.alive[p] = alive0;
+    if (!alive0) {
         k.P.scheme[p] = 0;
         k.P.iters[p] = 0;
         return;
@@ -428,6 +431,13 @@ __global__ void __launch_bounds__(128) k_explicit(const __grid_constant__ PushK 
     const RunK& R = BATCHED ? k.runs[run_of(k.runs, k.nruns, p)] : k.run;
     double z0[6], kk[6], acc[6], y[6];
     load_state(k.P, p, z0);
+    if (k.before.r) {
+        k.before.r[p] = z0[0];
+        k.before.th[p] = z0[1];
+        k.before.ur[p] = z0[3];
+        k.before.uth[p] = z0[4];
+        k.before.uph[p] = z0[5];
+    }
     const double qm = k.P.qm[p];
     const bool em = (R.has_fields || R.B0field != 0.0) && qm != 0.0;
     const double dt = k.dt, hdt = 0.5 * k.dt;
@@ -1609,6 +1619,14 @@ static int check_push_args(const fpic_ctx* c, const fpic_particles* p, const dou
         if (!c->has_grid) return set_error(FPIC_EINVAL, "%s: fields given but no grid set", who);
     }
     if (prm->guess) return set_error(FPIC_EINVAL, "%s: learned guesses need fpic_push_learned", who);
+    if (prm->before) {
+        const fpic_particles* b = prm->before;
+        if (prm->scheme != FPIC_RK4 && prm->scheme < FPIC_HYB1)
+            return set_error(FPIC_EINVAL, "%s: before needs RK4 or a hybrid scheme (the explicit pass writes it)", who);
+        if (!b->r || !b->th || !b->ur || !b->uth || !b->uph || !b->alive)
+            return set_error(FPIC_EINVAL, "%s: before has a NULL r, th, ur, uth, uph or alive array", who);
+        if (b->n < p->n) return set_error(FPIC_EINVAL, "%s: before holds fewer than n particles", who);
+    }
     return 0;
 }
 
@@ -1656,6 +1674,11 @@ static int push_core(fpic_ctx* c, fpic_particles* p, const double* const fields[
     k.n = n;
     k.P = PartDev{p->r, p->th, p->ph, p->ur, p->uth, p->uph, p->qm, p->H0, p->D0, p->Hn,
                   p->alive, p->scheme, p->iters, p->cell};
+    if (prm->before) {
+        const fpic_particles* b = prm->before;
+        k.before = PartDev{b->r, b->th, nullptr, b->ur, b->uth, b->uph, nullptr, nullptr, nullptr, nullptr,
+                           b->alive, nullptr, nullptr, nullptr};
+    }
     if (has_fields && n > 0) {
         rc = field_coefs(c, fields, k.run, s);
         if (rc) return rc;
@@ -1779,6 +1802,7 @@ extern "C" int fpic_push_host(fpic_ctx* c, fpic_particles* hp, const double* con
 {
     const int rc_args = check_push_args(c, hp, fields, prm, "fpic_push_host");
     if (rc_args) return rc_args;
+    if (prm->before) return set_error(FPIC_EINVAL, "fpic_push_host: before is not supported with host particles");
     const long long n = hp->n;
     cudaStream_t s = (cudaStream_t)stream;
     FPIC_CUDA(cudaSetDevice(c->device));
@@ -1978,6 +2002,7 @@ extern "C" int fpic_push_noalloc(double M, double a, fpic_particles* p, const fp
     if (!(prm->tol >= 0.0)) return set_error(FPIC_EINVAL, "fpic_push_noalloc: tol must be >= 0");
     if (prm->guess) return set_error(FPIC_EINVAL, "fpic_push_noalloc: learned guesses are not supported here");
     if (prm->imr_substeps != 0) return set_error(FPIC_EINVAL, "fpic_push_noalloc: imr_substeps is not supported here");
+    if (prm->before) return set_error(FPIC_EINVAL, "fpic_push_noalloc: before is not supported here");
     int dev = 0, sms = 0;
     void* scratch = nullptr;
     FPIC_CUDA(cudaGetDevice(&dev));
@@ -2522,6 +2547,7 @@ extern "C" int fpic_push_learned(fpic_ctx* c, fpic_mlp* m, fpic_particles* p, co
     if (prm->dt_implicit != 0.0 && prm->dt_implicit != prm->dt)
         return set_error(FPIC_EINVAL, "fpic_push_learned: the learned guess is trained for dt_implicit = dt");
     if (prm->B0field != 0.0) return set_error(FPIC_EINVAL, "fpic_push_learned: B0field is not supported");
+    if (prm->before) return set_error(FPIC_EINVAL, "fpic_push_learned: before is not supported");
     if (p->n < 0 || p->n >= (1LL << 31)) return set_error(FPIC_EINVAL, "fpic_push_learned: n out of range");
     if (!particles_ok(p, true)) return set_error(FPIC_EINVAL, "fpic_push_learned: NULL particle array");
     if (fields && !c->has_grid) return set_error(FPIC_EINVAL, "fpic_push_learned: fields given but no grid set");
@@ -2641,6 +2667,7 @@ static int push_batched(const fpic_run* runs, int nruns, fpic_mlp* m, fpic_parti
     if (!(std::isfinite(prm->dt)) || prm->dt == 0.0) return set_error(FPIC_EINVAL, "fpic_push_batched: bad dt");
     if (!dt_implicit_ok(prm)) return set_error(FPIC_EINVAL, "fpic_push_batched: bad dt_implicit");
     if (prm->B0field != 0.0) return set_error(FPIC_EINVAL, "fpic_push_batched: B0field is not supported");
+    if (prm->before) return set_error(FPIC_EINVAL, "fpic_push_batched: before is not supported");
     if (prm->scheme != FPIC_RK4 && prm->scheme != FPIC_IMR && prm->scheme != FPIC_HYB1 && prm->scheme != FPIC_HYB2)
         return set_error(FPIC_EINVAL, "fpic_push_batched: scheme must be RK4, IMR, Hyb1 or Hyb2");
     if (prm->scheme >= FPIC_HYB1 && prm->implicit != FPIC_IMR)

@@ -48,7 +48,8 @@ class fpic_push_params(C.Structure):
                 ("tol", C.c_double), ("max_iter", C.c_int), ("r_max", C.c_double),
                 ("dg_eps", C.c_double), ("B0pot", C.c_double), ("guess", C.c_void_p),
                 ("events", C.c_void_p), ("dt_implicit", C.c_double), ("t", C.c_void_p), ("B0field", C.c_double),
-                ("imr_newton", C.c_int), ("imr_substeps", C.c_int), ("substep_tol", C.c_double)]
+                ("imr_newton", C.c_int), ("imr_substeps", C.c_int), ("substep_tol", C.c_double),
+                ("before", C.POINTER(fpic_particles))]
 
 
 class fpic_push_stats(C.Structure):
@@ -335,6 +336,19 @@ def push_params(dt, scheme=FPIC_RK4, implicit=FPIC_IMR, thr=1e-12, tol=1e-14, ma
         prm._events_keepalive = arr
         prm.events = C.cast(arr, C.c_void_p)
     return prm
+
+
+def set_push_before(prm: fpic_push_params, before) -> None:
+    """Point prm.before at a Particles set (or None): the push then writes
+    each particle's r, th, ur, uth, uph and alive at the start of its step
+    into before's arrays (see fpic.h)."""
+    if before is None:
+        prm.before = None
+        prm._before_keepalive = None
+    else:
+        s = before.struct()
+        prm._before_keepalive = (before, s)
+        prm.before = C.pointer(s)
 
 
 def fpic_push(ctx: Ctx, p: Particles, fields, prm: fpic_push_params, stats: bool = False, stream=None):

@@ -24,8 +24,10 @@ class GRPIC:
     n         : particles in use
     push_prm  : F.push_params(...) of the push (its dt is the step)
     fdtd_prm  : F.fdtd_params(...) (its `conserving` flag is set here)
-    conserving: use fpic_deposit_conserving (keeps a copy of the state
-                before each push) instead of fpic_deposit
+    conserving: use fpic_deposit_conserving instead of fpic_deposit; the
+                push writes the state it starts from into a second store
+                (fpic_push_params.before), which the deposit reads as the
+                move's start
     clean     : (every, sweeps) or None
     inject    : (every, F.fpic_inject_params, draws tensor) or None
     """
@@ -78,8 +80,7 @@ class GRPIC:
         prev = None
         if self.conserving:
             prev = self.prev_store.head(self.n)
-            for nm in ("r", "th", "ur", "uth", "uph", "alive"):
-                getattr(prev, nm).copy_(getattr(p, nm))
+            F.set_push_before(self.push_prm, prev)
         rec(1)
         F.fpic_push(self.ctx, p, fl.push_fields(), self.push_prm)
         rec(2)

@@ -901,3 +901,49 @@ def test_full_theta_rejects_the_grid_side_solvers(F):
         F.fpic_div_clean(ctx, fl.D1, fl.rho1, 5)
     F.fpic_set_theta_mode(ctx, F.FPIC_THETA_HALF)
     F.fpic_deposit(ctx, p, g.size)          # the half-theta reading of the same tables
+
+
+@pytest.mark.parametrize("scheme", ["RK4", "HYB1"])
+def test_push_writes_the_state_it_starts_from(F, scheme):
+    """fpic_push_params.before: the explicit pass stores every particle's
+    r, th, ur, uth, uph and alive at the start of the step (removed ones
+    included, their flag 0) -- bitwise the state before the push -- and
+    leaves the other arrays of `before` alone; the pushed result is the
+    same as without it.  The batched, learned, host and allocation-free
+    pushes refuse it."""
+    a = 0.9
+    g = I.wald_grid(64, a)
+    Fo = O.wald_on_grid(a, 1.0, g)
+    ctx = _mk(F, a, g)
+    d, z, q = thermal_state(4001, g, a, theta=0.1, seed=71)
+    n = len(q)
+    H0, _, D0 = O.hamiltonian(1.0, a, 1.0, z, q)
+    alive = np.ones(n, np.uint8)
+    alive[::7] = 0
+    p = make_particles(z, q, H0, D0, H0.copy(), alive=alive)
+    p2 = make_particles(z, q, H0, D0, H0.copy(), alive=alive)
+    before = make_particles(np.full((n, 6), -1.0), np.full(n, -3.0))
+    before.alive.fill_(7)
+    fd = fields_dev(Fo)
+    sch = getattr(F, "FPIC_" + scheme)
+    prm = F.push_params(1e-3, scheme=sch, implicit=F.FPIC_IMR, thr=8e-5, r_max=g.rn[-1], B0pot=1.0, imr_newton=True)
+    F.fpic_push(ctx, p2, fd, prm)
+    F.set_push_before(prm, before)
+    F.fpic_push(ctx, p, fd, prm)
+    zb = before.state().cpu().numpy()
+    ab = before.alive.cpu().numpy()
+    assert np.array_equal(ab, alive)
+    live = alive == 1
+    for i in (0, 1, 3, 4, 5):
+        assert np.array_equal(zb[live, i], z[live, i]), i
+    assert np.all(zb[:, 2] == -1.0) and np.all(zb[~live] == -1.0)
+    assert np.all(before.qm.cpu().numpy() == -3.0)
+    assert np.array_equal(p.state().cpu().numpy(), p2.state().cpu().numpy())
+    with pytest.raises(F.FpicError, match="before"):
+        F.fpic_push_noalloc(1.0, a, p, prm)
+    short = make_particles(np.ones((n - 1, 6)), np.ones(n - 1))
+    F.set_push_before(prm, short)
+    with pytest.raises(F.FpicError, match="fewer"):
+        F.fpic_push(ctx, p, fd, prm)
+    F.set_push_before(prm, None)
+    F.fpic_push(ctx, p, fd, prm)
