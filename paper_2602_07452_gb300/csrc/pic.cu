@@ -248,6 +248,47 @@ __global__ void k_gather_perm(const T* __restrict__ src, T* __restrict__ dst, co
     if (i < n) dst[i] = src[perm[i]];
 }
 
+// Every particle array permuted at once (the deposit's sort): one pass
+// gathers them all through the permutation into a staging area (11 x n
+// doubles, then n u32, then 3 x n bytes), reading the permutation once, and
+// one pass copies them back, instead of a gather and a copy per array.
+struct PermArrays {
+    double* d[11];
+    uint8_t* b[3];
+    uint32_t* u;
+};
+
+__global__ void k_gather_all(PermArrays a, const uint32_t* __restrict__ perm, double* __restrict__ stage, long long n)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t j = perm[i];
+    uint32_t* su = (uint32_t*)(stage + 11 * n);
+    uint8_t* sb = (uint8_t*)(su + n);
+#pragma unroll
+    for (int k = 0; k < 11; ++k)
+        if (a.d[k]) stage[k * n + i] = a.d[k][j];
+    if (a.u) su[i] = a.u[j];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        if (a.b[k]) sb[k * n + i] = a.b[k][j];
+}
+
+__global__ void k_copy_all(PermArrays a, const double* __restrict__ stage, long long n)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t* su = (const uint32_t*)(stage + 11 * n);
+    const uint8_t* sb = (const uint8_t*)(su + n);
+#pragma unroll
+    for (int k = 0; k < 11; ++k)
+        if (a.d[k]) a.d[k][i] = stage[k * n + i];
+    if (a.u) a.u[i] = su[i];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        if (a.b[k]) a.b[k][i] = sb[k * n + i];
+}
+
 static int scan_u32(const uint32_t* in, uint32_t* out, uint32_t* bsum, long long m, cudaStream_t s)
 {
     const int nb = (int)((m + SCAN_B * SCAN_PER - 1) / (SCAN_B * SCAN_PER));
@@ -303,7 +344,9 @@ static int work_layout(fpic_ctx* c, long long n, bool deposit, Work& w, size_t e
     return 0;
 }
 
-static int sort_impl(fpic_ctx* c, fpic_particles* p, Work& w, cudaStream_t s)
+// stage: nullable, room for 12 x n doubles (the deposit's record buffer,
+// unused until the sort is done): every array is permuted in two passes.
+static int sort_impl(fpic_ctx* c, fpic_particles* p, Work& w, cudaStream_t s, double* stage = nullptr)
 {
     const long long n = p->n;
     const uint32_t C = (uint32_t)c->Nr * (uint32_t)c->Nth;
@@ -321,6 +364,16 @@ static int sort_impl(fpic_ctx* c, fpic_particles* p, Work& w, cudaStream_t s)
     k_dead_place<<<nb, 256, 0, s>>>(p->alive, w.pos, w.off, w.perm2, n, C);
     FPIC_CUDA(cudaGetLastError());
     double* d8[] = {p->r, p->th, p->ph, p->ur, p->uth, p->uph, p->qm, p->w, p->H0, p->D0, p->Hn};
+    if (stage) {
+        PermArrays a;
+        for (int k = 0; k < 11; ++k) a.d[k] = d8[k];
+        a.b[0] = p->alive; a.b[1] = p->scheme; a.b[2] = p->iters;
+        a.u = p->cell;
+        k_gather_all<<<nb, 256, 0, s>>>(a, w.perm2, stage, n);
+        k_copy_all<<<nb, 256, 0, s>>>(a, stage, n);
+        FPIC_CUDA(cudaGetLastError());
+        return 0;
+    }
     for (double* a : d8) {
         if (!a) continue;
         k_gather_perm<double><<<nb, 256, 0, s>>>(a, w.tmp, w.perm2, n);
@@ -1066,7 +1119,7 @@ extern "C" int fpic_deposit(fpic_ctx* c, fpic_particles* p, double* rho, double*
     int rc = work_layout(c, n > 0 ? n : 1, true, w);
     if (rc) return rc;
     if (n > 0) {
-        rc = sort_impl(c, p, w, s);
+        rc = sort_impl(c, p, w, s, w.rec);
         if (rc) return rc;
     } else {
         FPIC_CUDA(cudaMemsetAsync(w.off, 0, 4 * ((size_t)C + 2), s));

@@ -3,6 +3,7 @@ import math
 
 import numpy as np
 import pytest
+import torch
 
 import oracle as O
 from oracle import pic as P
@@ -47,6 +48,35 @@ def test_sort_is_the_stable_argsort(F):
     assert np.array_equal(p.Hn.cpu().numpy(), perm.astype(float))
     assert np.array_equal(p.alive.cpu().numpy(), alive[perm])
     assert np.array_equal(p.cell.cpu().numpy().view(np.uint32), cell[perm].astype(np.uint32))
+
+
+def test_deposit_permutes_every_array_like_fpic_sort(F):
+    """fpic_deposit permutes the particle arrays in two fused passes through
+    its record buffer; fpic_sort, one gather and one copy per array: the
+    two leave every array (the 11 FP64 ones, alive / scheme / iters, cell)
+    bit for bit alike, removed particles last."""
+    a = 0.9
+    g = I.log_grid(37, 29, 1.5, 30.0)
+    ctx = F.fpic_init_metric(1.0, a)
+    F.fpic_set_grid(ctx, g)
+    n = 30011
+    z, q, w, alive = _plasma(g, n, a, 13, dead_frac=0.2)
+    rng = np.random.default_rng(14)
+    ps = []
+    for _ in range(2):
+        p = make_particles(z, q, w=w, alive=alive)
+        for nm in ("H0", "D0", "Hn"):
+            getattr(p, nm).copy_(dev(np.arange(n, dtype=float) * (1 + 0.5 * len(ps))))
+        p.scheme.copy_(dev(np.arange(n) % 251, torch.uint8))
+        p.iters.copy_(dev((np.arange(n) * 7) % 253, torch.uint8))
+        ps.append(p)
+    F.fpic_sort(ctx, ps[0])
+    F.fpic_deposit(ctx, ps[1], g.size)
+    for nm in ("H0", "D0", "Hn"):
+        getattr(ps[0], nm).mul_(1.5)
+    for nm in ("r", "th", "ph", "ur", "uth", "uph", "qm", "w", "alive", "scheme", "iters", "cell", "H0", "D0", "Hn"):
+        a0, a1 = getattr(ps[0], nm).cpu().numpy(), getattr(ps[1], nm).cpu().numpy()
+        assert np.array_equal(a0, a1), nm
 
 
 @pytest.mark.parametrize("lattice", [1, 0])
