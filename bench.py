@@ -441,11 +441,26 @@ def run_gpu(args, ws, rank, local):
     for _ in range(2):
         F.fpic_push_host(ctx, hp, fields, prm_h)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    e2e_ps = 0
-    for _ in range(e2e_steps):
-        e2e_ps += F.fpic_push_host(ctx, hp, fields, prm_h, stats=True)["n_alive_before"]
-    e2e_t = time.perf_counter() - t0
+    # every step reads its inputs from and writes its results to the pinned
+    # host arrays and copies its stats to pinned host memory; with
+    # FPIC_TUNE_ASYNC the host enqueues step k+1 while step k runs, and
+    # waits once at the end
+    F.fpic_set_tuning(ctx, F.FPIC_TUNE_ASYNC, 1)
+    st_host = torch.zeros((e2e_steps, 8), dtype=torch.int64).pin_memory()
+    host_modes = {}
+    for staging in (0, 1):          # in place over the link / DMA-staged (the same results)
+        F.fpic_set_tuning(ctx, F.FPIC_TUNE_HOST_STAGING, staging)
+        F.fpic_push_host(ctx, hp, fields, prm_h)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(e2e_steps):
+            F.fpic_push_host(ctx, hp, fields, prm_h, stats_out=st_host[i])
+        torch.cuda.synchronize()
+        host_modes[staging] = (time.perf_counter() - t0, int(st_host[:, 0].sum().item()))
+    F.fpic_set_tuning(ctx, F.FPIC_TUNE_ASYNC, 0)
+    best = min(host_modes, key=lambda m: host_modes[m][0] / max(host_modes[m][1], 1))
+    F.fpic_set_tuning(ctx, F.FPIC_TUNE_HOST_STAGING, best)
+    e2e_t, e2e_ps = host_modes[best]
     e2e_T, e2e_W = aggregate(e2e_t, e2e_ps, device)
     # the same through pageable host arrays: staged chunked copies
     hq = F.HostParticles(p.n)
@@ -492,8 +507,10 @@ def run_gpu(args, ws, rank, local):
                    "autotune_ms_per_push": {str(k): round(v, 4) for k, v in tune_ms.items()}},
         "e2e": {"value": e2e_W / e2e_T, "unit": UNIT,
                 "h2d_bytes_per_step": hp.bytes_in(), "d2h_bytes_per_step": hp.bytes_out(),
-                "api": "fpic_push_host on pinned host SoA arrays: the kernels read the inputs and write "
-                       "the results in place over the CPU-GPU link, every step",
+                "api": "fpic_push_host on pinned host SoA arrays, FPIC_TUNE_ASYNC (one host wait after the last step; per-step stats copied to pinned memory), "
+                       + ("DMA-staged (FPIC_TUNE_HOST_STAGING: chunked copies in overlapping the explicit pass, copies back after the step)"
+                          if best else "the kernels read the inputs and write the results in place over the CPU-GPU link") + ", every step",
+                "host_modes_particle_steps_per_s": {("staged" if m else "in_place"): v[1] / v[0] for m, v in host_modes.items()},
                 "staged_pageable": {"value": st_W / st_T,
                                     "api": "fpic_push_host on pageable host arrays: chunked H2D copies "
                                            "overlapping the explicit pass, D2H after the step"}},

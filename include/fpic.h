@@ -301,7 +301,10 @@ int fpic_push_batched(const fpic_run *runs, int nruns, fpic_particles *p, const 
  * implicit pass then runs over all queued particles), and the state, Hn,
  * alive, scheme, iters and cell arrays are copied back on `stream`.  Either
  * way the push is exactly fpic_push's and `stream` is synchronised before
- * returning.  fields stay device arrays.  Errors: as fpic_push. */
+ * returning -- except on mapped arrays with FPIC_TUNE_ASYNC = 1, where the
+ * call only enqueues the push and the host arrays hold its results once
+ * `stream` has been synchronised.  fields stay device arrays.  Errors: as
+ * fpic_push. */
 int fpic_push_host(fpic_ctx *ctx, fpic_particles *host_p, const double *const fields[6],
                    const fpic_push_params *prm, fpic_push_stats *stats, void *stream);
 
@@ -391,9 +394,26 @@ int fpic_probe_fp64(double *gflops_out, int reps);
  *     the hardware estimate and one Goldschmidt step (2^-39.6 measured).
  *     Lattice points, weights and node shares are the same; results differ
  *     by rounding only (1e-13 relative and below on the deposited sources).
+ *   FPIC_TUNE_ASYNC: 1 = fpic_push and fpic_push_host never synchronise the
+ *     stream: requested stats are assembled on the device and copied into
+ *     *stats asynchronously (valid once `stream` has been synchronised; pass
+ *     page-locked host memory, else the copy itself blocks; FPIC_ETIMEOUT
+ *     and FPIC_ENOTCONVERGED are then not returned, read n_notconv), and
+ *     fpic_push_host on mapped host arrays returns before its results are
+ *     written (see there).  0 (default) = stats are read, and the host push
+ *     completed, before the call returns.
+ *   FPIC_TUNE_HOST_STAGING: 1 = fpic_push_host moves even mapped (pinned)
+ *     arrays through library-owned device buffers -- DMA copies in four
+ *     chunks overlapping the explicit pass, the push on the device, DMA
+ *     copies back -- instead of reading and writing them in place over the
+ *     link; the results are the same.  In place, the implicit pass's
+ *     write-back goes to scattered host addresses, one link transaction per
+ *     value; staged, every transfer is a sequential DMA.  0 (default) = in
+ *     place for mapped arrays.
  * Errors: FPIC_EINVAL (NULL, unknown key, value out of range). */
 enum { FPIC_TUNE_IMR_BLOCKS_PER_SM = 0, FPIC_TUNE_DEP_THREADS = 1, FPIC_TUNE_STATIC_FIELDS = 2,
-       FPIC_TUNE_REUSE_SLOPE = 3, FPIC_TUNE_STAGE_FIELDS = 4, FPIC_TUNE_DEP_LATTICE = 5 };
+       FPIC_TUNE_REUSE_SLOPE = 3, FPIC_TUNE_STAGE_FIELDS = 4, FPIC_TUNE_DEP_LATTICE = 5, FPIC_TUNE_ASYNC = 6,
+       FPIC_TUNE_HOST_STAGING = 7 };
 int fpic_set_tuning(fpic_ctx *ctx, int key, int value);
 int fpic_get_tuning(const fpic_ctx *ctx, int key, int *value);
 

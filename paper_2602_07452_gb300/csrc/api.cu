@@ -271,7 +271,9 @@ extern "C" int fpic_init_metric(fpic_ctx** out, double M, double a)
     int rc = check_cuda(cudaGetDevice(&c->device), "cudaGetDevice");
     if (!rc) rc = check_cuda(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device),
                              "cudaDeviceGetAttribute");
-    if (!rc) rc = check_cuda(cudaMalloc(&c->d_cnt, CNT_N * sizeof(long long)), "cudaMalloc(counters)");
+    // the counters, then room for one fpic_push_stats assembled on the device (FPIC_TUNE_ASYNC)
+    if (!rc) rc = check_cuda(cudaMalloc(&c->d_cnt, CNT_N * sizeof(long long) + sizeof(fpic_push_stats)),
+                             "cudaMalloc(counters)");
     if (!rc) rc = check_cuda(cudaMallocHost(&c->h_cnt, CNT_N * sizeof(long long)), "cudaMallocHost");
     if (rc) {
         fpic_destroy(c);

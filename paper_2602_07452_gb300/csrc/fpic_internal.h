@@ -46,6 +46,8 @@ struct fpic_ctx {
     int imr_blocks_per_sm = 4;
     int dep_threads = 128;           // threads per block of the deposit's particle kernel
     int dep_lattice = 1;             // FPIC_TUNE_DEP_LATTICE: 1 paired-FP32 trapezoid lattices, 0 FP64
+    int async = 0;                   // FPIC_TUNE_ASYNC: stats copied asynchronously, no host-side synchronisation
+    int host_staging = 0;            // FPIC_TUNE_HOST_STAGING: fpic_push_host copies even mapped arrays
     // per-cell field interpolation coefficients (rebuilt by every push with fields)
     void* d_fcoef = nullptr;
     size_t fcoef_bytes = 0;

@@ -1591,6 +1591,33 @@ static bool dt_implicit_ok(const fpic_push_params* prm)
     return prm->dt_implicit == 0.0 || (std::isfinite(prm->dt_implicit) && (prm->dt_implicit > 0.0) == (prm->dt > 0.0));
 }
 
+// fpic_push_stats from the push's counters (host after a synchronising
+// read, or on the device for FPIC_TUNE_ASYNC).  Slope reuse: k1 only where
+// not reused, the full right-hand side at every trial's end point and at
+// every converged IMR solve.
+__host__ __device__ inline void stats_from_counters(const long long* h, int scheme, int implicit, bool explicit_pass,
+                                                    bool slope, fpic_push_stats* st)
+{
+    st->n_alive_before = h[CNT_ALIVE];
+    st->n_implicit = scheme == FPIC_RK4 ? 0 : (scheme >= FPIC_HYB1 ? h[CNT_QUEUE] : h[CNT_ALIVE]);
+    st->n_iter_total = h[CNT_ITERS];
+    st->n_notconv = h[CNT_NOTCONV];
+    st->n_removed = h[CNT_REMOVED];
+    st->n_rhs_evals = h[CNT_EVALS] + (explicit_pass ? 4 * h[CNT_ALIVE] : 0);
+    st->n_slope_reused = h[CNT_SLOPE];
+    st->n_tiles_staged = h[CNT_STAGED];
+    if (slope) {
+        st->n_rhs_evals += h[CNT_ALIVE] - h[CNT_SLOPE];
+        if (scheme >= FPIC_HYB1 && implicit == FPIC_IMR) st->n_rhs_evals += h[CNT_QUEUE];
+    }
+}
+
+__global__ void k_stats_final(const long long* cnt, fpic_push_stats* out, int scheme, int implicit, int explicit_pass,
+                              int slope)
+{
+    stats_from_counters(cnt, scheme, implicit, explicit_pass != 0, slope != 0, out);
+}
+
 static int push_core(fpic_ctx* c, fpic_particles* p, const double* const fields[6], const fpic_push_params* prm,
                      fpic_push_stats* stats, cudaStream_t s, const PushChunks* ch, bool host_state = false);
 
@@ -1712,7 +1739,6 @@ static int push_core(fpic_ctx* c, fpic_particles* p, const double* const fields[
     }
     if (k.substeps > 0) FPIC_CUDA(cudaMemsetAsync(k.strag_flag, 0, (size_t)n, s));
     const int TB = 128;
-    const unsigned nb = (unsigned)((n + TB - 1) / TB);
     const unsigned persist = (unsigned)c->sm_count * 8u;
     const unsigned imr_grid = (unsigned)c->sm_count * (unsigned)c->imr_blocks_per_sm;
     cudaEvent_t* ev = prm->events ? (cudaEvent_t*)prm->events : nullptr;
@@ -1773,25 +1799,21 @@ static int push_core(fpic_ctx* c, fpic_particles* p, const double* const fields[
     }
     if (ev) FPIC_CUDA(cudaEventRecord(ev[3], s));
     FPIC_CUDA(cudaGetLastError());
+    if (stats && c->async) {
+        // assembled on the device, copied without waiting (FPIC_TUNE_ASYNC)
+        fpic_push_stats* d_st = (fpic_push_stats*)(c->d_cnt + CNT_N);
+        k_stats_final<<<1, 1, 0, s>>>(c->d_cnt, d_st, prm->scheme, prm->implicit, explicit_pass ? 1 : 0,
+                                      k.slope ? 1 : 0);
+        FPIC_CUDA(cudaMemcpyAsync(stats, d_st, sizeof(fpic_push_stats), cudaMemcpyDeviceToHost, s));
+        FPIC_CUDA(cudaGetLastError());
+        return FPIC_OK;
+    }
     if (stats) {
         FPIC_CUDA(cudaMemcpyAsync(c->h_cnt, c->d_cnt, CNT_N * sizeof(long long), cudaMemcpyDeviceToHost, s));
         FPIC_CUDA(cudaStreamSynchronize(s));
+        stats_from_counters(c->h_cnt, prm->scheme, prm->implicit, explicit_pass, k.slope != nullptr, stats);
         const long long* h = c->h_cnt;
-        stats->n_alive_before = h[CNT_ALIVE];
-        stats->n_implicit = prm->scheme == FPIC_RK4 ? 0 : (prm->scheme >= FPIC_HYB1 ? h[CNT_QUEUE] : h[CNT_ALIVE]);
-        stats->n_iter_total = h[CNT_ITERS];
-        stats->n_notconv = h[CNT_NOTCONV];
-        stats->n_removed = h[CNT_REMOVED];
-        stats->n_rhs_evals = h[CNT_EVALS] + (explicit_pass ? 4 * h[CNT_ALIVE] : 0);
-        stats->n_slope_reused = h[CNT_SLOPE];
-        stats->n_tiles_staged = h[CNT_STAGED];
         if (h[CNT_ERR] > 0) return set_error(FPIC_ETIMEOUT, "fpic_push: %lld field-tile loads timed out", h[CNT_ERR]);
-        if (k.slope) {
-            // slope reuse: k1 only where not reused, the full right-hand side
-            // at every trial's end point and at every converged IMR solve
-            stats->n_rhs_evals += h[CNT_ALIVE] - h[CNT_SLOPE];
-            if (prm->scheme >= FPIC_HYB1 && prm->implicit == FPIC_IMR) stats->n_rhs_evals += h[CNT_QUEUE];
-        }
         if (h[CNT_NOTCONV] > 0) return FPIC_ENOTCONVERGED;
     }
     return FPIC_OK;
@@ -1809,7 +1831,7 @@ extern "C" int fpic_push_host(fpic_ctx* c, fpic_particles* hp, const double* con
     // Pinned (page-locked, mapped) host arrays are reachable from the GPU over
     // NVLink-C2C: the push then reads and writes them in place, with no
     // staging copies (each byte still crosses the link once per direction).
-    if (n > 0) {
+    if (n > 0 && !c->host_staging) {
         fpic_particles z = *hp;
         bool mapped = true;
         void** fields_h[] = {(void**)&z.r, (void**)&z.th, (void**)&z.ph, (void**)&z.ur, (void**)&z.uth,
@@ -1830,7 +1852,7 @@ extern "C" int fpic_push_host(fpic_ctx* c, fpic_particles* hp, const double* con
         if (mapped) {
             int rc0 = push_core(c, &z, fields, prm, stats, s, nullptr, true);
             if (rc0 < 0) return rc0;
-            FPIC_CUDA(cudaStreamSynchronize(s));
+            if (!c->async) FPIC_CUDA(cudaStreamSynchronize(s));
             return rc0;
         }
     }
@@ -1881,7 +1903,7 @@ extern "C" int fpic_push_host(fpic_ctx* c, fpic_particles* hp, const double* con
         FPIC_CUDA(cudaMemcpyAsync(hp->iters, d.iters, nb, cudaMemcpyDeviceToHost, s));
         if (hp->cell) FPIC_CUDA(cudaMemcpyAsync(hp->cell, d.cell, n4, cudaMemcpyDeviceToHost, s));
     }
-    FPIC_CUDA(cudaStreamSynchronize(s));
+    if (!c->async) FPIC_CUDA(cudaStreamSynchronize(s));
     return rc;
 }
 
@@ -2880,6 +2902,16 @@ extern "C" int fpic_set_tuning(fpic_ctx* c, int key, int value)
             return set_error(FPIC_EINVAL, "fpic_set_tuning: deposit lattice must be 0 or 1, got %d", value);
         c->dep_lattice = value;
         return FPIC_OK;
+    case FPIC_TUNE_ASYNC:
+        if (value != 0 && value != 1)
+            return set_error(FPIC_EINVAL, "fpic_set_tuning: async must be 0 or 1, got %d", value);
+        c->async = value;
+        return FPIC_OK;
+    case FPIC_TUNE_HOST_STAGING:
+        if (value != 0 && value != 1)
+            return set_error(FPIC_EINVAL, "fpic_set_tuning: host staging must be 0 or 1, got %d", value);
+        c->host_staging = value;
+        return FPIC_OK;
     default:
         return set_error(FPIC_EINVAL, "fpic_set_tuning: unknown key %d", key);
     }
@@ -2906,6 +2938,12 @@ extern "C" int fpic_get_tuning(const fpic_ctx* c, int key, int* value)
         return FPIC_OK;
     case FPIC_TUNE_DEP_LATTICE:
         *value = c->dep_lattice;
+        return FPIC_OK;
+    case FPIC_TUNE_ASYNC:
+        *value = c->async;
+        return FPIC_OK;
+    case FPIC_TUNE_HOST_STAGING:
+        *value = c->host_staging;
         return FPIC_OK;
     default:
         return set_error(FPIC_EINVAL, "fpic_get_tuning: unknown key %d", key);

@@ -95,6 +95,8 @@ FPIC_LEARN_SKIP, FPIC_LEARN_CORRECT = 0, 1
 FPIC_TUNE_IMR_BLOCKS_PER_SM, FPIC_TUNE_DEP_THREADS, FPIC_TUNE_STATIC_FIELDS, FPIC_TUNE_REUSE_SLOPE = 0, 1, 2, 3
 FPIC_TUNE_STAGE_FIELDS = 4
 FPIC_TUNE_DEP_LATTICE = 5
+FPIC_TUNE_ASYNC = 6
+FPIC_TUNE_HOST_STAGING = 7
 FPIC_THETA_HALF, FPIC_THETA_FULL = 0, 1
 
 
@@ -351,12 +353,29 @@ def set_push_before(prm: fpic_push_params, before) -> None:
         prm.before = C.pointer(s)
 
 
-def fpic_push(ctx: Ctx, p: Particles, fields, prm: fpic_push_params, stats: bool = False, stream=None):
-    """One push of every alive particle; returns the stats dict if asked."""
+def _stats_ptr(stats_out):
+    """A page-locked int64 tensor of at least 8 elements as fpic_push_stats*
+    (FPIC_TUNE_ASYNC: the library copies the stats there asynchronously)."""
+    if stats_out.dtype != torch.int64 or stats_out.numel() < 8 or not stats_out.is_pinned():
+        raise ValueError("stats_out must be a pinned int64 tensor of >= 8 elements")
+    return C.cast(C.c_void_p(stats_out.data_ptr()), C.POINTER(fpic_push_stats))
+
+
+def stats_dict(stats_out) -> dict:
+    """The fpic_push_stats fields of an int64 tensor filled through stats_out."""
+    v = stats_out.tolist()
+    return {k: int(v[i]) for i, (k, _) in enumerate(fpic_push_stats._fields_)}
+
+
+def fpic_push(ctx: Ctx, p: Particles, fields, prm: fpic_push_params, stats: bool = False, stream=None,
+              stats_out=None):
+    """One push of every alive particle; returns the stats dict if asked.
+    stats_out (a pinned int64 tensor) receives the stats instead, without
+    synchronising when the context has FPIC_TUNE_ASYNC set."""
     s = p.struct()
-    st = fpic_push_stats() if stats else None
-    rc = lib().fpic_push(ctx.handle, C.byref(s), _fields_arg(fields), C.byref(prm),
-                         C.byref(st) if st is not None else None, _stream(stream))
+    st = fpic_push_stats() if stats and stats_out is None else None
+    sp = _stats_ptr(stats_out) if stats_out is not None else (C.byref(st) if st is not None else None)
+    rc = lib().fpic_push(ctx.handle, C.byref(s), _fields_arg(fields), C.byref(prm), sp, _stream(stream))
     _check(rc)
     return st.as_dict() if st is not None else None
 
@@ -409,11 +428,13 @@ class HostParticles:
 
 
 def fpic_push_host(ctx: Ctx, hp: HostParticles, fields, prm: fpic_push_params, stats: bool = False,
-                   stream=None):
+                   stream=None, stats_out=None):
+    """fpic_push on host arrays; stats_out as in fpic_push (with
+    FPIC_TUNE_ASYNC the call on pinned arrays only enqueues the push)."""
     s = hp.struct()
-    st = fpic_push_stats() if stats else None
-    rc = lib().fpic_push_host(ctx.handle, C.byref(s), _fields_arg(fields), C.byref(prm),
-                              C.byref(st) if st is not None else None, _stream(stream))
+    st = fpic_push_stats() if stats and stats_out is None else None
+    sp = _stats_ptr(stats_out) if stats_out is not None else (C.byref(st) if st is not None else None)
+    rc = lib().fpic_push_host(ctx.handle, C.byref(s), _fields_arg(fields), C.byref(prm), sp, _stream(stream))
     _check(rc)
     return st.as_dict() if st is not None else None
 

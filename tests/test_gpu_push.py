@@ -347,11 +347,12 @@ def test_imr_launch_shape_changes_no_result(newton):
 
 
 @pytest.mark.parametrize("n", [0, 3, 20011])
-@pytest.mark.parametrize("pinned", [True, False])
-def test_host_buffer_push_equals_device_push(n, pinned):
+@pytest.mark.parametrize("pinned,staging", [(True, 0), (True, 1), (False, 0)])
+def test_host_buffer_push_equals_device_push(n, pinned, staging):
     """fpic_push_host gives bitwise the device push's results, for ragged
-    chunk sizes and removed particles, both on pinned host arrays (read and
-    written in place by the kernels) and on pageable ones (chunked copies
+    chunk sizes and removed particles, on pinned host arrays (read and
+    written in place by the kernels, or DMA-staged with
+    FPIC_TUNE_HOST_STAGING) and on pageable ones (chunked copies
     overlapping the explicit pass); the host arrays hold the result
     afterwards."""
     cuda_or_skip()
@@ -361,6 +362,7 @@ def test_host_buffer_push_equals_device_push(n, pinned):
     Fo = O.wald_on_grid(a, 1.0, g)
     ctx = F.fpic_init_metric(1.0, a)
     F.fpic_set_grid(ctx, g)
+    F.fpic_set_tuning(ctx, F.FPIC_TUNE_HOST_STAGING, staging)
     prm = F.push_params(1e-3, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=8e-5, r_max=float(g.rn[-1]),
                         B0pot=1.0)
     if n:
@@ -947,3 +949,56 @@ def test_push_writes_the_state_it_starts_from(F, scheme):
         F.fpic_push(ctx, p, fd, prm)
     F.set_push_before(prm, None)
     F.fpic_push(ctx, p, fd, prm)
+
+
+def test_async_stats_and_host_push_match_the_synchronous_ones(F):
+    """FPIC_TUNE_ASYNC: fpic_push with stats assembled on the device and
+    copied to pinned memory without a wait, and fpic_push_host on pinned
+    arrays returning before its results land, give -- once the stream is
+    synchronised -- bitwise the synchronous calls' states and stats over
+    three steps each."""
+    import torch
+    a = 0.9
+    g = I.wald_grid(96, a)
+    Fo = O.wald_on_grid(a, 1.0, g)
+    ctx = _mk(F, a, g)
+    d, z, q = thermal_state(6007, g, a, theta=0.1, seed=83)
+    n = len(q)
+    H0, _, D0 = O.hamiltonian(1.0, a, 1.0, z, q)
+    alive = (np.arange(n) % 9 != 4).astype(np.uint8)
+    fd = fields_dev(Fo)
+    prm = F.push_params(1e-3, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=8e-5, r_max=float(g.rn[-1]),
+                        B0pot=1.0, imr_newton=True)
+    p1 = make_particles(z, q, H0, D0, H0.copy(), alive.copy())
+    p2 = make_particles(z, q, H0, D0, H0.copy(), alive.copy())
+    ref = [F.fpic_push(ctx, p1, fd, prm, stats=True) for _ in range(3)]
+    F.fpic_set_tuning(ctx, F.FPIC_TUNE_ASYNC, 1)
+    assert F.fpic_get_tuning(ctx, F.FPIC_TUNE_ASYNC) == 1
+    outs = torch.zeros((3, 8), dtype=torch.int64).pin_memory()
+    for i in range(3):
+        assert F.fpic_push(ctx, p2, fd, prm, stats_out=outs[i]) is None
+    torch.cuda.synchronize()
+    assert [F.stats_dict(outs[i]) for i in range(3)] == ref
+    assert np.array_equal(p1.state().cpu().numpy(), p2.state().cpu().numpy())
+    assert ref[0]["n_implicit"] > 0
+
+    def host_set():
+        hp = F.HostParticles(n)
+        for k, col in zip(("r", "th", "ph", "ur", "uth", "uph"), range(6)):
+            getattr(hp, k).copy_(torch_from(z[:, col]))
+        hp.qm.copy_(torch_from(q)); hp.H0.copy_(torch_from(H0)); hp.D0.copy_(torch_from(D0))
+        hp.Hn.copy_(torch_from(H0)); hp.alive.copy_(torch_from(alive))
+        return hp
+    F.fpic_set_tuning(ctx, F.FPIC_TUNE_ASYNC, 0)
+    hs = host_set()
+    ref_h = [F.fpic_push_host(ctx, hs, fd, prm, stats=True) for _ in range(3)]
+    F.fpic_set_tuning(ctx, F.FPIC_TUNE_ASYNC, 1)
+    ha = host_set()
+    outs.zero_()
+    for i in range(3):
+        F.fpic_push_host(ctx, ha, fd, prm, stats_out=outs[i])
+    torch.cuda.synchronize()
+    assert [F.stats_dict(outs[i]) for i in range(3)] == ref_h
+    for k in ("r", "th", "ph", "ur", "uth", "uph", "Hn", "alive", "scheme", "iters"):
+        assert np.array_equal(getattr(hs, k).numpy(), getattr(ha, k).numpy()), k
+    F.fpic_set_tuning(ctx, F.FPIC_TUNE_ASYNC, 0)
