@@ -1166,13 +1166,14 @@ struct CDepK {
     const double *r0, *t0, *ur0, *ut0, *up0;
     const uint8_t* alive0;
     const double *r1, *t1, *ur1, *ut1, *up1, *qm, *w;
+    const double* trig;      // sin tn[0..Nth], then cos tn[0..Nth]
 };
 
 __device__ __forceinline__ void cd_lin(const GridDev& G, double r, double t, int& i, double& fr, int& j, double& ft)
 {
-    const float lr = __logf((float)r);
+    const float lr = __logf(f32_est(r));
     locate(G.rn, G.irn, G.Nr + 1, r, (lr - G.lr0) * G.ilr, i, fr);
-    locate(G.tn, G.itn, G.Nth + 1, t, ((float)t - G.t0) * G.it, j, ft);
+    locate(G.tn, G.itn, G.Nth + 1, t, (f32_est(t) - G.t0) * G.it, j, ft);
 }
 
 // window base cell of each particle alive before the move (C: skipped / removed)
@@ -1193,15 +1194,21 @@ __global__ void k_cdep_keys(CDepK k, uint32_t* key, uint32_t* count, uint32_t C,
     atomicAdd(&count[kk], 1u);
 }
 
-// coordinate dph/dt = alpha gamma^{ph j} u_j / Gamma
-__device__ __forceinline__ double cd_phdot(const BH& bh, double r, double t, double ur, double ut, double up)
+// coordinate dph/dt = alpha gamma^{ph j} u_j / Gamma.  sin/cos th by angle
+// addition from the tabulated node tn[j] of the particle's cell (the step
+// t - tn[j] is under a cell, so its sin / cos - 1 come from the series), and
+// 1/Gamma as one reciprocal square root.
+__device__ __forceinline__ double cd_phdot(const BH& bh, const GridDev& G, const double* trig, int j, double r,
+                                           double t, double ur, double ut, double up)
 {
-    double s, c;
-    sincos(t, &s, &c);
+    double sh, cm;
+    sincos_step(t - G.tn[j], sh, cm);
+    const double s0 = trig[j], c0 = trig[G.Nth + 1 + j];
+    const double s = fma(s0, cm, fma(c0, sh, s0)), c = fma(c0, cm, fma(-s0, sh, c0));
     Geo g;
     geo_eval(bh, r, s, c, g);
-    const double G = sqrt(fma(g.gurr * ur, ur, fma(2.0 * g.gurp * ur, up, fma(g.gutt * ut, ut, fma(g.gupp * up, up, 1.0)))));
-    return g.alpha * fma(g.gurp, ur, g.gupp * up) / G;
+    const double iG = rsqrt(fma(g.gurr * ur, ur, fma(2.0 * g.gurp * ur, up, fma(g.gutt * ut, ut, fma(g.gupp * up, up, 1.0)))));
+    return g.alpha * fma(g.gurp, ur, g.gupp * up) * iG;
 }
 
 // one warp per window-base cell: its particles' 30 window partials, summed
@@ -1236,21 +1243,36 @@ __global__ void k_cdep_cell(CDepK k, const uint32_t* __restrict__ off, const uin
                 Stb[x] = x == eb ? 1.0 - ftb : (x == eb + 1 ? ftb : 0.0);
             }
             const double Q = k.w[p] * k.qm[p];
-            const double phd = 0.5 * (cd_phdot(k.bh, k.r0[p], k.t0[p], k.ur0[p], k.ut0[p], k.up0[p]) +
-                                      cd_phdot(k.bh, k.r1[p], k.t1[p], k.ur1[p], k.ut1[p], k.up1[p]));
+            const double phd = 0.5 * (cd_phdot(k.bh, k.G, k.trig, ja, k.r0[p], k.t0[p], k.ur0[p], k.ut0[p], k.up0[p]) +
+                                      cd_phdot(k.bh, k.G, k.trig, jb, k.r1[p], k.t1[p], k.ur1[p], k.ut1[p], k.up1[p]));
+            // factors shared by the slots: Q S_r^{n+1}, Q (dph/dt) / 2, the
+            // half differences and sums of the weights
+            const double Qh = 0.5 * Q * phd;
+            double QSrb[3], dSr[2], aSr[3], dSt[2], sSt[3];
+#pragma unroll
+            for (int x = 0; x < 3; ++x) {
+                QSrb[x] = Q * Srb[x];
+                aSr[x] = 0.5 * (Sra[x] + Srb[x]);
+                sSt[x] = Sta[x] + Stb[x];
+            }
+#pragma unroll
+            for (int x = 0; x < 2; ++x) {
+                dSr[x] = 0.5 * (Srb[x] - Sra[x]);
+                dSt[x] = Stb[x] - Sta[x];
+            }
 #pragma unroll
             for (int x = 0; x < 3; ++x)
 #pragma unroll
                 for (int y = 0; y < 3; ++y) {
-                    v[CD_Q + 3 * x + y] = Q * (Srb[x] * Stb[y]);
-                    v[CD_P + 3 * x + y] = Q * (0.5 * (Sra[x] * Sta[y] + Srb[x] * Stb[y])) * phd;
+                    v[CD_Q + 3 * x + y] = QSrb[x] * Stb[y];
+                    v[CD_P + 3 * x + y] = Qh * fma(Sra[x], Sta[y], Srb[x] * Stb[y]);
                 }
 #pragma unroll
             for (int y = 0; y < 3; ++y) {
                 double s_ = 0.0;
 #pragma unroll
                 for (int x = 0; x < 2; ++x) {
-                    s_ += 0.5 * (Srb[x] - Sra[x]) * (Sta[y] + Stb[y]);
+                    s_ = fma(dSr[x], sSt[y], s_);
                     v[CD_R + 3 * x + y] = -Q * s_;
                 }
             }
@@ -1259,7 +1281,7 @@ __global__ void k_cdep_cell(CDepK k, const uint32_t* __restrict__ off, const uin
                 double s_ = 0.0;
 #pragma unroll
                 for (int y = 0; y < 2; ++y) {
-                    s_ += 0.5 * (Sra[x] + Srb[x]) * (Stb[y] - Sta[y]);
+                    s_ = fma(aSr[x], dSt[y], s_);
                     v[CD_T + 2 * x + y] = -Q * s_;
                 }
             }
@@ -1347,7 +1369,8 @@ extern "C" int fpic_deposit_conserving(fpic_ctx* c, const fpic_particles* before
     if (rc) return rc;
     double* part = (double*)part_v;
     CDepK k{c->Nr, c->Nth, c->ld, c->G, c->bh, n, before->r, before->th, before->ur, before->uth, before->uph,
-            before->alive, after->r, after->th, after->ur, after->uth, after->uph, after->qm, after->w};
+            before->alive, after->r, after->th, after->ur, after->uth, after->uph, after->qm, after->w,
+            c->d_metric + (size_t)MT_N * c->metric_stride};
     FPIC_CUDA(cudaMemsetAsync(w.count, 0, 4 * ((size_t)C + 2), s));
     FPIC_CUDA(cudaMemsetAsync(w.cursor, 0, 4 * ((size_t)C + 2), s));
     FPIC_CUDA(cudaMemsetAsync(c->d_cnt + CNT_ERR, 0, sizeof(long long), s));
