@@ -1002,3 +1002,42 @@ def test_async_stats_and_host_push_match_the_synchronous_ones(F):
     for k in ("r", "th", "ph", "ur", "uth", "uph", "Hn", "alive", "scheme", "iters"):
         assert np.array_equal(getattr(hs, k).numpy(), getattr(ha, k).numpy()), k
     F.fpic_set_tuning(ctx, F.FPIC_TUNE_ASYNC, 0)
+
+
+def test_pushes_with_async_stats_replay_from_a_cuda_graph(F):
+    """Three hybrid pushes captured in one CUDA graph, each with its stats
+    copied asynchronously into its own pinned slot (FPIC_TUNE_ASYNC), then
+    replayed twice: states and every stat bitwise those of six eager pushes
+    from the same start."""
+    import torch
+    a = 0.9
+    g = I.wald_grid(96, a)
+    Fo = O.wald_on_grid(a, 1.0, g)
+    ctx = _mk(F, a, g)
+    F.fpic_set_tuning(ctx, F.FPIC_TUNE_STATIC_FIELDS, 1)
+    d, z, q = thermal_state(5003, g, a, theta=0.1, seed=91)
+    H0, _, D0 = O.hamiltonian(1.0, a, 1.0, z, q)
+    fd = fields_dev(Fo)
+    prm = F.push_params(1e-3, scheme=F.FPIC_HYB1, implicit=F.FPIC_IMR, thr=8e-5, r_max=float(g.rn[-1]),
+                        B0pot=1.0, imr_newton=True)
+    p1 = make_particles(z, q, H0, D0, H0.copy())
+    p2 = make_particles(z, q, H0, D0, H0.copy())
+    ref = [F.fpic_push(ctx, p1, fd, prm, stats=True) for _ in range(7)]
+    F.fpic_set_tuning(ctx, F.FPIC_TUNE_ASYNC, 1)
+    slots = torch.zeros((3, 8), dtype=torch.int64).pin_memory()
+    F.fpic_push(ctx, p2, fd, prm, stats_out=slots[0])          # eager: scratch in place before capture
+    torch.cuda.synchronize()
+    assert F.stats_dict(slots[0]) == ref[0]
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        for i in range(3):
+            F.fpic_push(ctx, p2, fd, prm, stats_out=slots[i])
+    got = []
+    for _ in range(2):
+        graph.replay()
+        torch.cuda.synchronize()
+        got += [F.stats_dict(slots[i]) for i in range(3)]
+    assert got == ref[1:]
+    assert np.array_equal(p1.state().cpu().numpy(), p2.state().cpu().numpy())
+    assert np.array_equal(p1.alive.cpu().numpy(), p2.alive.cpu().numpy())
+    F.fpic_set_tuning(ctx, F.FPIC_TUNE_ASYNC, 0)
