@@ -54,8 +54,9 @@ struct PushK {
     int imr_newton;         // IMR iteration: Newton form (fpic_push_params.imr_newton)
     double* t;              // nullable per-particle time, advanced by the step each particle took
     // particle arrays in host memory (read over the link): the implicit pass
-    // works from device copies by queue slot of z^n and q/m (7 x n) and of
-    // the iteration counts (n bytes); both null for device-resident particles
+    // works from device copies by queue slot of z^n, q/m, H^n and D_0 (9 x n)
+    // and of the iteration counts (n bytes); both null for device-resident
+    // particles
     double* z0s;
     uint8_t* its;
     int count_alive;        // the explicit pass also counts the alive particles (stats)
@@ -491,13 +492,17 @@ __global__ void __launch_bounds__(128) k_explicit(const __grid_constant__ PushK 
     if (keep) F_at_sc<false, STAGED>(R, y, sn, cn, qm, em, fy, H1, nullptr, &tile);
     else H1 = eval_H_sc(R.bh, y, sn, cn, qm, R.B0pot);
     bool accept = true;
+    double Hn0 = 0.0, D00 = 1.0;     // H^n and D_0, kept for the stash of a rejected particle
     if (MODE >= 1) {
         const double H0 = k.P.H0[p], D0 = k.P.D0[p];
         const double Ht1 = fabs(H1 - H0) / D0;
+        D00 = D0;
         if (k.scheme == FPIC_HYB2) {
             accept = Ht1 < k.thr;
+            if (!accept && k.z0s) Hn0 = k.P.Hn[p];
         } else {
-            const double Htn = fabs(k.P.Hn[p] - H0) / D0;
+            Hn0 = k.P.Hn[p];
+            const double Htn = fabs(Hn0 - H0) / D0;
             accept = (Ht1 - Htn) / dt < k.thr;
         }
     }
@@ -549,6 +554,8 @@ __global__ void __launch_bounds__(128) k_explicit(const __grid_constant__ PushK 
 #pragma unroll
                 for (int i = 0; i < 6; ++i) k.z0s[(size_t)i * k.n + idx] = z0[i];
                 k.z0s[(size_t)6 * k.n + idx] = qm;
+                k.z0s[(size_t)7 * k.n + idx] = Hn0;
+                k.z0s[(size_t)8 * k.n + idx] = D00;
             }
             if (MODE == 2) {
                 trial_store(k, idx, sk, acc, kk, z0, y);
@@ -579,7 +586,8 @@ __global__ void k_order(PushK k)
     const long long qn = k.cnt[CNT_QUEUE];
     for (long long slot = blockIdx.x * (long long)blockDim.x + threadIdx.x; slot < qn;
          slot += (long long)gridDim.x * blockDim.x) {
-        const double th = k.P.th[k.queue[slot]];
+        // host-resident particles: from the device stash, not over the link
+        const double th = k.z0s ? k.z0s[(size_t)1 * k.n + slot] : k.P.th[k.queue[slot]];
         const bool prio = th < AXIS_PRIORITY_TH || th > M_PI - AXIS_PRIORITY_TH;
         const unsigned act = __activemask();
         const unsigned pm = __ballot_sync(act, prio);
@@ -921,7 +929,9 @@ __global__ void __launch_bounds__(256) k_imr_finish(const __grid_constant__ Push
         else H = eval_H_sc(R.bh, z, sn, cn, qm, R.B0pot);
         if (k.substeps > 0 && !k.record) {
             const bool flagged = k.strag_flag[idx] != 0;
-            if (flagged || (k.substep_tol > 0.0 && fabs(H - k.P.Hn[p]) / k.P.D0[p] > k.substep_tol)) {
+            const double Hn_p = st ? k.z0s[(size_t)7 * k.n + idx] : k.P.Hn[p];
+            const double D0_p = st ? k.z0s[(size_t)8 * k.n + idx] : k.P.D0[p];
+            if (flagged || (k.substep_tol > 0.0 && fabs(H - Hn_p) / D0_p > k.substep_tol)) {
                 if (flagged) k.strag_flag[idx] = 0;
                 const unsigned long long e = atomicAdd((unsigned long long*)&k.cnt[CNT_STRAG], 1ull);
                 k.strag[e] = (uint32_t)idx | (flagged ? 0x80000000u : 0u);
@@ -969,7 +979,7 @@ __global__ void __launch_bounds__(128) k_imr_substep(const __grid_constant__ Pus
         }
         const double qm = st ? k.z0s[(size_t)6 * k.n + qi] : k.P.qm[p];
         const bool em = (R.has_fields || R.B0field != 0.0) && qm != 0.0;
-        const double Href = eval_H(R.bh, z0, qm, R.B0pot), D0 = k.P.D0[p];
+        const double Href = eval_H(R.bh, z0, qm, R.B0pot), D0 = st ? k.z0s[(size_t)8 * k.n + qi] : k.P.D0[p];
         double z[6];
 #pragma unroll
         for (int i = 0; i < 6; ++i) z[i] = k.guess[(size_t)i * k.n + p];     // the full step's result
@@ -1672,10 +1682,10 @@ static int push_core(fpic_ctx* c, fpic_particles* p, const double* const fields[
     const long long n = p->n;
     FPIC_CUDA(cudaSetDevice(c->device));
     // guess 6n, sin/cos 2n (doubles) | queue, order, straggler list (u32) |
-    // host state: z^n and q/m by slot 7n (doubles, 16-byte aligned), iteration
-    // counts n (bytes) | straggler flags n (bytes, 16-byte aligned)
+    // host state: z^n, q/m, H^n and D_0 by slot 9n (doubles, 16-byte aligned),
+    // iteration counts n (bytes) | straggler flags n (bytes, 16-byte aligned)
     const size_t base_need = ((size_t)n * (8 * sizeof(double) + 3 * sizeof(uint32_t)) + 15) & ~(size_t)15;
-    const size_t flag_off = (base_need + (host_state ? (size_t)n * (7 * sizeof(double) + 1) : 0) + 15) & ~(size_t)15;
+    const size_t flag_off = (base_need + (host_state ? (size_t)n * (9 * sizeof(double) + 1) : 0) + 15) & ~(size_t)15;
     const size_t need = flag_off + (size_t)n + 256;
     int rc = ensure_scratch(c, need);
     if (rc) return rc;
@@ -1728,7 +1738,7 @@ static int push_core(fpic_ctx* c, fpic_particles* p, const double* const fields[
     k.substep_tol = prm->substep_tol;
     if (host_state) {
         k.z0s = (double*)((char*)c->d_scratch + base_need);
-        k.its = (uint8_t*)(k.z0s + (size_t)n * 7);
+        k.its = (uint8_t*)(k.z0s + (size_t)n * 9);
     }
     k.cnt = c->d_cnt;
     k.learned = nullptr;
