@@ -6,8 +6,9 @@
 //   k_dep_particle  one thread per particle (in cell order): the 4x4
 //                   trapezoidal subvolumes of sqrt(gamma) on each sub-grid
 //                   -> 16 node shares (rho, j^ph, j^r, j^th);
-//   k_dep_cell      one warp per cell, one lane per stencil slot (20):
-//                   fixed-order sum of the cell's particles' shares;
+//   k_dep_cell      one warp per cell, one lane per record row and
+//                   particle parity: fixed-order sums of the cell's
+//                   particles' shares into its 20 stencil slots;
 //   k_dep_node      one thread per node: fixed-order sum of the slots of the
 //                   (up to six) cells touching it, / (2 pi V_dual).
 // The FDTD is HBM-bound; its metric factors come from tables built once.
@@ -745,47 +746,91 @@ __global__ void __launch_bounds__(256) k_dep_particle_ff(DepK k)
 
 // Slots of a cell (i0, j0): rho[a + 2b] (0..3), j^ph[a + 2b] (4..7),
 // j^r[k + 3b] at half-r node i0 - 1 + k (8..13), j^th[a + 2k] at half-th
-// node j0 - 1 + k (14..19).  Record row feeding slot q of a particle with
-// offsets (ko, kt), or -1 when the particle does not touch that slot.
-__device__ __forceinline__ int slot_row(int q, uint32_t cd)
+// node j0 - 1 + k (14..19).  A particle with offsets (ko, kt) (each 0 or 1)
+// puts record rows 0..7 in slots 0..7, rows 8 + 2b and 9 + 2b in slots
+// 8 + 3b + ko and 9 + 3b + ko, rows 12 + a and 14 + a in slots 14 + a + 2 kt
+// and 16 + a + 2 kt.
+//
+// One warp per cell, its particles 32 at a time: every lane loads one
+// particle's 16 shares and code (coalesced, no load depending on another)
+// into shared memory; then lane l sums record row l / 2 over the group's
+// particles of parity l & 1, into one of two accumulators chosen by the
+// particle's offset bit (ko for the j^r rows, kt for the j^th rows, none
+// for rows 0..7): 16 FP64 additions per particle, each lane busy.  The
+// accumulator is chosen by integer selects, so each addition is one FP64
+// instruction.  At the end the two parities are added and lane q < 20
+// assembles slot q from at most two (row, accumulator) pairs.  Every
+// addition has a fixed order: bitwise reproducible.
+constexpr int DEP_CELL_WARPS = 8, DEP_CELL_LD = 33;   // row stride 33: conflict-free shared-memory columns
+
+__device__ __forceinline__ double sel_bits(bool p, double a, double b)
 {
-    if (q < 8) return q;
-    if (q < 14) {
-        const int kk = (q - 8) % 3, b = (q - 8) / 3, ko = cd & 3;
-        return kk == ko ? 8 + 2 * b : (kk == ko + 1 ? 9 + 2 * b : -1);
-    }
-    const int a = (q - 14) & 1, kk = (q - 14) >> 1, kt = (cd >> 2) & 3;
-    return kk == kt ? 12 + a : (kk == kt + 1 ? 14 + a : -1);
+    double r;
+    asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\tselp.b64 %0, %1, %2, q;\n\t}"
+        : "=d"(r) : "d"(a), "d"(b), "r"((unsigned)p));
+    return r;
 }
 
-// One warp per cell; lane q < 20 owns slot q and adds the cell's particles
-// in their sorted order (fixed order: bitwise reproducible).  Four
-// particles' records are loaded ahead of the additions.
-__global__ void __launch_bounds__(256) k_dep_cell(const double* __restrict__ rec, const uint32_t* __restrict__ code,
-                                                   const uint32_t* __restrict__ off, double* __restrict__ part,
-                                                   long long n, uint32_t C)
+__global__ void __launch_bounds__(32 * DEP_CELL_WARPS) k_dep_cell(const double* __restrict__ rec,
+                                                                   const uint32_t* __restrict__ code,
+                                                                   const uint32_t* __restrict__ off,
+                                                                   double* __restrict__ part, long long n, uint32_t C)
 {
-    const long long cell = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    const int q = threadIdx.x & 31;
-    if (cell >= C || q >= 20) return;
+    __shared__ double sv[DEP_CELL_WARPS][16 * DEP_CELL_LD];
+    __shared__ uint32_t sc[DEP_CELL_WARPS][32];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long cell = blockIdx.x * (long long)DEP_CELL_WARPS + wid;
+    if (cell >= C) return;                  // whole warps: one cell per warp
+    double* v = sv[wid];
+    uint32_t* cw = sc[wid];
     const uint32_t b0 = off[cell], b1 = off[cell + 1];
-    double acc = 0.0;
-    uint32_t a = b0;
-    for (; a + 4 <= b1; a += 4) {
-        double v[4];
+    const int row = lane >> 1, par = lane & 1;
+    const int bsh = row >= 12 ? 2 : 0;      // the offset bit this row splits on
+    const uint32_t bmask = row >= 8 ? 1u : 0u;
+    double acc0 = 0.0, acc1 = 0.0;
+    for (uint32_t base = b0; base < b1; base += 32) {
+        const uint32_t cnt = min(32u, b1 - base);
+        const bool live = (uint32_t)lane < cnt;
+        const size_t a = (size_t)base + lane;
+        double x[16];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int row = slot_row(q, __ldg(code + a + u));
-            v[u] = row >= 0 ? __ldg(rec + (size_t)row * n + a + u) : 0.0;
+        for (int q = 0; q < 16; ++q) x[q] = live ? __ldg(rec + (size_t)q * n + a) : 0.0;
+        const uint32_t cd = live ? __ldg(code + a) : 0u;
+        __syncwarp();                       // the previous group's reads are done
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q * DEP_CELL_LD + lane] = x[q];
+        cw[lane] = cd;
+        __syncwarp();
+        const int kend = (int)(cnt + 1) >> 1;
+        for (int k = 0; k < kend; ++k) {
+            const int pp = 2 * k + par;     // a particle past the group's end holds zeros
+            const double y = v[row * DEP_CELL_LD + pp];
+            const bool bit = ((cw[pp] >> bsh) & bmask) != 0u;
+            const double s = sel_bits(bit, acc1, acc0) + y;
+            acc1 = sel_bits(bit, s, acc1);
+            acc0 = sel_bits(bit, acc0, s);
         }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) acc += v[u];
     }
-    for (; a < b1; ++a) {
-        const int row = slot_row(q, __ldg(code + a));
-        if (row >= 0) acc += __ldg(rec + (size_t)row * n + a);
+    acc0 += __shfl_xor_sync(0xffffffffu, acc0, 1);
+    acc1 += __shfl_xor_sync(0xffffffffu, acc1, 1);
+    // slot q = lane: rows ra (accumulator ua) and rb (accumulator 0, if any)
+    int ra = lane, rb = -1;
+    bool ua = false;
+    if (lane >= 8 && lane < 14) {
+        const int b = (lane - 8) / 3, kk = (lane - 8) % 3;
+        ra = kk == 2 ? 9 + 2 * b : 8 + 2 * b;
+        ua = kk != 0;
+        rb = kk == 1 ? 9 + 2 * b : -1;
+    } else if (lane >= 14 && lane < 20) {
+        const int aa = (lane - 14) & 1, kk = (lane - 14) >> 1;
+        ra = kk == 2 ? 14 + aa : 12 + aa;
+        ua = kk != 0;
+        rb = kk == 1 ? 14 + aa : -1;
     }
-    part[(size_t)q * C + cell] = acc;
+    const int la = 2 * (ra & 15), lb = 2 * (rb & 15);
+    const double xa0 = __shfl_sync(0xffffffffu, acc0, la), xa1 = __shfl_sync(0xffffffffu, acc1, la);
+    const double xb0 = __shfl_sync(0xffffffffu, acc0, lb);
+    if (lane < 20) part[(size_t)lane * C + cell] = (ua ? xa1 : xa0) + (rb >= 0 ? xb0 : 0.0);
 }
 
 struct NodeK {
@@ -1133,7 +1178,8 @@ extern "C" int fpic_deposit(fpic_ctx* c, fpic_particles* p, double* rho, double*
         if (c->dep_lattice) k_dep_particle_ff<<<nb, dt_, 0, s>>>(k);
         else k_dep_particle<<<nb, dt_, 0, s>>>(k);
     }
-    k_dep_cell<<<(unsigned)(((long long)C * 32 + 255) / 256), 256, 0, s>>>(w.rec, w.code, w.off, w.part, n > 0 ? n : 1, C);
+    k_dep_cell<<<(unsigned)(((long long)C + DEP_CELL_WARPS - 1) / DEP_CELL_WARPS), 32 * DEP_CELL_WARPS, 0, s>>>(
+        w.rec, w.code, w.off, w.part, n > 0 ? n : 1, C);
     NodeK nk{c->Nr, c->Nth, c->ld, w.part, C, tabs_of(c), rho, jr, jth, jph};
     k_dep_node<<<dim3(1, c->Nr + 1), 256, 0, s>>>(nk);
     FPIC_CUDA(cudaGetLastError());
