@@ -130,25 +130,38 @@ struct SortBufs {
     void* tmp;
 };
 
+// count[k] += 1 for each valid lane's key k, one atomic per distinct key of
+// the warp (particles arrive nearly sorted by cell: most of a warp shares one
+// key, and same-address atomics would serialise).  Every lane of the warp
+// calls it; an invalid lane's 64-bit key matches no valid one.
+__device__ __forceinline__ void count_key(uint32_t* count, uint32_t k, bool valid)
+{
+    const unsigned peers = __match_any_sync(0xffffffffu, valid ? (unsigned long long)k : (1ull << 32));
+    if (valid && (threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1)) atomicAdd(&count[k], (unsigned)__popc(peers));
+}
+
 __global__ void k_keys(GridDev G, const double* r, const double* th, const uint8_t* alive, uint32_t* key,
                        uint32_t* cell, uint32_t* count, long long n, uint32_t C)
 {
     const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    int i, j;
-    double w;
-    const double rr = r[p];
-    double tt, thv;
-    int mh;
-    theta_views(G, th[p], tt, thv, mh);
-    const float lr = __logf((float)rr);
-    locate(G.rn, G.irn, G.Nr + 1, rr, (lr - G.lr0) * G.ilr, i, w);
-    locate(G.tn, G.itn, G.Nth + 1, tt, ((float)tt - G.t0) * G.it, j, w);
-    const uint32_t c = (uint32_t)i * (uint32_t)G.Nth + (uint32_t)j;
-    if (cell) cell[p] = c;
-    const uint32_t k = alive[p] ? c : C;
-    key[p] = k;
-    atomicAdd(&count[k], 1u);
+    const bool valid = p < n;
+    uint32_t k = 0;
+    if (valid) {
+        int i, j;
+        double w;
+        const double rr = r[p];
+        double tt, thv;
+        int mh;
+        theta_views(G, th[p], tt, thv, mh);
+        const float lr = __logf((float)rr);
+        locate(G.rn, G.irn, G.Nr + 1, rr, (lr - G.lr0) * G.ilr, i, w);
+        locate(G.tn, G.itn, G.Nth + 1, tt, ((float)tt - G.t0) * G.it, j, w);
+        const uint32_t c = (uint32_t)i * (uint32_t)G.Nth + (uint32_t)j;
+        if (cell) cell[p] = c;
+        k = alive[p] ? c : C;
+        key[p] = k;
+    }
+    count_key(count, k, valid);
 }
 
 // exclusive scan of count[0..m) into off[0..m], m + 1 outputs; three phases
@@ -180,18 +193,41 @@ __global__ void k_scan_blocks(const uint32_t* in, uint32_t* out, uint32_t* bsum,
     if (threadIdx.x == SCAN_B - 1) bsum[blockIdx.x] = sh[SCAN_B - 1];
 }
 
-__global__ void k_scan_bsum(uint32_t* bsum, int nb)
+// In-place exclusive scan of bsum[0..nb), bsum[nb] = the total: one block of
+// SCAN_B threads, each over a contiguous run of ceil(nb / SCAN_B) entries.
+__global__ void __launch_bounds__(SCAN_B) k_scan_bsum(uint32_t* bsum, int nb)
 {
-    // single thread: nb is at most a few thousand
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        uint32_t run = 0;
-        for (int b = 0; b < nb; ++b) {
-            const uint32_t t = bsum[b];
-            bsum[b] = run;
-            run += t;
-        }
-        bsum[nb] = run;
+    __shared__ uint32_t wsum[SCAN_B / 32];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int per = (nb + SCAN_B - 1) / SCAN_B;
+    const int lo = min(nb, t * per), hi = min(nb, lo + per);
+    uint32_t tot = 0;
+    for (int b = lo; b < hi; ++b) tot += bsum[b];
+    uint32_t inc = tot;                 // inclusive scan of the thread totals
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
     }
+    if (lane == 31) wsum[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t w = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    uint32_t run = inc - tot + (wid > 0 ? wsum[wid - 1] : 0u);
+    for (int b = lo; b < hi; ++b) {
+        const uint32_t v = bsum[b];
+        bsum[b] = run;
+        run += v;
+    }
+    if (t == SCAN_B - 1) bsum[nb] = run;
 }
 
 __global__ void k_scan_add(uint32_t* out, const uint32_t* bsum, long long m, int nb)
@@ -204,9 +240,16 @@ __global__ void k_scan_add(uint32_t* out, const uint32_t* bsum, long long m, int
 __global__ void k_scatter(const uint32_t* key, const uint32_t* off, uint32_t* cursor, uint32_t* perm, long long n)
 {
     const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    const uint32_t k = key[p];
-    perm[off[k] + atomicAdd(&cursor[k], 1u)] = (uint32_t)p;
+    const bool valid = p < n;
+    const uint32_t k = valid ? key[p] : 0u;
+    // one atomic per distinct key of the warp; lanes of a key take
+    // consecutive places in lane order (every lane takes part in the match)
+    const unsigned peers = __match_any_sync(0xffffffffu, valid ? (unsigned long long)k : (1ull << 32));
+    const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (valid && lane == leader) base = atomicAdd(&cursor[k], (unsigned)__popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (valid) perm[off[k] + base + (uint32_t)__popc(peers & ((1u << lane) - 1u))] = (uint32_t)p;
 }
 
 // Order every bucket by particle index (rank = number of smaller indices in
@@ -218,6 +261,14 @@ __global__ void k_bucket_rank(const uint32_t* off, const uint32_t* perm, uint32_
     const int lane = threadIdx.x & 31;
     if (warp >= C) return;
     const uint32_t b0 = off[warp], b1 = off[warp + 1];
+    // a bucket already in index order (the usual case: nearly sorted input,
+    // whole warps placed in lane order) is copied as it is
+    bool sorted = true;
+    for (uint32_t a = b0 + lane; a + 1 < b1; a += 32) sorted = sorted && perm[a] < perm[a + 1];
+    if (__all_sync(0xffffffffu, sorted)) {
+        for (uint32_t a = b0 + lane; a < b1; a += 32) perm2[a] = perm[a];
+        return;
+    }
     for (uint32_t a = b0 + lane; a < b1; a += 32) {
         const uint32_t x = perm[a];
         uint32_t rank = 0;
@@ -227,18 +278,63 @@ __global__ void k_bucket_rank(const uint32_t* off, const uint32_t* perm, uint32_
 }
 
 // Removed particles keep their relative order: position = off[C] + number of
-// removed particles with a smaller index (block scan of the flags).
-__global__ void k_dead_flags(const uint8_t* alive, uint32_t* flag, long long n)
+// removed particles with a smaller index.  Blocks of DEAD_T threads cover
+// DEAD_PER x DEAD_T consecutive particles (thread t takes particles
+// base + k DEAD_T + t); k_dead_count writes each block's count, an exclusive
+// scan turns the counts into block offsets, and k_dead_place ranks the
+// block's removed particles by ballots in index order.
+constexpr int DEAD_T = 256, DEAD_PER = 16, DEAD_W = DEAD_T / 32;
+
+__global__ void __launch_bounds__(DEAD_T) k_dead_count(const uint8_t* alive, uint32_t* bcnt, long long n)
 {
-    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (p < n) flag[p] = alive[p] ? 0u : 1u;
+    __shared__ uint32_t ws[DEAD_W];
+    const long long base = (long long)blockIdx.x * DEAD_PER * DEAD_T;
+    uint32_t d = 0;
+#pragma unroll
+    for (int k = 0; k < DEAD_PER; ++k) {
+        const long long q = base + (long long)k * DEAD_T + threadIdx.x;
+        d += (q < n && !alive[q]) ? 1u : 0u;
+    }
+    d = __reduce_add_sync(0xffffffffu, d);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = d;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < DEAD_W; ++w) t += ws[w];
+        bcnt[blockIdx.x] = t;
+    }
 }
 
-__global__ void k_dead_place(const uint8_t* alive, const uint32_t* pos, const uint32_t* off, uint32_t* perm2,
-                             long long n, uint32_t C)
+__global__ void __launch_bounds__(DEAD_T) k_dead_place(const uint8_t* alive, const uint32_t* boff,
+                                                       const uint32_t* off, uint32_t* perm2, long long n, uint32_t C)
 {
-    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (p < n && !alive[p]) perm2[off[C] + pos[p]] = (uint32_t)p;
+    __shared__ uint32_t pre[DEAD_PER * DEAD_W];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const long long base = (long long)blockIdx.x * DEAD_PER * DEAD_T;
+    unsigned m[DEAD_PER];
+#pragma unroll
+    for (int k = 0; k < DEAD_PER; ++k) {
+        const long long q = base + (long long)k * DEAD_T + threadIdx.x;
+        m[k] = __ballot_sync(0xffffffffu, q < n && !alive[q]);
+        if (lane == 0) pre[k * DEAD_W + wid] = (uint32_t)__popc(m[k]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {             // exclusive prefix in index order (k, then warp)
+        uint32_t run = 0;
+        for (int e = 0; e < DEAD_PER * DEAD_W; ++e) {
+            const uint32_t v = pre[e];
+            pre[e] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+    const uint32_t at = off[C] + boff[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < DEAD_PER; ++k)
+        if ((m[k] >> lane) & 1u) {
+            const long long q = base + (long long)k * DEAD_T + threadIdx.x;
+            perm2[at + pre[k * DEAD_W + wid] + (uint32_t)__popc(m[k] & ((1u << lane) - 1u))] = (uint32_t)q;
+        }
 }
 
 template <typename T>
@@ -294,7 +390,7 @@ static int scan_u32(const uint32_t* in, uint32_t* out, uint32_t* bsum, long long
 {
     const int nb = (int)((m + SCAN_B * SCAN_PER - 1) / (SCAN_B * SCAN_PER));
     k_scan_blocks<<<nb, SCAN_B, 0, s>>>(in, out, bsum, m);
-    k_scan_bsum<<<1, 32, 0, s>>>(bsum, nb);
+    k_scan_bsum<<<1, SCAN_B, 0, s>>>(bsum, nb);
     k_scan_add<<<(unsigned)((m + 255) / 256 + 1), 256, 0, s>>>(out, bsum, m, nb);
     return check_cuda(cudaGetLastError(), "scan");
 }
@@ -359,10 +455,11 @@ static int sort_impl(fpic_ctx* c, fpic_particles* p, Work& w, cudaStream_t s, do
     if (rc) return rc;
     k_scatter<<<nb, 256, 0, s>>>(w.key, w.off, w.cursor, w.perm, n);
     k_bucket_rank<<<(unsigned)(((long long)C * 32 + 255) / 256), 256, 0, s>>>(w.off, w.perm, w.perm2, C);
-    k_dead_flags<<<nb, 256, 0, s>>>(p->alive, w.flag, n);
-    rc = scan_u32(w.flag, w.pos, w.bsum, n, s);
-    if (rc) return rc;
-    k_dead_place<<<nb, 256, 0, s>>>(p->alive, w.pos, w.off, w.perm2, n, C);
+    // removed particles: per-block counts in w.pos (nbd + 1 <= n + 1 entries)
+    const unsigned nbd = (unsigned)((n + DEAD_PER * DEAD_T - 1) / (DEAD_PER * DEAD_T));
+    k_dead_count<<<nbd, DEAD_T, 0, s>>>(p->alive, w.pos, n);
+    k_scan_bsum<<<1, SCAN_B, 0, s>>>(w.pos, (int)nbd);
+    k_dead_place<<<nbd, DEAD_T, 0, s>>>(p->alive, w.pos, w.off, w.perm2, n, C);
     FPIC_CUDA(cudaGetLastError());
     double* d8[] = {p->r, p->th, p->ph, p->ur, p->uth, p->uph, p->qm, p->w, p->H0, p->D0, p->Hn};
     if (stage) {
@@ -1226,9 +1323,9 @@ __device__ __forceinline__ void cd_lin(const GridDev& G, double r, double t, int
 __global__ void k_cdep_keys(CDepK k, uint32_t* key, uint32_t* count, uint32_t C, long long* n_skip)
 {
     const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (p >= k.n) return;
+    const bool valid = p < k.n;
     uint32_t kk = C;
-    if (k.alive0[p]) {
+    if (valid && k.alive0[p]) {
         int ia, ja, ib, jb;
         double f;
         cd_lin(k.G, k.r0[p], k.t0[p], ia, f, ja, f);
@@ -1236,8 +1333,8 @@ __global__ void k_cdep_keys(CDepK k, uint32_t* key, uint32_t* count, uint32_t C,
         if (abs(ia - ib) > 1 || abs(ja - jb) > 1) atomicAdd((unsigned long long*)n_skip, 1ull);
         else kk = (uint32_t)min(ia, ib) * (uint32_t)k.Nth + (uint32_t)min(ja, jb);
     }
-    key[p] = kk;
-    atomicAdd(&count[kk], 1u);
+    if (valid) key[p] = kk;
+    count_key(count, kk, valid);
 }
 
 // coordinate dph/dt = alpha gamma^{ph j} u_j / Gamma.  sin/cos th by angle

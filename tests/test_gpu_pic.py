@@ -48,6 +48,12 @@ def test_sort_is_the_stable_argsort(F):
     assert np.array_equal(p.Hn.cpu().numpy(), perm.astype(float))
     assert np.array_equal(p.alive.cpu().numpy(), alive[perm])
     assert np.array_equal(p.cell.cpu().numpy().view(np.uint32), cell[perm].astype(np.uint32))
+    # sorting the sorted set again (every bucket already in index order, the
+    # usual case between PIC steps) leaves every array as it is
+    F.fpic_sort(ctx, p)
+    assert np.array_equal(p.state().cpu().numpy(), z[perm])
+    assert np.array_equal(p.Hn.cpu().numpy(), perm.astype(float))
+    assert np.array_equal(p.alive.cpu().numpy(), alive[perm])
 
 
 def test_deposit_permutes_every_array_like_fpic_sort(F):
