@@ -58,13 +58,22 @@ __device__ __forceinline__ double sqrt_dep(double x)
 // h^5 / h^6 when |h| < 2^-10 (the first omitted terms are below 2^-62 of
 // sin h and 2^-63 of cos h - 1), through h^7 / h^8 when |h| < 2^-7 (below
 // 1e-22 relative), else libm.
+// |x| < 2^e for a power of two 2^e whose double has high word hi_pow2 (and
+// low word 0): the same result as the FP64 compare (false for a NaN), from
+// the high word by one integer compare, off the FP64 pipe.
+__device__ __forceinline__ bool abs_below_pow2(double x, unsigned hi_pow2)
+{
+    return ((unsigned)__double2hiint(x) & 0x7fffffffu) < hi_pow2;
+}
+constexpr unsigned HI_2M10 = 0x3f500000u, HI_2M7 = 0x3f800000u;   // 2^-10, 2^-7
+
 __device__ __forceinline__ void sincos_step(double h, double& sh, double& cm)
 {
-    if (fabs(h) < 0.0009765625) {
+    if (abs_below_pow2(h, HI_2M10)) {
         const double h2 = h * h;
         sh = h * fma(h2, fma(h2, 1.0 / 120.0, -1.0 / 6.0), 1.0);
         cm = h2 * fma(h2, fma(h2, -1.0 / 720.0, 1.0 / 24.0), -0.5);
-    } else if (fabs(h) < 0.0078125) {
+    } else if (abs_below_pow2(h, HI_2M7)) {
         const double h2 = h * h;
         sh = h * fma(h2, fma(h2, fma(h2, -1.0 / 5040.0, 1.0 / 120.0), -1.0 / 6.0), 1.0);
         cm = h2 * fma(h2, fma(h2, fma(h2, 1.0 / 40320.0, -1.0 / 720.0), 1.0 / 24.0), -0.5);
@@ -82,7 +91,7 @@ __device__ __forceinline__ void sincos_step(double h, double& sh, double& cm)
 __device__ __forceinline__ void sincos_near(double t0, double s0, double c0, double t, double& s, double& c)
 {
     const double d = t - t0;
-    if (fabs(d) < 0.0078125) {
+    if (abs_below_pow2(d, HI_2M7)) {
         double sd, cm;
         sincos_step(d, sd, cm);
         s = fma(s0, cm, fma(c0, sd, s0));

@@ -50,6 +50,7 @@ struct PushK {
     const RunK* runs;       // batched push: run table (nruns > 0), particle ranges [begin, end)
     int nruns;
     double dt, thr, tol, dg_eps;
+    double d6, thr_dt, imp_ratio;   // dt / 6, thr dt and dt_imp / dt, formed once on the host
     double dt_imp;          // step of the implicit solves (the hybrid's partner: fpic_push_params.dt_implicit)
     int imr_newton;         // IMR iteration: Newton form (fpic_push_params.imr_newton)
     double* t;              // nullable per-particle time, advanced by the step each particle took
@@ -98,6 +99,15 @@ struct PushK {
     double* slope;
     int slope_cold;         // the cache holds nothing for these particles: do not look
 };
+
+// Per-push constants the kernels would otherwise divide for per particle
+// (the same IEEE quotients, once).
+static void push_constants(PushK& k)
+{
+    k.d6 = k.dt / 6.0;
+    k.thr_dt = k.thr * k.dt;
+    k.imp_ratio = k.dt_imp / k.dt;
+}
 
 // Rows of the slope cache: the state z^{n+1} and q/m it was computed for
 // (the validity tag, compared bit for bit), F(z^{n+1}), sin and cos th^{n+1}.
@@ -481,7 +491,7 @@ __global__ void __launch_bounds__(128) k_explicit(const __grid_constant__ PushK 
     for (int i = 0; i < 6; ++i) { acc[i] = fma(2.0, kk[i], acc[i]); y[i] = fma(dt, kk[i], z0[i]); }
     sincos_near(z0[1], s0, c0, y[1], sn, cn);
     F_at_sc<false, STAGED>(R, y, sn, cn, qm, em, kk, Hd, nullptr, &tile);
-    const double d6 = dt / 6.0;
+    const double d6 = k.d6;
 #pragma unroll
     for (int i = 0; i < 6; ++i) y[i] = fma(d6, acc[i] + kk[i], z0[i]);
     sincos_near(z0[1], s0, c0, y[1], sn, cn);
@@ -494,16 +504,20 @@ __global__ void __launch_bounds__(128) k_explicit(const __grid_constant__ PushK 
     bool accept = true;
     double Hn0 = 0.0, D00 = 1.0;     // H^n and D_0, kept for the stash of a rejected particle
     if (MODE >= 1) {
+        // Hyb2: Ht^{n+1} = |H1 - H0| / D0 < thr; Hyb1: (Ht^{n+1} - Ht^n) / dt
+        // < thr.  With D0, dt > 0 both are taken as products,
+        // |H1 - H0| < thr D0 and |H1 - H0| - |H^n - H0| < (thr dt) D0: the
+        // same decisions up to the rounding of the quotients, without three
+        // FP64 divisions per particle.
         const double H0 = k.P.H0[p], D0 = k.P.D0[p];
-        const double Ht1 = fabs(H1 - H0) / D0;
+        const double e1 = fabs(H1 - H0);
         D00 = D0;
         if (k.scheme == FPIC_HYB2) {
-            accept = Ht1 < k.thr;
+            accept = e1 < k.thr * D0;
             if (!accept && k.z0s) Hn0 = k.P.Hn[p];
         } else {
             Hn0 = k.P.Hn[p];
-            const double Htn = fabs(Hn0 - H0) / D0;
-            accept = (Ht1 - Htn) / dt < k.thr;
+            accept = e1 - fabs(Hn0 - H0) < k.thr_dt * D0;
         }
     }
     const float label = accept ? 0.f : 1.f;
@@ -543,7 +557,7 @@ __global__ void __launch_bounds__(128) k_explicit(const __grid_constant__ PushK 
             } else {
                 // adaptive step: the trial's increment scaled to the implicit step
                 // (rounded product, then sum: the same value as the plain C form)
-                const double ratio = k.dt_imp / dt;
+                const double ratio = k.imp_ratio;
 #pragma unroll
                 for (int i = 0; i < 6; ++i)
                     k.guess[(size_t)i * k.n + p] = __dadd_rn(z0[i], __dmul_rn(__dsub_rn(y[i], z0[i]), ratio));
@@ -1700,6 +1714,7 @@ static int push_core(fpic_ctx* c, fpic_particles* p, const double* const fields[
     k.imr_newton = prm->imr_newton ? 1 : 0;
     k.t = prm->t;
     k.thr = prm->thr;
+    push_constants(k);
     k.tol = prm->tol;
     k.dg_eps = prm->dg_eps;
     k.run.B0pot = prm->B0pot;
@@ -2052,6 +2067,7 @@ extern "C" int fpic_push_noalloc(double M, double a, fpic_particles* p, const fp
     k.imr_newton = prm->imr_newton ? 1 : 0;
     k.t = prm->t;
     k.thr = prm->thr;
+    push_constants(k);
     k.tol = prm->tol;
     k.dg_eps = prm->dg_eps;
     k.run.B0pot = prm->B0pot;
@@ -2260,6 +2276,7 @@ static void fill_pushk(PushK& k, fpic_ctx* c, fpic_particles* p, const double* c
     k.imr_newton = prm->imr_newton ? 1 : 0;
     k.t = nullptr;
     k.thr = prm->thr;
+    push_constants(k);
     k.tol = prm->tol;
     k.dg_eps = prm->dg_eps;
     k.run.B0pot = prm->B0pot;
@@ -2779,6 +2796,7 @@ static int push_batched(const fpic_run* runs, int nruns, fpic_mlp* m, fpic_parti
     k.imr_newton = prm->imr_newton ? 1 : 0;
     k.t = prm->t;
     k.thr = prm->thr;
+    push_constants(k);
     k.tol = prm->tol;
     k.dg_eps = prm->dg_eps;
     k.scheme = prm->scheme;
