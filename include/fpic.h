@@ -427,7 +427,9 @@ int fpic_get_tuning(const fpic_ctx *ctx, int key, int *value);
  *         below 2^-7, libm above), as used by the angle-addition updates;
  *   fn 3: y = sqrt(x) in the deposit's paired-FP32 form (x split into two
  *         floats, the result's two floats summed in FP64);
- *   fn 4: as fn 2, in the deposit's paired-FP32 form.
+ *   fn 4: as fn 2, in the deposit's paired-FP32 form;
+ *   fn 5: 1/sqrt(x) by the hardware estimate and the second-order binomial
+ *         correction (push metric lapse and 1/Gamma), x > 0 normal.
  * Errors: FPIC_EINVAL (fn out of range, n < 0, NULL with n > 0). */
 int fpic_probe_math(int fn, const double *x, double *y, long long n, void *stream);
 

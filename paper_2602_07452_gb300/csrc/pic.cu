@@ -705,7 +705,7 @@ __global__ void __launch_bounds__(256) k_dep_particle(DepK k)
     geo_eval(k.bh, r, s, c, g);
     const double ur = k.ur[p], ut = k.uth[p], up = k.uph[p];
     const double Ur = fma(g.gurr, ur, g.gurp * up), Ut = g.gutt * ut, Up = fma(g.gurp, ur, g.gupp * up);
-    const double iG = rsqrt(fma(ur, Ur, fma(ut, Ut, fma(up, Up, 1.0))));
+    const double iG = rsqrt_nr(fma(ur, Ur, fma(ut, Ut, fma(up, Up, 1.0))));
     const double Q = k.w[p] * k.qm[p];
     const double vr = Ur * iG, vt = Ut * iG, vp = Up * iG;
     // clamped positions and cells on the integer and half node lists
@@ -779,7 +779,7 @@ __global__ void __launch_bounds__(256) k_dep_particle_ff(DepK k)
     geo_eval(k.bh, r, s, c, g);
     const double ur = k.ur[p], ut = k.uth[p], up = k.uph[p];
     const double Ur = fma(g.gurr, ur, g.gurp * up), Ut = g.gutt * ut, Up = fma(g.gurp, ur, g.gupp * up);
-    const double iG = rsqrt(fma(ur, Ur, fma(ut, Ut, fma(up, Up, 1.0))));
+    const double iG = rsqrt_nr(fma(ur, Ur, fma(ut, Ut, fma(up, Up, 1.0))));
     const double Q = k.w[p] * k.qm[p];
     const double vr = Ur * iG, vt = Ut * iG, vp = Up * iG;
     // clamped positions and cells on the integer and half node lists
@@ -1350,7 +1350,7 @@ __device__ __forceinline__ double cd_phdot(const BH& bh, const GridDev& G, const
     const double s = fma(s0, cm, fma(c0, sh, s0)), c = fma(c0, cm, fma(-s0, sh, c0));
     Geo g;
     geo_eval(bh, r, s, c, g);
-    const double iG = rsqrt(fma(g.gurr * ur, ur, fma(2.0 * g.gurp * ur, up, fma(g.gutt * ut, ut, fma(g.gupp * up, up, 1.0)))));
+    const double iG = rsqrt_nr(fma(g.gurr * ur, ur, fma(2.0 * g.gurp * ur, up, fma(g.gutt * ut, ut, fma(g.gupp * up, up, 1.0)))));
     return g.alpha * fma(g.gurp, ur, g.gupp * up) * iG;
 }
 

@@ -32,6 +32,22 @@ def test_reciprocal_within_two_ulp(F):
     assert rel.max() <= 2 * ULP, rel.max()
 
 
+def test_reciprocal_sqrt_within_two_ulp(F):
+    """1/sqrt(x) from the hardware estimate and the second-order binomial
+    correction (the push's lapse and 1/Gamma), over 60 decades, within two
+    ulp of an extended-precision reference (the first omitted term, of order
+    e^3, is far below double rounding)."""
+    x = _samples(1e-30, 1e30, 1 << 20, 5)
+    x[:4] = [1.0, 4.0, 2.0, 1.0 + 2.0 ** -52]    # exact squares and the next double above 1
+    got = F.fpic_probe_math(5, dev(x)).cpu().numpy()
+    ref = 1.0 / np.sqrt(x.astype(np.longdouble))
+    if np.finfo(np.longdouble).nmant < 60:
+        pytest.skip("no extended precision on this host")
+    rel = np.abs((got.astype(np.longdouble) - ref) / ref).astype(np.float64)
+    print("rsqrt max rel err", rel.max(), "= 2^%.1f" % np.log2(rel.max() + 1e-300))
+    assert rel.max() <= 2 * ULP, rel.max()
+
+
 def test_deposit_sqrt_error_bound(F):
     """One Goldschmidt step on the hardware estimate: relative error far
     below the deposit's 1e-10 tolerance (bound 2^-38; 2^-39.6 measured) over the radicands of
