@@ -429,7 +429,9 @@ int fpic_get_tuning(const fpic_ctx *ctx, int key, int *value);
  *         floats, the result's two floats summed in FP64);
  *   fn 4: as fn 2, in the deposit's paired-FP32 form;
  *   fn 5: 1/sqrt(x) by the hardware estimate and the second-order binomial
- *         correction (push metric lapse and 1/Gamma), x > 0 normal.
+ *         correction (push metric lapse and 1/Gamma), x > 0 normal;
+ *   fn 6: 1/x in the deposit's paired-FP32 form, x > 0 in the normal float
+ *         range.
  * Errors: FPIC_EINVAL (fn out of range, n < 0, NULL with n > 0). */
 int fpic_probe_math(int fn, const double *x, double *y, long long n, void *stream);
 

@@ -140,6 +140,20 @@ __device__ __forceinline__ ff ff_sqrt(ff a)
     return ff_fast2(s, __fmul_rn(d, __fmul_rn(0.5f, y)));
 }
 
+// 1/a for a > 0 in the normal float range: the FP32 estimate y of 1/a_hi
+// (relative error about 2^-23), e = 1 - a y from the exact product error of
+// a_hi y (1 - a_hi y is exact: the two are within a factor 2 of 1), and
+// 1/a = y / (1 - e) = y (1 + e + e^2 + ...) to second order: relative error
+// about 2^-46 (the rounding of y (e + e^2)); fpic_probe_math measures it.
+__device__ __forceinline__ ff ff_rcp(ff a)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(a.hi));
+    const float p = __fmul_rn(a.hi, y);
+    const float e = __fsub_rn(__fsub_rn(__fsub_rn(1.f, p), __fmaf_rn(a.hi, y, -p)), __fmul_rn(a.lo, y));
+    return ff_fast2(y, __fmul_rn(y, __fmaf_rn(e, e, e)));
+}
+
 // sin h and cos h - 1 of a step h in paired FP32 (the deposit's th
 // lattice rotations).  Below 2^-7 by the Maclaurin series: h - h^3/6 and
 // -h^2/2 in paired arithmetic, the next terms (h^5/120; h^4/24 - h^6/720),
@@ -147,12 +161,11 @@ __device__ __forceinline__ ff ff_sqrt(ff a)
 // result: sin h to about 2^-46 relative, cos h - 1 to about 2^-40 of
 // itself (2^-55 absolute, which is what the rotations need); larger steps
 // (coarse grids) through the FP64 routine sincos_step.
-__device__ __forceinline__ void sincos_step_ff(double hd, ff& sh, ff& cm)
+__device__ __forceinline__ void sincos_step_ff(ff h, ff& sh, ff& cm)
 {
-    const ff h = ff_from(hd);
     if (fabsf(h.hi) >= 0.0078125f) {
         double s, c;
-        sincos_step(hd, s, c);
+        sincos_step(ff_to(h), s, c);
         sh = ff_from(s);
         cm = ff_from(c);
         return;
@@ -164,6 +177,11 @@ __device__ __forceinline__ void sincos_step_ff(double hd, ff& sh, ff& cm)
     sh = ff_add(h, ff_add(ff_neg(ff_mul(h3, sixth)), ff_of(h5)));
     const float c4 = __fmul_rn(__fmul_rn(t.hi, t.hi), __fsub_rn(1.f / 24.f, __fmul_rn(t.hi, 1.f / 720.f)));
     cm = ff_add(ff_scale(t, -0.5f), ff_of(c4));
+}
+
+__device__ __forceinline__ void sincos_step_ff(double hd, ff& sh, ff& cm)
+{
+    sincos_step_ff(ff_from(hd), sh, cm);
 }
 
 }  // namespace fpic

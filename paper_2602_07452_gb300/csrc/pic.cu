@@ -582,14 +582,13 @@ __device__ __forceinline__ void subvolumes(const BH& bh, double x0, double x1, d
 }
 
 // The same lattices in paired-FP32 arithmetic (ff.cuh): the lattice
-// coordinates, the sin/cos rotations of the th lattice, the radicand, its
-// square root and the trapezoid sums run on the FP32 pipe (about 48 bits;
-// the square root to about 2^-44, against 2^-39.6 for the FP64 form above),
-// which issues 64 times the FP64 rate; the step sizes and the final
-// products stay in FP64, and the conversions between the two are integer
-// operations on the bits.  The values are sqrt(...) itself (no factor 2).
+// coordinates and step sizes, the sin/cos rotations of the th lattice, the
+// radicand, its square root, the trapezoid sums and the subvolumes run on
+// the FP32 pipe (about 48 bits; the square root to about 2^-44, against
+// 2^-39.6 for the FP64 form above), which issues 64 times the FP64 rate.
+// The values are sqrt(...) itself (no factor 2).
 struct BHff {
-    ff twoM, a2;
+    ff twoM, a2, third;
 };
 
 __device__ __forceinline__ void rotate_ff(ff s, ff c, ff sh, ff cm, ff& so, ff& co)
@@ -598,12 +597,24 @@ __device__ __forceinline__ void rotate_ff(ff s, ff c, ff sh, ff cm, ff& so, ff& 
     co = ff_add(c, ff_add(ff_neg(ff_mul(s, sh)), ff_mul(c, cm)));
 }
 
-__device__ __forceinline__ void theta_lattice_ff(double hc, double hd, double s0, double c0, double st, double ct,
-                                                 double s1, double c1, ff sy[7], ff cy[7])
+// sin and cos of th = x + d from those of a node x (table doubles) and an
+// offset d under a cell (a double: the difference of two close doubles,
+// formed in FP64).
+__device__ __forceinline__ void sincos_from_node(double s0, double c0, double d, ff& s, ff& c)
 {
-    sy[0] = ff_from(s0); cy[0] = ff_from(c0);
-    sy[3] = ff_from(st); cy[3] = ff_from(ct);
-    sy[6] = ff_from(s1); cy[6] = ff_from(c1);
+    ff sh, cm;
+    sincos_step_ff(d, sh, cm);
+    rotate_ff(ff_from(s0), ff_from(c0), sh, cm, s, c);
+}
+
+// The 7 th values of the lattice of [y0, y1] split at t: y0 + l hc
+// (l = 0..3), t + l hd (l = 1..3); the end points' sin/cos come in.
+__device__ __forceinline__ void theta_lattice_ff(ff hc, ff hd, ff s0, ff c0, ff st, ff ct, ff s1, ff c1, ff sy[7],
+                                                 ff cy[7])
+{
+    sy[0] = s0; cy[0] = c0;
+    sy[3] = st; cy[3] = ct;
+    sy[6] = s1; cy[6] = c1;
 #pragma unroll 1
     for (int half = 0; half < 2; ++half) {
         const int b = 3 * half;
@@ -619,24 +630,22 @@ __device__ __forceinline__ void theta_lattice_ff(double hc, double hd, double s0
 
 // One sub-grid lattice in paired FP32, row by row (the row loop is not
 // unrolled: one copy of the code serves every row and, through
-// k_dep_particle_ff's loop, every sub-grid).  col_in / row_in: take the
-// split column / row from col / row instead of evaluating them; put_shared:
-// store this lattice's split column and row there.
-__device__ __forceinline__ void subvolumes_ff(const BHff& bh, double x0, double x1, double r, double hc, double hd,
-                                              const ff* sy, const ff* cy, double V[4], ff* col, ff row[7],
+// k_dep_particle_ff's loop, every sub-grid): r columns x0 + k ha (k = 0..3,
+// x0 + 3 ha = r), r + k hb (k = 1..3).  col_in / row_in: take the split
+// column / row from col / row instead of evaluating them; put_shared: store
+// this lattice's split column and row there.  V: the four subvolumes.
+__device__ __forceinline__ void subvolumes_ff(const BHff& bh, ff x0f, ff rf, ff ha, ff hb, ff hc, ff hd,
+                                              const ff* sy, const ff* cy, ff V[4], ff* col, ff row[7],
                                               bool col_in, bool row_in, bool put_shared)
 {
-    const double third = 1.0 / 3.0;
-    const double ha = (r - x0) * third, hb = (x1 - r) * third;
-    const ff x0f = ff_from(x0), rf = ff_from(r), haf = ff_from(ha), hbf = ff_from(hb);
     ff P[7], Q[7];
 #pragma unroll
     for (int k = 0; k < 7; ++k) {
         ff x;
         if (k == 0) x = x0f;
-        else if (k < 3) x = ff_add(x0f, k == 1 ? haf : ff_scale(haf, 2.f));
+        else if (k < 3) x = ff_add(x0f, k == 1 ? ha : ff_scale(ha, 2.f));
         else if (k == 3) x = rf;
-        else x = ff_add(rf, k == 4 ? hbf : (k == 5 ? ff_scale(hbf, 2.f) : ff_mulf(hbf, 3.f)));
+        else x = ff_add(rf, k == 4 ? hb : (k == 5 ? ff_scale(hb, 2.f) : ff_mulf(hb, 3.f)));
         const ff X = ff_sqr(x), B = ff_add(X, ff_mul(bh.twoM, x));
         P[k] = ff_mul(X, B);
         Q[k] = ff_add(X, B);
@@ -670,10 +679,10 @@ __device__ __forceinline__ void subvolumes_ff(const BHff& bh, double x0, double 
         if (l <= 3) { S00 = ff_add(S00, ff_mul(ws, ra)); S10 = ff_add(S10, ff_mul(ws, rb)); }
         if (l >= 3) { S01 = ff_add(S01, ff_mul(ws, ra)); S11 = ff_add(S11, ff_mul(ws, rb)); }
     }
-    V[0] = ff_to(S00) * (ha * hc);
-    V[1] = ff_to(S10) * (hb * hc);
-    V[2] = ff_to(S01) * (ha * hd);
-    V[3] = ff_to(S11) * (hb * hd);
+    V[0] = ff_mul(S00, ff_mul(ha, hc));
+    V[1] = ff_mul(S10, ff_mul(hb, hc));
+    V[2] = ff_mul(S01, ff_mul(ha, hd));
+    V[3] = ff_mul(S11, ff_mul(hb, hd));
 }
 
 struct DepK {
@@ -766,46 +775,86 @@ __global__ void __launch_bounds__(256) k_dep_particle(DepK k)
     k.code[p] = (uint32_t)(i1 - i0 + 1) | ((uint32_t)(j1 - j0 + 1) << 2);
 }
 
+// x clamped to [lo, hi] by integer compares of the order-preserving keys:
+// the value the FP64 compares give for non-NaN x (a -0 below lo = +0 comes
+// back as +0), without FP64-pipe instructions.
+__device__ __forceinline__ double clamp_key(double x, double lo, double hi)
+{
+    const long long kx = okey(x);
+    return kx < okey(lo) ? lo : (kx > okey(hi) ? hi : x);
+}
+
+__device__ __forceinline__ bool same_bits(double a, double b)
+{
+    return __double_as_longlong(a) == __double_as_longlong(b);
+}
+
+// The deposit's per-particle pass: the sin/cos of the lattices' split
+// points (angle addition from the node tables by the in-cell offset), the
+// three sub-grid lattices, their subvolumes, weights and the charge products
+// in paired FP32; FP64 keeps the particle's sin/cos th and FIDO velocity,
+// the node-coordinate differences (the step sizes) and the final sum of
+// each share's two floats.
 __global__ void __launch_bounds__(256) k_dep_particle_ff(DepK k)
 {
     const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= k.n_alive) return;
     const GridDev& G = k.G;
+    const BHff& bh = k.bhf;
     const double r = k.r[p], t = k.th[p];
-    // FIDO three-velocity v^i = gamma^ij u_j / Gamma at the particle
-    double s, c;
-    sincos(t, &s, &c);
-    Geo g;
-    geo_eval(k.bh, r, s, c, g);
-    const double ur = k.ur[p], ut = k.uth[p], up = k.uph[p];
-    const double Ur = fma(g.gurr, ur, g.gurp * up), Ut = g.gutt * ut, Up = fma(g.gurp, ur, g.gupp * up);
-    const double iG = rsqrt_nr(fma(ur, Ur, fma(ut, Ut, fma(up, Up, 1.0))));
-    const double Q = k.w[p] * k.qm[p];
-    const double vr = Ur * iG, vt = Ut * iG, vp = Up * iG;
     // clamped positions and cells on the integer and half node lists
-    const double rn_c = clampd(r, G.rn[0], G.rn[G.Nr]), rh_c = clampd(r, G.rh[0], G.rh[G.Nr - 1]);
-    const double tn_c = clampd(t, G.tn[0], G.tn[G.Nth]), th_c = clampd(t, G.th[0], G.th[G.Nth - 1]);
+    const double rn_c = clamp_key(r, G.rn[0], G.rn[G.Nr]), rh_c = clamp_key(r, G.rh[0], G.rh[G.Nr - 1]);
+    const double tn_c = clamp_key(t, G.tn[0], G.tn[G.Nth]), th_c = clamp_key(t, G.th[0], G.th[G.Nth - 1]);
     int i0, i1, j0, j1;
     double wd;
-    const float lr = __logf((float)r);
+    const float lr = __logf(f32_est(r)), tf = f32_est(t);
     locate(G.rn, G.irn, G.Nr + 1, rn_c, (lr - G.lr0) * G.ilr, i0, wd);
     locate(G.rh, G.irh, G.Nr, rh_c, (lr - G.lrh0) * G.ilr, i1, wd);
-    locate(G.tn, G.itn, G.Nth + 1, tn_c, ((float)t - G.t0) * G.it, j0, wd);
-    locate(G.th, G.ith, G.Nth, th_c, ((float)t - G.th0) * G.it, j1, wd);
-    // sin/cos at the clamped th (the particle's own unless clamped at an edge)
-    double stn = s, ctn = c, sth = s, cth = c;
-    if (tn_c != t) sincos(tn_c, &stn, &ctn);
-    if (th_c != t) sincos(th_c, &sth, &cth);
+    locate(G.tn, G.itn, G.Nth + 1, tn_c, (tf - G.t0) * G.it, j0, wd);
+    locate(G.th, G.ith, G.Nth, th_c, (tf - G.th0) * G.it, j1, wd);
     const double* sn = k.trig;
     const double* cn = k.trig + (G.Nth + 1);
     const double* sh = k.trig + 2 * (G.Nth + 1);
     const double* ch = sh + G.Nth;
-    const double third = 1.0 / 3.0;
+    // sin/cos th of the particle in FP64 by angle addition from a node of
+    // its cell: the lower node where cos >= 0, the upper one elsewhere, so
+    // that sin(x + d) = sin x + (sin x (cos d - 1) + cos x sin d) adds terms
+    // of one sign and sin th keeps its relative accuracy up to the poles
+    // (g^pp = 1 / (rho^2 sin^2 th) in the velocity needs it); the offset's
+    // sin / cos - 1 by the series (libm beyond a cell: a clamped th).
+    const int jn = j0 + (__double2hiint(cn[j0]) < 0 ? 1 : 0);
+    double s, c;
+    {
+        double sd, cm;
+        sincos_step(t - G.tn[jn], sd, cm);
+        s = fma(sn[jn], cm, fma(cn[jn], sd, sn[jn]));
+        c = fma(cn[jn], cm, fma(-sn[jn], sd, cn[jn]));
+    }
+    // ... and at the split points of the two th lattices in paired FP32 (the
+    // integer lattice's is the particle's own th unless clamped)
+    ff stn, ctn, sth, cth;
+    if (same_bits(tn_c, t)) {
+        stn = ff_from(s);
+        ctn = ff_from(c);
+    } else {
+        sincos_from_node(sn[jn], cn[jn], tn_c - G.tn[jn], stn, ctn);
+    }
+    sincos_from_node(sh[j1], ch[j1], th_c - G.th[j1], sth, cth);
+    // FIDO three-velocity v^i = gamma^ij u_j / Gamma, in FP64 (the 1/sin^2 th
+    // of g^pp and the cancellation between the two terms of U^r and U^ph
+    // want more than paired FP32's 46 bits)
+    Geo g;
+    geo_eval(k.bh, r, s, c, g);
+    const double ur = k.ur[p], ut = k.uth[p], up = k.uph[p];
+    const double Ur = fma(g.gurr, ur, g.gurp * up), Ut = g.gutt * ut, Up = fma(g.gurp, ur, g.gupp * up);
+    const double Qd = k.w[p] * k.qm[p];
+    const double QiG = Qd * rsqrt_nr(fma(ur, Ur, fma(ut, Ut, fma(up, Up, 1.0))));
+    const ff Q = ff_from(Qd), Qr = ff_from(QiG * Ur), Qt = ff_from(QiG * Ut), Qp = ff_from(QiG * Up);
     const long long n = k.n_alive;
     // the split column / row are shared between the sub-grids unless clamped
-    const bool share = (rn_c == rh_c) && (tn_c == th_c);
+    const bool share = same_bits(rn_c, rh_c) && same_bits(tn_c, th_c);
     ff sy[7], cy[7], col[7], row[7];
-    double hc = 0.0, hd = 0.0;
+    ff hc = ff_of(0.f), hd = ff_of(0.f);
     // sub-grid 0: (i, j), rho and j^ph; 1: (i+1/2, j), j^r (the th lattice of
     // 0); 2: (i, j+1/2), j^th.  One copy of the lattice code serves all three.
 #pragma unroll 1
@@ -817,25 +866,28 @@ __global__ void __launch_bounds__(256) k_dep_particle_ff(DepK k)
             const double* sY = hth ? sh : sn;
             const double* cY = hth ? ch : cn;
             const double tc = hth ? th_c : tn_c;
-            hc = (tc - Y[jj]) * third;
-            hd = (Y[jj + 1] - tc) * third;
-            theta_lattice_ff(hc, hd, sY[jj], cY[jj], hth ? sth : stn, hth ? cth : ctn, sY[jj + 1], cY[jj + 1], sy, cy);
+            hc = ff_mul(ff_from(tc - Y[jj]), bh.third);
+            hd = ff_mul(ff_from(Y[jj + 1] - tc), bh.third);
+            theta_lattice_ff(hc, hd, ff_from(sY[jj]), ff_from(cY[jj]), hth ? sth : stn, hth ? cth : ctn,
+                             ff_from(sY[jj + 1]), ff_from(cY[jj + 1]), sy, cy);
         }
         const bool hr = sg == 1;
         const double x0 = hr ? G.rh[i1] : G.rn[i0], x1 = hr ? G.rh[i1 + 1] : G.rn[i0 + 1];
-        double V[4];
-        subvolumes_ff(k.bhf, x0, x1, hr ? rh_c : rn_c, hc, hd, sy, cy, V, col, row, share && sg == 1, share && sg == 2,
-                      sg == 0);
-        const double iV = rcp_nr(V[0] + V[1] + V[2] + V[3]);
+        const double rc = hr ? rh_c : rn_c;
+        const ff ha = ff_mul(ff_from(rc - x0), bh.third), hb = ff_mul(ff_from(x1 - rc), bh.third);
+        ff V[4];
+        subvolumes_ff(bh, ff_from(x0), ff_from(rc), ha, hb, hc, hd, sy, cy, V, col, row, share && sg == 1,
+                      share && sg == 2, sg == 0);
+        const ff iV = ff_rcp(ff_add(ff_add(V[0], V[1]), ff_add(V[2], V[3])));
         // share of node (i+a, j+b) = V(opposite corner) / V
-        const double w00 = V[3] * iV, w10 = V[2] * iV, w01 = V[1] * iV, w11 = V[0] * iV;
+        const ff w00 = ff_mul(V[3], iV), w10 = ff_mul(V[2], iV), w01 = ff_mul(V[1], iV), w11 = ff_mul(V[0], iV);
         const int b = sg == 0 ? 0 : 4 + 4 * sg;
-        const double Qs = sg == 0 ? Q : (sg == 1 ? Q * vr : Q * vt);
-        k.rec[(b + 0) * n + p] = Qs * w00; k.rec[(b + 1) * n + p] = Qs * w10;
-        k.rec[(b + 2) * n + p] = Qs * w01; k.rec[(b + 3) * n + p] = Qs * w11;
+        const ff Qs = sg == 0 ? Q : (sg == 1 ? Qr : Qt);
+        k.rec[(b + 0) * n + p] = ff_to(ff_mul(Qs, w00)); k.rec[(b + 1) * n + p] = ff_to(ff_mul(Qs, w10));
+        k.rec[(b + 2) * n + p] = ff_to(ff_mul(Qs, w01)); k.rec[(b + 3) * n + p] = ff_to(ff_mul(Qs, w11));
         if (sg == 0) {
-            const double Qp = Q * vp;
-            k.rec[4 * n + p] = Qp * w00; k.rec[5 * n + p] = Qp * w10; k.rec[6 * n + p] = Qp * w01; k.rec[7 * n + p] = Qp * w11;
+            k.rec[4 * n + p] = ff_to(ff_mul(Qp, w00)); k.rec[5 * n + p] = ff_to(ff_mul(Qp, w10));
+            k.rec[6 * n + p] = ff_to(ff_mul(Qp, w01)); k.rec[7 * n + p] = ff_to(ff_mul(Qp, w11));
         }
     }
     k.code[p] = (uint32_t)(i1 - i0 + 1) | ((uint32_t)(j1 - j0 + 1) << 2);
@@ -1241,7 +1293,7 @@ static ff ff_host(double x)
 
 static BHff bh_ff(const BH& bh)
 {
-    return {ff_host(bh.twoM), ff_host(bh.a2)};
+    return {ff_host(bh.twoM), ff_host(bh.a2), ff_host(1.0 / 3.0)};
 }
 }  // namespace fpic
 

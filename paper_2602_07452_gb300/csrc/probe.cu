@@ -34,6 +34,8 @@ __global__ void k_math(int fn, const double* __restrict__ x, double* __restrict_
         y[i] = ff_to(ff_sqrt(ff_from(v)));
     } else if (fn == 5) {
         y[i] = rsqrt_nr(v);
+    } else if (fn == 6) {
+        y[i] = ff_to(ff_rcp(ff_from(v)));
     } else if (fn == 4) {
         ff sh, cm;
         sincos_step_ff(v, sh, cm);
@@ -52,7 +54,7 @@ __global__ void k_math(int fn, const double* __restrict__ x, double* __restrict_
 extern "C" int fpic_probe_math(int fn, const double* x, double* y, long long n, void* stream)
 {
     using namespace fpic;
-    if (fn < 0 || fn > 5 || n < 0 || (n > 0 && (!x || !y))) return set_error(FPIC_EINVAL, "fpic_probe_math: bad argument");
+    if (fn < 0 || fn > 6 || n < 0 || (n > 0 && (!x || !y))) return set_error(FPIC_EINVAL, "fpic_probe_math: bad argument");
     if (n == 0) return FPIC_OK;
     k_math<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(fn, x, y, n);
     FPIC_CUDA(cudaGetLastError());

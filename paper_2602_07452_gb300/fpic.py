@@ -488,8 +488,8 @@ def fpic_get_tuning(ctx: Ctx, key: int) -> int:
 def fpic_probe_math(fn: int, x: torch.Tensor) -> torch.Tensor:
     """The library's elementary routine `fn` (0 reciprocal, 1 square root,
     2 small-step sin / cos - 1, 3 paired-FP32 square root, 4 paired-FP32
-    small-step sin / cos - 1, 5 reciprocal square root) applied to the
-    device tensor x."""
+    small-step sin / cos - 1, 5 reciprocal square root, 6 paired-FP32
+    reciprocal) applied to the device tensor x."""
     x = x.contiguous()
     y = torch.empty((x.numel(), 2) if fn in (2, 4) else (x.numel(),), dtype=torch.float64, device=x.device)
     _check(lib().fpic_probe_math(fn, x.data_ptr(), y.data_ptr(), x.numel(), _stream(None)))

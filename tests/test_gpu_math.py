@@ -73,6 +73,22 @@ def test_paired_sqrt_error_bound(F):
     assert rel.max() <= 2.0 ** -43, rel.max()
 
 
+def test_paired_reciprocal_error_bound(F):
+    """The deposit's paired-FP32 1/x (FP32 estimate, the exact product
+    errors, a second-order series) over 30 decades (where the input's and
+    the result's low floats are normal: the deposit's subvolume sums):
+    relative error below 2^-44 against an extended-precision reference
+    (about 2^-46 expected)."""
+    x = _samples(1e-15, 1e15, 1 << 20, 6)
+    if np.finfo(np.longdouble).nmant < 60:
+        pytest.skip("no extended precision on this host")
+    ref = 1.0 / x.astype(np.longdouble)
+    got = F.fpic_probe_math(6, dev(x)).cpu().numpy().astype(np.longdouble)
+    rel = np.abs((got - ref) / ref).astype(np.float64)
+    print("paired rcp max rel err", rel.max(), "= 2^%.1f" % np.log2(rel.max() + 1e-300))
+    assert rel.max() <= 2.0 ** -44, rel.max()
+
+
 def test_paired_small_step_sin_cos(F):
     """The deposit's paired-FP32 sin h, cos h - 1 of a lattice step: the
     series branch (|h| < 2^-7) to 2^-45 of sin h and 2^-54 absolute on
