@@ -329,11 +329,12 @@ extern "C" int fpic_set_grid(fpic_ctx* c, int Nr, int Nth, const double* rn, con
     FPIC_CUDA(cudaSetDevice(c->device));
     // the half-th list carries one more node, th[Nth] = th[0] + (tn[Nth] - tn[0]):
     // the upper end of the full-theta wrap cell (unused in the half-theta domain)
-    const size_t tot = 2 * ((size_t)(Nr + 1) + Nr + (Nth + 1) + (Nth + 1));
+    const size_t tot = 3 * ((size_t)(Nr + 1) + Nr + (Nth + 1) + (Nth + 1));
     std::vector<double> h(tot);
     double* p = h.data();
     size_t o_rn = 0, o_rh = o_rn + Nr + 1, o_tn = o_rh + Nr, o_th = o_tn + Nth + 1;
     size_t o_irn = o_th + Nth + 1, o_irh = o_irn + Nr + 1, o_itn = o_irh + Nr, o_ith = o_itn + Nth + 1;
+    size_t o_brn = o_ith + Nth + 1, o_brh = o_brn + Nr + 1, o_btn = o_brh + Nr, o_bth = o_btn + Nth + 1;
     memcpy(p + o_rn, rn, (Nr + 1) * sizeof(double));
     memcpy(p + o_rh, rh, Nr * sizeof(double));
     memcpy(p + o_tn, tn, (Nth + 1) * sizeof(double));
@@ -347,6 +348,15 @@ extern "C" int fpic_set_grid(fpic_ctx* c, int Nr, int Nth, const double* rn, con
     inv(rh, Nr, p + o_irh);
     inv(tn, Nth + 1, p + o_itn);
     inv(p + o_th, Nth + 1, p + o_ith);
+    // -X[i] / (X[i+1] - X[i]): a gather's cell weight (x - X[i]) / (X[i+1] - X[i])
+    // as one fused multiply-add, x iX[i] + B[i]
+    auto off = [](const double* X, const double* iX, int m, double* out) {
+        for (int i = 0; i < m; ++i) out[i] = -(X[i] * iX[i]);
+    };
+    off(p + o_rn, p + o_irn, Nr + 1, p + o_brn);
+    off(p + o_rh, p + o_irh, Nr, p + o_brh);
+    off(p + o_tn, p + o_itn, Nth + 1, p + o_btn);
+    off(p + o_th, p + o_ith, Nth + 1, p + o_bth);
     retire(c, (void**)&c->d_nodes);
     FPIC_CUDA(cudaMalloc(&c->d_nodes, tot * sizeof(double)));
     FPIC_CUDA(cudaMemcpy(c->d_nodes, p, tot * sizeof(double), cudaMemcpyHostToDevice));
@@ -358,6 +368,7 @@ extern "C" int fpic_set_grid(fpic_ctx* c, int Nr, int Nth, const double* rn, con
     G.ld = Nth + 1;
     G.rn = d + o_rn; G.rh = d + o_rh; G.tn = d + o_tn; G.th = d + o_th;
     G.irn = d + o_irn; G.irh = d + o_irh; G.itn = d + o_itn; G.ith = d + o_ith;
+    G.brn = d + o_brn; G.brh = d + o_brh; G.btn = d + o_btn; G.bth = d + o_bth;
     // FP32 index estimates (corrected exactly against the tables on device)
     const double l0 = log(rn[0]), l1 = log(rn[Nr]);
     G.lr0 = (float)l0;
