@@ -119,7 +119,7 @@ __device__ __forceinline__ void sincos_near(double t0, double s0, double c0, dou
 
 // Metric at a point (r, th) given sin/cos th.
 struct Geo {
-    double s, c, s2, rho2, irho2, t;  // t = 1/(rho^2 sin^2 th)
+    double s, c, s2, c2, r2, rho2, irho2, t;  // t = 1/(rho^2 sin^2 th)
     double twoMr, a2s2;               // 2 M r, a^2 sin^2 th
     double xi, alpha, ixi, beta;
     double gurr, gurp, gutt, gupp;
@@ -135,7 +135,9 @@ __device__ __forceinline__ void geo_eval(const BH& bh, double r, double s, doubl
     g.s = s;
     g.c = c;
     g.s2 = s2;
-    g.rho2 = fma(bh.a2, c2, r * r);
+    g.c2 = c2;
+    g.r2 = r * r;
+    g.rho2 = fma(bh.a2, c2, g.r2);
     g.t = rcp_nr(g.rho2 * s2);
     g.irho2 = g.t * s2;
     g.twoMr = bh.twoM * r;
@@ -174,7 +176,7 @@ __device__ __forceinline__ void geo_deriv(const BH& bh, double r, const Geo& g, 
     const double mr2 = -2.0 * r;
     d.tt[0] = mr2 * u;
     d.tt[1] = d.q * u;
-    d.xi[0] = fma(mr2, r, g.rho2) * (bh.twoM * u);
+    d.xi[0] = fma(bh.a2, g.c2, -g.r2) * (bh.twoM * u);   // rho^2 - 2 r^2 = a^2 cos^2 - r^2
     d.xi[1] = g.twoMr * d.tt[1];
     d.pp[0] = mr2 * (g.t * g.irho2);
     d.pp[1] = (-2.0 * sc) * (g.t * g.t) * (g.rho2 - g.a2s2);
@@ -449,7 +451,6 @@ __device__ __forceinline__ void eval_rhs_sc_t(const BH& bh, const double y[6], d
     const double Up = fma(g.gurp, ur, g.gupp * up);
     const double G2 = fma(ur, Ur, fma(ut, Ut, fma(up, Up, 1.0)));
     const double iG = rsqrt_nr(G2);
-    const double G = G2 * iG;
     const double aiG = g.alpha * iG;
     f[0] = fma(aiG, Ur, -g.beta);
     f[1] = aiG * Ut;
@@ -464,11 +465,13 @@ __device__ __forceinline__ void eval_rhs_sc_t(const BH& bh, const double y[6], d
     //   In r: W d_r g^tt + u_ph^2 d_r g^pp = -2 r (W / rho^4 + u_ph^2 / (rho^4 s^2))
     //   = -2 r / rho^2 (W / rho^2 + u_ph^2 t), t = 1 / (rho^2 s^2), so that
     //   h (...) = (alpha / Gamma) m0 with m0 = (r / rho^2) (W / rho^2 + u_ph^2 t).
+    //   With alpha^2 = 1/xi the d_i xi factor is
+    //   kap = (1/xi) ((1/xi) u_r (1 - h u_r) + alpha Gamma / 2), alpha Gamma / 2 = -h Gamma^2.
     const double h = -0.5 * aiG;
     const double urur = ur * ur, upup = up * up;
     const double W = fma(urur, g.a2s2, fma(2.0 * bh.a * ur, up, ut * ut));
-    const double a3h = (-0.5 * g.alpha) * g.ixi;      // -alpha^3 / 2
-    const double kap = fma(g.ixi * g.ixi * ur, fma(-h, ur, 1.0), -G * a3h);
+    const double haG = -h * G2;                       // alpha Gamma / 2
+    const double kap = g.ixi * fma(g.ixi * ur, fma(-h, ur, 1.0), haG);
     const double m0 = (y[0] * g.irho2) * fma(W, g.irho2, upup * g.t);
     f[3] = fma(aiG, m0, d.xi[0] * kap);
     f[4] = fma(h, fma(W, d.tt[1], fma(upup, d.pp[1], urur * d.q * g.irho2)), d.xi[1] * kap);
@@ -502,10 +505,10 @@ __device__ __forceinline__ void eval_rhs_sc_t(const BH& bh, const double y[6], d
             J->cx[0] = cr; J->cx[1] = ct; J->cx[2] = cp;
         }
     }
-    H = fma(g.alpha, G, -g.beta * ur);
+    H = fma(-g.beta, ur, haG + haG);                  // alpha Gamma - beta^r u_r
     if (B0pot != 0.0 && qm != 0.0) {
         // A_0 = B0 a r (1 + cos^2 th) / rho^2   (Sec. 3.1.3)
-        H = fma(-qm * B0pot * bh.a * y[0], (1.0 + c * c) * g.irho2, H);
+        H = fma(-qm * B0pot * bh.a * y[0], (1.0 + g.c2) * g.irho2, H);
     }
 }
 
