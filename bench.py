@@ -52,10 +52,10 @@ FLOP_RK4_TRIAL_REUSED = 4 * FLOP_EVAL + 79 + 5
 FLOP_IMR_FINAL_REUSE = FLOP_EVAL
 NOMINAL_FP64_GFLOPS = 1250.0
 # DRAM bytes (read + write) of one k_explicit<1> launch on this workload,
-# from one ncu capture of the current kernel (412.2 MB + 190.8 MB); the
+# from one ncu capture of the current kernel (412.4 MB + 191.1 MB); the
 # algorithmic bytes are ~420 B per particle with the slope cache (440 MB
 # for 2^20).
-TRAFFIC_K_EXPLICIT = 603.1e6   # ncu dram__bytes_read.sum + dram__bytes_write.sum, one warm 2^20 launch (slope cache on)
+TRAFFIC_K_EXPLICIT = 603.4e6   # ncu dram__bytes_read.sum + dram__bytes_write.sum, one warm 2^20 launch (slope cache on)
 # deposit: FIDO velocity (41) + 133 distinct sqrt(gamma) lattice points x 9
 # (3 sub-grids x 49, less the split column and row they share) + 3 sub-grids x
 # (lattice 14 + four 16-point sums 128 + weights 16) + 2 th lattices (56) + shares (30),

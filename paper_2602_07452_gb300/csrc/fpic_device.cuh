@@ -194,6 +194,28 @@ __device__ __forceinline__ float f32_est(double x)
     return __int_as_float((hi & (int)0x80000000) | (e << 23) | ((hi & 0xfffff) << 3));
 }
 
+// For a, b >= 0 or NaN (update sizes, tolerances): a <= b and a < b as the
+// FP64 compares give them (false when either is a NaN), and fmax(m, a) for a
+// running maximum m >= 0 (a NaN a is ignored), by integer compares of the
+// bit patterns -- non-negative doubles order like their bits -- off the
+// FP64 pipe.
+constexpr long long F64_INF_BITS = 0x7ff0000000000000LL;
+__device__ __forceinline__ bool le_nonneg(double a, double b)
+{
+    const long long ba = __double_as_longlong(a), bb = __double_as_longlong(b);
+    return ba <= bb && bb <= F64_INF_BITS;
+}
+__device__ __forceinline__ bool lt_nonneg(double a, double b)
+{
+    const long long ba = __double_as_longlong(a), bb = __double_as_longlong(b);
+    return ba < bb && bb <= F64_INF_BITS;
+}
+__device__ __forceinline__ double fmax_nonneg(double m, double a)
+{
+    const long long bm = __double_as_longlong(m), ba = __double_as_longlong(a);
+    return (ba > F64_INF_BITS || ba <= bm) ? m : a;
+}
+
 // Order-preserving integer key of a double (monotone for all non-NaN values).
 __device__ __forceinline__ long long okey(double x)
 {
@@ -491,14 +513,15 @@ __device__ __forceinline__ void eval_rhs_sc_t(const BH& bh, const double y[6], d
         //   r:  k xi X,  X = D^r - a s^2 D^ph
         //   ph: k s^2 (rho^2 D^ph - a xi X)
         const double k = qm * g.alpha;
+        const double kxi = k * g.xi, kr = k * g.rho2;
         const double ks = (qm * g.rho2) * (g.s * iG);    // k sqrt(gamma) / Gamma, alpha^2 xi = 1
         const double cr = fma(Ut, B[2], -Up * B[1]);
         const double ct = fma(Up, B[0], -Ur * B[2]);
         const double cp = fma(Ur, B[1], -Ut * B[0]);
         const double X = fma(-bh.a * g.s2, D[2], D[0]);
-        f[3] = fma(k * g.xi, X, fma(ks, cr, f[3]));
-        f[4] = fma(k, g.rho2 * D[1], fma(ks, ct, f[4]));
-        f[5] = fma(k * g.s2, fma(-bh.a * g.xi, X, g.rho2 * D[2]), ks * cp);
+        f[3] = fma(kxi, X, fma(ks, cr, f[3]));
+        f[4] = fma(kr, D[1], fma(ks, ct, f[4]));
+        f[5] = fma(g.s2, fma(kr, D[2], -(bh.a * kxi) * X), ks * cp);
         if (JAC) {
             J->ks = ks;
             J->B[0] = B[0]; J->B[1] = B[1]; J->B[2] = B[2];

@@ -583,7 +583,7 @@ __device__ __forceinline__ bool conv6(const double a[6], const double b[6], doub
 {
     bool ok = true;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) ok = ok && (fabs(a[i] - b[i]) <= tol * (fabs(a[i]) + 1.0));
+    for (int i = 0; i < 6; ++i) ok = ok && le_nonneg(fabs(a[i] - b[i]), tol * (fabs(a[i]) + 1.0));
     return ok;
 }
 
@@ -743,22 +743,23 @@ __global__ void __launch_bounds__(128, NEWTON ? 3 : 4) k_imr(const __grid_consta
                 for (int i = 0; i < 6; ++i) di[i] = fabs(zn[i] - zk[i]);
                 bool ok = true;
 #pragma unroll
-                for (int i = 0; i < 6; ++i) ok = ok && (di[i] <= k.tol * (fabs(zn[i]) + 1.0));
+                for (int i = 0; i < 6; ++i) ok = ok && le_nonneg(di[i], k.tol * (fabs(zn[i]) + 1.0));
                 if (NEWTON && !ok && it >= 1) {
                     // a-posteriori stop: theta_i / (1 - theta_i) d_i <= tol (|z_i| + 1),
                     // theta_i = d_i / p_i, written without division
                     ok = true;
 #pragma unroll
                     for (int i = 0; i < 6; ++i)
-                        ok = ok && (di[i] < dprev[i]) && (di[i] * di[i] <= k.tol * (fabs(zn[i]) + 1.0) * (dprev[i] - di[i]));
+                        ok = ok && lt_nonneg(di[i], dprev[i]) &&
+                             le_nonneg(di[i] * di[i], k.tol * (fabs(zn[i]) + 1.0) * (dprev[i] - di[i]));
                 }
                 double dz = 0.0;
 #pragma unroll
                 for (int i = 0; i < 6; ++i) {
-                    dz = fmax(dz, di[i]);
+                    dz = fmax_nonneg(dz, di[i]);
                     dprev[i] = di[i];
                 }
-                if (dz < best_dz) {
+                if (lt_nonneg(dz, best_dz)) {
                     best_dz = dz;
                     best_it = it + 1;
                 }
@@ -860,13 +861,14 @@ __device__ bool imr_solve_serial(const PushK& k, const RunK& R, const double zs[
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
             di[i] = fabs(zn[i] - zk[i]);
-            ok = ok && (di[i] <= k.tol * (fabs(zn[i]) + 1.0));
+            ok = ok && le_nonneg(di[i], k.tol * (fabs(zn[i]) + 1.0));
         }
         if (NEWTON && !ok && it >= 1) {
             ok = true;
 #pragma unroll
             for (int i = 0; i < 6; ++i)
-                ok = ok && (di[i] < dprev[i]) && (di[i] * di[i] <= k.tol * (fabs(zn[i]) + 1.0) * (dprev[i] - di[i]));
+                ok = ok && lt_nonneg(di[i], dprev[i]) &&
+                     le_nonneg(di[i] * di[i], k.tol * (fabs(zn[i]) + 1.0) * (dprev[i] - di[i]));
         }
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
