@@ -431,7 +431,12 @@ int fpic_get_tuning(const fpic_ctx *ctx, int key, int *value);
  *   fn 5: 1/sqrt(x) by the hardware estimate and the second-order binomial
  *         correction (push metric lapse and 1/Gamma), x > 0 normal;
  *   fn 6: 1/x in the deposit's paired-FP32 form, x > 0 in the normal float
- *         range.
+ *         range;
+ *   fn 7: pairs (a, b) = (x[2i], x[2i+1]), i < n/2, of non-negative
+ *         doubles or NaNs: y[6i..6i+5] = the integer-compare forms of
+ *         a <= b, then the FP64 a <= b, of a < b, then FP64 a < b (1 or 0),
+ *         of fmax(a, b) with a running maximum a, then FP64 fmax (the push's
+ *         IMR stopping tests); n even.
  * Errors: FPIC_EINVAL (fn out of range, n < 0, NULL with n > 0). */
 int fpic_probe_math(int fn, const double *x, double *y, long long n, void *stream);
 

@@ -88,6 +88,16 @@ __device__ __forceinline__ ff ff_add(ff a, ff b)
     return {s, __fadd_rn(e, __fadd_rn(a.lo, b.lo))};
 }
 
+// a + b when a_hi >= b_hi >= 0 (more generally: a_hi's exponent at least
+// b_hi's): Dekker's fast two-sum of the high parts gives the same sum and
+// the same exact error as the two-sum in ff_add, so the same pair, with
+// three additions fewer.
+__device__ __forceinline__ ff ff_add_ge(ff a, ff b)
+{
+    const float s = __fadd_rn(a.hi, b.hi);
+    return {s, __fadd_rn(__fsub_rn(b.hi, __fsub_rn(s, a.hi)), __fadd_rn(a.lo, b.lo))};
+}
+
 __device__ __forceinline__ ff ff_neg(ff a)
 {
     return {-a.hi, -a.lo};

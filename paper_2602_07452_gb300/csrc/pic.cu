@@ -648,7 +648,7 @@ __device__ __forceinline__ void subvolumes_ff(const BHff& bh, ff x0f, ff rf, ff 
         else x = ff_add(rf, k == 4 ? hb : (k == 5 ? ff_scale(hb, 2.f) : ff_mulf(hb, 3.f)));
         const ff X = ff_sqr(x), B = ff_add(X, ff_mul(bh.twoM, x));
         P[k] = ff_mul(X, B);
-        Q[k] = ff_add(X, B);
+        Q[k] = ff_add_ge(B, X);                        // B = X + 2 M x >= X
     }
     ff S00 = ff_of(0.f), S10 = ff_of(0.f), S01 = ff_of(0.f), S11 = ff_of(0.f);
 #pragma unroll 1
@@ -672,9 +672,11 @@ __device__ __forceinline__ void subvolumes_ff(const BHff& bh, ff x0f, ff rf, ff 
             }
         }
         // trapezoid weights 1/2, 1, 1, 1/2 along r on each half; the row's
-        // th weight (1/2 at the ends and the split row) times sin th
-        const ff ra = ff_add(ff_scale(ff_add(f[0], f[3]), 0.5f), ff_add(f[1], f[2]));
-        const ff rb = ff_add(ff_scale(ff_add(f[3], f[6]), 0.5f), ff_add(f[4], f[5]));
+        // th weight (1/2 at the ends and the split row) times sin th.  Along
+        // a row sqrt(gamma) grows with r (both factors of the radicand do),
+        // so f[k] <= f[k'] for k < k': the pair sums take the fast two-sum
+        const ff ra = ff_add(ff_scale(ff_add_ge(f[3], f[0]), 0.5f), ff_add_ge(f[2], f[1]));
+        const ff rb = ff_add(ff_scale(ff_add_ge(f[6], f[3]), 0.5f), ff_add_ge(f[5], f[4]));
         const ff ws = ff_scale(sy[l], (l == 0 || l == 3 || l == 6) ? 0.5f : 1.f);
         if (l <= 3) { S00 = ff_add(S00, ff_mul(ws, ra)); S10 = ff_add(S10, ff_mul(ws, rb)); }
         if (l >= 3) { S01 = ff_add(S01, ff_mul(ws, ra)); S11 = ff_add(S11, ff_mul(ws, rb)); }

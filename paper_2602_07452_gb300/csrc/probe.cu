@@ -36,6 +36,18 @@ __global__ void k_math(int fn, const double* __restrict__ x, double* __restrict_
         y[i] = rsqrt_nr(v);
     } else if (fn == 6) {
         y[i] = ff_to(ff_rcp(ff_from(v)));
+    } else if (fn == 7) {
+        // pair (a, b) = (x[2i], x[2i + 1]) of element i < n / 2: the integer
+        // compares of non-negative doubles beside the FP64 ones
+        if (2 * i + 1 >= n) return;
+        const double a = x[2 * i], b = x[2 * i + 1];
+        double* o = y + 6 * i;
+        o[0] = le_nonneg(a, b) ? 1.0 : 0.0;
+        o[1] = (a <= b) ? 1.0 : 0.0;
+        o[2] = lt_nonneg(a, b) ? 1.0 : 0.0;
+        o[3] = (a < b) ? 1.0 : 0.0;
+        o[4] = fmax_nonneg(a, b);
+        o[5] = fmax(a, b);
     } else if (fn == 4) {
         ff sh, cm;
         sincos_step_ff(v, sh, cm);
@@ -54,7 +66,7 @@ __global__ void k_math(int fn, const double* __restrict__ x, double* __restrict_
 extern "C" int fpic_probe_math(int fn, const double* x, double* y, long long n, void* stream)
 {
     using namespace fpic;
-    if (fn < 0 || fn > 6 || n < 0 || (n > 0 && (!x || !y))) return set_error(FPIC_EINVAL, "fpic_probe_math: bad argument");
+    if (fn < 0 || fn > 7 || n < 0 || (n > 0 && (!x || !y))) return set_error(FPIC_EINVAL, "fpic_probe_math: bad argument");
     if (n == 0) return FPIC_OK;
     k_math<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(fn, x, y, n);
     FPIC_CUDA(cudaGetLastError());

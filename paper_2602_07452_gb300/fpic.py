@@ -489,9 +489,15 @@ def fpic_probe_math(fn: int, x: torch.Tensor) -> torch.Tensor:
     """The library's elementary routine `fn` (0 reciprocal, 1 square root,
     2 small-step sin / cos - 1, 3 paired-FP32 square root, 4 paired-FP32
     small-step sin / cos - 1, 5 reciprocal square root, 6 paired-FP32
-    reciprocal) applied to the device tensor x."""
+    reciprocal, 7 the integer compares of non-negative doubles beside the
+    FP64 ones on the pairs (x[2i], x[2i+1]): rows of six) applied to the
+    device tensor x."""
     x = x.contiguous()
-    y = torch.empty((x.numel(), 2) if fn in (2, 4) else (x.numel(),), dtype=torch.float64, device=x.device)
+    if fn == 7:
+        shape = (x.numel() // 2, 6)
+    else:
+        shape = (x.numel(), 2) if fn in (2, 4) else (x.numel(),)
+    y = torch.empty(shape, dtype=torch.float64, device=x.device)
     _check(lib().fpic_probe_math(fn, x.data_ptr(), y.data_ptr(), x.numel(), _stream(None)))
     return y
 

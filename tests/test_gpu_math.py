@@ -89,6 +89,29 @@ def test_paired_reciprocal_error_bound(F):
     assert rel.max() <= 2.0 ** -44, rel.max()
 
 
+def test_integer_compares_of_nonnegative_doubles(F):
+    """The IMR stopping tests' integer compares of bit patterns (le_nonneg,
+    lt_nonneg, fmax_nonneg) give exactly the FP64 results on non-negative
+    doubles, zeros, subnormals, infinity and NaN on either side (a NaN
+    compares false; the running maximum ignores a NaN), against the GPU's
+    own FP64 compares and numpy's."""
+    rng = np.random.default_rng(8)
+    special = np.array([0.0, 5e-324, 1e-310, 2.2250738585072014e-308, 1e-300, 1e-16, 1.0,
+                        1.0 + 2.0 ** -52, 1e300, np.inf, np.nan])
+    a = np.concatenate([np.repeat(special, special.size), np.abs(rng.normal(size=4096)) * 10.0 ** rng.integers(-20, 20, 4096)])
+    b = np.concatenate([np.tile(special, special.size), np.abs(rng.normal(size=4096)) * 10.0 ** rng.integers(-20, 20, 4096)])
+    b[-2048:] = a[-2048:] * (1.0 + (rng.integers(0, 3, 2048) - 1) * 2.0 ** -52)   # neighbours and ties
+    x = np.empty(2 * a.size); x[0::2] = a; x[1::2] = b
+    got = F.fpic_probe_math(7, dev(x)).cpu().numpy()
+    with np.errstate(invalid="ignore"):
+        le, lt, mx = (a <= b).astype(float), (a < b).astype(float), np.fmax(a, b)
+    assert np.array_equal(got[:, 0], got[:, 1]) and np.array_equal(got[:, 0], le)
+    assert np.array_equal(got[:, 2], got[:, 3]) and np.array_equal(got[:, 2], lt)
+    ok_a = ~np.isnan(a)     # the running maximum a is never a NaN
+    assert np.array_equal(got[ok_a, 4].view(np.int64), got[ok_a, 5].view(np.int64))
+    assert np.array_equal(got[ok_a, 4], mx[ok_a])
+
+
 def test_paired_small_step_sin_cos(F):
     """The deposit's paired-FP32 sin h, cos h - 1 of a lattice step: the
     series branch (|h| < 2^-7) to 2^-45 of sin h and 2^-54 absolute on
