@@ -131,18 +131,17 @@ __device__ __forceinline__ ff ff_scale(ff a, float two_k)
     return {__fmul_rn(a.hi, two_k), __fmul_rn(a.lo, two_k)};
 }
 
-// sqrt(a) for a > 0 in the normal float range.  The FP32 estimate y of
-// 1/sqrt(a_hi) (relative error up to about 2^-22) takes one FP32 Newton
-// step y (3 - a_hi y^2) / 2, which leaves mostly its own rounding (order
-// 2^-24); s = a_hi y is then corrected by one Newton step for the square
-// root, s + (a - s^2) y / 2, with a - s^2 formed exactly from the product
-// error of s^2 (a_hi - s^2 is exact: the two are within a factor 2).  The
-// result's relative error is of order the square of the estimate's, about
-// 2^-44 (fpic_probe_math measures it).
+// sqrt(a) for a > 0 in the normal float range.  With the FP32 estimate y
+// of 1/sqrt(a_hi) (relative error e up to 2 ulp, about 2^-22), s = a_hi y
+// is corrected by one Newton step for the square root, s + (a - s^2) y / 2,
+// with a - s^2 formed exactly from the product error of s^2 (a_hi - s^2 is
+// exact: the two are within a factor 2).  The step leaves 3 e^2 / 2 of the
+// estimate's error (at most about 2^-43.4) beside the roundings of the
+// correction (about 2^-46): ample for the deposit's lattices, whose
+// shares are held to 1e-10 (fpic_probe_math measures it).
 __device__ __forceinline__ ff ff_sqrt(ff a)
 {
-    float y = rsqrtf(a.hi);
-    y = __fmul_rn(__fmul_rn(0.5f, y), __fsub_rn(3.f, __fmul_rn(__fmul_rn(a.hi, y), y)));
+    const float y = rsqrtf(a.hi);
     const float s = __fmul_rn(a.hi, y);
     const float p = __fmul_rn(s, s);
     const float pe = __fmaf_rn(s, s, -p);
